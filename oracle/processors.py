@@ -1,0 +1,247 @@
+"""Differentiable processors and their analytic adjoints in float64 (oracle; test
+infrastructure only, see ``oracle/__init__``).
+
+Every processor maps a stereo input u[2, L] and one parameter row p to y[2, L]
+(Sec. 3: processors take and produce stereo signals, C = 2).  Signals are zero
+outside [0, L) and outputs are truncated to L.  Every ``*_bwd`` takes the output
+adjoint ybar = dLoss/dy and returns (ubar, pbar) = (dLoss/du, dLoss/dp).
+
+Readings of points the paper leaves open (each is stated where used):
+  * EQ (Eq. 4): the index range printed for n has N+2 points; this oracle uses an odd
+    N and n in [-H, H], H = (N-1)/2, with K = (N+1)/2 log-magnitudes mirrored so the
+    filter is real and even; the Hann window is 0.5(1 + cos(2 pi n/(N+1))), which is
+    zero at n = +-(N+1)/2, the printed bounds.  The convolution of Eq. 5 is centred
+    (zero phase).  The 8 band gains in dB map to the K log-magnitudes by linear
+    interpolation in log2 frequency between log-spaced band centres
+    f_b = 20 * 1000^((b+0.5)/8) Hz, constant beyond the end centres.
+  * Compressor (Eq. 8-12): the mid signal is u_l + u_r (a sum, as in the text); the
+    one-pole recursion of Eq. 8 runs exactly with g[-1] = 0 (Eq. 9 with an FIR as
+    long as the signal); G_u = ln(g + eps) with eps = 1e-7; T and W are in natural-log
+    energy units.
+"""
+import numpy as np
+import scipy.signal
+
+LN10 = np.log(10.0)
+COMP_EPS = 1e-7
+EQ_BANDS = 8
+
+
+def _f64(x):
+    return np.asarray(x, dtype=np.float64)
+
+
+# ---------------------------------------------------------------- gain / panning (Eq. 2)
+def gain_fwd(u, p):
+    """y_c = exp(p_c) u_c, p in R^2 (log scale, one per channel)."""
+    u, p = _f64(u), _f64(p)
+    return np.exp(p)[:, None] * u
+
+
+def gain_bwd(u, p, ybar):
+    u, p, ybar = _f64(u), _f64(p), _f64(ybar)
+    a = np.exp(p)
+    ubar = a[:, None] * ybar
+    pbar = a * np.sum(ybar * u, axis=1)
+    return ubar, pbar
+
+
+# ---------------------------------------------------------------- stereo imager (Eq. 3a/3b)
+def imager_fwd(u, p):
+    """mid = l + r, side = exp(p_s)(l - r), then l = (mid+side)/2, r = (mid-side)/2."""
+    u, p = _f64(u), _f64(p)
+    mid = u[0] + u[1]
+    side = np.exp(p[0]) * (u[0] - u[1])
+    return np.stack([(mid + side) / 2, (mid - side) / 2])
+
+
+def imager_bwd(u, p, ybar):
+    u, p, ybar = _f64(u), _f64(p), _f64(ybar)
+    a = np.exp(p[0])
+    midbar = (ybar[0] + ybar[1]) / 2
+    sidebar = (ybar[0] - ybar[1]) / 2
+    ubar = np.stack([midbar + a * sidebar, midbar - a * sidebar])
+    pbar = np.array([a * np.sum(sidebar * (u[0] - u[1]))])
+    return ubar, pbar
+
+
+# ---------------------------------------------------------------- zero-phase FIR EQ (Eq. 4-5)
+def eq_band_centres(n_bands=EQ_BANDS):
+    return 20.0 * 1000.0 ** ((np.arange(n_bands) + 0.5) / n_bands)
+
+
+def eq_band_matrix(N, fs=44100, n_bands=EQ_BANDS):
+    """B (K x n_bands): dB of bin k = sum_b B[k, b] band_dB[b]; bin k sits at k fs / N."""
+    K = (N + 1) // 2
+    c = eq_band_centres(n_bands)
+    lc = np.log2(c)
+    B = np.zeros((K, n_bands))
+    for k in range(K):
+        f = k * fs / N
+        if f <= c[0]:
+            B[k, 0] = 1.0
+        elif f >= c[-1]:
+            B[k, -1] = 1.0
+        else:
+            b = int(np.searchsorted(c, f, side="right")) - 1
+            w = (np.log2(f) - lc[b]) / (lc[b + 1] - lc[b])
+            B[k, b] = 1.0 - w
+            B[k, b + 1] = w
+    return B
+
+
+def eq_logmag(bands_db, N, fs=44100):
+    """p_e[k] (natural-log magnitude) from band gains in dB."""
+    return eq_band_matrix(N, fs, len(bands_db)) @ _f64(bands_db) * LN10 / 20.0
+
+
+def hann_sym(N):
+    """v[n] = 0.5 (1 + cos(2 pi n / (N+1))), n in [-H, H]."""
+    H = (N - 1) // 2
+    n = np.arange(-H, H + 1)
+    return 0.5 * (1.0 + np.cos(2 * np.pi * n / (N + 1)))
+
+
+def zerophase_taps(logmag, N):
+    """Eq. 4: h[n] = v[n] (1/N) sum_k exp(p[k]) w_N^{kn}, magnitudes mirrored
+    (A_{N-k} = A_k) so that h is real and even.  Returns h[-H..H] as length N."""
+    H = (N - 1) // 2
+    K = (N + 1) // 2
+    A = np.exp(_f64(logmag))
+    assert A.shape[0] == K
+    n = np.arange(-H, H + 1)
+    k = np.arange(1, K)
+    h0 = (A[0] + 2.0 * np.cos(2 * np.pi * np.outer(n, k) / N) @ A[1:]) / N
+    return hann_sym(N) * h0
+
+
+def zerophase_taps_bwd(logmag, N, hbar):
+    """Adjoint of ``zerophase_taps``: dLoss/dp[k] from dLoss/dh[n]."""
+    H = (N - 1) // 2
+    K = (N + 1) // 2
+    A = np.exp(_f64(logmag))
+    n = np.arange(-H, H + 1)
+    h0bar = hann_sym(N) * _f64(hbar)
+    coef = np.full(K, 2.0 / N)
+    coef[0] = 1.0 / N
+    Abar = coef * (np.cos(2 * np.pi * np.outer(np.arange(K), n) / N) @ h0bar)
+    return A * Abar
+
+
+def eq_taps_from_bands(bands_db, N, fs=44100):
+    return zerophase_taps(eq_logmag(bands_db, N, fs), N)
+
+
+def fir_centred(u, h):
+    """Eq. 5, centred: y[t] = sum_{m=-H}^{H} h[m] u[t-m], u = 0 outside [0, L)."""
+    H = (len(h) - 1) // 2
+    L = u.shape[-1]
+    return scipy.signal.fftconvolve(u, h[None, :], axes=-1)[..., H:H + L]
+
+
+def fir_centred_adjoint(ybar, h):
+    """ubar[t] = sum_m h[m] ybar[t+m] (transpose of ``fir_centred``)."""
+    return fir_centred(ybar, h[::-1])
+
+
+def fir_centred_taps_grad(u, ybar, H):
+    """dLoss/dh[m] = sum_x sum_t ybar_x[t] u_x[t-m], m in [-H, H]."""
+    L = u.shape[-1]
+    # correlation via a library FFT convolution: c[j] = sum_t ybar[t] u[t - (j - L + 1)]
+    c = scipy.signal.fftconvolve(ybar, u[:, ::-1], axes=-1).sum(axis=0)
+    return c[L - 1 - H: L + H]
+
+
+def eq_fwd(u, p, N, fs=44100):
+    h = eq_taps_from_bands(p, N, fs)
+    return fir_centred(_f64(u), h)
+
+
+def eq_bwd(u, p, ybar, N, fs=44100):
+    u, ybar = _f64(u), _f64(ybar)
+    logmag = eq_logmag(p, N, fs)
+    h = zerophase_taps(logmag, N)
+    ubar = fir_centred_adjoint(ybar, h)
+    hbar = fir_centred_taps_grad(u, ybar, (N - 1) // 2)
+    lbar = zerophase_taps_bwd(logmag, N, hbar)
+    pbar = eq_band_matrix(N, fs, len(p)).T @ lbar * LN10 / 20.0
+    return ubar, pbar
+
+
+# ---------------------------------------------------------------- compressor (Eq. 8-12)
+def envelope(x, alpha):
+    """Eq. 8 with one coefficient: g[n] = alpha g[n-1] + (1-alpha) x[n], g[-1] = 0.
+    Run as the exact one-pole IIR (a library linear filter)."""
+    return scipy.signal.lfilter([1.0 - alpha], [1.0, -alpha], x)
+
+
+def envelope_reverse(a, alpha):
+    """lambda[n] = a[n] + alpha lambda[n+1], lambda[L] = 0 (adjoint recursion)."""
+    return scipy.signal.lfilter([1.0], [1.0, -alpha], a[::-1])[::-1]
+
+
+def knee(Gu, T, W, R):
+    """Eq. 10-11: quadratic-knee static curve and its partials
+    (dGy/dGu, dGy/dT, dGy/dW, dGy/dR)."""
+    above = Gu >= T + W
+    mid = (Gu >= T - W) & ~above
+    Gy = Gu.copy()
+    dGu = np.ones_like(Gu)
+    dT = np.zeros_like(Gu)
+    dW = np.zeros_like(Gu)
+    dR = np.zeros_like(Gu)
+    # above: T + (Gu - T)/R
+    Gy[above] = T + (Gu[above] - T) / R
+    dGu[above] = 1.0 / R
+    dT[above] = 1.0 - 1.0 / R
+    dR[above] = -(Gu[above] - T) / R ** 2
+    # mid: Gu + (1/R - 1) (Gu - T + W)^2 / (4W)
+    d = Gu[mid] - T + W
+    c = 1.0 / R - 1.0
+    Gy[mid] = Gu[mid] + c * d * d / (4 * W)
+    dGu[mid] = 1.0 + c * d / (2 * W)
+    dT[mid] = -c * d / (2 * W)
+    dW[mid] = c * (d / (2 * W) - d * d / (4 * W * W))
+    dR[mid] = -d * d / (4 * W * R ** 2)
+    return Gy, dGu, dT, dW, dR
+
+
+def compressor_fwd(u, p, eps=COMP_EPS, return_env=False):
+    u = _f64(u)
+    alpha, T, W, R = (float(v) for v in _f64(p))
+    um = u[0] + u[1]
+    g = envelope(um * um, alpha)
+    Gu = np.log(g + eps)
+    Gy = knee(Gu, T, W, R)[0]
+    y = np.exp(Gy - Gu)[None, :] * u
+    return (y, g) if return_env else y
+
+
+def compressor_bwd(u, p, ybar, eps=COMP_EPS):
+    u, ybar = _f64(u), _f64(ybar)
+    alpha, T, W, R = (float(v) for v in _f64(p))
+    um = u[0] + u[1]
+    x = um * um
+    g = envelope(x, alpha)
+    Gu = np.log(g + eps)
+    Gy, dGu, dT, dW, dR = knee(Gu, T, W, R)
+    k = np.exp(Gy - Gu)
+    kbar = np.sum(ybar * u, axis=0)
+    Gybar = kbar * k
+    gbar = Gybar * (dGu - 1.0) / (g + eps)
+    lam = envelope_reverse(gbar, alpha)
+    xbar = (1.0 - alpha) * lam
+    ubar = k[None, :] * ybar + (2.0 * um * xbar)[None, :]
+    gprev = np.concatenate([[0.0], g[:-1]])
+    pbar = np.array([np.sum(lam * (gprev - x)), np.sum(Gybar * dT),
+                     np.sum(Gybar * dW), np.sum(Gybar * dR)])
+    return ubar, pbar
+
+
+# ---------------------------------------------------------------- mix / output
+def identity_fwd(u, p=None):
+    return _f64(u).copy()
+
+
+def identity_bwd(u, p, ybar):
+    return _f64(ybar).copy(), np.zeros(0)

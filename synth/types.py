@@ -1,0 +1,18 @@
+"""Processor type ids and per-type parameter widths (fixed data, no arithmetic).
+
+Type letters follow the paper (Sec. 2 Fig. 1 legend, Fig. 2b legend): i input,
+o output, m mix, g gain/panning, s stereo imager, e equalizer, c compressor,
+d multitap delay, r reverb.
+
+Parameter widths N_t (the columns of P[t], Sec. 2 "Graph representations"):
+  g: 2   ln-gain per channel (Eq. 2)
+  s: 1   ln side gain (Eq. 3)
+  e: 8   band gains in dB (8-band design of the zero-phase FIR, Eq. 4)
+  c: 4   [alpha, T, W, R]; T and W in natural-log energy units (Eq. 8-12)
+  d: 176 2 channels x 4 taps x [Re z, Im z, 20 ln-magnitudes] (Eq. 14-15)
+  r: 50  [mid, side] x [H0, H_delta] x 12 bands (ln-magnitude), then q_dry, q_wet
+"""
+I, O, M, G, S, E, C, D, R = range(9)
+TYPE_LETTERS = "iomgsecdr"
+TYPE_IDS = {ch: k for k, ch in enumerate(TYPE_LETTERS)}
+PARAM_COLS = {I: 0, O: 0, M: 0, G: 2, S: 1, E: 8, C: 4, D: 176, R: 50}
