@@ -1,0 +1,211 @@
+/*
+ * grafx.h - C ABI of the B300 (sm_103a) GRAFX graph renderer.
+ *
+ * The library renders audio-processing graphs (arxiv 2408.03204, "GRAFX"):
+ * directed acyclic graphs of stereo processors, forward and backward.  The calls
+ * follow the paper's problem statement and its Fig. 2a usage: build a graph
+ * (GRAFX(), add, add_serial_chain, connect), compute the render data
+ * (compute_render_data = Algorithm 1 lines 1-4: type schedule, node reordering,
+ * read/write index maps), bind parameters, render (Algorithm 1 lines 5-13) and
+ * backpropagate.
+ *
+ * Conventions
+ *  - Every call returns an int status: GRAFX_OK (0) or a GRAFX_E* code.  On error
+ *    grafx_last_error() returns a message for the calling thread.
+ *  - Handles (grafx_graph, grafx_plan) are opaque and owned by the library; they
+ *    are freed with the matching *_destroy call.
+ *  - Device memory is owned by the caller.  The library allocates no device memory
+ *    in any call of this header; the caller passes a workspace of
+ *    grafx_plan_info.ws_bytes bytes (256-byte aligned) and binds it once.
+ *  - Streams are passed as void* and must be a cudaStream_t (NULL = legacy default
+ *    stream).  Device work is asynchronous on that stream; a plan must be used on
+ *    one stream at a time.  Device-side failures (a bounded wait that expired, an
+ *    index out of range) set a status word in the workspace that
+ *    grafx_sync_status() reports.
+ *  - Signals are float32 stereo rows laid out [channel][pitch] with
+ *    pitch = grafx_pitch(L) = L rounded up to a multiple of 4.  Samples at and past
+ *    L inside a row are padding: ignored on input, written as 0 on output.
+ *  - Node type ids: see GRAFX_T_*.  Parameter widths per type (columns of P[t]):
+ *    gain 2, imager 1, eq 8, compressor 4 (see grafx_bind_params).
+ */
+#ifndef GRAFX_H
+#define GRAFX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+enum {
+  GRAFX_OK = 0,
+  GRAFX_EINVAL = 1,    /* bad argument or graph rule broken (Sec. 2 Definitions) */
+  GRAFX_ECYCLE = 2,    /* graph has a cycle (Sec. 2: feedback loops are not allowed) */
+  GRAFX_ESHAPE = 3,    /* size / length / parameter-table shape mismatch */
+  GRAFX_ETYPE = 4,     /* unknown or unsupported node type */
+  GRAFX_ENOMEM = 5,    /* host allocation failed */
+  GRAFX_ECUDA = 6,     /* a CUDA runtime call failed */
+  GRAFX_ETIMEOUT = 7,  /* a bounded device-side wait expired (reported by grafx_sync_status) */
+  GRAFX_ESTATE = 8     /* call out of order (e.g. render before bind_workspace) */
+};
+
+/* ---------------------------------------------------------------- node types
+ * Letters of the paper (Fig. 1 and Fig. 2b legends).  in/out are the graph inputs
+ * and outputs; mix is an identity node whose input is the sum of its in-edges. */
+enum {
+  GRAFX_T_IN = 0, GRAFX_T_OUT = 1, GRAFX_T_MIX = 2, GRAFX_T_GAIN = 3, GRAFX_T_IMAGER = 4,
+  GRAFX_T_EQ = 5, GRAFX_T_COMP = 6, GRAFX_T_DELAY = 7, GRAFX_T_REVERB = 8,
+  GRAFX_N_TYPES = 9
+};
+
+/* ---------------------------------------------------------------- schedules (Sec. 2 "Type scheduling") */
+enum {
+  GRAFX_SCHED_BEAM = 0,       /* beam search keeping beam_width partial schedules */
+  GRAFX_SCHED_GREEDY = 1,     /* type with the most computable nodes; ties -> smallest type id */
+  GRAFX_SCHED_OPTIMAL = 2,    /* exhaustive shortest schedule; tiny graphs only (<= 28 processing nodes) */
+  GRAFX_SCHED_ONE_BY_ONE = 3  /* one processing node per step (the paper's baseline) */
+};
+
+typedef struct grafx_graph grafx_graph;
+typedef struct grafx_plan grafx_plan;
+
+/* Message for the last failed call on this thread ("" if none).  Owned by the
+ * library; valid until the next call on this thread. */
+const char* grafx_last_error(void);
+
+/* L rounded up to a multiple of 4: the channel stride of every signal row. */
+int64_t grafx_pitch(int64_t L);
+
+/* ---------------------------------------------------------------- graph building
+ * Sec. 2 "Graph representations" and Fig. 2a: a mutable graph G = (V, E).  Node ids
+ * are assigned in insertion order from 0.  Edges are SISO "cables" (Eq. 1b): the
+ * input of a node is the sum of the outputs of its in-edges; repeated edges add
+ * the same signal again.  Rules are checked when a plan is created: inputs have no
+ * in-edges, every other node has at least one, outputs have no out-edges, there is
+ * at least one output, and there is no cycle. */
+int grafx_graph_create(grafx_graph** out);
+int grafx_graph_destroy(grafx_graph* g);
+/* Append a node of `type` (GRAFX_T_*); its id is written to *id_out. */
+int grafx_graph_add(grafx_graph* g, int32_t type, int32_t* id_out);
+/* Append n nodes of types[0..n) connected in series; first/last ids are returned. */
+int grafx_graph_add_serial_chain(grafx_graph* g, const int32_t* types, int32_t n,
+                                 int32_t* first_id, int32_t* last_id);
+/* Append the edge src -> dst (ids must exist). */
+int grafx_graph_connect(grafx_graph* g, int32_t src, int32_t dst);
+int grafx_graph_size(const grafx_graph* g, int32_t* n_nodes, int32_t* n_edges);
+
+/* ---------------------------------------------------------------- planning
+ * compute_render_data: Algorithm 1 lines 1-4 on the host.  Several graphs may be
+ * planned together; they are treated as one disconnected graph (graph-level
+ * parallelism, Sec. 2 "Batched processing"), each with its own signal length.
+ * Node ids of the union are the per-graph ids offset by the node counts of the
+ * graphs before it; the k-th input of the union reads source row k, the j-th
+ * output writes output row j, and the l-th node of type t in the union owns row l
+ * of that type's parameter table. */
+typedef struct {
+  int32_t schedule;       /* GRAFX_SCHED_*; default BEAM */
+  int32_t beam_width;     /* default 32 (the paper's Sec. 4 setting) */
+  int32_t eq_taps;        /* odd FIR length N of the zero-phase EQ (Eq. 4); default 1023 */
+  int32_t sample_rate;    /* Hz, for the EQ band centres; default 44100 */
+  int32_t n_threads;      /* host threads for planning; 0 = hardware concurrency */
+  int32_t eq_fft;         /* EQ block FFT size (1024..8192, > 2*eq_taps); 0 = autotune default */
+  int32_t comp_chunk;     /* compressor scan chunk (1024 or 2048 samples); 0 = default */
+  int32_t reserved[9];
+} grafx_plan_opts;
+
+void grafx_plan_opts_default(grafx_plan_opts* o);
+
+/* graphs[0..n_graphs) with lengths[g] samples each (1 <= L <= 2^24).  The graphs
+ * are copied; they may be destroyed after this call.  Errors: EINVAL, ECYCLE,
+ * ETYPE (delay/reverb not supported by this build), ESHAPE. */
+int grafx_plan_create(const grafx_graph* const* graphs, int32_t n_graphs, const int64_t* lengths,
+                      const grafx_plan_opts* opts, grafx_plan** out);
+int grafx_plan_destroy(grafx_plan* p);
+
+typedef struct {
+  int32_t n_graphs, n_nodes, n_edges;
+  int32_t n_steps;            /* N: the schedule is V_0..V_N */
+  int32_t n_inputs, n_outputs;
+  int32_t n_type_rows[GRAFX_N_TYPES];  /* |V_t| per type */
+  int64_t src_elems;          /* floats in the source buffer: sum_g K_g * 2 * pitch_g */
+  int64_t out_elems;          /* floats in the output buffer: sum_g |O_g| * 2 * pitch_g */
+  int64_t node_samples;       /* sum over processing (non-input) nodes of L */
+  size_t ws_bytes;            /* device workspace bytes (render + backprop + loss) */
+  int32_t eq_fft, comp_chunk; /* the tile sizes in use */
+} grafx_plan_info_t;
+
+int grafx_plan_info(const grafx_plan* p, grafx_plan_info_t* info);
+
+/* Copy the plan's host index maps out (for checking them bit for bit).  Any pointer
+ * may be NULL.  Sizes: type_string N+1, step_ptr N+2, sigma |V| (original id of the
+ * union -> new id), csr_ptr |V|+1, csr_src |E| (in-edges by (dst, src) in new ids:
+ * I^G / I^A), tcsr_ptr |V|+1, tcsr_dst |E| (consumers by (src, dst)), param_row |V|
+ * (row of P[t] owned by each new id: I^P). */
+int grafx_plan_export(const grafx_plan* p, int32_t* type_string, int32_t* step_ptr,
+                      int32_t* sigma, int32_t* csr_ptr, int32_t* csr_src,
+                      int32_t* tcsr_ptr, int32_t* tcsr_dst, int32_t* param_row);
+
+/* ---------------------------------------------------------------- device binding
+ * Bind a caller-owned device workspace of at least info.ws_bytes bytes (256-byte
+ * aligned) and upload the plan's tables into it.  Blocks until the upload is done.
+ * The workspace holds the intermediate tensor U (Algorithm 1) and the adjoints, so
+ * it must stay untouched between a render and the backprop that follows it. */
+int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* stream);
+
+/* Bind the parameter table P[type]: a device float32 array [rows][cols], row-major,
+ * rows = |V_type| in the union's original node order (Sec. 2: the l-th row belongs
+ * to the l-th node of that type), cols = the type's width.  The pointer is kept and
+ * read at every render/backprop, so values may change in place between calls.
+ * Physical units: gain [ln g_l, ln g_r] (Eq. 2); imager [p_s] (Eq. 3); eq 8 band
+ * gains in dB at 20*1000^((b+0.5)/8) Hz (Eq. 4, log-frequency interpolation);
+ * compressor [alpha, T, W, R] with T, W in natural-log energy (Eq. 8-12), W > 0. */
+int grafx_bind_params(grafx_plan* p, int32_t type, const float* dev, int64_t rows, int64_t cols);
+
+/* ---------------------------------------------------------------- render / backprop
+ * grafx_render: Algorithm 1 lines 5-13.  sources: device float32 holding, graph after
+ * graph, K_g rows of [2][pitch_g] (src_elems floats).  out: device float32 of
+ * out_elems floats, the rows of the output nodes (Y_N).  Input rows are read in
+ * place (U = S (+) 0 without a copy); output rows are written in place. */
+int grafx_render(grafx_plan* p, const float* sources, float* out, void* stream);
+
+/* Reverse-mode pass of the last render (same sources, workspace untouched).
+ * d_out: dLoss/dY, laid out like `out`.  d_params[t] (t < GRAFX_N_TYPES): device
+ * float32 [rows][cols] like P[t], overwritten with dLoss/dP[t]; NULL entries (and
+ * types without parameters) are skipped, but every bound type with a non-NULL
+ * entry is written completely.  d_sources: NULL or a buffer like `sources`,
+ * overwritten with dLoss/dS. */
+int grafx_backprop(grafx_plan* p, const float* sources, const float* d_out,
+                   float* const* d_params, float* d_sources, void* stream);
+
+/* ---------------------------------------------------------------- loss
+ * Multi-resolution STFT magnitude loss between the output rows and a target laid
+ * out like `out` (the paper fits a rendered mix to a target, Sec. 4 Example usage;
+ * the loss itself is not specified there).  Per row and resolution M in
+ * {512, 1024, 2048}, hop M/4, periodic Hann, frames at f*hop with no padding, per
+ * channel: ||(|Y|-|T|)||_F / ||T||_F + mean|ln(|Y|+1e-7) - ln(|T|+1e-7)| over bins
+ * 0..M/2; averaged over the 6 (resolution, channel) pairs and summed over rows.
+ * Every output length must be >= 2048.  loss: device float32 scalar (written). */
+int grafx_mrstft_forward(grafx_plan* p, const float* out, const float* target, float* loss,
+                         void* stream);
+/* dLoss/dout into d_out (laid out like out; overwritten).  Uses the statistics of the
+ * last grafx_mrstft_forward on the same plan, which must have been run on the same
+ * out and target. */
+int grafx_mrstft_backward(grafx_plan* p, const float* out, const float* target, float* d_out,
+                          void* stream);
+
+/* ---------------------------------------------------------------- status
+ * Synchronise `stream` and report device-side failures recorded since the last
+ * call (GRAFX_ETIMEOUT for an expired bounded wait, GRAFX_EINVAL for an index that
+ * a device bounds check rejected), then clear them. */
+int grafx_sync_status(grafx_plan* p, void* stream);
+
+/* Number of kernel launches issued by the most recent grafx_render / grafx_backprop /
+ * grafx_mrstft_* call on this plan (for launch accounting). */
+int grafx_last_launch_count(const grafx_plan* p, int32_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRAFX_H */

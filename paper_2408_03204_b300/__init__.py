@@ -1,0 +1,292 @@
+"""Python binding of libgrafx (include/grafx.h): argument marshalling only.
+
+Every step of the render, its backward pass and the loss runs in the library's
+CUDA kernels; this module turns torch tensors into raw pointers and streams, and
+wraps the calls in ``torch.autograd.Function``s.  It fails loudly if the compiled
+library is missing: there is no CPU fallback.
+
+    g = Graph(); i = g.add(T_IN); a, b = g.add_serial_chain([T_GAIN, T_EQ]); ...
+    plan = Plan([g], [L])                         # compute_render_data (Alg. 1, 1-4)
+    plan.bind_workspace()                         # torch.empty on the current device
+    out = render(plan, sources, {T_GAIN: pg, T_EQ: pe})   # differentiable
+    loss = mrstft_loss(plan, out, target)
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgrafx.so")
+
+T_IN, T_OUT, T_MIX, T_GAIN, T_IMAGER, T_EQ, T_COMP, T_DELAY, T_REVERB = range(9)
+N_TYPES = 9
+PARAM_COLS = {T_GAIN: 2, T_IMAGER: 1, T_EQ: 8, T_COMP: 4}
+SCHED = {"beam": 0, "greedy": 1, "optimal": 2, "one_by_one": 3}
+ERRORS = {1: "EINVAL", 2: "ECYCLE", 3: "ESHAPE", 4: "ETYPE", 5: "ENOMEM", 6: "ECUDA", 7: "ETIMEOUT",
+          8: "ESTATE"}
+
+
+class GrafxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int32), ("beam_width", ctypes.c_int32), ("eq_taps", ctypes.c_int32),
+                ("sample_rate", ctypes.c_int32), ("n_threads", ctypes.c_int32), ("eq_fft", ctypes.c_int32),
+                ("comp_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_graphs", ctypes.c_int32), ("n_nodes", ctypes.c_int32), ("n_edges", ctypes.c_int32),
+                ("n_steps", ctypes.c_int32), ("n_inputs", ctypes.c_int32), ("n_outputs", ctypes.c_int32),
+                ("n_type_rows", ctypes.c_int32 * N_TYPES), ("src_elems", ctypes.c_int64),
+                ("out_elems", ctypes.c_int64), ("node_samples", ctypes.c_int64), ("ws_bytes", ctypes.c_size_t),
+                ("eq_fft", ctypes.c_int32), ("comp_chunk", ctypes.c_int32)]
+
+
+_lib = None
+# name -> (restype, argtypes); mirrors include/grafx.h
+_P, _I32, _I64, _SZ, _F = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p
+_I32P = ctypes.POINTER(ctypes.c_int32)
+SIGNATURES = {
+    "grafx_last_error": (ctypes.c_char_p, []),
+    "grafx_pitch": (_I64, [_I64]),
+    "grafx_graph_create": (ctypes.c_int, [ctypes.POINTER(_P)]),
+    "grafx_graph_destroy": (ctypes.c_int, [_P]),
+    "grafx_graph_add": (ctypes.c_int, [_P, _I32, _I32P]),
+    "grafx_graph_add_serial_chain": (ctypes.c_int, [_P, _I32P, _I32, _I32P, _I32P]),
+    "grafx_graph_connect": (ctypes.c_int, [_P, _I32, _I32]),
+    "grafx_graph_size": (ctypes.c_int, [_P, _I32P, _I32P]),
+    "grafx_plan_opts_default": (None, [ctypes.POINTER(PlanOpts)]),
+    "grafx_plan_create": (ctypes.c_int, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_I64),
+                                         ctypes.POINTER(PlanOpts), ctypes.POINTER(_P)]),
+    "grafx_plan_destroy": (ctypes.c_int, [_P]),
+    "grafx_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(PlanInfo)]),
+    "grafx_plan_export": (ctypes.c_int, [_P] + [_I32P] * 8),
+    "grafx_plan_bind_workspace": (ctypes.c_int, [_P, _P, _SZ, _P]),
+    "grafx_bind_params": (ctypes.c_int, [_P, _I32, _F, _I64, _I64]),
+    "grafx_render": (ctypes.c_int, [_P, _F, _F, _P]),
+    "grafx_backprop": (ctypes.c_int, [_P, _F, _F, ctypes.POINTER(_P), _F, _P]),
+    "grafx_mrstft_forward": (ctypes.c_int, [_P, _F, _F, _F, _P]),
+    "grafx_mrstft_backward": (ctypes.c_int, [_P, _F, _F, _F, _P]),
+    "grafx_sync_status": (ctypes.c_int, [_P, _P]),
+    "grafx_last_launch_count": (ctypes.c_int, [_P, _I32P]),
+}
+
+
+def lib():
+    """Load libgrafx.so (build it first with ``python -m paper_2408_03204_b300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgrafx.so is not built ({LIB_PATH}); run python -m paper_2408_03204_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise GrafxError(rc, lib().grafx_last_error().decode())
+
+
+def pitch(L):
+    return int(lib().grafx_pitch(int(L)))
+
+
+class Graph:
+    """Mutable graph (Sec. 2 "Graph representations"; Fig. 2a builder calls)."""
+
+    def __init__(self):
+        h = _P()
+        _check(lib().grafx_graph_create(ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.grafx_graph_destroy(self._h)
+            self._h = None
+
+    def add(self, t):
+        i = ctypes.c_int32()
+        _check(lib().grafx_graph_add(self._h, int(t), ctypes.byref(i)))
+        return i.value
+
+    def add_serial_chain(self, types):
+        arr = (ctypes.c_int32 * len(types))(*[int(t) for t in types])
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().grafx_graph_add_serial_chain(self._h, arr, len(types), ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def connect(self, src, dst):
+        _check(lib().grafx_graph_connect(self._h, int(src), int(dst)))
+
+    @classmethod
+    def from_lists(cls, types, edges):
+        g = cls()
+        for t in types:
+            g.add(t)
+        for s, d in edges:
+            g.connect(s, d)
+        return g
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(torch, device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Plan:
+    """Render data of one graph or a batch of graphs (Algorithm 1 lines 1-4)."""
+
+    def __init__(self, graphs, lengths, schedule="beam", beam_width=32, eq_taps=1023, sample_rate=44100,
+                 n_threads=0, eq_fft=0, comp_chunk=0):
+        o = PlanOpts()
+        lib().grafx_plan_opts_default(ctypes.byref(o))
+        o.schedule, o.beam_width, o.eq_taps = SCHED[schedule], beam_width, eq_taps
+        o.sample_rate, o.n_threads, o.eq_fft, o.comp_chunk = sample_rate, n_threads, eq_fft, comp_chunk
+        hs = (_P * len(graphs))(*[g._h for g in graphs])
+        ls = (ctypes.c_int64 * len(lengths))(*[int(x) for x in lengths])
+        h = _P()
+        _check(lib().grafx_plan_create(hs, len(graphs), ls, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.lengths = [int(x) for x in lengths]
+        inf = PlanInfo()
+        _check(lib().grafx_plan_info(self._h, ctypes.byref(inf)))
+        self.info = inf
+        self.ws = None
+        self.params = {}
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.grafx_plan_destroy(self._h)
+            self._h = None
+
+    # ---- host-side render data
+    def export(self):
+        import numpy as np
+        inf = self.info
+        n, e, N = inf.n_nodes, inf.n_edges, inf.n_steps
+        arrs = dict(type_string=np.zeros(N + 1, np.int32), step_ptr=np.zeros(N + 2, np.int32),
+                    sigma=np.zeros(n, np.int32), csr_ptr=np.zeros(n + 1, np.int32),
+                    csr_src=np.zeros(max(e, 1), np.int32), tcsr_ptr=np.zeros(n + 1, np.int32),
+                    tcsr_dst=np.zeros(max(e, 1), np.int32), param_row=np.zeros(n, np.int32))
+        ptrs = [a.ctypes.data_as(_I32P) for a in arrs.values()]
+        _check(lib().grafx_plan_export(self._h, *ptrs))
+        arrs["csr_src"] = arrs["csr_src"][:e]
+        arrs["tcsr_dst"] = arrs["tcsr_dst"][:e]
+        return {k: v.tolist() for k, v in arrs.items()}
+
+    # ---- device binding (torch supplies memory and streams only)
+    def bind_workspace(self, device="cuda"):
+        import torch
+        nbytes = int(self.info.ws_bytes)
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        off = (-ws.data_ptr()) % 256
+        self.ws = ws
+        self._ws_ptr = ws.data_ptr() + off
+        _check(lib().grafx_plan_bind_workspace(self._h, ctypes.c_void_p(self._ws_ptr), nbytes,
+                                               _stream(torch, ws.device)))
+        return self
+
+    def bind_params(self, params):
+        for t, p in params.items():
+            assert p.dtype.is_floating_point and p.is_contiguous()
+            _check(lib().grafx_bind_params(self._h, int(t), _ptr(p), p.shape[0], p.shape[1]))
+            self.params[int(t)] = p
+
+    def render_raw(self, sources, out, stream):
+        _check(lib().grafx_render(self._h, _ptr(sources), _ptr(out), stream))
+
+    def backprop_raw(self, sources, d_out, d_params, d_sources, stream):
+        arr = (_P * N_TYPES)(*[_ptr(d_params.get(t)) for t in range(N_TYPES)])
+        _check(lib().grafx_backprop(self._h, _ptr(sources), _ptr(d_out), arr, _ptr(d_sources), stream))
+
+    def loss_raw(self, out, target, loss, stream):
+        _check(lib().grafx_mrstft_forward(self._h, _ptr(out), _ptr(target), _ptr(loss), stream))
+
+    def loss_backward_raw(self, out, target, d_out, stream):
+        _check(lib().grafx_mrstft_backward(self._h, _ptr(out), _ptr(target), _ptr(d_out), stream))
+
+    def sync_status(self, stream=None):
+        import torch
+        s = stream if stream is not None else _stream(torch, self.ws.device)
+        _check(lib().grafx_sync_status(self._h, s))
+
+    def last_launches(self):
+        n = ctypes.c_int32()
+        _check(lib().grafx_last_launch_count(self._h, ctypes.byref(n)))
+        return n.value
+
+
+def _autograd():
+    import torch
+
+    class _Render(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, plan, types, sources, *ps):
+            plan.bind_params(dict(zip(types, ps)))
+            out = torch.empty(plan.info.out_elems, dtype=torch.float32, device=sources.device)
+            plan.render_raw(sources, out, _stream(torch, sources.device))
+            ctx.plan, ctx.types = plan, types
+            ctx.save_for_backward(sources, *ps)
+            return out
+
+        @staticmethod
+        def backward(ctx, d_out):
+            plan, types = ctx.plan, ctx.types
+            sources, *ps = ctx.saved_tensors
+            d_out = d_out.contiguous()
+            dps = {t: torch.empty_like(p) for t, p in zip(types, ps)}
+            d_src = torch.empty_like(sources) if ctx.needs_input_grad[2] else None
+            plan.backprop_raw(sources, d_out, dps, d_src, _stream(torch, sources.device))
+            return (None, None, d_src) + tuple(dps[t] for t in types)
+
+    class _Loss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, plan, out, target):
+            loss = torch.empty(1, dtype=torch.float32, device=out.device)
+            plan.loss_raw(out, target, loss, _stream(torch, out.device))
+            ctx.plan = plan
+            ctx.save_for_backward(out, target)
+            return loss[0]
+
+        @staticmethod
+        def backward(ctx, g):
+            out, target = ctx.saved_tensors
+            d_out = torch.empty_like(out)
+            ctx.plan.loss_backward_raw(out, target, d_out, _stream(torch, out.device))
+            return None, d_out * g, None
+
+    return _Render, _Loss
+
+
+_FN = None
+
+
+def _fns():
+    global _FN
+    if _FN is None:
+        _FN = _autograd()
+    return _FN
+
+
+def render(plan, sources, params):
+    """Differentiable render: ``sources`` flat float32 (src_elems), ``params`` {type: [rows, cols]}.
+    Returns the flat output buffer (out_elems floats)."""
+    types = tuple(sorted(params))
+    return _fns()[0].apply(plan, types, sources, *[params[t] for t in types])
+
+
+def mrstft_loss(plan, out, target):
+    """Differentiable multi-resolution STFT loss over the plan's output rows."""
+    return _fns()[1].apply(plan, out, target)

@@ -1,0 +1,402 @@
+// C ABI (include/grafx.h): graph building, planning, device binding, and the step
+// loops of Algorithm 1 (render) and its reverse (backprop), plus the loss.
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.h"
+#include "plan.h"
+
+using namespace grafx;
+
+namespace {
+
+#define GX_TRY try {
+#define GX_CATCH                                                              \
+  }                                                                           \
+  catch (const std::bad_alloc&) { return fail(GRAFX_ENOMEM, "host allocation failed"); } \
+  catch (...) { return fail(GRAFX_EINVAL, "unexpected exception"); }
+
+int cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return GRAFX_OK;
+  return fail(GRAFX_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+T* at(const Plan* p, size_t off) { return reinterpret_cast<T*>(p->dev_ws + off); }
+
+DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out, float* d_src) {
+  DevCtx c;
+  std::memset(&c, 0, sizeof(c));
+  c.nodes = at<const NodeDev>(p, p->ws.nodes);
+  c.ext = at<const int4_>(p, p->ws.node_ext);
+  c.csr_ptr = at<const int32_t>(p, p->ws.csr_ptr);
+  c.csr_src = at<const int32_t>(p, p->ws.csr_src);
+  c.tcsr_ptr = at<const int32_t>(p, p->ws.tcsr_ptr);
+  c.tcsr_dst = at<const int32_t>(p, p->ws.tcsr_dst);
+  c.items = at<const int4_>(p, p->ws.items);
+  c.tw = at<const float2_>(p, p->ws.twiddle);
+  c.eq_cos = at<const float>(p, p->ws.eq_cos);
+  c.eq_hann = at<const float>(p, p->ws.eq_hann);
+  c.eq_band = at<const float>(p, p->ws.eq_band);
+  c.status = at<uint32_t>(p, p->ws.status);
+  c.tickets = at<int32_t>(p, p->ws.tickets);
+  c.flags = at<unsigned long long>(p, p->ws.flags);
+  c.eq_spec = at<float>(p, p->ws.eq_spec);
+  c.comp_carry = at<float>(p, p->ws.comp_carry);
+  c.partial = at<float4>(p, p->ws.partial);
+  c.eq_partial = at<float2>(p, p->ws.eq_partial);
+  c.ybase[KIND_INPUT] = const_cast<float*>(src);
+  c.ybase[KIND_OUTPUT] = out;
+  c.ybase[KIND_INTERNAL] = at<float>(p, p->ws.U);
+  c.abase[KIND_INPUT] = d_src;
+  c.abase[KIND_OUTPUT] = const_cast<float*>(d_out);
+  c.abase[KIND_INTERNAL] = at<float>(p, p->ws.A);
+  c.eq_taps = p->eq_taps;
+  c.eq_H = p->eq_H;
+  c.eq_Hal = (p->eq_H + 3) & ~3;
+  c.eq_fft = p->eq_fft;
+  c.eq_step = p->eq_step;
+  c.comp_chunk = p->comp_chunk;
+  c.sample_rate = float(p->opts.sample_rate);
+  return c;
+}
+
+int check_ready(const Plan* p) {
+  if (!p->dev_ws) return fail(GRAFX_ESTATE, "workspace not bound (grafx_plan_bind_workspace)");
+  for (int t : {GRAFX_T_GAIN, GRAFX_T_IMAGER, GRAFX_T_EQ, GRAFX_T_COMP})
+    if (p->n_type_rows[t] > 0 && !p->params[t])
+      return fail(GRAFX_ESTATE, "parameters of type " + std::to_string(t) + " not bound");
+  return GRAFX_OK;
+}
+
+int param_cols(int t) {
+  switch (t) {
+    case GRAFX_T_GAIN: return 2;
+    case GRAFX_T_IMAGER: return 1;
+    case GRAFX_T_EQ: return 8;
+    case GRAFX_T_COMP: return 4;
+    default: return 0;
+  }
+}
+
+void clear_flags(const Plan* p, cudaStream_t s) {
+  cudaMemsetAsync(p->dev_ws + p->ws.tickets, 0, p->ws.eq_spec - p->ws.tickets, s);
+}
+
+LossLaunch make_loss(const Plan* p, const float* y, const float* tgt) {
+  LossLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.rows = at<const LossRow>(p, p->ws.loss_rows);
+  const int2_* items = at<const int2_>(p, p->ws.loss_items);
+  size_t off = 0;
+  for (int q = 0; q < N_RES; ++q) {
+    L.items[q] = items + off;
+    L.n_items[q] = int(p->loss.items[q].size());
+    off += p->loss.items[q].size();
+  }
+  L.y = y;
+  L.tgt = tgt;
+  L.part = at<float4>(p, p->ws.loss_part);
+  L.stats = at<float4>(p, p->ws.loss_stats);
+  L.frames = at<float>(p, p->ws.loss_frames);
+  L.tw = at<const float2_>(p, p->ws.twiddle);
+  L.n_rows = int(p->loss.rows.size());
+  for (auto& r : p->loss.rows) L.max_pitch = std::max(L.max_pitch, r.pitch);
+  return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* grafx_last_error(void) { return last_error_cstr(); }
+
+int64_t grafx_pitch(int64_t L) { return pitch_of(L); }
+
+int grafx_graph_create(grafx_graph** out) {
+  GX_TRY
+  if (!out) return fail(GRAFX_EINVAL, "null output pointer");
+  *out = new grafx_graph();
+  return GRAFX_OK;
+  GX_CATCH
+}
+
+int grafx_graph_destroy(grafx_graph* g) {
+  delete g;
+  return GRAFX_OK;
+}
+
+int grafx_graph_add(grafx_graph* g, int32_t type, int32_t* id_out) {
+  GX_TRY
+  if (!g) return fail(GRAFX_EINVAL, "null graph");
+  if (type < 0 || type >= GRAFX_N_TYPES) return fail(GRAFX_ETYPE, "unknown node type");
+  g->types.push_back(type);
+  if (id_out) *id_out = int32_t(g->types.size()) - 1;
+  return GRAFX_OK;
+  GX_CATCH
+}
+
+int grafx_graph_add_serial_chain(grafx_graph* g, const int32_t* types, int32_t n, int32_t* first_id,
+                                 int32_t* last_id) {
+  GX_TRY
+  if (!g || !types || n < 1) return fail(GRAFX_EINVAL, "bad chain");
+  for (int32_t i = 0; i < n; ++i)
+    if (types[i] < 0 || types[i] >= GRAFX_N_TYPES) return fail(GRAFX_ETYPE, "unknown node type");
+  int32_t first = int32_t(g->types.size());
+  for (int32_t i = 0; i < n; ++i) {
+    g->types.push_back(types[i]);
+    if (i) g->edges.push_back({first + i - 1, first + i});
+  }
+  if (first_id) *first_id = first;
+  if (last_id) *last_id = first + n - 1;
+  return GRAFX_OK;
+  GX_CATCH
+}
+
+int grafx_graph_connect(grafx_graph* g, int32_t src, int32_t dst) {
+  GX_TRY
+  if (!g) return fail(GRAFX_EINVAL, "null graph");
+  const int32_t n = int32_t(g->types.size());
+  if (src < 0 || src >= n || dst < 0 || dst >= n) return fail(GRAFX_EINVAL, "node id out of range");
+  g->edges.push_back({src, dst});
+  return GRAFX_OK;
+  GX_CATCH
+}
+
+int grafx_graph_size(const grafx_graph* g, int32_t* n_nodes, int32_t* n_edges) {
+  if (!g) return fail(GRAFX_EINVAL, "null graph");
+  if (n_nodes) *n_nodes = int32_t(g->types.size());
+  if (n_edges) *n_edges = int32_t(g->edges.size());
+  return GRAFX_OK;
+}
+
+void grafx_plan_opts_default(grafx_plan_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->schedule = GRAFX_SCHED_BEAM;
+  o->beam_width = 32;
+  o->eq_taps = 1023;
+  o->sample_rate = 44100;
+}
+
+int grafx_plan_create(const grafx_graph* const* graphs, int32_t n_graphs, const int64_t* lengths,
+                      const grafx_plan_opts* opts, grafx_plan** out) {
+  GX_TRY
+  if (!graphs || !lengths || !out || n_graphs < 1) return fail(GRAFX_EINVAL, "bad arguments");
+  grafx_plan_opts o;
+  if (opts) o = *opts;
+  else grafx_plan_opts_default(&o);
+  std::vector<const grafx_graph*> gs(graphs, graphs + n_graphs);
+  grafx_plan* p = new grafx_plan();
+  int rc = build_plan(gs, lengths, o, p);
+  if (rc) {
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return GRAFX_OK;
+  GX_CATCH
+}
+
+int grafx_plan_destroy(grafx_plan* p) {
+  delete p;
+  return GRAFX_OK;
+}
+
+int grafx_plan_info(const grafx_plan* p, grafx_plan_info_t* info) {
+  if (!p || !info) return fail(GRAFX_EINVAL, "null argument");
+  std::memset(info, 0, sizeof(*info));
+  info->n_graphs = p->n_graphs;
+  info->n_nodes = int32_t(p->types.size());
+  info->n_edges = int32_t(p->edges.size());
+  info->n_steps = int32_t(p->sched.string.size()) - 1;
+  info->n_inputs = p->step_ptr[1];
+  info->n_outputs = int32_t(p->outputs_new.size());
+  std::memcpy(info->n_type_rows, p->n_type_rows, sizeof(info->n_type_rows));
+  info->src_elems = p->src_elems;
+  info->out_elems = p->out_elems;
+  info->node_samples = p->node_samples;
+  info->ws_bytes = p->ws.total;
+  info->eq_fft = p->eq_fft;
+  info->comp_chunk = p->comp_chunk;
+  return GRAFX_OK;
+}
+
+int grafx_plan_export(const grafx_plan* p, int32_t* type_string, int32_t* step_ptr, int32_t* sigma,
+                      int32_t* csr_ptr, int32_t* csr_src, int32_t* tcsr_ptr, int32_t* tcsr_dst,
+                      int32_t* param_row) {
+  if (!p) return fail(GRAFX_EINVAL, "null plan");
+  auto cp = [](int32_t* dst, const std::vector<int32_t>& v) {
+    if (dst && !v.empty()) std::memcpy(dst, v.data(), v.size() * sizeof(int32_t));
+  };
+  cp(type_string, p->sched.string);
+  cp(step_ptr, p->step_ptr);
+  cp(sigma, p->sigma);
+  cp(csr_ptr, p->csr_ptr);
+  cp(csr_src, p->csr_src);
+  cp(tcsr_ptr, p->tcsr_ptr);
+  cp(tcsr_dst, p->tcsr_dst);
+  cp(param_row, p->param_row);
+  return GRAFX_OK;
+}
+
+int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* stream) {
+  GX_TRY
+  if (!p || !dev_ws) return fail(GRAFX_EINVAL, "null argument");
+  if (reinterpret_cast<uintptr_t>(dev_ws) % 256) return fail(GRAFX_EINVAL, "workspace must be 256-byte aligned");
+  if (bytes < p->ws.total) return fail(GRAFX_ESHAPE, "workspace too small");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<char> img(p->ws.tables_end, 0);
+  auto put = [&](size_t off, const void* src, size_t n) {
+    if (n) std::memcpy(img.data() + off, src, n);
+  };
+  put(p->ws.nodes, p->nodes.data(), p->nodes.size() * sizeof(NodeDev));
+  put(p->ws.node_ext, p->node_ext.data(), p->node_ext.size() * sizeof(int4_));
+  put(p->ws.csr_ptr, p->csr_ptr.data(), p->csr_ptr.size() * 4);
+  put(p->ws.csr_src, p->csr_src.data(), p->csr_src.size() * 4);
+  put(p->ws.tcsr_ptr, p->tcsr_ptr.data(), p->tcsr_ptr.size() * 4);
+  put(p->ws.tcsr_dst, p->tcsr_dst.data(), p->tcsr_dst.size() * 4);
+  put(p->ws.items, p->items.data(), p->items.size() * sizeof(int4_));
+  put(p->ws.twiddle, p->twiddle.data(), p->twiddle.size() * sizeof(float2_));
+  put(p->ws.eq_cos, p->eq_cos.data(), p->eq_cos.size() * 4);
+  put(p->ws.eq_hann, p->eq_hann.data(), p->eq_hann.size() * 4);
+  put(p->ws.eq_band, p->eq_band.data(), p->eq_band.size() * 4);
+  put(p->ws.loss_rows, p->loss.rows.data(), p->loss.rows.size() * sizeof(LossRow));
+  size_t off = p->ws.loss_items;
+  for (int q = 0; q < N_RES; ++q) {
+    put(off, p->loss.items[q].data(), p->loss.items[q].size() * sizeof(int2_));
+    off += p->loss.items[q].size() * sizeof(int2_);
+  }
+  int rc = cuda_check(cudaMemcpyAsync(dev_ws, img.data(), img.size(), cudaMemcpyHostToDevice, s), "upload tables");
+  if (rc) return rc;
+  rc = cuda_check(cudaMemsetAsync(static_cast<char*>(dev_ws) + p->ws.status, 0, 16, s), "clear status");
+  if (rc) return rc;
+  rc = cuda_check(cudaStreamSynchronize(s), "upload tables");
+  if (rc) return rc;
+  p->dev_ws = static_cast<char*>(dev_ws);
+  return GRAFX_OK;
+  GX_CATCH
+}
+
+int grafx_bind_params(grafx_plan* p, int32_t type, const float* dev, int64_t rows, int64_t cols) {
+  if (!p) return fail(GRAFX_EINVAL, "null plan");
+  if (type < 0 || type >= GRAFX_N_TYPES) return fail(GRAFX_ETYPE, "unknown node type");
+  if (param_cols(type) == 0) return fail(GRAFX_ETYPE, "type has no parameters");
+  if (rows != p->n_type_rows[type] || cols != param_cols(type))
+    return fail(GRAFX_ESHAPE, "parameter table shape mismatch");
+  if (rows > 0 && !dev) return fail(GRAFX_EINVAL, "null parameter pointer");
+  p->params[type] = dev;
+  p->param_rows[type] = rows;
+  return GRAFX_OK;
+}
+
+int grafx_render(grafx_plan* p, const float* sources, float* out, void* stream) {
+  if (!p || !sources || !out) return fail(GRAFX_EINVAL, "null argument");
+  int rc = check_ready(p);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevCtx c = make_ctx(p, sources, out, nullptr, nullptr);
+  int launches = 0;
+  clear_flags(p, s);
+  const int N = int(p->sched.string.size()) - 1;
+  for (int k = 1; k <= N; ++k) {
+    const StepInfo& st = p->steps[k];
+    c.params = p->params[st.type];
+    switch (st.type) {
+      case GRAFX_T_EQ:
+        launches += launch_eq(0, c, st.node_begin, st.node_end, s);
+        launches += launch_eq(1, c, st.fitem_begin, st.fitem_count, s);
+        break;
+      case GRAFX_T_COMP:
+        launches += launch_comp(0, c, st.fitem_begin, st.fitem_count, 2 * k, s);
+        break;
+      default:
+        launches += launch_ew_fwd(st.type, c, st.fitem_begin, st.fitem_count, s);
+    }
+  }
+  p->last_launches = launches;
+  return cuda_check(cudaGetLastError(), "render launch");
+}
+
+int grafx_backprop(grafx_plan* p, const float* sources, const float* d_out, float* const* d_params,
+                   float* d_sources, void* stream) {
+  if (!p || !sources || !d_out) return fail(GRAFX_EINVAL, "null argument");
+  int rc = check_ready(p);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevCtx c = make_ctx(p, sources, nullptr, d_out, d_sources);
+  int launches = 0;
+  clear_flags(p, s);
+  const int N = int(p->sched.string.size()) - 1;
+  for (int k = N; k >= 1; --k) {
+    const StepInfo& st = p->steps[k];
+    if (st.type == GRAFX_T_OUT) continue;  // adjoint rows of outputs are d_out itself
+    c.params = p->params[st.type];
+    c.dparams = d_params ? d_params[st.type] : nullptr;
+    switch (st.type) {
+      case GRAFX_T_EQ:
+        launches += launch_eq(2, c, st.bitem_begin, st.bitem_count, s);
+        if (c.dparams) launches += launch_eq(3, c, st.node_begin, st.node_end, s);
+        break;
+      case GRAFX_T_COMP:
+        launches += launch_comp(1, c, st.bitem_begin, st.bitem_count, 2 * k + 1, s);
+        if (c.dparams) launches += launch_comp(2, c, st.node_begin, st.node_end, 0, s);
+        break;
+      case GRAFX_T_GAIN:
+      case GRAFX_T_IMAGER:
+        launches += launch_ew_bwd(st.type, c, st.bitem_begin, st.bitem_count, s);
+        if (c.dparams) launches += launch_ew_finalize(c, st.node_begin, st.node_end, param_cols(st.type), s);
+        break;
+      default:
+        launches += launch_ew_bwd(GRAFX_T_MIX, c, st.bitem_begin, st.bitem_count, s);
+    }
+  }
+  if (d_sources) launches += launch_ew_bwd(GRAFX_T_MIX, c, p->in_bitem_begin, p->in_bitem_count, s);
+  p->last_launches = launches;
+  return cuda_check(cudaGetLastError(), "backprop launch");
+}
+
+int grafx_mrstft_forward(grafx_plan* p, const float* out, const float* target, float* loss, void* stream) {
+  if (!p || !out || !target || !loss) return fail(GRAFX_EINVAL, "null argument");
+  if (!p->dev_ws) return fail(GRAFX_ESTATE, "workspace not bound");
+  if (!p->loss.ok) return fail(GRAFX_ESHAPE, "every output length must be >= 2048 for the STFT loss");
+  LossLaunch L = make_loss(p, out, target);
+  L.loss = loss;
+  p->last_launches = launch_loss(0, L, static_cast<cudaStream_t>(stream));
+  return cuda_check(cudaGetLastError(), "loss launch");
+}
+
+int grafx_mrstft_backward(grafx_plan* p, const float* out, const float* target, float* d_out, void* stream) {
+  if (!p || !out || !target || !d_out) return fail(GRAFX_EINVAL, "null argument");
+  if (!p->dev_ws) return fail(GRAFX_ESTATE, "workspace not bound");
+  if (!p->loss.ok) return fail(GRAFX_ESHAPE, "every output length must be >= 2048 for the STFT loss");
+  LossLaunch L = make_loss(p, out, target);
+  L.d_out = d_out;
+  p->last_launches = launch_loss(2, L, static_cast<cudaStream_t>(stream));
+  return cuda_check(cudaGetLastError(), "loss launch");
+}
+
+int grafx_sync_status(grafx_plan* p, void* stream) {
+  if (!p || !p->dev_ws) return fail(GRAFX_ESTATE, "workspace not bound");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = cuda_check(cudaStreamSynchronize(s), "synchronize");
+  if (rc) return rc;
+  uint32_t st = 0;
+  rc = cuda_check(cudaMemcpy(&st, p->dev_ws + p->ws.status, 4, cudaMemcpyDeviceToHost), "read status");
+  if (rc) return rc;
+  if (st) {
+    cudaMemset(p->dev_ws + p->ws.status, 0, 4);
+    if (st & ST_TIMEOUT) return fail(GRAFX_ETIMEOUT, "a bounded device wait expired");
+    return fail(GRAFX_EINVAL, "a device bounds check failed");
+  }
+  return GRAFX_OK;
+}
+
+int grafx_last_launch_count(const grafx_plan* p, int32_t* n) {
+  if (!p || !n) return fail(GRAFX_EINVAL, "null argument");
+  *n = p->last_launches;
+  return GRAFX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// Device context and helpers shared by the step kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/grafx.h"
+#include "devtypes.h"
+
+namespace grafx {
+
+// Everything a step kernel needs, passed by value.  Row bases are indexed by
+// NodeKind: [0] sources (or d_sources), [1] the caller's out (or d_out), [2] the
+// workspace U (or adjoint A) region.
+struct DevCtx {
+  const NodeDev* nodes;
+  const int4_* ext;
+  const int32_t* csr_ptr;
+  const int32_t* csr_src;
+  const int32_t* tcsr_ptr;
+  const int32_t* tcsr_dst;
+  const int4_* items;
+  const float2_* tw;
+  const float* eq_cos;
+  const float* eq_hann;
+  const float* eq_band;
+  uint32_t* status;
+  int32_t* tickets;
+  unsigned long long* flags;
+  float* eq_spec;
+  float* comp_carry;
+  float4* partial;
+  float2* eq_partial;
+  float* ybase[3];
+  float* abase[3];
+  const float* params;  // P[t] of the launched step's type
+  float* dparams;       // dLoss/dP[t] (finalize kernels)
+  int32_t pcols;
+  int32_t eq_taps, eq_H, eq_Hal, eq_fft, eq_step;
+  int32_t comp_chunk;
+  float sample_rate;
+};
+
+__device__ __forceinline__ const float* yrow(const DevCtx& c, const NodeDev& n) {
+  return c.ybase[n.kind] + n.off_y;
+}
+__device__ __forceinline__ float* yrow_w(const DevCtx& c, const NodeDev& n) {
+  return c.ybase[n.kind] + n.off_y;
+}
+__device__ __forceinline__ const float* arow(const DevCtx& c, const NodeDev& n) {
+  return c.abase[n.kind] + n.off_a;
+}
+__device__ __forceinline__ float* arow_w(const DevCtx& c, const NodeDev& n) {
+  return c.abase[n.kind] + n.off_a;
+}
+
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 f4zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+// Keep only the samples of quad [t, t+4) that are < len (row padding reads as 0).
+__device__ __forceinline__ float4 mask4(float4 v, int t, int len) {
+  if (t + 4 <= len) return v;
+  if (t + 0 >= len) v.x = 0.f;
+  if (t + 1 >= len) v.y = 0.f;
+  if (t + 2 >= len) v.z = 0.f;
+  if (t + 3 >= len) v.w = 0.f;
+  return v;
+}
+
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+// Plain (coherent) load for rows written earlier in the same launch sequence.
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+// u_v: sum over the in-edges of v (Eq. 1b; I^G gather + I^A aggregate of Algorithm 1)
+// of the quad [t, t+4) of channel ch, in CSR order.  t must be a multiple of 4.
+__device__ __forceinline__ float4 gather_in(const DevCtx& c, int v, int ch, int t, int len, int pitch) {
+  float4 acc = f4zero();
+  const int e1 = c.csr_ptr[v + 1];
+  for (int e = c.csr_ptr[v]; e < e1; ++e) {
+    const NodeDev& s = c.nodes[c.csr_src[e]];
+    acc = f4add(acc, ld4(yrow(c, s) + ch * pitch + t));
+  }
+  return mask4(acc, t, len);
+}
+
+// ybar_v: sum over the consumers w of v of their input adjoints (transposed CSR).
+__device__ __forceinline__ float4 gather_out_adj(const DevCtx& c, int v, int ch, int t, int len, int pitch) {
+  float4 acc = f4zero();
+  const int e1 = c.tcsr_ptr[v + 1];
+  for (int e = c.tcsr_ptr[v]; e < e1; ++e) {
+    const NodeDev& w = c.nodes[c.tcsr_dst[e]];
+    acc = f4add(acc, ld4(arow(c, w) + ch * pitch + t));
+  }
+  return mask4(acc, t, len);
+}
+
+__device__ __forceinline__ void set_status(const DevCtx& c, uint32_t bits) { atomicOr(c.status, bits); }
+
+// Block-wide sum of up to 4 values (blockDim.x multiple of 32, <= 1024).  Result
+// valid in thread 0.  Uses `sh` of at least 4*32 floats.
+template <int NV>
+__device__ __forceinline__ void block_sum(float (&v)[NV], float* sh) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh[i * 32 + warp] = v[i];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      float x = lane < nw ? sh[i * 32 + lane] : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      v[i] = x;
+    }
+  }
+}
+
+}  // namespace grafx

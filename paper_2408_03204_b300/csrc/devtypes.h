@@ -1,0 +1,46 @@
+// Plain structs shared by the host planner and the device kernels (same layout on both).
+#pragma once
+#include <stdint.h>
+
+namespace grafx {
+
+enum NodeKind : int16_t { KIND_INPUT = 0, KIND_OUTPUT = 1, KIND_INTERNAL = 2 };
+
+// One node in reordered (new-id) order.  A node's output row Y_v lives in one of
+// three buffers chosen by `kind` (sources for inputs, the caller's out buffer for
+// outputs, the workspace U region otherwise); likewise its adjoint row.
+struct alignas(16) NodeDev {
+  int64_t off_y;   // float offset of the [2][pitch] output row inside its buffer
+  int64_t off_a;   // float offset of the [2][pitch] adjoint row inside its buffer
+  int32_t len;     // signal length L of the node's graph
+  int32_t pitch;   // channel stride (L rounded up to a multiple of 4)
+  int32_t prow;    // row of P[type] owned by the node (I^P of Algorithm 1)
+  int16_t kind;    // NodeKind
+  int16_t type;    // GRAFX_T_*
+};
+
+struct alignas(16) int4_ { int32_t x, y, z, w; };
+struct alignas(8) int2_ { int32_t x, y; };
+struct alignas(8) float2_ { float x, y; };
+
+// One output row of the loss.
+struct alignas(16) LossRow {
+  int64_t off;            // float offset of the row in out / target / d_out
+  int64_t frame_off[3];   // float offset of the row's frame buffer per resolution
+  int32_t len, pitch;
+  int32_t n_frames[3];
+  int32_t group_off[3];   // first partial-statistics group of the row per resolution
+  int32_t n_groups[3];
+  int32_t pad;
+};
+
+constexpr int TWIDDLE_N = 8192;   // twiddle table size: exp(-2 pi i m / 8192)
+constexpr int EW_TILE = 4096;     // samples per elementwise work item
+constexpr int N_RES = 3;          // loss resolutions 512, 1024, 2048
+constexpr int LOSS_FRAMES_PER_ITEM = 8;
+
+// status bits written by kernels
+constexpr uint32_t ST_TIMEOUT = 1u;
+constexpr uint32_t ST_BOUNDS = 2u;
+
+}  // namespace grafx

@@ -1,0 +1,203 @@
+// Shared-memory complex FFT for the block convolutions and the STFT loss.
+//
+// Stockham auto-sort formulation: M = 16^a * r points, one radix-16 pass per factor
+// 16 and one final radix-r pass (r in {2, 4, 8, 16}).  A transform is run by
+// T = M/16 threads; thread `tid` owns M/(16 T) = 1 radix-16 butterfly per pass (or
+// 16/r radix-r butterflies in the last pass), so every pass is: load the
+// butterfly inputs from shared memory into registers, barrier, apply the
+// twiddles W_{Ns R}^{r k} and an in-register DFT_R, write to the auto-sorted
+// positions, barrier.  Shared-memory indices are padded (i + i/16) so that the
+// stride-16 writes of the first pass are free of bank conflicts.
+//
+// Twiddles come from a table tw[m] = exp(-2 pi i m / 8192) built on the host in
+// double precision.  The forward transform uses exp(-2 pi i k n / M); an inverse is
+// obtained by conjugating the input and the output.
+//
+// The pass bodies are __host__ __device__ so that a CPU harness can run the same
+// arithmetic thread by thread.
+#pragma once
+#include "devtypes.h"
+
+#ifdef __CUDACC__
+#define GX_HD __host__ __device__ __forceinline__
+#else
+#define GX_HD inline
+struct float2 { float x, y; };
+inline float2 make_float2(float x, float y) { return float2{x, y}; }
+#endif
+
+namespace grafx {
+namespace fft {
+
+GX_HD int pad(int i) { return i + (i >> 4); }
+template <int M> struct Padded { static constexpr int size = M + M / 16; };
+
+GX_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+GX_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+GX_HD float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+GX_HD float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+GX_HD float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }  // a * (-i)
+
+// exp(-2 pi i m / 16) for the in-register radix-16 twiddles (m = n2*k1 <= 9)
+GX_HD float2 w16(int m) {
+  const float c = 0.92387953251128674f, s = 0.38268343236508978f, h = 0.70710678118654752f;
+  switch (m) {
+    case 0: return make_float2(1.f, 0.f);
+    case 1: return make_float2(c, -s);
+    case 2: return make_float2(h, -h);
+    case 3: return make_float2(s, -c);
+    case 4: return make_float2(0.f, -1.f);
+    case 6: return make_float2(-h, -h);
+    default: return make_float2(-c, s);  // m = 9
+  }
+}
+GX_HD float2 w8(int m) {
+  const float h = 0.70710678118654752f;
+  switch (m) {
+    case 0: return make_float2(1.f, 0.f);
+    case 1: return make_float2(h, -h);
+    case 2: return make_float2(0.f, -1.f);
+    default: return make_float2(-h, -h);  // m = 3
+  }
+}
+
+GX_HD void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+// forward 4-point DFT of (x0, x1, x2, x3) in place
+GX_HD void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+  float2 t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), t3 = mul_mi(csub(x1, x3));
+  x0 = cadd(t0, t2);
+  x2 = csub(t0, t2);
+  x1 = cadd(t1, t3);
+  x3 = csub(t1, t3);
+}
+
+template <int R> struct Dft;
+template <> struct Dft<2> {
+  GX_HD static void run(float2* v) { dft2(v[0], v[1]); }
+};
+template <> struct Dft<4> {
+  GX_HD static void run(float2* v) { dft4(v[0], v[1], v[2], v[3]); }
+};
+// 8 = 4 x 2: inner DFT4 over n1 of x[2 n1 + n2], twiddle W8^(n2 k1), outer DFT2;
+// output X[k1 + 4 k2]
+template <> struct Dft<8> {
+  GX_HD static void run(float2* v) {
+    float2 a[2][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 2; ++n2) {
+#pragma unroll
+      for (int n1 = 0; n1 < 4; ++n1) a[n2][n1] = v[2 * n1 + n2];
+      dft4(a[n2][0], a[n2][1], a[n2][2], a[n2][3]);
+    }
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1) a[1][k1] = cmul(a[1][k1], w8(k1));
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      float2 p = a[0][k1], q = a[1][k1];
+      dft2(p, q);
+      v[k1] = p;
+      v[k1 + 4] = q;
+    }
+  }
+};
+// 16 = 4 x 4: inner DFT4 over n1 of x[4 n1 + n2], twiddle W16^(n2 k1), outer DFT4
+template <> struct Dft<16> {
+  GX_HD static void run(float2* v) {
+    float2 a[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+#pragma unroll
+      for (int n1 = 0; n1 < 4; ++n1) a[n2][n1] = v[4 * n1 + n2];
+      dft4(a[n2][0], a[n2][1], a[n2][2], a[n2][3]);
+    }
+#pragma unroll
+    for (int n2 = 1; n2 < 4; ++n2)
+#pragma unroll
+      for (int k1 = 1; k1 < 4; ++k1) a[n2][k1] = cmul(a[n2][k1], w16(n2 * k1));
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      float2 x0 = a[0][k1], x1 = a[1][k1], x2 = a[2][k1], x3 = a[3][k1];
+      dft4(x0, x1, x2, x3);
+      v[k1] = x0;
+      v[k1 + 4] = x1;
+      v[k1 + 8] = x2;
+      v[k1 + 12] = x3;
+    }
+  }
+};
+
+// Pass geometry of an M-point transform.
+template <int M> struct Geo {
+  static constexpr int T = M / 16;  // threads per transform
+  static constexpr int n16 = (M >= 65536) ? 4 : (M >= 4096) ? 3 : (M >= 256) ? 2 : 1;
+  static constexpr int last = M / (n16 == 3 ? 4096 : n16 == 2 ? 256 : 16);  // radix of the final pass (1 = none)
+};
+
+// Phase 1 of a pass: read the butterfly inputs of thread `tid`.
+template <int M, int R>
+GX_HD void pass_load(const float2* buf, int tid, float2 (*v)[R]) {
+  constexpr int T = M / 16, BPT = 16 / R;
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) {
+    int j = tid + b * T;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[b][r] = buf[pad(j + r * (M / R))];
+  }
+}
+
+// Phase 2 of a pass: twiddle, DFT_R, auto-sorted store.  Ns = points already merged.
+template <int M, int R>
+GX_HD void pass_store(float2* buf, const float2_* tw, int tid, int Ns, float2 (*v)[R]) {
+  constexpr int T = M / 16, BPT = 16 / R;
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) {
+    int j = tid + b * T;
+    int k = j & (Ns - 1);
+    if (Ns > 1) {
+      int step = k * (TWIDDLE_N / (Ns * R));
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2_ w = tw[r * step];
+        v[b][r] = cmul(v[b][r], make_float2(w.x, w.y));
+      }
+    }
+    Dft<R>::run(v[b]);
+    int out = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[pad(out + r * Ns)] = v[b][r];
+  }
+}
+
+#ifdef __CUDACC__
+// Full forward transform of one M-point padded buffer by threads tid in [0, M/16).
+// Every thread of the CTA must call it (it contains __syncthreads); threads with
+// tid >= M/16 pass `active = false`.  The caller synchronises before the first pass.
+template <int M>
+__device__ __forceinline__ void forward(float2* buf, const float2_* __restrict__ tw, int tid, bool active) {
+  int Ns = 1;
+#pragma unroll
+  for (int p = 0; p < Geo<M>::n16; ++p) {
+    float2 v[1][16];
+    if (active) pass_load<M, 16>(buf, tid, v);
+    __syncthreads();
+    if (active) pass_store<M, 16>(buf, tw, tid, Ns, v);
+    __syncthreads();
+    Ns *= 16;
+  }
+  if constexpr (Geo<M>::last > 1) {
+    constexpr int R = Geo<M>::last;
+    float2 v[16 / R][R];
+    if (active) pass_load<M, R>(buf, tid, v);
+    __syncthreads();
+    if (active) pass_store<M, R>(buf, tw, tid, Ns, v);
+    __syncthreads();
+  }
+}
+#endif
+
+}  // namespace fft
+}  // namespace grafx

@@ -1,0 +1,366 @@
+// Compressor (Eq. 8-12): exact one-pole envelope g[n] = a g[n-1] + (1-a) x[n],
+// x = (u_l + u_r)^2, as a chunked linear-recurrence scan, then the quadratic-knee
+// static curve and the gain exp(G_y - G_u).
+//
+// One work item is a chunk of CH = 256 * SPT samples of one node.  Inside a chunk:
+// every thread runs the recursion over its SPT samples with zero initial state, a
+// warp-shuffle scan and a cross-warp scan combine the per-thread states with the
+// decay a^SPT, and the chunk's carry-in comes from the chunks before it by a
+// decoupled look-back: each chunk publishes its zero-start end state, then its
+// inclusive end state once its carry is known; a chunk walks back over published
+// states until it meets an inclusive one.  Chunks are handed out by an atomic
+// ticket in (node, chunk) order, so every chunk waited on is held by a CTA that is
+// already running; every wait is bounded and records ST_TIMEOUT on expiry.
+// The forward pass stores each chunk's carry-in (one float) so the backward pass
+// can recompute g[n] exactly without a scan across chunks.
+//
+// Backward: ybar gives a_n = dL/dg[n]; lambda[n] = a_n + alpha lambda[n+1] is the
+// same scan run in reverse (chunks handed out from the end of each node);
+// ubar_x = k ybar_x + 2 u_m (1 - alpha) lambda and the parameter partials
+// (sum lambda (g[n-1] - x[n]) for alpha, sum Gybar dGy/dT|W|R) go to one slot
+// per chunk.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace grafx {
+
+constexpr float COMP_EPS = 1e-7f;
+constexpr int SPIN_LIMIT = 1 << 22;
+
+struct Knee {
+  float gy, dgu, dt, dw, dr;
+};
+
+// Eq. 10-11 and the partial derivatives of G_y.
+__device__ __forceinline__ Knee knee(float gu, float T, float W, float R) {
+  Knee k;
+  const float cR = 1.f / R - 1.f;
+  if (gu >= T + W) {
+    k.gy = T + (gu - T) / R;
+    k.dgu = 1.f / R;
+    k.dt = -cR;
+    k.dw = 0.f;
+    k.dr = -(gu - T) / (R * R);
+  } else if (gu >= T - W) {
+    float d = gu - T + W;
+    k.gy = gu + cR * d * d / (4.f * W);
+    k.dgu = 1.f + cR * d / (2.f * W);
+    k.dt = -cR * d / (2.f * W);
+    k.dw = cR * (d / (2.f * W) - d * d / (4.f * W * W));
+    k.dr = -d * d / (4.f * W * R * R);
+  } else {
+    k.gy = gu;
+    k.dgu = 1.f;
+    k.dt = k.dw = k.dr = 0.f;
+  }
+  return k;
+}
+
+__device__ __forceinline__ unsigned long long pack_flag(unsigned st, float v) {
+  return (static_cast<unsigned long long>(st) << 32) | __float_as_uint(v);
+}
+
+// Wait (bounded) for flag j; returns status (1 aggregate, 2 inclusive) and value.
+__device__ __forceinline__ unsigned wait_flag(const DevCtx& c, int j, float* val) {
+  volatile unsigned long long* f = c.flags + j;
+  for (int i = 0; i < SPIN_LIMIT; ++i) {
+    unsigned long long w = *f;
+    unsigned st = unsigned(w >> 32);
+    if (st) {
+      *val = __uint_as_float(unsigned(w & 0xffffffffu));
+      return st;
+    }
+    __nanosleep(64);
+  }
+  set_status(c, ST_TIMEOUT);
+  *val = 0.f;
+  return 2;
+}
+
+__device__ __forceinline__ void publish(const DevCtx& c, int j, unsigned st, float v) {
+  __threadfence();
+  atomicExch(c.flags + j, pack_flag(st, v));
+}
+
+// Walk back from item `j` (the chunk before the current one in ticket order),
+// accumulating aggregates with decay `dc` per chunk until an inclusive state.
+__device__ float look_back(const DevCtx& c, int j, float dc) {
+  float acc = 0.f, dec = 1.f, val;
+  while (true) {
+    unsigned st = wait_flag(c, j, &val);
+    acc += dec * val;
+    if (st == 2) break;
+    dec *= dc;
+    --j;
+  }
+  return acc;
+}
+
+// Block-wide scan of per-thread states with a common decay D = exp(la_spt): a thread
+// maps the state entering it to D * state + b.  Forward: state flows from thread i-1
+// to thread i; reverse: from thread i+1 to thread i.  Returns the state entering this
+// thread when zero enters the chunk, and sets *total to the state leaving the chunk.
+// Requires blockDim.x == 256; `sh` holds >= 17 floats.
+template <bool REVERSE>
+__device__ __forceinline__ float block_affine_scan(float b, float la_spt, float* sh, float* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float incl = b;  // Hillis-Steele: incl_i += D^d incl_{i-d} (forward) / incl_{i+d} (reverse)
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    float o = REVERSE ? __shfl_down_sync(0xffffffffu, incl, d) : __shfl_up_sync(0xffffffffu, incl, d);
+    bool ok = REVERSE ? (lane + d < 32) : (lane >= d);
+    if (ok) incl += expf(la_spt * float(d)) * o;
+  }
+  float excl = REVERSE ? __shfl_down_sync(0xffffffffu, incl, 1) : __shfl_up_sync(0xffffffffu, incl, 1);
+  if (REVERSE ? (lane == 31) : (lane == 0)) excl = 0.f;
+  if (REVERSE ? (lane == 0) : (lane == 31)) sh[warp] = incl;  // state leaving the warp
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const float d32 = expf(la_spt * 32.f);
+    float run = 0.f;
+    for (int k = 0; k < 8; ++k) {
+      int wi = REVERSE ? 7 - k : k;
+      float tw = sh[wi];
+      sh[8 + wi] = run;          // state entering warp wi
+      run = d32 * run + tw;
+    }
+    sh[16] = run;
+  }
+  __syncthreads();
+  const int dist = REVERSE ? (31 - lane) : lane;  // threads between the warp edge and this one
+  *total = sh[16];
+  return excl + expf(la_spt * float(dist)) * sh[8 + warp];
+}
+
+template <int SPT>
+__device__ __forceinline__ void load_chunk(const DevCtx& c, int v, const NodeDev& nd, int t, float* ul, float* ur,
+                                           bool adj) {
+#pragma unroll
+  for (int q = 0; q < SPT / 4; ++q) {
+    float4 l, r;
+    if (t + 4 * q < nd.len) {
+      if (adj) {
+        l = gather_out_adj(c, v, 0, t + 4 * q, nd.len, nd.pitch);
+        r = gather_out_adj(c, v, 1, t + 4 * q, nd.len, nd.pitch);
+      } else {
+        l = gather_in(c, v, 0, t + 4 * q, nd.len, nd.pitch);
+        r = gather_in(c, v, 1, t + 4 * q, nd.len, nd.pitch);
+      }
+    } else {
+      l = r = f4zero();
+    }
+    ul[4 * q + 0] = l.x; ul[4 * q + 1] = l.y; ul[4 * q + 2] = l.z; ul[4 * q + 3] = l.w;
+    ur[4 * q + 0] = r.x; ur[4 * q + 1] = r.y; ur[4 * q + 2] = r.z; ur[4 * q + 3] = r.w;
+  }
+}
+
+template <int SPT>
+__device__ __forceinline__ void store_chunk(float* row, const NodeDev& nd, int t, const float* yl, const float* yr) {
+#pragma unroll
+  for (int q = 0; q < SPT / 4; ++q) {
+    if (t + 4 * q < nd.pitch) {
+      st4(row + t + 4 * q, make_float4(yl[4 * q], yl[4 * q + 1], yl[4 * q + 2], yl[4 * q + 3]));
+      st4(row + nd.pitch + t + 4 * q, make_float4(yr[4 * q], yr[4 * q + 1], yr[4 * q + 2], yr[4 * q + 3]));
+    }
+  }
+}
+
+// Envelope of the thread's SPT samples from the state entering the thread.
+// Identical arithmetic in the forward and backward kernels.
+template <int SPT>
+__device__ __forceinline__ void envelope(const float* x, float alpha, float cin, float* g) {
+  float s = cin;
+#pragma unroll
+  for (int i = 0; i < SPT; ++i) {
+    s = alpha * s + (1.f - alpha) * x[i];
+    g[i] = s;
+  }
+}
+
+template <int SPT>
+__global__ void __launch_bounds__(256) k_comp_fwd(DevCtx c, int item0, int n_items, int ticket) {
+  constexpr int CH = 256 * SPT;
+  __shared__ float sh[32];
+  __shared__ int s_it;
+  __shared__ float s_carry;
+  while (true) {
+    if (threadIdx.x == 0) s_it = atomicAdd(c.tickets + ticket, 1);
+    __syncthreads();
+    const int it = s_it;
+    if (it >= n_items) break;
+    const int4_ w = c.items[item0 + it];
+    const int v = w.x, chunk = w.y;
+    const NodeDev nd = c.nodes[v];
+    const float* p = c.params + nd.prow * 4;
+    const float alpha = p[0], T = p[1], W = p[2], R = p[3];
+    const float la = logf(alpha);
+    const int t = chunk * CH + threadIdx.x * SPT;
+    float ul[SPT], ur[SPT], x[SPT], g[SPT];
+    load_chunk<SPT>(c, v, nd, t, ul, ur, false);
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
+    // zero-start local state at the thread's end
+    float b = 0.f;
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) b = alpha * b + (1.f - alpha) * x[i];
+    float total;
+    float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
+    if (threadIdx.x == 0) {
+      float carry = 0.f;
+      if (chunk == 0) {
+        publish(c, item0 + it, 2, total);
+      } else {
+        publish(c, item0 + it, 1, total);
+        carry = look_back(c, item0 + it - 1, expf(la * CH));
+        publish(c, item0 + it, 2, expf(la * CH) * carry + total);
+      }
+      c.comp_carry[w.z] = carry;
+      s_carry = carry;
+    }
+    __syncthreads();
+    const float cin = excl + expf(la * float(SPT * threadIdx.x)) * s_carry;
+    envelope<SPT>(x, alpha, cin, g);
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) {
+      float gu = logf(g[i] + COMP_EPS);
+      Knee k = knee(gu, T, W, R);
+      float gain = expf(k.gy - gu);
+      ul[i] *= gain;
+      ur[i] *= gain;
+    }
+    store_chunk<SPT>(yrow_w(c, nd), nd, t, ul, ur);
+    __syncthreads();
+  }
+}
+
+template <int SPT>
+__global__ void __launch_bounds__(256) k_comp_bwd(DevCtx c, int item0, int n_items, int ticket) {
+  constexpr int CH = 256 * SPT;
+  __shared__ float sh[32];
+  __shared__ float glast[256];
+  __shared__ float red[4 * 32];
+  __shared__ int s_it;
+  __shared__ float s_lin;
+  while (true) {
+    if (threadIdx.x == 0) s_it = atomicAdd(c.tickets + ticket, 1);
+    __syncthreads();
+    const int it = s_it;
+    if (it >= n_items) break;
+    const int4_ w = c.items[item0 + it];
+    const int v = w.x, chunk = w.y;
+    const NodeDev nd = c.nodes[v];
+    const float* p = c.params + nd.prow * 4;
+    const float alpha = p[0], T = p[1], W = p[2], R = p[3];
+    const float la = logf(alpha);
+    const int t = chunk * CH + threadIdx.x * SPT;
+    const int n_chunks = (nd.len + CH - 1) / CH;
+    float ul[SPT], ur[SPT], bl[SPT], br[SPT], x[SPT], g[SPT], a[SPT];
+    load_chunk<SPT>(c, v, nd, t, ul, ur, false);
+    load_chunk<SPT>(c, v, nd, t, bl, br, true);
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
+    // recompute the envelope from the stored chunk carry-in (same arithmetic as forward)
+    const float carry_g = c.comp_carry[w.z];
+    float b = 0.f;
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) b = alpha * b + (1.f - alpha) * x[i];
+    float total;
+    float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
+    const float cin = excl + expf(la * float(SPT * threadIdx.x)) * carry_g;
+    envelope<SPT>(x, alpha, cin, g);
+    // local adjoints
+    float gain[SPT], gyb[SPT], dT = 0.f, dW = 0.f, dR = 0.f;
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) {
+      float gu = logf(g[i] + COMP_EPS);
+      Knee k = knee(gu, T, W, R);
+      gain[i] = expf(k.gy - gu);
+      float kbar = bl[i] * ul[i] + br[i] * ur[i];
+      gyb[i] = kbar * gain[i];
+      a[i] = gyb[i] * (k.dgu - 1.f) / (g[i] + COMP_EPS);
+      dT += gyb[i] * k.dt;
+      dW += gyb[i] * k.dw;
+      dR += gyb[i] * k.dr;
+    }
+    // reverse scan lambda[n] = a[n] + alpha lambda[n+1]
+    float lb = 0.f;
+#pragma unroll
+    for (int i = SPT - 1; i >= 0; --i) lb = a[i] + alpha * lb;
+    __syncthreads();  // sh reuse
+    float rtotal;
+    float rexcl = block_affine_scan<true>(lb, la * SPT, sh, &rtotal);
+    if (threadIdx.x == 0) {
+      float lin = 0.f;
+      if (chunk == n_chunks - 1) {
+        publish(c, item0 + it, 2, rtotal);
+      } else {
+        publish(c, item0 + it, 1, rtotal);
+        lin = look_back(c, item0 + it - 1, expf(la * CH));
+        publish(c, item0 + it, 2, expf(la * CH) * lin + rtotal);
+      }
+      s_lin = lin;
+    }
+    glast[threadIdx.x] = g[SPT - 1];
+    __syncthreads();
+    // state entering this thread from the right: within-chunk part + the chunk carry
+    const float lin_t = rexcl + expf(la * float(SPT * (255 - threadIdx.x))) * s_lin;
+    float lam[SPT];
+    {
+      float s = lin_t;
+#pragma unroll
+      for (int i = SPT - 1; i >= 0; --i) {
+        s = a[i] + alpha * s;
+        lam[i] = s;
+      }
+    }
+    float gprev = threadIdx.x > 0 ? glast[threadIdx.x - 1] : carry_g;
+    float dA = 0.f;
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) {
+      dA += lam[i] * (gprev - x[i]);
+      gprev = g[i];
+      float xb2 = 2.f * (ul[i] + ur[i]) * (1.f - alpha) * lam[i];
+      bl[i] = gain[i] * bl[i] + xb2;
+      br[i] = gain[i] * br[i] + xb2;
+    }
+    store_chunk<SPT>(arow_w(c, nd), nd, t, bl, br);
+    float acc[4] = {dA, dT, dW, dR};
+    block_sum<4>(acc, red);
+    if (threadIdx.x == 0) c.partial[w.w] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    __syncthreads();
+  }
+}
+
+__global__ void k_comp_finalize(DevCtx c, int node_begin, int node_end) {
+  int v = node_begin + blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= node_end) return;
+  const int4_ e = c.ext[v];
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k = 0; k < e.y; ++k) {
+    float4 q = c.partial[e.x + k];
+    s.x += q.x; s.y += q.y; s.z += q.z; s.w += q.w;
+  }
+  float* d = c.dparams + c.nodes[v].prow * 4;
+  d[0] = s.x; d[1] = s.y; d[2] = s.z; d[3] = s.w;
+}
+
+// what: 0 forward, 1 backward (items), 2 finalize (node range)
+int launch_comp(int what, const DevCtx& c, int a, int b, int ticket, cudaStream_t s) {
+  if (what == 2) {
+    if (b <= a) return 0;
+    k_comp_finalize<<<(b - a + 127) / 128, 128, 0, s>>>(c, a, b);
+    return 1;
+  }
+  if (b <= 0) return 0;
+  int g = grid_size(b, 4);
+  if (c.comp_chunk == 1024) {
+    if (what == 0) k_comp_fwd<4><<<g, 256, 0, s>>>(c, a, b, ticket);
+    else k_comp_bwd<4><<<g, 256, 0, s>>>(c, a, b, ticket);
+  } else {
+    if (what == 0) k_comp_fwd<8><<<g, 256, 0, s>>>(c, a, b, ticket);
+    else k_comp_bwd<8><<<g, 256, 0, s>>>(c, a, b, ticket);
+  }
+  return 1;
+}
+
+}  // namespace grafx

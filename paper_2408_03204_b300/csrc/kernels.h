@@ -1,0 +1,43 @@
+// Launch wrappers of the step kernels (one per .cu file).  Each returns the number of
+// kernels it launched.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace grafx {
+
+int grid_size(int n_items, int per_sm);
+
+// elementwise types (mix/out, gain, imager)
+int launch_ew_fwd(int type, const DevCtx& c, int item0, int n_items, cudaStream_t s);
+int launch_ew_bwd(int type, const DevCtx& c, int item0, int n_items, cudaStream_t s);
+int launch_ew_finalize(const DevCtx& c, int node_begin, int node_end, int cols, cudaStream_t s);
+
+// EQ: what = 0 design (a = node_begin, b = node_end), 1 forward (a = item0,
+// b = n_items), 2 backward (items), 3 gradient finalize (node range)
+int launch_eq(int what, const DevCtx& c, int a, int b, cudaStream_t s);
+
+// compressor: what = 0 forward, 1 backward (a = item0, b = n_items, ticket index),
+// 2 gradient finalize (a = node_begin, b = node_end)
+int launch_comp(int what, const DevCtx& c, int a, int b, int ticket, cudaStream_t s);
+
+struct LossLaunch {
+  const LossRow* rows;
+  const int2_* items[N_RES];
+  int n_items[N_RES];
+  const float* y;
+  const float* tgt;
+  float4* part;
+  float4* stats;
+  float* frames;
+  const float2_* tw;
+  int n_rows;
+  int max_pitch;
+  float* loss;
+  float* d_out;
+};
+// what = 0 forward (statistics + reduce into *loss), 2 backward (frames + overlap-add into d_out)
+int launch_loss(int what, const LossLaunch& L, cudaStream_t s);
+
+}  // namespace grafx

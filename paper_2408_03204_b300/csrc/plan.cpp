@@ -1,0 +1,368 @@
+// Plan building: Algorithm 1 lines 2-4 (reordering sigma, index maps) on the host,
+// plus the device-side work lists, constant tables and workspace layout.
+#include "plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <thread>
+
+namespace grafx {
+
+namespace {
+thread_local std::string g_err;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// EQ band matrix: bin k of an N-tap zero-phase FIR sits at k*fs/N; its gain in dB is
+// the linear interpolation in log2(f) between the two nearest of 8 log-spaced band
+// centres 20*1000^((b+0.5)/8) Hz, and the end bands' gains beyond the end centres.
+void eq_band_table(int N, int fs, std::vector<float>* out) {
+  const int K = (N + 1) / 2, NB = 8;
+  double c[NB], lc[NB];
+  for (int b = 0; b < NB; ++b) {
+    c[b] = 20.0 * std::pow(1000.0, (b + 0.5) / NB);
+    lc[b] = std::log2(c[b]);
+  }
+  out->assign(size_t(K) * NB, 0.f);
+  for (int k = 0; k < K; ++k) {
+    double f = double(k) * fs / N;
+    float* row = out->data() + size_t(k) * NB;
+    if (f <= c[0]) { row[0] = 1.f; continue; }
+    if (f >= c[NB - 1]) { row[NB - 1] = 1.f; continue; }
+    int b = 0;
+    while (b + 1 < NB && c[b + 1] <= f) ++b;
+    double w = (std::log2(f) - lc[b]) / (lc[b + 1] - lc[b]);
+    row[b] = float(1.0 - w);
+    row[b + 1] = float(w);
+  }
+}
+
+int pick_eq_fft(int taps) {
+  int H = (taps - 1) / 2;
+  int need = 2 * ((H + 3) & ~3) + 1024;
+  int m = 1024;
+  while (m < need) m *= 2;
+  return m;
+}
+}  // namespace
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+void clear_error() { g_err.clear(); }
+const char* last_error_cstr() { return g_err.c_str(); }
+
+int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* lengths,
+               const grafx_plan_opts& opts, Plan* p) {
+  p->opts = opts;
+  p->n_graphs = int32_t(graphs.size());
+  if (p->n_graphs < 1) return fail(GRAFX_EINVAL, "no graphs");
+  // ---- union (graph-level parallelism: one disconnected graph)
+  for (int32_t g = 0; g < p->n_graphs; ++g) {
+    if (!graphs[g]) return fail(GRAFX_EINVAL, "null graph");
+    int64_t L = lengths[g];
+    if (L < 1 || L > (int64_t(1) << 24)) return fail(GRAFX_ESHAPE, "length out of range [1, 2^24]");
+    p->L.push_back(L);
+    p->pitch.push_back(pitch_of(L));
+    int32_t off = int32_t(p->types.size());
+    for (int32_t t : graphs[g]->types) {
+      p->types.push_back(t);
+      p->node_graph.push_back(g);
+    }
+    for (auto& e : graphs[g]->edges) {
+      int32_t n_g = int32_t(graphs[g]->types.size());
+      if (e.first < 0 || e.first >= n_g || e.second < 0 || e.second >= n_g)
+        return fail(GRAFX_EINVAL, "edge out of range");
+      p->edges.push_back({e.first + off, e.second + off});
+    }
+  }
+  const int32_t n = int32_t(p->types.size());
+  const int32_t n_e = int32_t(p->edges.size());
+  int rc = validate(p->types, p->edges);
+  if (rc) return rc;
+  for (int32_t t : p->types)
+    if (t == GRAFX_T_DELAY || t == GRAFX_T_REVERB)
+      return fail(GRAFX_ETYPE, "delay and reverb nodes are not supported by this build");
+  if (opts.eq_taps < 3 || opts.eq_taps % 2 == 0 || opts.eq_taps > 2047)
+    return fail(GRAFX_EINVAL, "eq_taps must be odd in [3, 2047]");
+  int nthr = opts.n_threads > 0 ? opts.n_threads : int(std::max(1u, std::thread::hardware_concurrency()));
+  rc = make_schedule(p->types, p->edges, opts.schedule, opts.beam_width, nthr, &p->sched);
+  if (rc) return rc;
+
+  // ---- sigma: rank by (step, original id); steps become contiguous ranges (I^S)
+  const int32_t N = int32_t(p->sched.string.size()) - 1;
+  p->sigma.assign(n, 0);
+  p->step_ptr.assign(1, 0);
+  {
+    int32_t next = 0;
+    for (auto& st : p->sched.steps) {
+      std::vector<int32_t> s = st;
+      std::sort(s.begin(), s.end());
+      for (int32_t v : s) p->sigma[v] = next++;
+      p->step_ptr.push_back(next);
+    }
+  }
+  p->new_types.assign(n, 0);
+  p->param_row.assign(n, 0);
+  {
+    int32_t cnt[GRAFX_N_TYPES] = {0};
+    for (int32_t v = 0; v < n; ++v) {
+      p->new_types[p->sigma[v]] = p->types[v];
+      p->param_row[p->sigma[v]] = cnt[p->types[v]]++;
+    }
+    std::memcpy(p->n_type_rows, cnt, sizeof(cnt));
+  }
+  // ---- in-edge CSR by (dst, src) = I^G / I^A; consumer CSR by (src, dst) for backward
+  {
+    std::vector<std::pair<int32_t, int32_t>> ed(n_e), te(n_e);
+    for (int32_t e = 0; e < n_e; ++e) {
+      int32_t s = p->sigma[p->edges[e].first], d = p->sigma[p->edges[e].second];
+      ed[e] = {d, s};
+      te[e] = {s, d};
+    }
+    std::sort(ed.begin(), ed.end());
+    std::sort(te.begin(), te.end());
+    p->csr_ptr.assign(n + 1, 0);
+    p->tcsr_ptr.assign(n + 1, 0);
+    p->csr_src.resize(n_e);
+    p->tcsr_dst.resize(n_e);
+    for (int32_t e = 0; e < n_e; ++e) {
+      ++p->csr_ptr[ed[e].first + 1];
+      p->csr_src[e] = ed[e].second;
+      ++p->tcsr_ptr[te[e].first + 1];
+      p->tcsr_dst[e] = te[e].second;
+    }
+    for (int32_t v = 0; v < n; ++v) {
+      p->csr_ptr[v + 1] += p->csr_ptr[v];
+      p->tcsr_ptr[v + 1] += p->tcsr_ptr[v];
+    }
+  }
+  // ---- row placement: inputs read the caller's sources, outputs write the caller's
+  // out buffer, everything else lives in the workspace (U rows and adjoint rows)
+  p->nodes.assign(n, NodeDev{});
+  p->node_ext.assign(n, int4_{0, 0, 0, 0});
+  int64_t src_off = 0, out_off = 0, int_off = 0;
+  std::vector<int32_t> inv(n);
+  for (int32_t v = 0; v < n; ++v) inv[p->sigma[v]] = v;
+  p->src_graph_off.assign(p->n_graphs, -1);
+  p->out_graph_off.assign(p->n_graphs, -1);
+  for (int32_t vn = 0; vn < n; ++vn) {
+    int32_t vo = inv[vn];
+    int32_t g = p->node_graph[vo];
+    NodeDev& nd = p->nodes[vn];
+    nd.len = int32_t(p->L[g]);
+    nd.pitch = int32_t(p->pitch[g]);
+    nd.prow = p->param_row[vn];
+    nd.type = int16_t(p->types[vo]);
+    int64_t row = 2 * p->pitch[g];
+    if (nd.type == GRAFX_T_IN) {
+      nd.kind = KIND_INPUT;
+      nd.off_y = nd.off_a = src_off;
+      src_off += row;
+    } else if (nd.type == GRAFX_T_OUT) {
+      nd.kind = KIND_OUTPUT;
+      nd.off_y = nd.off_a = out_off;
+      out_off += row;
+      p->outputs_new.push_back(vn);
+    } else {
+      nd.kind = KIND_INTERNAL;
+      nd.off_y = nd.off_a = int_off;
+      int_off += int64_t(align_up(size_t(row), 64));
+      p->node_samples += nd.len;
+    }
+    if (nd.type == GRAFX_T_OUT) p->node_samples += nd.len;
+  }
+  // inputs and outputs are ordered graph-major because sigma keeps original order
+  // inside a step and the union concatenates graphs in order
+  p->src_elems = src_off;
+  p->out_elems = out_off;
+  const int64_t internal_floats = int_off;
+
+  // ---- tile sizes
+  p->eq_taps = opts.eq_taps;
+  p->eq_H = (opts.eq_taps - 1) / 2;
+  p->eq_fft = opts.eq_fft ? opts.eq_fft : pick_eq_fft(opts.eq_taps);
+  if (p->eq_fft != 1024 && p->eq_fft != 2048 && p->eq_fft != 4096 && p->eq_fft != 8192)
+    return fail(GRAFX_EINVAL, "eq_fft must be 1024, 2048, 4096 or 8192");
+  const int32_t Hal = (p->eq_H + 3) & ~3;
+  p->eq_step = (p->eq_fft - 2 * p->eq_H) & ~3;
+  if (p->eq_step < 256) return fail(GRAFX_EINVAL, "eq_fft too small for eq_taps");
+  p->comp_chunk = opts.comp_chunk ? opts.comp_chunk : 2048;
+  if (p->comp_chunk != 1024 && p->comp_chunk != 2048)
+    return fail(GRAFX_EINVAL, "comp_chunk must be 1024 or 2048");
+
+  // ---- work lists: forward items of every step, then backward items of every step
+  p->steps.assign(N + 1, StepInfo{});
+  std::vector<int4_> fwd, bwd;
+  int32_t slot = 0, run = 0, chunk_id = 0;
+  for (int32_t k = 1; k <= N; ++k) {
+    StepInfo& s = p->steps[k];
+    s.type = p->sched.string[k];
+    s.node_begin = p->step_ptr[k];
+    s.node_end = p->step_ptr[k + 1];
+    s.fitem_begin = int32_t(fwd.size());
+    for (int32_t v = s.node_begin; v < s.node_end; ++v) {
+      const int32_t L = p->nodes[v].len;
+      switch (s.type) {
+        case GRAFX_T_EQ: {
+          p->node_ext[v].z = p->n_eq++;
+          int32_t nb = int32_t((int64_t(L) + Hal - p->eq_H + p->eq_step - 1) / p->eq_step);
+          for (int32_t j = 0; j < nb; ++j) fwd.push_back({v, j, p->node_ext[v].z, 0});
+          break;
+        }
+        case GRAFX_T_COMP: {
+          int32_t nc = (L + p->comp_chunk - 1) / p->comp_chunk;
+          p->node_ext[v].z = chunk_id;
+          for (int32_t c = 0; c < nc; ++c) fwd.push_back({v, c, chunk_id + c, 0});
+          chunk_id += nc;
+          break;
+        }
+        default:
+          for (int32_t t0 = 0; t0 < L; t0 += EW_TILE) fwd.push_back({v, t0, 0, 0});
+      }
+    }
+    s.fitem_count = int32_t(fwd.size()) - s.fitem_begin;
+  }
+  for (int32_t k = N; k >= 1; --k) {
+    StepInfo& s = p->steps[k];
+    s.bitem_begin = int32_t(bwd.size());
+    if (s.type == GRAFX_T_OUT) { s.bitem_count = 0; continue; }  // adjoint rows alias d_out
+    // EQ: runs of consecutive blocks, sized for about two waves of resident CTAs
+    int32_t run_len = 1;
+    if (s.type == GRAFX_T_EQ) {
+      int64_t blocks = 0;
+      for (int32_t v = s.node_begin; v < s.node_end; ++v)
+        blocks += (int64_t(p->nodes[v].len) + Hal - p->eq_H + p->eq_step - 1) / p->eq_step;
+      const int64_t target = 148 * 3 * 2;
+      run_len = int32_t(std::max<int64_t>(1, (blocks + target - 1) / target));
+    }
+    for (int32_t v = s.node_begin; v < s.node_end; ++v) {
+      const int32_t L = p->nodes[v].len;
+      switch (s.type) {
+        case GRAFX_T_EQ: {
+          int32_t nb = int32_t((int64_t(L) + Hal - p->eq_H + p->eq_step - 1) / p->eq_step);
+          p->node_ext[v].x = run;
+          for (int32_t j = 0; j < nb; j += run_len) bwd.push_back({v, j, std::min(run_len, nb - j), run++});
+          p->node_ext[v].y = run - p->node_ext[v].x;
+          break;
+        }
+        case GRAFX_T_COMP: {
+          int32_t nc = (L + p->comp_chunk - 1) / p->comp_chunk;
+          p->node_ext[v].x = slot;
+          p->node_ext[v].y = nc;
+          for (int32_t c = nc - 1; c >= 0; --c) bwd.push_back({v, c, p->node_ext[v].z + c, slot++});
+          break;
+        }
+        default: {
+          bool has_p = s.type == GRAFX_T_GAIN || s.type == GRAFX_T_IMAGER;
+          p->node_ext[v].x = slot;
+          int32_t cnt = 0;
+          for (int32_t t0 = 0; t0 < L; t0 += EW_TILE, ++cnt) bwd.push_back({v, t0, 0, has_p ? slot++ : -1});
+          p->node_ext[v].y = has_p ? cnt : 0;
+        }
+      }
+    }
+    s.bitem_count = int32_t(bwd.size()) - s.bitem_begin;
+  }
+  // input step (adjoints of the sources), after the others in the backward list
+  p->in_bitem_begin = int32_t(bwd.size());
+  for (int32_t v = 0; v < p->step_ptr[1]; ++v)
+    for (int32_t t0 = 0; t0 < p->nodes[v].len; t0 += EW_TILE) bwd.push_back({v, t0, 0, -1});
+  p->in_bitem_count = int32_t(bwd.size()) - p->in_bitem_begin;
+  p->n_partials = slot;
+  p->n_eq_runs = run;
+  p->n_comp_chunks = chunk_id;
+  p->n_fitems = int32_t(fwd.size());
+  for (int32_t k = 1; k <= N; ++k) p->steps[k].bitem_begin += p->n_fitems;
+  p->in_bitem_begin += p->n_fitems;
+  p->items = fwd;
+  p->items.insert(p->items.end(), bwd.begin(), bwd.end());
+
+  // ---- constant tables (double precision on the host, stored as float)
+  p->twiddle.resize(TWIDDLE_N);
+  for (int m = 0; m < TWIDDLE_N; ++m) {
+    double a = 2.0 * M_PI * m / TWIDDLE_N;
+    p->twiddle[m] = float2_{float(std::cos(a)), float(-std::sin(a))};
+  }
+  {
+    const int Nt = p->eq_taps, H = p->eq_H;
+    p->eq_cos.resize(Nt);
+    for (int j = 0; j < Nt; ++j) p->eq_cos[j] = float(std::cos(2.0 * M_PI * j / Nt));
+    p->eq_hann.resize(H + 1);
+    for (int j = 0; j <= H; ++j) p->eq_hann[j] = float(0.5 * (1.0 + std::cos(2.0 * M_PI * j / (Nt + 1))));
+    eq_band_table(Nt, opts.sample_rate, &p->eq_band);
+  }
+
+  // ---- loss plan over the output rows
+  {
+    const int Ms[N_RES] = {512, 1024, 2048};
+    int64_t foff = 0;
+    int32_t groups = 0;
+    p->loss.ok = true;
+    for (int32_t j = 0; j < int32_t(p->outputs_new.size()); ++j) {
+      const NodeDev& nd = p->nodes[p->outputs_new[j]];
+      LossRow r{};
+      r.off = nd.off_y;
+      r.len = nd.len;
+      r.pitch = nd.pitch;
+      if (nd.len < 2048) p->loss.ok = false;
+      for (int q = 0; q < N_RES; ++q) {
+        int M = Ms[q], hop = M / 4;
+        int32_t F = nd.len >= M ? 1 + (nd.len - M) / hop : 0;
+        r.n_frames[q] = F;
+        r.frame_off[q] = foff;
+        foff += int64_t(F) * 2 * M;
+        r.group_off[q] = groups;
+        r.n_groups[q] = (F + LOSS_FRAMES_PER_ITEM - 1) / LOSS_FRAMES_PER_ITEM;
+        for (int32_t f = 0; f < F; f += LOSS_FRAMES_PER_ITEM) p->loss.items[q].push_back({j, f});
+        groups += r.n_groups[q];
+      }
+      p->loss.rows.push_back(r);
+    }
+    p->loss.frame_floats = foff;
+    p->loss.n_groups_total = groups;
+  }
+
+  // ---- workspace layout (every region 256-byte aligned)
+  {
+    WsLayout& w = p->ws;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+    w.nodes = take(sizeof(NodeDev) * n);
+    w.node_ext = take(sizeof(int4_) * n);
+    w.csr_ptr = take(4 * size_t(n + 1));
+    w.csr_src = take(4 * size_t(std::max(n_e, 1)));
+    w.tcsr_ptr = take(4 * size_t(n + 1));
+    w.tcsr_dst = take(4 * size_t(std::max(n_e, 1)));
+    w.items = take(sizeof(int4_) * std::max<size_t>(p->items.size(), 1));
+    w.twiddle = take(sizeof(float2_) * TWIDDLE_N);
+    w.eq_cos = take(4 * p->eq_cos.size());
+    w.eq_hann = take(4 * p->eq_hann.size());
+    w.eq_band = take(4 * p->eq_band.size());
+    size_t nrow = std::max<size_t>(p->loss.rows.size(), 1);
+    w.loss_rows = take(sizeof(LossRow) * nrow);
+    w.loss_items = take(sizeof(int2_) * std::max<size_t>(p->loss.items[0].size() + p->loss.items[1].size() + p->loss.items[2].size(), 1));
+    w.tables_end = o;
+    // cleared at the start of every render / backprop
+    w.status = take(16);
+    w.tickets = take(4 * size_t(2 * (N + 2)));
+    w.flags = take(8 * std::max<size_t>(p->items.size(), 1));
+    w.flags_bytes = o - w.status;
+    w.eq_spec = take(4 * size_t(std::max(p->n_eq, 1)) * (p->eq_fft / 2 + 1));
+    w.comp_carry = take(4 * size_t(std::max(p->n_comp_chunks, 1)));
+    w.partial = take(16 * size_t(std::max(p->n_partials, 1)));
+    w.eq_partial = take(8 * size_t(std::max(p->n_eq_runs, 1)) * (p->eq_fft / 2 + 1));
+    w.loss_part = take(32 * size_t(std::max(p->loss.n_groups_total, 1)));
+    w.loss_stats = take(32 * nrow * N_RES);
+    w.loss_frames = take(4 * size_t(std::max<int64_t>(p->loss.frame_floats, 1)));
+    w.U = take(4 * size_t(std::max<int64_t>(internal_floats, 1)));
+    w.A = take(4 * size_t(std::max<int64_t>(internal_floats, 1)));
+    w.total = o;
+  }
+  return GRAFX_OK;
+}
+
+}  // namespace grafx

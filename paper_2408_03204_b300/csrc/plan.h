@@ -1,0 +1,108 @@
+// Host-side plan: the render data of Algorithm 1 (schedule, reordering, index maps)
+// plus the device work lists and workspace layout for the sm_103a kernels.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/grafx.h"
+#include "devtypes.h"
+
+struct grafx_graph {
+  std::vector<int32_t> types;
+  std::vector<std::pair<int32_t, int32_t>> edges;
+};
+
+namespace grafx {
+
+// status helpers (thread-local last error)
+int fail(int code, const std::string& msg);
+void clear_error();
+const char* last_error_cstr();
+
+struct Schedule {
+  std::vector<int32_t> string;              // type string t_0..t_N
+  std::vector<std::vector<int32_t>> steps;  // V_0..V_N, original ids ascending
+};
+
+// Graph rules of Sec. 2 "Definitions"; returns GRAFX_OK or an error code (message set).
+int validate(const std::vector<int32_t>& types, const std::vector<std::pair<int32_t, int32_t>>& edges);
+// Type schedules of Sec. 2 "Type scheduling".
+int make_schedule(const std::vector<int32_t>& types, const std::vector<std::pair<int32_t, int32_t>>& edges,
+                  int method, int beam_width, int n_threads, Schedule* out);
+
+struct StepInfo {
+  int32_t type;
+  int32_t node_begin, node_end;    // new ids [begin, end)
+  int32_t fitem_begin, fitem_count;  // forward work items (global index)
+  int32_t bitem_begin, bitem_count;  // backward work items (global index)
+};
+
+// Byte offsets of the regions inside the caller's workspace.
+struct WsLayout {
+  size_t nodes, node_ext, csr_ptr, csr_src, tcsr_ptr, tcsr_dst, items;
+  size_t twiddle, eq_cos, eq_hann, eq_band;
+  size_t loss_rows, loss_items;
+  size_t tables_end;                           // [0, tables_end) is uploaded at bind time
+  size_t status, tickets, flags, flags_bytes;  // flags_bytes covers status+tickets+flags (cleared per call)
+  size_t eq_spec, comp_carry, partial, eq_partial;
+  size_t loss_part, loss_stats, loss_frames;
+  size_t U, A;
+  size_t total;
+};
+
+struct LossPlan {
+  // per output row j
+  std::vector<LossRow> rows;
+  // work items per resolution (row, first frame)
+  std::vector<int2_> items[3];
+  int64_t frame_floats = 0;  // total floats in the frame buffer
+  int32_t n_groups_total = 0;
+  bool ok = false;           // every output row is long enough (>= 2048 samples)
+};
+
+struct Plan {
+  grafx_plan_opts opts;
+  int32_t n_graphs = 0;
+  std::vector<int64_t> L, pitch;         // per graph
+  std::vector<int32_t> types;            // union, original ids
+  std::vector<std::pair<int32_t, int32_t>> edges;
+  std::vector<int32_t> node_graph;       // original id -> graph
+  Schedule sched;
+  std::vector<int32_t> step_ptr, sigma, csr_ptr, csr_src, tcsr_ptr, tcsr_dst, param_row;
+  std::vector<int32_t> new_types;
+  std::vector<NodeDev> nodes;            // new ids
+  // per node: x = first partial slot (gain/imager/compressor) or first EQ run,
+  // y = number of slots / runs, z = EQ spectrum index or first compressor chunk id
+  std::vector<int4_> node_ext;
+  std::vector<StepInfo> steps;           // index 1..N (steps[0] unused: inputs)
+  std::vector<int4_> items;              // all work items, forward lists then backward lists
+  int32_t n_type_rows[GRAFX_N_TYPES] = {0};
+  int32_t n_eq = 0, n_comp_chunks = 0, n_partials = 0, n_eq_runs = 0;
+  int32_t n_fitems = 0, in_bitem_begin = 0, in_bitem_count = 0;
+  int32_t eq_taps = 1023, eq_H = 511, eq_fft = 4096, eq_step = 0;  // eq_step: outputs per block
+  int32_t comp_chunk = 2048;
+  int64_t src_elems = 0, out_elems = 0, node_samples = 0;
+  std::vector<int64_t> src_graph_off, out_graph_off;
+  std::vector<int32_t> outputs_new;      // new ids of output rows in order
+  LossPlan loss;
+  WsLayout ws;
+  // host tables
+  std::vector<float2_> twiddle;
+  std::vector<float> eq_cos, eq_hann, eq_band;
+  // bindings
+  char* dev_ws = nullptr;
+  const float* params[GRAFX_N_TYPES] = {nullptr};
+  int64_t param_rows[GRAFX_N_TYPES] = {0};
+  int32_t last_launches = 0;
+};
+
+int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* lengths,
+               const grafx_plan_opts& opts, Plan* p);
+
+inline int64_t pitch_of(int64_t L) { return (L + 3) & ~int64_t(3); }
+
+}  // namespace grafx
+
+struct grafx_plan : public grafx::Plan {};

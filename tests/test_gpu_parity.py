@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle on the same
+seeded inputs.  Outputs within 1e-5 at full scale; parameter and source gradients
+within 1e-3 relative (floor 1e-2 of the tensor's largest entry)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import render as orr, loss as ol
+from tests.gpu_common import (GpuRun, assert_grad_close, assert_out_close, flat_sources, split_rows,
+                              union_params, per_graph_params)
+
+pytestmark = pytest.mark.gpu
+
+I, O, M, G, S, E, C = 0, 1, 2, 3, 4, 5, 6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2408_03204_b300 import build
+    build.build()
+
+
+def single_node_graph(t, fan_in=1):
+    g = synth.Graph()
+    ins = [g.add(I) for _ in range(fan_in)]
+    v = g.add(t)
+    o = g.add(O)
+    for i in ins:
+        g.connect(i, v)
+    g.connect(v, o)
+    return g
+
+
+def run_case(graphs, lengths, seed=11, eq_taps=63, linear_loss=True, **kw):
+    src_flat, src_per = flat_sources(graphs, lengths, [seed + k for k in range(len(graphs))])
+    P = union_params(graphs, seed)
+    run = GpuRun(graphs, lengths, P, src_flat, eq_taps=eq_taps, **kw)
+    out = run.render().cpu().numpy()
+    hp = dict(eq_taps=eq_taps)
+    got_rows = split_rows(out, graphs, lengths)
+    Pg = per_graph_params(graphs, P)
+    for g, L, src, p, got in zip(graphs, lengths, src_per, Pg, got_rows):
+        want = orr.outputs_of(g.types, orr.render_one_by_one(g.types, g.edges, src[:, :, :L], p, hp))
+        assert_out_close(got, want)
+    return run, P, src_per, out
+
+
+@pytest.mark.parametrize("t", [M, G, S, E, C])
+@pytest.mark.parametrize("L", [4096, 5003, 2 ** 14 + 2])
+def test_single_processor_fwd_bwd(t, L):
+    g = single_node_graph(t, fan_in=2)
+    run, P, src_per, out = run_case([g], [L])
+    rng = np.random.Generator(np.random.PCG64(L + t))
+    Pd = (L + 3) // 4 * 4
+    W = np.zeros((1, 2, Pd), np.float32)
+    W[:, :, :L] = rng.standard_normal((1, 2, L)).astype(np.float32)
+    dP, dS = run.backprop(W.reshape(-1))
+    wP, wS = orr.backward(g.types, g.edges, src_per[0][:, :, :L], P, W[:, :, :L], dict(eq_taps=63))
+    for tt in P:
+        assert_grad_close(dP[tt], wP[tt], what=f"type {tt}")
+    assert_grad_close(dS.reshape(-1, 2, Pd)[:, :, :L], wS, what="sources")
+
+
+@pytest.mark.parametrize("taps", [255, 1023])
+def test_eq_long_filters(taps):
+    g = single_node_graph(E)
+    run, P, src_per, _ = run_case([g], [20000], eq_taps=taps)
+    L, Pd = 20000, 20000
+    W = np.random.Generator(np.random.PCG64(9)).standard_normal((1, 2, L)).astype(np.float32)
+    dP, dS = run.backprop(W.reshape(-1))
+    wP, wS = orr.backward(g.types, g.edges, src_per[0], P, W, dict(eq_taps=taps))
+    assert_grad_close(dP[E], wP[E], what="eq bands")
+    assert_grad_close(dS.reshape(-1, 2, Pd), wS, what="sources")
+
+
+def test_cfg1_forward_full_size():
+    """8 tracks i->g->e(255)->c, 2 buses, master; 2^15 samples."""
+    run_case([synth.console_cfg1()], [2 ** 15], seed=1, eq_taps=255)
+
+
+def test_compressor_long_chunks_and_extreme_alpha():
+    g = single_node_graph(C)
+    L = 2 ** 17 + 8
+    src_flat, src_per = flat_sources([g], [L], [5])
+    for alpha in (0.9, 0.9999):
+        P = {C: np.array([[alpha, np.log(0.005), 0.6908, 6.0]], np.float32)}
+        run = GpuRun([g], [L], P, src_flat)
+        got = run.render().cpu().numpy().reshape(1, 2, L)
+        want = orr.outputs_of(g.types, orr.render_one_by_one(g.types, g.edges, src_per[0], P))
+        assert_out_close(got, want)
+        W = np.random.Generator(np.random.PCG64(3)).standard_normal((1, 2, L)).astype(np.float32)
+        dP, _ = run.backprop(W.reshape(-1), want_sources=False)
+        wP, _ = orr.backward(g.types, g.edges, src_per[0], P, W)
+        assert_grad_close(dP[C], wP[C], what=f"comp alpha={alpha}")
+
+
+def test_random_graphs_fwd_bwd():
+    from tests.helpers import random_dag
+    rng = np.random.Generator(np.random.PCG64(21))
+    for k in range(4):
+        g = random_dag(rng, n_inputs=3, n_mid=10, n_outputs=2, kinds=(M, G, S, E, C))
+        L = int(rng.integers(3000, 9000))
+        run, P, src_per, out = run_case([g], [L], seed=100 + k)
+        Pd = (L + 3) // 4 * 4
+        W = np.zeros((2, 2, Pd), np.float32)
+        W[:, :, :L] = rng.standard_normal((2, 2, L)).astype(np.float32)
+        dP, dS = run.backprop(W.reshape(-1))
+        wP, wS = orr.backward(g.types, g.edges, src_per[0][:, :, :L], P, W[:, :, :L], dict(eq_taps=63))
+        for t in P:
+            assert_grad_close(dP[t], wP[t], what=f"type {t}")
+        assert_grad_close(dS.reshape(-1, 2, Pd)[:, :, :L], wS, what="sources")
+
+
+def test_batched_equals_single_and_deterministic():
+    rng = np.random.Generator(np.random.PCG64(8))
+    graphs = [synth.random_console(rng, budget_lo=16, budget_hi=48, kinds=(G, S, E, C)) for _ in range(5)]
+    lengths = [int(rng.integers(4000, 12000)) for _ in graphs]
+    src_flat, _ = flat_sources(graphs, lengths, list(range(5)))
+    P = union_params(graphs, 4)
+    batched = GpuRun(graphs, lengths, P, src_flat, eq_taps=63)
+    ob = batched.render().cpu().numpy()
+    ob2 = batched.render().cpu().numpy()
+    assert np.array_equal(ob, ob2), "render is not deterministic"
+    rows_b = split_rows(ob, graphs, lengths)
+    off_s = 0
+    Pg = per_graph_params(graphs, P)
+    for g, L, p, rb in zip(graphs, lengths, Pg, rows_b):
+        n = g.count(I) * 2 * ((L + 3) // 4 * 4)
+        single = GpuRun([g], [L], p, src_flat[off_s:off_s + n], eq_taps=63)
+        off_s += n
+        rs = split_rows(single.render().cpu().numpy(), [g], [L])[0]
+        # identical per-node arithmetic; only the summation order of fan-in >= 3 may differ
+        assert_out_close(rb, rs, tol=1e-6)
+
+
+def test_schedule_methods_agree():
+    g = synth.console_cfg2(tracks=12, levels=2)
+    L = 6000
+    src_flat, _ = flat_sources([g], [L], [2])
+    P = union_params([g], 5)
+    outs = [GpuRun([g], [L], P, src_flat, eq_taps=63, schedule=m).render().cpu().numpy()
+            for m in ("beam", "greedy", "one_by_one")]
+    for o in outs[1:]:
+        assert_out_close(o, outs[0], tol=1e-6)
+
+
+def test_mrstft_loss_and_grad():
+    import torch
+    import paper_2408_03204_b300 as gx
+    g = single_node_graph(M)
+    L = 3 * 4096 + 7
+    Pd = (L + 3) // 4 * 4
+    rng = np.random.Generator(np.random.PCG64(17))
+    y = np.zeros((1, 2, Pd), np.float32)
+    t = np.zeros((1, 2, Pd), np.float32)
+    y[:, :, :L] = 0.3 * rng.standard_normal((1, 2, L))
+    t[:, :, :L] = 0.3 * rng.standard_normal((1, 2, L))
+    plan = gx.Plan([gx.Graph.from_lists(g.types, g.edges)], [L]).bind_workspace("cuda")
+    yd = torch.tensor(y.reshape(-1), device="cuda")
+    td = torch.tensor(t.reshape(-1), device="cuda")
+    loss = torch.empty(1, device="cuda")
+    st = gx._stream(torch, yd.device)
+    plan.loss_raw(yd, td, loss, st)
+    d = torch.empty_like(yd)
+    plan.loss_backward_raw(yd, td, d, st)
+    plan.sync_status()
+    want = ol.mrstft(y[:, :, :L].astype(np.float64), t[:, :, :L].astype(np.float64))
+    assert abs(loss.item() - want) <= 1e-4 * abs(want), (loss.item(), want)
+    wg = ol.mrstft_grad(y[:, :, :L].astype(np.float64), t[:, :, :L].astype(np.float64))
+    gd = d.cpu().numpy().reshape(1, 2, Pd)
+    assert np.all(gd[:, :, L:] == 0)
+    assert_grad_close(gd[:, :, :L], wg, what="dloss/dy")
+
+
+def test_cfg2_fwd_bwd_mrstft_reduced_length():
+    """The 64-track nested console with the full chain and the STFT loss against a
+    target rendered (by the oracle) from hidden parameters, at 2^15 samples."""
+    g = synth.console_cfg2()
+    L = 2 ** 15
+    src_flat, src_per = flat_sources([g], [L], [2])
+    P = union_params([g], 2)
+    Ph = union_params([g], 102)
+    hp = dict(eq_taps=1023)
+    target = orr.outputs_of(g.types, orr.render_one_by_one(g.types, g.edges, src_per[0], Ph, hp))
+    y_ref = orr.outputs_of(g.types, orr.render_one_by_one(g.types, g.edges, src_per[0], P, hp))
+    run = GpuRun([g], [L], P, src_flat, eq_taps=1023)
+    import torch
+    out = run.render()
+    assert_out_close(out.cpu().numpy().reshape(1, 2, L), y_ref)
+    tgt = torch.tensor(target.astype(np.float32).reshape(-1), device="cuda")
+    loss = torch.empty(1, device="cuda")
+    st = run.gx._stream(torch, out.device)
+    run.plan.loss_raw(out, tgt, loss, st)
+    d_out = torch.empty_like(out)
+    run.plan.loss_backward_raw(out, tgt, d_out, st)
+    dP, _ = run.backprop(d_out, want_sources=False)
+    want_loss = ol.mrstft(y_ref, target)
+    assert abs(loss.item() - want_loss) <= 1e-4 * abs(want_loss)
+    dY = ol.mrstft_grad(y_ref, target)
+    wP, _ = orr.backward(g.types, g.edges, src_per[0], P, dY, hp)
+    for t in P:
+        assert_grad_close(dP[t], wP[t], what=f"type {t}")

@@ -1,0 +1,127 @@
+"""Host side of the C-ABI library, no GPU: it loads, exports every symbol declared in
+include/grafx.h, and its schedules and index maps (Algorithm 1 lines 1-4) equal the
+oracle's bit for bit."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import graph as og
+from tests.helpers import random_dag
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def gx():
+    from paper_2408_03204_b300 import build
+    build.build()
+    import paper_2408_03204_b300 as gx
+    gx.lib()
+    return gx
+
+
+def test_exports_every_declared_symbol(gx):
+    header = open(os.path.join(ROOT, "include", "grafx.h")).read()
+    header = re.sub(r"/\*.*?\*/", "", header, flags=re.S)
+    declared = set(re.findall(r"\b(grafx_[a-z_]+)\s*\(", header))
+    assert len(declared) >= 20
+    lib = gx.lib()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(gx.SIGNATURES), declared ^ set(gx.SIGNATURES)
+
+
+def _to_gx(gx, g):
+    return gx.Graph.from_lists(g.types, g.edges)
+
+
+def _compare(gx, graphs, method, width=32, lengths=None):
+    lengths = lengths or [1024] * len(graphs)
+    plan = gx.Plan([_to_gx(gx, g) for g in graphs], lengths, schedule=method, beam_width=width, eq_taps=31)
+    got = plan.export()
+    types, edges, _ = og.union(graphs)
+    s, steps = og.schedule(types, edges, method, width)
+    want = og.index_maps(types, edges, steps)
+    assert got["type_string"] == list(s)
+    for k in ("step_ptr", "sigma", "csr_ptr", "csr_src", "tcsr_ptr", "tcsr_dst", "param_row"):
+        assert got[k] == list(want[k]), k
+    return plan
+
+
+@pytest.mark.parametrize("method", ["beam", "greedy", "optimal", "one_by_one"])
+@pytest.mark.parametrize("seed", range(12))
+def test_schedule_and_maps_bit_exact_random(gx, method, seed):
+    rng = np.random.Generator(np.random.PCG64(1000 + seed))
+    g = random_dag(rng, n_inputs=int(rng.integers(1, 4)), n_mid=int(rng.integers(2, 10)),
+                   n_outputs=int(rng.integers(1, 3)))
+    _compare(gx, [g], method)
+
+
+@pytest.mark.parametrize("width", [1, 2, 4, 32])
+def test_beam_widths_bit_exact(gx, width):
+    rng = np.random.Generator(np.random.PCG64(77))
+    for _ in range(5):
+        _compare(gx, [random_dag(rng, n_mid=14)], "beam", width)
+
+
+def test_consoles_bit_exact(gx):
+    p = _compare(gx, [synth.console_cfg1()], "beam")
+    assert p.info.n_steps == 5
+    _compare(gx, [synth.console_cfg2()], "beam")
+    _compare(gx, [synth.console_cfg2()], "greedy")
+
+
+def test_batched_union_bit_exact(gx):
+    rng = np.random.Generator(np.random.PCG64(3))
+    graphs = [synth.random_console(rng, budget_lo=16, budget_hi=64, kinds=(3, 4, 5, 6))
+              for _ in range(12)]
+    lengths = [int(rng.integers(3000, 9000)) for _ in graphs]
+    p = _compare(gx, graphs, "beam", lengths=lengths)
+    assert p.info.n_graphs == 12
+    assert p.info.src_elems == sum(g.count(0) * 2 * ((L + 3) // 4 * 4) for g, L in zip(graphs, lengths))
+
+
+def test_error_codes_match_oracle(gx):
+    I, O, M, G = 0, 1, 2, 3
+    cases = [([I, G, G, O], [(0, 1), (1, 2), (2, 1), (2, 3)], "ECYCLE"),
+             ([I, G, O], [(1, 0), (0, 1), (1, 2)], "EINVAL"),
+             ([I, G, G, O], [(0, 1), (1, 3)], "EINVAL"),
+             ([I, O, G], [(0, 1), (1, 2)], "EINVAL"),
+             ([I, G], [(0, 1)], "EINVAL")]
+    for types, edges, code in cases:
+        with pytest.raises(og.GraphError) as e:
+            og.validate(types, edges)
+        assert e.value.code == code
+        with pytest.raises(gx.GrafxError) as e2:
+            gx.Plan([gx.Graph.from_lists(types, edges)], [4096])
+        assert e2.value.name == code
+    g = gx.Graph()
+    with pytest.raises(gx.GrafxError) as e3:
+        g.add(42)
+    assert e3.value.name == "ETYPE"
+
+
+def test_bad_options_rejected(gx):
+    g = _to_gx(gx, synth.console_cfg1())
+    for kw in (dict(eq_taps=1024), dict(eq_taps=1), dict(eq_fft=3000), dict(comp_chunk=777)):
+        with pytest.raises(gx.GrafxError):
+            gx.Plan([g], [4096], **kw)
+    with pytest.raises(gx.GrafxError):
+        gx.Plan([g], [0])
+
+
+def test_optimal_size_limit(gx):
+    rng = np.random.Generator(np.random.PCG64(5))
+    g = random_dag(rng, n_mid=40)
+    with pytest.raises(gx.GrafxError):
+        gx.Plan([_to_gx(gx, g)], [4096], schedule="optimal")
+
+
+def test_workspace_requires_binding(gx):
+    p = gx.Plan([_to_gx(gx, synth.console_cfg1())], [4096])
+    with pytest.raises(gx.GrafxError) as e:
+        p.render_raw(None, None, None)
+    assert e.value.name == "EINVAL"
