@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Forward+backward render throughput of a nested 64-track mixing console.
+
+Workload (one "step" = one pass of the whole hot path over one synthetic batch):
+64 stereo tracks i -> g -> e(1023 taps) -> c -> s -> g, nested into 4 subgroup
+levels of mix nodes with fan-in U{2..8}, one master output; 2^17 samples at
+44.1 kHz; render, multi-resolution STFT loss (512/1024/2048, hop 1/4) against a
+target rendered from hidden parameters, the loss gradient, and the backward pass
+through every processor to every parameter.  Metric: processed node-samples per
+second (non-input nodes x samples, forward+backward).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  Under torchrun every rank renders its own replica
+(the single-graph path does not shard; graphs are independent units), the
+barrier + max-over-ranks time gives the whole-job rate.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L_FULL = 2 ** 17
+EQ_TAPS = 1023
+METRIC = "fwd+bwd graph-render node-samples/s"
+UNIT = "node-samples/s"
+CONFIG = {"workload": "nested 64-track console, chain g-e(1023)-c-s-g, 4 subgroup levels, "
+                      "2^17 stereo samples, fwd+bwd with multi-resolution STFT loss",
+          "tracks": 64, "subgroup_levels": 4, "samples": L_FULL, "eq_taps": EQ_TAPS,
+          "sample_rate": 44100, "schedule": "beam-32",
+          "l2": "working set (U + adjoint rows, ~850 MB) larger than L2; no flush"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    return ap.parse_args()
+
+
+def workload():
+    import synth
+    g = synth.console_cfg2()
+    return g
+
+
+def algorithmic_bytes(g, string, steps_nodes, L):
+    """Per schedule step: forward bytes 8*(indeg+1) per node-sample; backward bytes
+    8*outdeg (consumer adjoints) + 8*indeg (re-gathered input, only for processors
+    whose adjoint needs it) + 8 (input-adjoint write).  Output nodes alias dL/dY."""
+    n = g.n_nodes
+    indeg = [0] * n
+    outdeg = [0] * n
+    for s, d in g.edges:
+        indeg[d] += 1
+        outdeg[s] += 1
+    fwd, bwd = {}, {}
+    for k in range(1, len(string)):
+        t = string[k]
+        fb = bb = 0
+        for v in steps_nodes[k]:
+            fb += 8 * (indeg[v] + 1) * L
+            if t == 1:  # output: its adjoint row is d_out itself
+                continue
+            needs_u = t not in (1, 2)
+            bb += (8 * outdeg[v] + (8 * indeg[v] if needs_u else 0) + 8) * L
+        fwd[k], bwd[k] = fb, bb
+    return fwd, bwd
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.rows = []
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "100", "-i", str(index)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        self.t0 = time.time()
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def traffic_for(kernel_key):
+    """ncu DRAM bytes per launch recorded in profiles/dram_traffic.json, if the kernel
+    source has not changed since (sha1 of the .cu file)."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f).get(kernel_key)
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_2408_03204_b300", "csrc", d["source"])
+    h = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    return d["bytes_per_launch"] if h == d["sha1"] else None
+
+
+def cpu_baseline(L=L_FULL, steps=1):
+    """The FP64 oracle as it stands: one fwd+bwd step (render, loss, loss gradient,
+    backward) of the same console at full length, on this host."""
+    import numpy as np
+    import synth
+    from oracle import render as orr, loss as ol
+    g = workload()
+    src = synth.sources(2, g.count(synth.I), L)
+    P = synth.random_params(g, 2)
+    Ph = synth.random_params(g, 102)
+    hp = dict(eq_taps=EQ_TAPS)
+    tgt = orr.outputs_of(g.types, orr.render_one_by_one(g.types, g.edges, src, Ph, hp))
+    t0 = time.time()
+    for _ in range(steps):
+        Y = orr.outputs_of(g.types, orr.render_one_by_one(g.types, g.edges, src, P, hp))
+        ol.mrstft(Y, tgt)
+        dY = ol.mrstft_grad(Y, tgt)
+        orr.backward(g.types, g.edges, src, P, dY, hp)
+    dt = time.time() - t0
+    ns = sum(1 for t in g.types if t != synth.I) * L * steps
+    return {"value": ns / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} fwd+bwd step(s) of the same console at {L} samples "
+                      f"({dt:.1f} s; numpy/scipy FP64, single-threaded)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    L = 2 ** 13
+    cpu_baseline(L=2 ** 11, steps=1)                 # untimed warm-up (imports, caches)
+    cb = cpu_baseline(L=L, steps=max(1, args.steps))
+    val = cb["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(CONFIG, sample_samples=L),
+            "cpu_baseline": dict(cb, value=val),
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import synth
+    from paper_2408_03204_b300 import build
+    build.build()
+    import paper_2408_03204_b300 as gx
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    g = workload()
+    L = L_FULL
+    plan = gx.Plan([gx.Graph.from_lists(g.types, g.edges)], [L], eq_taps=EQ_TAPS)
+    plan.bind_workspace(dev)
+    info = plan.info
+    exp = plan.export()
+    string = exp["type_string"]
+    sp = exp["step_ptr"]
+    inv = [0] * g.n_nodes
+    for v, nv in enumerate(exp["sigma"]):
+        inv[nv] = v
+    steps_nodes = [[inv[x] for x in range(sp[k], sp[k + 1])] for k in range(len(string))]
+    fwd_b, bwd_b = algorithmic_bytes(g, string, steps_nodes, L)
+
+    src_h = synth.sources(2 + rank, g.count(synth.I), L).reshape(-1)
+    P_h = synth.random_params(g, 2)
+    Ph_h = synth.random_params(g, 102)
+    src = torch.tensor(src_h, device=dev)
+    P = {t: torch.tensor(v, device=dev) for t, v in P_h.items()}
+    Ph = {t: torch.tensor(v, device=dev) for t, v in Ph_h.items()}
+    stream = torch.cuda.current_stream(dev)
+    st = gx._stream(torch, dev)
+    out = torch.empty(info.out_elems, device=dev)
+    tgt = torch.empty_like(out)
+    plan.bind_params(Ph)
+    plan.render_raw(src, tgt, st)            # target from hidden parameters (input generation)
+    plan.bind_params(P)
+    loss = torch.empty(1, device=dev)
+    d_out = torch.empty_like(out)
+    dP = {t: torch.empty_like(p) for t, p in P.items()}
+    N = len(string) - 1
+
+    def step(evs=None):
+        i = 0
+        for k in range(1, N + 1):
+            plan.render_steps_raw(src, out, k, k + 1, st)
+            if evs is not None:
+                evs[i].record(stream); i += 1
+        plan.loss_raw(out, tgt, loss, st)
+        plan.loss_backward_raw(out, tgt, d_out, st)
+        if evs is not None:
+            evs[i].record(stream); i += 1
+        for k in range(N, 0, -1):
+            plan.backprop_steps_raw(src, d_out, dP, None, k, k + 1, st)
+            if evs is not None:
+                evs[i].record(stream); i += 1
+
+    def launches_per_step():
+        n = 0
+        for k in range(1, N + 1):
+            plan.render_steps_raw(src, out, k, k + 1, st)
+            n += plan.last_launches()
+        plan.loss_raw(out, tgt, loss, st)
+        n += plan.last_launches()
+        plan.loss_backward_raw(out, tgt, d_out, st)
+        n += plan.last_launches()
+        for k in range(N, 0, -1):
+            plan.backprop_steps_raw(src, d_out, dP, None, k, k + 1, st)
+            n += plan.last_launches()
+        return n
+
+    n_launch = launches_per_step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    plan.sync_status(st)
+
+    n_ev = N + 1 + N
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_start.record(stream)
+    for it in range(args.steps):
+        e0[it].record(stream)
+        step(evs[it])
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    plan.sync_status(st)
+    ms_total = t_start.elapsed_time(t_end)
+    if dist:
+        tt = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    node_samples = int(info.node_samples)
+    value = node_samples * world * args.steps / (ms_total / 1e3)
+
+    # per schedule-step durations (fwd k = 1..N, loss, bwd k = N..1)
+    labels = [f"fwd:{synth.TYPE_LETTERS[string[k]]}{k}" for k in range(1, N + 1)] + ["loss"] + \
+             [f"bwd:{synth.TYPE_LETTERS[string[k]]}{k}" for k in range(N, 0, -1)]
+    dur = np.zeros(n_ev)
+    for it in range(args.steps):
+        prev = e0[it]
+        for j in range(n_ev):
+            dur[j] += prev.elapsed_time(evs[it][j])
+            prev = evs[it][j]
+    dur /= args.steps
+    algo = [fwd_b[k] for k in range(1, N + 1)] + [0] + [bwd_b[k] for k in range(N, 0, -1)]
+    j = int(np.argmax(dur))
+    peak, peak_kind = peaks()
+    achieved = algo[j] / (dur[j] / 1e3) / 1e9
+    kernel_key = labels[j]
+    step_bytes = sum(algo)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic_for(kernel_key), "kernel": kernel_key,
+                "peak_source": peak_kind, "ms_per_launch": dur[j],
+                "algorithmic_bytes_per_launch": algo[j],
+                "step": {"algorithmic_bytes": step_bytes, "achieved": step_bytes / (ms_step / 1e3) / 1e9,
+                         "frac": step_bytes / (ms_step / 1e3) / 1e9 / peak},
+                "breakdown_ms": {lab: round(float(d), 4) for lab, d in zip(labels, dur)}}
+
+    # end to end through the C-ABI with host buffers: H2D of the step's inputs from pinned
+    # memory, the step, D2H of the loss and every parameter gradient
+    src_pin = torch.tensor(src_h).pin_memory()
+    tgt_pin = tgt.cpu().pin_memory()
+    P_pin = {t: v.cpu().pin_memory() for t, v in P.items()}
+    loss_pin = torch.empty(1).pin_memory()
+    dP_pin = {t: torch.empty(v.shape).pin_memory() for t, v in P.items()}
+    h2d = src_pin.numel() * 4 + tgt_pin.numel() * 4 + sum(v.numel() * 4 for v in P_pin.values())
+    d2h = 4 + sum(v.numel() * 4 for v in dP_pin.values())
+
+    def e2e_step():
+        src.copy_(src_pin, non_blocking=True)
+        tgt.copy_(tgt_pin, non_blocking=True)
+        for t in P:
+            P[t].copy_(P_pin[t], non_blocking=True)
+        step()
+        loss_pin.copy_(loss, non_blocking=True)
+        for t in dP:
+            dP_pin[t].copy_(dP[t], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    a.record(stream)
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_e2e = a.elapsed_time(b)
+    if dist:
+        tt = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_e2e = float(tt.item())
+    e2e = {"value": node_samples * world * args.e2e_steps / (ms_e2e / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e / args.e2e_steps,
+           "loss": float(loss_pin.item())}
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(CONFIG, nodes=int(info.n_nodes), processed_node_samples=node_samples,
+                               schedule_steps=N, parallelism=f"replicas{world}"),
+                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": n_launch * args.steps}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

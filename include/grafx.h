@@ -179,6 +179,17 @@ int grafx_render(grafx_plan* p, const float* sources, float* out, void* stream);
 int grafx_backprop(grafx_plan* p, const float* sources, const float* d_out,
                    float* const* d_params, float* d_sources, void* stream);
 
+/* Run only the schedule steps k in [first, last) of the render (1 <= first <= last <= N+1),
+ * in order; grafx_render is first = 1, last = N+1.  Used to time or re-run individual
+ * steps (Algorithm 1 iterations). */
+int grafx_render_steps(grafx_plan* p, const float* sources, float* out, int32_t first, int32_t last,
+                       void* stream);
+/* Backward over the steps k in [first, last) in reverse order (0 <= first <= last <= N+1);
+ * k = 0 stands for the source adjoints (written only if d_sources is not NULL).
+ * grafx_backprop is first = 0, last = N+1. */
+int grafx_backprop_steps(grafx_plan* p, const float* sources, const float* d_out, float* const* d_params,
+                         float* d_sources, int32_t first, int32_t last, void* stream);
+
 /* ---------------------------------------------------------------- loss
  * Multi-resolution STFT magnitude loss between the output rows and a target laid
  * out like `out` (the paper fits a rendered mix to a target, Sec. 4 Example usage;

@@ -69,6 +69,8 @@ SIGNATURES = {
     "grafx_bind_params": (ctypes.c_int, [_P, _I32, _F, _I64, _I64]),
     "grafx_render": (ctypes.c_int, [_P, _F, _F, _P]),
     "grafx_backprop": (ctypes.c_int, [_P, _F, _F, ctypes.POINTER(_P), _F, _P]),
+    "grafx_render_steps": (ctypes.c_int, [_P, _F, _F, _I32, _I32, _P]),
+    "grafx_backprop_steps": (ctypes.c_int, [_P, _F, _F, ctypes.POINTER(_P), _F, _I32, _I32, _P]),
     "grafx_mrstft_forward": (ctypes.c_int, [_P, _F, _F, _F, _P]),
     "grafx_mrstft_backward": (ctypes.c_int, [_P, _F, _F, _F, _P]),
     "grafx_sync_status": (ctypes.c_int, [_P, _P]),
@@ -210,6 +212,14 @@ class Plan:
     def backprop_raw(self, sources, d_out, d_params, d_sources, stream):
         arr = (_P * N_TYPES)(*[_ptr(d_params.get(t)) for t in range(N_TYPES)])
         _check(lib().grafx_backprop(self._h, _ptr(sources), _ptr(d_out), arr, _ptr(d_sources), stream))
+
+    def render_steps_raw(self, sources, out, first, last, stream):
+        _check(lib().grafx_render_steps(self._h, _ptr(sources), _ptr(out), int(first), int(last), stream))
+
+    def backprop_steps_raw(self, sources, d_out, d_params, d_sources, first, last, stream):
+        arr = (_P * N_TYPES)(*[_ptr(d_params.get(t)) for t in range(N_TYPES)])
+        _check(lib().grafx_backprop_steps(self._h, _ptr(sources), _ptr(d_out), arr, _ptr(d_sources),
+                                          int(first), int(last), stream))
 
     def loss_raw(self, out, target, loss, stream):
         _check(lib().grafx_mrstft_forward(self._h, _ptr(out), _ptr(target), _ptr(loss), stream))

@@ -80,8 +80,10 @@ int param_cols(int t) {
   }
 }
 
-void clear_flags(const Plan* p, cudaStream_t s) {
-  cudaMemsetAsync(p->dev_ws + p->ws.tickets, 0, p->ws.eq_spec - p->ws.tickets, s);
+// Look-back flags of the items [item0, item0+n) and the step's ticket counter start at 0.
+void clear_step_flags(const Plan* p, int item0, int n, int ticket, cudaStream_t s) {
+  cudaMemsetAsync(p->dev_ws + p->ws.flags + size_t(item0) * 8, 0, size_t(n) * 8, s);
+  cudaMemsetAsync(p->dev_ws + p->ws.tickets + size_t(ticket) * 4, 0, 4, s);
 }
 
 LossLaunch make_loss(const Plan* p, const float* y, const float* tgt) {
@@ -291,16 +293,17 @@ int grafx_bind_params(grafx_plan* p, int32_t type, const float* dev, int64_t row
   return GRAFX_OK;
 }
 
-int grafx_render(grafx_plan* p, const float* sources, float* out, void* stream) {
+int grafx_render_steps(grafx_plan* p, const float* sources, float* out, int32_t first, int32_t last,
+                       void* stream) {
   if (!p || !sources || !out) return fail(GRAFX_EINVAL, "null argument");
   int rc = check_ready(p);
   if (rc) return rc;
+  const int N = int(p->sched.string.size()) - 1;
+  if (first < 1 || last > N + 1 || first > last) return fail(GRAFX_EINVAL, "step range out of bounds");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DevCtx c = make_ctx(p, sources, out, nullptr, nullptr);
   int launches = 0;
-  clear_flags(p, s);
-  const int N = int(p->sched.string.size()) - 1;
-  for (int k = 1; k <= N; ++k) {
+  for (int k = first; k < last; ++k) {
     const StepInfo& st = p->steps[k];
     c.params = p->params[st.type];
     switch (st.type) {
@@ -309,6 +312,7 @@ int grafx_render(grafx_plan* p, const float* sources, float* out, void* stream) 
         launches += launch_eq(1, c, st.fitem_begin, st.fitem_count, s);
         break;
       case GRAFX_T_COMP:
+        clear_step_flags(p, st.fitem_begin, st.fitem_count, 2 * k, s);
         launches += launch_comp(0, c, st.fitem_begin, st.fitem_count, 2 * k, s);
         break;
       default:
@@ -319,17 +323,22 @@ int grafx_render(grafx_plan* p, const float* sources, float* out, void* stream) 
   return cuda_check(cudaGetLastError(), "render launch");
 }
 
-int grafx_backprop(grafx_plan* p, const float* sources, const float* d_out, float* const* d_params,
-                   float* d_sources, void* stream) {
+int grafx_render(grafx_plan* p, const float* sources, float* out, void* stream) {
+  if (!p) return fail(GRAFX_EINVAL, "null argument");
+  return grafx_render_steps(p, sources, out, 1, int32_t(p->sched.string.size()), stream);
+}
+
+int grafx_backprop_steps(grafx_plan* p, const float* sources, const float* d_out, float* const* d_params,
+                         float* d_sources, int32_t first, int32_t last, void* stream) {
   if (!p || !sources || !d_out) return fail(GRAFX_EINVAL, "null argument");
   int rc = check_ready(p);
   if (rc) return rc;
+  const int N = int(p->sched.string.size()) - 1;
+  if (first < 0 || last > N + 1 || first > last) return fail(GRAFX_EINVAL, "step range out of bounds");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DevCtx c = make_ctx(p, sources, nullptr, d_out, d_sources);
   int launches = 0;
-  clear_flags(p, s);
-  const int N = int(p->sched.string.size()) - 1;
-  for (int k = N; k >= 1; --k) {
+  for (int k = last - 1; k >= std::max(first, 1); --k) {
     const StepInfo& st = p->steps[k];
     if (st.type == GRAFX_T_OUT) continue;  // adjoint rows of outputs are d_out itself
     c.params = p->params[st.type];
@@ -340,6 +349,7 @@ int grafx_backprop(grafx_plan* p, const float* sources, const float* d_out, floa
         if (c.dparams) launches += launch_eq(3, c, st.node_begin, st.node_end, s);
         break;
       case GRAFX_T_COMP:
+        clear_step_flags(p, st.bitem_begin, st.bitem_count, 2 * k + 1, s);
         launches += launch_comp(1, c, st.bitem_begin, st.bitem_count, 2 * k + 1, s);
         if (c.dparams) launches += launch_comp(2, c, st.node_begin, st.node_end, 0, s);
         break;
@@ -352,9 +362,15 @@ int grafx_backprop(grafx_plan* p, const float* sources, const float* d_out, floa
         launches += launch_ew_bwd(GRAFX_T_MIX, c, st.bitem_begin, st.bitem_count, s);
     }
   }
-  if (d_sources) launches += launch_ew_bwd(GRAFX_T_MIX, c, p->in_bitem_begin, p->in_bitem_count, s);
+  if (first == 0 && d_sources) launches += launch_ew_bwd(GRAFX_T_MIX, c, p->in_bitem_begin, p->in_bitem_count, s);
   p->last_launches = launches;
   return cuda_check(cudaGetLastError(), "backprop launch");
+}
+
+int grafx_backprop(grafx_plan* p, const float* sources, const float* d_out, float* const* d_params,
+                   float* d_sources, void* stream) {
+  if (!p) return fail(GRAFX_EINVAL, "null argument");
+  return grafx_backprop_steps(p, sources, d_out, d_params, d_sources, 0, int32_t(p->sched.string.size()), stream);
 }
 
 int grafx_mrstft_forward(grafx_plan* p, const float* out, const float* target, float* loss, void* stream) {

@@ -1,10 +1,12 @@
 """Seeded synthetic stereo source tracks (the stand-in for multitrack stems).
 
 Each track is pink noise (white Gaussian shaped by 1/sqrt(f) in the rFFT domain),
-independent per channel, multiplied by a sum of note envelopes: onsets are a
-Poisson process at 2 notes/s, each note has amplitude U(0.3, 1) and decays as
-exp(-t/tau) with tau ~ U(0.05, 1.0) s.  Each track is scaled to a peak of
-0.5/sqrt(K) for K tracks so that mixes stay near full scale.
+independent per channel, multiplied by an envelope: a constant bed of 0.05
+(about -26 dB below a unit note; recorded stems carry room tone and bleed, so
+they are never digitally silent) plus a sum of notes with Poisson onsets at
+2 notes/s, amplitude U(0.3, 1) and decay exp(-t/tau), tau ~ U(0.05, 1.0) s.
+Each track is scaled to a peak of 0.5/sqrt(K) for K tracks so that mixes stay
+near full scale.
 """
 import numpy as np
 
@@ -19,8 +21,11 @@ def _pink(rng, n):
     return np.fft.irfft(spec, n)
 
 
+NOISE_BED = 0.05
+
+
 def _envelope(rng, n, fs):
-    env = np.zeros(n)
+    env = np.full(n, NOISE_BED)
     dur = n / fs
     n_notes = max(1, int(rng.poisson(2.0 * dur)))
     t = np.arange(n) / fs

