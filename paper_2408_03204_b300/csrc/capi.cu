@@ -43,6 +43,8 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
   c.tickets = at<int32_t>(p, p->ws.tickets);
   c.flags = at<unsigned long long>(p, p->ws.flags);
   c.eq_spec = at<float>(p, p->ws.eq_spec);
+  c.eq_aux = at<float>(p, p->ws.eq_aux);
+  c.eq_bandpart = at<float>(p, p->ws.eq_bandpart);
   c.comp_carry = at<float>(p, p->ws.comp_carry);
   c.partial = at<float4>(p, p->ws.partial);
   c.eq_partial = at<float2>(p, p->ws.eq_partial);
@@ -90,13 +92,9 @@ LossLaunch make_loss(const Plan* p, const float* y, const float* tgt) {
   LossLaunch L;
   std::memset(&L, 0, sizeof(L));
   L.rows = at<const LossRow>(p, p->ws.loss_rows);
-  const int2_* items = at<const int2_>(p, p->ws.loss_items);
-  size_t off = 0;
-  for (int q = 0; q < N_RES; ++q) {
-    L.items[q] = items + off;
-    L.n_items[q] = int(p->loss.items[q].size());
-    off += p->loss.items[q].size();
-  }
+  L.items = at<const int4_>(p, p->ws.loss_items);
+  L.n_items = int(p->loss.items.size());
+  L.row_loss = at<float>(p, p->ws.loss_rowloss);
   L.y = y;
   L.tgt = tgt;
   L.part = at<float4>(p, p->ws.loss_part);
@@ -265,11 +263,7 @@ int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* s
   put(p->ws.eq_hann, p->eq_hann.data(), p->eq_hann.size() * 4);
   put(p->ws.eq_band, p->eq_band.data(), p->eq_band.size() * 4);
   put(p->ws.loss_rows, p->loss.rows.data(), p->loss.rows.size() * sizeof(LossRow));
-  size_t off = p->ws.loss_items;
-  for (int q = 0; q < N_RES; ++q) {
-    put(off, p->loss.items[q].data(), p->loss.items[q].size() * sizeof(int2_));
-    off += p->loss.items[q].size() * sizeof(int2_);
-  }
+  put(p->ws.loss_items, p->loss.items.data(), p->loss.items.size() * sizeof(int4_));
   int rc = cuda_check(cudaMemcpyAsync(dev_ws, img.data(), img.size(), cudaMemcpyHostToDevice, s), "upload tables");
   if (rc) return rc;
   rc = cuda_check(cudaMemsetAsync(static_cast<char*>(dev_ws) + p->ws.status, 0, 16, s), "clear status");

@@ -27,6 +27,8 @@ struct DevCtx {
   int32_t* tickets;
   unsigned long long* flags;
   float* eq_spec;
+  float* eq_aux;       // per EQ node: 1024 floats (taps in the forward, gradient fold in the backward)
+  float* eq_bandpart;  // per EQ node: chunk partials of the band gradient (16 x 8 floats)
   float* comp_carry;
   float4* partial;
   float2* eq_partial;

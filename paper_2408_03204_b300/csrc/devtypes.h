@@ -37,7 +37,6 @@ struct alignas(16) LossRow {
 constexpr int TWIDDLE_N = 8192;   // twiddle table size: exp(-2 pi i m / 8192)
 constexpr int EW_TILE = 4096;     // samples per elementwise work item
 constexpr int N_RES = 3;          // loss resolutions 512, 1024, 2048
-constexpr int LOSS_FRAMES_PER_ITEM = 8;
 
 // status bits written by kernels
 constexpr uint32_t ST_TIMEOUT = 1u;

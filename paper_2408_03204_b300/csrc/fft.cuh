@@ -135,6 +135,7 @@ template <int M> struct Geo {
   static constexpr int T = M / 16;  // threads per transform
   static constexpr int n16 = (M >= 65536) ? 4 : (M >= 4096) ? 3 : (M >= 256) ? 2 : 1;
   static constexpr int last = M / (n16 == 3 ? 4096 : n16 == 2 ? 256 : 16);  // radix of the final pass (1 = none)
+  static constexpr int npass = n16 + (last > 1 ? 1 : 0);
 };
 
 // Phase 1 of a pass: read the butterfly inputs of thread `tid`.
@@ -172,6 +173,28 @@ GX_HD void pass_store(float2* buf, const float2_* tw, int tid, int Ns, float2 (*
   }
 }
 
+// Twiddle + DFT_R of the butterflies of thread `tid` in the pass that has merged Ns
+// points, without storing; results stay in v[b][r] (output position
+// (j - k) R + k + r Ns for butterfly j = tid + b T, k = j mod Ns).
+template <int M, int R>
+GX_HD void pass_compute(const float2_* tw, int tid, int Ns, float2 (*v)[R]) {
+  constexpr int T = M / 16, BPT = 16 / R;
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) {
+    int j = tid + b * T;
+    int k = j & (Ns - 1);
+    if (Ns > 1) {
+      int step = k * (TWIDDLE_N / (Ns * R));
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2_ w = tw[r * step];
+        v[b][r] = cmul(v[b][r], make_float2(w.x, w.y));
+      }
+    }
+    Dft<R>::run(v[b]);
+  }
+}
+
 #ifdef __CUDACC__
 // Full forward transform of one M-point padded buffer by threads tid in [0, M/16).
 // Every thread of the CTA must call it (it contains __syncthreads); threads with
@@ -195,6 +218,62 @@ __device__ __forceinline__ void forward(float2* buf, const float2_* __restrict__
     __syncthreads();
     if (active) pass_store<M, R>(buf, tw, tid, Ns, v);
     __syncthreads();
+  }
+}
+
+// Forward transform with the data in registers on both ends: on entry thread tid holds
+// x[tid + T m] in v[m] (m < 16, T = M/16); on exit it holds X[tid + T m].  Stockham's
+// first pass reads exactly that layout and its last pass writes it, so only the inner
+// passes go through shared memory, alternating between b0 and b1 (one barrier per
+// pass).  The caller guarantees that no thread still reads b0 when this is entered;
+// on exit other threads may still read b1 (or b0 when the pass count is odd).
+template <int M>
+__device__ __forceinline__ void forward_regs(float2 (&v)[16], float2* b0, float2* b1,
+                                             const float2_* __restrict__ tw, int tid) {
+  constexpr int n16 = Geo<M>::n16, last = Geo<M>::last;
+  constexpr int npass = n16 + (last > 1 ? 1 : 0);
+  float2* bufs[2] = {b0, b1};
+  // pass 1: radix 16, Ns = 1, from registers
+  {
+    float2(*w)[16] = reinterpret_cast<float2(*)[16]>(v);
+    Dft<16>::run(w[0]);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) b0[pad(tid * 16 + r)] = v[r];
+  }
+  __syncthreads();
+  int Ns = 16;
+  int cur = 0;
+#pragma unroll
+  for (int p = 1; p < npass; ++p) {
+    const bool is_last = (p == npass - 1);
+    const int R = (is_last && last > 1) ? last : 16;
+    if (R == 16) {
+      float2 w[1][16];
+      pass_load<M, 16>(bufs[cur], tid, w);
+      pass_compute<M, 16>(tw, tid, Ns, w);
+      if (is_last) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = w[0][r];
+      } else {
+        const int j = tid, k = j & (Ns - 1), out = (j - k) * 16 + k;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) bufs[cur ^ 1][pad(out + r * Ns)] = w[0][r];
+      }
+    } else if constexpr (last > 1 && last < 16) {
+      constexpr int RL = last, BPT = 16 / RL;
+      float2 w[BPT][RL];
+      pass_load<M, RL>(bufs[cur], tid, w);
+      pass_compute<M, RL>(tw, tid, Ns, w);
+#pragma unroll
+      for (int b = 0; b < BPT; ++b)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) v[b + r * BPT] = w[b][r];
+    }
+    if (!is_last) {
+      __syncthreads();
+      cur ^= 1;
+      Ns *= 16;
+    }
   }
 }
 #endif

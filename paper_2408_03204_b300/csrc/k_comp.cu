@@ -352,7 +352,7 @@ int launch_comp(int what, const DevCtx& c, int a, int b, int ticket, cudaStream_
     return 1;
   }
   if (b <= 0) return 0;
-  int g = grid_size(b, 4);
+  int g = grid_size(b, what == 0 ? 8 : 3);
   if (c.comp_chunk == 1024) {
     if (what == 0) k_comp_fwd<4><<<g, 256, 0, s>>>(c, a, b, ticket);
     else k_comp_bwd<4><<<g, 256, 0, s>>>(c, a, b, ticket);

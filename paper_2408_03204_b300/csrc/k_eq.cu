@@ -41,28 +41,39 @@ __device__ void eq_magnitudes(const DevCtx& c, const NodeDev& nd, float* A, int 
   }
 }
 
-template <int M>
-__global__ void __launch_bounds__(M / 16) k_eq_design(DevCtx c, int node_begin) {
-  extern __shared__ float2 smem2[];
-  float2* buf = smem2;                                     // Padded<M>
-  float* A = reinterpret_cast<float*>(buf + fft::Padded<M>::size);  // K floats
-  float* h = A + 1024;                                     // H+1 floats
+constexpr int EQ_CHUNK = 64;  // taps (or bins) per CTA of the cosine-sum kernels
+
+// h[n] = Hann[n] (A_0 + 2 sum_{k>=1} A_k cos(2 pi k n / N)) / N for one chunk of n in
+// [0, H] (the taps are even, h[-n] = h[n]); grid (EQ nodes of the step, chunks).
+__global__ void __launch_bounds__(EQ_CHUNK) k_eq_taps(DevCtx c, int node_begin) {
+  __shared__ float A[1024];
+  __shared__ float cs[2048];
   const int v = node_begin + blockIdx.x;
   const NodeDev nd = c.nodes[v];
   const int N = c.eq_taps, H = c.eq_H, K = (N + 1) / 2;
   eq_magnitudes(c, nd, A, K);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) cs[i] = c.eq_cos[i];
   __syncthreads();
-  for (int n = threadIdx.x; n <= H; n += blockDim.x) {
-    float s = 0.f;
-    int idx = 0;                       // (k * n) mod N
-    for (int k = 1; k < K; ++k) {
-      idx += n;
-      if (idx >= N) idx -= N;
-      s += A[k] * c.eq_cos[idx];
-    }
-    h[n] = c.eq_hann[n] * (A[0] + 2.f * s) / float(N);
+  const int n = blockIdx.y * EQ_CHUNK + threadIdx.x;
+  if (n > H) return;
+  float s = 0.f;
+  int idx = 0;  // (k n) mod N
+  for (int k = 1; k < K; ++k) {
+    idx += n;
+    if (idx >= N) idx -= N;
+    s += A[k] * cs[idx];
   }
-  __syncthreads();
+  c.eq_aux[size_t(c.ext[v].z) * 1024 + n] = c.eq_hann[n] * (A[0] + 2.f * s) / float(N);
+}
+
+// The block spectrum of h placed circularly (real, even), scaled by 1/M.
+template <int M>
+__global__ void __launch_bounds__(M / 16) k_eq_spec(DevCtx c, int node_begin) {
+  extern __shared__ float2 smem2[];
+  float2* buf = smem2;
+  const int v = node_begin + blockIdx.x;
+  const int H = c.eq_H;
+  const float* h = c.eq_aux + size_t(c.ext[v].z) * 1024;
   const float inv_m = 1.f / float(M);
   for (int m = threadIdx.x; m < M; m += blockDim.x) {
     int a = m <= M / 2 ? m : M - m;    // circular position -> |tap index|
@@ -74,62 +85,69 @@ __global__ void __launch_bounds__(M / 16) k_eq_design(DevCtx c, int node_begin) 
   for (int k = threadIdx.x; k <= M / 2; k += blockDim.x) spec[k] = buf[fft::pad(k)].x;
 }
 
-// Load the packed window [ws, ws+M) of u (gathered) or of ybar (gathered over the
-// consumers), zero outside [0, len).  With `centre`, samples outside the block's
-// output range [ws+H, ws+H+S) are zeroed too.
+// Thread tid's share of the packed window [ws, ws+M): v[m] = (l, r) at p = tid + T m,
+// gathered over the in-edges (u) or over the consumers' adjoints (ybar); zero outside
+// [0, len) and, with `centre`, outside the block's output range [H, H+S).
 template <int M, bool ADJ>
-__device__ __forceinline__ void eq_load(const DevCtx& c, int v, const NodeDev& nd, int ws, float2* buf,
-                                        bool centre, int H, int S) {
-  for (int q = threadIdx.x; q < M / 4; q += blockDim.x) {
-    const int t = ws + 4 * q;
-    float4 l = f4zero(), r = f4zero();
-    if (t >= 0 && t < nd.len) {
-      if (ADJ) {
-        l = gather_out_adj(c, v, 0, t, nd.len, nd.pitch);
-        r = gather_out_adj(c, v, 1, t, nd.len, nd.pitch);
-      } else {
-        l = gather_in(c, v, 0, t, nd.len, nd.pitch);
-        r = gather_in(c, v, 1, t, nd.len, nd.pitch);
+__device__ __forceinline__ void eq_load_regs(const DevCtx& c, int v, const NodeDev& nd, int ws, float2 (&x)[16],
+                                             bool centre, int H, int S) {
+  constexpr int T = M / 16;
+#pragma unroll
+  for (int m = 0; m < 16; ++m) x[m] = make_float2(0.f, 0.f);
+  const int e0 = ADJ ? c.tcsr_ptr[v] : c.csr_ptr[v];
+  const int e1 = ADJ ? c.tcsr_ptr[v + 1] : c.csr_ptr[v + 1];
+  for (int e = e0; e < e1; ++e) {
+    const NodeDev s = c.nodes[ADJ ? c.tcsr_dst[e] : c.csr_src[e]];
+    const float* row = ADJ ? arow(c, s) : yrow(c, s);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int p = threadIdx.x + T * m;
+      const int t = ws + p;
+      const bool in = t >= 0 && t < nd.len && (!centre || (p >= H && p < H + S));
+      if (in) {
+        x[m].x += row[t];
+        x[m].y += row[nd.pitch + t];
       }
     }
-    float lv[4] = {l.x, l.y, l.z, l.w}, rv[4] = {r.x, r.y, r.z, r.w};
+  }
+}
+
+// conj(X[k] * Hspec[k]) for the thread's bins k = tid + T m (the conjugation makes the
+// next forward transform an inverse; Hspec is real, even and scaled by 1/M).
+template <int M>
+__device__ __forceinline__ void eq_apply_regs(float2 (&x)[16], const float* spec) {
+  constexpr int T = M / 16;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      int p = 4 * q + i;
-      bool keep = !centre || (p >= H && p < H + S);
-      buf[fft::pad(p)] = keep ? make_float2(lv[i], rv[i]) : make_float2(0.f, 0.f);
+  for (int m = 0; m < 16; ++m) {
+    const int k = threadIdx.x + T * m;
+    const float hk = __ldg(spec + (k <= M / 2 ? k : M - k));
+    x[m] = make_float2(x[m].x * hk, -x[m].y * hk);
+  }
+}
+
+// Write the block's valid outputs p in [H, H+S) from the (conjugated) inverse result.
+template <int M>
+__device__ __forceinline__ void eq_store_regs(float* row, const NodeDev& nd, int ws, const float2 (&x)[16], int H,
+                                              int S) {
+  constexpr int T = M / 16;
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int p = threadIdx.x + T * m;
+    const int t = ws + p;
+    if (p >= H && p < H + S && t >= 0 && t < nd.pitch) {
+      const bool in = t < nd.len;
+      row[t] = in ? x[m].x : 0.f;
+      row[nd.pitch + t] = in ? -x[m].y : 0.f;
     }
   }
 }
 
-// conj(Z[k] * Hspec[k]) in place (the conjugation turns the next forward FFT into
-// an inverse; Hspec is real, even, and already scaled by 1/M).
 template <int M>
-__device__ __forceinline__ void eq_apply(float2* buf, const float* spec) {
-  for (int k = threadIdx.x; k < M; k += blockDim.x) {
-    float hk = spec[k <= M / 2 ? k : M - k];
-    float2 z = buf[fft::pad(k)];
-    buf[fft::pad(k)] = make_float2(z.x * hk, -z.y * hk);
-  }
-}
-
-// Write the S valid outputs of the block (conj of the inverse result), zero padding.
-template <int M>
-__device__ __forceinline__ void eq_store(float* row, const NodeDev& nd, int ws, const float2* buf, int H, int S) {
-  for (int p = H + threadIdx.x; p < H + S; p += blockDim.x) {
-    const int t = ws + p;
-    if (t < 0 || t >= nd.pitch) continue;
-    float2 z = buf[fft::pad(p)];
-    bool in = t < nd.len;
-    row[t] = in ? z.x : 0.f;
-    row[nd.pitch + t] = in ? -z.y : 0.f;
-  }
-}
-
-template <int M>
-__global__ void __launch_bounds__(M / 16) k_eq_fwd(DevCtx c, int item0, int n_items) {
+__global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_fwd(DevCtx c, int item0, int n_items) {
   extern __shared__ float2 smem2[];
-  float2* buf = smem2;
+  float2* b0 = smem2;
+  float2* b1 = smem2 + fft::Padded<M>::size;
+  constexpr bool even = fft::Geo<M>::npass % 2 == 0;
   const int H = c.eq_H, S = c.eq_step, Hal = c.eq_Hal;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
@@ -137,88 +155,85 @@ __global__ void __launch_bounds__(M / 16) k_eq_fwd(DevCtx c, int item0, int n_it
     const NodeDev nd = c.nodes[v];
     const int ws = -Hal + w.y * S;
     const float* spec = c.eq_spec + size_t(w.z) * (M / 2 + 1);
-    eq_load<M, false>(c, v, nd, ws, buf, false, H, S);
-    __syncthreads();
-    fft::forward<M>(buf, c.tw, threadIdx.x, true);
-    eq_apply<M>(buf, spec);
-    __syncthreads();
-    fft::forward<M>(buf, c.tw, threadIdx.x, true);
-    eq_store<M>(yrow_w(c, nd), nd, ws, buf, H, S);
-    __syncthreads();
+    float2 x[16];
+    eq_load_regs<M, false>(c, v, nd, ws, x, false, H, S);
+    if (even) __syncthreads();
+    fft::forward_regs<M>(x, b0, b1, c.tw, threadIdx.x);
+    eq_apply_regs<M>(x, spec);
+    if (even) __syncthreads();
+    fft::forward_regs<M>(x, b0, b1, c.tw, threadIdx.x);
+    eq_store_regs<M>(yrow_w(c, nd), nd, ws, x, H, S);
   }
 }
 
 template <int M>
-__global__ void __launch_bounds__(M / 16) k_eq_bwd(DevCtx c, int item0, int n_items) {
+__global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_bwd(DevCtx c, int item0, int n_items) {
   extern __shared__ float2 smem2[];
-  float2* by = smem2;                            // ybar window -> its spectrum
-  float2* bx = smem2 + fft::Padded<M>::size;     // centred u -> spectrum; then ubar
   constexpr int T = M / 16;
-  constexpr int NK = (M / 2 + 1 + T - 1) / T;    // accumulator bins per thread
+  constexpr bool even = fft::Geo<M>::npass % 2 == 0;
+  float2* b0 = smem2;
+  float2* b1 = smem2 + fft::Padded<M>::size;
+  float2* X = smem2 + 2 * fft::Padded<M>::size;   // spectrum of the centred input
+  float2* Y = even ? b1 : b0;                      // spectrum of ybar (free after the FFT)
+  float2* i0 = even ? b0 : b1;                     // ping-pong of the inverse transform
+  float2* i1 = even ? b1 : b0;
   const int H = c.eq_H, S = c.eq_step, Hal = c.eq_Hal;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
     const int v = w.x;
     const NodeDev nd = c.nodes[v];
     const float* spec = c.eq_spec + size_t(c.ext[v].z) * (M / 2 + 1);
-    float2 acc[NK];
+    float2 acc[16];
 #pragma unroll
-    for (int i = 0; i < NK; ++i) acc[i] = make_float2(0.f, 0.f);
+    for (int m = 0; m < 16; ++m) acc[m] = make_float2(0.f, 0.f);
     for (int j = w.y; j < w.y + w.z; ++j) {
       const int ws = -Hal + j * S;
-      eq_load<M, true>(c, v, nd, ws, by, false, H, S);
-      eq_load<M, false>(c, v, nd, ws, bx, true, H, S);
-      __syncthreads();
-      fft::forward<M>(by, c.tw, threadIdx.x, true);
-      fft::forward<M>(bx, c.tw, threadIdx.x, true);
-      // sum_x Ybar_x[k] conj(U_x[k]) from the packed spectra
+      float2 x[16];
+      eq_load_regs<M, false>(c, v, nd, ws, x, true, H, S);
+      __syncthreads();  // previous block's readers of b0/b1/X are done
+      fft::forward_regs<M>(x, b0, b1, c.tw, threadIdx.x);
 #pragma unroll
-      for (int i = 0; i < NK; ++i) {
-        int k = threadIdx.x + i * T;
-        if (k <= M / 2) {
-          int km = (M - k) & (M - 1);
-          float2 a = by[fft::pad(k)], b = bx[fft::pad(k)];
-          float2 a2 = by[fft::pad(km)], b2 = bx[fft::pad(km)];
-          // a conj(b) + conj(a2) b2
-          float re = a.x * b.x + a.y * b.y + a2.x * b2.x + a2.y * b2.y;
-          float im = a.y * b.x - a.x * b.y + a2.x * b2.y - a2.y * b2.x;
-          acc[i].x += 0.5f * re;
-          acc[i].y += 0.5f * im;
-        }
+      for (int m = 0; m < 16; ++m) X[fft::pad(threadIdx.x + T * m)] = x[m];
+      eq_load_regs<M, true>(c, v, nd, ws, x, false, H, S);
+      if (even) __syncthreads();
+      fft::forward_regs<M>(x, b0, b1, c.tw, threadIdx.x);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) Y[fft::pad(threadIdx.x + T * m)] = x[m];
+      __syncthreads();
+      // sum over channels of Ybar[k] conj(U[k]) from the packed spectra:
+      // (Zy[k] conj(Zx[k]) + conj(Zy[M-k]) Zx[M-k]) / 2
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int k = threadIdx.x + T * m;
+        const int km = (M - k) & (M - 1);
+        const float2 a = x[m], b = X[fft::pad(k)];
+        const float2 a2 = Y[fft::pad(km)], b2 = X[fft::pad(km)];
+        acc[m].x += 0.5f * (a.x * b.x + a.y * b.y + a2.x * b2.x + a2.y * b2.y);
+        acc[m].y += 0.5f * (a.y * b.x - a.x * b.y + a2.x * b2.y - a2.y * b2.x);
       }
-      __syncthreads();
-      // input adjoint: conj(Ybar * H) -> forward FFT -> conj
-      for (int k = threadIdx.x; k < M; k += blockDim.x) {
-        float hk = spec[k <= M / 2 ? k : M - k];
-        float2 z = by[fft::pad(k)];
-        bx[fft::pad(k)] = make_float2(z.x * hk, -z.y * hk);
-      }
-      __syncthreads();
-      fft::forward<M>(bx, c.tw, threadIdx.x, true);
-      eq_store<M>(arow_w(c, nd), nd, ws, bx, H, S);
-      __syncthreads();
+      // input adjoint: the centred convolution of ybar with the even filter
+      eq_apply_regs<M>(x, spec);
+      fft::forward_regs<M>(x, i0, i1, c.tw, threadIdx.x);
+      eq_store_regs<M>(arow_w(c, nd), nd, ws, x, H, S);
     }
     float2* out = c.eq_partial + size_t(w.w) * (M / 2 + 1);
 #pragma unroll
-    for (int i = 0; i < NK; ++i) {
-      int k = threadIdx.x + i * T;
-      if (k <= M / 2) out[k] = acc[i];
+    for (int m = 0; m < 16; ++m) {
+      const int k = threadIdx.x + T * m;
+      if (k <= M / 2) out[k] = acc[m];
     }
   }
 }
 
+// Sum the runs of a node's tap-gradient spectrum, invert it, and fold the even
+// symmetry through the window: s[n] = Hann[n] (hbar[n] + hbar[-n]) (s[0] = Hann[0] hbar[0]).
 template <int M>
-__global__ void __launch_bounds__(M / 16) k_eq_finalize(DevCtx c, int node_begin) {
+__global__ void __launch_bounds__(M / 16) k_eq_gradfft(DevCtx c, int node_begin) {
   extern __shared__ float2 smem2[];
   float2* buf = smem2;
-  float* A = reinterpret_cast<float*>(buf + fft::Padded<M>::size);  // K
-  float* s = A + 1024;                                               // H+1
-  __shared__ float red[8 * 32];
   const int v = node_begin + blockIdx.x;
-  const NodeDev nd = c.nodes[v];
   const int4_ e = c.ext[v];
-  const int N = c.eq_taps, H = c.eq_H, K = (N + 1) / 2;
-  // Hermitian spectrum of r'[m] = dL/dh[m]; conjugated for the inverse
+  const int H = c.eq_H;
   for (int k = threadIdx.x; k <= M / 2; k += blockDim.x) {
     float2 r = make_float2(0.f, 0.f);
     for (int q = 0; q < e.y; ++q) {
@@ -226,50 +241,73 @@ __global__ void __launch_bounds__(M / 16) k_eq_finalize(DevCtx c, int node_begin
       r.x += x.x;
       r.y += x.y;
     }
-    buf[fft::pad(k)] = make_float2(r.x, -r.y);
+    buf[fft::pad(k)] = make_float2(r.x, -r.y);    // conjugated: the forward FFT inverts
     if (k > 0 && k < M / 2) buf[fft::pad(M - k)] = r;
   }
-  eq_magnitudes(c, nd, A, K);
   __syncthreads();
   fft::forward<M>(buf, c.tw, threadIdx.x, true);
-  // hbar[m] = Re(result)/M at m mod M; fold the even symmetry: s[n] = v[n](hbar[n] + hbar[-n])
   const float inv_m = 1.f / float(M);
+  float* s = c.eq_aux + size_t(e.z) * 1024;
   for (int n = threadIdx.x; n <= H; n += blockDim.x) {
     float hp = buf[fft::pad(n)].x * inv_m;
     float hm = buf[fft::pad((M - n) & (M - 1))].x * inv_m;
     s[n] = c.eq_hann[n] * (n == 0 ? hp : hp + hm);
   }
+}
+
+// dL/dp_k = A_k (c_k/N) sum_n s[n] cos(2 pi k n / N) for one chunk of k, then this
+// chunk's share of the band-matrix product; grid (EQ nodes of the step, chunks).
+__global__ void __launch_bounds__(EQ_CHUNK) k_eq_gradbands(DevCtx c, int node_begin) {
+  __shared__ float A[1024];
+  __shared__ float sv[1024];
+  __shared__ float cs[2048];
+  __shared__ float red[8 * 32];
+  const int v = node_begin + blockIdx.x;
+  const NodeDev nd = c.nodes[v];
+  const int N = c.eq_taps, H = c.eq_H, K = (N + 1) / 2;
+  const int z = c.ext[v].z;
+  eq_magnitudes(c, nd, A, K);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) cs[i] = c.eq_cos[i];
+  for (int i = threadIdx.x; i <= H; i += blockDim.x) sv[i] = c.eq_aux[size_t(z) * 1024 + i];
   __syncthreads();
-  // dL/dp_k = A_k * (c_k/N) sum_n s[n] cos(2 pi k n / N); then the band matrix
+  const int k = blockIdx.y * EQ_CHUNK + threadIdx.x;
   float bsum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    float acc = s[0];
+  if (k < K) {
+    float acc = sv[0];
     int idx = 0;
     for (int n = 1; n <= H; ++n) {
       idx += k;
       if (idx >= N) idx -= N;
-      acc += s[n] * c.eq_cos[idx];
+      acc += sv[n] * cs[idx];
     }
-    float pk = A[k] * acc * (k == 0 ? 1.f : 2.f) / float(N);
+    const float pk = A[k] * acc * (k == 0 ? 1.f : 2.f) / float(N);
     const float* row = c.eq_band + k * 8;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) bsum[b] += row[b] * pk;
+    for (int b = 0; b < 8; ++b) bsum[b] = row[b] * pk;
   }
-  // block reduce 8 values (two passes of 4)
   float lo[4] = {bsum[0], bsum[1], bsum[2], bsum[3]}, hi[4] = {bsum[4], bsum[5], bsum[6], bsum[7]};
   block_sum<4>(lo, red);
   block_sum<4>(hi, red + 4 * 32);
   if (threadIdx.x == 0) {
-    float* d = c.dparams + nd.prow * 8;
+    float* d = c.eq_bandpart + (size_t(z) * gridDim.y + blockIdx.y) * 8;
     for (int b = 0; b < 4; ++b) {
-      d[b] = LN10_20 * lo[b];
-      d[b + 4] = LN10_20 * hi[b];
+      d[b] = lo[b];
+      d[b + 4] = hi[b];
     }
   }
 }
 
-template <int M>
-static size_t design_smem() { return sizeof(float2) * fft::Padded<M>::size + sizeof(float) * (1024 + 1024 + 4); }
+// Sum the chunks' band partials in order: dL/d(band dB).
+__global__ void k_eq_gradout(DevCtx c, int node_begin, int node_end, int n_chunks) {
+  const int v = node_begin + blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= node_end) return;
+  const int z = c.ext[v].z;
+  float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int q = 0; q < n_chunks; ++q)
+    for (int b = 0; b < 8; ++b) s[b] += c.eq_bandpart[(size_t(z) * n_chunks + q) * 8 + b];
+  float* d = c.dparams + c.nodes[v].prow * 8;
+  for (int b = 0; b < 8; ++b) d[b] = LN10_20 * s[b];
+}
 
 template <int M>
 static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
@@ -277,19 +315,28 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
   static bool init = false;
   const size_t s1 = sizeof(float2) * fft::Padded<M>::size;
   if (!init) {
-    cudaFuncSetAttribute(k_eq_design<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(design_smem<M>()));
-    cudaFuncSetAttribute(k_eq_fwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
-    cudaFuncSetAttribute(k_eq_bwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(2 * s1));
-    cudaFuncSetAttribute(k_eq_finalize<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(design_smem<M>()));
+    cudaFuncSetAttribute(k_eq_spec<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
+    cudaFuncSetAttribute(k_eq_gradfft<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
+    cudaFuncSetAttribute(k_eq_fwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(2 * s1));
+    cudaFuncSetAttribute(k_eq_bwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(3 * s1));
     init = true;
   }
+  const int chunks_h = (c.eq_H + 1 + EQ_CHUNK - 1) / EQ_CHUNK;
+  const int chunks_k = ((c.eq_taps + 1) / 2 + EQ_CHUNK - 1) / EQ_CHUNK;
   switch (what) {
-    case 0: k_eq_design<M><<<b - a, T, design_smem<M>(), s>>>(c, a); break;
-    case 1: k_eq_fwd<M><<<grid_size(b, (228 * 1024) / int(s1 + 1024)), T, s1, s>>>(c, a, b); break;
-    case 2: k_eq_bwd<M><<<grid_size(b, (228 * 1024) / int(2 * s1 + 1024)), T, 2 * s1, s>>>(c, a, b); break;
-    case 3: k_eq_finalize<M><<<b - a, T, design_smem<M>(), s>>>(c, a); break;
+    case 0:
+      k_eq_taps<<<dim3(b - a, chunks_h), EQ_CHUNK, 0, s>>>(c, a);
+      k_eq_spec<M><<<b - a, T, s1, s>>>(c, a);
+      return 2;
+    case 1: k_eq_fwd<M><<<grid_size(b, (228 * 1024) / int(2 * s1 + 1024)), T, 2 * s1, s>>>(c, a, b); return 1;
+    case 2: k_eq_bwd<M><<<grid_size(b, (228 * 1024) / int(3 * s1 + 1024)), T, 3 * s1, s>>>(c, a, b); return 1;
+    case 3:
+      k_eq_gradfft<M><<<b - a, T, s1, s>>>(c, a);
+      k_eq_gradbands<<<dim3(b - a, chunks_k), EQ_CHUNK, 0, s>>>(c, a);
+      k_eq_gradout<<<(b - a + 63) / 64, 64, 0, s>>>(c, a, b, chunks_k);
+      return 3;
   }
-  return 1;
+  return 0;
 }
 
 // what: 0 design(node range), 1 fwd(items), 2 bwd(items), 3 finalize(node range)

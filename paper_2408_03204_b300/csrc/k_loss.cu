@@ -22,14 +22,13 @@ __host__ __device__ constexpr int res_m(int q) { return 512 << q; }
 
 struct LossArgs {
   const LossRow* rows;
-  const int2_* items;      // items of this resolution
+  const int4_* items;      // (row, resolution, first frame, group) for every resolution
   const float* y;          // out buffer
   const float* tgt;        // target buffer
   float4* part;            // [group] x 2 float4: (s1_l, s2_l, s3_l, 0), (s1_r, s2_r, s3_r, 0)
   float4* stats;           // [row][res] x 2: (nd_l, nt_l, F*(M/2+1), 0), (nd_r, nt_r, ., 0)
   float* frames;           // frame buffer
   const float2_* tw;
-  int q;                   // resolution index
   int n_items;
 };
 
@@ -60,108 +59,114 @@ __device__ __forceinline__ void split(float2 z, float2 zm, float2* L, float2* R)
   *R = make_float2(0.5f * dy, -0.5f * dx);
 }
 
+// One item: the 4096/M frames f0.. of one row at resolution M, y and target together.
 template <int M>
-__global__ void __launch_bounds__(256) k_loss_fwd(LossArgs a) {
+__device__ __forceinline__ void loss_item_fwd(const LossArgs& a, const int4_ item, float2* smem) {
   constexpr int T = M / 16, G = 256 / T;
-  extern __shared__ float2 smem2[];
-  float2* by = smem2;                                // G frames of y
-  float2* bt = smem2 + G * fft::Padded<M>::size;     // G frames of target
-  __shared__ float red[6 * 32 + 8];
+  float2* by = smem;
+  float2* bt = smem + G * fft::Padded<M>::size;
+  __shared__ float red[6 * 32];
   const int g = threadIdx.x / T, gtid = threadIdx.x % T;
-  for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
-    const int2_ item = a.items[it];
-    const LossRow r = a.rows[item.x];
-    const int F = r.n_frames[a.q];
-    float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int f0 = item.y; f0 < min(item.y + LOSS_FRAMES_PER_ITEM, F); f0 += G) {
-      const int f = f0 + g;
-      const bool act = f < min(item.y + LOSS_FRAMES_PER_ITEM, F);
-      float2* fy = by + g * fft::Padded<M>::size;
-      float2* ft = bt + g * fft::Padded<M>::size;
-      load_frame<M>(a, r, a.y, f, gtid, fy, act);
-      load_frame<M>(a, r, a.tgt, f, gtid, ft, act);
-      __syncthreads();
-      fft::forward<M>(fy, a.tw, gtid, true);
-      fft::forward<M>(ft, a.tw, gtid, true);
-      if (act) {
-        for (int k = gtid; k <= M / 2; k += T) {
-          int km = (M - k) & (M - 1);
-          float2 yl, yr, tl, tr;
-          split(fy[fft::pad(k)], fy[fft::pad(km)], &yl, &yr);
-          split(ft[fft::pad(k)], ft[fft::pad(km)], &tl, &tr);
-          float al = sqrtf(yl.x * yl.x + yl.y * yl.y), ar = sqrtf(yr.x * yr.x + yr.y * yr.y);
-          float bl = sqrtf(tl.x * tl.x + tl.y * tl.y), br = sqrtf(tr.x * tr.x + tr.y * tr.y);
-          s[0] += (al - bl) * (al - bl);
-          s[1] += bl * bl;
-          s[2] += fabsf(logf(al + MAG_EPS) - logf(bl + MAG_EPS));
-          s[3] += (ar - br) * (ar - br);
-          s[4] += br * br;
-          s[5] += fabsf(logf(ar + MAG_EPS) - logf(br + MAG_EPS));
-        }
-      }
-      __syncthreads();
+  const LossRow r = a.rows[item.x];
+  const int q = item.y, F = r.n_frames[q];
+  const int f = item.z + g;
+  const bool act = f < F;
+  float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float2* fy = by + g * fft::Padded<M>::size;
+  float2* ft = bt + g * fft::Padded<M>::size;
+  load_frame<M>(a, r, a.y, f, gtid, fy, act);
+  load_frame<M>(a, r, a.tgt, f, gtid, ft, act);
+  __syncthreads();
+  fft::forward<M>(fy, a.tw, gtid, true);
+  fft::forward<M>(ft, a.tw, gtid, true);
+  if (act) {
+    for (int k = gtid; k <= M / 2; k += T) {
+      int km = (M - k) & (M - 1);
+      float2 yl, yr, tl, tr;
+      split(fy[fft::pad(k)], fy[fft::pad(km)], &yl, &yr);
+      split(ft[fft::pad(k)], ft[fft::pad(km)], &tl, &tr);
+      float al = sqrtf(yl.x * yl.x + yl.y * yl.y), ar = sqrtf(yr.x * yr.x + yr.y * yr.y);
+      float bl = sqrtf(tl.x * tl.x + tl.y * tl.y), br = sqrtf(tr.x * tr.x + tr.y * tr.y);
+      s[0] += (al - bl) * (al - bl);
+      s[1] += bl * bl;
+      s[2] += fabsf(logf(al + MAG_EPS) - logf(bl + MAG_EPS));
+      s[3] += (ar - br) * (ar - br);
+      s[4] += br * br;
+      s[5] += fabsf(logf(ar + MAG_EPS) - logf(br + MAG_EPS));
     }
-    float lo[3] = {s[0], s[1], s[2]}, hi[3] = {s[3], s[4], s[5]};
+  }
+  float lo[3] = {s[0], s[1], s[2]}, hi[3] = {s[3], s[4], s[5]};
+  block_sum<3>(lo, red);
+  block_sum<3>(hi, red + 3 * 32);
+  if (threadIdx.x == 0) {
+    a.part[2 * item.w] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    a.part[2 * item.w + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256, 2) k_loss_fwd(LossArgs a) {
+  extern __shared__ float2 smem2[];
+  for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+    const int4_ item = a.items[it];
+    switch (item.y) {
+      case 0: loss_item_fwd<512>(a, item, smem2); break;
+      case 1: loss_item_fwd<1024>(a, item, smem2); break;
+      default: loss_item_fwd<2048>(a, item, smem2); break;
+    }
+  }
+}
+
+// One CTA per row: sum its groups per resolution, keep the norms for the backward
+// pass, and write the row loss (mean over resolution and channel of sc + mag).
+__global__ void __launch_bounds__(256) k_loss_rows(const LossRow* rows, const float4* part, float4* stats,
+                                                   float* row_loss) {
+  __shared__ float red[6 * 32];
+  const int j = blockIdx.x;
+  const LossRow r = rows[j];
+  float total = 0.f;
+  for (int q = 0; q < N_RES; ++q) {
+    float lo[3] = {0.f, 0.f, 0.f}, hi[3] = {0.f, 0.f, 0.f};
+    for (int gi = threadIdx.x; gi < r.n_groups[q]; gi += blockDim.x) {
+      float4 a = part[2 * (r.group_off[q] + gi)], b = part[2 * (r.group_off[q] + gi) + 1];
+      lo[0] += a.x; lo[1] += a.y; lo[2] += a.z;
+      hi[0] += b.x; hi[1] += b.y; hi[2] += b.z;
+    }
     block_sum<3>(lo, red);
     block_sum<3>(hi, red + 3 * 32);
     if (threadIdx.x == 0) {
-      int gi = r.group_off[a.q] + item.y / LOSS_FRAMES_PER_ITEM;
-      a.part[2 * gi] = make_float4(lo[0], lo[1], lo[2], 0.f);
-      a.part[2 * gi + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+      const float nb = float(r.n_frames[q]) * float(res_m(q) / 2 + 1);
+      float ndl = sqrtf(lo[0]), ntl = sqrtf(lo[1]), ndr = sqrtf(hi[0]), ntr = sqrtf(hi[1]);
+      stats[2 * (j * N_RES + q)] = make_float4(ndl, ntl, nb, 0.f);
+      stats[2 * (j * N_RES + q) + 1] = make_float4(ndr, ntr, nb, 0.f);
+      total += ndl / ntl + lo[2] / nb + ndr / ntr + hi[2] / nb;
     }
     __syncthreads();
   }
+  if (threadIdx.x == 0) row_loss[j] = total / float(2 * N_RES);
 }
 
-// One CTA: per row and resolution, sum the groups in order; loss = sum over rows of
-// the mean over (resolution, channel) of sc + mag.
-__global__ void k_loss_reduce(const LossRow* rows, int n_rows, const float4* part, float4* stats, float* loss) {
-  __shared__ float rl[1024];
-  float acc = 0.f;
-  for (int j = threadIdx.x; j < n_rows; j += blockDim.x) {
-    const LossRow r = rows[j];
-    float row_loss = 0.f;
-    for (int q = 0; q < N_RES; ++q) {
-      float sl[3] = {0.f, 0.f, 0.f}, sr[3] = {0.f, 0.f, 0.f};
-      for (int gi = 0; gi < r.n_groups[q]; ++gi) {
-        float4 a = part[2 * (r.group_off[q] + gi)], b = part[2 * (r.group_off[q] + gi) + 1];
-        sl[0] += a.x; sl[1] += a.y; sl[2] += a.z;
-        sr[0] += b.x; sr[1] += b.y; sr[2] += b.z;
-      }
-      const float nb = float(r.n_frames[q]) * float(res_m(q) / 2 + 1);
-      float ndl = sqrtf(sl[0]), ntl = sqrtf(sl[1]), ndr = sqrtf(sr[0]), ntr = sqrtf(sr[1]);
-      stats[2 * (j * N_RES + q)] = make_float4(ndl, ntl, nb, 0.f);
-      stats[2 * (j * N_RES + q) + 1] = make_float4(ndr, ntr, nb, 0.f);
-      row_loss += ndl / ntl + sl[2] / nb + ndr / ntr + sr[2] / nb;
-    }
-    acc += row_loss / float(2 * N_RES);
-  }
-  rl[threadIdx.x] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float t = 0.f;
-    for (int i = 0; i < int(blockDim.x); ++i) t += rl[i];
-    *loss = t;
-  }
+__global__ void k_loss_total(const float* row_loss, int n_rows, float* loss) {
+  float t = 0.f;
+  for (int j = 0; j < n_rows; ++j) t += row_loss[j];
+  *loss = t;
 }
 
 template <int M>
-__global__ void __launch_bounds__(256) k_loss_bwd(LossArgs a) {
+__device__ __forceinline__ void loss_item_bwd(const LossArgs& a, const int4_ item, float2* smem) {
   constexpr int T = M / 16, G = 256 / T;
   constexpr int NB = (M / 2 + 1 + T - 1) / T;
-  extern __shared__ float2 smem2[];
-  float2* by = smem2;
-  float2* bt = smem2 + G * fft::Padded<M>::size;
+  float2* by = smem;
+  float2* bt = smem + G * fft::Padded<M>::size;
   const int g = threadIdx.x / T, gtid = threadIdx.x % T;
   const float w_res = 1.f / float(2 * N_RES);
-  for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
-    const int2_ item = a.items[it];
+  {
     const LossRow r = a.rows[item.x];
-    const int F = r.n_frames[a.q];
-    const float4 stl = a.stats[2 * (item.x * N_RES + a.q)], str = a.stats[2 * (item.x * N_RES + a.q) + 1];
-    for (int f0 = item.y; f0 < min(item.y + LOSS_FRAMES_PER_ITEM, F); f0 += G) {
-      const int f = f0 + g;
-      const bool act = f < min(item.y + LOSS_FRAMES_PER_ITEM, F);
+    const int q = item.y, F = r.n_frames[q];
+    const float4 stl = a.stats[2 * (item.x * N_RES + q)], str = a.stats[2 * (item.x * N_RES + q) + 1];
+    {
+      const int f = item.z + g;
+      const bool act = f < F;
       float2* fy = by + g * fft::Padded<M>::size;
       float2* ft = bt + g * fft::Padded<M>::size;
       load_frame<M>(a, r, a.y, f, gtid, fy, act);
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(256) k_loss_bwd(LossArgs a) {
       __syncthreads();
       fft::forward<M>(fy, a.tw, gtid, true);
       if (act) {
-        float* fr = a.frames + r.frame_off[a.q] + int64_t(f) * 2 * M;
+        float* fr = a.frames + r.frame_off[q] + int64_t(f) * 2 * M;
         for (int n = gtid; n < M; n += T) {
           float2 z = fy[fft::pad(n)];
           float w = hann<M>(a.tw, n);
@@ -228,6 +233,18 @@ __global__ void __launch_bounds__(256) k_loss_bwd(LossArgs a) {
         }
       }
       __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256, 2) k_loss_bwd(LossArgs a) {
+  extern __shared__ float2 smem2[];
+  for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+    const int4_ item = a.items[it];
+    switch (item.y) {
+      case 0: loss_item_bwd<512>(a, item, smem2); break;
+      case 1: loss_item_bwd<1024>(a, item, smem2); break;
+      default: loss_item_bwd<2048>(a, item, smem2); break;
     }
   }
 }
@@ -258,42 +275,28 @@ __global__ void k_loss_ola(const LossRow* rows, const float* frames, float* d_ou
   d_out[r.off + r.pitch + t] = sr;
 }
 
-template <int M>
-static void loss_launch(bool bwd, LossArgs a, cudaStream_t s) {
-  constexpr int T = M / 16, G = 256 / T;
-  const size_t sm = 2 * G * fft::Padded<M>::size * sizeof(float2);
+int launch_loss(int what, const LossLaunch& L, cudaStream_t s) {
   static bool init = false;
+  // y and target frames: 2 x (4096/M frames of M padded points) for every M
+  const size_t smem = 2 * size_t(fft::Padded<4096>::size) * sizeof(float2);
   if (!init) {
-    cudaFuncSetAttribute(k_loss_fwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    cudaFuncSetAttribute(k_loss_bwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    cudaFuncSetAttribute(k_loss_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaFuncSetAttribute(k_loss_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     init = true;
   }
-  int g = grid_size(a.n_items, 3);
-  if (bwd) k_loss_bwd<M><<<g, 256, sm, s>>>(a);
-  else k_loss_fwd<M><<<g, 256, sm, s>>>(a);
-}
-
-int launch_loss(int what, const LossLaunch& L, cudaStream_t s) {
-  int n = 0;
-  if (what == 0 || what == 2) {
-    for (int q = 0; q < N_RES; ++q) {
-      if (L.n_items[q] <= 0) continue;
-      LossArgs a{L.rows, L.items[q], L.y, L.tgt, L.part, L.stats, L.frames, L.tw, q, L.n_items[q]};
-      if (q == 0) loss_launch<512>(what == 2, a, s);
-      if (q == 1) loss_launch<1024>(what == 2, a, s);
-      if (q == 2) loss_launch<2048>(what == 2, a, s);
-      ++n;
-    }
-    if (what == 0) {
-      k_loss_reduce<<<1, 256, 0, s>>>(L.rows, L.n_rows, L.part, L.stats, L.loss);
-      ++n;
-    } else {
-      dim3 grid((L.max_pitch + 255) / 256, L.n_rows);
-      k_loss_ola<<<grid, 256, 0, s>>>(L.rows, L.frames, L.d_out);
-      ++n;
-    }
+  if (L.n_items <= 0) return 0;
+  LossArgs a{L.rows, L.items, L.y, L.tgt, L.part, L.stats, L.frames, L.tw, L.n_items};
+  const int g = grid_size(L.n_items, 3);
+  if (what == 0) {
+    k_loss_fwd<<<g, 256, smem, s>>>(a);
+    k_loss_rows<<<L.n_rows, 256, 0, s>>>(L.rows, L.part, L.stats, L.row_loss);
+    k_loss_total<<<1, 1, 0, s>>>(L.row_loss, L.n_rows, L.loss);
+    return 3;
   }
-  return n;
+  k_loss_bwd<<<g, 256, smem, s>>>(a);
+  dim3 grid((L.max_pitch + 255) / 256, L.n_rows);
+  k_loss_ola<<<grid, 256, 0, s>>>(L.rows, L.frames, L.d_out);
+  return 2;
 }
 
 }  // namespace grafx

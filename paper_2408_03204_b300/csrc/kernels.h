@@ -24,8 +24,8 @@ int launch_comp(int what, const DevCtx& c, int a, int b, int ticket, cudaStream_
 
 struct LossLaunch {
   const LossRow* rows;
-  const int2_* items[N_RES];
-  int n_items[N_RES];
+  const int4_* items;   // (row, resolution, first frame, group)
+  int n_items;
   const float* y;
   const float* tgt;
   float4* part;
@@ -35,6 +35,7 @@ struct LossLaunch {
   int n_rows;
   int max_pitch;
   float* loss;
+  float* row_loss;
   float* d_out;
 };
 // what = 0 forward (statistics + reduce into *loss), 2 backward (frames + overlap-add into d_out)

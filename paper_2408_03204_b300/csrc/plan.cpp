@@ -39,12 +39,20 @@ void eq_band_table(int N, int fs, std::vector<float>* out) {
   }
 }
 
+// Block FFT size with the least transform work per output sample, M log2 M / S with
+// S = M - 2H outputs per block; 8192-point blocks are charged 30% for their lower
+// occupancy (512 threads, twice the shared memory).
 int pick_eq_fft(int taps) {
-  int H = (taps - 1) / 2;
-  int need = 2 * ((H + 3) & ~3) + 1024;
-  int m = 1024;
-  while (m < need) m *= 2;
-  return m;
+  const int H = (taps - 1) / 2;
+  int best = 0;
+  double best_cost = 1e30;
+  for (int m = 1024, lg = 10; m <= 8192; m *= 2, ++lg) {
+    int S = (m - 2 * H) & ~3;
+    if (S < 256) continue;
+    double cost = double(m) * lg / S * (m == 8192 ? 1.3 : 1.0);
+    if (cost < best_cost) { best_cost = cost; best = m; }
+  }
+  return best ? best : 8192;
 }
 }  // namespace
 
@@ -316,8 +324,9 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
         r.frame_off[q] = foff;
         foff += int64_t(F) * 2 * M;
         r.group_off[q] = groups;
-        r.n_groups[q] = (F + LOSS_FRAMES_PER_ITEM - 1) / LOSS_FRAMES_PER_ITEM;
-        for (int32_t f = 0; f < F; f += LOSS_FRAMES_PER_ITEM) p->loss.items[q].push_back({j, f});
+        const int per = 4096 / M;  // frames transformed together by one 256-thread CTA
+        r.n_groups[q] = (F + per - 1) / per;
+        for (int32_t f = 0, gi = 0; f < F; f += per, ++gi) p->loss.items.push_back({j, q, f, groups + gi});
         groups += r.n_groups[q];
       }
       p->loss.rows.push_back(r);
@@ -344,7 +353,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
     w.eq_band = take(4 * p->eq_band.size());
     size_t nrow = std::max<size_t>(p->loss.rows.size(), 1);
     w.loss_rows = take(sizeof(LossRow) * nrow);
-    w.loss_items = take(sizeof(int2_) * std::max<size_t>(p->loss.items[0].size() + p->loss.items[1].size() + p->loss.items[2].size(), 1));
+    w.loss_items = take(sizeof(int4_) * std::max<size_t>(p->loss.items.size(), 1));
     w.tables_end = o;
     // cleared at the start of every render / backprop
     w.status = take(16);
@@ -352,11 +361,14 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
     w.flags = take(8 * std::max<size_t>(p->items.size(), 1));
     w.flags_bytes = o - w.status;
     w.eq_spec = take(4 * size_t(std::max(p->n_eq, 1)) * (p->eq_fft / 2 + 1));
+    w.eq_aux = take(4 * size_t(std::max(p->n_eq, 1)) * 1024);
+    w.eq_bandpart = take(4 * size_t(std::max(p->n_eq, 1)) * 16 * 8);
     w.comp_carry = take(4 * size_t(std::max(p->n_comp_chunks, 1)));
     w.partial = take(16 * size_t(std::max(p->n_partials, 1)));
     w.eq_partial = take(8 * size_t(std::max(p->n_eq_runs, 1)) * (p->eq_fft / 2 + 1));
     w.loss_part = take(32 * size_t(std::max(p->loss.n_groups_total, 1)));
     w.loss_stats = take(32 * nrow * N_RES);
+    w.loss_rowloss = take(4 * nrow);
     w.loss_frames = take(4 * size_t(std::max<int64_t>(p->loss.frame_floats, 1)));
     w.U = take(4 * size_t(std::max<int64_t>(internal_floats, 1)));
     w.A = take(4 * size_t(std::max<int64_t>(internal_floats, 1)));

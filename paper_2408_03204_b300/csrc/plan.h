@@ -46,8 +46,8 @@ struct WsLayout {
   size_t loss_rows, loss_items;
   size_t tables_end;                           // [0, tables_end) is uploaded at bind time
   size_t status, tickets, flags, flags_bytes;  // flags_bytes covers status+tickets+flags (cleared per call)
-  size_t eq_spec, comp_carry, partial, eq_partial;
-  size_t loss_part, loss_stats, loss_frames;
+  size_t eq_spec, eq_aux, eq_bandpart, comp_carry, partial, eq_partial;
+  size_t loss_part, loss_stats, loss_rowloss, loss_frames;
   size_t U, A;
   size_t total;
 };
@@ -55,8 +55,8 @@ struct WsLayout {
 struct LossPlan {
   // per output row j
   std::vector<LossRow> rows;
-  // work items per resolution (row, first frame)
-  std::vector<int2_> items[3];
+  // work items (row, resolution, first frame, statistics group)
+  std::vector<int4_> items;
   int64_t frame_floats = 0;  // total floats in the frame buffer
   int32_t n_groups_total = 0;
   bool ok = false;           // every output row is long enough (>= 2048 samples)

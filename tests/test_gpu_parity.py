@@ -179,11 +179,8 @@ def test_mrstft_loss_and_grad():
     assert_grad_close(gd[:, :, :L], wg, tol=5e-3, what="dloss/dy")
 
 
-def test_cfg2_fwd_bwd_mrstft_reduced_length():
-    """The 64-track nested console with the full chain and the STFT loss against a
-    target rendered (by the oracle) from hidden parameters, at 2^15 samples."""
+def _cfg2_case(L):
     g = synth.console_cfg2()
-    L = 2 ** 15
     src_flat, src_per = flat_sources([g], [L], [2])
     P = union_params([g], 2)
     Ph = union_params([g], 102)
@@ -191,7 +188,24 @@ def test_cfg2_fwd_bwd_mrstft_reduced_length():
     target = orr.outputs_of(g.types, orr.render_one_by_one(g.types, g.edges, src_per[0], Ph, hp))
     y_ref = orr.outputs_of(g.types, orr.render_one_by_one(g.types, g.edges, src_per[0], P, hp))
     run = GpuRun([g], [L], P, src_flat, eq_taps=1023)
+    return g, src_per, P, hp, target, y_ref, run
+
+
+# Measured conditioning of the loss path (FP64 oracle, 64-track console, 2^15 samples):
+# perturbing the rendered mix by 1e-7 (the FP32 rounding level at full scale) moves the
+# oracle's own parameter gradients by up to 5.7e-3 relative (compressor rows), because
+# the log-magnitude term's gradient sign(.)/|Y| flips and spikes on near-equal or tiny
+# bins.  Through the loss, the FP32 path is therefore held to 2e-2; through the same
+# adjoint dL/dY (given by the oracle) it is held to the 1e-3 bar.
+LOSS_CHAIN_TOL = 2e-2
+
+
+@pytest.mark.parametrize("L", [2 ** 15, 2 ** 17])
+def test_cfg2_fwd_bwd_mrstft(L):
+    """64-track nested console, full chain, STFT loss against a target rendered (by the
+    oracle) from hidden parameters; 2^17 is the benchmarked size and launch setup."""
     import torch
+    g, src_per, P, hp, target, y_ref, run = _cfg2_case(L)
     out = run.render()
     assert_out_close(out.cpu().numpy().reshape(1, 2, L), y_ref)
     tgt = torch.tensor(target.astype(np.float32).reshape(-1), device="cuda")
@@ -200,10 +214,15 @@ def test_cfg2_fwd_bwd_mrstft_reduced_length():
     run.plan.loss_raw(out, tgt, loss, st)
     d_out = torch.empty_like(out)
     run.plan.loss_backward_raw(out, tgt, d_out, st)
-    dP, _ = run.backprop(d_out, want_sources=False)
     want_loss = ol.mrstft(y_ref, target)
     assert abs(loss.item() - want_loss) <= 1e-4 * abs(want_loss)
     dY = ol.mrstft_grad(y_ref, target)
     wP, _ = orr.backward(g.types, g.edges, src_per[0], P, dY, hp)
+    # (1) backward through the graph from the oracle's dL/dY
+    dP1, _ = run.backprop(dY.astype(np.float32).reshape(-1), want_sources=False)
     for t in P:
-        assert_grad_close(dP[t], wP[t], what=f"type {t}")
+        assert_grad_close(dP1[t], wP[t], what=f"type {t} (oracle dL/dY)")
+    # (2) the whole FP32 chain: GPU loss gradient, then GPU backward
+    dP2, _ = run.backprop(d_out, want_sources=False)
+    for t in P:
+        assert_grad_close(dP2[t], wP[t], tol=LOSS_CHAIN_TOL, what=f"type {t} (GPU loss chain)")
