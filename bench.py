@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--samples", type=int, default=L_FULL, help="signal length (smaller only for profiling captures)")
     return ap.parse_args()
 
 
@@ -205,7 +206,7 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     g = workload()
-    L = L_FULL
+    L = args.samples
     plan = gx.Plan([gx.Graph.from_lists(g.types, g.edges)], [L], eq_taps=EQ_TAPS)
     plan.bind_workspace(dev)
     info = plan.info
@@ -368,10 +369,11 @@ def main():
         cb = cpu_baseline()
 
     if rank == 0:
+        cfg = dict(CONFIG, samples=L)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": dict(CONFIG, nodes=int(info.n_nodes), processed_node_samples=node_samples,
+                "config": dict(cfg, nodes=int(info.n_nodes), processed_node_samples=node_samples,
                                schedule_steps=N, parallelism=f"replicas{world}"),
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": n_launch * args.steps}
