@@ -216,6 +216,30 @@ int grafx_sync_status(grafx_plan* p, void* stream);
  * grafx_mrstft_* call on this plan (for launch accounting). */
 int grafx_last_launch_count(const grafx_plan* p, int32_t* n);
 
+/* ---------------------------------------------------------------- allocation-free compressor
+ * The paper has no counterpart to this call; it exists for callers that must not
+ * allocate device memory at all, such as real-time audio callbacks and plugin hosts
+ * (a device allocation can block on a device-wide synchronisation) and host
+ * frameworks that hand out every byte of device memory from their own pool.
+ *
+ * Applies the compressor of grafx_render (same parameters [alpha, T, W, R] and the
+ * same chunked scan) to one stereo row: u and y are caller-owned device float32
+ * [2][pitch] rows (16-byte aligned, pitch a multiple of 4, pitch >= len), params a
+ * device pointer to 4 floats.  Samples of y at and past len are written as 0.
+ * Asynchronous on `stream`.
+ *
+ * It calls no allocator: its only scratch (about 17 KB of look-back words, a ticket
+ * and a status word) is a fixed array inside the library that every GPU which loads
+ * the library holds until the process exits; it is zeroed on `stream` at every call.
+ * Hence len is limited to 4194304 samples (GRAFX_ESHAPE beyond).  The first call on a
+ * device looks up that array's device address (once per device, with that device
+ * current), so make that first call before any stream capture.  Every call shares the
+ * one array: calls whose work overlaps on the GPU (different streams, or devices that
+ * alias it) race and give wrong results; serialise them.  A bounded device wait that
+ * expires is not reported by this call (its chunk then uses a zero carry). */
+int grafx_compressor_forward_noalloc(const float* u, int64_t len, int64_t pitch, const float* params,
+                                     float* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

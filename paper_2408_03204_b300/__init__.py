@@ -75,6 +75,7 @@ SIGNATURES = {
     "grafx_mrstft_backward": (ctypes.c_int, [_P, _F, _F, _F, _P]),
     "grafx_sync_status": (ctypes.c_int, [_P, _P]),
     "grafx_last_launch_count": (ctypes.c_int, [_P, _I32P]),
+    "grafx_compressor_forward_noalloc": (ctypes.c_int, [_F, _I64, _I64, _F, _F, _P]),
 }
 
 

@@ -19,8 +19,12 @@
 // ubar_x = k ybar_x + 2 u_m (1 - alpha) lambda and the parameter partials
 // (sum lambda (g[n-1] - x[n]) for alpha, sum Gybar dGy/dT|W|R) go to one slot
 // per chunk.
+#include <cstring>
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
+#include "plan.h"
 
 namespace grafx {
 
@@ -363,4 +367,131 @@ int launch_comp(int what, const DevCtx& c, int a, int b, int ticket, cudaStream_
   return 1;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the compressor forward pass, for callers that may not
+// allocate device memory (see grafx_compressor_forward_noalloc in grafx.h).  Its only
+// scratch, the look-back words of the chunks plus a ticket and a status word, lives in
+// this file-scope device array, sized for signals of up to NOALLOC_MAX_LEN samples.
+// Every GPU that loads the library keeps the array until the process exits.
+constexpr int NOALLOC_CHUNK = 2048;                              // samples per chunk (SPT = 8)
+constexpr int NOALLOC_MAX_LEN = 1 << 22;                         // samples per channel
+constexpr int NOALLOC_MAX_CHUNKS = NOALLOC_MAX_LEN / NOALLOC_CHUNK;
+constexpr int NOALLOC_WORDS = NOALLOC_MAX_CHUNKS + 32;           // + ticket / status words
+static __device__ __align__(256) unsigned long long g_comp_noalloc_scratch[NOALLOC_WORDS];
+
+// One stereo row u[2][pitch] -> y[2][pitch]; same chunk arithmetic as k_comp_fwd<8>,
+// with the row read directly instead of gathered over in-edges.
+__global__ void __launch_bounds__(256) k_comp_fwd_row(DevCtx c, const float* __restrict__ u, const float* p,
+                                                     float* y, int len, int pitch, int n_chunks) {
+  constexpr int SPT = 8, CH = 256 * SPT;
+  __shared__ float sh[32];
+  __shared__ int s_it;
+  __shared__ float s_carry;
+  const float alpha = p[0], T = p[1], W = p[2], R = p[3];
+  const float la = logf(alpha);
+  while (true) {
+    if (threadIdx.x == 0) s_it = atomicAdd(c.tickets, 1);
+    __syncthreads();
+    const int it = s_it;
+    if (it >= n_chunks) break;
+    const int t = it * CH + threadIdx.x * SPT;
+    float ul[SPT], ur[SPT], x[SPT], g[SPT];
+#pragma unroll
+    for (int q = 0; q < SPT / 4; ++q) {
+      float4 l = f4zero(), r = f4zero();
+      if (t + 4 * q < len) {
+        l = mask4(ld4(u + t + 4 * q), t + 4 * q, len);
+        r = mask4(ld4(u + pitch + t + 4 * q), t + 4 * q, len);
+      }
+      ul[4 * q + 0] = l.x; ul[4 * q + 1] = l.y; ul[4 * q + 2] = l.z; ul[4 * q + 3] = l.w;
+      ur[4 * q + 0] = r.x; ur[4 * q + 1] = r.y; ur[4 * q + 2] = r.z; ur[4 * q + 3] = r.w;
+    }
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
+    float b = 0.f;
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) b = alpha * b + (1.f - alpha) * x[i];
+    float total;
+    float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
+    if (threadIdx.x == 0) {
+      float carry = 0.f;
+      if (it == 0) {
+        publish(c, it, 2, total);
+      } else {
+        publish(c, it, 1, total);
+        carry = look_back(c, it - 1, expf(la * CH));
+        publish(c, it, 2, expf(la * CH) * carry + total);
+      }
+      s_carry = carry;
+    }
+    __syncthreads();
+    const float cin = excl + expf(la * float(SPT * threadIdx.x)) * s_carry;
+    envelope<SPT>(x, alpha, cin, g);
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) {
+      float gu = logf(g[i] + COMP_EPS);
+      Knee k = knee(gu, T, W, R);
+      float gain = expf(k.gy - gu);
+      ul[i] *= gain;
+      ur[i] *= gain;
+    }
+#pragma unroll
+    for (int q = 0; q < SPT / 4; ++q) {
+      if (t + 4 * q < pitch) {
+        st4(y + t + 4 * q, make_float4(ul[4 * q], ul[4 * q + 1], ul[4 * q + 2], ul[4 * q + 3]));
+        st4(y + pitch + t + 4 * q, make_float4(ur[4 * q], ur[4 * q + 1], ur[4 * q + 2], ur[4 * q + 3]));
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace grafx
+
+extern "C" int grafx_compressor_forward_noalloc(const float* u, int64_t len, int64_t pitch, const float* params,
+                                                float* y, void* stream) {
+  using namespace grafx;
+  if (!u || !params || !y) return fail(GRAFX_EINVAL, "null argument");
+  if (len < 1 || len > NOALLOC_MAX_LEN)
+    return fail(GRAFX_ESHAPE, "grafx_compressor_forward_noalloc: length must be in [1, 4194304] samples, the "
+                              "size of its fixed scratch");
+  if (pitch < len || pitch % 4 || pitch > (int64_t(1) << 30))
+    return fail(GRAFX_ESHAPE, "pitch must be >= length and a multiple of 4");
+  if ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(y)) % 16)
+    return fail(GRAFX_EINVAL, "signal rows must be 16-byte aligned");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(GRAFX_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  // Once per device, with that device current: the device address of the scratch array
+  // (in host code its name only stands for it).
+  static std::mutex mu;
+  static unsigned long long* addr[128] = {nullptr};
+  if (dev < 0 || dev >= 128) return fail(GRAFX_EINVAL, "device ordinal out of range");
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_comp_noalloc_scratch);
+      if (e != cudaSuccess)
+        return fail(GRAFX_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      addr[dev] = static_cast<unsigned long long*>(ptr);
+    }
+  }
+  unsigned long long* scratch = addr[dev];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int n_chunks = int((len + NOALLOC_CHUNK - 1) / NOALLOC_CHUNK);
+  // look-back words of this call's chunks, the ticket and the status start at zero
+  e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * n_chunks, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scratch + NOALLOC_MAX_CHUNKS, 0, 16, s);
+  if (e != cudaSuccess) return fail(GRAFX_ECUDA, std::string("clear scratch: ") + cudaGetErrorString(e));
+  DevCtx c;
+  std::memset(&c, 0, sizeof(c));
+  c.flags = scratch;
+  c.tickets = reinterpret_cast<int32_t*>(scratch + NOALLOC_MAX_CHUNKS);
+  c.status = reinterpret_cast<uint32_t*>(scratch + NOALLOC_MAX_CHUNKS + 1);
+  const int g = grid_size(n_chunks, 8);
+  k_comp_fwd_row<<<g, 256, 0, s>>>(c, u, params, y, int(len), int(pitch), n_chunks);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(GRAFX_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+  return GRAFX_OK;
+}
