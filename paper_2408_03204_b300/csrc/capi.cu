@@ -36,6 +36,7 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
   c.tcsr_dst = at<const int32_t>(p, p->ws.tcsr_dst);
   c.items = at<const int4_>(p, p->ws.items);
   c.tw = at<const float2_>(p, p->ws.twiddle);
+  c.ptw = at<const float2_>(p, p->ws.ptw);
   c.eq_cos = at<const float>(p, p->ws.eq_cos);
   c.eq_hann = at<const float>(p, p->ws.eq_hann);
   c.eq_band = at<const float>(p, p->ws.eq_band);
@@ -101,6 +102,7 @@ LossLaunch make_loss(const Plan* p, const float* y, const float* tgt) {
   L.stats = at<float4>(p, p->ws.loss_stats);
   L.frames = at<float>(p, p->ws.loss_frames);
   L.tw = at<const float2_>(p, p->ws.twiddle);
+  L.ptw = at<const float2_>(p, p->ws.ptw);
   L.n_rows = int(p->loss.rows.size());
   for (auto& r : p->loss.rows) L.max_pitch = std::max(L.max_pitch, r.pitch);
   return L;
@@ -259,6 +261,7 @@ int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* s
   put(p->ws.tcsr_dst, p->tcsr_dst.data(), p->tcsr_dst.size() * 4);
   put(p->ws.items, p->items.data(), p->items.size() * sizeof(int4_));
   put(p->ws.twiddle, p->twiddle.data(), p->twiddle.size() * sizeof(float2_));
+  put(p->ws.ptw, p->ptw.data(), p->ptw.size() * sizeof(float2_));
   put(p->ws.eq_cos, p->eq_cos.data(), p->eq_cos.size() * 4);
   put(p->ws.eq_hann, p->eq_hann.data(), p->eq_hann.size() * 4);
   put(p->ws.eq_band, p->eq_band.data(), p->eq_band.size() * 4);

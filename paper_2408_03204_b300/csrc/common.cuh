@@ -19,7 +19,8 @@ struct DevCtx {
   const int32_t* tcsr_ptr;
   const int32_t* tcsr_dst;
   const int4_* items;
-  const float2_* tw;
+  const float2_* tw;    // exp(-2 pi i m / 8192), m < 8192 (window tables)
+  const float2_* ptw;   // FFT pass twiddle tables (fft.cuh)
   const float* eq_cos;
   const float* eq_hann;
   const float* eq_band;

@@ -9,8 +9,7 @@
 // positions, barrier.  Shared-memory indices are padded (i + i/16) so that the
 // stride-16 writes of the first pass are free of bank conflicts.
 //
-// Twiddles come from a table tw[m] = exp(-2 pi i m / 8192) built on the host in
-// double precision.  The forward transform uses exp(-2 pi i k n / M); an inverse is
+// Twiddles come from per-pass tables (ptw_*) built on the host in double precision.  The forward transform uses exp(-2 pi i k n / M); an inverse is
 // obtained by conjugating the input and the output.
 //
 // The pass bodies are __host__ __device__ so that a CPU harness can run the same
@@ -130,6 +129,24 @@ template <> struct Dft<16> {
   }
 };
 
+// Pass geometry: pass p (p = 0..npass-1) merges Ns = 16^p points into 16^p * R_p with
+// R_p = 16, except the last pass of an M that is not a power of 16 (radix M / 16^n16).
+GX_HD constexpr int geo_n16(int M) { return M >= 4096 ? 3 : M >= 256 ? 2 : 1; }
+GX_HD constexpr int ipow16(int p) { return p == 0 ? 1 : 16 * ipow16(p - 1); }
+GX_HD constexpr int geo_last(int M) { return M / ipow16(geo_n16(M)); }
+GX_HD constexpr int geo_npass(int M) { return geo_n16(M) + (geo_last(M) > 1 ? 1 : 0); }
+GX_HD constexpr int pass_radix(int M, int p) { return (p == geo_npass(M) - 1 && geo_last(M) > 1) ? geo_last(M) : 16; }
+
+// Pass twiddle tables: for every pass p >= 1 of an M-point transform, the entries
+// W_{Ns R}^{r k} = exp(-2 pi i r k / (Ns R)) for r in [1, R), k in [0, Ns), stored at
+// [(r-1) Ns + k] so that the threads of a warp (consecutive k) read consecutive
+// entries.  The tables of M = 512, 1024, ..., 8192 are concatenated in that order.
+GX_HD constexpr int ptw_pass_size(int M, int p) { return p == 0 ? 0 : (pass_radix(M, p) - 1) * ipow16(p); }
+GX_HD constexpr int ptw_pass_off(int M, int p) { return p == 0 ? 0 : ptw_pass_off(M, p - 1) + ptw_pass_size(M, p - 1); }
+GX_HD constexpr int ptw_size(int M) { return ptw_pass_off(M, geo_npass(M)); }
+GX_HD constexpr int ptw_base(int M) { return M <= 512 ? 0 : ptw_base(M / 2) + ptw_size(M / 2); }
+constexpr int PTW_TOTAL = ptw_base(8192) + ptw_size(8192);
+
 // Pass geometry of an M-point transform.
 template <int M> struct Geo {
   static constexpr int T = M / 16;  // threads per transform
@@ -150,7 +167,8 @@ GX_HD void pass_load(const float2* buf, int tid, float2 (*v)[R]) {
   }
 }
 
-// Phase 2 of a pass: twiddle, DFT_R, auto-sorted store.  Ns = points already merged.
+// Phase 2 of a pass: twiddle, DFT_R, auto-sorted store.  Ns = points already merged;
+// tw = this pass's twiddle table (see ptw_pass_off).
 template <int M, int R>
 GX_HD void pass_store(float2* buf, const float2_* tw, int tid, int Ns, float2 (*v)[R]) {
   constexpr int T = M / 16, BPT = 16 / R;
@@ -159,10 +177,9 @@ GX_HD void pass_store(float2* buf, const float2_* tw, int tid, int Ns, float2 (*
     int j = tid + b * T;
     int k = j & (Ns - 1);
     if (Ns > 1) {
-      int step = k * (TWIDDLE_N / (Ns * R));
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        float2_ w = tw[r * step];
+        float2_ w = tw[(r - 1) * Ns + k];
         v[b][r] = cmul(v[b][r], make_float2(w.x, w.y));
       }
     }
@@ -184,10 +201,9 @@ GX_HD void pass_compute(const float2_* tw, int tid, int Ns, float2 (*v)[R]) {
     int j = tid + b * T;
     int k = j & (Ns - 1);
     if (Ns > 1) {
-      int step = k * (TWIDDLE_N / (Ns * R));
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        float2_ w = tw[r * step];
+        float2_ w = tw[(r - 1) * Ns + k];
         v[b][r] = cmul(v[b][r], make_float2(w.x, w.y));
       }
     }
@@ -199,15 +215,17 @@ GX_HD void pass_compute(const float2_* tw, int tid, int Ns, float2 (*v)[R]) {
 // Full forward transform of one M-point padded buffer by threads tid in [0, M/16).
 // Every thread of the CTA must call it (it contains __syncthreads); threads with
 // tid >= M/16 pass `active = false`.  The caller synchronises before the first pass.
+// ptw: the concatenated pass twiddle tables (PTW_TOTAL entries).
 template <int M>
-__device__ __forceinline__ void forward(float2* buf, const float2_* __restrict__ tw, int tid, bool active) {
+__device__ __forceinline__ void forward(float2* buf, const float2_* __restrict__ ptw, int tid, bool active) {
+  const float2_* tw = ptw + ptw_base(M);
   int Ns = 1;
 #pragma unroll
   for (int p = 0; p < Geo<M>::n16; ++p) {
     float2 v[1][16];
     if (active) pass_load<M, 16>(buf, tid, v);
     __syncthreads();
-    if (active) pass_store<M, 16>(buf, tw, tid, Ns, v);
+    if (active) pass_store<M, 16>(buf, tw + ptw_pass_off(M, p), tid, Ns, v);
     __syncthreads();
     Ns *= 16;
   }
@@ -216,7 +234,7 @@ __device__ __forceinline__ void forward(float2* buf, const float2_* __restrict__
     float2 v[16 / R][R];
     if (active) pass_load<M, R>(buf, tid, v);
     __syncthreads();
-    if (active) pass_store<M, R>(buf, tw, tid, Ns, v);
+    if (active) pass_store<M, R>(buf, tw + ptw_pass_off(M, Geo<M>::n16), tid, Ns, v);
     __syncthreads();
   }
 }
@@ -229,7 +247,8 @@ __device__ __forceinline__ void forward(float2* buf, const float2_* __restrict__
 // on exit other threads may still read b1 (or b0 when the pass count is odd).
 template <int M>
 __device__ __forceinline__ void forward_regs(float2 (&v)[16], float2* b0, float2* b1,
-                                             const float2_* __restrict__ tw, int tid) {
+                                             const float2_* __restrict__ ptw, int tid) {
+  const float2_* tw = ptw + ptw_base(M);
   constexpr int n16 = Geo<M>::n16, last = Geo<M>::last;
   constexpr int npass = n16 + (last > 1 ? 1 : 0);
   float2* bufs[2] = {b0, b1};
@@ -250,7 +269,7 @@ __device__ __forceinline__ void forward_regs(float2 (&v)[16], float2* b0, float2
     if (R == 16) {
       float2 w[1][16];
       pass_load<M, 16>(bufs[cur], tid, w);
-      pass_compute<M, 16>(tw, tid, Ns, w);
+      pass_compute<M, 16>(tw + ptw_pass_off(M, p), tid, Ns, w);
       if (is_last) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = w[0][r];
@@ -263,7 +282,7 @@ __device__ __forceinline__ void forward_regs(float2 (&v)[16], float2* b0, float2
       constexpr int RL = last, BPT = 16 / RL;
       float2 w[BPT][RL];
       pass_load<M, RL>(bufs[cur], tid, w);
-      pass_compute<M, RL>(tw, tid, Ns, w);
+      pass_compute<M, RL>(tw + ptw_pass_off(M, p), tid, Ns, w);
 #pragma unroll
       for (int b = 0; b < BPT; ++b)
 #pragma unroll

@@ -7,8 +7,8 @@
 // warp-shuffle scan and a cross-warp scan combine the per-thread states with the
 // decay a^SPT, and the chunk's carry-in comes from the chunks before it by a
 // decoupled look-back: each chunk publishes its zero-start end state, then its
-// inclusive end state once its carry is known; a chunk walks back over published
-// states until it meets an inclusive one.  Chunks are handed out by an atomic
+// inclusive end state once its carry is known; one warp of a chunk reads the 32
+// preceding states at once and walks back until it meets an inclusive one.  Chunks are handed out by an atomic
 // ticket in (node, chunk) order, so every chunk waited on is held by a CTA that is
 // already running; every wait is bounded and records ST_TIMEOUT on expiry.
 // The forward pass stores each chunk's carry-in (one float) so the backward pass
@@ -86,16 +86,28 @@ __device__ __forceinline__ void publish(const DevCtx& c, int j, unsigned st, flo
   atomicExch(c.flags + j, pack_flag(st, v));
 }
 
-// Walk back from item `j` (the chunk before the current one in ticket order),
-// accumulating aggregates with decay `dc` per chunk until an inclusive state.
-__device__ float look_back(const DevCtx& c, int j, float dc) {
-  float acc = 0.f, dec = 1.f, val;
+// Carry into the current chunk from the chunks before it in ticket order, run by one
+// full warp: lane l examines item end - l, so 32 predecessors are read at once.  The
+// carry is sum_l exp(la_ch * l) * state(end - l) over the lanes up to the first one
+// whose state is inclusive, continuing 32 items further back if none is.  Items before
+// `first` (the node's first chunk, which always publishes an inclusive state) are not
+// read.  la_ch = ln(decay of one chunk).  Returns the carry in every lane.
+__device__ float look_back_warp(const DevCtx& c, int end, int first, float la_ch) {
+  const int lane = threadIdx.x & 31;
+  float acc = 0.f, dec = 1.f;
   while (true) {
-    unsigned st = wait_flag(c, j, &val);
-    acc += dec * val;
-    if (st == 2) break;
-    dec *= dc;
-    --j;
+    const int j = end - lane;
+    float val = 0.f;
+    const unsigned st = j < first ? 2u : wait_flag(c, j, &val);
+    const unsigned incl = __ballot_sync(0xffffffffu, st == 2u);
+    const int stop = incl ? __ffs(int(incl)) - 1 : 31;
+    float w = lane <= stop ? val * expf(la_ch * float(lane)) : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    acc += dec * w;
+    if (incl) break;
+    dec *= expf(la_ch * 32.f);
+    end -= 32;
   }
   return acc;
 }
@@ -209,17 +221,19 @@ __global__ void __launch_bounds__(256) k_comp_fwd(DevCtx c, int item0, int n_ite
     for (int i = 0; i < SPT; ++i) b = alpha * b + (1.f - alpha) * x[i];
     float total;
     float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
       float carry = 0.f;
       if (chunk == 0) {
-        publish(c, item0 + it, 2, total);
+        if (threadIdx.x == 0) publish(c, item0 + it, 2, total);
       } else {
-        publish(c, item0 + it, 1, total);
-        carry = look_back(c, item0 + it - 1, expf(la * CH));
-        publish(c, item0 + it, 2, expf(la * CH) * carry + total);
+        if (threadIdx.x == 0) publish(c, item0 + it, 1, total);
+        carry = look_back_warp(c, item0 + it - 1, item0 + it - chunk, la * CH);
+        if (threadIdx.x == 0) publish(c, item0 + it, 2, expf(la * CH) * carry + total);
       }
-      c.comp_carry[w.z] = carry;
-      s_carry = carry;
+      if (threadIdx.x == 0) {
+        c.comp_carry[w.z] = carry;
+        s_carry = carry;
+      }
     }
     __syncthreads();
     const float cin = excl + expf(la * float(SPT * threadIdx.x)) * s_carry;
@@ -293,16 +307,16 @@ __global__ void __launch_bounds__(256) k_comp_bwd(DevCtx c, int item0, int n_ite
     __syncthreads();  // sh reuse
     float rtotal;
     float rexcl = block_affine_scan<true>(lb, la * SPT, sh, &rtotal);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
       float lin = 0.f;
       if (chunk == n_chunks - 1) {
-        publish(c, item0 + it, 2, rtotal);
+        if (threadIdx.x == 0) publish(c, item0 + it, 2, rtotal);
       } else {
-        publish(c, item0 + it, 1, rtotal);
-        lin = look_back(c, item0 + it - 1, expf(la * CH));
-        publish(c, item0 + it, 2, expf(la * CH) * lin + rtotal);
+        if (threadIdx.x == 0) publish(c, item0 + it, 1, rtotal);
+        lin = look_back_warp(c, item0 + it - 1, item0 + it - (n_chunks - 1 - chunk), la * CH);
+        if (threadIdx.x == 0) publish(c, item0 + it, 2, expf(la * CH) * lin + rtotal);
       }
-      s_lin = lin;
+      if (threadIdx.x == 0) s_lin = lin;
     }
     glast[threadIdx.x] = g[SPT - 1];
     __syncthreads();
@@ -413,16 +427,16 @@ __global__ void __launch_bounds__(256) k_comp_fwd_row(DevCtx c, const float* __r
     for (int i = 0; i < SPT; ++i) b = alpha * b + (1.f - alpha) * x[i];
     float total;
     float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
       float carry = 0.f;
       if (it == 0) {
-        publish(c, it, 2, total);
+        if (threadIdx.x == 0) publish(c, it, 2, total);
       } else {
-        publish(c, it, 1, total);
-        carry = look_back(c, it - 1, expf(la * CH));
-        publish(c, it, 2, expf(la * CH) * carry + total);
+        if (threadIdx.x == 0) publish(c, it, 1, total);
+        carry = look_back_warp(c, it - 1, 0, la * CH);
+        if (threadIdx.x == 0) publish(c, it, 2, expf(la * CH) * carry + total);
       }
-      s_carry = carry;
+      if (threadIdx.x == 0) s_carry = carry;
     }
     __syncthreads();
     const float cin = excl + expf(la * float(SPT * threadIdx.x)) * s_carry;

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(M / 16) k_eq_spec(DevCtx c, int node_begin) {
     buf[fft::pad(m)] = make_float2(a <= H ? h[a] * inv_m : 0.f, 0.f);
   }
   __syncthreads();
-  fft::forward<M>(buf, c.tw, threadIdx.x, true);
+  fft::forward<M>(buf, c.ptw, threadIdx.x, true);
   float* spec = c.eq_spec + size_t(c.ext[v].z) * (M / 2 + 1);
   for (int k = threadIdx.x; k <= M / 2; k += blockDim.x) spec[k] = buf[fft::pad(k)].x;
 }
@@ -158,10 +158,10 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_fwd(DevCtx c, int item0
     float2 x[16];
     eq_load_regs<M, false>(c, v, nd, ws, x, false, H, S);
     if (even) __syncthreads();
-    fft::forward_regs<M>(x, b0, b1, c.tw, threadIdx.x);
+    fft::forward_regs<M>(x, b0, b1, c.ptw, threadIdx.x);
     eq_apply_regs<M>(x, spec);
     if (even) __syncthreads();
-    fft::forward_regs<M>(x, b0, b1, c.tw, threadIdx.x);
+    fft::forward_regs<M>(x, b0, b1, c.ptw, threadIdx.x);
     eq_store_regs<M>(yrow_w(c, nd), nd, ws, x, H, S);
   }
 }
@@ -191,12 +191,12 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_bwd(DevCtx c, int item0
       float2 x[16];
       eq_load_regs<M, false>(c, v, nd, ws, x, true, H, S);
       __syncthreads();  // previous block's readers of b0/b1/X are done
-      fft::forward_regs<M>(x, b0, b1, c.tw, threadIdx.x);
+      fft::forward_regs<M>(x, b0, b1, c.ptw, threadIdx.x);
 #pragma unroll
       for (int m = 0; m < 16; ++m) X[fft::pad(threadIdx.x + T * m)] = x[m];
       eq_load_regs<M, true>(c, v, nd, ws, x, false, H, S);
       if (even) __syncthreads();
-      fft::forward_regs<M>(x, b0, b1, c.tw, threadIdx.x);
+      fft::forward_regs<M>(x, b0, b1, c.ptw, threadIdx.x);
 #pragma unroll
       for (int m = 0; m < 16; ++m) Y[fft::pad(threadIdx.x + T * m)] = x[m];
       __syncthreads();
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_bwd(DevCtx c, int item0
       }
       // input adjoint: the centred convolution of ybar with the even filter
       eq_apply_regs<M>(x, spec);
-      fft::forward_regs<M>(x, i0, i1, c.tw, threadIdx.x);
+      fft::forward_regs<M>(x, i0, i1, c.ptw, threadIdx.x);
       eq_store_regs<M>(arow_w(c, nd), nd, ws, x, H, S);
     }
     float2* out = c.eq_partial + size_t(w.w) * (M / 2 + 1);
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(M / 16) k_eq_gradfft(DevCtx c, int node_begin)
     if (k > 0 && k < M / 2) buf[fft::pad(M - k)] = r;
   }
   __syncthreads();
-  fft::forward<M>(buf, c.tw, threadIdx.x, true);
+  fft::forward<M>(buf, c.ptw, threadIdx.x, true);
   const float inv_m = 1.f / float(M);
   float* s = c.eq_aux + size_t(e.z) * 1024;
   for (int n = threadIdx.x; n <= H; n += blockDim.x) {

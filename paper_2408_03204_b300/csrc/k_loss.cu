@@ -29,6 +29,7 @@ struct LossArgs {
   float4* stats;           // [row][res] x 2: (nd_l, nt_l, F*(M/2+1), 0), (nd_r, nt_r, ., 0)
   float* frames;           // frame buffer
   const float2_* tw;
+  const float2_* ptw;
   int n_items;
 };
 
@@ -77,8 +78,8 @@ __device__ __forceinline__ void loss_item_fwd(const LossArgs& a, const int4_ ite
   load_frame<M>(a, r, a.y, f, gtid, fy, act);
   load_frame<M>(a, r, a.tgt, f, gtid, ft, act);
   __syncthreads();
-  fft::forward<M>(fy, a.tw, gtid, true);
-  fft::forward<M>(ft, a.tw, gtid, true);
+  fft::forward<M>(fy, a.ptw, gtid, true);
+  fft::forward<M>(ft, a.ptw, gtid, true);
   if (act) {
     for (int k = gtid; k <= M / 2; k += T) {
       int km = (M - k) & (M - 1);
@@ -172,8 +173,8 @@ __device__ __forceinline__ void loss_item_bwd(const LossArgs& a, const int4_ ite
       load_frame<M>(a, r, a.y, f, gtid, fy, act);
       load_frame<M>(a, r, a.tgt, f, gtid, ft, act);
       __syncthreads();
-      fft::forward<M>(fy, a.tw, gtid, true);
-      fft::forward<M>(ft, a.tw, gtid, true);
+      fft::forward<M>(fy, a.ptw, gtid, true);
+      fft::forward<M>(ft, a.ptw, gtid, true);
       // dL/dY per bin, as the Hermitian spectra of both channels packed l + i r
       float2 wk[NB], wm[NB];
 #pragma unroll
@@ -222,7 +223,7 @@ __device__ __forceinline__ void loss_item_bwd(const LossArgs& a, const int4_ ite
         }
       }
       __syncthreads();
-      fft::forward<M>(fy, a.tw, gtid, true);
+      fft::forward<M>(fy, a.ptw, gtid, true);
       if (act) {
         float* fr = a.frames + r.frame_off[q] + int64_t(f) * 2 * M;
         for (int n = gtid; n < M; n += T) {
@@ -285,7 +286,7 @@ int launch_loss(int what, const LossLaunch& L, cudaStream_t s) {
     init = true;
   }
   if (L.n_items <= 0) return 0;
-  LossArgs a{L.rows, L.items, L.y, L.tgt, L.part, L.stats, L.frames, L.tw, L.n_items};
+  LossArgs a{L.rows, L.items, L.y, L.tgt, L.part, L.stats, L.frames, L.tw, L.ptw, L.n_items};
   const int g = grid_size(L.n_items, 3);
   if (what == 0) {
     k_loss_fwd<<<g, 256, smem, s>>>(a);

@@ -32,6 +32,7 @@ struct LossLaunch {
   float4* stats;
   float* frames;
   const float2_* tw;
+  const float2_* ptw;
   int n_rows;
   int max_pitch;
   float* loss;

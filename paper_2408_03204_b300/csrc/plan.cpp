@@ -2,6 +2,8 @@
 // plus the device-side work lists, constant tables and workspace layout.
 #include "plan.h"
 
+#include "fft.cuh"
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -295,6 +297,19 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
     double a = 2.0 * M_PI * m / TWIDDLE_N;
     p->twiddle[m] = float2_{float(std::cos(a)), float(-std::sin(a))};
   }
+  // FFT pass twiddles W_{Ns R}^{r k} at [(r-1) Ns + k] for every pass of every size
+  p->ptw.assign(fft::PTW_TOTAL, float2_{0.f, 0.f});
+  for (int M = 512; M <= 8192; M *= 2) {
+    for (int pass = 1, Ns = 16; pass < fft::geo_npass(M); ++pass, Ns *= 16) {
+      const int R = fft::pass_radix(M, pass);
+      float2_* t = p->ptw.data() + fft::ptw_base(M) + fft::ptw_pass_off(M, pass);
+      for (int r = 1; r < R; ++r)
+        for (int k = 0; k < Ns; ++k) {
+          double a = -2.0 * M_PI * double(r) * k / (double(Ns) * R);
+          t[(r - 1) * Ns + k] = float2_{float(std::cos(a)), float(std::sin(a))};
+        }
+    }
+  }
   {
     const int Nt = p->eq_taps, H = p->eq_H;
     p->eq_cos.resize(Nt);
@@ -348,6 +363,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
     w.tcsr_dst = take(4 * size_t(std::max(n_e, 1)));
     w.items = take(sizeof(int4_) * std::max<size_t>(p->items.size(), 1));
     w.twiddle = take(sizeof(float2_) * TWIDDLE_N);
+    w.ptw = take(sizeof(float2_) * fft::PTW_TOTAL);
     w.eq_cos = take(4 * p->eq_cos.size());
     w.eq_hann = take(4 * p->eq_hann.size());
     w.eq_band = take(4 * p->eq_band.size());

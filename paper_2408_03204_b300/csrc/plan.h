@@ -42,7 +42,7 @@ struct StepInfo {
 // Byte offsets of the regions inside the caller's workspace.
 struct WsLayout {
   size_t nodes, node_ext, csr_ptr, csr_src, tcsr_ptr, tcsr_dst, items;
-  size_t twiddle, eq_cos, eq_hann, eq_band;
+  size_t twiddle, ptw, eq_cos, eq_hann, eq_band;
   size_t loss_rows, loss_items;
   size_t tables_end;                           // [0, tables_end) is uploaded at bind time
   size_t status, tickets, flags, flags_bytes;  // flags_bytes covers status+tickets+flags (cleared per call)
@@ -89,7 +89,7 @@ struct Plan {
   LossPlan loss;
   WsLayout ws;
   // host tables
-  std::vector<float2_> twiddle;
+  std::vector<float2_> twiddle, ptw;
   std::vector<float> eq_cos, eq_hann, eq_band;
   // bindings
   char* dev_ws = nullptr;

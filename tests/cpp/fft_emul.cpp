@@ -10,11 +10,12 @@
 using namespace grafx;
 
 template <int M, int R>
-void run_pass(std::vector<float2>& buf, const std::vector<float2_>& tw, int Ns) {
+void run_pass(std::vector<float2>& buf, const std::vector<float2_>& tw, int Ns, int pass) {
   constexpr int T = M / 16;
+  const float2_* twp = tw.data() + fft::ptw_base(M) + fft::ptw_pass_off(M, pass);
   std::vector<std::array<std::array<float2, R>, 16 / R>> v(T);
   for (int t = 0; t < T; ++t) fft::pass_load<M, R>(buf.data(), t, reinterpret_cast<float2(*)[R]>(v[t].data()));
-  for (int t = 0; t < T; ++t) fft::pass_store<M, R>(buf.data(), tw.data(), t, Ns, reinterpret_cast<float2(*)[R]>(v[t].data()));
+  for (int t = 0; t < T; ++t) fft::pass_store<M, R>(buf.data(), twp, t, Ns, reinterpret_cast<float2(*)[R]>(v[t].data()));
 }
 
 template <int M>
@@ -27,8 +28,8 @@ double check(std::mt19937& g, const std::vector<float2_>& tw) {
     buf[fft::pad(i)] = make_float2(float(xr[i]), float(xi[i]));
   }
   int Ns = 1;
-  for (int p = 0; p < fft::Geo<M>::n16; ++p) { run_pass<M, 16>(buf, tw, Ns); Ns *= 16; }
-  if constexpr (fft::Geo<M>::last > 1) run_pass<M, fft::Geo<M>::last>(buf, tw, Ns);
+  for (int p = 0; p < fft::Geo<M>::n16; ++p) { run_pass<M, 16>(buf, tw, Ns, p); Ns *= 16; }
+  if constexpr (fft::Geo<M>::last > 1) run_pass<M, fft::Geo<M>::last>(buf, tw, Ns, fft::Geo<M>::n16);
   double err = 0, ref = 0;
   for (int k = 0; k < M; ++k) {
     double sr = 0, si = 0;
@@ -45,11 +46,17 @@ double check(std::mt19937& g, const std::vector<float2_>& tw) {
 }
 
 int main() {
-  std::vector<float2_> tw(TWIDDLE_N);
-  for (int m = 0; m < TWIDDLE_N; ++m) {
-    double a = 2.0 * M_PI * m / TWIDDLE_N;
-    tw[m] = float2_{float(std::cos(a)), float(-std::sin(a))};
-  }
+  // pass twiddle tables: W_{Ns R}^{r k} at [(r-1) Ns + k], concatenated over M
+  std::vector<float2_> tw(fft::PTW_TOTAL);
+  for (int M = 512; M <= 8192; M *= 2)
+    for (int pass = 1, Ns = 16; pass < fft::geo_npass(M); ++pass, Ns *= 16) {
+      const int R = fft::pass_radix(M, pass);
+      for (int r = 1; r < R; ++r)
+        for (int k = 0; k < Ns; ++k) {
+          double a = -2.0 * M_PI * double(r) * k / (double(Ns) * R);
+          tw[fft::ptw_base(M) + fft::ptw_pass_off(M, pass) + (r - 1) * Ns + k] = float2_{float(std::cos(a)), float(std::sin(a))};
+        }
+    }
   std::mt19937 g(5);
   std::printf("512 %.3e\n", check<512>(g, tw));
   std::printf("1024 %.3e\n", check<1024>(g, tw));

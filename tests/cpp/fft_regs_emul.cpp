@@ -34,7 +34,7 @@ double check(std::mt19937& g, const std::vector<float2_>& tw) {
       std::vector<std::array<float2, 16>> w(T);
       for (int t = 0; t < T; ++t) fft::pass_load<M, 16>(b[cur].data(), t, reinterpret_cast<float2(*)[16]>(w[t].data()));
       for (int t = 0; t < T; ++t) {
-        fft::pass_compute<M, 16>(tw.data(), t, Ns, reinterpret_cast<float2(*)[16]>(w[t].data()));
+        fft::pass_compute<M, 16>(tw.data() + fft::ptw_base(M) + fft::ptw_pass_off(M, p), t, Ns, reinterpret_cast<float2(*)[16]>(w[t].data()));
         if (is_last) { v[t] = w[t]; continue; }
         int k = t & (Ns - 1), out = (t - k) * 16 + k;
         for (int r = 0; r < 16; ++r) b[cur ^ 1][fft::pad(out + r * Ns)] = w[t][r];
@@ -45,7 +45,7 @@ double check(std::mt19937& g, const std::vector<float2_>& tw) {
       for (int t = 0; t < T; ++t) {
         auto* ww = reinterpret_cast<float2(*)[RL]>(w[t].data());
         fft::pass_load<M, RL>(b[cur].data(), t, ww);
-        fft::pass_compute<M, RL>(tw.data(), t, Ns, ww);
+        fft::pass_compute<M, RL>(tw.data() + fft::ptw_base(M) + fft::ptw_pass_off(M, p), t, Ns, ww);
         for (int bb = 0; bb < BPT; ++bb)
           for (int r = 0; r < RL; ++r) v[t][bb + r * BPT] = ww[bb][r];
       }
@@ -68,11 +68,17 @@ double check(std::mt19937& g, const std::vector<float2_>& tw) {
 }
 
 int main() {
-  std::vector<float2_> tw(TWIDDLE_N);
-  for (int m = 0; m < TWIDDLE_N; ++m) {
-    double a = 2.0 * M_PI * m / TWIDDLE_N;
-    tw[m] = float2_{float(std::cos(a)), float(-std::sin(a))};
-  }
+  // pass twiddle tables: W_{Ns R}^{r k} at [(r-1) Ns + k], concatenated over M
+  std::vector<float2_> tw(fft::PTW_TOTAL);
+  for (int M = 512; M <= 8192; M *= 2)
+    for (int pass = 1, Ns = 16; pass < fft::geo_npass(M); ++pass, Ns *= 16) {
+      const int R = fft::pass_radix(M, pass);
+      for (int r = 1; r < R; ++r)
+        for (int k = 0; k < Ns; ++k) {
+          double a = -2.0 * M_PI * double(r) * k / (double(Ns) * R);
+          tw[fft::ptw_base(M) + fft::ptw_pass_off(M, pass) + (r - 1) * Ns + k] = float2_{float(std::cos(a)), float(std::sin(a))};
+        }
+    }
   std::mt19937 g(7);
   std::printf("512 %.3e\n", check<512>(g, tw));
   std::printf("1024 %.3e\n", check<1024>(g, tw));
