@@ -80,42 +80,53 @@ def algorithmic_bytes(g, string, steps_nodes, L):
 
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock and throttle reasons sampled through NVML every ~2 ms in a thread
+    (the timed region can be far shorter than nvidia-smi's sampling period)."""
+    REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+               "sw_power_cap": 0x4}
 
     def __init__(self, index):
-        self.rows = []
+        import threading
+        self.sm, self.reasons, self.smax, self.err = [], set(), None, None
+        self.on = False
         try:
-            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                       "-lms", "100", "-i", str(index)], stdout=subprocess.PIPE,
-                                      stderr=subprocess.DEVNULL, text=True)
-        except OSError:
-            self.p = None
-        self.t0 = time.time()
+            import pynvml
+            pynvml.nvmlInit()
+            self.nv = pynvml
+            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
+            self.smax = float(pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM))
+        except Exception as e:  # no NVML: report it
+            self.nv, self.err = None, str(e)
+        self.stop_flag = False
+        self.t = threading.Thread(target=self._run, daemon=True)
+        self.t.start()
+
+    def _run(self):
+        while not self.stop_flag and self.nv is not None:
+            if self.on:
+                try:
+                    self.sm.append(float(self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM)))
+                    r = self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                    for nm, bit in self.REASONS.items():
+                        if r & bit:
+                            self.reasons.add(nm)
+                except Exception as e:
+                    self.err = str(e)
+            time.sleep(0.002)
+
+    def start(self):
+        self.on = True
 
     def stop(self):
-        if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.p.terminate()
-        out, _ = self.p.communicate(timeout=10)
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                smax = float(f[2])
-            except ValueError:
-                continue
-            for nm, val in zip(names, f[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(nm)
-        sm.sort()
+        self.on = False
+        self.stop_flag = True
+        self.t.join(timeout=5)
+        if self.nv is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "note": f"NVML unavailable: {self.err}"}
+        sm = sorted(self.sm)
         med = sm[len(sm) // 2] if sm else None
-        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": med, "sm_max_mhz": self.smax, "reasons": sorted(self.reasons), "samples": len(sm),
+                "source": "NVML during the timed region"}
 
 
 def peaks():
@@ -281,6 +292,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
+    sampler.start()
     t_start.record(stream)
     for it in range(args.steps):
         e0[it].record(stream)

@@ -35,7 +35,7 @@ struct alignas(16) LossRow {
 };
 
 constexpr int TWIDDLE_N = 8192;   // twiddle table size: exp(-2 pi i m / 8192)
-constexpr int EW_TILE = 1024;     // samples per elementwise work item (one float4 per thread)
+constexpr int EW_TILE = 4096;     // samples per elementwise work item (4 float4 per thread and channel)
 constexpr int N_RES = 3;          // loss resolutions 512, 1024, 2048
 
 // status bits written by kernels

@@ -28,23 +28,65 @@ struct Ew {
   }
 };
 
+constexpr int EW_Q = EW_TILE / 1024;  // quads per thread and channel in one tile
+
+// The thread's EW_Q quads (stride 1024 samples) of both channels, summed over the
+// in-edges (ADJ = false: u, Eq. 1b) or over the consumers' input adjoints (ADJ = true).
+// All loads of an edge are issued before any is used.
+template <bool ADJ>
+__device__ __forceinline__ void gather_q(const DevCtx& c, int v, int t, int len, int pitch, float4 (&l)[EW_Q],
+                                         float4 (&r)[EW_Q]) {
+#pragma unroll
+  for (int q = 0; q < EW_Q; ++q) l[q] = r[q] = f4zero();
+  const int e0 = ADJ ? c.tcsr_ptr[v] : c.csr_ptr[v];
+  const int e1 = ADJ ? c.tcsr_ptr[v + 1] : c.csr_ptr[v + 1];
+  for (int e = e0; e < e1; ++e) {
+    const NodeDev s = c.nodes[ADJ ? c.tcsr_dst[e] : c.csr_src[e]];
+    const float* row = ADJ ? arow(c, s) : yrow(c, s);
+    float4 a[EW_Q], b[EW_Q];
+#pragma unroll
+    for (int q = 0; q < EW_Q; ++q) {
+      const int tq = t + 1024 * q;
+      if (tq < len) {
+        a[q] = ld4(row + tq);
+        b[q] = ld4(row + pitch + tq);
+      } else {
+        a[q] = b[q] = f4zero();
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < EW_Q; ++q) {
+      l[q] = f4add(l[q], a[q]);
+      r[q] = f4add(r[q], b[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < EW_Q; ++q) {
+    l[q] = mask4(l[q], t + 1024 * q, len);
+    r[q] = mask4(r[q], t + 1024 * q, len);
+  }
+}
+
 template <int TYPE>
 __global__ void __launch_bounds__(256) k_ew_fwd(DevCtx c, int item0, int n_items) {
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
-    const int v = w.x, t0 = w.y;
+    const int v = w.x, t = w.y + 4 * threadIdx.x;
     const NodeDev nd = c.nodes[v];
     float p[2] = {0.f, 0.f};
     if (TYPE == GRAFX_T_GAIN) { p[0] = c.params[nd.prow * 2]; p[1] = c.params[nd.prow * 2 + 1]; }
     if (TYPE == GRAFX_T_IMAGER) p[0] = c.params[nd.prow];
     float* y = yrow_w(c, nd);
-    const int t1 = min(t0 + EW_TILE, nd.len);
-    for (int t = t0 + 4 * threadIdx.x; t < t1; t += 4 * blockDim.x) {
-      float4 l = gather_in(c, v, 0, t, nd.len, nd.pitch);
-      float4 r = gather_in(c, v, 1, t, nd.len, nd.pitch);
-      Ew<TYPE>::fwd(p, l, r);
-      st4(y + t, l);
-      st4(y + nd.pitch + t, r);
+    float4 l[EW_Q], r[EW_Q];
+    gather_q<false>(c, v, t, nd.len, nd.pitch, l, r);
+#pragma unroll
+    for (int q = 0; q < EW_Q; ++q) {
+      const int tq = t + 1024 * q;
+      if (tq < nd.len) {
+        Ew<TYPE>::fwd(p, l[q], r[q]);
+        st4(y + tq, l[q]);
+        st4(y + nd.pitch + tq, r[q]);
+      }
     }
   }
 }
@@ -54,39 +96,40 @@ __global__ void __launch_bounds__(256) k_ew_fwd(DevCtx c, int item0, int n_items
 template <int TYPE>
 __global__ void __launch_bounds__(256) k_ew_bwd(DevCtx c, int item0, int n_items) {
   __shared__ float sh[4 * 32];
+  constexpr bool needs_u = TYPE == GRAFX_T_GAIN || TYPE == GRAFX_T_IMAGER;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
-    const int v = w.x, t0 = w.y;
+    const int v = w.x, t = w.y + 4 * threadIdx.x;
     const NodeDev nd = c.nodes[v];
     float a0 = 1.f, a1 = 1.f;
     if (TYPE == GRAFX_T_GAIN) { a0 = expf(c.params[nd.prow * 2]); a1 = expf(c.params[nd.prow * 2 + 1]); }
     if (TYPE == GRAFX_T_IMAGER) a0 = expf(c.params[nd.prow]);
     float acc[2] = {0.f, 0.f};
     float* ub = arow_w(c, nd);
-    const int t1 = min(t0 + EW_TILE, nd.len);
-    for (int t = t0 + 4 * threadIdx.x; t < t1; t += 4 * blockDim.x) {
-      float4 bl = gather_out_adj(c, v, 0, t, nd.len, nd.pitch);
-      float4 br = gather_out_adj(c, v, 1, t, nd.len, nd.pitch);
+    float4 bl[EW_Q], br[EW_Q], ul[EW_Q], ur[EW_Q];
+    gather_q<true>(c, v, t, nd.len, nd.pitch, bl, br);
+    if (needs_u) gather_q<false>(c, v, t, nd.len, nd.pitch, ul, ur);
+#pragma unroll
+    for (int q = 0; q < EW_Q; ++q) {
+      const int tq = t + 1024 * q;
+      if (tq >= nd.len) continue;
       if (TYPE == GRAFX_T_GAIN) {
-        float4 ul = gather_in(c, v, 0, t, nd.len, nd.pitch);
-        float4 ur = gather_in(c, v, 1, t, nd.len, nd.pitch);
-        acc[0] += bl.x * ul.x + bl.y * ul.y + bl.z * ul.z + bl.w * ul.w;
-        acc[1] += br.x * ur.x + br.y * ur.y + br.z * ur.z + br.w * ur.w;
-        bl = make_float4(a0 * bl.x, a0 * bl.y, a0 * bl.z, a0 * bl.w);
-        br = make_float4(a1 * br.x, a1 * br.y, a1 * br.z, a1 * br.w);
+        acc[0] += bl[q].x * ul[q].x + bl[q].y * ul[q].y + bl[q].z * ul[q].z + bl[q].w * ul[q].w;
+        acc[1] += br[q].x * ur[q].x + br[q].y * ur[q].y + br[q].z * ur[q].z + br[q].w * ur[q].w;
+        bl[q] = make_float4(a0 * bl[q].x, a0 * bl[q].y, a0 * bl[q].z, a0 * bl[q].w);
+        br[q] = make_float4(a1 * br[q].x, a1 * br[q].y, a1 * br[q].z, a1 * br[q].w);
       } else if (TYPE == GRAFX_T_IMAGER) {
-        float4 ul = gather_in(c, v, 0, t, nd.len, nd.pitch);
-        float4 ur = gather_in(c, v, 1, t, nd.len, nd.pitch);
-        float4 mb = make_float4(0.5f * (bl.x + br.x), 0.5f * (bl.y + br.y), 0.5f * (bl.z + br.z), 0.5f * (bl.w + br.w));
-        float4 sb = make_float4(0.5f * (bl.x - br.x), 0.5f * (bl.y - br.y), 0.5f * (bl.z - br.z), 0.5f * (bl.w - br.w));
-        acc[0] += sb.x * (ul.x - ur.x) + sb.y * (ul.y - ur.y) + sb.z * (ul.z - ur.z) + sb.w * (ul.w - ur.w);
-        bl = make_float4(mb.x + a0 * sb.x, mb.y + a0 * sb.y, mb.z + a0 * sb.z, mb.w + a0 * sb.w);
-        br = make_float4(mb.x - a0 * sb.x, mb.y - a0 * sb.y, mb.z - a0 * sb.z, mb.w - a0 * sb.w);
+        const float4 L = bl[q], R = br[q], u0 = ul[q], u1 = ur[q];
+        float4 mb = make_float4(0.5f * (L.x + R.x), 0.5f * (L.y + R.y), 0.5f * (L.z + R.z), 0.5f * (L.w + R.w));
+        float4 sb = make_float4(0.5f * (L.x - R.x), 0.5f * (L.y - R.y), 0.5f * (L.z - R.z), 0.5f * (L.w - R.w));
+        acc[0] += sb.x * (u0.x - u1.x) + sb.y * (u0.y - u1.y) + sb.z * (u0.z - u1.z) + sb.w * (u0.w - u1.w);
+        bl[q] = make_float4(mb.x + a0 * sb.x, mb.y + a0 * sb.y, mb.z + a0 * sb.z, mb.w + a0 * sb.w);
+        br[q] = make_float4(mb.x - a0 * sb.x, mb.y - a0 * sb.y, mb.z - a0 * sb.z, mb.w - a0 * sb.w);
       }
-      st4(ub + t, bl);
-      st4(ub + nd.pitch + t, br);
+      st4(ub + tq, bl[q]);
+      st4(ub + nd.pitch + tq, br[q]);
     }
-    if (TYPE == GRAFX_T_GAIN || TYPE == GRAFX_T_IMAGER) {
+    if (needs_u) {
       block_sum<2>(acc, sh);
       if (threadIdx.x == 0) c.partial[w.w] = make_float4(a0 * acc[0], a1 * acc[1], 0.f, 0.f);
       __syncthreads();
