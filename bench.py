@@ -79,6 +79,40 @@ def algorithmic_bytes(g, string, steps_nodes, L):
     return fwd, bwd
 
 
+class _Nvml:
+    """The three NVML queries the sampler needs, through ctypes on libnvidia-ml."""
+
+    def __init__(self, index):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("nvmlDeviceGetHandleByIndex failed")
+
+    def _clock(self, fn):
+        v = self.ct.c_uint()
+        if fn(self.h, self.ct.c_int(1), self.ct.byref(v)) != 0:  # NVML_CLOCK_SM = 1
+            raise RuntimeError("clock query failed")
+        return v.value
+
+    def sm(self):
+        return self._clock(self.lib.nvmlDeviceGetClockInfo)
+
+    def max_sm(self):
+        return self._clock(self.lib.nvmlDeviceGetMaxClockInfo)
+
+    def reasons(self):
+        v = self.ct.c_ulonglong()
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        if fn(self.h, self.ct.byref(v)) != 0:
+            raise RuntimeError("reasons query failed")
+        return v.value
+
+
 class ClockSampler:
     """SM clock and throttle reasons sampled through NVML every ~2 ms in a thread
     (the timed region can be far shorter than nvidia-smi's sampling period)."""
@@ -90,11 +124,8 @@ class ClockSampler:
         self.sm, self.reasons, self.smax, self.err = [], set(), None, None
         self.on = False
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            self.nv = pynvml
-            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
-            self.smax = float(pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM))
+            self.nv = _Nvml(index)
+            self.smax = float(self.nv.max_sm())
         except Exception as e:  # no NVML: report it
             self.nv, self.err = None, str(e)
         self.stop_flag = False
@@ -105,8 +136,8 @@ class ClockSampler:
         while not self.stop_flag and self.nv is not None:
             if self.on:
                 try:
-                    self.sm.append(float(self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM)))
-                    r = self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                    self.sm.append(float(self.nv.sm()))
+                    r = self.nv.reasons()
                     for nm, bit in self.REASONS.items():
                         if r & bit:
                             self.reasons.add(nm)

@@ -216,6 +216,23 @@ int grafx_sync_status(grafx_plan* p, void* stream);
  * grafx_mrstft_* call on this plan (for launch accounting). */
 int grafx_last_launch_count(const grafx_plan* p, int32_t* n);
 
+/* ---------------------------------------------------------------- fitting (Adam)
+ * Gradient descent on every processor's parameters (Abstract; Sec. 4 "Example usage").
+ * The optimiser works on unconstrained theta; the processors see p = map(theta),
+ * element-wise by a per-column code (codes[i % cols]):
+ *   0 identity; 1 alpha = 0.9 + 0.0999 sigmoid(theta); 2 softplus(theta);
+ *   3 1 + softplus(theta); 4 -softplus(theta).
+ * grafx_adam_step: one Adam update (bias-corrected, step >= 1) of n elements, in place:
+ * theta, m, v (device float32, m and v zero before step 1) and param (written with
+ * map(theta_new)); grad_param = dLoss/dp from grafx_backprop at the old param.
+ * codes: device int8[cols].  Asynchronous on `stream`. */
+int grafx_adam_step(float* theta, float* m, float* v, const float* grad_param, float* param,
+                    const int8_t* codes, int32_t cols, int64_t n, int32_t step, float lr, float beta1,
+                    float beta2, float eps, void* stream);
+/* theta = inverse map of param (to start a fit from physical parameters). */
+int grafx_params_to_theta(const float* param, const int8_t* codes, int32_t cols, int64_t n, float* theta,
+                          void* stream);
+
 /* ---------------------------------------------------------------- allocation-free compressor
  * The paper has no counterpart to this call; it exists for callers that must not
  * allocate device memory at all, such as real-time audio callbacks and plugin hosts

@@ -1,0 +1,86 @@
+"""Parameter fitting by gradient descent: Adam on unconstrained parameters (FP64 oracle;
+test infrastructure only, see ``oracle/__init__``).
+
+The paper fits every processor's parameters of a large graph by gradient descent to
+match a target mix (Abstract; Sec. 4 "Example usage") without naming the optimiser or
+how constrained parameters are handled.  Reading used here: Adam (Kingma & Ba, the
+published algorithm with bias correction) on unconstrained theta; the processors take
+physical parameters p = map(theta), element-wise:
+
+  IDENT     p = theta                              (gains, bands, thresholds, ...)
+  ALPHA     p = 0.9 + 0.0999 * sigmoid(theta)      (compressor coefficient in (0.9, 0.9999))
+  SOFTPLUS  p = softplus(theta)                    (knee half-width W > 0)
+  RATIO     p = 1 + softplus(theta)                (ratio R > 1)
+  NEGSP     p = -softplus(theta)                   (per-frame decay, < 0)
+
+dLoss/dtheta = dLoss/dp * dp/dtheta.
+"""
+import numpy as np
+
+IDENT, ALPHA, SOFTPLUS, RATIO, NEGSP = range(5)
+
+
+def softplus(x):
+    return np.logaddexp(0.0, x)
+
+
+def sigmoid(x):
+    return 0.5 * (1.0 + np.tanh(0.5 * x))
+
+
+def to_param(theta, code):
+    theta = np.asarray(theta, dtype=np.float64)
+    code = np.broadcast_to(code, theta.shape)
+    out = theta.copy()
+    out = np.where(code == ALPHA, 0.9 + 0.0999 * sigmoid(theta), out)
+    out = np.where(code == SOFTPLUS, softplus(theta), out)
+    out = np.where(code == RATIO, 1.0 + softplus(theta), out)
+    out = np.where(code == NEGSP, -softplus(theta), out)
+    return out
+
+
+def dparam_dtheta(theta, code):
+    theta = np.asarray(theta, dtype=np.float64)
+    code = np.broadcast_to(code, theta.shape)
+    s = sigmoid(theta)
+    d = np.ones_like(theta)
+    d = np.where(code == ALPHA, 0.0999 * s * (1.0 - s), d)
+    d = np.where((code == SOFTPLUS) | (code == RATIO), s, d)   # softplus' = sigmoid
+    d = np.where(code == NEGSP, -s, d)
+    return d
+
+
+def to_theta(param, code):
+    """Inverse of ``to_param`` (for starting a fit from physical parameters)."""
+    p = np.asarray(param, dtype=np.float64)
+    code = np.broadcast_to(code, p.shape)
+    out = p.copy()
+    with np.errstate(divide="ignore", invalid="ignore"):
+        a = (p - 0.9) / 0.0999
+        out = np.where(code == ALPHA, np.log(a) - np.log1p(-a), out)
+        out = np.where(code == SOFTPLUS, p + np.log(-np.expm1(-p)), out)
+        out = np.where(code == RATIO, (p - 1) + np.log(-np.expm1(-(p - 1))), out)
+        out = np.where(code == NEGSP, -p + np.log(-np.expm1(p)), out)
+    return out
+
+
+def adam_step(theta, m, v, grad_theta, t, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (step t >= 1); returns new (theta, m, v)."""
+    g = np.asarray(grad_theta, dtype=np.float64)
+    m = beta1 * m + (1 - beta1) * g
+    v = beta2 * v + (1 - beta2) * g * g
+    mh = m / (1 - beta1 ** t)
+    vh = v / (1 - beta2 ** t)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def param_codes(t, cols):
+    """Map code of every column of P[t] (type ids as in synth.types)."""
+    codes = np.full(cols, IDENT, dtype=np.int8)
+    if t == 6:                       # compressor [alpha, T, W, R]
+        codes[:] = [ALPHA, IDENT, SOFTPLUS, RATIO]
+    if t == 8:                       # reverb: H_delta columns are decays
+        c = np.full(50, IDENT, dtype=np.int8)
+        c[:48] = np.tile(np.repeat([IDENT, NEGSP], 12), 2)
+        codes = c
+    return codes

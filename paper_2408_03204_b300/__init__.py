@@ -76,6 +76,9 @@ SIGNATURES = {
     "grafx_sync_status": (ctypes.c_int, [_P, _P]),
     "grafx_last_launch_count": (ctypes.c_int, [_P, _I32P]),
     "grafx_compressor_forward_noalloc": (ctypes.c_int, [_F, _I64, _I64, _F, _F, _P]),
+    "grafx_adam_step": (ctypes.c_int, [_F, _F, _F, _F, _F, _P, _I32, _I64, _I32, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_float, ctypes.c_float, _P]),
+    "grafx_params_to_theta": (ctypes.c_int, [_F, _P, _I32, _I64, _F, _P]),
 }
 
 

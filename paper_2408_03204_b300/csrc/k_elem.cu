@@ -68,7 +68,7 @@ __device__ __forceinline__ void gather_q(const DevCtx& c, int v, int t, int len,
 }
 
 template <int TYPE>
-__global__ void __launch_bounds__(256) k_ew_fwd(DevCtx c, int item0, int n_items) {
+__global__ void __launch_bounds__(256, 4) k_ew_fwd(DevCtx c, int item0, int n_items) {
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
     const int v = w.x, t = w.y + 4 * threadIdx.x;
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) k_ew_fwd(DevCtx c, int item0, int n_items
 // Backward: ybar = sum of the consumers' input adjoints; ubar = (df/du)^T ybar;
 // parameter-gradient partial of the tile into its own slot (no atomics).
 template <int TYPE>
-__global__ void __launch_bounds__(256) k_ew_bwd(DevCtx c, int item0, int n_items) {
+__global__ void __launch_bounds__(256, 3) k_ew_bwd(DevCtx c, int item0, int n_items) {
   __shared__ float sh[4 * 32];
   constexpr bool needs_u = TYPE == GRAFX_T_GAIN || TYPE == GRAFX_T_IMAGER;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {

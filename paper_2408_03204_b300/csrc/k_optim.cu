@@ -1,0 +1,104 @@
+// Gradient-descent fitting of processor parameters (the paper's GD application,
+// Abstract and Sec. 4): Adam on unconstrained theta, element-wise maps theta -> p to
+// the processors' physical parameters, and their chain rule, fused in one kernel.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "plan.h"
+
+namespace grafx {
+
+enum : int8_t { MAP_IDENT = 0, MAP_ALPHA = 1, MAP_SOFTPLUS = 2, MAP_RATIO = 3, MAP_NEGSP = 4 };
+
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.f / (1.f + expf(-x)); }
+__device__ __forceinline__ float softplusf_(float x) { return x > 20.f ? x : log1pf(expf(x)); }
+
+__device__ __forceinline__ float map_param(float th, int code) {
+  switch (code) {
+    case MAP_ALPHA: return 0.9f + 0.0999f * sigmoidf_(th);
+    case MAP_SOFTPLUS: return softplusf_(th);
+    case MAP_RATIO: return 1.f + softplusf_(th);
+    case MAP_NEGSP: return -softplusf_(th);
+    default: return th;
+  }
+}
+
+__device__ __forceinline__ float map_slope(float th, int code) {
+  const float s = sigmoidf_(th);
+  switch (code) {
+    case MAP_ALPHA: return 0.0999f * s * (1.f - s);
+    case MAP_SOFTPLUS:
+    case MAP_RATIO: return s;
+    case MAP_NEGSP: return -s;
+    default: return 1.f;
+  }
+}
+
+// theta <- inverse map of p (start of a fit from physical parameters).
+__device__ __forceinline__ float unmap_param(float p, int code) {
+  switch (code) {
+    case MAP_ALPHA: {
+      float a = (p - 0.9f) / 0.0999f;
+      return logf(a) - log1pf(-a);
+    }
+    case MAP_SOFTPLUS: return p + logf(-expm1f(-p));
+    case MAP_RATIO: return (p - 1.f) + logf(-expm1f(-(p - 1.f)));
+    case MAP_NEGSP: return -p + logf(-expm1f(p));
+    default: return p;
+  }
+}
+
+__global__ void k_adam(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ gp, float* __restrict__ p, const int8_t* __restrict__ codes,
+                       int cols, int64_t n, float lr, float b1, float b2, float eps, float bc1, float bc2) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int code = codes[i % cols];
+    const float th = theta[i];
+    const float g = gp[i] * map_slope(th, code);
+    const float mi = b1 * m[i] + (1.f - b1) * g;
+    const float vi = b2 * v[i] + (1.f - b2) * g * g;
+    const float nt = th - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    m[i] = mi;
+    v[i] = vi;
+    theta[i] = nt;
+    p[i] = map_param(nt, code);
+  }
+}
+
+__global__ void k_to_theta(const float* __restrict__ p, const int8_t* __restrict__ codes, int cols, int64_t n,
+                           float* __restrict__ theta) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    theta[i] = unmap_param(p[i], codes[i % cols]);
+}
+
+}  // namespace grafx
+
+using namespace grafx;
+
+extern "C" int grafx_adam_step(float* theta, float* m, float* v, const float* grad_param, float* param,
+                               const int8_t* codes, int32_t cols, int64_t n, int32_t step, float lr, float beta1,
+                               float beta2, float eps, void* stream) {
+  if (!theta || !m || !v || !grad_param || !param || !codes) return fail(GRAFX_EINVAL, "null argument");
+  if (n < 0 || cols < 1 || step < 1) return fail(GRAFX_EINVAL, "need n >= 0, cols >= 1, step >= 1");
+  if (n == 0) return GRAFX_OK;
+  const float bc1 = float(1.0 - std::pow(double(beta1), step));
+  const float bc2 = float(1.0 - std::pow(double(beta2), step));
+  const int g = int(std::min<int64_t>((n + 255) / 256, 148 * 8));
+  k_adam<<<g, 256, 0, static_cast<cudaStream_t>(stream)>>>(theta, m, v, grad_param, param, codes, cols, n, lr,
+                                                            beta1, beta2, eps, bc1, bc2);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GRAFX_OK : fail(GRAFX_ECUDA, cudaGetErrorString(e));
+}
+
+extern "C" int grafx_params_to_theta(const float* param, const int8_t* codes, int32_t cols, int64_t n, float* theta,
+                                     void* stream) {
+  if (!param || !codes || !theta) return fail(GRAFX_EINVAL, "null argument");
+  if (n < 0 || cols < 1) return fail(GRAFX_EINVAL, "need n >= 0, cols >= 1");
+  if (n == 0) return GRAFX_OK;
+  const int g = int(std::min<int64_t>((n + 255) / 256, 148 * 8));
+  k_to_theta<<<g, 256, 0, static_cast<cudaStream_t>(stream)>>>(param, codes, cols, n, theta);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GRAFX_OK : fail(GRAFX_ECUDA, cudaGetErrorString(e));
+}

@@ -1,0 +1,54 @@
+"""GPU parity of the fused Adam update with parameter maps (grafx_adam_step) and the
+inverse map (grafx_params_to_theta) against the FP64 oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import optim as oo
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2408_03204_b300 import build
+    build.build()
+
+
+def test_adam_steps_match_oracle():
+    import torch
+    import paper_2408_03204_b300 as gx
+    lib = gx.lib()
+    rng = np.random.Generator(np.random.PCG64(5))
+    rows, cols = 37, 4
+    codes = oo.param_codes(6, cols)
+    P0 = np.stack([rng.uniform(0.91, 0.999, rows), rng.uniform(-9, 0, rows), rng.uniform(0.3, 1.0, rows),
+                   rng.uniform(1.2, 8, rows)], axis=1).astype(np.float32)
+    dev = torch.device("cuda")
+    p = torch.tensor(P0, device=dev)
+    cd = torch.tensor(codes, device=dev)
+    th = torch.empty_like(p)
+    st = gx._stream(torch, dev)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    assert lib.grafx_params_to_theta(ptr(p), ptr(cd), cols, p.numel(), ptr(th), st) == 0
+    torch.cuda.synchronize()
+    th_ref = oo.to_theta(P0.astype(np.float64), codes)
+    np.testing.assert_allclose(th.cpu().numpy(), th_ref, rtol=2e-5, atol=2e-5)
+    th_o = th.cpu().numpy().astype(np.float64)      # continue both from the same theta
+    m, v = torch.zeros_like(p), torch.zeros_like(p)
+    mo, vo = np.zeros_like(th_o), np.zeros_like(th_o)
+    for t in range(1, 6):
+        gp = rng.standard_normal((rows, cols)).astype(np.float32)
+        g = torch.tensor(gp, device=dev)
+        assert lib.grafx_adam_step(ptr(th), ptr(m), ptr(v), ptr(g), ptr(p), ptr(cd), cols, p.numel(), t,
+                                   ctypes.c_float(1e-2), ctypes.c_float(0.9), ctypes.c_float(0.999),
+                                   ctypes.c_float(1e-8), st) == 0
+        gth = gp.astype(np.float64) * oo.dparam_dtheta(th_o, codes)
+        th_o, mo, vo = oo.adam_step(th_o, mo, vo, gth, t, lr=1e-2)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(th.cpu().numpy(), th_o, rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(p.cpu().numpy(), oo.to_param(th_o, codes), rtol=1e-5, atol=1e-6)
