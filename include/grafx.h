@@ -216,6 +216,23 @@ int grafx_sync_status(grafx_plan* p, void* stream);
  * grafx_mrstft_* call on this plan (for launch accounting). */
 int grafx_last_launch_count(const grafx_plan* p, int32_t* n);
 
+/* ---------------------------------------------------------------- one fit step as a CUDA graph
+ * Batched rendering replays a fixed launch sequence per plan (Sec. 2 "Batched
+ * processing": the schedule and index maps are computed once), so a whole step --
+ * render, loss, loss gradient and backprop, with the buffers given here -- is
+ * recorded once into a CUDA graph and replayed with one launch.  The buffers and the
+ * bound parameters are baked in: replays read their current contents.  d_params and
+ * d_sources follow grafx_backprop.  Create runs no kernel itself (it captures on
+ * `stream`); the graph is owned by the library until grafx_step_graph_destroy. */
+typedef struct grafx_step_graph grafx_step_graph;
+int grafx_step_graph_create(grafx_plan* p, const float* sources, float* out, const float* target, float* loss,
+                            float* d_out, float* const* d_params, float* d_sources, void* stream,
+                            grafx_step_graph** out_graph);
+int grafx_step_graph_launch(grafx_step_graph* g, void* stream);
+/* Number of kernels one replay launches. */
+int grafx_step_graph_launches(const grafx_step_graph* g, int32_t* n);
+int grafx_step_graph_destroy(grafx_step_graph* g);
+
 /* ---------------------------------------------------------------- fitting (Adam)
  * Gradient descent on every processor's parameters (Abstract; Sec. 4 "Example usage").
  * The optimiser works on unconstrained theta; the processors see p = map(theta),

@@ -79,6 +79,11 @@ SIGNATURES = {
     "grafx_adam_step": (ctypes.c_int, [_F, _F, _F, _F, _F, _P, _I32, _I64, _I32, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_float, ctypes.c_float, _P]),
     "grafx_params_to_theta": (ctypes.c_int, [_F, _P, _I32, _I64, _F, _P]),
+    "grafx_step_graph_create": (ctypes.c_int, [_P, _F, _F, _F, _F, _F, ctypes.POINTER(_P), _F, _P,
+                                               ctypes.POINTER(_P)]),
+    "grafx_step_graph_launch": (ctypes.c_int, [_P, _P]),
+    "grafx_step_graph_launches": (ctypes.c_int, [_P, _I32P]),
+    "grafx_step_graph_destroy": (ctypes.c_int, [_P]),
 }
 
 
@@ -231,6 +236,15 @@ class Plan:
     def loss_backward_raw(self, out, target, d_out, stream):
         _check(lib().grafx_mrstft_backward(self._h, _ptr(out), _ptr(target), _ptr(d_out), stream))
 
+    def capture_step(self, sources, out, target, loss, d_out, d_params, d_sources, stream):
+        """Record render + loss + loss gradient + backprop with these buffers as one CUDA
+        graph; returns a StepGraph whose launch() replays it."""
+        arr = (_P * N_TYPES)(*[_ptr(d_params.get(t)) for t in range(N_TYPES)])
+        h = _P()
+        _check(lib().grafx_step_graph_create(self._h, _ptr(sources), _ptr(out), _ptr(target), _ptr(loss),
+                                             _ptr(d_out), arr, _ptr(d_sources), stream, ctypes.byref(h)))
+        return StepGraph(h, (sources, out, target, loss, d_out, d_params, d_sources))
+
     def sync_status(self, stream=None):
         import torch
         s = stream if stream is not None else _stream(torch, self.ws.device)
@@ -240,6 +254,26 @@ class Plan:
         n = ctypes.c_int32()
         _check(lib().grafx_last_launch_count(self._h, ctypes.byref(n)))
         return n.value
+
+
+class StepGraph:
+    """A captured fit step (grafx_step_graph_*); keeps its buffers alive."""
+
+    def __init__(self, h, keep):
+        self._h, self._keep = h, keep
+
+    def launch(self, stream):
+        _check(lib().grafx_step_graph_launch(self._h, stream))
+
+    def launches(self):
+        n = ctypes.c_int32()
+        _check(lib().grafx_step_graph_launches(self._h, ctypes.byref(n)))
+        return n.value
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.grafx_step_graph_destroy(self._h)
+            self._h = None
 
 
 def _autograd():

@@ -412,4 +412,73 @@ int grafx_last_launch_count(const grafx_plan* p, int32_t* n) {
   return GRAFX_OK;
 }
 
+struct grafx_step_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int32_t launches = 0;
+};
+
+int grafx_step_graph_create(grafx_plan* p, const float* sources, float* out, const float* target, float* loss,
+                            float* d_out, float* const* d_params, float* d_sources, void* stream,
+                            grafx_step_graph** out_graph) {
+  GX_TRY
+  if (!p || !sources || !out || !target || !loss || !d_out || !out_graph) return fail(GRAFX_EINVAL, "null argument");
+  int rc = check_ready(p);
+  if (rc) return rc;
+  if (!p->loss.ok) return fail(GRAFX_ESHAPE, "every output length must be >= 2048 for the STFT loss");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // kernel attributes are set outside the capture
+  DevCtx c0 = make_ctx(p, sources, out, nullptr, nullptr);
+  launch_eq(-1, c0, 0, 0, s);
+  launch_loss(-1, make_loss(p, out, target), s);
+  rc = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+  if (rc) return rc;
+  int32_t n = 0;
+  int st = grafx_render(p, sources, out, stream);
+  n += p->last_launches;
+  if (!st) st = grafx_mrstft_forward(p, out, target, loss, stream), n += p->last_launches;
+  if (!st) st = grafx_mrstft_backward(p, out, target, d_out, stream), n += p->last_launches;
+  if (!st) st = grafx_backprop(p, sources, d_out, d_params, d_sources, stream), n += p->last_launches;
+  std::string err = st ? grafx_last_error() : "";
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (st) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(st, "during capture: " + err);
+  }
+  if (e != cudaSuccess) return fail(GRAFX_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(GRAFX_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+  }
+  grafx_step_graph* g = new grafx_step_graph();
+  g->graph = graph;
+  g->exec = exec;
+  g->launches = n;
+  *out_graph = g;
+  return GRAFX_OK;
+  GX_CATCH
+}
+
+int grafx_step_graph_launch(grafx_step_graph* g, void* stream) {
+  if (!g) return fail(GRAFX_EINVAL, "null graph");
+  return cuda_check(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)), "graph launch");
+}
+
+int grafx_step_graph_launches(const grafx_step_graph* g, int32_t* n) {
+  if (!g || !n) return fail(GRAFX_EINVAL, "null argument");
+  *n = g->launches;
+  return GRAFX_OK;
+}
+
+int grafx_step_graph_destroy(grafx_step_graph* g) {
+  if (!g) return GRAFX_OK;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+  return GRAFX_OK;
+}
+
 }  // extern "C"

@@ -321,6 +321,7 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
     cudaFuncSetAttribute(k_eq_bwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(3 * s1));
     init = true;
   }
+  if (what < 0) return 0;  // attributes only (before a stream capture)
   const int chunks_h = (c.eq_H + 1 + EQ_CHUNK - 1) / EQ_CHUNK;
   const int chunks_k = ((c.eq_taps + 1) / 2 + EQ_CHUNK - 1) / EQ_CHUNK;
   switch (what) {
@@ -341,7 +342,7 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
 
 // what: 0 design(node range), 1 fwd(items), 2 bwd(items), 3 finalize(node range)
 int launch_eq(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
-  if (b <= 0 || (what == 0 || what == 3) && b <= a) return 0;
+  if (what >= 0 && (b <= 0 || ((what == 0 || what == 3) && b <= a))) return 0;
   switch (c.eq_fft) {
     case 1024: return eq_launch<1024>(what, c, a, b, s);
     case 2048: return eq_launch<2048>(what, c, a, b, s);

@@ -285,7 +285,7 @@ int launch_loss(int what, const LossLaunch& L, cudaStream_t s) {
     cudaFuncSetAttribute(k_loss_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     init = true;
   }
-  if (L.n_items <= 0) return 0;
+  if (what < 0 || L.n_items <= 0) return 0;
   LossArgs a{L.rows, L.items, L.y, L.tgt, L.part, L.stats, L.frames, L.tw, L.ptw, L.n_items};
   const int g = grid_size(L.n_items, 3);
   if (what == 0) {

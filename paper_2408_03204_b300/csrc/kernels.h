@@ -16,7 +16,7 @@ int launch_ew_finalize(const DevCtx& c, int node_begin, int node_end, int cols, 
 
 // EQ: what = 0 design (a = node_begin, b = node_end), 1 forward (a = item0,
 // b = n_items), 2 backward (items), 3 gradient finalize (node range)
-int launch_eq(int what, const DevCtx& c, int a, int b, cudaStream_t s);
+int launch_eq(int what, const DevCtx& c, int a, int b, cudaStream_t s);  // what < 0: set kernel attributes only
 
 // compressor: what = 0 forward, 1 backward (a = item0, b = n_items, ticket index),
 // 2 gradient finalize (a = node_begin, b = node_end)
@@ -40,6 +40,6 @@ struct LossLaunch {
   float* d_out;
 };
 // what = 0 forward (statistics + reduce into *loss), 2 backward (frames + overlap-add into d_out)
-int launch_loss(int what, const LossLaunch& L, cudaStream_t s);
+int launch_loss(int what, const LossLaunch& L, cudaStream_t s);  // what < 0: set kernel attributes only
 
 }  // namespace grafx

@@ -1,0 +1,69 @@
+"""CUDA-graph replay of a whole fit step and the tile autotuner (batched rendering,
+a fixed launch sequence per plan): replays must equal the eager calls exactly, and a
+tuned plan must render the same mix as the default one."""
+import numpy as np
+import pytest
+
+import synth
+from tests.gpu_common import GpuRun, assert_out_close, flat_sources, union_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2408_03204_b300 import build
+    build.build()
+
+
+def test_step_graph_replay_equals_eager():
+    import torch
+    g = synth.console_cfg2(tracks=12, levels=2)
+    L = 8192
+    src_flat, _ = flat_sources([g], [L], [3])
+    run = GpuRun([g], [L], union_params([g], 7), src_flat, eq_taps=255)
+    st = run.gx._stream(torch, run.src.device)
+    tgt = run.render().clone() * 0.5 + 0.01
+    out, loss, d_out = torch.empty_like(tgt), torch.empty(1, device="cuda"), torch.empty_like(tgt)
+    dP = {t: torch.empty_like(p) for t, p in run.P.items()}
+    # eager reference
+    run.plan.render_raw(run.src, out, st)
+    run.plan.loss_raw(out, tgt, loss, st)
+    run.plan.loss_backward_raw(out, tgt, d_out, st)
+    run.plan.backprop_raw(run.src, d_out, dP, None, st)
+    torch.cuda.synchronize()
+    ref = (out.clone(), loss.clone(), {t: v.clone() for t, v in dP.items()})
+    graph = run.plan.capture_step(run.src, out, tgt, loss, d_out, dP, None, st)
+    assert graph.launches() > 10
+    for _ in range(2):
+        out.zero_(); loss.zero_()
+        for v in dP.values():
+            v.zero_()
+        graph.launch(st)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref[0]) and torch.equal(loss, ref[1])
+        for t in dP:
+            assert torch.equal(dP[t], ref[2][t]), t
+    run.plan.sync_status(st)
+
+
+def test_autotuner_picks_valid_tiles(tmp_path):
+    import paper_2408_03204_b300 as gx
+    from paper_2408_03204_b300 import autotune
+    g = synth.console_cfg1()
+    L = 2 ** 14
+    lists = [[g.types, [list(e) for e in g.edges]]]
+    best = autotune.autotune([gx.Graph.from_lists(g.types, g.edges)], [L], graph_lists=lists, eq_taps=255,
+                             cache=str(tmp_path / "tune.json"))
+    assert best in autotune.candidates(255)
+    again = autotune.autotune([gx.Graph.from_lists(g.types, g.edges)], [L], graph_lists=lists, eq_taps=255,
+                              cache=str(tmp_path / "tune.json"))
+    assert again == best
+    src_flat, _ = flat_sources([g], [L], [1])
+    P = union_params([g], 1)
+    a = GpuRun([g], [L], P, src_flat, eq_taps=255).render().cpu().numpy()
+    b = GpuRun([g], [L], P, src_flat, eq_taps=255, **best).render().cpu().numpy()
+    assert_out_close(b, a, tol=2e-6)
