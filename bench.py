@@ -367,6 +367,20 @@ def main():
                          "frac": step_bytes / (ms_step / 1e3) / 1e9 / peak},
                 "breakdown_ms": {lab: round(float(d), 4) for lab, d in zip(labels, dur)}}
 
+    # the same step replayed as one CUDA graph (one launch per step)
+    graph = plan.capture_step(src, out, tgt, loss, d_out, dP, None, st)
+    for _ in range(3):
+        graph.launch(st)
+    torch.cuda.synchronize(dev)
+    ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ga.record(stream)
+    for _ in range(args.steps):
+        graph.launch(st)
+    gb.record(stream)
+    torch.cuda.synchronize(dev)
+    graph_ms = ga.elapsed_time(gb) / args.steps
+    plan.sync_status(st)
+
     # end to end through the C-ABI with host buffers: H2D of the step's inputs from pinned
     # memory, the step, D2H of the loss and every parameter gradient
     src_pin = torch.tensor(src_h).pin_memory()
@@ -419,7 +433,9 @@ def main():
                 "config": dict(cfg, nodes=int(info.n_nodes), processed_node_samples=node_samples,
                                schedule_steps=N, parallelism=f"replicas{world}"),
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": n_launch * args.steps}
+                "gpu_launches": n_launch * args.steps,
+                "cuda_graph": {"ms_per_step": graph_ms, "value": node_samples * world / (graph_ms / 1e3),
+                               "launches_per_step": graph.launches()}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
