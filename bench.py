@@ -368,15 +368,18 @@ def main():
                 "breakdown_ms": {lab: round(float(d), 4) for lab, d in zip(labels, dur)}}
 
     # the same step replayed as one CUDA graph (one launch per step)
-    graph = plan.capture_step(src, out, tgt, loss, d_out, dP, None, st)
+    side = torch.cuda.Stream(dev)
+    ss = gx._stream_of(side)
+    torch.cuda.synchronize(dev)
+    graph = plan.capture_step(src, out, tgt, loss, d_out, dP, None, ss)
     for _ in range(3):
-        graph.launch(st)
+        graph.launch(ss)
     torch.cuda.synchronize(dev)
     ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ga.record(stream)
+    ga.record(side)
     for _ in range(args.steps):
-        graph.launch(st)
-    gb.record(stream)
+        graph.launch(ss)
+    gb.record(side)
     torch.cuda.synchronize(dev)
     graph_ms = ga.elapsed_time(gb) / args.steps
     plan.sync_status(st)

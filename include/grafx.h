@@ -223,7 +223,7 @@ int grafx_last_launch_count(const grafx_plan* p, int32_t* n);
  * recorded once into a CUDA graph and replayed with one launch.  The buffers and the
  * bound parameters are baked in: replays read their current contents.  d_params and
  * d_sources follow grafx_backprop.  Create runs no kernel itself (it captures on
- * `stream`); the graph is owned by the library until grafx_step_graph_destroy. */
+ * `stream`, which must not be the legacy NULL stream: EINVAL); the graph is owned by the library until grafx_step_graph_destroy. */
 typedef struct grafx_step_graph grafx_step_graph;
 int grafx_step_graph_create(grafx_plan* p, const float* sources, float* out, const float* target, float* loss,
                             float* d_out, float* const* d_params, float* d_sources, void* stream,

@@ -156,6 +156,11 @@ def _stream(torch, device):
     return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
+def _stream_of(s):
+    """ctypes handle of a torch.cuda.Stream."""
+    return ctypes.c_void_p(s.cuda_stream)
+
+
 class Plan:
     """Render data of one graph or a batch of graphs (Algorithm 1 lines 1-4)."""
 

@@ -426,6 +426,7 @@ int grafx_step_graph_create(grafx_plan* p, const float* sources, float* out, con
   int rc = check_ready(p);
   if (rc) return rc;
   if (!p->loss.ok) return fail(GRAFX_ESHAPE, "every output length must be >= 2048 for the STFT loss");
+  if (!stream) return fail(GRAFX_EINVAL, "capture needs a non-default stream (the legacy NULL stream cannot be captured)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // kernel attributes are set outside the capture
   DevCtx c0 = make_ctx(p, sources, out, nullptr, nullptr);

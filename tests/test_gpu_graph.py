@@ -36,13 +36,16 @@ def test_step_graph_replay_equals_eager():
     run.plan.backprop_raw(run.src, d_out, dP, None, st)
     torch.cuda.synchronize()
     ref = (out.clone(), loss.clone(), {t: v.clone() for t, v in dP.items()})
-    graph = run.plan.capture_step(run.src, out, tgt, loss, d_out, dP, None, st)
+    side = torch.cuda.Stream()
+    ss = run.gx._stream_of(side)
+    graph = run.plan.capture_step(run.src, out, tgt, loss, d_out, dP, None, ss)
     assert graph.launches() > 10
     for _ in range(2):
         out.zero_(); loss.zero_()
         for v in dP.values():
             v.zero_()
-        graph.launch(st)
+        torch.cuda.synchronize()
+        graph.launch(ss)
         torch.cuda.synchronize()
         assert torch.equal(out, ref[0]) and torch.equal(loss, ref[1])
         for t in dP:
