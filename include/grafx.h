@@ -26,7 +26,7 @@
  *    pitch = grafx_pitch(L) = L rounded up to a multiple of 4.  Samples at and past
  *    L inside a row are padding: ignored on input, written as 0 on output.
  *  - Node type ids: see GRAFX_T_*.  Parameter widths per type (columns of P[t]):
- *    gain 2, imager 1, eq 8, compressor 4 (see grafx_bind_params).
+ *    gain 2, imager 1, eq 8, compressor 4, delay 176 (see grafx_bind_params).
  */
 #ifndef GRAFX_H
 #define GRAFX_H
@@ -119,7 +119,8 @@ void grafx_plan_opts_default(grafx_plan_opts* o);
 
 /* graphs[0..n_graphs) with lengths[g] samples each (1 <= L <= 2^24).  The graphs
  * are copied; they may be destroyed after this call.  Errors: EINVAL, ECYCLE,
- * ETYPE (delay/reverb not supported by this build), ESHAPE. */
+ * ETYPE (reverb is not supported by this build), ESHAPE (graphs with delay nodes
+ * are limited to 2^19 samples). */
 int grafx_plan_create(const grafx_graph* const* graphs, int32_t n_graphs, const int64_t* lengths,
                       const grafx_plan_opts* opts, grafx_plan** out);
 int grafx_plan_destroy(grafx_plan* p);
@@ -160,7 +161,10 @@ int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* s
  * read at every render/backprop, so values may change in place between calls.
  * Physical units: gain [ln g_l, ln g_r] (Eq. 2); imager [p_s] (Eq. 3); eq 8 band
  * gains in dB at 20*1000^((b+0.5)/8) Hz (Eq. 4, log-frequency interpolation);
- * compressor [alpha, T, W, R] with T, W in natural-log energy (Eq. 8-12), W > 0. */
+ * compressor [alpha, T, W, R] with T, W in natural-log energy (Eq. 8-12), W > 0;
+ * delay 176 = [channel l, r][tap 0..3][Re z, Im z, 20 log-magnitudes of its 39-tap
+ * zero-phase FIR] (Eq. 14-15): the forward pass delays by round(32768 (-arg z)/2pi)
+ * mod 32768 samples, the backward pass takes the z-gradient of the surrogate of Eq. 15. */
 int grafx_bind_params(grafx_plan* p, int32_t type, const float* dev, int64_t rows, int64_t cols);
 
 /* ---------------------------------------------------------------- render / backprop

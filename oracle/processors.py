@@ -245,3 +245,128 @@ def identity_fwd(u, p=None):
 
 def identity_bwd(u, p, ybar):
     return _f64(ybar).copy(), np.zeros(0)
+
+
+# ---------------------------------------------------------------- multitap delay (Eq. 14-15)
+# Readings (the paper states the processor, not these constants): per channel 4 taps,
+# each a complex z = re + j im and a 39-tap zero-phase FIR built like the equalizer
+# from 20 log-magnitudes (K = 20, N = 39, same window and mirroring); the surrogate
+# transform length is N_d = 32768 (>= 500 ms at 44.1 kHz) and the delay used by the
+# forward pass is d = round(N_d (-arg z) / 2 pi) mod N_d, which makes Eq. 15 exact at
+# |z| = 1 with integer phase.  The forward pass uses the exact integer delays
+# (straight-through); the z-gradient is the gradient of the surrogate of Eq. 15,
+# s[n] = Re{(1/N_d) sum_k z^k w^{kn}}, taking the real part of the surrogate.
+# Parameter row: [channel][tap][re, im, 20 log-magnitudes] = 2 x 4 x 22 = 176.
+DELAY_NFFT = 32768
+DELAY_TAPS = 4
+DELAY_FIR = 39
+DELAY_K = 20
+
+
+def delay_split(p):
+    q = _f64(p).reshape(2, DELAY_TAPS, 2 + DELAY_K)
+    z = q[..., 0] + 1j * q[..., 1]
+    return z, q[..., 2:]
+
+
+def delay_samples(z, nfft=DELAY_NFFT):
+    """d = round(N_d (-arg z) / 2 pi) mod N_d."""
+    return np.mod(np.rint(nfft * (-np.angle(z)) / (2 * np.pi)).astype(np.int64), nfft)
+
+
+def delay_fir(p, nfft=DELAY_NFFT):
+    """Per channel the sparse FIR h_x[n] = sum_m c_m[n - d_m] as (offset, taps):
+    h_x is stored from n = offset."""
+    z, lm = delay_split(p)
+    d = delay_samples(z, nfft)
+    H = (DELAY_FIR - 1) // 2
+    out = []
+    for x in range(2):
+        lo = int(d[x].min()) - H
+        hi = int(d[x].max()) + H
+        h = np.zeros(hi - lo + 1)
+        for m in range(DELAY_TAPS):
+            c = zerophase_taps(lm[x, m], DELAY_FIR)
+            s = int(d[x, m]) - H - lo
+            h[s:s + DELAY_FIR] += c
+        out.append((lo, h))
+    return out
+
+
+def _fir_at(u, h, lo):
+    """y[t] = sum_i h[i] u[t - (lo + i)] (taps starting at delay lo), u = 0 outside
+    [0, L), truncated to [0, L)."""
+    L = u.shape[-1]
+    full = scipy.signal.fftconvolve(u, h)             # full[q] = sum_i h[i] u[q - i]
+    q = np.arange(L) - lo
+    ok = (q >= 0) & (q < full.shape[0])
+    y = np.zeros(L)
+    y[ok] = full[q[ok]]
+    return y
+
+
+def delay_fwd(u, p, nfft=DELAY_NFFT):
+    """Eq. 14 with the exact integer delays: y_x = sum_m c_{x,m} * delta[n - d_{x,m}] * u_x."""
+    u = _f64(u)
+    return np.stack([_fir_at(u[x], h, lo) for x, (lo, h) in enumerate(delay_fir(p, nfft))])
+
+
+def _corr_lags(u, ybar, lo, hi):
+    """r[n] = sum_t ybar[t] u[t - n] for n in [lo, hi]."""
+    L = u.shape[-1]
+    c = scipy.signal.fftconvolve(ybar, u[::-1])       # c[j] = sum_t ybar[t] u[t - (j - L + 1)]
+    n = np.arange(lo, hi + 1)
+    j = n + L - 1
+    ok = (j >= 0) & (j < c.shape[0])
+    r = np.zeros(n.shape[0])
+    r[ok] = c[j[ok]]
+    return r
+
+
+def delay_surrogate_dz(g, z, nfft=DELAY_NFFT):
+    """d/d(re, im) of sum_n g[n] s[n] with s[n] = Re{(1/N) sum_k z^k w^{kn}}, w = e^{2 pi j/N}:
+    Q = sum_k k z^{k-1} ifft(g)[k]; d/dre = Re Q, d/dim = -Im Q."""
+    G = np.fft.ifft(g)
+    k = np.arange(nfft)
+    zk = np.exp((k - 1) * np.log(complex(z))) if z != 0 else (k == 1).astype(complex)
+    Q = np.sum(k * zk * G)
+    return np.real(Q), -np.imag(Q)
+
+
+def delay_bwd(u, p, ybar, nfft=DELAY_NFFT):
+    u, ybar = _f64(u), _f64(ybar)
+    z, lm = delay_split(p)
+    d = delay_samples(z, nfft)
+    H = (DELAY_FIR - 1) // 2
+    firs = delay_fir(p, nfft)
+    ubar = np.stack([_fir_at(ybar[x], h[::-1], -(lo + h.shape[0] - 1)) for x, (lo, h) in enumerate(firs)])
+    pbar = np.zeros((2, DELAY_TAPS, 2 + DELAY_K))
+    for x in range(2):
+        r = _corr_lags(u[x], ybar[x], -H, nfft - 1 + H)          # r[n], n in [-H, N_d + H)
+        for m in range(DELAY_TAPS):
+            c = zerophase_taps(lm[x, m], DELAY_FIR)
+            # taps: dL/dc[j] = r[d + j], j in [-H, H]
+            cbar = r[d[x, m] + np.arange(-H, H + 1) + H]
+            pbar[x, m, 2:] = zerophase_taps_bwd(lm[x, m], DELAY_FIR, cbar)
+            # surrogate: g[n] = dL/ds[n] = sum_j c[j] r[n + j], n in [0, N_d)
+            g = np.zeros(nfft)
+            for jj, cj in enumerate(c):
+                g += cj * r[jj:jj + nfft]
+            pbar[x, m, 0], pbar[x, m, 1] = delay_surrogate_dz(g, z[x, m], nfft)
+    return ubar, pbar.reshape(-1)
+
+
+def delay_fwd_surrogate(u, p, nfft=DELAY_NFFT):
+    """Forward through the surrogate of Eq. 15 (for checking the z-gradient by finite
+    differences): y_x = sum_m s_m * c_m * u_x with s_m[n] = Re{IDFT(z^k)}[n]."""
+    u = _f64(u)
+    z, lm = delay_split(p)
+    H = (DELAY_FIR - 1) // 2
+    k = np.arange(nfft)
+    y = np.zeros_like(u)
+    for x in range(2):
+        for m in range(DELAY_TAPS):
+            s = np.real(np.fft.ifft(np.exp(k * np.log(complex(z[x, m])))))
+            c = zerophase_taps(lm[x, m], DELAY_FIR)
+            y[x] += _fir_at(u[x], np.convolve(s, c), -H)
+    return y

@@ -40,6 +40,8 @@ def process(t, u, p, hp):
         return op.eq_fwd(u, p, hp["eq_taps"], hp["fs"])
     if t == C_:
         return op.compressor_fwd(u, p, hp["comp_eps"])
+    if t == D_:
+        return op.delay_fwd(u, p, hp.get("delay_nfft", op.DELAY_NFFT))
     raise NotImplementedError(f"type {t}")
 
 
@@ -54,6 +56,8 @@ def process_bwd(t, u, p, ybar, hp):
         return op.eq_bwd(u, p, ybar, hp["eq_taps"], hp["fs"])
     if t == C_:
         return op.compressor_bwd(u, p, ybar, hp["comp_eps"])
+    if t == D_:
+        return op.delay_bwd(u, p, ybar, hp.get("delay_nfft", op.DELAY_NFFT))
     raise NotImplementedError(f"type {t}")
 
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libgrafx.so")
 
 T_IN, T_OUT, T_MIX, T_GAIN, T_IMAGER, T_EQ, T_COMP, T_DELAY, T_REVERB = range(9)
 N_TYPES = 9
-PARAM_COLS = {T_GAIN: 2, T_IMAGER: 1, T_EQ: 8, T_COMP: 4}
+PARAM_COLS = {T_GAIN: 2, T_IMAGER: 1, T_EQ: 8, T_COMP: 4, T_DELAY: 176}
 SCHED = {"beam": 0, "greedy": 1, "optimal": 2, "one_by_one": 3}
 ERRORS = {1: "EINVAL", 2: "ECYCLE", 3: "ESHAPE", 4: "ETYPE", 5: "ENOMEM", 6: "ECUDA", 7: "ETIMEOUT",
           8: "ESTATE"}

@@ -47,6 +47,11 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
   c.eq_aux = at<float>(p, p->ws.eq_aux);
   c.eq_bandpart = at<float>(p, p->ws.eq_bandpart);
   c.comp_carry = at<float>(p, p->ws.comp_carry);
+  c.dl_aux = at<float>(p, p->ws.dl_aux);
+  c.dl_spec = at<float2>(p, p->ws.dl_spec);
+  c.dl_R = at<float2>(p, p->ws.dl_R);
+  c.dl_r = at<float>(p, p->ws.dl_r);
+  for (int j = 0; j < 9; ++j) c.dl_taylor[j] = float(p->dl_taylor[j]);
   c.partial = at<float4>(p, p->ws.partial);
   c.eq_partial = at<float2>(p, p->ws.eq_partial);
   c.ybase[KIND_INPUT] = const_cast<float*>(src);
@@ -67,7 +72,7 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
 
 int check_ready(const Plan* p) {
   if (!p->dev_ws) return fail(GRAFX_ESTATE, "workspace not bound (grafx_plan_bind_workspace)");
-  for (int t : {GRAFX_T_GAIN, GRAFX_T_IMAGER, GRAFX_T_EQ, GRAFX_T_COMP})
+  for (int t : {GRAFX_T_GAIN, GRAFX_T_IMAGER, GRAFX_T_EQ, GRAFX_T_COMP, GRAFX_T_DELAY})
     if (p->n_type_rows[t] > 0 && !p->params[t])
       return fail(GRAFX_ESTATE, "parameters of type " + std::to_string(t) + " not bound");
   return GRAFX_OK;
@@ -79,6 +84,7 @@ int param_cols(int t) {
     case GRAFX_T_IMAGER: return 1;
     case GRAFX_T_EQ: return 8;
     case GRAFX_T_COMP: return 4;
+    case GRAFX_T_DELAY: return DL_COLS;
     default: return 0;
   }
 }
@@ -312,6 +318,10 @@ int grafx_render_steps(grafx_plan* p, const float* sources, float* out, int32_t 
         clear_step_flags(p, st.fitem_begin, st.fitem_count, 2 * k, s);
         launches += launch_comp(0, c, st.fitem_begin, st.fitem_count, 2 * k, s);
         break;
+      case GRAFX_T_DELAY:
+        launches += launch_delay(0, c, st.node_begin, st.node_end, s);
+        launches += launch_delay(1, c, st.fitem_begin, st.fitem_count, s);
+        break;
       default:
         launches += launch_ew_fwd(st.type, c, st.fitem_begin, st.fitem_count, s);
     }
@@ -349,6 +359,12 @@ int grafx_backprop_steps(grafx_plan* p, const float* sources, const float* d_out
         clear_step_flags(p, st.bitem_begin, st.bitem_count, 2 * k + 1, s);
         launches += launch_comp(1, c, st.bitem_begin, st.bitem_count, 2 * k + 1, s);
         if (c.dparams) launches += launch_comp(2, c, st.node_begin, st.node_end, 0, s);
+        break;
+      case GRAFX_T_DELAY:
+        launches += launch_delay(2, c, st.dsub_begin[0], st.dsub_count[0], s);
+        if (c.dparams) {
+          for (int i = 1; i < 5; ++i) launches += launch_delay(2 + i, c, st.dsub_begin[i], st.dsub_count[i], s);
+        }
         break;
       case GRAFX_T_GAIN:
       case GRAFX_T_IMAGER:
@@ -431,6 +447,7 @@ int grafx_step_graph_create(grafx_plan* p, const float* sources, float* out, con
   // kernel attributes are set outside the capture
   DevCtx c0 = make_ctx(p, sources, out, nullptr, nullptr);
   launch_eq(-1, c0, 0, 0, s);
+  launch_delay(-1, c0, 0, 0, s);
   launch_loss(-1, make_loss(p, out, target), s);
   rc = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
   if (rc) return rc;

@@ -31,6 +31,11 @@ struct DevCtx {
   float* eq_aux;       // per EQ node: 1024 floats (taps in the forward, gradient fold in the backward)
   float* eq_bandpart;  // per EQ node: chunk partials of the band gradient (16 x 8 floats)
   float* comp_carry;
+  float* dl_aux;        // per delay node: taps and delays (DL_AUX floats)
+  float2* dl_spec;      // block spectra of the lag correlation
+  float2* dl_R;         // per delay node and lag partition: accumulated spectra
+  float* dl_r;          // per delay node and channel: lags r[n], n from -DL_B
+  float dl_taylor[9];   // Taylor coefficients of sum_k k q^k near q = 1
   float4* partial;
   float2* eq_partial;
   float* ybase[3];

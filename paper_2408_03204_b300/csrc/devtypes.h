@@ -38,6 +38,20 @@ constexpr int TWIDDLE_N = 8192;   // twiddle table size: exp(-2 pi i m / 8192)
 constexpr int EW_TILE = 4096;     // samples per elementwise work item (4 float4 per thread and channel)
 constexpr int N_RES = 3;          // loss resolutions 512, 1024, 2048
 
+// multitap delay (Eq. 14-15)
+constexpr int DL_NFFT = 32768;     // surrogate transform length N_d
+constexpr int DL_TAPS = 4;         // taps per channel
+constexpr int DL_FIR = 39;         // zero-phase FIR per tap (20 log-magnitudes)
+constexpr int DL_COLS = 2 * DL_TAPS * (2 + (DL_FIR + 1) / 2);   // 176 parameters
+constexpr int DL_AUX = 2 * DL_TAPS * (DL_FIR + 1);             // taps + delay per (channel, tap)
+constexpr int DL_TILE = 1024;      // outputs per forward / adjoint work item
+constexpr int DL_B = 4096;         // block of the lag correlation
+constexpr int DL_M = 2 * DL_B;     // its FFT size
+constexpr int DL_P = 10;           // lag partitions: lags [-B, (P-1) B) cover [-19, N_d + 19)
+constexpr int DL_NLAG = DL_P * DL_B;
+constexpr int DL_CHUNK = 32;       // bins per accumulation work item
+constexpr int DL_MAX_BLOCKS = 128; // signals with delay nodes: at most 2^19 samples
+
 // status bits written by kernels
 constexpr uint32_t ST_TIMEOUT = 1u;
 constexpr uint32_t ST_BOUNDS = 2u;

@@ -22,6 +22,10 @@ int launch_eq(int what, const DevCtx& c, int a, int b, cudaStream_t s);  // what
 // 2 gradient finalize (a = node_begin, b = node_end)
 int launch_comp(int what, const DevCtx& c, int a, int b, int ticket, cudaStream_t s);
 
+// delay: what = 0 design (node range), 1 forward (items), 2 input adjoint, 3 block
+// spectra, 4 partition accumulation, 5 lags (inverse FFTs), 6 gradients; < 0 attributes
+int launch_delay(int what, const DevCtx& c, int a, int b, cudaStream_t s);
+
 struct LossLaunch {
   const LossRow* rows;
   const int4_* items;   // (row, resolution, first frame, group)

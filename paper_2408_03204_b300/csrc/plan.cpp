@@ -93,9 +93,11 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
   const int32_t n_e = int32_t(p->edges.size());
   int rc = validate(p->types, p->edges);
   if (rc) return rc;
-  for (int32_t t : p->types)
-    if (t == GRAFX_T_DELAY || t == GRAFX_T_REVERB)
-      return fail(GRAFX_ETYPE, "delay and reverb nodes are not supported by this build");
+  for (int32_t v = 0; v < n; ++v) {
+    if (p->types[v] == GRAFX_T_REVERB) return fail(GRAFX_ETYPE, "reverb nodes are not supported by this build");
+    if (p->types[v] == GRAFX_T_DELAY && p->L[p->node_graph[v]] > int64_t(DL_MAX_BLOCKS) * DL_B)
+      return fail(GRAFX_ESHAPE, "graphs with delay nodes are limited to 2^19 samples");
+  }
   if (opts.eq_taps < 3 || opts.eq_taps % 2 == 0 || opts.eq_taps > 2047)
     return fail(GRAFX_EINVAL, "eq_taps must be odd in [3, 2047]");
   int nthr = opts.n_threads > 0 ? opts.n_threads : int(std::max(1u, std::thread::hardware_concurrency()));
@@ -223,6 +225,14 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
           for (int32_t j = 0; j < nb; ++j) fwd.push_back({v, j, p->node_ext[v].z, 0});
           break;
         }
+        case GRAFX_T_DELAY: {
+          const int32_t nb = (L + DL_B - 1) / DL_B;
+          p->node_ext[v].z = p->n_delay++;
+          p->node_ext[v].w = nb;
+          for (int32_t ch = 0; ch < 2; ++ch)
+            for (int32_t t0 = 0; t0 < L; t0 += DL_TILE) fwd.push_back({v, t0, ch, 0});
+          break;
+        }
         case GRAFX_T_COMP: {
           int32_t nc = (L + p->comp_chunk - 1) / p->comp_chunk;
           p->node_ext[v].z = chunk_id;
@@ -240,6 +250,28 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
     StepInfo& s = p->steps[k];
     s.bitem_begin = int32_t(bwd.size());
     if (s.type == GRAFX_T_OUT) { s.bitem_count = 0; continue; }  // adjoint rows alias d_out
+    if (s.type == GRAFX_T_DELAY) {
+      std::vector<int4_> sub[5];
+      for (int32_t v = s.node_begin; v < s.node_end; ++v) {
+        const int32_t L = p->nodes[v].len, nb = p->node_ext[v].w;
+        for (int32_t ch = 0; ch < 2; ++ch)
+          for (int32_t t0 = 0; t0 < L; t0 += DL_TILE) sub[0].push_back({v, t0, ch, 0});
+        p->node_ext[v].x = p->n_dl_slots;
+        p->node_ext[v].y = p->node_ext[v].z * DL_P;
+        for (int32_t w = -DL_P; w < nb; ++w) sub[1].push_back({v, w, 0, p->n_dl_slots++});
+        for (int32_t b = 0; b < nb; ++b) sub[1].push_back({v, b, 1, p->n_dl_slots++});
+        for (int32_t ck = 0; ck < DL_M / DL_CHUNK; ++ck) sub[2].push_back({v, ck, 0, 0});
+        for (int32_t q = 0; q < DL_P; ++q) sub[3].push_back({v, q, 0, 0});
+        for (int32_t xm = 0; xm < 2 * DL_TAPS; ++xm) sub[4].push_back({v, xm, 0, 0});
+      }
+      for (int i = 0; i < 5; ++i) {
+        s.dsub_begin[i] = int32_t(bwd.size());
+        s.dsub_count[i] = int32_t(sub[i].size());
+        bwd.insert(bwd.end(), sub[i].begin(), sub[i].end());
+      }
+      s.bitem_count = int32_t(bwd.size()) - s.bitem_begin;
+      continue;
+    }
     // EQ: runs of consecutive blocks, sized for about two waves of resident CTAs
     int32_t run_len = 1;
     if (s.type == GRAFX_T_EQ) {
@@ -286,7 +318,10 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
   p->n_eq_runs = run;
   p->n_comp_chunks = chunk_id;
   p->n_fitems = int32_t(fwd.size());
-  for (int32_t k = 1; k <= N; ++k) p->steps[k].bitem_begin += p->n_fitems;
+  for (int32_t k = 1; k <= N; ++k) {
+    p->steps[k].bitem_begin += p->n_fitems;
+    for (int i = 0; i < 5; ++i) p->steps[k].dsub_begin[i] += p->n_fitems;
+  }
   p->in_bitem_begin += p->n_fitems;
   p->items = fwd;
   p->items.insert(p->items.end(), bwd.begin(), bwd.end());
@@ -296,6 +331,17 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
   for (int m = 0; m < TWIDDLE_N; ++m) {
     double a = 2.0 * M_PI * m / TWIDDLE_N;
     p->twiddle[m] = float2_{float(std::cos(a)), float(-std::sin(a))};
+  }
+  // Taylor coefficients of F(e^s) = sum_{k<N} k e^{ks} = N^2 sum_j e_j (N s)^j,
+  // e_j = sum_k (k/N)^(j+1) / (N j!)  (delay surrogate near its pole)
+  {
+    double fact = 1.0;
+    for (int j = 0; j < 9; ++j) {
+      if (j) fact *= j;
+      double s = 0.0;
+      for (int k = 0; k < DL_NFFT; ++k) s += std::pow(double(k) / DL_NFFT, j + 1);
+      p->dl_taylor[j] = s / DL_NFFT / fact;
+    }
   }
   // FFT pass twiddles W_{Ns R}^{r k} at [(r-1) Ns + k] for every pass of every size
   p->ptw.assign(fft::PTW_TOTAL, float2_{0.f, 0.f});
@@ -380,6 +426,10 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
     w.eq_aux = take(4 * size_t(std::max(p->n_eq, 1)) * 1024);
     w.eq_bandpart = take(4 * size_t(std::max(p->n_eq, 1)) * 16 * 8);
     w.comp_carry = take(4 * size_t(std::max(p->n_comp_chunks, 1)));
+    w.dl_aux = take(4 * size_t(std::max(p->n_delay, 1)) * DL_AUX);
+    w.dl_spec = take(8 * size_t(std::max(p->n_dl_slots, 1)) * DL_M);
+    w.dl_R = take(8 * size_t(std::max(p->n_delay, 1)) * DL_P * DL_M);
+    w.dl_r = take(4 * size_t(std::max(p->n_delay, 1)) * 2 * DL_NLAG);
     w.partial = take(16 * size_t(std::max(p->n_partials, 1)));
     w.eq_partial = take(8 * size_t(std::max(p->n_eq_runs, 1)) * (p->eq_fft / 2 + 1));
     w.loss_part = take(32 * size_t(std::max(p->loss.n_groups_total, 1)));

@@ -37,6 +37,7 @@ struct StepInfo {
   int32_t node_begin, node_end;    // new ids [begin, end)
   int32_t fitem_begin, fitem_count;  // forward work items (global index)
   int32_t bitem_begin, bitem_count;  // backward work items (global index)
+  int32_t dsub_begin[5], dsub_count[5];  // delay backward sub-lists: adjoint, spectra, acc, lags, grads
 };
 
 // Byte offsets of the regions inside the caller's workspace.
@@ -47,6 +48,7 @@ struct WsLayout {
   size_t tables_end;                           // [0, tables_end) is uploaded at bind time
   size_t status, tickets, flags, flags_bytes;  // flags_bytes covers status+tickets+flags (cleared per call)
   size_t eq_spec, eq_aux, eq_bandpart, comp_carry, partial, eq_partial;
+  size_t dl_aux, dl_spec, dl_R, dl_r;
   size_t loss_part, loss_stats, loss_rowloss, loss_frames;
   size_t U, A;
   size_t total;
@@ -81,6 +83,8 @@ struct Plan {
   int32_t n_type_rows[GRAFX_N_TYPES] = {0};
   int32_t n_eq = 0, n_comp_chunks = 0, n_partials = 0, n_eq_runs = 0;
   int32_t n_fitems = 0, in_bitem_begin = 0, in_bitem_count = 0;
+  int32_t n_delay = 0, n_dl_slots = 0;
+  double dl_taylor[9] = {0};
   int32_t eq_taps = 1023, eq_H = 511, eq_fft = 4096, eq_step = 0;  // eq_step: outputs per block
   int32_t comp_chunk = 2048;
   int64_t src_elems = 0, out_elems = 0, node_samples = 0;

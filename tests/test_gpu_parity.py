@@ -231,3 +231,42 @@ def test_cfg2_fwd_bwd_mrstft(L):
         rel = np.linalg.norm(a - b) / np.linalg.norm(b)
         cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
         assert rel <= LOSS_CHAIN_NORM_TOL and cos > 0.998, (t, rel, cos)
+
+
+D = 7
+
+
+@pytest.mark.parametrize("L", [5003, 20000])
+def test_delay_fwd_bwd(L):
+    """Multitap delay: exact integer-delay forward; backward adjoint, FIR gradients and
+    the surrogate z-gradient (Eq. 15)."""
+    g = single_node_graph(D, fan_in=2)
+    run, P, src_per, out = run_case([g], [L], seed=41)
+    rng = np.random.Generator(np.random.PCG64(L))
+    Pd = (L + 3) // 4 * 4
+    W = np.zeros((1, 2, Pd), np.float32)
+    W[:, :, :L] = rng.standard_normal((1, 2, L)).astype(np.float32)
+    dP, dS = run.backprop(W.reshape(-1))
+    wP, wS = orr.backward(g.types, g.edges, src_per[0][:, :, :L], P, W[:, :, :L])
+    q = dP[D].reshape(-1, 2, 4, 22)
+    wq = wP[D].reshape(-1, 2, 4, 22)
+    assert_grad_close(q[..., :2], wq[..., :2], what="delay z (surrogate)")
+    assert_grad_close(q[..., 2:], wq[..., 2:], what="delay FIR log-magnitudes")
+    assert_grad_close(dS.reshape(-1, 2, Pd)[:, :, :L], wS, what="sources")
+
+
+def test_random_graphs_with_delay():
+    from tests.helpers import random_dag
+    rng = np.random.Generator(np.random.PCG64(77))
+    for k in range(2):
+        g = random_dag(rng, n_inputs=2, n_mid=7, n_outputs=1, kinds=(M, G, S, E, C, D))
+        L = int(rng.integers(5000, 9000))
+        run, P, src_per, out = run_case([g], [L], seed=300 + k)
+        Pd = (L + 3) // 4 * 4
+        W = np.zeros((1, 2, Pd), np.float32)
+        W[:, :, :L] = rng.standard_normal((1, 2, L)).astype(np.float32)
+        dP, dS = run.backprop(W.reshape(-1))
+        wP, wS = orr.backward(g.types, g.edges, src_per[0][:, :, :L], P, W[:, :, :L], dict(eq_taps=63))
+        for t in P:
+            assert_grad_close(dP[t], wP[t], what=f"type {t}")
+        assert_grad_close(dS.reshape(-1, 2, Pd)[:, :, :L], wS, what="sources")
