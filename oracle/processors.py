@@ -370,3 +370,163 @@ def delay_fwd_surrogate(u, p, nfft=DELAY_NFFT):
             c = zerophase_taps(lm[x, m], DELAY_FIR)
             y[x] += _fir_at(u[x], np.convolve(s, c), -H)
     return y
+
+
+# ---------------------------------------------------------------- filtered-noise reverb (Eq. 6-7)
+# Readings (the paper gives the model, not these constants): two noise buffers (mid,
+# side) of 2 s = 88200 samples, U(-1, 1), are inputs shared by every reverb node (the
+# random numbers the method draws are passed in); STFT with FFT 1024, hop 256,
+# periodic Hann, frames m = 1..F starting at (m-1) hop, F = ceil(88200 / 256), signal
+# zero past its end; masks M_x[k, m] = exp(H0_x[k] + (m-1) Hd_x[k]) with H0, Hd
+# interpolated from 12 log-spaced bands like the EQ (natural-log magnitudes); ISTFT by
+# windowed overlap-add divided by sum w^2 (0 where that sum is < 1e-8); h_l =
+# (h_m + h_s)/2, h_r = (h_m - h_s)/2 (the imager's convention); y = e^{q_dry} u +
+# e^{q_wet} (h * u), causal, truncated to L.
+# Parameter row (50): [mid, side] x [H0 (12), Hd (12)], then q_dry, q_wet.
+RV_LEN = 88200
+RV_NFFT = 1024
+RV_HOP = 256
+RV_BANDS = 12
+
+
+def rv_hp(hp=None):
+    d = dict(rv_len=RV_LEN, rv_nfft=RV_NFFT, rv_hop=RV_HOP, fs=44100)
+    if hp:
+        d.update({k: v for k, v in hp.items() if k in d})
+    return d
+
+
+def rv_band_matrix(nfft, fs=44100, n_bands=RV_BANDS):
+    """Bins 0..nfft/2 at k fs / nfft; the same log2-interpolation rule as the EQ."""
+    c = 20.0 * 1000.0 ** ((np.arange(n_bands) + 0.5) / n_bands)
+    lc = np.log2(c)
+    B = np.zeros((nfft // 2 + 1, n_bands))
+    for k in range(nfft // 2 + 1):
+        f = k * fs / nfft
+        if f <= c[0]:
+            B[k, 0] = 1.0
+        elif f >= c[-1]:
+            B[k, -1] = 1.0
+        else:
+            b = int(np.searchsorted(c, f, side="right")) - 1
+            w = (np.log2(f) - lc[b]) / (lc[b + 1] - lc[b])
+            B[k, b], B[k, b + 1] = 1.0 - w, w
+    return B
+
+
+def rv_window(n):
+    return 0.5 - 0.5 * np.cos(2 * np.pi * np.arange(n) / n)
+
+
+def rv_frames(length, nfft, hop):
+    return -(-length // hop)
+
+
+def rv_stft(x, nfft, hop):
+    """[F, nfft/2+1] one-sided spectra of frames (m-1) hop, zero past the end."""
+    F = rv_frames(x.shape[0], nfft, hop)
+    pad = np.zeros((F - 1) * hop + nfft)
+    pad[:x.shape[0]] = x
+    idx = np.arange(F)[:, None] * hop + np.arange(nfft)[None, :]
+    return np.fft.rfft(pad[idx] * rv_window(nfft)[None, :], axis=-1)
+
+
+def rv_ola_norm(length, nfft, hop):
+    F = rv_frames(length, nfft, hop)
+    D = np.zeros((F - 1) * hop + nfft)
+    w2 = rv_window(nfft) ** 2
+    for m in range(F):
+        D[m * hop:m * hop + nfft] += w2
+    return D[:length]
+
+
+def rv_istft(S, length, nfft, hop):
+    """Windowed overlap-add of irfft frames divided by sum w^2 (0 where < 1e-8)."""
+    F = S.shape[0]
+    fr = np.fft.irfft(S, nfft, axis=-1) * rv_window(nfft)[None, :]
+    out = np.zeros((F - 1) * hop + nfft)
+    for m in range(F):
+        out[m * hop:m * hop + nfft] += fr[m]
+    D = rv_ola_norm(length, nfft, hop)
+    h = np.zeros(length)
+    ok = D > 1e-8
+    h[ok] = out[:length][ok] / D[ok]
+    return h
+
+
+def rv_masks(p, nfft, F, fs=44100):
+    q = _f64(p)
+    B = rv_band_matrix(nfft, fs)
+    out = []
+    for x in range(2):
+        H0 = B @ q[x * 24:x * 24 + 12]
+        Hd = B @ q[x * 24 + 12:x * 24 + 24]
+        out.append(np.exp(H0[None, :] + np.arange(F)[:, None] * Hd[None, :]))
+    return out
+
+
+def rv_ir(p, noise, hp=None):
+    """Stereo IR [2, length] of one reverb node from its parameters and the noise."""
+    hp = rv_hp(hp)
+    n, hop, length = hp["rv_nfft"], hp["rv_hop"], hp["rv_len"]
+    F = rv_frames(length, n, hop)
+    Ms = rv_masks(p, n, F, hp["fs"])
+    hm = rv_istft(rv_stft(_f64(noise[0][:length]), n, hop) * Ms[0], length, n, hop)
+    hs = rv_istft(rv_stft(_f64(noise[1][:length]), n, hop) * Ms[1], length, n, hop)
+    return np.stack([(hm + hs) / 2, (hm - hs) / 2])
+
+
+def _causal(u, h):
+    L = u.shape[-1]
+    return scipy.signal.fftconvolve(u, h)[:L]
+
+
+def reverb_fwd(u, p, noise, hp=None):
+    u, q = _f64(u), _f64(p)
+    h = rv_ir(q, noise, hp)
+    return np.exp(q[48]) * u + np.exp(q[49]) * np.stack([_causal(u[x], h[x]) for x in range(2)])
+
+
+def reverb_bwd(u, p, ybar, noise, hp=None):
+    hp = rv_hp(hp)
+    u, q, ybar = _f64(u), _f64(p), _f64(ybar)
+    n, hop, length = hp["rv_nfft"], hp["rv_hop"], hp["rv_len"]
+    F = rv_frames(length, n, hop)
+    h = rv_ir(q, noise, hp)
+    a_dry, a_wet = np.exp(q[48]), np.exp(q[49])
+    L = u.shape[-1]
+    # input adjoint: dry + correlation with the IR
+    ubar = a_dry * ybar + a_wet * np.stack([scipy.signal.fftconvolve(ybar[x][::-1], h[x])[:L][::-1]
+                                            for x in range(2)])
+    # r_x[n] = sum_t ybar[t] u[t - n], n in [0, length)
+    r = np.stack([scipy.signal.fftconvolve(ybar[x], u[x][::-1])[L - 1:L - 1 + length] for x in range(2)])
+    if r.shape[1] < length:
+        r = np.pad(r, ((0, 0), (0, length - r.shape[1])))
+    pbar = np.zeros(50)
+    pbar[48] = a_dry * np.sum(ybar * u)
+    pbar[49] = a_wet * np.sum(h * r)
+    hbar = a_wet * r                                       # dL/dh_l, dL/dh_r
+    hbar_ms = [(hbar[0] + hbar[1]) / 2, (hbar[0] - hbar[1]) / 2]
+    D = rv_ola_norm(length, n, hop)
+    Ms = rv_masks(q, n, F, hp["fs"])
+    B = rv_band_matrix(n, hp["fs"])
+    w = rv_window(n)
+    ck = np.full(n // 2 + 1, 2.0)
+    ck[0] = ck[-1] = 1.0
+    for x in range(2):
+        g = np.zeros(length)
+        ok = D > 1e-8
+        g[ok] = hbar_ms[x][ok] / D[ok]
+        gp = np.zeros((F - 1) * hop + n)
+        gp[:length] = g
+        idx = np.arange(F)[:, None] * hop + np.arange(n)[None, :]
+        xbar = gp[idx] * w[None, :]                          # dL/d(irfft frame)
+        Gb = ck[None, :] / n * np.fft.rfft(xbar, axis=-1)    # dL/dRe H + j dL/dIm H
+        Ux = rv_stft(_f64(noise[x][:length]), n, hop)
+        Mbar = np.real(Gb) * np.real(Ux) + np.imag(Gb) * np.imag(Ux)
+        MM = Ms[x] * Mbar
+        dH0 = MM.sum(axis=0)
+        dHd = (np.arange(F)[:, None] * MM).sum(axis=0)
+        pbar[x * 24:x * 24 + 12] = B.T @ dH0
+        pbar[x * 24 + 12:x * 24 + 24] = B.T @ dHd
+    return ubar, pbar

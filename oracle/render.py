@@ -42,6 +42,8 @@ def process(t, u, p, hp):
         return op.compressor_fwd(u, p, hp["comp_eps"])
     if t == D_:
         return op.delay_fwd(u, p, hp.get("delay_nfft", op.DELAY_NFFT))
+    if t == R_:
+        return op.reverb_fwd(u, p, hp["reverb_noise"], hp)
     raise NotImplementedError(f"type {t}")
 
 
@@ -58,6 +60,8 @@ def process_bwd(t, u, p, ybar, hp):
         return op.compressor_bwd(u, p, ybar, hp["comp_eps"])
     if t == D_:
         return op.delay_bwd(u, p, ybar, hp.get("delay_nfft", op.DELAY_NFFT))
+    if t == R_:
+        return op.reverb_bwd(u, p, ybar, hp["reverb_noise"], hp)
     raise NotImplementedError(f"type {t}")
 
 

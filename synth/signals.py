@@ -53,3 +53,10 @@ def sources(seed: int, K: int, L: int, fs: int = 44100, pitch: int = None) -> np
             x = x * (peak / m)
         out[k, :, :L] = x.astype(np.float32)
     return out
+
+
+def reverb_noise(seed: int = 8, length: int = 88200) -> np.ndarray:
+    """The two uniform noise buffers (mid, side) of the filtered-noise reverb, U(-1, 1),
+    float32 [2, length] (2 s at 44.1 kHz by default)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(-1.0, 1.0, (2, length)).astype(np.float32)
