@@ -26,7 +26,7 @@
  *    pitch = grafx_pitch(L) = L rounded up to a multiple of 4.  Samples at and past
  *    L inside a row are padding: ignored on input, written as 0 on output.
  *  - Node type ids: see GRAFX_T_*.  Parameter widths per type (columns of P[t]):
- *    gain 2, imager 1, eq 8, compressor 4, delay 176 (see grafx_bind_params).
+ *    gain 2, imager 1, eq 8, compressor 4, delay 176, reverb 50 (see grafx_bind_params).
  */
 #ifndef GRAFX_H
 #define GRAFX_H
@@ -119,8 +119,7 @@ void grafx_plan_opts_default(grafx_plan_opts* o);
 
 /* graphs[0..n_graphs) with lengths[g] samples each (1 <= L <= 2^24).  The graphs
  * are copied; they may be destroyed after this call.  Errors: EINVAL, ECYCLE,
- * ETYPE (reverb is not supported by this build), ESHAPE (graphs with delay nodes
- * are limited to 2^19 samples). */
+ * ETYPE, ESHAPE (graphs with delay or reverb nodes are limited to 2^19 samples). */
 int grafx_plan_create(const grafx_graph* const* graphs, int32_t n_graphs, const int64_t* lengths,
                       const grafx_plan_opts* opts, grafx_plan** out);
 int grafx_plan_destroy(grafx_plan* p);
@@ -164,8 +163,16 @@ int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* s
  * compressor [alpha, T, W, R] with T, W in natural-log energy (Eq. 8-12), W > 0;
  * delay 176 = [channel l, r][tap 0..3][Re z, Im z, 20 log-magnitudes of its 39-tap
  * zero-phase FIR] (Eq. 14-15): the forward pass delays by round(32768 (-arg z)/2pi)
- * mod 32768 samples, the backward pass takes the z-gradient of the surrogate of Eq. 15. */
+ * mod 32768 samples, the backward pass takes the z-gradient of the surrogate of Eq. 15;
+ * reverb 50 = [mid, side][H0 (12 bands), Hd (12 bands)] natural-log magnitudes and
+ * per-frame decays of the noise masks (Eq. 7), then q_dry, q_wet (log gains):
+ * y = e^{q_dry} u + e^{q_wet} (h * u) with the 88200-tap IR h of Eq. 6-7. */
 int grafx_bind_params(grafx_plan* p, int32_t type, const float* dev, int64_t rows, int64_t cols);
+
+/* Bind the two noise buffers of the filtered-noise reverb (Sec. 3 "Reverb", Eq. 6-7):
+ * device float32 [2][88200] (mid, side; 2 s at 44.1 kHz), shared by every reverb node;
+ * kept by pointer.  Required when the plan has reverb nodes. */
+int grafx_bind_reverb_noise(grafx_plan* p, const float* dev, int64_t n);
 
 /* ---------------------------------------------------------------- render / backprop
  * grafx_render: Algorithm 1 lines 5-13.  sources: device float32 holding, graph after

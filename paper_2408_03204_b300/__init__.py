@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libgrafx.so")
 
 T_IN, T_OUT, T_MIX, T_GAIN, T_IMAGER, T_EQ, T_COMP, T_DELAY, T_REVERB = range(9)
 N_TYPES = 9
-PARAM_COLS = {T_GAIN: 2, T_IMAGER: 1, T_EQ: 8, T_COMP: 4, T_DELAY: 176}
+PARAM_COLS = {T_GAIN: 2, T_IMAGER: 1, T_EQ: 8, T_COMP: 4, T_DELAY: 176, T_REVERB: 50}
 SCHED = {"beam": 0, "greedy": 1, "optimal": 2, "one_by_one": 3}
 ERRORS = {1: "EINVAL", 2: "ECYCLE", 3: "ESHAPE", 4: "ETYPE", 5: "ENOMEM", 6: "ECUDA", 7: "ETIMEOUT",
           8: "ESTATE"}
@@ -67,6 +67,7 @@ SIGNATURES = {
     "grafx_plan_export": (ctypes.c_int, [_P] + [_I32P] * 8),
     "grafx_plan_bind_workspace": (ctypes.c_int, [_P, _P, _SZ, _P]),
     "grafx_bind_params": (ctypes.c_int, [_P, _I32, _F, _I64, _I64]),
+    "grafx_bind_reverb_noise": (ctypes.c_int, [_P, _F, _I64]),
     "grafx_render": (ctypes.c_int, [_P, _F, _F, _P]),
     "grafx_backprop": (ctypes.c_int, [_P, _F, _F, ctypes.POINTER(_P), _F, _P]),
     "grafx_render_steps": (ctypes.c_int, [_P, _F, _F, _I32, _I32, _P]),
@@ -219,6 +220,11 @@ class Plan:
             assert p.dtype.is_floating_point and p.is_contiguous()
             _check(lib().grafx_bind_params(self._h, int(t), _ptr(p), p.shape[0], p.shape[1]))
             self.params[int(t)] = p
+
+    def bind_reverb_noise(self, noise):
+        """noise: device float32 [2, 88200] (mid, side), kept by reference."""
+        _check(lib().grafx_bind_reverb_noise(self._h, _ptr(noise), noise.numel()))
+        self.rv_noise = noise
 
     def render_raw(self, sources, out, stream):
         _check(lib().grafx_render(self._h, _ptr(sources), _ptr(out), stream))

@@ -52,6 +52,17 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
   c.dl_R = at<float2>(p, p->ws.dl_R);
   c.dl_r = at<float>(p, p->ws.dl_r);
   for (int j = 0; j < 9; ++j) c.dl_taylor[j] = float(p->dl_taylor[j]);
+  c.rv_noise = p->rv_noise;
+  c.rv_band = at<const float>(p, p->ws.rv_band);
+  c.rv_U = at<float2>(p, p->ws.rv_U);
+  c.rv_fr = at<float2>(p, p->ws.rv_fr);
+  c.rv_h = at<float>(p, p->ws.rv_h);
+  c.rv_H = at<float2>(p, p->ws.rv_H);
+  c.rv_Y = at<float2>(p, p->ws.rv_Y);
+  c.rv_R = at<float2>(p, p->ws.rv_R);
+  c.rv_r = at<float>(p, p->ws.rv_r);
+  c.rv_mm = at<float2>(p, p->ws.rv_mm);
+  c.rv_nbmax = p->rv_nbmax;
   c.partial = at<float4>(p, p->ws.partial);
   c.eq_partial = at<float2>(p, p->ws.eq_partial);
   c.ybase[KIND_INPUT] = const_cast<float*>(src);
@@ -72,9 +83,11 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
 
 int check_ready(const Plan* p) {
   if (!p->dev_ws) return fail(GRAFX_ESTATE, "workspace not bound (grafx_plan_bind_workspace)");
-  for (int t : {GRAFX_T_GAIN, GRAFX_T_IMAGER, GRAFX_T_EQ, GRAFX_T_COMP, GRAFX_T_DELAY})
+  for (int t : {GRAFX_T_GAIN, GRAFX_T_IMAGER, GRAFX_T_EQ, GRAFX_T_COMP, GRAFX_T_DELAY, GRAFX_T_REVERB})
     if (p->n_type_rows[t] > 0 && !p->params[t])
       return fail(GRAFX_ESTATE, "parameters of type " + std::to_string(t) + " not bound");
+  if (p->n_type_rows[GRAFX_T_REVERB] > 0 && !p->rv_noise)
+    return fail(GRAFX_ESTATE, "reverb noise not bound (grafx_bind_reverb_noise)");
   return GRAFX_OK;
 }
 
@@ -85,6 +98,7 @@ int param_cols(int t) {
     case GRAFX_T_EQ: return 8;
     case GRAFX_T_COMP: return 4;
     case GRAFX_T_DELAY: return DL_COLS;
+    case GRAFX_T_REVERB: return RV_COLS;
     default: return 0;
   }
 }
@@ -271,6 +285,7 @@ int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* s
   put(p->ws.eq_cos, p->eq_cos.data(), p->eq_cos.size() * 4);
   put(p->ws.eq_hann, p->eq_hann.data(), p->eq_hann.size() * 4);
   put(p->ws.eq_band, p->eq_band.data(), p->eq_band.size() * 4);
+  put(p->ws.rv_band, p->rv_band.data(), p->rv_band.size() * 4);
   put(p->ws.loss_rows, p->loss.rows.data(), p->loss.rows.size() * sizeof(LossRow));
   put(p->ws.loss_items, p->loss.items.data(), p->loss.items.size() * sizeof(int4_));
   int rc = cuda_check(cudaMemcpyAsync(dev_ws, img.data(), img.size(), cudaMemcpyHostToDevice, s), "upload tables");
@@ -293,6 +308,14 @@ int grafx_bind_params(grafx_plan* p, int32_t type, const float* dev, int64_t row
   if (rows > 0 && !dev) return fail(GRAFX_EINVAL, "null parameter pointer");
   p->params[type] = dev;
   p->param_rows[type] = rows;
+  return GRAFX_OK;
+}
+
+int grafx_bind_reverb_noise(grafx_plan* p, const float* dev, int64_t n) {
+  if (!p) return fail(GRAFX_EINVAL, "null plan");
+  if (n != 2 * int64_t(RV_LEN)) return fail(GRAFX_ESHAPE, "reverb noise must hold 2 x 88200 floats");
+  if (!dev) return fail(GRAFX_EINVAL, "null noise pointer");
+  p->rv_noise = dev;
   return GRAFX_OK;
 }
 
@@ -321,6 +344,11 @@ int grafx_render_steps(grafx_plan* p, const float* sources, float* out, int32_t 
       case GRAFX_T_DELAY:
         launches += launch_delay(0, c, st.node_begin, st.node_end, s);
         launches += launch_delay(1, c, st.fitem_begin, st.fitem_count, s);
+        break;
+      case GRAFX_T_REVERB:
+        launches += launch_delay(3, c, st.fitem_begin, st.fitem_count, s);   // u window spectra
+        launches += launch_reverb(0, c, st.node_begin, st.node_end, s);
+        launches += launch_reverb(1, c, st.node_begin, st.node_end, s);
         break;
       default:
         launches += launch_ew_fwd(st.type, c, st.fitem_begin, st.fitem_count, s);
@@ -359,6 +387,11 @@ int grafx_backprop_steps(grafx_plan* p, const float* sources, const float* d_out
         clear_step_flags(p, st.bitem_begin, st.bitem_count, 2 * k + 1, s);
         launches += launch_comp(1, c, st.bitem_begin, st.bitem_count, 2 * k + 1, s);
         if (c.dparams) launches += launch_comp(2, c, st.node_begin, st.node_end, 0, s);
+        break;
+      case GRAFX_T_REVERB:
+        launches += launch_delay(3, c, st.dsub_begin[0], st.dsub_count[0], s);   // ybar spectra
+        launches += launch_reverb(2, c, st.node_begin, st.node_end, s);
+        if (c.dparams) launches += launch_reverb(3, c, st.node_begin, st.node_end, s);
         break;
       case GRAFX_T_DELAY:
         launches += launch_delay(2, c, st.dsub_begin[0], st.dsub_count[0], s);
@@ -448,6 +481,7 @@ int grafx_step_graph_create(grafx_plan* p, const float* sources, float* out, con
   DevCtx c0 = make_ctx(p, sources, out, nullptr, nullptr);
   launch_eq(-1, c0, 0, 0, s);
   launch_delay(-1, c0, 0, 0, s);
+  launch_reverb(-1, c0, 0, 0, s);
   launch_loss(-1, make_loss(p, out, target), s);
   rc = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
   if (rc) return rc;

@@ -36,6 +36,17 @@ struct DevCtx {
   float2* dl_R;         // per delay node and lag partition: accumulated spectra
   float* dl_r;          // per delay node and channel: lags r[n], n from -DL_B
   float dl_taylor[9];   // Taylor coefficients of sum_k k q^k near q = 1
+  const float* rv_noise;  // reverb noise [2][RV_LEN] (mid, side)
+  const float* rv_band;   // [RV_BINS][RV_BANDS] band interpolation
+  float2* rv_U;           // noise STFT [2][RV_F][RV_BINS]
+  float2* rv_fr;          // per reverb node: IR frames [RV_F][RV_N] (mid, side)
+  float* rv_h;            // per reverb node: h_l, h_r [2][RV_HLEN]
+  float2* rv_H;           // per reverb node: partition spectra [RV_P][DL_M]
+  float2* rv_Y;           // per reverb node: block spectra [rv_nbmax][DL_M]
+  float2* rv_R;           // per reverb node: lag partition spectra [RV_P][DL_M]
+  float* rv_r;            // per reverb node: lags [2][RV_HLEN]
+  float2* rv_mm;          // per reverb node: mask-gradient terms [RV_F][2][RV_BINS]
+  int32_t rv_nbmax;
   float4* partial;
   float2* eq_partial;
   float* ybase[3];

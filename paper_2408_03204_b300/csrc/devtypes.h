@@ -52,6 +52,17 @@ constexpr int DL_NLAG = DL_P * DL_B;
 constexpr int DL_CHUNK = 32;       // bins per accumulation work item
 constexpr int DL_MAX_BLOCKS = 128; // signals with delay nodes: at most 2^19 samples
 
+// filtered-noise reverb (Eq. 6-7)
+constexpr int RV_LEN = 88200;      // impulse response: 2 s at 44.1 kHz
+constexpr int RV_N = 1024;         // STFT size
+constexpr int RV_HOP = 256;
+constexpr int RV_F = (RV_LEN + RV_HOP - 1) / RV_HOP;   // 345 frames
+constexpr int RV_BINS = RV_N / 2 + 1;
+constexpr int RV_BANDS = 12;
+constexpr int RV_COLS = 50;        // [mid, side] x [H0, Hd] x 12 bands, q_dry, q_wet
+constexpr int RV_P = (RV_LEN + DL_B - 1) / DL_B;       // 22 partitions of 4096 taps
+constexpr int RV_HLEN = RV_P * DL_B;
+
 // status bits written by kernels
 constexpr uint32_t ST_TIMEOUT = 1u;
 constexpr uint32_t ST_BOUNDS = 2u;

@@ -123,8 +123,9 @@ __global__ void __launch_bounds__(DL_M / 16) k_delay_spec(DevCtx c, int item0, i
     const int4_ w = c.items[item0 + it];
     const int v = w.x, idx = w.y, kind = w.z;
     const NodeDev nd = c.nodes[v];
-    const bool adj = kind == 1;
-    const int start = idx * DL_B, count = adj ? DL_B : 2 * DL_B;
+    // kind 0: u window of 2B; 1: ybar block of B (zero-padded); 2: ybar window of 2B
+    const bool adj = kind != 0;
+    const int start = idx * DL_B, count = kind == 1 ? DL_B : 2 * DL_B;
     const int e0 = adj ? c.tcsr_ptr[v] : c.csr_ptr[v];
     const int e1 = adj ? c.tcsr_ptr[v + 1] : c.csr_ptr[v + 1];
     __syncthreads();

@@ -1,0 +1,407 @@
+// Filtered-noise reverb (Sec. 3 "Reverb", Eq. 6-7).
+//
+// Impulse response per node (forward): the STFT of the two noise buffers (mid, side;
+// FFT 1024, hop 256, periodic Hann; computed once per render) is multiplied by the
+// masks M_x[k, m] = exp(H0_x[k] + m Hd_x[k]) (12-band log-frequency interpolation),
+// inverted frame by frame (mid + i side packed in one complex FFT), windowed and
+// overlap-added, divided by sum w^2, and turned into left/right as (mid +- side)/2.
+// Convolution: 22 partitions of 4096 taps; y = e^{q_dry} u + e^{q_wet} (h * u) by
+// overlap-save with 8192-point spectra: Y_b = sum_p H_p X_{b-1-p} per channel (u
+// windows of 2B samples from the delay's spectrum kernel), one inverse per block.
+// Backward: the input adjoint correlates ybar with h through the same partitions
+// (Ubar_b = sum_p conj(H_p) Ybar_{b+p} on 2B windows of ybar); the lags
+// r_x[n] = sum_t ybar[t] u[t - n] come from R_p = sum_b X_{b-p-1} conj(Ybar_b) on
+// B blocks of ybar; dL/dh = e^{q_wet} r is pushed back through the overlap-add, the
+// per-frame inverse FFT (its adjoint is a forward FFT with the one-sided weights c_k/N),
+// the masks and the band matrix; dq_dry = e^{q_dry} sum_x r_x[0] and
+// dq_wet = e^{q_wet} sum_x sum_n h_x[n] r_x[n].
+#include <cmath>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "kernels.h"
+
+namespace grafx {
+
+__device__ __forceinline__ float rv_hann(const float2_* tw, int j) { return 0.5f - 0.5f * tw[j * (TWIDDLE_N / RV_N)].x; }
+
+// Split a packed spectrum Z of a + i b (a, b real) at bin k into A[k], B[k].
+__device__ __forceinline__ void rv_split(float2 z, float2 zm, float2* a, float2* b) {
+  *a = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+  *b = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+}
+
+__device__ __forceinline__ void rv_masks(const DevCtx& c, const float* q, int k, int m, float* M) {
+  const float* row = c.rv_band + k * RV_BANDS;
+#pragma unroll
+  for (int x = 0; x < 2; ++x) {
+    float h0 = 0.f, hd = 0.f;
+    for (int b = 0; b < RV_BANDS; ++b) {
+      h0 += row[b] * q[x * 24 + b];
+      hd += row[b] * q[x * 24 + 12 + b];
+    }
+    M[x] = expf(h0 + float(m) * hd);
+  }
+}
+
+// U_x[m][k], k <= 512, of both noise buffers (packed mid + i side per frame).
+__global__ void __launch_bounds__(RV_N / 16) k_rv_noise_stft(DevCtx c) {
+  __shared__ float2 buf[fft::Padded<RV_N>::size];
+  const int m = blockIdx.x;
+  for (int j = threadIdx.x; j < RV_N; j += blockDim.x) {
+    const int t = m * RV_HOP + j;
+    const float w = rv_hann(c.tw, j);
+    buf[fft::pad(j)] = t < RV_LEN ? make_float2(w * c.rv_noise[t], w * c.rv_noise[RV_LEN + t]) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft::forward<RV_N>(buf, c.ptw, threadIdx.x, true);
+  for (int k = threadIdx.x; k <= RV_N / 2; k += blockDim.x) {
+    float2 a, b;
+    rv_split(buf[fft::pad(k)], buf[fft::pad((RV_N - k) & (RV_N - 1))], &a, &b);
+    c.rv_U[size_t(m) * RV_BINS + k] = a;
+    c.rv_U[size_t(RV_F + m) * RV_BINS + k] = b;
+  }
+}
+
+// Masked noise frame m of one node, inverted and windowed: (mid, side) per sample.
+__global__ void __launch_bounds__(RV_N / 16) k_rv_ir_frames(DevCtx c, int node_begin) {
+  __shared__ float2 buf[fft::Padded<RV_N>::size];
+  const int m = blockIdx.x, v = node_begin + blockIdx.y;
+  const NodeDev nd = c.nodes[v];
+  const int ri = c.ext[v].z;
+  const float* q = c.params + size_t(nd.prow) * RV_COLS;
+  for (int k = threadIdx.x; k <= RV_N / 2; k += blockDim.x) {
+    float M[2];
+    rv_masks(c, q, k, m, M);
+    float2 hm = c.rv_U[size_t(m) * RV_BINS + k], hs = c.rv_U[size_t(RV_F + m) * RV_BINS + k];
+    hm = make_float2(hm.x * M[0], hm.y * M[0]);
+    hs = make_float2(hs.x * M[1], hs.y * M[1]);
+    if (k == 0 || k == RV_N / 2) hm.y = hs.y = 0.f;   // real DC / Nyquist (one-sided inverse)
+    // W = Hm + i Hs at k, conj(Hm) + i conj(Hs) at N - k; stored conjugated for the inverse
+    const float2 wk = make_float2(hm.x - hs.y, hm.y + hs.x);
+    buf[fft::pad(k)] = make_float2(wk.x, -wk.y);
+    if (k > 0 && k < RV_N / 2) {
+      const float2 wm = make_float2(hm.x + hs.y, -hm.y + hs.x);
+      buf[fft::pad(RV_N - k)] = make_float2(wm.x, -wm.y);
+    }
+  }
+  __syncthreads();
+  fft::forward<RV_N>(buf, c.ptw, threadIdx.x, true);
+  float2* fr = c.rv_fr + (size_t(ri) * RV_F + m) * RV_N;
+  const float inv = 1.f / float(RV_N);
+  for (int j = threadIdx.x; j < RV_N; j += blockDim.x) {
+    const float2 z = buf[fft::pad(j)];
+    const float w = rv_hann(c.tw, j) * inv;
+    fr[j] = make_float2(w * z.x, -w * z.y);   // conj of the result: (mid, side)
+  }
+}
+
+__device__ __forceinline__ float rv_ola_norm(const float2_* tw, int n, int* m0, int* m1) {
+  const int hi = min(RV_F - 1, n / RV_HOP);
+  const int lo = n - RV_N + 1 <= 0 ? 0 : (n - RV_N + 1 + RV_HOP - 1) / RV_HOP;
+  float D = 0.f;
+  for (int m = lo; m <= hi; ++m) {
+    const float w = rv_hann(tw, n - m * RV_HOP);
+    D += w * w;
+  }
+  *m0 = lo;
+  *m1 = hi;
+  return D;
+}
+
+// h_l, h_r of one node (overlap-add / sum w^2, mid/side -> left/right), zero past RV_LEN.
+__global__ void k_rv_ir_ola(DevCtx c, int node_begin) {
+  const int v = node_begin + blockIdx.y;
+  const int ri = c.ext[v].z;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= RV_HLEN) return;
+  float hl = 0.f, hr = 0.f;
+  if (n < RV_LEN) {
+    int lo, hi;
+    const float D = rv_ola_norm(c.tw, n, &lo, &hi);
+    if (D > 1e-8f) {
+      float sm = 0.f, ss = 0.f;
+      const float2* fr = c.rv_fr + size_t(ri) * RV_F * RV_N;
+      for (int m = lo; m <= hi; ++m) {
+        const float2 z = fr[size_t(m) * RV_N + n - m * RV_HOP];
+        sm += z.x;
+        ss += z.y;
+      }
+      sm /= D;
+      ss /= D;
+      hl = 0.5f * (sm + ss);
+      hr = 0.5f * (sm - ss);
+    }
+  }
+  c.rv_h[(size_t(ri) * 2) * RV_HLEN + n] = hl;
+  c.rv_h[(size_t(ri) * 2 + 1) * RV_HLEN + n] = hr;
+}
+
+// Partition spectra H_p = FFT([h_l + i h_r over [pB, pB+B), zeros]).
+__global__ void __launch_bounds__(DL_M / 16) k_rv_hspec(DevCtx c, int node_begin) {
+  extern __shared__ float2 smem2[];
+  float2* buf = smem2;
+  const int p = blockIdx.x, v = node_begin + blockIdx.y;
+  const int ri = c.ext[v].z;
+  const float* hl = c.rv_h + (size_t(ri) * 2) * RV_HLEN + p * DL_B;
+  const float* hr = hl + RV_HLEN;
+  for (int i = threadIdx.x; i < DL_M; i += blockDim.x)
+    buf[fft::pad(i)] = i < DL_B ? make_float2(hl[i], hr[i]) : make_float2(0.f, 0.f);
+  __syncthreads();
+  fft::forward<DL_M>(buf, c.ptw, threadIdx.x, true);
+  float2* out = c.rv_H + (size_t(ri) * RV_P + p) * DL_M;
+  for (int k = threadIdx.x; k < DL_M; k += blockDim.x) out[k] = buf[fft::pad(k)];
+}
+
+// Load the channel-split spectra of `count` slots for DL_CHUNK bins into smem
+// ([slot][bin][2 ch]).
+__device__ __forceinline__ void rv_load_split(const float2* base, int count, int k0, float2* dst) {
+  for (int i = threadIdx.x; i < count * DL_CHUNK; i += blockDim.x) {
+    const int s = i / DL_CHUNK, kk = i % DL_CHUNK, k = k0 + kk, km = (DL_M - k) & (DL_M - 1);
+    const float2* spec = base + size_t(s) * DL_M;
+    float2 a, b;
+    rv_split(spec[k], spec[km], &a, &b);
+    dst[(size_t(s) * DL_CHUNK + kk) * 2] = a;
+    dst[(size_t(s) * DL_CHUNK + kk) * 2 + 1] = b;
+  }
+}
+
+__device__ __forceinline__ float2 cmac(float2 acc, float2 a, float2 b, bool conj_a) {
+  const float ay = conj_a ? -a.y : a.y;
+  return make_float2(acc.x + a.x * b.x - ay * b.y, acc.y + a.x * b.y + ay * b.x);
+}
+
+// what = 0: forward Y_b = sum_p H_p X_{b-1-p}; 1: input adjoint
+// Ubar_b = sum_p conj(H_p) Ybarwin_{b+p}; 2: lags R_p = sum_b X_{b-p-1} conj(Ybarblk_b).
+// grid (DL_M / DL_CHUNK, reverb nodes), 256 threads: bin kk = tid % 32, lane group g.
+template <int WHAT>
+__global__ void __launch_bounds__(256) k_rv_acc(DevCtx c, int node_begin) {
+  extern __shared__ float2 sm[];
+  const int v = node_begin + blockIdx.y, k0 = blockIdx.x * DL_CHUNK;
+  const int4_ e = c.ext[v];
+  const int ri = e.z, nb = e.w, nw = nb + RV_P;
+  const int kk = threadIdx.x % DL_CHUNK, g = threadIdx.x / DL_CHUNK, ng = blockDim.x / DL_CHUNK;
+  // slots: [0, nw) u windows from -RV_P; [nw, nw + nb) ybar blocks; [nw + nb, 2 nw + nb) ybar windows from 0
+  const float2* spec = c.dl_spec + size_t(e.x) * DL_M;
+  float2* Hs = sm;                                        // [RV_P][chunk][2]
+  float2* S = WHAT == 2 ? sm : sm + size_t(RV_P) * DL_CHUNK * 2;
+  if (WHAT != 2) rv_load_split(c.rv_H + size_t(ri) * RV_P * DL_M, RV_P, k0, Hs);
+  if (WHAT == 0) rv_load_split(spec, nw, k0, S);
+  if (WHAT == 1) rv_load_split(spec + size_t(nw + nb) * DL_M, nw, k0, S);
+  if (WHAT == 2) {
+    rv_load_split(spec, nw, k0, S);
+    rv_load_split(spec + size_t(nw) * DL_M, nb, k0, S + size_t(nw) * DL_CHUNK * 2);
+  }
+  __syncthreads();
+  const int k = k0 + kk;
+  if (WHAT == 0 || WHAT == 1) {
+    for (int b = g; b < nb; b += ng) {
+      float2 al = make_float2(0.f, 0.f), ar = make_float2(0.f, 0.f);
+      for (int p = 0; p < RV_P; ++p) {
+        const int s = WHAT == 0 ? b - 1 - p + RV_P : b + p;
+        const float2 hl = Hs[(size_t(p) * DL_CHUNK + kk) * 2], hr = Hs[(size_t(p) * DL_CHUNK + kk) * 2 + 1];
+        const float2 xl = S[(size_t(s) * DL_CHUNK + kk) * 2], xr = S[(size_t(s) * DL_CHUNK + kk) * 2 + 1];
+        al = cmac(al, hl, xl, WHAT == 1);
+        ar = cmac(ar, hr, xr, WHAT == 1);
+      }
+      c.rv_Y[(size_t(ri) * c.rv_nbmax + b) * DL_M + k] = make_float2(al.x - ar.y, al.y + ar.x);
+    }
+  } else {
+    const float2* X = S;
+    const float2* Yb = S + size_t(nw) * DL_CHUNK * 2;
+    for (int p = g; p < RV_P; p += ng) {
+      float2 al = make_float2(0.f, 0.f), ar = make_float2(0.f, 0.f);
+      for (int b = 0; b < nb; ++b) {
+        const int s = b - p - 1 + RV_P;
+        const float2 yl = Yb[(size_t(b) * DL_CHUNK + kk) * 2], yr = Yb[(size_t(b) * DL_CHUNK + kk) * 2 + 1];
+        const float2 xl = X[(size_t(s) * DL_CHUNK + kk) * 2], xr = X[(size_t(s) * DL_CHUNK + kk) * 2 + 1];
+        al = cmac(al, yl, xl, true);   // x conj(y) = conj(y) x
+        ar = cmac(ar, yr, xr, true);
+      }
+      c.rv_R[(size_t(ri) * RV_P + p) * DL_M + k] = make_float2(al.x - ar.y, al.y + ar.x);
+    }
+  }
+}
+
+// Inverse of a packed block spectrum; what = 0: forward output block b (samples
+// [B, 2B) of the circular result are the linear convolution), 1: input adjoint block
+// b (samples [0, B) are the correlation), 2: lags of partition p (IDFT[B - nu]).
+template <int WHAT>
+__global__ void __launch_bounds__(DL_M / 16) k_rv_inv(DevCtx c, int node_begin) {
+  extern __shared__ float2 smem2[];
+  float2* buf = smem2;
+  const int b = blockIdx.x, v = node_begin + blockIdx.y;
+  const int4_ e = c.ext[v];
+  const int ri = e.z, nb = e.w;
+  if (WHAT != 2 && b >= nb) return;
+  const NodeDev nd = c.nodes[v];
+  const float2* Z = WHAT == 2 ? c.rv_R + (size_t(ri) * RV_P + b) * DL_M : c.rv_Y + (size_t(ri) * c.rv_nbmax + b) * DL_M;
+  for (int k = threadIdx.x; k < DL_M; k += blockDim.x) {
+    const float2 z = Z[k];
+    buf[fft::pad(k)] = make_float2(z.x, -z.y);
+  }
+  __syncthreads();
+  fft::forward<DL_M>(buf, c.ptw, threadIdx.x, true);
+  const float inv = 1.f / float(DL_M);
+  if (WHAT == 2) {
+    for (int nu = threadIdx.x; nu < DL_B; nu += blockDim.x) {
+      const float2 z = buf[fft::pad((DL_B - nu) & (DL_M - 1))];
+      c.rv_r[(size_t(ri) * 2) * RV_HLEN + b * DL_B + nu] = z.x * inv;
+      c.rv_r[(size_t(ri) * 2 + 1) * RV_HLEN + b * DL_B + nu] = -z.y * inv;
+    }
+    return;
+  }
+  const float* q = c.params + size_t(nd.prow) * RV_COLS;
+  const float a_dry = expf(q[48]), a_wet = expf(q[49]);
+  float* row = WHAT == 0 ? yrow_w(c, nd) : arow_w(c, nd);
+  const int e0 = WHAT == 0 ? c.csr_ptr[v] : c.tcsr_ptr[v];
+  const int e1 = WHAT == 0 ? c.csr_ptr[v + 1] : c.tcsr_ptr[v + 1];
+  for (int j = threadIdx.x; j < DL_B; j += blockDim.x) {
+    const int t = b * DL_B + j;
+    if (t >= nd.pitch) continue;
+    const float2 z = buf[fft::pad(WHAT == 0 ? DL_B + j : j)];
+    float dl = 0.f, dr = 0.f;
+    if (t < nd.len)
+      for (int ed = e0; ed < e1; ++ed) {
+        const NodeDev s = c.nodes[WHAT == 0 ? c.csr_src[ed] : c.tcsr_dst[ed]];
+        const float* r = WHAT == 0 ? yrow(c, s) : arow(c, s);
+        dl += r[t];
+        dr += r[nd.pitch + t];
+      }
+    const bool in = t < nd.len;
+    row[t] = in ? a_dry * dl + a_wet * z.x * inv : 0.f;
+    row[nd.pitch + t] = in ? a_dry * dr - a_wet * z.y * inv : 0.f;
+  }
+}
+
+// Adjoint of the IR synthesis for frame m of one node: per channel and bin, the mask
+// gradient times the mask, M dL/dM, and m M dL/dM.
+__global__ void __launch_bounds__(RV_N / 16) k_rv_gfr(DevCtx c, int node_begin) {
+  __shared__ float2 buf[fft::Padded<RV_N>::size];
+  const int m = blockIdx.x, v = node_begin + blockIdx.y;
+  const NodeDev nd = c.nodes[v];
+  const int ri = c.ext[v].z;
+  const float* q = c.params + size_t(nd.prow) * RV_COLS;
+  const float a_wet = expf(q[49]);
+  const float* rl = c.rv_r + (size_t(ri) * 2) * RV_HLEN;
+  const float* rr = rl + RV_HLEN;
+  for (int j = threadIdx.x; j < RV_N; j += blockDim.x) {
+    const int n = m * RV_HOP + j;
+    float gm = 0.f, gs = 0.f;
+    if (n < RV_LEN) {
+      int lo, hi;
+      const float D = rv_ola_norm(c.tw, n, &lo, &hi);
+      if (D > 1e-8f) {
+        const float hbl = a_wet * rl[n], hbr = a_wet * rr[n];
+        const float w = rv_hann(c.tw, j) / D;
+        gm = w * 0.5f * (hbl + hbr);
+        gs = w * 0.5f * (hbl - hbr);
+      }
+    }
+    buf[fft::pad(j)] = make_float2(gm, gs);
+  }
+  __syncthreads();
+  fft::forward<RV_N>(buf, c.ptw, threadIdx.x, true);
+  float2* out = c.rv_mm + (size_t(ri) * RV_F + m) * 2 * RV_BINS;
+  for (int k = threadIdx.x; k <= RV_N / 2; k += blockDim.x) {
+    float2 A[2];
+    rv_split(buf[fft::pad(k)], buf[fft::pad((RV_N - k) & (RV_N - 1))], &A[0], &A[1]);
+    const float ck = (k == 0 || k == RV_N / 2 ? 1.f : 2.f) / float(RV_N);
+    float M[2];
+    rv_masks(c, q, k, m, M);
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+      const float2 U = c.rv_U[size_t(x * RV_F + m) * RV_BINS + k];
+      const float mbar = ck * (A[x].x * U.x + A[x].y * U.y);
+      const float mm = M[x] * mbar;
+      out[x * RV_BINS + k] = make_float2(mm, float(m) * mm);
+    }
+  }
+}
+
+// Band gradients (sum over frames, then the band matrix), dq_dry and dq_wet.
+__global__ void __launch_bounds__(256) k_rv_grad(DevCtx c, int node_begin) {
+  __shared__ float g0[2][RV_BINS], gd[2][RV_BINS];
+  __shared__ float red[2 * 32];
+  const int v = node_begin + blockIdx.x;
+  const NodeDev nd = c.nodes[v];
+  const int ri = c.ext[v].z;
+  const float* q = c.params + size_t(nd.prow) * RV_COLS;
+  float* out = c.dparams + size_t(nd.prow) * RV_COLS;
+  const float2* mm = c.rv_mm + size_t(ri) * RV_F * 2 * RV_BINS;
+  for (int i = threadIdx.x; i < 2 * RV_BINS; i += blockDim.x) {
+    float s0 = 0.f, s1 = 0.f;
+    for (int m = 0; m < RV_F; ++m) {
+      const float2 z = mm[size_t(m) * 2 * RV_BINS + i];
+      s0 += z.x;
+      s1 += z.y;
+    }
+    g0[i / RV_BINS][i % RV_BINS] = s0;
+    gd[i / RV_BINS][i % RV_BINS] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 48) {
+    const int x = threadIdx.x / 24, r = threadIdx.x % 24, b = r % 12;
+    const float* src = r < 12 ? g0[x] : gd[x];
+    float s = 0.f;
+    for (int k = 0; k < RV_BINS; ++k) s += c.rv_band[k * RV_BANDS + b] * src[k];
+    out[threadIdx.x] = s;
+  }
+  const float* rl = c.rv_r + (size_t(ri) * 2) * RV_HLEN;
+  const float* hl = c.rv_h + (size_t(ri) * 2) * RV_HLEN;
+  float acc[2] = {0.f, 0.f};
+  for (int n = threadIdx.x; n < RV_LEN; n += blockDim.x)
+    acc[0] += hl[n] * rl[n] + hl[RV_HLEN + n] * rl[RV_HLEN + n];
+  block_sum<2>(acc, red);
+  if (threadIdx.x == 0) {
+    out[48] = expf(q[48]) * (rl[0] + rl[RV_HLEN]);
+    out[49] = expf(q[49]) * acc[0];
+  }
+}
+
+int launch_reverb(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
+  static bool init = false;
+  const size_t sm_fft = sizeof(float2) * fft::Padded<DL_M>::size;
+  const int nbm = c.rv_nbmax;
+  const size_t sm0 = sizeof(float2) * 2 * DL_CHUNK * size_t(RV_P + nbm + RV_P);
+  const size_t sm2 = sizeof(float2) * 2 * DL_CHUNK * size_t(nbm + RV_P + nbm);
+  if (!init) {
+    cudaFuncSetAttribute(k_rv_hspec, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_fft));
+    cudaFuncSetAttribute(k_rv_inv<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_fft));
+    cudaFuncSetAttribute(k_rv_inv<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_fft));
+    cudaFuncSetAttribute(k_rv_inv<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_fft));
+    const int maxsm = int(sizeof(float2) * 2 * DL_CHUNK * size_t(2 * DL_MAX_BLOCKS + RV_P + RV_P));
+    cudaFuncSetAttribute(k_rv_acc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
+    cudaFuncSetAttribute(k_rv_acc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
+    cudaFuncSetAttribute(k_rv_acc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
+    init = true;
+  }
+  if (what < 0 || b <= a) return 0;
+  const int n = b - a;   // reverb nodes of the step: [a, b)
+  const dim3 chunks(DL_M / DL_CHUNK, n);
+  switch (what) {
+    case 0:  // impulse responses and their partition spectra
+      k_rv_noise_stft<<<RV_F, RV_N / 16, 0, s>>>(c);
+      k_rv_ir_frames<<<dim3(RV_F, n), RV_N / 16, 0, s>>>(c, a);
+      k_rv_ir_ola<<<dim3((RV_HLEN + 255) / 256, n), 256, 0, s>>>(c, a);
+      k_rv_hspec<<<dim3(RV_P, n), DL_M / 16, sm_fft, s>>>(c, a);
+      return 4;
+    case 1:  // forward convolution (after the u window spectra)
+      k_rv_acc<0><<<chunks, 256, sm0, s>>>(c, a);
+      k_rv_inv<0><<<dim3(nbm, n), DL_M / 16, sm_fft, s>>>(c, a);
+      return 2;
+    case 2:  // input adjoint (after the ybar spectra)
+      k_rv_acc<1><<<chunks, 256, sm0, s>>>(c, a);
+      k_rv_inv<1><<<dim3(nbm, n), DL_M / 16, sm_fft, s>>>(c, a);
+      return 2;
+    case 3:  // parameter gradients
+      k_rv_acc<2><<<chunks, 256, sm2, s>>>(c, a);
+      k_rv_inv<2><<<dim3(RV_P, n), DL_M / 16, sm_fft, s>>>(c, a);
+      k_rv_gfr<<<dim3(RV_F, n), RV_N / 16, 0, s>>>(c, a);
+      k_rv_grad<<<n, 256, 0, s>>>(c, a);
+      return 4;
+  }
+  return 0;
+}
+
+}  // namespace grafx

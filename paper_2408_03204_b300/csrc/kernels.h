@@ -26,6 +26,10 @@ int launch_comp(int what, const DevCtx& c, int a, int b, int ticket, cudaStream_
 // spectra, 4 partition accumulation, 5 lags (inverse FFTs), 6 gradients; < 0 attributes
 int launch_delay(int what, const DevCtx& c, int a, int b, cudaStream_t s);
 
+// reverb over the reverb nodes [a, b) of a step: what = 0 impulse responses, 1 forward
+// convolution, 2 input adjoint, 3 parameter gradients; < 0 attributes only
+int launch_reverb(int what, const DevCtx& c, int a, int b, cudaStream_t s);
+
 struct LossLaunch {
   const LossRow* rows;
   const int4_* items;   // (row, resolution, first frame, group)

@@ -94,9 +94,9 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
   int rc = validate(p->types, p->edges);
   if (rc) return rc;
   for (int32_t v = 0; v < n; ++v) {
-    if (p->types[v] == GRAFX_T_REVERB) return fail(GRAFX_ETYPE, "reverb nodes are not supported by this build");
-    if (p->types[v] == GRAFX_T_DELAY && p->L[p->node_graph[v]] > int64_t(DL_MAX_BLOCKS) * DL_B)
-      return fail(GRAFX_ESHAPE, "graphs with delay nodes are limited to 2^19 samples");
+    if ((p->types[v] == GRAFX_T_DELAY || p->types[v] == GRAFX_T_REVERB) &&
+        p->L[p->node_graph[v]] > int64_t(DL_MAX_BLOCKS) * DL_B)
+      return fail(GRAFX_ESHAPE, "graphs with delay or reverb nodes are limited to 2^19 samples");
   }
   if (opts.eq_taps < 3 || opts.eq_taps % 2 == 0 || opts.eq_taps > 2047)
     return fail(GRAFX_EINVAL, "eq_taps must be odd in [3, 2047]");
@@ -233,6 +233,15 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
             for (int32_t t0 = 0; t0 < L; t0 += DL_TILE) fwd.push_back({v, t0, ch, 0});
           break;
         }
+        case GRAFX_T_REVERB: {
+          // u window spectra (kind 0) from window -RV_P; slots: windows, ybar blocks, ybar windows
+          const int32_t nb = (L + DL_B - 1) / DL_B, nw = nb + RV_P;
+          p->node_ext[v] = int4_{p->n_dl_slots, 0, p->n_reverb++, nb};
+          p->rv_nbmax = std::max(p->rv_nbmax, nb);
+          for (int32_t w = -RV_P; w < nb; ++w) fwd.push_back({v, w, 0, p->n_dl_slots + w + RV_P});
+          p->n_dl_slots += nw + nb + nw;
+          break;
+        }
         case GRAFX_T_COMP: {
           int32_t nc = (L + p->comp_chunk - 1) / p->comp_chunk;
           p->node_ext[v].z = chunk_id;
@@ -250,6 +259,17 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
     StepInfo& s = p->steps[k];
     s.bitem_begin = int32_t(bwd.size());
     if (s.type == GRAFX_T_OUT) { s.bitem_count = 0; continue; }  // adjoint rows alias d_out
+    if (s.type == GRAFX_T_REVERB) {
+      for (int i = 0; i < 5; ++i) s.dsub_begin[i] = int32_t(bwd.size()), s.dsub_count[i] = 0;
+      for (int32_t v = s.node_begin; v < s.node_end; ++v) {
+        const int32_t nb = p->node_ext[v].w, nw = nb + RV_P, base = p->node_ext[v].x;
+        for (int32_t b = 0; b < nb; ++b) bwd.push_back({v, b, 1, base + nw + b});
+        for (int32_t w = 0; w < nw; ++w) bwd.push_back({v, w, 2, base + nw + nb + w});
+      }
+      s.dsub_count[0] = int32_t(bwd.size()) - s.dsub_begin[0];
+      s.bitem_count = int32_t(bwd.size()) - s.bitem_begin;
+      continue;
+    }
     if (s.type == GRAFX_T_DELAY) {
       std::vector<int4_> sub[5];
       for (int32_t v = s.node_begin; v < s.node_end; ++v) {
@@ -343,6 +363,27 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
       p->dl_taylor[j] = s / DL_NFFT / fact;
     }
   }
+  // reverb band interpolation over the 513 STFT bins (same rule as the EQ's bands)
+  {
+    const int NB = RV_BANDS;
+    double cb[RV_BANDS], lc[RV_BANDS];
+    for (int b = 0; b < NB; ++b) {
+      cb[b] = 20.0 * std::pow(1000.0, (b + 0.5) / NB);
+      lc[b] = std::log2(cb[b]);
+    }
+    p->rv_band.assign(size_t(RV_BINS) * NB, 0.f);
+    for (int k = 0; k < RV_BINS; ++k) {
+      const double f = double(k) * opts.sample_rate / RV_N;
+      float* row = p->rv_band.data() + size_t(k) * NB;
+      if (f <= cb[0]) { row[0] = 1.f; continue; }
+      if (f >= cb[NB - 1]) { row[NB - 1] = 1.f; continue; }
+      int b = 0;
+      while (b + 1 < NB && cb[b + 1] <= f) ++b;
+      const double w = (std::log2(f) - lc[b]) / (lc[b + 1] - lc[b]);
+      row[b] = float(1.0 - w);
+      row[b + 1] = float(w);
+    }
+  }
   // FFT pass twiddles W_{Ns R}^{r k} at [(r-1) Ns + k] for every pass of every size
   p->ptw.assign(fft::PTW_TOTAL, float2_{0.f, 0.f});
   for (int M = 512; M <= 8192; M *= 2) {
@@ -413,6 +454,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
     w.eq_cos = take(4 * p->eq_cos.size());
     w.eq_hann = take(4 * p->eq_hann.size());
     w.eq_band = take(4 * p->eq_band.size());
+    w.rv_band = take(4 * p->rv_band.size());
     size_t nrow = std::max<size_t>(p->loss.rows.size(), 1);
     w.loss_rows = take(sizeof(LossRow) * nrow);
     w.loss_items = take(sizeof(int4_) * std::max<size_t>(p->loss.items.size(), 1));
@@ -430,6 +472,15 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
     w.dl_spec = take(8 * size_t(std::max(p->n_dl_slots, 1)) * DL_M);
     w.dl_R = take(8 * size_t(std::max(p->n_delay, 1)) * DL_P * DL_M);
     w.dl_r = take(4 * size_t(std::max(p->n_delay, 1)) * 2 * DL_NLAG);
+    const size_t nr = size_t(std::max(p->n_reverb, 1));
+    w.rv_U = take(8 * size_t(2) * RV_F * RV_BINS);
+    w.rv_fr = take(8 * nr * RV_F * RV_N);
+    w.rv_h = take(4 * nr * 2 * RV_HLEN);
+    w.rv_H = take(8 * nr * RV_P * DL_M);
+    w.rv_Y = take(8 * nr * size_t(std::max(p->rv_nbmax, 1)) * DL_M);
+    w.rv_R = take(8 * nr * RV_P * DL_M);
+    w.rv_r = take(4 * nr * 2 * RV_HLEN);
+    w.rv_mm = take(8 * nr * RV_F * 2 * RV_BINS);
     w.partial = take(16 * size_t(std::max(p->n_partials, 1)));
     w.eq_partial = take(8 * size_t(std::max(p->n_eq_runs, 1)) * (p->eq_fft / 2 + 1));
     w.loss_part = take(32 * size_t(std::max(p->loss.n_groups_total, 1)));

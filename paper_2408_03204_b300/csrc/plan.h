@@ -49,6 +49,7 @@ struct WsLayout {
   size_t status, tickets, flags, flags_bytes;  // flags_bytes covers status+tickets+flags (cleared per call)
   size_t eq_spec, eq_aux, eq_bandpart, comp_carry, partial, eq_partial;
   size_t dl_aux, dl_spec, dl_R, dl_r;
+  size_t rv_band, rv_U, rv_fr, rv_h, rv_H, rv_Y, rv_R, rv_r, rv_mm;
   size_t loss_part, loss_stats, loss_rowloss, loss_frames;
   size_t U, A;
   size_t total;
@@ -83,7 +84,7 @@ struct Plan {
   int32_t n_type_rows[GRAFX_N_TYPES] = {0};
   int32_t n_eq = 0, n_comp_chunks = 0, n_partials = 0, n_eq_runs = 0;
   int32_t n_fitems = 0, in_bitem_begin = 0, in_bitem_count = 0;
-  int32_t n_delay = 0, n_dl_slots = 0;
+  int32_t n_delay = 0, n_dl_slots = 0, n_reverb = 0, rv_nbmax = 0;
   double dl_taylor[9] = {0};
   int32_t eq_taps = 1023, eq_H = 511, eq_fft = 4096, eq_step = 0;  // eq_step: outputs per block
   int32_t comp_chunk = 2048;
@@ -94,10 +95,11 @@ struct Plan {
   WsLayout ws;
   // host tables
   std::vector<float2_> twiddle, ptw;
-  std::vector<float> eq_cos, eq_hann, eq_band;
+  std::vector<float> eq_cos, eq_hann, eq_band, rv_band;
   // bindings
   char* dev_ws = nullptr;
   const float* params[GRAFX_N_TYPES] = {nullptr};
+  const float* rv_noise = nullptr;
   int64_t param_rows[GRAFX_N_TYPES] = {0};
   int32_t last_launches = 0;
 };

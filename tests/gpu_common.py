@@ -86,6 +86,10 @@ class GpuRun:
         self.P = {t: torch.tensor(v, dtype=torch.float32, device="cuda").contiguous() for t, v in P.items()}
         self.src = torch.tensor(src_flat, dtype=torch.float32, device="cuda")
         self.plan.bind_params(self.P)
+        if any(g.count(8) for g in graphs):
+            import synth
+            self.noise = torch.tensor(synth.reverb_noise(), device="cuda").contiguous()
+            self.plan.bind_reverb_noise(self.noise)
 
     def render(self):
         torch = self.torch
@@ -102,3 +106,8 @@ class GpuRun:
         self.plan.backprop_raw(self.src, d_out, dP, dS, self.gx._stream(torch, d_out.device))
         self.plan.sync_status()
         return {t: v.cpu().numpy() for t, v in dP.items()}, (dS.cpu().numpy() if want_sources else None)
+
+
+def reverb_noise_device(torch):
+    import synth
+    return torch.tensor(synth.reverb_noise(), device="cuda").contiguous()

@@ -14,6 +14,10 @@ pytestmark = pytest.mark.gpu
 I, O, M, G, S, E, C = 0, 1, 2, 3, 4, 5, 6
 
 
+def hparams(eq_taps=63):
+    return dict(eq_taps=eq_taps, reverb_noise=synth.reverb_noise().astype(np.float64))
+
+
 @pytest.fixture(scope="module", autouse=True)
 def _lib():
     torch = pytest.importorskip("torch")
@@ -39,7 +43,7 @@ def run_case(graphs, lengths, seed=11, eq_taps=63, linear_loss=True, **kw):
     P = union_params(graphs, seed)
     run = GpuRun(graphs, lengths, P, src_flat, eq_taps=eq_taps, **kw)
     out = run.render().cpu().numpy()
-    hp = dict(eq_taps=eq_taps)
+    hp = hparams(eq_taps)
     got_rows = split_rows(out, graphs, lengths)
     Pg = per_graph_params(graphs, P)
     for g, L, src, p, got in zip(graphs, lengths, src_per, Pg, got_rows):
@@ -270,3 +274,22 @@ def test_random_graphs_with_delay():
         for t in P:
             assert_grad_close(dP[t], wP[t], what=f"type {t}")
         assert_grad_close(dS.reshape(-1, 2, Pd)[:, :, :L], wS, what="sources")
+
+
+R = 8
+
+
+@pytest.mark.parametrize("L", [6001, 20000])
+def test_reverb_fwd_bwd(L):
+    """Filtered-noise reverb: 88200-tap masked-noise IR, partitioned FFT convolution,
+    and the adjoint through convolution, ISTFT, masks and bands."""
+    g = single_node_graph(R, fan_in=2)
+    run, P, src_per, out = run_case([g], [L], seed=51)
+    rng = np.random.Generator(np.random.PCG64(L + 1))
+    Pd = (L + 3) // 4 * 4
+    W = np.zeros((1, 2, Pd), np.float32)
+    W[:, :, :L] = rng.standard_normal((1, 2, L)).astype(np.float32)
+    dP, dS = run.backprop(W.reshape(-1))
+    wP, wS = orr.backward(g.types, g.edges, src_per[0][:, :, :L], P, W[:, :, :L], hparams())
+    assert_grad_close(dP[R], wP[R], what="reverb parameters")
+    assert_grad_close(dS.reshape(-1, 2, Pd)[:, :, :L], wS, what="sources")

@@ -127,13 +127,11 @@ def test_workspace_requires_binding(gx):
     assert e.value.name == "EINVAL"
 
 
-def test_delay_length_limit_and_reverb_rejected(gx):
+def test_delay_and_reverb_length_limit(gx):
     I, O, D, R = 0, 1, 7, 8
-    ok = gx.Graph.from_lists([I, D, O], [(0, 1), (1, 2)])
-    gx.Plan([ok], [1 << 19])
-    with pytest.raises(gx.GrafxError) as e:
-        gx.Plan([ok], [(1 << 19) + 1])
-    assert e.value.name == "ESHAPE"
-    with pytest.raises(gx.GrafxError) as e:
-        gx.Plan([gx.Graph.from_lists([I, R, O], [(0, 1), (1, 2)])], [4096])
-    assert e.value.name == "ETYPE"
+    for t in (D, R):
+        ok = gx.Graph.from_lists([I, t, O], [(0, 1), (1, 2)])
+        gx.Plan([ok], [1 << 19])
+        with pytest.raises(gx.GrafxError) as e:
+            gx.Plan([ok], [(1 << 19) + 1])
+        assert e.value.name == "ESHAPE"
