@@ -376,10 +376,11 @@ def delay_fwd_surrogate(u, p, nfft=DELAY_NFFT):
 # Readings (the paper gives the model, not these constants): two noise buffers (mid,
 # side) of 2 s = 88200 samples, U(-1, 1), are inputs shared by every reverb node (the
 # random numbers the method draws are passed in); STFT with FFT 1024, hop 256,
-# periodic Hann, frames m = 1..F starting at (m-1) hop, F = ceil(88200 / 256), signal
-# zero past its end; masks M_x[k, m] = exp(H0_x[k] + (m-1) Hd_x[k]) with H0, Hd
-# interpolated from 12 log-spaced bands like the EQ (natural-log magnitudes); ISTFT by
-# windowed overlap-add divided by sum w^2 (0 where that sum is < 1e-8); h_l =
+# periodic Hann, centred frames (frame m = 1..F covers [(m-1) hop - N/2, (m-1) hop + N/2),
+# the signal zero outside [0, 88200)), F = 1 + 88200 // 256; masks
+# M_x[k, m] = exp(H0_x[k] + (m-1) Hd_x[k]) with H0, Hd interpolated from 12
+# log-spaced bands like the EQ (natural-log magnitudes); ISTFT by windowed
+# overlap-add divided by the window envelope sum w^2 (bounded below by centring); h_l =
 # (h_m + h_s)/2, h_r = (h_m - h_s)/2 (the imager's convention); y = e^{q_dry} u +
 # e^{q_wet} (h * u), causal, truncated to L.
 # Parameter row (50): [mid, side] x [H0 (12), Hd (12)], then q_dry, q_wet.
@@ -419,38 +420,44 @@ def rv_window(n):
 
 
 def rv_frames(length, nfft, hop):
-    return -(-length // hop)
+    return 1 + length // hop
+
+
+def _rv_padded_len(length, nfft, hop):
+    return (rv_frames(length, nfft, hop) - 1) * hop + nfft
 
 
 def rv_stft(x, nfft, hop):
-    """[F, nfft/2+1] one-sided spectra of frames (m-1) hop, zero past the end."""
+    """[F, nfft/2+1] one-sided spectra of centred frames (frame m covers
+    [m hop - nfft/2, m hop + nfft/2)), zero outside the signal."""
     F = rv_frames(x.shape[0], nfft, hop)
-    pad = np.zeros((F - 1) * hop + nfft)
-    pad[:x.shape[0]] = x
+    pad = np.zeros(_rv_padded_len(x.shape[0], nfft, hop))
+    pad[nfft // 2:nfft // 2 + x.shape[0]] = x
     idx = np.arange(F)[:, None] * hop + np.arange(nfft)[None, :]
     return np.fft.rfft(pad[idx] * rv_window(nfft)[None, :], axis=-1)
 
 
 def rv_ola_norm(length, nfft, hop):
+    """Window envelope sum_m w^2 at every sample of [0, length)."""
     F = rv_frames(length, nfft, hop)
-    D = np.zeros((F - 1) * hop + nfft)
+    D = np.zeros(_rv_padded_len(length, nfft, hop))
     w2 = rv_window(nfft) ** 2
     for m in range(F):
         D[m * hop:m * hop + nfft] += w2
-    return D[:length]
+    return D[nfft // 2:nfft // 2 + length]
 
 
 def rv_istft(S, length, nfft, hop):
-    """Windowed overlap-add of irfft frames divided by sum w^2 (0 where < 1e-8)."""
+    """Windowed overlap-add of irfft frames divided by the window envelope."""
     F = S.shape[0]
     fr = np.fft.irfft(S, nfft, axis=-1) * rv_window(nfft)[None, :]
-    out = np.zeros((F - 1) * hop + nfft)
+    out = np.zeros(_rv_padded_len(length, nfft, hop))
     for m in range(F):
         out[m * hop:m * hop + nfft] += fr[m]
     D = rv_ola_norm(length, nfft, hop)
     h = np.zeros(length)
     ok = D > 1e-8
-    h[ok] = out[:length][ok] / D[ok]
+    h[ok] = out[nfft // 2:nfft // 2 + length][ok] / D[ok]
     return h
 
 
@@ -517,8 +524,8 @@ def reverb_bwd(u, p, ybar, noise, hp=None):
         g = np.zeros(length)
         ok = D > 1e-8
         g[ok] = hbar_ms[x][ok] / D[ok]
-        gp = np.zeros((F - 1) * hop + n)
-        gp[:length] = g
+        gp = np.zeros(_rv_padded_len(length, n, hop))
+        gp[n // 2:n // 2 + length] = g
         idx = np.arange(F)[:, None] * hop + np.arange(n)[None, :]
         xbar = gp[idx] * w[None, :]                          # dL/d(irfft frame)
         Gb = ck[None, :] / n * np.fft.rfft(xbar, axis=-1)    # dL/dRe H + j dL/dIm H

@@ -56,7 +56,7 @@ constexpr int DL_MAX_BLOCKS = 128; // signals with delay nodes: at most 2^19 sam
 constexpr int RV_LEN = 88200;      // impulse response: 2 s at 44.1 kHz
 constexpr int RV_N = 1024;         // STFT size
 constexpr int RV_HOP = 256;
-constexpr int RV_F = (RV_LEN + RV_HOP - 1) / RV_HOP;   // 345 frames
+constexpr int RV_F = 1 + RV_LEN / RV_HOP;              // 345 centred frames
 constexpr int RV_BINS = RV_N / 2 + 1;
 constexpr int RV_BANDS = 12;
 constexpr int RV_COLS = 50;        // [mid, side] x [H0, Hd] x 12 bands, q_dry, q_wet

@@ -1,7 +1,7 @@
 // Filtered-noise reverb (Sec. 3 "Reverb", Eq. 6-7).
 //
 // Impulse response per node (forward): the STFT of the two noise buffers (mid, side;
-// FFT 1024, hop 256, periodic Hann; computed once per render) is multiplied by the
+// FFT 1024, hop 256, periodic Hann, centred frames; computed once per render) is multiplied by the
 // masks M_x[k, m] = exp(H0_x[k] + m Hd_x[k]) (12-band log-frequency interpolation),
 // inverted frame by frame (mid + i side packed in one complex FFT), windowed and
 // overlap-added, divided by sum w^2, and turned into left/right as (mid +- side)/2.
@@ -49,9 +49,9 @@ __global__ void __launch_bounds__(RV_N / 16) k_rv_noise_stft(DevCtx c) {
   __shared__ float2 buf[fft::Padded<RV_N>::size];
   const int m = blockIdx.x;
   for (int j = threadIdx.x; j < RV_N; j += blockDim.x) {
-    const int t = m * RV_HOP + j;
+    const int t = m * RV_HOP + j - RV_N / 2;   // centred frame
     const float w = rv_hann(c.tw, j);
-    buf[fft::pad(j)] = t < RV_LEN ? make_float2(w * c.rv_noise[t], w * c.rv_noise[RV_LEN + t]) : make_float2(0.f, 0.f);
+    buf[fft::pad(j)] = t >= 0 && t < RV_LEN ? make_float2(w * c.rv_noise[t], w * c.rv_noise[RV_LEN + t]) : make_float2(0.f, 0.f);
   }
   __syncthreads();
   fft::forward<RV_N>(buf, c.ptw, threadIdx.x, true);
@@ -96,12 +96,15 @@ __global__ void __launch_bounds__(RV_N / 16) k_rv_ir_frames(DevCtx c, int node_b
   }
 }
 
+// Window envelope at sample n and the frames covering it (frame m starts at
+// m hop - N/2 in signal coordinates; np = n + N/2 in padded coordinates).
 __device__ __forceinline__ float rv_ola_norm(const float2_* tw, int n, int* m0, int* m1) {
-  const int hi = min(RV_F - 1, n / RV_HOP);
-  const int lo = n - RV_N + 1 <= 0 ? 0 : (n - RV_N + 1 + RV_HOP - 1) / RV_HOP;
+  const int np = n + RV_N / 2;
+  const int hi = min(RV_F - 1, np / RV_HOP);
+  const int lo = np - RV_N + 1 <= 0 ? 0 : (np - RV_N + 1 + RV_HOP - 1) / RV_HOP;
   float D = 0.f;
   for (int m = lo; m <= hi; ++m) {
-    const float w = rv_hann(tw, n - m * RV_HOP);
+    const float w = rv_hann(tw, np - m * RV_HOP);
     D += w * w;
   }
   *m0 = lo;
@@ -123,7 +126,7 @@ __global__ void k_rv_ir_ola(DevCtx c, int node_begin) {
       float sm = 0.f, ss = 0.f;
       const float2* fr = c.rv_fr + size_t(ri) * RV_F * RV_N;
       for (int m = lo; m <= hi; ++m) {
-        const float2 z = fr[size_t(m) * RV_N + n - m * RV_HOP];
+        const float2 z = fr[size_t(m) * RV_N + n + RV_N / 2 - m * RV_HOP];
         sm += z.x;
         ss += z.y;
       }
@@ -286,9 +289,9 @@ __global__ void __launch_bounds__(RV_N / 16) k_rv_gfr(DevCtx c, int node_begin) 
   const float* rl = c.rv_r + (size_t(ri) * 2) * RV_HLEN;
   const float* rr = rl + RV_HLEN;
   for (int j = threadIdx.x; j < RV_N; j += blockDim.x) {
-    const int n = m * RV_HOP + j;
+    const int n = m * RV_HOP + j - RV_N / 2;   // centred frame
     float gm = 0.f, gs = 0.f;
-    if (n < RV_LEN) {
+    if (n >= 0 && n < RV_LEN) {
       int lo, hi;
       const float D = rv_ola_norm(c.tw, n, &lo, &hi);
       if (D > 1e-8f) {

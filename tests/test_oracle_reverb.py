@@ -27,10 +27,9 @@ def test_unit_mask_reconstructs_the_noise(rng):
     h = op.rv_ir(np.zeros(50), nz, HP)
     hm, hs = h[0] + h[1], h[0] - h[1]
     D = op.rv_ola_norm(1500, 64, 16)
-    ok = D > 1e-8
-    np.testing.assert_allclose(hm[ok], nz[0][ok], atol=1e-12)
-    np.testing.assert_allclose(hs[ok], nz[1][ok], atol=1e-12)
-    assert not ok[0] and ok[1:].all()
+    assert D.min() > 0.5                      # centred frames: the envelope is bounded below
+    np.testing.assert_allclose(hm, nz[0], atol=1e-12)
+    np.testing.assert_allclose(hs, nz[1], atol=1e-12)
 
 
 def test_stft_matches_direct_dft(rng):
@@ -38,8 +37,9 @@ def test_stft_matches_direct_dft(rng):
     S = op.rv_stft(x, 32, 8)
     w = op.rv_window(32)
     n = np.arange(32)
-    xp = np.zeros(40 * 8 + 32)
-    xp[:200] = x
+    xp = np.zeros((S.shape[0] - 1) * 8 + 32)
+    xp[16:216] = x                            # centred frames: N/2 zeros before the signal
+    assert S.shape[0] == 1 + 200 // 8
     for m in (0, 5, S.shape[0] - 1):
         fr = xp[m * 8:m * 8 + 32] * w
         for k in (0, 3, 16):
