@@ -261,6 +261,77 @@ int grafx_adam_step(float* theta, float* m, float* v, const float* grad_param, f
 int grafx_params_to_theta(const float* param, const int8_t* codes, int32_t cols, int64_t n, float* theta,
                           void* stream);
 
+/* ---------------------------------------------------------------- learned warm-start
+ * The paper motivates estimating processor parameters with a trained network
+ * (Sec. 1) and leaves the estimator open; this is the library's own: it predicts the
+ * unconstrained parameters theta of every processor node (the variables of
+ * grafx_adam_step) from audio, as a starting point for the gradient fit.
+ *
+ * Node inputs: after grafx_render(p, sources, out) (typically with neutral
+ * parameters), writes u_v (Eq. 1b: the sum of the node's in-edge sources) of the n
+ * nodes `ids` (host int32, ids in the plan's union numbering: graph g's node j is
+ * j + the node counts of graphs 0..g-1) into device rows dst[i][2][dst_pitch]
+ * (dst_pitch a multiple of 4 and >= the node's length; samples past the length are
+ * 0).  Input nodes are rejected (GRAFX_EINVAL).  Asynchronous on `stream`. */
+int grafx_node_inputs(grafx_plan* p, const float* sources, const float* out, const int32_t* ids, int32_t n,
+                      float* dst, int64_t dst_pitch, void* stream);
+
+/* Network (weights: one flat device float32 buffer, layout below, owned by the caller):
+ *   features  [B][256][32]: log-mel (frames 2048, hop 512, no padding, periodic Hann,
+ *             power, 128 HTK-mel triangles over 0..fs/2, ln(mel + 1e-5), frames
+ *             average-pooled to 32) of the node input (channels 0..127) and of the
+ *             target mix (128..255);
+ *   encoder   4 x conv1d (kernel 5, zero padding 2) 256->128->128->128->128, bias,
+ *             exact GELU; mean over the 32 frames;
+ *   heads     per type (gain, imager, EQ, compressor, delay, reverb) an MLP
+ *             128->288->288->N_t (N_t = 2, 1, 8, 4, 176, 50), GELU, GELU, linear.
+ *   weights   conv{l}.w [Cout][Cin][5], conv{l}.b for l = 0..3, then per head in that
+ *             type order w1 [288][128], b1, w2 [288][288], b2, w3 [N_t][288], b3.
+ * Every matrix product runs on the tensor cores with BF16 operands (rounded to
+ * nearest even from float32) and float32 accumulation.
+ *
+ * A net handle holds host tables only; its device workspace (caller-owned, 256-byte
+ * aligned, grafx_ws_workspace_bytes for up to max_rows log-mel rows of up to
+ * max_len samples) is attached by grafx_ws_bind, which uploads the constant tables
+ * (synchronous on `stream`).  Calls on one net are stream-ordered and share the
+ * workspace: grafx_ws_backward must follow the grafx_ws_forward of the same batch with
+ * no other forward in between. */
+typedef struct grafx_wsnet grafx_wsnet;
+int grafx_ws_create(int32_t max_batch, int32_t sample_rate, grafx_wsnet** out);
+int grafx_ws_destroy(grafx_wsnet* n);
+int grafx_ws_param_count(const grafx_wsnet* n, int64_t* count);
+int grafx_ws_workspace_bytes(const grafx_wsnet* n, int32_t max_rows, int64_t max_len, size_t* bytes);
+int grafx_ws_bind(grafx_wsnet* n, void* ws, size_t bytes, void* stream);
+/* Log-mel features of n_rows stereo rows (device, row r at rows + r*row_stride,
+ * channel stride pitch, len >= 2048 samples each) into feats[i][coff..coff+127][32]
+ * for the n_samples samples (sample i takes row row_of_sample[i], a device int32 array;
+ * NULL means sample i = row i; an index outside [0, n_rows) gives zero features).
+ * coff is 0 (node input) or 128 (target mix).  Asynchronous on `stream`. */
+int grafx_ws_logmel(grafx_wsnet* n, const float* rows, int32_t n_rows, int64_t row_stride, int64_t pitch, int64_t len,
+                    const int32_t* row_of_sample, int32_t n_samples, int32_t coff, float* feats, void* stream);
+/* Forward of a batch of B <= max_batch samples sorted by head: head_count (host
+ * int32[6]) gives how many consecutive samples use each head, in the type order above
+ * (their sum must be B: GRAFX_ESHAPE otherwise).  out: device [B][176]; row i holds the
+ * N_t outputs of its head and zeros after them.  Asynchronous on `stream`. */
+int grafx_ws_forward(grafx_wsnet* n, const float* weights, const float* feats, const int32_t* head_count, int32_t B,
+                     float* out, void* stream);
+/* Gradient of <d_out, out> with respect to the weights after grafx_ws_forward on the
+ * same inputs; d_weights (device, param_count floats) is overwritten.  Column sums are
+ * taken in a fixed order (deterministic).  Asynchronous on `stream`. */
+int grafx_ws_backward(grafx_wsnet* n, const float* weights, const float* feats, const int32_t* head_count, int32_t B,
+                      const float* d_out, float* d_weights, void* stream);
+/* Masked mean-squared error over the first n_out[i] (device int32) columns of each row
+ * of out and target (device [B][176]): *loss (device float) and d_out = dloss/dout (0 in
+ * unused columns).  Asynchronous on `stream`. */
+int grafx_ws_mse(const float* out, const float* target, const int32_t* n_out, int32_t B, float* loss, float* d_out,
+                 void* stream);
+/* The network's matrix product on its own: C = alpha A B + beta C over device float32
+ * buffers with A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn], C row-major with
+ * leading dimension ldc >= N; A and B are rounded to BF16 (nearest even) and the sums
+ * accumulate in float32.  M <= 4194240.  Asynchronous on `stream`. */
+int grafx_gemm_bf16(int32_t M, int32_t N, int32_t K, const float* A, int64_t sam, int64_t sak, const float* B,
+                    int64_t sbk, int64_t sbn, float* C, int64_t ldc, float alpha, float beta, void* stream);
+
 /* ---------------------------------------------------------------- allocation-free compressor
  * The paper has no counterpart to this call; it exists for callers that must not
  * allocate device memory at all, such as real-time audio callbacks and plugin hosts

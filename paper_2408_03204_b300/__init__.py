@@ -85,6 +85,18 @@ SIGNATURES = {
     "grafx_step_graph_launch": (ctypes.c_int, [_P, _P]),
     "grafx_step_graph_launches": (ctypes.c_int, [_P, _I32P]),
     "grafx_step_graph_destroy": (ctypes.c_int, [_P]),
+    "grafx_node_inputs": (ctypes.c_int, [_P, _F, _F, _I32P, _I32, _F, _I64, _P]),
+    "grafx_ws_create": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_P)]),
+    "grafx_ws_destroy": (ctypes.c_int, [_P]),
+    "grafx_ws_param_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "grafx_ws_workspace_bytes": (ctypes.c_int, [_P, _I32, _I64, ctypes.POINTER(_SZ)]),
+    "grafx_ws_bind": (ctypes.c_int, [_P, _P, _SZ, _P]),
+    "grafx_ws_logmel": (ctypes.c_int, [_P, _F, _I32, _I64, _I64, _I64, _P, _I32, _I32, _F, _P]),
+    "grafx_ws_forward": (ctypes.c_int, [_P, _F, _F, _I32P, _I32, _F, _P]),
+    "grafx_ws_backward": (ctypes.c_int, [_P, _F, _F, _I32P, _I32, _F, _F, _P]),
+    "grafx_ws_mse": (ctypes.c_int, [_F, _F, _P, _I32, _F, _F, _P]),
+    "grafx_gemm_bf16": (ctypes.c_int, [_I32, _I32, _I32, _F, _I64, _I64, _F, _I64, _I64, _F, _I64, ctypes.c_float,
+                                       ctypes.c_float, _P]),
 }
 
 
@@ -247,6 +259,12 @@ class Plan:
     def loss_backward_raw(self, out, target, d_out, stream):
         _check(lib().grafx_mrstft_backward(self._h, _ptr(out), _ptr(target), _ptr(d_out), stream))
 
+    def node_inputs_raw(self, sources, out, ids, dst, dst_pitch, stream):
+        """u_v of the nodes ``ids`` (union numbering) into dst [n][2][dst_pitch] after a render."""
+        arr = (ctypes.c_int32 * max(len(ids), 1))(*[int(i) for i in ids])
+        _check(lib().grafx_node_inputs(self._h, _ptr(sources), _ptr(out), arr, len(ids), _ptr(dst),
+                                       int(dst_pitch), stream))
+
     def capture_step(self, sources, out, target, loss, d_out, d_params, d_sources, stream):
         """Record render + loss + loss gradient + backprop with these buffers as one CUDA
         graph; returns a StepGraph whose launch() replays it."""
@@ -265,6 +283,68 @@ class Plan:
         n = ctypes.c_int32()
         _check(lib().grafx_last_launch_count(self._h, ctypes.byref(n)))
         return n.value
+
+
+WS_HEAD_TYPES = (T_GAIN, T_IMAGER, T_EQ, T_COMP, T_DELAY, T_REVERB)
+WS_HEAD_OUT = (2, 1, 8, 4, 176, 50)
+WS_OUTMAX = 176
+WS_T = 32
+
+
+class WarmStartNet:
+    """Handle of the warm-start network (grafx_ws_*): host tables plus a device workspace
+    sized for ``max_batch`` samples and ``max_rows`` log-mel rows of ``max_len`` samples.
+    Weights and gradients are caller tensors (flat float32, ``n_params``)."""
+
+    def __init__(self, max_batch, max_rows, max_len, sample_rate=44100, device="cuda"):
+        import torch
+        h = _P()
+        _check(lib().grafx_ws_create(int(max_batch), int(sample_rate), ctypes.byref(h)))
+        self._h = h
+        c = ctypes.c_int64()
+        _check(lib().grafx_ws_param_count(self._h, ctypes.byref(c)))
+        self.n_params = c.value
+        self.max_batch = int(max_batch)
+        nb = ctypes.c_size_t()
+        _check(lib().grafx_ws_workspace_bytes(self._h, int(max_rows), int(max_len), ctypes.byref(nb)))
+        ws = torch.empty(nb.value + 256, dtype=torch.uint8, device=device)
+        off = (-ws.data_ptr()) % 256
+        self.ws = ws
+        _check(lib().grafx_ws_bind(self._h, ctypes.c_void_p(ws.data_ptr() + off), nb.value,
+                                   _stream(torch, ws.device)))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.grafx_ws_destroy(self._h)
+            self._h = None
+
+    def logmel_raw(self, rows, n_rows, row_stride, pitch, length, row_of_sample, n_samples, coff, feats, stream):
+        _check(lib().grafx_ws_logmel(self._h, _ptr(rows), int(n_rows), int(row_stride), int(pitch), int(length),
+                                     _ptr(row_of_sample), int(n_samples), int(coff), _ptr(feats), stream))
+
+    @staticmethod
+    def _heads(head_count):
+        return (ctypes.c_int32 * 6)(*[int(x) for x in head_count])
+
+    def forward_raw(self, weights, feats, head_count, out, stream):
+        B = int(sum(head_count))
+        _check(lib().grafx_ws_forward(self._h, _ptr(weights), _ptr(feats), self._heads(head_count), B, _ptr(out),
+                                      stream))
+
+    def backward_raw(self, weights, feats, head_count, d_out, d_weights, stream):
+        B = int(sum(head_count))
+        _check(lib().grafx_ws_backward(self._h, _ptr(weights), _ptr(feats), self._heads(head_count), B,
+                                       _ptr(d_out), _ptr(d_weights), stream))
+
+    @staticmethod
+    def mse_raw(out, target, n_out, loss, d_out, stream):
+        _check(lib().grafx_ws_mse(_ptr(out), _ptr(target), _ptr(n_out), out.shape[0], _ptr(loss), _ptr(d_out),
+                                  stream))
+
+
+def gemm_bf16_raw(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta, stream):
+    _check(lib().grafx_gemm_bf16(int(M), int(N), int(K), _ptr(A), int(sam), int(sak), _ptr(B), int(sbk), int(sbn),
+                                 _ptr(C), int(ldc), float(alpha), float(beta), stream))
 
 
 class StepGraph:

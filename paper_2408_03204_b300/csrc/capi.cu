@@ -1,5 +1,6 @@
 // C ABI (include/grafx.h): graph building, planning, device binding, and the step
 // loops of Algorithm 1 (render) and its reverse (backprop), plus the loss.
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -361,6 +362,33 @@ int grafx_render_steps(grafx_plan* p, const float* sources, float* out, int32_t 
 int grafx_render(grafx_plan* p, const float* sources, float* out, void* stream) {
   if (!p) return fail(GRAFX_EINVAL, "null argument");
   return grafx_render_steps(p, sources, out, 1, int32_t(p->sched.string.size()), stream);
+}
+
+int grafx_node_inputs(grafx_plan* p, const float* sources, const float* out, const int32_t* ids, int32_t n,
+                      float* dst, int64_t dst_pitch, void* stream) {
+  if (!p || !sources || !out || (!ids && n > 0) || (!dst && n > 0)) return fail(GRAFX_EINVAL, "null argument");
+  int rc = check_ready(p);
+  if (rc) return rc;
+  const int32_t nv = int32_t(p->types.size());
+  if (n < 0 || dst_pitch < 4 || (dst_pitch & 3)) return fail(GRAFX_ESHAPE, "bad node-input shape");
+  for (int32_t i = 0; i < n; ++i) {
+    if (ids[i] < 0 || ids[i] >= nv) return fail(GRAFX_EINVAL, "node id out of range");
+    if (p->types[ids[i]] == GRAFX_T_IN) return fail(GRAFX_EINVAL, "input nodes have no node input");
+    if (p->L[p->node_graph[ids[i]]] > dst_pitch) return fail(GRAFX_ESHAPE, "dst_pitch below the node's length");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevCtx c = make_ctx(p, sources, const_cast<float*>(out), nullptr, nullptr);
+  int launches = 0;
+  for (int32_t i0 = 0; i0 < n; i0 += NI_MAX) {
+    NodeIds b;
+    std::memset(&b, 0, sizeof(b));
+    b.first = i0;
+    const int m = std::min<int32_t>(NI_MAX, n - i0);
+    for (int j = 0; j < m; ++j) b.v[j] = p->sigma[ids[i0 + j]];
+    launches += launch_node_inputs(c, b, m, dst, dst_pitch, s);
+  }
+  p->last_launches = launches;
+  return cuda_check(cudaGetLastError(), "node-input launch");
 }
 
 int grafx_backprop_steps(grafx_plan* p, const float* sources, const float* d_out, float* const* d_params,

@@ -1,0 +1,646 @@
+// Learned warm-start network: predicts every node's unconstrained processor parameters
+// theta from audio.  The paper motivates a trained parameter estimator (Sec. 1) without
+// fixing one; this network is the library's own.
+//
+// Features: log-mel of the mono mix of a stereo row (frames 2048, hop 512, no padding,
+// periodic Hann, power spectrum, 128 HTK-mel triangles over 0..fs/2, ln(mel + 1e-5)),
+// frames average-pooled to WS_T = 32.  A sample is [256][32]: the log-mel of a node's
+// input (rendered with neutral parameters) in channels 0..127 and of the target mix in
+// 128..255.
+// Network: 4 conv1d layers (kernel 5, 'same' zero padding) 256->128->128->128->128 with
+// bias and exact GELU, mean over time, then one MLP head per parameterised type
+// 128->288->288->N_t.  Weights: one flat FP32 buffer in the order conv0.w [128][256][5],
+// conv0.b, conv1.w ... conv3.b, then per head (g, s, e, c, d, r) w1 [288][128], b1,
+// w2 [288][288], b2, w3 [N_t][288], b3.
+// Every product runs on the tensor cores in BF16 with FP32 accumulation (mma.sync
+// m16n8k16): operands are rounded to BF16 (nearest even) as they are staged into shared
+// memory; activations, gradients and weights stay FP32 in HBM.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "kernels.h"
+#include "plan.h"
+
+namespace grafx {
+
+constexpr int WS_T = 32, WS_IN = 256, WS_CH = 128, WS_KW = 5, WS_HID = 288, WS_NHEAD = 6;
+constexpr int WS_MEL = 128, WS_NFFT = 2048, WS_HOP = 512, WS_BINS = WS_NFFT / 2 + 1;
+constexpr int WS_OUTMAX = 176;
+static const int kHeadOut[WS_NHEAD] = {2, 1, 8, 4, 176, 50};
+
+// ------------------------------------------------------------------ BF16 GEMM
+// C[M,N] = alpha * A B + beta * C with A(m, k) = A[m sam + k sak] and
+// B(k, n) = B[k sbk + n sbn] (FP32 in memory, BF16 in shared memory), C row-major (ldc).
+// 64x64 tile per CTA of 4 warps, each warp 32x32 = 2x4 m16n8k16 fragments.
+constexpr int GB_M = 64, GB_N = 64, GB_K = 32, GB_P = GB_K + 8;
+
+__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// stage a GB_R x GB_K tile of op(X) (row r, column kk) into S[r][kk]; the loop order
+// follows the unit-stride dimension so that global reads coalesce
+template <int GB_R>
+__device__ __forceinline__ void stage(__nv_bfloat16 (*S)[GB_P], const float* __restrict__ X, int64_t sr, int64_t sk,
+                                      int r0, int R, int k0, int K) {
+  if (sk == 1) {
+    for (int idx = threadIdx.x; idx < GB_R * GB_K; idx += blockDim.x) {
+      const int r = idx / GB_K, kk = idx % GB_K, m = r0 + r, k = k0 + kk;
+      S[r][kk] = __float2bfloat16_rn(m < R && k < K ? X[m * sr + k] : 0.f);
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < GB_R * GB_K; idx += blockDim.x) {
+      const int kk = idx / GB_R, r = idx % GB_R, m = r0 + r, k = k0 + kk;
+      S[r][kk] = __float2bfloat16_rn(m < R && k < K ? X[m * sr + k * sk] : 0.f);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const float* __restrict__ A, int64_t sam,
+                                                   int64_t sak, const float* __restrict__ B, int64_t sbk,
+                                                   int64_t sbn, float* __restrict__ C, int64_t ldc, float alpha,
+                                                   float beta) {
+  __shared__ __align__(16) __nv_bfloat16 As[GB_M][GB_P];
+  __shared__ __align__(16) __nv_bfloat16 Bs[GB_N][GB_P];
+  const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int g = lane >> 2, t = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += GB_K) {
+    stage<GB_M>(As, A, sam, sak, m0, M, k0, K);
+    stage<GB_N>(Bs, B, sbn, sbk, n0, N, k0, K);
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GB_K; kk += 16) {
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + i * 16 + g;
+        a[i][0] = ld_pair(&As[r][kk + 2 * t]);
+        a[i][1] = ld_pair(&As[r + 8][kk + 2 * t]);
+        a[i][2] = ld_pair(&As[r][kk + 2 * t + 8]);
+        a[i][3] = ld_pair(&As[r + 8][kk + 2 * t + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = wn + j * 8 + g;
+        b[j][0] = ld_pair(&Bs[c][kk + 2 * t]);
+        b[j][1] = ld_pair(&Bs[c][kk + 2 * t + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};\n"
+              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+              : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int m = m0 + wm + i * 16 + g + (r >= 2 ? 8 : 0);
+        const int n = n0 + wn + j * 8 + 2 * t + (r & 1);
+        if (m < M && n < N) {
+          float* cp = C + m * ldc + n;
+          *cp = alpha * acc[i][j][r] + (beta != 0.f ? beta * *cp : 0.f);
+        }
+      }
+}
+
+static void gemm(int M, int N, int K, const float* A, int64_t sam, int64_t sak, const float* B, int64_t sbk,
+                 int64_t sbn, float* C, int64_t ldc, float alpha, float beta, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid((N + GB_N - 1) / GB_N, (M + GB_M - 1) / GB_M);
+  k_gemm_bf16<<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta);
+}
+
+// ------------------------------------------------------------------ elementwise pieces
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
+// im2col: A[(b,t)][(c,k)] = H(b, c, t+k-2), zero outside [0, T).  H is [B][T][C]
+// (time-major activations) or, for the features, [B][C][T] (feat_layout = 1).
+__global__ void k_im2col(const float* __restrict__ H, int B, int C, int feat_layout, float* __restrict__ A) {
+  const int64_t n = int64_t(B) * WS_T * C * WS_KW;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int k = int(i % WS_KW), c = int((i / WS_KW) % C);
+    const int64_t bt = i / (int64_t(WS_KW) * C);
+    const int t = int(bt % WS_T), b = int(bt / WS_T);
+    const int ts = t + k - 2;
+    float v = 0.f;
+    if (ts >= 0 && ts < WS_T)
+      v = feat_layout ? H[(int64_t(b) * C + c) * WS_T + ts] : H[(int64_t(b) * WS_T + ts) * C + c];
+    A[i] = v;
+  }
+}
+
+// dH[(b,t)][c] = sum_k dA[(b, t-k+2)][(c,k)]  (adjoint of k_im2col, time-major)
+__global__ void k_col2im(const float* __restrict__ dA, int B, int C, float* __restrict__ dH) {
+  const int64_t n = int64_t(B) * WS_T * C;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int c = int(i % C);
+    const int64_t bt = i / C;
+    const int t = int(bt % WS_T), b = int(bt / WS_T);
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < WS_KW; ++k) {
+      const int tt = t - k + 2;
+      if (tt >= 0 && tt < WS_T) s += dA[((int64_t(b) * WS_T + tt) * C + c) * WS_KW + k];
+    }
+    dH[i] = s;
+  }
+}
+
+// z[r][c] += bias[c]; h = gelu(z) (or a copy without GELU); rows x cols with row stride ld
+__global__ void k_bias_act(float* __restrict__ z, const float* __restrict__ bias, float* __restrict__ h, int64_t rows,
+                           int cols, int64_t ld, int apply_gelu) {
+  const int64_t n = rows * cols;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / cols;
+    const int c = int(i % cols);
+    const float v = z[r * ld + c] + bias[c];
+    z[r * ld + c] = v;
+    if (h) h[r * ld + c] = apply_gelu ? gelu(v) : v;
+  }
+}
+
+__global__ void k_gelu_bwd(float* __restrict__ d, const float* __restrict__ z, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    d[i] *= gelu_d(z[i]);
+}
+
+// out[c] = sum_r x[r ld + c] for c < cols (bias gradients).  Block: 32 columns x 32 row
+// slices; each slice sums rows slice, slice+32, ..., then a fixed-order tree (deterministic).
+__global__ void __launch_bounds__(1024) k_colsum(const float* __restrict__ x, int64_t rows, int cols, int64_t ld,
+                                                 float* __restrict__ out) {
+  __shared__ float red[32][33];
+  const int cx = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + cx;
+  float s = 0.f;
+  if (c < cols)
+    for (int64_t r = sl; r < rows; r += 32) s += x[r * ld + c];
+  red[sl][cx] = s;
+  __syncthreads();
+  for (int w = 16; w > 0; w >>= 1) {
+    if (sl < w) red[sl][cx] += red[sl + w][cx];
+    __syncthreads();
+  }
+  if (sl == 0 && c < cols) out[c] = red[0][cx];
+}
+
+__global__ void k_time_mean(const float* __restrict__ h, int B, float* __restrict__ e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * WS_CH) return;
+  const int b = i / WS_CH, c = i % WS_CH;
+  float s = 0.f;
+  for (int t = 0; t < WS_T; ++t) s += h[(int64_t(b) * WS_T + t) * WS_CH + c];
+  e[i] = s / float(WS_T);
+}
+
+__global__ void k_time_mean_bwd(const float* __restrict__ de, int B, float* __restrict__ dh) {
+  const int64_t n = int64_t(B) * WS_T * WS_CH;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int c = int(i % WS_CH);
+    const int b = int(i / (int64_t(WS_T) * WS_CH));
+    dh[i] = de[b * WS_CH + c] / float(WS_T);
+  }
+}
+
+// Masked mean-squared error: loss = sum over rows b and columns j < n_out[b] of
+// (out - tgt)^2 / count, d = 2 (out - tgt) / count (0 in unused columns).
+__global__ void __launch_bounds__(1024) k_ws_mse(const float* __restrict__ out, const float* __restrict__ tgt,
+                                                 const int32_t* __restrict__ nout, int B,
+                                                 float* __restrict__ loss, float* __restrict__ d) {
+  __shared__ float red[4 * 32];
+  float cnt = 0.f;
+  for (int b = 0; b < B; ++b) cnt += float(nout[b]);
+  float s = 0.f;
+  for (int i = threadIdx.x; i < B * WS_OUTMAX; i += blockDim.x) {
+    const int b = i / WS_OUTMAX, j = i % WS_OUTMAX;
+    float g = 0.f;
+    if (j < nout[b]) {
+      const float r = out[i] - tgt[i];
+      s += r * r;
+      g = 2.f * r / cnt;
+    }
+    d[i] = g;
+  }
+  float v[1] = {s};
+  block_sum<1>(v, red);
+  if (threadIdx.x == 0) *loss = cnt > 0.f ? v[0] / cnt : 0.f;
+}
+
+// ------------------------------------------------------------------ log-mel features
+// Frames 2q and 2q+1 of a row packed as the real and imaginary parts of one complex
+// 2048-point FFT; writes ln(mel + 1e-5) of both into fr[row][frame][128].
+__global__ void __launch_bounds__(WS_NFFT / 16) k_logmel_frames(const float* __restrict__ rows, int64_t rstride,
+                                                                int64_t pitch, int nframes,
+                                                                const float* __restrict__ melw,
+                                                                const int2_* __restrict__ mel_rng,
+                                                                const float2_* __restrict__ tw,
+                                                                const float2_* __restrict__ ptw,
+                                                                float* __restrict__ fr) {
+  __shared__ float2 buf[fft::Padded<WS_NFFT>::size];
+  __shared__ float pw[2][WS_BINS];
+  const int r = blockIdx.y, f = 2 * blockIdx.x;
+  const float* x = rows + int64_t(r) * rstride;
+  for (int j = threadIdx.x; j < WS_NFFT; j += blockDim.x) {
+    const float w = 0.5f - 0.5f * tw[j * (TWIDDLE_N / WS_NFFT)].x;
+    const int64_t t0 = int64_t(f) * WS_HOP + j, t1 = t0 + WS_HOP;
+    const float a = (f < nframes) ? 0.5f * (x[t0] + x[pitch + t0]) : 0.f;
+    const float b = (f + 1 < nframes) ? 0.5f * (x[t1] + x[pitch + t1]) : 0.f;
+    buf[fft::pad(j)] = make_float2(w * a, w * b);
+  }
+  __syncthreads();
+  fft::forward<WS_NFFT>(buf, ptw, threadIdx.x, true);
+  for (int k = threadIdx.x; k < WS_BINS; k += blockDim.x) {
+    const float2 z = buf[fft::pad(k)], zm = buf[fft::pad((WS_NFFT - k) & (WS_NFFT - 1))];
+    const float ax = 0.5f * (z.x + zm.x), ay = 0.5f * (z.y - zm.y);
+    const float bx = 0.5f * (z.y + zm.y), by = 0.5f * (zm.x - z.x);
+    pw[0][k] = ax * ax + ay * ay;
+    pw[1][k] = bx * bx + by * by;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * WS_MEL; i += blockDim.x) {
+    const int q = i / WS_MEL, m = i % WS_MEL;
+    if (f + q >= nframes) continue;
+    const int2_ rg = mel_rng[m];
+    float s = 0.f;
+    for (int k = rg.x; k < rg.y; ++k) s += melw[m * WS_BINS + k] * pw[q][k];
+    fr[(int64_t(r) * nframes + f + q) * WS_MEL + m] = logf(s + 1e-5f);
+  }
+}
+
+// Average-pool the frames to WS_T: feats[i][coff + m][t] for sample i, which takes
+// row row_of[i] (or row i when row_of is null).
+__global__ void k_logmel_pool(const float* __restrict__ fr, int nframes, int n_rows, int n_samples,
+                              const int32_t* __restrict__ row_of, int coff, float* __restrict__ feats) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_samples * WS_MEL * WS_T) return;
+  const int t = i % WS_T, m = (i / WS_T) % WS_MEL, smp = i / (WS_T * WS_MEL);
+  const int r = row_of ? row_of[smp] : smp;
+  float* o = feats + (int64_t(smp) * WS_IN + coff + m) * WS_T + t;
+  if (r < 0 || r >= n_rows) {  // invalid row index: zero features
+    *o = 0.f;
+    return;
+  }
+  const int a = (t * nframes) / WS_T, b = max(((t + 1) * nframes) / WS_T, a + 1);
+  float s = 0.f;
+  for (int f = a; f < b; ++f) s += fr[(int64_t(r) * nframes + f) * WS_MEL + m];
+  *o = s / float(b - a);
+}
+
+// ------------------------------------------------------------------ node inputs
+// u_v (Eq. 1b, gathered exactly like the step kernels) of the nodes ids.v[0..n) into
+// rows dst[ids.first + i][2][dst_pitch]; samples in [len, dst_pitch) are zero.
+__global__ void k_node_inputs(DevCtx c, NodeIds ids, float* __restrict__ dst, int64_t dst_pitch) {
+  const int i = blockIdx.y;
+  const int v = ids.v[i];
+  const NodeDev& n = c.nodes[v];
+  float* o = dst + int64_t(ids.first + i) * 2 * dst_pitch;
+  const int64_t quads = dst_pitch / 4;
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < 2 * quads;
+       q += int64_t(gridDim.x) * blockDim.x) {
+    const int ch = int(q / quads);
+    const int t = int(q % quads) * 4;
+    float4 val = f4zero();
+    if (t < n.len) val = gather_in(c, v, ch, t, n.len, n.pitch);
+    st4(o + ch * dst_pitch + t, val);
+  }
+}
+
+int launch_node_inputs(const DevCtx& c, const NodeIds& ids, int n, float* dst, int64_t dst_pitch, cudaStream_t s) {
+  if (n <= 0) return 0;
+  const int gx = int(std::min<int64_t>((2 * (dst_pitch / 4) + 255) / 256, 64));
+  k_node_inputs<<<dim3(gx, n), 256, 0, s>>>(c, ids, dst, dst_pitch);
+  return 1;
+}
+
+}  // namespace grafx
+
+// ====================================================================== host side
+using namespace grafx;
+
+struct grafx_wsnet {
+  int64_t off[4][2];          // conv weight / bias offsets in the flat buffer
+  int64_t hoff[WS_NHEAD][6];  // per head: w1 b1 w2 b2 w3 b3
+  int64_t n_params = 0;
+  int32_t max_batch = 0;
+  char* ws = nullptr;         // bound workspace
+  size_t ws_bytes = 0;
+  std::vector<float> melw;    // [128][1025] mel triangles
+  std::vector<int2_> mel_rng; // nonzero bin range of each triangle
+  std::vector<float2_> tw, ptw;
+};
+
+namespace {
+
+struct WsNetLayout {
+  size_t melw, melrng, tw, ptw;
+  size_t im2col, z[4], h[4], e, a1, g1, a2, g2, dbig, dsmall, dh, frames, total;
+};
+
+// frame_floats: log-mel frame scratch (rows x frames x 128) in floats
+WsNetLayout ws_layout(const grafx_wsnet* n, int64_t frame_floats) {
+  WsNetLayout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t r = o;
+    o = (o + bytes + 255) / 256 * 256;
+    return r;
+  };
+  const size_t B = size_t(n->max_batch), rows = B * WS_T;
+  L.melw = take(4 * n->melw.size());
+  L.melrng = take(sizeof(int2_) * n->mel_rng.size());
+  L.tw = take(sizeof(float2_) * n->tw.size());
+  L.ptw = take(sizeof(float2_) * n->ptw.size());
+  L.im2col = take(4 * rows * WS_IN * WS_KW);
+  for (int l = 0; l < 4; ++l) {
+    L.z[l] = take(4 * rows * WS_CH);
+    L.h[l] = take(4 * rows * WS_CH);
+  }
+  L.e = take(4 * B * WS_CH);
+  L.a1 = take(4 * B * WS_HID);
+  L.g1 = take(4 * B * WS_HID);
+  L.a2 = take(4 * B * WS_HID);
+  L.g2 = take(4 * B * WS_HID);
+  L.dbig = take(4 * rows * WS_CH * WS_KW);
+  L.dsmall = take(4 * B * WS_HID * 2);
+  L.dh = take(4 * (B * WS_CH + rows * WS_CH));
+  L.frames = take(4 * size_t(std::max<int64_t>(frame_floats, 1)));
+  L.total = o;
+  return L;
+}
+
+int grid1(int64_t n) { return int(std::min<int64_t>((n + 255) / 256, 148 * 16)); }
+
+int cuda_status() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GRAFX_OK : fail(GRAFX_ECUDA, cudaGetErrorString(e));
+}
+
+int n_frames_of(int64_t len) { return int(1 + (len - WS_NFFT) / WS_HOP); }
+
+int check_heads(const int32_t* head_count, int32_t B) {
+  int64_t sum = 0;
+  for (int h = 0; h < WS_NHEAD; ++h) {
+    if (head_count[h] < 0) return fail(GRAFX_ESHAPE, "negative head count");
+    sum += head_count[h];
+  }
+  if (sum != B) return fail(GRAFX_ESHAPE, "head counts must sum to the batch");
+  return GRAFX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int grafx_ws_create(int32_t max_batch, int32_t sample_rate, grafx_wsnet** out) {
+  if (!out) return fail(GRAFX_EINVAL, "null argument");
+  *out = nullptr;
+  if (max_batch < 1 || max_batch > 65536 || sample_rate < 8000) return fail(GRAFX_EINVAL, "bad batch or rate");
+  grafx_wsnet* n = new (std::nothrow) grafx_wsnet();
+  if (!n) return fail(GRAFX_ENOMEM, "host allocation failed");
+  n->max_batch = max_batch;
+  int64_t o = 0;
+  const int cin[4] = {WS_IN, WS_CH, WS_CH, WS_CH};
+  for (int l = 0; l < 4; ++l) {
+    n->off[l][0] = o;
+    o += int64_t(WS_CH) * cin[l] * WS_KW;
+    n->off[l][1] = o;
+    o += WS_CH;
+  }
+  for (int h = 0; h < WS_NHEAD; ++h) {
+    const int64_t sz[6] = {int64_t(WS_HID) * WS_CH, WS_HID, int64_t(WS_HID) * WS_HID, WS_HID,
+                           int64_t(kHeadOut[h]) * WS_HID, kHeadOut[h]};
+    for (int i = 0; i < 6; ++i) {
+      n->hoff[h][i] = o;
+      o += sz[i];
+    }
+  }
+  n->n_params = o;
+  // HTK-mel triangles over the one-sided bins of a 2048-point frame, edges equally
+  // spaced in mel between 0 and fs/2
+  auto hz2mel = [](double f) { return 2595.0 * std::log10(1.0 + f / 700.0); };
+  auto mel2hz = [](double m) { return 700.0 * (std::pow(10.0, m / 2595.0) - 1.0); };
+  const double mtop = hz2mel(sample_rate / 2.0);
+  n->melw.assign(size_t(WS_MEL) * WS_BINS, 0.f);
+  n->mel_rng.assign(WS_MEL, int2_{0, 0});
+  for (int m = 0; m < WS_MEL; ++m) {
+    const double lo = mel2hz(mtop * m / (WS_MEL + 1)), c = mel2hz(mtop * (m + 1) / (WS_MEL + 1)),
+                 hi = mel2hz(mtop * (m + 2) / (WS_MEL + 1));
+    int first = WS_BINS, last = 0;
+    for (int k = 0; k < WS_BINS; ++k) {
+      const double f = double(k) * sample_rate / WS_NFFT;
+      const double w = std::max(0.0, std::min((f - lo) / (c - lo), (hi - f) / (hi - c)));
+      n->melw[size_t(m) * WS_BINS + k] = float(w);
+      if (w > 0) {
+        first = std::min(first, k);
+        last = std::max(last, k + 1);
+      }
+    }
+    n->mel_rng[m] = int2_{first < WS_BINS ? first : 0, last};
+  }
+  fill_fft_tables(n->tw, n->ptw);
+  *out = n;
+  return GRAFX_OK;
+}
+
+int grafx_ws_destroy(grafx_wsnet* n) {
+  delete n;
+  return GRAFX_OK;
+}
+
+int grafx_ws_param_count(const grafx_wsnet* n, int64_t* count) {
+  if (!n || !count) return fail(GRAFX_EINVAL, "null argument");
+  *count = n->n_params;
+  return GRAFX_OK;
+}
+
+int grafx_ws_workspace_bytes(const grafx_wsnet* n, int32_t max_rows, int64_t max_len, size_t* bytes) {
+  if (!n || !bytes) return fail(GRAFX_EINVAL, "null argument");
+  if (max_rows < 0 || max_rows > 65535 || max_len < WS_NFFT)
+    return fail(GRAFX_ESHAPE, "log-mel rows: at most 65535, each at least 2048 samples");
+  *bytes = ws_layout(n, int64_t(max_rows) * n_frames_of(max_len) * WS_MEL).total;
+  return GRAFX_OK;
+}
+
+int grafx_ws_bind(grafx_wsnet* n, void* ws, size_t bytes, void* stream) {
+  if (!n || !ws) return fail(GRAFX_EINVAL, "null argument");
+  if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return fail(GRAFX_EINVAL, "workspace must be 256-byte aligned");
+  WsNetLayout L = ws_layout(n, 0);
+  if (bytes < L.total) return fail(GRAFX_ESHAPE, "workspace too small");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  cudaMemcpyAsync(w + L.melw, n->melw.data(), 4 * n->melw.size(), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(w + L.melrng, n->mel_rng.data(), sizeof(int2_) * n->mel_rng.size(), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(w + L.tw, n->tw.data(), sizeof(float2_) * n->tw.size(), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(w + L.ptw, n->ptw.data(), sizeof(float2_) * n->ptw.size(), cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(GRAFX_ECUDA, cudaGetErrorString(e));
+  n->ws = w;
+  n->ws_bytes = bytes;
+  return GRAFX_OK;
+}
+
+int grafx_ws_logmel(grafx_wsnet* n, const float* rows, int32_t n_rows, int64_t row_stride, int64_t pitch, int64_t len,
+                    const int32_t* row_of_sample, int32_t n_samples, int32_t coff, float* feats, void* stream) {
+  if (!n || !rows || !feats) return fail(GRAFX_EINVAL, "null argument");
+  if (!n->ws) return fail(GRAFX_ESTATE, "workspace not bound (grafx_ws_bind)");
+  if (n_rows < 1 || n_rows > 65535 || n_samples < 1 || len < WS_NFFT || pitch < len || row_stride < 2 * pitch ||
+      (coff != 0 && coff != WS_MEL) || (!row_of_sample && n_samples != n_rows) ||
+      int64_t(n_samples) * WS_MEL * WS_T > INT32_MAX)
+    return fail(GRAFX_ESHAPE, "bad log-mel shape");
+  const int nframes = n_frames_of(len);
+  WsNetLayout L = ws_layout(n, int64_t(n_rows) * nframes * WS_MEL);
+  if (L.total > n->ws_bytes) return fail(GRAFX_ESHAPE, "workspace too small for these log-mel rows");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float* fr = reinterpret_cast<float*>(n->ws + L.frames);
+  k_logmel_frames<<<dim3((nframes + 1) / 2, n_rows), WS_NFFT / 16, 0, s>>>(
+      rows, row_stride, pitch, nframes, reinterpret_cast<const float*>(n->ws + L.melw),
+      reinterpret_cast<const int2_*>(n->ws + L.melrng), reinterpret_cast<const float2_*>(n->ws + L.tw),
+      reinterpret_cast<const float2_*>(n->ws + L.ptw), fr);
+  k_logmel_pool<<<(n_samples * WS_MEL * WS_T + 255) / 256, 256, 0, s>>>(fr, nframes, n_rows, n_samples,
+                                                                          row_of_sample, coff, feats);
+  return cuda_status();
+}
+
+int grafx_ws_forward(grafx_wsnet* n, const float* weights, const float* feats, const int32_t* head_count, int32_t B,
+                     float* out, void* stream) {
+  if (!n || !weights || !feats || !head_count || !out) return fail(GRAFX_EINVAL, "null argument");
+  if (!n->ws) return fail(GRAFX_ESTATE, "workspace not bound (grafx_ws_bind)");
+  if (B < 1 || B > n->max_batch) return fail(GRAFX_ESHAPE, "batch out of range");
+  if (int rc = check_heads(head_count, B)) return rc;
+  WsNetLayout L = ws_layout(n, 0);
+  auto F = [&](size_t off) { return reinterpret_cast<float*>(n->ws + off); };
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int rows = B * WS_T;
+  const int cin[4] = {WS_IN, WS_CH, WS_CH, WS_CH};
+  for (int l = 0; l < 4; ++l) {
+    const float* src = l == 0 ? feats : F(L.h[l - 1]);
+    const int K = cin[l] * WS_KW;
+    k_im2col<<<grid1(int64_t(rows) * K), 256, 0, s>>>(src, B, cin[l], l == 0, F(L.im2col));
+    gemm(rows, WS_CH, K, F(L.im2col), K, 1, weights + n->off[l][0], 1, K, F(L.z[l]), WS_CH, 1.f, 0.f, s);
+    k_bias_act<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(F(L.z[l]), weights + n->off[l][1], F(L.h[l]), rows, WS_CH,
+                                                              WS_CH, 1);
+  }
+  k_time_mean<<<(B * WS_CH + 255) / 256, 256, 0, s>>>(F(L.h[3]), B, F(L.e));
+  cudaMemsetAsync(out, 0, sizeof(float) * size_t(B) * WS_OUTMAX, s);
+  int r0 = 0;
+  for (int h = 0; h < WS_NHEAD; ++h) {
+    const int nb = head_count[h];
+    if (nb == 0) continue;
+    const int64_t* o = n->hoff[h];
+    float *a1 = F(L.a1) + r0 * WS_HID, *g1 = F(L.g1) + r0 * WS_HID;
+    float *a2 = F(L.a2) + r0 * WS_HID, *g2 = F(L.g2) + r0 * WS_HID;
+    gemm(nb, WS_HID, WS_CH, F(L.e) + r0 * WS_CH, WS_CH, 1, weights + o[0], 1, WS_CH, a1, WS_HID, 1.f, 0.f, s);
+    k_bias_act<<<grid1(int64_t(nb) * WS_HID), 256, 0, s>>>(a1, weights + o[1], g1, nb, WS_HID, WS_HID, 1);
+    gemm(nb, WS_HID, WS_HID, g1, WS_HID, 1, weights + o[2], 1, WS_HID, a2, WS_HID, 1.f, 0.f, s);
+    k_bias_act<<<grid1(int64_t(nb) * WS_HID), 256, 0, s>>>(a2, weights + o[3], g2, nb, WS_HID, WS_HID, 1);
+    float* ob = out + int64_t(r0) * WS_OUTMAX;
+    gemm(nb, kHeadOut[h], WS_HID, g2, WS_HID, 1, weights + o[4], 1, WS_HID, ob, WS_OUTMAX, 1.f, 0.f, s);
+    k_bias_act<<<grid1(int64_t(nb) * kHeadOut[h]), 256, 0, s>>>(ob, weights + o[5], nullptr, nb, kHeadOut[h],
+                                                                  WS_OUTMAX, 0);
+    r0 += nb;
+  }
+  return cuda_status();
+}
+
+int grafx_ws_backward(grafx_wsnet* n, const float* weights, const float* feats, const int32_t* head_count, int32_t B,
+                      const float* d_out, float* d_weights, void* stream) {
+  if (!n || !weights || !feats || !head_count || !d_out || !d_weights) return fail(GRAFX_EINVAL, "null argument");
+  if (!n->ws) return fail(GRAFX_ESTATE, "workspace not bound (grafx_ws_bind)");
+  if (B < 1 || B > n->max_batch) return fail(GRAFX_ESHAPE, "batch out of range");
+  if (int rc = check_heads(head_count, B)) return rc;
+  WsNetLayout L = ws_layout(n, 0);
+  auto F = [&](size_t off) { return reinterpret_cast<float*>(n->ws + off); };
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaMemsetAsync(d_weights, 0, sizeof(float) * size_t(n->n_params), s);
+  float* de = F(L.dh);                                 // [B][128]
+  float* dh = F(L.dh) + size_t(n->max_batch) * WS_CH;  // [rows][128]
+  int r0 = 0;
+  for (int h = 0; h < WS_NHEAD; ++h) {
+    const int nb = head_count[h];
+    if (nb == 0) continue;
+    const int64_t* o = n->hoff[h];
+    const int no = kHeadOut[h];
+    const float* dO = d_out + int64_t(r0) * WS_OUTMAX;
+    float* da2 = F(L.dsmall) + r0 * WS_HID;
+    float* da1 = F(L.dsmall) + size_t(n->max_batch) * WS_HID + r0 * WS_HID;
+    const float *a1 = F(L.a1) + r0 * WS_HID, *g1 = F(L.g1) + r0 * WS_HID;
+    const float *a2 = F(L.a2) + r0 * WS_HID, *g2 = F(L.g2) + r0 * WS_HID;
+    // dW3 = dO^T g2, db3 = column sums of dO, da2 = (dO W3) gelu'(a2)
+    gemm(no, WS_HID, nb, dO, 1, WS_OUTMAX, g2, WS_HID, 1, d_weights + o[4], WS_HID, 1.f, 0.f, s);
+    k_colsum<<<(no + 31) / 32, 1024, 0, s>>>(dO, nb, no, WS_OUTMAX, d_weights + o[5]);
+    gemm(nb, WS_HID, no, dO, WS_OUTMAX, 1, weights + o[4], WS_HID, 1, da2, WS_HID, 1.f, 0.f, s);
+    k_gelu_bwd<<<grid1(int64_t(nb) * WS_HID), 256, 0, s>>>(da2, a2, int64_t(nb) * WS_HID);
+    // dW2 = da2^T g1, db2, da1 = (da2 W2) gelu'(a1)
+    gemm(WS_HID, WS_HID, nb, da2, 1, WS_HID, g1, WS_HID, 1, d_weights + o[2], WS_HID, 1.f, 0.f, s);
+    k_colsum<<<(WS_HID + 31) / 32, 1024, 0, s>>>(da2, nb, WS_HID, WS_HID, d_weights + o[3]);
+    gemm(nb, WS_HID, WS_HID, da2, WS_HID, 1, weights + o[2], WS_HID, 1, da1, WS_HID, 1.f, 0.f, s);
+    k_gelu_bwd<<<grid1(int64_t(nb) * WS_HID), 256, 0, s>>>(da1, a1, int64_t(nb) * WS_HID);
+    // dW1 = da1^T e, db1, de = da1 W1
+    gemm(WS_HID, WS_CH, nb, da1, 1, WS_HID, F(L.e) + r0 * WS_CH, WS_CH, 1, d_weights + o[0], WS_CH, 1.f, 0.f, s);
+    k_colsum<<<(WS_HID + 31) / 32, 1024, 0, s>>>(da1, nb, WS_HID, WS_HID, d_weights + o[1]);
+    gemm(nb, WS_CH, WS_HID, da1, WS_HID, 1, weights + o[0], WS_CH, 1, de + r0 * WS_CH, WS_CH, 1.f, 0.f, s);
+    r0 += nb;
+  }
+  const int rows = B * WS_T;
+  k_time_mean_bwd<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(de, B, dh);
+  const int cin[4] = {WS_IN, WS_CH, WS_CH, WS_CH};
+  for (int l = 3; l >= 0; --l) {
+    const int K = cin[l] * WS_KW;
+    // dz = dh gelu'(z); dW = dz^T im2col(input); db = column sums of dz
+    k_gelu_bwd<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(dh, F(L.z[l]), int64_t(rows) * WS_CH);
+    const float* src = l == 0 ? feats : F(L.h[l - 1]);
+    k_im2col<<<grid1(int64_t(rows) * K), 256, 0, s>>>(src, B, cin[l], l == 0, F(L.im2col));
+    gemm(WS_CH, K, rows, dh, 1, WS_CH, F(L.im2col), K, 1, d_weights + n->off[l][0], K, 1.f, 0.f, s);
+    k_colsum<<<WS_CH / 32, 1024, 0, s>>>(dh, rows, WS_CH, WS_CH, d_weights + n->off[l][1]);
+    if (l > 0) {
+      // d im2col = dz W, then its adjoint scatter gives dh of the previous layer
+      gemm(rows, K, WS_CH, dh, WS_CH, 1, weights + n->off[l][0], K, 1, F(L.dbig), K, 1.f, 0.f, s);
+      k_col2im<<<grid1(int64_t(rows) * cin[l]), 256, 0, s>>>(F(L.dbig), B, cin[l], dh);
+    }
+  }
+  return cuda_status();
+}
+
+int grafx_ws_mse(const float* out, const float* target, const int32_t* n_out, int32_t B, float* loss, float* d_out,
+                 void* stream) {
+  if (!out || !target || !n_out || !loss || !d_out) return fail(GRAFX_EINVAL, "null argument");
+  if (B < 1 || int64_t(B) * WS_OUTMAX > INT32_MAX) return fail(GRAFX_ESHAPE, "bad batch");
+  k_ws_mse<<<1, 1024, 0, static_cast<cudaStream_t>(stream)>>>(out, target, n_out, B, loss, d_out);
+  return cuda_status();
+}
+
+int grafx_gemm_bf16(int32_t M, int32_t N, int32_t K, const float* A, int64_t sam, int64_t sak, const float* B,
+                    int64_t sbk, int64_t sbn, float* C, int64_t ldc, float alpha, float beta, void* stream) {
+  if (!A || !B || !C) return fail(GRAFX_EINVAL, "null argument");
+  if (M < 0 || N < 0 || K < 0 || ldc < N || M > 65535 * GB_M) return fail(GRAFX_ESHAPE, "bad GEMM shape");
+  gemm(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta, static_cast<cudaStream_t>(stream));
+  return cuda_status();
+}
+
+}  // extern "C"

@@ -30,6 +30,15 @@ int launch_delay(int what, const DevCtx& c, int a, int b, cudaStream_t s);
 // convolution, 2 input adjoint, 3 parameter gradients; < 0 attributes only
 int launch_reverb(int what, const DevCtx& c, int a, int b, cudaStream_t s);
 
+// Node inputs u_v of a batch of nodes (new ids), gathered after a render into rows
+// dst[first + i][2][dst_pitch] (warm-start features).
+constexpr int NI_MAX = 256;
+struct NodeIds {
+  int32_t first;
+  int32_t v[NI_MAX];
+};
+int launch_node_inputs(const DevCtx& c, const NodeIds& ids, int n, float* dst, int64_t dst_pitch, cudaStream_t s);
+
 struct LossLaunch {
   const LossRow* rows;
   const int4_* items;   // (row, resolution, first frame, group)

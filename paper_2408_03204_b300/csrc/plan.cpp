@@ -65,6 +65,27 @@ int fail(int code, const std::string& msg) {
 void clear_error() { g_err.clear(); }
 const char* last_error_cstr() { return g_err.c_str(); }
 
+void fill_fft_tables(std::vector<float2_>& twiddle, std::vector<float2_>& ptw) {
+  twiddle.resize(TWIDDLE_N);
+  for (int m = 0; m < TWIDDLE_N; ++m) {
+    double a = 2.0 * M_PI * m / TWIDDLE_N;
+    twiddle[m] = float2_{float(std::cos(a)), float(-std::sin(a))};
+  }
+  // FFT pass twiddles W_{Ns R}^{r k} at [(r-1) Ns + k] for every pass of every size
+  ptw.assign(fft::PTW_TOTAL, float2_{0.f, 0.f});
+  for (int M = 512; M <= 8192; M *= 2) {
+    for (int pass = 1, Ns = 16; pass < fft::geo_npass(M); ++pass, Ns *= 16) {
+      const int R = fft::pass_radix(M, pass);
+      float2_* t = ptw.data() + fft::ptw_base(M) + fft::ptw_pass_off(M, pass);
+      for (int r = 1; r < R; ++r)
+        for (int k = 0; k < Ns; ++k) {
+          double a = -2.0 * M_PI * double(r) * k / (double(Ns) * R);
+          t[(r - 1) * Ns + k] = float2_{float(std::cos(a)), float(std::sin(a))};
+        }
+    }
+  }
+}
+
 int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* lengths,
                const grafx_plan_opts& opts, Plan* p) {
   p->opts = opts;
@@ -347,11 +368,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
   p->items.insert(p->items.end(), bwd.begin(), bwd.end());
 
   // ---- constant tables (double precision on the host, stored as float)
-  p->twiddle.resize(TWIDDLE_N);
-  for (int m = 0; m < TWIDDLE_N; ++m) {
-    double a = 2.0 * M_PI * m / TWIDDLE_N;
-    p->twiddle[m] = float2_{float(std::cos(a)), float(-std::sin(a))};
-  }
+  fill_fft_tables(p->twiddle, p->ptw);
   // Taylor coefficients of F(e^s) = sum_{k<N} k e^{ks} = N^2 sum_j e_j (N s)^j,
   // e_j = sum_k (k/N)^(j+1) / (N j!)  (delay surrogate near its pole)
   {
@@ -382,19 +399,6 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
       const double w = (std::log2(f) - lc[b]) / (lc[b + 1] - lc[b]);
       row[b] = float(1.0 - w);
       row[b + 1] = float(w);
-    }
-  }
-  // FFT pass twiddles W_{Ns R}^{r k} at [(r-1) Ns + k] for every pass of every size
-  p->ptw.assign(fft::PTW_TOTAL, float2_{0.f, 0.f});
-  for (int M = 512; M <= 8192; M *= 2) {
-    for (int pass = 1, Ns = 16; pass < fft::geo_npass(M); ++pass, Ns *= 16) {
-      const int R = fft::pass_radix(M, pass);
-      float2_* t = p->ptw.data() + fft::ptw_base(M) + fft::ptw_pass_off(M, pass);
-      for (int r = 1; r < R; ++r)
-        for (int k = 0; k < Ns; ++k) {
-          double a = -2.0 * M_PI * double(r) * k / (double(Ns) * R);
-          t[(r - 1) * Ns + k] = float2_{float(std::cos(a)), float(std::sin(a))};
-        }
     }
   }
   {

@@ -107,6 +107,9 @@ struct Plan {
 int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* lengths,
                const grafx_plan_opts& opts, Plan* p);
 
+// Twiddle table exp(-2 pi i m / TWIDDLE_N) and the per-pass FFT twiddle tables (fft.cuh)
+void fill_fft_tables(std::vector<float2_>& twiddle, std::vector<float2_>& ptw);
+
 inline int64_t pitch_of(int64_t L) { return (L + 3) & ~int64_t(3); }
 
 }  // namespace grafx

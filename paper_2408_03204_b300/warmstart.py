@@ -1,0 +1,393 @@
+"""Learned warm start for the parameter fit (grafx_ws_* kernels): a network that maps
+the log-mel of a node's input (rendered with neutral parameters) and of the target mix
+to the node's unconstrained parameters theta.  The paper motivates such a trained
+estimator (Sec. 1) and leaves it open; this is the library's own.
+
+Everything numeric runs in the library's kernels: renders and node inputs, log-mel
+features, the network forward/backward (BF16 tensor-core products, FP32 accumulation),
+the masked MSE and the Adam update.  torch provides device memory, streams, random
+initial weights and the index bookkeeping of minibatches.
+
+    python -m paper_2408_03204_b300.warmstart --train-graphs 512 --test-graphs 8
+trains on random consoles and prints one JSON line comparing the fit from the
+predicted start (inference + 200 Adam steps) with 1000 Adam steps from neutral.
+"""
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import (PARAM_COLS, T_COMP, T_DELAY, T_EQ, T_GAIN, T_IMAGER, T_IN, T_OUT, T_MIX, T_REVERB, WS_HEAD_OUT,
+               WS_HEAD_TYPES, WS_OUTMAX, Graph, Plan, WarmStartNet, _check, _ptr, _stream_of, lib)
+from . import fit as gfit
+
+HEAD_OF = {t: i for i, t in enumerate(WS_HEAD_TYPES)}
+
+
+def param_shapes():
+    """(name, shape) of every weight tensor in the flat order of the kernels."""
+    s = []
+    cin = (256, 128, 128, 128)
+    for l in range(4):
+        s += [(f"conv{l}.w", (128, cin[l], 5)), (f"conv{l}.b", (128,))]
+    for t, n in zip(WS_HEAD_TYPES, WS_HEAD_OUT):
+        s += [(f"h{t}.w1", (288, 128)), (f"h{t}.b1", (288,)), (f"h{t}.w2", (288, 288)), (f"h{t}.b2", (288,)),
+              (f"h{t}.w3", (n, 288)), (f"h{t}.b3", (n,))]
+    return s
+
+
+def init_weights(torch, device, seed=0):
+    """He-normal weights, zero biases; the first layer is scaled by 1/8 because log-mel
+    inputs have magnitudes of about 6."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    parts = []
+    for name, sh in param_shapes():
+        n = int(np.prod(sh))
+        if ".w" in name:
+            fan_in = int(np.prod(sh[1:]))
+            w = torch.randn(n, generator=g) * math.sqrt(2.0 / fan_in)
+            if name == "conv0.w":
+                w *= 0.125
+            parts.append(w)
+        else:
+            parts.append(torch.zeros(n))
+    return torch.cat(parts).to(device=device, dtype=torch.float32).contiguous()
+
+
+class GraphBatch:
+    """A plan over a batch of graphs plus host bookkeeping of its processor nodes:
+    union id, type, row within the type's parameter table, output row of its graph."""
+
+    def __init__(self, graph_lists, L, eq_taps=1023, schedule="beam"):
+        self.graph_lists = graph_lists
+        self.L = L
+        self.plan = Plan([Graph.from_lists(t, e) for t, e in graph_lists], [L] * len(graph_lists),
+                         eq_taps=eq_taps, schedule=schedule)
+        ids, types, rows, outrow, graph_of = [], [], [], [], []
+        cnt = {t: 0 for t in PARAM_COLS}
+        base, n_out = 0, 0
+        for gi, (tys, _) in enumerate(graph_lists):
+            first_out = n_out
+            for v, t in enumerate(tys):
+                if t in PARAM_COLS:
+                    ids.append(base + v)
+                    types.append(t)
+                    rows.append(cnt[t])
+                    outrow.append(first_out)
+                    graph_of.append(gi)
+                    cnt[t] += 1
+            n_out += sum(1 for t in tys if t == T_OUT)
+            base += len(tys)
+        # samples sorted by head, then union id
+        order = sorted(range(len(ids)), key=lambda i: (HEAD_OF[types[i]], ids[i]))
+        self.ids = [ids[i] for i in order]
+        self.types = [types[i] for i in order]
+        self.rows = [rows[i] for i in order]
+        self.outrow = [outrow[i] for i in order]
+        self.graph_of = [graph_of[i] for i in order]
+        self.head_count = [sum(1 for t in self.types if t == ht) for ht in WS_HEAD_TYPES]
+        self.n_out_rows = n_out
+
+
+class WarmStart:
+    """Network weights, Adam state, target standardisation and the feature pipeline."""
+
+    def __init__(self, max_batch=2048, max_rows=4096, max_len=2 ** 16, device="cuda", seed=0, lr=1e-3):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.net = WarmStartNet(max_batch, max_rows, max_len, device=device)
+        self.max_batch, self.max_rows = max_batch, max_rows
+        self.W = init_weights(torch, self.device, seed)
+        assert self.W.numel() == self.net.n_params
+        self.m = torch.zeros_like(self.W)
+        self.v = torch.zeros_like(self.W)
+        self.dW = torch.zeros_like(self.W)
+        self.code = torch.zeros(1, dtype=torch.int8, device=self.device)
+        self.step_no = 0
+        self.lr = lr
+        # per head-column standardisation of theta (fitted on the training targets)
+        self.mu = torch.zeros(len(WS_HEAD_TYPES), WS_OUTMAX, device=self.device)
+        self.sd = torch.ones(len(WS_HEAD_TYPES), WS_OUTMAX, device=self.device)
+        # the caller's current stream: torch bookkeeping and library calls stay ordered
+        self.stream = torch.cuda.current_stream(self.device)
+        self.st = _stream_of(self.stream)
+
+    # ---------------------------------------------------------------- features
+    def features(self, batch, sources, target, neutral):
+        """feats [n, 256, 32] for the batch's processor nodes (sorted by head): node input
+        under ``neutral`` parameters and the target mix of the node's graph."""
+        torch = self.torch
+        plan, L = batch.plan, batch.L
+        P = (L + 3) // 4 * 4
+        n = len(batch.ids)
+        feats = torch.empty((n, 256, 32), dtype=torch.float32, device=self.device)
+        with torch.cuda.stream(self.stream):
+            plan.bind_params(neutral)
+            out = torch.empty(plan.info.out_elems, dtype=torch.float32, device=self.device)
+            plan.render_raw(sources, out, self.st)
+            for a in range(0, n, self.max_rows):
+                b = min(n, a + self.max_rows)
+                u = torch.empty((b - a, 2, P), dtype=torch.float32, device=self.device)
+                plan.node_inputs_raw(sources, out, batch.ids[a:b], u, P, self.st)
+                self.net.logmel_raw(u, b - a, 2 * P, P, L, None, b - a, 0, feats[a:], self.st)
+            rmap = torch.tensor(batch.outrow, dtype=torch.int32, device=self.device)
+            self.net.logmel_raw(target, batch.n_out_rows, 2 * P, P, L, rmap, n, 128, feats, self.st)
+        return feats
+
+    def theta_targets(self, batch, hidden):
+        """[n, 176] theta of the hidden physical parameters, rows sorted like the samples."""
+        torch = self.torch
+        tgt = torch.zeros((len(batch.ids), WS_OUTMAX), dtype=torch.float32, device=self.device)
+        with torch.cuda.stream(self.stream):
+            for t in WS_HEAD_TYPES:
+                if t not in hidden:
+                    continue
+                p = hidden[t]
+                codes = torch.tensor(gfit.param_codes(t), dtype=torch.int8, device=self.device)
+                th = torch.empty_like(p)
+                _check(lib().grafx_params_to_theta(_ptr(p), _ptr(codes), p.shape[1], p.numel(), _ptr(th), self.st))
+                sel = [i for i, tt in enumerate(batch.types) if tt == t]
+                if sel:
+                    rows = torch.tensor([batch.rows[i] for i in sel], device=self.device)
+                    tgt[sel[0]:sel[-1] + 1, :p.shape[1]] = th.index_select(0, rows)
+        return tgt
+
+    # ---------------------------------------------------------------- network
+    def fit_standardisation(self, targets, types):
+        torch = self.torch
+        types = torch.as_tensor(types, device=self.device)
+        for h, t in enumerate(WS_HEAD_TYPES):
+            m = types == t
+            if int(m.sum()) > 1:
+                x = targets[m]
+                self.mu[h] = x.mean(0)
+                self.sd[h] = x.std(0).clamp_min(1e-3)
+
+    def _std(self, targets, heads):
+        return (targets - self.mu[heads]) / self.sd[heads]
+
+    def train_step(self, feats, targets, types):
+        """One Adam step on a minibatch (feats [B,256,32], targets theta [B,176], types
+        sorted by head).  Returns the device loss tensor."""
+        torch = self.torch
+        B = feats.shape[0]
+        heads = torch.as_tensor([HEAD_OF[t] for t in types], device=self.device)
+        hc = [sum(1 for t in types if t == ht) for ht in WS_HEAD_TYPES]
+        n_out = torch.as_tensor([WS_HEAD_OUT[HEAD_OF[t]] for t in types], dtype=torch.int32, device=self.device)
+        with torch.cuda.stream(self.stream):
+            y = self._std(targets, heads).contiguous()
+            out = torch.empty((B, WS_OUTMAX), dtype=torch.float32, device=self.device)
+            d = torch.empty_like(out)
+            loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+            self.net.forward_raw(self.W, feats, hc, out, self.st)
+            WarmStartNet.mse_raw(out, y, n_out, loss, d, self.st)
+            self.net.backward_raw(self.W, feats, hc, d, self.dW, self.st)
+            self.step_no += 1
+            _check(lib().grafx_adam_step(_ptr(self.W), _ptr(self.m), _ptr(self.v), _ptr(self.dW), _ptr(self.W),
+                                         _ptr(self.code), 1, self.W.numel(), self.step_no, float(self.lr), 0.9,
+                                         0.999, 1e-8, self.st))
+        return loss
+
+    def predict(self, feats, types):
+        """theta [n, 176] (un-standardised) for samples sorted by head."""
+        torch = self.torch
+        heads = torch.as_tensor([HEAD_OF[t] for t in types], device=self.device)
+        hc = [sum(1 for t in types if t == ht) for ht in WS_HEAD_TYPES]
+        outs = []
+        with torch.cuda.stream(self.stream):
+            for a in range(0, feats.shape[0], self.max_batch):
+                b = min(feats.shape[0], a + self.max_batch)
+                sub = list(types[a:b])
+                hcs = [sum(1 for t in sub if t == ht) for ht in WS_HEAD_TYPES]
+                out = torch.empty((b - a, WS_OUTMAX), dtype=torch.float32, device=self.device)
+                self.net.forward_raw(self.W, feats[a:b], hcs, out, self.st)
+                outs.append(out)
+            out = torch.cat(outs)
+            mask = torch.arange(WS_OUTMAX, device=self.device)[None, :] < torch.as_tensor(
+                [WS_HEAD_OUT[HEAD_OF[t]] for t in types], device=self.device)[:, None]
+            theta = torch.where(mask, out * self.sd[heads] + self.mu[heads], torch.zeros_like(out))
+        del hc
+        return theta
+
+    def theta_tables(self, batch, theta):
+        """Scatter per-sample theta back into per-type [rows, cols] tables of the plan."""
+        torch = self.torch
+        tabs = {}
+        with torch.cuda.stream(self.stream):
+            for t in WS_HEAD_TYPES:
+                rows = batch.plan.info.n_type_rows[t]
+                if not rows:
+                    continue
+                sel = [i for i, tt in enumerate(batch.types) if tt == t]
+                tab = torch.zeros((rows, PARAM_COLS[t]), dtype=torch.float32, device=self.device)
+                idx = torch.tensor([batch.rows[i] for i in sel], device=self.device)
+                tab.index_copy_(0, idx, theta[sel[0]:sel[-1] + 1, :PARAM_COLS[t]])
+                tabs[t] = tab
+        return tabs
+
+
+# -------------------------------------------------------------------- synthetic data
+def random_graph_lists(rng, n, lo=32, hi=200, kinds=(T_GAIN, T_EQ, T_COMP, T_IMAGER, T_DELAY)):
+    import synth
+    out = []
+    for _ in range(n):
+        g = synth.random_console(rng, budget_lo=lo, budget_hi=hi, kinds=kinds)
+        out.append((list(g.types), list(g.edges)))
+    return out
+
+
+def make_batch(ws, graph_lists, L, seed, hidden_seed):
+    """Plan, sources, hidden parameters, target mix and neutral parameters of a batch."""
+    import synth
+    torch = ws.torch
+    batch = GraphBatch(graph_lists, L)
+    plan = batch.plan
+    plan.bind_workspace(ws.device)
+    P = (L + 3) // 4 * 4
+    src = np.concatenate([synth.sources(seed + k, sum(1 for t in tys if t == T_IN), L, pitch=P).reshape(-1)
+                          for k, (tys, _) in enumerate(graph_lists)])
+    src = torch.tensor(src, device=ws.device)
+    hidden = {}
+    for k, (tys, eds) in enumerate(graph_lists):
+        g = synth.Graph(list(tys), list(eds))
+        for t, a in synth.random_params(g, hidden_seed + k).items():
+            hidden.setdefault(t, []).append(a)
+    hidden = {t: torch.tensor(np.concatenate(v), device=ws.device).contiguous() for t, v in hidden.items()}
+    target = torch.empty(plan.info.out_elems, dtype=torch.float32, device=ws.device)
+    with torch.cuda.stream(ws.stream):
+        plan.bind_params(hidden)
+        plan.render_raw(src, target, ws.st)
+    neutral = gfit.neutral_params(plan, torch, ws.device)
+    ws.stream.synchronize()
+    return batch, src, hidden, target, neutral
+
+
+def train(ws, n_graphs, L, graphs_per_batch=16, epochs=4, minibatch=512, seed=5, log=None):
+    """Generate n_graphs random consoles, build their features and theta targets, fit the
+    standardisation and train.  Returns (losses per step, data seconds, train seconds)."""
+    torch = ws.torch
+    rng = np.random.Generator(np.random.PCG64(seed))
+    feats, targets, types = [], [], []
+    t0 = time.time()
+    for b0 in range(0, n_graphs, graphs_per_batch):
+        gl = random_graph_lists(rng, min(graphs_per_batch, n_graphs - b0))
+        batch, src, hidden, target, neutral = make_batch(ws, gl, L, seed * 100000 + b0 * 37, seed * 7919 + b0)
+        feats.append(ws.features(batch, src, target, neutral))
+        targets.append(ws.theta_targets(batch, hidden))
+        types += batch.types
+        ws.stream.synchronize()
+        del batch, src, hidden, target, neutral
+    feats = torch.cat(feats)
+    targets = torch.cat(targets)
+    t_data = time.time() - t0
+    ws.fit_standardisation(targets, types)
+    types_t = torch.as_tensor(types, device=ws.device)
+    head_of = torch.as_tensor([HEAD_OF.get(t, 0) for t in range(9)], device=ws.device)
+    n = feats.shape[0]
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    losses = []
+    t1 = time.time()
+    for ep in range(epochs):
+        perm = torch.randperm(n, generator=g).to(ws.device)
+        for a in range(0, n - minibatch + 1, minibatch):
+            idx = perm[a:a + minibatch]
+            hk = head_of[types_t[idx]]
+            idx = idx[torch.argsort(hk * n + idx)]
+            tl = types_t[idx].tolist()
+            loss = ws.train_step(feats.index_select(0, idx), targets.index_select(0, idx), tl)
+            losses.append(loss)
+        if log:
+            ws.stream.synchronize()
+            log(f"epoch {ep}: loss {float(torch.stack(losses[-10:]).mean()):.4f}")
+    ws.stream.synchronize()
+    t_train = time.time() - t1
+    return [float(x) for x in torch.cat(losses).cpu()], t_data, t_train, n
+
+
+def evaluate(ws, graph_lists, L, seed, plain_steps=1000, warm_steps=200, lr=1e-2):
+    """Per test graph: loss curve of plain Adam from neutral and of Adam from the
+    predicted start; wall times (CUDA events) of the inference and of the steps."""
+    torch = ws.torch
+    res = []
+    for k, gl in enumerate(graph_lists):
+        batch, src, hidden, target, neutral = make_batch(ws, [gl], L, seed + 1000 * k, seed + 7 * k + 1)
+        # plain fit from neutral (its own stream; the captured step needs one)
+        P0 = {t: p.clone() for t, p in neutral.items()}
+        f = gfit.Fit(batch.plan, src, target, P0, lr=lr)
+        hist = torch.zeros(plain_steps, device=ws.device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f.stream.wait_stream(ws.stream)
+        with torch.cuda.stream(f.stream):
+            e0.record(f.stream)
+            for i in range(plain_steps):
+                f.step()
+                hist[i:i + 1].copy_(f.loss)
+            e1.record(f.stream)
+        f.stream.synchronize()
+        plain = hist.cpu().numpy()
+        t_plain = e0.elapsed_time(e1) / 1e3
+        # warm start: neutral render, node inputs, features and network, then Adam
+        e2, e3, e4, e5 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+        e2.record(ws.stream)
+        feats = ws.features(batch, src, target, neutral)
+        theta = ws.predict(feats, batch.types)
+        th0 = ws.theta_tables(batch, theta)
+        e3.record(ws.stream)
+        P1 = {t: p.clone() for t, p in neutral.items()}
+        f2 = gfit.Fit(batch.plan, src, target, P1, lr=lr, theta0=th0)
+        hist2 = torch.zeros(warm_steps, device=ws.device)
+        f2.stream.wait_stream(ws.stream)
+        with torch.cuda.stream(f2.stream):
+            e5.record(f2.stream)
+            for i in range(warm_steps):
+                f2.step()
+                hist2[i:i + 1].copy_(f2.loss)
+            e4.record(f2.stream)
+        f2.stream.synchronize()
+        ws.stream.synchronize()
+        warm = hist2.cpu().numpy()
+        t_inf = e2.elapsed_time(e3) / 1e3
+        t_warm_steps = e5.elapsed_time(e4) / 1e3
+        final = float(plain[-1])
+        reach = np.nonzero(warm <= final)[0]
+        step_time = t_warm_steps / warm_steps
+        t_reach = t_inf + (int(reach[0]) + 1) * step_time if reach.size else None
+        res.append(dict(nodes=len(gl[0]), plain_final=final, plain_first=float(plain[0]), warm_first=float(warm[0]),
+                        warm_final=float(warm[-1]), warm_best=float(warm.min()), t_plain=t_plain, t_inference=t_inf,
+                        t_warm_steps=t_warm_steps, steps_to_plain_final=int(reach[0]) + 1 if reach.size else None,
+                        t_warm_to_plain_final=t_reach,
+                        speedup=(t_plain / t_reach) if t_reach else None))
+        del f, f2, batch
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train-graphs", type=int, default=256)
+    ap.add_argument("--test-graphs", type=int, default=4)
+    ap.add_argument("--length", type=int, default=2 ** 16)
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--minibatch", type=int, default=512)
+    ap.add_argument("--plain-steps", type=int, default=1000)
+    ap.add_argument("--warm-steps", type=int, default=200)
+    args = ap.parse_args()
+    import torch
+    ws = WarmStart(max_batch=max(2048, args.minibatch), max_rows=1024, max_len=args.length)
+    losses, t_data, t_train, n = train(ws, args.train_graphs, args.length, epochs=args.epochs,
+                                       minibatch=args.minibatch, log=lambda s: print(s, flush=True))
+    rng = np.random.Generator(np.random.PCG64(555))
+    tests = random_graph_lists(rng, args.test_graphs)
+    res = evaluate(ws, tests, args.length, 9000, args.plain_steps, args.warm_steps)
+    sp = [r["speedup"] for r in res if r["speedup"]]
+    print(json.dumps(dict(train_graphs=args.train_graphs, train_samples=n, length=args.length,
+                          data_s=round(t_data, 2), train_s=round(t_train, 2), train_steps=len(losses),
+                          loss_first=losses[0], loss_last=float(np.mean(losses[-20:])),
+                          median_speedup=float(np.median(sp)) if sp else None,
+                          reached=len(sp), tests=res, gpu=torch.cuda.get_device_name())))
+
+
+if __name__ == "__main__":
+    main()

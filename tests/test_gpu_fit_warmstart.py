@@ -1,0 +1,112 @@
+"""The fit loop (paper_2408_03204_b300.fit) and the warm-start pipeline
+(paper_2408_03204_b300.warmstart) on the GPU: composition and training behaviour.
+The kernels they call are checked against the oracle elsewhere."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import paper_2408_03204_b300 as gx
+    from paper_2408_03204_b300 import fit as gfit
+    from paper_2408_03204_b300 import warmstart as gws
+    return gx, torch, gfit, gws
+
+
+def _small_batch(gws, ws, n_graphs=3, L=8192, seed=1):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gl = gws.random_graph_lists(rng, n_graphs, lo=20, hi=40)
+    return gws.make_batch(ws, gl, L, 100 + seed, 200 + seed)
+
+
+def test_fit_graph_replay_equals_eager_and_descends(env):
+    gx, torch, gfit, gws = env
+    ws = gws.WarmStart(max_batch=256, max_rows=256, max_len=8192)
+    batch, src, hidden, target, neutral = _small_batch(gws, ws)
+    runs = []
+    for use_graph in (True, False):
+        P = {t: p.clone() for t, p in neutral.items()}
+        f = gfit.Fit(batch.plan, src, target, P, lr=1e-2, use_graph=use_graph)
+        losses = []
+        for _ in range(25):
+            f.step()
+            losses.append(f.current_loss())
+        runs.append((losses, {t: p.cpu().numpy() for t, p in P.items()}))
+    assert runs[0][0] == runs[1][0]
+    for t in runs[0][1]:
+        np.testing.assert_array_equal(runs[0][1][t], runs[1][1][t])
+    losses = runs[0][0]
+    assert losses[-1] < 0.9 * losses[0], losses
+
+
+def test_fit_from_theta0_maps_parameters(env):
+    gx, torch, gfit, gws = env
+    ws = gws.WarmStart(max_batch=256, max_rows=256, max_len=8192)
+    batch, src, hidden, target, neutral = _small_batch(gws, ws, seed=2)
+    th0 = {}
+    for t, p in hidden.items():
+        codes = torch.tensor(gfit.param_codes(t), dtype=torch.int8, device="cuda")
+        th = torch.empty_like(p)
+        gx._check(gx.lib().grafx_params_to_theta(gx._ptr(p), gx._ptr(codes), p.shape[1], p.numel(), gx._ptr(th),
+                                                  gx._stream(torch, p.device)))
+        th0[t] = th
+    P = {t: p.clone() for t, p in neutral.items()}
+    f = gfit.Fit(batch.plan, src, target, P, lr=1e-2, theta0=th0)
+    for t in hidden:
+        np.testing.assert_allclose(P[t].cpu().numpy(), hidden[t].cpu().numpy(), rtol=2e-4, atol=2e-4)
+    # started at the hidden parameters: the loss is (close to) zero
+    f.step()
+    assert f.current_loss() < 1e-3
+
+
+def test_features_compose_node_inputs_and_mix(env):
+    gx, torch, gfit, gws = env
+    ws = gws.WarmStart(max_batch=512, max_rows=64, max_len=8192)
+    batch, src, hidden, target, neutral = _small_batch(gws, ws, seed=3)
+    feats = ws.features(batch, src, target, neutral)
+    torch.cuda.synchronize()
+    n = len(batch.ids)
+    assert feats.shape == (n, 256, 32) and torch.isfinite(feats).all()
+    # mix channels: identical for the samples of one graph, different across graphs
+    f = feats.cpu().numpy()
+    for i in range(n):
+        j = batch.graph_of.index(batch.graph_of[i])
+        np.testing.assert_array_equal(f[i, 128:], f[j, 128:])
+    # node-input channels: the log-mel of grafx_node_inputs rows, recomputed separately
+    P = (8192 + 3) // 4 * 4
+    out = torch.empty(batch.plan.info.out_elems, device="cuda")
+    st = gx._stream(torch, out.device)
+    batch.plan.bind_params(neutral)
+    batch.plan.render_raw(src, out, st)
+    u = torch.empty((5, 2, P), device="cuda")
+    batch.plan.node_inputs_raw(src, out, batch.ids[-5:], u, P, st)
+    f2 = torch.empty((5, 256, 32), device="cuda")
+    ws.net.logmel_raw(u, 5, 2 * P, P, 8192, None, 5, 0, f2, st)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(f2[:, :128].cpu().numpy(), f[-5:, :128])
+    # the samples are sorted by head and their counts match the graphs' processors
+    heads = [gws.HEAD_OF[t] for t in batch.types]
+    assert heads == sorted(heads)
+    want = sum(sum(1 for t in tys if t in gx.PARAM_COLS) for tys, _ in batch.graph_lists)
+    assert n == want
+
+
+def test_warm_start_training_reduces_loss_and_predicts(env):
+    gx, torch, gfit, gws = env
+    ws = gws.WarmStart(max_batch=256, max_rows=512, max_len=8192, lr=1e-3)
+    losses, t_data, t_train, n = gws.train(ws, 12, 8192, graphs_per_batch=6, epochs=12, minibatch=64, seed=7)
+    assert n > 64
+    assert np.mean(losses[-5:]) < 0.8 * np.mean(losses[:5]), (losses[:5], losses[-5:])
+    batch, src, hidden, target, neutral = _small_batch(gws, ws, seed=9)
+    feats = ws.features(batch, src, target, neutral)
+    theta = ws.predict(feats, batch.types)
+    tabs = ws.theta_tables(batch, theta)
+    torch.cuda.synchronize()
+    assert torch.isfinite(theta).all()
+    for t, tab in tabs.items():
+        assert tab.shape == (batch.plan.info.n_type_rows[t], gx.PARAM_COLS[t])

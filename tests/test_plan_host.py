@@ -26,7 +26,7 @@ def gx():
 def test_exports_every_declared_symbol(gx):
     header = open(os.path.join(ROOT, "include", "grafx.h")).read()
     header = re.sub(r"/\*.*?\*/", "", header, flags=re.S)
-    declared = set(re.findall(r"\b(grafx_[a-z_]+)\s*\(", header))
+    declared = set(re.findall(r"\b(grafx_[a-z0-9_]+)\s*\(", header))
     assert len(declared) >= 20
     lib = gx.lib()
     for name in declared:
