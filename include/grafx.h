@@ -112,7 +112,14 @@ typedef struct {
   int32_t n_threads;      /* host threads for planning; 0 = hardware concurrency */
   int32_t eq_fft;         /* EQ block FFT size (1024..8192, > 2*eq_taps); 0 = autotune default */
   int32_t comp_chunk;     /* compressor scan chunk (1024 or 2048 samples); 0 = default */
-  int32_t reserved[9];
+  int32_t checkpoint_steps; /* signal checkpointing: 0 = off (every node row kept from the
+                             * forward to the backward pass); k > 0 = the schedule steps are
+                             * cut into segments of k steps, only rows read by a later
+                             * segment are kept, the other rows of all segments share one
+                             * scratch region, and grafx_backprop recomputes the forward of
+                             * every segment but the last before running its backward
+                             * (smaller workspace, one extra forward of steps 1..N-k). */
+  int32_t reserved[8];
 } grafx_plan_opts;
 
 void grafx_plan_opts_default(grafx_plan_opts* o);
@@ -197,7 +204,9 @@ int grafx_render_steps(grafx_plan* p, const float* sources, float* out, int32_t 
                        void* stream);
 /* Backward over the steps k in [first, last) in reverse order (0 <= first <= last <= N+1);
  * k = 0 stands for the source adjoints (written only if d_sources is not NULL).
- * grafx_backprop is first = 0, last = N+1. */
+ * Without checkpointing grafx_backprop is first = 0, last = N+1.  With checkpointing
+ * the node rows of a step are valid only while its segment is the one rendered last,
+ * so a range must lie in that segment (grafx_backprop orders this itself). */
 int grafx_backprop_steps(grafx_plan* p, const float* sources, const float* d_out, float* const* d_params,
                          float* d_sources, int32_t first, int32_t last, void* stream);
 
@@ -272,7 +281,8 @@ int grafx_params_to_theta(const float* param, const int8_t* codes, int32_t cols,
  * nodes `ids` (host int32, ids in the plan's union numbering: graph g's node j is
  * j + the node counts of graphs 0..g-1) into device rows dst[i][2][dst_pitch]
  * (dst_pitch a multiple of 4 and >= the node's length; samples past the length are
- * 0).  Input nodes are rejected (GRAFX_EINVAL).  Asynchronous on `stream`. */
+ * 0).  Input nodes are rejected (GRAFX_EINVAL), and so are plans with checkpointing
+ * (GRAFX_ESTATE: their scratch rows do not outlive a segment).  Asynchronous on `stream`. */
 int grafx_node_inputs(grafx_plan* p, const float* sources, const float* out, const int32_t* ids, int32_t n,
                       float* dst, int64_t dst_pitch, void* stream);
 

@@ -35,7 +35,8 @@ class GrafxError(RuntimeError):
 class PlanOpts(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("beam_width", ctypes.c_int32), ("eq_taps", ctypes.c_int32),
                 ("sample_rate", ctypes.c_int32), ("n_threads", ctypes.c_int32), ("eq_fft", ctypes.c_int32),
-                ("comp_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("comp_chunk", ctypes.c_int32), ("checkpoint_steps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 8)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -178,11 +179,12 @@ class Plan:
     """Render data of one graph or a batch of graphs (Algorithm 1 lines 1-4)."""
 
     def __init__(self, graphs, lengths, schedule="beam", beam_width=32, eq_taps=1023, sample_rate=44100,
-                 n_threads=0, eq_fft=0, comp_chunk=0):
+                 n_threads=0, eq_fft=0, comp_chunk=0, checkpoint_steps=0):
         o = PlanOpts()
         lib().grafx_plan_opts_default(ctypes.byref(o))
         o.schedule, o.beam_width, o.eq_taps = SCHED[schedule], beam_width, eq_taps
         o.sample_rate, o.n_threads, o.eq_fft, o.comp_chunk = sample_rate, n_threads, eq_fft, comp_chunk
+        o.checkpoint_steps = checkpoint_steps
         hs = (_P * len(graphs))(*[g._h for g in graphs])
         ls = (ctypes.c_int64 * len(lengths))(*[int(x) for x in lengths])
         h = _P()

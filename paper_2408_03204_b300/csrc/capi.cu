@@ -320,14 +320,9 @@ int grafx_bind_reverb_noise(grafx_plan* p, const float* dev, int64_t n) {
   return GRAFX_OK;
 }
 
-int grafx_render_steps(grafx_plan* p, const float* sources, float* out, int32_t first, int32_t last,
-                       void* stream) {
-  if (!p || !sources || !out) return fail(GRAFX_EINVAL, "null argument");
-  int rc = check_ready(p);
-  if (rc) return rc;
-  const int N = int(p->sched.string.size()) - 1;
-  if (first < 1 || last > N + 1 || first > last) return fail(GRAFX_EINVAL, "step range out of bounds");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+// Forward steps [first, last) (already validated); returns the number of launches.
+static int render_range(grafx_plan* p, const float* sources, float* out, int32_t first, int32_t last,
+                        cudaStream_t s) {
   DevCtx c = make_ctx(p, sources, out, nullptr, nullptr);
   int launches = 0;
   for (int k = first; k < last; ++k) {
@@ -355,7 +350,17 @@ int grafx_render_steps(grafx_plan* p, const float* sources, float* out, int32_t 
         launches += launch_ew_fwd(st.type, c, st.fitem_begin, st.fitem_count, s);
     }
   }
-  p->last_launches = launches;
+  return launches;
+}
+
+int grafx_render_steps(grafx_plan* p, const float* sources, float* out, int32_t first, int32_t last,
+                       void* stream) {
+  if (!p || !sources || !out) return fail(GRAFX_EINVAL, "null argument");
+  int rc = check_ready(p);
+  if (rc) return rc;
+  const int N = int(p->sched.string.size()) - 1;
+  if (first < 1 || last > N + 1 || first > last) return fail(GRAFX_EINVAL, "step range out of bounds");
+  p->last_launches = render_range(p, sources, out, first, last, static_cast<cudaStream_t>(stream));
   return cuda_check(cudaGetLastError(), "render launch");
 }
 
@@ -369,6 +374,7 @@ int grafx_node_inputs(grafx_plan* p, const float* sources, const float* out, con
   if (!p || !sources || !out || (!ids && n > 0) || (!dst && n > 0)) return fail(GRAFX_EINVAL, "null argument");
   int rc = check_ready(p);
   if (rc) return rc;
+  if (!p->seg_ptr.empty()) return fail(GRAFX_ESTATE, "node inputs need a plan without checkpointing");
   const int32_t nv = int32_t(p->types.size());
   if (n < 0 || dst_pitch < 4 || (dst_pitch & 3)) return fail(GRAFX_ESHAPE, "bad node-input shape");
   for (int32_t i = 0; i < n; ++i) {
@@ -391,6 +397,9 @@ int grafx_node_inputs(grafx_plan* p, const float* sources, const float* out, con
   return cuda_check(cudaGetLastError(), "node-input launch");
 }
 
+static int backprop_range(grafx_plan* p, const float* sources, const float* d_out, float* const* d_params,
+                          float* d_sources, int32_t first, int32_t last, cudaStream_t s);
+
 int grafx_backprop_steps(grafx_plan* p, const float* sources, const float* d_out, float* const* d_params,
                          float* d_sources, int32_t first, int32_t last, void* stream) {
   if (!p || !sources || !d_out) return fail(GRAFX_EINVAL, "null argument");
@@ -398,7 +407,14 @@ int grafx_backprop_steps(grafx_plan* p, const float* sources, const float* d_out
   if (rc) return rc;
   const int N = int(p->sched.string.size()) - 1;
   if (first < 0 || last > N + 1 || first > last) return fail(GRAFX_EINVAL, "step range out of bounds");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->last_launches = backprop_range(p, sources, d_out, d_params, d_sources, first, last,
+                                    static_cast<cudaStream_t>(stream));
+  return cuda_check(cudaGetLastError(), "backprop launch");
+}
+
+// Backward steps [first, last) in reverse (already validated); returns the launches.
+static int backprop_range(grafx_plan* p, const float* sources, const float* d_out, float* const* d_params,
+                          float* d_sources, int32_t first, int32_t last, cudaStream_t s) {
   DevCtx c = make_ctx(p, sources, nullptr, d_out, d_sources);
   int launches = 0;
   for (int k = last - 1; k >= std::max(first, 1); --k) {
@@ -437,14 +453,29 @@ int grafx_backprop_steps(grafx_plan* p, const float* sources, const float* d_out
     }
   }
   if (first == 0 && d_sources) launches += launch_ew_bwd(GRAFX_T_MIX, c, p->in_bitem_begin, p->in_bitem_count, s);
-  p->last_launches = launches;
-  return cuda_check(cudaGetLastError(), "backprop launch");
+  return launches;
 }
 
 int grafx_backprop(grafx_plan* p, const float* sources, const float* d_out, float* const* d_params,
                    float* d_sources, void* stream) {
   if (!p) return fail(GRAFX_EINVAL, "null argument");
-  return grafx_backprop_steps(p, sources, d_out, d_params, d_sources, 0, int32_t(p->sched.string.size()), stream);
+  const int32_t end = int32_t(p->sched.string.size());
+  if (p->seg_ptr.empty()) return grafx_backprop_steps(p, sources, d_out, d_params, d_sources, 0, end, stream);
+  if (!sources || !d_out) return fail(GRAFX_EINVAL, "null argument");
+  int rc = check_ready(p);
+  if (rc) return rc;
+  // checkpointed: segments in reverse; every segment but the last (whose rows the
+  // forward pass left in place) is re-rendered before its backward steps
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nseg = int(p->seg_ptr.size()) - 1;
+  int launches = 0;
+  for (int j = nseg - 1; j >= 0; --j) {
+    const int32_t a = p->seg_ptr[j], b = p->seg_ptr[j + 1];
+    if (j < nseg - 1) launches += render_range(p, sources, nullptr, a, b, s);
+    launches += backprop_range(p, sources, d_out, d_params, d_sources, j == 0 ? 0 : a, b, s);
+  }
+  p->last_launches = launches;
+  return cuda_check(cudaGetLastError(), "checkpointed backprop launch");
 }
 
 int grafx_mrstft_forward(grafx_plan* p, const float* out, const float* target, float* loss, void* stream) {

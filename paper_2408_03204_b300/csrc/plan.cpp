@@ -5,6 +5,8 @@
 #include "fft.cuh"
 
 #include <algorithm>
+#include <functional>
+#include <map>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -212,7 +214,90 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
   // inside a step and the union concatenates graphs in order
   p->src_elems = src_off;
   p->out_elems = out_off;
-  const int64_t internal_floats = int_off;
+  const int64_t internal_floats = int_off;  // adjoint rows: one per internal node
+  // ---- signal checkpointing: with segments of opts.checkpoint_steps schedule steps,
+  // a U row is kept for the whole pass only if a consumer lies in a later segment
+  // (its forward value is needed when a later segment is recomputed or run); all other
+  // rows of a segment share one scratch region, reused by every segment.  The backward
+  // pass recomputes each earlier segment's forward before its own steps.
+  // ---- adjoint rows by liveness: a_w (the input adjoint of w) is written by the backward
+  // step of w and read by the backward steps of w's producers (step 0 = the source
+  // adjoints), so in backward order it lives over [N - step(w), N - min step(producer)].
+  // Rows of the same size whose intervals do not meet share memory (first free slot).
+  int64_t a_floats = 0;
+  {
+    std::vector<int32_t> step_of(n, 0);
+    for (int32_t st = 0; st <= N; ++st)
+      for (int32_t v = p->step_ptr[st]; v < p->step_ptr[st + 1]; ++v) step_of[v] = st;
+    struct Live { int32_t start, end, v; int64_t size; };
+    std::vector<Live> lives;
+    for (int32_t v = 0; v < n; ++v) {
+      if (p->nodes[v].kind != KIND_INTERNAL) continue;
+      int32_t lo = step_of[v];
+      for (int32_t e = p->csr_ptr[v]; e < p->csr_ptr[v + 1]; ++e) lo = std::min(lo, step_of[p->csr_src[e]]);
+      lives.push_back({N - step_of[v], N - lo, v, int64_t(align_up(size_t(2 * p->nodes[v].pitch), 64))});
+    }
+    std::stable_sort(lives.begin(), lives.end(), [](const Live& a, const Live& b) { return a.start < b.start; });
+    struct Pool { std::vector<int64_t> free_slots; std::vector<std::pair<int32_t, int64_t>> busy; };
+    std::map<int64_t, Pool> pools;
+    for (const Live& l : lives) {
+      Pool& pl = pools[l.size];
+      for (size_t i = 0; i < pl.busy.size();) {  // release slots whose interval ended
+        if (pl.busy[i].first < l.start) {
+          pl.free_slots.push_back(pl.busy[i].second);
+          pl.busy[i] = pl.busy.back();
+          pl.busy.pop_back();
+        } else {
+          ++i;
+        }
+      }
+      int64_t off;
+      if (!pl.free_slots.empty()) {
+        std::sort(pl.free_slots.begin(), pl.free_slots.end(), std::greater<int64_t>());
+        off = pl.free_slots.back();
+        pl.free_slots.pop_back();
+      } else {
+        off = a_floats;
+        a_floats += l.size;
+      }
+      p->nodes[l.v].off_a = off;
+      pl.busy.push_back({l.end, off});
+    }
+  }
+  int64_t u_floats = internal_floats;
+  p->ckpt_steps = opts.checkpoint_steps;
+  p->seg_ptr.clear();
+  if (opts.checkpoint_steps < 0) return fail(GRAFX_EINVAL, "checkpoint_steps must be >= 0");
+  if (opts.checkpoint_steps > 0) {
+    const int32_t k = opts.checkpoint_steps;
+    for (int32_t s0 = 1; s0 <= N; s0 += k) p->seg_ptr.push_back(s0);
+    p->seg_ptr.push_back(N + 1);
+    std::vector<int32_t> seg_of_node(n, -1);
+    for (int32_t st = 1; st <= N; ++st)
+      for (int32_t v = p->step_ptr[st]; v < p->step_ptr[st + 1]; ++v) seg_of_node[v] = (st - 1) / k;
+    std::vector<char> keep(n, 0);
+    for (int32_t v = 0; v < n; ++v) {
+      if (p->nodes[v].kind != KIND_INTERNAL) continue;
+      for (int32_t e = p->tcsr_ptr[v]; e < p->tcsr_ptr[v + 1]; ++e)
+        if (seg_of_node[p->tcsr_dst[e]] > seg_of_node[v]) keep[v] = 1;
+    }
+    int64_t kept = 0;
+    for (int32_t v = 0; v < n; ++v)
+      if (keep[v]) {
+        p->nodes[v].off_y = kept;
+        kept += int64_t(align_up(size_t(2 * p->nodes[v].pitch), 64));
+      }
+    int64_t scratch = 0, cur = 0;
+    int32_t cur_seg = -1;
+    for (int32_t v = 0; v < n; ++v) {  // new ids run step by step, so segment by segment
+      if (p->nodes[v].kind != KIND_INTERNAL || keep[v]) continue;
+      if (seg_of_node[v] != cur_seg) cur_seg = seg_of_node[v], cur = 0;
+      p->nodes[v].off_y = kept + cur;
+      cur += int64_t(align_up(size_t(2 * p->nodes[v].pitch), 64));
+      scratch = std::max(scratch, cur);
+    }
+    u_floats = kept + scratch;
+  }
 
   // ---- tile sizes
   p->eq_taps = opts.eq_taps;
@@ -491,8 +576,8 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
     w.loss_stats = take(32 * nrow * N_RES);
     w.loss_rowloss = take(4 * nrow);
     w.loss_frames = take(4 * size_t(std::max<int64_t>(p->loss.frame_floats, 1)));
-    w.U = take(4 * size_t(std::max<int64_t>(internal_floats, 1)));
-    w.A = take(4 * size_t(std::max<int64_t>(internal_floats, 1)));
+    w.U = take(4 * size_t(std::max<int64_t>(u_floats, 1)));
+    w.A = take(4 * size_t(std::max<int64_t>(a_floats, 1)));
     w.total = o;
   }
   return GRAFX_OK;

@@ -88,6 +88,8 @@ struct Plan {
   double dl_taylor[9] = {0};
   int32_t eq_taps = 1023, eq_H = 511, eq_fft = 4096, eq_step = 0;  // eq_step: outputs per block
   int32_t comp_chunk = 2048;
+  int32_t ckpt_steps = 0;                // signal checkpointing: steps per segment (0 = off)
+  std::vector<int32_t> seg_ptr;          // first step of each segment, then N + 1
   int64_t src_elems = 0, out_elems = 0, node_samples = 0;
   std::vector<int64_t> src_graph_off, out_graph_off;
   std::vector<int32_t> outputs_new;      // new ids of output rows in order

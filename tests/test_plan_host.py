@@ -135,3 +135,31 @@ def test_delay_and_reverb_length_limit(gx):
         with pytest.raises(gx.GrafxError) as e:
             gx.Plan([ok], [(1 << 19) + 1])
         assert e.value.name == "ESHAPE"
+
+
+def test_checkpointing_shrinks_the_workspace(gx):
+    g = _to_gx(gx, synth.console_cfg2())
+    row = 2 * (1 << 17) * 4
+    base = gx.Plan([g], [1 << 17]).info.ws_bytes
+    size = {k: gx.Plan([g], [1 << 17], checkpoint_steps=k).info.ws_bytes for k in (1, 2, 3, 100)}
+    # a consumer always runs in a later step: one-step segments keep every row, and one
+    # segment spanning the schedule holds every row in its scratch region
+    assert size[1] == base and size[100] == base
+    # cfg2's chains (g e c s g) cut into 2- or 3-step segments recycle one row per track
+    # and segment boundary crossed inside a segment: at least 64 rows fewer
+    assert size[2] < base - 64 * row and size[3] < base - 64 * row
+    with pytest.raises(gx.GrafxError):
+        gx.Plan([g], [4096], checkpoint_steps=-1)
+
+
+def test_adjoint_rows_are_recycled(gx):
+    """Adjoint rows live from their node's backward step to their producers' steps; the
+    chains of cfg2 need far fewer rows than one per internal node."""
+    cfg2 = synth.console_cfg2()
+    g = _to_gx(gx, cfg2)
+    L = 1 << 17
+    row = 2 * L * 4
+    internal = sum(1 for t in cfg2.types if t not in (synth.I, synth.O))
+    info = gx.Plan([g], [L]).info
+    # workspace = U (one row per internal node) + A + small tables; A < internal / 2 rows
+    assert info.ws_bytes < (internal + internal / 2) * row + 64 * 2 ** 20
