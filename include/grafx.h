@@ -338,9 +338,12 @@ int grafx_ws_mse(const float* out, const float* target, const int32_t* n_out, in
 /* The network's matrix product on its own: C = alpha A B + beta C over device float32
  * buffers with A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn], C row-major with
  * leading dimension ldc >= N; A and B are rounded to BF16 (nearest even) and the sums
- * accumulate in float32.  M <= 4194240.  Asynchronous on `stream`. */
+ * accumulate in float32.  M <= 8388480.  scratch (device, scratch_floats floats, may be
+ * NULL) lets a product with few output tiles split K over more CTAs: the partial tiles
+ * (M*N floats each) are summed in a fixed order afterwards.  Asynchronous on `stream`. */
 int grafx_gemm_bf16(int32_t M, int32_t N, int32_t K, const float* A, int64_t sam, int64_t sak, const float* B,
-                    int64_t sbk, int64_t sbn, float* C, int64_t ldc, float alpha, float beta, void* stream);
+                    int64_t sbk, int64_t sbn, float* C, int64_t ldc, float alpha, float beta, float* scratch,
+                    int64_t scratch_floats, void* stream);
 
 /* ---------------------------------------------------------------- allocation-free compressor
  * The paper has no counterpart to this call; it exists for callers that must not

@@ -97,7 +97,7 @@ SIGNATURES = {
     "grafx_ws_backward": (ctypes.c_int, [_P, _F, _F, _I32P, _I32, _F, _F, _P]),
     "grafx_ws_mse": (ctypes.c_int, [_F, _F, _P, _I32, _F, _F, _P]),
     "grafx_gemm_bf16": (ctypes.c_int, [_I32, _I32, _I32, _F, _I64, _I64, _F, _I64, _I64, _F, _I64, ctypes.c_float,
-                                       ctypes.c_float, _P]),
+                                       ctypes.c_float, _F, _I64, _P]),
 }
 
 
@@ -344,9 +344,10 @@ class WarmStartNet:
                                   stream))
 
 
-def gemm_bf16_raw(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta, stream):
+def gemm_bf16_raw(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta, stream, scratch=None):
     _check(lib().grafx_gemm_bf16(int(M), int(N), int(K), _ptr(A), int(sam), int(sak), _ptr(B), int(sbk), int(sbn),
-                                 _ptr(C), int(ldc), float(alpha), float(beta), stream))
+                                 _ptr(C), int(ldc), float(alpha), float(beta), _ptr(scratch),
+                                 0 if scratch is None else scratch.numel(), stream))
 
 
 class StepGraph:

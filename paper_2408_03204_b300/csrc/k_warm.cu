@@ -39,69 +39,143 @@ static const int kHeadOut[WS_NHEAD] = {2, 1, 8, 4, 176, 50};
 // ------------------------------------------------------------------ BF16 GEMM
 // C[M,N] = alpha * A B + beta * C with A(m, k) = A[m sam + k sak] and
 // B(k, n) = B[k sbk + n sbn] (FP32 in memory, BF16 in shared memory), C row-major (ldc).
-// 64x64 tile per CTA of 4 warps, each warp 32x32 = 2x4 m16n8k16 fragments.
-constexpr int GB_M = 64, GB_N = 64, GB_K = 32, GB_P = GB_K + 8;
+// CTA tile 128 x 128 x 32, 8 warps of 64 x 32 (4 x 4 m16n8k16 fragments).  The next
+// k-tile is loaded into registers while the current one is multiplied out of the other
+// shared-memory buffer (one barrier per k-tile).  Loads are float4 along whichever
+// dimension has unit stride when it is a multiple of 4 (mode VK: along k, VR: along the
+// row dimension m or n), else scalar (mode SC).  Split-K (gridDim.z > 1) writes partial
+// tiles to `part` [z][M][N], summed in z order by k_gemm_reduce (deterministic).
+constexpr int GB_M = 128, GB_N = 128, GB_K = 32, GB_P = GB_K + 8, GB_THREADS = 256;
+enum : int { LD_SC = 0, LD_VK = 1, LD_VR = 2 };
+
+struct GemmArgs {
+  int M, N, K, kchunk;
+  const float* A;
+  int64_t sam, sak;
+  const float* B;
+  int64_t sbk, sbn;
+  float* C;
+  int64_t ldc;
+  float alpha, beta;
+  float* part;  // split-K partials or null
+};
 
 __device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
-// stage a GB_R x GB_K tile of op(X) (row r, column kk) into S[r][kk]; the loop order
-// follows the unit-stride dimension so that global reads coalesce
-template <int GB_R>
-__device__ __forceinline__ void stage(__nv_bfloat16 (*S)[GB_P], const float* __restrict__ X, int64_t sr, int64_t sk,
-                                      int r0, int R, int k0, int K) {
-  if (sk == 1) {
-    for (int idx = threadIdx.x; idx < GB_R * GB_K; idx += blockDim.x) {
-      const int r = idx / GB_K, kk = idx % GB_K, m = r0 + r, k = k0 + kk;
-      S[r][kk] = __float2bfloat16_rn(m < R && k < K ? X[m * sr + k] : 0.f);
+// Registers of one 128 x 32 operand tile: 16 values per thread.
+// Operand X(r, k) = X[r sr + k sk], rows [r0, r0+128) of R, k in [k0, k0+32) of kend.
+template <int MODE>
+__device__ __forceinline__ void gload(float (&v)[16], const float* __restrict__ X, int64_t sr, int64_t sk, int r0,
+                                      int R, int k0, int kend) {
+  const int tid = threadIdx.x;
+  if constexpr (MODE == LD_VK) {  // float4 along k: 128 rows x 8 quads
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int f = tid + i * GB_THREADS, r = f >> 3, kq = (f & 7) * 4;
+      const int m = r0 + r, k = k0 + kq;
+      float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m < R && k < kend) q = __ldg(reinterpret_cast<const float4*>(X + m * sr + k));
+      v[4 * i] = q.x, v[4 * i + 1] = q.y, v[4 * i + 2] = q.z, v[4 * i + 3] = q.w;
     }
-  } else {
-    for (int idx = threadIdx.x; idx < GB_R * GB_K; idx += blockDim.x) {
-      const int kk = idx / GB_R, r = idx % GB_R, m = r0 + r, k = k0 + kk;
-      S[r][kk] = __float2bfloat16_rn(m < R && k < K ? X[m * sr + k * sk] : 0.f);
+  } else if constexpr (MODE == LD_VR) {  // float4 along the rows: 32 k x 32 quads
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int f = tid + i * GB_THREADS, kk = f >> 5, rq = (f & 31) * 4;
+      const int m = r0 + rq, k = k0 + kk;
+      float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m < R && k < kend) q = __ldg(reinterpret_cast<const float4*>(X + m + k * sk));
+      v[4 * i] = q.x, v[4 * i + 1] = q.y, v[4 * i + 2] = q.z, v[4 * i + 3] = q.w;
+    }
+  } else {  // scalar, k fastest (rows r = f / 32)
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int f = tid + i * GB_THREADS, r = f >> 5, kk = f & 31;
+      const int m = r0 + r, k = k0 + kk;
+      v[i] = (m < R && k < kend) ? X[m * sr + k * sk] : 0.f;
     }
   }
 }
 
-__global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const float* __restrict__ A, int64_t sam,
-                                                   int64_t sak, const float* __restrict__ B, int64_t sbk,
-                                                   int64_t sbn, float* __restrict__ C, int64_t ldc, float alpha,
-                                                   float beta) {
-  __shared__ __align__(16) __nv_bfloat16 As[GB_M][GB_P];
-  __shared__ __align__(16) __nv_bfloat16 Bs[GB_N][GB_P];
-  const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int g = lane >> 2, t = lane & 3;
-  float acc[2][4][4];
+template <int MODE>
+__device__ __forceinline__ void gstore(__nv_bfloat16 (*S)[GB_P], const float (&v)[16]) {
+  const int tid = threadIdx.x;
+  if constexpr (MODE == LD_VK) {
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 4; ++i) {
+      const int f = tid + i * GB_THREADS, r = f >> 3, kq = (f & 7) * 4;
+      __nv_bfloat162 lo = __floats2bfloat162_rn(v[4 * i], v[4 * i + 1]);
+      __nv_bfloat162 hi = __floats2bfloat162_rn(v[4 * i + 2], v[4 * i + 3]);
+      uint2 w;
+      w.x = *reinterpret_cast<uint32_t*>(&lo);
+      w.y = *reinterpret_cast<uint32_t*>(&hi);
+      *reinterpret_cast<uint2*>(&S[r][kq]) = w;
+    }
+  } else if constexpr (MODE == LD_VR) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int f = tid + i * GB_THREADS, kk = f >> 5, rq = (f & 31) * 4;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) S[rq + j][kk] = __float2bfloat16_rn(v[4 * i + j]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int f = tid + i * GB_THREADS, r = f >> 5, kk = f & 31;
+      S[r][kk] = __float2bfloat16_rn(v[i]);
+    }
+  }
+}
+
+template <int AM, int BM>
+__global__ void __launch_bounds__(GB_THREADS) k_gemm_bf16(GemmArgs g) {
+  __shared__ __align__(16) __nv_bfloat16 As[2][GB_M][GB_P];
+  __shared__ __align__(16) __nv_bfloat16 Bs[2][GB_N][GB_P];
+  const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
+  const int kbeg = blockIdx.z * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
+  const int gr = lane >> 2, t = lane & 3;
+  float acc[4][4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += GB_K) {
-    stage<GB_M>(As, A, sam, sak, m0, M, k0, K);
-    stage<GB_N>(Bs, B, sbn, sbk, n0, N, k0, K);
-    __syncthreads();
+  float va[16], vb[16];
+  int cur = 0;
+  if (kbeg < kend) {
+    gload<AM>(va, g.A, g.sam, g.sak, m0, g.M, kbeg, kend);
+    gload<BM>(vb, g.B, g.sbn, g.sbk, n0, g.N, kbeg, kend);
+    gstore<AM>(As[0], va);
+    gstore<BM>(Bs[0], vb);
+  }
+  __syncthreads();
+  for (int k0 = kbeg; k0 < kend; k0 += GB_K) {
+    const bool more = k0 + GB_K < kend;
+    if (more) {
+      gload<AM>(va, g.A, g.sam, g.sak, m0, g.M, k0 + GB_K, kend);
+      gload<BM>(vb, g.B, g.sbn, g.sbk, n0, g.N, k0 + GB_K, kend);
+    }
 #pragma unroll
     for (int kk = 0; kk < GB_K; kk += 16) {
-      uint32_t a[2][4], b[4][2];
+      uint32_t a[4][4], b[4][2];
 #pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + i * 16 + g;
-        a[i][0] = ld_pair(&As[r][kk + 2 * t]);
-        a[i][1] = ld_pair(&As[r + 8][kk + 2 * t]);
-        a[i][2] = ld_pair(&As[r][kk + 2 * t + 8]);
-        a[i][3] = ld_pair(&As[r + 8][kk + 2 * t + 8]);
+      for (int i = 0; i < 4; ++i) {
+        const int r = wm + i * 16 + gr;
+        a[i][0] = ld_pair(&As[cur][r][kk + 2 * t]);
+        a[i][1] = ld_pair(&As[cur][r + 8][kk + 2 * t]);
+        a[i][2] = ld_pair(&As[cur][r][kk + 2 * t + 8]);
+        a[i][3] = ld_pair(&As[cur][r + 8][kk + 2 * t + 8]);
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int c = wn + j * 8 + g;
-        b[j][0] = ld_pair(&Bs[c][kk + 2 * t]);
-        b[j][1] = ld_pair(&Bs[c][kk + 2 * t + 8]);
+        const int c = wn + j * 8 + gr;
+        b[j][0] = ld_pair(&Bs[cur][c][kk + 2 * t]);
+        b[j][1] = ld_pair(&Bs[cur][c][kk + 2 * t + 8]);
       }
 #pragma unroll
-      for (int i = 0; i < 2; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           asm volatile(
@@ -110,28 +184,92 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const fl
               : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
               : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
     }
+    if (more) {
+      gstore<AM>(As[cur ^ 1], va);
+      gstore<BM>(Bs[cur ^ 1], vb);
+    }
     __syncthreads();
+    cur ^= 1;
   }
+  float* part = g.part ? g.part + int64_t(blockIdx.z) * g.M * g.N : nullptr;
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const int m = m0 + wm + i * 16 + g + (r >= 2 ? 8 : 0);
+        const int m = m0 + wm + i * 16 + gr + (r >= 2 ? 8 : 0);
         const int n = n0 + wn + j * 8 + 2 * t + (r & 1);
-        if (m < M && n < N) {
-          float* cp = C + m * ldc + n;
-          *cp = alpha * acc[i][j][r] + (beta != 0.f ? beta * *cp : 0.f);
+        if (m < g.M && n < g.N) {
+          if (part) {
+            part[int64_t(m) * g.N + n] = acc[i][j][r];
+          } else {
+            float* cp = g.C + m * g.ldc + n;
+            *cp = g.alpha * acc[i][j][r] + (g.beta != 0.f ? g.beta * *cp : 0.f);
+          }
         }
       }
 }
 
+// C = alpha * sum_z part[z] + beta * C, z in order
+__global__ void k_gemm_reduce(const float* __restrict__ part, int splits, int M, int N, float* __restrict__ C,
+                              int64_t ldc, float alpha, float beta) {
+  const int64_t MN = int64_t(M) * N;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < MN; i += int64_t(gridDim.x) * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += part[z * MN + i];
+    float* cp = C + (i / N) * ldc + i % N;
+    *cp = alpha * s + (beta != 0.f ? beta * *cp : 0.f);
+  }
+}
+
+// Load mode of an operand X(r, k) = X[r sr + k sk] with R rows and K columns.
+static int load_mode(const float* X, int64_t sr, int64_t sk, int R, int K) {
+  const bool al = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  if (al && sk == 1 && sr % 4 == 0 && K % 4 == 0) return LD_VK;
+  if (al && sr == 1 && sk % 4 == 0 && R % 4 == 0) return LD_VR;
+  return LD_SC;
+}
+
+template <int AM>
+static void launch_gemm_b(int bm, dim3 grid, const GemmArgs& a, cudaStream_t s) {
+  switch (bm) {
+    case LD_VK: k_gemm_bf16<AM, LD_VK><<<grid, GB_THREADS, 0, s>>>(a); break;
+    case LD_VR: k_gemm_bf16<AM, LD_VR><<<grid, GB_THREADS, 0, s>>>(a); break;
+    default: k_gemm_bf16<AM, LD_SC><<<grid, GB_THREADS, 0, s>>>(a);
+  }
+}
+
+// scratch: optional float buffer for split-K partials (scratch_floats capacity).
 static void gemm(int M, int N, int K, const float* A, int64_t sam, int64_t sak, const float* B, int64_t sbk,
-                 int64_t sbn, float* C, int64_t ldc, float alpha, float beta, cudaStream_t s) {
+                 int64_t sbn, float* C, int64_t ldc, float alpha, float beta, cudaStream_t s,
+                 float* scratch = nullptr, int64_t scratch_floats = 0) {
   if (M <= 0 || N <= 0) return;
-  dim3 grid((N + GB_N - 1) / GB_N, (M + GB_M - 1) / GB_M);
-  k_gemm_bf16<<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta);
+  GemmArgs a{M, N, K, 0, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta, nullptr};
+  const int tm = (M + GB_M - 1) / GB_M, tn = (N + GB_N - 1) / GB_N;
+  const int ktiles = std::max(1, (K + GB_K - 1) / GB_K);
+  int splits = 1;
+  if (scratch && tm * tn < 2 * 148 && ktiles >= 8) {
+    splits = std::min((2 * 148 + tm * tn - 1) / (tm * tn), ktiles / 4);
+    splits = int(std::min<int64_t>(splits, scratch_floats / (int64_t(M) * N)));
+    splits = std::max(splits, 1);
+  }
+  const int kt_per = (ktiles + splits - 1) / splits;
+  a.kchunk = kt_per * GB_K;
+  splits = (ktiles + kt_per - 1) / kt_per;
+  if (splits > 1) a.part = scratch;
+  dim3 grid(tn, tm, splits);
+  const int am = load_mode(A, sam, sak, M, K), bm = load_mode(B, sbn, sbk, N, K);
+  switch (am) {
+    case LD_VK: launch_gemm_b<LD_VK>(bm, grid, a, s); break;
+    case LD_VR: launch_gemm_b<LD_VR>(bm, grid, a, s); break;
+    default: launch_gemm_b<LD_SC>(bm, grid, a, s);
+  }
+  if (splits > 1) {
+    const int64_t MN = int64_t(M) * N;
+    k_gemm_reduce<<<int(std::min<int64_t>((MN + 255) / 256, 148 * 8)), 256, 0, s>>>(scratch, splits, M, N, C, ldc,
+                                                                                     alpha, beta);
+  }
 }
 
 // ------------------------------------------------------------------ elementwise pieces
@@ -537,12 +675,14 @@ int grafx_ws_forward(grafx_wsnet* n, const float* weights, const float* feats, c
   auto F = [&](size_t off) { return reinterpret_cast<float*>(n->ws + off); };
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int rows = B * WS_T;
+  const int64_t dbig_floats = int64_t(n->max_batch) * WS_T * WS_CH * WS_KW;
   const int cin[4] = {WS_IN, WS_CH, WS_CH, WS_CH};
   for (int l = 0; l < 4; ++l) {
     const float* src = l == 0 ? feats : F(L.h[l - 1]);
     const int K = cin[l] * WS_KW;
     k_im2col<<<grid1(int64_t(rows) * K), 256, 0, s>>>(src, B, cin[l], l == 0, F(L.im2col));
-    gemm(rows, WS_CH, K, F(L.im2col), K, 1, weights + n->off[l][0], 1, K, F(L.z[l]), WS_CH, 1.f, 0.f, s);
+    gemm(rows, WS_CH, K, F(L.im2col), K, 1, weights + n->off[l][0], 1, K, F(L.z[l]), WS_CH, 1.f, 0.f, s,
+         F(L.dbig), dbig_floats);
     k_bias_act<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(F(L.z[l]), weights + n->off[l][1], F(L.h[l]), rows, WS_CH,
                                                               WS_CH, 1);
   }
@@ -608,6 +748,7 @@ int grafx_ws_backward(grafx_wsnet* n, const float* weights, const float* feats, 
     r0 += nb;
   }
   const int rows = B * WS_T;
+  const int64_t dbig_floats = int64_t(n->max_batch) * WS_T * WS_CH * WS_KW;
   k_time_mean_bwd<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(de, B, dh);
   const int cin[4] = {WS_IN, WS_CH, WS_CH, WS_CH};
   for (int l = 3; l >= 0; --l) {
@@ -616,7 +757,8 @@ int grafx_ws_backward(grafx_wsnet* n, const float* weights, const float* feats, 
     k_gelu_bwd<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(dh, F(L.z[l]), int64_t(rows) * WS_CH);
     const float* src = l == 0 ? feats : F(L.h[l - 1]);
     k_im2col<<<grid1(int64_t(rows) * K), 256, 0, s>>>(src, B, cin[l], l == 0, F(L.im2col));
-    gemm(WS_CH, K, rows, dh, 1, WS_CH, F(L.im2col), K, 1, d_weights + n->off[l][0], K, 1.f, 0.f, s);
+    gemm(WS_CH, K, rows, dh, 1, WS_CH, F(L.im2col), K, 1, d_weights + n->off[l][0], K, 1.f, 0.f, s, F(L.dbig),
+         dbig_floats);
     k_colsum<<<WS_CH / 32, 1024, 0, s>>>(dh, rows, WS_CH, WS_CH, d_weights + n->off[l][1]);
     if (l > 0) {
       // d im2col = dz W, then its adjoint scatter gives dh of the previous layer
@@ -636,10 +778,13 @@ int grafx_ws_mse(const float* out, const float* target, const int32_t* n_out, in
 }
 
 int grafx_gemm_bf16(int32_t M, int32_t N, int32_t K, const float* A, int64_t sam, int64_t sak, const float* B,
-                    int64_t sbk, int64_t sbn, float* C, int64_t ldc, float alpha, float beta, void* stream) {
+                    int64_t sbk, int64_t sbn, float* C, int64_t ldc, float alpha, float beta, float* scratch,
+                    int64_t scratch_floats, void* stream) {
   if (!A || !B || !C) return fail(GRAFX_EINVAL, "null argument");
-  if (M < 0 || N < 0 || K < 0 || ldc < N || M > 65535 * GB_M) return fail(GRAFX_ESHAPE, "bad GEMM shape");
-  gemm(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta, static_cast<cudaStream_t>(stream));
+  if (M < 0 || N < 0 || K < 0 || ldc < N || M > 65535 * GB_M || scratch_floats < 0)
+    return fail(GRAFX_ESHAPE, "bad GEMM shape");
+  gemm(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta, static_cast<cudaStream_t>(stream), scratch,
+       scratch ? scratch_floats : 0);
   return cuda_status();
 }
 

@@ -38,9 +38,11 @@ def _bf16_gemm_ref(A, B):
     return Ar @ Br, np.abs(Ar) @ np.abs(Br)
 
 
-@pytest.mark.parametrize("M,N,K,ta,tb", [(1, 1, 1, 0, 0), (70, 130, 45, 0, 0), (64, 64, 32, 1, 0),
-                                         (129, 65, 1280, 0, 1), (200, 288, 3, 1, 1), (5, 176, 288, 0, 1)])
-def test_gemm_bf16_matches_rounded_product(env, M, N, K, ta, tb):
+@pytest.mark.parametrize("M,N,K,ta,tb,split", [(1, 1, 1, 0, 0, 0), (70, 130, 45, 0, 0, 0), (64, 64, 32, 1, 0, 0),
+                                               (129, 65, 1280, 0, 1, 0), (200, 288, 3, 1, 1, 0),
+                                               (5, 176, 288, 0, 1, 0), (128, 640, 4096, 1, 0, 1),
+                                               (130, 260, 2000, 1, 1, 1), (257, 129, 999, 0, 0, 1)])
+def test_gemm_bf16_matches_rounded_product(env, M, N, K, ta, tb, split):
     gx, torch = env
     rng = np.random.Generator(np.random.PCG64(M * 1000 + N + K))
     A = rng.standard_normal((M, K)).astype(np.float32)
@@ -52,7 +54,8 @@ def test_gemm_bf16_matches_rounded_product(env, M, N, K, ta, tb):
     sam, sak = (1, M) if ta else (K, 1)
     sbk, sbn = (1, K) if tb else (N, 1)
     C = torch.tensor(C0, device="cuda")
-    gx.gemm_bf16_raw(M, N, K, Ad, sam, sak, Bd, sbk, sbn, C, N, 0.5, 2.0, gx._stream(torch, C.device))
+    scratch = torch.empty(64 * M * N, device="cuda") if split else None
+    gx.gemm_bf16_raw(M, N, K, Ad, sam, sak, Bd, sbk, sbn, C, N, 0.5, 2.0, gx._stream(torch, C.device), scratch)
     torch.cuda.synchronize()
     want, mag = _bf16_gemm_ref(A, B)
     want = 0.5 * want + 2.0 * C0.astype(np.float64)
