@@ -266,6 +266,12 @@ int grafx_step_graph_destroy(grafx_step_graph* g);
 int grafx_adam_step(float* theta, float* m, float* v, const float* grad_param, float* param,
                     const int8_t* codes, int32_t cols, int64_t n, int32_t step, float lr, float beta1,
                     float beta2, float eps, void* stream);
+/* grafx_adam_step with the step number read from device memory (*step, int32, >= 1;
+ * values below 1 count as 1), so that a captured fit step can advance its own counter.
+ * The bias corrections are computed in double precision like grafx_adam_step's. */
+int grafx_adam_step_dev(float* theta, float* m, float* v, const float* grad_param, float* param,
+                        const int8_t* codes, int32_t cols, int64_t n, const int32_t* step, float lr, float beta1,
+                        float beta2, float eps, void* stream);
 /* theta = inverse map of param (to start a fit from physical parameters). */
 int grafx_params_to_theta(const float* param, const int8_t* codes, int32_t cols, int64_t n, float* theta,
                           void* stream);

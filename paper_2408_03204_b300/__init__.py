@@ -81,6 +81,8 @@ SIGNATURES = {
     "grafx_adam_step": (ctypes.c_int, [_F, _F, _F, _F, _F, _P, _I32, _I64, _I32, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_float, ctypes.c_float, _P]),
     "grafx_params_to_theta": (ctypes.c_int, [_F, _P, _I32, _I64, _F, _P]),
+    "grafx_adam_step_dev": (ctypes.c_int, [_F, _F, _F, _F, _F, _P, _I32, _I64, _P, ctypes.c_float, ctypes.c_float,
+                                           ctypes.c_float, ctypes.c_float, _P]),
     "grafx_step_graph_create": (ctypes.c_int, [_P, _F, _F, _F, _F, _F, ctypes.POINTER(_P), _F, _P,
                                                ctypes.POINTER(_P)]),
     "grafx_step_graph_launch": (ctypes.c_int, [_P, _P]),

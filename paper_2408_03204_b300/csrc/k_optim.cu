@@ -67,6 +67,34 @@ __global__ void k_adam(float* __restrict__ theta, float* __restrict__ m, float* 
   }
 }
 
+// Same update with the step number read from device memory (for a captured fit step
+// whose step counter advances on the device); bias corrections in double once per block.
+__global__ void k_adam_dev(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
+                           const float* __restrict__ gp, float* __restrict__ p, const int8_t* __restrict__ codes,
+                           int cols, int64_t n, float lr, float b1, float b2, float eps,
+                           const int32_t* __restrict__ step) {
+  __shared__ float bc[2];
+  if (threadIdx.x == 0) {
+    const int st = max(*step, 1);
+    bc[0] = float(1.0 - pow(double(b1), double(st)));
+    bc[1] = float(1.0 - pow(double(b2), double(st)));
+  }
+  __syncthreads();
+  const float bc1 = bc[0], bc2 = bc[1];
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int code = codes[i % cols];
+    const float th = theta[i];
+    const float g = gp[i] * map_slope(th, code);
+    const float mi = b1 * m[i] + (1.f - b1) * g;
+    const float vi = b2 * v[i] + (1.f - b2) * g * g;
+    const float nt = th - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    m[i] = mi;
+    v[i] = vi;
+    theta[i] = nt;
+    p[i] = map_param(nt, code);
+  }
+}
+
 __global__ void k_to_theta(const float* __restrict__ p, const int8_t* __restrict__ codes, int cols, int64_t n,
                            float* __restrict__ theta) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
@@ -88,6 +116,19 @@ extern "C" int grafx_adam_step(float* theta, float* m, float* v, const float* gr
   const int g = int(std::min<int64_t>((n + 255) / 256, 148 * 8));
   k_adam<<<g, 256, 0, static_cast<cudaStream_t>(stream)>>>(theta, m, v, grad_param, param, codes, cols, n, lr,
                                                             beta1, beta2, eps, bc1, bc2);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GRAFX_OK : fail(GRAFX_ECUDA, cudaGetErrorString(e));
+}
+
+extern "C" int grafx_adam_step_dev(float* theta, float* m, float* v, const float* grad_param, float* param,
+                                   const int8_t* codes, int32_t cols, int64_t n, const int32_t* step, float lr,
+                                   float beta1, float beta2, float eps, void* stream) {
+  if (!theta || !m || !v || !grad_param || !param || !codes || !step) return fail(GRAFX_EINVAL, "null argument");
+  if (n < 0 || cols < 1) return fail(GRAFX_EINVAL, "need n >= 0, cols >= 1");
+  if (n == 0) return GRAFX_OK;
+  const int g = int(std::min<int64_t>((n + 255) / 256, 148 * 8));
+  k_adam_dev<<<g, 256, 0, static_cast<cudaStream_t>(stream)>>>(theta, m, v, grad_param, param, codes, cols, n, lr,
+                                                                beta1, beta2, eps, step);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GRAFX_OK : fail(GRAFX_ECUDA, cudaGetErrorString(e));
 }

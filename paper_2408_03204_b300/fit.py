@@ -1,7 +1,7 @@
 """Gradient-descent fit of every processor parameter of a plan to a target mix (the
 paper's example application, Sec. 4): render, MRSTFT loss, loss gradient, backprop and
-a fused Adam step per type, all through the C-ABI library on one stream.  The render,
-loss and backprop of a step can be replayed as one captured CUDA graph.
+a fused Adam step per type, all through the C-ABI library on one stream.  A whole step
+(Adam included, its step counter on the device) can be replayed as one CUDA graph.
 
 Unconstrained variables theta map to the processors' parameters column by column
 (grafx_adam_step codes): compressor [alpha, T, W, R] -> [alpha map, identity, softplus,
@@ -86,12 +86,18 @@ class Fit:
             self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
         if theta0 is not None:
             self._apply_map()
+        with torch.cuda.stream(self.stream):
+            self.step_dev = torch.zeros(1, dtype=torch.int32, device=dev)
         self.t = 0
         self.graph = None
         if use_graph:
+            # the whole step (render, loss, loss gradient, backprop, step counter, Adam of
+            # every type) as one CUDA graph replayed with a single launch
             self.stream.synchronize()
-            self.graph = plan.capture_step(self.src, self.out, self.tgt, self.loss, self.d_out, self.g, None,
-                                           self.st)
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph, stream=self.stream):
+                self._body()
+            self.stream.synchronize()
 
     def _apply_map(self):
         # param = map(theta) via a zero-learning-rate Adam step on zero gradients
@@ -104,21 +110,28 @@ class Fit:
                                          ctypes.c_float(self.eps), self.st))
             self.stream.synchronize()
 
-    def step(self):
-        """One fit step (loss of the current parameters, then the Adam update)."""
-        self.t += 1
-        if self.graph is not None:
-            self.graph.launch(self.st)
-        else:
-            self.plan.render_raw(self.src, self.out, self.st)
-            self.plan.loss_raw(self.out, self.tgt, self.loss, self.st)
-            self.plan.loss_backward_raw(self.out, self.tgt, self.d_out, self.st)
-            self.plan.backprop_raw(self.src, self.d_out, self.g, None, self.st)
+    def _body(self):
+        st = _stream_of(self.torch.cuda.current_stream(self.src.device))
+        self.plan.render_raw(self.src, self.out, st)
+        self.plan.loss_raw(self.out, self.tgt, self.loss, st)
+        self.plan.loss_backward_raw(self.out, self.tgt, self.d_out, st)
+        self.plan.backprop_raw(self.src, self.d_out, self.g, None, st)
+        self.step_dev.add_(1)
         for t, p in self.P.items():
-            _check(lib().grafx_adam_step(_ptr(self.theta[t]), _ptr(self.m[t]), _ptr(self.v[t]), _ptr(self.g[t]),
-                                         _ptr(p), _ptr(self.codes[t]), p.shape[1], p.numel(), self.t,
-                                         ctypes.c_float(self.lr), ctypes.c_float(self.b1), ctypes.c_float(self.b2),
-                                         ctypes.c_float(self.eps), self.st))
+            _check(lib().grafx_adam_step_dev(_ptr(self.theta[t]), _ptr(self.m[t]), _ptr(self.v[t]), _ptr(self.g[t]),
+                                             _ptr(p), _ptr(self.codes[t]), p.shape[1], p.numel(), _ptr(self.step_dev),
+                                             ctypes.c_float(self.lr), ctypes.c_float(self.b1),
+                                             ctypes.c_float(self.b2), ctypes.c_float(self.eps), st))
+
+    def step(self):
+        """One fit step (loss of the current parameters, then the Adam update), queued on
+        the fit's stream."""
+        self.t += 1
+        with self.torch.cuda.stream(self.stream):
+            if self.graph is not None:
+                self.graph.replay()
+            else:
+                self._body()
 
     def current_loss(self):
         """Loss of the parameters before the last step (synchronises the stream)."""
@@ -131,3 +144,66 @@ class Fit:
         self.plan.loss_raw(self.out, self.tgt, self.loss, self.st)
         self.stream.synchronize()
         return float(self.loss.item())
+
+
+def main():
+    """Fit of a random console with every processor type (reverb included) to a target
+    rendered from hidden parameters; prints one JSON line with the time per step, the
+    total time and the loss curve summary.
+
+        python -m paper_2408_03204_b300.fit --budget 200 --length 262144 --steps 1000
+    """
+    import argparse
+    import json
+
+    import numpy as np
+    import torch
+
+    import synth
+    from . import Graph, Plan
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--budget", type=int, default=200)
+    ap.add_argument("--length", type=int, default=2 ** 18)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--lr", type=float, default=1e-2)
+    ap.add_argument("--checkpoint-steps", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=4)
+    args = ap.parse_args()
+    g = synth.console_all_types(args.seed, args.budget)
+    L = args.length
+    dev = torch.device("cuda")
+    plan = Plan([Graph.from_lists(g.types, g.edges)], [L], checkpoint_steps=args.checkpoint_steps)
+    ws_plain = Plan([Graph.from_lists(g.types, g.edges)], [L]).info.ws_bytes
+    plan.bind_workspace(dev)
+    noise = torch.tensor(synth.reverb_noise(), device=dev).contiguous()
+    plan.bind_reverb_noise(noise)
+    P = (L + 3) // 4 * 4
+    src = torch.tensor(synth.sources(args.seed, g.count(synth.I), L, pitch=P).reshape(-1), device=dev)
+    hidden = {t: torch.tensor(a, device=dev).contiguous() for t, a in synth.random_params(g, 100 + args.seed).items()}
+    target = torch.empty(plan.info.out_elems, device=dev)
+    plan.bind_params(hidden)
+    plan.render_raw(src, target, _stream_of(torch.cuda.current_stream(dev)))
+    f = Fit(plan, src, target, neutral_params(plan, torch, dev), lr=args.lr)
+    hist = torch.zeros(args.steps, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(f.stream):
+        e0.record(f.stream)
+        for i in range(args.steps):
+            f.step()
+            hist[i:i + 1].copy_(f.loss)
+        e1.record(f.stream)
+    f.stream.synchronize()
+    plan.sync_status(f.st)
+    h = hist.cpu().numpy()
+    ms = e0.elapsed_time(e1)
+    print(json.dumps(dict(nodes=g.n_nodes, types="".join("iomgsecdr"[t] for t in sorted(set(g.types))), length=L,
+                          steps=args.steps, lr=args.lr, checkpoint_steps=args.checkpoint_steps,
+                          ws_bytes=int(plan.info.ws_bytes), ws_bytes_without_checkpointing=int(ws_plain),
+                          ms_per_step=ms / args.steps, total_s=ms / 1e3, loss_first=float(h[0]),
+                          loss_at=[float(h[min(k, args.steps - 1)]) for k in (10, 100, 200, 500, 999)],
+                          loss_final=float(h[-1]), loss_min=float(np.min(h)), gpu=torch.cuda.get_device_name())))
+
+
+if __name__ == "__main__":
+    main()
