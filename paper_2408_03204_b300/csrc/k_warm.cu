@@ -279,18 +279,20 @@ __device__ __forceinline__ float gelu_d(float x) {
 }
 
 // im2col: A[(b,t)][(c,k)] = H(b, c, t+k-2), zero outside [0, T).  H is [B][T][C]
-// (time-major activations) or, for the features, [B][C][T] (feat_layout = 1).
+// (time-major activations) or, for the features, [B][C][T] (feat_layout = 1).  One
+// thread per (b, t, c) writes its 5 taps.
 __global__ void k_im2col(const float* __restrict__ H, int B, int C, int feat_layout, float* __restrict__ A) {
-  const int64_t n = int64_t(B) * WS_T * C * WS_KW;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const int k = int(i % WS_KW), c = int((i / WS_KW) % C);
-    const int64_t bt = i / (int64_t(WS_KW) * C);
-    const int t = int(bt % WS_T), b = int(bt / WS_T);
-    const int ts = t + k - 2;
-    float v = 0.f;
-    if (ts >= 0 && ts < WS_T)
-      v = feat_layout ? H[(int64_t(b) * C + c) * WS_T + ts] : H[(int64_t(b) * WS_T + ts) * C + c];
-    A[i] = v;
+  const int n = B * WS_T * C;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int c = i % C, bt = i / C, t = bt % WS_T, b = bt / WS_T;
+    float* o = A + int64_t(i) * WS_KW;
+#pragma unroll
+    for (int k = 0; k < WS_KW; ++k) {
+      const int ts = t + k - 2;
+      float v = 0.f;
+      if (ts >= 0 && ts < WS_T) v = feat_layout ? H[(b * C + c) * WS_T + ts] : H[(b * WS_T + ts) * C + c];
+      o[k] = v;
+    }
   }
 }
 
@@ -329,23 +331,41 @@ __global__ void k_gelu_bwd(float* __restrict__ d, const float* __restrict__ z, i
     d[i] *= gelu_d(z[i]);
 }
 
-// out[c] = sum_r x[r ld + c] for c < cols (bias gradients).  Block: 32 columns x 32 row
-// slices; each slice sums rows slice, slice+32, ..., then a fixed-order tree (deterministic).
+// Column sums out[c] = sum_r x[r ld + c], c < cols (bias gradients), in two
+// deterministic stages: CTA (cx, ry) sums rows ry, ry + 32 * gridDim.y, ... of its 32
+// columns with 32 row slices and a fixed-order tree into part[ry][c]; then
+// k_colsum_final adds the gridDim.y partials in order.
+constexpr int CS_SPLIT = 64;
 __global__ void __launch_bounds__(1024) k_colsum(const float* __restrict__ x, int64_t rows, int cols, int64_t ld,
-                                                 float* __restrict__ out) {
+                                                 float* __restrict__ part) {
   __shared__ float red[32][33];
   const int cx = threadIdx.x & 31, sl = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + cx;
+  const int64_t stride = 32 * int64_t(gridDim.y);
   float s = 0.f;
   if (c < cols)
-    for (int64_t r = sl; r < rows; r += 32) s += x[r * ld + c];
+    for (int64_t r = int64_t(blockIdx.y) * 32 + sl; r < rows; r += stride) s += x[r * ld + c];
   red[sl][cx] = s;
   __syncthreads();
   for (int w = 16; w > 0; w >>= 1) {
     if (sl < w) red[sl][cx] += red[sl + w][cx];
     __syncthreads();
   }
-  if (sl == 0 && c < cols) out[c] = red[0][cx];
+  if (sl == 0 && c < cols) part[int64_t(blockIdx.y) * cols + c] = red[0][cx];
+}
+
+__global__ void k_colsum_final(const float* __restrict__ part, int splits, int cols, float* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  float s = 0.f;
+  for (int z = 0; z < splits; ++z) s += part[z * cols + c];
+  out[c] = s;
+}
+
+static void colsum(const float* x, int64_t rows, int cols, int64_t ld, float* out, float* part, cudaStream_t s) {
+  const int splits = int(std::min<int64_t>(CS_SPLIT, std::max<int64_t>(1, rows / 256)));
+  k_colsum<<<dim3((cols + 31) / 32, splits), 1024, 0, s>>>(x, rows, cols, ld, part);
+  k_colsum_final<<<(cols + 127) / 128, 128, 0, s>>>(part, splits, cols, out);
 }
 
 __global__ void k_time_mean(const float* __restrict__ h, int B, float* __restrict__ e) {
@@ -497,7 +517,7 @@ namespace {
 
 struct WsNetLayout {
   size_t melw, melrng, tw, ptw;
-  size_t im2col, z[4], h[4], e, a1, g1, a2, g2, dbig, dsmall, dh, frames, total;
+  size_t im2col, z[4], h[4], e, a1, g1, a2, g2, dbig, dsmall, dh, cspart, frames, total;
 };
 
 // frame_floats: log-mel frame scratch (rows x frames x 128) in floats
@@ -527,6 +547,7 @@ WsNetLayout ws_layout(const grafx_wsnet* n, int64_t frame_floats) {
   L.dbig = take(4 * rows * WS_CH * WS_KW);
   L.dsmall = take(4 * B * WS_HID * 2);
   L.dh = take(4 * (B * WS_CH + rows * WS_CH));
+  L.cspart = take(4 * size_t(CS_SPLIT) * WS_HID);
   L.frames = take(4 * size_t(std::max<int64_t>(frame_floats, 1)));
   L.total = o;
   return L;
@@ -680,7 +701,7 @@ int grafx_ws_forward(grafx_wsnet* n, const float* weights, const float* feats, c
   for (int l = 0; l < 4; ++l) {
     const float* src = l == 0 ? feats : F(L.h[l - 1]);
     const int K = cin[l] * WS_KW;
-    k_im2col<<<grid1(int64_t(rows) * K), 256, 0, s>>>(src, B, cin[l], l == 0, F(L.im2col));
+    k_im2col<<<grid1(int64_t(rows) * cin[l]), 256, 0, s>>>(src, B, cin[l], l == 0, F(L.im2col));
     gemm(rows, WS_CH, K, F(L.im2col), K, 1, weights + n->off[l][0], 1, K, F(L.z[l]), WS_CH, 1.f, 0.f, s,
          F(L.dbig), dbig_floats);
     k_bias_act<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(F(L.z[l]), weights + n->off[l][1], F(L.h[l]), rows, WS_CH,
@@ -733,17 +754,17 @@ int grafx_ws_backward(grafx_wsnet* n, const float* weights, const float* feats, 
     const float *a2 = F(L.a2) + r0 * WS_HID, *g2 = F(L.g2) + r0 * WS_HID;
     // dW3 = dO^T g2, db3 = column sums of dO, da2 = (dO W3) gelu'(a2)
     gemm(no, WS_HID, nb, dO, 1, WS_OUTMAX, g2, WS_HID, 1, d_weights + o[4], WS_HID, 1.f, 0.f, s);
-    k_colsum<<<(no + 31) / 32, 1024, 0, s>>>(dO, nb, no, WS_OUTMAX, d_weights + o[5]);
+    colsum(dO, nb, no, WS_OUTMAX, d_weights + o[5], F(L.cspart), s);
     gemm(nb, WS_HID, no, dO, WS_OUTMAX, 1, weights + o[4], WS_HID, 1, da2, WS_HID, 1.f, 0.f, s);
     k_gelu_bwd<<<grid1(int64_t(nb) * WS_HID), 256, 0, s>>>(da2, a2, int64_t(nb) * WS_HID);
     // dW2 = da2^T g1, db2, da1 = (da2 W2) gelu'(a1)
     gemm(WS_HID, WS_HID, nb, da2, 1, WS_HID, g1, WS_HID, 1, d_weights + o[2], WS_HID, 1.f, 0.f, s);
-    k_colsum<<<(WS_HID + 31) / 32, 1024, 0, s>>>(da2, nb, WS_HID, WS_HID, d_weights + o[3]);
+    colsum(da2, nb, WS_HID, WS_HID, d_weights + o[3], F(L.cspart), s);
     gemm(nb, WS_HID, WS_HID, da2, WS_HID, 1, weights + o[2], WS_HID, 1, da1, WS_HID, 1.f, 0.f, s);
     k_gelu_bwd<<<grid1(int64_t(nb) * WS_HID), 256, 0, s>>>(da1, a1, int64_t(nb) * WS_HID);
     // dW1 = da1^T e, db1, de = da1 W1
     gemm(WS_HID, WS_CH, nb, da1, 1, WS_HID, F(L.e) + r0 * WS_CH, WS_CH, 1, d_weights + o[0], WS_CH, 1.f, 0.f, s);
-    k_colsum<<<(WS_HID + 31) / 32, 1024, 0, s>>>(da1, nb, WS_HID, WS_HID, d_weights + o[1]);
+    colsum(da1, nb, WS_HID, WS_HID, d_weights + o[1], F(L.cspart), s);
     gemm(nb, WS_CH, WS_HID, da1, WS_HID, 1, weights + o[0], WS_CH, 1, de + r0 * WS_CH, WS_CH, 1.f, 0.f, s);
     r0 += nb;
   }
@@ -756,10 +777,10 @@ int grafx_ws_backward(grafx_wsnet* n, const float* weights, const float* feats, 
     // dz = dh gelu'(z); dW = dz^T im2col(input); db = column sums of dz
     k_gelu_bwd<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(dh, F(L.z[l]), int64_t(rows) * WS_CH);
     const float* src = l == 0 ? feats : F(L.h[l - 1]);
-    k_im2col<<<grid1(int64_t(rows) * K), 256, 0, s>>>(src, B, cin[l], l == 0, F(L.im2col));
+    k_im2col<<<grid1(int64_t(rows) * cin[l]), 256, 0, s>>>(src, B, cin[l], l == 0, F(L.im2col));
     gemm(WS_CH, K, rows, dh, 1, WS_CH, F(L.im2col), K, 1, d_weights + n->off[l][0], K, 1.f, 0.f, s, F(L.dbig),
          dbig_floats);
-    k_colsum<<<WS_CH / 32, 1024, 0, s>>>(dh, rows, WS_CH, WS_CH, d_weights + n->off[l][1]);
+    colsum(dh, rows, WS_CH, WS_CH, d_weights + n->off[l][1], F(L.cspart), s);
     if (l > 0) {
       // d im2col = dz W, then its adjoint scatter gives dh of the previous layer
       gemm(rows, K, WS_CH, dh, WS_CH, 1, weights + n->off[l][0], K, 1, F(L.dbig), K, 1.f, 0.f, s);

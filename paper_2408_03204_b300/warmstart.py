@@ -364,6 +364,34 @@ def evaluate(ws, graph_lists, L, seed, plain_steps=1000, warm_steps=200, lr=1e-2
     return res
 
 
+def train_bench(steps, minibatch=512, warmup=5):
+    """Time training steps (forward, MSE, backward, Adam) on random log-mel-like features
+    of one minibatch; prints one JSON line (ms per step, TFLOP/s of the products)."""
+    import torch
+    ws = WarmStart(max_batch=max(minibatch, 2048), max_rows=64, max_len=2 ** 16)
+    g = torch.Generator(device="cpu").manual_seed(1)
+    feats = (-6.0 + 3.0 * torch.randn(minibatch, 256, 32, generator=g)).to(ws.device).contiguous()
+    types = sorted((WS_HEAD_TYPES[i] for i in torch.randint(0, 5, (minibatch,), generator=g).tolist()),
+                   key=lambda t: HEAD_OF[t])
+    tgt = torch.randn(minibatch, WS_OUTMAX, generator=g).to(ws.device)
+    for _ in range(warmup):
+        ws.train_step(feats, tgt, types)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(ws.stream)
+    for _ in range(steps):
+        loss = ws.train_step(feats, tgt, types)
+    e1.record(ws.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    rows = minibatch * 32
+    conv = sum(2 * rows * k * 128 for k in (1280, 640, 640, 640))
+    flops = conv + 2 * conv - 2 * rows * 1280 * 128          # forward, weight grads, input grads (l > 0)
+    heads = 2 * minibatch * (128 * 288 + 288 * 288 + 288 * 60) * 3
+    print(json.dumps(dict(minibatch=minibatch, steps=steps, ms_per_step=ms, loss=float(loss),
+                          gemm_tflops=(flops + heads) / ms / 1e9, gpu=torch.cuda.get_device_name())))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train-graphs", type=int, default=256)
@@ -373,8 +401,12 @@ def main():
     ap.add_argument("--minibatch", type=int, default=512)
     ap.add_argument("--plain-steps", type=int, default=1000)
     ap.add_argument("--warm-steps", type=int, default=200)
+    ap.add_argument("--train-bench", type=int, default=0,
+                    help="only time this many training steps on random features (no data, no fit)")
     args = ap.parse_args()
     import torch
+    if args.train_bench:
+        return train_bench(args.train_bench, args.minibatch)
     ws = WarmStart(max_batch=max(2048, args.minibatch), max_rows=1024, max_len=args.length)
     losses, t_data, t_train, n = train(ws, args.train_graphs, args.length, epochs=args.epochs,
                                        minibatch=args.minibatch, log=lambda s: print(s, flush=True))
