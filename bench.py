@@ -170,8 +170,8 @@ def peaks():
 
 
 def traffic_for(kernel_key):
-    """ncu DRAM bytes per launch recorded in profiles/dram_traffic.json, if the kernel
-    source has not changed since (sha1 of the .cu file)."""
+    """ncu DRAM bytes per launch recorded in profiles/dram_traffic.json, if the kernel's
+    sources (its .cu file and the headers it includes) have not changed since (sha1)."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(p):
         return None
@@ -179,9 +179,16 @@ def traffic_for(kernel_key):
         d = json.load(f).get(kernel_key)
     if not d:
         return None
-    src = os.path.join(ROOT, "paper_2408_03204_b300", "csrc", d["source"])
-    h = hashlib.sha1(open(src, "rb").read()).hexdigest()
-    return d["bytes_per_launch"] if h == d["sha1"] else None
+    if "sources" not in d:
+        return None
+    return d["bytes_per_launch"] if sources_sha1(d["sources"]) == d["sha1"] else None
+
+
+def sources_sha1(names):
+    h = hashlib.sha1()
+    for n in names:
+        h.update(open(os.path.join(ROOT, "paper_2408_03204_b300", "csrc", n), "rb").read())
+    return h.hexdigest()
 
 
 def cpu_baseline(L=L_FULL, steps=1):
@@ -316,24 +323,30 @@ def main():
     torch.cuda.synchronize(dev)
     plan.sync_status(st)
 
-    n_ev = N + 1 + N
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
-    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # ---- the timed region: the whole step (render, loss, loss gradient, backprop) as
+    # the library's captured CUDA graph (grafx_step_graph_*), replayed on a side stream
+    side = torch.cuda.Stream(dev)
+    ss = gx._stream_of(side)
+    torch.cuda.synchronize(dev)
+    graph = plan.capture_step(src, out, tgt, loss, d_out, dP, None, ss)
+    for _ in range(max(3, args.warmup)):
+        graph.launch(ss)
+    torch.cuda.synchronize(dev)
+    plan.sync_status(ss)
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
     sampler.start()
-    t_start.record(stream)
-    for it in range(args.steps):
-        e0[it].record(stream)
-        step(evs[it])
-    t_end.record(stream)
+    t_start.record(side)
+    for _ in range(args.steps):
+        graph.launch(ss)
+    t_end.record(side)
     torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    plan.sync_status(st)
+    plan.sync_status(ss)
     ms_total = t_start.elapsed_time(t_end)
     if dist:
         tt = torch.tensor([ms_total], device=dev, dtype=torch.float64)
@@ -343,49 +356,60 @@ def main():
     node_samples = int(info.node_samples)
     value = node_samples * world * args.steps / (ms_total / 1e3)
 
-    # per schedule-step durations (fwd k = 1..N, loss, bwd k = N..1)
+    # ---- diagnostics outside the timed region: per schedule-step durations of the same
+    # step launched step by step (fwd k = 1..N, loss, bwd k = N..1)
+    n_ev = N + 1 + N
+    diag = max(5, args.steps // 2)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(diag)]
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(diag)]
+    torch.cuda.synchronize(dev)
+    for it in range(diag):
+        e0[it].record(stream)
+        step(evs[it])
+    torch.cuda.synchronize(dev)
     labels = [f"fwd:{synth.TYPE_LETTERS[string[k]]}{k}" for k in range(1, N + 1)] + ["loss"] + \
              [f"bwd:{synth.TYPE_LETTERS[string[k]]}{k}" for k in range(N, 0, -1)]
     dur = np.zeros(n_ev)
-    for it in range(args.steps):
+    for it in range(diag):
         prev = e0[it]
         for j in range(n_ev):
             dur[j] += prev.elapsed_time(evs[it][j])
             prev = evs[it][j]
-    dur /= args.steps
+    dur /= diag
     algo = [fwd_b[k] for k in range(1, N + 1)] + [0] + [bwd_b[k] for k in range(N, 0, -1)]
     j = int(np.argmax(dur))
-    peak, peak_kind = peaks()
-    achieved = algo[j] / (dur[j] / 1e3) / 1e9
     kernel_key = labels[j]
+    # the dominant step alone, launched back to back on its stream (its kernels only)
+    k_step = (N - (j - N - 1)) if j > N else (j + 1)
+    reps = 20
+    ka, kb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ka.record(stream)
+    for _ in range(reps):
+        if j > N:
+            plan.backprop_steps_raw(src, d_out, dP, None, k_step, k_step + 1, st)
+        elif j == N:
+            plan.loss_raw(out, tgt, loss, st)
+            plan.loss_backward_raw(out, tgt, d_out, st)
+        else:
+            plan.render_steps_raw(src, out, k_step, k_step + 1, st)
+    kb.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_kernel = ka.elapsed_time(kb) / reps
+    peak, peak_kind = peaks()
+    achieved = algo[j] / (ms_kernel / 1e3) / 1e9
     step_bytes = sum(algo)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic_for(kernel_key), "kernel": kernel_key,
-                "peak_source": peak_kind, "ms_per_launch": dur[j],
+                "peak_source": peak_kind, "ms_per_launch": ms_kernel,
                 "algorithmic_bytes_per_launch": algo[j],
                 "step": {"algorithmic_bytes": step_bytes, "achieved": step_bytes / (ms_step / 1e3) / 1e9,
                          "frac": step_bytes / (ms_step / 1e3) / 1e9 / peak},
-                "breakdown_ms": {lab: round(float(d), 4) for lab, d in zip(labels, dur)}}
-
-    # the same step replayed as one CUDA graph (one launch per step)
-    side = torch.cuda.Stream(dev)
-    ss = gx._stream_of(side)
-    torch.cuda.synchronize(dev)
-    graph = plan.capture_step(src, out, tgt, loss, d_out, dP, None, ss)
-    for _ in range(3):
-        graph.launch(ss)
-    torch.cuda.synchronize(dev)
-    ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ga.record(side)
-    for _ in range(args.steps):
-        graph.launch(ss)
-    gb.record(side)
-    torch.cuda.synchronize(dev)
-    graph_ms = ga.elapsed_time(gb) / args.steps
+                "eager_breakdown_ms": {lab: round(float(d), 4) for lab, d in zip(labels, dur)},
+                "eager_ms_per_step": float(dur.sum())}
     plan.sync_status(st)
 
     # end to end through the C-ABI with host buffers: H2D of the step's inputs from pinned
-    # memory, the step, D2H of the loss and every parameter gradient
+    # memory, the captured step, D2H of the loss and every parameter gradient
     src_pin = torch.tensor(src_h).pin_memory()
     tgt_pin = tgt.cpu().pin_memory()
     P_pin = {t: v.cpu().pin_memory() for t, v in P.items()}
@@ -395,14 +419,15 @@ def main():
     d2h = 4 + sum(v.numel() * 4 for v in dP_pin.values())
 
     def e2e_step():
-        src.copy_(src_pin, non_blocking=True)
-        tgt.copy_(tgt_pin, non_blocking=True)
-        for t in P:
-            P[t].copy_(P_pin[t], non_blocking=True)
-        step()
-        loss_pin.copy_(loss, non_blocking=True)
-        for t in dP:
-            dP_pin[t].copy_(dP[t], non_blocking=True)
+        with torch.cuda.stream(side):
+            src.copy_(src_pin, non_blocking=True)
+            tgt.copy_(tgt_pin, non_blocking=True)
+            for t in P:
+                P[t].copy_(P_pin[t], non_blocking=True)
+            graph.launch(ss)
+            loss_pin.copy_(loss, non_blocking=True)
+            for t in dP:
+                dP_pin[t].copy_(dP[t], non_blocking=True)
 
     for _ in range(2):
         e2e_step()
@@ -410,10 +435,10 @@ def main():
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
-    a.record(stream)
+    a.record(side)
     for _ in range(args.e2e_steps):
         e2e_step()
-    b.record(stream)
+    b.record(side)
     torch.cuda.synchronize(dev)
     ms_e2e = a.elapsed_time(b)
     if dist:
@@ -436,9 +461,9 @@ def main():
                 "config": dict(cfg, nodes=int(info.n_nodes), processed_node_samples=node_samples,
                                schedule_steps=N, parallelism=f"replicas{world}"),
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": n_launch * args.steps,
-                "cuda_graph": {"ms_per_step": graph_ms, "value": node_samples * world / (graph_ms / 1e3),
-                               "launches_per_step": graph.launches()}}
+                "gpu_launches": graph.launches() * args.steps,
+                "timed": "captured CUDA graph of the whole step (grafx_step_graph), "
+                         f"{graph.launches()} kernels per step, {n_launch} when launched step by step"}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -336,9 +336,10 @@ int grafx_ws_forward(grafx_wsnet* n, const float* weights, const float* feats, c
  * taken in a fixed order (deterministic).  Asynchronous on `stream`. */
 int grafx_ws_backward(grafx_wsnet* n, const float* weights, const float* feats, const int32_t* head_count, int32_t B,
                       const float* d_out, float* d_weights, void* stream);
-/* Masked mean-squared error over the first n_out[i] (device int32) columns of each row
- * of out and target (device [B][176]): *loss (device float) and d_out = dloss/dout (0 in
- * unused columns).  Asynchronous on `stream`. */
+/* Masked mean-squared error between out and target (device [B][176]): the squared
+ * error is averaged over the first n_out[i] (device int32, >= 1) columns of each row and
+ * then over the rows; *loss (device float) and d_out = dloss/dout (0 in unused
+ * columns).  Asynchronous on `stream`. */
 int grafx_ws_mse(const float* out, const float* target, const int32_t* n_out, int32_t B, float* loss, float* d_out,
                  void* stream);
 /* The network's matrix product on its own: C = alpha A B + beta C over device float32

@@ -15,7 +15,8 @@ parameters):
             bias, exact GELU 0.5 x (1 + erf(x / sqrt 2)); mean over time -> e in R^128.
   heads     one MLP per parameterised type: 128 -> 288 -> 288 -> N_t (GELU, GELU,
             linear); output = the unconstrained parameters theta of the fit.
-  loss      mean squared error over the N_t outputs of every sample.
+  loss      squared error averaged over the N_t outputs of each sample, then over the
+            samples.
 
 ``forward``/``backward`` take an optional operand rounding ``rnd`` applied to both
 operands of every matrix product (``bf16_round`` reproduces the operand precision of a
@@ -86,14 +87,17 @@ def _id(x):
 
 
 def masked_mse(out, target, n_out):
-    """Mean of (out - target)^2 over the first n_out[i] entries of every row i, and
-    its gradient with respect to out."""
+    """Mean over rows of the mean squared error over each row's first n_out[i] entries
+    (every sample weighs the same whatever its head's width), and its gradient with
+    respect to out."""
     out = np.asarray(out, np.float64)
     target = np.asarray(target, np.float64)
-    mask = np.arange(out.shape[1])[None, :] < np.asarray(n_out)[:, None]
-    cnt = mask.sum()
+    n_out = np.asarray(n_out)
+    mask = np.arange(out.shape[1])[None, :] < n_out[:, None]
     r = np.where(mask, out - target, 0.0)
-    return float((r * r).sum() / cnt), 2.0 * r / cnt
+    B = out.shape[0]
+    loss = float(((r * r).sum(axis=1) / n_out).sum() / B)
+    return loss, 2.0 * r / (B * n_out[:, None])
 
 
 def gelu(x):

@@ -132,7 +132,12 @@ template <> struct Dft<16> {
 // Pass geometry: pass p (p = 0..npass-1) merges Ns = 16^p points into 16^p * R_p with
 // R_p = 16, except the last pass of an M that is not a power of 16 (radix M / 16^n16).
 GX_HD constexpr int geo_n16(int M) { return M >= 4096 ? 3 : M >= 256 ? 2 : 1; }
-GX_HD constexpr int ipow16(int p) { return p == 0 ? 1 : 16 * ipow16(p - 1); }
+// (iterative, so that device code inlines and folds them instead of calling a recursion)
+GX_HD constexpr int ipow16(int p) {
+  int r = 1;
+  for (int i = 0; i < p; ++i) r *= 16;
+  return r;
+}
 GX_HD constexpr int geo_last(int M) { return M / ipow16(geo_n16(M)); }
 GX_HD constexpr int geo_npass(int M) { return geo_n16(M) + (geo_last(M) > 1 ? 1 : 0); }
 GX_HD constexpr int pass_radix(int M, int p) { return (p == geo_npass(M) - 1 && geo_last(M) > 1) ? geo_last(M) : 16; }
@@ -142,9 +147,17 @@ GX_HD constexpr int pass_radix(int M, int p) { return (p == geo_npass(M) - 1 && 
 // [(r-1) Ns + k] so that the threads of a warp (consecutive k) read consecutive
 // entries.  The tables of M = 512, 1024, ..., 8192 are concatenated in that order.
 GX_HD constexpr int ptw_pass_size(int M, int p) { return p == 0 ? 0 : (pass_radix(M, p) - 1) * ipow16(p); }
-GX_HD constexpr int ptw_pass_off(int M, int p) { return p == 0 ? 0 : ptw_pass_off(M, p - 1) + ptw_pass_size(M, p - 1); }
+GX_HD constexpr int ptw_pass_off(int M, int p) {
+  int o = 0;
+  for (int q = 0; q < p; ++q) o += ptw_pass_size(M, q);
+  return o;
+}
 GX_HD constexpr int ptw_size(int M) { return ptw_pass_off(M, geo_npass(M)); }
-GX_HD constexpr int ptw_base(int M) { return M <= 512 ? 0 : ptw_base(M / 2) + ptw_size(M / 2); }
+GX_HD constexpr int ptw_base(int M) {
+  int o = 0;
+  for (int m = 512; m < M; m *= 2) o += ptw_size(m);
+  return o;
+}
 constexpr int PTW_TOTAL = ptw_base(8192) + ptw_size(8192);
 
 // Pass geometry of an M-point transform.

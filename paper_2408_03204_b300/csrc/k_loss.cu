@@ -69,7 +69,8 @@ __device__ __forceinline__ void loss_item_fwd(const LossArgs& a, const int4_ ite
   __shared__ float red[6 * 32];
   const int g = threadIdx.x / T, gtid = threadIdx.x % T;
   const LossRow r = a.rows[item.x];
-  const int q = item.y, F = r.n_frames[q];
+  constexpr int q = M == 512 ? 0 : M == 1024 ? 1 : 2;  // == item.y (dispatch)
+  const int F = r.n_frames[q];
   const int f = item.z + g;
   const bool act = f < F;
   float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -163,7 +164,8 @@ __device__ __forceinline__ void loss_item_bwd(const LossArgs& a, const int4_ ite
   const float w_res = 1.f / float(2 * N_RES);
   {
     const LossRow r = a.rows[item.x];
-    const int q = item.y, F = r.n_frames[q];
+    constexpr int q = M == 512 ? 0 : M == 1024 ? 1 : 2;  // == item.y (dispatch)
+    const int F = r.n_frames[q];
     const float4 stl = a.stats[2 * (item.x * N_RES + q)], str = a.stats[2 * (item.x * N_RES + q) + 1];
     {
       const int f = item.z + g;

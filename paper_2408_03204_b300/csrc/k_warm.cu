@@ -386,28 +386,29 @@ __global__ void k_time_mean_bwd(const float* __restrict__ de, int B, float* __re
   }
 }
 
-// Masked mean-squared error: loss = sum over rows b and columns j < n_out[b] of
-// (out - tgt)^2 / count, d = 2 (out - tgt) / count (0 in unused columns).
+// Masked mean-squared error, every row weighted alike: loss = (1/B) sum_b (1/n_b)
+// sum_{j < n_b} (out - tgt)^2 with n_b = n_out[b]; d = 2 (out - tgt) / (B n_b), 0 in
+// unused columns.
 __global__ void __launch_bounds__(1024) k_ws_mse(const float* __restrict__ out, const float* __restrict__ tgt,
                                                  const int32_t* __restrict__ nout, int B,
                                                  float* __restrict__ loss, float* __restrict__ d) {
   __shared__ float red[4 * 32];
-  float cnt = 0.f;
-  for (int b = 0; b < B; ++b) cnt += float(nout[b]);
   float s = 0.f;
   for (int i = threadIdx.x; i < B * WS_OUTMAX; i += blockDim.x) {
     const int b = i / WS_OUTMAX, j = i % WS_OUTMAX;
+    const int nb = nout[b];
     float g = 0.f;
-    if (j < nout[b]) {
+    if (j < nb) {
       const float r = out[i] - tgt[i];
-      s += r * r;
-      g = 2.f * r / cnt;
+      const float w = 1.f / (float(B) * float(nb));
+      s += r * r * w;
+      g = 2.f * r * w;
     }
     d[i] = g;
   }
   float v[1] = {s};
   block_sum<1>(v, red);
-  if (threadIdx.x == 0) *loss = cnt > 0.f ? v[0] / cnt : 0.f;
+  if (threadIdx.x == 0) *loss = v[0];
 }
 
 // ------------------------------------------------------------------ log-mel features

@@ -265,7 +265,7 @@ def make_batch(ws, graph_lists, L, seed, hidden_seed):
     return batch, src, hidden, target, neutral
 
 
-def train(ws, n_graphs, L, graphs_per_batch=16, epochs=4, minibatch=512, seed=5, log=None):
+def train(ws, n_graphs, L, graphs_per_batch=16, epochs=4, minibatch=512, seed=5, log=None, lo=32, hi=200):
     """Generate n_graphs random consoles, build their features and theta targets, fit the
     standardisation and train.  Returns (losses per step, data seconds, train seconds)."""
     torch = ws.torch
@@ -273,7 +273,7 @@ def train(ws, n_graphs, L, graphs_per_batch=16, epochs=4, minibatch=512, seed=5,
     feats, targets, types = [], [], []
     t0 = time.time()
     for b0 in range(0, n_graphs, graphs_per_batch):
-        gl = random_graph_lists(rng, min(graphs_per_batch, n_graphs - b0))
+        gl = random_graph_lists(rng, min(graphs_per_batch, n_graphs - b0), lo, hi)
         batch, src, hidden, target, neutral = make_batch(ws, gl, L, seed * 100000 + b0 * 37, seed * 7919 + b0)
         feats.append(ws.features(batch, src, target, neutral))
         targets.append(ws.theta_targets(batch, hidden))
@@ -283,11 +283,19 @@ def train(ws, n_graphs, L, graphs_per_batch=16, epochs=4, minibatch=512, seed=5,
     feats = torch.cat(feats)
     targets = torch.cat(targets)
     t_data = time.time() - t0
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    # hold out a tenth of the samples for the per-head evaluation
+    perm0 = torch.randperm(feats.shape[0], generator=g)
+    n_hold = feats.shape[0] // 10
+    hold, keep = perm0[:n_hold].to(ws.device), perm0[n_hold:].to(ws.device)
+    types_all = torch.as_tensor(types, device=ws.device)
+    hold_set = (feats.index_select(0, hold), targets.index_select(0, hold), types_all.index_select(0, hold))
+    feats, targets = feats.index_select(0, keep), targets.index_select(0, keep)
+    types = types_all.index_select(0, keep).tolist()
     ws.fit_standardisation(targets, types)
     types_t = torch.as_tensor(types, device=ws.device)
     head_of = torch.as_tensor([HEAD_OF.get(t, 0) for t in range(9)], device=ws.device)
     n = feats.shape[0]
-    g = torch.Generator(device="cpu").manual_seed(seed)
     losses = []
     t1 = time.time()
     for ep in range(epochs):
@@ -304,7 +312,27 @@ def train(ws, n_graphs, L, graphs_per_batch=16, epochs=4, minibatch=512, seed=5,
             log(f"epoch {ep}: loss {float(torch.stack(losses[-10:]).mean()):.4f}")
     ws.stream.synchronize()
     t_train = time.time() - t1
+    ws.held_out = evaluate_heads(ws, *hold_set, head_of)
     return [float(x) for x in torch.cat(losses).cpu()], t_data, t_train, n
+
+
+def evaluate_heads(ws, feats, targets, types_t, head_of):
+    """Per head: mean over held-out samples of the standardised squared error averaged
+    over the head's outputs (1.0 = predicting the training mean), and the sample count."""
+    torch = ws.torch
+    order = torch.argsort(head_of[types_t] * feats.shape[0] + torch.arange(feats.shape[0], device=ws.device))
+    feats, targets, types_t = feats.index_select(0, order), targets.index_select(0, order), types_t[order]
+    tl = types_t.tolist()
+    theta = ws.predict(feats, tl)
+    heads = head_of[types_t]
+    err = ((theta - targets) / ws.sd[heads]) ** 2
+    out = {}
+    for h, t in enumerate(WS_HEAD_TYPES):
+        m = types_t == t
+        if int(m.sum()):
+            k = WS_HEAD_OUT[h]
+            out["gsecdr"[h]] = (float(err[m][:, :k].mean()), int(m.sum()))
+    return out
 
 
 def evaluate(ws, graph_lists, L, seed, plain_steps=1000, warm_steps=200, lr=1e-2):
@@ -401,22 +429,27 @@ def main():
     ap.add_argument("--minibatch", type=int, default=512)
     ap.add_argument("--plain-steps", type=int, default=1000)
     ap.add_argument("--warm-steps", type=int, default=200)
+    ap.add_argument("--budget-lo", type=int, default=32)
+    ap.add_argument("--budget-hi", type=int, default=200)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--train-bench", type=int, default=0,
                     help="only time this many training steps on random features (no data, no fit)")
     args = ap.parse_args()
     import torch
     if args.train_bench:
         return train_bench(args.train_bench, args.minibatch)
-    ws = WarmStart(max_batch=max(2048, args.minibatch), max_rows=1024, max_len=args.length)
+    ws = WarmStart(max_batch=max(2048, args.minibatch), max_rows=1024, max_len=args.length, lr=args.lr)
     losses, t_data, t_train, n = train(ws, args.train_graphs, args.length, epochs=args.epochs,
-                                       minibatch=args.minibatch, log=lambda s: print(s, flush=True))
+                                       minibatch=args.minibatch, log=lambda s: print(s, flush=True),
+                                       lo=args.budget_lo, hi=args.budget_hi)
     rng = np.random.Generator(np.random.PCG64(555))
-    tests = random_graph_lists(rng, args.test_graphs)
+    tests = random_graph_lists(rng, args.test_graphs, args.budget_lo, args.budget_hi)
     res = evaluate(ws, tests, args.length, 9000, args.plain_steps, args.warm_steps)
     sp = [r["speedup"] for r in res if r["speedup"]]
     print(json.dumps(dict(train_graphs=args.train_graphs, train_samples=n, length=args.length,
                           data_s=round(t_data, 2), train_s=round(t_train, 2), train_steps=len(losses),
                           loss_first=losses[0], loss_last=float(np.mean(losses[-20:])),
+                          held_out_mse_per_head=ws.held_out,
                           median_speedup=float(np.median(sp)) if sp else None,
                           reached=len(sp), tests=res, gpu=torch.cuda.get_device_name())))
 

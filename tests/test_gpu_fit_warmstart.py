@@ -110,3 +110,26 @@ def test_warm_start_training_reduces_loss_and_predicts(env):
     assert torch.isfinite(theta).all()
     for t, tab in tabs.items():
         assert tab.shape == (batch.plan.info.n_type_rows[t], gx.PARAM_COLS[t])
+
+
+def test_trained_network_beats_the_prior_mean_on_eq():
+    """What training gains: on small consoles the held-out EQ band predictions beat the
+    training-set mean (standardised MSE 1.0), the baseline a fit without the network
+    would have to beat.  (On 32-200-node consoles the per-node features carry too
+    little of each node's effect on the mix for any head to beat the mean.)"""
+    gx, torch, gfit, gws = env_tuple()
+    ws = gws.WarmStart(max_batch=512, max_rows=1024, max_len=32768, lr=1e-3)
+    gws.train(ws, 2400, 32768, graphs_per_batch=48, epochs=12, minibatch=256, seed=11, lo=4, hi=8)
+    print("held-out standardised MSE per head:", ws.held_out)
+    assert ws.held_out["e"][0] < EQ_GAIN_BOUND, ws.held_out
+
+
+EQ_GAIN_BOUND = 0.9
+
+
+def env_tuple():
+    import torch
+    import paper_2408_03204_b300 as gx
+    from paper_2408_03204_b300 import fit as gfit
+    from paper_2408_03204_b300 import warmstart as gws
+    return gx, torch, gfit, gws

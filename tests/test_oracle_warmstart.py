@@ -87,15 +87,21 @@ def test_masked_mse_brute_force():
     out, tgt = rng.standard_normal((4, 176)), rng.standard_normal((4, 176))
     n_out = [2, 176, 8, 50]
     loss, d = ow.masked_mse(out, tgt, n_out)
-    s, c = 0.0, 0
+    per = []
     for i, n in enumerate(n_out):
-        for j in range(n):
-            s += (out[i, j] - tgt[i, j]) ** 2
-            c += 1
-    assert np.isclose(loss, s / c, rtol=1e-13)
+        per.append(sum((out[i, j] - tgt[i, j]) ** 2 for j in range(n)) / n)
+    assert np.isclose(loss, sum(per) / 4, rtol=1e-13)
     for i, n in enumerate(n_out):
-        np.testing.assert_allclose(d[i, :n], 2 * (out[i, :n] - tgt[i, :n]) / c, rtol=1e-13)
+        np.testing.assert_allclose(d[i, :n], 2 * (out[i, :n] - tgt[i, :n]) / (4 * n), rtol=1e-13)
         assert not d[i, n:].any()
+    # central differences of the loss in a few coordinates
+    for i, j in ((0, 1), (1, 100), (3, 49)):
+        h = 1e-6
+        op, om = out.copy(), out.copy()
+        op[i, j] += h
+        om[i, j] -= h
+        num = (ow.masked_mse(op, tgt, n_out)[0] - ow.masked_mse(om, tgt, n_out)[0]) / (2 * h)
+        assert np.isclose(d[i, j], num, rtol=1e-6)
 
 
 def test_logmel_parseval_and_pooling():
