@@ -258,10 +258,9 @@ __device__ __forceinline__ void forward(float2* buf, const float2_* __restrict__
 // passes go through shared memory, alternating between b0 and b1 (one barrier per
 // pass).  The caller guarantees that no thread still reads b0 when this is entered;
 // on exit other threads may still read b1 (or b0 when the pass count is odd).
+// tw: this size's pass tables (ptw + ptw_base(M)), in global or shared memory.
 template <int M>
-__device__ __forceinline__ void forward_regs(float2 (&v)[16], float2* b0, float2* b1,
-                                             const float2_* __restrict__ ptw, int tid) {
-  const float2_* tw = ptw + ptw_base(M);
+__device__ __forceinline__ void forward_regs_tw(float2 (&v)[16], float2* b0, float2* b1, const float2_* tw, int tid) {
   constexpr int n16 = Geo<M>::n16, last = Geo<M>::last;
   constexpr int npass = n16 + (last > 1 ? 1 : 0);
   float2* bufs[2] = {b0, b1};
@@ -307,6 +306,11 @@ __device__ __forceinline__ void forward_regs(float2 (&v)[16], float2* b0, float2
       Ns *= 16;
     }
   }
+}
+template <int M>
+__device__ __forceinline__ void forward_regs(float2 (&v)[16], float2* b0, float2* b1,
+                                             const float2_* __restrict__ ptw, int tid) {
+  forward_regs_tw<M>(v, b0, b1, ptw + ptw_base(M), tid);
 }
 #endif
 

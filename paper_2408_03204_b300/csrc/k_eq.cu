@@ -147,6 +147,10 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_fwd(DevCtx c, int item0
   extern __shared__ float2 smem2[];
   float2* b0 = smem2;
   float2* b1 = smem2 + fft::Padded<M>::size;
+  // this size's FFT pass twiddles, staged once per CTA (the CTA loops over many blocks)
+  float2_* stw = reinterpret_cast<float2_*>(smem2 + 2 * fft::Padded<M>::size);
+  for (int i = threadIdx.x; i < fft::ptw_size(M); i += blockDim.x) stw[i] = c.ptw[fft::ptw_base(M) + i];
+  __syncthreads();
   constexpr bool even = fft::Geo<M>::npass % 2 == 0;
   const int H = c.eq_H, S = c.eq_step, Hal = c.eq_Hal;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -158,10 +162,10 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_fwd(DevCtx c, int item0
     float2 x[16];
     eq_load_regs<M, false>(c, v, nd, ws, x, false, H, S);
     if (even) __syncthreads();
-    fft::forward_regs<M>(x, b0, b1, c.ptw, threadIdx.x);
+    fft::forward_regs_tw<M>(x, b0, b1, stw, threadIdx.x);
     eq_apply_regs<M>(x, spec);
     if (even) __syncthreads();
-    fft::forward_regs<M>(x, b0, b1, c.ptw, threadIdx.x);
+    fft::forward_regs_tw<M>(x, b0, b1, stw, threadIdx.x);
     eq_store_regs<M>(yrow_w(c, nd), nd, ws, x, H, S);
   }
 }
@@ -314,10 +318,11 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
   constexpr int T = M / 16;
   static bool init = false;
   const size_t s1 = sizeof(float2) * fft::Padded<M>::size;
+  const size_t stw_bytes = sizeof(float2_) * fft::ptw_size(M);
   if (!init) {
     cudaFuncSetAttribute(k_eq_spec<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
     cudaFuncSetAttribute(k_eq_gradfft<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
-    cudaFuncSetAttribute(k_eq_fwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(2 * s1));
+    cudaFuncSetAttribute(k_eq_fwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(2 * s1 + stw_bytes));
     cudaFuncSetAttribute(k_eq_bwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(3 * s1));
     init = true;
   }
@@ -329,7 +334,9 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
       k_eq_taps<<<dim3(b - a, chunks_h), EQ_CHUNK, 0, s>>>(c, a);
       k_eq_spec<M><<<b - a, T, s1, s>>>(c, a);
       return 2;
-    case 1: k_eq_fwd<M><<<grid_size(b, (228 * 1024) / int(2 * s1 + 1024)), T, 2 * s1, s>>>(c, a, b); return 1;
+    case 1:
+      k_eq_fwd<M><<<grid_size(b, (228 * 1024) / int(2 * s1 + stw_bytes + 1024)), T, 2 * s1 + stw_bytes, s>>>(c, a, b);
+      return 1;
     case 2: k_eq_bwd<M><<<grid_size(b, (228 * 1024) / int(3 * s1 + 1024)), T, 3 * s1, s>>>(c, a, b); return 1;
     case 3:
       k_eq_gradfft<M><<<b - a, T, s1, s>>>(c, a);
