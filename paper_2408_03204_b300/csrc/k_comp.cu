@@ -121,18 +121,20 @@ template <bool REVERSE>
 __device__ __forceinline__ float block_affine_scan(float b, float la_spt, float* sh, float* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float incl = b;  // Hillis-Steele: incl_i += D^d incl_{i-d} (forward) / incl_{i+d} (reverse)
+  float Dd = expf(la_spt);  // D^d for d = 1, 2, 4, ... by squaring
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     float o = REVERSE ? __shfl_down_sync(0xffffffffu, incl, d) : __shfl_up_sync(0xffffffffu, incl, d);
     bool ok = REVERSE ? (lane + d < 32) : (lane >= d);
-    if (ok) incl += expf(la_spt * float(d)) * o;
+    if (ok) incl += Dd * o;
+    Dd *= Dd;
   }
   float excl = REVERSE ? __shfl_down_sync(0xffffffffu, incl, 1) : __shfl_up_sync(0xffffffffu, incl, 1);
   if (REVERSE ? (lane == 31) : (lane == 0)) excl = 0.f;
   if (REVERSE ? (lane == 0) : (lane == 31)) sh[warp] = incl;  // state leaving the warp
   __syncthreads();
   if (threadIdx.x == 0) {
-    const float d32 = expf(la_spt * 32.f);
+    const float d32 = Dd;  // D^32
     float run = 0.f;
     for (int k = 0; k < 8; ++k) {
       int wi = REVERSE ? 7 - k : k;
@@ -148,9 +150,33 @@ __device__ __forceinline__ float block_affine_scan(float b, float la_spt, float*
   return excl + expf(la_spt * float(dist)) * sh[8 + warp];
 }
 
+// The single row feeding node v (its in-edge source, or with adj the one consumer's
+// input-adjoint row), or null when there are several.
+__device__ __forceinline__ const float* single_row(const DevCtx& c, int v, bool adj) {
+  if (!adj) {
+    const int e0 = c.csr_ptr[v];
+    return c.csr_ptr[v + 1] - e0 == 1 ? yrow(c, c.nodes[c.csr_src[e0]]) : nullptr;
+  }
+  const int e0 = c.tcsr_ptr[v];
+  return c.tcsr_ptr[v + 1] - e0 == 1 ? arow(c, c.nodes[c.tcsr_dst[e0]]) : nullptr;
+}
+
 template <int SPT>
 __device__ __forceinline__ void load_chunk(const DevCtx& c, int v, const NodeDev& nd, int t, float* ul, float* ur,
                                            bool adj) {
+  if (const float* row = single_row(c, v, adj)) {  // one row: resolve it once, then plain loads
+#pragma unroll
+    for (int q = 0; q < SPT / 4; ++q) {
+      float4 l = f4zero(), r = f4zero();
+      if (t + 4 * q < nd.len) {
+        l = mask4(ld4(row + t + 4 * q), t + 4 * q, nd.len);
+        r = mask4(ld4(row + nd.pitch + t + 4 * q), t + 4 * q, nd.len);
+      }
+      ul[4 * q + 0] = l.x; ul[4 * q + 1] = l.y; ul[4 * q + 2] = l.z; ul[4 * q + 3] = l.w;
+      ur[4 * q + 0] = r.x; ur[4 * q + 1] = r.y; ur[4 * q + 2] = r.z; ur[4 * q + 3] = r.w;
+    }
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < SPT / 4; ++q) {
     float4 l, r;
@@ -168,6 +194,66 @@ __device__ __forceinline__ void load_chunk(const DevCtx& c, int v, const NodeDev
     ul[4 * q + 0] = l.x; ul[4 * q + 1] = l.y; ul[4 * q + 2] = l.z; ul[4 * q + 3] = l.w;
     ur[4 * q + 0] = r.x; ur[4 * q + 1] = r.y; ur[4 * q + 2] = r.z; ur[4 * q + 3] = r.w;
   }
+}
+
+// cp.async of 16 bytes into shared memory; src_bytes = 0 writes zeros (nothing read)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Prefetch: this thread's SPT samples of both channels of `row` from t into its own
+// slots dst[ch * 256 * SPT + threadIdx.x * SPT ...] (zeros past the node's length).
+// Every thread reads back only its own slots, so one buffer serves consecutive chunks.
+template <int SPT>
+__device__ __forceinline__ void prefetch_rows(float* dst, const float* row, const NodeDev& nd, int t) {
+  constexpr int CH = 256 * SPT;
+#pragma unroll
+  for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+    for (int q = 0; q < SPT / 4; ++q) {
+      const int tq = t + 4 * q;
+      const bool in = tq < nd.len;
+      cp_async16(dst + ch * CH + threadIdx.x * SPT + 4 * q, in ? row + ch * nd.pitch + tq : row, in ? 16 : 0);
+    }
+}
+
+template <int SPT>
+__device__ __forceinline__ void read_rows(const float* src, const NodeDev& nd, int t, float* l, float* r) {
+  constexpr int CH = 256 * SPT;
+#pragma unroll
+  for (int q = 0; q < SPT / 4; ++q) {
+    float4 a = *reinterpret_cast<const float4*>(src + threadIdx.x * SPT + 4 * q);
+    float4 b = *reinterpret_cast<const float4*>(src + CH + threadIdx.x * SPT + 4 * q);
+    a = mask4(a, t + 4 * q, nd.len);
+    b = mask4(b, t + 4 * q, nd.len);
+    l[4 * q] = a.x, l[4 * q + 1] = a.y, l[4 * q + 2] = a.z, l[4 * q + 3] = a.w;
+    r[4 * q] = b.x, r[4 * q + 1] = b.y, r[4 * q + 2] = b.z, r[4 * q + 3] = b.w;
+  }
+}
+
+// Start the copies of item `it`'s single-row inputs (u, and with ADJ also ybar) into buf.
+template <int SPT, bool ADJ>
+__device__ __forceinline__ void prefetch_item(const DevCtx& c, int item, float* buf) {
+  constexpr int CH = 256 * SPT;
+  const int4_ w = c.items[item];
+  const NodeDev nd = c.nodes[w.x];
+  const int t = w.y * CH + threadIdx.x * SPT;
+  if (const float* row = single_row(c, w.x, false)) prefetch_rows<SPT>(buf, row, nd, t);
+  if (ADJ)
+    if (const float* row = single_row(c, w.x, true)) prefetch_rows<SPT>(buf + 2 * CH, row, nd, t);
+  cp_async_commit();
+}
+
+// This thread's u (and ybar) of the current chunk: from the prefetch buffer when the
+// node has a single row feeding it, else gathered.
+template <int SPT>
+__device__ __forceinline__ void fetch_rows(const DevCtx& c, int v, const NodeDev& nd, int t, const float* buf,
+                                           float* l, float* r, bool adj) {
+  if (single_row(c, v, adj)) read_rows<SPT>(buf, nd, t, l, r);
+  else load_chunk<SPT>(c, v, nd, t, l, r, adj);
 }
 
 template <int SPT>
@@ -193,17 +279,21 @@ __device__ __forceinline__ void envelope(const float* x, float alpha, float cin,
   }
 }
 
+// Software-pipelined over tickets: once a chunk's inputs are in registers, the next
+// ticket's copies start (cp.async) and run under this chunk's scan, look-back and gain.
 template <int SPT>
 __global__ void __launch_bounds__(256) k_comp_fwd(DevCtx c, int item0, int n_items, int ticket) {
   constexpr int CH = 256 * SPT;
+  __shared__ __align__(16) float buf[2 * CH];
   __shared__ float sh[32];
-  __shared__ int s_it;
+  __shared__ int s_it[2];
   __shared__ float s_carry;
-  while (true) {
-    if (threadIdx.x == 0) s_it = atomicAdd(c.tickets + ticket, 1);
-    __syncthreads();
-    const int it = s_it;
-    if (it >= n_items) break;
+  if (threadIdx.x == 0) s_it[0] = atomicAdd(c.tickets + ticket, 1);
+  __syncthreads();
+  int it = s_it[0], slot = 0;
+  if (it < n_items) prefetch_item<SPT, false>(c, item0 + it, buf);
+  while (it < n_items) {
+    if (threadIdx.x == 0) s_it[slot ^ 1] = atomicAdd(c.tickets + ticket, 1);  // read after the scan's barriers
     const int4_ w = c.items[item0 + it];
     const int v = w.x, chunk = w.y;
     const NodeDev nd = c.nodes[v];
@@ -212,7 +302,8 @@ __global__ void __launch_bounds__(256) k_comp_fwd(DevCtx c, int item0, int n_ite
     const float la = logf(alpha);
     const int t = chunk * CH + threadIdx.x * SPT;
     float ul[SPT], ur[SPT], x[SPT], g[SPT];
-    load_chunk<SPT>(c, v, nd, t, ul, ur, false);
+    cp_async_wait_all();
+    fetch_rows<SPT>(c, v, nd, t, buf, ul, ur, false);
 #pragma unroll
     for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
     // zero-start local state at the thread's end
@@ -221,6 +312,8 @@ __global__ void __launch_bounds__(256) k_comp_fwd(DevCtx c, int item0, int n_ite
     for (int i = 0; i < SPT; ++i) b = alpha * b + (1.f - alpha) * x[i];
     float total;
     float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
+    const int next = s_it[slot ^ 1];
+    if (next < n_items) prefetch_item<SPT, false>(c, item0 + next, buf);
     if (threadIdx.x < 32) {
       float carry = 0.f;
       if (chunk == 0) {
@@ -248,22 +341,27 @@ __global__ void __launch_bounds__(256) k_comp_fwd(DevCtx c, int item0, int n_ite
     }
     store_chunk<SPT>(yrow_w(c, nd), nd, t, ul, ur);
     __syncthreads();
+    it = next;
+    slot ^= 1;
   }
+  cp_async_wait_all();
 }
 
 template <int SPT>
 __global__ void __launch_bounds__(256) k_comp_bwd(DevCtx c, int item0, int n_items, int ticket) {
   constexpr int CH = 256 * SPT;
+  __shared__ __align__(16) float buf[4 * CH];
   __shared__ float sh[32];
   __shared__ float glast[256];
   __shared__ float red[4 * 32];
-  __shared__ int s_it;
+  __shared__ int s_it[2];
   __shared__ float s_lin;
-  while (true) {
-    if (threadIdx.x == 0) s_it = atomicAdd(c.tickets + ticket, 1);
-    __syncthreads();
-    const int it = s_it;
-    if (it >= n_items) break;
+  if (threadIdx.x == 0) s_it[0] = atomicAdd(c.tickets + ticket, 1);
+  __syncthreads();
+  int it = s_it[0], slot = 0;
+  if (it < n_items) prefetch_item<SPT, true>(c, item0 + it, buf);
+  while (it < n_items) {
+    if (threadIdx.x == 0) s_it[slot ^ 1] = atomicAdd(c.tickets + ticket, 1);  // read after the scan's barriers
     const int4_ w = c.items[item0 + it];
     const int v = w.x, chunk = w.y;
     const NodeDev nd = c.nodes[v];
@@ -273,8 +371,9 @@ __global__ void __launch_bounds__(256) k_comp_bwd(DevCtx c, int item0, int n_ite
     const int t = chunk * CH + threadIdx.x * SPT;
     const int n_chunks = (nd.len + CH - 1) / CH;
     float ul[SPT], ur[SPT], bl[SPT], br[SPT], x[SPT], g[SPT], a[SPT];
-    load_chunk<SPT>(c, v, nd, t, ul, ur, false);
-    load_chunk<SPT>(c, v, nd, t, bl, br, true);
+    cp_async_wait_all();
+    fetch_rows<SPT>(c, v, nd, t, buf, ul, ur, false);
+    fetch_rows<SPT>(c, v, nd, t, buf + 2 * CH, bl, br, true);
 #pragma unroll
     for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
     // recompute the envelope from the stored chunk carry-in (same arithmetic as forward)
@@ -284,6 +383,8 @@ __global__ void __launch_bounds__(256) k_comp_bwd(DevCtx c, int item0, int n_ite
     for (int i = 0; i < SPT; ++i) b = alpha * b + (1.f - alpha) * x[i];
     float total;
     float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
+    const int next = s_it[slot ^ 1];
+    if (next < n_items) prefetch_item<SPT, true>(c, item0 + next, buf);
     const float cin = excl + expf(la * float(SPT * threadIdx.x)) * carry_g;
     envelope<SPT>(x, alpha, cin, g);
     // local adjoints
@@ -346,7 +447,10 @@ __global__ void __launch_bounds__(256) k_comp_bwd(DevCtx c, int item0, int n_ite
     block_sum<4>(acc, red);
     if (threadIdx.x == 0) c.partial[w.w] = make_float4(acc[0], acc[1], acc[2], acc[3]);
     __syncthreads();
+    it = next;
+    slot ^= 1;
   }
+  cp_async_wait_all();
 }
 
 __global__ void k_comp_finalize(DevCtx c, int node_begin, int node_end) {
