@@ -107,8 +107,35 @@ __global__ void __launch_bounds__(256, 3) k_ew_bwd(DevCtx c, int item0, int n_it
     float acc[2] = {0.f, 0.f};
     float* ub = arow_w(c, nd);
     float4 bl[EW_Q], br[EW_Q], ul[EW_Q], ur[EW_Q];
-    gather_q<true>(c, v, t, nd.len, nd.pitch, bl, br);
-    if (needs_u) gather_q<false>(c, v, t, nd.len, nd.pitch, ul, ur);
+    const int ce = c.tcsr_ptr[v], pe = c.csr_ptr[v];
+    if (needs_u && c.tcsr_ptr[v + 1] - ce == 1 && c.csr_ptr[v + 1] - pe == 1) {
+      // one consumer and one producer (chains): issue all 4 * EW_Q loads at once
+      const float* ar = arow(c, c.nodes[c.tcsr_dst[ce]]);
+      const float* yr = yrow(c, c.nodes[c.csr_src[pe]]);
+#pragma unroll
+      for (int q = 0; q < EW_Q; ++q) {
+        const int tq = t + 1024 * q;
+        if (tq < nd.len) {
+          bl[q] = ld4(ar + tq);
+          br[q] = ld4(ar + nd.pitch + tq);
+          ul[q] = ld4(yr + tq);
+          ur[q] = ld4(yr + nd.pitch + tq);
+        } else {
+          bl[q] = br[q] = ul[q] = ur[q] = f4zero();
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < EW_Q; ++q) {
+        const int tq = t + 1024 * q;
+        bl[q] = mask4(bl[q], tq, nd.len);
+        br[q] = mask4(br[q], tq, nd.len);
+        ul[q] = mask4(ul[q], tq, nd.len);
+        ur[q] = mask4(ur[q], tq, nd.len);
+      }
+    } else {
+      gather_q<true>(c, v, t, nd.len, nd.pitch, bl, br);
+      if (needs_u) gather_q<false>(c, v, t, nd.len, nd.pitch, ul, ur);
+    }
 #pragma unroll
     for (int q = 0; q < EW_Q; ++q) {
       const int tq = t + 1024 * q;
