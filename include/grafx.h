@@ -303,8 +303,8 @@ int grafx_node_inputs(grafx_plan* p, const float* sources, const float* out, con
  *             128->288->288->N_t (N_t = 2, 1, 8, 4, 176, 50), GELU, GELU, linear.
  *   weights   conv{l}.w [Cout][Cin][5], conv{l}.b for l = 0..3, then per head in that
  *             type order w1 [288][128], b1, w2 [288][288], b2, w3 [N_t][288], b3.
- * Every matrix product runs on the tensor cores with BF16 operands (rounded to
- * nearest even from float32) and float32 accumulation.
+ * Every matrix product runs on the tensor cores (tcgen05, accumulator in tensor memory)
+ * with BF16 operands (rounded to nearest even from float32) and float32 accumulation.
  *
  * A net handle holds host tables only; its device workspace (caller-owned, 256-byte
  * aligned, grafx_ws_workspace_bytes for up to max_rows log-mel rows of up to
@@ -342,6 +342,9 @@ int grafx_ws_backward(grafx_wsnet* n, const float* weights, const float* feats, 
  * columns).  Asynchronous on `stream`. */
 int grafx_ws_mse(const float* out, const float* target, const int32_t* n_out, int32_t B, float* loss, float* d_out,
                  void* stream);
+/* Synchronise `stream` and report (and clear) a bounded tensor-core wait of the net's
+ * products that expired since the last call: GRAFX_ETIMEOUT, else GRAFX_OK. */
+int grafx_ws_sync_status(grafx_wsnet* n, void* stream);
 /* The network's matrix product on its own: C = alpha A B + beta C over device float32
  * buffers with A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn], C row-major with
  * leading dimension ldc >= N; A and B are rounded to BF16 (nearest even) and the sums

@@ -98,6 +98,7 @@ SIGNATURES = {
     "grafx_ws_forward": (ctypes.c_int, [_P, _F, _F, _I32P, _I32, _F, _P]),
     "grafx_ws_backward": (ctypes.c_int, [_P, _F, _F, _I32P, _I32, _F, _F, _P]),
     "grafx_ws_mse": (ctypes.c_int, [_F, _F, _P, _I32, _F, _F, _P]),
+    "grafx_ws_sync_status": (ctypes.c_int, [_P, _P]),
     "grafx_gemm_bf16": (ctypes.c_int, [_I32, _I32, _I32, _F, _I64, _I64, _F, _I64, _I64, _F, _I64, ctypes.c_float,
                                        ctypes.c_float, _F, _I64, _P]),
 }
@@ -339,6 +340,9 @@ class WarmStartNet:
         B = int(sum(head_count))
         _check(lib().grafx_ws_backward(self._h, _ptr(weights), _ptr(feats), self._heads(head_count), B,
                                        _ptr(d_out), _ptr(d_weights), stream))
+
+    def sync_status(self, stream):
+        _check(lib().grafx_ws_sync_status(self._h, stream))
 
     @staticmethod
     def mse_raw(out, target, n_out, loss, d_out, stream):

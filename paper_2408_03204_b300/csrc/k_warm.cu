@@ -12,9 +12,9 @@
 // 128->288->288->N_t.  Weights: one flat FP32 buffer in the order conv0.w [128][256][5],
 // conv0.b, conv1.w ... conv3.b, then per head (g, s, e, c, d, r) w1 [288][128], b1,
 // w2 [288][288], b2, w3 [N_t][288], b3.
-// Every product runs on the tensor cores in BF16 with FP32 accumulation (mma.sync
-// m16n8k16): operands are rounded to BF16 (nearest even) as they are staged into shared
-// memory; activations, gradients and weights stay FP32 in HBM.
+// Every product runs on the 5th-generation tensor cores (tcgen05.mma, FP32 accumulator
+// in tensor memory) with BF16 operands, rounded (nearest even) as they are staged into
+// shared memory; activations, gradients and weights stay FP32 in HBM.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -39,20 +39,17 @@ static const int kHeadOut[WS_NHEAD] = {2, 1, 8, 4, 176, 50};
 // ------------------------------------------------------------------ BF16 GEMM
 // C[M,N] = alpha * A B + beta * C with A(m, k) = A[m sam + k sak] and
 // B(k, n) = B[k sbk + n sbn] (FP32 in memory, BF16 in shared memory), C row-major (ldc).
-// CTA tile 128 x 128 x 32, 8 warps of 64 x 32 (4 x 4 m16n8k16 fragments).  The next
-// k-tile is loaded into registers while the current one is multiplied out of the other
-// shared-memory buffer (one barrier per k-tile).  Loads are float4 along whichever
-// dimension has unit stride when it is a multiple of 4 (mode VK: along k, VR: along the
-// row dimension m or n), else scalar (mode SC).  Split-K (gridDim.z > 1) writes partial
-// tiles to `part` [z][M][N], summed in z order by k_gemm_reduce (deterministic).
-constexpr int GB_M = 128, GB_N = 128, GB_K = 32, GB_P = GB_K + 8, GB_THREADS = 256;
-enum : int { LD_SC = 0, LD_VK = 1, LD_VR = 2 };
+// Operand tiles are loaded with float4 along whichever dimension has unit stride when
+// it is a multiple of 4 (mode VK: along k, VR: along the row dimension m or n), else
+// scalar (mode SC).  Split-K (gridDim.z > 1) writes partial tiles to `part` [z][M][N],
+// summed in z order by k_gemm_reduce (deterministic).
+enum : int { LD_SC = 0, LD_VK = 1, LD_VR = 2, LD_BK = 3, LD_BR = 4 };  // BK/BR: BF16 operand, 8 per load
 
 struct GemmArgs {
   int M, N, K, kchunk;
-  const float* A;
+  const void* A;  // float, or __nv_bfloat16 in the BF16 load modes
   int64_t sam, sak;
-  const float* B;
+  const void* B;
   int64_t sbk, sbn;
   float* C;
   int64_t ldc;
@@ -60,155 +57,312 @@ struct GemmArgs {
   float* part;  // split-K partials or null
 };
 
-__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+// ------------------------------------------------------------------ tcgen05 GEMM
+// The same product on the 5th-generation tensor cores: a 128 x 128 FP32 accumulator
+// in tensor memory (128 columns of TMEM), BF16 operand tiles of 128 x 64 in shared
+// memory in the canonical K-major 128-byte-swizzled layout, one elected thread issuing
+// tcgen05.mma (M = 128, N = 128, K = 16 per instruction, 4 per k-tile) whose completion
+// is signalled on an mbarrier by tcgen05.commit.  Two shared-memory stages: the 128
+// threads convert and store k-tile kt + 1 (FP32 loads, BF16 rounding) while the tensor
+// cores consume k-tile kt.  Epilogue: tcgen05.ld 32x32b (warp w reads TMEM lanes
+// 32 (w mod 4).. = rows, half of the columns each), alpha/beta, store (or the split-K
+// partial tile).
+// Every mbarrier wait is bounded; on expiry the kernel records GEMM_TIMEOUT in
+// *status (if given), still waits for its own MMAs with a bound, frees its TMEM and
+// returns.
+constexpr int TC_M = 128, TC_N = 128, TC_K = 64, TC_THREADS = 256;
+constexpr int TC_TMEM_COLS = 128;  // the 128 x 128 FP32 accumulator
+constexpr int TC_TILE_BYTES = TC_M * TC_K * 2;              // one operand tile (16 KB)
+// 2 stages x (A, B), reused by the epilogue as a padded 128 x 132 FP32 tile, + alignment
+// + barriers: at most 3 CTAs per SM, 3 x 128 TMEM columns
+constexpr int TC_EPI_LD = TC_N + 4;
+constexpr int TC_SMEM = TC_M * TC_EPI_LD * 4 + 1024 + 64;
+static_assert(TC_M * TC_EPI_LD * 4 >= 4 * TC_TILE_BYTES, "epilogue tile covers the operand stages");
+constexpr uint32_t GEMM_TIMEOUT = 1u << 8;
+constexpr int TC_SPIN = 1 << 22;
 
-// Registers of one 128 x 32 operand tile: 16 values per thread.
-// Operand X(r, k) = X[r sr + k sk], rows [r0, r0+128) of R, k in [k0, k0+32) of kend.
+// byte offset of element (r, k) of a 128 x 64 BF16 tile: rows of 128 B, 8-row atoms of
+// 1024 B, 16-byte chunk index XOR (row mod 8)
+__device__ __forceinline__ uint32_t sw128(int r, int k) {
+  const uint32_t lin = uint32_t(r) * 128u + uint32_t(k) * 2u;
+  return lin ^ (((lin >> 7) & 7u) << 4);
+}
+
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle, atoms of 8 rows x 128 B
+// (stride between 8-row groups 1024 B), version 1.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+  return uint64_t((saddr >> 4) & 0x3FFFu) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) |
+         (uint64_t(1) << 46) | (uint64_t(2) << 61);
+}
+
+// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, N = 128, M = 128
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(TC_N >> 3) << 17) |
+                              (uint32_t(TC_M >> 4) << 24);
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int i = 0; i < TC_SPIN; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (i > 64) __nanosleep(32);
+  }
+  return false;
+}
+
+// This thread's share of a 128 x 64 operand tile X(r, k) = X[r sr + k sk] (rows r0..,
+// k0..; zero outside R x kend): TC_V values, loaded into registers (tc_load) and stored
+// as BF16 into the swizzled shared-memory tile (tc_store).
+constexpr int TC_V = 128 * TC_K / TC_THREADS;  // 32 words (FP32 modes) or 16 (BF16 modes)
 template <int MODE>
-__device__ __forceinline__ void gload(float (&v)[16], const float* __restrict__ X, int64_t sr, int64_t sk, int r0,
-                                      int R, int k0, int kend) {
+__device__ __forceinline__ void tc_load(uint32_t (&v)[TC_V], const void* Xv, int64_t sr, int64_t sk, int r0, int R,
+                                        int k0, int kend) {
   const int tid = threadIdx.x;
-  if constexpr (MODE == LD_VK) {  // float4 along k: 128 rows x 8 quads
+  const float* __restrict__ X = static_cast<const float*>(Xv);
+  const __nv_bfloat16* __restrict__ Xh = static_cast<const __nv_bfloat16*>(Xv);
+  if constexpr (MODE == LD_VK) {  // float4 along k: 128 rows x 16 quads
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int f = tid + i * GB_THREADS, r = f >> 3, kq = (f & 7) * 4;
+    for (int i = 0; i < TC_V / 4; ++i) {
+      const int f = tid + i * TC_THREADS, r = f >> 4, kq = (f & 15) * 4;
       const int m = r0 + r, k = k0 + kq;
       float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
       if (m < R && k < kend) q = __ldg(reinterpret_cast<const float4*>(X + m * sr + k));
-      v[4 * i] = q.x, v[4 * i + 1] = q.y, v[4 * i + 2] = q.z, v[4 * i + 3] = q.w;
+      v[4 * i] = __float_as_uint(q.x), v[4 * i + 1] = __float_as_uint(q.y);
+      v[4 * i + 2] = __float_as_uint(q.z), v[4 * i + 3] = __float_as_uint(q.w);
     }
-  } else if constexpr (MODE == LD_VR) {  // float4 along the rows: 32 k x 32 quads
+  } else if constexpr (MODE == LD_VR) {  // float4 along the rows: 64 k x 32 row quads
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int f = tid + i * GB_THREADS, kk = f >> 5, rq = (f & 31) * 4;
+    for (int i = 0; i < TC_V / 4; ++i) {
+      const int f = tid + i * TC_THREADS, kk = f >> 5, rq = (f & 31) * 4;
       const int m = r0 + rq, k = k0 + kk;
       float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
       if (m < R && k < kend) q = __ldg(reinterpret_cast<const float4*>(X + m + k * sk));
+      v[4 * i] = __float_as_uint(q.x), v[4 * i + 1] = __float_as_uint(q.y);
+      v[4 * i + 2] = __float_as_uint(q.z), v[4 * i + 3] = __float_as_uint(q.w);
+    }
+  } else if constexpr (MODE == LD_BK) {  // 8 BF16 along k: 128 rows x 8 chunks
+#pragma unroll
+    for (int i = 0; i < TC_V / 8; ++i) {
+      const int f = tid + i * TC_THREADS, r = f >> 3, k8 = (f & 7) * 8;
+      const int m = r0 + r, k = k0 + k8;
+      uint4 q = make_uint4(0u, 0u, 0u, 0u);
+      if (m < R && k < kend) q = __ldg(reinterpret_cast<const uint4*>(Xh + m * sr + k));
       v[4 * i] = q.x, v[4 * i + 1] = q.y, v[4 * i + 2] = q.z, v[4 * i + 3] = q.w;
     }
-  } else {  // scalar, k fastest (rows r = f / 32)
+  } else if constexpr (MODE == LD_BR) {  // 8 BF16 along the rows: 64 k x 16 row octets
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int f = tid + i * GB_THREADS, r = f >> 5, kk = f & 31;
+    for (int i = 0; i < TC_V / 8; ++i) {
+      const int f = tid + i * TC_THREADS, kk = f >> 4, r8 = (f & 15) * 8;
+      const int m = r0 + r8, k = k0 + kk;
+      uint4 q = make_uint4(0u, 0u, 0u, 0u);
+      if (m < R && k < kend) q = __ldg(reinterpret_cast<const uint4*>(Xh + m + k * sk));
+      v[4 * i] = q.x, v[4 * i + 1] = q.y, v[4 * i + 2] = q.z, v[4 * i + 3] = q.w;
+    }
+  } else {  // scalar FP32, k fastest
+#pragma unroll
+    for (int i = 0; i < TC_V; ++i) {
+      const int f = tid + i * TC_THREADS, r = f >> 6, kk = f & 63;
       const int m = r0 + r, k = k0 + kk;
-      v[i] = (m < R && k < kend) ? X[m * sr + k * sk] : 0.f;
+      v[i] = __float_as_uint((m < R && k < kend) ? X[m * sr + k * sk] : 0.f);
     }
   }
 }
 
+__device__ __forceinline__ void st_bf16(char* p, float x) {
+  *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(x);
+}
+
 template <int MODE>
-__device__ __forceinline__ void gstore(__nv_bfloat16 (*S)[GB_P], const float (&v)[16]) {
+__device__ __forceinline__ void tc_store(char* tile, const uint32_t (&v)[TC_V]) {
   const int tid = threadIdx.x;
   if constexpr (MODE == LD_VK) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int f = tid + i * GB_THREADS, r = f >> 3, kq = (f & 7) * 4;
-      __nv_bfloat162 lo = __floats2bfloat162_rn(v[4 * i], v[4 * i + 1]);
-      __nv_bfloat162 hi = __floats2bfloat162_rn(v[4 * i + 2], v[4 * i + 3]);
+    for (int i = 0; i < TC_V / 4; ++i) {
+      const int f = tid + i * TC_THREADS, r = f >> 4, kq = (f & 15) * 4;
+      __nv_bfloat162 lo = __floats2bfloat162_rn(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1]));
+      __nv_bfloat162 hi = __floats2bfloat162_rn(__uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3]));
       uint2 w;
       w.x = *reinterpret_cast<uint32_t*>(&lo);
       w.y = *reinterpret_cast<uint32_t*>(&hi);
-      *reinterpret_cast<uint2*>(&S[r][kq]) = w;
+      *reinterpret_cast<uint2*>(tile + sw128(r, kq)) = w;
     }
   } else if constexpr (MODE == LD_VR) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int f = tid + i * GB_THREADS, kk = f >> 5, rq = (f & 31) * 4;
+    for (int i = 0; i < TC_V / 4; ++i) {
+      const int f = tid + i * TC_THREADS, kk = f >> 5, rq = (f & 31) * 4;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) S[rq + j][kk] = __float2bfloat16_rn(v[4 * i + j]);
+      for (int j = 0; j < 4; ++j) st_bf16(tile + sw128(rq + j, kk), __uint_as_float(v[4 * i + j]));
+    }
+  } else if constexpr (MODE == LD_BK) {  // one 16-byte chunk of a row: already BF16
+#pragma unroll
+    for (int i = 0; i < TC_V / 8; ++i) {
+      const int f = tid + i * TC_THREADS, r = f >> 3, k8 = (f & 7) * 8;
+      *reinterpret_cast<uint4*>(tile + sw128(r, k8)) = make_uint4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    }
+  } else if constexpr (MODE == LD_BR) {  // 8 rows of one k
+#pragma unroll
+    for (int i = 0; i < TC_V / 8; ++i) {
+      const int f = tid + i * TC_THREADS, kk = f >> 4, r8 = (f & 15) * 8;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t w = v[4 * i + j];
+        *reinterpret_cast<uint16_t*>(tile + sw128(r8 + 2 * j, kk)) = uint16_t(w & 0xFFFFu);
+        *reinterpret_cast<uint16_t*>(tile + sw128(r8 + 2 * j + 1, kk)) = uint16_t(w >> 16);
+      }
     }
   } else {
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int f = tid + i * GB_THREADS, r = f >> 5, kk = f & 31;
-      S[r][kk] = __float2bfloat16_rn(v[i]);
+    for (int i = 0; i < TC_V; ++i) {
+      const int f = tid + i * TC_THREADS, r = f >> 6, kk = f & 63;
+      st_bf16(tile + sw128(r, kk), __uint_as_float(v[i]));
     }
   }
 }
 
 template <int AM, int BM>
-__global__ void __launch_bounds__(GB_THREADS) k_gemm_bf16(GemmArgs g) {
-  __shared__ __align__(16) __nv_bfloat16 As[2][GB_M][GB_P];
-  __shared__ __align__(16) __nv_bfloat16 Bs[2][GB_N][GB_P];
-  const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
-  const int kbeg = blockIdx.z * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(GemmArgs g, uint32_t* status) {
+  extern __shared__ __align__(1024) char tc_smem_raw[];
+  // 1024-byte aligned operand stages, then two mbarriers and the TMEM address
+  char* base = tc_smem_raw + ((1024 - (reinterpret_cast<uintptr_t>(tc_smem_raw) & 1023)) & 1023);
+  // stage st: A tile at base + st * TILE, B tile at base + (2 + st) * TILE
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + TC_M * TC_EPI_LD * 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  const uint32_t bar0 = static_cast<uint32_t>(__cvta_generic_to_shared(bars));  // bar of stage st: bar0 + 8 st
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
-  const int gr = lane >> 2, t = lane & 3;
-  float acc[4][4][4];
+  const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TC_N;
+  const int kbeg = blockIdx.z * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
+  const int ntiles = max(0, (kend - kbeg + TC_K - 1) / TC_K);
+
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0 + 8) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {  // TMEM columns for the 128 x 128 FP32 accumulator
+    const uint32_t slot = static_cast<uint32_t>(__cvta_generic_to_shared(tmem_slot));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot), "n"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  bool ok = true;
+  int issued = 0;  // k-tiles whose MMAs were issued and committed
+  uint32_t va[TC_V], vb[TC_V];  // k-tile kt + 1, loading while k-tile kt is stored and multiplied
+  if (ntiles > 0) {
+    tc_load<AM>(va, g.A, g.sam, g.sak, m0, g.M, kbeg, kend);
+    tc_load<BM>(vb, g.B, g.sbn, g.sbk, n0, g.N, kbeg, kend);
+  }
+  for (int kt = 0; kt < ntiles; ++kt) {
+    const int st = kt & 1;
+    char* tA = base + st * TC_TILE_BYTES;
+    char* tB = base + (2 + st) * TC_TILE_BYTES;
+    // the MMAs of k-tile kt - 2 read this stage: wait for their commit
+    if (kt >= 2) ok = __syncthreads_and(mbar_wait(bar0 + 8 * st, uint32_t(((kt - 2) >> 1) & 1))) != 0;
+    if (!ok) break;  // an expiry (agreed by the whole CTA): stop issuing
+    tc_store<AM>(tA, va);
+    tc_store<BM>(tB, vb);
+    if (kt + 1 < ntiles) {
+      const int k1 = kbeg + (kt + 1) * TC_K;
+      tc_load<AM>(va, g.A, g.sam, g.sak, m0, g.M, k1, kend);
+      tc_load<BM>(vb, g.B, g.sbn, g.sbk, n0, g.N, k1, kend);
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic stores -> async proxy
+    __syncthreads();
+    issued = kt + 1;
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t a0 = static_cast<uint32_t>(__cvta_generic_to_shared(tA));
+      const uint32_t b0 = static_cast<uint32_t>(__cvta_generic_to_shared(tB));
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < TC_K / 16; ++j) {
+        const uint64_t ad = umma_desc(a0 + 32u * j), bd = umma_desc(b0 + 32u * j);
+        const uint32_t acc = (kt > 0 || j > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       bar0 + 8 * st)
+                   : "memory");
+    }
+  }
+  // the last commit covers every MMA issued before it (waited for, bounded, even after
+  // an expiry, so that no MMA still writes the TMEM that is freed below)
+  if (issued > 0) {
+    const int last = issued - 1;
+    const bool done = __syncthreads_and(mbar_wait(bar0 + 8 * (last & 1), uint32_t((last >> 1) & 1))) != 0;
+    ok = ok && done;
+  }
+  if (!ok && threadIdx.x == 0 && status) atomicOr(status, GEMM_TIMEOUT);
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+
+  // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows), columns 64 (w / 4)
+  // .. + 63, 16 per tcgen05.ld, into a padded FP32 tile in the (now idle) operand
+  // stages; then every warp writes whole rows (coalesced float4).
+  const int quarter = warp & 3, half = warp >> 2;
+  float* E = reinterpret_cast<float*>(base);
+  {
+    const int row = quarter * 32 + lane;
+#pragma unroll 1
+    for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
+      uint32_t r[16];
+      const uint32_t taddr = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(c0);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-  float va[16], vb[16];
-  int cur = 0;
-  if (kbeg < kend) {
-    gload<AM>(va, g.A, g.sam, g.sak, m0, g.M, kbeg, kend);
-    gload<BM>(vb, g.B, g.sbn, g.sbk, n0, g.N, kbeg, kend);
-    gstore<AM>(As[0], va);
-    gstore<BM>(Bs[0], vb);
+      for (int j = 0; j < 16; j += 4)
+        *reinterpret_cast<float4*>(E + row * TC_EPI_LD + c0 + j) =
+            ntiles > 0 ? make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                     __uint_as_float(r[j + 3]))
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
   }
   __syncthreads();
-  for (int k0 = kbeg; k0 < kend; k0 += GB_K) {
-    const bool more = k0 + GB_K < kend;
-    if (more) {
-      gload<AM>(va, g.A, g.sam, g.sak, m0, g.M, k0 + GB_K, kend);
-      gload<BM>(vb, g.B, g.sbn, g.sbk, n0, g.N, k0 + GB_K, kend);
-    }
-#pragma unroll
-    for (int kk = 0; kk < GB_K; kk += 16) {
-      uint32_t a[4][4], b[4][2];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int r = wm + i * 16 + gr;
-        a[i][0] = ld_pair(&As[cur][r][kk + 2 * t]);
-        a[i][1] = ld_pair(&As[cur][r + 8][kk + 2 * t]);
-        a[i][2] = ld_pair(&As[cur][r][kk + 2 * t + 8]);
-        a[i][3] = ld_pair(&As[cur][r + 8][kk + 2 * t + 8]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = wn + j * 8 + gr;
-        b[j][0] = ld_pair(&Bs[cur][c][kk + 2 * t]);
-        b[j][1] = ld_pair(&Bs[cur][c][kk + 2 * t + 8]);
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
+  if (ok) {
+    float* part = g.part ? g.part + int64_t(blockIdx.z) * g.M * g.N : nullptr;
+    float* dst = part ? part : g.C;
+    const int64_t ld = part ? g.N : g.ldc;
+    const bool vec = (ld % 4) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+    const float alpha = part ? 1.f : g.alpha, beta = part ? 0.f : g.beta;
+    const int qd = threadIdx.x & 31;  // float4 column of the row
+#pragma unroll 1
+    for (int rr = threadIdx.x >> 5; rr < TC_M; rr += TC_THREADS / 32) {
+      const int m = m0 + rr, n = n0 + 4 * qd;
+      if (m >= g.M || n >= g.N) continue;
+      const float4 v = *reinterpret_cast<const float4*>(E + rr * TC_EPI_LD + 4 * qd);
+      float* cp = dst + int64_t(m) * ld + n;
+      if (vec && n + 3 < g.N) {
+        float4 o = make_float4(alpha * v.x, alpha * v.y, alpha * v.z, alpha * v.w);
+        if (beta != 0.f) {
+          const float4 c = *reinterpret_cast<const float4*>(cp);
+          o.x += beta * c.x, o.y += beta * c.y, o.z += beta * c.z, o.w += beta * c.w;
+        }
+        *reinterpret_cast<float4*>(cp) = o;
+      } else {
+        const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-              "{%0,%1,%2,%3};\n"
-              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-              : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
-    }
-    if (more) {
-      gstore<AM>(As[cur ^ 1], va);
-      gstore<BM>(Bs[cur ^ 1], vb);
-    }
-    __syncthreads();
-    cur ^= 1;
-  }
-  float* part = g.part ? g.part + int64_t(blockIdx.z) * g.M * g.N : nullptr;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int m = m0 + wm + i * 16 + gr + (r >= 2 ? 8 : 0);
-        const int n = n0 + wn + j * 8 + 2 * t + (r & 1);
-        if (m < g.M && n < g.N) {
-          if (part) {
-            part[int64_t(m) * g.N + n] = acc[i][j][r];
-          } else {
-            float* cp = g.C + m * g.ldc + n;
-            *cp = g.alpha * acc[i][j][r] + (g.beta != 0.f ? g.beta * *cp : 0.f);
-          }
-        }
+          if (n + j < g.N) cp[j] = alpha * vv[j] + (beta != 0.f ? beta * cp[j] : 0.f);
       }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(TC_TMEM_COLS) : "memory");
 }
 
 // C = alpha * sum_z part[z] + beta * C, z in order
@@ -224,52 +378,78 @@ __global__ void k_gemm_reduce(const float* __restrict__ part, int splits, int M,
 }
 
 // Load mode of an operand X(r, k) = X[r sr + k sk] with R rows and K columns.
-static int load_mode(const float* X, int64_t sr, int64_t sk, int R, int K) {
+static int load_mode(const void* X, int64_t sr, int64_t sk, int R, int K, bool bf16) {
   const bool al = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  if (bf16) {
+    if (al && sk == 1 && sr % 8 == 0 && K % 8 == 0) return LD_BK;
+    if (al && sr == 1 && sk % 8 == 0 && R % 8 == 0) return LD_BR;
+    return -1;  // BF16 operands must be 8-element aligned along their unit-stride dimension
+  }
   if (al && sk == 1 && sr % 4 == 0 && K % 4 == 0) return LD_VK;
   if (al && sr == 1 && sk % 4 == 0 && R % 4 == 0) return LD_VR;
   return LD_SC;
 }
 
+template <int AM, int BM>
+static void launch_tc_one(dim3 grid, const GemmArgs& a, uint32_t* status, cudaStream_t s) {
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(k_gemm_tc<AM, BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    init = true;
+  }
+  k_gemm_tc<AM, BM><<<grid, TC_THREADS, TC_SMEM, s>>>(a, status);
+}
+
 template <int AM>
-static void launch_gemm_b(int bm, dim3 grid, const GemmArgs& a, cudaStream_t s) {
+static void launch_tc_b(int bm, dim3 grid, const GemmArgs& a, uint32_t* status, cudaStream_t s) {
   switch (bm) {
-    case LD_VK: k_gemm_bf16<AM, LD_VK><<<grid, GB_THREADS, 0, s>>>(a); break;
-    case LD_VR: k_gemm_bf16<AM, LD_VR><<<grid, GB_THREADS, 0, s>>>(a); break;
-    default: k_gemm_bf16<AM, LD_SC><<<grid, GB_THREADS, 0, s>>>(a);
+    case LD_VK: launch_tc_one<AM, LD_VK>(grid, a, status, s); break;
+    case LD_VR: launch_tc_one<AM, LD_VR>(grid, a, status, s); break;
+    case LD_BR: launch_tc_one<AM, LD_BR>(grid, a, status, s); break;
+    case LD_BK: launch_tc_one<AM, LD_BK>(grid, a, status, s); break;
+    default: launch_tc_one<AM, LD_SC>(grid, a, status, s);
   }
 }
 
-// scratch: optional float buffer for split-K partials (scratch_floats capacity).
-static void gemm(int M, int N, int K, const float* A, int64_t sam, int64_t sak, const float* B, int64_t sbk,
+// C = alpha op(A) op(B) + beta C on the tensor cores (tcgen05).  scratch: optional float
+// buffer for split-K partials (scratch_floats capacity); status: optional device word
+// that records a bounded wait's expiry.
+static int gemm(int M, int N, int K, const void* A, int64_t sam, int64_t sak, const void* B, int64_t sbk,
                  int64_t sbn, float* C, int64_t ldc, float alpha, float beta, cudaStream_t s,
-                 float* scratch = nullptr, int64_t scratch_floats = 0) {
-  if (M <= 0 || N <= 0) return;
+                 float* scratch = nullptr, int64_t scratch_floats = 0, uint32_t* status = nullptr,
+                 bool a_bf16 = false, bool b_bf16 = false) {
+  if (M <= 0 || N <= 0) return GRAFX_OK;
   GemmArgs a{M, N, K, 0, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta, nullptr};
-  const int tm = (M + GB_M - 1) / GB_M, tn = (N + GB_N - 1) / GB_N;
-  const int ktiles = std::max(1, (K + GB_K - 1) / GB_K);
+  const int tm = (M + TC_M - 1) / TC_M, tn = (N + TC_N - 1) / TC_N;
+  const int ktiles = std::max(1, (K + TC_K - 1) / TC_K);
   int splits = 1;
-  if (scratch && tm * tn < 2 * 148 && ktiles >= 8) {
-    splits = std::min((2 * 148 + tm * tn - 1) / (tm * tn), ktiles / 4);
+  if (scratch && tm * tn < 2 * 148 && ktiles >= 4) {
+    splits = std::min((2 * 148 + tm * tn - 1) / (tm * tn), ktiles / 2);
     splits = int(std::min<int64_t>(splits, scratch_floats / (int64_t(M) * N)));
     splits = std::max(splits, 1);
   }
   const int kt_per = (ktiles + splits - 1) / splits;
-  a.kchunk = kt_per * GB_K;
+  a.kchunk = kt_per * TC_K;
   splits = (ktiles + kt_per - 1) / kt_per;
   if (splits > 1) a.part = scratch;
   dim3 grid(tn, tm, splits);
-  const int am = load_mode(A, sam, sak, M, K), bm = load_mode(B, sbn, sbk, N, K);
+  const int am = load_mode(A, sam, sak, M, K, a_bf16), bm = load_mode(B, sbn, sbk, N, K, b_bf16);
+  if (am < 0 || bm < 0 || am == LD_BR)
+    return fail(GRAFX_ESHAPE, "BF16 GEMM operand not 8-element aligned along its unit-stride dimension");
+  // the BF16 modes used by the network: A along k (im2col rows), B along n (im2col as the
+  // weight-gradient operand)
   switch (am) {
-    case LD_VK: launch_gemm_b<LD_VK>(bm, grid, a, s); break;
-    case LD_VR: launch_gemm_b<LD_VR>(bm, grid, a, s); break;
-    default: launch_gemm_b<LD_SC>(bm, grid, a, s);
+    case LD_VK: launch_tc_b<LD_VK>(bm, grid, a, status, s); break;
+    case LD_VR: launch_tc_b<LD_VR>(bm, grid, a, status, s); break;
+    case LD_BK: launch_tc_b<LD_BK>(bm, grid, a, status, s); break;
+    default: launch_tc_b<LD_SC>(bm, grid, a, status, s);
   }
   if (splits > 1) {
     const int64_t MN = int64_t(M) * N;
     k_gemm_reduce<<<int(std::min<int64_t>((MN + 255) / 256, 148 * 8)), 256, 0, s>>>(scratch, splits, M, N, C, ldc,
                                                                                      alpha, beta);
   }
+  return GRAFX_OK;
 }
 
 // ------------------------------------------------------------------ elementwise pieces
@@ -278,20 +458,21 @@ __device__ __forceinline__ float gelu_d(float x) {
   return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
 }
 
-// im2col: A[(b,t)][(c,k)] = H(b, c, t+k-2), zero outside [0, T).  H is [B][T][C]
-// (time-major activations) or, for the features, [B][C][T] (feat_layout = 1).  One
-// thread per (b, t, c) writes its 5 taps.
-__global__ void k_im2col(const float* __restrict__ H, int B, int C, int feat_layout, float* __restrict__ A) {
+// im2col: A[(b,t)][(c,k)] = H(b, c, t+k-2), zero outside [0, T), stored as BF16 (the
+// products round their operands to BF16 anyway).  H is [B][T][C] (time-major
+// activations) or, for the features, [B][C][T] (feat_layout = 1).  One thread per
+// (b, t, c) writes its 5 taps.
+__global__ void k_im2col(const float* __restrict__ H, int B, int C, int feat_layout, __nv_bfloat16* __restrict__ A) {
   const int n = B * WS_T * C;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int c = i % C, bt = i / C, t = bt % WS_T, b = bt / WS_T;
-    float* o = A + int64_t(i) * WS_KW;
+    __nv_bfloat16* o = A + int64_t(i) * WS_KW;
 #pragma unroll
     for (int k = 0; k < WS_KW; ++k) {
       const int ts = t + k - 2;
       float v = 0.f;
       if (ts >= 0 && ts < WS_T) v = feat_layout ? H[(b * C + c) * WS_T + ts] : H[(b * WS_T + ts) * C + c];
-      o[k] = v;
+      o[k] = __float2bfloat16_rn(v);
     }
   }
 }
@@ -411,6 +592,19 @@ __global__ void __launch_bounds__(1024) k_ws_mse(const float* __restrict__ out, 
   if (threadIdx.x == 0) *loss = v[0];
 }
 
+// BF16 copies of the weight matrices, each at a 16-byte aligned offset of the shadow
+// buffer (the products read them as 8-element BF16 loads)
+constexpr int WB_MATS = 4 + 3 * WS_NHEAD;
+struct WeightCopies {
+  int64_t src[WB_MATS], dst[WB_MATS], n[WB_MATS];
+};
+
+__global__ void k_weights_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, WeightCopies cp) {
+  const int j = blockIdx.y;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < cp.n[j]; i += int64_t(gridDim.x) * blockDim.x)
+    wb[cp.dst[j] + i] = __float2bfloat16_rn(w[cp.src[j] + i]);
+}
+
 // ------------------------------------------------------------------ log-mel features
 // Frames 2q and 2q+1 of a row packed as the real and imaginary parts of one complex
 // 2048-point FFT; writes ln(mel + 1e-5) of both into fr[row][frame][128].
@@ -506,6 +700,8 @@ struct grafx_wsnet {
   int64_t off[4][2];          // conv weight / bias offsets in the flat buffer
   int64_t hoff[WS_NHEAD][6];  // per head: w1 b1 w2 b2 w3 b3
   int64_t n_params = 0;
+  WeightCopies wcp;           // BF16 shadow: conv w (4), then per head w1, w2, w3
+  int64_t wb_elems = 0;
   int32_t max_batch = 0;
   char* ws = nullptr;         // bound workspace
   size_t ws_bytes = 0;
@@ -517,8 +713,8 @@ struct grafx_wsnet {
 namespace {
 
 struct WsNetLayout {
-  size_t melw, melrng, tw, ptw;
-  size_t im2col, z[4], h[4], e, a1, g1, a2, g2, dbig, dsmall, dh, cspart, frames, total;
+  size_t melw, melrng, tw, ptw, status;
+  size_t im2col, z[4], h[4], e, a1, g1, a2, g2, dbig, dsmall, dh, cspart, wbf, frames, total;
 };
 
 // frame_floats: log-mel frame scratch (rows x frames x 128) in floats
@@ -535,6 +731,7 @@ WsNetLayout ws_layout(const grafx_wsnet* n, int64_t frame_floats) {
   L.melrng = take(sizeof(int2_) * n->mel_rng.size());
   L.tw = take(sizeof(float2_) * n->tw.size());
   L.ptw = take(sizeof(float2_) * n->ptw.size());
+  L.status = take(sizeof(uint32_t));
   L.im2col = take(4 * rows * WS_IN * WS_KW);
   for (int l = 0; l < 4; ++l) {
     L.z[l] = take(4 * rows * WS_CH);
@@ -549,6 +746,7 @@ WsNetLayout ws_layout(const grafx_wsnet* n, int64_t frame_floats) {
   L.dsmall = take(4 * B * WS_HID * 2);
   L.dh = take(4 * (B * WS_CH + rows * WS_CH));
   L.cspart = take(4 * size_t(CS_SPLIT) * WS_HID);
+  L.wbf = take(2 * size_t(n->wb_elems));
   L.frames = take(4 * size_t(std::max<int64_t>(frame_floats, 1)));
   L.total = o;
   return L;
@@ -601,6 +799,22 @@ int grafx_ws_create(int32_t max_batch, int32_t sample_rate, grafx_wsnet** out) {
     }
   }
   n->n_params = o;
+  {
+    int64_t d = 0;
+    auto add = [&](int j, int64_t src, int64_t cnt) {
+      n->wcp.src[j] = src;
+      n->wcp.dst[j] = d;
+      n->wcp.n[j] = cnt;
+      d += (cnt + 7) / 8 * 8;
+    };
+    for (int l = 0; l < 4; ++l) add(l, n->off[l][0], int64_t(WS_CH) * cin[l] * WS_KW);
+    for (int h = 0; h < WS_NHEAD; ++h) {
+      add(4 + 3 * h, n->hoff[h][0], int64_t(WS_HID) * WS_CH);
+      add(5 + 3 * h, n->hoff[h][2], int64_t(WS_HID) * WS_HID);
+      add(6 + 3 * h, n->hoff[h][4], int64_t(kHeadOut[h]) * WS_HID);
+    }
+    n->wb_elems = d;
+  }
   // HTK-mel triangles over the one-sided bins of a 2048-point frame, edges equally
   // spaced in mel between 0 and fs/2
   auto hz2mel = [](double f) { return 2595.0 * std::log10(1.0 + f / 700.0); };
@@ -658,6 +872,7 @@ int grafx_ws_bind(grafx_wsnet* n, void* ws, size_t bytes, void* stream) {
   cudaMemcpyAsync(w + L.melrng, n->mel_rng.data(), sizeof(int2_) * n->mel_rng.size(), cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(w + L.tw, n->tw.data(), sizeof(float2_) * n->tw.size(), cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(w + L.ptw, n->ptw.data(), sizeof(float2_) * n->ptw.size(), cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(w + L.status, 0, sizeof(uint32_t), s);
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(GRAFX_ECUDA, cudaGetErrorString(e));
   n->ws = w;
@@ -695,16 +910,22 @@ int grafx_ws_forward(grafx_wsnet* n, const float* weights, const float* feats, c
   if (int rc = check_heads(head_count, B)) return rc;
   WsNetLayout L = ws_layout(n, 0);
   auto F = [&](size_t off) { return reinterpret_cast<float*>(n->ws + off); };
+  uint32_t* st = reinterpret_cast<uint32_t*>(n->ws + L.status);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int rows = B * WS_T;
   const int64_t dbig_floats = int64_t(n->max_batch) * WS_T * WS_CH * WS_KW;
   const int cin[4] = {WS_IN, WS_CH, WS_CH, WS_CH};
+  __nv_bfloat16* wbf = reinterpret_cast<__nv_bfloat16*>(n->ws + L.wbf);
+  auto WB = [&](int j) { return wbf + n->wcp.dst[j]; };  // BF16 weight matrix j
+  k_weights_bf16<<<dim3(64, WB_MATS), 256, 0, s>>>(weights, wbf, n->wcp);
   for (int l = 0; l < 4; ++l) {
     const float* src = l == 0 ? feats : F(L.h[l - 1]);
     const int K = cin[l] * WS_KW;
-    k_im2col<<<grid1(int64_t(rows) * cin[l]), 256, 0, s>>>(src, B, cin[l], l == 0, F(L.im2col));
-    gemm(rows, WS_CH, K, F(L.im2col), K, 1, weights + n->off[l][0], 1, K, F(L.z[l]), WS_CH, 1.f, 0.f, s,
-         F(L.dbig), dbig_floats);
+    __nv_bfloat16* a2c = reinterpret_cast<__nv_bfloat16*>(F(L.im2col));
+    k_im2col<<<grid1(int64_t(rows) * cin[l]), 256, 0, s>>>(src, B, cin[l], l == 0, a2c);
+    if (int rc = gemm(rows, WS_CH, K, a2c, K, 1, WB(l), 1, K, F(L.z[l]), WS_CH, 1.f, 0.f, s, F(L.dbig), dbig_floats,
+                      st, true, true))
+      return rc;
     k_bias_act<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(F(L.z[l]), weights + n->off[l][1], F(L.h[l]), rows, WS_CH,
                                                               WS_CH, 1);
   }
@@ -717,12 +938,18 @@ int grafx_ws_forward(grafx_wsnet* n, const float* weights, const float* feats, c
     const int64_t* o = n->hoff[h];
     float *a1 = F(L.a1) + r0 * WS_HID, *g1 = F(L.g1) + r0 * WS_HID;
     float *a2 = F(L.a2) + r0 * WS_HID, *g2 = F(L.g2) + r0 * WS_HID;
-    gemm(nb, WS_HID, WS_CH, F(L.e) + r0 * WS_CH, WS_CH, 1, weights + o[0], 1, WS_CH, a1, WS_HID, 1.f, 0.f, s);
+    if (int rc = gemm(nb, WS_HID, WS_CH, F(L.e) + r0 * WS_CH, WS_CH, 1, WB(4 + 3 * h), 1, WS_CH, a1, WS_HID, 1.f,
+                      0.f, s, nullptr, 0, st, false, true))
+      return rc;
     k_bias_act<<<grid1(int64_t(nb) * WS_HID), 256, 0, s>>>(a1, weights + o[1], g1, nb, WS_HID, WS_HID, 1);
-    gemm(nb, WS_HID, WS_HID, g1, WS_HID, 1, weights + o[2], 1, WS_HID, a2, WS_HID, 1.f, 0.f, s);
+    if (int rc = gemm(nb, WS_HID, WS_HID, g1, WS_HID, 1, WB(5 + 3 * h), 1, WS_HID, a2, WS_HID, 1.f, 0.f, s, nullptr,
+                      0, st, false, true))
+      return rc;
     k_bias_act<<<grid1(int64_t(nb) * WS_HID), 256, 0, s>>>(a2, weights + o[3], g2, nb, WS_HID, WS_HID, 1);
     float* ob = out + int64_t(r0) * WS_OUTMAX;
-    gemm(nb, kHeadOut[h], WS_HID, g2, WS_HID, 1, weights + o[4], 1, WS_HID, ob, WS_OUTMAX, 1.f, 0.f, s);
+    if (int rc = gemm(nb, kHeadOut[h], WS_HID, g2, WS_HID, 1, WB(6 + 3 * h), 1, WS_HID, ob, WS_OUTMAX, 1.f, 0.f, s,
+                      nullptr, 0, st, false, true))
+      return rc;
     k_bias_act<<<grid1(int64_t(nb) * kHeadOut[h]), 256, 0, s>>>(ob, weights + o[5], nullptr, nb, kHeadOut[h],
                                                                   WS_OUTMAX, 0);
     r0 += nb;
@@ -738,8 +965,12 @@ int grafx_ws_backward(grafx_wsnet* n, const float* weights, const float* feats, 
   if (int rc = check_heads(head_count, B)) return rc;
   WsNetLayout L = ws_layout(n, 0);
   auto F = [&](size_t off) { return reinterpret_cast<float*>(n->ws + off); };
+  uint32_t* st = reinterpret_cast<uint32_t*>(n->ws + L.status);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaMemsetAsync(d_weights, 0, sizeof(float) * size_t(n->n_params), s);
+  __nv_bfloat16* wbf = reinterpret_cast<__nv_bfloat16*>(n->ws + L.wbf);
+  auto WB = [&](int j) { return wbf + n->wcp.dst[j]; };  // BF16 weight matrix j
+  k_weights_bf16<<<dim3(64, WB_MATS), 256, 0, s>>>(weights, wbf, n->wcp);
   float* de = F(L.dh);                                 // [B][128]
   float* dh = F(L.dh) + size_t(n->max_batch) * WS_CH;  // [rows][128]
   int r0 = 0;
@@ -754,19 +985,31 @@ int grafx_ws_backward(grafx_wsnet* n, const float* weights, const float* feats, 
     const float *a1 = F(L.a1) + r0 * WS_HID, *g1 = F(L.g1) + r0 * WS_HID;
     const float *a2 = F(L.a2) + r0 * WS_HID, *g2 = F(L.g2) + r0 * WS_HID;
     // dW3 = dO^T g2, db3 = column sums of dO, da2 = (dO W3) gelu'(a2)
-    gemm(no, WS_HID, nb, dO, 1, WS_OUTMAX, g2, WS_HID, 1, d_weights + o[4], WS_HID, 1.f, 0.f, s);
+    if (int rc = gemm(no, WS_HID, nb, dO, 1, WS_OUTMAX, g2, WS_HID, 1, d_weights + o[4], WS_HID, 1.f, 0.f, s,
+                      nullptr, 0, st))
+      return rc;
     colsum(dO, nb, no, WS_OUTMAX, d_weights + o[5], F(L.cspart), s);
-    gemm(nb, WS_HID, no, dO, WS_OUTMAX, 1, weights + o[4], WS_HID, 1, da2, WS_HID, 1.f, 0.f, s);
+    if (int rc = gemm(nb, WS_HID, no, dO, WS_OUTMAX, 1, WB(6 + 3 * h), WS_HID, 1, da2, WS_HID, 1.f, 0.f, s, nullptr,
+                      0, st, false, true))
+      return rc;
     k_gelu_bwd<<<grid1(int64_t(nb) * WS_HID), 256, 0, s>>>(da2, a2, int64_t(nb) * WS_HID);
     // dW2 = da2^T g1, db2, da1 = (da2 W2) gelu'(a1)
-    gemm(WS_HID, WS_HID, nb, da2, 1, WS_HID, g1, WS_HID, 1, d_weights + o[2], WS_HID, 1.f, 0.f, s);
+    if (int rc = gemm(WS_HID, WS_HID, nb, da2, 1, WS_HID, g1, WS_HID, 1, d_weights + o[2], WS_HID, 1.f, 0.f, s,
+                      nullptr, 0, st))
+      return rc;
     colsum(da2, nb, WS_HID, WS_HID, d_weights + o[3], F(L.cspart), s);
-    gemm(nb, WS_HID, WS_HID, da2, WS_HID, 1, weights + o[2], WS_HID, 1, da1, WS_HID, 1.f, 0.f, s);
+    if (int rc = gemm(nb, WS_HID, WS_HID, da2, WS_HID, 1, WB(5 + 3 * h), WS_HID, 1, da1, WS_HID, 1.f, 0.f, s,
+                      nullptr, 0, st, false, true))
+      return rc;
     k_gelu_bwd<<<grid1(int64_t(nb) * WS_HID), 256, 0, s>>>(da1, a1, int64_t(nb) * WS_HID);
     // dW1 = da1^T e, db1, de = da1 W1
-    gemm(WS_HID, WS_CH, nb, da1, 1, WS_HID, F(L.e) + r0 * WS_CH, WS_CH, 1, d_weights + o[0], WS_CH, 1.f, 0.f, s);
+    if (int rc = gemm(WS_HID, WS_CH, nb, da1, 1, WS_HID, F(L.e) + r0 * WS_CH, WS_CH, 1, d_weights + o[0], WS_CH, 1.f,
+                      0.f, s, nullptr, 0, st))
+      return rc;
     colsum(da1, nb, WS_HID, WS_HID, d_weights + o[1], F(L.cspart), s);
-    gemm(nb, WS_CH, WS_HID, da1, WS_HID, 1, weights + o[0], WS_CH, 1, de + r0 * WS_CH, WS_CH, 1.f, 0.f, s);
+    if (int rc = gemm(nb, WS_CH, WS_HID, da1, WS_HID, 1, WB(4 + 3 * h), WS_CH, 1, de + r0 * WS_CH, WS_CH, 1.f, 0.f,
+                      s, nullptr, 0, st, false, true))
+      return rc;
     r0 += nb;
   }
   const int rows = B * WS_T;
@@ -778,13 +1021,17 @@ int grafx_ws_backward(grafx_wsnet* n, const float* weights, const float* feats, 
     // dz = dh gelu'(z); dW = dz^T im2col(input); db = column sums of dz
     k_gelu_bwd<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(dh, F(L.z[l]), int64_t(rows) * WS_CH);
     const float* src = l == 0 ? feats : F(L.h[l - 1]);
-    k_im2col<<<grid1(int64_t(rows) * cin[l]), 256, 0, s>>>(src, B, cin[l], l == 0, F(L.im2col));
-    gemm(WS_CH, K, rows, dh, 1, WS_CH, F(L.im2col), K, 1, d_weights + n->off[l][0], K, 1.f, 0.f, s, F(L.dbig),
-         dbig_floats);
+    __nv_bfloat16* a2c = reinterpret_cast<__nv_bfloat16*>(F(L.im2col));
+    k_im2col<<<grid1(int64_t(rows) * cin[l]), 256, 0, s>>>(src, B, cin[l], l == 0, a2c);
+    if (int rc = gemm(WS_CH, K, rows, dh, 1, WS_CH, a2c, K, 1, d_weights + n->off[l][0], K, 1.f, 0.f, s, F(L.dbig),
+                      dbig_floats, st, false, true))
+      return rc;
     colsum(dh, rows, WS_CH, WS_CH, d_weights + n->off[l][1], F(L.cspart), s);
     if (l > 0) {
       // d im2col = dz W, then its adjoint scatter gives dh of the previous layer
-      gemm(rows, K, WS_CH, dh, WS_CH, 1, weights + n->off[l][0], K, 1, F(L.dbig), K, 1.f, 0.f, s);
+      if (int rc = gemm(rows, K, WS_CH, dh, WS_CH, 1, WB(l), K, 1, F(L.dbig), K, 1.f, 0.f, s, nullptr, 0, st, false,
+                        true))
+        return rc;
       k_col2im<<<grid1(int64_t(rows) * cin[l]), 256, 0, s>>>(F(L.dbig), B, cin[l], dh);
     }
   }
@@ -803,11 +1050,27 @@ int grafx_gemm_bf16(int32_t M, int32_t N, int32_t K, const float* A, int64_t sam
                     int64_t sbk, int64_t sbn, float* C, int64_t ldc, float alpha, float beta, float* scratch,
                     int64_t scratch_floats, void* stream) {
   if (!A || !B || !C) return fail(GRAFX_EINVAL, "null argument");
-  if (M < 0 || N < 0 || K < 0 || ldc < N || M > 65535 * GB_M || scratch_floats < 0)
+  if (M < 0 || N < 0 || K < 0 || ldc < N || M > 65535 * TC_M || scratch_floats < 0)
     return fail(GRAFX_ESHAPE, "bad GEMM shape");
-  gemm(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta, static_cast<cudaStream_t>(stream), scratch,
-       scratch ? scratch_floats : 0);
+  if (int rc = gemm(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta, static_cast<cudaStream_t>(stream),
+                    scratch, scratch ? scratch_floats : 0))
+    return rc;
   return cuda_status();
+}
+
+int grafx_ws_sync_status(grafx_wsnet* n, void* stream) {
+  if (!n || !n->ws) return fail(GRAFX_ESTATE, "workspace not bound (grafx_ws_bind)");
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(GRAFX_ECUDA, cudaGetErrorString(e));
+  const WsNetLayout L = ws_layout(n, 0);
+  uint32_t st = 0;
+  e = cudaMemcpy(&st, n->ws + L.status, sizeof(st), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(GRAFX_ECUDA, cudaGetErrorString(e));
+  if (st) {
+    cudaMemset(n->ws + L.status, 0, sizeof(st));
+    return fail(GRAFX_ETIMEOUT, "a bounded tensor-core wait expired");
+  }
+  return GRAFX_OK;
 }
 
 }  // extern "C"

@@ -175,7 +175,7 @@ def _gpu(gx, torch, flat, feats, counts, d_out):
     st = gx._stream(torch, W.device)
     net.forward_raw(W, Fd, counts, out, st)
     net.backward_raw(W, Fd, counts, torch.tensor(d_out, dtype=torch.float32, device="cuda"), dW, st)
-    torch.cuda.synchronize()
+    net.sync_status(st)
     return out.cpu().numpy().astype(np.float64), dW.cpu().numpy().astype(np.float64)
 
 
