@@ -276,6 +276,16 @@ int grafx_adam_step_dev(float* theta, float* m, float* v, const float* grad_para
 int grafx_params_to_theta(const float* param, const int8_t* codes, int32_t cols, int64_t n, float* theta,
                           void* stream);
 
+/* ---------------------------------------------------------------- failure detection
+ * The paper has no counterpart; this exists so that the bounded device waits can be
+ * tested without hanging a GPU.  One warp polls the device word *flag at most `limit`
+ * times (1 <= limit <= 4194304, each poll followed by a short sleep), exactly like a
+ * look-back of the compressor scan: if the word's upper half is nonzero, *value = the
+ * float in its lower half; otherwise the wait expires, ST_TIMEOUT (1) is OR-ed into the
+ * device word *status and *value = 0.  Asynchronous on `stream`. */
+int grafx_selftest_bounded_wait(const unsigned long long* flag, uint32_t* status, int32_t limit, float* value,
+                                void* stream);
+
 /* ---------------------------------------------------------------- learned warm-start
  * The paper motivates estimating processor parameters with a trained network
  * (Sec. 1) and leaves the estimator open; this is the library's own: it predicts the

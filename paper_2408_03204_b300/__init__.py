@@ -89,6 +89,7 @@ SIGNATURES = {
     "grafx_step_graph_launches": (ctypes.c_int, [_P, _I32P]),
     "grafx_step_graph_destroy": (ctypes.c_int, [_P]),
     "grafx_node_inputs": (ctypes.c_int, [_P, _F, _F, _I32P, _I32, _F, _I64, _P]),
+    "grafx_selftest_bounded_wait": (ctypes.c_int, [_P, _P, _I32, _F, _P]),
     "grafx_ws_create": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_P)]),
     "grafx_ws_destroy": (ctypes.c_int, [_P]),
     "grafx_ws_param_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),

@@ -64,10 +64,12 @@ __device__ __forceinline__ unsigned long long pack_flag(unsigned st, float v) {
   return (static_cast<unsigned long long>(st) << 32) | __float_as_uint(v);
 }
 
-// Wait (bounded) for flag j; returns status (1 aggregate, 2 inclusive) and value.
-__device__ __forceinline__ unsigned wait_flag(const DevCtx& c, int j, float* val) {
-  volatile unsigned long long* f = c.flags + j;
-  for (int i = 0; i < SPIN_LIMIT; ++i) {
+// Wait (bounded by `limit` polls) for the flag word *f; returns its status (1 aggregate,
+// 2 inclusive) and value, or on expiry records ST_TIMEOUT in *status and returns 2 with
+// a zero value.
+__device__ __forceinline__ unsigned wait_word(const unsigned long long* fp, uint32_t* status, int limit, float* val) {
+  volatile const unsigned long long* f = fp;
+  for (int i = 0; i < limit; ++i) {
     unsigned long long w = *f;
     unsigned st = unsigned(w >> 32);
     if (st) {
@@ -76,9 +78,21 @@ __device__ __forceinline__ unsigned wait_flag(const DevCtx& c, int j, float* val
     }
     __nanosleep(64);
   }
-  set_status(c, ST_TIMEOUT);
+  atomicOr(status, ST_TIMEOUT);
   *val = 0.f;
   return 2;
+}
+
+// Wait (bounded) for the look-back flag of item j.
+__device__ __forceinline__ unsigned wait_flag(const DevCtx& c, int j, float* val) {
+  return wait_word(c.flags + j, c.status, SPIN_LIMIT, val);
+}
+
+// One warp polls `flag` as a look-back does (failure-detection self-test).
+__global__ void k_wait_selftest(const unsigned long long* flag, uint32_t* status, int limit, float* value) {
+  float v = 0.f;
+  const unsigned st = wait_word(flag, status, limit, &v);
+  if (threadIdx.x == 0) *value = st == 2 ? v : -1.f;
 }
 
 __device__ __forceinline__ void publish(const DevCtx& c, int j, unsigned st, float v) {
@@ -612,4 +626,17 @@ extern "C" int grafx_compressor_forward_noalloc(const float* u, int64_t len, int
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(GRAFX_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
   return GRAFX_OK;
+}
+
+// Failure-detection self-test of the bounded look-back wait: one warp polls *flag at most
+// `limit` times.  A flag that nothing sets makes the wait expire: ST_TIMEOUT is OR-ed into
+// *status and *value = 0; a flag already set to (2 << 32 | bits of v) gives *value = v.
+extern "C" int grafx_selftest_bounded_wait(const unsigned long long* flag, uint32_t* status, int32_t limit,
+                                           float* value, void* stream) {
+  using namespace grafx;
+  if (!flag || !status || !value) return fail(GRAFX_EINVAL, "null argument");
+  if (limit < 1 || limit > SPIN_LIMIT) return fail(GRAFX_EINVAL, "limit out of range");
+  k_wait_selftest<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(flag, status, limit, value);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GRAFX_OK : fail(GRAFX_ECUDA, cudaGetErrorString(e));
 }

@@ -133,6 +133,35 @@ class Fit:
             else:
                 self._body()
 
+    def save(self, path):
+        """Write the fit's state (theta, Adam moments and step of every type) to `path`."""
+        from .state import save_state
+        self.stream.synchronize()
+        tensors = {}
+        for t in self.P:
+            tensors[f"theta.{t}"], tensors[f"m.{t}"], tensors[f"v.{t}"] = self.theta[t], self.m[t], self.v[t]
+        tensors["step"] = self.step_dev
+        save_state(path, tensors, {"kind": "fit", "t": self.t, "lr": self.lr, "betas": [self.b1, self.b2],
+                                   "eps": self.eps, "types": sorted(int(t) for t in self.P)})
+
+    def load(self, path):
+        """Resume from a file written by save() for the same plan: theta, moments and step
+        are restored and the parameters set to map(theta)."""
+        from .state import load_state
+        tensors, meta = load_state(path, self.src.device)
+        if meta.get("kind") != "fit" or sorted(meta["types"]) != sorted(int(t) for t in self.P):
+            raise ValueError(f"{path}: not a fit state for these parameter types")
+        with self.torch.cuda.stream(self.stream):
+            for t in self.P:
+                for name, dst in (("theta", self.theta[t]), ("m", self.m[t]), ("v", self.v[t])):
+                    src = tensors[f"{name}.{t}"]
+                    if src.shape != dst.shape:
+                        raise ValueError(f"{path}: {name}.{t} has shape {tuple(src.shape)}, want {tuple(dst.shape)}")
+                    dst.copy_(src)
+            self.step_dev.copy_(tensors["step"])
+        self.t = int(meta["t"])
+        self._apply_map()
+
     def current_loss(self):
         """Loss of the parameters before the last step (synchronises the stream)."""
         self.stream.synchronize()

@@ -115,6 +115,24 @@ class WarmStart:
         self.stream = torch.cuda.current_stream(self.device)
         self.st = _stream_of(self.stream)
 
+    # ---------------------------------------------------------------- state
+    def save(self, path):
+        """Weights, Adam moments and step, target standardisation (resumable training)."""
+        from .state import save_state
+        self.stream.synchronize()
+        save_state(path, {"W": self.W, "m": self.m, "v": self.v, "mu": self.mu, "sd": self.sd},
+                   {"kind": "warmstart", "step": self.step_no, "lr": self.lr, "n_params": int(self.W.numel())})
+
+    def load(self, path):
+        from .state import load_state
+        tensors, meta = load_state(path, self.device)
+        if meta.get("kind") != "warmstart" or meta.get("n_params") != int(self.W.numel()):
+            raise ValueError(f"{path}: not a warm-start state of this network")
+        for name in ("W", "m", "v", "mu", "sd"):
+            getattr(self, name).copy_(tensors[name])
+        self.step_no = int(meta["step"])
+        self.lr = float(meta["lr"])
+
     # ---------------------------------------------------------------- features
     def features(self, batch, sources, target, neutral):
         """feats [n, 256, 32] for the batch's processor nodes (sorted by head): node input

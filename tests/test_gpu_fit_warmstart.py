@@ -133,3 +133,45 @@ def env_tuple():
     from paper_2408_03204_b300 import fit as gfit
     from paper_2408_03204_b300 import warmstart as gws
     return gx, torch, gfit, gws
+
+
+def test_fit_resume_from_saved_state_is_bitwise_identical(env, tmp_path):
+    gx, torch, gfit, gws = env
+    ws = gws.WarmStart(max_batch=256, max_rows=256, max_len=8192)
+    batch, src, hidden, target, neutral = _small_batch(gws, ws, seed=4)
+    P = {t: p.clone() for t, p in neutral.items()}
+    f = gfit.Fit(batch.plan, src, target, P, lr=1e-2)
+    for _ in range(10):
+        f.step()
+    path = str(tmp_path / "fit.bin")
+    f.save(path)
+    ref = []
+    for _ in range(10):
+        f.step()
+        ref.append(f.current_loss())
+    P2 = {t: p.clone() for t, p in neutral.items()}
+    f2 = gfit.Fit(batch.plan, src, target, P2, lr=1e-2)
+    f2.load(path)
+    got = []
+    for _ in range(10):
+        f2.step()
+        got.append(f2.current_loss())
+    assert got == ref
+
+
+def test_warmstart_resume_from_saved_state(env, tmp_path):
+    gx, torch, gfit, gws = env
+    a = gws.WarmStart(max_batch=64, max_rows=64, max_len=8192, seed=3)
+    feats = (-6 + 3 * torch.randn(32, 256, 32, device="cuda")).contiguous()
+    types = sorted([3] * 8 + [5] * 12 + [6] * 12, key=lambda t: gws.HEAD_OF[t])
+    tgt = torch.randn(32, 176, device="cuda")
+    for _ in range(3):
+        a.train_step(feats, tgt, types)
+    path = str(tmp_path / "ws.bin")
+    a.save(path)
+    la = [float(a.train_step(feats, tgt, types)) for _ in range(3)]
+    b = gws.WarmStart(max_batch=64, max_rows=64, max_len=8192, seed=99)
+    b.load(path)
+    lb = [float(b.train_step(feats, tgt, types)) for _ in range(3)]
+    assert la == lb
+    assert torch.equal(a.W, b.W)
