@@ -1,9 +1,12 @@
 // C ABI (include/grafx.h): graph building, planning, device binding, and the step
 // loops of Algorithm 1 (render) and its reverse (backprop), plus the loss.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "kernels.h"
 #include "plan.h"
@@ -321,12 +324,23 @@ int grafx_bind_reverb_noise(grafx_plan* p, const float* dev, int64_t n) {
 }
 
 // Forward steps [first, last) (already validated); returns the number of launches.
+// NVTX range per schedule step (visible in a profiler's timeline; no cost otherwise)
+struct StepRange {
+  StepRange(const char* dir, int k, int type) {
+    char name[48];
+    std::snprintf(name, sizeof(name), "grafx %s step %d type %d", dir, k, type);
+    nvtxRangePushA(name);
+  }
+  ~StepRange() { nvtxRangePop(); }
+};
+
 static int render_range(grafx_plan* p, const float* sources, float* out, int32_t first, int32_t last,
                         cudaStream_t s) {
   DevCtx c = make_ctx(p, sources, out, nullptr, nullptr);
   int launches = 0;
   for (int k = first; k < last; ++k) {
     const StepInfo& st = p->steps[k];
+    StepRange range("fwd", k, st.type);
     c.params = p->params[st.type];
     switch (st.type) {
       case GRAFX_T_EQ:
@@ -420,6 +434,7 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
   for (int k = last - 1; k >= std::max(first, 1); --k) {
     const StepInfo& st = p->steps[k];
     if (st.type == GRAFX_T_OUT) continue;  // adjoint rows of outputs are d_out itself
+    StepRange range("bwd", k, st.type);
     c.params = p->params[st.type];
     c.dparams = d_params ? d_params[st.type] : nullptr;
     switch (st.type) {
