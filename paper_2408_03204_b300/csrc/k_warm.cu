@@ -434,14 +434,13 @@ static int gemm(int M, int N, int K, const void* A, int64_t sam, int64_t sak, co
   if (splits > 1) a.part = scratch;
   dim3 grid(tn, tm, splits);
   const int am = load_mode(A, sam, sak, M, K, a_bf16), bm = load_mode(B, sbn, sbk, N, K, b_bf16);
-  if (am < 0 || bm < 0 || am == LD_BR)
+  if (am < 0 || bm < 0)
     return fail(GRAFX_ESHAPE, "BF16 GEMM operand not 8-element aligned along its unit-stride dimension");
-  // the BF16 modes used by the network: A along k (im2col rows), B along n (im2col as the
-  // weight-gradient operand)
   switch (am) {
     case LD_VK: launch_tc_b<LD_VK>(bm, grid, a, status, s); break;
     case LD_VR: launch_tc_b<LD_VR>(bm, grid, a, status, s); break;
     case LD_BK: launch_tc_b<LD_BK>(bm, grid, a, status, s); break;
+    case LD_BR: launch_tc_b<LD_BR>(bm, grid, a, status, s); break;
     default: launch_tc_b<LD_SC>(bm, grid, a, status, s);
   }
   if (splits > 1) {
@@ -507,9 +506,14 @@ __global__ void k_bias_act(float* __restrict__ z, const float* __restrict__ bias
   }
 }
 
-__global__ void k_gelu_bwd(float* __restrict__ d, const float* __restrict__ z, int64_t n) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    d[i] *= gelu_d(z[i]);
+// d *= gelu'(z); with db also a BF16 copy of the result (the products' operand)
+__global__ void k_gelu_bwd(float* __restrict__ d, const float* __restrict__ z, int64_t n,
+                           __nv_bfloat16* __restrict__ db = nullptr) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const float v = d[i] * gelu_d(z[i]);
+    d[i] = v;
+    if (db) db[i] = __float2bfloat16_rn(v);
+  }
 }
 
 // Column sums out[c] = sum_r x[r ld + c], c < cols (bias gradients), in two
@@ -714,7 +718,7 @@ namespace {
 
 struct WsNetLayout {
   size_t melw, melrng, tw, ptw, status;
-  size_t im2col, z[4], h[4], e, a1, g1, a2, g2, dbig, dsmall, dh, cspart, wbf, frames, total;
+  size_t im2col, z[4], h[4], e, a1, g1, a2, g2, dbig, dsmall, dh, dzb, cspart, wbf, frames, total;
 };
 
 // frame_floats: log-mel frame scratch (rows x frames x 128) in floats
@@ -745,6 +749,7 @@ WsNetLayout ws_layout(const grafx_wsnet* n, int64_t frame_floats) {
   L.dbig = take(4 * rows * WS_CH * WS_KW);
   L.dsmall = take(4 * B * WS_HID * 2);
   L.dh = take(4 * (B * WS_CH + rows * WS_CH));
+  L.dzb = take(2 * rows * WS_CH);
   L.cspart = take(4 * size_t(CS_SPLIT) * WS_HID);
   L.wbf = take(2 * size_t(n->wb_elems));
   L.frames = take(4 * size_t(std::max<int64_t>(frame_floats, 1)));
@@ -1019,17 +1024,18 @@ int grafx_ws_backward(grafx_wsnet* n, const float* weights, const float* feats, 
   for (int l = 3; l >= 0; --l) {
     const int K = cin[l] * WS_KW;
     // dz = dh gelu'(z); dW = dz^T im2col(input); db = column sums of dz
-    k_gelu_bwd<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(dh, F(L.z[l]), int64_t(rows) * WS_CH);
+    __nv_bfloat16* dzb = reinterpret_cast<__nv_bfloat16*>(n->ws + L.dzb);
+    k_gelu_bwd<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(dh, F(L.z[l]), int64_t(rows) * WS_CH, dzb);
     const float* src = l == 0 ? feats : F(L.h[l - 1]);
     __nv_bfloat16* a2c = reinterpret_cast<__nv_bfloat16*>(F(L.im2col));
     k_im2col<<<grid1(int64_t(rows) * cin[l]), 256, 0, s>>>(src, B, cin[l], l == 0, a2c);
-    if (int rc = gemm(WS_CH, K, rows, dh, 1, WS_CH, a2c, K, 1, d_weights + n->off[l][0], K, 1.f, 0.f, s, F(L.dbig),
-                      dbig_floats, st, false, true))
+    if (int rc = gemm(WS_CH, K, rows, dzb, 1, WS_CH, a2c, K, 1, d_weights + n->off[l][0], K, 1.f, 0.f, s, F(L.dbig),
+                      dbig_floats, st, true, true))
       return rc;
     colsum(dh, rows, WS_CH, WS_CH, d_weights + n->off[l][1], F(L.cspart), s);
     if (l > 0) {
       // d im2col = dz W, then its adjoint scatter gives dh of the previous layer
-      if (int rc = gemm(rows, K, WS_CH, dh, WS_CH, 1, WB(l), K, 1, F(L.dbig), K, 1.f, 0.f, s, nullptr, 0, st, false,
+      if (int rc = gemm(rows, K, WS_CH, dzb, WS_CH, 1, WB(l), K, 1, F(L.dbig), K, 1.f, 0.f, s, nullptr, 0, st, true,
                         true))
         return rc;
       k_col2im<<<grid1(int64_t(rows) * cin[l]), 256, 0, s>>>(F(L.dbig), B, cin[l], dh);
