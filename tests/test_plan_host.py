@@ -163,3 +163,21 @@ def test_adjoint_rows_are_recycled(gx):
     info = gx.Plan([g], [L]).info
     # workspace = U (one row per internal node) + A + small tables; A < internal / 2 rows
     assert info.ws_bytes < (internal + internal / 2) * row + 64 * 2 ** 20
+
+
+def test_schedule_benchmark_consoles_step_counts(gx):
+    """The schedule-method benchmark's consoles: the exact search is never beaten, and
+    type scheduling needs far fewer steps than one node per step on the larger ones."""
+    from paper_2408_03204_b300 import schedules as S
+    gs = S.consoles(8, seed=5)
+    for g in gs:
+        n_proc = sum(1 for t in g.types if t not in (synth.I, synth.O))
+        steps = {m: gx.Plan([_to_gx(gx, g)], [4096], schedule=m).info.n_steps
+                 for m in S.METHODS if m != "optimal" or n_proc <= S.OPTIMAL_MAX_PROC}
+        if "optimal" in steps:
+            assert steps["optimal"] <= min(steps.values())
+        assert steps["one_by_one"] == n_proc + 1 or steps["one_by_one"] >= steps["beam"]
+    big = gs[-1]
+    nb = gx.Plan([_to_gx(gx, big)], [4096], schedule="beam").info.n_steps
+    no = gx.Plan([_to_gx(gx, big)], [4096], schedule="one_by_one").info.n_steps
+    assert no >= 2 * nb
