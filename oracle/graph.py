@@ -47,7 +47,7 @@ def preds_succs(n, edges):
     return preds, succs
 
 
-def validate(types, edges, n_types=9):
+def validate(types, edges, n_types=10):
     """Reject what the paper's graph model does not allow (Sec. 2 Definitions)."""
     n = len(types)
     if n == 0:

@@ -206,25 +206,52 @@ def knee(Gu, T, W, R):
     return Gy, dGu, dT, dW, dR
 
 
-def compressor_fwd(u, p, eps=COMP_EPS, return_env=False):
+def gate_curve(Gu, T, W, R):
+    """Eq. 13 (noisegate): G_y = G_u above T + W; G_u + (1 - R)(G_u - T - W)^2 / (4W)
+    inside the knee; T + R (G_u - T) below T - W; with the partials
+    (dGy/dGu, dGy/dT, dGy/dW, dGy/dR)."""
+    above = Gu >= T + W
+    mid = (Gu >= T - W) & ~above
+    below = ~(above | mid)
+    Gy = Gu.copy()
+    dGu = np.ones_like(Gu)
+    dT = np.zeros_like(Gu)
+    dW = np.zeros_like(Gu)
+    dR = np.zeros_like(Gu)
+    d = Gu[mid] - T - W
+    c = 1.0 - R
+    Gy[mid] = Gu[mid] + c * d * d / (4 * W)
+    dGu[mid] = 1.0 + c * d / (2 * W)
+    dT[mid] = -c * d / (2 * W)
+    dW[mid] = c * (-d / (2 * W) - d * d / (4 * W * W))
+    dR[mid] = -d * d / (4 * W)
+    Gy[below] = T + R * (Gu[below] - T)
+    dGu[below] = R
+    dT[below] = 1.0 - R
+    dR[below] = Gu[below] - T
+    return Gy, dGu, dT, dW, dR
+
+
+def compressor_fwd(u, p, eps=COMP_EPS, return_env=False, curve=knee):
+    """Eq. 8-12 (curve = knee); the noisegate is the same with curve = gate_curve."""
     u = _f64(u)
     alpha, T, W, R = (float(v) for v in _f64(p))
     um = u[0] + u[1]
     g = envelope(um * um, alpha)
     Gu = np.log(g + eps)
-    Gy = knee(Gu, T, W, R)[0]
+    Gy = curve(Gu, T, W, R)[0]
     y = np.exp(Gy - Gu)[None, :] * u
     return (y, g) if return_env else y
 
 
-def compressor_bwd(u, p, ybar, eps=COMP_EPS):
+def compressor_bwd(u, p, ybar, eps=COMP_EPS, curve=knee):
     u, ybar = _f64(u), _f64(ybar)
     alpha, T, W, R = (float(v) for v in _f64(p))
     um = u[0] + u[1]
     x = um * um
     g = envelope(x, alpha)
     Gu = np.log(g + eps)
-    Gy, dGu, dT, dW, dR = knee(Gu, T, W, R)
+    Gy, dGu, dT, dW, dR = curve(Gu, T, W, R)
     k = np.exp(Gy - Gu)
     kbar = np.sum(ybar * u, axis=0)
     Gybar = kbar * k
@@ -236,6 +263,15 @@ def compressor_bwd(u, p, ybar, eps=COMP_EPS):
     pbar = np.array([np.sum(lam * (gprev - x)), np.sum(Gybar * dT),
                      np.sum(Gybar * dW), np.sum(Gybar * dR)])
     return ubar, pbar
+
+
+# ---------------------------------------------------------------- noisegate (Eq. 13)
+def noisegate_fwd(u, p, eps=COMP_EPS):
+    return compressor_fwd(u, p, eps, curve=gate_curve)
+
+
+def noisegate_bwd(u, p, ybar, eps=COMP_EPS):
+    return compressor_bwd(u, p, ybar, eps, curve=gate_curve)
 
 
 # ---------------------------------------------------------------- mix / output

@@ -16,7 +16,7 @@ import numpy as np
 from . import graph as og
 from . import processors as op
 
-I_, O_, M_, G_, S_, E_, C_, D_, R_ = range(9)
+I_, O_, M_, G_, S_, E_, C_, D_, R_, N_ = range(10)
 
 DEFAULT_HP = dict(eq_taps=1023, fs=44100, comp_eps=op.COMP_EPS)
 
@@ -40,6 +40,8 @@ def process(t, u, p, hp):
         return op.eq_fwd(u, p, hp["eq_taps"], hp["fs"])
     if t == C_:
         return op.compressor_fwd(u, p, hp["comp_eps"])
+    if t == N_:
+        return op.noisegate_fwd(u, p, hp["comp_eps"])
     if t == D_:
         return op.delay_fwd(u, p, hp.get("delay_nfft", op.DELAY_NFFT))
     if t == R_:
@@ -58,6 +60,8 @@ def process_bwd(t, u, p, ybar, hp):
         return op.eq_bwd(u, p, ybar, hp["eq_taps"], hp["fs"])
     if t == C_:
         return op.compressor_bwd(u, p, ybar, hp["comp_eps"])
+    if t == N_:
+        return op.noisegate_bwd(u, p, ybar, hp["comp_eps"])
     if t == D_:
         return op.delay_bwd(u, p, ybar, hp.get("delay_nfft", op.DELAY_NFFT))
     if t == R_:

@@ -10,7 +10,7 @@ from typing import List, Tuple
 
 import numpy as np
 
-from .types import I, O, M, G, S, E, C, D, R
+from .types import I, O, M, G, S, E, C, D, R, N
 
 
 @dataclass

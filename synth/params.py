@@ -14,7 +14,7 @@ belongs to the l-th type-t node of T_V).  Distributions:
 """
 import numpy as np
 
-from .types import G, S, E, C, D, R, PARAM_COLS
+from .types import G, S, E, C, D, R, N, PARAM_COLS
 
 LN10 = np.log(10.0)
 DELAY_FFT = 32768
@@ -40,6 +40,14 @@ def _rows(rng, t, n, fs=44100):
         p[:, 1] = rng.uniform(-40, 0, n) * LN10 / 10.0
         p[:, 2] = 3.0 * LN10 / 10.0
         p[:, 3] = rng.uniform(1, 8, n)
+        return p
+    if t == N:
+        # noisegate: threshold -60..-30 dB, expansion ratio 1..4, W = 3 dB
+        p = np.empty((n, 4))
+        p[:, 0] = rng.uniform(0.9, 0.9999, n)
+        p[:, 1] = rng.uniform(-60, -30, n) * LN10 / 10.0
+        p[:, 2] = 3.0 * LN10 / 10.0
+        p[:, 3] = rng.uniform(1, 4, n)
         return p
     if t == D:
         p = np.empty((n, 2, DELAY_TAPS, 2 + DELAY_MAGS))
@@ -81,7 +89,7 @@ def neutral_params(graph):
         if PARAM_COLS[t] == 0:
             continue
         p = np.zeros((n, PARAM_COLS[t]))
-        if t == C:
+        if t in (C, N):
             p[:, 0] = 0.99
             p[:, 2] = 3.0 * LN10 / 10.0
             p[:, 3] = 1.0

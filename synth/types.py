@@ -2,7 +2,7 @@
 
 Type letters follow the paper (Sec. 2 Fig. 1 legend, Fig. 2b legend): i input,
 o output, m mix, g gain/panning, s stereo imager, e equalizer, c compressor,
-d multitap delay, r reverb.
+d multitap delay, r reverb, n noisegate.
 
 Parameter widths N_t (the columns of P[t], Sec. 2 "Graph representations"):
   g: 2   ln-gain per channel (Eq. 2)
@@ -11,8 +11,9 @@ Parameter widths N_t (the columns of P[t], Sec. 2 "Graph representations"):
   c: 4   [alpha, T, W, R]; T and W in natural-log energy units (Eq. 8-12)
   d: 176 2 channels x 4 taps x [Re z, Im z, 20 ln-magnitudes] (Eq. 14-15)
   r: 50  [mid, side] x [H0, H_delta] x 12 bands (ln-magnitude), then q_dry, q_wet
+  n: 4   [alpha, T, W, R] like the compressor, with the gate curve (Eq. 13)
 """
-I, O, M, G, S, E, C, D, R = range(9)
-TYPE_LETTERS = "iomgsecdr"
+I, O, M, G, S, E, C, D, R, N = range(10)
+TYPE_LETTERS = "iomgsecdrn"
 TYPE_IDS = {ch: k for k, ch in enumerate(TYPE_LETTERS)}
-PARAM_COLS = {I: 0, O: 0, M: 0, G: 2, S: 1, E: 8, C: 4, D: 176, R: 50}
+PARAM_COLS = {I: 0, O: 0, M: 0, G: 2, S: 1, E: 8, C: 4, D: 176, R: 50, N: 4}
