@@ -26,7 +26,8 @@
  *    pitch = grafx_pitch(L) = L rounded up to a multiple of 4.  Samples at and past
  *    L inside a row are padding: ignored on input, written as 0 on output.
  *  - Node type ids: see GRAFX_T_*.  Parameter widths per type (columns of P[t]):
- *    gain 2, imager 1, eq 8, compressor 4, delay 176, reverb 50 (see grafx_bind_params).
+ *    gain 2, imager 1, eq 8, compressor 4, delay 176, reverb 50, noisegate 4 (see
+ *    grafx_bind_params).
  */
 #ifndef GRAFX_H
 #define GRAFX_H
@@ -56,8 +57,8 @@ enum {
  * and outputs; mix is an identity node whose input is the sum of its in-edges. */
 enum {
   GRAFX_T_IN = 0, GRAFX_T_OUT = 1, GRAFX_T_MIX = 2, GRAFX_T_GAIN = 3, GRAFX_T_IMAGER = 4,
-  GRAFX_T_EQ = 5, GRAFX_T_COMP = 6, GRAFX_T_DELAY = 7, GRAFX_T_REVERB = 8,
-  GRAFX_N_TYPES = 9
+  GRAFX_T_EQ = 5, GRAFX_T_COMP = 6, GRAFX_T_DELAY = 7, GRAFX_T_REVERB = 8, GRAFX_T_GATE = 9,
+  GRAFX_N_TYPES = 10
 };
 
 /* ---------------------------------------------------------------- schedules (Sec. 2 "Type scheduling") */
@@ -173,7 +174,9 @@ int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* s
  * mod 32768 samples, the backward pass takes the z-gradient of the surrogate of Eq. 15;
  * reverb 50 = [mid, side][H0 (12 bands), Hd (12 bands)] natural-log magnitudes and
  * per-frame decays of the noise masks (Eq. 7), then q_dry, q_wet (log gains):
- * y = e^{q_dry} u + e^{q_wet} (h * u) with the 88200-tap IR h of Eq. 6-7. */
+ * y = e^{q_dry} u + e^{q_wet} (h * u) with the 88200-tap IR h of Eq. 6-7;
+ * noisegate [alpha, T, W, R] like the compressor, with the gate curve of Eq. 13
+ * (unchanged above T + W, expansion by R below T - W, a quadratic knee between). */
 int grafx_bind_params(grafx_plan* p, int32_t type, const float* dev, int64_t rows, int64_t cols);
 
 /* Bind the two noise buffers of the filtered-noise reverb (Sec. 3 "Reverb", Eq. 6-7):

@@ -17,9 +17,9 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgrafx.so")
 
-T_IN, T_OUT, T_MIX, T_GAIN, T_IMAGER, T_EQ, T_COMP, T_DELAY, T_REVERB = range(9)
-N_TYPES = 9
-PARAM_COLS = {T_GAIN: 2, T_IMAGER: 1, T_EQ: 8, T_COMP: 4, T_DELAY: 176, T_REVERB: 50}
+T_IN, T_OUT, T_MIX, T_GAIN, T_IMAGER, T_EQ, T_COMP, T_DELAY, T_REVERB, T_GATE = range(10)
+N_TYPES = 10
+PARAM_COLS = {T_GAIN: 2, T_IMAGER: 1, T_EQ: 8, T_COMP: 4, T_DELAY: 176, T_REVERB: 50, T_GATE: 4}
 SCHED = {"beam": 0, "greedy": 1, "optimal": 2, "one_by_one": 3}
 ERRORS = {1: "EINVAL", 2: "ECYCLE", 3: "ESHAPE", 4: "ETYPE", 5: "ENOMEM", 6: "ECUDA", 7: "ETIMEOUT",
           8: "ESTATE"}

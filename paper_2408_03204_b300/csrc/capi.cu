@@ -87,7 +87,7 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
 
 int check_ready(const Plan* p) {
   if (!p->dev_ws) return fail(GRAFX_ESTATE, "workspace not bound (grafx_plan_bind_workspace)");
-  for (int t : {GRAFX_T_GAIN, GRAFX_T_IMAGER, GRAFX_T_EQ, GRAFX_T_COMP, GRAFX_T_DELAY, GRAFX_T_REVERB})
+  for (int t : {GRAFX_T_GAIN, GRAFX_T_IMAGER, GRAFX_T_EQ, GRAFX_T_COMP, GRAFX_T_DELAY, GRAFX_T_REVERB, GRAFX_T_GATE})
     if (p->n_type_rows[t] > 0 && !p->params[t])
       return fail(GRAFX_ESTATE, "parameters of type " + std::to_string(t) + " not bound");
   if (p->n_type_rows[GRAFX_T_REVERB] > 0 && !p->rv_noise)
@@ -101,6 +101,7 @@ int param_cols(int t) {
     case GRAFX_T_IMAGER: return 1;
     case GRAFX_T_EQ: return 8;
     case GRAFX_T_COMP: return 4;
+    case GRAFX_T_GATE: return 4;
     case GRAFX_T_DELAY: return DL_COLS;
     case GRAFX_T_REVERB: return RV_COLS;
     default: return 0;
@@ -348,8 +349,9 @@ static int render_range(grafx_plan* p, const float* sources, float* out, int32_t
         launches += launch_eq(1, c, st.fitem_begin, st.fitem_count, s);
         break;
       case GRAFX_T_COMP:
+      case GRAFX_T_GATE:
         clear_step_flags(p, st.fitem_begin, st.fitem_count, 2 * k, s);
-        launches += launch_comp(0, c, st.fitem_begin, st.fitem_count, 2 * k, s);
+        launches += launch_comp(0, c, st.fitem_begin, st.fitem_count, 2 * k, st.type == GRAFX_T_GATE, s);
         break;
       case GRAFX_T_DELAY:
         launches += launch_delay(0, c, st.node_begin, st.node_end, s);
@@ -443,9 +445,10 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
         if (c.dparams) launches += launch_eq(3, c, st.node_begin, st.node_end, s);
         break;
       case GRAFX_T_COMP:
+      case GRAFX_T_GATE:
         clear_step_flags(p, st.bitem_begin, st.bitem_count, 2 * k + 1, s);
-        launches += launch_comp(1, c, st.bitem_begin, st.bitem_count, 2 * k + 1, s);
-        if (c.dparams) launches += launch_comp(2, c, st.node_begin, st.node_end, 0, s);
+        launches += launch_comp(1, c, st.bitem_begin, st.bitem_count, 2 * k + 1, st.type == GRAFX_T_GATE, s);
+        if (c.dparams) launches += launch_comp(2, c, st.node_begin, st.node_end, 0, false, s);
         break;
       case GRAFX_T_REVERB:
         launches += launch_delay(3, c, st.dsub_begin[0], st.dsub_count[0], s);   // ybar spectra

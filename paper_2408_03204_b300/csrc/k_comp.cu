@@ -35,6 +35,31 @@ struct Knee {
   float gy, dgu, dt, dw, dr;
 };
 
+// Eq. 13 (noisegate): G_y = G_u above T + W, G_u + (1-R)(G_u-T-W)^2/(4W) in the knee,
+// T + R (G_u - T) below T - W; with the partial derivatives of G_y.
+__device__ __forceinline__ Knee gate_knee(float gu, float T, float W, float R) {
+  Knee k;
+  if (gu >= T + W) {
+    k.gy = gu;
+    k.dgu = 1.f;
+    k.dt = k.dw = k.dr = 0.f;
+  } else if (gu >= T - W) {
+    const float d = gu - T - W, c = 1.f - R;
+    k.gy = gu + c * d * d / (4.f * W);
+    k.dgu = 1.f + c * d / (2.f * W);
+    k.dt = -c * d / (2.f * W);
+    k.dw = c * (-d / (2.f * W) - d * d / (4.f * W * W));
+    k.dr = -d * d / (4.f * W);
+  } else {
+    k.gy = T + R * (gu - T);
+    k.dgu = R;
+    k.dt = 1.f - R;
+    k.dw = 0.f;
+    k.dr = gu - T;
+  }
+  return k;
+}
+
 // Eq. 10-11 and the partial derivatives of G_y.
 __device__ __forceinline__ Knee knee(float gu, float T, float W, float R) {
   Knee k;
@@ -295,7 +320,7 @@ __device__ __forceinline__ void envelope(const float* x, float alpha, float cin,
 
 // Software-pipelined over tickets: once a chunk's inputs are in registers, the next
 // ticket's copies start (cp.async) and run under this chunk's scan, look-back and gain.
-template <int SPT>
+template <int SPT, bool GATE>
 __global__ void __launch_bounds__(256) k_comp_fwd(DevCtx c, int item0, int n_items, int ticket) {
   constexpr int CH = 256 * SPT;
   __shared__ __align__(16) float buf[2 * CH];
@@ -348,7 +373,7 @@ __global__ void __launch_bounds__(256) k_comp_fwd(DevCtx c, int item0, int n_ite
 #pragma unroll
     for (int i = 0; i < SPT; ++i) {
       float gu = logf(g[i] + COMP_EPS);
-      Knee k = knee(gu, T, W, R);
+      Knee k = GATE ? gate_knee(gu, T, W, R) : knee(gu, T, W, R);
       float gain = expf(k.gy - gu);
       ul[i] *= gain;
       ur[i] *= gain;
@@ -361,7 +386,7 @@ __global__ void __launch_bounds__(256) k_comp_fwd(DevCtx c, int item0, int n_ite
   cp_async_wait_all();
 }
 
-template <int SPT>
+template <int SPT, bool GATE>
 __global__ void __launch_bounds__(256) k_comp_bwd(DevCtx c, int item0, int n_items, int ticket) {
   constexpr int CH = 256 * SPT;
   __shared__ __align__(16) float buf[4 * CH];
@@ -406,7 +431,7 @@ __global__ void __launch_bounds__(256) k_comp_bwd(DevCtx c, int item0, int n_ite
 #pragma unroll
     for (int i = 0; i < SPT; ++i) {
       float gu = logf(g[i] + COMP_EPS);
-      Knee k = knee(gu, T, W, R);
+      Knee k = GATE ? gate_knee(gu, T, W, R) : knee(gu, T, W, R);
       gain[i] = expf(k.gy - gu);
       float kbar = bl[i] * ul[i] + br[i] * ur[i];
       gyb[i] = kbar * gain[i];
@@ -480,21 +505,28 @@ __global__ void k_comp_finalize(DevCtx c, int node_begin, int node_end) {
   d[0] = s.x; d[1] = s.y; d[2] = s.z; d[3] = s.w;
 }
 
-// what: 0 forward, 1 backward (items), 2 finalize (node range)
-int launch_comp(int what, const DevCtx& c, int a, int b, int ticket, cudaStream_t s) {
+// what: 0 forward, 1 backward (items), 2 finalize (node range); gate: the noisegate
+// curve (Eq. 13) instead of the compressor's (Eq. 10-11)
+template <int SPT, bool GATE>
+static void comp_launch(int what, const DevCtx& c, int a, int b, int ticket, cudaStream_t s) {
+  const int g = grid_size(b, what == 0 ? 8 : 3);
+  if (what == 0) k_comp_fwd<SPT, GATE><<<g, 256, 0, s>>>(c, a, b, ticket);
+  else k_comp_bwd<SPT, GATE><<<g, 256, 0, s>>>(c, a, b, ticket);
+}
+
+int launch_comp(int what, const DevCtx& c, int a, int b, int ticket, bool gate, cudaStream_t s) {
   if (what == 2) {
     if (b <= a) return 0;
     k_comp_finalize<<<(b - a + 127) / 128, 128, 0, s>>>(c, a, b);
     return 1;
   }
   if (b <= 0) return 0;
-  int g = grid_size(b, what == 0 ? 8 : 3);
   if (c.comp_chunk == 1024) {
-    if (what == 0) k_comp_fwd<4><<<g, 256, 0, s>>>(c, a, b, ticket);
-    else k_comp_bwd<4><<<g, 256, 0, s>>>(c, a, b, ticket);
+    if (gate) comp_launch<4, true>(what, c, a, b, ticket, s);
+    else comp_launch<4, false>(what, c, a, b, ticket, s);
   } else {
-    if (what == 0) k_comp_fwd<8><<<g, 256, 0, s>>>(c, a, b, ticket);
-    else k_comp_bwd<8><<<g, 256, 0, s>>>(c, a, b, ticket);
+    if (gate) comp_launch<8, true>(what, c, a, b, ticket, s);
+    else comp_launch<8, false>(what, c, a, b, ticket, s);
   }
   return 1;
 }

@@ -348,7 +348,8 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
           p->n_dl_slots += nw + nb + nw;
           break;
         }
-        case GRAFX_T_COMP: {
+        case GRAFX_T_COMP:
+        case GRAFX_T_GATE: {
           int32_t nc = (L + p->comp_chunk - 1) / p->comp_chunk;
           p->node_ext[v].z = chunk_id;
           for (int32_t c = 0; c < nc; ++c) fwd.push_back({v, c, chunk_id + c, 0});
@@ -417,7 +418,8 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
           p->node_ext[v].y = run - p->node_ext[v].x;
           break;
         }
-        case GRAFX_T_COMP: {
+        case GRAFX_T_COMP:
+        case GRAFX_T_GATE: {
           int32_t nc = (L + p->comp_chunk - 1) / p->comp_chunk;
           p->node_ext[v].x = slot;
           p->node_ext[v].y = nc;

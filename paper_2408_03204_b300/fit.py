@@ -4,12 +4,13 @@ a fused Adam step per type, all through the C-ABI library on one stream.  A whol
 (Adam included, its step counter on the device) can be replayed as one CUDA graph.
 
 Unconstrained variables theta map to the processors' parameters column by column
-(grafx_adam_step codes): compressor [alpha, T, W, R] -> [alpha map, identity, softplus,
-1 + softplus]; reverb decay columns -> -softplus; everything else identity.
+(grafx_adam_step codes): compressor and noisegate [alpha, T, W, R] -> [alpha map,
+identity, softplus, 1 + softplus]; reverb decay columns -> -softplus; everything else
+identity.
 """
 import ctypes
 
-from . import PARAM_COLS, T_COMP, T_DELAY, T_REVERB, _check, _ptr, _stream_of, lib
+from . import PARAM_COLS, T_COMP, T_DELAY, T_GATE, T_REVERB, _check, _ptr, _stream_of, lib
 
 MAP_IDENT, MAP_ALPHA, MAP_SOFTPLUS, MAP_RATIO, MAP_NEGSP = range(5)
 
@@ -17,7 +18,7 @@ MAP_IDENT, MAP_ALPHA, MAP_SOFTPLUS, MAP_RATIO, MAP_NEGSP = range(5)
 def param_codes(t):
     """Per-column map codes of parameter type t (a list of PARAM_COLS[t] ints)."""
     cols = PARAM_COLS[t]
-    if t == T_COMP:
+    if t in (T_COMP, T_GATE):
         return [MAP_ALPHA, MAP_IDENT, MAP_SOFTPLUS, MAP_RATIO]
     if t == T_REVERB:
         # [mid/side][H0 x 12, H_delta x 12], then wet and dry gains
@@ -27,7 +28,7 @@ def param_codes(t):
 
 def neutral_params(plan, torch, device):
     """Nearly transparent physical parameters for every type the plan holds: 0 dB gains,
-    flat EQ, centred image, compressor with ratio 1.001 at a 0 dB threshold, delays of
+    flat EQ, centred image, compressor and noisegate with ratio 1.001, delays of
     44 samples (1 ms) through four 0.25 taps, reverb dry only (wet gain e^-30)."""
     import math
     P = {}
@@ -36,7 +37,7 @@ def neutral_params(plan, torch, device):
         if not rows:
             continue
         p = torch.zeros((rows, cols), dtype=torch.float32, device=device)
-        if t == T_COMP:
+        if t in (T_COMP, T_GATE):  # ratio 1.001: (nearly) no compression / expansion
             p[:, 0], p[:, 1], p[:, 2], p[:, 3] = 0.99, 0.0, 3.0 * math.log(10.0) / 10.0, 1.001
         if t == T_DELAY:
             q = p.view(rows, 2, 4, 22)
@@ -226,7 +227,7 @@ def main():
     plan.sync_status(f.st)
     h = hist.cpu().numpy()
     ms = e0.elapsed_time(e1)
-    print(json.dumps(dict(nodes=g.n_nodes, types="".join("iomgsecdr"[t] for t in sorted(set(g.types))), length=L,
+    print(json.dumps(dict(nodes=g.n_nodes, types="".join(synth.TYPE_LETTERS[t] for t in sorted(set(g.types))), length=L,
                           steps=args.steps, lr=args.lr, checkpoint_steps=args.checkpoint_steps,
                           ws_bytes=int(plan.info.ws_bytes), ws_bytes_without_checkpointing=int(ws_plain),
                           ms_per_step=ms / args.steps, total_s=ms / 1e3, loss_first=float(h[0]),

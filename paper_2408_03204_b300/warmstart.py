@@ -71,7 +71,7 @@ class GraphBatch:
         for gi, (tys, _) in enumerate(graph_lists):
             first_out = n_out
             for v, t in enumerate(tys):
-                if t in PARAM_COLS:
+                if t in HEAD_OF:  # types without a head (noisegate) keep their start
                     ids.append(base + v)
                     types.append(t)
                     rows.append(cnt[t])

@@ -92,7 +92,7 @@ def test_features_compose_node_inputs_and_mix(env):
     # the samples are sorted by head and their counts match the graphs' processors
     heads = [gws.HEAD_OF[t] for t in batch.types]
     assert heads == sorted(heads)
-    want = sum(sum(1 for t in tys if t in gx.PARAM_COLS) for tys, _ in batch.graph_lists)
+    want = sum(sum(1 for t in tys if t in gws.HEAD_OF) for tys, _ in batch.graph_lists)
     assert n == want
 
 
