@@ -557,6 +557,7 @@ int grafx_step_graph_create(grafx_plan* p, const float* sources, float* out, con
   // kernel attributes are set outside the capture
   DevCtx c0 = make_ctx(p, sources, out, nullptr, nullptr);
   launch_eq(-1, c0, 0, 0, s);
+  launch_comp(-1, c0, 0, 0, 0, false, s);
   launch_delay(-1, c0, 0, 0, s);
   launch_reverb(-1, c0, 0, 0, s);
   launch_loss(-1, make_loss(p, out, target), s);

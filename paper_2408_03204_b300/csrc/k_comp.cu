@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(256) k_comp_fwd(DevCtx c, int item0, int n_ite
 template <int SPT, bool GATE>
 __global__ void __launch_bounds__(256) k_comp_bwd(DevCtx c, int item0, int n_items, int ticket) {
   constexpr int CH = 256 * SPT;
-  __shared__ __align__(16) float buf[4 * CH];
+  extern __shared__ __align__(16) float buf[];  // 4 * CH floats: prefetched u and ybar rows
   __shared__ float sh[32];
   __shared__ float glast[256];
   __shared__ float red[4 * 32];
@@ -509,12 +509,25 @@ __global__ void k_comp_finalize(DevCtx c, int node_begin, int node_end) {
 // curve (Eq. 13) instead of the compressor's (Eq. 10-11)
 template <int SPT, bool GATE>
 static void comp_launch(int what, const DevCtx& c, int a, int b, int ticket, cudaStream_t s) {
+  constexpr int bwd_smem = 4 * 256 * SPT * sizeof(float);
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(k_comp_bwd<SPT, GATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem);
+    init = true;
+  }
+  if (what < 0) return;  // attributes only (before a stream capture)
   const int g = grid_size(b, what == 0 ? 8 : 3);
   if (what == 0) k_comp_fwd<SPT, GATE><<<g, 256, 0, s>>>(c, a, b, ticket);
-  else k_comp_bwd<SPT, GATE><<<g, 256, 0, s>>>(c, a, b, ticket);
+  else k_comp_bwd<SPT, GATE><<<g, 256, bwd_smem, s>>>(c, a, b, ticket);
 }
 
 int launch_comp(int what, const DevCtx& c, int a, int b, int ticket, bool gate, cudaStream_t s) {
+  if (what < 0) {  // kernel attributes of every variant
+    comp_launch<4, false>(-1, c, 0, 0, 0, s), comp_launch<4, true>(-1, c, 0, 0, 0, s);
+    comp_launch<8, false>(-1, c, 0, 0, 0, s), comp_launch<8, true>(-1, c, 0, 0, 0, s);
+    comp_launch<16, false>(-1, c, 0, 0, 0, s), comp_launch<16, true>(-1, c, 0, 0, 0, s);
+    return 0;
+  }
   if (what == 2) {
     if (b <= a) return 0;
     k_comp_finalize<<<(b - a + 127) / 128, 128, 0, s>>>(c, a, b);
@@ -524,6 +537,9 @@ int launch_comp(int what, const DevCtx& c, int a, int b, int ticket, bool gate, 
   if (c.comp_chunk == 1024) {
     if (gate) comp_launch<4, true>(what, c, a, b, ticket, s);
     else comp_launch<4, false>(what, c, a, b, ticket, s);
+  } else if (c.comp_chunk == 4096) {
+    if (gate) comp_launch<16, true>(what, c, a, b, ticket, s);
+    else comp_launch<16, false>(what, c, a, b, ticket, s);
   } else {
     if (gate) comp_launch<8, true>(what, c, a, b, ticket, s);
     else comp_launch<8, false>(what, c, a, b, ticket, s);

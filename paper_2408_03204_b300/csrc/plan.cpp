@@ -309,8 +309,8 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
   p->eq_step = (p->eq_fft - 2 * p->eq_H) & ~3;
   if (p->eq_step < 256) return fail(GRAFX_EINVAL, "eq_fft too small for eq_taps");
   p->comp_chunk = opts.comp_chunk ? opts.comp_chunk : 2048;
-  if (p->comp_chunk != 1024 && p->comp_chunk != 2048)
-    return fail(GRAFX_EINVAL, "comp_chunk must be 1024 or 2048");
+  if (p->comp_chunk != 1024 && p->comp_chunk != 2048 && p->comp_chunk != 4096)
+    return fail(GRAFX_EINVAL, "comp_chunk must be 1024, 2048 or 4096");
 
   // ---- work lists: forward items of every step, then backward items of every step
   p->steps.assign(N + 1, StepInfo{});

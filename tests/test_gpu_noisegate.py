@@ -56,3 +56,21 @@ def test_random_graphs_with_gates():
         for t in P:
             assert_grad_close(dP[t], wP[t], what=f"type {t}")
         assert_grad_close(dS.reshape(-1, 2, Pd)[:, :, :L], wS, what="sources")
+
+
+@pytest.mark.parametrize("chunk", [1024, 4096])
+def test_compressor_and_gate_other_chunk_sizes(chunk):
+    """The 1024- and 4096-sample chunk variants (4 and 16 samples per thread) against the
+    oracle, forward and backward."""
+    from tests.helpers import random_dag
+    rng = np.random.Generator(np.random.PCG64(chunk))
+    g = random_dag(rng, n_inputs=2, n_mid=6, n_outputs=1, kinds=(synth.C, N, synth.G))
+    L = 3 * chunk + 77
+    run, P, src_per, out = run_case([g], [L], seed=chunk, comp_chunk=chunk)
+    Pd = (L + 3) // 4 * 4
+    W = np.zeros((1, 2, Pd), np.float32)
+    W[:, :, :L] = rng.standard_normal((1, 2, L)).astype(np.float32)
+    dP, dS = run.backprop(W.reshape(-1))
+    wP, wS = orr.backward(g.types, g.edges, src_per[0][:, :, :L], P, W[:, :, :L], dict(eq_taps=63))
+    for t in P:
+        assert_grad_close(dP[t], wP[t], what=f"type {t} chunk {chunk}")
