@@ -168,6 +168,20 @@ def eq_bwd(u, p, ybar, N, fs=44100):
     return ubar, pbar
 
 
+# The paper's own EQ parameter (Sec. 3 "Equalizer"): p_e holds the K = (N+1)/2
+# log-magnitudes themselves (N = 2047 -> 1024 values), no band interpolation.
+def eq_fwd_logmag(u, p, N):
+    return fir_centred(_f64(u), zerophase_taps(p, N))
+
+
+def eq_bwd_logmag(u, p, ybar, N):
+    u, ybar = _f64(u), _f64(ybar)
+    h = zerophase_taps(p, N)
+    ubar = fir_centred_adjoint(ybar, h)
+    hbar = fir_centred_taps_grad(u, ybar, (N - 1) // 2)
+    return ubar, zerophase_taps_bwd(p, N, hbar)
+
+
 # ---------------------------------------------------------------- compressor (Eq. 8-12)
 def envelope(x, alpha):
     """Eq. 8 with one coefficient: g[n] = alpha g[n-1] + (1-alpha) x[n], g[-1] = 0.
@@ -284,44 +298,56 @@ def identity_bwd(u, p, ybar):
 
 
 # ---------------------------------------------------------------- multitap delay (Eq. 14-15)
-# Readings (the paper states the processor, not these constants): per channel 4 taps,
-# each a complex z = re + j im and a 39-tap zero-phase FIR built like the equalizer
-# from 20 log-magnitudes (K = 20, N = 39, same window and mirroring); the surrogate
-# transform length is N_d = 32768 (>= 500 ms at 44.1 kHz) and the delay used by the
-# forward pass is d = round(N_d (-arg z) / 2 pi) mod N_d, which makes Eq. 15 exact at
-# |z| = 1 with integer phase.  The forward pass uses the exact integer delays
-# (straight-through); the z-gradient is the gradient of the surrogate of Eq. 15,
-# s[n] = Re{(1/N_d) sum_k z^k w^{kn}}, taking the real part of the surrogate.
-# Parameter row: [channel][tap][re, im, 20 log-magnitudes] = 2 x 4 x 22 = 176.
+# Readings: each channel has M taps, each a delay d_m and a 39-tap zero-phase FIR
+# c_m built like the EQ from 20 log-magnitudes.  Two layouts:
+#   * compact (default): M = 4 taps, each anywhere in [0, N_d), N_d = 32768
+#     (>= 500 ms at 44.1 kHz);
+#   * the paper's setting: a 2 s effect with at most one delay in every 100 ms
+#     (M = 20): tap m lives in its own slot [m S, m S + S), S = fs / 10 = 4410
+#     samples, and its surrogate transform spans the slot (N_d = S).
+# The delay used by the forward pass is d_m = m S + (round(N_d (-arg z_m) / 2 pi)
+# mod N_d) (S = 0 in the compact layout), which makes Eq. 15 exact at |z| = 1 with
+# integer phase.  The forward pass uses the exact integer delays (straight-through);
+# the z-gradient is the gradient of the surrogate of Eq. 15 placed at the slot,
+# s_m[n] = Re{(1/N_d) sum_k z^k w^{k (n - m S)}}, n in [m S, m S + N_d).
+# Parameter row: [channel][tap][re, im, 20 log-magnitudes] = 2 x M x 22
+# (176 compact, 880 paper).
 DELAY_NFFT = 32768
 DELAY_TAPS = 4
 DELAY_FIR = 39
 DELAY_K = 20
+DELAY_PAPER_TAPS = 20
 
 
-def delay_split(p):
-    q = _f64(p).reshape(2, DELAY_TAPS, 2 + DELAY_K)
+def delay_paper_hp(fs=44100):
+    """Layout of the paper's multitap delay: 20 taps per channel in 100 ms slots."""
+    return dict(delay_taps=DELAY_PAPER_TAPS, delay_nfft=fs // 10, delay_slot=fs // 10)
+
+
+def delay_split(p, taps=DELAY_TAPS):
+    q = _f64(p).reshape(2, taps, 2 + DELAY_K)
     z = q[..., 0] + 1j * q[..., 1]
     return z, q[..., 2:]
 
 
-def delay_samples(z, nfft=DELAY_NFFT):
-    """d = round(N_d (-arg z) / 2 pi) mod N_d."""
-    return np.mod(np.rint(nfft * (-np.angle(z)) / (2 * np.pi)).astype(np.int64), nfft)
+def delay_samples(z, nfft=DELAY_NFFT, slot=0):
+    """d_m = m S + (round(N_d (-arg z_m) / 2 pi) mod N_d), m along the last axis."""
+    d = np.mod(np.rint(nfft * (-np.angle(z)) / (2 * np.pi)).astype(np.int64), nfft)
+    return d + slot * np.arange(np.shape(z)[-1])
 
 
-def delay_fir(p, nfft=DELAY_NFFT):
+def delay_fir(p, nfft=DELAY_NFFT, taps=DELAY_TAPS, slot=0):
     """Per channel the sparse FIR h_x[n] = sum_m c_m[n - d_m] as (offset, taps):
     h_x is stored from n = offset."""
-    z, lm = delay_split(p)
-    d = delay_samples(z, nfft)
+    z, lm = delay_split(p, taps)
+    d = delay_samples(z, nfft, slot)
     H = (DELAY_FIR - 1) // 2
     out = []
     for x in range(2):
         lo = int(d[x].min()) - H
         hi = int(d[x].max()) + H
         h = np.zeros(hi - lo + 1)
-        for m in range(DELAY_TAPS):
+        for m in range(taps):
             c = zerophase_taps(lm[x, m], DELAY_FIR)
             s = int(d[x, m]) - H - lo
             h[s:s + DELAY_FIR] += c
@@ -341,10 +367,10 @@ def _fir_at(u, h, lo):
     return y
 
 
-def delay_fwd(u, p, nfft=DELAY_NFFT):
+def delay_fwd(u, p, nfft=DELAY_NFFT, taps=DELAY_TAPS, slot=0):
     """Eq. 14 with the exact integer delays: y_x = sum_m c_{x,m} * delta[n - d_{x,m}] * u_x."""
     u = _f64(u)
-    return np.stack([_fir_at(u[x], h, lo) for x, (lo, h) in enumerate(delay_fir(p, nfft))])
+    return np.stack([_fir_at(u[x], h, lo) for x, (lo, h) in enumerate(delay_fir(p, nfft, taps, slot))])
 
 
 def _corr_lags(u, ybar, lo, hi):
@@ -369,42 +395,44 @@ def delay_surrogate_dz(g, z, nfft=DELAY_NFFT):
     return np.real(Q), -np.imag(Q)
 
 
-def delay_bwd(u, p, ybar, nfft=DELAY_NFFT):
+def delay_bwd(u, p, ybar, nfft=DELAY_NFFT, taps=DELAY_TAPS, slot=0):
     u, ybar = _f64(u), _f64(ybar)
-    z, lm = delay_split(p)
-    d = delay_samples(z, nfft)
+    z, lm = delay_split(p, taps)
+    d = delay_samples(z, nfft, slot)
     H = (DELAY_FIR - 1) // 2
-    firs = delay_fir(p, nfft)
+    firs = delay_fir(p, nfft, taps, slot)
     ubar = np.stack([_fir_at(ybar[x], h[::-1], -(lo + h.shape[0] - 1)) for x, (lo, h) in enumerate(firs)])
-    pbar = np.zeros((2, DELAY_TAPS, 2 + DELAY_K))
+    pbar = np.zeros((2, taps, 2 + DELAY_K))
+    reach = (taps - 1) * slot + nfft                    # surrogates cover n in [0, reach)
     for x in range(2):
-        r = _corr_lags(u[x], ybar[x], -H, nfft - 1 + H)          # r[n], n in [-H, N_d + H)
-        for m in range(DELAY_TAPS):
+        r = _corr_lags(u[x], ybar[x], -H, reach - 1 + H)  # r[n], n in [-H, reach + H)
+        for m in range(taps):
             c = zerophase_taps(lm[x, m], DELAY_FIR)
             # taps: dL/dc[j] = r[d + j], j in [-H, H]
             cbar = r[d[x, m] + np.arange(-H, H + 1) + H]
             pbar[x, m, 2:] = zerophase_taps_bwd(lm[x, m], DELAY_FIR, cbar)
-            # surrogate: g[n] = dL/ds[n] = sum_j c[j] r[n + j], n in [0, N_d)
+            # surrogate at the slot: g[n] = dL/ds_m[m S + n] = sum_j c[j] r[m S + n + j], n in [0, N_d)
             g = np.zeros(nfft)
+            base = m * slot
             for jj, cj in enumerate(c):
-                g += cj * r[jj:jj + nfft]
+                g += cj * r[base + jj:base + jj + nfft]
             pbar[x, m, 0], pbar[x, m, 1] = delay_surrogate_dz(g, z[x, m], nfft)
     return ubar, pbar.reshape(-1)
 
 
-def delay_fwd_surrogate(u, p, nfft=DELAY_NFFT):
+def delay_fwd_surrogate(u, p, nfft=DELAY_NFFT, taps=DELAY_TAPS, slot=0):
     """Forward through the surrogate of Eq. 15 (for checking the z-gradient by finite
-    differences): y_x = sum_m s_m * c_m * u_x with s_m[n] = Re{IDFT(z^k)}[n]."""
+    differences): y_x = sum_m s_m * c_m * u_x with s_m[n] = Re{IDFT(z^k)}[n - m S]."""
     u = _f64(u)
-    z, lm = delay_split(p)
+    z, lm = delay_split(p, taps)
     H = (DELAY_FIR - 1) // 2
     k = np.arange(nfft)
     y = np.zeros_like(u)
     for x in range(2):
-        for m in range(DELAY_TAPS):
+        for m in range(taps):
             s = np.real(np.fft.ifft(np.exp(k * np.log(complex(z[x, m])))))
             c = zerophase_taps(lm[x, m], DELAY_FIR)
-            y[x] += _fir_at(u[x], np.convolve(s, c), -H)
+            y[x] += _fir_at(u[x], np.convolve(s, c), m * slot - H)
     return y
 
 
@@ -420,17 +448,28 @@ def delay_fwd_surrogate(u, p, nfft=DELAY_NFFT):
 # (h_m + h_s)/2, h_r = (h_m - h_s)/2 (the imager's convention); y = e^{q_dry} u +
 # e^{q_wet} (h * u), causal, truncated to L.
 # Parameter row (50): [mid, side] x [H0 (12), Hd (12)], then q_dry, q_wet.
+# The paper's own setting (rv_mode "paper"): FFT 384, hop 192, the masks' log-magnitudes
+# are the parameters themselves, 192 per filter for bins 0..191 (the one-sided spectrum
+# has 193 bins: the Nyquist bin 192 is dropped, mask 0), and the output is the wet
+# convolution alone, y = h * u.  Parameter row (768): [mid, side] x [H0 (192), Hd (192)].
 RV_LEN = 88200
 RV_NFFT = 1024
 RV_HOP = 256
 RV_BANDS = 12
+RV_PAPER = dict(rv_nfft=384, rv_hop=192, rv_mode="paper")
 
 
 def rv_hp(hp=None):
-    d = dict(rv_len=RV_LEN, rv_nfft=RV_NFFT, rv_hop=RV_HOP, fs=44100)
+    d = dict(rv_len=RV_LEN, rv_nfft=RV_NFFT, rv_hop=RV_HOP, fs=44100, rv_mode="bands")
     if hp:
         d.update({k: v for k, v in hp.items() if k in d})
     return d
+
+
+def rv_cols(hp=None):
+    """Parameter columns of one reverb row."""
+    h = rv_hp(hp)
+    return 4 * (h["rv_nfft"] // 2) if h["rv_mode"] == "paper" else 50
 
 
 def rv_band_matrix(nfft, fs=44100, n_bands=RV_BANDS):
@@ -497,14 +536,30 @@ def rv_istft(S, length, nfft, hop):
     return h
 
 
-def rv_masks(p, nfft, F, fs=44100):
+def rv_log_filters(p, nfft, fs=44100, mode="bands"):
+    """Per channel x (mid, side) the per-bin log-magnitudes (H0_x[k], Hd_x[k]) of Eq. 7
+    over the nfft/2+1 one-sided bins; in the paper's mode the Nyquist bin is None."""
     q = _f64(p)
-    B = rv_band_matrix(nfft, fs)
     out = []
+    if mode == "paper":
+        K = nfft // 2
+        for x in range(2):
+            out.append((q[x * 2 * K:x * 2 * K + K], q[x * 2 * K + K:x * 2 * K + 2 * K]))
+        return out
+    B = rv_band_matrix(nfft, fs)
     for x in range(2):
-        H0 = B @ q[x * 24:x * 24 + 12]
-        Hd = B @ q[x * 24 + 12:x * 24 + 24]
-        out.append(np.exp(H0[None, :] + np.arange(F)[:, None] * Hd[None, :]))
+        out.append((B @ q[x * 24:x * 24 + 12], B @ q[x * 24 + 12:x * 24 + 24]))
+    return out
+
+
+def rv_masks(p, nfft, F, fs=44100, mode="bands"):
+    """M_x[m, k] = exp(H0_x[k] + m Hd_x[k]) (Eq. 7, m the 0-based frame), [F, nfft/2+1]."""
+    out = []
+    for H0, Hd in rv_log_filters(p, nfft, fs, mode):
+        M = np.zeros((F, nfft // 2 + 1))
+        K = H0.shape[0]
+        M[:, :K] = np.exp(H0[None, :] + np.arange(F)[:, None] * Hd[None, :])
+        out.append(M)
     return out
 
 
@@ -513,7 +568,7 @@ def rv_ir(p, noise, hp=None):
     hp = rv_hp(hp)
     n, hop, length = hp["rv_nfft"], hp["rv_hop"], hp["rv_len"]
     F = rv_frames(length, n, hop)
-    Ms = rv_masks(p, n, F, hp["fs"])
+    Ms = rv_masks(p, n, F, hp["fs"], hp["rv_mode"])
     hm = rv_istft(rv_stft(_f64(noise[0][:length]), n, hop) * Ms[0], length, n, hop)
     hs = rv_istft(rv_stft(_f64(noise[1][:length]), n, hop) * Ms[1], length, n, hop)
     return np.stack([(hm + hs) / 2, (hm - hs) / 2])
@@ -525,18 +580,23 @@ def _causal(u, h):
 
 
 def reverb_fwd(u, p, noise, hp=None):
+    h_ = rv_hp(hp)
     u, q = _f64(u), _f64(p)
     h = rv_ir(q, noise, hp)
-    return np.exp(q[48]) * u + np.exp(q[49]) * np.stack([_causal(u[x], h[x]) for x in range(2)])
+    wet = np.stack([_causal(u[x], h[x]) for x in range(2)])
+    if h_["rv_mode"] == "paper":
+        return wet
+    return np.exp(q[48]) * u + np.exp(q[49]) * wet
 
 
 def reverb_bwd(u, p, ybar, noise, hp=None):
     hp = rv_hp(hp)
+    paper = hp["rv_mode"] == "paper"
     u, q, ybar = _f64(u), _f64(p), _f64(ybar)
     n, hop, length = hp["rv_nfft"], hp["rv_hop"], hp["rv_len"]
     F = rv_frames(length, n, hop)
     h = rv_ir(q, noise, hp)
-    a_dry, a_wet = np.exp(q[48]), np.exp(q[49])
+    a_dry, a_wet = (0.0, 1.0) if paper else (np.exp(q[48]), np.exp(q[49]))
     L = u.shape[-1]
     # input adjoint: dry + correlation with the IR
     ubar = a_dry * ybar + a_wet * np.stack([scipy.signal.fftconvolve(ybar[x][::-1], h[x])[:L][::-1]
@@ -545,14 +605,14 @@ def reverb_bwd(u, p, ybar, noise, hp=None):
     r = np.stack([scipy.signal.fftconvolve(ybar[x], u[x][::-1])[L - 1:L - 1 + length] for x in range(2)])
     if r.shape[1] < length:
         r = np.pad(r, ((0, 0), (0, length - r.shape[1])))
-    pbar = np.zeros(50)
-    pbar[48] = a_dry * np.sum(ybar * u)
-    pbar[49] = a_wet * np.sum(h * r)
+    pbar = np.zeros(rv_cols(hp))
+    if not paper:
+        pbar[48] = a_dry * np.sum(ybar * u)
+        pbar[49] = a_wet * np.sum(h * r)
     hbar = a_wet * r                                       # dL/dh_l, dL/dh_r
     hbar_ms = [(hbar[0] + hbar[1]) / 2, (hbar[0] - hbar[1]) / 2]
     D = rv_ola_norm(length, n, hop)
-    Ms = rv_masks(q, n, F, hp["fs"])
-    B = rv_band_matrix(n, hp["fs"])
+    Ms = rv_masks(q, n, F, hp["fs"], hp["rv_mode"])
     w = rv_window(n)
     ck = np.full(n // 2 + 1, 2.0)
     ck[0] = ck[-1] = 1.0
@@ -570,6 +630,12 @@ def reverb_bwd(u, p, ybar, noise, hp=None):
         MM = Ms[x] * Mbar
         dH0 = MM.sum(axis=0)
         dHd = (np.arange(F)[:, None] * MM).sum(axis=0)
-        pbar[x * 24:x * 24 + 12] = B.T @ dH0
-        pbar[x * 24 + 12:x * 24 + 24] = B.T @ dHd
+        if paper:
+            K = n // 2
+            pbar[x * 2 * K:x * 2 * K + K] = dH0[:K]
+            pbar[x * 2 * K + K:x * 2 * K + 2 * K] = dHd[:K]
+        else:
+            B = rv_band_matrix(n, hp["fs"])
+            pbar[x * 24:x * 24 + 12] = B.T @ dH0
+            pbar[x * 24 + 12:x * 24 + 24] = B.T @ dHd
     return ubar, pbar

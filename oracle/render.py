@@ -18,7 +18,23 @@ from . import processors as op
 
 I_, O_, M_, G_, S_, E_, C_, D_, R_, N_ = range(10)
 
-DEFAULT_HP = dict(eq_taps=1023, fs=44100, comp_eps=op.COMP_EPS)
+DEFAULT_HP = dict(eq_taps=1023, fs=44100, comp_eps=op.COMP_EPS, eq_params="bands")
+
+
+def paper_hp(fs=44100):
+    """The processor settings of the paper's Sec. 3: EQ of 2047 taps parameterised by
+    its 1024 log-magnitudes, multitap delay with 20 taps per channel in 100 ms slots
+    (880 parameters), reverb with FFT 384 / hop 192 and 192 log-magnitudes per
+    filter (768 parameters)."""
+    hp = dict(eq_taps=2047, fs=fs, eq_params="logmag")
+    hp.update(op.delay_paper_hp(fs))
+    hp.update(op.RV_PAPER)
+    return hp
+
+
+def _delay_args(hp):
+    return dict(nfft=hp.get("delay_nfft", op.DELAY_NFFT), taps=hp.get("delay_taps", op.DELAY_TAPS),
+                slot=hp.get("delay_slot", 0))
 
 
 def _hp(hp):
@@ -37,13 +53,15 @@ def process(t, u, p, hp):
     if t == S_:
         return op.imager_fwd(u, p)
     if t == E_:
+        if hp["eq_params"] == "logmag":
+            return op.eq_fwd_logmag(u, p, hp["eq_taps"])
         return op.eq_fwd(u, p, hp["eq_taps"], hp["fs"])
     if t == C_:
         return op.compressor_fwd(u, p, hp["comp_eps"])
     if t == N_:
         return op.noisegate_fwd(u, p, hp["comp_eps"])
     if t == D_:
-        return op.delay_fwd(u, p, hp.get("delay_nfft", op.DELAY_NFFT))
+        return op.delay_fwd(u, p, **_delay_args(hp))
     if t == R_:
         return op.reverb_fwd(u, p, hp["reverb_noise"], hp)
     raise NotImplementedError(f"type {t}")
@@ -57,13 +75,15 @@ def process_bwd(t, u, p, ybar, hp):
     if t == S_:
         return op.imager_bwd(u, p, ybar)
     if t == E_:
+        if hp["eq_params"] == "logmag":
+            return op.eq_bwd_logmag(u, p, ybar, hp["eq_taps"])
         return op.eq_bwd(u, p, ybar, hp["eq_taps"], hp["fs"])
     if t == C_:
         return op.compressor_bwd(u, p, ybar, hp["comp_eps"])
     if t == N_:
         return op.noisegate_bwd(u, p, ybar, hp["comp_eps"])
     if t == D_:
-        return op.delay_bwd(u, p, ybar, hp.get("delay_nfft", op.DELAY_NFFT))
+        return op.delay_bwd(u, p, ybar, **_delay_args(hp))
     if t == R_:
         return op.reverb_bwd(u, p, ybar, hp["reverb_noise"], hp)
     raise NotImplementedError(f"type {t}")

@@ -12,8 +12,22 @@ Parameter widths N_t (the columns of P[t], Sec. 2 "Graph representations"):
   d: 176 2 channels x 4 taps x [Re z, Im z, 20 ln-magnitudes] (Eq. 14-15)
   r: 50  [mid, side] x [H0, H_delta] x 12 bands (ln-magnitude), then q_dry, q_wet
   n: 4   [alpha, T, W, R] like the compressor, with the gate curve (Eq. 13)
+
+Widths of the paper's own processor settings (Sec. 3), ``PAPER_PARAM_COLS``:
+  e: 1024 ln-magnitudes of the 2047-tap zero-phase FIR
+  d: 880  2 channels x 20 taps (one per 100 ms slot) x [Re z, Im z, 20 ln-magnitudes]
+  r: 768  [mid, side] x [H0, H_delta] x 192 ln-magnitudes (STFT 384 / hop 192)
 """
 I, O, M, G, S, E, C, D, R, N = range(10)
 TYPE_LETTERS = "iomgsecdrn"
 TYPE_IDS = {ch: k for k, ch in enumerate(TYPE_LETTERS)}
 PARAM_COLS = {I: 0, O: 0, M: 0, G: 2, S: 1, E: 8, C: 4, D: 176, R: 50, N: 4}
+PAPER_PARAM_COLS = dict(PARAM_COLS)
+PAPER_PARAM_COLS.update({E: 1024, D: 880, R: 768})
+
+
+def param_cols(preset="compact"):
+    """Parameter widths per type for a processor preset ("compact" or "paper")."""
+    if preset not in ("compact", "paper"):
+        raise ValueError(preset)
+    return PAPER_PARAM_COLS if preset == "paper" else PARAM_COLS
