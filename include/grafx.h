@@ -26,8 +26,9 @@
  *    pitch = grafx_pitch(L) = L rounded up to a multiple of 4.  Samples at and past
  *    L inside a row are padding: ignored on input, written as 0 on output.
  *  - Node type ids: see GRAFX_T_*.  Parameter widths per type (columns of P[t]):
- *    gain 2, imager 1, eq 8, compressor 4, delay 176, reverb 50, noisegate 4 (see
- *    grafx_bind_params).
+ *    gain 2, imager 1, compressor 4, noisegate 4; eq 8, delay 176, reverb 50 in the
+ *    compact layouts, eq (eq_taps+1)/2, delay 880, reverb 768 in the paper's
+ *    (grafx_plan_opts, grafx_plan_info.param_cols, grafx_bind_params).
  */
 #ifndef GRAFX_H
 #define GRAFX_H
@@ -120,8 +121,34 @@ typedef struct {
                              * scratch region, and grafx_backprop recomputes the forward of
                              * every segment but the last before running its backward
                              * (smaller workspace, one extra forward of steps 1..N-k). */
-  int32_t reserved[8];
+  int32_t eq_params;      /* GRAFX_EQ_*: what a row of P[eq] holds (default BANDS) */
+  int32_t delay_layout;   /* GRAFX_DELAY_*: taps of the multitap delay (default COMPACT) */
+  int32_t reverb_layout;  /* GRAFX_REVERB_*: STFT and masks of the reverb (default COMPACT) */
+  int32_t reserved[5];
 } grafx_plan_opts;
+
+/* Processor settings (Sec. 3).  The COMPACT layouts are small parameter sets for
+ * fitting and batching; the PAPER layouts are the paper's own settings. */
+enum {
+  GRAFX_EQ_BANDS = 0,     /* 8 band gains in dB, interpolated in log2 frequency onto the
+                           * (eq_taps+1)/2 log-magnitudes: 8 columns */
+  GRAFX_EQ_LOGMAG = 1     /* the (eq_taps+1)/2 natural-log magnitudes p_e[k] of Eq. 4
+                           * themselves (eq_taps = 2047 -> 1024 columns, the paper's EQ) */
+};
+enum {
+  GRAFX_DELAY_COMPACT = 0, /* 4 taps per channel, each delay anywhere in [0, 32768)
+                            * samples (surrogate length N_d = 32768): 176 columns */
+  GRAFX_DELAY_SLOTS = 1    /* the paper's 2 s delay: 20 taps per channel, tap m in its own
+                            * 100 ms slot [m S, m S + S), S = sample_rate / 10, surrogate
+                            * length N_d = S: 880 columns */
+};
+enum {
+  GRAFX_REVERB_COMPACT = 0, /* STFT 1024 / hop 256, masks from 12 log-spaced bands, dry and
+                             * wet gains: 50 columns */
+  GRAFX_REVERB_PAPER = 1    /* STFT 384 / hop 192, masks from 192 log-magnitudes per filter
+                             * (bins 0..191; the Nyquist bin is dropped), wet output only:
+                             * 768 columns */
+};
 
 void grafx_plan_opts_default(grafx_plan_opts* o);
 
@@ -142,6 +169,7 @@ typedef struct {
   int64_t node_samples;       /* sum over processing (non-input) nodes of L */
   size_t ws_bytes;            /* device workspace bytes (render + backprop + loss) */
   int32_t eq_fft, comp_chunk; /* the tile sizes in use */
+  int32_t param_cols[GRAFX_N_TYPES];  /* columns of P[t] under the plan's layouts (0: none) */
 } grafx_plan_info_t;
 
 int grafx_plan_info(const grafx_plan* p, grafx_plan_info_t* info);
@@ -176,7 +204,14 @@ int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* s
  * per-frame decays of the noise masks (Eq. 7), then q_dry, q_wet (log gains):
  * y = e^{q_dry} u + e^{q_wet} (h * u) with the 88200-tap IR h of Eq. 6-7;
  * noisegate [alpha, T, W, R] like the compressor, with the gate curve of Eq. 13
- * (unchanged above T + W, expansion by R below T - W, a quadratic knee between). */
+ * (unchanged above T + W, expansion by R below T - W, a quadratic knee between).
+ * Paper layouts: eq (eq_taps+1)/2 = the log-magnitudes p_e[k] of Eq. 4 (GRAFX_EQ_LOGMAG);
+ * delay 880 = [channel][tap 0..19][Re z, Im z, 20 log-magnitudes], tap m delayed by
+ * m S + (round(S (-arg z)/2pi) mod S), S = sample_rate/10, the surrogate of Eq. 15 of
+ * length S placed at the slot (GRAFX_DELAY_SLOTS); reverb 768 = [mid, side][H0 (192),
+ * Hd (192)] per-bin log-magnitudes of the masks on bins 0..191 of the 384-point STFT
+ * (hop 192), the Nyquist bin masked to 0, y = h * u (GRAFX_REVERB_PAPER).
+ * cols must equal grafx_plan_info.param_cols[type]; otherwise GRAFX_ESHAPE. */
 int grafx_bind_params(grafx_plan* p, int32_t type, const float* dev, int64_t rows, int64_t cols);
 
 /* Bind the two noise buffers of the filtered-noise reverb (Sec. 3 "Reverb", Eq. 6-7):

@@ -79,8 +79,11 @@ def param_codes(t, cols):
     codes = np.full(cols, IDENT, dtype=np.int8)
     if t in (6, 9):                  # compressor / noisegate [alpha, T, W, R]
         codes[:] = [ALPHA, IDENT, SOFTPLUS, RATIO]
-    if t == 8:                       # reverb: H_delta columns are decays
+    if t == 8 and cols == 50:        # reverb (12 bands): H_delta columns are decays
         c = np.full(50, IDENT, dtype=np.int8)
         c[:48] = np.tile(np.repeat([IDENT, NEGSP], 12), 2)
         codes = c
+    elif t == 8:                     # reverb, per-bin layout [mid, side] x [H0 (K), H_delta (K)]
+        K = cols // 4
+        codes = np.tile(np.repeat(np.array([IDENT, NEGSP], dtype=np.int8), K), 2)
     return codes

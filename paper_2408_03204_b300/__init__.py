@@ -20,6 +20,12 @@ LIB_PATH = os.path.join(HERE, "libgrafx.so")
 T_IN, T_OUT, T_MIX, T_GAIN, T_IMAGER, T_EQ, T_COMP, T_DELAY, T_REVERB, T_GATE = range(10)
 N_TYPES = 10
 PARAM_COLS = {T_GAIN: 2, T_IMAGER: 1, T_EQ: 8, T_COMP: 4, T_DELAY: 176, T_REVERB: 50, T_GATE: 4}
+# processor layouts (grafx_plan_opts): "compact" (the widths above) or "paper" (Sec. 3)
+EQ_PARAMS = {"bands": 0, "logmag": 1}
+DELAY_LAYOUT = {"compact": 0, "slots": 1}
+REVERB_LAYOUT = {"compact": 0, "paper": 1}
+PRESETS = {"compact": dict(eq_taps=1023, eq_params="bands", delay_layout="compact", reverb_layout="compact"),
+           "paper": dict(eq_taps=2047, eq_params="logmag", delay_layout="slots", reverb_layout="paper")}
 SCHED = {"beam": 0, "greedy": 1, "optimal": 2, "one_by_one": 3}
 ERRORS = {1: "EINVAL", 2: "ECYCLE", 3: "ESHAPE", 4: "ETYPE", 5: "ENOMEM", 6: "ECUDA", 7: "ETIMEOUT",
           8: "ESTATE"}
@@ -36,7 +42,8 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("beam_width", ctypes.c_int32), ("eq_taps", ctypes.c_int32),
                 ("sample_rate", ctypes.c_int32), ("n_threads", ctypes.c_int32), ("eq_fft", ctypes.c_int32),
                 ("comp_chunk", ctypes.c_int32), ("checkpoint_steps", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("eq_params", ctypes.c_int32), ("delay_layout", ctypes.c_int32), ("reverb_layout", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -44,7 +51,8 @@ class PlanInfo(ctypes.Structure):
                 ("n_steps", ctypes.c_int32), ("n_inputs", ctypes.c_int32), ("n_outputs", ctypes.c_int32),
                 ("n_type_rows", ctypes.c_int32 * N_TYPES), ("src_elems", ctypes.c_int64),
                 ("out_elems", ctypes.c_int64), ("node_samples", ctypes.c_int64), ("ws_bytes", ctypes.c_size_t),
-                ("eq_fft", ctypes.c_int32), ("comp_chunk", ctypes.c_int32)]
+                ("eq_fft", ctypes.c_int32), ("comp_chunk", ctypes.c_int32),
+                ("param_cols", ctypes.c_int32 * N_TYPES)]
 
 
 _lib = None
@@ -182,22 +190,35 @@ def _stream_of(s):
 class Plan:
     """Render data of one graph or a batch of graphs (Algorithm 1 lines 1-4)."""
 
-    def __init__(self, graphs, lengths, schedule="beam", beam_width=32, eq_taps=1023, sample_rate=44100,
-                 n_threads=0, eq_fft=0, comp_chunk=0, checkpoint_steps=0):
+    def __init__(self, graphs, lengths, schedule="beam", beam_width=32, eq_taps=None, sample_rate=44100,
+                 n_threads=0, eq_fft=0, comp_chunk=0, checkpoint_steps=0, preset="compact", eq_params=None,
+                 delay_layout=None, reverb_layout=None):
+        """preset "compact" (8 EQ bands, 4-tap delays, 1024/256 reverb with 12 bands) or
+        "paper" (Sec. 3: 2047-tap EQ by its 1024 log-magnitudes, 20 delay taps in 100 ms
+        slots, 384/192 reverb with 192 log-magnitudes per filter); the keyword
+        arguments override single settings of the preset."""
+        pre = PRESETS[preset]
         o = PlanOpts()
         lib().grafx_plan_opts_default(ctypes.byref(o))
-        o.schedule, o.beam_width, o.eq_taps = SCHED[schedule], beam_width, eq_taps
+        o.schedule, o.beam_width = SCHED[schedule], beam_width
+        o.eq_taps = pre["eq_taps"] if eq_taps is None else eq_taps
         o.sample_rate, o.n_threads, o.eq_fft, o.comp_chunk = sample_rate, n_threads, eq_fft, comp_chunk
         o.checkpoint_steps = checkpoint_steps
+        o.eq_params = EQ_PARAMS[eq_params or pre["eq_params"]]
+        o.delay_layout = DELAY_LAYOUT[delay_layout or pre["delay_layout"]]
+        o.reverb_layout = REVERB_LAYOUT[reverb_layout or pre["reverb_layout"]]
         hs = (_P * len(graphs))(*[g._h for g in graphs])
         ls = (ctypes.c_int64 * len(lengths))(*[int(x) for x in lengths])
         h = _P()
         _check(lib().grafx_plan_create(hs, len(graphs), ls, ctypes.byref(o), ctypes.byref(h)))
         self._h = h
         self.lengths = [int(x) for x in lengths]
+        self.sample_rate = int(sample_rate)
         inf = PlanInfo()
         _check(lib().grafx_plan_info(self._h, ctypes.byref(inf)))
         self.info = inf
+        # columns of P[t] under this plan's layouts
+        self.param_cols = {t: int(inf.param_cols[t]) for t in range(N_TYPES) if inf.param_cols[t] > 0}
         self.ws = None
         self.params = {}
 

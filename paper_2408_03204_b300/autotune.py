@@ -9,7 +9,7 @@ import hashlib
 import json
 import os
 
-from . import PARAM_COLS, T_COMP, Plan, _stream
+from . import T_COMP, Plan, _stream
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "grafx_autotune.json")
 
@@ -28,7 +28,7 @@ def candidates(eq_taps):
 
 def _neutral_params(plan, torch, device):
     P = {}
-    for t, cols in PARAM_COLS.items():
+    for t, cols in plan.param_cols.items():
         rows = plan.info.n_type_rows[t]
         if rows:
             p = torch.zeros((rows, cols), dtype=torch.float32, device=device)

@@ -58,6 +58,8 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
   for (int j = 0; j < 9; ++j) c.dl_taylor[j] = float(p->dl_taylor[j]);
   c.rv_noise = p->rv_noise;
   c.rv_band = at<const float>(p, p->ws.rv_band);
+  c.rv_win = at<const float>(p, p->ws.rv_win);
+  c.rv_cs = at<const float2_>(p, p->ws.rv_cs);
   c.rv_U = at<float2>(p, p->ws.rv_U);
   c.rv_fr = at<float2>(p, p->ws.rv_fr);
   c.rv_h = at<float>(p, p->ws.rv_h);
@@ -82,6 +84,15 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
   c.eq_step = p->eq_step;
   c.comp_chunk = p->comp_chunk;
   c.sample_rate = float(p->opts.sample_rate);
+  c.eq_logmag = p->eq_logmag;
+  c.dl_taps = p->dl_taps;
+  c.dl_nd = p->dl_nd;
+  c.dl_slot = p->dl_slot;
+  c.dl_P = p->dl_P;
+  c.rv_paper = p->rv_paper;
+  c.rv_n = p->rv_n;
+  c.rv_hop = p->rv_hop;
+  c.rv_f = p->rv_f;
   return c;
 }
 
@@ -95,18 +106,7 @@ int check_ready(const Plan* p) {
   return GRAFX_OK;
 }
 
-int param_cols(int t) {
-  switch (t) {
-    case GRAFX_T_GAIN: return 2;
-    case GRAFX_T_IMAGER: return 1;
-    case GRAFX_T_EQ: return 8;
-    case GRAFX_T_COMP: return 4;
-    case GRAFX_T_GATE: return 4;
-    case GRAFX_T_DELAY: return DL_COLS;
-    case GRAFX_T_REVERB: return RV_COLS;
-    default: return 0;
-  }
-}
+int param_cols(const Plan* p, int t) { return t >= 0 && t < GRAFX_N_TYPES ? p->pcols[t] : 0; }
 
 // Look-back flags of the items [item0, item0+n) and the step's ticket counter start at 0.
 void clear_step_flags(const Plan* p, int item0, int n, int ticket, cudaStream_t s) {
@@ -247,6 +247,7 @@ int grafx_plan_info(const grafx_plan* p, grafx_plan_info_t* info) {
   info->ws_bytes = p->ws.total;
   info->eq_fft = p->eq_fft;
   info->comp_chunk = p->comp_chunk;
+  std::memcpy(info->param_cols, p->pcols, sizeof(info->param_cols));
   return GRAFX_OK;
 }
 
@@ -291,6 +292,8 @@ int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* s
   put(p->ws.eq_hann, p->eq_hann.data(), p->eq_hann.size() * 4);
   put(p->ws.eq_band, p->eq_band.data(), p->eq_band.size() * 4);
   put(p->ws.rv_band, p->rv_band.data(), p->rv_band.size() * 4);
+  put(p->ws.rv_win, p->rv_win.data(), p->rv_win.size() * 4);
+  put(p->ws.rv_cs, p->rv_cs.data(), p->rv_cs.size() * sizeof(float2_));
   put(p->ws.loss_rows, p->loss.rows.data(), p->loss.rows.size() * sizeof(LossRow));
   put(p->ws.loss_items, p->loss.items.data(), p->loss.items.size() * sizeof(int4_));
   int rc = cuda_check(cudaMemcpyAsync(dev_ws, img.data(), img.size(), cudaMemcpyHostToDevice, s), "upload tables");
@@ -307,8 +310,8 @@ int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* s
 int grafx_bind_params(grafx_plan* p, int32_t type, const float* dev, int64_t rows, int64_t cols) {
   if (!p) return fail(GRAFX_EINVAL, "null plan");
   if (type < 0 || type >= GRAFX_N_TYPES) return fail(GRAFX_ETYPE, "unknown node type");
-  if (param_cols(type) == 0) return fail(GRAFX_ETYPE, "type has no parameters");
-  if (rows != p->n_type_rows[type] || cols != param_cols(type))
+  if (param_cols(p, type) == 0) return fail(GRAFX_ETYPE, "type has no parameters");
+  if (rows != p->n_type_rows[type] || cols != param_cols(p, type))
     return fail(GRAFX_ESHAPE, "parameter table shape mismatch");
   if (rows > 0 && !dev) return fail(GRAFX_EINVAL, "null parameter pointer");
   p->params[type] = dev;
@@ -343,6 +346,7 @@ static int render_range(grafx_plan* p, const float* sources, float* out, int32_t
     const StepInfo& st = p->steps[k];
     StepRange range("fwd", k, st.type);
     c.params = p->params[st.type];
+    c.pcols = param_cols(p, st.type);
     switch (st.type) {
       case GRAFX_T_EQ:
         launches += launch_eq(0, c, st.node_begin, st.node_end, s);
@@ -438,6 +442,7 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
     if (st.type == GRAFX_T_OUT) continue;  // adjoint rows of outputs are d_out itself
     StepRange range("bwd", k, st.type);
     c.params = p->params[st.type];
+    c.pcols = param_cols(p, st.type);
     c.dparams = d_params ? d_params[st.type] : nullptr;
     switch (st.type) {
       case GRAFX_T_EQ:
@@ -464,7 +469,7 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
       case GRAFX_T_GAIN:
       case GRAFX_T_IMAGER:
         launches += launch_ew_bwd(st.type, c, st.bitem_begin, st.bitem_count, s);
-        if (c.dparams) launches += launch_ew_finalize(c, st.node_begin, st.node_end, param_cols(st.type), s);
+        if (c.dparams) launches += launch_ew_finalize(c, st.node_begin, st.node_end, param_cols(p, st.type), s);
         break;
       default:
         launches += launch_ew_bwd(GRAFX_T_MIX, c, st.bitem_begin, st.bitem_count, s);

@@ -31,21 +31,23 @@ struct DevCtx {
   float* eq_aux;       // per EQ node: 1024 floats (taps in the forward, gradient fold in the backward)
   float* eq_bandpart;  // per EQ node: chunk partials of the band gradient (16 x 8 floats)
   float* comp_carry;
-  float* dl_aux;        // per delay node: taps and delays (DL_AUX floats)
+  float* dl_aux;        // per delay node: [channel][tap][39 taps, delay] (2 dl_taps 40 floats)
   float2* dl_spec;      // block spectra of the lag correlation
   float2* dl_R;         // per delay node and lag partition: accumulated spectra
-  float* dl_r;          // per delay node and channel: lags r[n], n from -DL_B
+  float* dl_r;          // per delay node and channel: lags r[n], n from -DL_B (dl_P DL_B each)
   float dl_taylor[9];   // Taylor coefficients of sum_k k q^k near q = 1
   const float* rv_noise;  // reverb noise [2][RV_LEN] (mid, side)
-  const float* rv_band;   // [RV_BINS][RV_BANDS] band interpolation
-  float2* rv_U;           // noise STFT [2][RV_F][RV_BINS]
-  float2* rv_fr;          // per reverb node: IR frames [RV_F][RV_N] (mid, side)
+  const float* rv_band;   // [RV_BINS][RV_BANDS] band interpolation (compact layout)
+  const float* rv_win;    // [rv_n] periodic Hann window of the reverb STFT
+  const float2_* rv_cs;   // [rv_n] (cos, sin)(2 pi j / rv_n): direct frame DFTs (paper layout)
+  float2* rv_U;           // noise STFT [2][rv_f][rv_n/2+1]
+  float2* rv_fr;          // per reverb node: IR frames [rv_f][rv_n] (mid, side)
   float* rv_h;            // per reverb node: h_l, h_r [2][RV_HLEN]
   float2* rv_H;           // per reverb node: partition spectra [RV_P][DL_M]
   float2* rv_Y;           // per reverb node: block spectra [rv_nbmax][DL_M]
   float2* rv_R;           // per reverb node: lag partition spectra [RV_P][DL_M]
   float* rv_r;            // per reverb node: lags [2][RV_HLEN]
-  float2* rv_mm;          // per reverb node: mask-gradient terms [RV_F][2][RV_BINS]
+  float2* rv_mm;          // per reverb node: mask-gradient terms [rv_f][2][rv_n/2+1]
   int32_t rv_nbmax;
   float4* partial;
   float2* eq_partial;
@@ -57,6 +59,10 @@ struct DevCtx {
   int32_t eq_taps, eq_H, eq_Hal, eq_fft, eq_step;
   int32_t comp_chunk;
   float sample_rate;
+  // processor layouts
+  int32_t eq_logmag;                        // P[eq] rows hold the (eq_taps+1)/2 log-magnitudes
+  int32_t dl_taps, dl_nd, dl_slot, dl_P;    // delay taps per channel, surrogate length, slot width, lag partitions
+  int32_t rv_paper, rv_n, rv_hop, rv_f;     // reverb: paper layout, STFT size, hop, frames
 };
 
 __device__ __forceinline__ const float* yrow(const DevCtx& c, const NodeDev& n) {

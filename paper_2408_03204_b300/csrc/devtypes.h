@@ -38,28 +38,35 @@ constexpr int TWIDDLE_N = 8192;   // twiddle table size: exp(-2 pi i m / 8192)
 constexpr int EW_TILE = 4096;     // samples per elementwise work item (4 float4 per thread and channel)
 constexpr int N_RES = 3;          // loss resolutions 512, 1024, 2048
 
-// multitap delay (Eq. 14-15)
-constexpr int DL_NFFT = 32768;     // surrogate transform length N_d
-constexpr int DL_TAPS = 4;         // taps per channel
+// multitap delay (Eq. 14-15).  Compact layout: 4 taps per channel, each anywhere in
+// [0, N_d), N_d = 32768.  Slot layout (the paper's): 20 taps per channel, tap m in
+// [m S, m S + S) with the surrogate of length N_d = S = fs / 10.  The tap count, N_d,
+// the slot width and the lag partitions are runtime values of the plan (DevCtx).
+constexpr int DL_NFFT = 32768;     // compact surrogate transform length N_d
+constexpr int DL_TAPS = 4;         // compact taps per channel
+constexpr int DL_SLOT_TAPS = 20;   // slot-layout taps per channel (2 s in 100 ms slots)
 constexpr int DL_FIR = 39;         // zero-phase FIR per tap (20 log-magnitudes)
-constexpr int DL_COLS = 2 * DL_TAPS * (2 + (DL_FIR + 1) / 2);   // 176 parameters
-constexpr int DL_AUX = 2 * DL_TAPS * (DL_FIR + 1);             // taps + delay per (channel, tap)
+constexpr int DL_K = (DL_FIR + 1) / 2;
+constexpr int DL_ROW = 2 + DL_K;   // parameters per (channel, tap): Re z, Im z, 20 log-magnitudes
 constexpr int DL_TILE = 1024;      // outputs per forward / adjoint work item
 constexpr int DL_B = 4096;         // block of the lag correlation
 constexpr int DL_M = 2 * DL_B;     // its FFT size
-constexpr int DL_P = 10;           // lag partitions: lags [-B, (P-1) B) cover [-19, N_d + 19)
-constexpr int DL_NLAG = DL_P * DL_B;
+constexpr int DL_PMAX = 32;        // lag partitions: lags [-B, (P-1) B) cover [-19, reach + 19)
 constexpr int DL_CHUNK = 32;       // bins per accumulation work item
 constexpr int DL_MAX_BLOCKS = 128; // signals with delay nodes: at most 2^19 samples
 
-// filtered-noise reverb (Eq. 6-7)
+// filtered-noise reverb (Eq. 6-7).  Compact layout: STFT 1024 / hop 256, 12 bands,
+// dry and wet gains.  Paper layout: STFT 384 / hop 192, 192 per-bin log-magnitudes
+// per filter, wet only.  The STFT size, hop and frame count are runtime values.
 constexpr int RV_LEN = 88200;      // impulse response: 2 s at 44.1 kHz
-constexpr int RV_N = 1024;         // STFT size
+constexpr int RV_N = 1024;         // compact STFT size
 constexpr int RV_HOP = 256;
 constexpr int RV_F = 1 + RV_LEN / RV_HOP;              // 345 centred frames
 constexpr int RV_BINS = RV_N / 2 + 1;
 constexpr int RV_BANDS = 12;
 constexpr int RV_COLS = 50;        // [mid, side] x [H0, Hd] x 12 bands, q_dry, q_wet
+constexpr int RV_PN = 384;         // paper STFT size
+constexpr int RV_PHOP = 192;
 constexpr int RV_P = (RV_LEN + DL_B - 1) / DL_B;       // 22 partitions of 4096 taps
 constexpr int RV_HLEN = RV_P * DL_B;
 

@@ -2,23 +2,26 @@
 //
 // Per channel x and tap m: a 39-tap zero-phase FIR c_{x,m} built like the equalizer
 // from 20 log-magnitudes, and a complex z_{x,m} whose phase gives the integer delay
-// d = round(N_d (-arg z) / 2 pi) mod N_d, N_d = 32768.  Forward (exact, as the paper's
-// straight-through estimator prescribes): y_x[t] = sum_m sum_j c[j] u_x[t - d_m - j],
-// a sparse FIR run from shared-memory windows.  Backward:
+// d = m S + (round(N_d (-arg z) / 2 pi) mod N_d).  Compact layout: 4 taps, S = 0,
+// N_d = 32768.  Slot layout (the paper's 2 s effect): 20 taps, tap m in its own 100 ms
+// slot, S = N_d = fs / 10.  Forward (exact, as the paper's straight-through estimator
+// prescribes): y_x[t] = sum_m sum_j c[j] u_x[t - d_m - j], a sparse FIR run from
+// shared-memory windows, four taps at a time.  Backward:
 //   * input adjoint: the transposed sparse FIR over ybar;
 //   * FIR taps: dL/dc_m[j] = r_x[d_m + j] with r_x[n] = sum_t ybar_x[t] u_x[t - n];
-//   * z (surrogate of Eq. 15, s[n] = Re{(1/N_d) sum_k z^k w^{kn}}): with
-//     g[n] = sum_j c[j] r_x[n + j] = dL/ds[n] over n in [0, N_d),
+//   * z (surrogate of Eq. 15 placed at the slot, s[n] = Re{(1/N_d) sum_k z^k w^{k(n - m S)}}):
+//     with g[n] = sum_j c[j] r_x[m S + n + j] = dL/ds[m S + n] over n in [0, N_d),
 //     Q = sum_n g[n] phi[n], phi[n] = (1/N_d) sum_k k z^{k-1} w^{kn}, and
 //     dL/dRe z = Re Q, dL/dIm z = -Im Q.  phi has the closed form
 //     F(q)/(N_d z), q = z w^n, F(q) = sum_k k q^k = (-a (1 + (N_d - 1) z^N) - b) / a^2
 //     with a = 1 - q and b = z^N - 1 evaluated without cancellation; within
 //     |N_d ln q| < 1/2 (the lag next to the delay) F uses its Taylor series in
 //     t = N_d ln q instead.
-// The correlation r over the N_d + 38 lags is a partitioned frequency-domain
-// accumulation: 8192-point spectra of 2B-sample windows of u and of B-sample blocks
-// of ybar (B = 4096, both channels packed as l + i r), R_p = sum_b X_{b-p} conj(Ybar_b)
-// per lag partition p (10 partitions of B lags from -B), one inverse FFT per partition.
+// The correlation r over the lags [-19, reach + 19), reach = (M - 1) S + N_d, is a
+// partitioned frequency-domain accumulation: 8192-point spectra of 2B-sample windows
+// of u and of B-sample blocks of ybar (B = 4096, both channels packed as l + i r),
+// R_p = sum_b X_{b-p} conj(Ybar_b) per lag partition p (P partitions of B lags from
+// -B), one inverse FFT per partition.
 #include <cmath>
 
 #include "common.cuh"
@@ -27,7 +30,7 @@
 
 namespace grafx {
 
-// shared-memory windows of the four taps for a 1024-sample tile of one channel
+// shared-memory window of one tap for a 1024-sample tile of one channel
 template <bool ADJ>
 __device__ __forceinline__ void dl_window(const DevCtx& c, int v, const NodeDev& nd, int ch, int start, float* win) {
   const int e0 = ADJ ? c.tcsr_ptr[v] : c.csr_ptr[v];
@@ -44,39 +47,46 @@ __device__ __forceinline__ void dl_window(const DevCtx& c, int v, const NodeDev&
   }
 }
 
+constexpr int DL_GROUP = 4;   // taps whose windows are staged in shared memory together
+
 // Forward (ADJ = false) or input adjoint (ADJ = true) of the sparse FIR for one
 // (node, tile, channel) item; 256 threads x 4 consecutive outputs.
 template <bool ADJ>
 __global__ void __launch_bounds__(256) k_delay_fir(DevCtx c, int item0, int n_items) {
-  __shared__ float win[DL_TAPS][DL_TILE + DL_FIR - 1];
-  __shared__ float taps[DL_TAPS][DL_FIR];
-  __shared__ int dly[DL_TAPS];
+  __shared__ float win[DL_GROUP][DL_TILE + DL_FIR - 1];
+  __shared__ float taps[DL_GROUP][DL_FIR];
+  __shared__ int dly[DL_GROUP];
   constexpr int H = (DL_FIR - 1) / 2;
+  const int ntap = c.dl_taps;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
     const int v = w.x, t0 = w.y, ch = w.z;
     const NodeDev nd = c.nodes[v];
-    const float* aux = c.dl_aux + size_t(c.ext[v].z) * DL_AUX;
-    if (threadIdx.x < DL_TAPS) dly[threadIdx.x] = int(aux[(ch * DL_TAPS + threadIdx.x) * (DL_FIR + 1) + DL_FIR]);
-    for (int i = threadIdx.x; i < DL_TAPS * DL_FIR; i += blockDim.x)
-      taps[i / DL_FIR][i % DL_FIR] = aux[(ch * DL_TAPS + i / DL_FIR) * (DL_FIR + 1) + i % DL_FIR];
-    __syncthreads();
-    for (int m = 0; m < DL_TAPS; ++m) {
-      // forward: win[k] = u[t0 - d - H + k]; adjoint: win[k] = ybar[t0 + d - H + k]
-      dl_window<ADJ>(c, v, nd, ch, ADJ ? t0 + dly[m] - H : t0 - dly[m] - H, win[m]);
-    }
-    __syncthreads();
+    const float* aux = c.dl_aux + size_t(c.ext[v].z) * 2 * ntap * (DL_FIR + 1) + size_t(ch) * ntap * (DL_FIR + 1);
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     const int i0 = 4 * threadIdx.x;
-    for (int m = 0; m < DL_TAPS; ++m) {
-      float x[4 + DL_FIR - 1];
+    for (int g0 = 0; g0 < ntap; g0 += DL_GROUP) {
+      const int ng = min(DL_GROUP, ntap - g0);
+      __syncthreads();   // readers of the previous group (or item) are done
+      if (threadIdx.x < ng) dly[threadIdx.x] = int(aux[(g0 + threadIdx.x) * (DL_FIR + 1) + DL_FIR]);
+      for (int i = threadIdx.x; i < ng * DL_FIR; i += blockDim.x)
+        taps[i / DL_FIR][i % DL_FIR] = aux[(g0 + i / DL_FIR) * (DL_FIR + 1) + i % DL_FIR];
+      __syncthreads();
+      for (int m = 0; m < ng; ++m) {
+        // forward: win[k] = u[t0 - d - H + k]; adjoint: win[k] = ybar[t0 + d - H + k]
+        dl_window<ADJ>(c, v, nd, ch, ADJ ? t0 + dly[m] - H : t0 - dly[m] - H, win[m]);
+      }
+      __syncthreads();
+      for (int m = 0; m < ng; ++m) {
+        float x[4 + DL_FIR - 1];
 #pragma unroll
-      for (int k = 0; k < 4 + DL_FIR - 1; ++k) x[k] = win[m][i0 + k];
+        for (int k = 0; k < 4 + DL_FIR - 1; ++k) x[k] = win[m][i0 + k];
 #pragma unroll
-      for (int jj = 0; jj < DL_FIR; ++jj) {
-        const float cj = taps[m][jj];
+        for (int jj = 0; jj < DL_FIR; ++jj) {
+          const float cj = taps[m][jj];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] += cj * x[q + (ADJ ? jj : DL_FIR - 1 - jj)];
+          for (int q = 0; q < 4; ++q) acc[q] += cj * x[q + (ADJ ? jj : DL_FIR - 1 - jj)];
+        }
       }
     }
     float* row = (ADJ ? arow_w(c, nd) : yrow_w(c, nd)) + ch * nd.pitch;
@@ -85,32 +95,33 @@ __global__ void __launch_bounds__(256) k_delay_fir(DevCtx c, int item0, int n_it
       const int t = t0 + i0 + q;
       if (t < nd.pitch) row[t] = t < nd.len ? acc[q] : 0.f;
     }
-    __syncthreads();
   }
 }
 
-// Per delay node: the taps c_{x,m} (Eq. 4 with N = 39, K = 20) and the delays d_{x,m}.
+// Per delay node: the taps c_{x,m} (Eq. 4 with N = 39, K = 20) and the delays
+// d_{x,m} = m S + (round(N_d (-arg z) / 2 pi) mod N_d).
 __global__ void k_delay_design(DevCtx c, int node_begin) {
   const int v = node_begin + blockIdx.x;
   const NodeDev nd = c.nodes[v];
-  float* aux = c.dl_aux + size_t(c.ext[v].z) * DL_AUX;
-  const float* p = c.params + size_t(nd.prow) * DL_COLS;
-  constexpr int H = (DL_FIR - 1) / 2, K = (DL_FIR + 1) / 2;
-  for (int i = threadIdx.x; i < 2 * DL_TAPS * DL_FIR; i += blockDim.x) {
+  const int ntap = c.dl_taps, Nd = c.dl_nd;
+  float* aux = c.dl_aux + size_t(c.ext[v].z) * 2 * ntap * (DL_FIR + 1);
+  const float* p = c.params + size_t(nd.prow) * c.pcols;
+  constexpr int H = (DL_FIR - 1) / 2, K = DL_K;
+  for (int i = threadIdx.x; i < 2 * ntap * DL_FIR; i += blockDim.x) {
     const int xm = i / DL_FIR, n = i % DL_FIR - H;
-    const float* q = p + xm * (2 + K);
+    const float* q = p + xm * DL_ROW;
     double s = exp(double(q[2]));
     for (int k = 1; k < K; ++k) s += 2.0 * exp(double(q[2 + k])) * cospi(2.0 * k * n / DL_FIR);
     const double hann = 0.5 * (1.0 + cospi(2.0 * n / (DL_FIR + 1)));
     aux[xm * (DL_FIR + 1) + n + H] = float(hann * s / DL_FIR);
   }
-  if (threadIdx.x < 2 * DL_TAPS) {
-    const float* q = p + threadIdx.x * (2 + K);
+  for (int xm = threadIdx.x; xm < 2 * ntap; xm += blockDim.x) {
+    const float* q = p + xm * DL_ROW;
     const double ang = atan2(double(q[1]), double(q[0]));
-    long long d = llrint(double(DL_NFFT) * (-ang) / (2.0 * M_PI));
-    d %= DL_NFFT;
-    if (d < 0) d += DL_NFFT;
-    aux[threadIdx.x * (DL_FIR + 1) + DL_FIR] = float(d);
+    long long d = llrint(double(Nd) * (-ang) / (2.0 * M_PI));
+    d %= Nd;
+    if (d < 0) d += Nd;
+    aux[xm * (DL_FIR + 1) + DL_FIR] = float(d + (long long)(xm % ntap) * c.dl_slot);
   }
 }
 
@@ -150,13 +161,15 @@ __global__ void __launch_bounds__(DL_M / 16) k_delay_spec(DevCtx c, int item0, i
 
 // R_p[k] for one node and DL_CHUNK bins, all lag partitions: per channel
 // sum_b X_{b-p}[k] conj(Ybar_b[k]), packed as R_l + i R_r for the joint inverse.
-__global__ void __launch_bounds__(DL_CHUNK * DL_P) k_delay_acc(DevCtx c, int item0, int n_items) {
+// Launched with DL_CHUNK * dl_P threads (one per bin and partition).
+__global__ void __launch_bounds__(DL_CHUNK * DL_PMAX) k_delay_acc(DevCtx c, int item0, int n_items) {
   extern __shared__ float2 sm[];
+  const int P = c.dl_P;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
     const int v = w.x, k0 = w.y * DL_CHUNK;
     const int4_ e = c.ext[v];
-    const int nb = e.w, nw = nb + DL_P;
+    const int nb = e.w, nw = nb + P;
     float2* X = sm;                         // [nw][DL_CHUNK][2 ch]
     float2* Y = sm + size_t(nw) * DL_CHUNK * 2;
     __syncthreads();
@@ -175,7 +188,7 @@ __global__ void __launch_bounds__(DL_CHUNK * DL_P) k_delay_acc(DevCtx c, int ite
     const int kk = threadIdx.x % DL_CHUNK, p = threadIdx.x / DL_CHUNK;
     float2 al = make_float2(0.f, 0.f), ar = make_float2(0.f, 0.f);
     for (int b = 0; b < nb; ++b) {
-      const int ws = b - p + DL_P;            // window index b - p, stored from -DL_P
+      const int ws = b - p + P;               // window index b - p, stored from -P
       const float2 xl = X[(size_t(ws) * DL_CHUNK + kk) * 2], xr = X[(size_t(ws) * DL_CHUNK + kk) * 2 + 1];
       const float2 yl = Y[(size_t(b) * DL_CHUNK + kk) * 2], yr = Y[(size_t(b) * DL_CHUNK + kk) * 2 + 1];
       al.x += xl.x * yl.x + xl.y * yl.y;
@@ -204,12 +217,13 @@ __global__ void __launch_bounds__(DL_M / 16) k_delay_lags(DevCtx c, int item0, i
     }
     __syncthreads();
     fft::forward<DL_M>(buf, c.ptw, threadIdx.x, true);
-    float* rl = c.dl_r + size_t(e.z) * 2 * DL_NLAG;
+    const int nlag = c.dl_P * DL_B;
+    float* rl = c.dl_r + size_t(e.z) * 2 * nlag;
     const float inv = 1.f / float(DL_M);
     for (int nu = threadIdx.x; nu < DL_B; nu += blockDim.x) {
       const float2 z = buf[fft::pad(DL_B - nu)];         // conj(result) / M = (l, r)
       rl[p * DL_B + nu] = z.x * inv;
-      rl[DL_NLAG + p * DL_B + nu] = -z.y * inv;
+      rl[nlag + p * DL_B + nu] = -z.y * inv;
     }
   }
 }
@@ -227,16 +241,18 @@ __device__ __forceinline__ cplx cdv(cplx a, cplx b) {
 __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_items) {
   __shared__ float cs[DL_FIR];
   __shared__ float red[2 * 32];
-  constexpr int H = (DL_FIR - 1) / 2, K = (DL_FIR + 1) / 2;
+  constexpr int H = (DL_FIR - 1) / 2, K = DL_K;
+  const int ntap = c.dl_taps, Nd = c.dl_nd, nlag = c.dl_P * DL_B;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
-    const int v = w.x, x = w.y / DL_TAPS, m = w.y % DL_TAPS;
+    const int v = w.x, x = w.y / ntap, m = w.y % ntap;
     const NodeDev nd = c.nodes[v];
     const int4_ e = c.ext[v];
-    const float* aux = c.dl_aux + size_t(e.z) * DL_AUX + (x * DL_TAPS + m) * (DL_FIR + 1);
-    const float* r = c.dl_r + size_t(e.z) * 2 * DL_NLAG + x * DL_NLAG + DL_B;  // r[n] at r + n
-    const float* q = c.params + size_t(nd.prow) * DL_COLS + (x * DL_TAPS + m) * (2 + K);
-    float* out = c.dparams + size_t(nd.prow) * DL_COLS + (x * DL_TAPS + m) * (2 + K);
+    const float* aux = c.dl_aux + size_t(e.z) * 2 * ntap * (DL_FIR + 1) + (x * ntap + m) * (DL_FIR + 1);
+    const float* r = c.dl_r + size_t(e.z) * 2 * nlag + x * nlag + DL_B;  // r[n] at r + n
+    const float* rs = r + m * c.dl_slot;                                 // the tap's slot: rs[n] = r[m S + n]
+    const float* q = c.params + size_t(nd.prow) * c.pcols + (x * ntap + m) * DL_ROW;
+    float* out = c.dparams + size_t(nd.prow) * c.pcols + (x * ntap + m) * DL_ROW;
     const int d = int(aux[DL_FIR]);
     __syncthreads();
     if (threadIdx.x < DL_FIR) cs[threadIdx.x] = aux[threadIdx.x];
@@ -255,25 +271,25 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
     const double zr = q[0], zi = q[1];
     const double rho = sqrt(zr * zr + zi * zi), th = atan2(zi, zr);
     const double lr = log(rho);
-    const double rN = exp(DL_NFFT * lr);
+    const double rN = exp(Nd * lr);
     double sN, cN;
-    sincos(0.5 * DL_NFFT * th, &sN, &cN);
+    sincos(0.5 * Nd * th, &sN, &cN);
     const double c1 = -2.0 * sN * sN;                   // cos(N th) - 1
     const double s1 = 2.0 * sN * cN;                    // sin(N th)
     const cplx zN = {float(rN * (1.0 + c1)), float(rN * s1)};
     const cplx bz = {float(rN * c1 + (rN - 1.0)), float(rN * s1)};   // z^N - 1
-    const cplx zinv = {float(zr / (rho * rho) / DL_NFFT), float(-zi / (rho * rho) / DL_NFFT)};
+    const cplx zinv = {float(zr / (rho * rho) / Nd), float(-zi / (rho * rho) / Nd)};
     const double thn = th / M_PI;                       // phase in units of pi
     float qx = 0.f, qy = 0.f;
-    for (int n = threadIdx.x; n < DL_NFFT; n += blockDim.x) {
+    for (int n = threadIdx.x; n < Nd; n += blockDim.x) {
       float g = 0.f;
 #pragma unroll
-      for (int jj = 0; jj < DL_FIR; ++jj) g += cs[jj] * r[n + jj - H];
-      double ph = thn + 2.0 * n / DL_NFFT;              // arg q / pi, reduced to (-1, 1]
+      for (int jj = 0; jj < DL_FIR; ++jj) g += cs[jj] * rs[n + jj - H];
+      double ph = thn + 2.0 * n / Nd;                   // arg q / pi, reduced to (-1, 1]
       ph -= 2.0 * floor(0.5 * ph + 0.5);
       const float phf = float(ph);
       cplx F;
-      const float tx = float(DL_NFFT * lr), ty = float(DL_NFFT * M_PI) * phf;   // t = N ln q
+      const float tx = float(Nd * lr), ty = float(Nd * M_PI) * phf;   // t = N ln q
       if (tx * tx + ty * ty < 0.25f) {
         // F = N^2 sum_j e_j t^j with e_j = (sum_k k^(j+1)) / (N^(j+2) j!)
         cplx t = {tx, ty}, tp = {1.f, 0.f};
@@ -284,15 +300,15 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
           F.y += c.dl_taylor[j] * tp.y;
           tp = cm(tp, t);
         }
-        F.x *= float(DL_NFFT) * DL_NFFT;
-        F.y *= float(DL_NFFT) * DL_NFFT;
+        F.x *= float(Nd) * float(Nd);
+        F.y *= float(Nd) * float(Nd);
       } else {
         float sh, chh;
         sincospif(0.5f * phf, &sh, &chh);
         const float rf = float(rho);
         // a = 1 - q = (1 - rho) + 2 rho sin^2(ph/2) - i rho sin(ph)
         const cplx a = {float(1.0 - rho) + 2.f * rf * sh * sh, -rf * 2.f * sh * chh};
-        const cplx t1 = {1.f + float(DL_NFFT - 1) * zN.x, float(DL_NFFT - 1) * zN.y};
+        const cplx t1 = {1.f + float(Nd - 1) * zN.x, float(Nd - 1) * zN.y};
         const cplx am = cm(a, t1);
         const cplx num = {-am.x - bz.x, -am.y - bz.y};
         F = cdv(num, cm(a, a));
@@ -313,11 +329,12 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
 int launch_delay(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
   static bool init = false;
   const size_t sm_fft = sizeof(float2) * fft::Padded<DL_M>::size;
-  const size_t sm_acc = sizeof(float2) * 2 * DL_CHUNK * size_t(2 * DL_MAX_BLOCKS + DL_P);
+  const size_t sm_acc = sizeof(float2) * 2 * DL_CHUNK * size_t(2 * DL_MAX_BLOCKS + c.dl_P);
   if (!init) {
+    const size_t sm_acc_max = sizeof(float2) * 2 * DL_CHUNK * size_t(2 * DL_MAX_BLOCKS + DL_PMAX);
     cudaFuncSetAttribute(k_delay_spec, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_fft));
     cudaFuncSetAttribute(k_delay_lags, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_fft));
-    cudaFuncSetAttribute(k_delay_acc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_acc));
+    cudaFuncSetAttribute(k_delay_acc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_acc_max));
     init = true;
   }
   if (what < 0) return 0;
@@ -329,7 +346,7 @@ int launch_delay(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
     case 1: if (b > 0) k_delay_fir<false><<<grid_size(b, 4), 256, 0, s>>>(c, a, b); return b > 0;
     case 2: if (b > 0) k_delay_fir<true><<<grid_size(b, 4), 256, 0, s>>>(c, a, b); return b > 0;
     case 3: if (b > 0) k_delay_spec<<<grid_size(b, 3), DL_M / 16, sm_fft, s>>>(c, a, b); return b > 0;
-    case 4: if (b > 0) k_delay_acc<<<grid_size(b, 1), DL_CHUNK * DL_P, sm_acc, s>>>(c, a, b); return b > 0;
+    case 4: if (b > 0) k_delay_acc<<<grid_size(b, 1), DL_CHUNK * c.dl_P, sm_acc, s>>>(c, a, b); return b > 0;
     case 5: if (b > 0) k_delay_lags<<<grid_size(b, 3), DL_M / 16, sm_fft, s>>>(c, a, b); return b > 0;
     case 6: if (b > 0) k_delay_grad<<<grid_size(b, 4), 256, 0, s>>>(c, a, b); return b > 0;
   }

@@ -26,8 +26,14 @@ namespace grafx {
 
 constexpr float LN10_20 = 0.11512925464970229f;  // ln(10)/20
 
-// A_k = exp(ln10/20 * sum_b B[k][b] band_dB[b]) for k < K, into smem A.
+// A_k for k < K into smem A: exp(p_e[k]) when the row holds the log-magnitudes
+// themselves (the paper's parameter), else exp(ln10/20 * sum_b B[k][b] band_dB[b]).
 __device__ void eq_magnitudes(const DevCtx& c, const NodeDev& nd, float* A, int K) {
+  if (c.eq_logmag) {
+    const float* lm = c.params + size_t(nd.prow) * K;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) A[k] = expf(lm[k]);
+    return;
+  }
   const float* bands = c.params + nd.prow * 8;
   float b[8];
 #pragma unroll
@@ -260,7 +266,8 @@ __global__ void __launch_bounds__(M / 16) k_eq_gradfft(DevCtx c, int node_begin)
 }
 
 // dL/dp_k = A_k (c_k/N) sum_n s[n] cos(2 pi k n / N) for one chunk of k, then this
-// chunk's share of the band-matrix product; grid (EQ nodes of the step, chunks).
+// chunk's share of the band-matrix product (with log-magnitude rows, dL/dp_k is the
+// gradient itself and is stored directly); grid (EQ nodes of the step, chunks).
 __global__ void __launch_bounds__(EQ_CHUNK) k_eq_gradbands(DevCtx c, int node_begin) {
   __shared__ float A[1024];
   __shared__ float sv[1024];
@@ -285,10 +292,15 @@ __global__ void __launch_bounds__(EQ_CHUNK) k_eq_gradbands(DevCtx c, int node_be
       acc += sv[n] * cs[idx];
     }
     const float pk = A[k] * acc * (k == 0 ? 1.f : 2.f) / float(N);
-    const float* row = c.eq_band + k * 8;
+    if (c.eq_logmag) {   // the row is p_e itself: dL/dp_e[k], no band matrix
+      c.dparams[size_t(nd.prow) * K + k] = pk;
+    } else {
+      const float* row = c.eq_band + k * 8;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) bsum[b] = row[b] * pk;
+      for (int b = 0; b < 8; ++b) bsum[b] = row[b] * pk;
+    }
   }
+  if (c.eq_logmag) return;   // uniform over the launch: no thread reaches the block sums
   float lo[4] = {bsum[0], bsum[1], bsum[2], bsum[3]}, hi[4] = {bsum[4], bsum[5], bsum[6], bsum[7]};
   block_sum<4>(lo, red);
   block_sum<4>(hi, red + 4 * 32);
@@ -341,6 +353,7 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
     case 3:
       k_eq_gradfft<M><<<b - a, T, s1, s>>>(c, a);
       k_eq_gradbands<<<dim3(b - a, chunks_k), EQ_CHUNK, 0, s>>>(c, a);
+      if (c.eq_logmag) return 2;
       k_eq_gradout<<<(b - a + 63) / 64, 64, 0, s>>>(c, a, b, chunks_k);
       return 3;
   }

@@ -1,20 +1,25 @@
 // Filtered-noise reverb (Sec. 3 "Reverb", Eq. 6-7).
 //
 // Impulse response per node (forward): the STFT of the two noise buffers (mid, side;
-// FFT 1024, hop 256, periodic Hann, centred frames; computed once per render) is multiplied by the
-// masks M_x[k, m] = exp(H0_x[k] + m Hd_x[k]) (12-band log-frequency interpolation),
-// inverted frame by frame (mid + i side packed in one complex FFT), windowed and
+// periodic Hann, centred frames; computed once per render) is multiplied by the
+// masks M_x[k, m] = exp(H0_x[k] + m Hd_x[k]), inverted frame by frame, windowed and
 // overlap-added, divided by sum w^2, and turned into left/right as (mid +- side)/2.
-// Convolution: 22 partitions of 4096 taps; y = e^{q_dry} u + e^{q_wet} (h * u) by
-// overlap-save with 8192-point spectra: Y_b = sum_p H_p X_{b-1-p} per channel (u
-// windows of 2B samples from the delay's spectrum kernel), one inverse per block.
+// Two layouts: compact (FFT 1024, hop 256, H0/Hd interpolated from 12 log-spaced
+// bands, y = e^{q_dry} u + e^{q_wet} (h * u); the frames go through the 1024-point
+// shared-memory FFT with mid + i side packed in one complex transform) and the
+// paper's (FFT 384, hop 192, H0/Hd given per bin for bins 0..191 with the Nyquist
+// bin dropped, y = h * u; 384 is not a power of two and the frames are short, so
+// their transforms are direct DFT sums over a twiddle table in shared memory).
+// Convolution: 22 partitions of 4096 taps by overlap-save with 8192-point spectra:
+// Y_b = sum_p H_p X_{b-1-p} per channel (u windows of 2B samples from the delay's
+// spectrum kernel), one inverse per block.
 // Backward: the input adjoint correlates ybar with h through the same partitions
 // (Ubar_b = sum_p conj(H_p) Ybar_{b+p} on 2B windows of ybar); the lags
 // r_x[n] = sum_t ybar[t] u[t - n] come from R_p = sum_b X_{b-p-1} conj(Ybar_b) on
 // B blocks of ybar; dL/dh = e^{q_wet} r is pushed back through the overlap-add, the
-// per-frame inverse FFT (its adjoint is a forward FFT with the one-sided weights c_k/N),
-// the masks and the band matrix; dq_dry = e^{q_dry} sum_x r_x[0] and
-// dq_wet = e^{q_wet} sum_x sum_n h_x[n] r_x[n].
+// per-frame inverse transform (its adjoint is a forward transform with the one-sided
+// weights c_k/N), the masks and (compact) the band matrix; dq_dry = e^{q_dry} sum_x r_x[0]
+// and dq_wet = e^{q_wet} sum_x sum_n h_x[n] r_x[n].
 #include <cmath>
 
 #include "common.cuh"
@@ -23,7 +28,6 @@
 
 namespace grafx {
 
-__device__ __forceinline__ float rv_hann(const float2_* tw, int j) { return 0.5f - 0.5f * tw[j * (TWIDDLE_N / RV_N)].x; }
 
 // Split a packed spectrum Z of a + i b (a, b real) at bin k into A[k], B[k].
 __device__ __forceinline__ void rv_split(float2 z, float2 zm, float2* a, float2* b) {
@@ -31,7 +35,14 @@ __device__ __forceinline__ void rv_split(float2 z, float2 zm, float2* a, float2*
   *b = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
 }
 
+// M_x[k, m] (Eq. 7) of both channels at bin k and frame m.
 __device__ __forceinline__ void rv_masks(const DevCtx& c, const float* q, int k, int m, float* M) {
+  if (c.rv_paper) {   // per-bin log-magnitudes on bins 0..K-1; the Nyquist bin K is dropped
+    const int K = c.rv_n / 2;
+#pragma unroll
+    for (int x = 0; x < 2; ++x) M[x] = k < K ? expf(q[x * 2 * K + k] + float(m) * q[x * 2 * K + K + k]) : 0.f;
+    return;
+  }
   const float* row = c.rv_band + k * RV_BANDS;
 #pragma unroll
   for (int x = 0; x < 2; ++x) {
@@ -50,7 +61,7 @@ __global__ void __launch_bounds__(RV_N / 16) k_rv_noise_stft(DevCtx c) {
   const int m = blockIdx.x;
   for (int j = threadIdx.x; j < RV_N; j += blockDim.x) {
     const int t = m * RV_HOP + j - RV_N / 2;   // centred frame
-    const float w = rv_hann(c.tw, j);
+    const float w = c.rv_win[j];
     buf[fft::pad(j)] = t >= 0 && t < RV_LEN ? make_float2(w * c.rv_noise[t], w * c.rv_noise[RV_LEN + t]) : make_float2(0.f, 0.f);
   }
   __syncthreads();
@@ -69,7 +80,7 @@ __global__ void __launch_bounds__(RV_N / 16) k_rv_ir_frames(DevCtx c, int node_b
   const int m = blockIdx.x, v = node_begin + blockIdx.y;
   const NodeDev nd = c.nodes[v];
   const int ri = c.ext[v].z;
-  const float* q = c.params + size_t(nd.prow) * RV_COLS;
+  const float* q = c.params + size_t(nd.prow) * c.pcols;
   for (int k = threadIdx.x; k <= RV_N / 2; k += blockDim.x) {
     float M[2];
     rv_masks(c, q, k, m, M);
@@ -91,20 +102,90 @@ __global__ void __launch_bounds__(RV_N / 16) k_rv_ir_frames(DevCtx c, int node_b
   const float inv = 1.f / float(RV_N);
   for (int j = threadIdx.x; j < RV_N; j += blockDim.x) {
     const float2 z = buf[fft::pad(j)];
-    const float w = rv_hann(c.tw, j) * inv;
+    const float w = c.rv_win[j] * inv;
     fr[j] = make_float2(w * z.x, -w * z.y);   // conj of the result: (mid, side)
+  }
+}
+
+// Paper layout: U_x[m][k], k <= N/2, of both noise buffers by direct DFT sums of the
+// windowed centred frame m; one CTA per frame.
+__global__ void __launch_bounds__(256) k_rv_noise_dft(DevCtx c) {
+  __shared__ float2 fr[RV_PN];
+  __shared__ float2_ cs[RV_PN];
+  const int m = blockIdx.x, N = c.rv_n, bins = N / 2 + 1;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const int t = m * c.rv_hop + j - N / 2;
+    const float w = c.rv_win[j];
+    fr[j] = t >= 0 && t < RV_LEN ? make_float2(w * c.rv_noise[t], w * c.rv_noise[RV_LEN + t]) : make_float2(0.f, 0.f);
+    cs[j] = c.rv_cs[j];
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < bins; k += blockDim.x) {
+    float2 am = make_float2(0.f, 0.f), as = make_float2(0.f, 0.f);
+    int idx = 0;   // (j k) mod N
+    for (int j = 0; j < N; ++j) {
+      const float2_ e = cs[idx];   // e^{-i a} = (cos a, -sin a)
+      am.x += fr[j].x * e.x;
+      am.y -= fr[j].x * e.y;
+      as.x += fr[j].y * e.x;
+      as.y -= fr[j].y * e.y;
+      idx += k;
+      if (idx >= N) idx -= N;
+    }
+    c.rv_U[size_t(m) * bins + k] = am;
+    c.rv_U[size_t(c.rv_f + m) * bins + k] = as;
+  }
+}
+
+// Paper layout: masked noise frame m of one node, inverted by the one-sided inverse
+// DFT sum x[j] = (Re Y_0 + 2 sum_{0<k<K} Re(Y_k e^{i 2 pi j k / N}) + Re Y_K (-1)^j) / N
+// and windowed: (mid, side) per sample.
+__global__ void __launch_bounds__(128) k_rv_ir_frames_dft(DevCtx c, int node_begin) {
+  __shared__ float2 Ym[RV_PN / 2 + 1], Ys[RV_PN / 2 + 1];
+  __shared__ float2_ cs[RV_PN];
+  const int m = blockIdx.x, v = node_begin + blockIdx.y;
+  const NodeDev nd = c.nodes[v];
+  const int ri = c.ext[v].z, N = c.rv_n, K = N / 2, bins = K + 1;
+  const float* q = c.params + size_t(nd.prow) * c.pcols;
+  for (int k = threadIdx.x; k < bins; k += blockDim.x) {
+    float M[2];
+    rv_masks(c, q, k, m, M);
+    const float2 hm = c.rv_U[size_t(m) * bins + k], hs = c.rv_U[size_t(c.rv_f + m) * bins + k];
+    Ym[k] = make_float2(hm.x * M[0], hm.y * M[0]);
+    Ys[k] = make_float2(hs.x * M[1], hs.y * M[1]);
+  }
+  for (int j = threadIdx.x; j < N; j += blockDim.x) cs[j] = c.rv_cs[j];
+  __syncthreads();
+  float2* fr = c.rv_fr + (size_t(ri) * c.rv_f + m) * N;
+  const float inv = 1.f / float(N);
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    float sm = 0.f, ss = 0.f;
+    int idx = 0;   // (j k) mod N
+    for (int k = 1; k < K; ++k) {
+      idx += j;
+      if (idx >= N) idx -= N;
+      const float2_ e = cs[idx];   // e^{i a} = (cos a, sin a)
+      sm += Ym[k].x * e.x - Ym[k].y * e.y;
+      ss += Ys[k].x * e.x - Ys[k].y * e.y;
+    }
+    const float sg = (j & 1) ? -1.f : 1.f;
+    sm = Ym[0].x + 2.f * sm + sg * Ym[K].x;
+    ss = Ys[0].x + 2.f * ss + sg * Ys[K].x;
+    const float w = c.rv_win[j] * inv;
+    fr[j] = make_float2(w * sm, w * ss);
   }
 }
 
 // Window envelope at sample n and the frames covering it (frame m starts at
 // m hop - N/2 in signal coordinates; np = n + N/2 in padded coordinates).
-__device__ __forceinline__ float rv_ola_norm(const float2_* tw, int n, int* m0, int* m1) {
-  const int np = n + RV_N / 2;
-  const int hi = min(RV_F - 1, np / RV_HOP);
-  const int lo = np - RV_N + 1 <= 0 ? 0 : (np - RV_N + 1 + RV_HOP - 1) / RV_HOP;
+__device__ __forceinline__ float rv_ola_norm(const DevCtx& c, int n, int* m0, int* m1) {
+  const int N = c.rv_n, hop = c.rv_hop;
+  const int np = n + N / 2;
+  const int hi = min(c.rv_f - 1, np / hop);
+  const int lo = np - N + 1 <= 0 ? 0 : (np - N + 1 + hop - 1) / hop;
   float D = 0.f;
   for (int m = lo; m <= hi; ++m) {
-    const float w = rv_hann(tw, np - m * RV_HOP);
+    const float w = c.rv_win[np - m * hop];
     D += w * w;
   }
   *m0 = lo;
@@ -121,12 +202,13 @@ __global__ void k_rv_ir_ola(DevCtx c, int node_begin) {
   float hl = 0.f, hr = 0.f;
   if (n < RV_LEN) {
     int lo, hi;
-    const float D = rv_ola_norm(c.tw, n, &lo, &hi);
+    const float D = rv_ola_norm(c, n, &lo, &hi);
     if (D > 1e-8f) {
       float sm = 0.f, ss = 0.f;
-      const float2* fr = c.rv_fr + size_t(ri) * RV_F * RV_N;
+      const int N = c.rv_n;
+      const float2* fr = c.rv_fr + size_t(ri) * c.rv_f * N;
       for (int m = lo; m <= hi; ++m) {
-        const float2 z = fr[size_t(m) * RV_N + n + RV_N / 2 - m * RV_HOP];
+        const float2 z = fr[size_t(m) * N + n + N / 2 - m * c.rv_hop];
         sm += z.x;
         ss += z.y;
       }
@@ -254,8 +336,9 @@ __global__ void __launch_bounds__(DL_M / 16) k_rv_inv(DevCtx c, int node_begin) 
     }
     return;
   }
-  const float* q = c.params + size_t(nd.prow) * RV_COLS;
-  const float a_dry = expf(q[48]), a_wet = expf(q[49]);
+  const float* q = c.params + size_t(nd.prow) * c.pcols;
+  const bool dry = !c.rv_paper;   // the paper's reverb is wet only
+  const float a_dry = dry ? expf(q[48]) : 0.f, a_wet = dry ? expf(q[49]) : 1.f;
   float* row = WHAT == 0 ? yrow_w(c, nd) : arow_w(c, nd);
   const int e0 = WHAT == 0 ? c.csr_ptr[v] : c.tcsr_ptr[v];
   const int e1 = WHAT == 0 ? c.csr_ptr[v + 1] : c.tcsr_ptr[v + 1];
@@ -264,7 +347,7 @@ __global__ void __launch_bounds__(DL_M / 16) k_rv_inv(DevCtx c, int node_begin) 
     if (t >= nd.pitch) continue;
     const float2 z = buf[fft::pad(WHAT == 0 ? DL_B + j : j)];
     float dl = 0.f, dr = 0.f;
-    if (t < nd.len)
+    if (dry && t < nd.len)
       for (int ed = e0; ed < e1; ++ed) {
         const NodeDev s = c.nodes[WHAT == 0 ? c.csr_src[ed] : c.tcsr_dst[ed]];
         const float* r = WHAT == 0 ? yrow(c, s) : arow(c, s);
@@ -284,7 +367,7 @@ __global__ void __launch_bounds__(RV_N / 16) k_rv_gfr(DevCtx c, int node_begin) 
   const int m = blockIdx.x, v = node_begin + blockIdx.y;
   const NodeDev nd = c.nodes[v];
   const int ri = c.ext[v].z;
-  const float* q = c.params + size_t(nd.prow) * RV_COLS;
+  const float* q = c.params + size_t(nd.prow) * c.pcols;
   const float a_wet = expf(q[49]);
   const float* rl = c.rv_r + (size_t(ri) * 2) * RV_HLEN;
   const float* rr = rl + RV_HLEN;
@@ -293,10 +376,10 @@ __global__ void __launch_bounds__(RV_N / 16) k_rv_gfr(DevCtx c, int node_begin) 
     float gm = 0.f, gs = 0.f;
     if (n >= 0 && n < RV_LEN) {
       int lo, hi;
-      const float D = rv_ola_norm(c.tw, n, &lo, &hi);
+      const float D = rv_ola_norm(c, n, &lo, &hi);
       if (D > 1e-8f) {
         const float hbl = a_wet * rl[n], hbr = a_wet * rr[n];
-        const float w = rv_hann(c.tw, j) / D;
+        const float w = c.rv_win[j] / D;
         gm = w * 0.5f * (hbl + hbr);
         gs = w * 0.5f * (hbl - hbr);
       }
@@ -322,27 +405,89 @@ __global__ void __launch_bounds__(RV_N / 16) k_rv_gfr(DevCtx c, int node_begin) 
   }
 }
 
-// Band gradients (sum over frames, then the band matrix), dq_dry and dq_wet.
+// Paper layout: the adjoint of the IR synthesis for frame m of one node by direct DFT
+// sums (the adjoint of the one-sided inverse is a forward DFT with weights c_k/N); per
+// channel and bin, M dL/dM and m M dL/dM.
+__global__ void __launch_bounds__(128) k_rv_gfr_dft(DevCtx c, int node_begin) {
+  __shared__ float2 g[RV_PN];
+  __shared__ float2_ cs[RV_PN];
+  const int m = blockIdx.x, v = node_begin + blockIdx.y;
+  const NodeDev nd = c.nodes[v];
+  const int ri = c.ext[v].z, N = c.rv_n, K = N / 2, bins = K + 1;
+  const float* q = c.params + size_t(nd.prow) * c.pcols;
+  const float* rl = c.rv_r + (size_t(ri) * 2) * RV_HLEN;
+  const float* rr = rl + RV_HLEN;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const int n = m * c.rv_hop + j - N / 2;   // centred frame
+    float gm = 0.f, gs = 0.f;
+    if (n >= 0 && n < RV_LEN) {
+      int lo, hi;
+      const float D = rv_ola_norm(c, n, &lo, &hi);
+      if (D > 1e-8f) {
+        const float w = c.rv_win[j] / D;
+        gm = w * 0.5f * (rl[n] + rr[n]);
+        gs = w * 0.5f * (rl[n] - rr[n]);
+      }
+    }
+    g[j] = make_float2(gm, gs);
+    cs[j] = c.rv_cs[j];
+  }
+  __syncthreads();
+  float2* out = c.rv_mm + (size_t(ri) * c.rv_f + m) * 2 * bins;
+  for (int k = threadIdx.x; k < bins; k += blockDim.x) {
+    float2 A[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    int idx = 0;   // (j k) mod N
+    for (int j = 0; j < N; ++j) {
+      const float2_ e = cs[idx];   // e^{-i a}
+      A[0].x += g[j].x * e.x;
+      A[0].y -= g[j].x * e.y;
+      A[1].x += g[j].y * e.x;
+      A[1].y -= g[j].y * e.y;
+      idx += k;
+      if (idx >= N) idx -= N;
+    }
+    const float ck = (k == 0 || k == K ? 1.f : 2.f) / float(N);
+    float M[2];
+    rv_masks(c, q, k, m, M);
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+      const float2 U = c.rv_U[size_t(x * c.rv_f + m) * bins + k];
+      const float mm = M[x] * ck * (A[x].x * U.x + A[x].y * U.y);
+      out[x * bins + k] = make_float2(mm, float(m) * mm);
+    }
+  }
+}
+
+// Mask gradients summed over frames; compact: through the band matrix, then dq_dry
+// and dq_wet; paper: the per-bin H0 and Hd gradients themselves.
 __global__ void __launch_bounds__(256) k_rv_grad(DevCtx c, int node_begin) {
   __shared__ float g0[2][RV_BINS], gd[2][RV_BINS];
   __shared__ float red[2 * 32];
   const int v = node_begin + blockIdx.x;
   const NodeDev nd = c.nodes[v];
-  const int ri = c.ext[v].z;
-  const float* q = c.params + size_t(nd.prow) * RV_COLS;
-  float* out = c.dparams + size_t(nd.prow) * RV_COLS;
-  const float2* mm = c.rv_mm + size_t(ri) * RV_F * 2 * RV_BINS;
-  for (int i = threadIdx.x; i < 2 * RV_BINS; i += blockDim.x) {
+  const int ri = c.ext[v].z, bins = c.rv_n / 2 + 1;
+  const float* q = c.params + size_t(nd.prow) * c.pcols;
+  float* out = c.dparams + size_t(nd.prow) * c.pcols;
+  const float2* mm = c.rv_mm + size_t(ri) * c.rv_f * 2 * bins;
+  for (int i = threadIdx.x; i < 2 * bins; i += blockDim.x) {
     float s0 = 0.f, s1 = 0.f;
-    for (int m = 0; m < RV_F; ++m) {
-      const float2 z = mm[size_t(m) * 2 * RV_BINS + i];
+    for (int m = 0; m < c.rv_f; ++m) {
+      const float2 z = mm[size_t(m) * 2 * bins + i];
       s0 += z.x;
       s1 += z.y;
     }
-    g0[i / RV_BINS][i % RV_BINS] = s0;
-    gd[i / RV_BINS][i % RV_BINS] = s1;
+    g0[i / bins][i % bins] = s0;
+    gd[i / bins][i % bins] = s1;
   }
   __syncthreads();
+  if (c.rv_paper) {   // uniform over the launch
+    const int K = c.rv_n / 2;
+    for (int i = threadIdx.x; i < 4 * K; i += blockDim.x) {
+      const int x = i / (2 * K), r = i % (2 * K);
+      out[i] = r < K ? g0[x][r] : gd[x][r - K];
+    }
+    return;
+  }
   if (threadIdx.x < 48) {
     const int x = threadIdx.x / 24, r = threadIdx.x % 24, b = r % 12;
     const float* src = r < 12 ? g0[x] : gd[x];
@@ -384,8 +529,13 @@ int launch_reverb(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
   const dim3 chunks(DL_M / DL_CHUNK, n);
   switch (what) {
     case 0:  // impulse responses and their partition spectra
-      k_rv_noise_stft<<<RV_F, RV_N / 16, 0, s>>>(c);
-      k_rv_ir_frames<<<dim3(RV_F, n), RV_N / 16, 0, s>>>(c, a);
+      if (c.rv_paper) {
+        k_rv_noise_dft<<<c.rv_f, 256, 0, s>>>(c);
+        k_rv_ir_frames_dft<<<dim3(c.rv_f, n), 128, 0, s>>>(c, a);
+      } else {
+        k_rv_noise_stft<<<RV_F, RV_N / 16, 0, s>>>(c);
+        k_rv_ir_frames<<<dim3(RV_F, n), RV_N / 16, 0, s>>>(c, a);
+      }
       k_rv_ir_ola<<<dim3((RV_HLEN + 255) / 256, n), 256, 0, s>>>(c, a);
       k_rv_hspec<<<dim3(RV_P, n), DL_M / 16, sm_fft, s>>>(c, a);
       return 4;
@@ -400,7 +550,10 @@ int launch_reverb(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
     case 3:  // parameter gradients
       k_rv_acc<2><<<chunks, 256, sm2, s>>>(c, a);
       k_rv_inv<2><<<dim3(RV_P, n), DL_M / 16, sm_fft, s>>>(c, a);
-      k_rv_gfr<<<dim3(RV_F, n), RV_N / 16, 0, s>>>(c, a);
+      if (c.rv_paper)
+        k_rv_gfr_dft<<<dim3(c.rv_f, n), 128, 0, s>>>(c, a);
+      else
+        k_rv_gfr<<<dim3(RV_F, n), RV_N / 16, 0, s>>>(c, a);
       k_rv_grad<<<n, 256, 0, s>>>(c, a);
       return 4;
   }

@@ -123,6 +123,41 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
   }
   if (opts.eq_taps < 3 || opts.eq_taps % 2 == 0 || opts.eq_taps > 2047)
     return fail(GRAFX_EINVAL, "eq_taps must be odd in [3, 2047]");
+  if (opts.sample_rate < 8000 || opts.sample_rate > 192000)
+    return fail(GRAFX_EINVAL, "sample_rate must be in [8000, 192000] Hz");
+  // ---- processor layouts (Sec. 3 settings)
+  if (opts.eq_params != GRAFX_EQ_BANDS && opts.eq_params != GRAFX_EQ_LOGMAG)
+    return fail(GRAFX_EINVAL, "eq_params must be GRAFX_EQ_BANDS or GRAFX_EQ_LOGMAG");
+  if (opts.delay_layout != GRAFX_DELAY_COMPACT && opts.delay_layout != GRAFX_DELAY_SLOTS)
+    return fail(GRAFX_EINVAL, "delay_layout must be GRAFX_DELAY_COMPACT or GRAFX_DELAY_SLOTS");
+  if (opts.reverb_layout != GRAFX_REVERB_COMPACT && opts.reverb_layout != GRAFX_REVERB_PAPER)
+    return fail(GRAFX_EINVAL, "reverb_layout must be GRAFX_REVERB_COMPACT or GRAFX_REVERB_PAPER");
+  p->eq_logmag = opts.eq_params == GRAFX_EQ_LOGMAG;
+  if (opts.delay_layout == GRAFX_DELAY_SLOTS) {
+    p->dl_taps = DL_SLOT_TAPS;
+    p->dl_nd = p->dl_slot = opts.sample_rate / 10;   // 100 ms
+  }
+  {
+    // lags [-B, (P-1) B) must cover [-H, reach + H), reach = (taps-1) slot + N_d
+    const int64_t reach = int64_t(p->dl_taps - 1) * p->dl_slot + p->dl_nd + (DL_FIR - 1) / 2;
+    p->dl_P = int32_t(1 + (reach + DL_B - 1) / DL_B);
+    if (p->dl_P > DL_PMAX) return fail(GRAFX_EINVAL, "delay slots too long for this sample rate (at most 65 kHz)");
+  }
+  if (opts.reverb_layout == GRAFX_REVERB_PAPER) {
+    p->rv_paper = 1;
+    p->rv_n = RV_PN;
+    p->rv_hop = RV_PHOP;
+    p->rv_f = 1 + RV_LEN / RV_PHOP;
+  }
+  {
+    int32_t* c = p->pcols;
+    c[GRAFX_T_GAIN] = 2;
+    c[GRAFX_T_IMAGER] = 1;
+    c[GRAFX_T_EQ] = p->eq_logmag ? (opts.eq_taps + 1) / 2 : 8;
+    c[GRAFX_T_COMP] = c[GRAFX_T_GATE] = 4;
+    c[GRAFX_T_DELAY] = 2 * p->dl_taps * DL_ROW;
+    c[GRAFX_T_REVERB] = p->rv_paper ? 4 * (p->rv_n / 2) : RV_COLS;
+  }
   int nthr = opts.n_threads > 0 ? opts.n_threads : int(std::max(1u, std::thread::hardware_concurrency()));
   rc = make_schedule(p->types, p->edges, opts.schedule, opts.beam_width, nthr, &p->sched);
   if (rc) return rc;
@@ -384,12 +419,12 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
         for (int32_t ch = 0; ch < 2; ++ch)
           for (int32_t t0 = 0; t0 < L; t0 += DL_TILE) sub[0].push_back({v, t0, ch, 0});
         p->node_ext[v].x = p->n_dl_slots;
-        p->node_ext[v].y = p->node_ext[v].z * DL_P;
-        for (int32_t w = -DL_P; w < nb; ++w) sub[1].push_back({v, w, 0, p->n_dl_slots++});
+        p->node_ext[v].y = p->node_ext[v].z * p->dl_P;
+        for (int32_t w = -p->dl_P; w < nb; ++w) sub[1].push_back({v, w, 0, p->n_dl_slots++});
         for (int32_t b = 0; b < nb; ++b) sub[1].push_back({v, b, 1, p->n_dl_slots++});
         for (int32_t ck = 0; ck < DL_M / DL_CHUNK; ++ck) sub[2].push_back({v, ck, 0, 0});
-        for (int32_t q = 0; q < DL_P; ++q) sub[3].push_back({v, q, 0, 0});
-        for (int32_t xm = 0; xm < 2 * DL_TAPS; ++xm) sub[4].push_back({v, xm, 0, 0});
+        for (int32_t q = 0; q < p->dl_P; ++q) sub[3].push_back({v, q, 0, 0});
+        for (int32_t xm = 0; xm < 2 * p->dl_taps; ++xm) sub[4].push_back({v, xm, 0, 0});
       }
       for (int i = 0; i < 5; ++i) {
         s.dsub_begin[i] = int32_t(bwd.size());
@@ -463,9 +498,17 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
     for (int j = 0; j < 9; ++j) {
       if (j) fact *= j;
       double s = 0.0;
-      for (int k = 0; k < DL_NFFT; ++k) s += std::pow(double(k) / DL_NFFT, j + 1);
-      p->dl_taylor[j] = s / DL_NFFT / fact;
+      for (int k = 0; k < p->dl_nd; ++k) s += std::pow(double(k) / p->dl_nd, j + 1);
+      p->dl_taylor[j] = s / p->dl_nd / fact;
     }
+  }
+  // reverb frame window (periodic Hann) and DFT twiddles of its STFT size
+  p->rv_win.resize(p->rv_n);
+  p->rv_cs.resize(p->rv_n);
+  for (int j = 0; j < p->rv_n; ++j) {
+    const double a = 2.0 * M_PI * j / p->rv_n;
+    p->rv_win[j] = float(0.5 - 0.5 * std::cos(a));
+    p->rv_cs[j] = float2_{float(std::cos(a)), float(std::sin(a))};
   }
   // reverb band interpolation over the 513 STFT bins (same rule as the EQ's bands)
   {
@@ -546,6 +589,8 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
     w.eq_hann = take(4 * p->eq_hann.size());
     w.eq_band = take(4 * p->eq_band.size());
     w.rv_band = take(4 * p->rv_band.size());
+    w.rv_win = take(4 * p->rv_win.size());
+    w.rv_cs = take(sizeof(float2_) * p->rv_cs.size());
     size_t nrow = std::max<size_t>(p->loss.rows.size(), 1);
     w.loss_rows = take(sizeof(LossRow) * nrow);
     w.loss_items = take(sizeof(int4_) * std::max<size_t>(p->loss.items.size(), 1));
@@ -559,19 +604,20 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
     w.eq_aux = take(4 * size_t(std::max(p->n_eq, 1)) * 1024);
     w.eq_bandpart = take(4 * size_t(std::max(p->n_eq, 1)) * 16 * 8);
     w.comp_carry = take(4 * size_t(std::max(p->n_comp_chunks, 1)));
-    w.dl_aux = take(4 * size_t(std::max(p->n_delay, 1)) * DL_AUX);
+    w.dl_aux = take(4 * size_t(std::max(p->n_delay, 1)) * 2 * p->dl_taps * (DL_FIR + 1));
     w.dl_spec = take(8 * size_t(std::max(p->n_dl_slots, 1)) * DL_M);
-    w.dl_R = take(8 * size_t(std::max(p->n_delay, 1)) * DL_P * DL_M);
-    w.dl_r = take(4 * size_t(std::max(p->n_delay, 1)) * 2 * DL_NLAG);
+    w.dl_R = take(8 * size_t(std::max(p->n_delay, 1)) * p->dl_P * DL_M);
+    w.dl_r = take(4 * size_t(std::max(p->n_delay, 1)) * 2 * p->dl_P * DL_B);
     const size_t nr = size_t(std::max(p->n_reverb, 1));
-    w.rv_U = take(8 * size_t(2) * RV_F * RV_BINS);
-    w.rv_fr = take(8 * nr * RV_F * RV_N);
+    const size_t rbins = size_t(p->rv_n / 2 + 1);
+    w.rv_U = take(8 * size_t(2) * p->rv_f * rbins);
+    w.rv_fr = take(8 * nr * p->rv_f * p->rv_n);
     w.rv_h = take(4 * nr * 2 * RV_HLEN);
     w.rv_H = take(8 * nr * RV_P * DL_M);
     w.rv_Y = take(8 * nr * size_t(std::max(p->rv_nbmax, 1)) * DL_M);
     w.rv_R = take(8 * nr * RV_P * DL_M);
     w.rv_r = take(4 * nr * 2 * RV_HLEN);
-    w.rv_mm = take(8 * nr * RV_F * 2 * RV_BINS);
+    w.rv_mm = take(8 * nr * p->rv_f * 2 * rbins);
     w.partial = take(16 * size_t(std::max(p->n_partials, 1)));
     w.eq_partial = take(8 * size_t(std::max(p->n_eq_runs, 1)) * (p->eq_fft / 2 + 1));
     w.loss_part = take(32 * size_t(std::max(p->loss.n_groups_total, 1)));

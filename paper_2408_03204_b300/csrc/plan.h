@@ -43,7 +43,7 @@ struct StepInfo {
 // Byte offsets of the regions inside the caller's workspace.
 struct WsLayout {
   size_t nodes, node_ext, csr_ptr, csr_src, tcsr_ptr, tcsr_dst, items;
-  size_t twiddle, ptw, eq_cos, eq_hann, eq_band;
+  size_t twiddle, ptw, eq_cos, eq_hann, eq_band, rv_win, rv_cs;
   size_t loss_rows, loss_items;
   size_t tables_end;                           // [0, tables_end) is uploaded at bind time
   size_t status, tickets, flags, flags_bytes;  // flags_bytes covers status+tickets+flags (cleared per call)
@@ -88,6 +88,11 @@ struct Plan {
   double dl_taylor[9] = {0};
   int32_t eq_taps = 1023, eq_H = 511, eq_fft = 4096, eq_step = 0;  // eq_step: outputs per block
   int32_t comp_chunk = 2048;
+  // processor layouts (grafx_plan_opts eq_params, delay_layout, reverb_layout)
+  int32_t eq_logmag = 0;
+  int32_t dl_taps = DL_TAPS, dl_nd = DL_NFFT, dl_slot = 0, dl_P = 10;
+  int32_t rv_paper = 0, rv_n = RV_N, rv_hop = RV_HOP, rv_f = RV_F;
+  int32_t pcols[GRAFX_N_TYPES] = {0};    // columns of P[t]
   int32_t ckpt_steps = 0;                // signal checkpointing: steps per segment (0 = off)
   std::vector<int32_t> seg_ptr;          // first step of each segment, then N + 1
   int64_t src_elems = 0, out_elems = 0, node_samples = 0;
@@ -97,7 +102,8 @@ struct Plan {
   WsLayout ws;
   // host tables
   std::vector<float2_> twiddle, ptw;
-  std::vector<float> eq_cos, eq_hann, eq_band, rv_band;
+  std::vector<float> eq_cos, eq_hann, eq_band, rv_band, rv_win;
+  std::vector<float2_> rv_cs;            // (cos, sin)(2 pi j / rv_n): the reverb's frame DFTs
   // bindings
   char* dev_ws = nullptr;
   const float* params[GRAFX_N_TYPES] = {nullptr};

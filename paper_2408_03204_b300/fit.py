@@ -15,24 +15,30 @@ from . import PARAM_COLS, T_COMP, T_DELAY, T_GATE, T_REVERB, _check, _ptr, _stre
 MAP_IDENT, MAP_ALPHA, MAP_SOFTPLUS, MAP_RATIO, MAP_NEGSP = range(5)
 
 
-def param_codes(t):
-    """Per-column map codes of parameter type t (a list of PARAM_COLS[t] ints)."""
-    cols = PARAM_COLS[t]
+def param_codes(t, cols=None):
+    """Per-column map codes of parameter type t (a list of cols ints; cols defaults to
+    the compact layout's width PARAM_COLS[t])."""
+    cols = PARAM_COLS[t] if cols is None else cols
     if t in (T_COMP, T_GATE):
         return [MAP_ALPHA, MAP_IDENT, MAP_SOFTPLUS, MAP_RATIO]
-    if t == T_REVERB:
+    if t == T_REVERB and cols == 50:
         # [mid/side][H0 x 12, H_delta x 12], then wet and dry gains
         return ([MAP_IDENT] * 12 + [MAP_NEGSP] * 12) * 2 + [MAP_IDENT, MAP_IDENT]
+    if t == T_REVERB:
+        # per-bin layout: [mid/side][H0 x K, H_delta x K]
+        K = cols // 4
+        return ([MAP_IDENT] * K + [MAP_NEGSP] * K) * 2
     return [MAP_IDENT] * cols
 
 
 def neutral_params(plan, torch, device):
     """Nearly transparent physical parameters for every type the plan holds: 0 dB gains,
     flat EQ, centred image, compressor and noisegate with ratio 1.001, delays of
-    44 samples (1 ms) through four 0.25 taps, reverb dry only (wet gain e^-30)."""
+    44 samples (1 ms) into each slot through taps of 1/(taps per channel), reverb dry
+    only (wet gain e^-30; the paper's wet-only reverb gets a quiet -36 dB, 0.5 s tail)."""
     import math
     P = {}
-    for t, cols in PARAM_COLS.items():
+    for t, cols in plan.param_cols.items():
         rows = plan.info.n_type_rows[t]
         if not rows:
             continue
@@ -40,13 +46,19 @@ def neutral_params(plan, torch, device):
         if t in (T_COMP, T_GATE):  # ratio 1.001: (nearly) no compression / expansion
             p[:, 0], p[:, 1], p[:, 2], p[:, 3] = 0.99, 0.0, 3.0 * math.log(10.0) / 10.0, 1.001
         if t == T_DELAY:
-            q = p.view(rows, 2, 4, 22)
-            ang = -2.0 * math.pi * 44 / 32768
-            q[..., 0], q[..., 1], q[..., 2:] = math.cos(ang), math.sin(ang), math.log(0.25)
-        if t == T_REVERB:
+            taps = cols // 44
+            q = p.view(rows, 2, taps, 22)
+            ang = -2.0 * math.pi * 44 / (32768 if taps == 4 else plan.sample_rate // 10)
+            q[..., 0], q[..., 1], q[..., 2:] = math.cos(ang), math.sin(ang), math.log(1.0 / taps)
+        if t == T_REVERB and cols == 50:
             p[:, 12:24] = -0.05
             p[:, 36:48] = -0.05
             p[:, 49] = -30.0
+        elif t == T_REVERB:
+            K = cols // 4
+            q = p.view(rows, 2, 2, K)
+            q[:, :, 0] = -36.0 * math.log(10.0) / 20.0
+            q[:, :, 1] = -3.0 * math.log(10.0) * 192 / (0.5 * plan.sample_rate)
         P[t] = p
     return P
 
@@ -69,7 +81,8 @@ class Fit:
         self.lr, self.b1, self.b2, self.eps = lr, betas[0], betas[1], eps
         self.P = params
         plan.bind_params(self.P)
-        self.codes = {t: torch.tensor(param_codes(t), dtype=torch.int8, device=dev) for t in self.P}
+        self.codes = {t: torch.tensor(param_codes(t, self.P[t].shape[1]), dtype=torch.int8, device=dev)
+                      for t in self.P}
         self.theta, self.m, self.v, self.g = {}, {}, {}, {}
         with torch.cuda.stream(self.stream):
             for t, p in self.P.items():

@@ -51,11 +51,11 @@ def split_rows(flat, graphs, lengths, kind=synth.O):
     return out
 
 
-def union_params(graphs, seed):
+def union_params(graphs, seed, preset="compact"):
     """One parameter table per type over the union (original order), seeded per graph."""
     tabs = {}
     for k, g in enumerate(graphs):
-        for t, a in synth.random_params(g, seed + k).items():
+        for t, a in synth.random_params(g, seed + k, preset=preset).items():
             tabs.setdefault(t, []).append(a)
     return {t: np.concatenate(v) for t, v in tabs.items()}
 

@@ -113,6 +113,40 @@ def test_bad_options_rejected(gx):
         gx.Plan([g], [0])
 
 
+def test_paper_layout_widths_and_bad_layouts(gx):
+    """The paper's processor settings (Sec. 3) as plan options: parameter widths from the
+    plan match the paper's sizes; unknown layouts and sample rates the slot delay cannot
+    cover are rejected."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_param_sizes.json")))
+    g = gx.Graph.from_lists([0, 5, 7, 8, 3, 4, 6, 9, 1], [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 6),
+                                                         (6, 7), (7, 8)])
+    p = gx.Plan([g], [8192], preset="paper")
+    assert p.param_cols[5] == gold["eq_params"] and p.param_cols[7] == gold["delay_params"]
+    assert p.param_cols[8] == gold["reverb_params"] and p.param_cols[3] == gold["gain_params"]
+    assert p.param_cols[4] == gold["imager_params"] and p.param_cols[6] == gold["compressor_params"]
+    c = gx.Plan([g], [8192])
+    assert c.param_cols == {3: 2, 4: 1, 5: 8, 6: 4, 7: 176, 8: 50, 9: 4}
+    # one setting of the preset overridden: band EQ on the paper's other layouts
+    m = gx.Plan([g], [8192], preset="paper", eq_params="bands")
+    assert m.param_cols[5] == 8 and m.param_cols[7] == 880
+    # EQ log-magnitudes follow eq_taps
+    assert gx.Plan([g], [8192], eq_params="logmag", eq_taps=255).param_cols[5] == 128
+    o = gx.PlanOpts()
+    gx.lib().grafx_plan_opts_default(gx.ctypes.byref(o))
+    for field, bad in (("eq_params", 2), ("delay_layout", 5), ("reverb_layout", -1)):
+        o2 = gx.PlanOpts.from_buffer_copy(o)
+        setattr(o2, field, bad)
+        h = gx._P()
+        hs = (gx._P * 1)(g._h)
+        ls = (gx.ctypes.c_int64 * 1)(8192)
+        assert gx.lib().grafx_plan_create(hs, 1, ls, gx.ctypes.byref(o2), gx.ctypes.byref(h)) == 1
+    with pytest.raises(gx.GrafxError):
+        gx.Plan([g], [8192], preset="paper", sample_rate=96000)
+    gx.Plan([g], [8192], preset="paper", sample_rate=48000)
+
+
 def test_optimal_size_limit(gx):
     rng = np.random.Generator(np.random.PCG64(5))
     g = random_dag(rng, n_mid=40)
