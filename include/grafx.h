@@ -124,7 +124,12 @@ typedef struct {
   int32_t eq_params;      /* GRAFX_EQ_*: what a row of P[eq] holds (default BANDS) */
   int32_t delay_layout;   /* GRAFX_DELAY_*: taps of the multitap delay (default COMPACT) */
   int32_t reverb_layout;  /* GRAFX_REVERB_*: STFT and masks of the reverb (default COMPACT) */
-  int32_t reserved[5];
+  int32_t source_batch;   /* source-level batch B (Sec. 2 "Batched processing"): 0 or 1 = none;
+                           * B > 1 renders the graphs B times on B source sets with the same
+                           * parameters.  Sources and outputs are [B][the rows of one pass]
+                           * (copy-major); parameter tables keep the rows of one pass and
+                           * their gradients are summed over the B copies in copy order. */
+  int32_t reserved[4];
 } grafx_plan_opts;
 
 /* Processor settings (Sec. 3).  The COMPACT layouts are small parameter sets for
@@ -170,6 +175,9 @@ typedef struct {
   size_t ws_bytes;            /* device workspace bytes (render + backprop + loss) */
   int32_t eq_fft, comp_chunk; /* the tile sizes in use */
   int32_t param_cols[GRAFX_N_TYPES];  /* columns of P[t] under the plan's layouts (0: none) */
+  int32_t source_batch;       /* B (1 without a source batch); n_graphs, n_nodes, n_edges,
+                               * n_inputs, n_outputs, src_elems, out_elems and node_samples
+                               * count all B copies, n_type_rows one copy */
 } grafx_plan_info_t;
 
 int grafx_plan_info(const grafx_plan* p, grafx_plan_info_t* info);
@@ -244,7 +252,9 @@ int grafx_render_steps(grafx_plan* p, const float* sources, float* out, int32_t 
  * k = 0 stands for the source adjoints (written only if d_sources is not NULL).
  * Without checkpointing grafx_backprop is first = 0, last = N+1.  With checkpointing
  * the node rows of a step are valid only while its segment is the one rendered last,
- * so a range must lie in that segment (grafx_backprop orders this itself). */
+ * so a range must lie in that segment (grafx_backprop orders this itself).  With a
+ * source batch (B > 1) only the whole range first = 0, last = N+1 is accepted (the
+ * gradients of the copies are summed after the last step); otherwise GRAFX_ESTATE. */
 int grafx_backprop_steps(grafx_plan* p, const float* sources, const float* d_out, float* const* d_params,
                          float* d_sources, int32_t first, int32_t last, void* stream);
 

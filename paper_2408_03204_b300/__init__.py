@@ -43,7 +43,7 @@ class PlanOpts(ctypes.Structure):
                 ("sample_rate", ctypes.c_int32), ("n_threads", ctypes.c_int32), ("eq_fft", ctypes.c_int32),
                 ("comp_chunk", ctypes.c_int32), ("checkpoint_steps", ctypes.c_int32),
                 ("eq_params", ctypes.c_int32), ("delay_layout", ctypes.c_int32), ("reverb_layout", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("source_batch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -52,7 +52,7 @@ class PlanInfo(ctypes.Structure):
                 ("n_type_rows", ctypes.c_int32 * N_TYPES), ("src_elems", ctypes.c_int64),
                 ("out_elems", ctypes.c_int64), ("node_samples", ctypes.c_int64), ("ws_bytes", ctypes.c_size_t),
                 ("eq_fft", ctypes.c_int32), ("comp_chunk", ctypes.c_int32),
-                ("param_cols", ctypes.c_int32 * N_TYPES)]
+                ("param_cols", ctypes.c_int32 * N_TYPES), ("source_batch", ctypes.c_int32)]
 
 
 _lib = None
@@ -192,11 +192,13 @@ class Plan:
 
     def __init__(self, graphs, lengths, schedule="beam", beam_width=32, eq_taps=None, sample_rate=44100,
                  n_threads=0, eq_fft=0, comp_chunk=0, checkpoint_steps=0, preset="compact", eq_params=None,
-                 delay_layout=None, reverb_layout=None):
+                 delay_layout=None, reverb_layout=None, source_batch=1):
         """preset "compact" (8 EQ bands, 4-tap delays, 1024/256 reverb with 12 bands) or
         "paper" (Sec. 3: 2047-tap EQ by its 1024 log-magnitudes, 20 delay taps in 100 ms
         slots, 384/192 reverb with 192 log-magnitudes per filter); the keyword
-        arguments override single settings of the preset."""
+        arguments override single settings of the preset.  source_batch B > 1 renders
+        the graphs on B source sets with shared parameters: sources and outputs are
+        [B][rows of one pass], gradients are summed over the copies."""
         pre = PRESETS[preset]
         o = PlanOpts()
         lib().grafx_plan_opts_default(ctypes.byref(o))
@@ -207,6 +209,7 @@ class Plan:
         o.eq_params = EQ_PARAMS[eq_params or pre["eq_params"]]
         o.delay_layout = DELAY_LAYOUT[delay_layout or pre["delay_layout"]]
         o.reverb_layout = REVERB_LAYOUT[reverb_layout or pre["reverb_layout"]]
+        o.source_batch = int(source_batch)
         hs = (_P * len(graphs))(*[g._h for g in graphs])
         ls = (ctypes.c_int64 * len(lengths))(*[int(x) for x in lengths])
         h = _P()

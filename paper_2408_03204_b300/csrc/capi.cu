@@ -248,6 +248,7 @@ int grafx_plan_info(const grafx_plan* p, grafx_plan_info_t* info) {
   info->eq_fft = p->eq_fft;
   info->comp_chunk = p->comp_chunk;
   std::memcpy(info->param_cols, p->pcols, sizeof(info->param_cols));
+  info->source_batch = p->source_batch;
   return GRAFX_OK;
 }
 
@@ -420,6 +421,17 @@ int grafx_node_inputs(grafx_plan* p, const float* sources, const float* out, con
 static int backprop_range(grafx_plan* p, const float* sources, const float* d_out, float* const* d_params,
                           float* d_sources, int32_t first, int32_t last, cudaStream_t s);
 
+// Source batch: sum the B copies' gradient rows into the caller's tables.
+static int fold_copies(grafx_plan* p, float* const* d_params, cudaStream_t s) {
+  if (p->source_batch <= 1 || !d_params) return 0;
+  int launches = 0;
+  for (int t = 0; t < GRAFX_N_TYPES; ++t)
+    if (d_params[t] && p->n_type_rows[t] > 0 && p->pcols[t] > 0)
+      launches += launch_fold_copies(at<float>(p, p->ws.dgrad) + p->dgrad_off[t], d_params[t],
+                                     int64_t(p->n_type_rows[t]) * p->pcols[t], p->source_batch, s);
+  return launches;
+}
+
 int grafx_backprop_steps(grafx_plan* p, const float* sources, const float* d_out, float* const* d_params,
                          float* d_sources, int32_t first, int32_t last, void* stream) {
   if (!p || !sources || !d_out) return fail(GRAFX_EINVAL, "null argument");
@@ -427,8 +439,11 @@ int grafx_backprop_steps(grafx_plan* p, const float* sources, const float* d_out
   if (rc) return rc;
   const int N = int(p->sched.string.size()) - 1;
   if (first < 0 || last > N + 1 || first > last) return fail(GRAFX_EINVAL, "step range out of bounds");
-  p->last_launches = backprop_range(p, sources, d_out, d_params, d_sources, first, last,
-                                    static_cast<cudaStream_t>(stream));
+  if (p->source_batch > 1 && (first != 0 || last != N + 1))
+    return fail(GRAFX_ESTATE, "with a source batch the backward runs over every step");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->last_launches = backprop_range(p, sources, d_out, d_params, d_sources, first, last, s);
+  p->last_launches += fold_copies(p, d_params, s);
   return cuda_check(cudaGetLastError(), "backprop launch");
 }
 
@@ -444,6 +459,7 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
     c.params = p->params[st.type];
     c.pcols = param_cols(p, st.type);
     c.dparams = d_params ? d_params[st.type] : nullptr;
+    if (c.dparams && p->source_batch > 1) c.dparams = at<float>(p, p->ws.dgrad) + p->dgrad_off[st.type];
     switch (st.type) {
       case GRAFX_T_EQ:
         launches += launch_eq(2, c, st.bitem_begin, st.bitem_count, s);
@@ -497,6 +513,7 @@ int grafx_backprop(grafx_plan* p, const float* sources, const float* d_out, floa
     if (j < nseg - 1) launches += render_range(p, sources, nullptr, a, b, s);
     launches += backprop_range(p, sources, d_out, d_params, d_sources, j == 0 ? 0 : a, b, s);
   }
+  launches += fold_copies(p, d_params, s);
   p->last_launches = launches;
   return cuda_check(cudaGetLastError(), "checkpointed backprop launch");
 }

@@ -14,9 +14,12 @@ struct alignas(16) NodeDev {
   int64_t off_a;   // float offset of the [2][pitch] adjoint row inside its buffer
   int32_t len;     // signal length L of the node's graph
   int32_t pitch;   // channel stride (L rounded up to a multiple of 4)
-  int32_t prow;    // row of P[type] owned by the node (I^P of Algorithm 1)
+  int32_t prow;    // row of P[type] read by the node (I^P of Algorithm 1)
   int16_t kind;    // NodeKind
   int16_t type;    // GRAFX_T_*
+  int32_t grow;    // row of the gradient table the backward writes: prow, or with a
+                   // source batch the node's own row of the per-copy gradient table
+  int32_t pad[3];
 };
 
 struct alignas(16) int4_ { int32_t x, y, z, w; };

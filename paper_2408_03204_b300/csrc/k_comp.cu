@@ -501,7 +501,7 @@ __global__ void k_comp_finalize(DevCtx c, int node_begin, int node_end) {
     float4 q = c.partial[e.x + k];
     s.x += q.x; s.y += q.y; s.z += q.z; s.w += q.w;
   }
-  float* d = c.dparams + c.nodes[v].prow * 4;
+  float* d = c.dparams + c.nodes[v].grow * 4;
   d[0] = s.x; d[1] = s.y; d[2] = s.z; d[3] = s.w;
 }
 

@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
     const float* r = c.dl_r + size_t(e.z) * 2 * nlag + x * nlag + DL_B;  // r[n] at r + n
     const float* rs = r + m * c.dl_slot;                                 // the tap's slot: rs[n] = r[m S + n]
     const float* q = c.params + size_t(nd.prow) * c.pcols + (x * ntap + m) * DL_ROW;
-    float* out = c.dparams + size_t(nd.prow) * c.pcols + (x * ntap + m) * DL_ROW;
+    float* out = c.dparams + size_t(nd.grow) * c.pcols + (x * ntap + m) * DL_ROW;
     const int d = int(aux[DL_FIR]);
     __syncthreads();
     if (threadIdx.x < DL_FIR) cs[threadIdx.x] = aux[threadIdx.x];

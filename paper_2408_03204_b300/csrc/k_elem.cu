@@ -4,6 +4,8 @@
 // aggregation (Algorithm 1 Gather + Aggregate) are fused into the loads, the store
 // (Algorithm 1 Store) into the epilogue.  HBM-bound: 8 B x in-degree read and 8 B
 // written per node-sample forward.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -176,9 +178,26 @@ __global__ void k_ew_finalize(DevCtx c, int node_begin, int node_end, int cols) 
     s0 += q.x;
     s1 += q.y;
   }
-  const int row = c.nodes[v].prow;
+  const int row = c.nodes[v].grow;
   c.dparams[row * cols] = s0;
   if (cols > 1) c.dparams[row * cols + 1] = s1;
+}
+
+// Source batch: dst[i] = sum_b part[b n + i] over the B copies in copy order (the
+// gradient of a shared parameter row is the sum of its copies' gradients).
+__global__ void k_fold_copies(const float* __restrict__ part, float* __restrict__ dst, int64_t n, int B) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s += part[int64_t(b) * n + i];
+    dst[i] = s;
+  }
+}
+
+int launch_fold_copies(const float* part, float* dst, int64_t n, int B, cudaStream_t s) {
+  if (n <= 0) return 0;
+  const int blocks = int(std::min<int64_t>((n + 255) / 256, 148 * 8));
+  k_fold_copies<<<blocks, 256, 0, s>>>(part, dst, n, B);
+  return 1;
 }
 
 static int grid_for(int n_items, int per_sm) {

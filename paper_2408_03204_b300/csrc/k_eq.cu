@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(EQ_CHUNK) k_eq_gradbands(DevCtx c, int node_be
     }
     const float pk = A[k] * acc * (k == 0 ? 1.f : 2.f) / float(N);
     if (c.eq_logmag) {   // the row is p_e itself: dL/dp_e[k], no band matrix
-      c.dparams[size_t(nd.prow) * K + k] = pk;
+      c.dparams[size_t(nd.grow) * K + k] = pk;
     } else {
       const float* row = c.eq_band + k * 8;
 #pragma unroll
@@ -321,7 +321,7 @@ __global__ void k_eq_gradout(DevCtx c, int node_begin, int node_end, int n_chunk
   float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int q = 0; q < n_chunks; ++q)
     for (int b = 0; b < 8; ++b) s[b] += c.eq_bandpart[(size_t(z) * n_chunks + q) * 8 + b];
-  float* d = c.dparams + c.nodes[v].prow * 8;
+  float* d = c.dparams + c.nodes[v].grow * 8;
   for (int b = 0; b < 8; ++b) d[b] = LN10_20 * s[b];
 }
 

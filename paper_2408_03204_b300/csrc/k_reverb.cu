@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(256) k_rv_grad(DevCtx c, int node_begin) {
   const NodeDev nd = c.nodes[v];
   const int ri = c.ext[v].z, bins = c.rv_n / 2 + 1;
   const float* q = c.params + size_t(nd.prow) * c.pcols;
-  float* out = c.dparams + size_t(nd.prow) * c.pcols;
+  float* out = c.dparams + size_t(nd.grow) * c.pcols;
   const float2* mm = c.rv_mm + size_t(ri) * c.rv_f * 2 * bins;
   for (int i = threadIdx.x; i < 2 * bins; i += blockDim.x) {
     float s0 = 0.f, s1 = 0.f;

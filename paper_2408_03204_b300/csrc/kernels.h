@@ -13,6 +13,8 @@ int grid_size(int n_items, int per_sm);
 int launch_ew_fwd(int type, const DevCtx& c, int item0, int n_items, cudaStream_t s);
 int launch_ew_bwd(int type, const DevCtx& c, int item0, int n_items, cudaStream_t s);
 int launch_ew_finalize(const DevCtx& c, int node_begin, int node_end, int cols, cudaStream_t s);
+// source batch: dst[i] = sum over the B copies of part[b n + i]
+int launch_fold_copies(const float* part, float* dst, int64_t n, int B, cudaStream_t s);
 
 // EQ: what = 0 design (a = node_begin, b = node_end), 1 forward (a = item0,
 // b = n_items), 2 backward (items), 3 gradient finalize (node range)

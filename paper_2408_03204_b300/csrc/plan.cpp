@@ -88,11 +88,23 @@ void fill_fft_tables(std::vector<float2_>& twiddle, std::vector<float2_>& ptw) {
   }
 }
 
-int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* lengths,
+int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* lengths_in,
                const grafx_plan_opts& opts, Plan* p) {
   p->opts = opts;
+  if (graphs_in.empty()) return fail(GRAFX_EINVAL, "no graphs");
+  // source-level batch: B copies of the graph list, copy-major (copy b's rows follow copy b-1's)
+  if (opts.source_batch < 0 || opts.source_batch > 65536) return fail(GRAFX_EINVAL, "source_batch must be in [0, 65536]");
+  p->source_batch = std::max(opts.source_batch, 1);
+  p->graphs_per_copy = int32_t(graphs_in.size());
+  std::vector<const grafx_graph*> graphs;
+  std::vector<int64_t> lens;
+  for (int32_t b = 0; b < p->source_batch; ++b)
+    for (size_t g = 0; g < graphs_in.size(); ++g) {
+      graphs.push_back(graphs_in[g]);
+      lens.push_back(lengths_in[g]);
+    }
+  const int64_t* lengths = lens.data();
   p->n_graphs = int32_t(graphs.size());
-  if (p->n_graphs < 1) return fail(GRAFX_EINVAL, "no graphs");
   // ---- union (graph-level parallelism: one disconnected graph)
   for (int32_t g = 0; g < p->n_graphs; ++g) {
     if (!graphs[g]) return fail(GRAFX_EINVAL, "null graph");
@@ -177,13 +189,20 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
   }
   p->new_types.assign(n, 0);
   p->param_row.assign(n, 0);
+  p->grad_row.assign(n, 0);
   {
     int32_t cnt[GRAFX_N_TYPES] = {0};
     for (int32_t v = 0; v < n; ++v) {
       p->new_types[p->sigma[v]] = p->types[v];
-      p->param_row[p->sigma[v]] = cnt[p->types[v]]++;
+      p->grad_row[p->sigma[v]] = cnt[p->types[v]]++;
     }
-    std::memcpy(p->n_type_rows, cnt, sizeof(cnt));
+    std::memcpy(p->n_rows_union, cnt, sizeof(cnt));
+    // the copies are identical and copy-major: union row r of type t is row r mod R_t of copy r / R_t
+    for (int t = 0; t < GRAFX_N_TYPES; ++t) p->n_type_rows[t] = cnt[t] / p->source_batch;
+    for (int32_t v = 0; v < n; ++v) {
+      const int32_t R = p->n_type_rows[p->new_types[v]];
+      p->param_row[v] = R > 0 ? p->grad_row[v] % R : 0;
+    }
   }
   // ---- in-edge CSR by (dst, src) = I^G / I^A; consumer CSR by (src, dst) for backward
   {
@@ -226,6 +245,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
     nd.len = int32_t(p->L[g]);
     nd.pitch = int32_t(p->pitch[g]);
     nd.prow = p->param_row[vn];
+    nd.grow = p->source_batch > 1 ? p->grad_row[vn] : p->param_row[vn];
     nd.type = int16_t(p->types[vo]);
     int64_t row = 2 * p->pitch[g];
     if (nd.type == GRAFX_T_IN) {
@@ -624,6 +644,14 @@ int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* len
     w.loss_stats = take(32 * nrow * N_RES);
     w.loss_rowloss = take(4 * nrow);
     w.loss_frames = take(4 * size_t(std::max<int64_t>(p->loss.frame_floats, 1)));
+    {
+      int64_t fl = 0;
+      for (int t = 0; t < GRAFX_N_TYPES; ++t) {
+        p->dgrad_off[t] = fl;
+        if (p->source_batch > 1) fl += int64_t(p->n_rows_union[t]) * p->pcols[t];
+      }
+      w.dgrad = take(4 * size_t(std::max<int64_t>(fl, 1)));
+    }
     w.U = take(4 * size_t(std::max<int64_t>(u_floats, 1)));
     w.A = take(4 * size_t(std::max<int64_t>(a_floats, 1)));
     w.total = o;

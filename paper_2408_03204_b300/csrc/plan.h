@@ -51,6 +51,7 @@ struct WsLayout {
   size_t dl_aux, dl_spec, dl_R, dl_r;
   size_t rv_band, rv_U, rv_fr, rv_h, rv_H, rv_Y, rv_R, rv_r, rv_mm;
   size_t loss_part, loss_stats, loss_rowloss, loss_frames;
+  size_t dgrad;                                // per-copy parameter gradients (source batch)
   size_t U, A;
   size_t total;
 };
@@ -93,6 +94,11 @@ struct Plan {
   int32_t dl_taps = DL_TAPS, dl_nd = DL_NFFT, dl_slot = 0, dl_P = 10;
   int32_t rv_paper = 0, rv_n = RV_N, rv_hop = RV_HOP, rv_f = RV_F;
   int32_t pcols[GRAFX_N_TYPES] = {0};    // columns of P[t]
+  // source-level batch: B copies of the graphs (copy-major); n_type_rows counts one copy
+  int32_t source_batch = 1, graphs_per_copy = 0;
+  int32_t n_rows_union[GRAFX_N_TYPES] = {0};
+  int64_t dgrad_off[GRAFX_N_TYPES] = {0};  // float offsets of the per-copy gradient tables (B > 1)
+  std::vector<int32_t> grad_row;         // per new id: row of the per-copy gradient table
   int32_t ckpt_steps = 0;                // signal checkpointing: steps per segment (0 = off)
   std::vector<int32_t> seg_ptr;          // first step of each segment, then N + 1
   int64_t src_elems = 0, out_elems = 0, node_samples = 0;

@@ -147,6 +147,29 @@ def test_paper_layout_widths_and_bad_layouts(gx):
     gx.Plan([g], [8192], preset="paper", sample_rate=48000)
 
 
+def test_source_batch_rows(gx):
+    """Source-level batch (Sec. 2 "Batched processing"): B copies of the graph share the
+    parameter rows of one pass (I^P of every copy equals copy 0's); sources and outputs
+    grow by B; a partial backward range is refused."""
+    g = synth.console_cfg1()
+    h = _to_gx(gx, g)
+    one = gx.Plan([h], [4096])
+    three = gx.Plan([h], [4096], source_batch=3)
+    assert three.info.source_batch == 3 and one.info.source_batch == 1
+    assert list(three.info.n_type_rows) == list(one.info.n_type_rows)
+    assert three.info.src_elems == 3 * one.info.src_elems and three.info.out_elems == 3 * one.info.out_elems
+    assert three.info.n_nodes == 3 * one.info.n_nodes and three.info.node_samples == 3 * one.info.node_samples
+    e1, e3 = one.export(), three.export()
+    assert e3["type_string"] == e1["type_string"]          # the copies run in the same steps
+    n = one.info.n_nodes
+    # new id of copy b's node v is sigma3[b n + v]; its parameter row is copy 0's
+    for b in range(3):
+        for v in range(n):
+            assert e3["param_row"][e3["sigma"][b * n + v]] == e1["param_row"][e1["sigma"][v]]
+    with pytest.raises(gx.GrafxError):
+        gx.Plan([h], [4096], source_batch=-2)
+
+
 def test_optimal_size_limit(gx):
     rng = np.random.Generator(np.random.PCG64(5))
     g = random_dag(rng, n_mid=40)
