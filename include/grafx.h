@@ -268,9 +268,9 @@ int grafx_backprop_steps(grafx_plan* p, const float* sources, const float* d_out
  * Every output length must be >= 2048.  loss: device float32 scalar (written). */
 int grafx_mrstft_forward(grafx_plan* p, const float* out, const float* target, float* loss,
                          void* stream);
-/* dLoss/dout into d_out (laid out like out; overwritten).  Uses the statistics of the
- * last grafx_mrstft_forward on the same plan, which must have been run on the same
- * out and target. */
+/* dLoss/dout into d_out (laid out like out; overwritten).  Uses the statistics and
+ * the per-bin spectra that the last grafx_mrstft_forward on the same plan stored in the
+ * workspace, which must have been run on the same out and target. */
 int grafx_mrstft_backward(grafx_plan* p, const float* out, const float* target, float* d_out,
                           void* stream);
 

@@ -126,6 +126,7 @@ LossLaunch make_loss(const Plan* p, const float* y, const float* tgt) {
   L.part = at<float4>(p, p->ws.loss_part);
   L.stats = at<float4>(p, p->ws.loss_stats);
   L.frames = at<float>(p, p->ws.loss_frames);
+  L.spec = at<float2>(p, p->ws.loss_spec);
   L.tw = at<const float2_>(p, p->ws.twiddle);
   L.ptw = at<const float2_>(p, p->ws.ptw);
   L.n_rows = int(p->loss.rows.size());

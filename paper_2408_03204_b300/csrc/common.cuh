@@ -65,6 +65,15 @@ struct DevCtx {
   int32_t rv_paper, rv_n, rv_hop, rv_f;     // reverb: paper layout, STFT size, hop, frames
 };
 
+// cp.async of 16 bytes into shared memory; the bytes past src_bytes (all 16 when
+// src_bytes = 0, nothing read) are written as zeros.  Both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 __device__ __forceinline__ const float* yrow(const DevCtx& c, const NodeDev& n) {
   return c.ybase[n.kind] + n.off_y;
 }

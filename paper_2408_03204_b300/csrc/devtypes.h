@@ -30,6 +30,8 @@ struct alignas(8) float2_ { float x, y; };
 struct alignas(16) LossRow {
   int64_t off;            // float offset of the row in out / target / d_out
   int64_t frame_off[3];   // float offset of the row's frame buffer per resolution
+  int64_t spec_off[3];    // float2 offset of the row's spectra per resolution: planes
+                          // Y_l, Y_r, (|T_l|, |T_r|) of [frames][M/2+1] each
   int32_t len, pitch;
   int32_t n_frames[3];
   int32_t group_off[3];   // first partial-statistics group of the row per resolution

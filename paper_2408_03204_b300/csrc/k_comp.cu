@@ -235,14 +235,6 @@ __device__ __forceinline__ void load_chunk(const DevCtx& c, int v, const NodeDev
   }
 }
 
-// cp.async of 16 bytes into shared memory; src_bytes = 0 writes zeros (nothing read)
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
-  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 // Prefetch: this thread's SPT samples of both channels of `row` from t into its own
 // slots dst[ch * 256 * SPT + threadIdx.x * SPT ...] (zeros past the node's length).
 // Every thread reads back only its own slots, so one buffer serves consecutive chunks.

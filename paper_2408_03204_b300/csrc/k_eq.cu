@@ -49,9 +49,17 @@ __device__ void eq_magnitudes(const DevCtx& c, const NodeDev& nd, float* A, int 
 
 constexpr int EQ_CHUNK = 64;  // taps (or bins) per CTA of the cosine-sum kernels
 
+// Row stride of the filter spectra (M/2+1 real bins): a multiple of 4 floats so that
+// every row starts 16-byte aligned (staged with cp.async).
+__host__ __device__ constexpr int eq_spec_stride(int M) { return M / 2 + 4; }
+
+constexpr int EQ_SPLIT = 4;    // lanes sharing one cosine sum (adjacent lanes of a warp)
+
 // h[n] = Hann[n] (A_0 + 2 sum_{k>=1} A_k cos(2 pi k n / N)) / N for one chunk of n in
-// [0, H] (the taps are even, h[-n] = h[n]); grid (EQ nodes of the step, chunks).
-__global__ void __launch_bounds__(EQ_CHUNK) k_eq_taps(DevCtx c, int node_begin) {
+// [0, H] (the taps are even, h[-n] = h[n]); grid (EQ nodes of the step, chunks).  The
+// sum over k is split over EQ_SPLIT lanes (k = 1 + part + EQ_SPLIT j) and combined by
+// shuffles in a fixed order.
+__global__ void __launch_bounds__(EQ_CHUNK * EQ_SPLIT) k_eq_taps(DevCtx c, int node_begin) {
   __shared__ float A[1024];
   __shared__ float cs[2048];
   const int v = node_begin + blockIdx.x;
@@ -60,16 +68,20 @@ __global__ void __launch_bounds__(EQ_CHUNK) k_eq_taps(DevCtx c, int node_begin) 
   eq_magnitudes(c, nd, A, K);
   for (int i = threadIdx.x; i < N; i += blockDim.x) cs[i] = c.eq_cos[i];
   __syncthreads();
-  const int n = blockIdx.y * EQ_CHUNK + threadIdx.x;
-  if (n > H) return;
+  const int n = blockIdx.y * EQ_CHUNK + threadIdx.x / EQ_SPLIT, part = threadIdx.x % EQ_SPLIT;
   float s = 0.f;
-  int idx = 0;  // (k n) mod N
-  for (int k = 1; k < K; ++k) {
-    idx += n;
-    if (idx >= N) idx -= N;
-    s += A[k] * cs[idx];
+  if (n <= H) {
+    const int step = (EQ_SPLIT * n) % N;
+    int idx = ((1 + part) * n) % N;  // (k n) mod N
+    for (int k = 1 + part; k < K; k += EQ_SPLIT) {
+      s += A[k] * cs[idx];
+      idx += step;
+      if (idx >= N) idx -= N;
+    }
   }
-  c.eq_aux[size_t(c.ext[v].z) * 1024 + n] = c.eq_hann[n] * (A[0] + 2.f * s) / float(N);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  if (part == 0 && n <= H) c.eq_aux[size_t(c.ext[v].z) * 1024 + n] = c.eq_hann[n] * (A[0] + 2.f * s) / float(N);
 }
 
 // The block spectrum of h placed circularly (real, even), scaled by 1/M.
@@ -87,7 +99,7 @@ __global__ void __launch_bounds__(M / 16) k_eq_spec(DevCtx c, int node_begin) {
   }
   __syncthreads();
   fft::forward<M>(buf, c.ptw, threadIdx.x, true);
-  float* spec = c.eq_spec + size_t(c.ext[v].z) * (M / 2 + 1);
+  float* spec = c.eq_spec + size_t(c.ext[v].z) * eq_spec_stride(M);
   for (int k = threadIdx.x; k <= M / 2; k += blockDim.x) spec[k] = buf[fft::pad(k)].x;
 }
 
@@ -164,7 +176,7 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_fwd(DevCtx c, int item0
     const int v = w.x;
     const NodeDev nd = c.nodes[v];
     const int ws = -Hal + w.y * S;
-    const float* spec = c.eq_spec + size_t(w.z) * (M / 2 + 1);
+    const float* spec = c.eq_spec + size_t(w.z) * eq_spec_stride(M);
     float2 x[16];
     eq_load_regs<M, false>(c, v, nd, ws, x, false, H, S);
     if (even) __syncthreads();
@@ -192,7 +204,7 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_bwd(DevCtx c, int item0
     const int4_ w = c.items[item0 + it];
     const int v = w.x;
     const NodeDev nd = c.nodes[v];
-    const float* spec = c.eq_spec + size_t(c.ext[v].z) * (M / 2 + 1);
+    const float* spec = c.eq_spec + size_t(c.ext[v].z) * eq_spec_stride(M);
     float2 acc[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) acc[m] = make_float2(0.f, 0.f);
@@ -268,7 +280,7 @@ __global__ void __launch_bounds__(M / 16) k_eq_gradfft(DevCtx c, int node_begin)
 // dL/dp_k = A_k (c_k/N) sum_n s[n] cos(2 pi k n / N) for one chunk of k, then this
 // chunk's share of the band-matrix product (with log-magnitude rows, dL/dp_k is the
 // gradient itself and is stored directly); grid (EQ nodes of the step, chunks).
-__global__ void __launch_bounds__(EQ_CHUNK) k_eq_gradbands(DevCtx c, int node_begin) {
+__global__ void __launch_bounds__(EQ_CHUNK * EQ_SPLIT) k_eq_gradbands(DevCtx c, int node_begin) {
   __shared__ float A[1024];
   __shared__ float sv[1024];
   __shared__ float cs[2048];
@@ -281,17 +293,22 @@ __global__ void __launch_bounds__(EQ_CHUNK) k_eq_gradbands(DevCtx c, int node_be
   for (int i = threadIdx.x; i < N; i += blockDim.x) cs[i] = c.eq_cos[i];
   for (int i = threadIdx.x; i <= H; i += blockDim.x) sv[i] = c.eq_aux[size_t(z) * 1024 + i];
   __syncthreads();
-  const int k = blockIdx.y * EQ_CHUNK + threadIdx.x;
-  float bsum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int k = blockIdx.y * EQ_CHUNK + threadIdx.x / EQ_SPLIT, part = threadIdx.x % EQ_SPLIT;
+  float acc = 0.f;
   if (k < K) {
-    float acc = sv[0];
-    int idx = 0;
-    for (int n = 1; n <= H; ++n) {
-      idx += k;
-      if (idx >= N) idx -= N;
+    const int step = (EQ_SPLIT * k) % N;
+    int idx = ((1 + part) * k) % N;  // (k n) mod N
+    for (int n = 1 + part; n <= H; n += EQ_SPLIT) {
       acc += sv[n] * cs[idx];
+      idx += step;
+      if (idx >= N) idx -= N;
     }
-    const float pk = A[k] * acc * (k == 0 ? 1.f : 2.f) / float(N);
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  float bsum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (k < K && part == 0) {
+    const float pk = A[k] * (sv[0] + acc) * (k == 0 ? 1.f : 2.f) / float(N);
     if (c.eq_logmag) {   // the row is p_e itself: dL/dp_e[k], no band matrix
       c.dparams[size_t(nd.grow) * K + k] = pk;
     } else {
@@ -330,11 +347,11 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
   constexpr int T = M / 16;
   static bool init = false;
   const size_t s1 = sizeof(float2) * fft::Padded<M>::size;
-  const size_t stw_bytes = sizeof(float2_) * fft::ptw_size(M);
+  const size_t sf = 2 * s1 + sizeof(float2_) * fft::ptw_size(M);   // two FFT buffers + pass twiddles
   if (!init) {
     cudaFuncSetAttribute(k_eq_spec<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
     cudaFuncSetAttribute(k_eq_gradfft<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
-    cudaFuncSetAttribute(k_eq_fwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(2 * s1 + stw_bytes));
+    cudaFuncSetAttribute(k_eq_fwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sf));
     cudaFuncSetAttribute(k_eq_bwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(3 * s1));
     init = true;
   }
@@ -343,16 +360,16 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
   const int chunks_k = ((c.eq_taps + 1) / 2 + EQ_CHUNK - 1) / EQ_CHUNK;
   switch (what) {
     case 0:
-      k_eq_taps<<<dim3(b - a, chunks_h), EQ_CHUNK, 0, s>>>(c, a);
+      k_eq_taps<<<dim3(b - a, chunks_h), EQ_CHUNK * EQ_SPLIT, 0, s>>>(c, a);
       k_eq_spec<M><<<b - a, T, s1, s>>>(c, a);
       return 2;
     case 1:
-      k_eq_fwd<M><<<grid_size(b, (228 * 1024) / int(2 * s1 + stw_bytes + 1024)), T, 2 * s1 + stw_bytes, s>>>(c, a, b);
+      k_eq_fwd<M><<<grid_size(b, (228 * 1024) / int(sf + 1024)), T, sf, s>>>(c, a, b);
       return 1;
     case 2: k_eq_bwd<M><<<grid_size(b, (228 * 1024) / int(3 * s1 + 1024)), T, 3 * s1, s>>>(c, a, b); return 1;
     case 3:
       k_eq_gradfft<M><<<b - a, T, s1, s>>>(c, a);
-      k_eq_gradbands<<<dim3(b - a, chunks_k), EQ_CHUNK, 0, s>>>(c, a);
+      k_eq_gradbands<<<dim3(b - a, chunks_k), EQ_CHUNK * EQ_SPLIT, 0, s>>>(c, a);
       if (c.eq_logmag) return 2;
       k_eq_gradout<<<(b - a + 63) / 64, 64, 0, s>>>(c, a, b, chunks_k);
       return 3;

@@ -4,13 +4,14 @@
 // (hop M/4, periodic Hann, no padding).  4096/M frames are transformed at once by
 // groups of M/16 threads; left and right are packed as l + i r and separated from
 // the packed spectrum by conjugate symmetry.  The forward pass writes per-item
-// partial sums (sum (|Y|-|T|)^2, sum |T|^2, sum |ln(|Y|+e) - ln(|T|+e)| per channel);
-// a single-CTA reduce turns them into the loss and keeps the norms for the
-// backward pass.  The backward pass recomputes the spectra, forms dL/dY per bin,
-// builds the Hermitian spectra of both channels, packs them and inverts with one
-// FFT, windows the frame and writes it to a frame buffer; an overlap-add kernel
-// then sums the (at most 4 per resolution) frames covering each sample, so no
-// atomics are used anywhere.
+// partial sums (sum (|Y|-|T|)^2, sum |T|^2, sum |ln(|Y|+e) - ln(|T|+e)| per channel)
+// and keeps every bin's Y_l, Y_r and |T_l|, |T_r| in a spectrum cache; a per-row
+// reduce turns the partials into the loss and keeps the norms for the backward pass.
+// The backward pass reads the cached spectra (no transforms of y or the target),
+// forms dL/dY per bin, builds the Hermitian spectra of both channels, packs them and
+// inverts with one FFT, windows the frame and writes it to a frame buffer; an
+// overlap-add kernel then sums the (at most 4 per resolution) frames covering each
+// sample, so no atomics are used anywhere.
 #include "common.cuh"
 #include "fft.cuh"
 #include "kernels.h"
@@ -28,6 +29,7 @@ struct LossArgs {
   float4* part;            // [group] x 2 float4: (s1_l, s2_l, s3_l, 0), (s1_r, s2_r, s3_r, 0)
   float4* stats;           // [row][res] x 2: (nd_l, nt_l, F*(M/2+1), 0), (nd_r, nt_r, ., 0)
   float* frames;           // frame buffer
+  float2* spec;            // spectrum cache: per (row, resolution) planes Y_l, Y_r, (|T_l|, |T_r|)
   const float2_* tw;
   const float2_* ptw;
   int n_items;
@@ -82,6 +84,9 @@ __device__ __forceinline__ void loss_item_fwd(const LossArgs& a, const int4_ ite
   fft::forward<M>(fy, a.ptw, gtid, true);
   fft::forward<M>(ft, a.ptw, gtid, true);
   if (act) {
+    constexpr int nb = M / 2 + 1;
+    float2* sp = a.spec + r.spec_off[q] + int64_t(f) * nb;
+    const int64_t plane = int64_t(F) * nb;
     for (int k = gtid; k <= M / 2; k += T) {
       int km = (M - k) & (M - 1);
       float2 yl, yr, tl, tr;
@@ -89,6 +94,9 @@ __device__ __forceinline__ void loss_item_fwd(const LossArgs& a, const int4_ ite
       split(ft[fft::pad(k)], ft[fft::pad(km)], &tl, &tr);
       float al = sqrtf(yl.x * yl.x + yl.y * yl.y), ar = sqrtf(yr.x * yr.x + yr.y * yr.y);
       float bl = sqrtf(tl.x * tl.x + tl.y * tl.y), br = sqrtf(tr.x * tr.x + tr.y * tr.y);
+      sp[k] = yl;
+      sp[plane + k] = yr;
+      sp[2 * plane + k] = make_float2(bl, br);
       s[0] += (al - bl) * (al - bl);
       s[1] += bl * bl;
       s[2] += fabsf(logf(al + MAG_EPS) - logf(bl + MAG_EPS));
@@ -156,91 +164,65 @@ __global__ void k_loss_total(const float* row_loss, int n_rows, float* loss) {
 
 template <int M>
 __device__ __forceinline__ void loss_item_bwd(const LossArgs& a, const int4_ item, float2* smem) {
-  constexpr int T = M / 16, G = 256 / T;
-  constexpr int NB = (M / 2 + 1 + T - 1) / T;
-  float2* by = smem;
-  float2* bt = smem + G * fft::Padded<M>::size;
+  constexpr int T = M / 16;
+  constexpr int nb = M / 2 + 1;
   const int g = threadIdx.x / T, gtid = threadIdx.x % T;
   const float w_res = 1.f / float(2 * N_RES);
-  {
-    const LossRow r = a.rows[item.x];
-    constexpr int q = M == 512 ? 0 : M == 1024 ? 1 : 2;  // == item.y (dispatch)
-    const int F = r.n_frames[q];
-    const float4 stl = a.stats[2 * (item.x * N_RES + q)], str = a.stats[2 * (item.x * N_RES + q) + 1];
-    {
-      const int f = item.z + g;
-      const bool act = f < F;
-      float2* fy = by + g * fft::Padded<M>::size;
-      float2* ft = bt + g * fft::Padded<M>::size;
-      load_frame<M>(a, r, a.y, f, gtid, fy, act);
-      load_frame<M>(a, r, a.tgt, f, gtid, ft, act);
-      __syncthreads();
-      fft::forward<M>(fy, a.ptw, gtid, true);
-      fft::forward<M>(ft, a.ptw, gtid, true);
-      // dL/dY per bin, as the Hermitian spectra of both channels packed l + i r
-      float2 wk[NB], wm[NB];
+  const LossRow r = a.rows[item.x];
+  constexpr int q = M == 512 ? 0 : M == 1024 ? 1 : 2;  // == item.y (dispatch)
+  const int F = r.n_frames[q];
+  const float4 stl = a.stats[2 * (item.x * N_RES + q)], str = a.stats[2 * (item.x * N_RES + q) + 1];
+  const int f = item.z + g;
+  const bool act = f < F;
+  float2* fy = smem + g * fft::Padded<M>::size;
+  __syncthreads();   // the previous item's readers of the buffers are done
+  if (act) {
+    // dL/dY per bin from the forward's cached spectra, as the Hermitian spectra of
+    // both channels packed l + i r (stored conjugated: the forward FFT then inverts)
+    const float2* sp = a.spec + r.spec_off[q] + int64_t(f) * nb;
+    const int64_t plane = int64_t(F) * nb;
+    for (int k = gtid; k <= M / 2; k += T) {
+      const float2 yv[2] = {sp[k], sp[plane + k]};
+      const float2 bt = sp[2 * plane + k];
+      float2 gh[2];
 #pragma unroll
-      for (int i = 0; i < NB; ++i) {
-        int k = gtid + i * T;
-        wk[i] = wm[i] = make_float2(0.f, 0.f);
-        if (act && k <= M / 2) {
-          int km = (M - k) & (M - 1);
-          float2 yv[2], tv[2];
-          split(fy[fft::pad(k)], fy[fft::pad(km)], &yv[0], &yv[1]);
-          split(ft[fft::pad(k)], ft[fft::pad(km)], &tv[0], &tv[1]);
-          float2 gh[2];
-#pragma unroll
-          for (int ch = 0; ch < 2; ++ch) {
-            const float4 st = ch ? str : stl;
-            float A = sqrtf(yv[ch].x * yv[ch].x + yv[ch].y * yv[ch].y);
-            float B = sqrtf(tv[ch].x * tv[ch].x + tv[ch].y * tv[ch].y);
-            float dA = 0.f;
-            if (st.x > 0.f) dA += (A - B) / (st.x * st.y);
-            float dl = logf(A + MAG_EPS) - logf(B + MAG_EPS);
-            float sg = dl > 0.f ? 1.f : (dl < 0.f ? -1.f : 0.f);
-            dA += sg / ((A + MAG_EPS) * st.z);
-            dA *= w_res;
-            float2 G2 = A > 0.f ? make_float2(dA * yv[ch].x / A, dA * yv[ch].y / A) : make_float2(0.f, 0.f);
-            // Hermitian fill: DC and Nyquist keep their real part, others are halved
-            if (k == 0 || k == M / 2) G2 = make_float2(G2.x, 0.f);
-            else G2 = make_float2(0.5f * G2.x, 0.5f * G2.y);
-            gh[ch] = G2;
-          }
-          // W[k] = Gl[k] + i Gr[k]; W[M-k] = conj(Gl[k]) + i conj(Gr[k]); stored conjugated
-          float2 Wk = make_float2(gh[0].x - gh[1].y, gh[0].y + gh[1].x);
-          float2 Wm = make_float2(gh[0].x + gh[1].y, -gh[0].y + gh[1].x);
-          wk[i] = make_float2(Wk.x, -Wk.y);
-          wm[i] = make_float2(Wm.x, -Wm.y);
-        }
+      for (int ch = 0; ch < 2; ++ch) {
+        const float4 st = ch ? str : stl;
+        float A = sqrtf(yv[ch].x * yv[ch].x + yv[ch].y * yv[ch].y);
+        float B = ch ? bt.y : bt.x;
+        float dA = 0.f;
+        if (st.x > 0.f) dA += (A - B) / (st.x * st.y);
+        float dl = logf(A + MAG_EPS) - logf(B + MAG_EPS);
+        float sg = dl > 0.f ? 1.f : (dl < 0.f ? -1.f : 0.f);
+        dA += sg / ((A + MAG_EPS) * st.z);
+        dA *= w_res;
+        float2 G2 = A > 0.f ? make_float2(dA * yv[ch].x / A, dA * yv[ch].y / A) : make_float2(0.f, 0.f);
+        // Hermitian fill: DC and Nyquist keep their real part, others are halved
+        if (k == 0 || k == M / 2) G2 = make_float2(G2.x, 0.f);
+        else G2 = make_float2(0.5f * G2.x, 0.5f * G2.y);
+        gh[ch] = G2;
       }
-      __syncthreads();
-      if (act) {
-#pragma unroll
-        for (int i = 0; i < NB; ++i) {
-          int k = gtid + i * T;
-          if (k <= M / 2) {
-            fy[fft::pad(k)] = wk[i];
-            if (k > 0 && k < M / 2) fy[fft::pad(M - k)] = wm[i];
-          }
-        }
-      }
-      __syncthreads();
-      fft::forward<M>(fy, a.ptw, gtid, true);
-      if (act) {
-        float* fr = a.frames + r.frame_off[q] + int64_t(f) * 2 * M;
-        for (int n = gtid; n < M; n += T) {
-          float2 z = fy[fft::pad(n)];
-          float w = hann<M>(a.tw, n);
-          fr[n] = w * z.x;          // conj of the result: real part is l
-          fr[M + n] = -w * z.y;     // minus imaginary part is r
-        }
-      }
-      __syncthreads();
+      // W[k] = Gl[k] + i Gr[k]; W[M-k] = conj(Gl[k]) + i conj(Gr[k]); stored conjugated
+      const float2 Wk = make_float2(gh[0].x - gh[1].y, gh[0].y + gh[1].x);
+      const float2 Wm = make_float2(gh[0].x + gh[1].y, -gh[0].y + gh[1].x);
+      fy[fft::pad(k)] = make_float2(Wk.x, -Wk.y);
+      if (k > 0 && k < M / 2) fy[fft::pad(M - k)] = make_float2(Wm.x, -Wm.y);
+    }
+  }
+  __syncthreads();
+  fft::forward<M>(fy, a.ptw, gtid, true);
+  if (act) {
+    float* fr = a.frames + r.frame_off[q] + int64_t(f) * 2 * M;
+    for (int n = gtid; n < M; n += T) {
+      float2 z = fy[fft::pad(n)];
+      float w = hann<M>(a.tw, n);
+      fr[n] = w * z.x;          // conj of the result: real part is l
+      fr[M + n] = -w * z.y;     // minus imaginary part is r
     }
   }
 }
 
-__global__ void __launch_bounds__(256, 2) k_loss_bwd(LossArgs a) {
+__global__ void __launch_bounds__(256, 3) k_loss_bwd(LossArgs a) {
   extern __shared__ float2 smem2[];
   for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
     const int4_ item = a.items[it];
@@ -280,23 +262,24 @@ __global__ void k_loss_ola(const LossRow* rows, const float* frames, float* d_ou
 
 int launch_loss(int what, const LossLaunch& L, cudaStream_t s) {
   static bool init = false;
-  // y and target frames: 2 x (4096/M frames of M padded points) for every M
+  // forward: y and target frames, 2 x (4096/M frames of M padded points) for every M;
+  // backward: one set of frames
   const size_t smem = 2 * size_t(fft::Padded<4096>::size) * sizeof(float2);
+  const size_t smem_b = size_t(fft::Padded<4096>::size) * sizeof(float2);
   if (!init) {
     cudaFuncSetAttribute(k_loss_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    cudaFuncSetAttribute(k_loss_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaFuncSetAttribute(k_loss_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_b));
     init = true;
   }
   if (what < 0 || L.n_items <= 0) return 0;
-  LossArgs a{L.rows, L.items, L.y, L.tgt, L.part, L.stats, L.frames, L.tw, L.ptw, L.n_items};
-  const int g = grid_size(L.n_items, 3);
+  LossArgs a{L.rows, L.items, L.y, L.tgt, L.part, L.stats, L.frames, L.spec, L.tw, L.ptw, L.n_items};
   if (what == 0) {
-    k_loss_fwd<<<g, 256, smem, s>>>(a);
+    k_loss_fwd<<<grid_size(L.n_items, 3), 256, smem, s>>>(a);
     k_loss_rows<<<L.n_rows, 256, 0, s>>>(L.rows, L.part, L.stats, L.row_loss);
     k_loss_total<<<1, 1, 0, s>>>(L.row_loss, L.n_rows, L.loss);
     return 3;
   }
-  k_loss_bwd<<<g, 256, smem, s>>>(a);
+  k_loss_bwd<<<grid_size(L.n_items, 3), 256, smem_b, s>>>(a);
   dim3 grid((L.max_pitch + 255) / 256, L.n_rows);
   k_loss_ola<<<grid, 256, 0, s>>>(L.rows, L.frames, L.d_out);
   return 2;

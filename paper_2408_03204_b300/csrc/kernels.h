@@ -50,6 +50,7 @@ struct LossLaunch {
   float4* part;
   float4* stats;
   float* frames;
+  float2* spec;         // spectrum cache written by the forward, read by the backward
   const float2_* tw;
   const float2_* ptw;
   int n_rows;

@@ -563,7 +563,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
   // ---- loss plan over the output rows
   {
     const int Ms[N_RES] = {512, 1024, 2048};
-    int64_t foff = 0;
+    int64_t foff = 0, soff = 0;
     int32_t groups = 0;
     p->loss.ok = true;
     for (int32_t j = 0; j < int32_t(p->outputs_new.size()); ++j) {
@@ -579,6 +579,8 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
         r.n_frames[q] = F;
         r.frame_off[q] = foff;
         foff += int64_t(F) * 2 * M;
+        r.spec_off[q] = soff;
+        soff += int64_t(F) * 3 * (M / 2 + 1);
         r.group_off[q] = groups;
         const int per = 4096 / M;  // frames transformed together by one 256-thread CTA
         r.n_groups[q] = (F + per - 1) / per;
@@ -588,6 +590,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
       p->loss.rows.push_back(r);
     }
     p->loss.frame_floats = foff;
+    p->loss.spec_float2s = soff;
     p->loss.n_groups_total = groups;
   }
 
@@ -620,7 +623,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     w.tickets = take(4 * size_t(2 * (N + 2)));
     w.flags = take(8 * std::max<size_t>(p->items.size(), 1));
     w.flags_bytes = o - w.status;
-    w.eq_spec = take(4 * size_t(std::max(p->n_eq, 1)) * (p->eq_fft / 2 + 1));
+    w.eq_spec = take(4 * size_t(std::max(p->n_eq, 1)) * (p->eq_fft / 2 + 4));   // 16-byte aligned rows
     w.eq_aux = take(4 * size_t(std::max(p->n_eq, 1)) * 1024);
     w.eq_bandpart = take(4 * size_t(std::max(p->n_eq, 1)) * 16 * 8);
     w.comp_carry = take(4 * size_t(std::max(p->n_comp_chunks, 1)));
@@ -644,6 +647,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     w.loss_stats = take(32 * nrow * N_RES);
     w.loss_rowloss = take(4 * nrow);
     w.loss_frames = take(4 * size_t(std::max<int64_t>(p->loss.frame_floats, 1)));
+    w.loss_spec = take(8 * size_t(std::max<int64_t>(p->loss.spec_float2s, 1)));
     {
       int64_t fl = 0;
       for (int t = 0; t < GRAFX_N_TYPES; ++t) {

@@ -50,7 +50,7 @@ struct WsLayout {
   size_t eq_spec, eq_aux, eq_bandpart, comp_carry, partial, eq_partial;
   size_t dl_aux, dl_spec, dl_R, dl_r;
   size_t rv_band, rv_U, rv_fr, rv_h, rv_H, rv_Y, rv_R, rv_r, rv_mm;
-  size_t loss_part, loss_stats, loss_rowloss, loss_frames;
+  size_t loss_part, loss_stats, loss_rowloss, loss_frames, loss_spec;
   size_t dgrad;                                // per-copy parameter gradients (source batch)
   size_t U, A;
   size_t total;
@@ -62,6 +62,7 @@ struct LossPlan {
   // work items (row, resolution, first frame, statistics group)
   std::vector<int4_> items;
   int64_t frame_floats = 0;  // total floats in the frame buffer
+  int64_t spec_float2s = 0;  // total float2 in the spectrum cache (forward -> backward)
   int32_t n_groups_total = 0;
   bool ok = false;           // every output row is long enough (>= 2048 samples)
 };
