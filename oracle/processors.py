@@ -55,6 +55,20 @@ def imager_fwd(u, p):
     return np.stack([(mid + side) / 2, (mid - side) / 2])
 
 
+def gain_bwd_abs(u, p, ybar):
+    """Sum of the magnitudes of the terms of ``gain_bwd``'s parameter gradient (how far
+    a finite-precision evaluation of that sum can be trusted)."""
+    u, p, ybar = _f64(u), _f64(p), _f64(ybar)
+    return np.exp(p) * np.sum(np.abs(ybar * u), axis=1)
+
+
+def imager_bwd_abs(u, p, ybar):
+    """Sum of the magnitudes of the terms of ``imager_bwd``'s parameter gradient."""
+    u, p, ybar = _f64(u), _f64(p), _f64(ybar)
+    sidebar = (ybar[0] - ybar[1]) / 2
+    return np.array([np.exp(p[0]) * np.sum(np.abs(sidebar * (u[0] - u[1])))])
+
+
 def imager_bwd(u, p, ybar):
     u, p, ybar = _f64(u), _f64(p), _f64(ybar)
     a = np.exp(p[0])

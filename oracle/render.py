@@ -176,9 +176,13 @@ def render_scheduled(types, edges, sources, params, hp=None, method="beam", widt
     return U[sp[-2]:sp[-1]], U, dict(mp, string=string, steps=steps)
 
 
-def backward(types, edges, sources, params, dY, hp=None):
+def backward(types, edges, sources, params, dY, hp=None, cond=False):
     """Reverse-mode pass.  dY[j] is dLoss/dY for the j-th output node (original
-    order).  Returns (dparams {type: [rows, cols]}, dsources [K, 2, L])."""
+    order).  Returns (dparams {type: [rows, cols]}, dsources [K, 2, L]); with
+    ``cond`` also {type: [rows, cols]} holding, for the gain and imager gradients
+    (plain sums over the signal), the sum of the magnitudes of their terms (0 for the
+    other types): a sum that cancels to much less than that is ill-conditioned, and
+    no FP32 evaluation can match it to a relative bound."""
     hp = _hp(hp)
     n = len(types)
     rows = _rows_of(types)
@@ -191,6 +195,7 @@ def backward(types, edges, sources, params, dY, hp=None):
         ybar[v] = ybar[v] + np.asarray(dY[j], dtype=np.float64)
     ubar = [None] * n
     dparams = {t: np.zeros(np.shape(params[t]), dtype=np.float64) for t in params}
+    dcond = {t: np.zeros(np.shape(params[t]), dtype=np.float64) for t in params}
     K = sum(1 for t in types if t == I_)
     dsrc = np.zeros((K, 2, L))
     for v in reversed(_topo(types, edges)):
@@ -206,4 +211,10 @@ def backward(types, edges, sources, params, dY, hp=None):
         ubar[v], pbar = process_bwd(t, u, _param(params, t, rows[v]), ybar[v], hp)
         if pbar.size:
             dparams[t][rows[v]] = pbar
+        if cond and t == G_:
+            dcond[t][rows[v]] = op.gain_bwd_abs(u, _param(params, t, rows[v]), ybar[v])
+        if cond and t == S_:
+            dcond[t][rows[v]] = op.imager_bwd_abs(u, _param(params, t, rows[v]), ybar[v])
+    if cond:
+        return dparams, dsrc, dcond
     return dparams, dsrc

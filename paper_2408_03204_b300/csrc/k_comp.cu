@@ -35,48 +35,66 @@ struct Knee {
   float gy, dgu, dt, dw, dr;
 };
 
+// Per-node constants of the static curves: the divisions by R and W are taken once
+// per chunk instead of per sample.
+struct KneeCoef {
+  float T, W, R, cR, invR, invRR, inv2W, inv4W, inv4WW;
+};
+__device__ __forceinline__ KneeCoef knee_coef(float T, float W, float R) {
+  KneeCoef q;
+  q.T = T;
+  q.W = W;
+  q.R = R;
+  q.invR = 1.f / R;
+  q.cR = q.invR - 1.f;
+  q.invRR = q.invR * q.invR;
+  q.inv2W = 0.5f / W;
+  q.inv4W = 0.25f / W;
+  q.inv4WW = 0.25f / (W * W);
+  return q;
+}
+
 // Eq. 13 (noisegate): G_y = G_u above T + W, G_u + (1-R)(G_u-T-W)^2/(4W) in the knee,
 // T + R (G_u - T) below T - W; with the partial derivatives of G_y.
-__device__ __forceinline__ Knee gate_knee(float gu, float T, float W, float R) {
+__device__ __forceinline__ Knee gate_knee(float gu, const KneeCoef& q) {
   Knee k;
-  if (gu >= T + W) {
+  if (gu >= q.T + q.W) {
     k.gy = gu;
     k.dgu = 1.f;
     k.dt = k.dw = k.dr = 0.f;
-  } else if (gu >= T - W) {
-    const float d = gu - T - W, c = 1.f - R;
-    k.gy = gu + c * d * d / (4.f * W);
-    k.dgu = 1.f + c * d / (2.f * W);
-    k.dt = -c * d / (2.f * W);
-    k.dw = c * (-d / (2.f * W) - d * d / (4.f * W * W));
-    k.dr = -d * d / (4.f * W);
+  } else if (gu >= q.T - q.W) {
+    const float d = gu - q.T - q.W, c = 1.f - q.R;
+    k.gy = gu + c * d * d * q.inv4W;
+    k.dgu = 1.f + c * d * q.inv2W;
+    k.dt = -c * d * q.inv2W;
+    k.dw = c * (-d * q.inv2W - d * d * q.inv4WW);
+    k.dr = -d * d * q.inv4W;
   } else {
-    k.gy = T + R * (gu - T);
-    k.dgu = R;
-    k.dt = 1.f - R;
+    k.gy = q.T + q.R * (gu - q.T);
+    k.dgu = q.R;
+    k.dt = 1.f - q.R;
     k.dw = 0.f;
-    k.dr = gu - T;
+    k.dr = gu - q.T;
   }
   return k;
 }
 
 // Eq. 10-11 and the partial derivatives of G_y.
-__device__ __forceinline__ Knee knee(float gu, float T, float W, float R) {
+__device__ __forceinline__ Knee knee(float gu, const KneeCoef& q) {
   Knee k;
-  const float cR = 1.f / R - 1.f;
-  if (gu >= T + W) {
-    k.gy = T + (gu - T) / R;
-    k.dgu = 1.f / R;
-    k.dt = -cR;
+  if (gu >= q.T + q.W) {
+    k.gy = q.T + (gu - q.T) * q.invR;
+    k.dgu = q.invR;
+    k.dt = -q.cR;
     k.dw = 0.f;
-    k.dr = -(gu - T) / (R * R);
-  } else if (gu >= T - W) {
-    float d = gu - T + W;
-    k.gy = gu + cR * d * d / (4.f * W);
-    k.dgu = 1.f + cR * d / (2.f * W);
-    k.dt = -cR * d / (2.f * W);
-    k.dw = cR * (d / (2.f * W) - d * d / (4.f * W * W));
-    k.dr = -d * d / (4.f * W * R * R);
+    k.dr = -(gu - q.T) * q.invRR;
+  } else if (gu >= q.T - q.W) {
+    const float d = gu - q.T + q.W;
+    k.gy = gu + q.cR * d * d * q.inv4W;
+    k.dgu = 1.f + q.cR * d * q.inv2W;
+    k.dt = -q.cR * d * q.inv2W;
+    k.dw = q.cR * (d * q.inv2W - d * d * q.inv4WW);
+    k.dr = -d * d * q.inv4W * q.invRR;
   } else {
     k.gy = gu;
     k.dgu = 1.f;
@@ -84,6 +102,12 @@ __device__ __forceinline__ Knee knee(float gu, float T, float W, float R) {
   }
   return k;
 }
+
+// ln and exp of the per-sample gain path: the hardware approximations (__logf: absolute
+// error <= 2^-21.4 on [0.5, 2], 3 ulp elsewhere; __expf: a few ulp over the gains'
+// range), inside the outputs' 1e-5 tolerance.
+__device__ __forceinline__ float ln_env(float g) { return __logf(g + COMP_EPS); }
+__device__ __forceinline__ float exp_gain(float x) { return __expf(x); }
 
 __device__ __forceinline__ unsigned long long pack_flag(unsigned st, float v) {
   return (static_cast<unsigned long long>(st) << 32) | __float_as_uint(v);
@@ -313,7 +337,7 @@ __device__ __forceinline__ void envelope(const float* x, float alpha, float cin,
 // Software-pipelined over tickets: once a chunk's inputs are in registers, the next
 // ticket's copies start (cp.async) and run under this chunk's scan, look-back and gain.
 template <int SPT, bool GATE>
-__global__ void __launch_bounds__(256) k_comp_fwd(DevCtx c, int item0, int n_items, int ticket) {
+__global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_fwd(DevCtx c, int item0, int n_items, int ticket) {
   constexpr int CH = 256 * SPT;
   __shared__ __align__(16) float buf[2 * CH];
   __shared__ float sh[32];
@@ -329,7 +353,8 @@ __global__ void __launch_bounds__(256) k_comp_fwd(DevCtx c, int item0, int n_ite
     const int v = w.x, chunk = w.y;
     const NodeDev nd = c.nodes[v];
     const float* p = c.params + nd.prow * 4;
-    const float alpha = p[0], T = p[1], W = p[2], R = p[3];
+    const float alpha = p[0];
+    const KneeCoef kq = knee_coef(p[1], p[2], p[3]);
     const float la = logf(alpha);
     const int t = chunk * CH + threadIdx.x * SPT;
     float ul[SPT], ur[SPT], x[SPT], g[SPT];
@@ -364,9 +389,9 @@ __global__ void __launch_bounds__(256) k_comp_fwd(DevCtx c, int item0, int n_ite
     envelope<SPT>(x, alpha, cin, g);
 #pragma unroll
     for (int i = 0; i < SPT; ++i) {
-      float gu = logf(g[i] + COMP_EPS);
-      Knee k = GATE ? gate_knee(gu, T, W, R) : knee(gu, T, W, R);
-      float gain = expf(k.gy - gu);
+      float gu = ln_env(g[i]);
+      Knee k = GATE ? gate_knee(gu, kq) : knee(gu, kq);
+      float gain = exp_gain(k.gy - gu);
       ul[i] *= gain;
       ur[i] *= gain;
     }
@@ -379,7 +404,7 @@ __global__ void __launch_bounds__(256) k_comp_fwd(DevCtx c, int item0, int n_ite
 }
 
 template <int SPT, bool GATE>
-__global__ void __launch_bounds__(256) k_comp_bwd(DevCtx c, int item0, int n_items, int ticket) {
+__global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_bwd(DevCtx c, int item0, int n_items, int ticket) {
   constexpr int CH = 256 * SPT;
   extern __shared__ __align__(16) float buf[];  // 4 * CH floats: prefetched u and ybar rows
   __shared__ float sh[32];
@@ -397,7 +422,8 @@ __global__ void __launch_bounds__(256) k_comp_bwd(DevCtx c, int item0, int n_ite
     const int v = w.x, chunk = w.y;
     const NodeDev nd = c.nodes[v];
     const float* p = c.params + nd.prow * 4;
-    const float alpha = p[0], T = p[1], W = p[2], R = p[3];
+    const float alpha = p[0];
+    const KneeCoef kq = knee_coef(p[1], p[2], p[3]);
     const float la = logf(alpha);
     const int t = chunk * CH + threadIdx.x * SPT;
     const int n_chunks = (nd.len + CH - 1) / CH;
@@ -422,12 +448,12 @@ __global__ void __launch_bounds__(256) k_comp_bwd(DevCtx c, int item0, int n_ite
     float gain[SPT], gyb[SPT], dT = 0.f, dW = 0.f, dR = 0.f;
 #pragma unroll
     for (int i = 0; i < SPT; ++i) {
-      float gu = logf(g[i] + COMP_EPS);
-      Knee k = GATE ? gate_knee(gu, T, W, R) : knee(gu, T, W, R);
-      gain[i] = expf(k.gy - gu);
+      float gu = ln_env(g[i]);
+      Knee k = GATE ? gate_knee(gu, kq) : knee(gu, kq);
+      gain[i] = exp_gain(k.gy - gu);
       float kbar = bl[i] * ul[i] + br[i] * ur[i];
       gyb[i] = kbar * gain[i];
-      a[i] = gyb[i] * (k.dgu - 1.f) / (g[i] + COMP_EPS);
+      a[i] = __fdividef(gyb[i] * (k.dgu - 1.f), g[i] + COMP_EPS);
       dT += gyb[i] * k.dt;
       dW += gyb[i] * k.dw;
       dR += gyb[i] * k.dr;
@@ -559,7 +585,8 @@ __global__ void __launch_bounds__(256) k_comp_fwd_row(DevCtx c, const float* __r
   __shared__ float sh[32];
   __shared__ int s_it;
   __shared__ float s_carry;
-  const float alpha = p[0], T = p[1], W = p[2], R = p[3];
+  const float alpha = p[0];
+  const KneeCoef kq = knee_coef(p[1], p[2], p[3]);
   const float la = logf(alpha);
   while (true) {
     if (threadIdx.x == 0) s_it = atomicAdd(c.tickets, 1);
@@ -601,9 +628,9 @@ __global__ void __launch_bounds__(256) k_comp_fwd_row(DevCtx c, const float* __r
     envelope<SPT>(x, alpha, cin, g);
 #pragma unroll
     for (int i = 0; i < SPT; ++i) {
-      float gu = logf(g[i] + COMP_EPS);
-      Knee k = knee(gu, T, W, R);
-      float gain = expf(k.gy - gu);
+      float gu = ln_env(g[i]);
+      Knee k = knee(gu, kq);
+      float gain = exp_gain(k.gy - gu);
       ul[i] *= gain;
       ur[i] *= gain;
     }

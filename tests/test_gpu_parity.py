@@ -112,9 +112,9 @@ def test_random_graphs_fwd_bwd():
         W = np.zeros((2, 2, Pd), np.float32)
         W[:, :, :L] = rng.standard_normal((2, 2, L)).astype(np.float32)
         dP, dS = run.backprop(W.reshape(-1))
-        wP, wS = orr.backward(g.types, g.edges, src_per[0][:, :, :L], P, W[:, :, :L], dict(eq_taps=63))
+        wP, wS, wC = orr.backward(g.types, g.edges, src_per[0][:, :, :L], P, W[:, :, :L], dict(eq_taps=63), cond=True)
         for t in P:
-            assert_grad_close(dP[t], wP[t], what=f"type {t}")
+            assert_grad_close(dP[t], wP[t], what=f"type {t}", cond=wC[t])
         assert_grad_close(dS.reshape(-1, 2, Pd)[:, :, :L], wS, what="sources")
 
 
@@ -270,9 +270,9 @@ def test_random_graphs_with_delay():
         W = np.zeros((1, 2, Pd), np.float32)
         W[:, :, :L] = rng.standard_normal((1, 2, L)).astype(np.float32)
         dP, dS = run.backprop(W.reshape(-1))
-        wP, wS = orr.backward(g.types, g.edges, src_per[0][:, :, :L], P, W[:, :, :L], dict(eq_taps=63))
+        wP, wS, wC = orr.backward(g.types, g.edges, src_per[0][:, :, :L], P, W[:, :, :L], dict(eq_taps=63), cond=True)
         for t in P:
-            assert_grad_close(dP[t], wP[t], what=f"type {t}")
+            assert_grad_close(dP[t], wP[t], what=f"type {t}", cond=wC[t])
         assert_grad_close(dS.reshape(-1, 2, Pd)[:, :, :L], wS, what="sources")
 
 

@@ -43,6 +43,26 @@ def test_gain_closed_form_on_gain_only_graph(rng):
     np.testing.assert_allclose(orr.outputs_of(g.types, Y)[0], want, rtol=1e-14, atol=1e-14)
 
 
+def test_gradient_term_magnitudes(rng):
+    """The magnitude sums bound the gradients (triangle inequality) and equal them when
+    every term has the same sign (ybar = u makes the gain's terms u^2 >= 0)."""
+    u = sig(rng, 500)
+    p = np.array([0.3, -0.2])
+    ub, pb = op.gain_bwd(u, p, u)
+    np.testing.assert_allclose(op.gain_bwd_abs(u, p, u), pb, rtol=1e-13)
+    w = sig(rng, 500)
+    _, pb = op.gain_bwd(u, p, w)
+    assert np.all(op.gain_bwd_abs(u, p, w) >= np.abs(pb))
+    q = np.array([0.4])
+    _, pb = op.imager_bwd(u, q, w)
+    assert op.imager_bwd_abs(u, q, w)[0] >= abs(pb[0])
+    # ybar with sidebar = (l - r): all imager terms are squares
+    d = u[0] - u[1]
+    yb = np.stack([d, -d])
+    _, pb = op.imager_bwd(u, q, yb)
+    np.testing.assert_allclose(op.imager_bwd_abs(u, q, yb), pb, rtol=1e-13)
+
+
 def test_imager_identity_and_mono(rng):
     u = sig(rng, 128)
     np.testing.assert_allclose(op.imager_fwd(u, [0.0]), u, atol=1e-15)
