@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--samples", type=int, default=L_FULL, help="signal length (smaller only for profiling captures)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the plan's default tiles (keeps the launch list short for profiling captures)")
     return ap.parse_args()
 
 
@@ -256,7 +258,13 @@ def main():
 
     g = workload()
     L = args.samples
-    plan = gx.Plan([gx.Graph.from_lists(g.types, g.edges)], [L], eq_taps=EQ_TAPS)
+    graphs = [gx.Graph.from_lists(g.types, g.edges)]
+    tiles = {}
+    if not args.no_autotune:
+        # tile sizes timed on this GPU for this graph (outside the timed region)
+        from paper_2408_03204_b300 import autotune as gat
+        tiles = gat.autotune(graphs, [L], eq_taps=EQ_TAPS, cache=None, device=str(dev))
+    plan = gx.Plan(graphs, [L], eq_taps=EQ_TAPS, **tiles)
     plan.bind_workspace(dev)
     info = plan.info
     exp = plan.export()
@@ -459,7 +467,9 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(cfg, nodes=int(info.n_nodes), processed_node_samples=node_samples,
-                               schedule_steps=N, parallelism=f"replicas{world}"),
+                               schedule_steps=N, parallelism=f"replicas{world}",
+                               tiles={"eq_fft": int(info.eq_fft), "comp_chunk": int(info.comp_chunk),
+                                      "chosen_by": "defaults" if args.no_autotune else "autotune"}),
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": graph.launches() * args.steps,
                 "timed": "captured CUDA graph of the whole step (grafx_step_graph), "
