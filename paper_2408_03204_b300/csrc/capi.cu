@@ -227,7 +227,42 @@ int grafx_plan_create(const grafx_graph* const* graphs, int32_t n_graphs, const 
   GX_CATCH
 }
 
+static void release_side(Plan* p) {
+  for (void* e : p->events) cudaEventDestroy(static_cast<cudaEvent_t>(e));
+  p->events.clear();
+  if (p->side) cudaStreamDestroy(static_cast<cudaStream_t>(p->side));
+  p->side = nullptr;
+}
+
+// The side stream and its events, created once per plan (no device memory).
+static int ensure_side(Plan* p) {
+  if (p->side) return GRAFX_OK;
+  cudaStream_t st;
+  int rc = cuda_check(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "side stream");
+  if (rc) return rc;
+  p->side = st;
+  const int N = int(p->sched.string.size()) - 1;
+  for (int i = 0; i < 2 * (N + 1) + 2; ++i) {
+    cudaEvent_t e;
+    rc = cuda_check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "side events");
+    if (rc) {
+      release_side(p);
+      return rc;
+    }
+    p->events.push_back(e);
+  }
+  return GRAFX_OK;
+}
+
+static cudaEvent_t ev_fork(const Plan* p) { return static_cast<cudaEvent_t>(p->events[0]); }
+static cudaEvent_t ev_join(const Plan* p) { return static_cast<cudaEvent_t>(p->events[1]); }
+static cudaEvent_t ev_fwd(const Plan* p, int k) { return static_cast<cudaEvent_t>(p->events[2 + k]); }
+static cudaEvent_t ev_bwd(const Plan* p, int k) {
+  return static_cast<cudaEvent_t>(p->events[2 + (p->sched.string.size()) + k]);
+}
+
 int grafx_plan_destroy(grafx_plan* p) {
+  if (p) release_side(p);
   delete p;
   return GRAFX_OK;
 }
@@ -304,6 +339,8 @@ int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* s
   if (rc) return rc;
   rc = cuda_check(cudaStreamSynchronize(s), "upload tables");
   if (rc) return rc;
+  rc = ensure_side(p);
+  if (rc) return rc;
   p->dev_ws = static_cast<char*>(dev_ws);
   return GRAFX_OK;
   GX_CATCH
@@ -340,18 +377,42 @@ struct StepRange {
   ~StepRange() { nvtxRangePop(); }
 };
 
+// Forward steps whose processors have a parameter-only design (EQ filter spectra,
+// delay taps, reverb impulse responses): the design depends on no signal, so it runs on
+// the side stream from the start of the range and the step waits for it.
+static bool has_design(int type) {
+  return type == GRAFX_T_EQ || type == GRAFX_T_DELAY || type == GRAFX_T_REVERB;
+}
+
 static int render_range(grafx_plan* p, const float* sources, float* out, int32_t first, int32_t last,
                         cudaStream_t s) {
   DevCtx c = make_ctx(p, sources, out, nullptr, nullptr);
   int launches = 0;
+  cudaStream_t side = static_cast<cudaStream_t>(p->side);
+  bool forked = false;
+  for (int k = first; k < last; ++k) {
+    const StepInfo& st = p->steps[k];
+    if (!has_design(st.type)) continue;
+    if (!forked) {
+      cudaEventRecord(ev_fork(p), s);
+      cudaStreamWaitEvent(side, ev_fork(p), 0);
+      forked = true;
+    }
+    c.params = p->params[st.type];
+    c.pcols = param_cols(p, st.type);
+    if (st.type == GRAFX_T_EQ) launches += launch_eq(0, c, st.node_begin, st.node_end, side);
+    if (st.type == GRAFX_T_DELAY) launches += launch_delay(0, c, st.node_begin, st.node_end, side);
+    if (st.type == GRAFX_T_REVERB) launches += launch_reverb(0, c, st.node_begin, st.node_end, side);
+    cudaEventRecord(ev_fwd(p, k), side);
+  }
   for (int k = first; k < last; ++k) {
     const StepInfo& st = p->steps[k];
     StepRange range("fwd", k, st.type);
     c.params = p->params[st.type];
     c.pcols = param_cols(p, st.type);
+    if (has_design(st.type)) cudaStreamWaitEvent(s, ev_fwd(p, k), 0);
     switch (st.type) {
       case GRAFX_T_EQ:
-        launches += launch_eq(0, c, st.node_begin, st.node_end, s);
         launches += launch_eq(1, c, st.fitem_begin, st.fitem_count, s);
         break;
       case GRAFX_T_COMP:
@@ -360,12 +421,10 @@ static int render_range(grafx_plan* p, const float* sources, float* out, int32_t
         launches += launch_comp(0, c, st.fitem_begin, st.fitem_count, 2 * k, st.type == GRAFX_T_GATE, s);
         break;
       case GRAFX_T_DELAY:
-        launches += launch_delay(0, c, st.node_begin, st.node_end, s);
         launches += launch_delay(1, c, st.fitem_begin, st.fitem_count, s);
         break;
       case GRAFX_T_REVERB:
         launches += launch_delay(3, c, st.fitem_begin, st.fitem_count, s);   // u window spectra
-        launches += launch_reverb(0, c, st.node_begin, st.node_end, s);
         launches += launch_reverb(1, c, st.node_begin, st.node_end, s);
         break;
       default:
@@ -453,6 +512,18 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
                           float* d_sources, int32_t first, int32_t last, cudaStream_t s) {
   DevCtx c = make_ctx(p, sources, nullptr, d_out, d_sources);
   int launches = 0;
+  // Parameter-gradient finalizers that read only their step's private partial slots and
+  // spectra (EQ, compressor/noisegate, gain/imager, reverb) run on the side stream after
+  // their step's kernels, off the critical path of the input adjoints; the range joins
+  // the side stream at its end.  (The delay's gradient kernels read signal rows, whose
+  // adjoint storage is recycled by later steps, and stay on the main stream.)
+  cudaStream_t side = static_cast<cudaStream_t>(p->side);
+  bool used_side = false;
+  auto to_side = [&](int k) {
+    cudaEventRecord(ev_bwd(p, k), s);
+    cudaStreamWaitEvent(side, ev_bwd(p, k), 0);
+    used_side = true;
+  };
   for (int k = last - 1; k >= std::max(first, 1); --k) {
     const StepInfo& st = p->steps[k];
     if (st.type == GRAFX_T_OUT) continue;  // adjoint rows of outputs are d_out itself
@@ -464,18 +535,27 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
     switch (st.type) {
       case GRAFX_T_EQ:
         launches += launch_eq(2, c, st.bitem_begin, st.bitem_count, s);
-        if (c.dparams) launches += launch_eq(3, c, st.node_begin, st.node_end, s);
+        if (c.dparams) {
+          to_side(k);
+          launches += launch_eq(3, c, st.node_begin, st.node_end, side);
+        }
         break;
       case GRAFX_T_COMP:
       case GRAFX_T_GATE:
         clear_step_flags(p, st.bitem_begin, st.bitem_count, 2 * k + 1, s);
         launches += launch_comp(1, c, st.bitem_begin, st.bitem_count, 2 * k + 1, st.type == GRAFX_T_GATE, s);
-        if (c.dparams) launches += launch_comp(2, c, st.node_begin, st.node_end, 0, false, s);
+        if (c.dparams) {
+          to_side(k);
+          launches += launch_comp(2, c, st.node_begin, st.node_end, 0, false, side);
+        }
         break;
       case GRAFX_T_REVERB:
         launches += launch_delay(3, c, st.dsub_begin[0], st.dsub_count[0], s);   // ybar spectra
         launches += launch_reverb(2, c, st.node_begin, st.node_end, s);
-        if (c.dparams) launches += launch_reverb(3, c, st.node_begin, st.node_end, s);
+        if (c.dparams) {
+          to_side(k);
+          launches += launch_reverb(3, c, st.node_begin, st.node_end, side);
+        }
         break;
       case GRAFX_T_DELAY:
         launches += launch_delay(2, c, st.dsub_begin[0], st.dsub_count[0], s);
@@ -486,13 +566,20 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
       case GRAFX_T_GAIN:
       case GRAFX_T_IMAGER:
         launches += launch_ew_bwd(st.type, c, st.bitem_begin, st.bitem_count, s);
-        if (c.dparams) launches += launch_ew_finalize(c, st.node_begin, st.node_end, param_cols(p, st.type), s);
+        if (c.dparams) {
+          to_side(k);
+          launches += launch_ew_finalize(c, st.node_begin, st.node_end, param_cols(p, st.type), side);
+        }
         break;
       default:
         launches += launch_ew_bwd(GRAFX_T_MIX, c, st.bitem_begin, st.bitem_count, s);
     }
   }
   if (first == 0 && d_sources) launches += launch_ew_bwd(GRAFX_T_MIX, c, p->in_bitem_begin, p->in_bitem_count, s);
+  if (used_side) {   // join: the gradients are complete when the main stream moves on
+    cudaEventRecord(ev_join(p), side);
+    cudaStreamWaitEvent(s, ev_join(p), 0);
+  }
   return launches;
 }
 

@@ -117,6 +117,10 @@ struct Plan {
   const float* rv_noise = nullptr;
   int64_t param_rows[GRAFX_N_TYPES] = {0};
   int32_t last_launches = 0;
+  // side stream (cudaStream_t) and events (cudaEvent_t) for work off the critical path:
+  // parameter-only designs in the forward, parameter-gradient finalizers in the backward
+  void* side = nullptr;
+  std::vector<void*> events;             // [0] fork, [1] join, [2 + k] forward step k, [2 + N + 1 + k] backward step k
 };
 
 int build_plan(const std::vector<const grafx_graph*>& graphs, const int64_t* lengths,
