@@ -89,6 +89,7 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
   c.dl_nd = p->dl_nd;
   c.dl_slot = p->dl_slot;
   c.dl_P = p->dl_P;
+  c.dl_nbmax = p->dl_nbmax;
   c.rv_paper = p->rv_paper;
   c.rv_n = p->rv_n;
   c.rv_hop = p->rv_hop;

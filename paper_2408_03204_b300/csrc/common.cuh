@@ -62,6 +62,7 @@ struct DevCtx {
   // processor layouts
   int32_t eq_logmag;                        // P[eq] rows hold the (eq_taps+1)/2 log-magnitudes
   int32_t dl_taps, dl_nd, dl_slot, dl_P;    // delay taps per channel, surrogate length, slot width, lag partitions
+  int32_t dl_nbmax;                         // most B-sample blocks of any delay node's signal
   int32_t rv_paper, rv_n, rv_hop, rv_f;     // reverb: paper layout, STFT size, hop, frames
 };
 

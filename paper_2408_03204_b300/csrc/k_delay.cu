@@ -22,6 +22,7 @@
 // of u and of B-sample blocks of ybar (B = 4096, both channels packed as l + i r),
 // R_p = sum_b X_{b-p} conj(Ybar_b) per lag partition p (P partitions of B lags from
 // -B), one inverse FFT per partition.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -30,9 +31,28 @@
 
 namespace grafx {
 
+// The row feeding node v (forward) or the adjoint row of its only consumer (adjoint)
+// when there is exactly one, else nullptr (the window is then summed over the edges).
+template <bool ADJ>
+__device__ __forceinline__ const float* dl_single_row(const DevCtx& c, int v) {
+  const int e0 = ADJ ? c.tcsr_ptr[v] : c.csr_ptr[v];
+  const int e1 = ADJ ? c.tcsr_ptr[v + 1] : c.csr_ptr[v + 1];
+  if (e1 - e0 != 1) return nullptr;
+  return ADJ ? arow(c, c.nodes[c.tcsr_dst[e0]]) : yrow(c, c.nodes[c.csr_src[e0]]);
+}
+
 // shared-memory window of one tap for a 1024-sample tile of one channel
 template <bool ADJ>
-__device__ __forceinline__ void dl_window(const DevCtx& c, int v, const NodeDev& nd, int ch, int start, float* win) {
+__device__ __forceinline__ void dl_window(const DevCtx& c, int v, const NodeDev& nd, int ch, int start, float* win,
+                                          const float* single) {
+  if (single) {
+    const float* row = single + size_t(ch) * nd.pitch;
+    for (int i = threadIdx.x; i < DL_TILE + DL_FIR - 1; i += blockDim.x) {
+      const int t = start + i;
+      win[i] = (t >= 0 && t < nd.len) ? row[t] : 0.f;
+    }
+    return;
+  }
   const int e0 = ADJ ? c.tcsr_ptr[v] : c.csr_ptr[v];
   const int e1 = ADJ ? c.tcsr_ptr[v + 1] : c.csr_ptr[v + 1];
   for (int i = threadIdx.x; i < DL_TILE + DL_FIR - 1; i += blockDim.x) {
@@ -63,6 +83,7 @@ __global__ void __launch_bounds__(256) k_delay_fir(DevCtx c, int item0, int n_it
     const int v = w.x, t0 = w.y, ch = w.z;
     const NodeDev nd = c.nodes[v];
     const float* aux = c.dl_aux + size_t(c.ext[v].z) * 2 * ntap * (DL_FIR + 1) + size_t(ch) * ntap * (DL_FIR + 1);
+    const float* single = dl_single_row<ADJ>(c, v);
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     const int i0 = 4 * threadIdx.x;
     for (int g0 = 0; g0 < ntap; g0 += DL_GROUP) {
@@ -74,7 +95,7 @@ __global__ void __launch_bounds__(256) k_delay_fir(DevCtx c, int item0, int n_it
       __syncthreads();
       for (int m = 0; m < ng; ++m) {
         // forward: win[k] = u[t0 - d - H + k]; adjoint: win[k] = ybar[t0 + d - H + k]
-        dl_window<ADJ>(c, v, nd, ch, ADJ ? t0 + dly[m] - H : t0 - dly[m] - H, win[m]);
+        dl_window<ADJ>(c, v, nd, ch, ADJ ? t0 + dly[m] - H : t0 - dly[m] - H, win[m], single);
       }
       __syncthreads();
       for (int m = 0; m < ng; ++m) {
@@ -98,22 +119,40 @@ __global__ void __launch_bounds__(256) k_delay_fir(DevCtx c, int item0, int n_it
   }
 }
 
-// Per delay node: the taps c_{x,m} (Eq. 4 with N = 39, K = 20) and the delays
+// cos(2 pi j / 39) and the 39-tap design's Hann v[j - H] = 0.5 (1 + cos(2 pi (j - H) / 40)).
+__device__ __forceinline__ void dl_tables(float* cos39, float* hann39) {
+  constexpr int H = (DL_FIR - 1) / 2;
+  if (threadIdx.x < DL_FIR) {
+    cos39[threadIdx.x] = cospif(2.f * float(threadIdx.x) / float(DL_FIR));
+    hann39[threadIdx.x] = 0.5f * (1.f + cospif(2.f * float(int(threadIdx.x) - H) / float(DL_FIR + 1)));
+  }
+}
+
+// Per delay node: the taps c_{x,m} (Eq. 4 with N = 39, K = 20; FP32 with exp and cosine
+// tables, the cosine indexed exactly by (k |n|) mod 39) and the delays
 // d_{x,m} = m S + (round(N_d (-arg z) / 2 pi) mod N_d).
 __global__ void k_delay_design(DevCtx c, int node_begin) {
+  __shared__ float A[2 * DL_SLOT_TAPS][DL_K];
+  __shared__ float cos39[DL_FIR], hann39[DL_FIR];
   const int v = node_begin + blockIdx.x;
   const NodeDev nd = c.nodes[v];
   const int ntap = c.dl_taps, Nd = c.dl_nd;
   float* aux = c.dl_aux + size_t(c.ext[v].z) * 2 * ntap * (DL_FIR + 1);
   const float* p = c.params + size_t(nd.prow) * c.pcols;
   constexpr int H = (DL_FIR - 1) / 2, K = DL_K;
+  for (int i = threadIdx.x; i < 2 * ntap * K; i += blockDim.x) A[i / K][i % K] = expf(p[(i / K) * DL_ROW + 2 + i % K]);
+  dl_tables(cos39, hann39);
+  __syncthreads();
   for (int i = threadIdx.x; i < 2 * ntap * DL_FIR; i += blockDim.x) {
-    const int xm = i / DL_FIR, n = i % DL_FIR - H;
-    const float* q = p + xm * DL_ROW;
-    double s = exp(double(q[2]));
-    for (int k = 1; k < K; ++k) s += 2.0 * exp(double(q[2 + k])) * cospi(2.0 * k * n / DL_FIR);
-    const double hann = 0.5 * (1.0 + cospi(2.0 * n / (DL_FIR + 1)));
-    aux[xm * (DL_FIR + 1) + n + H] = float(hann * s / DL_FIR);
+    const int xm = i / DL_FIR, j = i % DL_FIR, an = j < H ? H - j : j - H;
+    float s = 0.f;
+    int idx = 0;   // (k |n|) mod 39
+    for (int k = 1; k < K; ++k) {
+      idx += an;
+      if (idx >= DL_FIR) idx -= DL_FIR;
+      s += A[xm][k] * cos39[idx];
+    }
+    aux[xm * (DL_FIR + 1) + j] = hann39[j] * (A[xm][0] + 2.f * s) / float(DL_FIR);
   }
   for (int xm = threadIdx.x; xm < 2 * ntap; xm += blockDim.x) {
     const float* q = p + xm * DL_ROW;
@@ -238,11 +277,19 @@ __device__ __forceinline__ cplx cdv(cplx a, cplx b) {
 }
 
 // Gradients of one (node, channel, tap): FIR log-magnitudes and the surrogate z.
+// The phase of q = z w^n is taken relative to the tap's integer delay bin d0 (the n with
+// q closest to 1): arg q / pi = delta + 2 m / N_d with m = (n - d0) mod N_d in
+// (-N_d/2, N_d/2] exact in integers and delta = arg z / pi + 2 d0 / N_d (|delta| <= 1/N_d)
+// formed once in double, so the lag next to the pole (m = 0, the Taylor branch) keeps
+// its full precision in FP32.  Each thread runs over RUN consecutive lags with a
+// register window of r for the 39-tap correlation g.
 __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_items) {
   __shared__ float cs[DL_FIR];
+  __shared__ float cos39[DL_FIR], hann39[DL_FIR];
   __shared__ float red[2 * 32];
-  constexpr int H = (DL_FIR - 1) / 2, K = DL_K;
+  constexpr int H = (DL_FIR - 1) / 2, K = DL_K, RUN = 8;
   const int ntap = c.dl_taps, Nd = c.dl_nd, nlag = c.dl_P * DL_B;
+  dl_tables(cos39, hann39);
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
     const int v = w.x, x = w.y / ntap, m = w.y % ntap;
@@ -260,12 +307,12 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
     // FIR taps: dL/dc[j] = r[d + j]; chain through the window, cosine sum and exp
     if (threadIdx.x < K) {
       const int k = threadIdx.x;
-      double acc = 0.0;
-      for (int n = -H; n <= H; ++n) {
-        const double hann = 0.5 * (1.0 + cospi(2.0 * n / (DL_FIR + 1)));
-        acc += hann * double(r[d + n]) * cospi(2.0 * k * n / DL_FIR);
+      float acc = 0.f;
+      for (int j = 0; j < DL_FIR; ++j) {
+        const int an = j < H ? H - j : j - H;
+        acc += hann39[j] * r[d + j - H] * cos39[(k * an) % DL_FIR];
       }
-      out[2 + k] = float(exp(double(q[2 + k])) * acc * (k == 0 ? 1.0 : 2.0) / DL_FIR);
+      out[2 + k] = expf(q[2 + k]) * acc * (k == 0 ? 1.f : 2.f) / float(DL_FIR);
     }
     // surrogate z: Q = sum_n g[n] phi[n]
     const double zr = q[0], zi = q[1];
@@ -279,43 +326,61 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
     const cplx zN = {float(rN * (1.0 + c1)), float(rN * s1)};
     const cplx bz = {float(rN * c1 + (rN - 1.0)), float(rN * s1)};   // z^N - 1
     const cplx zinv = {float(zr / (rho * rho) / Nd), float(-zi / (rho * rho) / Nd)};
-    const double thn = th / M_PI;                       // phase in units of pi
+    const long long d0r = llrint(double(Nd) * (-th) / (2.0 * M_PI));   // |arg z / pi + 2 d0r / N_d| <= 1/N_d
+    const float dlt = float(th / M_PI + 2.0 * double(d0r) / Nd);
+    long long d0l = d0r % Nd;
+    if (d0l < 0) d0l += Nd;
+    const int d0 = int(d0l);
+    const float two_n = 2.f / float(Nd), tx = float(Nd * lr), npi = float(Nd * M_PI);
+    const float rf = float(rho), one_m_rho = float(1.0 - rho);
     float qx = 0.f, qy = 0.f;
-    for (int n = threadIdx.x; n < Nd; n += blockDim.x) {
-      float g = 0.f;
+    for (int n0 = threadIdx.x * RUN; n0 < Nd; n0 += blockDim.x * RUN) {
+      float win[RUN + DL_FIR - 1];
 #pragma unroll
-      for (int jj = 0; jj < DL_FIR; ++jj) g += cs[jj] * rs[n + jj - H];
-      double ph = thn + 2.0 * n / Nd;                   // arg q / pi, reduced to (-1, 1]
-      ph -= 2.0 * floor(0.5 * ph + 0.5);
-      const float phf = float(ph);
-      cplx F;
-      const float tx = float(Nd * lr), ty = float(Nd * M_PI) * phf;   // t = N ln q
-      if (tx * tx + ty * ty < 0.25f) {
-        // F = N^2 sum_j e_j t^j with e_j = (sum_k k^(j+1)) / (N^(j+2) j!)
-        cplx t = {tx, ty}, tp = {1.f, 0.f};
-        F = {0.f, 0.f};
-#pragma unroll
-        for (int j = 0; j < 9; ++j) {
-          F.x += c.dl_taylor[j] * tp.x;
-          F.y += c.dl_taylor[j] * tp.y;
-          tp = cm(tp, t);
-        }
-        F.x *= float(Nd) * float(Nd);
-        F.y *= float(Nd) * float(Nd);
-      } else {
-        float sh, chh;
-        sincospif(0.5f * phf, &sh, &chh);
-        const float rf = float(rho);
-        // a = 1 - q = (1 - rho) + 2 rho sin^2(ph/2) - i rho sin(ph)
-        const cplx a = {float(1.0 - rho) + 2.f * rf * sh * sh, -rf * 2.f * sh * chh};
-        const cplx t1 = {1.f + float(Nd - 1) * zN.x, float(Nd - 1) * zN.y};
-        const cplx am = cm(a, t1);
-        const cplx num = {-am.x - bz.x, -am.y - bz.y};
-        F = cdv(num, cm(a, a));
+      for (int i = 0; i < RUN + DL_FIR - 1; ++i) {
+        const int n = n0 + i - H;   // needed for n < N_d + H only (the lag range of the tap)
+        win[i] = n < Nd + H ? rs[n] : 0.f;
       }
-      const cplx ph2 = cm(F, zinv);
-      qx += g * ph2.x;
-      qy += g * ph2.y;
+#pragma unroll
+      for (int u = 0; u < RUN; ++u) {
+        const int n = n0 + u;
+        if (n < Nd) {
+          float g = 0.f;
+#pragma unroll
+          for (int jj = 0; jj < DL_FIR; ++jj) g += cs[jj] * win[u + jj];
+          int mm = n - d0;
+          if (mm < 0) mm += Nd;
+          if (2 * mm > Nd) mm -= Nd;
+          const float phf = dlt + float(mm) * two_n;   // arg q / pi
+          const float ty = npi * phf;                   // t = N ln q = tx + i ty
+          cplx F;
+          if (tx * tx + ty * ty < 0.25f) {
+            // F = N^2 sum_j e_j t^j with e_j = (sum_k k^(j+1)) / (N^(j+2) j!)
+            cplx t = {tx, ty}, tp = {1.f, 0.f};
+            F = {0.f, 0.f};
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+              F.x += c.dl_taylor[j] * tp.x;
+              F.y += c.dl_taylor[j] * tp.y;
+              tp = cm(tp, t);
+            }
+            F.x *= float(Nd) * float(Nd);
+            F.y *= float(Nd) * float(Nd);
+          } else {
+            float sh, chh;
+            sincospif(0.5f * phf, &sh, &chh);
+            // a = 1 - q = (1 - rho) + 2 rho sin^2(ph/2) - i rho sin(ph)
+            const cplx a = {one_m_rho + 2.f * rf * sh * sh, -rf * 2.f * sh * chh};
+            const cplx t1 = {1.f + float(Nd - 1) * zN.x, float(Nd - 1) * zN.y};
+            const cplx am = cm(a, t1);
+            const cplx num = {-am.x - bz.x, -am.y - bz.y};
+            F = cdv(num, cm(a, a));
+          }
+          const cplx ph2 = cm(F, zinv);
+          qx += g * ph2.x;
+          qy += g * ph2.y;
+        }
+      }
     }
     float vq[2] = {qx, qy};
     block_sum<2>(vq, red);
@@ -329,7 +394,10 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
 int launch_delay(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
   static bool init = false;
   const size_t sm_fft = sizeof(float2) * fft::Padded<DL_M>::size;
-  const size_t sm_acc = sizeof(float2) * 2 * DL_CHUNK * size_t(2 * DL_MAX_BLOCKS + c.dl_P);
+  // the accumulation stages nb + P u windows and nb ybar blocks of DL_CHUNK bins: sized by
+  // the plan's longest delay signal, so that short signals keep several CTAs per SM
+  const size_t sm_acc = sizeof(float2) * 2 * DL_CHUNK * size_t(2 * std::max(c.dl_nbmax, 1) + c.dl_P);
+  const int acc_per_sm = std::max(1, std::min(4, int((228 * 1024) / (sm_acc + 1024))));
   if (!init) {
     const size_t sm_acc_max = sizeof(float2) * 2 * DL_CHUNK * size_t(2 * DL_MAX_BLOCKS + DL_PMAX);
     cudaFuncSetAttribute(k_delay_spec, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_fft));
@@ -346,7 +414,7 @@ int launch_delay(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
     case 1: if (b > 0) k_delay_fir<false><<<grid_size(b, 4), 256, 0, s>>>(c, a, b); return b > 0;
     case 2: if (b > 0) k_delay_fir<true><<<grid_size(b, 4), 256, 0, s>>>(c, a, b); return b > 0;
     case 3: if (b > 0) k_delay_spec<<<grid_size(b, 3), DL_M / 16, sm_fft, s>>>(c, a, b); return b > 0;
-    case 4: if (b > 0) k_delay_acc<<<grid_size(b, 1), DL_CHUNK * c.dl_P, sm_acc, s>>>(c, a, b); return b > 0;
+    case 4: if (b > 0) k_delay_acc<<<grid_size(b, acc_per_sm), DL_CHUNK * c.dl_P, sm_acc, s>>>(c, a, b); return b > 0;
     case 5: if (b > 0) k_delay_lags<<<grid_size(b, 3), DL_M / 16, sm_fft, s>>>(c, a, b); return b > 0;
     case 6: if (b > 0) k_delay_grad<<<grid_size(b, 4), 256, 0, s>>>(c, a, b); return b > 0;
   }

@@ -390,6 +390,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
           const int32_t nb = (L + DL_B - 1) / DL_B;
           p->node_ext[v].z = p->n_delay++;
           p->node_ext[v].w = nb;
+          p->dl_nbmax = std::max(p->dl_nbmax, nb);
           for (int32_t ch = 0; ch < 2; ++ch)
             for (int32_t t0 = 0; t0 < L; t0 += DL_TILE) fwd.push_back({v, t0, ch, 0});
           break;

@@ -86,7 +86,7 @@ struct Plan {
   int32_t n_type_rows[GRAFX_N_TYPES] = {0};
   int32_t n_eq = 0, n_comp_chunks = 0, n_partials = 0, n_eq_runs = 0;
   int32_t n_fitems = 0, in_bitem_begin = 0, in_bitem_count = 0;
-  int32_t n_delay = 0, n_dl_slots = 0, n_reverb = 0, rv_nbmax = 0;
+  int32_t n_delay = 0, n_dl_slots = 0, n_reverb = 0, rv_nbmax = 0, dl_nbmax = 0;
   double dl_taylor[9] = {0};
   int32_t eq_taps = 1023, eq_H = 511, eq_fft = 4096, eq_step = 0;  // eq_step: outputs per block
   int32_t comp_chunk = 2048;
