@@ -30,6 +30,13 @@ Readings of what the paper leaves open:
 import heapq
 
 I_TYPE, O_TYPE = 0, 1
+N_TYPES = 13
+
+# (inputs M, outputs N) of every type (Eq. 1a): the sources have no input; split gives
+# two outputs (mid, side); merge and the sidechain compressor take two inputs (merge:
+# mid, side; sidechain: main, key); every other processor, mix and output is 1 x 1.
+PORTS = {t: (1, 1) for t in range(N_TYPES)}
+PORTS.update({0: (0, 1), 10: (1, 2), 11: (2, 1), 12: (2, 1)})
 
 
 class GraphError(ValueError):
@@ -47,8 +54,10 @@ def preds_succs(n, edges):
     return preds, succs
 
 
-def validate(types, edges, n_types=10):
-    """Reject what the paper's graph model does not allow (Sec. 2 Definitions)."""
+def validate(types, edges, n_types=N_TYPES, ports=None):
+    """Reject what the paper's graph model does not allow (Sec. 2 Definitions).  With
+    ``ports`` (one (k, l) per edge) an edge must leave an existing output k of its
+    source and enter an existing input l of its destination."""
     n = len(types)
     if n == 0:
         raise GraphError("EINVAL", "empty graph")
@@ -58,6 +67,12 @@ def validate(types, edges, n_types=10):
     for s, d in edges:
         if not (0 <= s < n and 0 <= d < n):
             raise GraphError("EINVAL", f"edge ({s},{d}) out of range")
+    if ports is not None:
+        if len(ports) != len(edges):
+            raise GraphError("EINVAL", "one port pair per edge")
+        for (s, d), (k, l) in zip(edges, ports):
+            if not (0 <= k < PORTS[types[s]][1] and 0 <= l < PORTS[types[d]][0]):
+                raise GraphError("EINVAL", f"edge ({s},{d}) ports ({k},{l}) out of range")
     preds, succs = preds_succs(n, edges)
     for v in range(n):
         if types[v] == I_TYPE and preds[v]:

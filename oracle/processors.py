@@ -260,11 +260,14 @@ def gate_curve(Gu, T, W, R):
     return Gy, dGu, dT, dW, dR
 
 
-def compressor_fwd(u, p, eps=COMP_EPS, return_env=False, curve=knee):
-    """Eq. 8-12 (curve = knee); the noisegate is the same with curve = gate_curve."""
+def compressor_fwd(u, p, eps=COMP_EPS, return_env=False, curve=knee, key=None):
+    """Eq. 8-12 (curve = knee); the noisegate is the same with curve = gate_curve.  With
+    ``key`` (a sidechain input) the envelope of Eq. 8 follows the key's mid signal and
+    the gain of Eq. 12 applies to u."""
     u = _f64(u)
     alpha, T, W, R = (float(v) for v in _f64(p))
-    um = u[0] + u[1]
+    src = u if key is None else _f64(key)
+    um = src[0] + src[1]
     g = envelope(um * um, alpha)
     Gu = np.log(g + eps)
     Gy = curve(Gu, T, W, R)[0]
@@ -272,10 +275,12 @@ def compressor_fwd(u, p, eps=COMP_EPS, return_env=False, curve=knee):
     return (y, g) if return_env else y
 
 
-def compressor_bwd(u, p, ybar, eps=COMP_EPS, curve=knee):
+def compressor_bwd(u, p, ybar, eps=COMP_EPS, curve=knee, key=None):
+    """Adjoint of ``compressor_fwd``: (ubar, pbar), or (ubar, keybar, pbar) with a key."""
     u, ybar = _f64(u), _f64(ybar)
     alpha, T, W, R = (float(v) for v in _f64(p))
-    um = u[0] + u[1]
+    src = u if key is None else _f64(key)
+    um = src[0] + src[1]
     x = um * um
     g = envelope(x, alpha)
     Gu = np.log(g + eps)
@@ -286,11 +291,57 @@ def compressor_bwd(u, p, ybar, eps=COMP_EPS, curve=knee):
     gbar = Gybar * (dGu - 1.0) / (g + eps)
     lam = envelope_reverse(gbar, alpha)
     xbar = (1.0 - alpha) * lam
-    ubar = k[None, :] * ybar + (2.0 * um * xbar)[None, :]
+    srcbar = (2.0 * um * xbar)[None, :] * np.ones((2, 1))
     gprev = np.concatenate([[0.0], g[:-1]])
     pbar = np.array([np.sum(lam * (gprev - x)), np.sum(Gybar * dT),
                      np.sum(Gybar * dW), np.sum(Gybar * dR)])
-    return ubar, pbar
+    if key is None:
+        return k[None, :] * ybar + srcbar, pbar
+    return k[None, :] * ybar, srcbar, pbar
+
+
+# ---------------------------------------------------------------- MIMO processors (Sec. 2 Definitions, Eq. 1a/1b)
+# The paper's nodes take M inputs and give N outputs, each edge carrying its (output,
+# input) port pair.  Its Sec. 3 processors are all single-input single-output; these
+# three multi-port processors of a mixing console exercise the general form:
+#   * split (1 in, 2 out): mid and side as separate stereo rows, y0 = (m, m) with
+#     m = (l + r)/2, y1 = (s, s) with s = (l - r)/2;
+#   * merge (2 in, 1 out): back to left/right, y = (u0_l + u1_l, u0_r - u1_r), so that
+#     merge(split(u)) = u;
+#   * sidechain compressor (2 in: main, key; 1 out): the compressor of Eq. 8-12 with
+#     the envelope computed from the key input and the gain applied to the main input.
+def split_fwd(u):
+    u = _f64(u)
+    m = (u[0] + u[1]) / 2
+    s = (u[0] - u[1]) / 2
+    return [np.stack([m, m]), np.stack([s, s])]
+
+
+def split_bwd(u, ybars):
+    """ybars: the adjoints of both outputs; returns [ubar]."""
+    a = np.sum(_f64(ybars[0]), axis=0) / 2
+    b = np.sum(_f64(ybars[1]), axis=0) / 2
+    return [np.stack([a + b, a - b])]
+
+
+def merge_fwd(us):
+    u0, u1 = _f64(us[0]), _f64(us[1])
+    return np.stack([u0[0] + u1[0], u0[1] - u1[1]])
+
+
+def merge_bwd(us, ybar):
+    ybar = _f64(ybar)
+    return [ybar.copy(), np.stack([ybar[0], -ybar[1]])]
+
+
+def sidechain_fwd(us, p, eps=COMP_EPS):
+    return compressor_fwd(us[0], p, eps, key=us[1])
+
+
+def sidechain_bwd(us, p, ybar, eps=COMP_EPS):
+    """Returns ([ubar_main, ubar_key], pbar)."""
+    ub, kb, pb = compressor_bwd(us[0], p, ybar, eps, key=us[1])
+    return [ub, kb], pb
 
 
 # ---------------------------------------------------------------- noisegate (Eq. 13)

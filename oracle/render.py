@@ -10,13 +10,20 @@ processing"):
 ``backward`` walks the nodes in reverse topological order: a node's output adjoint
 is the sum of its consumers' input adjoints (plus dLoss/dY at outputs), and each
 processor adjoint gives the node's input adjoint and parameter gradient.
+
+Ports (Eq. 1a/1b with M inputs and N outputs): ``ports[e] = (k, l)`` says that edge e
+carries output k of its source to input l of its destination (default (0, 0) for every
+edge).  Input l of a node is the sum of its edges into l; U holds one row per output
+port (N_sum rows).  ``render_ports`` returns every node's list of outputs;
+``render_one_by_one`` returns each node's first output (the only one of a
+single-output node).
 """
 import numpy as np
 
 from . import graph as og
 from . import processors as op
 
-I_, O_, M_, G_, S_, E_, C_, D_, R_, N_ = range(10)
+I_, O_, M_, G_, S_, E_, C_, D_, R_, N_, P_, J_, K_ = range(13)
 
 DEFAULT_HP = dict(eq_taps=1023, fs=44100, comp_eps=op.COMP_EPS, eq_params="bands")
 
@@ -89,6 +96,33 @@ def process_bwd(t, u, p, ybar, hp):
     raise NotImplementedError(f"type {t}")
 
 
+def process_ports(t, us, p, hp):
+    """Process of a node with its list of inputs; returns its list of outputs."""
+    if t == P_:
+        return op.split_fwd(us[0])
+    if t == J_:
+        return [op.merge_fwd(us)]
+    if t == K_:
+        return [op.sidechain_fwd(us, p, hp["comp_eps"])]
+    return [process(t, us[0], p, hp)]
+
+
+def process_bwd_ports(t, us, p, ybars, hp):
+    """Adjoint of ``process_ports``: (list of input adjoints, parameter gradient)."""
+    if t == P_:
+        return op.split_bwd(us[0], ybars), np.zeros(0)
+    if t == J_:
+        return op.merge_bwd(us, ybars[0]), np.zeros(0)
+    if t == K_:
+        return op.sidechain_bwd(us, p, ybars[0], hp["comp_eps"])
+    ub, pb = process_bwd(t, us[0], p, ybars[0], hp)
+    return [ub], pb
+
+
+def _ports(edges, ports):
+    return list(ports) if ports is not None else [(0, 0)] * len(edges)
+
+
 def _rows_of(types):
     """Row of each node inside P[t] (original order of that type)."""
     cnt, rows = {}, []
@@ -117,66 +151,89 @@ def _topo(types, edges):
 
 
 def _param(params, t, row):
-    if t in (I_, O_, M_):
+    if t in (I_, O_, M_, P_, J_):
         return None
     return np.asarray(params[t][row], dtype=np.float64)
 
 
-def render_one_by_one(types, edges, sources, params, hp=None):
-    """All node outputs Y[v] (original ids), nodes visited in topological order.
-    Aggregation (Eq. 1b) sums in-edges in edge-insertion order."""
+def render_ports(types, edges, sources, params, hp=None, ports=None):
+    """Every node's list of outputs (original ids), nodes visited in topological order.
+    Aggregation (Eq. 1b) sums each input's edges in edge-insertion order."""
     hp = _hp(hp)
-    og.validate(types, edges)
+    og.validate(types, edges, ports=ports)
+    pt = _ports(edges, ports)
     n = len(types)
     rows = _rows_of(types)
     L = sources.shape[-1]
     in_edges = [[] for _ in range(n)]
-    for s, d in edges:
-        in_edges[d].append(s)
+    for (s, d), (k, l) in zip(edges, pt):
+        in_edges[d].append((s, k, l))
     Y = [None] * n
     for v in _topo(types, edges):
         t = types[v]
         if t == I_:
-            Y[v] = np.asarray(sources[rows[v]], dtype=np.float64)
+            Y[v] = [np.asarray(sources[rows[v]], dtype=np.float64)]
             continue
-        u = np.zeros((2, L))
-        for s in in_edges[v]:
-            u = u + Y[s]
-        Y[v] = process(t, u, _param(params, t, rows[v]), hp)
+        us = [np.zeros((2, L)) for _ in range(og.PORTS[t][0])]
+        for s, k, l in in_edges[v]:
+            us[l] = us[l] + Y[s][k]
+        Y[v] = process_ports(t, us, _param(params, t, rows[v]), hp)
     return Y
+
+
+def render_one_by_one(types, edges, sources, params, hp=None, ports=None):
+    """All node outputs Y[v] (original ids; a multi-output node's first output)."""
+    return [ys[0] for ys in render_ports(types, edges, sources, params, hp, ports)]
 
 
 def outputs_of(types, Y):
     return np.stack([Y[v] for v in range(len(types)) if types[v] == O_])
 
 
-def render_scheduled(types, edges, sources, params, hp=None, method="beam", width=32):
-    """Algorithm 1: returns (Y_N stacked over output nodes, U in new order, maps)."""
+def render_scheduled(types, edges, sources, params, hp=None, method="beam", width=32, ports=None):
+    """Algorithm 1: returns (Y_N stacked over output nodes, U in new order with one row
+    per output port (N_sum rows), maps)."""
     hp = _hp(hp)
+    pt = _ports(edges, ports)
+    og.validate(types, edges, ports=ports)
     string, steps = og.schedule(types, edges, method, width)
     mp = og.index_maps(types, edges, steps)
     n = len(types)
     L = sources.shape[-1]
     K = sum(1 for t in types if t == I_)
-    U = np.zeros((n, 2, L))
+    sigma = mp["sigma"]
+    inv = [0] * n
+    for v in range(n):
+        inv[sigma[v]] = v
+    new_types = [types[inv[v]] for v in range(n)]
+    # first U row of each node (new order): its output ports are consecutive rows
+    first = [0] * (n + 1)
+    for v in range(n):
+        first[v + 1] = first[v] + og.PORTS[new_types[v]][1]
+    U = np.zeros((first[n], 2, L))
     U[:K] = np.asarray(sources, dtype=np.float64)          # U = S (+) 0
-    sp, cp, cs = mp["step_ptr"], mp["csr_ptr"], mp["csr_src"]
-    for k in range(1, len(string)):
-        t = string[k]
-        a, b = sp[k], sp[k + 1]                            # I^S_n: a slice
-        # gather + aggregate (I^G_n, I^A_n)
-        Un = np.zeros((b - a, 2, L))
+    # in-edges of each new id with their ports
+    ins = [[] for _ in range(n)]
+    for (s, d), (k, l) in zip(edges, pt):
+        ins[sigma[d]].append((sigma[s], k, l))
+    sp = mp["step_ptr"]
+    for st in range(1, len(string)):
+        t = string[st]
+        a, b = sp[st], sp[st + 1]                            # I^S_n: a slice
+        # gather + aggregate per input port (I^G_n, I^A_n)
+        Un = [[np.zeros((2, L)) for _ in range(og.PORTS[t][0])] for _ in range(a, b)]
         for v in range(a, b):
-            for e in range(cp[v], cp[v + 1]):
-                Un[v - a] += U[cs[e]]
+            for s, k, l in sorted(ins[v]):
+                Un[v - a][l] += U[first[s] + k]
         # parameter slice (I^P_n) and processing
         for v in range(a, b):
             p = _param(params, t, mp["param_row"][v])
-            U[v] = process(t, Un[v - a], p, hp)
-    return U[sp[-2]:sp[-1]], U, dict(mp, string=string, steps=steps)
+            for k, y in enumerate(process_ports(t, Un[v - a], p, hp)):
+                U[first[v] + k] = y
+    return U[first[sp[-2]]:first[sp[-1]]], U, dict(mp, string=string, steps=steps)
 
 
-def backward(types, edges, sources, params, dY, hp=None, cond=False):
+def backward(types, edges, sources, params, dY, hp=None, cond=False, ports=None):
     """Reverse-mode pass.  dY[j] is dLoss/dY for the j-th output node (original
     order).  Returns (dparams {type: [rows, cols]}, dsources [K, 2, L]); with
     ``cond`` also {type: [rows, cols]} holding, for the gain and imager gradients
@@ -184,15 +241,20 @@ def backward(types, edges, sources, params, dY, hp=None, cond=False):
     other types): a sum that cancels to much less than that is ill-conditioned, and
     no FP32 evaluation can match it to a relative bound."""
     hp = _hp(hp)
+    pt = _ports(edges, ports)
     n = len(types)
     rows = _rows_of(types)
     L = sources.shape[-1]
-    Y = render_one_by_one(types, edges, sources, params, hp)
-    preds, succs = og.preds_succs(n, edges)
+    Y = render_ports(types, edges, sources, params, hp, ports)
+    in_edges = [[] for _ in range(n)]
+    out_edges = [[] for _ in range(n)]
+    for (s, d), (k, l) in zip(edges, pt):
+        in_edges[d].append((s, k, l))
+        out_edges[s].append((d, k, l))
     outs = [v for v in range(n) if types[v] == O_]
-    ybar = [np.zeros((2, L)) for _ in range(n)]
+    ybar = [[np.zeros((2, L)) for _ in range(og.PORTS[types[v]][1])] for v in range(n)]
     for j, v in enumerate(outs):
-        ybar[v] = ybar[v] + np.asarray(dY[j], dtype=np.float64)
+        ybar[v][0] = ybar[v][0] + np.asarray(dY[j], dtype=np.float64)
     ubar = [None] * n
     dparams = {t: np.zeros(np.shape(params[t]), dtype=np.float64) for t in params}
     dcond = {t: np.zeros(np.shape(params[t]), dtype=np.float64) for t in params}
@@ -200,21 +262,22 @@ def backward(types, edges, sources, params, dY, hp=None, cond=False):
     dsrc = np.zeros((K, 2, L))
     for v in reversed(_topo(types, edges)):
         t = types[v]
-        for w in succs[v]:          # each edge v -> w contributes w's input adjoint
-            ybar[v] = ybar[v] + ubar[w]
+        for w, k, l in out_edges[v]:   # each edge v:k -> w:l contributes w's input-l adjoint
+            ybar[v][k] = ybar[v][k] + ubar[w][l]
         if t == I_:
-            dsrc[rows[v]] = ybar[v]
+            dsrc[rows[v]] = ybar[v][0]
             continue
-        u = np.zeros((2, L))
-        for s in preds[v]:
-            u = u + Y[s]
-        ubar[v], pbar = process_bwd(t, u, _param(params, t, rows[v]), ybar[v], hp)
+        us = [np.zeros((2, L)) for _ in range(og.PORTS[t][0])]
+        for s, k, l in in_edges[v]:
+            us[l] = us[l] + Y[s][k]
+        p = _param(params, t, rows[v])
+        ubar[v], pbar = process_bwd_ports(t, us, p, ybar[v], hp)
         if pbar.size:
             dparams[t][rows[v]] = pbar
         if cond and t == G_:
-            dcond[t][rows[v]] = op.gain_bwd_abs(u, _param(params, t, rows[v]), ybar[v])
+            dcond[t][rows[v]] = op.gain_bwd_abs(us[0], p, ybar[v][0])
         if cond and t == S_:
-            dcond[t][rows[v]] = op.imager_bwd_abs(u, _param(params, t, rows[v]), ybar[v])
+            dcond[t][rows[v]] = op.imager_bwd_abs(us[0], p, ybar[v][0])
     if cond:
         return dparams, dsrc, dcond
     return dparams, dsrc

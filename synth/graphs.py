@@ -2,8 +2,9 @@
 
 A graph is a node-type list and an edge list ``(src, dst)`` in insertion order
 (multi-edges allowed), the tensor form of Sec. 2 "Graph representations"
-(T_V and E).  The builders only draw structure; scheduling and rendering live
-elsewhere.
+(T_V and E), with the edge types T_E as ``ports[e] = (output k, input l)`` (all
+(0, 0) unless a multi-port node is connected).  The builders only draw structure;
+scheduling and rendering live elsewhere.
 """
 from dataclasses import dataclass, field
 from typing import List, Tuple
@@ -17,6 +18,11 @@ from .types import I, O, M, G, S, E, C, D, R, N
 class Graph:
     types: List[int] = field(default_factory=list)
     edges: List[Tuple[int, int]] = field(default_factory=list)
+    ports: List[Tuple[int, int]] = field(default_factory=list)
+
+    def __post_init__(self):
+        if len(self.ports) != len(self.edges):   # built from (types, edges) alone
+            self.ports = [(0, 0)] * len(self.edges)
 
     # builder calls named after the paper's API (Fig. 2a)
     def add(self, t: int) -> int:
@@ -29,8 +35,13 @@ class Graph:
             self.connect(a, b)
         return ids[0], ids[-1]
 
-    def connect(self, src: int, dst: int):
+    def connect(self, src: int, dst: int, out_port: int = 0, in_port: int = 0):
         self.edges.append((int(src), int(dst)))
+        self.ports.append((int(out_port), int(in_port)))
+
+    @property
+    def has_ports(self):
+        return any(p != (0, 0) for p in self.ports)
 
     @property
     def n_nodes(self):

@@ -23,7 +23,7 @@ The paper's own settings (preset "paper", widths in ``types.PAPER_PARAM_COLS``):
 """
 import numpy as np
 
-from .types import G, S, E, C, D, R, N, PARAM_COLS, param_cols
+from .types import G, S, E, C, D, R, N, K, PARAM_COLS, param_cols
 
 LN10 = np.log(10.0)
 DELAY_FFT = 32768
@@ -50,6 +50,9 @@ def _rows(rng, t, n, fs=44100):
         p[:, 2] = 3.0 * LN10 / 10.0
         p[:, 3] = rng.uniform(1, 8, n)
         return p
+    if t == K:
+        # sidechain compressor: the compressor's distributions
+        return _rows(rng, C, n, fs)
     if t == N:
         # noisegate: threshold -60..-30 dB, expansion ratio 1..4, W = 3 dB
         p = np.empty((n, 4))
@@ -135,7 +138,7 @@ def neutral_params(graph, preset="compact"):
         if cols[t] == 0:
             continue
         p = np.zeros((n, cols[t]))
-        if t in (C, N):
+        if t in (C, N, K):
             p[:, 0] = 0.99
             p[:, 2] = 3.0 * LN10 / 10.0
             p[:, 3] = 1.0
