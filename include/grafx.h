@@ -26,7 +26,8 @@
  *    pitch = grafx_pitch(L) = L rounded up to a multiple of 4.  Samples at and past
  *    L inside a row are padding: ignored on input, written as 0 on output.
  *  - Node type ids: see GRAFX_T_*.  Parameter widths per type (columns of P[t]):
- *    gain 2, imager 1, compressor 4, noisegate 4; eq 8, delay 176, reverb 50 in the
+ *    gain 2, imager 1, compressor 4, noisegate 4, sidechain 4, split and merge none;
+ *    eq 8, delay 176, reverb 50 in the
  *    compact layouts, eq (eq_taps+1)/2, delay 880, reverb 768 in the paper's
  *    (grafx_plan_opts, grafx_plan_info.param_cols, grafx_bind_params).
  */
@@ -59,8 +60,19 @@ enum {
 enum {
   GRAFX_T_IN = 0, GRAFX_T_OUT = 1, GRAFX_T_MIX = 2, GRAFX_T_GAIN = 3, GRAFX_T_IMAGER = 4,
   GRAFX_T_EQ = 5, GRAFX_T_COMP = 6, GRAFX_T_DELAY = 7, GRAFX_T_REVERB = 8, GRAFX_T_GATE = 9,
-  GRAFX_N_TYPES = 10
+  /* multi-port processors (Sec. 2 Definitions, Eq. 1a with M inputs and N outputs):
+   * SPLIT: 1 input, 2 outputs (port 0 = (m, m), port 1 = (s, s), m = (l + r)/2,
+   *        s = (l - r)/2); MERGE: 2 inputs (0 = mid path, 1 = side path), 1 output
+   *        (u0_l + u1_l, u0_r - u1_r), the inverse of SPLIT; SIDECHAIN: the compressor
+   *        of Eq. 8-12 with 2 inputs (0 = main, 1 = key): the envelope follows the key,
+   *        the gain applies to the main input. */
+  GRAFX_T_SPLIT = 10, GRAFX_T_MERGE = 11, GRAFX_T_SIDECHAIN = 12,
+  GRAFX_N_TYPES = 13
 };
+
+/* Inputs M and outputs N of a node type (GRAFX_EINVAL for an unknown type): sources
+ * 0 x 1, SPLIT 1 x 2, MERGE and SIDECHAIN 2 x 1, every other type 1 x 1. */
+int grafx_type_ports(int32_t type, int32_t* n_inputs, int32_t* n_outputs);
 
 /* ---------------------------------------------------------------- schedules (Sec. 2 "Type scheduling") */
 enum {
@@ -94,8 +106,13 @@ int grafx_graph_add(grafx_graph* g, int32_t type, int32_t* id_out);
 /* Append n nodes of types[0..n) connected in series; first/last ids are returned. */
 int grafx_graph_add_serial_chain(grafx_graph* g, const int32_t* types, int32_t n,
                                  int32_t* first_id, int32_t* last_id);
-/* Append the edge src -> dst (ids must exist). */
+/* Append the edge src -> dst (ids must exist): output 0 of src to input 0 of dst. */
 int grafx_graph_connect(grafx_graph* g, int32_t src, int32_t dst);
+/* Append the edge from output `src_port` of src to input `dst_port` of dst: the edge
+ * type t_ij = (k, l) of Sec. 2 (the edge type tensor T_E).  Input l of a node is the
+ * sum of the signals on its edges into l; an input with no edge reads zeros.  Ports
+ * are checked against grafx_type_ports when a plan is created (GRAFX_EINVAL). */
+int grafx_graph_connect_ports(grafx_graph* g, int32_t src, int32_t dst, int32_t src_port, int32_t dst_port);
 int grafx_graph_size(const grafx_graph* g, int32_t* n_nodes, int32_t* n_edges);
 
 /* ---------------------------------------------------------------- planning
@@ -212,7 +229,8 @@ int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* s
  * per-frame decays of the noise masks (Eq. 7), then q_dry, q_wet (log gains):
  * y = e^{q_dry} u + e^{q_wet} (h * u) with the 88200-tap IR h of Eq. 6-7;
  * noisegate [alpha, T, W, R] like the compressor, with the gate curve of Eq. 13
- * (unchanged above T + W, expansion by R below T - W, a quadratic knee between).
+ * (unchanged above T + W, expansion by R below T - W, a quadratic knee between);
+ * sidechain [alpha, T, W, R] as the compressor, the envelope taken from input 1.
  * Paper layouts: eq (eq_taps+1)/2 = the log-magnitudes p_e[k] of Eq. 4 (GRAFX_EQ_LOGMAG);
  * delay 880 = [channel][tap 0..19][Re z, Im z, 20 log-magnitudes], tap m delayed by
  * m S + (round(S (-arg z)/2pi) mod S), S = sample_rate/10, the surrogate of Eq. 15 of

@@ -77,7 +77,7 @@ def adam_step(theta, m, v, grad_theta, t, lr=1e-2, beta1=0.9, beta2=0.999, eps=1
 def param_codes(t, cols):
     """Map code of every column of P[t] (type ids as in synth.types)."""
     codes = np.full(cols, IDENT, dtype=np.int8)
-    if t in (6, 9):                  # compressor / noisegate [alpha, T, W, R]
+    if t in (6, 9, 12):              # compressor / noisegate / sidechain [alpha, T, W, R]
         codes[:] = [ALPHA, IDENT, SOFTPLUS, RATIO]
     if t == 8 and cols == 50:        # reverb (12 bands): H_delta columns are decays
         c = np.full(50, IDENT, dtype=np.int8)

@@ -18,8 +18,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgrafx.so")
 
 T_IN, T_OUT, T_MIX, T_GAIN, T_IMAGER, T_EQ, T_COMP, T_DELAY, T_REVERB, T_GATE = range(10)
-N_TYPES = 10
-PARAM_COLS = {T_GAIN: 2, T_IMAGER: 1, T_EQ: 8, T_COMP: 4, T_DELAY: 176, T_REVERB: 50, T_GATE: 4}
+T_SPLIT, T_MERGE, T_SIDECHAIN = 10, 11, 12   # multi-port processors (inputs x outputs: 1x2, 2x1, 2x1)
+N_TYPES = 13
+PARAM_COLS = {T_GAIN: 2, T_IMAGER: 1, T_EQ: 8, T_COMP: 4, T_DELAY: 176, T_REVERB: 50, T_GATE: 4, T_SIDECHAIN: 4}
 # processor layouts (grafx_plan_opts): "compact" (the widths above) or "paper" (Sec. 3)
 EQ_PARAMS = {"bands": 0, "logmag": 1}
 DELAY_LAYOUT = {"compact": 0, "slots": 1}
@@ -67,6 +68,8 @@ SIGNATURES = {
     "grafx_graph_add": (ctypes.c_int, [_P, _I32, _I32P]),
     "grafx_graph_add_serial_chain": (ctypes.c_int, [_P, _I32P, _I32, _I32P, _I32P]),
     "grafx_graph_connect": (ctypes.c_int, [_P, _I32, _I32]),
+    "grafx_graph_connect_ports": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32]),
+    "grafx_type_ports": (ctypes.c_int, [_I32, _I32P, _I32P]),
     "grafx_graph_size": (ctypes.c_int, [_P, _I32P, _I32P]),
     "grafx_plan_opts_default": (None, [ctypes.POINTER(PlanOpts)]),
     "grafx_plan_create": (ctypes.c_int, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_I64),
@@ -161,17 +164,29 @@ class Graph:
         _check(lib().grafx_graph_add_serial_chain(self._h, arr, len(types), ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
-    def connect(self, src, dst):
-        _check(lib().grafx_graph_connect(self._h, int(src), int(dst)))
+    def connect(self, src, dst, out_port=0, in_port=0):
+        """Edge from output ``out_port`` of src to input ``in_port`` of dst (T_E)."""
+        if out_port or in_port:
+            _check(lib().grafx_graph_connect_ports(self._h, int(src), int(dst), int(out_port), int(in_port)))
+        else:
+            _check(lib().grafx_graph_connect(self._h, int(src), int(dst)))
 
     @classmethod
-    def from_lists(cls, types, edges):
+    def from_lists(cls, types, edges, ports=None):
         g = cls()
         for t in types:
             g.add(t)
-        for s, d in edges:
-            g.connect(s, d)
+        for e, (s, d) in enumerate(edges):
+            k, l = ports[e] if ports is not None else (0, 0)
+            g.connect(s, d, k, l)
         return g
+
+
+def type_ports(t):
+    """(inputs, outputs) of node type t (Eq. 1a)."""
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().grafx_type_ports(int(t), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def _ptr(t):

@@ -39,6 +39,10 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
   c.tcsr_ptr = at<const int32_t>(p, p->ws.tcsr_ptr);
   c.tcsr_dst = at<const int32_t>(p, p->ws.tcsr_dst);
   c.items = at<const int4_>(p, p->ws.items);
+  c.csr_row = at<const int64_t>(p, p->ws.csr_row);
+  c.tcsr_row = at<const int64_t>(p, p->ws.tcsr_row);
+  c.in1_begin = at<const int32_t>(p, p->ws.in1_begin);
+  c.out1_begin = at<const int32_t>(p, p->ws.out1_begin);
   c.tw = at<const float2_>(p, p->ws.twiddle);
   c.ptw = at<const float2_>(p, p->ws.ptw);
   c.eq_cos = at<const float>(p, p->ws.eq_cos);
@@ -99,7 +103,8 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
 
 int check_ready(const Plan* p) {
   if (!p->dev_ws) return fail(GRAFX_ESTATE, "workspace not bound (grafx_plan_bind_workspace)");
-  for (int t : {GRAFX_T_GAIN, GRAFX_T_IMAGER, GRAFX_T_EQ, GRAFX_T_COMP, GRAFX_T_DELAY, GRAFX_T_REVERB, GRAFX_T_GATE})
+  for (int t : {GRAFX_T_GAIN, GRAFX_T_IMAGER, GRAFX_T_EQ, GRAFX_T_COMP, GRAFX_T_DELAY, GRAFX_T_REVERB, GRAFX_T_GATE,
+                GRAFX_T_SIDECHAIN})
     if (p->n_type_rows[t] > 0 && !p->params[t])
       return fail(GRAFX_ESTATE, "parameters of type " + std::to_string(t) + " not bound");
   if (p->n_type_rows[GRAFX_T_REVERB] > 0 && !p->rv_noise)
@@ -175,7 +180,10 @@ int grafx_graph_add_serial_chain(grafx_graph* g, const int32_t* types, int32_t n
   int32_t first = int32_t(g->types.size());
   for (int32_t i = 0; i < n; ++i) {
     g->types.push_back(types[i]);
-    if (i) g->edges.push_back({first + i - 1, first + i});
+    if (i) {
+      g->edges.push_back({first + i - 1, first + i});
+      g->ports.push_back({0, 0});
+    }
   }
   if (first_id) *first_id = first;
   if (last_id) *last_id = first + n - 1;
@@ -184,13 +192,28 @@ int grafx_graph_add_serial_chain(grafx_graph* g, const int32_t* types, int32_t n
 }
 
 int grafx_graph_connect(grafx_graph* g, int32_t src, int32_t dst) {
+  return grafx_graph_connect_ports(g, src, dst, 0, 0);
+}
+
+int grafx_graph_connect_ports(grafx_graph* g, int32_t src, int32_t dst, int32_t src_port, int32_t dst_port) {
   GX_TRY
   if (!g) return fail(GRAFX_EINVAL, "null graph");
   const int32_t n = int32_t(g->types.size());
   if (src < 0 || src >= n || dst < 0 || dst >= n) return fail(GRAFX_EINVAL, "node id out of range");
+  if (src_port < 0 || src_port >= type_outputs(g->types[src]) || dst_port < 0 ||
+      dst_port >= type_inputs(g->types[dst]))
+    return fail(GRAFX_EINVAL, "port out of range for the node types");
   g->edges.push_back({src, dst});
+  g->ports.push_back({src_port, dst_port});
   return GRAFX_OK;
   GX_CATCH
+}
+
+int grafx_type_ports(int32_t type, int32_t* n_inputs, int32_t* n_outputs) {
+  if (type < 0 || type >= GRAFX_N_TYPES) return fail(GRAFX_EINVAL, "unknown node type");
+  if (n_inputs) *n_inputs = type_inputs(type);
+  if (n_outputs) *n_outputs = type_outputs(type);
+  return GRAFX_OK;
 }
 
 int grafx_graph_size(const grafx_graph* g, int32_t* n_nodes, int32_t* n_edges) {
@@ -324,6 +347,10 @@ int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* s
   put(p->ws.tcsr_ptr, p->tcsr_ptr.data(), p->tcsr_ptr.size() * 4);
   put(p->ws.tcsr_dst, p->tcsr_dst.data(), p->tcsr_dst.size() * 4);
   put(p->ws.items, p->items.data(), p->items.size() * sizeof(int4_));
+  put(p->ws.csr_row, p->csr_row.data(), p->csr_row.size() * 8);
+  put(p->ws.tcsr_row, p->tcsr_row.data(), p->tcsr_row.size() * 8);
+  put(p->ws.in1_begin, p->in1_begin.data(), p->in1_begin.size() * 4);
+  put(p->ws.out1_begin, p->out1_begin.data(), p->out1_begin.size() * 4);
   put(p->ws.twiddle, p->twiddle.data(), p->twiddle.size() * sizeof(float2_));
   put(p->ws.ptw, p->ptw.data(), p->ptw.size() * sizeof(float2_));
   put(p->ws.eq_cos, p->eq_cos.data(), p->eq_cos.size() * 4);
@@ -381,6 +408,9 @@ struct StepRange {
 // Forward steps whose processors have a parameter-only design (EQ filter spectra,
 // delay taps, reverb impulse responses): the design depends on no signal, so it runs on
 // the side stream from the start of the range and the step waits for it.
+// kernel variant of the compressor family (compressor, noisegate, sidechain)
+static int comp_mode_of(int type) { return type == GRAFX_T_GATE ? 1 : type == GRAFX_T_SIDECHAIN ? 2 : 0; }
+
 static bool has_design(int type) {
   return type == GRAFX_T_EQ || type == GRAFX_T_DELAY || type == GRAFX_T_REVERB;
 }
@@ -418,8 +448,9 @@ static int render_range(grafx_plan* p, const float* sources, float* out, int32_t
         break;
       case GRAFX_T_COMP:
       case GRAFX_T_GATE:
+      case GRAFX_T_SIDECHAIN:
         clear_step_flags(p, st.fitem_begin, st.fitem_count, 2 * k, s);
-        launches += launch_comp(0, c, st.fitem_begin, st.fitem_count, 2 * k, st.type == GRAFX_T_GATE, s);
+        launches += launch_comp(0, c, st.fitem_begin, st.fitem_count, 2 * k, comp_mode_of(st.type), s);
         break;
       case GRAFX_T_DELAY:
         launches += launch_delay(1, c, st.fitem_begin, st.fitem_count, s);
@@ -543,11 +574,12 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
         break;
       case GRAFX_T_COMP:
       case GRAFX_T_GATE:
+      case GRAFX_T_SIDECHAIN:
         clear_step_flags(p, st.bitem_begin, st.bitem_count, 2 * k + 1, s);
-        launches += launch_comp(1, c, st.bitem_begin, st.bitem_count, 2 * k + 1, st.type == GRAFX_T_GATE, s);
+        launches += launch_comp(1, c, st.bitem_begin, st.bitem_count, 2 * k + 1, comp_mode_of(st.type), s);
         if (c.dparams) {
           to_side(k);
-          launches += launch_comp(2, c, st.node_begin, st.node_end, 0, false, side);
+          launches += launch_comp(2, c, st.node_begin, st.node_end, 0, 0, side);
         }
         break;
       case GRAFX_T_REVERB:
@@ -571,6 +603,10 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
           to_side(k);
           launches += launch_ew_finalize(c, st.node_begin, st.node_end, param_cols(p, st.type), side);
         }
+        break;
+      case GRAFX_T_SPLIT:
+      case GRAFX_T_MERGE:
+        launches += launch_ew_bwd(st.type, c, st.bitem_begin, st.bitem_count, s);
         break;
       default:
         launches += launch_ew_bwd(GRAFX_T_MIX, c, st.bitem_begin, st.bitem_count, s);
@@ -668,7 +704,7 @@ int grafx_step_graph_create(grafx_plan* p, const float* sources, float* out, con
   // kernel attributes are set outside the capture
   DevCtx c0 = make_ctx(p, sources, out, nullptr, nullptr);
   launch_eq(-1, c0, 0, 0, s);
-  launch_comp(-1, c0, 0, 0, 0, false, s);
+  launch_comp(-1, c0, 0, 0, 0, 0, s);
   launch_delay(-1, c0, 0, 0, s);
   launch_reverb(-1, c0, 0, 0, s);
   launch_loss(-1, make_loss(p, out, target), s);

@@ -18,6 +18,10 @@ struct DevCtx {
   const int32_t* csr_src;
   const int32_t* tcsr_ptr;
   const int32_t* tcsr_dst;
+  const int64_t* csr_row;     // per in-edge (CSR order): the source's output-port row (REF_SHIFT)
+  const int64_t* tcsr_row;    // per consumer edge: the consumer's input-port adjoint row
+  const int32_t* in1_begin;   // per node: first in-edge of input 1 (= csr_ptr[v+1] with one input)
+  const int32_t* out1_begin;  // per node: first consumer edge of output 1
   const int4_* items;
   const float2_* tw;    // exp(-2 pi i m / 8192), m < 8192 (window tables)
   const float2_* ptw;   // FFT pass twiddle tables (fft.cuh)
@@ -91,6 +95,10 @@ __device__ __forceinline__ float* arow_w(const DevCtx& c, const NodeDev& n) {
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) {
   return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
+__device__ __forceinline__ float4 f4sub(float4 a, float4 b) {
+  return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+__device__ __forceinline__ float4 f4scale(float4 a, float s) { return make_float4(s * a.x, s * a.y, s * a.z, s * a.w); }
 __device__ __forceinline__ float4 f4zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
 // Keep only the samples of quad [t, t+4) that are < len (row padding reads as 0).
@@ -108,26 +116,33 @@ __device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpre
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
+// The row an in-edge e reads (the source's output port k) and the adjoint row a consumer
+// edge e reads (the consumer's input-port-l adjoint), from the planner's row references.
+__device__ __forceinline__ const float* in_row(const DevCtx& c, int e) {
+  const int64_t r = c.csr_row[e];
+  return c.ybase[r >> REF_SHIFT] + (r & REF_MASK);
+}
+__device__ __forceinline__ const float* out_adj_row(const DevCtx& c, int e) {
+  const int64_t r = c.tcsr_row[e];
+  return c.abase[r >> REF_SHIFT] + (r & REF_MASK);
+}
+
 // u_v: sum over the in-edges of v (Eq. 1b; I^G gather + I^A aggregate of Algorithm 1)
 // of the quad [t, t+4) of channel ch, in CSR order.  t must be a multiple of 4.
+// (Single-input nodes: every in-edge enters input 0.)
 __device__ __forceinline__ float4 gather_in(const DevCtx& c, int v, int ch, int t, int len, int pitch) {
   float4 acc = f4zero();
   const int e1 = c.csr_ptr[v + 1];
-  for (int e = c.csr_ptr[v]; e < e1; ++e) {
-    const NodeDev& s = c.nodes[c.csr_src[e]];
-    acc = f4add(acc, ld4(yrow(c, s) + ch * pitch + t));
-  }
+  for (int e = c.csr_ptr[v]; e < e1; ++e) acc = f4add(acc, ld4(in_row(c, e) + ch * pitch + t));
   return mask4(acc, t, len);
 }
 
 // ybar_v: sum over the consumers w of v of their input adjoints (transposed CSR).
+// (Single-output nodes: every consumer edge leaves output 0.)
 __device__ __forceinline__ float4 gather_out_adj(const DevCtx& c, int v, int ch, int t, int len, int pitch) {
   float4 acc = f4zero();
   const int e1 = c.tcsr_ptr[v + 1];
-  for (int e = c.tcsr_ptr[v]; e < e1; ++e) {
-    const NodeDev& w = c.nodes[c.tcsr_dst[e]];
-    acc = f4add(acc, ld4(arow(c, w) + ch * pitch + t));
-  }
+  for (int e = c.tcsr_ptr[v]; e < e1; ++e) acc = f4add(acc, ld4(out_adj_row(c, e) + ch * pitch + t));
   return mask4(acc, t, len);
 }
 

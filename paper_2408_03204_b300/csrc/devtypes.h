@@ -19,8 +19,15 @@ struct alignas(16) NodeDev {
   int16_t type;    // GRAFX_T_*
   int32_t grow;    // row of the gradient table the backward writes: prow, or with a
                    // source batch the node's own row of the per-copy gradient table
-  int32_t pad[3];
+  int32_t rstride; // floats between the node's consecutive port rows (output port k at
+                   // off_y + k rstride, input-port adjoint l at off_a + l rstride)
+  int32_t pad[2];
 };
+
+// Row reference of a CSR entry: the buffer (NodeKind) in the top bits, the float offset
+// of the row inside it below.
+constexpr int REF_SHIFT = 60;
+constexpr int64_t REF_MASK = (int64_t(1) << REF_SHIFT) - 1;
 
 struct alignas(16) int4_ { int32_t x, y, z, w; };
 struct alignas(8) int2_ { int32_t x, y; };

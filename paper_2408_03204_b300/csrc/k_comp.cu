@@ -218,10 +218,10 @@ __device__ __forceinline__ float block_affine_scan(float b, float la_spt, float*
 __device__ __forceinline__ const float* single_row(const DevCtx& c, int v, bool adj) {
   if (!adj) {
     const int e0 = c.csr_ptr[v];
-    return c.csr_ptr[v + 1] - e0 == 1 ? yrow(c, c.nodes[c.csr_src[e0]]) : nullptr;
+    return c.csr_ptr[v + 1] - e0 == 1 ? in_row(c, e0) : nullptr;
   }
   const int e0 = c.tcsr_ptr[v];
-  return c.tcsr_ptr[v + 1] - e0 == 1 ? arow(c, c.nodes[c.tcsr_dst[e0]]) : nullptr;
+  return c.tcsr_ptr[v + 1] - e0 == 1 ? out_adj_row(c, e0) : nullptr;
 }
 
 template <int SPT>
@@ -258,6 +258,31 @@ __device__ __forceinline__ void load_chunk(const DevCtx& c, int v, const NodeDev
     ur[4 * q + 0] = r.x; ur[4 * q + 1] = r.y; ur[4 * q + 2] = r.z; ur[4 * q + 3] = r.w;
   }
 }
+
+// This thread's SPT samples of both channels summed over the in-edges [e0, e1) (one
+// input port of a multi-input node).
+template <int SPT>
+__device__ __forceinline__ void load_range(const DevCtx& c, int e0, int e1, const NodeDev& nd, int t, float* l,
+                                           float* r) {
+#pragma unroll
+  for (int q = 0; q < SPT / 4; ++q) {
+    float4 a = f4zero(), b = f4zero();
+    if (t + 4 * q < nd.len)
+      for (int e = e0; e < e1; ++e) {
+        const float* row = in_row(c, e);
+        a = f4add(a, ld4(row + t + 4 * q));
+        b = f4add(b, ld4(row + nd.pitch + t + 4 * q));
+      }
+    a = mask4(a, t + 4 * q, nd.len);
+    b = mask4(b, t + 4 * q, nd.len);
+    l[4 * q + 0] = a.x; l[4 * q + 1] = a.y; l[4 * q + 2] = a.z; l[4 * q + 3] = a.w;
+    r[4 * q + 0] = b.x; r[4 * q + 1] = b.y; r[4 * q + 2] = b.z; r[4 * q + 3] = b.w;
+  }
+}
+
+// Kernel variants: the compressor (Eq. 10-11), the noisegate (Eq. 13) and the sidechain
+// compressor (the compressor's curve; envelope from input 1, gain on input 0).
+constexpr int MODE_COMP = 0, MODE_GATE = 1, MODE_SC = 2;
 
 // Prefetch: this thread's SPT samples of both channels of `row` from t into its own
 // slots dst[ch * 256 * SPT + threadIdx.x * SPT ...] (zeros past the node's length).
@@ -336,9 +361,10 @@ __device__ __forceinline__ void envelope(const float* x, float alpha, float cin,
 
 // Software-pipelined over tickets: once a chunk's inputs are in registers, the next
 // ticket's copies start (cp.async) and run under this chunk's scan, look-back and gain.
-template <int SPT, bool GATE>
+template <int SPT, int MODE>
 __global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_fwd(DevCtx c, int item0, int n_items, int ticket) {
   constexpr int CH = 256 * SPT;
+  constexpr bool GATE = MODE == MODE_GATE, SC = MODE == MODE_SC;
   __shared__ __align__(16) float buf[2 * CH];
   __shared__ float sh[32];
   __shared__ int s_it[2];
@@ -346,7 +372,7 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_fwd(DevCtx c, i
   if (threadIdx.x == 0) s_it[0] = atomicAdd(c.tickets + ticket, 1);
   __syncthreads();
   int it = s_it[0], slot = 0;
-  if (it < n_items) prefetch_item<SPT, false>(c, item0 + it, buf);
+  if (!SC && it < n_items) prefetch_item<SPT, false>(c, item0 + it, buf);
   while (it < n_items) {
     if (threadIdx.x == 0) s_it[slot ^ 1] = atomicAdd(c.tickets + ticket, 1);  // read after the scan's barriers
     const int4_ w = c.items[item0 + it];
@@ -359,9 +385,17 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_fwd(DevCtx c, i
     const int t = chunk * CH + threadIdx.x * SPT;
     float ul[SPT], ur[SPT], x[SPT], g[SPT];
     cp_async_wait_all();
-    fetch_rows<SPT>(c, v, nd, t, buf, ul, ur, false);
+    if constexpr (SC) {
+      float kl[SPT], kr[SPT];
+      load_range<SPT>(c, c.csr_ptr[v], c.in1_begin[v], nd, t, ul, ur);      // main (input 0)
+      load_range<SPT>(c, c.in1_begin[v], c.csr_ptr[v + 1], nd, t, kl, kr);  // key (input 1)
 #pragma unroll
-    for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
+      for (int i = 0; i < SPT; ++i) { float m = kl[i] + kr[i]; x[i] = m * m; }
+    } else {
+      fetch_rows<SPT>(c, v, nd, t, buf, ul, ur, false);
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
+    }
     // zero-start local state at the thread's end
     float b = 0.f;
 #pragma unroll
@@ -369,7 +403,7 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_fwd(DevCtx c, i
     float total;
     float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
     const int next = s_it[slot ^ 1];
-    if (next < n_items) prefetch_item<SPT, false>(c, item0 + next, buf);
+    if (!SC && next < n_items) prefetch_item<SPT, false>(c, item0 + next, buf);
     if (threadIdx.x < 32) {
       float carry = 0.f;
       if (chunk == 0) {
@@ -403,9 +437,10 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_fwd(DevCtx c, i
   cp_async_wait_all();
 }
 
-template <int SPT, bool GATE>
+template <int SPT, int MODE>
 __global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_bwd(DevCtx c, int item0, int n_items, int ticket) {
   constexpr int CH = 256 * SPT;
+  constexpr bool GATE = MODE == MODE_GATE, SC = MODE == MODE_SC;
   extern __shared__ __align__(16) float buf[];  // 4 * CH floats: prefetched u and ybar rows
   __shared__ float sh[32];
   __shared__ float glast[256];
@@ -415,7 +450,7 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_bwd(DevCtx c, i
   if (threadIdx.x == 0) s_it[0] = atomicAdd(c.tickets + ticket, 1);
   __syncthreads();
   int it = s_it[0], slot = 0;
-  if (it < n_items) prefetch_item<SPT, true>(c, item0 + it, buf);
+  if (!SC && it < n_items) prefetch_item<SPT, true>(c, item0 + it, buf);
   while (it < n_items) {
     if (threadIdx.x == 0) s_it[slot ^ 1] = atomicAdd(c.tickets + ticket, 1);  // read after the scan's barriers
     const int4_ w = c.items[item0 + it];
@@ -428,11 +463,21 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_bwd(DevCtx c, i
     const int t = chunk * CH + threadIdx.x * SPT;
     const int n_chunks = (nd.len + CH - 1) / CH;
     float ul[SPT], ur[SPT], bl[SPT], br[SPT], x[SPT], g[SPT], a[SPT];
+    float km[SC ? SPT : 1];   // sidechain: the key's mid l + r
     cp_async_wait_all();
-    fetch_rows<SPT>(c, v, nd, t, buf, ul, ur, false);
-    fetch_rows<SPT>(c, v, nd, t, buf + 2 * CH, bl, br, true);
+    if constexpr (SC) {
+      float kr[SPT];
+      load_range<SPT>(c, c.csr_ptr[v], c.in1_begin[v], nd, t, ul, ur);      // main (input 0)
+      load_range<SPT>(c, c.in1_begin[v], c.csr_ptr[v + 1], nd, t, km, kr);  // key (input 1)
+      load_chunk<SPT>(c, v, nd, t, bl, br, true);
 #pragma unroll
-    for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
+      for (int i = 0; i < SPT; ++i) { km[i] += kr[i]; x[i] = km[i] * km[i]; }
+    } else {
+      fetch_rows<SPT>(c, v, nd, t, buf, ul, ur, false);
+      fetch_rows<SPT>(c, v, nd, t, buf + 2 * CH, bl, br, true);
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
+    }
     // recompute the envelope from the stored chunk carry-in (same arithmetic as forward)
     const float carry_g = c.comp_carry[w.z];
     float b = 0.f;
@@ -441,7 +486,7 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_bwd(DevCtx c, i
     float total;
     float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
     const int next = s_it[slot ^ 1];
-    if (next < n_items) prefetch_item<SPT, true>(c, item0 + next, buf);
+    if (!SC && next < n_items) prefetch_item<SPT, true>(c, item0 + next, buf);
     const float cin = excl + expf(la * float(SPT * threadIdx.x)) * carry_g;
     envelope<SPT>(x, alpha, cin, g);
     // local adjoints
@@ -491,15 +536,29 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_bwd(DevCtx c, i
     }
     float gprev = threadIdx.x > 0 ? glast[threadIdx.x - 1] : carry_g;
     float dA = 0.f;
+    if constexpr (SC) {
+      // input 0 (main): gain ybar; input 1 (key): 2 (k_l + k_r)(1 - alpha) lambda on both channels
 #pragma unroll
-    for (int i = 0; i < SPT; ++i) {
-      dA += lam[i] * (gprev - x[i]);
-      gprev = g[i];
-      float xb2 = 2.f * (ul[i] + ur[i]) * (1.f - alpha) * lam[i];
-      bl[i] = gain[i] * bl[i] + xb2;
-      br[i] = gain[i] * br[i] + xb2;
+      for (int i = 0; i < SPT; ++i) {
+        dA += lam[i] * (gprev - x[i]);
+        gprev = g[i];
+        bl[i] *= gain[i];
+        br[i] *= gain[i];
+        km[i] = 2.f * km[i] * (1.f - alpha) * lam[i];
+      }
+      store_chunk<SPT>(arow_w(c, nd), nd, t, bl, br);
+      store_chunk<SPT>(arow_w(c, nd) + nd.rstride, nd, t, km, km);
+    } else {
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) {
+        dA += lam[i] * (gprev - x[i]);
+        gprev = g[i];
+        float xb2 = 2.f * (ul[i] + ur[i]) * (1.f - alpha) * lam[i];
+        bl[i] = gain[i] * bl[i] + xb2;
+        br[i] = gain[i] * br[i] + xb2;
+      }
+      store_chunk<SPT>(arow_w(c, nd), nd, t, bl, br);
     }
-    store_chunk<SPT>(arow_w(c, nd), nd, t, bl, br);
     float acc[4] = {dA, dT, dW, dR};
     block_sum<4>(acc, red);
     if (threadIdx.x == 0) c.partial[w.w] = make_float4(acc[0], acc[1], acc[2], acc[3]);
@@ -523,27 +582,36 @@ __global__ void k_comp_finalize(DevCtx c, int node_begin, int node_end) {
   d[0] = s.x; d[1] = s.y; d[2] = s.z; d[3] = s.w;
 }
 
-// what: 0 forward, 1 backward (items), 2 finalize (node range); gate: the noisegate
-// curve (Eq. 13) instead of the compressor's (Eq. 10-11)
-template <int SPT, bool GATE>
+// what: 0 forward, 1 backward (items), 2 finalize (node range); mode: MODE_COMP, MODE_GATE
+// (the noisegate curve of Eq. 13) or MODE_SC (the sidechain compressor)
+template <int SPT, int MODE>
 static void comp_launch(int what, const DevCtx& c, int a, int b, int ticket, cudaStream_t s) {
   constexpr int bwd_smem = 4 * 256 * SPT * sizeof(float);
   static bool init = false;
   if (!init) {
-    cudaFuncSetAttribute(k_comp_bwd<SPT, GATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem);
+    cudaFuncSetAttribute(k_comp_bwd<SPT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem);
     init = true;
   }
   if (what < 0) return;  // attributes only (before a stream capture)
   const int g = grid_size(b, what == 0 ? 8 : 3);
-  if (what == 0) k_comp_fwd<SPT, GATE><<<g, 256, 0, s>>>(c, a, b, ticket);
-  else k_comp_bwd<SPT, GATE><<<g, 256, bwd_smem, s>>>(c, a, b, ticket);
+  if (what == 0) k_comp_fwd<SPT, MODE><<<g, 256, 0, s>>>(c, a, b, ticket);
+  else k_comp_bwd<SPT, MODE><<<g, 256, bwd_smem, s>>>(c, a, b, ticket);
 }
 
-int launch_comp(int what, const DevCtx& c, int a, int b, int ticket, bool gate, cudaStream_t s) {
+template <int SPT>
+static void comp_mode(int what, const DevCtx& c, int a, int b, int ticket, int mode, cudaStream_t s) {
+  if (mode == MODE_GATE) comp_launch<SPT, MODE_GATE>(what, c, a, b, ticket, s);
+  else if (mode == MODE_SC) comp_launch<SPT, MODE_SC>(what, c, a, b, ticket, s);
+  else comp_launch<SPT, MODE_COMP>(what, c, a, b, ticket, s);
+}
+
+int launch_comp(int what, const DevCtx& c, int a, int b, int ticket, int mode, cudaStream_t s) {
   if (what < 0) {  // kernel attributes of every variant
-    comp_launch<4, false>(-1, c, 0, 0, 0, s), comp_launch<4, true>(-1, c, 0, 0, 0, s);
-    comp_launch<8, false>(-1, c, 0, 0, 0, s), comp_launch<8, true>(-1, c, 0, 0, 0, s);
-    comp_launch<16, false>(-1, c, 0, 0, 0, s), comp_launch<16, true>(-1, c, 0, 0, 0, s);
+    for (int m : {MODE_COMP, MODE_GATE, MODE_SC}) {
+      comp_mode<4>(-1, c, 0, 0, 0, m, s);
+      comp_mode<8>(-1, c, 0, 0, 0, m, s);
+      comp_mode<16>(-1, c, 0, 0, 0, m, s);
+    }
     return 0;
   }
   if (what == 2) {
@@ -552,16 +620,9 @@ int launch_comp(int what, const DevCtx& c, int a, int b, int ticket, bool gate, 
     return 1;
   }
   if (b <= 0) return 0;
-  if (c.comp_chunk == 1024) {
-    if (gate) comp_launch<4, true>(what, c, a, b, ticket, s);
-    else comp_launch<4, false>(what, c, a, b, ticket, s);
-  } else if (c.comp_chunk == 4096) {
-    if (gate) comp_launch<16, true>(what, c, a, b, ticket, s);
-    else comp_launch<16, false>(what, c, a, b, ticket, s);
-  } else {
-    if (gate) comp_launch<8, true>(what, c, a, b, ticket, s);
-    else comp_launch<8, false>(what, c, a, b, ticket, s);
-  }
+  if (c.comp_chunk == 1024) comp_mode<4>(what, c, a, b, ticket, mode, s);
+  else if (c.comp_chunk == 4096) comp_mode<16>(what, c, a, b, ticket, mode, s);
+  else comp_mode<8>(what, c, a, b, ticket, mode, s);
   return 1;
 }
 

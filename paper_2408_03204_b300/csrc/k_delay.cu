@@ -38,7 +38,7 @@ __device__ __forceinline__ const float* dl_single_row(const DevCtx& c, int v) {
   const int e0 = ADJ ? c.tcsr_ptr[v] : c.csr_ptr[v];
   const int e1 = ADJ ? c.tcsr_ptr[v + 1] : c.csr_ptr[v + 1];
   if (e1 - e0 != 1) return nullptr;
-  return ADJ ? arow(c, c.nodes[c.tcsr_dst[e0]]) : yrow(c, c.nodes[c.csr_src[e0]]);
+  return ADJ ? out_adj_row(c, e0) : in_row(c, e0);
 }
 
 // shared-memory window of one tap for a 1024-sample tile of one channel
@@ -59,10 +59,7 @@ __device__ __forceinline__ void dl_window(const DevCtx& c, int v, const NodeDev&
     const int t = start + i;
     float s = 0.f;
     if (t >= 0 && t < nd.len)
-      for (int e = e0; e < e1; ++e) {
-        const NodeDev src = c.nodes[ADJ ? c.tcsr_dst[e] : c.csr_src[e]];
-        s += (ADJ ? arow(c, src) : yrow(c, src))[ch * nd.pitch + t];
-      }
+      for (int e = e0; e < e1; ++e) s += (ADJ ? out_adj_row(c, e) : in_row(c, e))[ch * nd.pitch + t];
     win[i] = s;
   }
 }
@@ -184,8 +181,7 @@ __global__ void __launch_bounds__(DL_M / 16) k_delay_spec(DevCtx c, int item0, i
       float l = 0.f, r = 0.f;
       if (i < count && t >= 0 && t < nd.len)
         for (int e = e0; e < e1; ++e) {
-          const NodeDev src = c.nodes[adj ? c.tcsr_dst[e] : c.csr_src[e]];
-          const float* row = adj ? arow(c, src) : yrow(c, src);
+          const float* row = adj ? out_adj_row(c, e) : in_row(c, e);
           l += row[t];
           r += row[nd.pitch + t];
         }

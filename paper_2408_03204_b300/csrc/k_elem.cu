@@ -33,18 +33,16 @@ struct Ew {
 constexpr int EW_Q = EW_TILE / 1024;  // quads per thread and channel in one tile
 
 // The thread's EW_Q quads (stride 1024 samples) of both channels, summed over the
-// in-edges (ADJ = false: u, Eq. 1b) or over the consumers' input adjoints (ADJ = true).
-// All loads of an edge are issued before any is used.
+// edges [e0, e1): in-edges (ADJ = false: an input u, Eq. 1b) or consumer edges
+// (ADJ = true: the adjoint of an output).  All loads of an edge are issued before any
+// is used.
 template <bool ADJ>
-__device__ __forceinline__ void gather_q(const DevCtx& c, int v, int t, int len, int pitch, float4 (&l)[EW_Q],
-                                         float4 (&r)[EW_Q]) {
+__device__ __forceinline__ void gather_range(const DevCtx& c, int e0, int e1, int t, int len, int pitch,
+                                             float4 (&l)[EW_Q], float4 (&r)[EW_Q]) {
 #pragma unroll
   for (int q = 0; q < EW_Q; ++q) l[q] = r[q] = f4zero();
-  const int e0 = ADJ ? c.tcsr_ptr[v] : c.csr_ptr[v];
-  const int e1 = ADJ ? c.tcsr_ptr[v + 1] : c.csr_ptr[v + 1];
   for (int e = e0; e < e1; ++e) {
-    const NodeDev s = c.nodes[ADJ ? c.tcsr_dst[e] : c.csr_src[e]];
-    const float* row = ADJ ? arow(c, s) : yrow(c, s);
+    const float* row = ADJ ? out_adj_row(c, e) : in_row(c, e);
     float4 a[EW_Q], b[EW_Q];
 #pragma unroll
     for (int q = 0; q < EW_Q; ++q) {
@@ -66,6 +64,91 @@ __device__ __forceinline__ void gather_q(const DevCtx& c, int v, int t, int len,
   for (int q = 0; q < EW_Q; ++q) {
     l[q] = mask4(l[q], t + 1024 * q, len);
     r[q] = mask4(r[q], t + 1024 * q, len);
+  }
+}
+
+// Every in-edge (ADJ = false) or every consumer edge (ADJ = true) of a single-port node.
+template <bool ADJ>
+__device__ __forceinline__ void gather_q(const DevCtx& c, int v, int t, int len, int pitch, float4 (&l)[EW_Q],
+                                         float4 (&r)[EW_Q]) {
+  gather_range<ADJ>(c, ADJ ? c.tcsr_ptr[v] : c.csr_ptr[v], ADJ ? c.tcsr_ptr[v + 1] : c.csr_ptr[v + 1], t, len,
+                    pitch, l, r);
+}
+
+__device__ __forceinline__ void store_q(float* row, int pitch, int t, int len, const float4 (&l)[EW_Q],
+                                        const float4 (&r)[EW_Q]) {
+#pragma unroll
+  for (int q = 0; q < EW_Q; ++q) {
+    const int tq = t + 1024 * q;
+    if (tq < len) {
+      st4(row + tq, l[q]);
+      st4(row + pitch + tq, r[q]);
+    }
+  }
+}
+
+// Multi-port elementwise nodes (Eq. 1a with M, N > 1).  split: output 0 = (m, m),
+// output 1 = (s, s) with m = (l + r)/2, s = (l - r)/2; merge: (u0_l + u1_l, u0_r - u1_r)
+// of its inputs 0 and 1.  Backward: split's input adjoint from its two outputs'
+// adjoints, merge's two input adjoints from its output's.
+template <bool SPLIT>
+__global__ void __launch_bounds__(256, 2) k_ms_fwd(DevCtx c, int item0, int n_items) {
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int4_ w = c.items[item0 + it];
+    const int v = w.x, t = w.y + 4 * threadIdx.x;
+    const NodeDev nd = c.nodes[v];
+    float4 l[EW_Q], r[EW_Q];
+    float* y = yrow_w(c, nd);
+    if (SPLIT) {
+      gather_q<false>(c, v, t, nd.len, nd.pitch, l, r);
+#pragma unroll
+      for (int q = 0; q < EW_Q; ++q) {
+        const float4 m = f4scale(f4add(l[q], r[q]), 0.5f), s = f4scale(f4sub(l[q], r[q]), 0.5f);
+        l[q] = m;
+        r[q] = s;
+      }
+      store_q(y, nd.pitch, t, nd.len, l, l);                 // output 0: (m, m)
+      store_q(y + nd.rstride, nd.pitch, t, nd.len, r, r);    // output 1: (s, s)
+    } else {
+      float4 a[EW_Q], b[EW_Q];
+      gather_range<false>(c, c.csr_ptr[v], c.in1_begin[v], t, nd.len, nd.pitch, l, r);
+      gather_range<false>(c, c.in1_begin[v], c.csr_ptr[v + 1], t, nd.len, nd.pitch, a, b);
+#pragma unroll
+      for (int q = 0; q < EW_Q; ++q) {
+        l[q] = f4add(l[q], a[q]);
+        r[q] = f4sub(r[q], b[q]);
+      }
+      store_q(y, nd.pitch, t, nd.len, l, r);
+    }
+  }
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(256, 2) k_ms_bwd(DevCtx c, int item0, int n_items) {
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int4_ w = c.items[item0 + it];
+    const int v = w.x, t = w.y + 4 * threadIdx.x;
+    const NodeDev nd = c.nodes[v];
+    float4 l[EW_Q], r[EW_Q];
+    float* ub = arow_w(c, nd);
+    if (SPLIT) {
+      float4 a[EW_Q], b[EW_Q];
+      gather_range<true>(c, c.tcsr_ptr[v], c.out1_begin[v], t, nd.len, nd.pitch, l, r);   // output 0
+      gather_range<true>(c, c.out1_begin[v], c.tcsr_ptr[v + 1], t, nd.len, nd.pitch, a, b);   // output 1
+#pragma unroll
+      for (int q = 0; q < EW_Q; ++q) {
+        const float4 m = f4scale(f4add(l[q], r[q]), 0.5f), s = f4scale(f4add(a[q], b[q]), 0.5f);
+        l[q] = f4add(m, s);
+        r[q] = f4sub(m, s);
+      }
+      store_q(ub, nd.pitch, t, nd.len, l, r);
+    } else {
+      gather_q<true>(c, v, t, nd.len, nd.pitch, l, r);
+      store_q(ub, nd.pitch, t, nd.len, l, r);                // input 0: ybar
+#pragma unroll
+      for (int q = 0; q < EW_Q; ++q) r[q] = f4scale(r[q], -1.f);
+      store_q(ub + nd.rstride, nd.pitch, t, nd.len, l, r);   // input 1: (ybar_l, -ybar_r)
+    }
   }
 }
 
@@ -112,8 +195,8 @@ __global__ void __launch_bounds__(256, 3) k_ew_bwd(DevCtx c, int item0, int n_it
     const int ce = c.tcsr_ptr[v], pe = c.csr_ptr[v];
     if (needs_u && c.tcsr_ptr[v + 1] - ce == 1 && c.csr_ptr[v + 1] - pe == 1) {
       // one consumer and one producer (chains): issue all 4 * EW_Q loads at once
-      const float* ar = arow(c, c.nodes[c.tcsr_dst[ce]]);
-      const float* yr = yrow(c, c.nodes[c.csr_src[pe]]);
+      const float* ar = out_adj_row(c, ce);
+      const float* yr = in_row(c, pe);
 #pragma unroll
       for (int q = 0; q < EW_Q; ++q) {
         const int tq = t + 1024 * q;
@@ -217,6 +300,8 @@ int launch_ew_fwd(int type, const DevCtx& c, int item0, int n_items, cudaStream_
   switch (type) {
     case GRAFX_T_GAIN: k_ew_fwd<GRAFX_T_GAIN><<<g, 256, 0, s>>>(c, item0, n_items); break;
     case GRAFX_T_IMAGER: k_ew_fwd<GRAFX_T_IMAGER><<<g, 256, 0, s>>>(c, item0, n_items); break;
+    case GRAFX_T_SPLIT: k_ms_fwd<true><<<g, 256, 0, s>>>(c, item0, n_items); break;
+    case GRAFX_T_MERGE: k_ms_fwd<false><<<g, 256, 0, s>>>(c, item0, n_items); break;
     default: k_ew_fwd<GRAFX_T_MIX><<<g, 256, 0, s>>>(c, item0, n_items); break;
   }
   return 1;
@@ -228,6 +313,8 @@ int launch_ew_bwd(int type, const DevCtx& c, int item0, int n_items, cudaStream_
   switch (type) {
     case GRAFX_T_GAIN: k_ew_bwd<GRAFX_T_GAIN><<<g, 256, 0, s>>>(c, item0, n_items); break;
     case GRAFX_T_IMAGER: k_ew_bwd<GRAFX_T_IMAGER><<<g, 256, 0, s>>>(c, item0, n_items); break;
+    case GRAFX_T_SPLIT: k_ms_bwd<true><<<g, 256, 0, s>>>(c, item0, n_items); break;
+    case GRAFX_T_MERGE: k_ms_bwd<false><<<g, 256, 0, s>>>(c, item0, n_items); break;
     default: k_ew_bwd<GRAFX_T_MIX><<<g, 256, 0, s>>>(c, item0, n_items); break;
   }
   return 1;

@@ -115,8 +115,7 @@ __device__ __forceinline__ void eq_load_regs(const DevCtx& c, int v, const NodeD
   const int e0 = ADJ ? c.tcsr_ptr[v] : c.csr_ptr[v];
   const int e1 = ADJ ? c.tcsr_ptr[v + 1] : c.csr_ptr[v + 1];
   for (int e = e0; e < e1; ++e) {
-    const NodeDev s = c.nodes[ADJ ? c.tcsr_dst[e] : c.csr_src[e]];
-    const float* row = ADJ ? arow(c, s) : yrow(c, s);
+    const float* row = ADJ ? out_adj_row(c, e) : in_row(c, e);
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int p = threadIdx.x + T * m;

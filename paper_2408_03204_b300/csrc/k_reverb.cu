@@ -349,8 +349,7 @@ __global__ void __launch_bounds__(DL_M / 16) k_rv_inv(DevCtx c, int node_begin) 
     float dl = 0.f, dr = 0.f;
     if (dry && t < nd.len)
       for (int ed = e0; ed < e1; ++ed) {
-        const NodeDev s = c.nodes[WHAT == 0 ? c.csr_src[ed] : c.tcsr_dst[ed]];
-        const float* r = WHAT == 0 ? yrow(c, s) : arow(c, s);
+        const float* r = WHAT == 0 ? in_row(c, ed) : out_adj_row(c, ed);
         dl += r[t];
         dr += r[nd.pitch + t];
       }

@@ -5,6 +5,7 @@
 #include "fft.cuh"
 
 #include <algorithm>
+#include <array>
 #include <functional>
 #include <map>
 #include <cmath>
@@ -117,17 +118,24 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
       p->types.push_back(t);
       p->node_graph.push_back(g);
     }
-    for (auto& e : graphs[g]->edges) {
+    for (size_t i = 0; i < graphs[g]->edges.size(); ++i) {
+      const auto& e = graphs[g]->edges[i];
       int32_t n_g = int32_t(graphs[g]->types.size());
       if (e.first < 0 || e.first >= n_g || e.second < 0 || e.second >= n_g)
         return fail(GRAFX_EINVAL, "edge out of range");
       p->edges.push_back({e.first + off, e.second + off});
+      p->ports.push_back(i < graphs[g]->ports.size() ? graphs[g]->ports[i] : std::pair<int32_t, int32_t>{0, 0});
     }
   }
   const int32_t n = int32_t(p->types.size());
   const int32_t n_e = int32_t(p->edges.size());
   int rc = validate(p->types, p->edges);
   if (rc) return rc;
+  for (int32_t e = 0; e < n_e; ++e) {   // edge types t_ij = (k, l) against the node types' ports
+    const int32_t k = p->ports[e].first, l = p->ports[e].second;
+    if (k < 0 || k >= type_outputs(p->types[p->edges[e].first]) || l < 0 || l >= type_inputs(p->types[p->edges[e].second]))
+      return fail(GRAFX_EINVAL, "edge port out of range for its node types");
+  }
   for (int32_t v = 0; v < n; ++v) {
     if ((p->types[v] == GRAFX_T_DELAY || p->types[v] == GRAFX_T_REVERB) &&
         p->L[p->node_graph[v]] > int64_t(DL_MAX_BLOCKS) * DL_B)
@@ -166,7 +174,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     c[GRAFX_T_GAIN] = 2;
     c[GRAFX_T_IMAGER] = 1;
     c[GRAFX_T_EQ] = p->eq_logmag ? (opts.eq_taps + 1) / 2 : 8;
-    c[GRAFX_T_COMP] = c[GRAFX_T_GATE] = 4;
+    c[GRAFX_T_COMP] = c[GRAFX_T_GATE] = c[GRAFX_T_SIDECHAIN] = 4;
     c[GRAFX_T_DELAY] = 2 * p->dl_taps * DL_ROW;
     c[GRAFX_T_REVERB] = p->rv_paper ? 4 * (p->rv_n / 2) : RV_COLS;
   }
@@ -204,13 +212,17 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
       p->param_row[v] = R > 0 ? p->grad_row[v] % R : 0;
     }
   }
-  // ---- in-edge CSR by (dst, src) = I^G / I^A; consumer CSR by (src, dst) for backward
+  // ---- in-edge CSR by (dst, input port, src, output port) = I^G / I^A; consumer CSR by
+  // (src, output port, dst, input port) for backward.  Each node's in-edges are grouped
+  // by input port, its consumer edges by output port (in1_begin / out1_begin split them).
+  std::vector<int32_t> csr_k(n_e), tcsr_l(n_e);   // the other end's port of each entry
   {
-    std::vector<std::pair<int32_t, int32_t>> ed(n_e), te(n_e);
+    std::vector<std::array<int32_t, 4>> ed(n_e), te(n_e);
     for (int32_t e = 0; e < n_e; ++e) {
       int32_t s = p->sigma[p->edges[e].first], d = p->sigma[p->edges[e].second];
-      ed[e] = {d, s};
-      te[e] = {s, d};
+      const int32_t k = p->ports[e].first, l = p->ports[e].second;
+      ed[e] = {d, l, s, k};
+      te[e] = {s, k, d, l};
     }
     std::sort(ed.begin(), ed.end());
     std::sort(te.begin(), te.end());
@@ -219,14 +231,26 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     p->csr_src.resize(n_e);
     p->tcsr_dst.resize(n_e);
     for (int32_t e = 0; e < n_e; ++e) {
-      ++p->csr_ptr[ed[e].first + 1];
-      p->csr_src[e] = ed[e].second;
-      ++p->tcsr_ptr[te[e].first + 1];
-      p->tcsr_dst[e] = te[e].second;
+      ++p->csr_ptr[ed[e][0] + 1];
+      p->csr_src[e] = ed[e][2];
+      csr_k[e] = ed[e][3];
+      ++p->tcsr_ptr[te[e][0] + 1];
+      p->tcsr_dst[e] = te[e][2];
+      tcsr_l[e] = te[e][3];
     }
     for (int32_t v = 0; v < n; ++v) {
       p->csr_ptr[v + 1] += p->csr_ptr[v];
       p->tcsr_ptr[v + 1] += p->tcsr_ptr[v];
+    }
+    p->in1_begin.assign(n, 0);
+    p->out1_begin.assign(n, 0);
+    for (int32_t v = 0; v < n; ++v) {
+      int32_t e = p->csr_ptr[v];
+      while (e < p->csr_ptr[v + 1] && ed[e][1] < 1) ++e;
+      p->in1_begin[v] = e;
+      e = p->tcsr_ptr[v];
+      while (e < p->tcsr_ptr[v + 1] && te[e][1] < 1) ++e;
+      p->out1_begin[v] = e;
     }
   }
   // ---- row placement: inputs read the caller's sources, outputs write the caller's
@@ -260,16 +284,18 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     } else {
       nd.kind = KIND_INTERNAL;
       nd.off_y = nd.off_a = int_off;
-      int_off += int64_t(align_up(size_t(row), 64));
+      nd.rstride = int32_t(align_up(size_t(row), 64));
+      int_off += int64_t(type_outputs(nd.type)) * nd.rstride;   // one row per output port
       p->node_samples += nd.len;
     }
+    if (nd.kind != KIND_INTERNAL) nd.rstride = int32_t(row);
     if (nd.type == GRAFX_T_OUT) p->node_samples += nd.len;
   }
   // inputs and outputs are ordered graph-major because sigma keeps original order
   // inside a step and the union concatenates graphs in order
   p->src_elems = src_off;
   p->out_elems = out_off;
-  const int64_t internal_floats = int_off;  // adjoint rows: one per internal node
+  const int64_t internal_floats = int_off;  // U rows: one per output port of each internal node
   // ---- signal checkpointing: with segments of opts.checkpoint_steps schedule steps,
   // a U row is kept for the whole pass only if a consumer lies in a later segment
   // (its forward value is needed when a later segment is recomputed or run); all other
@@ -290,7 +316,8 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
       if (p->nodes[v].kind != KIND_INTERNAL) continue;
       int32_t lo = step_of[v];
       for (int32_t e = p->csr_ptr[v]; e < p->csr_ptr[v + 1]; ++e) lo = std::min(lo, step_of[p->csr_src[e]]);
-      lives.push_back({N - step_of[v], N - lo, v, int64_t(align_up(size_t(2 * p->nodes[v].pitch), 64))});
+      // one adjoint row per input port
+      lives.push_back({N - step_of[v], N - lo, v, int64_t(type_inputs(p->nodes[v].type)) * p->nodes[v].rstride});
     }
     std::stable_sort(lives.begin(), lives.end(), [](const Live& a, const Live& b) { return a.start < b.start; });
     struct Pool { std::vector<int64_t> free_slots; std::vector<std::pair<int32_t, int64_t>> busy; };
@@ -340,7 +367,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     for (int32_t v = 0; v < n; ++v)
       if (keep[v]) {
         p->nodes[v].off_y = kept;
-        kept += int64_t(align_up(size_t(2 * p->nodes[v].pitch), 64));
+        kept += int64_t(type_outputs(p->nodes[v].type)) * p->nodes[v].rstride;
       }
     int64_t scratch = 0, cur = 0;
     int32_t cur_seg = -1;
@@ -348,10 +375,20 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
       if (p->nodes[v].kind != KIND_INTERNAL || keep[v]) continue;
       if (seg_of_node[v] != cur_seg) cur_seg = seg_of_node[v], cur = 0;
       p->nodes[v].off_y = kept + cur;
-      cur += int64_t(align_up(size_t(2 * p->nodes[v].pitch), 64));
+      cur += int64_t(type_outputs(p->nodes[v].type)) * p->nodes[v].rstride;
       scratch = std::max(scratch, cur);
     }
     u_floats = kept + scratch;
+  }
+  // ---- row references of the CSR entries (the rows are placed now): the source's output
+  // port row for every in-edge, the consumer's input-port adjoint row for every consumer edge
+  p->csr_row.resize(n_e);
+  p->tcsr_row.resize(n_e);
+  for (int32_t e = 0; e < n_e; ++e) {
+    const NodeDev& s = p->nodes[p->csr_src[e]];
+    p->csr_row[e] = (int64_t(s.kind) << REF_SHIFT) | (s.off_y + int64_t(csr_k[e]) * s.rstride);
+    const NodeDev& w = p->nodes[p->tcsr_dst[e]];
+    p->tcsr_row[e] = (int64_t(w.kind) << REF_SHIFT) | (w.off_a + int64_t(tcsr_l[e]) * w.rstride);
   }
 
   // ---- tile sizes
@@ -405,7 +442,8 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
           break;
         }
         case GRAFX_T_COMP:
-        case GRAFX_T_GATE: {
+        case GRAFX_T_GATE:
+        case GRAFX_T_SIDECHAIN: {
           int32_t nc = (L + p->comp_chunk - 1) / p->comp_chunk;
           p->node_ext[v].z = chunk_id;
           for (int32_t c = 0; c < nc; ++c) fwd.push_back({v, c, chunk_id + c, 0});
@@ -475,7 +513,8 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
           break;
         }
         case GRAFX_T_COMP:
-        case GRAFX_T_GATE: {
+        case GRAFX_T_GATE:
+        case GRAFX_T_SIDECHAIN: {
           int32_t nc = (L + p->comp_chunk - 1) / p->comp_chunk;
           p->node_ext[v].x = slot;
           p->node_ext[v].y = nc;
@@ -607,6 +646,10 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     w.tcsr_ptr = take(4 * size_t(n + 1));
     w.tcsr_dst = take(4 * size_t(std::max(n_e, 1)));
     w.items = take(sizeof(int4_) * std::max<size_t>(p->items.size(), 1));
+    w.csr_row = take(8 * size_t(std::max(n_e, 1)));
+    w.tcsr_row = take(8 * size_t(std::max(n_e, 1)));
+    w.in1_begin = take(4 * size_t(n));
+    w.out1_begin = take(4 * size_t(n));
     w.twiddle = take(sizeof(float2_) * TWIDDLE_N);
     w.ptw = take(sizeof(float2_) * fft::PTW_TOTAL);
     w.eq_cos = take(4 * p->eq_cos.size());

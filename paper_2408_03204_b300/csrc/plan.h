@@ -12,9 +12,16 @@
 struct grafx_graph {
   std::vector<int32_t> types;
   std::vector<std::pair<int32_t, int32_t>> edges;
+  std::vector<std::pair<int32_t, int32_t>> ports;   // per edge: (output of src, input of dst)
 };
 
 namespace grafx {
+
+// Inputs M and outputs N of a node type (Eq. 1a).
+inline int type_inputs(int t) {
+  return t == GRAFX_T_IN ? 0 : (t == GRAFX_T_MERGE || t == GRAFX_T_SIDECHAIN) ? 2 : 1;
+}
+inline int type_outputs(int t) { return t == GRAFX_T_SPLIT ? 2 : 1; }
 
 // status helpers (thread-local last error)
 int fail(int code, const std::string& msg);
@@ -43,6 +50,7 @@ struct StepInfo {
 // Byte offsets of the regions inside the caller's workspace.
 struct WsLayout {
   size_t nodes, node_ext, csr_ptr, csr_src, tcsr_ptr, tcsr_dst, items;
+  size_t csr_row, tcsr_row, in1_begin, out1_begin;
   size_t twiddle, ptw, eq_cos, eq_hann, eq_band, rv_win, rv_cs;
   size_t loss_rows, loss_items;
   size_t tables_end;                           // [0, tables_end) is uploaded at bind time
@@ -73,6 +81,13 @@ struct Plan {
   std::vector<int64_t> L, pitch;         // per graph
   std::vector<int32_t> types;            // union, original ids
   std::vector<std::pair<int32_t, int32_t>> edges;
+  std::vector<std::pair<int32_t, int32_t>> ports;   // per edge (output k of src, input l of dst)
+  // per new id: first in-edge of input 1 and first consumer edge of output 1 (the ends
+  // of the nodes' edge ranges when they have a single input / output)
+  std::vector<int32_t> in1_begin, out1_begin;
+  // per edge in CSR order: the source's output row; per edge in consumer-CSR order: the
+  // consumer's input-adjoint row (row references: NodeKind << 60 | float offset)
+  std::vector<int64_t> csr_row, tcsr_row;
   std::vector<int32_t> node_graph;       // original id -> graph
   Schedule sched;
   std::vector<int32_t> step_ptr, sigma, csr_ptr, csr_src, tcsr_ptr, tcsr_dst, param_row;

@@ -88,7 +88,7 @@ class GpuRun:
         import paper_2408_03204_b300 as gx
         self.gx, self.torch = gx, torch
         self.graphs, self.lengths = graphs, lengths
-        self.plan = gx.Plan([gx.Graph.from_lists(g.types, g.edges) for g in graphs], lengths, **plan_kw)
+        self.plan = gx.Plan([gx.Graph.from_lists(g.types, g.edges, g.ports) for g in graphs], lengths, **plan_kw)
         self.plan.bind_workspace("cuda")
         self.P = {t: torch.tensor(v, dtype=torch.float32, device="cuda").contiguous() for t, v in P.items()}
         self.src = torch.tensor(src_flat, dtype=torch.float32, device="cuda")

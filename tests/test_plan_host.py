@@ -127,7 +127,7 @@ def test_paper_layout_widths_and_bad_layouts(gx):
     assert p.param_cols[8] == gold["reverb_params"] and p.param_cols[3] == gold["gain_params"]
     assert p.param_cols[4] == gold["imager_params"] and p.param_cols[6] == gold["compressor_params"]
     c = gx.Plan([g], [8192])
-    assert c.param_cols == {3: 2, 4: 1, 5: 8, 6: 4, 7: 176, 8: 50, 9: 4}
+    assert c.param_cols == {3: 2, 4: 1, 5: 8, 6: 4, 7: 176, 8: 50, 9: 4, 12: 4}
     # one setting of the preset overridden: band EQ on the paper's other layouts
     m = gx.Plan([g], [8192], preset="paper", eq_params="bands")
     assert m.param_cols[5] == 8 and m.param_cols[7] == 880
@@ -168,6 +168,28 @@ def test_source_batch_rows(gx):
             assert e3["param_row"][e3["sigma"][b * n + v]] == e1["param_row"][e1["sigma"][v]]
     with pytest.raises(gx.GrafxError):
         gx.Plan([h], [4096], source_batch=-2)
+
+
+def test_type_ports_and_port_checks(gx):
+    """Eq. 1a: the port counts of every type; an edge must leave an existing output and
+    enter an existing input (checked when connecting and when planning)."""
+    want = {0: (0, 1), 1: (1, 1), 10: (1, 2), 11: (2, 1), 12: (2, 1)}
+    for t in range(gx.N_TYPES):
+        assert gx.type_ports(t) == want.get(t, (1, 1))
+    with pytest.raises(gx.GrafxError):
+        gx.type_ports(13)
+    g = gx.Graph()
+    i, sp, mg, o = g.add(0), g.add(10), g.add(11), g.add(1)
+    g.connect(i, sp)
+    g.connect(sp, mg, 0, 0)
+    g.connect(sp, mg, 1, 1)
+    g.connect(mg, o)
+    for bad in ((sp, mg, 2, 0), (sp, mg, 0, 2), (i, sp, 1, 0), (mg, o, 0, 1)):
+        with pytest.raises(gx.GrafxError) as e:
+            g.connect(*bad)
+        assert e.value.name == "EINVAL"
+    p = gx.Plan([g], [4096])
+    assert p.info.n_steps >= 3
 
 
 def test_optimal_size_limit(gx):
