@@ -7,7 +7,9 @@ Cases (2^17 stereo samples unless --length):
   * delay bank: 64 independent i -> d -> o chains, 4 taps anywhere in 32768 samples
     (compact) or 20 taps per channel in 100 ms slots (paper);
   * reverb bank: 64 independent i -> r -> o chains, STFT 1024/256 with 12 bands and
-    dry/wet (compact) or 384/192 with 192 log-magnitudes per filter, wet only (paper).
+    dry/wet (compact) or 384/192 with 192 log-magnitudes per filter, wet only (paper);
+  * multi-port nodes: a mid/side console (64 tracks split -> gain on mid and on side ->
+    merge, mixed) and a bank of 64 sidechain compressors keyed by a second source.
 
     python -m paper_2408_03204_b300.presets --reps 10
 """
@@ -32,10 +34,49 @@ def bank(t, n=64):
     return g
 
 
+def mid_side_console(n=64):
+    """n tracks i -> split -> (mid: gain, side: gain) -> merge, all merged into one output."""
+    import synth
+    g = synth.Graph()
+    mix = None
+    outs = []
+    for _ in range(n):
+        i = g.add(synth.I)
+        sp = g.add(synth.P)
+        gm, gs = g.add(synth.G), g.add(synth.G)
+        mg = g.add(synth.J)
+        g.connect(i, sp)
+        g.connect(sp, gm, 0, 0)
+        g.connect(sp, gs, 1, 0)
+        g.connect(gm, mg, 0, 0)
+        g.connect(gs, mg, 0, 1)
+        outs.append(mg)
+    mix = g.add(synth.M)
+    for v in outs:
+        g.connect(v, mix)
+    o = g.add(synth.O)
+    g.connect(mix, o)
+    return g
+
+
+def sidechain_bank(n=64):
+    """n chains main input -> sidechain compressor -> output, keyed by their own second input."""
+    import synth
+    g = synth.Graph()
+    for _ in range(n):
+        i, key = g.add(synth.I), g.add(synth.I)
+        k = g.add(synth.K)
+        o = g.add(synth.O)
+        g.connect(i, k, 0, 0)
+        g.connect(key, k, 0, 1)
+        g.connect(k, o)
+    return g
+
+
 def time_case(g, L, preset, reps, torch):
     """(ms per render + backprop, processed node-samples per step, workspace GB)."""
     import synth
-    plan = Plan([Graph.from_lists(g.types, g.edges)], [L], preset=preset)
+    plan = Plan([Graph.from_lists(g.types, g.edges, g.ports)], [L], preset=preset)
     plan.bind_workspace("cuda")
     P = {t: torch.tensor(v, device="cuda").contiguous() for t, v in synth.random_params(g, 7, preset=preset).items()}
     plan.bind_params(P)
@@ -68,12 +109,14 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--length", type=int, default=2 ** 17)
     ap.add_argument("--reps", type=int, default=10)
-    ap.add_argument("--case", choices=["console", "delay", "reverb"], default=None, help="one case only")
+    ap.add_argument("--case", choices=["console", "delay", "reverb", "mid", "sidechain"], default=None,
+                    help="one case only")
     ap.add_argument("--preset", choices=["compact", "paper"], default=None, help="one preset only")
     args = ap.parse_args()
     import torch
     import synth
-    cases = {"console": synth.console_cfg2(), "delay bank": bank(synth.D), "reverb bank": bank(synth.R)}
+    cases = {"console": synth.console_cfg2(), "delay bank": bank(synth.D), "reverb bank": bank(synth.R),
+             "mid/side console": mid_side_console(), "sidechain bank": sidechain_bank()}
     rows = []
     for name, g in cases.items():
         if args.case and not name.startswith(args.case):
@@ -81,6 +124,8 @@ def main():
         for preset in ("compact", "paper"):
             if args.preset and preset != args.preset:
                 continue
+            if name in ("mid/side console", "sidechain bank") and preset == "paper":
+                continue   # no processor with a paper layout in these graphs
             ms, ns, ws = time_case(g, args.length, preset, args.reps, torch)
             rows.append({"case": name, "preset": preset, "ms_fwd_bwd": ms, "node_samples_per_s": ns / (ms / 1e3),
                          "workspace_gb": ws})
