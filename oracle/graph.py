@@ -30,7 +30,7 @@ Readings of what the paper leaves open:
 import heapq
 
 I_TYPE, O_TYPE = 0, 1
-N_TYPES = 13
+N_TYPES = 14
 
 # (inputs M, outputs N) of every type (Eq. 1a): the sources have no input; split gives
 # two outputs (mid, side); merge and the sidechain compressor take two inputs (merge:

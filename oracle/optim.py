@@ -79,6 +79,8 @@ def param_codes(t, cols):
     codes = np.full(cols, IDENT, dtype=np.int8)
     if t in (6, 9, 12):              # compressor / noisegate / sidechain [alpha, T, W, R]
         codes[:] = [ALPHA, IDENT, SOFTPLUS, RATIO]
+    if t == 13:                      # attack/release compressor [alpha_a, alpha_r, T, W, R]
+        codes[:] = [ALPHA, ALPHA, IDENT, SOFTPLUS, RATIO]
     if t == 8 and cols == 50:        # reverb (12 bands): H_delta columns are decays
         c = np.full(50, IDENT, dtype=np.int8)
         c[:48] = np.tile(np.repeat([IDENT, NEGSP], 12), 2)

@@ -300,6 +300,63 @@ def compressor_bwd(u, p, ybar, eps=COMP_EPS, curve=knee, key=None):
     return k[None, :] * ybar, srcbar, pbar
 
 
+# ---------------------------------------------------------------- attack/release ballistics (Sec. 3, Eq. 8)
+# Eq. 8 with the coefficient the paper describes before restricting it: alpha[n] is the
+# attack constant while the envelope rises (x[n] > g[n-1]) and the release constant while
+# it falls, g[n] = alpha[n] g[n-1] + (1 - alpha[n]) x[n], g[-1] = 0.  The rest is the
+# compressor of Eq. 9-12.  Parameter row [alpha_attack, alpha_release, T, W, R].  The
+# branch is a comparison, so the derivative treats it as fixed (ties have measure zero).
+def envelope_ar(x, aa, ar):
+    """(g, attack mask) of the attack/release recursion, run sample by sample."""
+    x = _f64(x)
+    g = np.empty_like(x)
+    att = np.empty(x.shape[0], dtype=bool)
+    prev = 0.0
+    for n in range(x.shape[0]):
+        att[n] = x[n] > prev
+        a = aa if att[n] else ar
+        prev = a * prev + (1.0 - a) * x[n]
+        g[n] = prev
+    return g, att
+
+
+def ballistic_fwd(u, p, eps=COMP_EPS):
+    u = _f64(u)
+    aa, ar, T, W, R = (float(v) for v in _f64(p))
+    um = u[0] + u[1]
+    g, _ = envelope_ar(um * um, aa, ar)
+    Gu = np.log(g + eps)
+    Gy = knee(Gu, T, W, R)[0]
+    return np.exp(Gy - Gu)[None, :] * u
+
+
+def ballistic_bwd(u, p, ybar, eps=COMP_EPS):
+    u, ybar = _f64(u), _f64(ybar)
+    aa, ar, T, W, R = (float(v) for v in _f64(p))
+    um = u[0] + u[1]
+    x = um * um
+    g, att = envelope_ar(x, aa, ar)
+    alpha = np.where(att, aa, ar)
+    Gu = np.log(g + eps)
+    Gy, dGu, dT, dW, dR = knee(Gu, T, W, R)
+    k = np.exp(Gy - Gu)
+    Gybar = np.sum(ybar * u, axis=0) * k
+    gbar = Gybar * (dGu - 1.0) / (g + eps)
+    # lambda[n] = gbar[n] + alpha[n+1] lambda[n+1] (the coefficient of step n+1)
+    lam = np.empty_like(gbar)
+    acc = 0.0
+    for n in range(gbar.shape[0] - 1, -1, -1):
+        acc = gbar[n] + (alpha[n + 1] * acc if n + 1 < gbar.shape[0] else 0.0)
+        lam[n] = acc
+    xbar = (1.0 - alpha) * lam
+    ubar = k[None, :] * ybar + (2.0 * um * xbar)[None, :]
+    gprev = np.concatenate([[0.0], g[:-1]])
+    da = lam * (gprev - x)
+    pbar = np.array([np.sum(da[att]), np.sum(da[~att]), np.sum(Gybar * dT), np.sum(Gybar * dW),
+                     np.sum(Gybar * dR)])
+    return ubar, pbar
+
+
 # ---------------------------------------------------------------- MIMO processors (Sec. 2 Definitions, Eq. 1a/1b)
 # The paper's nodes take M inputs and give N outputs, each edge carrying its (output,
 # input) port pair.  Its Sec. 3 processors are all single-input single-output; these

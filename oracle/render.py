@@ -23,7 +23,7 @@ import numpy as np
 from . import graph as og
 from . import processors as op
 
-I_, O_, M_, G_, S_, E_, C_, D_, R_, N_, P_, J_, K_ = range(13)
+I_, O_, M_, G_, S_, E_, C_, D_, R_, N_, P_, J_, K_, A_ = range(14)
 
 DEFAULT_HP = dict(eq_taps=1023, fs=44100, comp_eps=op.COMP_EPS, eq_params="bands")
 
@@ -67,6 +67,8 @@ def process(t, u, p, hp):
         return op.compressor_fwd(u, p, hp["comp_eps"])
     if t == N_:
         return op.noisegate_fwd(u, p, hp["comp_eps"])
+    if t == A_:
+        return op.ballistic_fwd(u, p, hp["comp_eps"])
     if t == D_:
         return op.delay_fwd(u, p, **_delay_args(hp))
     if t == R_:
@@ -89,6 +91,8 @@ def process_bwd(t, u, p, ybar, hp):
         return op.compressor_bwd(u, p, ybar, hp["comp_eps"])
     if t == N_:
         return op.noisegate_bwd(u, p, ybar, hp["comp_eps"])
+    if t == A_:
+        return op.ballistic_bwd(u, p, ybar, hp["comp_eps"])
     if t == D_:
         return op.delay_bwd(u, p, ybar, **_delay_args(hp))
     if t == R_:

@@ -7,9 +7,9 @@ random physical parameters and random source audio from numpy PCG64 streams, so
 that both sides receive bit-identical FP32 inputs.
 
 Node type ids are fixed data (the paper's type letters, Sec. 2, Fig. 1 and 2b):
-``i=0 o=1 m=2 g=3 s=4 e=5 c=6 d=7 r=8 n=9 p=10 j=11 k=12``.
+``i=0 o=1 m=2 g=3 s=4 e=5 c=6 d=7 r=8 n=9 p=10 j=11 k=12 a=13``.
 """
-from .types import TYPE_IDS, TYPE_LETTERS, I, O, M, G, S, E, C, D, R, N, P, J, K, PARAM_COLS, PAPER_PARAM_COLS, param_cols  # noqa: F401
+from .types import TYPE_IDS, TYPE_LETTERS, I, O, M, G, S, E, C, D, R, N, P, J, K, A, PARAM_COLS, PAPER_PARAM_COLS, param_cols  # noqa: F401
 from .graphs import Graph, console_cfg1, console_cfg2, random_console, batch_cfg3, console_all_types  # noqa: F401
 from .signals import sources, reverb_noise  # noqa: F401
 from .params import random_params, neutral_params  # noqa: F401

@@ -23,7 +23,7 @@ The paper's own settings (preset "paper", widths in ``types.PAPER_PARAM_COLS``):
 """
 import numpy as np
 
-from .types import G, S, E, C, D, R, N, K, PARAM_COLS, param_cols
+from .types import G, S, E, C, D, R, N, K, A, PARAM_COLS, param_cols
 
 LN10 = np.log(10.0)
 DELAY_FFT = 32768
@@ -53,6 +53,15 @@ def _rows(rng, t, n, fs=44100):
     if t == K:
         # sidechain compressor: the compressor's distributions
         return _rows(rng, C, n, fs)
+    if t == A:
+        # attack/release: a fast attack U(0.5, 0.99), a slow release U(0.999, 0.9999), the
+        # compressor's T, W, R
+        q = _rows(rng, C, n, fs)
+        p = np.empty((n, 5))
+        p[:, 0] = rng.uniform(0.5, 0.99, n)
+        p[:, 1] = rng.uniform(0.999, 0.9999, n)
+        p[:, 2:] = q[:, 1:]
+        return p
     if t == N:
         # noisegate: threshold -60..-30 dB, expansion ratio 1..4, W = 3 dB
         p = np.empty((n, 4))
@@ -138,6 +147,8 @@ def neutral_params(graph, preset="compact"):
         if cols[t] == 0:
             continue
         p = np.zeros((n, cols[t]))
+        if t == A:
+            p[:, 0], p[:, 1], p[:, 3], p[:, 4] = 0.9, 0.999, 3.0 * LN10 / 10.0, 1.0
         if t in (C, N, K):
             p[:, 0] = 0.99
             p[:, 2] = 3.0 * LN10 / 10.0

@@ -16,16 +16,17 @@ Parameter widths N_t (the columns of P[t], Sec. 2 "Graph representations"):
   p: 0   split (1 input, 2 outputs: mid, side)
   j: 0   merge (2 inputs: mid, side; 1 output)
   k: 4   sidechain compressor (2 inputs: main, key) [alpha, T, W, R] as the compressor
+  a: 5   compressor with attack/release ballistics [alpha_attack, alpha_release, T, W, R]
 
 Widths of the paper's own processor settings (Sec. 3), ``PAPER_PARAM_COLS``:
   e: 1024 ln-magnitudes of the 2047-tap zero-phase FIR
   d: 880  2 channels x 20 taps (one per 100 ms slot) x [Re z, Im z, 20 ln-magnitudes]
   r: 768  [mid, side] x [H0, H_delta] x 192 ln-magnitudes (STFT 384 / hop 192)
 """
-I, O, M, G, S, E, C, D, R, N, P, J, K = range(13)
-TYPE_LETTERS = "iomgsecdrnpjk"
+I, O, M, G, S, E, C, D, R, N, P, J, K, A = range(14)
+TYPE_LETTERS = "iomgsecdrnpjka"
 TYPE_IDS = {ch: k for k, ch in enumerate(TYPE_LETTERS)}
-PARAM_COLS = {I: 0, O: 0, M: 0, G: 2, S: 1, E: 8, C: 4, D: 176, R: 50, N: 4, P: 0, J: 0, K: 4}
+PARAM_COLS = {I: 0, O: 0, M: 0, G: 2, S: 1, E: 8, C: 4, D: 176, R: 50, N: 4, P: 0, J: 0, K: 4, A: 5}
 PAPER_PARAM_COLS = dict(PARAM_COLS)
 PAPER_PARAM_COLS.update({E: 1024, D: 880, R: 768})
 
