@@ -26,7 +26,7 @@
  *    pitch = grafx_pitch(L) = L rounded up to a multiple of 4.  Samples at and past
  *    L inside a row are padding: ignored on input, written as 0 on output.
  *  - Node type ids: see GRAFX_T_*.  Parameter widths per type (columns of P[t]):
- *    gain 2, imager 1, compressor 4, noisegate 4, sidechain 4, split and merge none;
+ *    gain 2, imager 1, compressor 4, noisegate 4, sidechain 4, ballistic 5, split and merge none;
  *    eq 8, delay 176, reverb 50 in the
  *    compact layouts, eq (eq_taps+1)/2, delay 880, reverb 768 in the paper's
  *    (grafx_plan_opts, grafx_plan_info.param_cols, grafx_bind_params).
@@ -67,7 +67,10 @@ enum {
    *        of Eq. 8-12 with 2 inputs (0 = main, 1 = key): the envelope follows the key,
    *        the gain applies to the main input. */
   GRAFX_T_SPLIT = 10, GRAFX_T_MERGE = 11, GRAFX_T_SIDECHAIN = 12,
-  GRAFX_N_TYPES = 13
+  /* the compressor with attack/release ballistics (Eq. 8 with alpha[n] = alpha_attack while
+   * the envelope rises, alpha_release while it falls; the recursion is sample-serial) */
+  GRAFX_T_BALLISTIC = 13,
+  GRAFX_N_TYPES = 14
 };
 
 /* Inputs M and outputs N of a node type (GRAFX_EINVAL for an unknown type): sources
@@ -230,7 +233,9 @@ int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* s
  * y = e^{q_dry} u + e^{q_wet} (h * u) with the 88200-tap IR h of Eq. 6-7;
  * noisegate [alpha, T, W, R] like the compressor, with the gate curve of Eq. 13
  * (unchanged above T + W, expansion by R below T - W, a quadratic knee between);
- * sidechain [alpha, T, W, R] as the compressor, the envelope taken from input 1.
+ * sidechain [alpha, T, W, R] as the compressor, the envelope taken from input 1;
+ * ballistic [alpha_attack, alpha_release, T, W, R]: the compressor with the coefficient
+ * of Eq. 8 switched per sample by whether the envelope rises (x[n] > g[n-1]).
  * Paper layouts: eq (eq_taps+1)/2 = the log-magnitudes p_e[k] of Eq. 4 (GRAFX_EQ_LOGMAG);
  * delay 880 = [channel][tap 0..19][Re z, Im z, 20 log-magnitudes], tap m delayed by
  * m S + (round(S (-arg z)/2pi) mod S), S = sample_rate/10, the surrogate of Eq. 15 of

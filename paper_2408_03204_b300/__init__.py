@@ -19,8 +19,10 @@ LIB_PATH = os.path.join(HERE, "libgrafx.so")
 
 T_IN, T_OUT, T_MIX, T_GAIN, T_IMAGER, T_EQ, T_COMP, T_DELAY, T_REVERB, T_GATE = range(10)
 T_SPLIT, T_MERGE, T_SIDECHAIN = 10, 11, 12   # multi-port processors (inputs x outputs: 1x2, 2x1, 2x1)
-N_TYPES = 13
-PARAM_COLS = {T_GAIN: 2, T_IMAGER: 1, T_EQ: 8, T_COMP: 4, T_DELAY: 176, T_REVERB: 50, T_GATE: 4, T_SIDECHAIN: 4}
+T_BALLISTIC = 13                              # compressor with attack/release ballistics
+N_TYPES = 14
+PARAM_COLS = {T_GAIN: 2, T_IMAGER: 1, T_EQ: 8, T_COMP: 4, T_DELAY: 176, T_REVERB: 50, T_GATE: 4, T_SIDECHAIN: 4,
+              T_BALLISTIC: 5}
 # processor layouts (grafx_plan_opts): "compact" (the widths above) or "paper" (Sec. 3)
 EQ_PARAMS = {"bands": 0, "logmag": 1}
 DELAY_LAYOUT = {"compact": 0, "slots": 1}

@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgrafx.so")
-SOURCES = ["capi.cu", "k_elem.cu", "k_eq.cu", "k_comp.cu", "k_loss.cu", "k_optim.cu", "k_delay.cu", "k_reverb.cu", "k_warm.cu", "plan.cpp", "schedule.cpp"]
+SOURCES = ["capi.cu", "k_elem.cu", "k_eq.cu", "k_comp.cu", "k_loss.cu", "k_optim.cu", "k_delay.cu", "k_reverb.cu", "k_warm.cu", "k_bal.cu", "plan.cpp", "schedule.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -73,6 +73,7 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
   c.rv_r = at<float>(p, p->ws.rv_r);
   c.rv_mm = at<float2>(p, p->ws.rv_mm);
   c.rv_nbmax = p->rv_nbmax;
+  c.bal = at<float>(p, p->ws.bal);
   c.partial = at<float4>(p, p->ws.partial);
   c.eq_partial = at<float2>(p, p->ws.eq_partial);
   c.ybase[KIND_INPUT] = const_cast<float*>(src);
@@ -104,7 +105,7 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
 int check_ready(const Plan* p) {
   if (!p->dev_ws) return fail(GRAFX_ESTATE, "workspace not bound (grafx_plan_bind_workspace)");
   for (int t : {GRAFX_T_GAIN, GRAFX_T_IMAGER, GRAFX_T_EQ, GRAFX_T_COMP, GRAFX_T_DELAY, GRAFX_T_REVERB, GRAFX_T_GATE,
-                GRAFX_T_SIDECHAIN})
+                GRAFX_T_SIDECHAIN, GRAFX_T_BALLISTIC})
     if (p->n_type_rows[t] > 0 && !p->params[t])
       return fail(GRAFX_ESTATE, "parameters of type " + std::to_string(t) + " not bound");
   if (p->n_type_rows[GRAFX_T_REVERB] > 0 && !p->rv_noise)
@@ -446,6 +447,9 @@ static int render_range(grafx_plan* p, const float* sources, float* out, int32_t
       case GRAFX_T_EQ:
         launches += launch_eq(1, c, st.fitem_begin, st.fitem_count, s);
         break;
+      case GRAFX_T_BALLISTIC:
+        launches += launch_bal_fwd(c, st.fitem_begin, st.fitem_count, st.node_begin, st.node_end, s);
+        break;
       case GRAFX_T_COMP:
       case GRAFX_T_GATE:
       case GRAFX_T_SIDECHAIN:
@@ -607,6 +611,13 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
       case GRAFX_T_SPLIT:
       case GRAFX_T_MERGE:
         launches += launch_ew_bwd(st.type, c, st.bitem_begin, st.bitem_count, s);
+        break;
+      case GRAFX_T_BALLISTIC:
+        launches += launch_bal_bwd(c, st.bitem_begin, st.bitem_count, st.node_begin, st.node_end, s);
+        if (c.dparams) {
+          to_side(k);
+          launches += launch_bal_finalize(c, st.node_begin, st.node_end, side);
+        }
         break;
       default:
         launches += launch_ew_bwd(GRAFX_T_MIX, c, st.bitem_begin, st.bitem_count, s);

@@ -53,6 +53,7 @@ struct DevCtx {
   float* rv_r;            // per reverb node: lags [2][RV_HLEN]
   float2* rv_mm;          // per reverb node: mask-gradient terms [rv_f][2][rv_n/2+1]
   int32_t rv_nbmax;
+  float* bal;            // per ballistic node: mid, envelope, envelope-adjoint and coefficient rows
   float4* partial;
   float2* eq_partial;
   float* ybase[3];

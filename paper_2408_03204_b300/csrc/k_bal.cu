@@ -1,0 +1,370 @@
+// Compressor with attack/release ballistics (Sec. 3, Eq. 8 with alpha[n] = alpha_attack
+// while the envelope rises, x[n] > g[n-1], and alpha_release while it falls; Eq. 9-12 for
+// the rest).  The coefficient depends on the state, so the recursion has no associative
+// form to scan: it runs sample by sample, one warp per node (lane 0 runs the recursion on
+// a 512-sample block in shared memory while the warp's loads of the next block are in
+// flight).  Everything else is per sample and runs as tiles over all nodes:
+//   forward:  k_bal_mid (u -> the mid m = l + r into scratch), k_bal_env (serial g),
+//             k_bal_gain (gain from g, y = gain u);
+//   backward: k_bal_adj (ybar, u, g -> the main adjoint gain ybar, the envelope adjoint
+//             a[n] = dL/dg[n], the coefficient alpha[n] of each step and the T, W, R
+//             partials per tile), k_bal_rev (serial lambda[n] = a[n] + alpha[n+1]
+//             lambda[n+1] in place: one FMA per sample), k_bal_in (adds
+//             2 m (1 - alpha[n]) lambda[n] to both channels' adjoint; the attack and
+//             release gradient partials per tile), k_bal_fin (parameter gradients).
+// Per node the scratch holds four rows of pitch floats (rounded up to 64): the mid, the
+// envelope, the envelope adjoint and the per-step coefficient.  Backward tiles own two
+// partial slots (T, W, R and attack, release).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace grafx {
+
+constexpr float BAL_EPS = 1e-7f;
+constexpr int BAL_BLOCK = 512;   // samples per block of the serial kernels
+constexpr int BAL_PT = BAL_BLOCK / 32;
+
+__device__ __forceinline__ int bal_rs(const NodeDev& nd) { return (nd.pitch + 63) & ~63; }
+__device__ __forceinline__ float* bal_row(const DevCtx& c, int v, const NodeDev& nd, int i) {
+  return c.bal + 64 * int64_t(c.ext[v].w) + int64_t(i) * bal_rs(nd);
+}
+
+// The compressor's curve (Eq. 10-11) with its partials dGy/dGu, dT, dW, dR.
+struct BalKnee {
+  float gy, dgu, dt, dw, dr;
+};
+__device__ __forceinline__ BalKnee bal_knee(float gu, float T, float W, float R) {
+  BalKnee k;
+  const float invR = 1.f / R, cR = invR - 1.f;
+  if (gu >= T + W) {
+    k.gy = T + (gu - T) * invR;
+    k.dgu = invR;
+    k.dt = -cR;
+    k.dw = 0.f;
+    k.dr = -(gu - T) * invR * invR;
+  } else if (gu >= T - W) {
+    const float d = gu - T + W;
+    k.gy = gu + cR * d * d / (4.f * W);
+    k.dgu = 1.f + cR * d / (2.f * W);
+    k.dt = -cR * d / (2.f * W);
+    k.dw = cR * (d / (2.f * W) - d * d / (4.f * W * W));
+    k.dr = -d * d / (4.f * W) * invR * invR;
+  } else {
+    k.gy = gu;
+    k.dgu = 1.f;
+    k.dt = k.dw = k.dr = 0.f;
+  }
+  return k;
+}
+
+// forward, per tile: m = l + r of the gathered input
+__global__ void __launch_bounds__(256) k_bal_mid(DevCtx c, int item0, int n_items) {
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int4_ w = c.items[item0 + it];
+    const int v = w.x;
+    const NodeDev nd = c.nodes[v];
+    float* X = bal_row(c, v, nd, 0);
+    for (int t = w.y + 4 * threadIdx.x; t < min(w.y + EW_TILE, nd.pitch); t += 1024) {
+      const float4 l = gather_in(c, v, 0, t, nd.len, nd.pitch), r = gather_in(c, v, 1, t, nd.len, nd.pitch);
+      st4(X + t, f4add(l, r));
+    }
+  }
+}
+
+// One block of the envelope recursion on lane 0, from the previous envelope value.  Both
+// candidate steps are continuous in g[n-1] and meet at x, so the branch of Eq. 8 is the
+// larger candidate when the attack coefficient is the smaller one (attack: both below x,
+// the attack step nearer; release: both above x, the release step nearer) and the smaller
+// one otherwise: a max (or min) replaces the compare and select on the serial chain.
+// Groups of 8 samples in registers, the next group's loads issued before this group's chain.
+template <bool ATTACK_FASTER>
+__device__ __forceinline__ float bal_env_block(const float* xs, float* gs, int n, float aa, float ar, float prev) {
+  const float4* xb = reinterpret_cast<const float4*>(xs);
+  float4* gb = reinterpret_cast<float4*>(gs);
+  const float ba = 1.f - aa, br = 1.f - ar;
+  const int ng = (n + 7) / 8;   // zero-filled past len
+  float4 n0 = xb[0], n1 = xb[1];
+  for (int q = 0; q < ng; ++q) {
+    const float m[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+    if (q + 1 < ng) {
+      n0 = xb[2 * q + 2];
+      n1 = xb[2 * q + 3];
+    }
+    float o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float x = m[j] * m[j];
+      const float ga = fmaf(aa, prev, ba * x), gr = fmaf(ar, prev, br * x);
+      prev = ATTACK_FASTER ? fmaxf(ga, gr) : fminf(ga, gr);
+      o[j] = prev;
+    }
+    gb[2 * q] = make_float4(o[0], o[1], o[2], o[3]);
+    gb[2 * q + 1] = make_float4(o[4], o[5], o[6], o[7]);
+  }
+  return prev;
+}
+
+// forward, serial per node: g[n] = x + alpha (g[n-1] - x), x = m^2, alpha by the branch
+__global__ void __launch_bounds__(32) k_bal_env(DevCtx c, int node_begin) {
+  __shared__ __align__(16) float xs[2][BAL_BLOCK];
+  __shared__ __align__(16) float gs[BAL_BLOCK];
+  const int v = node_begin + blockIdx.x;
+  const NodeDev nd = c.nodes[v];
+  const float* p = c.params + size_t(nd.prow) * 5;
+  const float aa = p[0], ar = p[1];
+  const float* X = bal_row(c, v, nd, 0);
+  float* G = bal_row(c, v, nd, 1);
+  const int nb = (nd.len + BAL_BLOCK - 1) / BAL_BLOCK;
+  const int lane = threadIdx.x;
+  float reg[BAL_PT];
+  // block 0 into shared memory
+#pragma unroll
+  for (int i = 0; i < BAL_PT; ++i) {
+    const int t = lane + 32 * i;
+    xs[0][lane + 32 * i] = t < nd.len ? X[t] : 0.f;
+  }
+  __syncwarp();
+  float prev = 0.f;
+  for (int b = 0; b < nb; ++b) {
+    // loads of block b + 1 issued before the serial part
+#pragma unroll
+    for (int i = 0; i < BAL_PT; ++i) {
+      const int t = (b + 1) * BAL_BLOCK + lane + 32 * i;
+      reg[i] = t < nd.len ? X[t] : 0.f;
+    }
+    if (lane == 0) {
+      const int n = min(BAL_BLOCK, nd.len - b * BAL_BLOCK);
+      prev = aa <= ar ? bal_env_block<true>(xs[b & 1], gs, n, aa, ar, prev)
+                      : bal_env_block<false>(xs[b & 1], gs, n, aa, ar, prev);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < BAL_PT; ++i) {
+      const int t = b * BAL_BLOCK + lane + 32 * i;
+      if (t < nd.len) G[t] = gs[lane + 32 * i];
+      xs[(b + 1) & 1][lane + 32 * i] = reg[i];
+    }
+    __syncwarp();
+  }
+}
+
+// forward, per tile: y = exp(Gy - Gu) u with Gu = ln(g + eps)
+__global__ void __launch_bounds__(256) k_bal_gain(DevCtx c, int item0, int n_items) {
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int4_ w = c.items[item0 + it];
+    const int v = w.x;
+    const NodeDev nd = c.nodes[v];
+    const float* p = c.params + size_t(nd.prow) * 5;
+    const float T = p[2], W = p[3], R = p[4];
+    const float* G = bal_row(c, v, nd, 1);
+    float* y = yrow_w(c, nd);
+    for (int t = w.y + 4 * threadIdx.x; t < min(w.y + EW_TILE, nd.pitch); t += 1024) {
+      float4 l = gather_in(c, v, 0, t, nd.len, nd.pitch), r = gather_in(c, v, 1, t, nd.len, nd.pitch);
+      float gain[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float g = t + q < nd.len ? G[t + q] : 0.f;
+        const float gu = logf(g + BAL_EPS);
+        gain[q] = expf(bal_knee(gu, T, W, R).gy - gu);
+      }
+      l = make_float4(gain[0] * l.x, gain[1] * l.y, gain[2] * l.z, gain[3] * l.w);
+      r = make_float4(gain[0] * r.x, gain[1] * r.y, gain[2] * r.z, gain[3] * r.w);
+      st4(y + t, l);
+      st4(y + nd.pitch + t, r);
+    }
+  }
+}
+
+// backward, per tile: main adjoint gain ybar into the node's adjoint row, the envelope
+// adjoint a[n] = (sum_ch ybar u) gain (dGy/dGu - 1) / (g + eps), and the tile's T, W, R partials
+__global__ void __launch_bounds__(256) k_bal_adj(DevCtx c, int item0, int n_items) {
+  __shared__ float red[4 * 32];
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int4_ w = c.items[item0 + it];
+    const int v = w.x;
+    const NodeDev nd = c.nodes[v];
+    const float* p = c.params + size_t(nd.prow) * 5;
+    const float T = p[2], W = p[3], R = p[4];
+    const float aa = p[0], ar = p[1];
+    const float* X = bal_row(c, v, nd, 0);
+    const float* G = bal_row(c, v, nd, 1);
+    float* A = bal_row(c, v, nd, 2);
+    float* AL = bal_row(c, v, nd, 3);
+    float* ub = arow_w(c, nd);
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int t = w.y + 4 * threadIdx.x; t < min(w.y + EW_TILE, nd.pitch); t += 1024) {
+      const float4 ul = gather_in(c, v, 0, t, nd.len, nd.pitch), ur = gather_in(c, v, 1, t, nd.len, nd.pitch);
+      float4 bl = gather_out_adj(c, v, 0, t, nd.len, nd.pitch), br = gather_out_adj(c, v, 1, t, nd.len, nd.pitch);
+      const float uL[4] = {ul.x, ul.y, ul.z, ul.w}, uR[4] = {ur.x, ur.y, ur.z, ur.w};
+      float bL[4] = {bl.x, bl.y, bl.z, bl.w}, bR[4] = {br.x, br.y, br.z, br.w}, a[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float g = t + q < nd.len ? G[t + q] : 0.f;
+        const float gu = logf(g + BAL_EPS);
+        const BalKnee k = bal_knee(gu, T, W, R);
+        const float gain = expf(k.gy - gu);
+        const float gyb = (bL[q] * uL[q] + bR[q] * uR[q]) * gain;
+        a[q] = gyb * (k.dgu - 1.f) / (g + BAL_EPS);
+        acc[0] += gyb * k.dt;
+        acc[1] += gyb * k.dw;
+        acc[2] += gyb * k.dr;
+        bL[q] *= gain;
+        bR[q] *= gain;
+      }
+      st4(A + t, make_float4(a[0], a[1], a[2], a[3]));
+      float al[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {   // the coefficient of step t + q (by the branch of Eq. 8)
+        const float m = t + q < nd.len ? X[t + q] : 0.f, gp = t + q > 0 && t + q <= nd.len ? G[t + q - 1] : 0.f;
+        al[q] = m * m > gp ? aa : ar;
+      }
+      st4(AL + t, make_float4(al[0], al[1], al[2], al[3]));
+      st4(ub + t, make_float4(bL[0], bL[1], bL[2], bL[3]));
+      st4(ub + nd.pitch + t, make_float4(bR[0], bR[1], bR[2], bR[3]));
+    }
+    block_sum<3>(acc, red);
+    if (threadIdx.x == 0) c.partial[w.w] = make_float4(acc[0], acc[1], acc[2], 0.f);
+    __syncthreads();
+  }
+}
+
+// backward, per node from the end: lambda[n] = a[n] + alpha[n+1] lambda[n+1], in place of
+// a.  With alpha[n] known per sample the recursion is linear, so it runs as a warp scan:
+// lane l owns 16 samples of each 512-sample block; with mu[n] = alpha[n] lambda[n] (the
+// term handed to step n-1), a lane's segment maps its end value to its start value,
+// mu_s = C + Q mu_e; the maps compose across lanes by a shuffle scan from the right, the
+// block's carry enters at lane 31, and a second pass over the segment writes lambda.
+__global__ void __launch_bounds__(32) k_bal_rev(DevCtx c, int node_begin) {
+  constexpr int SEG = BAL_BLOCK / 32, SQ = SEG / 4;
+  const int v = node_begin + blockIdx.x;
+  const NodeDev nd = c.nodes[v];
+  float* A = bal_row(c, v, nd, 2);
+  const float* AL = bal_row(c, v, nd, 3);
+  const int nb = (nd.len + BAL_BLOCK - 1) / BAL_BLOCK;
+  const int lane = threadIdx.x;
+  float4 na[SQ], nl[SQ];
+  auto load = [&](int b) {   // quads past len read as a = 0 (lambda and mu stay 0 there)
+#pragma unroll
+    for (int j = 0; j < SQ; ++j) {
+      const int t = b * BAL_BLOCK + SEG * lane + 4 * j;
+      const bool in = b >= 0 && t < nd.len;
+      na[j] = in ? mask4(ld4(A + t), t, nd.len) : f4zero();
+      nl[j] = in ? ld4(AL + t) : f4zero();
+    }
+  };
+  load(nb - 1);
+  float mu_in = 0.f;   // mu at the end of the block (0 past the end of the signal)
+  for (int b = nb - 1; b >= 0; --b) {
+    float a[SEG], al[SEG];
+#pragma unroll
+    for (int j = 0; j < SQ; ++j) {
+      a[4 * j] = na[j].x, a[4 * j + 1] = na[j].y, a[4 * j + 2] = na[j].z, a[4 * j + 3] = na[j].w;
+      al[4 * j] = nl[j].x, al[4 * j + 1] = nl[j].y, al[4 * j + 2] = nl[j].z, al[4 * j + 3] = nl[j].w;
+    }
+    load(b - 1);   // the block before, in flight under this one
+    float C = 0.f, Q = 1.f;
+#pragma unroll
+    for (int j = SEG - 1; j >= 0; --j) {
+      C = al[j] * (a[j] + C);
+      Q *= al[j];
+    }
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {   // lane l: the map of segments l..31
+      const float C2 = __shfl_down_sync(0xffffffffu, C, d), Q2 = __shfl_down_sync(0xffffffffu, Q, d);
+      if (lane + d < 32) {
+        C = fmaf(Q, C2, C);
+        Q *= Q2;
+      }
+    }
+    const float mu_s = fmaf(Q, mu_in, C);   // mu at the start of this lane's segment
+    float mu = __shfl_down_sync(0xffffffffu, mu_s, 1);
+    if (lane == 31) mu = mu_in;
+#pragma unroll
+    for (int j = SEG - 1; j >= 0; --j) {
+      a[j] += mu;
+      mu = al[j] * a[j];
+    }
+#pragma unroll
+    for (int j = 0; j < SQ; ++j) {
+      const int t = b * BAL_BLOCK + SEG * lane + 4 * j;
+      if (t < nd.len) st4(A + t, make_float4(a[4 * j], a[4 * j + 1], a[4 * j + 2], a[4 * j + 3]));
+    }
+    mu_in = __shfl_sync(0xffffffffu, mu_s, 0);
+  }
+}
+
+// backward, per tile: adds 2 m (1 - alpha[n]) lambda[n] to both channels of the adjoint,
+// and the tile's sums of lambda[n] (g[n-1] - x[n]) over attack and release steps
+__global__ void __launch_bounds__(256) k_bal_in(DevCtx c, int item0, int n_items) {
+  __shared__ float red[4 * 32];
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int4_ w = c.items[item0 + it];
+    const int v = w.x;
+    const NodeDev nd = c.nodes[v];
+    const float* p = c.params + size_t(nd.prow) * 5;
+    const float aa = p[0], ar = p[1];
+    const float* X = bal_row(c, v, nd, 0);
+    const float* G = bal_row(c, v, nd, 1);
+    const float* L = bal_row(c, v, nd, 2);
+    float* ub = arow_w(c, nd);
+    float acc[2] = {0.f, 0.f};
+    for (int t = w.y + threadIdx.x; t < min(w.y + EW_TILE, nd.len); t += 256) {
+      const float m = X[t], x = m * m, gp = t > 0 ? G[t - 1] : 0.f, lam = L[t];
+      const bool att = x > gp;   // the branch the forward took (same fp32 operands)
+      const float e = 2.f * m * (1.f - (att ? aa : ar)) * lam;
+      ub[t] += e;
+      ub[nd.pitch + t] += e;
+      const float d = lam * (gp - x);
+      acc[0] += att ? d : 0.f;
+      acc[1] += att ? 0.f : d;
+    }
+    block_sum<2>(acc, red);
+    if (threadIdx.x == 0) c.partial[w.w + 1] = make_float4(acc[0], acc[1], 0.f, 0.f);
+    __syncthreads();
+  }
+}
+
+// parameter gradients [alpha_attack, alpha_release, T, W, R] of a node range
+__global__ void k_bal_fin(DevCtx c, int node_begin, int node_end) {
+  const int v = node_begin + blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= node_end) return;
+  const int4_ e = c.ext[v];
+  float s[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int k = 0; k < e.y; ++k) {   // two slots per tile: (T, W, R), (attack, release)
+    const float4 q = c.partial[e.x + 2 * k], r = c.partial[e.x + 2 * k + 1];
+    s[0] += r.x;
+    s[1] += r.y;
+    s[2] += q.x;
+    s[3] += q.y;
+    s[4] += q.z;
+  }
+  float* d = c.dparams + size_t(c.nodes[v].grow) * 5;
+  for (int i = 0; i < 5; ++i) d[i] = s[i];
+}
+
+int launch_bal_fwd(const DevCtx& c, int item0, int n_items, int node_begin, int node_end, cudaStream_t s) {
+  if (n_items <= 0 || node_end <= node_begin) return 0;
+  const int g = grid_size(n_items, 8);
+  k_bal_mid<<<g, 256, 0, s>>>(c, item0, n_items);
+  k_bal_env<<<node_end - node_begin, 32, 0, s>>>(c, node_begin);
+  k_bal_gain<<<g, 256, 0, s>>>(c, item0, n_items);
+  return 3;
+}
+
+int launch_bal_bwd(const DevCtx& c, int item0, int n_items, int node_begin, int node_end, cudaStream_t s) {
+  if (n_items <= 0 || node_end <= node_begin) return 0;
+  const int g = grid_size(n_items, 8);
+  k_bal_adj<<<g, 256, 0, s>>>(c, item0, n_items);
+  k_bal_rev<<<node_end - node_begin, 32, 0, s>>>(c, node_begin);
+  k_bal_in<<<g, 256, 0, s>>>(c, item0, n_items);
+  return 3;
+}
+
+int launch_bal_finalize(const DevCtx& c, int node_begin, int node_end, cudaStream_t s) {
+  const int n = node_end - node_begin;
+  if (n <= 0) return 0;
+  k_bal_fin<<<(n + 127) / 128, 128, 0, s>>>(c, node_begin, node_end);
+  return 1;
+}
+
+}  // namespace grafx

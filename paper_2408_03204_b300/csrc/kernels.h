@@ -29,6 +29,12 @@ int launch_comp(int what, const DevCtx& c, int a, int b, int ticket, int mode, c
 // spectra, 4 partition accumulation, 5 lags (inverse FFTs), 6 gradients; < 0 attributes
 int launch_delay(int what, const DevCtx& c, int a, int b, cudaStream_t s);
 
+// compressor with attack/release ballistics: forward (items + node range), backward,
+// parameter-gradient finalize (node range)
+int launch_bal_fwd(const DevCtx& c, int item0, int n_items, int node_begin, int node_end, cudaStream_t s);
+int launch_bal_bwd(const DevCtx& c, int item0, int n_items, int node_begin, int node_end, cudaStream_t s);
+int launch_bal_finalize(const DevCtx& c, int node_begin, int node_end, cudaStream_t s);
+
 // reverb over the reverb nodes [a, b) of a step: what = 0 impulse responses, 1 forward
 // convolution, 2 input adjoint, 3 parameter gradients; < 0 attributes only
 int launch_reverb(int what, const DevCtx& c, int a, int b, cudaStream_t s);

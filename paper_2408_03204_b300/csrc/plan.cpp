@@ -175,6 +175,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     c[GRAFX_T_IMAGER] = 1;
     c[GRAFX_T_EQ] = p->eq_logmag ? (opts.eq_taps + 1) / 2 : 8;
     c[GRAFX_T_COMP] = c[GRAFX_T_GATE] = c[GRAFX_T_SIDECHAIN] = 4;
+    c[GRAFX_T_BALLISTIC] = 5;
     c[GRAFX_T_DELAY] = 2 * p->dl_taps * DL_ROW;
     c[GRAFX_T_REVERB] = p->rv_paper ? 4 * (p->rv_n / 2) : RV_COLS;
   }
@@ -441,6 +442,14 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
           p->n_dl_slots += nw + nb + nw;
           break;
         }
+        case GRAFX_T_BALLISTIC: {
+          // scratch block of 4 rows (mid, envelope, adjoint, coefficient), offset in 64-float units
+          p->node_ext[v].z = p->n_bal++;
+          p->node_ext[v].w = int32_t(p->bal_floats / 64);
+          p->bal_floats += 4 * int64_t(align_up(size_t(p->nodes[v].pitch), 64));
+          for (int32_t t0 = 0; t0 < L; t0 += EW_TILE) fwd.push_back({v, t0, 0, 0});
+          break;
+        }
         case GRAFX_T_COMP:
         case GRAFX_T_GATE:
         case GRAFX_T_SIDECHAIN: {
@@ -522,10 +531,14 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
           break;
         }
         default: {
-          bool has_p = s.type == GRAFX_T_GAIN || s.type == GRAFX_T_IMAGER;
+          bool has_p = s.type == GRAFX_T_GAIN || s.type == GRAFX_T_IMAGER || s.type == GRAFX_T_BALLISTIC;
           p->node_ext[v].x = slot;
           int32_t cnt = 0;
-          for (int32_t t0 = 0; t0 < L; t0 += EW_TILE, ++cnt) bwd.push_back({v, t0, 0, has_p ? slot++ : -1});
+          const int32_t per = s.type == GRAFX_T_BALLISTIC ? 2 : 1;   // partial slots per tile
+          for (int32_t t0 = 0; t0 < L; t0 += EW_TILE, ++cnt) {
+            bwd.push_back({v, t0, 0, has_p ? slot : -1});
+            if (has_p) slot += per;
+          }
           p->node_ext[v].y = has_p ? cnt : 0;
         }
       }
@@ -700,6 +713,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
       }
       w.dgrad = take(4 * size_t(std::max<int64_t>(fl, 1)));
     }
+    w.bal = take(4 * size_t(std::max<int64_t>(p->bal_floats, 1)));
     w.U = take(4 * size_t(std::max<int64_t>(u_floats, 1)));
     w.A = take(4 * size_t(std::max<int64_t>(a_floats, 1)));
     w.total = o;

@@ -60,6 +60,7 @@ struct WsLayout {
   size_t rv_band, rv_U, rv_fr, rv_h, rv_H, rv_Y, rv_R, rv_r, rv_mm;
   size_t loss_part, loss_stats, loss_rowloss, loss_frames, loss_spec;
   size_t dgrad;                                // per-copy parameter gradients (source batch)
+  size_t bal;                                  // ballistic scratch rows
   size_t U, A;
   size_t total;
 };
@@ -102,6 +103,8 @@ struct Plan {
   int32_t n_eq = 0, n_comp_chunks = 0, n_partials = 0, n_eq_runs = 0;
   int32_t n_fitems = 0, in_bitem_begin = 0, in_bitem_count = 0;
   int32_t n_delay = 0, n_dl_slots = 0, n_reverb = 0, rv_nbmax = 0, dl_nbmax = 0;
+  int32_t n_bal = 0;                     // ballistic nodes
+  int64_t bal_floats = 0;                // their scratch (mid, envelope, adjoint, coefficient per sample)
   double dl_taylor[9] = {0};
   int32_t eq_taps = 1023, eq_H = 511, eq_fft = 4096, eq_step = 0;  // eq_step: outputs per block
   int32_t comp_chunk = 2048;

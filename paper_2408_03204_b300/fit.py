@@ -10,7 +10,7 @@ identity.
 """
 import ctypes
 
-from . import PARAM_COLS, T_COMP, T_DELAY, T_GATE, T_REVERB, T_SIDECHAIN, _check, _ptr, _stream_of, lib
+from . import PARAM_COLS, T_BALLISTIC, T_COMP, T_DELAY, T_GATE, T_REVERB, T_SIDECHAIN, _check, _ptr, _stream_of, lib
 
 MAP_IDENT, MAP_ALPHA, MAP_SOFTPLUS, MAP_RATIO, MAP_NEGSP = range(5)
 
@@ -21,6 +21,8 @@ def param_codes(t, cols=None):
     cols = PARAM_COLS[t] if cols is None else cols
     if t in (T_COMP, T_GATE, T_SIDECHAIN):
         return [MAP_ALPHA, MAP_IDENT, MAP_SOFTPLUS, MAP_RATIO]
+    if t == T_BALLISTIC:
+        return [MAP_ALPHA, MAP_ALPHA, MAP_IDENT, MAP_SOFTPLUS, MAP_RATIO]
     if t == T_REVERB and cols == 50:
         # [mid/side][H0 x 12, H_delta x 12], then wet and dry gains
         return ([MAP_IDENT] * 12 + [MAP_NEGSP] * 12) * 2 + [MAP_IDENT, MAP_IDENT]
@@ -43,6 +45,8 @@ def neutral_params(plan, torch, device):
         if not rows:
             continue
         p = torch.zeros((rows, cols), dtype=torch.float32, device=device)
+        if t == T_BALLISTIC:
+            p[:, 0], p[:, 1], p[:, 2], p[:, 3], p[:, 4] = 0.95, 0.999, 0.0, 3.0 * math.log(10.0) / 10.0, 1.001
         if t in (T_COMP, T_GATE, T_SIDECHAIN):  # ratio 1.001: (nearly) no compression / expansion
             p[:, 0], p[:, 1], p[:, 2], p[:, 3] = 0.99, 0.0, 3.0 * math.log(10.0) / 10.0, 1.001
         if t == T_DELAY:

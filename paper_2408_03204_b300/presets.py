@@ -9,7 +9,8 @@ Cases (2^17 stereo samples unless --length):
   * reverb bank: 64 independent i -> r -> o chains, STFT 1024/256 with 12 bands and
     dry/wet (compact) or 384/192 with 192 log-magnitudes per filter, wet only (paper);
   * multi-port nodes: a mid/side console (64 tracks split -> gain on mid and on side ->
-    merge, mixed) and a bank of 64 sidechain compressors keyed by a second source.
+    merge, mixed) and a bank of 64 sidechain compressors keyed by a second source;
+  * 64 compressors with attack/release ballistics next to 64 single-coefficient ones.
 
     python -m paper_2408_03204_b300.presets --reps 10
 """
@@ -109,14 +110,16 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--length", type=int, default=2 ** 17)
     ap.add_argument("--reps", type=int, default=10)
-    ap.add_argument("--case", choices=["console", "delay", "reverb", "mid", "sidechain"], default=None,
+    ap.add_argument("--case", choices=["console", "delay", "reverb", "mid", "sidechain", "ballistic", "compressor"],
+                    default=None,
                     help="one case only")
     ap.add_argument("--preset", choices=["compact", "paper"], default=None, help="one preset only")
     args = ap.parse_args()
     import torch
     import synth
     cases = {"console": synth.console_cfg2(), "delay bank": bank(synth.D), "reverb bank": bank(synth.R),
-             "mid/side console": mid_side_console(), "sidechain bank": sidechain_bank()}
+             "mid/side console": mid_side_console(), "sidechain bank": sidechain_bank(),
+             "ballistic bank": bank(synth.A), "compressor bank": bank(synth.C)}
     rows = []
     for name, g in cases.items():
         if args.case and not name.startswith(args.case):
@@ -124,7 +127,7 @@ def main():
         for preset in ("compact", "paper"):
             if args.preset and preset != args.preset:
                 continue
-            if name in ("mid/side console", "sidechain bank") and preset == "paper":
+            if name in ("mid/side console", "sidechain bank", "ballistic bank", "compressor bank") and preset == "paper":
                 continue   # no processor with a paper layout in these graphs
             ms, ns, ws = time_case(g, args.length, preset, args.reps, torch)
             rows.append({"case": name, "preset": preset, "ms_fwd_bwd": ms, "node_samples_per_s": ns / (ms / 1e3),

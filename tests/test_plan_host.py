@@ -127,7 +127,7 @@ def test_paper_layout_widths_and_bad_layouts(gx):
     assert p.param_cols[8] == gold["reverb_params"] and p.param_cols[3] == gold["gain_params"]
     assert p.param_cols[4] == gold["imager_params"] and p.param_cols[6] == gold["compressor_params"]
     c = gx.Plan([g], [8192])
-    assert c.param_cols == {3: 2, 4: 1, 5: 8, 6: 4, 7: 176, 8: 50, 9: 4, 12: 4}
+    assert c.param_cols == {3: 2, 4: 1, 5: 8, 6: 4, 7: 176, 8: 50, 9: 4, 12: 4, 13: 5}
     # one setting of the preset overridden: band EQ on the paper's other layouts
     m = gx.Plan([g], [8192], preset="paper", eq_params="bands")
     assert m.param_cols[5] == 8 and m.param_cols[7] == 880
@@ -177,7 +177,7 @@ def test_type_ports_and_port_checks(gx):
     for t in range(gx.N_TYPES):
         assert gx.type_ports(t) == want.get(t, (1, 1))
     with pytest.raises(gx.GrafxError):
-        gx.type_ports(13)
+        gx.type_ports(14)
     g = gx.Graph()
     i, sp, mg, o = g.add(0), g.add(10), g.add(11), g.add(1)
     g.connect(i, sp)
