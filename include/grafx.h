@@ -329,7 +329,8 @@ int grafx_step_graph_destroy(grafx_step_graph* g);
  * The optimiser works on unconstrained theta; the processors see p = map(theta),
  * element-wise by a per-column code (codes[i % cols]):
  *   0 identity; 1 alpha = 0.9 + 0.0999 sigmoid(theta); 2 softplus(theta);
- *   3 1 + softplus(theta); 4 -softplus(theta).
+ *   3 1 + softplus(theta); 4 -softplus(theta); 5 attack coefficient
+ *   0.5 + 0.4999 sigmoid(theta).
  * grafx_adam_step: one Adam update (bias-corrected, step >= 1) of n elements, in place:
  * theta, m, v (device float32, m and v zero before step 1) and param (written with
  * map(theta_new)); grad_param = dLoss/dp from grafx_backprop at the old param.

@@ -12,12 +12,13 @@ physical parameters p = map(theta), element-wise:
   SOFTPLUS  p = softplus(theta)                    (knee half-width W > 0)
   RATIO     p = 1 + softplus(theta)                (ratio R > 1)
   NEGSP     p = -softplus(theta)                   (per-frame decay, < 0)
+  ATTACK    p = 0.5 + 0.4999 * sigmoid(theta)      (attack coefficient in (0.5, 0.9999))
 
 dLoss/dtheta = dLoss/dp * dp/dtheta.
 """
 import numpy as np
 
-IDENT, ALPHA, SOFTPLUS, RATIO, NEGSP = range(5)
+IDENT, ALPHA, SOFTPLUS, RATIO, NEGSP, ATTACK = range(6)
 
 
 def softplus(x):
@@ -36,6 +37,7 @@ def to_param(theta, code):
     out = np.where(code == SOFTPLUS, softplus(theta), out)
     out = np.where(code == RATIO, 1.0 + softplus(theta), out)
     out = np.where(code == NEGSP, -softplus(theta), out)
+    out = np.where(code == ATTACK, 0.5 + 0.4999 * sigmoid(theta), out)
     return out
 
 
@@ -47,6 +49,7 @@ def dparam_dtheta(theta, code):
     d = np.where(code == ALPHA, 0.0999 * s * (1.0 - s), d)
     d = np.where((code == SOFTPLUS) | (code == RATIO), s, d)   # softplus' = sigmoid
     d = np.where(code == NEGSP, -s, d)
+    d = np.where(code == ATTACK, 0.4999 * s * (1.0 - s), d)
     return d
 
 
@@ -61,6 +64,8 @@ def to_theta(param, code):
         out = np.where(code == SOFTPLUS, p + np.log(-np.expm1(-p)), out)
         out = np.where(code == RATIO, (p - 1) + np.log(-np.expm1(-(p - 1))), out)
         out = np.where(code == NEGSP, -p + np.log(-np.expm1(p)), out)
+        b = (p - 0.5) / 0.4999
+        out = np.where(code == ATTACK, np.log(b) - np.log1p(-b), out)
     return out
 
 
@@ -80,7 +85,7 @@ def param_codes(t, cols):
     if t in (6, 9, 12):              # compressor / noisegate / sidechain [alpha, T, W, R]
         codes[:] = [ALPHA, IDENT, SOFTPLUS, RATIO]
     if t == 13:                      # attack/release compressor [alpha_a, alpha_r, T, W, R]
-        codes[:] = [ALPHA, ALPHA, IDENT, SOFTPLUS, RATIO]
+        codes[:] = [ATTACK, ALPHA, IDENT, SOFTPLUS, RATIO]
     if t == 8 and cols == 50:        # reverb (12 bands): H_delta columns are decays
         c = np.full(50, IDENT, dtype=np.int8)
         c[:48] = np.tile(np.repeat([IDENT, NEGSP], 12), 2)

@@ -236,32 +236,46 @@ __global__ void __launch_bounds__(256) k_bal_adj(DevCtx c, int item0, int n_item
 // block's carry enters at lane 31, and a second pass over the segment writes lambda.
 __global__ void __launch_bounds__(32) k_bal_rev(DevCtx c, int node_begin) {
   constexpr int SEG = BAL_BLOCK / 32, SQ = SEG / 4;
+  constexpr int ST = 4;          // blocks in flight: a ring of cp.async stages
+  constexpr int LP = SEG + 4;    // floats per lane in a stage (padded: conflict-free float4 reads)
+  __shared__ __align__(16) float ring[ST][2][32 * LP];
   const int v = node_begin + blockIdx.x;
   const NodeDev nd = c.nodes[v];
   float* A = bal_row(c, v, nd, 2);
   const float* AL = bal_row(c, v, nd, 3);
   const int nb = (nd.len + BAL_BLOCK - 1) / BAL_BLOCK;
   const int lane = threadIdx.x;
-  float4 na[SQ], nl[SQ];
-  auto load = [&](int b) {   // quads past len read as a = 0 (lambda and mu stay 0 there)
+  // each lane copies (and later reads) only its own 16 samples of a and alpha; quads at
+  // or past len are zero-filled without a read (a straddling quad's tail is 0 in a)
+  auto issue = [&](int b) {
+    if (b >= 0) {
+      float* da = ring[b % ST][0] + LP * lane;
+      float* dl = ring[b % ST][1] + LP * lane;
 #pragma unroll
-    for (int j = 0; j < SQ; ++j) {
-      const int t = b * BAL_BLOCK + SEG * lane + 4 * j;
-      const bool in = b >= 0 && t < nd.len;
-      na[j] = in ? mask4(ld4(A + t), t, nd.len) : f4zero();
-      nl[j] = in ? ld4(AL + t) : f4zero();
+      for (int j = 0; j < SQ; ++j) {
+        const int t = b * BAL_BLOCK + SEG * lane + 4 * j;
+        const bool in = t < nd.len;
+        cp_async16(da + 4 * j, in ? A + t : A, in ? 16 : 0);
+        cp_async16(dl + 4 * j, in ? AL + t : AL, in ? 16 : 0);
+      }
     }
+    cp_async_commit();
   };
-  load(nb - 1);
+#pragma unroll
+  for (int k = 1; k < ST; ++k) issue(nb - k);
   float mu_in = 0.f;   // mu at the end of the block (0 past the end of the signal)
   for (int b = nb - 1; b >= 0; --b) {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(ST - 2) : "memory");   // block b landed
     float a[SEG], al[SEG];
+    const float4* ra = reinterpret_cast<const float4*>(ring[b % ST][0] + LP * lane);
+    const float4* rl = reinterpret_cast<const float4*>(ring[b % ST][1] + LP * lane);
 #pragma unroll
     for (int j = 0; j < SQ; ++j) {
-      a[4 * j] = na[j].x, a[4 * j + 1] = na[j].y, a[4 * j + 2] = na[j].z, a[4 * j + 3] = na[j].w;
-      al[4 * j] = nl[j].x, al[4 * j + 1] = nl[j].y, al[4 * j + 2] = nl[j].z, al[4 * j + 3] = nl[j].w;
+      const float4 x = ra[j], y = rl[j];
+      a[4 * j] = x.x, a[4 * j + 1] = x.y, a[4 * j + 2] = x.z, a[4 * j + 3] = x.w;
+      al[4 * j] = y.x, al[4 * j + 1] = y.y, al[4 * j + 2] = y.z, al[4 * j + 3] = y.w;
     }
-    load(b - 1);   // the block before, in flight under this one
+    issue(b - (ST - 1));   // into the stage block b + 1 used
     float C = 0.f, Q = 1.f;
 #pragma unroll
     for (int j = SEG - 1; j >= 0; --j) {
@@ -291,6 +305,7 @@ __global__ void __launch_bounds__(32) k_bal_rev(DevCtx c, int node_begin) {
     }
     mu_in = __shfl_sync(0xffffffffu, mu_s, 0);
   }
+  cp_async_wait_all();
 }
 
 // backward, per tile: adds 2 m (1 - alpha[n]) lambda[n] to both channels of the adjoint,

@@ -10,7 +10,7 @@
 
 namespace grafx {
 
-enum : int8_t { MAP_IDENT = 0, MAP_ALPHA = 1, MAP_SOFTPLUS = 2, MAP_RATIO = 3, MAP_NEGSP = 4 };
+enum : int8_t { MAP_IDENT = 0, MAP_ALPHA = 1, MAP_SOFTPLUS = 2, MAP_RATIO = 3, MAP_NEGSP = 4, MAP_ATTACK = 5 };
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.f / (1.f + expf(-x)); }
 __device__ __forceinline__ float softplusf_(float x) { return x > 20.f ? x : log1pf(expf(x)); }
@@ -18,6 +18,7 @@ __device__ __forceinline__ float softplusf_(float x) { return x > 20.f ? x : log
 __device__ __forceinline__ float map_param(float th, int code) {
   switch (code) {
     case MAP_ALPHA: return 0.9f + 0.0999f * sigmoidf_(th);
+    case MAP_ATTACK: return 0.5f + 0.4999f * sigmoidf_(th);
     case MAP_SOFTPLUS: return softplusf_(th);
     case MAP_RATIO: return 1.f + softplusf_(th);
     case MAP_NEGSP: return -softplusf_(th);
@@ -29,6 +30,7 @@ __device__ __forceinline__ float map_slope(float th, int code) {
   const float s = sigmoidf_(th);
   switch (code) {
     case MAP_ALPHA: return 0.0999f * s * (1.f - s);
+    case MAP_ATTACK: return 0.4999f * s * (1.f - s);
     case MAP_SOFTPLUS:
     case MAP_RATIO: return s;
     case MAP_NEGSP: return -s;
@@ -42,6 +44,10 @@ __device__ __forceinline__ float unmap_param(float p, int code) {
     case MAP_ALPHA: {
       float a = (p - 0.9f) / 0.0999f;
       return logf(a) - log1pf(-a);
+    }
+    case MAP_ATTACK: {
+      float b = (p - 0.5f) / 0.4999f;
+      return logf(b) - log1pf(-b);
     }
     case MAP_SOFTPLUS: return p + logf(-expm1f(-p));
     case MAP_RATIO: return (p - 1.f) + logf(-expm1f(-(p - 1.f)));

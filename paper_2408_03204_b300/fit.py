@@ -12,7 +12,7 @@ import ctypes
 
 from . import PARAM_COLS, T_BALLISTIC, T_COMP, T_DELAY, T_GATE, T_REVERB, T_SIDECHAIN, _check, _ptr, _stream_of, lib
 
-MAP_IDENT, MAP_ALPHA, MAP_SOFTPLUS, MAP_RATIO, MAP_NEGSP = range(5)
+MAP_IDENT, MAP_ALPHA, MAP_SOFTPLUS, MAP_RATIO, MAP_NEGSP, MAP_ATTACK = range(6)
 
 
 def param_codes(t, cols=None):
@@ -22,7 +22,7 @@ def param_codes(t, cols=None):
     if t in (T_COMP, T_GATE, T_SIDECHAIN):
         return [MAP_ALPHA, MAP_IDENT, MAP_SOFTPLUS, MAP_RATIO]
     if t == T_BALLISTIC:
-        return [MAP_ALPHA, MAP_ALPHA, MAP_IDENT, MAP_SOFTPLUS, MAP_RATIO]
+        return [MAP_ATTACK, MAP_ALPHA, MAP_IDENT, MAP_SOFTPLUS, MAP_RATIO]
     if t == T_REVERB and cols == 50:
         # [mid/side][H0 x 12, H_delta x 12], then wet and dry gains
         return ([MAP_IDENT] * 12 + [MAP_NEGSP] * 12) * 2 + [MAP_IDENT, MAP_IDENT]

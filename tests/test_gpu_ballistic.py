@@ -43,3 +43,42 @@ def test_ballistic_nodes_sharing_steps_and_random_graphs():
         L = int(rng.integers(3000, 9000))
         run, P, src_per, _ = run_case([g], [L], seed=700 + k)
         backward_check(run, g, L, P, src_per[0], 800 + k)
+
+
+def test_ballistic_coefficient_orders_and_short_signals():
+    """A slower attack than release (the envelope takes the smaller candidate step), equal
+    coefficients (the one-pole filter) and the usual order, on signals of 3 samples (one
+    partial block) and 1029 samples (two blocks and a ragged tail)."""
+    from tests.gpu_common import GpuRun, flat_sources, split_rows
+
+    def bank_graph(n):
+        g = synth.Graph()
+        for _ in range(n):
+            i, v, o = g.add(synth.I), g.add(A), g.add(synth.O)
+            g.connect(i, v)
+            g.connect(v, o)
+        return g
+    graphs = [bank_graph(3), bank_graph(3)]
+    lengths = [3, 1029]
+    src_flat, src_per = flat_sources(graphs, lengths, [41, 42])
+    T, W, R = np.log(10 ** (-20 / 10)), 3.0 * np.log(10) / 10, 4.0
+    rows = np.array([[0.7, 0.9995, T, W, R], [0.9995, 0.7, T, W, R], [0.98, 0.98, T, W, R]])
+    P = {A: np.concatenate([rows, rows])}
+    run = GpuRun(graphs, lengths, P, src_flat)
+    got = split_rows(run.render().cpu().numpy(), graphs, lengths)
+    Pd = [(L + 3) // 4 * 4 for L in lengths]
+    rng = np.random.Generator(np.random.PCG64(5))
+    Wf = [np.zeros((3, 2, p), np.float32) for p in Pd]
+    for w, L in zip(Wf, lengths):
+        w[:, :, :L] = rng.standard_normal((3, 2, L)).astype(np.float32)
+    dP, dS = run.backprop(np.concatenate([w.reshape(-1) for w in Wf]))
+    off = 0
+    for k, (g, L, src) in enumerate(zip(graphs, lengths, src_per)):
+        p = {A: rows}
+        want = orr.outputs_of(g.types, orr.render_one_by_one(g.types, g.edges, src[:, :, :L], p, dict(eq_taps=63)))
+        np.testing.assert_allclose(got[k], want, atol=1e-5 * max(1.0, np.abs(want).max()), rtol=0)
+        wP, wS, wC = orr.backward(g.types, g.edges, src[:, :, :L], p, Wf[k][:, :, :L], dict(eq_taps=63), cond=True)
+        assert_grad_close(dP[A][3 * k:3 * k + 3], wP[A], what=f"graph {k}", cond=wC[A])
+        n = 3 * 2 * Pd[k]
+        assert_grad_close(dS[off:off + n].reshape(3, 2, Pd[k])[:, :, :L], wS, what=f"sources {k}")
+        off += n

@@ -19,15 +19,20 @@ def _lib():
     build.build()
 
 
-def test_adam_steps_match_oracle():
+@pytest.mark.parametrize("t", [6, 13])
+def test_adam_steps_match_oracle(t):
+    """Compressor columns [alpha, T, W, R] and attack/release columns [alpha_attack,
+    alpha_release, T, W, R] (the attack map reaches down to 0.5)."""
     import torch
     import paper_2408_03204_b300 as gx
     lib = gx.lib()
     rng = np.random.Generator(np.random.PCG64(5))
-    rows, cols = 37, 4
-    codes = oo.param_codes(6, cols)
-    P0 = np.stack([rng.uniform(0.91, 0.999, rows), rng.uniform(-9, 0, rows), rng.uniform(0.3, 1.0, rows),
-                   rng.uniform(1.2, 8, rows)], axis=1).astype(np.float32)
+    rows = 37
+    cols = 4 if t == 6 else 5
+    codes = oo.param_codes(t, cols)
+    lead = [rng.uniform(0.91, 0.999, rows)] if t == 6 else [rng.uniform(0.55, 0.98, rows), rng.uniform(0.91, 0.999, rows)]
+    P0 = np.stack(lead + [rng.uniform(-9, 0, rows), rng.uniform(0.3, 1.0, rows),
+                          rng.uniform(1.2, 8, rows)], axis=1).astype(np.float32)
     dev = torch.device("cuda")
     p = torch.tensor(P0, device=dev)
     cd = torch.tensor(codes, device=dev)

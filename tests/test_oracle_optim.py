@@ -5,7 +5,7 @@ import pytest
 
 from oracle import optim as oo
 
-CODES = [oo.IDENT, oo.ALPHA, oo.SOFTPLUS, oo.RATIO, oo.NEGSP]
+CODES = [oo.IDENT, oo.ALPHA, oo.SOFTPLUS, oo.RATIO, oo.NEGSP, oo.ATTACK]
 
 
 @pytest.mark.parametrize("code", CODES)
@@ -25,6 +25,8 @@ def test_map_ranges():
     assert oo.to_param(th, oo.SOFTPLUS).min() > 0
     assert oo.to_param(th, oo.RATIO).min() > 1
     assert oo.to_param(th, oo.NEGSP).max() < 0
+    b = oo.to_param(th, oo.ATTACK)
+    assert b.min() >= 0.5 and b.max() <= 0.9999
 
 
 def test_adam_first_step_moves_by_lr(rng):
@@ -48,3 +50,4 @@ def test_param_codes_layout():
     rc = oo.param_codes(8, 50)
     assert list(rc[12:24]) == [oo.NEGSP] * 12 and list(rc[36:48]) == [oo.NEGSP] * 12
     assert list(rc[:12]) == [oo.IDENT] * 12 and rc[48] == rc[49] == oo.IDENT
+    assert list(oo.param_codes(13, 5)) == [oo.ATTACK, oo.ALPHA, oo.IDENT, oo.SOFTPLUS, oo.RATIO]
