@@ -224,6 +224,34 @@ GX_HD void pass_compute(const float2_* tw, int tid, int Ns, float2 (*v)[R]) {
   }
 }
 
+// 384-point transform (the paper reverb's STFT size), 384 = 3 x 128.  With j = 128 j1 + j2
+// and k = k1 + 3 k2:
+//   X[k1 + 3 k2] = sum_{j2} W_128^{j2 k2} W_384^{j2 k1} sum_{j1} x[128 j1 + j2] W_3^{j1 k1},
+// i.e. a radix-3 stage over the three rows x[128 j1 + .] with the twiddles W_384^{j2 k1},
+// then a 128-point Stockham transform of each row (a radix-16 pass, then a radix-8 pass
+// with the table W_128^{r k} at [(r-1) 16 + k], r < 8, k < 16).  Layout: three padded
+// rows of 128 points, row r at r * R128; x[j] enters at in384(j), X[k] leaves at out384(k).
+constexpr int R128 = Padded<128>::size;
+GX_HD int in384(int j) { return (j >> 7) * R128 + pad(j & 127); }
+GX_HD int out384(int k) { return (k % 3) * R128 + pad(k / 3); }
+
+// The radix-3 stage for column j2 (< 128), in place.  cs[m] = (cos, sin)(2 pi m / 384).
+GX_HD void r3_stage384(float2* buf, int j2, const float2_* cs) {
+  const float s3 = 0.86602540378443865f;   // sin(2 pi / 3)
+  float2* a = buf + pad(j2);
+  const float2 x0 = a[0], x1 = a[R128], x2 = a[2 * R128];
+  const float2 t = cadd(x1, x2), d = csub(x1, x2);
+  const float2 h = make_float2(x0.x - 0.5f * t.x, x0.y - 0.5f * t.y);
+  float2 y1 = make_float2(h.x + s3 * d.y, h.y - s3 * d.x);   // x0 + x1 W_3 + x2 W_3^2
+  float2 y2 = make_float2(h.x - s3 * d.y, h.y + s3 * d.x);   // x0 + x1 W_3^2 + x2 W_3^4
+  const float2_ w1 = cs[j2], w2 = cs[2 * j2];                // W_384^m = (cos, -sin)
+  y1 = cmul(y1, make_float2(w1.x, -w1.y));
+  y2 = cmul(y2, make_float2(w2.x, -w2.y));
+  a[0] = cadd(x0, t);
+  a[R128] = y1;
+  a[2 * R128] = y2;
+}
+
 #ifdef __CUDACC__
 // Full forward transform of one M-point padded buffer by threads tid in [0, M/16).
 // Every thread of the CTA must call it (it contains __syncthreads); threads with
@@ -248,6 +276,33 @@ __device__ __forceinline__ void forward(float2* buf, const float2_* __restrict__
     if (active) pass_load<M, R>(buf, tid, v);
     __syncthreads();
     if (active) pass_store<M, R>(buf, tw + ptw_pass_off(M, Geo<M>::n16), tid, Ns, v);
+    __syncthreads();
+  }
+}
+
+// Forward 384-point transforms of F frames (frame f at buf + f * 3 * R128, layout
+// in384 -> out384) by a CTA of at least 24 F threads; every thread calls it (barriers).
+// The caller synchronises before it; tw128: W_128^{r k} at [(r-1) 16 + k].
+template <int F>
+__device__ __forceinline__ void forward384(float2* buf, const float2_* cs, const float2_* tw128) {
+  for (int i = threadIdx.x; i < F * 128; i += blockDim.x) r3_stage384(buf + (i >> 7) * 3 * R128, i & 127, cs);
+  __syncthreads();
+  const int t = threadIdx.x;
+  const bool act = t < 24 * F;
+  float2* rb = buf + (act ? (t / 24) * 3 * R128 + ((t >> 3) % 3) * R128 : 0);
+  const int t8 = t & 7;
+  {
+    float2 v[1][16];
+    if (act) pass_load<128, 16>(rb, t8, v);
+    __syncthreads();
+    if (act) pass_store<128, 16>(rb, tw128, t8, 1, v);
+    __syncthreads();
+  }
+  {
+    float2 v[2][8];
+    if (act) pass_load<128, 8>(rb, t8, v);
+    __syncthreads();
+    if (act) pass_store<128, 8>(rb, tw128, t8, 16, v);
     __syncthreads();
   }
 }

@@ -8,8 +8,8 @@
 // bands, y = e^{q_dry} u + e^{q_wet} (h * u); the frames go through the 1024-point
 // shared-memory FFT with mid + i side packed in one complex transform) and the
 // paper's (FFT 384, hop 192, H0/Hd given per bin for bins 0..191 with the Nyquist
-// bin dropped, y = h * u; 384 is not a power of two and the frames are short, so
-// their transforms are direct DFT sums over a twiddle table in shared memory).
+// bin dropped, y = h * u; 384 is not a power of two: its frames go through the 3 x 128
+// mixed-radix transform of fft.cuh, five frames per CTA).
 // Convolution: 22 partitions of 4096 taps by overlap-save with 8192-point spectra:
 // Y_b = sum_p H_p X_{b-1-p} per channel (u windows of 2B samples from the delay's
 // spectrum kernel), one inverse per block.
@@ -107,72 +107,84 @@ __global__ void __launch_bounds__(RV_N / 16) k_rv_ir_frames(DevCtx c, int node_b
   }
 }
 
-// Paper layout: U_x[m][k], k <= N/2, of both noise buffers by direct DFT sums of the
-// windowed centred frame m; one CTA per frame.
-__global__ void __launch_bounds__(256) k_rv_noise_dft(DevCtx c) {
-  __shared__ float2 fr[RV_PN];
-  __shared__ float2_ cs[RV_PN];
-  const int m = blockIdx.x, N = c.rv_n, bins = N / 2 + 1;
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const int t = m * c.rv_hop + j - N / 2;
+// Paper layout (N = 384): frames per CTA of the 384-point transforms, the shared tables.
+constexpr int RV_FPC = 5;
+constexpr int RV_FS = 3 * fft::R128;   // floats2 per frame buffer
+struct Rv384Smem {
+  float2 buf[RV_FPC * RV_FS];
+  float2_ cs[RV_PN];     // (cos, sin)(2 pi j / 384)
+  float2_ tw[7 * 16];    // W_128^{r k} at [(r-1) 16 + k]
+};
+__device__ __forceinline__ void rv384_tables(const DevCtx& c, Rv384Smem& sm) {
+  for (int j = threadIdx.x; j < RV_PN; j += blockDim.x) sm.cs[j] = c.rv_cs[j];
+  for (int i = threadIdx.x; i < 7 * 16; i += blockDim.x) {
+    const float2_ e = c.rv_cs[(3 * (i / 16 + 1) * (i % 16)) % RV_PN];
+    sm.tw[i] = float2_{e.x, -e.y};
+  }
+}
+
+// Paper layout: U_x[m][k], k <= N/2, of both noise buffers: the windowed centred frames
+// (mid + i side) through the 384-point transform, split per channel; five frames per CTA.
+__global__ void __launch_bounds__(128) k_rv_noise_384(DevCtx c) {
+  __shared__ Rv384Smem sm;
+  const int N = RV_PN, bins = N / 2 + 1, m0 = blockIdx.x * RV_FPC, nf = min(RV_FPC, c.rv_f - m0);
+  rv384_tables(c, sm);
+  for (int i = threadIdx.x; i < RV_FPC * N; i += blockDim.x) {
+    const int f = i / N, j = i % N;
+    const int t = (m0 + f) * c.rv_hop + j - N / 2;
     const float w = c.rv_win[j];
-    fr[j] = t >= 0 && t < RV_LEN ? make_float2(w * c.rv_noise[t], w * c.rv_noise[RV_LEN + t]) : make_float2(0.f, 0.f);
-    cs[j] = c.rv_cs[j];
+    const bool in = f < nf && t >= 0 && t < RV_LEN;
+    sm.buf[f * RV_FS + fft::in384(j)] = in ? make_float2(w * c.rv_noise[t], w * c.rv_noise[RV_LEN + t]) : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < bins; k += blockDim.x) {
-    float2 am = make_float2(0.f, 0.f), as = make_float2(0.f, 0.f);
-    int idx = 0;   // (j k) mod N
-    for (int j = 0; j < N; ++j) {
-      const float2_ e = cs[idx];   // e^{-i a} = (cos a, -sin a)
-      am.x += fr[j].x * e.x;
-      am.y -= fr[j].x * e.y;
-      as.x += fr[j].y * e.x;
-      as.y -= fr[j].y * e.y;
-      idx += k;
-      if (idx >= N) idx -= N;
-    }
+  fft::forward384<RV_FPC>(sm.buf, sm.cs, sm.tw);
+  for (int i = threadIdx.x; i < nf * bins; i += blockDim.x) {
+    const int f = i / bins, k = i % bins, m = m0 + f;
+    const float2* fb = sm.buf + f * RV_FS;
+    float2 am, as;
+    rv_split(fb[fft::out384(k)], fb[fft::out384((N - k) % N)], &am, &as);
     c.rv_U[size_t(m) * bins + k] = am;
     c.rv_U[size_t(c.rv_f + m) * bins + k] = as;
   }
 }
 
-// Paper layout: masked noise frame m of one node, inverted by the one-sided inverse
-// DFT sum x[j] = (Re Y_0 + 2 sum_{0<k<K} Re(Y_k e^{i 2 pi j k / N}) + Re Y_K (-1)^j) / N
-// and windowed: (mid, side) per sample.
-__global__ void __launch_bounds__(128) k_rv_ir_frames_dft(DevCtx c, int node_begin) {
-  __shared__ float2 Ym[RV_PN / 2 + 1], Ys[RV_PN / 2 + 1];
-  __shared__ float2_ cs[RV_PN];
-  const int m = blockIdx.x, v = node_begin + blockIdx.y;
+// Paper layout: masked noise frames of one node, inverted and windowed: (mid, side) per
+// sample.  The masked spectra of both channels (Nyquist dropped: M = 0 there) are packed
+// as one Hermitian-extended spectrum Hm + i Hs, conjugated, transformed forward and
+// conjugated back (the inverse); five frames per CTA.
+__global__ void __launch_bounds__(128) k_rv_ir_frames_384(DevCtx c, int node_begin) {
+  __shared__ Rv384Smem sm;
+  const int N = RV_PN, K = N / 2, bins = K + 1;
+  const int m0 = blockIdx.x * RV_FPC, nf = min(RV_FPC, c.rv_f - m0), v = node_begin + blockIdx.y;
   const NodeDev nd = c.nodes[v];
-  const int ri = c.ext[v].z, N = c.rv_n, K = N / 2, bins = K + 1;
+  const int ri = c.ext[v].z;
   const float* q = c.params + size_t(nd.prow) * c.pcols;
-  for (int k = threadIdx.x; k < bins; k += blockDim.x) {
-    float M[2];
-    rv_masks(c, q, k, m, M);
-    const float2 hm = c.rv_U[size_t(m) * bins + k], hs = c.rv_U[size_t(c.rv_f + m) * bins + k];
-    Ym[k] = make_float2(hm.x * M[0], hm.y * M[0]);
-    Ys[k] = make_float2(hs.x * M[1], hs.y * M[1]);
-  }
-  for (int j = threadIdx.x; j < N; j += blockDim.x) cs[j] = c.rv_cs[j];
-  __syncthreads();
-  float2* fr = c.rv_fr + (size_t(ri) * c.rv_f + m) * N;
-  const float inv = 1.f / float(N);
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    float sm = 0.f, ss = 0.f;
-    int idx = 0;   // (j k) mod N
-    for (int k = 1; k < K; ++k) {
-      idx += j;
-      if (idx >= N) idx -= N;
-      const float2_ e = cs[idx];   // e^{i a} = (cos a, sin a)
-      sm += Ym[k].x * e.x - Ym[k].y * e.y;
-      ss += Ys[k].x * e.x - Ys[k].y * e.y;
+  rv384_tables(c, sm);
+  for (int i = threadIdx.x; i < RV_FPC * bins; i += blockDim.x) {
+    const int f = i / bins, k = i % bins, m = m0 + f;
+    float2* fb = sm.buf + f * RV_FS;
+    float2 hm = make_float2(0.f, 0.f), hs = hm;
+    if (f < nf) {
+      float M[2];
+      rv_masks(c, q, k, m, M);
+      hm = c.rv_U[size_t(m) * bins + k];
+      hs = c.rv_U[size_t(c.rv_f + m) * bins + k];
+      hm = make_float2(hm.x * M[0], hm.y * M[0]);
+      hs = make_float2(hs.x * M[1], hs.y * M[1]);
     }
-    const float sg = (j & 1) ? -1.f : 1.f;
-    sm = Ym[0].x + 2.f * sm + sg * Ym[K].x;
-    ss = Ys[0].x + 2.f * ss + sg * Ys[K].x;
+    if (k == 0 || k == K) hm.y = hs.y = 0.f;   // real DC / Nyquist (one-sided inverse)
+    // W = Hm + i Hs at k, conj(Hm) + i conj(Hs) at N - k; stored conjugated
+    fb[fft::in384(k)] = make_float2(hm.x - hs.y, -(hm.y + hs.x));
+    if (k > 0 && k < K) fb[fft::in384(N - k)] = make_float2(hm.x + hs.y, hm.y - hs.x);
+  }
+  __syncthreads();
+  fft::forward384<RV_FPC>(sm.buf, sm.cs, sm.tw);
+  const float inv = 1.f / float(N);
+  for (int i = threadIdx.x; i < nf * N; i += blockDim.x) {
+    const int f = i / N, j = i % N;
+    const float2 z = sm.buf[f * RV_FS + fft::out384(j)];
     const float w = c.rv_win[j] * inv;
-    fr[j] = make_float2(w * sm, w * ss);
+    c.rv_fr[(size_t(ri) * c.rv_f + m0 + f) * N + j] = make_float2(w * z.x, -w * z.y);   // conj: (mid, side)
   }
 }
 
@@ -256,9 +268,22 @@ __device__ __forceinline__ float2 cmac(float2 acc, float2 a, float2 b, bool conj
   return make_float2(acc.x + a.x * b.x - ay * b.y, acc.y + a.x * b.y + ay * b.x);
 }
 
+// Packed spectrum l + i r of two real signals from their bin-k spectra A_l, A_r, at k
+// and (0 < k < M/2) at M - k, where each real signal's spectrum is the conjugate:
+// Z[k] = A_l + i A_r, Z[M-k] = conj(A_l) + i conj(A_r).
+__device__ __forceinline__ void rv_store_sym(float2* Z, int k, float2 al, float2 ar) {
+  Z[k] = make_float2(al.x - ar.y, al.y + ar.x);
+  if (k > 0 && k < DL_M / 2) Z[DL_M - k] = make_float2(al.x + ar.y, ar.x - al.y);
+}
+
+constexpr int RV_PCH = 6;   // partitions per warp (lags): 4 chunks x 6 >= RV_P, two block halves
+static_assert(4 * RV_PCH >= RV_P, "lag chunks must cover the partitions");
+
 // what = 0: forward Y_b = sum_p H_p X_{b-1-p}; 1: input adjoint
 // Ubar_b = sum_p conj(H_p) Ybarwin_{b+p}; 2: lags R_p = sum_b X_{b-p-1} conj(Ybarblk_b).
-// grid (DL_M / DL_CHUNK, reverb nodes), 256 threads: bin kk = tid % 32, lane group g.
+// The products of two real signals' spectra are conjugate-symmetric, so only bins
+// 0..M/2 are computed and bin M - k is written from bin k: grid (DL_M / 2 / DL_CHUNK + 1,
+// reverb nodes), 256 threads: bin kk = tid % 32, lane group g.
 template <int WHAT>
 __global__ void __launch_bounds__(256) k_rv_acc(DevCtx c, int node_begin) {
   extern __shared__ float2 sm[];
@@ -283,28 +308,73 @@ __global__ void __launch_bounds__(256) k_rv_acc(DevCtx c, int node_begin) {
     for (int b = g; b < nb; b += ng) {
       float2 al = make_float2(0.f, 0.f), ar = make_float2(0.f, 0.f);
       for (int p = 0; p < RV_P; ++p) {
-        const int s = WHAT == 0 ? b - 1 - p + RV_P : b + p;
+        const int sl = WHAT == 0 ? b - 1 - p + RV_P : b + p;
         const float2 hl = Hs[(size_t(p) * DL_CHUNK + kk) * 2], hr = Hs[(size_t(p) * DL_CHUNK + kk) * 2 + 1];
-        const float2 xl = S[(size_t(s) * DL_CHUNK + kk) * 2], xr = S[(size_t(s) * DL_CHUNK + kk) * 2 + 1];
+        const float2 xl = S[(size_t(sl) * DL_CHUNK + kk) * 2], xr = S[(size_t(sl) * DL_CHUNK + kk) * 2 + 1];
         al = cmac(al, hl, xl, WHAT == 1);
         ar = cmac(ar, hr, xr, WHAT == 1);
       }
-      c.rv_Y[(size_t(ri) * c.rv_nbmax + b) * DL_M + k] = make_float2(al.x - ar.y, al.y + ar.x);
+      if (k <= DL_M / 2) rv_store_sym(c.rv_Y + (size_t(ri) * c.rv_nbmax + b) * DL_M, k, al, ar);
     }
   } else {
+    // warp g: partitions [p0, p0 + RV_PCH) over half h of the blocks, the X slots of
+    // those partitions in a register window that slides by one slot per block; the two
+    // halves are added in shared memory (fixed order)
     const float2* X = S;
     const float2* Yb = S + size_t(nw) * DL_CHUNK * 2;
-    for (int p = g; p < RV_P; p += ng) {
-      float2 al = make_float2(0.f, 0.f), ar = make_float2(0.f, 0.f);
-      for (int b = 0; b < nb; ++b) {
-        const int s = b - p - 1 + RV_P;
-        const float2 yl = Yb[(size_t(b) * DL_CHUNK + kk) * 2], yr = Yb[(size_t(b) * DL_CHUNK + kk) * 2 + 1];
-        const float2 xl = X[(size_t(s) * DL_CHUNK + kk) * 2], xr = X[(size_t(s) * DL_CHUNK + kk) * 2 + 1];
-        al = cmac(al, yl, xl, true);   // x conj(y) = conj(y) x
-        ar = cmac(ar, yr, xr, true);
+    const int pc = g % (ng / 2), h = g / (ng / 2), p0 = pc * RV_PCH;
+    const int bs = h == 0 ? 0 : nb / 2, be = h == 0 ? nb / 2 : nb;
+    auto ldx = [&](int sl, float2& l, float2& r) {
+      l = r = make_float2(0.f, 0.f);
+      if (sl >= 0 && sl < nw) {
+        l = X[(size_t(sl) * DL_CHUNK + kk) * 2];
+        r = X[(size_t(sl) * DL_CHUNK + kk) * 2 + 1];
       }
-      c.rv_R[(size_t(ri) * RV_P + p) * DL_M + k] = make_float2(al.x - ar.y, al.y + ar.x);
+    };
+    float2 acc[RV_PCH][2], wl[RV_PCH], wr[RV_PCH];
+#pragma unroll
+    for (int j = 0; j < RV_PCH; ++j) {
+      acc[j][0] = acc[j][1] = make_float2(0.f, 0.f);
+      wl[j] = wr[j] = make_float2(0.f, 0.f);
     }
+    // window slot of partition p0 + j at block b: b - 1 + RV_P - p0 - j
+#pragma unroll
+    for (int j = 0; j + 1 < RV_PCH; ++j) ldx(bs - 1 + RV_P - p0 - (j + 1), wl[j], wr[j]);
+    for (int b = bs; b < be; ++b) {
+#pragma unroll
+      for (int j = RV_PCH - 1; j > 0; --j) {
+        wl[j] = wl[j - 1];
+        wr[j] = wr[j - 1];
+      }
+      ldx(b - 1 + RV_P - p0, wl[0], wr[0]);
+      const float2 yl = Yb[(size_t(b) * DL_CHUNK + kk) * 2], yr = Yb[(size_t(b) * DL_CHUNK + kk) * 2 + 1];
+#pragma unroll
+      for (int j = 0; j < RV_PCH; ++j) {
+        acc[j][0] = cmac(acc[j][0], yl, wl[j], true);   // x conj(y) = conj(y) x
+        acc[j][1] = cmac(acc[j][1], yr, wr[j], true);
+      }
+    }
+    __syncthreads();   // the staged spectra are no longer read: reuse them for the halves
+    float2* red = sm;  // [pc][j][kk][2]
+    if (h == 1)
+#pragma unroll
+      for (int j = 0; j < RV_PCH; ++j) {
+        red[((size_t(pc) * RV_PCH + j) * DL_CHUNK + kk) * 2] = acc[j][0];
+        red[((size_t(pc) * RV_PCH + j) * DL_CHUNK + kk) * 2 + 1] = acc[j][1];
+      }
+    __syncthreads();
+    if (h == 0)
+#pragma unroll
+      for (int j = 0; j < RV_PCH; ++j) {
+        const int p = p0 + j;
+        if (p < RV_P) {
+          const float2 ol = red[((size_t(pc) * RV_PCH + j) * DL_CHUNK + kk) * 2];
+          const float2 orr = red[((size_t(pc) * RV_PCH + j) * DL_CHUNK + kk) * 2 + 1];
+          const float2 al = make_float2(acc[j][0].x + ol.x, acc[j][0].y + ol.y);
+          const float2 ar = make_float2(acc[j][1].x + orr.x, acc[j][1].y + orr.y);
+          if (k <= DL_M / 2) rv_store_sym(c.rv_R + (size_t(ri) * RV_P + p) * DL_M, k, al, ar);
+        }
+      }
   }
 }
 
@@ -404,22 +474,25 @@ __global__ void __launch_bounds__(RV_N / 16) k_rv_gfr(DevCtx c, int node_begin) 
   }
 }
 
-// Paper layout: the adjoint of the IR synthesis for frame m of one node by direct DFT
-// sums (the adjoint of the one-sided inverse is a forward DFT with weights c_k/N); per
-// channel and bin, M dL/dM and m M dL/dM.
-__global__ void __launch_bounds__(128) k_rv_gfr_dft(DevCtx c, int node_begin) {
-  __shared__ float2 g[RV_PN];
-  __shared__ float2_ cs[RV_PN];
-  const int m = blockIdx.x, v = node_begin + blockIdx.y;
+// Paper layout: the adjoint of the IR synthesis for the frames of one node (the adjoint
+// of the one-sided inverse is a forward transform with weights c_k/N): the frame
+// adjoints (mid + i side) through the 384-point transform, split per channel; per
+// channel and bin, M dL/dM and m M dL/dM.  Five frames per CTA.
+__global__ void __launch_bounds__(128) k_rv_gfr_384(DevCtx c, int node_begin) {
+  __shared__ Rv384Smem sm;
+  const int N = RV_PN, K = N / 2, bins = K + 1;
+  const int m0 = blockIdx.x * RV_FPC, nf = min(RV_FPC, c.rv_f - m0), v = node_begin + blockIdx.y;
   const NodeDev nd = c.nodes[v];
-  const int ri = c.ext[v].z, N = c.rv_n, K = N / 2, bins = K + 1;
+  const int ri = c.ext[v].z;
   const float* q = c.params + size_t(nd.prow) * c.pcols;
   const float* rl = c.rv_r + (size_t(ri) * 2) * RV_HLEN;
   const float* rr = rl + RV_HLEN;
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const int n = m * c.rv_hop + j - N / 2;   // centred frame
+  rv384_tables(c, sm);
+  for (int i = threadIdx.x; i < RV_FPC * N; i += blockDim.x) {
+    const int f = i / N, j = i % N;
+    const int n = (m0 + f) * c.rv_hop + j - N / 2;   // centred frame
     float gm = 0.f, gs = 0.f;
-    if (n >= 0 && n < RV_LEN) {
+    if (f < nf && n >= 0 && n < RV_LEN) {
       int lo, hi;
       const float D = rv_ola_norm(c, n, &lo, &hi);
       if (D > 1e-8f) {
@@ -428,26 +501,19 @@ __global__ void __launch_bounds__(128) k_rv_gfr_dft(DevCtx c, int node_begin) {
         gs = w * 0.5f * (rl[n] - rr[n]);
       }
     }
-    g[j] = make_float2(gm, gs);
-    cs[j] = c.rv_cs[j];
+    sm.buf[f * RV_FS + fft::in384(j)] = make_float2(gm, gs);
   }
   __syncthreads();
-  float2* out = c.rv_mm + (size_t(ri) * c.rv_f + m) * 2 * bins;
-  for (int k = threadIdx.x; k < bins; k += blockDim.x) {
-    float2 A[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    int idx = 0;   // (j k) mod N
-    for (int j = 0; j < N; ++j) {
-      const float2_ e = cs[idx];   // e^{-i a}
-      A[0].x += g[j].x * e.x;
-      A[0].y -= g[j].x * e.y;
-      A[1].x += g[j].y * e.x;
-      A[1].y -= g[j].y * e.y;
-      idx += k;
-      if (idx >= N) idx -= N;
-    }
+  fft::forward384<RV_FPC>(sm.buf, sm.cs, sm.tw);
+  for (int i = threadIdx.x; i < nf * bins; i += blockDim.x) {
+    const int f = i / bins, k = i % bins, m = m0 + f;
+    const float2* fb = sm.buf + f * RV_FS;
+    float2 A[2];
+    rv_split(fb[fft::out384(k)], fb[fft::out384((N - k) % N)], &A[0], &A[1]);
     const float ck = (k == 0 || k == K ? 1.f : 2.f) / float(N);
     float M[2];
     rv_masks(c, q, k, m, M);
+    float2* out = c.rv_mm + (size_t(ri) * c.rv_f + m) * 2 * bins;
 #pragma unroll
     for (int x = 0; x < 2; ++x) {
       const float2 U = c.rv_U[size_t(x * c.rv_f + m) * bins + k];
@@ -457,8 +523,44 @@ __global__ void __launch_bounds__(128) k_rv_gfr_dft(DevCtx c, int node_begin) {
   }
 }
 
-// Mask gradients summed over frames; compact: through the band matrix, then dq_dry
-// and dq_wet; paper: the per-bin H0 and Hd gradients themselves.
+// Mask-gradient terms summed over frames, (channel, bin) items in parallel: a CTA takes
+// 32 items of one node and eight frame groups, added in a fixed order.  Paper layout:
+// the sums are the per-bin H0 and Hd gradients (written out); compact: they replace
+// frame 0's row of the terms, for k_rv_grad (every frame of these items has been read
+// by then, and no other CTA touches them).
+__global__ void __launch_bounds__(256) k_rv_msum(DevCtx c, int node_begin) {
+  __shared__ float2 red[8][32];
+  const int v = node_begin + blockIdx.y;
+  const NodeDev nd = c.nodes[v];
+  const int ri = c.ext[v].z, bins = c.rv_n / 2 + 1;
+  const int lane = threadIdx.x & 31, fg = threadIdx.x >> 5, i = blockIdx.x * 32 + lane;
+  float2* mm = c.rv_mm + size_t(ri) * c.rv_f * 2 * bins;
+  float2 t = make_float2(0.f, 0.f);
+  if (i < 2 * bins)
+    for (int m = fg; m < c.rv_f; m += 8) {
+      const float2 z = mm[size_t(m) * 2 * bins + i];
+      t.x += z.x;
+      t.y += z.y;
+    }
+  red[fg][lane] = t;
+  __syncthreads();
+  if (fg != 0 || i >= 2 * bins) return;
+#pragma unroll
+  for (int g = 1; g < 8; ++g) t = make_float2(t.x + red[g][lane].x, t.y + red[g][lane].y);
+  if (c.rv_paper) {   // uniform over the launch
+    const int K = bins - 1, x = i / bins, k = i % bins;
+    float* out = c.dparams + size_t(nd.grow) * c.pcols;
+    if (k < K) {   // the Nyquist bin carries no parameter
+      out[x * 2 * K + k] = t.x;
+      out[x * 2 * K + K + k] = t.y;
+    }
+  } else {
+    mm[i] = t;
+  }
+}
+
+// Compact layout: the frame sums (frame 0's row after k_rv_msum) through the band
+// matrix, then dq_dry and dq_wet.
 __global__ void __launch_bounds__(256) k_rv_grad(DevCtx c, int node_begin) {
   __shared__ float g0[2][RV_BINS], gd[2][RV_BINS];
   __shared__ float red[2 * 32];
@@ -469,24 +571,11 @@ __global__ void __launch_bounds__(256) k_rv_grad(DevCtx c, int node_begin) {
   float* out = c.dparams + size_t(nd.grow) * c.pcols;
   const float2* mm = c.rv_mm + size_t(ri) * c.rv_f * 2 * bins;
   for (int i = threadIdx.x; i < 2 * bins; i += blockDim.x) {
-    float s0 = 0.f, s1 = 0.f;
-    for (int m = 0; m < c.rv_f; ++m) {
-      const float2 z = mm[size_t(m) * 2 * bins + i];
-      s0 += z.x;
-      s1 += z.y;
-    }
-    g0[i / bins][i % bins] = s0;
-    gd[i / bins][i % bins] = s1;
+    const float2 z = mm[i];
+    g0[i / bins][i % bins] = z.x;
+    gd[i / bins][i % bins] = z.y;
   }
   __syncthreads();
-  if (c.rv_paper) {   // uniform over the launch
-    const int K = c.rv_n / 2;
-    for (int i = threadIdx.x; i < 4 * K; i += blockDim.x) {
-      const int x = i / (2 * K), r = i % (2 * K);
-      out[i] = r < K ? g0[x][r] : gd[x][r - K];
-    }
-    return;
-  }
   if (threadIdx.x < 48) {
     const int x = threadIdx.x / 24, r = threadIdx.x % 24, b = r % 12;
     const float* src = r < 12 ? g0[x] : gd[x];
@@ -525,12 +614,13 @@ int launch_reverb(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
   }
   if (what < 0 || b <= a) return 0;
   const int n = b - a;   // reverb nodes of the step: [a, b)
-  const dim3 chunks(DL_M / DL_CHUNK, n);
+  const dim3 chunks(DL_M / 2 / DL_CHUNK + 1, n);   // bins 0..M/2 (conjugate symmetry)
   switch (what) {
     case 0:  // impulse responses and their partition spectra
       if (c.rv_paper) {
-        k_rv_noise_dft<<<c.rv_f, 256, 0, s>>>(c);
-        k_rv_ir_frames_dft<<<dim3(c.rv_f, n), 128, 0, s>>>(c, a);
+        const int fg = (c.rv_f + RV_FPC - 1) / RV_FPC;
+        k_rv_noise_384<<<fg, 128, 0, s>>>(c);
+        k_rv_ir_frames_384<<<dim3(fg, n), 128, 0, s>>>(c, a);
       } else {
         k_rv_noise_stft<<<RV_F, RV_N / 16, 0, s>>>(c);
         k_rv_ir_frames<<<dim3(RV_F, n), RV_N / 16, 0, s>>>(c, a);
@@ -550,11 +640,13 @@ int launch_reverb(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
       k_rv_acc<2><<<chunks, 256, sm2, s>>>(c, a);
       k_rv_inv<2><<<dim3(RV_P, n), DL_M / 16, sm_fft, s>>>(c, a);
       if (c.rv_paper)
-        k_rv_gfr_dft<<<dim3(c.rv_f, n), 128, 0, s>>>(c, a);
+        k_rv_gfr_384<<<dim3((c.rv_f + RV_FPC - 1) / RV_FPC, n), 128, 0, s>>>(c, a);
       else
         k_rv_gfr<<<dim3(RV_F, n), RV_N / 16, 0, s>>>(c, a);
+      k_rv_msum<<<dim3((2 * (c.rv_n / 2 + 1) + 31) / 32, n), 256, 0, s>>>(c, a);
+      if (c.rv_paper) return 4;
       k_rv_grad<<<n, 256, 0, s>>>(c, a);
-      return 4;
+      return 5;
   }
   return 0;
 }
