@@ -76,6 +76,8 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
   c.bal = at<float>(p, p->ws.bal);
   c.partial = at<float4>(p, p->ws.partial);
   c.eq_partial = at<float2>(p, p->ws.eq_partial);
+  c.eq_uspec = at<float2>(p, p->ws.eq_uspec);
+  c.eq_ola = at<float>(p, p->ws.eq_ola);
   c.ybase[KIND_INPUT] = const_cast<float*>(src);
   c.ybase[KIND_OUTPUT] = out;
   c.ybase[KIND_INTERNAL] = at<float>(p, p->ws.U);

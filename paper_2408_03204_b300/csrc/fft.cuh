@@ -312,7 +312,8 @@ __device__ __forceinline__ void forward384(float2* buf, const float2_* cs, const
 // first pass reads exactly that layout and its last pass writes it, so only the inner
 // passes go through shared memory, alternating between b0 and b1 (one barrier per
 // pass).  The caller guarantees that no thread still reads b0 when this is entered;
-// on exit other threads may still read b1 (or b0 when the pass count is odd).
+// on exit other threads may still read the buffer of the last inner pass: b1 when the
+// pass count is odd, b0 when it is even.
 // tw: this size's pass tables (ptw + ptw_base(M)), in global or shared memory.
 template <int M>
 __device__ __forceinline__ void forward_regs_tw(float2 (&v)[16], float2* b0, float2* b1, const float2_* tw, int tid) {

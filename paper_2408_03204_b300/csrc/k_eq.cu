@@ -12,12 +12,20 @@
 // complex FFT; the filter spectrum is real, so one forward and one inverse transform
 // serve both channels.  The gather of predecessors is fused into the window load.
 //
-// Backward (one CTA per run of consecutive blocks): the input adjoint is the same
-// centred convolution applied to ybar (h is even); the tap gradient
-// dL/dh[m] = sum_t ybar[t] u[t-m] is accumulated in the frequency domain as
-// sum_blocks Ybar[k] conj(Ucentre[k]) (both channels combined from the packed
-// spectra) and written once per run; a finalize kernel sums the runs of a node,
-// inverts, and chains through Hann, the cosine sum, exp and the band matrix.
+// The forward keeps every block's input spectrum U[k] (the first transform's result).
+//
+// Backward (one CTA per run of consecutive blocks): ybar restricted to the block's output
+// range [H, H+S) is transformed once.  The tap gradient dL/dh[m] = sum_t ybar[t] u[t-m]
+// is accumulated in the frequency domain as sum_blocks Ybarc[k] conj(U[k]) (both
+// channels combined from the packed spectra; every t lies in one block's range and
+// t - m in that block's window) and written once per run; a finalize kernel sums the
+// runs of a node, inverts, and chains through Hann, the cosine sum, exp and the band
+// matrix.  The input adjoint (the correlation of ybar with h, h even) is assembled by
+// overlap-add: the inverse of Ybarc[k] Hspec[k] is the block's contribution on window
+// positions [0, S + 2H); its own range [H, H+S) goes to the adjoint row, the head
+// [0, H) and the tail [S+H, S+2H) to a scratch, and k_eq_ola adds the neighbours'
+// head and tail into each block's range (S >= H: only the two neighbours reach it).
+// Two transforms per block instead of three (ybar window, centred u, inverse).
 #include "common.cuh"
 #include "fft.cuh"
 #include "kernels.h"
@@ -180,6 +188,9 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_fwd(DevCtx c, int item0
     eq_load_regs<M, false>(c, v, nd, ws, x, false, H, S);
     if (even) __syncthreads();
     fft::forward_regs_tw<M>(x, b0, b1, stw, threadIdx.x);
+    float2* us = c.eq_uspec + size_t(w.w) * M;   // kept for the backward
+#pragma unroll
+    for (int m = 0; m < 16; ++m) us[threadIdx.x + (M / 16) * m] = x[m];
     eq_apply_regs<M>(x, spec);
     if (even) __syncthreads();
     fft::forward_regs_tw<M>(x, b0, b1, stw, threadIdx.x);
@@ -194,8 +205,8 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_bwd(DevCtx c, int item0
   constexpr bool even = fft::Geo<M>::npass % 2 == 0;
   float2* b0 = smem2;
   float2* b1 = smem2 + fft::Padded<M>::size;
-  float2* X = smem2 + 2 * fft::Padded<M>::size;   // spectrum of the centred input
-  float2* Y = even ? b1 : b0;                      // spectrum of ybar (free after the FFT)
+  float2* X = smem2 + 2 * fft::Padded<M>::size;   // the block's input spectrum (unpadded)
+  float2* Y = even ? b1 : b0;                      // centred ybar spectrum (free after the FFT)
   float2* i0 = even ? b0 : b1;                     // ping-pong of the inverse transform
   float2* i1 = even ? b1 : b0;
   const int H = c.eq_H, S = c.eq_step, Hal = c.eq_Hal;
@@ -203,45 +214,85 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_bwd(DevCtx c, int item0
     const int4_ w = c.items[item0 + it];
     const int v = w.x;
     const NodeDev nd = c.nodes[v];
-    const float* spec = c.eq_spec + size_t(c.ext[v].z) * eq_spec_stride(M);
+    const int4_ e = c.ext[v];
+    const float* spec = c.eq_spec + size_t(e.z) * eq_spec_stride(M);
     float2 acc[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) acc[m] = make_float2(0.f, 0.f);
     for (int j = w.y; j < w.y + w.z; ++j) {
       const int ws = -Hal + j * S;
-      float2 x[16];
-      eq_load_regs<M, false>(c, v, nd, ws, x, true, H, S);
+      const size_t g = size_t(e.w) + j;
       __syncthreads();  // previous block's readers of b0/b1/X are done
-      fft::forward_regs<M>(x, b0, b1, c.ptw, threadIdx.x);
-#pragma unroll
-      for (int m = 0; m < 16; ++m) X[fft::pad(threadIdx.x + T * m)] = x[m];
-      eq_load_regs<M, true>(c, v, nd, ws, x, false, H, S);
-      if (even) __syncthreads();
+      // the forward's spectrum of this block, in flight under the ybar load and transform
+      const float2* us = c.eq_uspec + g * M;
+      for (int i = threadIdx.x; i < M / 2; i += T) cp_async16(X + 2 * i, us + 2 * i, 16);
+      cp_async_commit();
+      float2 x[16];
+      eq_load_regs<M, true>(c, v, nd, ws, x, true, H, S);
       fft::forward_regs<M>(x, b0, b1, c.ptw, threadIdx.x);
 #pragma unroll
       for (int m = 0; m < 16; ++m) Y[fft::pad(threadIdx.x + T * m)] = x[m];
+      cp_async_wait_all();
       __syncthreads();
-      // sum over channels of Ybar[k] conj(U[k]) from the packed spectra:
-      // (Zy[k] conj(Zx[k]) + conj(Zy[M-k]) Zx[M-k]) / 2
+      // sum over channels of Ybarc[k] conj(U[k]) from the packed spectra:
+      // (Zy[k] conj(Zu[k]) + conj(Zy[M-k]) Zu[M-k]) / 2
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         const int k = threadIdx.x + T * m;
         const int km = (M - k) & (M - 1);
-        const float2 a = x[m], b = X[fft::pad(k)];
-        const float2 a2 = Y[fft::pad(km)], b2 = X[fft::pad(km)];
+        const float2 a = x[m], b = X[k];
+        const float2 a2 = Y[fft::pad(km)], b2 = X[km];
         acc[m].x += 0.5f * (a.x * b.x + a.y * b.y + a2.x * b2.x + a2.y * b2.y);
         acc[m].y += 0.5f * (a.y * b.x - a.x * b.y + a2.x * b2.y - a2.y * b2.x);
       }
-      // input adjoint: the centred convolution of ybar with the even filter
+      // input adjoint: this block's share of the correlation with the even filter
       eq_apply_regs<M>(x, spec);
       fft::forward_regs<M>(x, i0, i1, c.ptw, threadIdx.x);
       eq_store_regs<M>(arow_w(c, nd), nd, ws, x, H, S);
+      float* hd = c.eq_ola + g * 4 * H;   // [head, tail][l, r][H]
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int p = threadIdx.x + T * m;
+        const int q = p < H ? p : p - (S + H);
+        if (p < H || (p >= S + H && p < S + 2 * H)) {
+          float* d = hd + (p < H ? 0 : 2 * H);
+          d[q] = x[m].x;
+          d[H + q] = -x[m].y;
+        }
+      }
     }
     float2* out = c.eq_partial + size_t(w.w) * (M / 2 + 1);
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int k = threadIdx.x + T * m;
       if (k <= M / 2) out[k] = acc[m];
+    }
+  }
+}
+
+// Overlap-add of the input adjoint (after k_eq_bwd): into block j's range [H, H+S) go
+// block j-1's tail (its window positions [S+H, S+2H) = j's [H, 2H)) and block j+1's
+// head (its [0, H) = j's [S, S+H)), for samples inside [0, len); one CTA per run.
+__global__ void __launch_bounds__(256) k_eq_ola(DevCtx c, int item0, int n_items) {
+  const int H = c.eq_H, S = c.eq_step, Hal = c.eq_Hal;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int4_ w = c.items[item0 + it];
+    const int v = w.x;
+    const NodeDev nd = c.nodes[v];
+    const int nb = (nd.len + Hal - H + S - 1) / S;
+    const size_t base = size_t(c.ext[v].w);
+    float* row = arow_w(c, nd);
+    for (int j = w.y; j < w.y + w.z; ++j) {
+      const int ws = -Hal + j * S;
+      for (int i = threadIdx.x; i < 2 * H; i += blockDim.x) {
+        const bool left = i < H;           // from block j-1's tail, else from j+1's head
+        const int src = left ? j - 1 : j + 1, q = left ? i : i - H;
+        const int t = ws + (left ? H + q : S + q);
+        if (src < 0 || src >= nb || t < 0 || t >= nd.len) continue;
+        const float* part = c.eq_ola + (base + src) * 4 * H + (left ? 2 * H : 0);
+        row[t] += part[q];
+        row[nd.pitch + t] += part[H + q];
+      }
     }
   }
 }
@@ -365,7 +416,10 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
     case 1:
       k_eq_fwd<M><<<grid_size(b, (228 * 1024) / int(sf + 1024)), T, sf, s>>>(c, a, b);
       return 1;
-    case 2: k_eq_bwd<M><<<grid_size(b, (228 * 1024) / int(3 * s1 + 1024)), T, 3 * s1, s>>>(c, a, b); return 1;
+    case 2:
+      k_eq_bwd<M><<<grid_size(b, (228 * 1024) / int(3 * s1 + 1024)), T, 3 * s1, s>>>(c, a, b);
+      k_eq_ola<<<grid_size(b, 8), 256, 0, s>>>(c, a, b);
+      return 2;
     case 3:
       k_eq_gradfft<M><<<b - a, T, s1, s>>>(c, a);
       k_eq_gradbands<<<dim3(b - a, chunks_k), EQ_CHUNK * EQ_SPLIT, 0, s>>>(c, a);

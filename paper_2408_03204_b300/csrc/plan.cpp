@@ -53,7 +53,7 @@ int pick_eq_fft(int taps) {
   double best_cost = 1e30;
   for (int m = 1024, lg = 10; m <= 8192; m *= 2, ++lg) {
     int S = (m - 2 * H) & ~3;
-    if (S < 256) continue;
+    if (S < 256 || S < H) continue;
     double cost = double(m) * lg / S * (m == 8192 ? 1.3 : 1.0);
     if (cost < best_cost) { best_cost = cost; best = m; }
   }
@@ -400,7 +400,8 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     return fail(GRAFX_EINVAL, "eq_fft must be 1024, 2048, 4096 or 8192");
   const int32_t Hal = (p->eq_H + 3) & ~3;
   p->eq_step = (p->eq_fft - 2 * p->eq_H) & ~3;
-  if (p->eq_step < 256) return fail(GRAFX_EINVAL, "eq_fft too small for eq_taps");
+  // S >= H: an input-adjoint block's overlap-add tails reach only its two neighbours
+  if (p->eq_step < 256 || p->eq_step < p->eq_H) return fail(GRAFX_EINVAL, "eq_fft too small for eq_taps");
   p->comp_chunk = opts.comp_chunk ? opts.comp_chunk : 2048;
   if (p->comp_chunk != 1024 && p->comp_chunk != 2048 && p->comp_chunk != 4096)
     return fail(GRAFX_EINVAL, "comp_chunk must be 1024, 2048 or 4096");
@@ -421,7 +422,11 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
         case GRAFX_T_EQ: {
           p->node_ext[v].z = p->n_eq++;
           int32_t nb = int32_t((int64_t(L) + Hal - p->eq_H + p->eq_step - 1) / p->eq_step);
-          for (int32_t j = 0; j < nb; ++j) fwd.push_back({v, j, p->node_ext[v].z, 0});
+          // w: the node's first block in the input-spectrum store (the forward writes block
+          // j's spectrum at w + j, the backward reads it)
+          p->node_ext[v].w = int32_t(p->n_eq_blocks);
+          for (int32_t j = 0; j < nb; ++j) fwd.push_back({v, j, p->node_ext[v].z, int32_t(p->n_eq_blocks + j)});
+          p->n_eq_blocks += nb;
           break;
         }
         case GRAFX_T_DELAY: {
@@ -700,6 +705,8 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     w.rv_mm = take(8 * nr * p->rv_f * 2 * rbins);
     w.partial = take(16 * size_t(std::max(p->n_partials, 1)));
     w.eq_partial = take(8 * size_t(std::max(p->n_eq_runs, 1)) * (p->eq_fft / 2 + 1));
+    w.eq_uspec = take(8 * size_t(std::max<int64_t>(p->n_eq_blocks, 1)) * p->eq_fft);
+    w.eq_ola = take(4 * size_t(std::max<int64_t>(p->n_eq_blocks, 1)) * 4 * size_t(std::max(p->eq_H, 1)));
     w.loss_part = take(32 * size_t(std::max(p->loss.n_groups_total, 1)));
     w.loss_stats = take(32 * nrow * N_RES);
     w.loss_rowloss = take(4 * nrow);

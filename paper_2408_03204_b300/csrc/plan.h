@@ -56,6 +56,7 @@ struct WsLayout {
   size_t tables_end;                           // [0, tables_end) is uploaded at bind time
   size_t status, tickets, flags, flags_bytes;  // flags_bytes covers status+tickets+flags (cleared per call)
   size_t eq_spec, eq_aux, eq_bandpart, comp_carry, partial, eq_partial;
+  size_t eq_uspec, eq_ola;                     // EQ input block spectra (forward), adjoint heads/tails
   size_t dl_aux, dl_spec, dl_R, dl_r;
   size_t rv_band, rv_U, rv_fr, rv_h, rv_H, rv_Y, rv_R, rv_r, rv_mm;
   size_t loss_part, loss_stats, loss_rowloss, loss_frames, loss_spec;
@@ -101,6 +102,7 @@ struct Plan {
   std::vector<int4_> items;              // all work items, forward lists then backward lists
   int32_t n_type_rows[GRAFX_N_TYPES] = {0};
   int32_t n_eq = 0, n_comp_chunks = 0, n_partials = 0, n_eq_runs = 0;
+  int64_t n_eq_blocks = 0;               // overlap-save blocks of all EQ nodes
   int32_t n_fitems = 0, in_bitem_begin = 0, in_bitem_count = 0;
   int32_t n_delay = 0, n_dl_slots = 0, n_reverb = 0, rv_nbmax = 0, dl_nbmax = 0;
   int32_t n_bal = 0;                     // ballistic nodes

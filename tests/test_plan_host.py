@@ -240,8 +240,13 @@ def test_adjoint_rows_are_recycled(gx):
     row = 2 * L * 4
     internal = sum(1 for t in cfg2.types if t not in (synth.I, synth.O))
     info = gx.Plan([g], [L]).info
-    # workspace = U (one row per internal node) + A + small tables; A < internal / 2 rows
-    assert info.ws_bytes < (internal + internal / 2) * row + 64 * 2 ** 20
+    # the EQ's per-block input spectra (kept by the forward for the backward): M bins of
+    # 8 bytes per overlap-save block, S = M - 2H outputs per block (1023 taps)
+    M, H = info.eq_fft, 511
+    Hal, S = (H + 3) & ~3, (info.eq_fft - 2 * H) & ~3
+    spectra = cfg2.types.count(synth.E) * ((L + Hal - H + S - 1) // S) * M * 8
+    # workspace = U (one row per internal node) + A + spectra + small tables; A < internal / 2 rows
+    assert info.ws_bytes < (internal + internal / 2) * row + spectra + 64 * 2 ** 20
 
 
 def test_schedule_benchmark_consoles_step_counts(gx):
