@@ -218,6 +218,21 @@ def cpu_baseline(L=L_FULL, steps=1):
                       f"({dt:.1f} s; numpy/scipy FP64, single-threaded)"}
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time: the whole job ends with it (no-op on one rank)."""
+    if dist is None:
+        return ms
+    import torch
+    tt = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(units_per_rank_step, world, steps, ms_total):
+    """Whole-job throughput: every rank processes its own replica's units each step."""
+    return units_per_rank_step * world * steps / (ms_total / 1e3)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -355,14 +370,10 @@ def main():
         dist.barrier()
     clocks = sampler.stop()
     plan.sync_status(ss)
-    ms_total = t_start.elapsed_time(t_end)
-    if dist:
-        tt = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = max_over_ranks(t_start.elapsed_time(t_end), dist, dev)
     ms_step = ms_total / args.steps
     node_samples = int(info.node_samples)
-    value = node_samples * world * args.steps / (ms_total / 1e3)
+    value = job_rate(node_samples, world, args.steps, ms_total)
 
     # ---- diagnostics outside the timed region: per schedule-step durations of the same
     # step launched step by step (fwd k = 1..N, loss, bwd k = N..1)
@@ -471,12 +482,8 @@ def main():
     e2e_steps(args.e2e_steps)
     b.record(side)
     torch.cuda.synchronize(dev)
-    ms_e2e = a.elapsed_time(b)
-    if dist:
-        tt = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_e2e = float(tt.item())
-    e2e = {"value": node_samples * world * args.e2e_steps / (ms_e2e / 1e3), "unit": UNIT,
+    ms_e2e = max_over_ranks(a.elapsed_time(b), dist, dev)
+    e2e = {"value": job_rate(node_samples, world, args.e2e_steps, ms_e2e), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e / args.e2e_steps,
            "loss": float(loss_pin.item())}
 
