@@ -16,11 +16,12 @@
 //
 // Backward (one CTA per run of consecutive blocks): ybar restricted to the block's output
 // range [H, H+S) is transformed once.  The tap gradient dL/dh[m] = sum_t ybar[t] u[t-m]
-// is accumulated in the frequency domain as sum_blocks Ybarc[k] conj(U[k]) (both
-// channels combined from the packed spectra; every t lies in one block's range and
-// t - m in that block's window) and written once per run; a finalize kernel sums the
-// runs of a node, inverts, and chains through Hann, the cosine sum, exp and the band
-// matrix.  The input adjoint (the correlation of ybar with h, h even) is assembled by
+// is accumulated in the frequency domain (every t lies in one block's range and t - m in
+// that block's window): with the packed spectra Zy = Yl + i Yr and Zu = Ul + i Ur of
+// real signals, P[k] = sum_blocks Zy[k] conj(Zu[k]) is accumulated over all M bins and
+// Yl conj(Ul) + Yr conj(Ur) = (P[k] + conj(P[M-k])) / 2 written once per run for
+// k <= M/2; a finalize kernel sums the runs of a node, inverts, and chains through Hann,
+// the cosine sum, exp and the band matrix.  The input adjoint (the correlation of ybar with h, h even) is assembled by
 // overlap-add: the inverse of Ybarc[k] Hspec[k] is the block's contribution on window
 // positions [0, S + 2H); its own range [H, H+S) goes to the adjoint row, the head
 // [0, H) and the tail [S+H, S+2H) to a scratch, and k_eq_ola adds the neighbours'
@@ -206,8 +207,7 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_bwd(DevCtx c, int item0
   float2* b0 = smem2;
   float2* b1 = smem2 + fft::Padded<M>::size;
   float2* X = smem2 + 2 * fft::Padded<M>::size;   // the block's input spectrum (unpadded)
-  float2* Y = even ? b1 : b0;                      // centred ybar spectrum (free after the FFT)
-  float2* i0 = even ? b0 : b1;                     // ping-pong of the inverse transform
+  float2* i0 = even ? b0 : b1;   // ping-pong of the inverse transform (after a barrier)
   float2* i1 = even ? b1 : b0;
   const int H = c.eq_H, S = c.eq_step, Hal = c.eq_Hal;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -223,27 +223,22 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_bwd(DevCtx c, int item0
       const int ws = -Hal + j * S;
       const size_t g = size_t(e.w) + j;
       __syncthreads();  // previous block's readers of b0/b1/X are done
-      // the forward's spectrum of this block, in flight under the ybar load and transform
+      // the forward's spectrum of this block's window, in flight under the ybar load and
+      // transform
       const float2* us = c.eq_uspec + g * M;
       for (int i = threadIdx.x; i < M / 2; i += T) cp_async16(X + 2 * i, us + 2 * i, 16);
       cp_async_commit();
       float2 x[16];
       eq_load_regs<M, true>(c, v, nd, ws, x, true, H, S);
       fft::forward_regs<M>(x, b0, b1, c.ptw, threadIdx.x);
-#pragma unroll
-      for (int m = 0; m < 16; ++m) Y[fft::pad(threadIdx.x + T * m)] = x[m];
       cp_async_wait_all();
       __syncthreads();
-      // sum over channels of Ybarc[k] conj(U[k]) from the packed spectra:
-      // (Zy[k] conj(Zu[k]) + conj(Zy[M-k]) Zu[M-k]) / 2
+      // P[k] += Zy[k] conj(Zu[k])
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
-        const int k = threadIdx.x + T * m;
-        const int km = (M - k) & (M - 1);
-        const float2 a = x[m], b = X[k];
-        const float2 a2 = Y[fft::pad(km)], b2 = X[km];
-        acc[m].x += 0.5f * (a.x * b.x + a.y * b.y + a2.x * b2.x + a2.y * b2.y);
-        acc[m].y += 0.5f * (a.y * b.x - a.x * b.y + a2.x * b2.y - a2.y * b2.x);
+        const float2 a = x[m], b = X[threadIdx.x + T * m];
+        acc[m].x += a.x * b.x + a.y * b.y;
+        acc[m].y += a.y * b.x - a.x * b.y;
       }
       // input adjoint: this block's share of the correlation with the even filter
       eq_apply_regs<M>(x, spec);
@@ -261,11 +256,20 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_bwd(DevCtx c, int item0
         }
       }
     }
+    // the run's both-channel sum (P[k] + conj(P[M-k])) / 2 for k <= M/2 (P[M-k] is held by
+    // thread T - tid: exchanged through b0 once per run)
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) b0[fft::pad(threadIdx.x + T * m)] = acc[m];
+    __syncthreads();
     float2* out = c.eq_partial + size_t(w.w) * (M / 2 + 1);
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int k = threadIdx.x + T * m;
-      if (k <= M / 2) out[k] = acc[m];
+      if (k <= M / 2) {
+        const float2 y = b0[fft::pad((M - k) & (M - 1))];
+        out[k] = make_float2(0.5f * (acc[m].x + y.x), 0.5f * (acc[m].y - y.y));
+      }
     }
   }
 }
@@ -398,11 +402,12 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
   static bool init = false;
   const size_t s1 = sizeof(float2) * fft::Padded<M>::size;
   const size_t sf = 2 * s1 + sizeof(float2_) * fft::ptw_size(M);   // two FFT buffers + pass twiddles
+  const size_t sb = 2 * s1 + sizeof(float2) * M;                    // two FFT buffers + the kept spectrum
   if (!init) {
     cudaFuncSetAttribute(k_eq_spec<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
     cudaFuncSetAttribute(k_eq_gradfft<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
     cudaFuncSetAttribute(k_eq_fwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sf));
-    cudaFuncSetAttribute(k_eq_bwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(3 * s1));
+    cudaFuncSetAttribute(k_eq_bwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sb));
     init = true;
   }
   if (what < 0) return 0;  // attributes only (before a stream capture)
@@ -417,7 +422,7 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
       k_eq_fwd<M><<<grid_size(b, (228 * 1024) / int(sf + 1024)), T, sf, s>>>(c, a, b);
       return 1;
     case 2:
-      k_eq_bwd<M><<<grid_size(b, (228 * 1024) / int(3 * s1 + 1024)), T, 3 * s1, s>>>(c, a, b);
+      k_eq_bwd<M><<<grid_size(b, (228 * 1024) / int(sb + 1024)), T, sb, s>>>(c, a, b);
       k_eq_ola<<<grid_size(b, 8), 256, 0, s>>>(c, a, b);
       return 2;
     case 3:
