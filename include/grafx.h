@@ -132,7 +132,7 @@ typedef struct {
   int32_t eq_taps;        /* odd FIR length N of the zero-phase EQ (Eq. 4); default 1023 */
   int32_t sample_rate;    /* Hz, for the EQ band centres; default 44100 */
   int32_t n_threads;      /* host threads for planning; 0 = hardware concurrency */
-  int32_t eq_fft;         /* EQ block FFT size (1024..8192, > 2*eq_taps); 0 = autotune default */
+  int32_t eq_fft;         /* EQ block FFT size (1024..8192, at least 2 eq_taps + 2); 0 = default */
   int32_t comp_chunk;     /* compressor scan chunk (1024, 2048 or 4096 samples); 0 = default */
   int32_t checkpoint_steps; /* signal checkpointing: 0 = off (every node row kept from the
                              * forward to the backward pass); k > 0 = the schedule steps are

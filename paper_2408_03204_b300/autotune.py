@@ -22,7 +22,7 @@ def _key(graph_lists, lengths, eq_taps):
 
 def candidates(eq_taps):
     H = (eq_taps - 1) // 2
-    ffts = [m for m in (1024, 2048, 4096, 8192) if ((m - 2 * H) & ~3) >= max(256, m // 4, H)]
+    ffts = [m for m in (1024, 2048, 4096, 8192) if ((m - 2 * H) & ~3) >= max(256, m // 4, 2 * H)]
     return [{"eq_fft": m, "comp_chunk": cc} for m in ffts for cc in (1024, 2048, 4096)]
 
 

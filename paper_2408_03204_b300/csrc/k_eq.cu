@@ -23,10 +23,13 @@
 // k <= M/2; a finalize kernel sums the runs of a node, inverts, and chains through Hann,
 // the cosine sum, exp and the band matrix.  The input adjoint (the correlation of ybar with h, h even) is assembled by
 // overlap-add: the inverse of Ybarc[k] Hspec[k] is the block's contribution on window
-// positions [0, S + 2H); its own range [H, H+S) goes to the adjoint row, the head
-// [0, H) and the tail [S+H, S+2H) to a scratch, and k_eq_ola adds the neighbours'
-// head and tail into each block's range (S >= H: only the two neighbours reach it).
-// Two transforms per block instead of three (ybar window, centred u, inverse).
+// positions [0, S + 2H); its own range [H, H+S) goes to the adjoint row, its head
+// [0, H) belongs to the previous block's [S, S+H) and its tail [S+H, S+2H) to the next
+// block's [H, 2H) (S >= 2H: only the two neighbours, into disjoint parts).  Inside a run
+// the CTA adds the previous block's tail (kept in shared memory) before storing and its
+// head into the stored previous block; across runs the head and tail go to a scratch and
+// k_eq_ola adds them.  Two transforms per block instead of three (ybar window, centred
+// u, inverse).
 #include "common.cuh"
 #include "fft.cuh"
 #include "kernels.h"
@@ -207,6 +210,7 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_bwd(DevCtx c, int item0
   float2* b0 = smem2;
   float2* b1 = smem2 + fft::Padded<M>::size;
   float2* X = smem2 + 2 * fft::Padded<M>::size;   // the block's input spectrum (unpadded)
+  float* tl = reinterpret_cast<float*>(X + M);     // the previous block's tail [l, r][H]
   float2* i0 = even ? b0 : b1;   // ping-pong of the inverse transform (after a barrier)
   float2* i1 = even ? b1 : b0;
   const int H = c.eq_H, S = c.eq_step, Hal = c.eq_Hal;
@@ -240,19 +244,47 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_bwd(DevCtx c, int item0
         acc[m].x += a.x * b.x + a.y * b.y;
         acc[m].y += a.y * b.x - a.x * b.y;
       }
-      // input adjoint: this block's share of the correlation with the even filter
+      // input adjoint: this block's share of the correlation with the even filter;
+      // x[m] = (l, -r) at window position p = tid + T m
       eq_apply_regs<M>(x, spec);
       fft::forward_regs<M>(x, i0, i1, c.ptw, threadIdx.x);
-      eq_store_regs<M>(arow_w(c, nd), nd, ws, x, H, S);
-      float* hd = c.eq_ola + g * 4 * H;   // [head, tail][l, r][H]
+      const bool first = j == w.y, last = j == w.y + w.z - 1;
+      if (!first)   // the previous block's tail falls on [H, 2H)
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const int p = threadIdx.x + T * m;
+          if (p >= H && p < 2 * H) {
+            x[m].x += tl[p - H];
+            x[m].y -= tl[H + p - H];
+          }
+        }
+      __syncthreads();   // every thread has read tl before it is rewritten below
+      float* row = arow_w(c, nd);
+      eq_store_regs<M>(row, nd, ws, x, H, S);
+      float* hd = c.eq_ola + g * 4 * H;   // run boundaries: [head, tail][l, r][H]
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         const int p = threadIdx.x + T * m;
-        const int q = p < H ? p : p - (S + H);
-        if (p < H || (p >= S + H && p < S + 2 * H)) {
-          float* d = hd + (p < H ? 0 : 2 * H);
-          d[q] = x[m].x;
-          d[H + q] = -x[m].y;
+        if (p < H) {   // head: the previous block's [S, S+H)
+          const int t = ws + p;
+          if (!first) {
+            if (t >= 0 && t < nd.len) {   // stored by this CTA before the block's first barrier
+              row[t] += x[m].x;
+              row[nd.pitch + t] -= x[m].y;
+            }
+          } else if (j > 0) {
+            hd[p] = x[m].x;
+            hd[H + p] = -x[m].y;
+          }
+        } else if (p >= S + H && p < S + 2 * H) {   // tail: the next block's [H, 2H)
+          const int q = p - (S + H);
+          if (!last) {
+            tl[q] = x[m].x;
+            tl[H + q] = -x[m].y;
+          } else {
+            hd[2 * H + q] = x[m].x;
+            hd[3 * H + q] = -x[m].y;
+          }
         }
       }
     }
@@ -274,9 +306,10 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_bwd(DevCtx c, int item0
   }
 }
 
-// Overlap-add of the input adjoint (after k_eq_bwd): into block j's range [H, H+S) go
-// block j-1's tail (its window positions [S+H, S+2H) = j's [H, 2H)) and block j+1's
-// head (its [0, H) = j's [S, S+H)), for samples inside [0, len); one CTA per run.
+// Overlap-add of the input adjoint across runs (after k_eq_bwd): into a run's first
+// block j0 goes block j0-1's tail (its window positions [S+H, S+2H) = j0's [H, 2H)), into
+// its last block j1 block j1+1's head (its [0, H) = j1's [S, S+H)), for samples inside
+// [0, len); one CTA per run.
 __global__ void __launch_bounds__(256) k_eq_ola(DevCtx c, int item0, int n_items) {
   const int H = c.eq_H, S = c.eq_step, Hal = c.eq_Hal;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -286,17 +319,16 @@ __global__ void __launch_bounds__(256) k_eq_ola(DevCtx c, int item0, int n_items
     const int nb = (nd.len + Hal - H + S - 1) / S;
     const size_t base = size_t(c.ext[v].w);
     float* row = arow_w(c, nd);
-    for (int j = w.y; j < w.y + w.z; ++j) {
-      const int ws = -Hal + j * S;
-      for (int i = threadIdx.x; i < 2 * H; i += blockDim.x) {
-        const bool left = i < H;           // from block j-1's tail, else from j+1's head
-        const int src = left ? j - 1 : j + 1, q = left ? i : i - H;
-        const int t = ws + (left ? H + q : S + q);
-        if (src < 0 || src >= nb || t < 0 || t >= nd.len) continue;
-        const float* part = c.eq_ola + (base + src) * 4 * H + (left ? 2 * H : 0);
-        row[t] += part[q];
-        row[nd.pitch + t] += part[H + q];
-      }
+    const int j0 = w.y, j1 = w.y + w.z - 1;
+    for (int i = threadIdx.x; i < 2 * H; i += blockDim.x) {
+      const bool left = i < H;
+      const int q = left ? i : i - H;
+      const int j = left ? j0 : j1, src = left ? j0 - 1 : j1 + 1;
+      const int t = -Hal + j * S + (left ? H + q : S + q);
+      if (src < 0 || src >= nb || t < 0 || t >= nd.len) continue;
+      const float* part = c.eq_ola + (base + src) * 4 * H + (left ? 2 * H : 0);
+      row[t] += part[q];
+      row[nd.pitch + t] += part[H + q];
     }
   }
 }
@@ -402,7 +434,8 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
   static bool init = false;
   const size_t s1 = sizeof(float2) * fft::Padded<M>::size;
   const size_t sf = 2 * s1 + sizeof(float2_) * fft::ptw_size(M);   // two FFT buffers + pass twiddles
-  const size_t sb = 2 * s1 + sizeof(float2) * M;                    // two FFT buffers + the kept spectrum
+  // two FFT buffers, the kept spectrum, the previous block's tail (2H floats, H <= M/4)
+  const size_t sb = 2 * s1 + sizeof(float2) * M + sizeof(float) * M / 2;
   if (!init) {
     cudaFuncSetAttribute(k_eq_spec<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
     cudaFuncSetAttribute(k_eq_gradfft<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));

@@ -53,7 +53,7 @@ int pick_eq_fft(int taps) {
   double best_cost = 1e30;
   for (int m = 1024, lg = 10; m <= 8192; m *= 2, ++lg) {
     int S = (m - 2 * H) & ~3;
-    if (S < 256 || S < H) continue;
+    if (S < 256 || S < 2 * H) continue;
     double cost = double(m) * lg / S * (m == 8192 ? 1.3 : 1.0);
     if (cost < best_cost) { best_cost = cost; best = m; }
   }
@@ -400,8 +400,9 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     return fail(GRAFX_EINVAL, "eq_fft must be 1024, 2048, 4096 or 8192");
   const int32_t Hal = (p->eq_H + 3) & ~3;
   p->eq_step = (p->eq_fft - 2 * p->eq_H) & ~3;
-  // S >= H: an input-adjoint block's overlap-add tails reach only its two neighbours
-  if (p->eq_step < 256 || p->eq_step < p->eq_H) return fail(GRAFX_EINVAL, "eq_fft too small for eq_taps");
+  // S >= 2H: an input-adjoint block's head and tail reach only its two neighbours, and
+  // into disjoint parts of their output ranges
+  if (p->eq_step < 256 || p->eq_step < 2 * p->eq_H) return fail(GRAFX_EINVAL, "eq_fft too small for eq_taps");
   p->comp_chunk = opts.comp_chunk ? opts.comp_chunk : 2048;
   if (p->comp_chunk != 1024 && p->comp_chunk != 2048 && p->comp_chunk != 4096)
     return fail(GRAFX_EINVAL, "comp_chunk must be 1024, 2048 or 4096");

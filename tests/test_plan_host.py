@@ -106,7 +106,9 @@ def test_error_codes_match_oracle(gx):
 
 def test_bad_options_rejected(gx):
     g = _to_gx(gx, synth.console_cfg1())
-    for kw in (dict(eq_taps=1024), dict(eq_taps=1), dict(eq_fft=3000), dict(comp_chunk=777)):
+    # eq_fft=1024 with 601 taps leaves S = 424 outputs per block < 2H = 600
+    for kw in (dict(eq_taps=1024), dict(eq_taps=1), dict(eq_fft=3000), dict(comp_chunk=777),
+               dict(eq_taps=601, eq_fft=1024)):
         with pytest.raises(gx.GrafxError):
             gx.Plan([g], [4096], **kw)
     with pytest.raises(gx.GrafxError):
