@@ -64,15 +64,27 @@ __device__ __forceinline__ void dl_window(const DevCtx& c, int v, const NodeDev&
   }
 }
 
-constexpr int DL_GROUP = 4;   // taps whose windows are staged in shared memory together
+constexpr int DL_GROUP = 4;                  // taps whose windows are staged together
+constexpr int DL_OPT = 8;                    // consecutive outputs per thread
+constexpr int DL_FT = DL_TILE / DL_OPT;      // threads of the FIR kernels
+constexpr int DL_WL = (DL_TILE + DL_FIR - 1 + 3) & ~3;   // window floats (16-byte rows)
+
+// cp.async of 4 bytes into shared memory; nothing is read (zero written) when !in.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool in) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(in ? 4 : 0) : "memory");
+}
 
 // Forward (ADJ = false) or input adjoint (ADJ = true) of the sparse FIR for one
-// (node, tile, channel) item; 256 threads x 4 consecutive outputs.
+// (node, tile, channel) item; DL_FT threads x DL_OPT consecutive outputs.  The windows of
+// a group of DL_GROUP taps are staged in shared memory while the previous group is
+// computed (cp.async from a single source row; a sum over several rows is staged
+// synchronously), double-buffered.
 template <bool ADJ>
-__global__ void __launch_bounds__(256) k_delay_fir(DevCtx c, int item0, int n_items) {
-  __shared__ float win[DL_GROUP][DL_TILE + DL_FIR - 1];
-  __shared__ float taps[DL_GROUP][DL_FIR];
-  __shared__ int dly[DL_GROUP];
+__global__ void __launch_bounds__(DL_FT) k_delay_fir(DevCtx c, int item0, int n_items) {
+  __shared__ __align__(16) float win[2][DL_GROUP][DL_WL];
+  __shared__ float taps[DL_SLOT_TAPS][DL_FIR];
+  __shared__ int dly[DL_SLOT_TAPS];
   constexpr int H = (DL_FIR - 1) / 2;
   const int ntap = c.dl_taps;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -81,35 +93,62 @@ __global__ void __launch_bounds__(256) k_delay_fir(DevCtx c, int item0, int n_it
     const NodeDev nd = c.nodes[v];
     const float* aux = c.dl_aux + size_t(c.ext[v].z) * 2 * ntap * (DL_FIR + 1) + size_t(ch) * ntap * (DL_FIR + 1);
     const float* single = dl_single_row<ADJ>(c, v);
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    const int i0 = 4 * threadIdx.x;
-    for (int g0 = 0; g0 < ntap; g0 += DL_GROUP) {
+    __syncthreads();   // readers of the previous item's taps and windows are done
+    for (int i = threadIdx.x; i < ntap; i += blockDim.x) dly[i] = int(aux[i * (DL_FIR + 1) + DL_FIR]);
+    for (int i = threadIdx.x; i < ntap * DL_FIR; i += blockDim.x)
+      taps[i / DL_FIR][i % DL_FIR] = aux[(i / DL_FIR) * (DL_FIR + 1) + i % DL_FIR];
+    __syncthreads();
+    // forward: win[k] = u[t0 - d - H + k]; adjoint: win[k] = ybar[t0 + d - H + k]
+    auto stage = [&](int g0, int buf) {
       const int ng = min(DL_GROUP, ntap - g0);
-      __syncthreads();   // readers of the previous group (or item) are done
-      if (threadIdx.x < ng) dly[threadIdx.x] = int(aux[(g0 + threadIdx.x) * (DL_FIR + 1) + DL_FIR]);
-      for (int i = threadIdx.x; i < ng * DL_FIR; i += blockDim.x)
-        taps[i / DL_FIR][i % DL_FIR] = aux[(g0 + i / DL_FIR) * (DL_FIR + 1) + i % DL_FIR];
-      __syncthreads();
       for (int m = 0; m < ng; ++m) {
-        // forward: win[k] = u[t0 - d - H + k]; adjoint: win[k] = ybar[t0 + d - H + k]
-        dl_window<ADJ>(c, v, nd, ch, ADJ ? t0 + dly[m] - H : t0 - dly[m] - H, win[m], single);
-      }
-      __syncthreads();
-      for (int m = 0; m < ng; ++m) {
-        float x[4 + DL_FIR - 1];
-#pragma unroll
-        for (int k = 0; k < 4 + DL_FIR - 1; ++k) x[k] = win[m][i0 + k];
-#pragma unroll
-        for (int jj = 0; jj < DL_FIR; ++jj) {
-          const float cj = taps[m][jj];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[q] += cj * x[q + (ADJ ? jj : DL_FIR - 1 - jj)];
+        const int start = ADJ ? t0 + dly[g0 + m] - H : t0 - dly[g0 + m] - H;
+        if (single) {
+          const float* row = single + size_t(ch) * nd.pitch;
+          for (int i = threadIdx.x; i < DL_TILE + DL_FIR - 1; i += blockDim.x) {
+            const int t = start + i;
+            const bool in = t >= 0 && t < nd.len;
+            cp_async4(&win[buf][m][i], in ? row + t : row, in);
+          }
+        } else {
+          dl_window<ADJ>(c, v, nd, ch, start, win[buf][m], nullptr);
         }
       }
+      cp_async_commit();
+    };
+    stage(0, 0);
+    float acc[DL_OPT];
+#pragma unroll
+    for (int q = 0; q < DL_OPT; ++q) acc[q] = 0.f;
+    const int i0 = DL_OPT * threadIdx.x;
+    for (int g0 = 0, buf = 0; g0 < ntap; g0 += DL_GROUP, buf ^= 1) {
+      if (g0 + DL_GROUP < ntap) stage(g0 + DL_GROUP, buf ^ 1);
+      else cp_async_commit();   // an empty group keeps the wait count uniform
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // this group's windows landed
+      __syncthreads();
+      const int ng = min(DL_GROUP, ntap - g0);
+      for (int m = 0; m < ng; ++m) {
+        constexpr int XL = (DL_OPT + DL_FIR - 1 + 3) & ~3;   // 46 used, read as 12 float4
+        static_assert(XL >= DL_OPT + DL_FIR - 1 && DL_OPT * (DL_FT - 1) + XL <= DL_WL, "window reads in bounds");
+        float x[XL];
+        const float4* w4 = reinterpret_cast<const float4*>(&win[buf][m][i0]);
+#pragma unroll
+        for (int k = 0; k < XL / 4; ++k) {
+          const float4 q4 = w4[k];
+          x[4 * k] = q4.x, x[4 * k + 1] = q4.y, x[4 * k + 2] = q4.z, x[4 * k + 3] = q4.w;
+        }
+#pragma unroll
+        for (int jj = 0; jj < DL_FIR; ++jj) {
+          const float cj = taps[g0 + m][jj];
+#pragma unroll
+          for (int q = 0; q < DL_OPT; ++q) acc[q] += cj * x[q + (ADJ ? jj : DL_FIR - 1 - jj)];
+        }
+      }
+      __syncthreads();   // readers of win[buf] are done before it is staged again
     }
     float* row = (ADJ ? arow_w(c, nd) : yrow_w(c, nd)) + ch * nd.pitch;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < DL_OPT; ++q) {
       const int t = t0 + i0 + q;
       if (t < nd.pitch) row[t] = t < nd.len ? acc[q] : 0.f;
     }
@@ -407,8 +446,8 @@ int launch_delay(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
       if (b <= a) return 0;
       k_delay_design<<<b - a, 128, 0, s>>>(c, a);
       return 1;
-    case 1: if (b > 0) k_delay_fir<false><<<grid_size(b, 4), 256, 0, s>>>(c, a, b); return b > 0;
-    case 2: if (b > 0) k_delay_fir<true><<<grid_size(b, 4), 256, 0, s>>>(c, a, b); return b > 0;
+    case 1: if (b > 0) k_delay_fir<false><<<grid_size(b, 8), DL_FT, 0, s>>>(c, a, b); return b > 0;
+    case 2: if (b > 0) k_delay_fir<true><<<grid_size(b, 8), DL_FT, 0, s>>>(c, a, b); return b > 0;
     case 3: if (b > 0) k_delay_spec<<<grid_size(b, 3), DL_M / 16, sm_fft, s>>>(c, a, b); return b > 0;
     case 4: if (b > 0) k_delay_acc<<<grid_size(b, acc_per_sm), DL_CHUNK * c.dl_P, sm_acc, s>>>(c, a, b); return b > 0;
     case 5: if (b > 0) k_delay_lags<<<grid_size(b, 3), DL_M / 16, sm_fft, s>>>(c, a, b); return b > 0;
