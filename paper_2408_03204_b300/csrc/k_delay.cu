@@ -241,8 +241,10 @@ __global__ void __launch_bounds__(DL_M / 16) k_delay_spec(DevCtx c, int item0, i
 }
 
 // R_p[k] for one node and DL_CHUNK bins, all lag partitions: per channel
-// sum_b X_{b-p}[k] conj(Ybar_b[k]), packed as R_l + i R_r for the joint inverse.
-// Launched with DL_CHUNK * dl_P threads (one per bin and partition).
+// sum_b X_{b-p}[k] conj(Ybar_b[k]), packed as R_l + i R_r for the joint inverse.  The
+// per-channel products of real signals' spectra are conjugate-symmetric, so the work
+// items cover bins 0..M/2 and bin M - k is written from bin k.  Launched with
+// DL_CHUNK * dl_P threads (one per bin and partition).
 __global__ void __launch_bounds__(DL_CHUNK * DL_PMAX) k_delay_acc(DevCtx c, int item0, int n_items) {
   extern __shared__ float2 sm[];
   const int P = c.dl_P;
@@ -277,8 +279,13 @@ __global__ void __launch_bounds__(DL_CHUNK * DL_PMAX) k_delay_acc(DevCtx c, int 
       ar.x += xr.x * yr.x + xr.y * yr.y;
       ar.y += xr.y * yr.x - xr.x * yr.y;
     }
-    // R_l + i R_r
-    c.dl_R[(size_t(e.y) + p) * DL_M + k0 + kk] = make_float2(al.x - ar.y, al.y + ar.x);
+    // R_l + i R_r at k, conj(R_l) + i conj(R_r) at M - k
+    const int k = k0 + kk;
+    float2* R = c.dl_R + (size_t(e.y) + p) * DL_M;
+    if (k <= DL_M / 2) {
+      R[k] = make_float2(al.x - ar.y, al.y + ar.x);
+      if (k > 0 && k < DL_M / 2) R[DL_M - k] = make_float2(al.x + ar.y, ar.x - al.y);
+    }
   }
 }
 

@@ -496,7 +496,8 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
         p->node_ext[v].y = p->node_ext[v].z * p->dl_P;
         for (int32_t w = -p->dl_P; w < nb; ++w) sub[1].push_back({v, w, 0, p->n_dl_slots++});
         for (int32_t b = 0; b < nb; ++b) sub[1].push_back({v, b, 1, p->n_dl_slots++});
-        for (int32_t ck = 0; ck < DL_M / DL_CHUNK; ++ck) sub[2].push_back({v, ck, 0, 0});
+        // bins 0..M/2 (the lag spectra are conjugate-symmetric per channel)
+        for (int32_t ck = 0; ck <= DL_M / 2 / DL_CHUNK; ++ck) sub[2].push_back({v, ck, 0, 0});
         for (int32_t q = 0; q < p->dl_P; ++q) sub[3].push_back({v, q, 0, 0});
         for (int32_t xm = 0; xm < 2 * p->dl_taps; ++xm) sub[4].push_back({v, xm, 0, 0});
       }
