@@ -159,11 +159,16 @@ def fir_centred_adjoint(ybar, h):
 
 
 def fir_centred_taps_grad(u, ybar, H):
-    """dLoss/dh[m] = sum_x sum_t ybar_x[t] u_x[t-m], m in [-H, H]."""
+    """dLoss/dh[m] = sum_x sum_t ybar_x[t] u_x[t-m], m in [-H, H] (zero for |m| >= L:
+    no sample pair is that far apart)."""
     L = u.shape[-1]
     # correlation via a library FFT convolution: c[j] = sum_t ybar[t] u[t - (j - L + 1)]
     c = scipy.signal.fftconvolve(ybar, u[:, ::-1], axes=-1).sum(axis=0)
-    return c[L - 1 - H: L + H]
+    lag = np.arange(-H, H + 1)
+    out = np.zeros(2 * H + 1)
+    ok = np.abs(lag) <= L - 1
+    out[ok] = c[lag[ok] + L - 1]
+    return out
 
 
 def eq_fwd(u, p, N, fs=44100):

@@ -47,7 +47,7 @@ def run_case(graphs, lengths, seed=11, eq_taps=63, linear_loss=True, **kw):
     got_rows = split_rows(out, graphs, lengths)
     Pg = per_graph_params(graphs, P)
     for g, L, src, p, got in zip(graphs, lengths, src_per, Pg, got_rows):
-        want = orr.outputs_of(g.types, orr.render_one_by_one(g.types, g.edges, src[:, :, :L], p, hp))
+        want = orr.outputs_of(g.types, orr.render_one_by_one(g.types, g.edges, src[:, :, :L], p, hp, ports=g.ports))
         assert_out_close(got, want)
     return run, P, src_per, out
 

@@ -116,8 +116,10 @@ def test_eq_band_matrix():
     np.testing.assert_allclose(op.eq_logmag(np.full(8, 6.0), 1023), 6.0 * np.log(10) / 20, atol=1e-14)
 
 
-def test_fir_centred_brute_force(rng):
-    N, L = 9, 30
+@pytest.mark.parametrize("N, L", [(9, 30), (9, 3), (63, 5), (63, 1)])
+def test_fir_centred_brute_force(rng, N, L):
+    """Brute-force sums, including signals shorter than the filter (lags beyond the
+    signal carry no pair of samples)."""
     h = rng.standard_normal(N)
     u = rng.standard_normal((2, L))
     H = (N - 1) // 2
