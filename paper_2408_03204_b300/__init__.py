@@ -55,7 +55,8 @@ class PlanInfo(ctypes.Structure):
                 ("n_type_rows", ctypes.c_int32 * N_TYPES), ("src_elems", ctypes.c_int64),
                 ("out_elems", ctypes.c_int64), ("node_samples", ctypes.c_int64), ("ws_bytes", ctypes.c_size_t),
                 ("eq_fft", ctypes.c_int32), ("comp_chunk", ctypes.c_int32),
-                ("param_cols", ctypes.c_int32 * N_TYPES), ("source_batch", ctypes.c_int32)]
+                ("param_cols", ctypes.c_int32 * N_TYPES), ("source_batch", ctypes.c_int32),
+                ("fused_pairs", ctypes.c_int32)]
 
 
 _lib = None

@@ -312,6 +312,7 @@ int grafx_plan_info(const grafx_plan* p, grafx_plan_info_t* info) {
   info->comp_chunk = p->comp_chunk;
   std::memcpy(info->param_cols, p->pcols, sizeof(info->param_cols));
   info->source_batch = p->source_batch;
+  for (const StepInfo& st : p->steps) info->fused_pairs += st.fuse_next;
   return GRAFX_OK;
 }
 
@@ -442,6 +443,14 @@ static int render_range(grafx_plan* p, const float* sources, float* out, int32_t
   for (int k = first; k < last; ++k) {
     const StepInfo& st = p->steps[k];
     StepRange range("fwd", k, st.type);
+    if (st.fuse_next && k + 1 < last) {   // gain/imager pair: one kernel over step k+1's items
+      const StepInfo& sw = p->steps[k + 1];
+      c.params = p->params[sw.type];
+      c.params2 = p->params[st.type];
+      launches += launch_ew2(false, st.type, sw.type, c, sw.fitem_begin, sw.fitem_count, s);
+      ++k;
+      continue;
+    }
     c.params = p->params[st.type];
     c.pcols = param_cols(p, st.type);
     if (has_design(st.type)) cudaStreamWaitEvent(s, ev_fwd(p, k), 0);
@@ -562,14 +571,37 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
     cudaStreamWaitEvent(side, ev_bwd(p, k), 0);
     used_side = true;
   };
+  auto dparams_of = [&](int type) -> float* {
+    float* d = d_params ? d_params[type] : nullptr;
+    if (d && p->source_batch > 1) d = at<float>(p, p->ws.dgrad) + p->dgrad_off[type];
+    return d;
+  };
   for (int k = last - 1; k >= std::max(first, 1); --k) {
     const StepInfo& st = p->steps[k];
     if (st.type == GRAFX_T_OUT) continue;  // adjoint rows of outputs are d_out itself
     StepRange range("bwd", k, st.type);
+    if (k - 1 >= std::max(first, 1) && p->steps[k - 1].fuse_next) {   // fused gain/imager pair
+      const StepInfo& sv = p->steps[k - 1];
+      c.params = p->params[st.type];
+      c.params2 = p->params[sv.type];
+      launches += launch_ew2(true, sv.type, st.type, c, st.bitem_begin, st.bitem_count, s);
+      float* dw = dparams_of(st.type);
+      float* dv = dparams_of(sv.type);
+      if (dw || dv) to_side(k);
+      if (dw) {
+        c.dparams = dw;
+        launches += launch_ew_finalize(c, st.node_begin, st.node_end, param_cols(p, st.type), side);
+      }
+      if (dv) {
+        c.dparams = dv;
+        launches += launch_ew_finalize(c, sv.node_begin, sv.node_end, param_cols(p, sv.type), side);
+      }
+      --k;
+      continue;
+    }
     c.params = p->params[st.type];
     c.pcols = param_cols(p, st.type);
-    c.dparams = d_params ? d_params[st.type] : nullptr;
-    if (c.dparams && p->source_batch > 1) c.dparams = at<float>(p, p->ws.dgrad) + p->dgrad_off[st.type];
+    c.dparams = dparams_of(st.type);
     switch (st.type) {
       case GRAFX_T_EQ:
         launches += launch_eq(2, c, st.bitem_begin, st.bitem_count, s);

@@ -61,6 +61,7 @@ struct DevCtx {
   float* ybase[3];
   float* abase[3];
   const float* params;  // P[t] of the launched step's type
+  const float* params2; // fused elementwise pairs: P[t] of the first step's type
   float* dparams;       // dLoss/dP[t] (finalize kernels)
   int32_t pcols;
   int32_t eq_taps, eq_H, eq_Hal, eq_fft, eq_step;

@@ -16,9 +16,11 @@ struct Ew {
   // forward: y = f(u) for one quad of both channels
   __device__ static void fwd(const float* p, float4& l, float4& r) {
     if (TYPE == GRAFX_T_GAIN) {
+      // rounded products (never contracted into a following add): a fused pair of steps
+      // rounds exactly where the separate kernels' stored rows do
       float gl = expf(p[0]), gr = expf(p[1]);
-      l = make_float4(gl * l.x, gl * l.y, gl * l.z, gl * l.w);
-      r = make_float4(gr * r.x, gr * r.y, gr * r.z, gr * r.w);
+      l = make_float4(__fmul_rn(gl, l.x), __fmul_rn(gl, l.y), __fmul_rn(gl, l.z), __fmul_rn(gl, l.w));
+      r = make_float4(__fmul_rn(gr, r.x), __fmul_rn(gr, r.y), __fmul_rn(gr, r.z), __fmul_rn(gr, r.w));
     } else if (TYPE == GRAFX_T_IMAGER) {
       // mid = l + r, side = e^{p} (l - r); l' = (mid + side)/2, r' = (mid - side)/2
       float a = expf(p[0]);
@@ -176,6 +178,27 @@ __global__ void __launch_bounds__(256, 4) k_ew_fwd(DevCtx c, int item0, int n_it
   }
 }
 
+// One quad of the backward of a gain or imager: the parameter-gradient terms into acc
+// and ybar (bl, br) replaced by ubar = (df/du)^T ybar, from the input quad (ul, ur);
+// a0, a1 = e^p of the parameters.
+template <int TYPE>
+__device__ __forceinline__ void ew_bwd_quad(float a0, float a1, float4& bl, float4& br, float4 ul, float4 ur,
+                                            float (&acc)[2]) {
+  if (TYPE == GRAFX_T_GAIN) {
+    acc[0] += bl.x * ul.x + bl.y * ul.y + bl.z * ul.z + bl.w * ul.w;
+    acc[1] += br.x * ur.x + br.y * ur.y + br.z * ur.z + br.w * ur.w;
+    bl = make_float4(__fmul_rn(a0, bl.x), __fmul_rn(a0, bl.y), __fmul_rn(a0, bl.z), __fmul_rn(a0, bl.w));
+    br = make_float4(__fmul_rn(a1, br.x), __fmul_rn(a1, br.y), __fmul_rn(a1, br.z), __fmul_rn(a1, br.w));
+  } else if (TYPE == GRAFX_T_IMAGER) {
+    const float4 L = bl, R = br, u0 = ul, u1 = ur;
+    float4 mb = make_float4(0.5f * (L.x + R.x), 0.5f * (L.y + R.y), 0.5f * (L.z + R.z), 0.5f * (L.w + R.w));
+    float4 sb = make_float4(0.5f * (L.x - R.x), 0.5f * (L.y - R.y), 0.5f * (L.z - R.z), 0.5f * (L.w - R.w));
+    acc[0] += sb.x * (u0.x - u1.x) + sb.y * (u0.y - u1.y) + sb.z * (u0.z - u1.z) + sb.w * (u0.w - u1.w);
+    bl = make_float4(mb.x + a0 * sb.x, mb.y + a0 * sb.y, mb.z + a0 * sb.z, mb.w + a0 * sb.w);
+    br = make_float4(mb.x - a0 * sb.x, mb.y - a0 * sb.y, mb.z - a0 * sb.z, mb.w - a0 * sb.w);
+  }
+}
+
 // Backward: ybar = sum of the consumers' input adjoints; ubar = (df/du)^T ybar;
 // parameter-gradient partial of the tile into its own slot (no atomics).
 template <int TYPE>
@@ -225,19 +248,7 @@ __global__ void __launch_bounds__(256, 3) k_ew_bwd(DevCtx c, int item0, int n_it
     for (int q = 0; q < EW_Q; ++q) {
       const int tq = t + 1024 * q;
       if (tq >= nd.len) continue;
-      if (TYPE == GRAFX_T_GAIN) {
-        acc[0] += bl[q].x * ul[q].x + bl[q].y * ul[q].y + bl[q].z * ul[q].z + bl[q].w * ul[q].w;
-        acc[1] += br[q].x * ur[q].x + br[q].y * ur[q].y + br[q].z * ur[q].z + br[q].w * ur[q].w;
-        bl[q] = make_float4(a0 * bl[q].x, a0 * bl[q].y, a0 * bl[q].z, a0 * bl[q].w);
-        br[q] = make_float4(a1 * br[q].x, a1 * br[q].y, a1 * br[q].z, a1 * br[q].w);
-      } else if (TYPE == GRAFX_T_IMAGER) {
-        const float4 L = bl[q], R = br[q], u0 = ul[q], u1 = ur[q];
-        float4 mb = make_float4(0.5f * (L.x + R.x), 0.5f * (L.y + R.y), 0.5f * (L.z + R.z), 0.5f * (L.w + R.w));
-        float4 sb = make_float4(0.5f * (L.x - R.x), 0.5f * (L.y - R.y), 0.5f * (L.z - R.z), 0.5f * (L.w - R.w));
-        acc[0] += sb.x * (u0.x - u1.x) + sb.y * (u0.y - u1.y) + sb.z * (u0.z - u1.z) + sb.w * (u0.w - u1.w);
-        bl[q] = make_float4(mb.x + a0 * sb.x, mb.y + a0 * sb.y, mb.z + a0 * sb.z, mb.w + a0 * sb.w);
-        br[q] = make_float4(mb.x - a0 * sb.x, mb.y - a0 * sb.y, mb.z - a0 * sb.z, mb.w - a0 * sb.w);
-      }
+      ew_bwd_quad<TYPE>(a0, a1, bl[q], br[q], ul[q], ur[q], acc);
       st4(ub + tq, bl[q]);
       st4(ub + nd.pitch + tq, br[q]);
     }
@@ -246,6 +257,93 @@ __global__ void __launch_bounds__(256, 3) k_ew_bwd(DevCtx c, int item0, int n_it
       if (threadIdx.x == 0) c.partial[w.w] = make_float4(a0 * acc[0], a1 * acc[1], 0.f, 0.f);
       __syncthreads();
     }
+  }
+}
+
+// Fused pair of elementwise steps (the planner's fuse_next): node w of the second step
+// (type TW, parameters c.params) has a single input, node v of the first step (type TV,
+// parameters c.params2), whose only consumer is w.  Forward over w's tiles: u_v
+// gathered once, y_v = f_v(u_v) stored (the row stays valid for every reader), y_w =
+// f_w(y_v) stored.  The same arithmetic as the two separate kernels: bit-identical rows.
+__device__ __forceinline__ void ew_params(int type, const float* tab, int prow, float (&p)[2]) {
+  p[0] = p[1] = 0.f;
+  if (type == GRAFX_T_GAIN) { p[0] = tab[prow * 2]; p[1] = tab[prow * 2 + 1]; }
+  if (type == GRAFX_T_IMAGER) p[0] = tab[prow];
+}
+
+template <int TV, int TW>
+__global__ void __launch_bounds__(256, 4) k_ew2_fwd(DevCtx c, int item0, int n_items) {
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int4_ w = c.items[item0 + it];
+    const int nw = w.x, t = w.y + 4 * threadIdx.x;
+    const NodeDev ndw = c.nodes[nw];
+    const int nv = c.csr_src[c.csr_ptr[nw]];
+    const NodeDev ndv = c.nodes[nv];
+    float pv[2], pw[2];
+    ew_params(TV, c.params2, ndv.prow, pv);
+    ew_params(TW, c.params, ndw.prow, pw);
+    float* yv = yrow_w(c, ndv);
+    float* yw = yrow_w(c, ndw);
+    float4 l[EW_Q], r[EW_Q];
+    gather_q<false>(c, nv, t, ndv.len, ndv.pitch, l, r);
+#pragma unroll
+    for (int q = 0; q < EW_Q; ++q) {
+      const int tq = t + 1024 * q;
+      if (tq < ndw.len) {
+        Ew<TV>::fwd(pv, l[q], r[q]);
+        st4(yv + tq, l[q]);
+        st4(yv + ndv.pitch + tq, r[q]);
+        Ew<TW>::fwd(pw, l[q], r[q]);
+        st4(yw + tq, l[q]);
+        st4(yw + ndw.pitch + tq, r[q]);
+      }
+    }
+  }
+}
+
+// Backward of a fused pair over w's tiles: ybar_w gathered over w's consumers, u_v
+// over v's inputs, y_v = f_v(u_v) recomputed (equal to the stored row); w's gradient
+// terms and ybar_v = J_w^T ybar_w stay in registers (w's input adjoint row is read by v
+// alone), then v's terms and ubar_v = J_v^T ybar_v go to v's adjoint row.  The tile's
+// partials go to w's slot and to v's slot for the same tile (v's slots are its tiles in
+// order from ext.x).
+template <int TV, int TW>
+__global__ void __launch_bounds__(256, 3) k_ew2_bwd(DevCtx c, int item0, int n_items) {
+  __shared__ float sh[4 * 32];
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int4_ w = c.items[item0 + it];
+    const int nw = w.x, t = w.y + 4 * threadIdx.x;
+    const NodeDev ndw = c.nodes[nw];
+    const int nv = c.csr_src[c.csr_ptr[nw]];
+    const NodeDev ndv = c.nodes[nv];
+    float pv[2], pw[2];
+    ew_params(TV, c.params2, ndv.prow, pv);
+    ew_params(TW, c.params, ndw.prow, pw);
+    const float av0 = expf(pv[0]), av1 = TV == GRAFX_T_GAIN ? expf(pv[1]) : 1.f;
+    const float aw0 = expf(pw[0]), aw1 = TW == GRAFX_T_GAIN ? expf(pw[1]) : 1.f;
+    float4 bl[EW_Q], br[EW_Q], ul[EW_Q], ur[EW_Q];
+    gather_q<true>(c, nw, t, ndw.len, ndw.pitch, bl, br);
+    gather_q<false>(c, nv, t, ndv.len, ndv.pitch, ul, ur);
+    float accw[2] = {0.f, 0.f}, accv[2] = {0.f, 0.f};
+    float* ub = arow_w(c, ndv);
+#pragma unroll
+    for (int q = 0; q < EW_Q; ++q) {
+      const int tq = t + 1024 * q;
+      if (tq >= ndw.len) continue;
+      float4 yl = ul[q], yr = ur[q];
+      Ew<TV>::fwd(pv, yl, yr);   // u_w = y_v
+      ew_bwd_quad<TW>(aw0, aw1, bl[q], br[q], yl, yr, accw);
+      ew_bwd_quad<TV>(av0, av1, bl[q], br[q], ul[q], ur[q], accv);
+      st4(ub + tq, bl[q]);
+      st4(ub + ndv.pitch + tq, br[q]);
+    }
+    float acc[4] = {accw[0], accw[1], accv[0], accv[1]};
+    block_sum<4>(acc, sh);
+    if (threadIdx.x == 0) {
+      c.partial[w.w] = make_float4(aw0 * acc[0], aw1 * acc[1], 0.f, 0.f);
+      c.partial[c.ext[nv].x + w.y / EW_TILE] = make_float4(av0 * acc[2], av1 * acc[3], 0.f, 0.f);
+    }
+    __syncthreads();
   }
 }
 
@@ -293,6 +391,25 @@ static int grid_for(int n_items, int per_sm) {
   }
   return std::max(1, std::min(n_items, sms * per_sm));
 }
+
+int launch_ew2(bool bwd, int tv, int tw, const DevCtx& c, int item0, int n_items, cudaStream_t s) {
+  if (n_items <= 0) return 0;
+  const int g = grid_for(n_items, 8);
+  constexpr int G = GRAFX_T_GAIN, S = GRAFX_T_IMAGER;
+  if (bwd) {
+    if (tv == G && tw == G) k_ew2_bwd<G, G><<<g, 256, 0, s>>>(c, item0, n_items);
+    else if (tv == G) k_ew2_bwd<G, S><<<g, 256, 0, s>>>(c, item0, n_items);
+    else if (tw == G) k_ew2_bwd<S, G><<<g, 256, 0, s>>>(c, item0, n_items);
+    else k_ew2_bwd<S, S><<<g, 256, 0, s>>>(c, item0, n_items);
+  } else {
+    if (tv == G && tw == G) k_ew2_fwd<G, G><<<g, 256, 0, s>>>(c, item0, n_items);
+    else if (tv == G) k_ew2_fwd<G, S><<<g, 256, 0, s>>>(c, item0, n_items);
+    else if (tw == G) k_ew2_fwd<S, G><<<g, 256, 0, s>>>(c, item0, n_items);
+    else k_ew2_fwd<S, S><<<g, 256, 0, s>>>(c, item0, n_items);
+  }
+  return 1;
+}
+
 
 int launch_ew_fwd(int type, const DevCtx& c, int item0, int n_items, cudaStream_t s) {
   if (n_items <= 0) return 0;

@@ -13,6 +13,8 @@ int grid_size(int n_items, int per_sm);
 int launch_ew_fwd(int type, const DevCtx& c, int item0, int n_items, cudaStream_t s);
 int launch_ew_bwd(int type, const DevCtx& c, int item0, int n_items, cudaStream_t s);
 int launch_ew_finalize(const DevCtx& c, int node_begin, int node_end, int cols, cudaStream_t s);
+// fused pair of gain/imager steps (types tv then tw) over the second step's items
+int launch_ew2(bool bwd, int tv, int tw, const DevCtx& c, int item0, int n_items, cudaStream_t s);
 // source batch: dst[i] = sum over the B copies of part[b n + i]
 int launch_fold_copies(const float* part, float* dst, int64_t n, int B, cudaStream_t s);
 
