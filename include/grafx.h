@@ -198,12 +198,14 @@ typedef struct {
   int32_t source_batch;       /* B (1 without a source batch); n_graphs, n_nodes, n_edges,
                                * n_inputs, n_outputs, src_elems, out_elems and node_samples
                                * count all B copies, n_type_rows one copy */
-  int32_t fused_pairs;        /* schedule steps k (gain/imager) fused with step k+1 (gain/imager):
-                               * every node of k+1 has one input, a node of k whose only
-                               * consumer it is.  A render or backprop whose step range holds
-                               * both steps runs them as one kernel (same results, bit for bit;
-                               * the intermediate rows are written forward, the intermediate
-                               * adjoint rows are not); never with checkpointing */
+  int32_t fused_pairs;        /* schedule steps k fused with step k+1: every node of k+1 has one
+                               * input, a node of k whose only consumer it is, and the types are
+                               * gain/imager then gain/imager (forward and backward fused) or gain
+                               * then EQ (the EQ forward applies the gain on load).  A render or
+                               * backprop whose step range holds both steps runs them as one
+                               * kernel (same results, bit for bit; the intermediate rows are
+                               * written forward, the intermediate adjoint rows of a gain/imager
+                               * pair are not); never with checkpointing */
 } grafx_plan_info_t;
 
 int grafx_plan_info(const grafx_plan* p, grafx_plan_info_t* info);

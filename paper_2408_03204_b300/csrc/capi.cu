@@ -312,7 +312,7 @@ int grafx_plan_info(const grafx_plan* p, grafx_plan_info_t* info) {
   info->comp_chunk = p->comp_chunk;
   std::memcpy(info->param_cols, p->pcols, sizeof(info->param_cols));
   info->source_batch = p->source_batch;
-  for (const StepInfo& st : p->steps) info->fused_pairs += st.fuse_next;
+  for (const StepInfo& st : p->steps) info->fused_pairs += st.fuse_next != 0;
   return GRAFX_OK;
 }
 
@@ -443,11 +443,17 @@ static int render_range(grafx_plan* p, const float* sources, float* out, int32_t
   for (int k = first; k < last; ++k) {
     const StepInfo& st = p->steps[k];
     StepRange range("fwd", k, st.type);
-    if (st.fuse_next && k + 1 < last) {   // gain/imager pair: one kernel over step k+1's items
+    if (st.fuse_next && k + 1 < last) {   // fused pair: one kernel over step k+1's items
       const StepInfo& sw = p->steps[k + 1];
       c.params = p->params[sw.type];
       c.params2 = p->params[st.type];
-      launches += launch_ew2(false, st.type, sw.type, c, sw.fitem_begin, sw.fitem_count, s);
+      if (st.fuse_next == 1) {
+        launches += launch_ew2(false, st.type, sw.type, c, sw.fitem_begin, sw.fitem_count, s);
+      } else {   // gain -> EQ: the EQ forward with the gain prologue
+        c.pcols = param_cols(p, sw.type);
+        cudaStreamWaitEvent(s, ev_fwd(p, k + 1), 0);
+        launches += launch_eq(4, c, sw.fitem_begin, sw.fitem_count, s);
+      }
       ++k;
       continue;
     }
@@ -580,7 +586,7 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
     const StepInfo& st = p->steps[k];
     if (st.type == GRAFX_T_OUT) continue;  // adjoint rows of outputs are d_out itself
     StepRange range("bwd", k, st.type);
-    if (k - 1 >= std::max(first, 1) && p->steps[k - 1].fuse_next) {   // fused gain/imager pair
+    if (k - 1 >= std::max(first, 1) && p->steps[k - 1].fuse_next == 1) {   // fused gain/imager pair
       const StepInfo& sv = p->steps[k - 1];
       c.params = p->params[st.type];
       c.params2 = p->params[sv.type];

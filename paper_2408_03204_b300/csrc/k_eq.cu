@@ -171,7 +171,11 @@ __device__ __forceinline__ void eq_store_regs(float* row, const NodeDev& nd, int
   }
 }
 
-template <int M>
+// PRO: the EQ node's single input is a gain node fused into this step (the planner's
+// fuse_next = 2): the window is gathered over the gain's inputs and scaled by its gains
+// (c.params2) on load, and the block's output range [H, H+S) of the gain's row is stored
+// here (every sample once), so the row stays valid for every reader.
+template <int M, bool PRO>
 __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_fwd(DevCtx c, int item0, int n_items) {
   extern __shared__ float2 smem2[];
   float2* b0 = smem2;
@@ -189,7 +193,24 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_fwd(DevCtx c, int item0
     const int ws = -Hal + w.y * S;
     const float* spec = c.eq_spec + size_t(w.z) * eq_spec_stride(M);
     float2 x[16];
-    eq_load_regs<M, false>(c, v, nd, ws, x, false, H, S);
+    if constexpr (PRO) {
+      const int gv = c.csr_src[c.csr_ptr[v]];   // the gain node
+      const NodeDev ng = c.nodes[gv];
+      eq_load_regs<M, false>(c, gv, ng, ws, x, false, H, S);
+      const float gl = expf(c.params2[ng.prow * 2]), gr = expf(c.params2[ng.prow * 2 + 1]);
+      float* yg = yrow_w(c, ng);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        x[m] = make_float2(__fmul_rn(gl, x[m].x), __fmul_rn(gr, x[m].y));   // as the gain kernel rounds
+        const int p = threadIdx.x + (M / 16) * m, t = ws + p;
+        if (p >= H && p < H + S && t >= 0 && t < ng.pitch) {
+          yg[t] = t < ng.len ? x[m].x : 0.f;
+          yg[ng.pitch + t] = t < ng.len ? x[m].y : 0.f;
+        }
+      }
+    } else {
+      eq_load_regs<M, false>(c, v, nd, ws, x, false, H, S);
+    }
     if (even) __syncthreads();
     fft::forward_regs_tw<M>(x, b0, b1, stw, threadIdx.x);
     float2* us = c.eq_uspec + size_t(w.w) * M;   // kept for the backward
@@ -439,7 +460,8 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
   if (!init) {
     cudaFuncSetAttribute(k_eq_spec<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
     cudaFuncSetAttribute(k_eq_gradfft<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
-    cudaFuncSetAttribute(k_eq_fwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sf));
+    cudaFuncSetAttribute(k_eq_fwd<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sf));
+    cudaFuncSetAttribute(k_eq_fwd<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sf));
     cudaFuncSetAttribute(k_eq_bwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sb));
     init = true;
   }
@@ -452,7 +474,9 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
       k_eq_spec<M><<<b - a, T, s1, s>>>(c, a);
       return 2;
     case 1:
-      k_eq_fwd<M><<<grid_size(b, (228 * 1024) / int(sf + 1024)), T, sf, s>>>(c, a, b);
+    case 4:   // 4: with the fused gain prologue
+      if (what == 4) k_eq_fwd<M, true><<<grid_size(b, (228 * 1024) / int(sf + 1024)), T, sf, s>>>(c, a, b);
+      else k_eq_fwd<M, false><<<grid_size(b, (228 * 1024) / int(sf + 1024)), T, sf, s>>>(c, a, b);
       return 1;
     case 2:
       k_eq_bwd<M><<<grid_size(b, (228 * 1024) / int(sb + 1024)), T, sb, s>>>(c, a, b);
@@ -468,9 +492,10 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
   return 0;
 }
 
-// what: 0 design(node range), 1 fwd(items), 2 bwd(items), 3 finalize(node range)
+// what: 0 design(node range), 1 fwd(items), 2 bwd(items), 3 finalize(node range),
+// 4 fwd(items) with the fused gain prologue
 int launch_eq(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
-  if (what >= 0 && (b <= 0 || ((what == 0 || what == 3) && b <= a))) return 0;
+  if (what >= 0 && (b <= 0 || ((what == 0 || what == 3) && b <= a))) return 0;   // what 4: fwd + gain prologue
   switch (c.eq_fft) {
     case 1024: return eq_launch<1024>(what, c, a, b, s);
     case 2048: return eq_launch<2048>(what, c, a, b, s);

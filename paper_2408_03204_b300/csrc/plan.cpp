@@ -302,17 +302,21 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
   // (its forward value is needed when a later segment is recomputed or run); all other
   // rows of a segment share one scratch region, reused by every segment.  The backward
   // pass recomputes each earlier segment's forward before its own steps.
-  // ---- fusable elementwise step pairs (k, k+1): both gain/imager, every node w of step
-  // k+1 has one in-edge, from a node v of step k whose only consumer is w, and the node
-  // counts agree (so the map is a bijection).  Not with checkpointing (a pair could
-  // straddle a segment).  A fused backward writes a_v while it reads the adjoints of w's
-  // consumers, so a_v's life starts at step k+1's backward (below).
+  // ---- fusable step pairs (k, k+1): every node w of step k+1 has one in-edge, from a
+  // node v of step k whose only consumer is w, and the node counts agree (so the map is a
+  // bijection).  Both gain/imager: fused forward and backward (fuse 1); gain then EQ: the
+  // EQ forward applies the gain on load (fuse 2, backward unfused).  Not with
+  // checkpointing (a pair could straddle a segment).  A fused backward writes a_v while
+  // it reads the adjoints of w's consumers, so a_v's life starts at step k+1's backward
+  // (below).
   std::vector<int8_t> fuse(N + 1, 0);
   {
     auto pointwise = [](int t) { return t == GRAFX_T_GAIN || t == GRAFX_T_IMAGER; };
     for (int32_t k = 1; opts.checkpoint_steps == 0 && k + 1 < N; ++k) {
       const int32_t a0 = p->step_ptr[k], a1 = p->step_ptr[k + 1], b0 = p->step_ptr[k + 1], b1 = p->step_ptr[k + 2];
-      if (!pointwise(p->sched.string[k]) || !pointwise(p->sched.string[k + 1]) || a1 - a0 != b1 - b0) continue;
+      const int32_t ta = p->sched.string[k], tb = p->sched.string[k + 1];
+      const int8_t kind = pointwise(ta) && pointwise(tb) ? 1 : (ta == GRAFX_T_GAIN && tb == GRAFX_T_EQ ? 2 : 0);
+      if (!kind || a1 - a0 != b1 - b0) continue;
       bool ok = true;
       for (int32_t w = b0; ok && w < b1; ++w) {
         ok = p->csr_ptr[w + 1] - p->csr_ptr[w] == 1;
@@ -321,7 +325,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
         ok = v >= a0 && v < a1 && p->tcsr_ptr[v + 1] - p->tcsr_ptr[v] == 1;
       }
       if (ok) {
-        fuse[k] = 1;
+        fuse[k] = kind;
         ++k;   // a fused pair does not chain into a third step
       }
     }
@@ -342,7 +346,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
       int32_t lo = step_of[v];
       for (int32_t e = p->csr_ptr[v]; e < p->csr_ptr[v + 1]; ++e) lo = std::min(lo, step_of[p->csr_src[e]]);
       // one adjoint row per input port; a fused pair's first node is written one step early
-      const int32_t written = fuse[step_of[v]] ? step_of[v] + 1 : step_of[v];
+      const int32_t written = fuse[step_of[v]] == 1 ? step_of[v] + 1 : step_of[v];
       lives.push_back({N - written, N - lo, v, int64_t(type_inputs(p->nodes[v].type)) * p->nodes[v].rstride});
     }
     std::stable_sort(lives.begin(), lives.end(), [](const Live& a, const Live& b) { return a.start < b.start; });

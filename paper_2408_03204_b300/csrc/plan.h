@@ -45,8 +45,10 @@ struct StepInfo {
   int32_t fitem_begin, fitem_count;  // forward work items (global index)
   int32_t bitem_begin, bitem_count;  // backward work items (global index)
   int32_t dsub_begin[5], dsub_count[5];  // delay backward sub-lists: adjoint, spectra, acc, lags, grads
-  // gain/imager step whose every node feeds exactly one node of the next step (also
-  // gain/imager, each with that single input): the two steps run as one fused kernel
+  // 1: gain/imager step whose every node feeds exactly one node of the next step (also
+  // gain/imager, each with that single input): the two steps run as one fused kernel;
+  // 2: gain step whose every node is the single input of one EQ node of the next step,
+  // and feeds only it: the EQ forward applies the gain on load (backward unfused)
   int32_t fuse_next = 0;
 };
 

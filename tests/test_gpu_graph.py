@@ -73,9 +73,9 @@ def test_autotuner_picks_valid_tiles(tmp_path):
 
 
 def test_fused_step_pair_matches_step_by_step():
-    """The nested console's imager -> gain steps run fused in a whole render and backprop;
-    one step at a time they run unfused.  Outputs, parameter gradients and source
-    adjoints agree bit for bit."""
+    """The nested console's gain -> EQ and imager -> gain steps run fused in a whole render
+    and backprop; one step at a time they run unfused.  Outputs, parameter gradients and
+    source adjoints agree bit for bit."""
     import torch
     import paper_2408_03204_b300 as gx
     g = synth.console_cfg2()
@@ -84,7 +84,7 @@ def test_fused_step_pair_matches_step_by_step():
     P = union_params([g], 3)
     run = GpuRun([g], [L], P, src_flat, eq_taps=255)
     plan = run.plan
-    assert plan.info.fused_pairs == 1
+    assert plan.info.fused_pairs == 2
     N = plan.info.n_steps
     st = gx._stream(torch, run.src.device)
     out_f = torch.empty(plan.info.out_elems, device="cuda")
