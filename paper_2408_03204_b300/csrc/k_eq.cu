@@ -67,47 +67,46 @@ __host__ __device__ constexpr int eq_spec_stride(int M) { return M / 2 + 4; }
 
 constexpr int EQ_SPLIT = 4;    // lanes sharing one cosine sum (adjacent lanes of a warp)
 
-// h[n] = Hann[n] (A_0 + 2 sum_{k>=1} A_k cos(2 pi k n / N)) / N for one chunk of n in
-// [0, H] (the taps are even, h[-n] = h[n]); grid (EQ nodes of the step, chunks).  The
-// sum over k is split over EQ_SPLIT lanes (k = 1 + part + EQ_SPLIT j) and combined by
-// shuffles in a fixed order.
-__global__ void __launch_bounds__(EQ_CHUNK * EQ_SPLIT) k_eq_taps(DevCtx c, int node_begin) {
+// The filter design of one EQ node in one CTA (M/16 threads): A_k, then the even taps
+// h[n] = Hann[n] (A_0 + 2 sum_{k>=1} A_k cos(2 pi k n / N)) / N for n in [0, H] (Eq. 4;
+// the cosine indexed exactly by (k n) mod N), placed circularly (real, even) and scaled
+// by 1/M, then the block spectrum by the FFT.  Parameter only: it runs on the side stream
+// from the start of the render.
+template <int M>
+__global__ void __launch_bounds__(M / 16) k_eq_design(DevCtx c, int node_begin) {
+  extern __shared__ float2 smem2[];
+  float2* buf = smem2;
   __shared__ float A[1024];
   __shared__ float cs[2048];
+  __shared__ float hs[1024];
   const int v = node_begin + blockIdx.x;
   const NodeDev nd = c.nodes[v];
   const int N = c.eq_taps, H = c.eq_H, K = (N + 1) / 2;
   eq_magnitudes(c, nd, A, K);
   for (int i = threadIdx.x; i < N; i += blockDim.x) cs[i] = c.eq_cos[i];
   __syncthreads();
-  const int n = blockIdx.y * EQ_CHUNK + threadIdx.x / EQ_SPLIT, part = threadIdx.x % EQ_SPLIT;
-  float s = 0.f;
-  if (n <= H) {
-    const int step = (EQ_SPLIT * n) % N;
-    int idx = ((1 + part) * n) % N;  // (k n) mod N
-    for (int k = 1 + part; k < K; k += EQ_SPLIT) {
-      s += A[k] * cs[idx];
+  for (int n = threadIdx.x; n <= H; n += blockDim.x) {
+    float s0 = 0.f, s1 = 0.f;   // two interleaved partial sums (odd and even k)
+    int idx = n % N;            // (k n) mod N for k = 1
+    const int step = (2 * n) % N;
+    int idx2 = (2 * n) % N;     // k = 2
+    int k = 1;
+    for (; k + 1 < K; k += 2) {
+      s0 += A[k] * cs[idx];
+      s1 += A[k + 1] * cs[idx2];
       idx += step;
       if (idx >= N) idx -= N;
+      idx2 += step;
+      if (idx2 >= N) idx2 -= N;
     }
+    if (k < K) s0 += A[k] * cs[idx];
+    hs[n] = c.eq_hann[n] * (A[0] + 2.f * (s0 + s1)) / float(N);
   }
-  s += __shfl_xor_sync(0xffffffffu, s, 1);
-  s += __shfl_xor_sync(0xffffffffu, s, 2);
-  if (part == 0 && n <= H) c.eq_aux[size_t(c.ext[v].z) * 1024 + n] = c.eq_hann[n] * (A[0] + 2.f * s) / float(N);
-}
-
-// The block spectrum of h placed circularly (real, even), scaled by 1/M.
-template <int M>
-__global__ void __launch_bounds__(M / 16) k_eq_spec(DevCtx c, int node_begin) {
-  extern __shared__ float2 smem2[];
-  float2* buf = smem2;
-  const int v = node_begin + blockIdx.x;
-  const int H = c.eq_H;
-  const float* h = c.eq_aux + size_t(c.ext[v].z) * 1024;
+  __syncthreads();
   const float inv_m = 1.f / float(M);
   for (int m = threadIdx.x; m < M; m += blockDim.x) {
-    int a = m <= M / 2 ? m : M - m;    // circular position -> |tap index|
-    buf[fft::pad(m)] = make_float2(a <= H ? h[a] * inv_m : 0.f, 0.f);
+    const int a = m <= M / 2 ? m : M - m;    // circular position -> |tap index|
+    buf[fft::pad(m)] = make_float2(a <= H ? hs[a] * inv_m : 0.f, 0.f);
   }
   __syncthreads();
   fft::forward<M>(buf, c.ptw, threadIdx.x, true);
@@ -458,7 +457,7 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
   // two FFT buffers, the kept spectrum, the previous block's tail (2H floats, H <= M/4)
   const size_t sb = 2 * s1 + sizeof(float2) * M + sizeof(float) * M / 2;
   if (!init) {
-    cudaFuncSetAttribute(k_eq_spec<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
+    cudaFuncSetAttribute(k_eq_design<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
     cudaFuncSetAttribute(k_eq_gradfft<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
     cudaFuncSetAttribute(k_eq_fwd<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sf));
     cudaFuncSetAttribute(k_eq_fwd<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sf));
@@ -466,13 +465,11 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
     init = true;
   }
   if (what < 0) return 0;  // attributes only (before a stream capture)
-  const int chunks_h = (c.eq_H + 1 + EQ_CHUNK - 1) / EQ_CHUNK;
   const int chunks_k = ((c.eq_taps + 1) / 2 + EQ_CHUNK - 1) / EQ_CHUNK;
   switch (what) {
     case 0:
-      k_eq_taps<<<dim3(b - a, chunks_h), EQ_CHUNK * EQ_SPLIT, 0, s>>>(c, a);
-      k_eq_spec<M><<<b - a, T, s1, s>>>(c, a);
-      return 2;
+      k_eq_design<M><<<b - a, T, s1, s>>>(c, a);
+      return 1;
     case 1:
     case 4:   // 4: with the fused gain prologue
       if (what == 4) k_eq_fwd<M, true><<<grid_size(b, (228 * 1024) / int(sf + 1024)), T, sf, s>>>(c, a, b);
