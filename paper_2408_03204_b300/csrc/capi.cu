@@ -74,6 +74,7 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
   c.rv_mm = at<float2>(p, p->ws.rv_mm);
   c.rv_nbmax = p->rv_nbmax;
   c.bal = at<float>(p, p->ws.bal);
+  c.bal_maxlen = int32_t(p->L.empty() ? 0 : *std::max_element(p->L.begin(), p->L.end()));
   c.partial = at<float4>(p, p->ws.partial);
   c.eq_partial = at<float2>(p, p->ws.eq_partial);
   c.eq_uspec = at<float2>(p, p->ws.eq_uspec);

@@ -56,6 +56,7 @@ struct DevCtx {
   float2* rv_mm;          // per reverb node: mask-gradient terms [rv_f][2][rv_n/2+1]
   int32_t rv_nbmax;
   float* bal;            // per ballistic node: mid, envelope, envelope-adjoint and coefficient rows
+  int32_t bal_maxlen;    // the longest signal of the plan (grids of the ballistic chunk kernels)
   float4* partial;
   float2* eq_partial;
   float* ybase[3];

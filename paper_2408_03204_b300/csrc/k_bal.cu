@@ -1,15 +1,16 @@
 // Compressor with attack/release ballistics (Sec. 3, Eq. 8 with alpha[n] = alpha_attack
 // while the envelope rises, x[n] > g[n-1], and alpha_release while it falls; Eq. 9-12 for
-// the rest).  The coefficient depends on the state, so the recursion has no associative
-// form to scan: it runs sample by sample, one warp per node (lane 0 runs the recursion on
-// a 512-sample block in shared memory while the warp's loads of the next block are in
-// flight).  Everything else is per sample and runs as tiles over all nodes:
-//   forward:  k_bal_mid (u -> the mid m = l + r into scratch), k_bal_env (serial g),
-//             k_bal_gain (gain from g, y = gain u);
+// the rest).  The coefficient depends on the state, so the recursion is not a linear
+// scan; it is a composition of max (or min) of two affine maps, which stays a max of
+// affine maps over a chunk: the forward composes 64-sample chunks in parallel, walks the
+// chunk starts serially (one reduction per chunk) and re-runs every chunk from its start
+// in parallel.  Everything else is per sample and runs as tiles over all nodes:
+//   forward:  k_bal_mid (u -> the mid m = l + r into scratch), k_bal_maps, k_bal_starts
+//             and k_bal_run (g by chunk maps, below), k_bal_gain (gain from g, y = gain u);
 //   backward: k_bal_adj (ybar, u, g -> the main adjoint gain ybar, the envelope adjoint
 //             a[n] = dL/dg[n], the coefficient alpha[n] of each step and the T, W, R
-//             partials per tile), k_bal_rev (serial lambda[n] = a[n] + alpha[n+1]
-//             lambda[n+1] in place: one FMA per sample), k_bal_in (adds
+//             partials per tile), k_bal_rev (lambda[n] = a[n] + alpha[n+1] lambda[n+1] in
+//             place, a warp scan of affine maps), k_bal_in (adds
 //             2 m (1 - alpha[n]) lambda[n] to both channels' adjoint; the attack and
 //             release gradient partials per tile), k_bal_fin (parameter gradients).
 // Per node the scratch holds four rows of pitch floats (rounded up to 64): the mid, the
@@ -21,8 +22,7 @@
 namespace grafx {
 
 constexpr float BAL_EPS = 1e-7f;
-constexpr int BAL_BLOCK = 512;   // samples per block of the serial kernels
-constexpr int BAL_PT = BAL_BLOCK / 32;
+constexpr int BAL_BLOCK = 512;   // samples per block of the reverse scan
 
 __device__ __forceinline__ int bal_rs(const NodeDev& nd) { return (nd.pitch + 63) & ~63; }
 __device__ __forceinline__ float* bal_row(const DevCtx& c, int v, const NodeDev& nd, int i) {
@@ -71,81 +71,180 @@ __global__ void __launch_bounds__(256) k_bal_mid(DevCtx c, int item0, int n_item
   }
 }
 
-// One block of the envelope recursion on lane 0, from the previous envelope value.  Both
-// candidate steps are continuous in g[n-1] and meet at x, so the branch of Eq. 8 is the
-// larger candidate when the attack coefficient is the smaller one (attack: both below x,
-// the attack step nearer; release: both above x, the release step nearer) and the smaller
-// one otherwise: a max (or min) replaces the compare and select on the serial chain.
-// Groups of 8 samples in registers, the next group's loads issued before this group's chain.
-template <bool ATTACK_FASTER>
-__device__ __forceinline__ float bal_env_block(const float* xs, float* gs, int n, float aa, float ar, float prev) {
-  const float4* xb = reinterpret_cast<const float4*>(xs);
-  float4* gb = reinterpret_cast<float4*>(gs);
-  const float ba = 1.f - aa, br = 1.f - ar;
-  const int ng = (n + 7) / 8;   // zero-filled past len
-  float4 n0 = xb[0], n1 = xb[1];
-  for (int q = 0; q < ng; ++q) {
-    const float m[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
-    if (q + 1 < ng) {
-      n0 = xb[2 * q + 2];
-      n1 = xb[2 * q + 3];
-    }
-    float o[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float x = m[j] * m[j];
-      const float ga = fmaf(aa, prev, ba * x), gr = fmaf(ar, prev, br * x);
-      prev = ATTACK_FASTER ? fmaxf(ga, gr) : fminf(ga, gr);
-      o[j] = prev;
-    }
-    gb[2 * q] = make_float4(o[0], o[1], o[2], o[3]);
-    gb[2 * q + 1] = make_float4(o[4], o[5], o[6], o[7]);
-  }
-  return prev;
+// The envelope recursion in parallel.  With the larger candidate taken when the attack
+// is the faster coefficient (the smaller one otherwise; the two candidate steps meet at
+// x, so this is the branch of Eq. 8), one step is the map
+//   F_t(g) = OP(aa g + (1 - aa) x_t, ar g + (1 - ar) x_t),  OP = max (aa <= ar) or min,
+// and since both slopes are positive, a chunk of n steps composes to
+//   F(g) = OP_k (s_k g + c_k),  s_k = aa^k ar^(n-k),  k = number of attack steps,
+// with c_k the OP over the paths with k attacks of their intercepts, found by the
+// dynamic programme c'_k = OP(aa c_{k-1} + (1-aa) x, ar c_k + (1-ar) x) (c_0 = 0 and the
+// others +-inf at the start).  The forward runs in three kernels: the programme for every
+// BAL_N-sample chunk (one warp per chunk), the chunk starts g_in (one warp per node,
+// serial over chunks, OP of the lines by a warp reduction), and the recursion inside
+// every chunk from its start (one thread per chunk).
+constexpr int BAL_N = 64;                  // samples per chunk
+constexpr int BAL_L = BAL_N + 1;           // lines per chunk map
+__device__ __forceinline__ int bal_chunks(const NodeDev& nd) { return (nd.len + BAL_N - 1) / BAL_N; }
+// chunk maps (intercepts, BAL_L per chunk) then the chunk starts, in the node's adjoint
+// and coefficient rows (free during the forward): 66 floats per chunk <= 2 rows
+__device__ __forceinline__ float* bal_maps(const DevCtx& c, int v, const NodeDev& nd) { return bal_row(c, v, nd, 2); }
+__device__ __forceinline__ float* bal_starts(const DevCtx& c, int v, const NodeDev& nd) {
+  return bal_row(c, v, nd, 2) + size_t(BAL_L) * bal_chunks(nd);
 }
 
-// forward, serial per node: g[n] = x + alpha (g[n-1] - x), x = m^2, alpha by the branch
-__global__ void __launch_bounds__(32) k_bal_env(DevCtx c, int node_begin) {
-  __shared__ __align__(16) float xs[2][BAL_BLOCK];
-  __shared__ __align__(16) float gs[BAL_BLOCK];
+template <bool MAX>
+__device__ __forceinline__ float bal_op(float a, float b) { return MAX ? fmaxf(a, b) : fminf(a, b); }
+
+// forward 1: the chunk maps.  Lane l holds c_{2l}, c_{2l+1} (lane 31 also c_64); the
+// attack step from c_{2l-1} comes from lane l-1.  Samples past len are taken as 0 (only
+// the last chunk has them, and its map is not used).
+template <bool MAX>
+__device__ void bal_chunk_map(const DevCtx& c, int v, const NodeDev& nd, int ck, float aa, float ar, float* xs) {
+  const int lane = threadIdx.x & 31;
+  const float* X = bal_row(c, v, nd, 0);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int t = ck * BAL_N + lane + 32 * i;
+    const float m = t < nd.len ? X[t] : 0.f;
+    xs[lane + 32 * i] = m * m;
+  }
+  __syncwarp();
+  const float unreach = MAX ? -INFINITY : INFINITY;
+  const float ba = 1.f - aa, br = 1.f - ar;
+  float c0 = lane == 0 ? 0.f : unreach, c1 = unreach, c64 = unreach;
+  for (int t = 0; t < BAL_N; ++t) {
+    const float x = xs[t];
+    const float ax = ba * x, rx = br * x;
+    float lo = __shfl_up_sync(0xffffffffu, c1, 1);   // c_{2l-1}
+    if (lane == 0) lo = unreach;
+    const float n0 = bal_op<MAX>(fmaf(aa, lo, ax), fmaf(ar, c0, rx));
+    const float n1 = bal_op<MAX>(fmaf(aa, c0, ax), fmaf(ar, c1, rx));
+    const float n64 = bal_op<MAX>(fmaf(aa, c1, ax), fmaf(ar, c64, rx));   // used by lane 31
+    c0 = n0;
+    c1 = n1;
+    c64 = n64;
+  }
+  float* out = bal_maps(c, v, nd) + size_t(ck) * BAL_L;
+  out[2 * lane] = c0;
+  out[2 * lane + 1] = c1;
+  if (lane == 31) out[BAL_N] = c64;
+}
+
+// grid (ceil(max chunks / 8), ballistic nodes of the step), 8 warps: one chunk each
+__global__ void __launch_bounds__(256) k_bal_maps(DevCtx c, int node_begin) {
+  __shared__ float xs[8][BAL_N];
+  const int v = node_begin + blockIdx.y;
+  const NodeDev nd = c.nodes[v];
+  const int ck = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (ck >= bal_chunks(nd)) return;   // whole warps leave together
+  const float* p = c.params + size_t(nd.prow) * 5;
+  const float aa = p[0], ar = p[1];
+  if (aa <= ar) bal_chunk_map<true>(c, v, nd, ck, aa, ar, xs[threadIdx.x >> 5]);
+  else bal_chunk_map<false>(c, v, nd, ck, aa, ar, xs[threadIdx.x >> 5]);
+}
+
+// forward 2: one warp per node, serial over chunks: g_in of chunk 0 is 0, then
+// g_in(c+1) = OP_k (s_k g_in(c) + c_k(c)); every line value is >= 0 (or unreachable), so
+// the warp's OP reduces the float bit patterns as unsigned integers.  The slopes are
+// formed once in double.  The chunk maps stream through shared memory in batches of
+// BAL_BB chunks, a ring of BAL_ST batches in flight (cp.async), so the serial chain waits
+// on shared-memory loads only.
+constexpr int BAL_BB = 32, BAL_ST = 3;
+
+template <bool MAX>
+__device__ void bal_chunk_starts(const DevCtx& c, int v, const NodeDev& nd, float aa, float ar, float (*sm)[BAL_BB * BAL_L]) {
+  const int lane = threadIdx.x;
+  const int nck = bal_chunks(nd), nbat = (nck + BAL_BB - 1) / BAL_BB;
+  const float* maps = bal_maps(c, v, nd);
+  float* starts = bal_starts(c, v, nd);
+  float sl[3];
+  const int ks[3] = {2 * lane, 2 * lane + 1, BAL_N};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) sl[i] = float(pow(double(aa), ks[i]) * pow(double(ar), BAL_N - ks[i]));
+  const float unreach = MAX ? -INFINITY : INFINITY;
+  auto issue = [&](int b) {   // batch b's maps (chunks past the last read as nothing)
+    if (b < nbat) {
+      const int nfl = min(BAL_BB, nck - b * BAL_BB) * BAL_L;   // floats that exist
+      const float* src = maps + size_t(b) * BAL_BB * BAL_L;   // 16-byte aligned: 32 x 65 x 4 B
+      float* dst = sm[b % BAL_ST];
+      for (int i = lane; i < BAL_BB * BAL_L / 4; i += 32) {
+        const int n = max(0, min(4, nfl - 4 * i));
+        cp_async16(dst + 4 * i, n ? src + 4 * i : src, 4 * n);
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int b = 0; b < BAL_ST - 1; ++b) issue(b);
+  float g = 0.f;
+  for (int b = 0; b < nbat; ++b) {
+    issue(b + BAL_ST - 1);
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(BAL_ST - 1) : "memory");   // batch b landed
+    __syncwarp();
+    const float* m = sm[b % BAL_ST];
+    const int nj = min(BAL_BB, nck - b * BAL_BB);
+#pragma unroll 4
+    for (int j = 0; j < nj; ++j) {
+      const int ck = b * BAL_BB + j;
+      if (lane == 0) starts[ck] = g;
+      if (ck + 1 == nck) break;
+      const float* mj = m + j * BAL_L;
+      const float c0 = mj[2 * lane], c1 = mj[2 * lane + 1], c2 = lane == 31 ? mj[BAL_N] : unreach;
+      float best = bal_op<MAX>(fmaf(sl[0], g, c0), fmaf(sl[1], g, c1));
+      best = bal_op<MAX>(best, fmaf(sl[2], g, c2));
+      const unsigned u = __float_as_uint(MAX ? fmaxf(best, 0.f) : best);
+      g = __uint_as_float(MAX ? __reduce_max_sync(0xffffffffu, u) : __reduce_min_sync(0xffffffffu, u));
+    }
+    __syncwarp();   // every lane is done with this stage before it is staged again
+  }
+  cp_async_wait_all();
+}
+
+__global__ void __launch_bounds__(32) k_bal_starts(DevCtx c, int node_begin) {
+  __shared__ __align__(16) float sm[BAL_ST][BAL_BB * BAL_L];
   const int v = node_begin + blockIdx.x;
   const NodeDev nd = c.nodes[v];
   const float* p = c.params + size_t(nd.prow) * 5;
   const float aa = p[0], ar = p[1];
+  if (aa <= ar) bal_chunk_starts<true>(c, v, nd, aa, ar, sm);
+  else bal_chunk_starts<false>(c, v, nd, aa, ar, sm);
+}
+
+// forward 3: one thread per chunk: the recursion of Eq. 8 over the chunk's samples from
+// its start, written to the envelope row.  grid (ceil(max chunks / 128), nodes), 128
+// threads.
+template <bool MAX>
+__device__ void bal_chunk_run(const DevCtx& c, int v, const NodeDev& nd, int ck, float aa, float ar) {
   const float* X = bal_row(c, v, nd, 0);
   float* G = bal_row(c, v, nd, 1);
-  const int nb = (nd.len + BAL_BLOCK - 1) / BAL_BLOCK;
-  const int lane = threadIdx.x;
-  float reg[BAL_PT];
-  // block 0 into shared memory
+  const float ba = 1.f - aa, br = 1.f - ar;
+  float g = bal_starts(c, v, nd)[ck];
+  const int t0 = ck * BAL_N, n = min(BAL_N, nd.len - t0);
+  for (int q = 0; q < BAL_N / 4; ++q) {
+    if (4 * q >= n) break;
+    const float4 m4 = ld4(X + t0 + 4 * q);   // rows are 64-float aligned; X is 0 past len
+    const float m[4] = {m4.x, m4.y, m4.z, m4.w};
+    float o[4];
 #pragma unroll
-  for (int i = 0; i < BAL_PT; ++i) {
-    const int t = lane + 32 * i;
-    xs[0][lane + 32 * i] = t < nd.len ? X[t] : 0.f;
+    for (int j = 0; j < 4; ++j) {
+      const float x = m[j] * m[j];
+      g = bal_op<MAX>(fmaf(aa, g, ba * x), fmaf(ar, g, br * x));
+      o[j] = g;
+    }
+    st4(G + t0 + 4 * q, make_float4(o[0], o[1], o[2], o[3]));
   }
-  __syncwarp();
-  float prev = 0.f;
-  for (int b = 0; b < nb; ++b) {
-    // loads of block b + 1 issued before the serial part
-#pragma unroll
-    for (int i = 0; i < BAL_PT; ++i) {
-      const int t = (b + 1) * BAL_BLOCK + lane + 32 * i;
-      reg[i] = t < nd.len ? X[t] : 0.f;
-    }
-    if (lane == 0) {
-      const int n = min(BAL_BLOCK, nd.len - b * BAL_BLOCK);
-      prev = aa <= ar ? bal_env_block<true>(xs[b & 1], gs, n, aa, ar, prev)
-                      : bal_env_block<false>(xs[b & 1], gs, n, aa, ar, prev);
-    }
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < BAL_PT; ++i) {
-      const int t = b * BAL_BLOCK + lane + 32 * i;
-      if (t < nd.len) G[t] = gs[lane + 32 * i];
-      xs[(b + 1) & 1][lane + 32 * i] = reg[i];
-    }
-    __syncwarp();
-  }
+}
+
+__global__ void __launch_bounds__(128) k_bal_run(DevCtx c, int node_begin) {
+  const int v = node_begin + blockIdx.y;
+  const NodeDev nd = c.nodes[v];
+  const int ck = blockIdx.x * 128 + threadIdx.x;
+  if (ck >= bal_chunks(nd)) return;
+  const float* p = c.params + size_t(nd.prow) * 5;
+  const float aa = p[0], ar = p[1];
+  if (aa <= ar) bal_chunk_run<true>(c, v, nd, ck, aa, ar);
+  else bal_chunk_run<false>(c, v, nd, ck, aa, ar);
 }
 
 // forward, per tile: y = exp(Gy - Gu) u with Gu = ln(g + eps)
@@ -361,9 +460,12 @@ int launch_bal_fwd(const DevCtx& c, int item0, int n_items, int node_begin, int 
   if (n_items <= 0 || node_end <= node_begin) return 0;
   const int g = grid_size(n_items, 8);
   k_bal_mid<<<g, 256, 0, s>>>(c, item0, n_items);
-  k_bal_env<<<node_end - node_begin, 32, 0, s>>>(c, node_begin);
+  const int nb = node_end - node_begin, mck = (c.bal_maxlen + BAL_N - 1) / BAL_N;
+  k_bal_maps<<<dim3((mck + 7) / 8, nb), 256, 0, s>>>(c, node_begin);
+  k_bal_starts<<<nb, 32, 0, s>>>(c, node_begin);
+  k_bal_run<<<dim3((mck + 127) / 128, nb), 128, 0, s>>>(c, node_begin);
   k_bal_gain<<<g, 256, 0, s>>>(c, item0, n_items);
-  return 3;
+  return 5;
 }
 
 int launch_bal_bwd(const DevCtx& c, int item0, int n_items, int node_begin, int node_end, cudaStream_t s) {
