@@ -16,6 +16,8 @@
 // Per node the scratch holds four rows of pitch floats (rounded up to 64): the mid, the
 // envelope, the envelope adjoint and the per-step coefficient.  Backward tiles own two
 // partial slots (T, W, R and attack, release).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -460,12 +462,17 @@ int launch_bal_fwd(const DevCtx& c, int item0, int n_items, int node_begin, int 
   if (n_items <= 0 || node_end <= node_begin) return 0;
   const int g = grid_size(n_items, 8);
   k_bal_mid<<<g, 256, 0, s>>>(c, item0, n_items);
-  const int nb = node_end - node_begin, mck = (c.bal_maxlen + BAL_N - 1) / BAL_N;
-  k_bal_maps<<<dim3((mck + 7) / 8, nb), 256, 0, s>>>(c, node_begin);
-  k_bal_starts<<<nb, 32, 0, s>>>(c, node_begin);
-  k_bal_run<<<dim3((mck + 127) / 128, nb), 128, 0, s>>>(c, node_begin);
+  const int mck = (c.bal_maxlen + BAL_N - 1) / BAL_N;
+  int launches = 2;
+  for (int n0 = node_begin; n0 < node_end; n0 += 65535) {   // nodes on grid.y
+    const int nb = std::min(65535, node_end - n0);
+    k_bal_maps<<<dim3((mck + 7) / 8, nb), 256, 0, s>>>(c, n0);
+    k_bal_starts<<<nb, 32, 0, s>>>(c, n0);
+    k_bal_run<<<dim3((mck + 127) / 128, nb), 128, 0, s>>>(c, n0);
+    launches += 3;
+  }
   k_bal_gain<<<g, 256, 0, s>>>(c, item0, n_items);
-  return 5;
+  return launches;
 }
 
 int launch_bal_bwd(const DevCtx& c, int item0, int n_items, int node_begin, int node_end, cudaStream_t s) {
