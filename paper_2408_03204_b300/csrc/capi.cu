@@ -72,6 +72,8 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
   c.rv_R = at<float2>(p, p->ws.rv_R);
   c.rv_r = at<float>(p, p->ws.rv_r);
   c.rv_mm = at<float2>(p, p->ws.rv_mm);
+  c.rv_lm = at<float>(p, p->ws.rv_lm);
+  c.rv_dot = at<float>(p, p->ws.rv_dot);
   c.rv_nbmax = p->rv_nbmax;
   c.bal = at<float>(p, p->ws.bal);
   c.bal_maxlen = int32_t(p->L.empty() ? 0 : *std::max_element(p->L.begin(), p->L.end()));

@@ -54,6 +54,8 @@ struct DevCtx {
   float2* rv_R;           // per reverb node: lag partition spectra [RV_P][DL_M]
   float* rv_r;            // per reverb node: lags [2][RV_HLEN]
   float2* rv_mm;          // per reverb node: mask-gradient terms [rv_f][2][rv_n/2+1]
+  float* rv_lm;           // per reverb node (compact layout): [mid, side][H0, Hd][RV_BINS]
+  float* rv_dot;          // per reverb node: sum_n h_x[n] r_x[n] over each lag partition
   int32_t rv_nbmax;
   float* bal;            // per ballistic node: mid, envelope, envelope-adjoint and coefficient rows
   int32_t bal_maxlen;    // the longest signal of the plan (grids of the ballistic chunk kernels)

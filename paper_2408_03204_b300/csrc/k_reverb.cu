@@ -35,23 +35,39 @@ __device__ __forceinline__ void rv_split(float2 z, float2 zm, float2* a, float2*
   *b = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
 }
 
-// M_x[k, m] (Eq. 7) of both channels at bin k and frame m.
-__device__ __forceinline__ void rv_masks(const DevCtx& c, const float* q, int k, int m, float* M) {
+// M_x[k, m] (Eq. 7) of both channels at bin k and frame m of reverb node ri.
+__device__ __forceinline__ void rv_masks(const DevCtx& c, const float* q, int ri, int k, int m, float* M) {
   if (c.rv_paper) {   // per-bin log-magnitudes on bins 0..K-1; the Nyquist bin K is dropped
     const int K = c.rv_n / 2;
 #pragma unroll
     for (int x = 0; x < 2; ++x) M[x] = k < K ? expf(q[x * 2 * K + k] + float(m) * q[x * 2 * K + K + k]) : 0.f;
     return;
   }
-  const float* row = c.rv_band + k * RV_BANDS;
+  const float* lm = c.rv_lm + size_t(ri) * 4 * RV_BINS;   // k_rv_bands
 #pragma unroll
-  for (int x = 0; x < 2; ++x) {
-    float h0 = 0.f, hd = 0.f;
-    for (int b = 0; b < RV_BANDS; ++b) {
-      h0 += row[b] * q[x * 24 + b];
-      hd += row[b] * q[x * 24 + 12 + b];
+  for (int x = 0; x < 2; ++x) M[x] = expf(lm[(2 * x) * RV_BINS + k] + float(m) * lm[(2 * x + 1) * RV_BINS + k]);
+}
+
+// Compact layout: H0_x[k] and Hd_x[k] interpolated from the 12 bands once per node (they
+// do not depend on the frame); grid (reverb nodes of the step).
+__global__ void __launch_bounds__(256) k_rv_bands(DevCtx c, int node_begin) {
+  const int v = node_begin + blockIdx.x;
+  const NodeDev nd = c.nodes[v];
+  const int ri = c.ext[v].z;
+  const float* q = c.params + size_t(nd.prow) * c.pcols;
+  float* lm = c.rv_lm + size_t(ri) * 4 * RV_BINS;
+  for (int k = threadIdx.x; k < RV_BINS; k += blockDim.x) {
+    const float* row = c.rv_band + k * RV_BANDS;
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+      float h0 = 0.f, hd = 0.f;
+      for (int b = 0; b < RV_BANDS; ++b) {
+        h0 += row[b] * q[x * 24 + b];
+        hd += row[b] * q[x * 24 + 12 + b];
+      }
+      lm[(2 * x) * RV_BINS + k] = h0;
+      lm[(2 * x + 1) * RV_BINS + k] = hd;
     }
-    M[x] = expf(h0 + float(m) * hd);
   }
 }
 
@@ -83,7 +99,7 @@ __global__ void __launch_bounds__(RV_N / 16) k_rv_ir_frames(DevCtx c, int node_b
   const float* q = c.params + size_t(nd.prow) * c.pcols;
   for (int k = threadIdx.x; k <= RV_N / 2; k += blockDim.x) {
     float M[2];
-    rv_masks(c, q, k, m, M);
+    rv_masks(c, q, ri, k, m, M);
     float2 hm = c.rv_U[size_t(m) * RV_BINS + k], hs = c.rv_U[size_t(RV_F + m) * RV_BINS + k];
     hm = make_float2(hm.x * M[0], hm.y * M[0]);
     hs = make_float2(hs.x * M[1], hs.y * M[1]);
@@ -166,7 +182,7 @@ __global__ void __launch_bounds__(128) k_rv_ir_frames_384(DevCtx c, int node_beg
     float2 hm = make_float2(0.f, 0.f), hs = hm;
     if (f < nf) {
       float M[2];
-      rv_masks(c, q, k, m, M);
+      rv_masks(c, q, ri, k, m, M);
       hm = c.rv_U[size_t(m) * bins + k];
       hs = c.rv_U[size_t(c.rv_f + m) * bins + k];
       hm = make_float2(hm.x * M[0], hm.y * M[0]);
@@ -399,10 +415,22 @@ __global__ void __launch_bounds__(DL_M / 16) k_rv_inv(DevCtx c, int node_begin) 
   fft::forward<DL_M>(buf, c.ptw, threadIdx.x, true);
   const float inv = 1.f / float(DL_M);
   if (WHAT == 2) {
+    // the lags of partition b, and (compact layout) this partition's sum_x sum_n h_x r_x
+    // for dq_wet, reduced in a fixed order
+    const float* hl = c.rv_h + (size_t(ri) * 2) * RV_HLEN;
+    float acc[1] = {0.f};
     for (int nu = threadIdx.x; nu < DL_B; nu += blockDim.x) {
       const float2 z = buf[fft::pad((DL_B - nu) & (DL_M - 1))];
-      c.rv_r[(size_t(ri) * 2) * RV_HLEN + b * DL_B + nu] = z.x * inv;
-      c.rv_r[(size_t(ri) * 2 + 1) * RV_HLEN + b * DL_B + nu] = -z.y * inv;
+      const int n = b * DL_B + nu;
+      const float rl = z.x * inv, rr = -z.y * inv;
+      c.rv_r[(size_t(ri) * 2) * RV_HLEN + n] = rl;
+      c.rv_r[(size_t(ri) * 2 + 1) * RV_HLEN + n] = rr;
+      if (n < RV_LEN) acc[0] += hl[n] * rl + hl[RV_HLEN + n] * rr;
+    }
+    if (!c.rv_paper) {
+      __syncthreads();   // buf is reused as the reduction scratch
+      block_sum<1>(acc, reinterpret_cast<float*>(buf));
+      if (threadIdx.x == 0) c.rv_dot[size_t(ri) * RV_P + b] = acc[0];
     }
     return;
   }
@@ -463,7 +491,7 @@ __global__ void __launch_bounds__(RV_N / 16) k_rv_gfr(DevCtx c, int node_begin) 
     rv_split(buf[fft::pad(k)], buf[fft::pad((RV_N - k) & (RV_N - 1))], &A[0], &A[1]);
     const float ck = (k == 0 || k == RV_N / 2 ? 1.f : 2.f) / float(RV_N);
     float M[2];
-    rv_masks(c, q, k, m, M);
+    rv_masks(c, q, ri, k, m, M);
 #pragma unroll
     for (int x = 0; x < 2; ++x) {
       const float2 U = c.rv_U[size_t(x * RV_F + m) * RV_BINS + k];
@@ -512,7 +540,7 @@ __global__ void __launch_bounds__(128) k_rv_gfr_384(DevCtx c, int node_begin) {
     rv_split(fb[fft::out384(k)], fb[fft::out384((N - k) % N)], &A[0], &A[1]);
     const float ck = (k == 0 || k == K ? 1.f : 2.f) / float(N);
     float M[2];
-    rv_masks(c, q, k, m, M);
+    rv_masks(c, q, ri, k, m, M);
     float2* out = c.rv_mm + (size_t(ri) * c.rv_f + m) * 2 * bins;
 #pragma unroll
     for (int x = 0; x < 2; ++x) {
@@ -563,7 +591,6 @@ __global__ void __launch_bounds__(256) k_rv_msum(DevCtx c, int node_begin) {
 // matrix, then dq_dry and dq_wet.
 __global__ void __launch_bounds__(256) k_rv_grad(DevCtx c, int node_begin) {
   __shared__ float g0[2][RV_BINS], gd[2][RV_BINS];
-  __shared__ float red[2 * 32];
   const int v = node_begin + blockIdx.x;
   const NodeDev nd = c.nodes[v];
   const int ri = c.ext[v].z, bins = c.rv_n / 2 + 1;
@@ -584,14 +611,11 @@ __global__ void __launch_bounds__(256) k_rv_grad(DevCtx c, int node_begin) {
     out[threadIdx.x] = s;
   }
   const float* rl = c.rv_r + (size_t(ri) * 2) * RV_HLEN;
-  const float* hl = c.rv_h + (size_t(ri) * 2) * RV_HLEN;
-  float acc[2] = {0.f, 0.f};
-  for (int n = threadIdx.x; n < RV_LEN; n += blockDim.x)
-    acc[0] += hl[n] * rl[n] + hl[RV_HLEN + n] * rl[RV_HLEN + n];
-  block_sum<2>(acc, red);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {   // sum_x sum_n h_x[n] r_x[n] from the lag kernel's partition partials
+    float dot = 0.f;
+    for (int b = 0; b < RV_P; ++b) dot += c.rv_dot[size_t(ri) * RV_P + b];
     out[48] = expf(q[48]) * (rl[0] + rl[RV_HLEN]);
-    out[49] = expf(q[49]) * acc[0];
+    out[49] = expf(q[49]) * dot;
   }
 }
 
@@ -623,11 +647,12 @@ int launch_reverb(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
         k_rv_ir_frames_384<<<dim3(fg, n), 128, 0, s>>>(c, a);
       } else {
         k_rv_noise_stft<<<RV_F, RV_N / 16, 0, s>>>(c);
+        k_rv_bands<<<n, 256, 0, s>>>(c, a);
         k_rv_ir_frames<<<dim3(RV_F, n), RV_N / 16, 0, s>>>(c, a);
       }
       k_rv_ir_ola<<<dim3((RV_HLEN + 255) / 256, n), 256, 0, s>>>(c, a);
       k_rv_hspec<<<dim3(RV_P, n), DL_M / 16, sm_fft, s>>>(c, a);
-      return 4;
+      return c.rv_paper ? 4 : 5;
     case 1:  // forward convolution (after the u window spectra)
       k_rv_acc<0><<<chunks, 256, sm0, s>>>(c, a);
       k_rv_inv<0><<<dim3(nbm, n), DL_M / 16, sm_fft, s>>>(c, a);

@@ -735,6 +735,8 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     w.rv_R = take(8 * nr * RV_P * DL_M);
     w.rv_r = take(4 * nr * 2 * RV_HLEN);
     w.rv_mm = take(8 * nr * p->rv_f * 2 * rbins);
+    w.rv_lm = take(4 * nr * 4 * size_t(RV_BINS));
+    w.rv_dot = take(4 * nr * size_t(RV_P));
     w.partial = take(16 * size_t(std::max(p->n_partials, 1)));
     w.eq_partial = take(8 * size_t(std::max(p->n_eq_runs, 1)) * (p->eq_fft / 2 + 1));
     w.eq_uspec = take(8 * size_t(std::max<int64_t>(p->n_eq_blocks, 1)) * p->eq_fft);

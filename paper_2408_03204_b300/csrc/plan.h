@@ -64,6 +64,7 @@ struct WsLayout {
   size_t eq_uspec, eq_ola;                     // EQ input block spectra (forward), adjoint heads/tails
   size_t dl_aux, dl_spec, dl_R, dl_r;
   size_t rv_band, rv_U, rv_fr, rv_h, rv_H, rv_Y, rv_R, rv_r, rv_mm;
+  size_t rv_lm, rv_dot;                        // per reverb node: band-interpolated H0/Hd, h.r partials
   size_t loss_part, loss_stats, loss_rowloss, loss_frames, loss_spec;
   size_t dgrad;                                // per-copy parameter gradients (source batch)
   size_t bal;                                  // ballistic scratch rows
