@@ -209,7 +209,9 @@ __global__ void k_delay_design(DevCtx c, int node_begin) {
 
 // 8192-point spectrum of a u window (kind 0: samples [w B, w B + 2B)) or of a ybar
 // block (kind 1: samples [b B, b B + B), zero-padded), both channels packed l + i r.
-__global__ void __launch_bounds__(DL_M / 16) k_delay_spec(DevCtx c, int item0, int n_items) {
+// Windows that hold no sample of the signal (those before its start and past its end)
+// get the zero spectrum without a transform.
+__global__ void __launch_bounds__(DL_M / 16, 2) k_delay_spec(DevCtx c, int item0, int n_items) {
   extern __shared__ float2 smem2[];
   float2* buf = smem2;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -219,6 +221,11 @@ __global__ void __launch_bounds__(DL_M / 16) k_delay_spec(DevCtx c, int item0, i
     // kind 0: u window of 2B; 1: ybar block of B (zero-padded); 2: ybar window of 2B
     const bool adj = kind != 0;
     const int start = idx * DL_B, count = kind == 1 ? DL_B : 2 * DL_B;
+    float2* out = c.dl_spec + size_t(w.w) * DL_M;
+    if (start + count <= 0 || start >= nd.len) {   // no sample of the signal: the zero spectrum
+      for (int k = threadIdx.x; k < DL_M; k += blockDim.x) out[k] = make_float2(0.f, 0.f);
+      continue;   // uniform over the CTA
+    }
     const int e0 = adj ? c.tcsr_ptr[v] : c.csr_ptr[v];
     const int e1 = adj ? c.tcsr_ptr[v + 1] : c.csr_ptr[v + 1];
     __syncthreads();
@@ -235,7 +242,6 @@ __global__ void __launch_bounds__(DL_M / 16) k_delay_spec(DevCtx c, int item0, i
     }
     __syncthreads();
     fft::forward<DL_M>(buf, c.ptw, threadIdx.x, true);
-    float2* out = c.dl_spec + size_t(w.w) * DL_M;
     for (int k = threadIdx.x; k < DL_M; k += blockDim.x) out[k] = buf[fft::pad(k)];
   }
 }
