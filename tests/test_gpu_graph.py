@@ -107,3 +107,46 @@ def test_fused_step_pair_matches_step_by_step():
     for t in dP_f:
         assert torch.equal(dP_f[t], dP_s[t]), t
     assert torch.equal(dS_f, dS_s)
+
+
+def test_fused_steps_with_a_source_batch():
+    """Two source sets through the nested console in one plan (source_batch = 2; both
+    fused step pairs apply to the union): each copy's output equals a one-copy plan's
+    bit for bit, and the parameter gradients equal the sum of the one-copy plans'."""
+    import torch
+    import paper_2408_03204_b300 as gx
+    g = synth.console_cfg2()
+    L, B = 4096, 2
+    P = union_params([g], 5)
+    Pt = {t: torch.tensor(v, dtype=torch.float32, device="cuda").contiguous() for t, v in P.items()}
+    srcs = [flat_sources([g], [L], [40 + b])[0] for b in range(B)]
+    G = gx.Graph.from_lists(g.types, g.edges)
+    batched = gx.Plan([G], [L], eq_taps=255, source_batch=B).bind_workspace("cuda")
+    single = gx.Plan([G], [L], eq_taps=255).bind_workspace("cuda")
+    assert batched.info.fused_pairs == 2 and single.info.fused_pairs == 2
+    batched.bind_params(Pt)
+    single.bind_params(Pt)
+    st = gx._stream(torch, torch.device("cuda"))
+    src_b = torch.tensor(np.concatenate(srcs), device="cuda")
+    out_b = torch.empty(batched.info.out_elems, device="cuda")
+    batched.render_raw(src_b, out_b, st)
+    rng = np.random.Generator(np.random.PCG64(8))
+    d_b = torch.tensor(rng.standard_normal(batched.info.out_elems).astype(np.float32), device="cuda")
+    dP_b = {t: torch.empty_like(p) for t, p in Pt.items()}
+    batched.backprop_raw(src_b, d_b, dP_b, None, st)
+    n_out = single.info.out_elems
+    sum_P = {t: torch.zeros_like(p, dtype=torch.float64) for t, p in Pt.items()}
+    for b in range(B):
+        src = torch.tensor(srcs[b], device="cuda")
+        out = torch.empty(n_out, device="cuda")
+        single.render_raw(src, out, st)
+        torch.cuda.synchronize()
+        assert torch.equal(out, out_b[b * n_out:(b + 1) * n_out])
+        dP = {t: torch.empty_like(p) for t, p in Pt.items()}
+        single.backprop_raw(src, d_b[b * n_out:(b + 1) * n_out].contiguous(), dP, None, st)
+        torch.cuda.synchronize()
+        for t in dP:
+            sum_P[t] += dP[t].double()
+    batched.sync_status(st)
+    for t in dP_b:   # the batched plan folds the copies' gradients in copy order
+        np.testing.assert_allclose(dP_b[t].cpu().numpy(), sum_P[t].cpu().numpy(), rtol=1e-5, atol=1e-6)
