@@ -338,7 +338,14 @@ __device__ __forceinline__ cplx cdv(cplx a, cplx b) {
 // formed once in double, so the lag next to the pole (m = 0, the Taylor branch) keeps
 // its full precision in FP32.  Each thread runs over RUN consecutive lags with a
 // register window of r for the 39-tap correlation g.
+struct DlSurrogate {
+  cplx zN, bz, zinv;
+  float dlt, tx, npi, rf, one_m_rho;
+  int d0;
+};
+
 __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_items) {
+  __shared__ DlSurrogate sc;
   __shared__ float cs[DL_FIR];
   __shared__ float cos39[DL_FIR], hann39[DL_FIR];
   __shared__ float red[2 * 32];
@@ -358,6 +365,30 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
     const int d = int(aux[DL_FIR]);
     __syncthreads();
     if (threadIdx.x < DL_FIR) cs[threadIdx.x] = aux[threadIdx.x];
+    if (threadIdx.x == 0) {
+      // the tap's surrogate constants, once per item in double (B300's FP64 rate is a
+      // small fraction of FP32: every thread forming them was most of this kernel's time)
+      const double zr = q[0], zi = q[1];
+      const double rho = sqrt(zr * zr + zi * zi), th = atan2(zi, zr);
+      const double lr = log(rho);
+      const double rN = exp(Nd * lr);
+      double sN, cN;
+      sincos(0.5 * Nd * th, &sN, &cN);
+      const double c1 = -2.0 * sN * sN;                   // cos(N th) - 1
+      const double s1 = 2.0 * sN * cN;                    // sin(N th)
+      const long long d0r = llrint(double(Nd) * (-th) / (2.0 * M_PI));   // |arg z / pi + 2 d0r / N_d| <= 1/N_d
+      long long d0l = d0r % Nd;
+      if (d0l < 0) d0l += Nd;
+      sc.zN = {float(rN * (1.0 + c1)), float(rN * s1)};
+      sc.bz = {float(rN * c1 + (rN - 1.0)), float(rN * s1)};   // z^N - 1
+      sc.zinv = {float(zr / (rho * rho) / Nd), float(-zi / (rho * rho) / Nd)};
+      sc.dlt = float(th / M_PI + 2.0 * double(d0r) / Nd);
+      sc.d0 = int(d0l);
+      sc.tx = float(Nd * lr);
+      sc.npi = float(Nd * M_PI);
+      sc.rf = float(rho);
+      sc.one_m_rho = float(1.0 - rho);
+    }
     __syncthreads();
     // FIR taps: dL/dc[j] = r[d + j]; chain through the window, cosine sum and exp
     if (threadIdx.x < K) {
@@ -370,24 +401,10 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
       out[2 + k] = expf(q[2 + k]) * acc * (k == 0 ? 1.f : 2.f) / float(DL_FIR);
     }
     // surrogate z: Q = sum_n g[n] phi[n]
-    const double zr = q[0], zi = q[1];
-    const double rho = sqrt(zr * zr + zi * zi), th = atan2(zi, zr);
-    const double lr = log(rho);
-    const double rN = exp(Nd * lr);
-    double sN, cN;
-    sincos(0.5 * Nd * th, &sN, &cN);
-    const double c1 = -2.0 * sN * sN;                   // cos(N th) - 1
-    const double s1 = 2.0 * sN * cN;                    // sin(N th)
-    const cplx zN = {float(rN * (1.0 + c1)), float(rN * s1)};
-    const cplx bz = {float(rN * c1 + (rN - 1.0)), float(rN * s1)};   // z^N - 1
-    const cplx zinv = {float(zr / (rho * rho) / Nd), float(-zi / (rho * rho) / Nd)};
-    const long long d0r = llrint(double(Nd) * (-th) / (2.0 * M_PI));   // |arg z / pi + 2 d0r / N_d| <= 1/N_d
-    const float dlt = float(th / M_PI + 2.0 * double(d0r) / Nd);
-    long long d0l = d0r % Nd;
-    if (d0l < 0) d0l += Nd;
-    const int d0 = int(d0l);
-    const float two_n = 2.f / float(Nd), tx = float(Nd * lr), npi = float(Nd * M_PI);
-    const float rf = float(rho), one_m_rho = float(1.0 - rho);
+    const cplx zN = sc.zN, bz = sc.bz, zinv = sc.zinv;
+    const float dlt = sc.dlt, tx = sc.tx, npi = sc.npi, rf = sc.rf, one_m_rho = sc.one_m_rho;
+    const int d0 = sc.d0;
+    const float two_n = 2.f / float(Nd);
     float qx = 0.f, qy = 0.f;
     for (int n0 = threadIdx.x * RUN; n0 < Nd; n0 += blockDim.x * RUN) {
       float win[RUN + DL_FIR - 1];
