@@ -98,52 +98,73 @@ __device__ __forceinline__ float* bal_starts(const DevCtx& c, int v, const NodeD
 template <bool MAX>
 __device__ __forceinline__ float bal_op(float a, float b) { return MAX ? fmaxf(a, b) : fminf(a, b); }
 
-// forward 1: the chunk maps.  Lane l holds c_{2l}, c_{2l+1} (lane 31 also c_64); the
-// attack step from c_{2l-1} comes from lane l-1.  Samples past len are taken as 0 (only
-// the last chunk has them, and its map is not used).
+// forward 1: the chunk maps, one chunk per half-warp.  Lane h (0..15) of a half holds
+// c_4h .. c_4h+3; the attack step into c_4h comes from lane h-1.  c_64 (64 attacks in
+// 64 steps) has a single path, so it is the plain sum over t of aa^(63-t) (1-aa) x_t,
+// formed after the programme by the half's lanes and a shuffle reduction.  Samples past
+// len are taken as 0 (only the last chunk has them, and its map is not used).
 template <bool MAX>
-__device__ void bal_chunk_map(const DevCtx& c, int v, const NodeDev& nd, int ck, float aa, float ar, float* xs) {
-  const int lane = threadIdx.x & 31;
+__device__ void bal_chunk_map(const DevCtx& c, int v, const NodeDev& nd, int ck, float aa, float ar, float* xs,
+                              bool store) {
+  const int h = threadIdx.x & 15;
   const float* X = bal_row(c, v, nd, 0);
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const int t = ck * BAL_N + lane + 32 * i;
+  for (int i = 0; i < 4; ++i) {
+    const int t = ck * BAL_N + h + 16 * i;
     const float m = t < nd.len ? X[t] : 0.f;
-    xs[lane + 32 * i] = m * m;
+    xs[h + 16 * i] = m * m;
   }
   __syncwarp();
   const float unreach = MAX ? -INFINITY : INFINITY;
   const float ba = 1.f - aa, br = 1.f - ar;
-  float c0 = lane == 0 ? 0.f : unreach, c1 = unreach, c64 = unreach;
+  float c0 = h == 0 ? 0.f : unreach, c1 = unreach, c2 = unreach, c3 = unreach;
   for (int t = 0; t < BAL_N; ++t) {
     const float x = xs[t];
     const float ax = ba * x, rx = br * x;
-    float lo = __shfl_up_sync(0xffffffffu, c1, 1);   // c_{2l-1}
-    if (lane == 0) lo = unreach;
+    float lo = __shfl_up_sync(0xffffffffu, c3, 1, 16);   // c_{4h-1}
+    if (h == 0) lo = unreach;
     const float n0 = bal_op<MAX>(fmaf(aa, lo, ax), fmaf(ar, c0, rx));
     const float n1 = bal_op<MAX>(fmaf(aa, c0, ax), fmaf(ar, c1, rx));
-    const float n64 = bal_op<MAX>(fmaf(aa, c1, ax), fmaf(ar, c64, rx));   // used by lane 31
+    const float n2 = bal_op<MAX>(fmaf(aa, c1, ax), fmaf(ar, c2, rx));
+    const float n3 = bal_op<MAX>(fmaf(aa, c2, ax), fmaf(ar, c3, rx));
     c0 = n0;
     c1 = n1;
-    c64 = n64;
+    c2 = n2;
+    c3 = n3;
   }
+  float all = 0.f;   // c_64: sum_t aa^(63-t) (1-aa) x_t over the lane's 4 samples
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int t = h + 16 * i;
+    all += powf(aa, float(BAL_N - 1 - t)) * (ba * xs[t]);
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) all += __shfl_xor_sync(0xffffffffu, all, o, 16);
+  if (!store) return;
   float* out = bal_maps(c, v, nd) + size_t(ck) * BAL_L;
-  out[2 * lane] = c0;
-  out[2 * lane + 1] = c1;
-  if (lane == 31) out[BAL_N] = c64;
+  out[4 * h] = c0;
+  out[4 * h + 1] = c1;
+  out[4 * h + 2] = c2;
+  out[4 * h + 3] = c3;
+  if (h == 0) out[BAL_N] = all;
 }
 
-// grid (ceil(max chunks / 8), ballistic nodes of the step), 8 warps: one chunk each
+// grid (ceil(max chunks / 16), ballistic nodes of the step), 8 warps: one chunk per half
 __global__ void __launch_bounds__(256) k_bal_maps(DevCtx c, int node_begin) {
-  __shared__ float xs[8][BAL_N];
+  __shared__ float xs[16][BAL_N];
   const int v = node_begin + blockIdx.y;
   const NodeDev nd = c.nodes[v];
-  const int ck = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (ck >= bal_chunks(nd)) return;   // whole warps leave together
+  const int half = threadIdx.x >> 4;
+  const int ck = blockIdx.x * 16 + half;
+  // both halves of a warp take part in its shuffles: a half past the last chunk runs on
+  // a copy of the last chunk and does not store
+  const int nck = bal_chunks(nd);
   const float* p = c.params + size_t(nd.prow) * 5;
   const float aa = p[0], ar = p[1];
-  if (aa <= ar) bal_chunk_map<true>(c, v, nd, ck, aa, ar, xs[threadIdx.x >> 5]);
-  else bal_chunk_map<false>(c, v, nd, ck, aa, ar, xs[threadIdx.x >> 5]);
+  if ((blockIdx.x * 16 + (half & ~1)) >= nck) return;   // whole warps leave together
+  const int cr = min(ck, nck - 1);
+  if (aa <= ar) bal_chunk_map<true>(c, v, nd, cr, aa, ar, xs[half], ck < nck);
+  else bal_chunk_map<false>(c, v, nd, cr, aa, ar, xs[half], ck < nck);
 }
 
 // forward 2: one warp per node, serial over chunks: g_in of chunk 0 is 0, then
@@ -466,7 +487,7 @@ int launch_bal_fwd(const DevCtx& c, int item0, int n_items, int node_begin, int 
   int launches = 2;
   for (int n0 = node_begin; n0 < node_end; n0 += 65535) {   // nodes on grid.y
     const int nb = std::min(65535, node_end - n0);
-    k_bal_maps<<<dim3((mck + 7) / 8, nb), 256, 0, s>>>(c, n0);
+    k_bal_maps<<<dim3((mck + 15) / 16, nb), 256, 0, s>>>(c, n0);
     k_bal_starts<<<nb, 32, 0, s>>>(c, n0);
     k_bal_run<<<dim3((mck + 127) / 128, nb), 128, 0, s>>>(c, n0);
     launches += 3;
