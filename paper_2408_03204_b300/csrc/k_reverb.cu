@@ -292,6 +292,7 @@ __device__ __forceinline__ void rv_store_sym(float2* Z, int k, float2 al, float2
   if (k > 0 && k < DL_M / 2) Z[DL_M - k] = make_float2(al.x + ar.y, ar.x - al.y);
 }
 
+constexpr int RV_NBO = 4;   // output blocks per warp pass (forward, adjoint)
 constexpr int RV_PCH = 6;   // partitions per warp (lags): 4 chunks x 6 >= RV_P, two block halves
 static_assert(4 * RV_PCH >= RV_P, "lag chunks must cover the partitions");
 
@@ -321,16 +322,36 @@ __global__ void __launch_bounds__(256) k_rv_acc(DevCtx c, int node_begin) {
   __syncthreads();
   const int k = k0 + kk;
   if (WHAT == 0 || WHAT == 1) {
-    for (int b = g; b < nb; b += ng) {
-      float2 al = make_float2(0.f, 0.f), ar = make_float2(0.f, 0.f);
-      for (int p = 0; p < RV_P; ++p) {
-        const int sl = WHAT == 0 ? b - 1 - p + RV_P : b + p;
-        const float2 hl = Hs[(size_t(p) * DL_CHUNK + kk) * 2], hr = Hs[(size_t(p) * DL_CHUNK + kk) * 2 + 1];
+    // RV_NBO consecutive output blocks per warp pass: each staged slot is read once and
+    // feeds every output it reaches (u = i - p forward, u = i + p adjoint; the partition
+    // spectra stay in shared memory)
+    for (int b0 = g * RV_NBO; b0 < nb; b0 += ng * RV_NBO) {
+      float2 acc[RV_NBO][2];
+#pragma unroll
+      for (int i = 0; i < RV_NBO; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
+      constexpr int U0 = WHAT == 0 ? -(RV_P - 1) : 0, U1 = WHAT == 0 ? RV_NBO : RV_NBO + RV_P - 1;
+#pragma unroll 1
+      for (int u = U0; u < U1; ++u) {
+        // forward: slot b - 1 - p + RV_P with p = i - u; adjoint: slot b + p with p = u - i
+        const int sl = WHAT == 0 ? b0 - 1 + RV_P + u : b0 + u;
+        if (sl >= nw) continue;
         const float2 xl = S[(size_t(sl) * DL_CHUNK + kk) * 2], xr = S[(size_t(sl) * DL_CHUNK + kk) * 2 + 1];
-        al = cmac(al, hl, xl, WHAT == 1);
-        ar = cmac(ar, hr, xr, WHAT == 1);
+#pragma unroll
+        for (int i = 0; i < RV_NBO; ++i) {
+          const int p = WHAT == 0 ? i - u : u - i;
+          if (p >= 0 && p < RV_P) {
+            const float2 hl = Hs[(size_t(p) * DL_CHUNK + kk) * 2], hr = Hs[(size_t(p) * DL_CHUNK + kk) * 2 + 1];
+            acc[i][0] = cmac(acc[i][0], hl, xl, WHAT == 1);
+            acc[i][1] = cmac(acc[i][1], hr, xr, WHAT == 1);
+          }
+        }
       }
-      if (k <= DL_M / 2) rv_store_sym(c.rv_Y + (size_t(ri) * c.rv_nbmax + b) * DL_M, k, al, ar);
+#pragma unroll
+      for (int i = 0; i < RV_NBO; ++i) {
+        const int b = b0 + i;
+        if (b < nb && k <= DL_M / 2)
+          rv_store_sym(c.rv_Y + (size_t(ri) * c.rv_nbmax + b) * DL_M, k, acc[i][0], acc[i][1]);
+      }
     }
   } else {
     // warp g: partitions [p0, p0 + RV_PCH) over half h of the blocks, the X slots of
