@@ -80,7 +80,7 @@ def per_graph_params(graphs, P):
     return out
 
 
-class GpuRun:
+class DeviceRun:
     """One plan bound to a workspace, with device copies of sources and parameters."""
 
     def __init__(self, graphs, lengths, P, src_flat, **plan_kw):

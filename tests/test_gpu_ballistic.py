@@ -49,7 +49,7 @@ def test_ballistic_coefficient_orders_and_short_signals():
     """A slower attack than release (the envelope takes the smaller candidate step), equal
     coefficients (the one-pole filter) and the usual order, on signals of 3 samples (one
     partial block) and 1029 samples (two blocks and a ragged tail)."""
-    from tests.gpu_common import GpuRun, flat_sources, split_rows
+    from tests.gpu_common import DeviceRun, flat_sources, split_rows
 
     def bank_graph(n):
         g = synth.Graph()
@@ -64,7 +64,7 @@ def test_ballistic_coefficient_orders_and_short_signals():
     T, W, R = np.log(10 ** (-20 / 10)), 3.0 * np.log(10) / 10, 4.0
     rows = np.array([[0.7, 0.9995, T, W, R], [0.9995, 0.7, T, W, R], [0.98, 0.98, T, W, R]])
     P = {A: np.concatenate([rows, rows])}
-    run = GpuRun(graphs, lengths, P, src_flat)
+    run = DeviceRun(graphs, lengths, P, src_flat)
     got = split_rows(run.render().cpu().numpy(), graphs, lengths)
     Pd = [(L + 3) // 4 * 4 for L in lengths]
     rng = np.random.Generator(np.random.PCG64(5))

@@ -6,14 +6,14 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_common import GRAD_TOL, GpuRun, assert_grad_close, flat_sources, union_params
+from gpu_common import GRAD_TOL, DeviceRun, assert_grad_close, flat_sources, union_params
 from oracle import render as orr
 
 pytestmark = pytest.mark.gpu
 
 
 def _run(graphs, lengths, P, src, d_seed, **kw):
-    run = GpuRun(graphs, lengths, P, src, **kw)
+    run = DeviceRun(graphs, lengths, P, src, **kw)
     out = run.render().cpu().numpy()
     rng = np.random.Generator(np.random.PCG64(d_seed))
     d_out = rng.standard_normal(out.shape).astype(np.float32)
@@ -29,7 +29,7 @@ def test_checkpointed_equals_plain_cfg1(k):
     P = union_params([g], 32)
     _, o0, d, dP0, dS0 = _run([g], [L], P, src, 5, eq_taps=255)
     run, o1, _, dP1, dS1 = _run([g], [L], P, src, 5, eq_taps=255, checkpoint_steps=k)
-    assert run.plan.info.ws_bytes <= GpuRun([g], [L], P, src, eq_taps=255).plan.info.ws_bytes
+    assert run.plan.info.ws_bytes <= DeviceRun([g], [L], P, src, eq_taps=255).plan.info.ws_bytes
     np.testing.assert_array_equal(o0, o1)
     for t in dP0:
         np.testing.assert_array_equal(dP0[t], dP1[t])
@@ -68,7 +68,7 @@ def test_checkpointed_step_graph_replay_equals_eager():
     L = 8192
     src, per = flat_sources([g], [L], [71])
     P = union_params([g], 72)
-    run = GpuRun([g], [L], P, src, eq_taps=255, checkpoint_steps=2)
+    run = DeviceRun([g], [L], P, src, eq_taps=255, checkpoint_steps=2)
     plan = run.plan
     tgt = run.render().clone() * 0.5
     out = torch.empty_like(tgt)
@@ -99,7 +99,7 @@ def test_node_inputs_rejected_with_checkpointing():
     import paper_2408_03204_b300 as gx
     g = synth.console_cfg1()
     src, per = flat_sources([g], [4096], [1])
-    run = GpuRun([g], [4096], union_params([g], 2), src, eq_taps=255, checkpoint_steps=2)
+    run = DeviceRun([g], [4096], union_params([g], 2), src, eq_taps=255, checkpoint_steps=2)
     out = run.render()
     dst = torch.empty((1, 2, 4096), device="cuda")
     with pytest.raises(gx.GrafxError):

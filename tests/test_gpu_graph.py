@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import synth
-from tests.gpu_common import GpuRun, assert_out_close, flat_sources, union_params
+from tests.gpu_common import DeviceRun, assert_out_close, flat_sources, union_params
 
 pytestmark = pytest.mark.gpu
 
@@ -24,7 +24,7 @@ def test_step_graph_replay_equals_eager():
     g = synth.console_cfg2(tracks=12, levels=2)
     L = 8192
     src_flat, _ = flat_sources([g], [L], [3])
-    run = GpuRun([g], [L], union_params([g], 7), src_flat, eq_taps=255)
+    run = DeviceRun([g], [L], union_params([g], 7), src_flat, eq_taps=255)
     st = run.gx._stream(torch, run.src.device)
     tgt = run.render().clone() * 0.5 + 0.01
     out, loss, d_out = torch.empty_like(tgt), torch.empty(1, device="cuda"), torch.empty_like(tgt)
@@ -67,8 +67,8 @@ def test_autotuner_picks_valid_tiles(tmp_path):
     assert again == best
     src_flat, _ = flat_sources([g], [L], [1])
     P = union_params([g], 1)
-    a = GpuRun([g], [L], P, src_flat, eq_taps=255).render().cpu().numpy()
-    b = GpuRun([g], [L], P, src_flat, eq_taps=255, **best).render().cpu().numpy()
+    a = DeviceRun([g], [L], P, src_flat, eq_taps=255).render().cpu().numpy()
+    b = DeviceRun([g], [L], P, src_flat, eq_taps=255, **best).render().cpu().numpy()
     assert_out_close(b, a, tol=2e-6)
 
 
@@ -82,7 +82,7 @@ def test_fused_step_pair_matches_step_by_step():
     L = 8192
     src_flat, _ = flat_sources([g], [L], [3])
     P = union_params([g], 3)
-    run = GpuRun([g], [L], P, src_flat, eq_taps=255)
+    run = DeviceRun([g], [L], P, src_flat, eq_taps=255)
     plan = run.plan
     assert plan.info.fused_pairs == 2
     N = plan.info.n_steps

@@ -8,7 +8,7 @@ import pytest
 
 import synth
 from oracle import render as orr
-from tests.gpu_common import GpuRun, assert_grad_close, assert_out_close, flat_sources, union_params
+from tests.gpu_common import DeviceRun, assert_grad_close, assert_out_close, flat_sources, union_params
 
 pytestmark = pytest.mark.gpu
 
@@ -28,7 +28,7 @@ def _chain(kinds):
 def _check(g, L, seed, eq_taps=63):
     src_flat, src_per = flat_sources([g], [L], [seed])
     P = union_params([g], seed)
-    run = GpuRun([g], [L], P, src_flat, eq_taps=eq_taps)
+    run = DeviceRun([g], [L], P, src_flat, eq_taps=eq_taps)
     got = run.render().cpu().numpy().reshape(-1, 2, (L + 3) // 4 * 4)[:, :, :L]
     hp = dict(eq_taps=eq_taps, reverb_noise=synth.reverb_noise().astype(np.float64))
     src = src_per[0][:, :, :L]

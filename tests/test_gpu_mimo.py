@@ -7,7 +7,7 @@ import pytest
 
 import synth
 from oracle import render as orr
-from tests.gpu_common import GpuRun, assert_grad_close, assert_out_close, flat_sources, per_graph_params, split_rows, union_params
+from tests.gpu_common import DeviceRun, assert_grad_close, assert_out_close, flat_sources, per_graph_params, split_rows, union_params
 from tests.helpers import random_mimo_dag
 
 pytestmark = pytest.mark.gpu
@@ -25,7 +25,7 @@ def _lib():
 def check(graphs, lengths, seed, **plan_kw):
     src_flat, src_per = flat_sources(graphs, lengths, [seed + k for k in range(len(graphs))])
     P = union_params(graphs, seed)
-    run = GpuRun(graphs, lengths, P, src_flat, eq_taps=63, **plan_kw)
+    run = DeviceRun(graphs, lengths, P, src_flat, eq_taps=63, **plan_kw)
     out = run.render().cpu().numpy()
     Pg = per_graph_params(graphs, P)
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -65,7 +65,7 @@ def test_mid_side_round_trip_is_exact_on_the_gpu():
     g.connect(mg, o)
     L = 10007
     src_flat, src_per = flat_sources([g], [L], [3])
-    run = GpuRun([g], [L], {}, src_flat)
+    run = DeviceRun([g], [L], {}, src_flat)
     out = run.render().cpu().numpy()
     got = split_rows(out, [g], [L])[0]
     np.testing.assert_allclose(got[0], src_per[0][0, :, :L], atol=1e-6)

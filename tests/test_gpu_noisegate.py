@@ -6,7 +6,7 @@ import pytest
 
 import synth
 from oracle import render as orr
-from tests.gpu_common import GpuRun, assert_grad_close, assert_out_close, flat_sources
+from tests.gpu_common import DeviceRun, assert_grad_close, assert_out_close, flat_sources
 from tests.test_gpu_parity import run_case, single_node_graph
 
 pytestmark = pytest.mark.gpu
@@ -20,7 +20,7 @@ def test_noisegate_long_signal(alpha):
     src_flat, src_per = flat_sources([g], [L], [6])
     # threshold near the sources' envelope so that all three regions of the curve occur
     P = {N: np.array([[alpha, np.log(0.004), 0.6908, 3.0]], np.float32)}
-    run = GpuRun([g], [L], P, src_flat)
+    run = DeviceRun([g], [L], P, src_flat)
     got = run.render().cpu().numpy().reshape(1, 2, L)
     want = orr.outputs_of(g.types, orr.render_one_by_one(g.types, g.edges, src_per[0], P))
     assert_out_close(got, want)
@@ -35,7 +35,7 @@ def test_noisegate_ratio_one_passes_through():
     g = single_node_graph(N)
     L = 9001
     src_flat, src_per = flat_sources([g], [L], [8])
-    run = GpuRun([g], [L], {N: np.array([[0.99, -3.0, 0.69, 1.0]], np.float32)}, src_flat)
+    run = DeviceRun([g], [L], {N: np.array([[0.99, -3.0, 0.69, 1.0]], np.float32)}, src_flat)
     got = run.render().cpu().numpy().reshape(1, 2, -1)[:, :, :L]
     assert_out_close(got, src_per[0][:, :, :L])
 

@@ -6,7 +6,7 @@ import pytest
 
 import synth
 from oracle import render as orr, loss as ol
-from tests.gpu_common import (GpuRun, assert_grad_close, assert_out_close, flat_sources, split_rows,
+from tests.gpu_common import (DeviceRun, assert_grad_close, assert_out_close, flat_sources, split_rows,
                               union_params, per_graph_params)
 
 pytestmark = pytest.mark.gpu
@@ -41,7 +41,7 @@ def single_node_graph(t, fan_in=1):
 def run_case(graphs, lengths, seed=11, eq_taps=63, linear_loss=True, **kw):
     src_flat, src_per = flat_sources(graphs, lengths, [seed + k for k in range(len(graphs))])
     P = union_params(graphs, seed)
-    run = GpuRun(graphs, lengths, P, src_flat, eq_taps=eq_taps, **kw)
+    run = DeviceRun(graphs, lengths, P, src_flat, eq_taps=eq_taps, **kw)
     out = run.render().cpu().numpy()
     hp = hparams(eq_taps)
     got_rows = split_rows(out, graphs, lengths)
@@ -91,7 +91,7 @@ def test_compressor_long_chunks_and_extreme_alpha():
     src_flat, src_per = flat_sources([g], [L], [5])
     for alpha in (0.9, 0.9999):
         P = {C: np.array([[alpha, np.log(0.005), 0.6908, 6.0]], np.float32)}
-        run = GpuRun([g], [L], P, src_flat)
+        run = DeviceRun([g], [L], P, src_flat)
         got = run.render().cpu().numpy().reshape(1, 2, L)
         want = orr.outputs_of(g.types, orr.render_one_by_one(g.types, g.edges, src_per[0], P))
         assert_out_close(got, want)
@@ -124,7 +124,7 @@ def test_batched_equals_single_and_deterministic():
     lengths = [int(rng.integers(4000, 12000)) for _ in graphs]
     src_flat, _ = flat_sources(graphs, lengths, list(range(5)))
     P = union_params(graphs, 4)
-    batched = GpuRun(graphs, lengths, P, src_flat, eq_taps=63)
+    batched = DeviceRun(graphs, lengths, P, src_flat, eq_taps=63)
     ob = batched.render().cpu().numpy()
     ob2 = batched.render().cpu().numpy()
     assert np.array_equal(ob, ob2), "render is not deterministic"
@@ -133,7 +133,7 @@ def test_batched_equals_single_and_deterministic():
     Pg = per_graph_params(graphs, P)
     for g, L, p, rb in zip(graphs, lengths, Pg, rows_b):
         n = g.count(I) * 2 * ((L + 3) // 4 * 4)
-        single = GpuRun([g], [L], p, src_flat[off_s:off_s + n], eq_taps=63)
+        single = DeviceRun([g], [L], p, src_flat[off_s:off_s + n], eq_taps=63)
         off_s += n
         rs = split_rows(single.render().cpu().numpy(), [g], [L])[0]
         # identical per-node arithmetic; only the summation order of fan-in >= 3 may differ
@@ -145,7 +145,7 @@ def test_schedule_methods_agree():
     L = 6000
     src_flat, _ = flat_sources([g], [L], [2])
     P = union_params([g], 5)
-    outs = [GpuRun([g], [L], P, src_flat, eq_taps=63, schedule=m).render().cpu().numpy()
+    outs = [DeviceRun([g], [L], P, src_flat, eq_taps=63, schedule=m).render().cpu().numpy()
             for m in ("beam", "greedy", "one_by_one")]
     for o in outs[1:]:
         assert_out_close(o, outs[0], tol=1e-6)
@@ -191,7 +191,7 @@ def _cfg2_case(L):
     hp = dict(eq_taps=1023)
     target = orr.outputs_of(g.types, orr.render_one_by_one(g.types, g.edges, src_per[0], Ph, hp))
     y_ref = orr.outputs_of(g.types, orr.render_one_by_one(g.types, g.edges, src_per[0], P, hp))
-    run = GpuRun([g], [L], P, src_flat, eq_taps=1023)
+    run = DeviceRun([g], [L], P, src_flat, eq_taps=1023)
     return g, src_per, P, hp, target, y_ref, run
 
 

@@ -12,7 +12,7 @@ import pytest
 
 import synth
 from oracle import render as orr
-from tests.gpu_common import (GpuRun, assert_grad_close, assert_out_close, flat_sources, split_rows,
+from tests.gpu_common import (DeviceRun, assert_grad_close, assert_out_close, flat_sources, split_rows,
                               union_params, per_graph_params)
 
 pytestmark = pytest.mark.gpu
@@ -47,7 +47,7 @@ def single_node_graph(t, fan_in=2):
 def run_paper(graphs, lengths, seed):
     src_flat, src_per = flat_sources(graphs, lengths, [seed + k for k in range(len(graphs))])
     P = union_params(graphs, seed, preset="paper")
-    run = GpuRun(graphs, lengths, P, src_flat, preset="paper")
+    run = DeviceRun(graphs, lengths, P, src_flat, preset="paper")
     for t, a in P.items():
         assert run.plan.param_cols[t] == a.shape[1] == synth.PAPER_PARAM_COLS[t]
     out = run.render().cpu().numpy()

@@ -249,13 +249,13 @@ def test_masked_mse_matches_oracle(env):
 
 def test_node_inputs_match_oracle_render(env):
     gx, torch = env
-    from gpu_common import GpuRun, assert_out_close, flat_sources, union_params
+    from gpu_common import DeviceRun, assert_out_close, flat_sources, union_params
     from oracle import render as orr
     g = synth.console_cfg1()
     L = 5003
     src_flat, per = flat_sources([g], [L], [71])
     P = union_params([g], 72)
-    run = GpuRun([g], [L], P, src_flat, eq_taps=255)
+    run = DeviceRun([g], [L], P, src_flat, eq_taps=255)
     out = run.render()
     ids = [v for v, t in enumerate(g.types) if t != synth.I]
     pitch = (L + 3) // 4 * 4 + 8

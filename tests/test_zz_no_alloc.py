@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import synth
-from tests.gpu_common import OUT_TOL, GpuRun, assert_out_close, flat_sources
+from tests.gpu_common import OUT_TOL, DeviceRun, assert_out_close, flat_sources
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +40,7 @@ def test_noalloc_compressor_matches_render_twice():
     pitch = (L + 3) // 4 * 4
     src_flat, _ = flat_sources([g], [L], [31])
     P = {synth.C: np.array([[0.999, np.log(0.01), 0.6908, 5.0]], np.float32)}
-    run = GpuRun([g], [L], P, src_flat)   # ordinary path: grafx_render of i -> c -> o
+    run = DeviceRun([g], [L], P, src_flat)   # ordinary path: grafx_render of i -> c -> o
     want = run.render().cpu().numpy().reshape(2, pitch)
     lib = gx.lib()
     stream = gx._stream(torch, run.src.device)
