@@ -645,7 +645,10 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
         break;
       case GRAFX_T_GAIN:
       case GRAFX_T_IMAGER:
-        launches += launch_ew_bwd(st.type, c, st.bitem_begin, st.bitem_count, s);
+        if (!d_sources && st.in_from_sources)   // the input adjoints would have no reader
+          launches += launch_ew_bwd_nostore(st.type, c, st.bitem_begin, st.bitem_count, s);
+        else
+          launches += launch_ew_bwd(st.type, c, st.bitem_begin, st.bitem_count, s);
         if (c.dparams) {
           to_side(k);
           launches += launch_ew_finalize(c, st.node_begin, st.node_end, param_cols(p, st.type), side);
@@ -663,6 +666,7 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
         }
         break;
       default:
+        if (!d_sources && st.in_from_sources) break;   // a mix of sources: no adjoint has a reader
         launches += launch_ew_bwd(GRAFX_T_MIX, c, st.bitem_begin, st.bitem_count, s);
     }
   }

@@ -201,7 +201,9 @@ __device__ __forceinline__ void ew_bwd_quad(float a0, float a1, float4& bl, floa
 
 // Backward: ybar = sum of the consumers' input adjoints; ubar = (df/du)^T ybar;
 // parameter-gradient partial of the tile into its own slot (no atomics).
-template <int TYPE>
+// STORE = false: the input adjoints have no reader (the inputs are sources and no source
+// adjoint is requested); only the parameter-gradient partials are formed.
+template <int TYPE, bool STORE = true>
 __global__ void __launch_bounds__(256, 3) k_ew_bwd(DevCtx c, int item0, int n_items) {
   __shared__ float sh[4 * 32];
   constexpr bool needs_u = TYPE == GRAFX_T_GAIN || TYPE == GRAFX_T_IMAGER;
@@ -249,8 +251,10 @@ __global__ void __launch_bounds__(256, 3) k_ew_bwd(DevCtx c, int item0, int n_it
       const int tq = t + 1024 * q;
       if (tq >= nd.len) continue;
       ew_bwd_quad<TYPE>(a0, a1, bl[q], br[q], ul[q], ur[q], acc);
-      st4(ub + tq, bl[q]);
-      st4(ub + nd.pitch + tq, br[q]);
+      if (STORE) {
+        st4(ub + tq, bl[q]);
+        st4(ub + nd.pitch + tq, br[q]);
+      }
     }
     if (needs_u) {
       block_sum<2>(acc, sh);
@@ -421,6 +425,15 @@ int launch_ew_fwd(int type, const DevCtx& c, int item0, int n_items, cudaStream_
     case GRAFX_T_MERGE: k_ms_fwd<false><<<g, 256, 0, s>>>(c, item0, n_items); break;
     default: k_ew_fwd<GRAFX_T_MIX><<<g, 256, 0, s>>>(c, item0, n_items); break;
   }
+  return 1;
+}
+
+int launch_ew_bwd_nostore(int type, const DevCtx& c, int item0, int n_items, cudaStream_t s) {
+  if (n_items <= 0) return 0;
+  const int g = grid_for(n_items, 8);
+  if (type == GRAFX_T_GAIN) k_ew_bwd<GRAFX_T_GAIN, false><<<g, 256, 0, s>>>(c, item0, n_items);
+  else if (type == GRAFX_T_IMAGER) k_ew_bwd<GRAFX_T_IMAGER, false><<<g, 256, 0, s>>>(c, item0, n_items);
+  else return 0;   // mix/output: nothing but the adjoints
   return 1;
 }
 

@@ -12,6 +12,8 @@ int grid_size(int n_items, int per_sm);
 // elementwise types (mix/out, gain, imager)
 int launch_ew_fwd(int type, const DevCtx& c, int item0, int n_items, cudaStream_t s);
 int launch_ew_bwd(int type, const DevCtx& c, int item0, int n_items, cudaStream_t s);
+// the same without the input-adjoint stores (gain/imager: partials only; mix: nothing)
+int launch_ew_bwd_nostore(int type, const DevCtx& c, int item0, int n_items, cudaStream_t s);
 int launch_ew_finalize(const DevCtx& c, int node_begin, int node_end, int cols, cudaStream_t s);
 // fused pair of gain/imager steps (types tv then tw) over the second step's items
 int launch_ew2(bool bwd, int tv, int tw, const DevCtx& c, int item0, int n_items, cudaStream_t s);

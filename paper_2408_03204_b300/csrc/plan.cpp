@@ -444,6 +444,10 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     StepInfo& s = p->steps[k];
     s.type = p->sched.string[k];
     s.fuse_next = fuse[k];
+    s.in_from_sources = 1;
+    for (int32_t v = p->step_ptr[k]; s.in_from_sources && v < p->step_ptr[k + 1]; ++v)
+      for (int32_t e = p->csr_ptr[v]; e < p->csr_ptr[v + 1]; ++e)
+        if (p->nodes[p->csr_src[e]].kind != KIND_INPUT) s.in_from_sources = 0;
     s.node_begin = p->step_ptr[k];
     s.node_end = p->step_ptr[k + 1];
     s.fitem_begin = int32_t(fwd.size());

@@ -50,6 +50,9 @@ struct StepInfo {
   // 2: gain step whose every node is the single input of one EQ node of the next step,
   // and feeds only it: the EQ forward applies the gain on load (backward unfused)
   int32_t fuse_next = 0;
+  // every in-edge of the step's nodes comes from an input node: without requested source
+  // adjoints the step's input adjoints have no reader
+  int32_t in_from_sources = 0;
 };
 
 // Byte offsets of the regions inside the caller's workspace.
