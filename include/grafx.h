@@ -200,8 +200,9 @@ typedef struct {
                                * count all B copies, n_type_rows one copy */
   int32_t fused_pairs;        /* schedule steps k fused with step k+1: every node of k+1 has one
                                * input, a node of k whose only consumer it is, and the types are
-                               * gain/imager then gain/imager (forward and backward fused) or gain
-                               * then EQ (the EQ forward applies the gain on load).  A render or
+                               * gain/imager then gain/imager (forward and backward fused), gain
+                               * then EQ (the EQ forward applies the gain on load) or mix then
+                               * output (one forward kernel writes both rows).  A render or
                                * backprop whose step range holds both steps runs them as one
                                * kernel (same results, bit for bit; the intermediate rows are
                                * written forward, the intermediate adjoint rows of a gain/imager

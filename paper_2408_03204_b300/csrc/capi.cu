@@ -450,7 +450,7 @@ static int render_range(grafx_plan* p, const float* sources, float* out, int32_t
       const StepInfo& sw = p->steps[k + 1];
       c.params = p->params[sw.type];
       c.params2 = p->params[st.type];
-      if (st.fuse_next == 1) {
+      if (st.fuse_next == 1 || st.fuse_next == 3) {
         launches += launch_ew2(false, st.type, sw.type, c, sw.fitem_begin, sw.fitem_count, s);
       } else {   // gain -> EQ: the EQ forward with the gain prologue
         c.pcols = param_cols(p, sw.type);

@@ -400,6 +400,10 @@ int launch_ew2(bool bwd, int tv, int tw, const DevCtx& c, int item0, int n_items
   if (n_items <= 0) return 0;
   const int g = grid_for(n_items, 8);
   constexpr int G = GRAFX_T_GAIN, S = GRAFX_T_IMAGER;
+  if (tv == GRAFX_T_MIX) {   // mix -> output: forward only (both identities on the summed input)
+    if (!bwd) k_ew2_fwd<GRAFX_T_MIX, GRAFX_T_OUT><<<g, 256, 0, s>>>(c, item0, n_items);
+    return bwd ? 0 : 1;
+  }
   if (bwd) {
     if (tv == G && tw == G) k_ew2_bwd<G, G><<<g, 256, 0, s>>>(c, item0, n_items);
     else if (tv == G) k_ew2_bwd<G, S><<<g, 256, 0, s>>>(c, item0, n_items);

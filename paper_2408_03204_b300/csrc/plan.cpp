@@ -312,10 +312,13 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
   std::vector<int8_t> fuse(N + 1, 0);
   {
     auto pointwise = [](int t) { return t == GRAFX_T_GAIN || t == GRAFX_T_IMAGER; };
-    for (int32_t k = 1; opts.checkpoint_steps == 0 && k + 1 < N; ++k) {
+    for (int32_t k = 1; opts.checkpoint_steps == 0 && k + 1 <= N; ++k) {
       const int32_t a0 = p->step_ptr[k], a1 = p->step_ptr[k + 1], b0 = p->step_ptr[k + 1], b1 = p->step_ptr[k + 2];
       const int32_t ta = p->sched.string[k], tb = p->sched.string[k + 1];
-      const int8_t kind = pointwise(ta) && pointwise(tb) ? 1 : (ta == GRAFX_T_GAIN && tb == GRAFX_T_EQ ? 2 : 0);
+      int8_t kind = 0;
+      if (tb != GRAFX_T_OUT && pointwise(ta) && pointwise(tb)) kind = 1;
+      else if (ta == GRAFX_T_GAIN && tb == GRAFX_T_EQ) kind = 2;
+      else if (ta == GRAFX_T_MIX && tb == GRAFX_T_OUT) kind = 3;   // the output copies its mix
       if (!kind || a1 - a0 != b1 - b0) continue;
       bool ok = true;
       for (int32_t w = b0; ok && w < b1; ++w) {

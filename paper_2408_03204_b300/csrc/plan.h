@@ -48,7 +48,9 @@ struct StepInfo {
   // 1: gain/imager step whose every node feeds exactly one node of the next step (also
   // gain/imager, each with that single input): the two steps run as one fused kernel;
   // 2: gain step whose every node is the single input of one EQ node of the next step,
-  // and feeds only it: the EQ forward applies the gain on load (backward unfused)
+  // and feeds only it: the EQ forward applies the gain on load (backward unfused);
+  // 3: mix step whose every node is the single input of one output node of the next
+  // step: one forward kernel writes both rows (outputs have no backward step)
   int32_t fuse_next = 0;
   // every in-edge of the step's nodes comes from an input node: without requested source
   // adjoints the step's input adjoints have no reader

@@ -73,8 +73,8 @@ def test_autotuner_picks_valid_tiles(tmp_path):
 
 
 def test_fused_step_pair_matches_step_by_step():
-    """The nested console's gain -> EQ and imager -> gain steps run fused in a whole render
-    and backprop; one step at a time they run unfused.  Outputs, parameter gradients and
+    """The nested console's gain -> EQ, imager -> gain and mix -> output steps run fused
+    in a whole render and backprop; one step at a time they run unfused.  Outputs, parameter gradients and
     source adjoints agree bit for bit."""
     import torch
     import paper_2408_03204_b300 as gx
@@ -84,7 +84,7 @@ def test_fused_step_pair_matches_step_by_step():
     P = union_params([g], 3)
     run = DeviceRun([g], [L], P, src_flat, eq_taps=255)
     plan = run.plan
-    assert plan.info.fused_pairs == 2
+    assert plan.info.fused_pairs == 3
     N = plan.info.n_steps
     st = gx._stream(torch, run.src.device)
     out_f = torch.empty(plan.info.out_elems, device="cuda")
@@ -123,7 +123,7 @@ def test_fused_steps_with_a_source_batch():
     G = gx.Graph.from_lists(g.types, g.edges)
     batched = gx.Plan([G], [L], eq_taps=255, source_batch=B).bind_workspace("cuda")
     single = gx.Plan([G], [L], eq_taps=255).bind_workspace("cuda")
-    assert batched.info.fused_pairs == 2 and single.info.fused_pairs == 2
+    assert batched.info.fused_pairs == 3 and single.info.fused_pairs == 3
     batched.bind_params(Pt)
     single.bind_params(Pt)
     st = gx._stream(torch, torch.device("cuda"))

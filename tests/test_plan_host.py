@@ -272,11 +272,11 @@ def test_schedule_benchmark_consoles_step_counts(gx):
 
 
 def test_fused_elementwise_step_pairs(gx):
-    """The nested console's first gain step feeds its EQ step and its imager step its last
-    gain step node for node: two fused pairs; none with checkpointing; none when an imager
-    feeds two gains."""
+    """The nested console's first gain step feeds its EQ step, its imager step its last
+    gain step and its master mix its output node for node: three fused pairs; none with
+    checkpointing; none when an imager feeds two gains."""
     cfg2 = _to_gx(gx, synth.console_cfg2())
-    assert gx.Plan([cfg2], [4096]).info.fused_pairs == 2
+    assert gx.Plan([cfg2], [4096]).info.fused_pairs == 3
     assert gx.Plan([cfg2], [4096], checkpoint_steps=2).info.fused_pairs == 0
     g = synth.Graph()
     i, s = g.add(synth.I), g.add(synth.S)
@@ -292,7 +292,7 @@ def test_fused_elementwise_step_pairs(gx):
     h.connect(i, s)
     h.connect(s, g1)
     h.connect(g1, o)
-    assert gx.Plan([_to_gx(gx, h)], [4096]).info.fused_pairs == 1
+    assert gx.Plan([_to_gx(gx, h)], [4096]).info.fused_pairs == 1   # g -> o is not a pair
     q = synth.Graph()
     i, g1, e, o = q.add(synth.I), q.add(synth.G), q.add(synth.E), q.add(synth.O)
     q.connect(i, g1)
