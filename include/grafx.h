@@ -455,20 +455,25 @@ int grafx_gemm_bf16(int32_t M, int32_t N, int32_t K, const float* A, int64_t sam
  * Applies the compressor of grafx_render (same parameters [alpha, T, W, R] and the
  * same chunked scan) to one stereo row: u and y are caller-owned device float32
  * [2][pitch] rows (16-byte aligned, pitch a multiple of 4, pitch >= len), params a
- * device pointer to 4 floats.  Samples of y at and past len are written as 0.
- * Asynchronous on `stream`.
+ * device pointer to 4 floats.  Every sample of y at and past len, up to pitch, is
+ * written as 0.  status (device, 4-byte aligned, may be NULL) is a caller-owned word
+ * into which the kernel ORs GRAFX status bits: bit 0 (1) means a bounded device wait
+ * expired and some chunk used a zero carry, i.e. y is wrong; the call never clears it.
+ * Read it after the stream has passed the call.  With status NULL an expiry is not
+ * reported.  Asynchronous on `stream`.
  *
  * It calls no allocator: its only scratch (about 17 KB of look-back words, a ticket
- * and a status word) is a fixed array inside the library that every GPU which loads
- * the library holds until the process exits; it is zeroed on `stream` at every call.
- * Hence len is limited to 4194304 samples (GRAFX_ESHAPE beyond).  The first call on a
- * device looks up that array's device address (once per device, with that device
- * current), so make that first call before any stream capture.  Every call shares the
- * one array: calls whose work overlaps on the GPU (different streams, or devices that
- * alias it) race and give wrong results; serialise them.  A bounded device wait that
- * expires is not reported by this call (its chunk then uses a zero carry). */
+ * and an internal status word) is a fixed array inside the library that every GPU
+ * which loads the library holds until the process exits; the part a call uses is
+ * zeroed on `stream` at every call.  Hence len is limited to 4194304 samples
+ * (GRAFX_ESHAPE beyond).  The first call on a device looks up that array's device
+ * address (once per device, with that device current; again only if the device's
+ * context was destroyed and re-created, e.g. by cudaDeviceReset), so make that first
+ * call before any stream capture.  Every call shares the one array: calls whose work
+ * overlaps on the GPU (different streams, or devices that alias it) race and give
+ * wrong results; serialise them. */
 int grafx_compressor_forward_noalloc(const float* u, int64_t len, int64_t pitch, const float* params,
-                                     float* y, void* stream);
+                                     float* y, uint32_t* status, void* stream);
 
 #ifdef __cplusplus
 }

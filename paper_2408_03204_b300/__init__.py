@@ -91,7 +91,7 @@ SIGNATURES = {
     "grafx_mrstft_backward": (ctypes.c_int, [_P, _F, _F, _F, _P]),
     "grafx_sync_status": (ctypes.c_int, [_P, _P]),
     "grafx_last_launch_count": (ctypes.c_int, [_P, _I32P]),
-    "grafx_compressor_forward_noalloc": (ctypes.c_int, [_F, _I64, _I64, _F, _F, _P]),
+    "grafx_compressor_forward_noalloc": (ctypes.c_int, [_F, _I64, _I64, _F, _F, _P, _P]),
     "grafx_adam_step": (ctypes.c_int, [_F, _F, _F, _F, _F, _P, _I32, _I64, _I32, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_float, ctypes.c_float, _P]),
     "grafx_params_to_theta": (ctypes.c_int, [_F, _P, _I32, _I64, _F, _P]),
@@ -242,6 +242,12 @@ class Plan:
         self.param_cols = {t: int(inf.param_cols[t]) for t in range(N_TYPES) if inf.param_cols[t] > 0}
         self.ws = None
         self.params = {}
+        # Workspace generations: bumped by every call that rewrites the rows a backprop
+        # reads (a render, a parameter binding) or the spectra a loss gradient reads (a
+        # loss forward), so the autograd functions can tell whether their forward's state
+        # is still the plan's.
+        self.render_gen = 0
+        self.loss_gen = 0
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -280,6 +286,7 @@ class Plan:
             assert p.dtype.is_floating_point and p.is_contiguous()
             _check(lib().grafx_bind_params(self._h, int(t), _ptr(p), p.shape[0], p.shape[1]))
             self.params[int(t)] = p
+        self.render_gen += 1
 
     def bind_reverb_noise(self, noise):
         """noise: device float32 [2, 88200] (mid, side), kept by reference."""
@@ -287,6 +294,7 @@ class Plan:
         self.rv_noise = noise
 
     def render_raw(self, sources, out, stream):
+        self.render_gen += 1
         _check(lib().grafx_render(self._h, _ptr(sources), _ptr(out), stream))
 
     def backprop_raw(self, sources, d_out, d_params, d_sources, stream):
@@ -294,6 +302,7 @@ class Plan:
         _check(lib().grafx_backprop(self._h, _ptr(sources), _ptr(d_out), arr, _ptr(d_sources), stream))
 
     def render_steps_raw(self, sources, out, first, last, stream):
+        self.render_gen += 1
         _check(lib().grafx_render_steps(self._h, _ptr(sources), _ptr(out), int(first), int(last), stream))
 
     def backprop_steps_raw(self, sources, d_out, d_params, d_sources, first, last, stream):
@@ -302,6 +311,7 @@ class Plan:
                                           int(first), int(last), stream))
 
     def loss_raw(self, out, target, loss, stream):
+        self.loss_gen += 1
         _check(lib().grafx_mrstft_forward(self._h, _ptr(out), _ptr(target), _ptr(loss), stream))
 
     def loss_backward_raw(self, out, target, d_out, stream):
@@ -320,7 +330,7 @@ class Plan:
         h = _P()
         _check(lib().grafx_step_graph_create(self._h, _ptr(sources), _ptr(out), _ptr(target), _ptr(loss),
                                              _ptr(d_out), arr, _ptr(d_sources), stream, ctypes.byref(h)))
-        return StepGraph(h, (sources, out, target, loss, d_out, d_params, d_sources))
+        return StepGraph(h, (sources, out, target, loss, d_out, d_params, d_sources), self)
 
     def sync_status(self, stream=None):
         import torch
@@ -402,10 +412,13 @@ def gemm_bf16_raw(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta, stream
 class StepGraph:
     """A captured fit step (grafx_step_graph_*); keeps its buffers alive."""
 
-    def __init__(self, h, keep):
-        self._h, self._keep = h, keep
+    def __init__(self, h, keep, plan=None):
+        self._h, self._keep, self._plan = h, keep, plan
 
     def launch(self, stream):
+        if self._plan is not None:          # the step renders and evaluates the loss
+            self._plan.render_gen += 1
+            self._plan.loss_gen += 1
         _check(lib().grafx_step_graph_launch(self._h, stream))
 
     def launches(self):
@@ -428,7 +441,7 @@ def _autograd():
             plan.bind_params(dict(zip(types, ps)))
             out = torch.empty(plan.info.out_elems, dtype=torch.float32, device=sources.device)
             plan.render_raw(sources, out, _stream(torch, sources.device))
-            ctx.plan, ctx.types = plan, types
+            ctx.plan, ctx.types, ctx.gen = plan, types, plan.render_gen
             ctx.save_for_backward(sources, *ps)
             return out
 
@@ -436,6 +449,12 @@ def _autograd():
         def backward(ctx, d_out):
             plan, types = ctx.plan, ctx.types
             sources, *ps = ctx.saved_tensors
+            if plan.render_gen != ctx.gen:
+                # The plan rendered or re-bound parameters since this forward: its rows
+                # belong to another render.  Restore this forward's state first.
+                plan.bind_params(dict(zip(types, ps)))
+                scratch = torch.empty(plan.info.out_elems, dtype=torch.float32, device=sources.device)
+                plan.render_raw(sources, scratch, _stream(torch, sources.device))
             d_out = d_out.contiguous()
             dps = {t: torch.empty_like(p) for t, p in zip(types, ps)}
             d_src = torch.empty_like(sources) if ctx.needs_input_grad[2] else None
@@ -447,13 +466,17 @@ def _autograd():
         def forward(ctx, plan, out, target):
             loss = torch.empty(1, dtype=torch.float32, device=out.device)
             plan.loss_raw(out, target, loss, _stream(torch, out.device))
-            ctx.plan = plan
+            ctx.plan, ctx.gen = plan, plan.loss_gen
             ctx.save_for_backward(out, target)
             return loss[0]
 
         @staticmethod
         def backward(ctx, g):
             out, target = ctx.saved_tensors
+            if ctx.plan.loss_gen != ctx.gen:
+                # another loss forward replaced the cached spectra: recompute this one's
+                scratch = torch.empty(1, dtype=torch.float32, device=out.device)
+                ctx.plan.loss_raw(out, target, scratch, _stream(torch, out.device))
             d_out = torch.empty_like(out)
             ctx.plan.loss_backward_raw(out, target, d_out, _stream(torch, out.device))
             return None, d_out * g, None

@@ -704,12 +704,18 @@ __global__ void __launch_bounds__(256) k_comp_fwd_row(DevCtx c, const float* __r
     }
     __syncthreads();
   }
+  // padding past the last chunk (pitch may exceed n_chunks * CH): zeros, both channels
+  for (int64_t t = int64_t(n_chunks) * CH + 4 * (int64_t(blockIdx.x) * blockDim.x + threadIdx.x); t < pitch;
+       t += 4 * int64_t(gridDim.x) * blockDim.x) {
+    st4(y + t, f4zero());
+    st4(y + pitch + t, f4zero());
+  }
 }
 
 }  // namespace grafx
 
 extern "C" int grafx_compressor_forward_noalloc(const float* u, int64_t len, int64_t pitch, const float* params,
-                                                float* y, void* stream) {
+                                                float* y, uint32_t* status, void* stream) {
   using namespace grafx;
   if (!u || !params || !y) return fail(GRAFX_EINVAL, "null argument");
   if (len < 1 || len > NOALLOC_MAX_LEN)
@@ -719,28 +725,49 @@ extern "C" int grafx_compressor_forward_noalloc(const float* u, int64_t len, int
     return fail(GRAFX_ESHAPE, "pitch must be >= length and a multiple of 4");
   if ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(y)) % 16)
     return fail(GRAFX_EINVAL, "signal rows must be 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(status) % 4) return fail(GRAFX_EINVAL, "status word must be 4-byte aligned");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(GRAFX_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  // Once per device, with that device current: the device address of the scratch array
-  // (in host code its name only stands for it).
+  if (dev < 0 || dev >= 128) return fail(GRAFX_EINVAL, "device ordinal out of range");
+  // The context's id (unique for the life of the process) keys the cached address, so a
+  // context destroyed and re-created on this device (cudaDeviceReset) gets a fresh lookup.
+  using CtxGetId = int (*)(void*, unsigned long long*);
+  static CtxGetId ctx_get_id = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<CtxGetId>(fn);
+  }();
+  if (!ctx_get_id) return fail(GRAFX_ECUDA, "cuCtxGetId is not available from the driver");
+  e = cudaSetDevice(dev);  // initialises the device's primary context if nothing has yet
+  if (e != cudaSuccess) return fail(GRAFX_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  unsigned long long ctx = 0;
+  if (ctx_get_id(nullptr, &ctx) != 0) return fail(GRAFX_ECUDA, "cuCtxGetId failed");
+  // Set-up, once per device (and again only after its context was re-created), with that
+  // device current: the device address of the scratch array (in host code its name only
+  // stands for it).
   static std::mutex mu;
   static unsigned long long* addr[128] = {nullptr};
-  if (dev < 0 || dev >= 128) return fail(GRAFX_EINVAL, "device ordinal out of range");
+  static unsigned long long addr_ctx[128] = {0};
+  unsigned long long* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    if (!addr[dev] || addr_ctx[dev] != ctx) {
       void* ptr = nullptr;
       e = cudaGetSymbolAddress(&ptr, g_comp_noalloc_scratch);
       if (e != cudaSuccess)
         return fail(GRAFX_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       addr[dev] = static_cast<unsigned long long*>(ptr);
+      addr_ctx[dev] = ctx;
     }
+    scratch = addr[dev];
   }
-  unsigned long long* scratch = addr[dev];
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int n_chunks = int((len + NOALLOC_CHUNK - 1) / NOALLOC_CHUNK);
-  // look-back words of this call's chunks, the ticket and the status start at zero
+  // look-back words of this call's chunks, the ticket and the internal status start at zero
   e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * n_chunks, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(scratch + NOALLOC_MAX_CHUNKS, 0, 16, s);
   if (e != cudaSuccess) return fail(GRAFX_ECUDA, std::string("clear scratch: ") + cudaGetErrorString(e));
@@ -748,7 +775,7 @@ extern "C" int grafx_compressor_forward_noalloc(const float* u, int64_t len, int
   std::memset(&c, 0, sizeof(c));
   c.flags = scratch;
   c.tickets = reinterpret_cast<int32_t*>(scratch + NOALLOC_MAX_CHUNKS);
-  c.status = reinterpret_cast<uint32_t*>(scratch + NOALLOC_MAX_CHUNKS + 1);
+  c.status = status ? status : reinterpret_cast<uint32_t*>(scratch + NOALLOC_MAX_CHUNKS + 1);
   const int g = grid_size(n_chunks, 8);
   k_comp_fwd_row<<<g, 256, 0, s>>>(c, u, params, y, int(len), int(pitch), n_chunks);
   e = cudaGetLastError();
