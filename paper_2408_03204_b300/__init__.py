@@ -15,7 +15,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libgrafx.so")
+# GRAFX_VARIANT=precise selects the measurement build of build.py (libgrafx_precise.so)
+LIB_PATH = os.path.join(HERE, "libgrafx_precise.so" if os.environ.get("GRAFX_VARIANT") == "precise"
+                        else "libgrafx.so")
 
 T_IN, T_OUT, T_MIX, T_GAIN, T_IMAGER, T_EQ, T_COMP, T_DELAY, T_REVERB, T_GATE = range(10)
 T_SPLIT, T_MERGE, T_SIDECHAIN = 10, 11, 12   # multi-port processors (inputs x outputs: 1x2, 2x1, 2x1)
@@ -124,7 +126,8 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"libgrafx.so is not built ({LIB_PATH}); run python -m paper_2408_03204_b300.build")
+            raise RuntimeError(f"{os.path.basename(LIB_PATH)} is not built ({LIB_PATH}); "
+                               "run python -m paper_2408_03204_b300.build")
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(L, name)

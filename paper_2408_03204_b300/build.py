@@ -8,7 +8,14 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-LIB = os.path.join(HERE, "libgrafx.so")
+# GRAFX_VARIANT=precise builds libgrafx_precise.so: the compressor's per-sample gain path
+# with correctly rounded ln / exp and IEEE division instead of the hardware
+# approximations (a measurement build; the package loads it under the same variable).
+VARIANT = os.environ.get("GRAFX_VARIANT", "")
+VARIANTS = {"": ("libgrafx.so", "_build", []),
+            "precise": ("libgrafx_precise.so", "_build_precise", ["-DGRAFX_PRECISE_GAIN"])}
+LIB_NAME, OBJDIR, VARIANT_FLAGS = VARIANTS[VARIANT]
+LIB = os.path.join(HERE, LIB_NAME)
 SOURCES = ["capi.cu", "k_elem.cu", "k_eq.cu", "k_comp.cu", "k_loss.cu", "k_optim.cu", "k_delay.cu", "k_reverb.cu", "k_warm.cu", "k_bal.cu", "plan.cpp", "schedule.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -32,10 +39,10 @@ def needs_build():
 def build(force=False, verbose=False, jobs=None):
     if not force and not needs_build():
         return LIB
-    objdir = os.path.join(HERE, "_build")
+    objdir = os.path.join(HERE, OBJDIR)
     os.makedirs(objdir, exist_ok=True)
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                     "-Xptxas", "-O3"]
+                     "-Xptxas", "-O3"] + VARIANT_FLAGS
     procs, objs = [], []
     for s in SOURCES:
         src = os.path.join(CSRC, s)

@@ -105,9 +105,18 @@ __device__ __forceinline__ Knee knee(float gu, const KneeCoef& q) {
 
 // ln and exp of the per-sample gain path: the hardware approximations (__logf: absolute
 // error <= 2^-21.4 on [0.5, 2], 3 ulp elsewhere; __expf: a few ulp over the gains'
-// range), inside the outputs' 1e-5 tolerance.
+// range), inside the outputs' 1e-5 tolerance.  Built with GRAFX_PRECISE_GAIN, the
+// library's correctly rounded logf / expf and an IEEE division instead (the build
+// variant "precise" of build.py), to measure what the approximations cost.
+#ifdef GRAFX_PRECISE_GAIN
+__device__ __forceinline__ float ln_env(float g) { return logf(g + COMP_EPS); }
+__device__ __forceinline__ float exp_gain(float x) { return expf(x); }
+__device__ __forceinline__ float env_div(float a, float b) { return __fdiv_rn(a, b); }
+#else
 __device__ __forceinline__ float ln_env(float g) { return __logf(g + COMP_EPS); }
 __device__ __forceinline__ float exp_gain(float x) { return __expf(x); }
+__device__ __forceinline__ float env_div(float a, float b) { return __fdividef(a, b); }
+#endif
 
 __device__ __forceinline__ unsigned long long pack_flag(unsigned st, float v) {
   return (static_cast<unsigned long long>(st) << 32) | __float_as_uint(v);
@@ -498,7 +507,7 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_bwd(DevCtx c, i
       gain[i] = exp_gain(k.gy - gu);
       float kbar = bl[i] * ul[i] + br[i] * ur[i];
       gyb[i] = kbar * gain[i];
-      a[i] = __fdividef(gyb[i] * (k.dgu - 1.f), g[i] + COMP_EPS);
+      a[i] = env_div(gyb[i] * (k.dgu - 1.f), g[i] + COMP_EPS);
       dT += gyb[i] * k.dt;
       dW += gyb[i] * k.dw;
       dR += gyb[i] * k.dr;

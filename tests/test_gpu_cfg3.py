@@ -1,8 +1,9 @@
 """The batched workload at full size (128 random consoles, uneven L up to 2^18, one
 plan, one launch sequence per schedule step): sampled graphs of the batch against the
-FP64 oracle, forward and backward.  Only the sampled graphs get synthetic sources from
-the shared generator; the other graphs get seeded noise made on the device (their
-renders are independent of the sampled ones: the batch is a disjoint union)."""
+FP64 oracle, forward and backward: the two cheapest, the one with the longest signal,
+the one with the most nodes and the deepest one.  Only the sampled graphs get synthetic
+sources from the shared generator; the other graphs get seeded noise made on the device
+(their renders are independent of the sampled ones: the batch is a disjoint union)."""
 import numpy as np
 import pytest
 
@@ -11,6 +12,20 @@ from gpu_common import GRAD_TOL, assert_grad_close, assert_out_close, union_para
 from oracle import render as orr
 
 pytestmark = pytest.mark.gpu
+
+
+def _depth(g):
+    """Nodes on the longest input -> output path."""
+    preds = {}
+    for s_, d_ in g.edges:
+        preds.setdefault(d_, []).append(s_)
+    done = {}
+
+    def f(v):
+        if v not in done:
+            done[v] = 1 + max((f(u) for u in preds.get(v, [])), default=0)
+        return done[v]
+    return max(f(v) for v in range(g.n_nodes))
 
 
 def test_cfg3_full_batch_sampled_graphs_match_oracle():
@@ -33,7 +48,13 @@ def test_cfg3_full_batch_sampled_graphs_match_oracle():
     gen = torch.Generator(device="cuda").manual_seed(3)
     src = (0.05 * torch.randn(o, device="cuda", generator=gen)).contiguous()
     cost = [g.n_nodes * L for g, L in zip(graphs, lengths)]
+    # the two cheapest graphs, the longest signal, the most nodes and the deepest graph
+    # (longest input -> output path: the largest work lists and scan chunk counts)
     sampled = sorted(range(len(graphs)), key=lambda k: cost[k])[:2]
+    for key in (lambda k: lengths[k], lambda k: graphs[k].n_nodes, lambda k: _depth(graphs[k])):
+        k = max(range(len(graphs)), key=key)
+        if k not in sampled:
+            sampled.append(k)
     per = {}
     for k in sampled:
         g, L, p = graphs[k], lengths[k], pitches[k]
