@@ -339,7 +339,12 @@ int grafx_step_graph_destroy(grafx_step_graph* g);
  * element-wise by a per-column code (codes[i % cols]):
  *   0 identity; 1 alpha = 0.9 + 0.0999 sigmoid(theta); 2 softplus(theta);
  *   3 1 + softplus(theta); 4 -softplus(theta); 5 attack coefficient
- *   0.5 + 0.4999 sigmoid(theta).
+ *   0.5 + 0.4999 sigmoid(theta); 6, 7 a multitap delay tap's Re z and Im z (identity
+ *   maps; a 6 must be followed by a 7 in the same row).
+ * A (6, 7) pair is updated together (Sec. 3 "Multitap delay", after Eq. 15: the paper
+ * normalises the surrogate's z-gradient and pulls z towards the unit circle): its
+ * gradient 2-vector is scaled to unit length (zero stays zero) and the gradient of the
+ * penalty 1e-2 (|z| - 1)^2 at the old z is added before the Adam moments.
  * grafx_adam_step: one Adam update (bias-corrected, step >= 1) of n elements, in place:
  * theta, m, v (device float32, m and v zero before step 1) and param (written with
  * map(theta_new)); grad_param = dLoss/dp from grafx_backprop at the old param.

@@ -13,12 +13,21 @@ physical parameters p = map(theta), element-wise:
   RATIO     p = 1 + softplus(theta)                (ratio R > 1)
   NEGSP     p = -softplus(theta)                   (per-frame decay, < 0)
   ATTACK    p = 0.5 + 0.4999 * sigmoid(theta)      (attack coefficient in (0.5, 0.9999))
+  ZRE, ZIM  p = theta                              (a delay tap's Re z and Im z, a pair)
 
 dLoss/dtheta = dLoss/dp * dp/dtheta.
+
+Multitap delay (Sec. 3, the sentences after Eq. 15): the paper normalises the
+surrogate's z-gradients and pulls z towards the unit circle, without constants.
+Reading (``delay_z_grad``): per (channel, tap) the 2-vector (dL/dRe z, dL/dIm z) is
+scaled to unit L2 norm (a zero vector stays zero), then the gradient of the penalty
+LAMBDA_Z (|z| - 1)^2, LAMBDA_Z = 1e-2, is added; Adam takes that as the pair's
+gradient.  The penalty enters the update only, not the reported loss.
 """
 import numpy as np
 
-IDENT, ALPHA, SOFTPLUS, RATIO, NEGSP, ATTACK = range(6)
+IDENT, ALPHA, SOFTPLUS, RATIO, NEGSP, ATTACK, ZRE, ZIM = range(8)
+LAMBDA_Z = 1e-2
 
 
 def softplus(x):
@@ -69,6 +78,31 @@ def to_theta(param, code):
     return out
 
 
+def z_penalty(zr, zi, lam=LAMBDA_Z):
+    """The unit-circle regulariser lam (|z| - 1)^2 of a delay tap."""
+    return lam * (np.hypot(zr, zi) - 1.0) ** 2
+
+
+def delay_z_grad(theta, grad_theta, code, lam=LAMBDA_Z):
+    """The delay taps' update direction: every (ZRE, ZIM) column pair of grad_theta
+    scaled to unit length, plus the gradient of z_penalty at theta's (Re z, Im z); other
+    columns unchanged.  Rows are the last axis's column layout ``code``."""
+    theta = np.asarray(theta, dtype=np.float64)
+    g = np.array(grad_theta, dtype=np.float64, copy=True)
+    code = np.asarray(code)
+    for j in np.flatnonzero(code == ZRE):
+        assert code[j + 1] == ZIM
+        gr, gi = g[..., j], g[..., j + 1]
+        n = np.hypot(gr, gi)
+        safe = np.where(n > 0, n, 1.0)
+        gr, gi = np.where(n > 0, gr / safe, 0.0), np.where(n > 0, gi / safe, 0.0)
+        zr, zi = theta[..., j], theta[..., j + 1]
+        r = np.hypot(zr, zi)
+        k = np.where(r > 0, 2.0 * lam * (r - 1.0) / np.where(r > 0, r, 1.0), 0.0)
+        g[..., j], g[..., j + 1] = gr + k * zr, gi + k * zi
+    return g
+
+
 def adam_step(theta, m, v, grad_theta, t, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update (step t >= 1); returns new (theta, m, v)."""
     g = np.asarray(grad_theta, dtype=np.float64)
@@ -93,4 +127,6 @@ def param_codes(t, cols):
     elif t == 8:                     # reverb, per-bin layout [mid, side] x [H0 (K), H_delta (K)]
         K = cols // 4
         codes = np.tile(np.repeat(np.array([IDENT, NEGSP], dtype=np.int8), K), 2)
+    if t == 7:                       # delay: per (channel, tap) [Re z, Im z, 20 log-magnitudes]
+        codes = np.tile(np.array([ZRE, ZIM] + [IDENT] * 20, dtype=np.int8), cols // 22)
     return codes

@@ -10,7 +10,13 @@
 
 namespace grafx {
 
-enum : int8_t { MAP_IDENT = 0, MAP_ALPHA = 1, MAP_SOFTPLUS = 2, MAP_RATIO = 3, MAP_NEGSP = 4, MAP_ATTACK = 5 };
+enum : int8_t {
+  MAP_IDENT = 0, MAP_ALPHA = 1, MAP_SOFTPLUS = 2, MAP_RATIO = 3, MAP_NEGSP = 4, MAP_ATTACK = 5,
+  MAP_ZRE = 6, MAP_ZIM = 7   // a multitap delay tap's (Re z, Im z): identity maps, updated as a pair
+};
+// Weight of the delay taps' unit-circle penalty lam (|z| - 1)^2 (Sec. 3 "Multitap delay":
+// the paper pulls z towards the unit circle without giving a weight; 1e-2 is a reading).
+constexpr float Z_PENALTY = 1e-2f;
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.f / (1.f + expf(-x)); }
 __device__ __forceinline__ float softplusf_(float x) { return x > 20.f ? x : log1pf(expf(x)); }
@@ -56,20 +62,49 @@ __device__ __forceinline__ float unmap_param(float p, int code) {
   }
 }
 
+// One Adam update of element i with gradient g (dLoss/dtheta).
+__device__ __forceinline__ void adam_elem(float* theta, float* m, float* v, float* p, int64_t i, float g, int code,
+                                          float b1, float b2, float lr, float eps, float bc1, float bc2) {
+  const float mi = b1 * m[i] + (1.f - b1) * g;
+  const float vi = b2 * v[i] + (1.f - b2) * g * g;
+  const float nt = theta[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  m[i] = mi;
+  v[i] = vi;
+  theta[i] = nt;
+  p[i] = map_param(nt, code);
+}
+
+// The update direction of one delay tap's z = (zr, zi) from its gradient (gr, gi): the
+// 2-vector scaled to unit length (zero stays zero), plus the gradient of the penalty
+// Z_PENALTY (|z| - 1)^2, 2 Z_PENALTY (|z| - 1) z / |z| (zero at z = 0).
+__device__ __forceinline__ void delay_z_grad(float zr, float zi, float gr, float gi, float* outr, float* outi) {
+  const float n = hypotf(gr, gi);
+  if (n > 0.f) {
+    gr /= n;
+    gi /= n;
+  } else {
+    gr = gi = 0.f;
+  }
+  const float r = hypotf(zr, zi);
+  const float k = r > 0.f ? 2.f * Z_PENALTY * (r - 1.f) / r : 0.f;
+  *outr = gr + k * zr;
+  *outi = gi + k * zi;
+}
+
 __global__ void k_adam(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
                        const float* __restrict__ gp, float* __restrict__ p, const int8_t* __restrict__ codes,
                        int cols, int64_t n, float lr, float b1, float b2, float eps, float bc1, float bc2) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const int code = codes[i % cols];
-    const float th = theta[i];
-    const float g = gp[i] * map_slope(th, code);
-    const float mi = b1 * m[i] + (1.f - b1) * g;
-    const float vi = b2 * v[i] + (1.f - b2) * g * g;
-    const float nt = th - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-    m[i] = mi;
-    v[i] = vi;
-    theta[i] = nt;
-    p[i] = map_param(nt, code);
+    if (code == MAP_ZIM) continue;   // updated with its Re z partner
+    if (code == MAP_ZRE) {
+      float gr, gi;
+      delay_z_grad(theta[i], theta[i + 1], gp[i], gp[i + 1], &gr, &gi);
+      adam_elem(theta, m, v, p, i, gr, MAP_IDENT, b1, b2, lr, eps, bc1, bc2);
+      adam_elem(theta, m, v, p, i + 1, gi, MAP_IDENT, b1, b2, lr, eps, bc1, bc2);
+      continue;
+    }
+    adam_elem(theta, m, v, p, i, gp[i] * map_slope(theta[i], code), code, b1, b2, lr, eps, bc1, bc2);
   }
 }
 
@@ -89,15 +124,15 @@ __global__ void k_adam_dev(float* __restrict__ theta, float* __restrict__ m, flo
   const float bc1 = bc[0], bc2 = bc[1];
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const int code = codes[i % cols];
-    const float th = theta[i];
-    const float g = gp[i] * map_slope(th, code);
-    const float mi = b1 * m[i] + (1.f - b1) * g;
-    const float vi = b2 * v[i] + (1.f - b2) * g * g;
-    const float nt = th - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-    m[i] = mi;
-    v[i] = vi;
-    theta[i] = nt;
-    p[i] = map_param(nt, code);
+    if (code == MAP_ZIM) continue;   // updated with its Re z partner
+    if (code == MAP_ZRE) {
+      float gr, gi;
+      delay_z_grad(theta[i], theta[i + 1], gp[i], gp[i + 1], &gr, &gi);
+      adam_elem(theta, m, v, p, i, gr, MAP_IDENT, b1, b2, lr, eps, bc1, bc2);
+      adam_elem(theta, m, v, p, i + 1, gi, MAP_IDENT, b1, b2, lr, eps, bc1, bc2);
+      continue;
+    }
+    adam_elem(theta, m, v, p, i, gp[i] * map_slope(theta[i], code), code, b1, b2, lr, eps, bc1, bc2);
   }
 }
 

@@ -5,14 +5,15 @@ a fused Adam step per type, all through the C-ABI library on one stream.  A whol
 
 Unconstrained variables theta map to the processors' parameters column by column
 (grafx_adam_step codes): compressor and noisegate [alpha, T, W, R] -> [alpha map,
-identity, softplus, 1 + softplus]; reverb decay columns -> -softplus; everything else
-identity.
+identity, softplus, 1 + softplus]; reverb decay columns -> -softplus; a delay tap's
+(Re z, Im z) is updated with its gradient normalised and a unit-circle penalty added
+(Sec. 3 "Multitap delay"); everything else identity.
 """
 import ctypes
 
 from . import PARAM_COLS, T_BALLISTIC, T_COMP, T_DELAY, T_GATE, T_REVERB, T_SIDECHAIN, _check, _ptr, _stream_of, lib
 
-MAP_IDENT, MAP_ALPHA, MAP_SOFTPLUS, MAP_RATIO, MAP_NEGSP, MAP_ATTACK = range(6)
+MAP_IDENT, MAP_ALPHA, MAP_SOFTPLUS, MAP_RATIO, MAP_NEGSP, MAP_ATTACK, MAP_ZRE, MAP_ZIM = range(8)
 
 
 def param_codes(t, cols=None):
@@ -30,6 +31,9 @@ def param_codes(t, cols=None):
         # per-bin layout: [mid/side][H0 x K, H_delta x K]
         K = cols // 4
         return ([MAP_IDENT] * K + [MAP_NEGSP] * K) * 2
+    if t == T_DELAY:
+        # per (channel, tap): [Re z, Im z, 20 log-magnitudes]; z normalised and regularised
+        return ([MAP_ZRE, MAP_ZIM] + [MAP_IDENT] * 20) * (cols // 22)
     return [MAP_IDENT] * cols
 
 

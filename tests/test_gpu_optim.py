@@ -57,3 +57,37 @@ def test_adam_steps_match_oracle(t):
     torch.cuda.synchronize()
     np.testing.assert_allclose(th.cpu().numpy(), th_o, rtol=1e-5, atol=1e-5)
     np.testing.assert_allclose(p.cpu().numpy(), oo.to_param(th_o, codes), rtol=1e-5, atol=1e-6)
+
+
+def test_adam_delay_taps_normalised_and_regularised():
+    """Delay rows (Sec. 3 after Eq. 15): each tap's z-gradient scaled to unit length plus
+    the unit-circle penalty's gradient, then Adam; the FIR log-magnitudes as plain Adam."""
+    import torch
+    import paper_2408_03204_b300 as gx
+    lib = gx.lib()
+    rng = np.random.Generator(np.random.PCG64(7))
+    rows, cols = 29, 176
+    codes = oo.param_codes(7, cols)
+    P0 = rng.uniform(-1.3, 1.3, (rows, cols)).astype(np.float32)
+    P0[3, 0:2] = 0.0                                   # z = 0 (penalty gradient taken as 0)
+    dev = torch.device("cuda")
+    p = torch.tensor(P0, device=dev)
+    cd = torch.tensor(codes, device=dev)
+    th = p.clone()
+    st = gx._stream(torch, dev)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    th_o = P0.astype(np.float64)
+    m, v = torch.zeros_like(p), torch.zeros_like(p)
+    mo, vo = np.zeros_like(th_o), np.zeros_like(th_o)
+    for t in range(1, 7):
+        gp = (rng.standard_normal((rows, cols)) * 10.0 ** rng.uniform(-6, 3, (rows, cols))).astype(np.float32)
+        gp[5, 22:24] = 0.0                             # a zero z-gradient stays zero
+        g = torch.tensor(gp, device=dev)
+        assert lib.grafx_adam_step(ptr(th), ptr(m), ptr(v), ptr(g), ptr(p), ptr(cd), cols, p.numel(), t,
+                                   ctypes.c_float(1e-2), ctypes.c_float(0.9), ctypes.c_float(0.999),
+                                   ctypes.c_float(1e-8), st) == 0
+        gth = oo.delay_z_grad(th_o, gp.astype(np.float64), codes)
+        th_o, mo, vo = oo.adam_step(th_o, mo, vo, gth, t, lr=1e-2)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(th.cpu().numpy(), th_o, rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(p.cpu().numpy(), th_o, rtol=1e-5, atol=1e-5)
