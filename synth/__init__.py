@@ -12,4 +12,4 @@ Node type ids are fixed data (the paper's type letters, Sec. 2, Fig. 1 and 2b):
 from .types import TYPE_IDS, TYPE_LETTERS, I, O, M, G, S, E, C, D, R, N, P, J, K, A, PARAM_COLS, PAPER_PARAM_COLS, param_cols  # noqa: F401
 from .graphs import Graph, console_cfg1, console_cfg2, random_console, batch_cfg3, console_all_types  # noqa: F401
 from .signals import sources, reverb_noise  # noqa: F401
-from .params import random_params, neutral_params  # noqa: F401
+from .params import random_params, neutral_params, union_params  # noqa: F401

@@ -136,6 +136,16 @@ def random_params(graph, seed: int, preset="compact"):
     return out
 
 
+def union_params(graphs, seed: int, preset="compact"):
+    """One table per type over a batch of graphs (the union's original order: graph by
+    graph), graph k's rows drawn by ``random_params(graphs[k], seed + k)``."""
+    tabs = {}
+    for k, g in enumerate(graphs):
+        for t, a in random_params(g, seed + k, preset=preset).items():
+            tabs.setdefault(t, []).append(a)
+    return {t: np.concatenate(v) for t, v in tabs.items()}
+
+
 def neutral_params(graph, preset="compact"):
     """Parameters that make g, s, e and c (nearly) transparent: 0 dB gains, flat EQ,
     ratio 1; reverb fully dry (compact) or a short quiet tail (paper: no dry path);
