@@ -731,10 +731,11 @@ def main():
                 not args.no_autotune, dist, e2e_steps=args.e2e_steps)
     units = sum_over_ranks(r["node_samples"], dist, dev)        # node-samples of one whole-job step
     value = units * args.steps / (r["ms_total"] / 1e3)
-    e = r["e2e"]
-    e2e_line = {"value": units * e["steps"] / (e["ms_total"] / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": e["h2d_bytes_per_step"], "d2h_bytes_per_step": e["d2h_bytes_per_step"],
-                "ms_per_step": e["ms_per_step"], "loss": e["loss"]}
+    e = r.get("e2e")
+    e2e_line = None if e is None else {
+        "value": units * e["steps"] / (e["ms_total"] / 1e3), "unit": UNIT,
+        "h2d_bytes_per_step": e["h2d_bytes_per_step"], "d2h_bytes_per_step": e["d2h_bytes_per_step"],
+        "ms_per_step": e["ms_per_step"], "loss": e["loss"]}
 
     secondary = None
     if name == "batch128" and not args.no_secondary:

@@ -55,6 +55,7 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
   c.eq_aux = at<float>(p, p->ws.eq_aux);
   c.eq_bandpart = at<float>(p, p->ws.eq_bandpart);
   c.comp_carry = at<float>(p, p->ws.comp_carry);
+  c.comp_agg = at<float>(p, p->ws.comp_agg);
   c.dl_aux = at<float>(p, p->ws.dl_aux);
   c.dl_spec = at<float2>(p, p->ws.dl_spec);
   c.dl_R = at<float2>(p, p->ws.dl_R);
@@ -120,11 +121,6 @@ int check_ready(const Plan* p) {
 
 int param_cols(const Plan* p, int t) { return t >= 0 && t < GRAFX_N_TYPES ? p->pcols[t] : 0; }
 
-// Look-back flags of the items [item0, item0+n) and the step's ticket counter start at 0.
-void clear_step_flags(const Plan* p, int item0, int n, int ticket, cudaStream_t s) {
-  cudaMemsetAsync(p->dev_ws + p->ws.flags + size_t(item0) * 8, 0, size_t(n) * 8, s);
-  cudaMemsetAsync(p->dev_ws + p->ws.tickets + size_t(ticket) * 4, 0, 4, s);
-}
 
 LossLaunch make_loss(const Plan* p, const float* y, const float* tgt) {
   LossLaunch L;
@@ -473,8 +469,8 @@ static int render_range(grafx_plan* p, const float* sources, float* out, int32_t
       case GRAFX_T_COMP:
       case GRAFX_T_GATE:
       case GRAFX_T_SIDECHAIN:
-        clear_step_flags(p, st.fitem_begin, st.fitem_count, 2 * k, s);
-        launches += launch_comp(0, c, st.fitem_begin, st.fitem_count, 2 * k, comp_mode_of(st.type), s);
+        launches += launch_comp(0, c, st.fitem_begin, st.fitem_count, st.node_begin, st.node_end,
+                                comp_mode_of(st.type), s);
         break;
       case GRAFX_T_DELAY:
         launches += launch_delay(1, c, st.fitem_begin, st.fitem_count, s);
@@ -622,11 +618,11 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
       case GRAFX_T_COMP:
       case GRAFX_T_GATE:
       case GRAFX_T_SIDECHAIN:
-        clear_step_flags(p, st.bitem_begin, st.bitem_count, 2 * k + 1, s);
-        launches += launch_comp(1, c, st.bitem_begin, st.bitem_count, 2 * k + 1, comp_mode_of(st.type), s);
+        launches += launch_comp(1, c, st.bitem_begin, st.bitem_count, st.node_begin, st.node_end,
+                                comp_mode_of(st.type), s);
         if (c.dparams) {
           to_side(k);
-          launches += launch_comp(2, c, st.node_begin, st.node_end, 0, 0, side);
+          launches += launch_comp(2, c, 0, 0, st.node_begin, st.node_end, 0, side);
         }
         break;
       case GRAFX_T_REVERB:
@@ -762,7 +758,7 @@ int grafx_step_graph_create(grafx_plan* p, const float* sources, float* out, con
   // kernel attributes are set outside the capture
   DevCtx c0 = make_ctx(p, sources, out, nullptr, nullptr);
   launch_eq(-1, c0, 0, 0, s);
-  launch_comp(-1, c0, 0, 0, 0, 0, s);
+  launch_comp(-1, c0, 0, 0, 0, 0, 0, s);
   launch_delay(-1, c0, 0, 0, s);
   launch_reverb(-1, c0, 0, 0, s);
   launch_loss(-1, make_loss(p, out, target), s);

@@ -5,20 +5,23 @@
 // One work item is a chunk of CH = 256 * SPT samples of one node.  Inside a chunk:
 // every thread runs the recursion over its SPT samples with zero initial state, a
 // warp-shuffle scan and a cross-warp scan combine the per-thread states with the
-// decay a^SPT, and the chunk's carry-in comes from the chunks before it by a
-// decoupled look-back: each chunk publishes its zero-start end state, then its
-// inclusive end state once its carry is known; one warp of a chunk reads the 32
-// preceding states at once and walks back until it meets an inclusive one.  Chunks are handed out by an atomic
-// ticket in (node, chunk) order, so every chunk waited on is held by a CTA that is
-// already running; every wait is bounded and records ST_TIMEOUT on expiry.
-// The forward pass stores each chunk's carry-in (one float) so the backward pass
-// can recompute g[n] exactly without a scan across chunks.
+// decay a^SPT.  Across chunks (the render path): three passes, with no chunk waiting
+// for another -- every chunk's zero-start end state (its aggregate), a per-node scan of
+// the aggregates with the decay of one chunk, then every chunk from its entering state.
+// The forward pass stores each chunk's entering state (one float) so the backward pass
+// can recompute g[n] exactly.
 //
 // Backward: ybar gives a_n = dL/dg[n]; lambda[n] = a_n + alpha lambda[n+1] is the
-// same scan run in reverse (chunks handed out from the end of each node);
-// ubar_x = k ybar_x + 2 u_m (1 - alpha) lambda and the parameter partials
-// (sum lambda (g[n-1] - x[n]) for alpha, sum Gybar dGy/dT|W|R) go to one slot
-// per chunk.
+// same three passes run in reverse; ubar_x = k ybar_x + 2 u_m (1 - alpha) lambda and the
+// parameter partials (sum lambda (g[n-1] - x[n]) for alpha, sum Gybar dGy/dT|W|R) go to
+// one slot per chunk.
+//
+// The allocation-free single-row forward at the end of this file keeps one pass over the
+// signal with a decoupled look-back instead: each chunk publishes its zero-start end
+// state, then its inclusive end state once its carry is known; one warp of a chunk reads
+// the 32 preceding states at once and walks back until it meets an inclusive one.  Chunks
+// are handed out by an atomic ticket in chunk order, so every chunk waited on is held by
+// a CTA that is already running; every wait is bounded and records ST_TIMEOUT on expiry.
 #include <cstring>
 #include <mutex>
 
@@ -293,58 +296,6 @@ __device__ __forceinline__ void load_range(const DevCtx& c, int e0, int e1, cons
 // compressor (the compressor's curve; envelope from input 1, gain on input 0).
 constexpr int MODE_COMP = 0, MODE_GATE = 1, MODE_SC = 2;
 
-// Prefetch: this thread's SPT samples of both channels of `row` from t into its own
-// slots dst[ch * 256 * SPT + threadIdx.x * SPT ...] (zeros past the node's length).
-// Every thread reads back only its own slots, so one buffer serves consecutive chunks.
-template <int SPT>
-__device__ __forceinline__ void prefetch_rows(float* dst, const float* row, const NodeDev& nd, int t) {
-  constexpr int CH = 256 * SPT;
-#pragma unroll
-  for (int ch = 0; ch < 2; ++ch)
-#pragma unroll
-    for (int q = 0; q < SPT / 4; ++q) {
-      const int tq = t + 4 * q;
-      const bool in = tq < nd.len;
-      cp_async16(dst + ch * CH + threadIdx.x * SPT + 4 * q, in ? row + ch * nd.pitch + tq : row, in ? 16 : 0);
-    }
-}
-
-template <int SPT>
-__device__ __forceinline__ void read_rows(const float* src, const NodeDev& nd, int t, float* l, float* r) {
-  constexpr int CH = 256 * SPT;
-#pragma unroll
-  for (int q = 0; q < SPT / 4; ++q) {
-    float4 a = *reinterpret_cast<const float4*>(src + threadIdx.x * SPT + 4 * q);
-    float4 b = *reinterpret_cast<const float4*>(src + CH + threadIdx.x * SPT + 4 * q);
-    a = mask4(a, t + 4 * q, nd.len);
-    b = mask4(b, t + 4 * q, nd.len);
-    l[4 * q] = a.x, l[4 * q + 1] = a.y, l[4 * q + 2] = a.z, l[4 * q + 3] = a.w;
-    r[4 * q] = b.x, r[4 * q + 1] = b.y, r[4 * q + 2] = b.z, r[4 * q + 3] = b.w;
-  }
-}
-
-// Start the copies of item `it`'s single-row inputs (u, and with ADJ also ybar) into buf.
-template <int SPT, bool ADJ>
-__device__ __forceinline__ void prefetch_item(const DevCtx& c, int item, float* buf) {
-  constexpr int CH = 256 * SPT;
-  const int4_ w = c.items[item];
-  const NodeDev nd = c.nodes[w.x];
-  const int t = w.y * CH + threadIdx.x * SPT;
-  if (const float* row = single_row(c, w.x, false)) prefetch_rows<SPT>(buf, row, nd, t);
-  if (ADJ)
-    if (const float* row = single_row(c, w.x, true)) prefetch_rows<SPT>(buf + 2 * CH, row, nd, t);
-  cp_async_commit();
-}
-
-// This thread's u (and ybar) of the current chunk: from the prefetch buffer when the
-// node has a single row feeding it, else gathered.
-template <int SPT>
-__device__ __forceinline__ void fetch_rows(const DevCtx& c, int v, const NodeDev& nd, int t, const float* buf,
-                                           float* l, float* r, bool adj) {
-  if (single_row(c, v, adj)) read_rows<SPT>(buf, nd, t, l, r);
-  else load_chunk<SPT>(c, v, nd, t, l, r, adj);
-}
-
 template <int SPT>
 __device__ __forceinline__ void store_chunk(float* row, const NodeDev& nd, int t, const float* yl, const float* yr) {
 #pragma unroll
@@ -368,67 +319,116 @@ __device__ __forceinline__ void envelope(const float* x, float alpha, float cin,
   }
 }
 
-// Software-pipelined over tickets: once a chunk's inputs are in registers, the next
-// ticket's copies start (cp.async) and run under this chunk's scan, look-back and gain.
+// The envelope recursion g[n] = alpha g[n-1] + (1 - alpha) x[n] is linear, so a chunk's
+// effect on the chunks after it is one number: its state at the chunk's end with zero
+// entering it (its aggregate).  Forward: (1) every chunk's aggregate (k_comp_agg), (2)
+// per node, the state entering every chunk by a scan over its aggregates with the decay
+// D = alpha^CH of one chunk (k_comp_scan, one warp per node), (3) every chunk again
+// from its entering state: envelope, gain, output (k_comp_apply).  The backward does
+// the same for the reverse recursion lambda[n] = a[n] + alpha lambda[n+1].  No chunk
+// waits for another; the inputs are read twice.
+
+// The envelope input x[n] of this thread's samples: the squared mid of the node's input
+// (the compressor and the noisegate) or of its key, input 1 (the sidechain compressor).
 template <int SPT, int MODE>
-__global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_fwd(DevCtx c, int item0, int n_items, int ticket) {
+__device__ __forceinline__ void env_input(const DevCtx& c, int v, const NodeDev& nd, int t, float* x) {
+  float l[SPT], r[SPT];
+  if constexpr (MODE == MODE_SC) load_range<SPT>(c, c.in1_begin[v], c.csr_ptr[v + 1], nd, t, l, r);
+  else load_chunk<SPT>(c, v, nd, t, l, r, false);
+#pragma unroll
+  for (int i = 0; i < SPT; ++i) {
+    const float m = l[i] + r[i];
+    x[i] = m * m;
+  }
+}
+
+// Forward pass 1: the chunk's envelope state at its end with zero entering it.
+template <int SPT, int MODE>
+__global__ void __launch_bounds__(256, SPT >= 16 ? 3 : 4) k_comp_agg(DevCtx c, int item0, int n_items) {
+  constexpr int CH = 256 * SPT;
+  __shared__ float sh[32];
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int4_ w = c.items[item0 + it];
+    const int v = w.x;
+    const NodeDev nd = c.nodes[v];
+    const float alpha = c.params[nd.prow * 4];
+    const float la = logf(alpha);
+    float x[SPT];
+    env_input<SPT, MODE>(c, v, nd, w.y * CH + threadIdx.x * SPT, x);
+    float b = 0.f;
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) b = alpha * b + (1.f - alpha) * x[i];
+    float total;
+    block_affine_scan<false>(b, la * SPT, sh, &total);
+    if (threadIdx.x == 0) c.comp_agg[w.z] = total;
+    __syncthreads();   // sh is reused by the next item
+  }
+}
+
+// Pass 2: per node (one warp), the state entering every chunk from its chunks' aggregates
+// src[z0 + j] (z0 = the node's first chunk slot): forward, enter_j = D enter_(j-1) +
+// src[j-1] with enter_0 = 0; REVERSE, the same from the node's last chunk down.  Written
+// to dst[z0 + j] (dst may be src: every lane reads its chunk before writing it).
+template <bool REVERSE>
+__global__ void __launch_bounds__(256) k_comp_scan(DevCtx c, int node_begin, int node_end, int ch_len,
+                                                   const float* src, float* dst) {
+  const int lane = threadIdx.x & 31;
+  const int v = node_begin + int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (v >= node_end) return;   // the whole warp
+  const NodeDev nd = c.nodes[v];
+  const int z0 = c.ext[v].z, nc = (nd.len + ch_len - 1) / ch_len;
+  const float lc = logf(c.params[nd.prow * 4]) * float(ch_len);   // ln D
+  const float d_lane = expf(lc * float(lane)), d_32 = expf(lc * 32.f);
+  float run = 0.f;   // state entering this block of 32 chunks (in scan order)
+  for (int base = 0; base < nc; base += 32) {
+    const int q = base + lane;
+    const int j = REVERSE ? nc - 1 - q : q;
+    const float a = q < nc ? src[z0 + j] : 0.f;
+    float s = a, dd = expf(lc);   // inclusive: s_l = D s_(l-1) + a_l; dd = D^d
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const float o = __shfl_up_sync(0xffffffffu, s, d);
+      if (lane >= d) s += dd * o;
+      dd *= dd;
+    }
+    float prev = __shfl_up_sync(0xffffffffu, s, 1);
+    if (lane == 0) prev = 0.f;
+    if (q < nc) dst[z0 + j] = d_lane * run + prev;
+    run = d_32 * run + __shfl_sync(0xffffffffu, s, 31);
+  }
+}
+
+// Forward pass 3: the chunk from its entering state (stored for the backward).
+template <int SPT, int MODE>
+__global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_apply(DevCtx c, int item0, int n_items) {
   constexpr int CH = 256 * SPT;
   constexpr bool GATE = MODE == MODE_GATE, SC = MODE == MODE_SC;
-  __shared__ __align__(16) float buf[2 * CH];
   __shared__ float sh[32];
-  __shared__ int s_it[2];
-  __shared__ float s_carry;
-  if (threadIdx.x == 0) s_it[0] = atomicAdd(c.tickets + ticket, 1);
-  __syncthreads();
-  int it = s_it[0], slot = 0;
-  if (!SC && it < n_items) prefetch_item<SPT, false>(c, item0 + it, buf);
-  while (it < n_items) {
-    if (threadIdx.x == 0) s_it[slot ^ 1] = atomicAdd(c.tickets + ticket, 1);  // read after the scan's barriers
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
-    const int v = w.x, chunk = w.y;
+    const int v = w.x;
     const NodeDev nd = c.nodes[v];
     const float* p = c.params + nd.prow * 4;
     const float alpha = p[0];
     const KneeCoef kq = knee_coef(p[1], p[2], p[3]);
     const float la = logf(alpha);
-    const int t = chunk * CH + threadIdx.x * SPT;
+    const int t = w.y * CH + threadIdx.x * SPT;
     float ul[SPT], ur[SPT], x[SPT], g[SPT];
-    cp_async_wait_all();
     if constexpr (SC) {
-      float kl[SPT], kr[SPT];
-      load_range<SPT>(c, c.csr_ptr[v], c.in1_begin[v], nd, t, ul, ur);      // main (input 0)
-      load_range<SPT>(c, c.in1_begin[v], c.csr_ptr[v + 1], nd, t, kl, kr);  // key (input 1)
-#pragma unroll
-      for (int i = 0; i < SPT; ++i) { float m = kl[i] + kr[i]; x[i] = m * m; }
+      load_range<SPT>(c, c.csr_ptr[v], c.in1_begin[v], nd, t, ul, ur);   // main (input 0)
+      env_input<SPT, MODE>(c, v, nd, t, x);                               // key (input 1)
     } else {
-      fetch_rows<SPT>(c, v, nd, t, buf, ul, ur, false);
+      load_chunk<SPT>(c, v, nd, t, ul, ur, false);
 #pragma unroll
       for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
     }
-    // zero-start local state at the thread's end
     float b = 0.f;
 #pragma unroll
     for (int i = 0; i < SPT; ++i) b = alpha * b + (1.f - alpha) * x[i];
     float total;
-    float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
-    const int next = s_it[slot ^ 1];
-    if (!SC && next < n_items) prefetch_item<SPT, false>(c, item0 + next, buf);
-    if (threadIdx.x < 32) {
-      float carry = 0.f;
-      if (chunk == 0) {
-        if (threadIdx.x == 0) publish(c, item0 + it, 2, total);
-      } else {
-        if (threadIdx.x == 0) publish(c, item0 + it, 1, total);
-        carry = look_back_warp(c, item0 + it - 1, item0 + it - chunk, la * CH);
-        if (threadIdx.x == 0) publish(c, item0 + it, 2, expf(la * CH) * carry + total);
-      }
-      if (threadIdx.x == 0) {
-        c.comp_carry[w.z] = carry;
-        s_carry = carry;
-      }
-    }
-    __syncthreads();
-    const float cin = excl + expf(la * float(SPT * threadIdx.x)) * s_carry;
+    const float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
+    const float carry = c.comp_carry[w.z];
+    const float cin = excl + expf(la * float(SPT * threadIdx.x)) * carry;
     envelope<SPT>(x, alpha, cin, g);
 #pragma unroll
     for (int i = 0; i < SPT; ++i) {
@@ -439,101 +439,82 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_fwd(DevCtx c, i
       ur[i] *= gain;
     }
     store_chunk<SPT>(yrow_w(c, nd), nd, t, ul, ur);
-    __syncthreads();
-    it = next;
-    slot ^= 1;
+    __syncthreads();   // sh is reused by the next item
   }
-  cp_async_wait_all();
 }
 
-template <int SPT, int MODE>
-__global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_bwd(DevCtx c, int item0, int n_items, int ticket) {
+// Backward of one chunk.  APPLY = false (pass 1): the chunk's reverse state at its start
+// with zero entering from its end, to comp_agg.  APPLY = true (pass 3): lambda from the
+// state entering from the right (comp_agg after the reverse scan), the input adjoints
+// and the parameter-gradient partials of the chunk.
+template <int SPT, int MODE, bool APPLY>
+__global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_back(DevCtx c, int item0, int n_items) {
   constexpr int CH = 256 * SPT;
   constexpr bool GATE = MODE == MODE_GATE, SC = MODE == MODE_SC;
-  extern __shared__ __align__(16) float buf[];  // 4 * CH floats: prefetched u and ybar rows
   __shared__ float sh[32];
   __shared__ float glast[256];
   __shared__ float red[4 * 32];
-  __shared__ int s_it[2];
-  __shared__ float s_lin;
-  if (threadIdx.x == 0) s_it[0] = atomicAdd(c.tickets + ticket, 1);
-  __syncthreads();
-  int it = s_it[0], slot = 0;
-  if (!SC && it < n_items) prefetch_item<SPT, true>(c, item0 + it, buf);
-  while (it < n_items) {
-    if (threadIdx.x == 0) s_it[slot ^ 1] = atomicAdd(c.tickets + ticket, 1);  // read after the scan's barriers
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
-    const int v = w.x, chunk = w.y;
+    const int v = w.x;
     const NodeDev nd = c.nodes[v];
     const float* p = c.params + nd.prow * 4;
     const float alpha = p[0];
     const KneeCoef kq = knee_coef(p[1], p[2], p[3]);
     const float la = logf(alpha);
-    const int t = chunk * CH + threadIdx.x * SPT;
-    const int n_chunks = (nd.len + CH - 1) / CH;
+    const int t = w.y * CH + threadIdx.x * SPT;
     float ul[SPT], ur[SPT], bl[SPT], br[SPT], x[SPT], g[SPT], a[SPT];
     float km[SC ? SPT : 1];   // sidechain: the key's mid l + r
-    cp_async_wait_all();
     if constexpr (SC) {
       float kr[SPT];
       load_range<SPT>(c, c.csr_ptr[v], c.in1_begin[v], nd, t, ul, ur);      // main (input 0)
       load_range<SPT>(c, c.in1_begin[v], c.csr_ptr[v + 1], nd, t, km, kr);  // key (input 1)
-      load_chunk<SPT>(c, v, nd, t, bl, br, true);
 #pragma unroll
       for (int i = 0; i < SPT; ++i) { km[i] += kr[i]; x[i] = km[i] * km[i]; }
     } else {
-      fetch_rows<SPT>(c, v, nd, t, buf, ul, ur, false);
-      fetch_rows<SPT>(c, v, nd, t, buf + 2 * CH, bl, br, true);
+      load_chunk<SPT>(c, v, nd, t, ul, ur, false);
 #pragma unroll
       for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
     }
-    // recompute the envelope from the stored chunk carry-in (same arithmetic as forward)
+    load_chunk<SPT>(c, v, nd, t, bl, br, true);
+    // the envelope from the forward's stored chunk state (same arithmetic as the forward)
     const float carry_g = c.comp_carry[w.z];
     float b = 0.f;
 #pragma unroll
     for (int i = 0; i < SPT; ++i) b = alpha * b + (1.f - alpha) * x[i];
     float total;
-    float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
-    const int next = s_it[slot ^ 1];
-    if (!SC && next < n_items) prefetch_item<SPT, true>(c, item0 + next, buf);
+    const float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
     const float cin = excl + expf(la * float(SPT * threadIdx.x)) * carry_g;
     envelope<SPT>(x, alpha, cin, g);
     // local adjoints
-    float gain[SPT], gyb[SPT], dT = 0.f, dW = 0.f, dR = 0.f;
+    float gain[SPT], dT = 0.f, dW = 0.f, dR = 0.f;
 #pragma unroll
     for (int i = 0; i < SPT; ++i) {
       float gu = ln_env(g[i]);
       Knee k = GATE ? gate_knee(gu, kq) : knee(gu, kq);
       gain[i] = exp_gain(k.gy - gu);
-      float kbar = bl[i] * ul[i] + br[i] * ur[i];
-      gyb[i] = kbar * gain[i];
-      a[i] = env_div(gyb[i] * (k.dgu - 1.f), g[i] + COMP_EPS);
-      dT += gyb[i] * k.dt;
-      dW += gyb[i] * k.dw;
-      dR += gyb[i] * k.dr;
+      const float gyb = (bl[i] * ul[i] + br[i] * ur[i]) * gain[i];
+      a[i] = env_div(gyb * (k.dgu - 1.f), g[i] + COMP_EPS);
+      dT += gyb * k.dt;
+      dW += gyb * k.dw;
+      dR += gyb * k.dr;
     }
     // reverse scan lambda[n] = a[n] + alpha lambda[n+1]
     float lb = 0.f;
 #pragma unroll
     for (int i = SPT - 1; i >= 0; --i) lb = a[i] + alpha * lb;
-    __syncthreads();  // sh reuse
+    __syncthreads();   // sh reuse
     float rtotal;
-    float rexcl = block_affine_scan<true>(lb, la * SPT, sh, &rtotal);
-    if (threadIdx.x < 32) {
-      float lin = 0.f;
-      if (chunk == n_chunks - 1) {
-        if (threadIdx.x == 0) publish(c, item0 + it, 2, rtotal);
-      } else {
-        if (threadIdx.x == 0) publish(c, item0 + it, 1, rtotal);
-        lin = look_back_warp(c, item0 + it - 1, item0 + it - (n_chunks - 1 - chunk), la * CH);
-        if (threadIdx.x == 0) publish(c, item0 + it, 2, expf(la * CH) * lin + rtotal);
-      }
-      if (threadIdx.x == 0) s_lin = lin;
+    const float rexcl = block_affine_scan<true>(lb, la * SPT, sh, &rtotal);
+    if constexpr (!APPLY) {
+      if (threadIdx.x == 0) c.comp_agg[w.z] = rtotal;
+      __syncthreads();   // sh is reused by the next item
+      continue;
     }
     glast[threadIdx.x] = g[SPT - 1];
     __syncthreads();
-    // state entering this thread from the right: within-chunk part + the chunk carry
-    const float lin_t = rexcl + expf(la * float(SPT * (255 - threadIdx.x))) * s_lin;
+    // state entering this thread from the right: within-chunk part + the chunk's state
+    const float lin_t = rexcl + expf(la * float(SPT * (255 - threadIdx.x))) * c.comp_agg[w.z];
     float lam[SPT];
     {
       float s = lin_t;
@@ -572,10 +553,7 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_bwd(DevCtx c, i
     block_sum<4>(acc, red);
     if (threadIdx.x == 0) c.partial[w.w] = make_float4(acc[0], acc[1], acc[2], acc[3]);
     __syncthreads();
-    it = next;
-    slot ^= 1;
   }
-  cp_async_wait_all();
 }
 
 __global__ void k_comp_finalize(DevCtx c, int node_begin, int node_end) {
@@ -591,48 +569,43 @@ __global__ void k_comp_finalize(DevCtx c, int node_begin, int node_end) {
   d[0] = s.x; d[1] = s.y; d[2] = s.z; d[3] = s.w;
 }
 
-// what: 0 forward, 1 backward (items), 2 finalize (node range); mode: MODE_COMP, MODE_GATE
-// (the noisegate curve of Eq. 13) or MODE_SC (the sidechain compressor)
+// what: 0 forward (items [a, a + b), nodes [n0, n1)), 1 backward (the same), 2 finalize
+// (nodes [n0, n1)); mode: MODE_COMP, MODE_GATE (the noisegate curve of Eq. 13) or MODE_SC
+// (the sidechain compressor).  Returns the number of kernels launched.
 template <int SPT, int MODE>
-static void comp_launch(int what, const DevCtx& c, int a, int b, int ticket, cudaStream_t s) {
-  constexpr int bwd_smem = 4 * 256 * SPT * sizeof(float);
-  static bool init = false;
-  if (!init) {
-    cudaFuncSetAttribute(k_comp_bwd<SPT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem);
-    init = true;
+static int comp_launch(int what, const DevCtx& c, int a, int b, int n0, int n1, cudaStream_t s) {
+  constexpr int CH = 256 * SPT;
+  const int scan_grid = ((n1 - n0) * 32 + 255) / 256;
+  if (what == 0) {
+    k_comp_agg<SPT, MODE><<<grid_size(b, 8), 256, 0, s>>>(c, a, b);
+    k_comp_scan<false><<<scan_grid, 256, 0, s>>>(c, n0, n1, CH, c.comp_agg, c.comp_carry);
+    k_comp_apply<SPT, MODE><<<grid_size(b, 8), 256, 0, s>>>(c, a, b);
+  } else {
+    k_comp_back<SPT, MODE, false><<<grid_size(b, 4), 256, 0, s>>>(c, a, b);
+    k_comp_scan<true><<<scan_grid, 256, 0, s>>>(c, n0, n1, CH, c.comp_agg, c.comp_agg);
+    k_comp_back<SPT, MODE, true><<<grid_size(b, 4), 256, 0, s>>>(c, a, b);
   }
-  if (what < 0) return;  // attributes only (before a stream capture)
-  const int g = grid_size(b, what == 0 ? 8 : 3);
-  if (what == 0) k_comp_fwd<SPT, MODE><<<g, 256, 0, s>>>(c, a, b, ticket);
-  else k_comp_bwd<SPT, MODE><<<g, 256, bwd_smem, s>>>(c, a, b, ticket);
+  return 3;
 }
 
 template <int SPT>
-static void comp_mode(int what, const DevCtx& c, int a, int b, int ticket, int mode, cudaStream_t s) {
-  if (mode == MODE_GATE) comp_launch<SPT, MODE_GATE>(what, c, a, b, ticket, s);
-  else if (mode == MODE_SC) comp_launch<SPT, MODE_SC>(what, c, a, b, ticket, s);
-  else comp_launch<SPT, MODE_COMP>(what, c, a, b, ticket, s);
+static int comp_mode(int what, const DevCtx& c, int a, int b, int n0, int n1, int mode, cudaStream_t s) {
+  if (mode == MODE_GATE) return comp_launch<SPT, MODE_GATE>(what, c, a, b, n0, n1, s);
+  if (mode == MODE_SC) return comp_launch<SPT, MODE_SC>(what, c, a, b, n0, n1, s);
+  return comp_launch<SPT, MODE_COMP>(what, c, a, b, n0, n1, s);
 }
 
-int launch_comp(int what, const DevCtx& c, int a, int b, int ticket, int mode, cudaStream_t s) {
-  if (what < 0) {  // kernel attributes of every variant
-    for (int m : {MODE_COMP, MODE_GATE, MODE_SC}) {
-      comp_mode<4>(-1, c, 0, 0, 0, m, s);
-      comp_mode<8>(-1, c, 0, 0, 0, m, s);
-      comp_mode<16>(-1, c, 0, 0, 0, m, s);
-    }
-    return 0;
-  }
+int launch_comp(int what, const DevCtx& c, int a, int b, int n0, int n1, int mode, cudaStream_t s) {
+  if (what < 0) return 0;   // no kernel attributes to set (static shared memory only)
   if (what == 2) {
-    if (b <= a) return 0;
-    k_comp_finalize<<<(b - a + 127) / 128, 128, 0, s>>>(c, a, b);
+    if (n1 <= n0) return 0;
+    k_comp_finalize<<<(n1 - n0 + 127) / 128, 128, 0, s>>>(c, n0, n1);
     return 1;
   }
   if (b <= 0) return 0;
-  if (c.comp_chunk == 1024) comp_mode<4>(what, c, a, b, ticket, mode, s);
-  else if (c.comp_chunk == 4096) comp_mode<16>(what, c, a, b, ticket, mode, s);
-  else comp_mode<8>(what, c, a, b, ticket, mode, s);
-  return 1;
+  if (c.comp_chunk == 1024) return comp_mode<4>(what, c, a, b, n0, n1, mode, s);
+  if (c.comp_chunk == 4096) return comp_mode<16>(what, c, a, b, n0, n1, mode, s);
+  return comp_mode<8>(what, c, a, b, n0, n1, mode, s);
 }
 
 // ---------------------------------------------------------------------------

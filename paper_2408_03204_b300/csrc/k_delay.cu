@@ -226,19 +226,23 @@ __global__ void __launch_bounds__(DL_M / 16, 2) k_delay_spec(DevCtx c, int item0
       for (int k = threadIdx.x; k < DL_M; k += blockDim.x) out[k] = make_float2(0.f, 0.f);
       continue;   // uniform over the CTA
     }
-    const int e0 = adj ? c.tcsr_ptr[v] : c.csr_ptr[v];
-    const int e1 = adj ? c.tcsr_ptr[v + 1] : c.csr_ptr[v + 1];
     __syncthreads();
-    for (int i = threadIdx.x; i < DL_M; i += blockDim.x) {
+    // quads of 4 samples (start and count are multiples of 4, so a quad lies wholly
+    // before the signal or starts inside it), all of a thread's loads issued together
+    constexpr int Q = DL_M / (4 * (DL_M / 16));
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int i = 4 * (threadIdx.x + q * (DL_M / 16));
       const int t = start + i;
-      float l = 0.f, r = 0.f;
-      if (i < count && t >= 0 && t < nd.len)
-        for (int e = e0; e < e1; ++e) {
-          const float* row = adj ? out_adj_row(c, e) : in_row(c, e);
-          l += row[t];
-          r += row[nd.pitch + t];
-        }
-      buf[fft::pad(i)] = make_float2(l, r);
+      float4 l = f4zero(), r = f4zero();
+      if (i < count && t >= 0 && t < nd.len) {
+        l = adj ? gather_out_adj(c, v, 0, t, nd.len, nd.pitch) : gather_in(c, v, 0, t, nd.len, nd.pitch);
+        r = adj ? gather_out_adj(c, v, 1, t, nd.len, nd.pitch) : gather_in(c, v, 1, t, nd.len, nd.pitch);
+      }
+      buf[fft::pad(i)] = make_float2(l.x, r.x);
+      buf[fft::pad(i + 1)] = make_float2(l.y, r.y);
+      buf[fft::pad(i + 2)] = make_float2(l.z, r.z);
+      buf[fft::pad(i + 3)] = make_float2(l.w, r.w);
     }
     __syncthreads();
     fft::forward<DL_M>(buf, c.ptw, threadIdx.x, true);
@@ -262,6 +266,7 @@ __global__ void __launch_bounds__(DL_CHUNK * DL_PMAX) k_delay_acc(DevCtx c, int 
     float2* X = sm;                         // [nw][DL_CHUNK][2 ch]
     float2* Y = sm + size_t(nw) * DL_CHUNK * 2;
     __syncthreads();
+#pragma unroll 4
     for (int i = threadIdx.x; i < (nw + nb) * DL_CHUNK; i += blockDim.x) {
       const int s = i / DL_CHUNK, kk = i % DL_CHUNK, k = k0 + kk, km = (DL_M - k) & (DL_M - 1);
       const float2* spec = c.dl_spec + size_t(e.x + s) * DL_M;
@@ -276,6 +281,7 @@ __global__ void __launch_bounds__(DL_CHUNK * DL_PMAX) k_delay_acc(DevCtx c, int 
     __syncthreads();
     const int kk = threadIdx.x % DL_CHUNK, p = threadIdx.x / DL_CHUNK;
     float2 al = make_float2(0.f, 0.f), ar = make_float2(0.f, 0.f);
+#pragma unroll 4
     for (int b = 0; b < nb; ++b) {
       const int ws = b - p + P;               // window index b - p, stored from -P
       const float2 xl = X[(size_t(ws) * DL_CHUNK + kk) * 2], xr = X[(size_t(ws) * DL_CHUNK + kk) * 2 + 1];
