@@ -296,6 +296,58 @@ __device__ __forceinline__ void load_range(const DevCtx& c, int e0, int e1, cons
 // compressor (the compressor's curve; envelope from input 1, gain on input 0).
 constexpr int MODE_COMP = 0, MODE_GATE = 1, MODE_SC = 2;
 
+// Prefetch: this thread's SPT samples of both channels of `row` from t into its own
+// slots dst[ch * 256 * SPT + threadIdx.x * SPT ...] (zeros past the node's length).
+// Every thread reads back only its own slots, so one buffer serves consecutive chunks.
+template <int SPT>
+__device__ __forceinline__ void prefetch_rows(float* dst, const float* row, const NodeDev& nd, int t) {
+  constexpr int CH = 256 * SPT;
+#pragma unroll
+  for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+    for (int q = 0; q < SPT / 4; ++q) {
+      const int tq = t + 4 * q;
+      const bool in = tq < nd.len;
+      cp_async16(dst + ch * CH + threadIdx.x * SPT + 4 * q, in ? row + ch * nd.pitch + tq : row, in ? 16 : 0);
+    }
+}
+
+template <int SPT>
+__device__ __forceinline__ void read_rows(const float* src, const NodeDev& nd, int t, float* l, float* r) {
+  constexpr int CH = 256 * SPT;
+#pragma unroll
+  for (int q = 0; q < SPT / 4; ++q) {
+    float4 a = *reinterpret_cast<const float4*>(src + threadIdx.x * SPT + 4 * q);
+    float4 b = *reinterpret_cast<const float4*>(src + CH + threadIdx.x * SPT + 4 * q);
+    a = mask4(a, t + 4 * q, nd.len);
+    b = mask4(b, t + 4 * q, nd.len);
+    l[4 * q] = a.x, l[4 * q + 1] = a.y, l[4 * q + 2] = a.z, l[4 * q + 3] = a.w;
+    r[4 * q] = b.x, r[4 * q + 1] = b.y, r[4 * q + 2] = b.z, r[4 * q + 3] = b.w;
+  }
+}
+
+// Start the copies of item `it`'s single-row inputs (u, and with ADJ also ybar) into buf.
+template <int SPT, bool ADJ>
+__device__ __forceinline__ void prefetch_item(const DevCtx& c, int item, float* buf) {
+  constexpr int CH = 256 * SPT;
+  const int4_ w = c.items[item];
+  const NodeDev nd = c.nodes[w.x];
+  const int t = w.y * CH + threadIdx.x * SPT;
+  if (const float* row = single_row(c, w.x, false)) prefetch_rows<SPT>(buf, row, nd, t);
+  if (ADJ)
+    if (const float* row = single_row(c, w.x, true)) prefetch_rows<SPT>(buf + 2 * CH, row, nd, t);
+  cp_async_commit();
+}
+
+// This thread's u (and ybar) of the current chunk: from the prefetch buffer when the
+// node has a single row feeding it, else gathered.
+template <int SPT>
+__device__ __forceinline__ void fetch_rows(const DevCtx& c, int v, const NodeDev& nd, int t, const float* buf,
+                                           float* l, float* r, bool adj) {
+  if (single_row(c, v, adj)) read_rows<SPT>(buf, nd, t, l, r);
+  else load_chunk<SPT>(c, v, nd, t, l, r, adj);
+}
+
 template <int SPT>
 __device__ __forceinline__ void store_chunk(float* row, const NodeDev& nd, int t, const float* yl, const float* yr) {
 #pragma unroll
@@ -346,15 +398,28 @@ __device__ __forceinline__ void env_input(const DevCtx& c, int v, const NodeDev&
 template <int SPT, int MODE>
 __global__ void __launch_bounds__(256, SPT >= 16 ? 3 : 4) k_comp_agg(DevCtx c, int item0, int n_items) {
   constexpr int CH = 256 * SPT;
+  extern __shared__ __align__(16) float buf[];   // 2 CH floats: the next chunk's u (prefetched)
   __shared__ float sh[32];
+  if (MODE != MODE_SC && blockIdx.x < n_items) prefetch_item<SPT, false>(c, item0 + blockIdx.x, buf);
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
     const int v = w.x;
     const NodeDev nd = c.nodes[v];
     const float alpha = c.params[nd.prow * 4];
     const float la = logf(alpha);
+    const int t = w.y * CH + threadIdx.x * SPT;
     float x[SPT];
-    env_input<SPT, MODE>(c, v, nd, w.y * CH + threadIdx.x * SPT, x);
+    cp_async_wait_all();
+    if constexpr (MODE == MODE_SC) {
+      env_input<SPT, MODE>(c, v, nd, t, x);
+    } else {
+      float l[SPT], r[SPT];
+      fetch_rows<SPT>(c, v, nd, t, buf, l, r, false);
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) { const float m = l[i] + r[i]; x[i] = m * m; }
+      // every thread has read its own slots: start the next chunk's copies into them
+      if (it + int(gridDim.x) < n_items) prefetch_item<SPT, false>(c, item0 + it + gridDim.x, buf);
+    }
     float b = 0.f;
 #pragma unroll
     for (int i = 0; i < SPT; ++i) b = alpha * b + (1.f - alpha) * x[i];
@@ -363,6 +428,7 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 3 : 4) k_comp_agg(DevCtx c, i
     if (threadIdx.x == 0) c.comp_agg[w.z] = total;
     __syncthreads();   // sh is reused by the next item
   }
+  cp_async_wait_all();
 }
 
 // Pass 2: per node (one warp), the state entering every chunk from its chunks' aggregates
@@ -403,7 +469,9 @@ template <int SPT, int MODE>
 __global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_apply(DevCtx c, int item0, int n_items) {
   constexpr int CH = 256 * SPT;
   constexpr bool GATE = MODE == MODE_GATE, SC = MODE == MODE_SC;
+  extern __shared__ __align__(16) float buf[];   // 2 CH floats: the next chunk's u (prefetched)
   __shared__ float sh[32];
+  if (!SC && blockIdx.x < n_items) prefetch_item<SPT, false>(c, item0 + blockIdx.x, buf);
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
     const int v = w.x;
@@ -414,13 +482,15 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_apply(DevCtx c,
     const float la = logf(alpha);
     const int t = w.y * CH + threadIdx.x * SPT;
     float ul[SPT], ur[SPT], x[SPT], g[SPT];
+    cp_async_wait_all();
     if constexpr (SC) {
       load_range<SPT>(c, c.csr_ptr[v], c.in1_begin[v], nd, t, ul, ur);   // main (input 0)
       env_input<SPT, MODE>(c, v, nd, t, x);                               // key (input 1)
     } else {
-      load_chunk<SPT>(c, v, nd, t, ul, ur, false);
+      fetch_rows<SPT>(c, v, nd, t, buf, ul, ur, false);
 #pragma unroll
       for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
+      if (it + int(gridDim.x) < n_items) prefetch_item<SPT, false>(c, item0 + it + gridDim.x, buf);
     }
     float b = 0.f;
 #pragma unroll
@@ -441,6 +511,7 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_apply(DevCtx c,
     store_chunk<SPT>(yrow_w(c, nd), nd, t, ul, ur);
     __syncthreads();   // sh is reused by the next item
   }
+  cp_async_wait_all();
 }
 
 // Backward of one chunk.  APPLY = false (pass 1): the chunk's reverse state at its start
@@ -451,9 +522,11 @@ template <int SPT, int MODE, bool APPLY>
 __global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_back(DevCtx c, int item0, int n_items) {
   constexpr int CH = 256 * SPT;
   constexpr bool GATE = MODE == MODE_GATE, SC = MODE == MODE_SC;
+  extern __shared__ __align__(16) float buf[];   // 4 CH floats: the next chunk's u and ybar
   __shared__ float sh[32];
   __shared__ float glast[256];
   __shared__ float red[4 * 32];
+  if (!SC && blockIdx.x < n_items) prefetch_item<SPT, true>(c, item0 + blockIdx.x, buf);
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
     const int v = w.x;
@@ -465,18 +538,21 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_back(DevCtx c, 
     const int t = w.y * CH + threadIdx.x * SPT;
     float ul[SPT], ur[SPT], bl[SPT], br[SPT], x[SPT], g[SPT], a[SPT];
     float km[SC ? SPT : 1];   // sidechain: the key's mid l + r
+    cp_async_wait_all();
     if constexpr (SC) {
       float kr[SPT];
       load_range<SPT>(c, c.csr_ptr[v], c.in1_begin[v], nd, t, ul, ur);      // main (input 0)
       load_range<SPT>(c, c.in1_begin[v], c.csr_ptr[v + 1], nd, t, km, kr);  // key (input 1)
 #pragma unroll
       for (int i = 0; i < SPT; ++i) { km[i] += kr[i]; x[i] = km[i] * km[i]; }
+      load_chunk<SPT>(c, v, nd, t, bl, br, true);
     } else {
-      load_chunk<SPT>(c, v, nd, t, ul, ur, false);
+      fetch_rows<SPT>(c, v, nd, t, buf, ul, ur, false);
+      fetch_rows<SPT>(c, v, nd, t, buf + 2 * CH, bl, br, true);
 #pragma unroll
       for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
+      if (it + int(gridDim.x) < n_items) prefetch_item<SPT, true>(c, item0 + it + gridDim.x, buf);
     }
-    load_chunk<SPT>(c, v, nd, t, bl, br, true);
     // the envelope from the forward's stored chunk state (same arithmetic as the forward)
     const float carry_g = c.comp_carry[w.z];
     float b = 0.f;
@@ -554,6 +630,7 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_back(DevCtx c, 
     if (threadIdx.x == 0) c.partial[w.w] = make_float4(acc[0], acc[1], acc[2], acc[3]);
     __syncthreads();
   }
+  cp_async_wait_all();
 }
 
 __global__ void k_comp_finalize(DevCtx c, int node_begin, int node_end) {
@@ -575,15 +652,23 @@ __global__ void k_comp_finalize(DevCtx c, int node_begin, int node_end) {
 template <int SPT, int MODE>
 static int comp_launch(int what, const DevCtx& c, int a, int b, int n0, int n1, cudaStream_t s) {
   constexpr int CH = 256 * SPT;
+  constexpr int fwd_smem = 2 * CH * sizeof(float), bwd_smem = 4 * CH * sizeof(float);
+  static bool init = false;
+  if (!init) {   // first call (also the attributes-only call made before a stream capture)
+    cudaFuncSetAttribute(k_comp_back<SPT, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem);
+    cudaFuncSetAttribute(k_comp_back<SPT, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem);
+    init = true;
+  }
+  if (what < 0) return 0;
   const int scan_grid = ((n1 - n0) * 32 + 255) / 256;
   if (what == 0) {
-    k_comp_agg<SPT, MODE><<<grid_size(b, 8), 256, 0, s>>>(c, a, b);
+    k_comp_agg<SPT, MODE><<<grid_size(b, 8), 256, fwd_smem, s>>>(c, a, b);
     k_comp_scan<false><<<scan_grid, 256, 0, s>>>(c, n0, n1, CH, c.comp_agg, c.comp_carry);
-    k_comp_apply<SPT, MODE><<<grid_size(b, 8), 256, 0, s>>>(c, a, b);
+    k_comp_apply<SPT, MODE><<<grid_size(b, 8), 256, fwd_smem, s>>>(c, a, b);
   } else {
-    k_comp_back<SPT, MODE, false><<<grid_size(b, 4), 256, 0, s>>>(c, a, b);
+    k_comp_back<SPT, MODE, false><<<grid_size(b, 4), 256, bwd_smem, s>>>(c, a, b);
     k_comp_scan<true><<<scan_grid, 256, 0, s>>>(c, n0, n1, CH, c.comp_agg, c.comp_agg);
-    k_comp_back<SPT, MODE, true><<<grid_size(b, 4), 256, 0, s>>>(c, a, b);
+    k_comp_back<SPT, MODE, true><<<grid_size(b, 4), 256, bwd_smem, s>>>(c, a, b);
   }
   return 3;
 }
@@ -596,7 +681,14 @@ static int comp_mode(int what, const DevCtx& c, int a, int b, int n0, int n1, in
 }
 
 int launch_comp(int what, const DevCtx& c, int a, int b, int n0, int n1, int mode, cudaStream_t s) {
-  if (what < 0) return 0;   // no kernel attributes to set (static shared memory only)
+  if (what < 0) {   // kernel attributes of every variant
+    for (int m : {MODE_COMP, MODE_GATE, MODE_SC}) {
+      comp_mode<4>(-1, c, 0, 0, 0, 0, m, s);
+      comp_mode<8>(-1, c, 0, 0, 0, 0, m, s);
+      comp_mode<16>(-1, c, 0, 0, 0, 0, m, s);
+    }
+    return 0;
+  }
   if (what == 2) {
     if (n1 <= n0) return 0;
     k_comp_finalize<<<(n1 - n0 + 127) / 128, 128, 0, s>>>(c, n0, n1);

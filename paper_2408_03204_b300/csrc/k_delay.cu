@@ -63,28 +63,28 @@ __device__ __forceinline__ void dl_window_sum(const DevCtx& c, int v, const Node
 constexpr int DL_GROUP = 4;                  // taps whose windows are staged together
 constexpr int DL_OPT = 8;                    // consecutive outputs per thread
 constexpr int DL_FT = DL_TILE / DL_OPT;      // threads of the FIR kernels
-constexpr int DL_WL = (DL_TILE + DL_FIR - 1 + 3) & ~3;   // window elements read (16-byte groups)
-constexpr int DL_WP = DL_WL + ((DL_WL + 31) / 32) * 4;   // padded window floats
-
-// cp.async of 4 bytes into shared memory; nothing is read (zero written) when !in.
-__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool in) {
-  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(in ? 4 : 0) : "memory");
-}
+constexpr int DL_SH = DL_FIR + 3;            // taps of the shifted filters (alignment shift 0..3)
+constexpr int DL_XL = (DL_OPT + DL_SH - 1 + 3) & ~3;   // window floats a thread reads (13 float4)
+constexpr int DL_WL = DL_OPT * (DL_FT - 1) + DL_XL;     // window floats staged (16-byte groups)
+constexpr int DL_WP = DL_WL + ((DL_WL + 31) / 32) * 4;  // padded window floats
+static_assert(DL_WL % 4 == 0 && DL_WL >= DL_TILE + DL_SH - 1, "window covers the tile");
 
 // Forward (ADJ = false) or input adjoint (ADJ = true) of the sparse FIR for one
-// (node, tile, channel) item; DL_FT threads x DL_OPT consecutive outputs.  The windows of
-// a group of DL_GROUP taps are staged in shared memory while the previous group is
-// computed (cp.async from a single source row; a sum over several rows is staged
-// synchronously), double-buffered, with 4 floats of padding after every 32 so that the
-// threads' float4 reads (8 floats apart) fall in distinct banks.  (Staging 16-byte
-// chunks from an aligned start with four unrolled variants for the misalignment was
-// measured slower: 0.84 -> 1.00 ms for the adjoint at 20 taps.)
+// (node, tile, channel) item; DL_FT threads x DL_OPT consecutive outputs.  A tap's window
+// starts at s = t0 -+ d - H, which has any alignment; it is staged from s0 = s rounded down
+// to a multiple of 4 with 16-byte copies (zero-filled outside the signal), and the
+// misalignment o = s - s0 moves into the filter instead: the tap's 39 coefficients are
+// placed in a 42-tap filter at offset 3 - o (forward) or o (adjoint), so every thread runs
+// the same unrolled loop over aligned float4 reads.  The windows of a group of DL_GROUP
+// taps are staged while the previous group is computed (cp.async from a single source
+// row; a sum over several rows is staged synchronously), double-buffered, with 4 floats of
+// padding after every 32 so that the threads' float4 reads (8 floats apart) fall in
+// distinct banks.
 template <bool ADJ>
 __global__ void __launch_bounds__(DL_FT) k_delay_fir(DevCtx c, int item0, int n_items) {
   __shared__ __align__(16) float win[2][DL_GROUP][DL_WP];
-  __shared__ __align__(16) float taps[DL_SLOT_TAPS][DL_FIR + 1];   // rows of 40: float4 reads
-  __shared__ int dly[DL_SLOT_TAPS];
+  __shared__ __align__(16) float taps[DL_SLOT_TAPS][DL_SH + 2];   // rows of 44: float4 reads
+  __shared__ int wst[DL_SLOT_TAPS];                                // aligned window starts
   constexpr int H = (DL_FIR - 1) / 2;
   const int ntap = c.dl_taps;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -94,24 +94,34 @@ __global__ void __launch_bounds__(DL_FT) k_delay_fir(DevCtx c, int item0, int n_
     const float* aux = c.dl_aux + size_t(c.ext[v].z) * 2 * ntap * (DL_FIR + 1) + size_t(ch) * ntap * (DL_FIR + 1);
     const float* single = dl_single_row<ADJ>(c, v);
     __syncthreads();   // readers of the previous item's taps and windows are done
-    for (int i = threadIdx.x; i < ntap; i += blockDim.x) dly[i] = int(aux[i * (DL_FIR + 1) + DL_FIR]);
-    for (int i = threadIdx.x; i < ntap * (DL_FIR + 1); i += blockDim.x)
-      taps[i / (DL_FIR + 1)][i % (DL_FIR + 1)] = i % (DL_FIR + 1) < DL_FIR ? aux[i] : 0.f;
+    for (int m = threadIdx.x; m < ntap; m += blockDim.x) {
+      const int d = int(aux[m * (DL_FIR + 1) + DL_FIR]);
+      const int st = ADJ ? t0 + d - H : t0 - d - H;     // window start (forward: u[t0 - d - H + k])
+      wst[m] = st - (((st % 4) + 4) % 4);
+    }
     __syncthreads();
-    // forward: win[k] = u[t0 - d - H + k]; adjoint: win[k] = ybar[t0 + d - H + k]
+    for (int i = threadIdx.x; i < ntap * (DL_SH + 2); i += blockDim.x) {
+      const int m = i / (DL_SH + 2), jp = i % (DL_SH + 2);
+      const int d = int(aux[m * (DL_FIR + 1) + DL_FIR]);
+      const int o = (ADJ ? t0 + d - H : t0 - d - H) - wst[m];
+      const int j = ADJ ? jp - o : jp - (3 - o);       // the original tap index at shifted position jp
+      taps[m][jp] = (jp < DL_SH && j >= 0 && j < DL_FIR) ? aux[m * (DL_FIR + 1) + j] : 0.f;
+    }
+    __syncthreads();
+    // window k of tap m: u[s0 + k] (forward) or ybar[s0 + k] (adjoint), s0 = wst[m]
     auto stage = [&](int g0, int buf) {
       const int ng = min(DL_GROUP, ntap - g0);
       for (int m = 0; m < ng; ++m) {
-        const int start = ADJ ? t0 + dly[g0 + m] - H : t0 - dly[g0 + m] - H;
+        const int s0 = wst[g0 + m];
         if (single) {
           const float* row = single + size_t(ch) * nd.pitch;
-          for (int i = threadIdx.x; i < DL_TILE + DL_FIR - 1; i += blockDim.x) {
-            const int t = start + i;
-            const bool in = t >= 0 && t < nd.len;
-            cp_async4(&win[buf][m][dl_pidx(i)], in ? row + t : row, in);
+          for (int q = threadIdx.x; q < DL_WL / 4; q += blockDim.x) {
+            const int t = s0 + 4 * q;   // a multiple of 4: the quad lies wholly before 0 or starts inside
+            const int nbytes = (t < 0 || t >= nd.len) ? 0 : 4 * min(4, nd.len - t);
+            cp_async16(&win[buf][m][dl_pidx(4 * q)], nbytes ? row + t : row, nbytes);
           }
         } else {
-          dl_window_sum<ADJ>(c, v, nd, ch, start, win[buf][m], DL_TILE + DL_FIR - 1);
+          dl_window_sum<ADJ>(c, v, nd, ch, s0, win[buf][m], DL_WL);
         }
       }
       cp_async_commit();
@@ -128,26 +138,24 @@ __global__ void __launch_bounds__(DL_FT) k_delay_fir(DevCtx c, int item0, int n_
       __syncthreads();
       const int ng = min(DL_GROUP, ntap - g0);
       for (int m = 0; m < ng; ++m) {
-        constexpr int XL = (DL_OPT + DL_FIR - 1 + 3) & ~3;   // 46 used, read as 12 float4
-        static_assert(XL >= DL_OPT + DL_FIR - 1 && DL_OPT * (DL_FT - 1) + XL <= DL_WL, "window reads in bounds");
-        float x[XL];
+        float x[DL_XL];
         const float* wb = win[buf][m];
 #pragma unroll
-        for (int k = 0; k < XL / 4; ++k) {   // a float4 never crosses a padding point
+        for (int k = 0; k < DL_XL / 4; ++k) {   // a float4 never crosses a padding point
           const float4 q4 = *reinterpret_cast<const float4*>(wb + dl_pidx(i0 + 4 * k));
           x[4 * k] = q4.x, x[4 * k + 1] = q4.y, x[4 * k + 2] = q4.z, x[4 * k + 3] = q4.w;
         }
         const float4* t4 = reinterpret_cast<const float4*>(taps[g0 + m]);
 #pragma unroll
-        for (int j4 = 0; j4 < (DL_FIR + 1) / 4; ++j4) {
+        for (int j4 = 0; j4 < (DL_SH + 2) / 4; ++j4) {
           const float4 c4 = t4[j4];   // the same address in every lane: one broadcast
           const float cs[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
             const int jj = 4 * j4 + r;
-            if (jj < DL_FIR)
+            if (jj < DL_SH)
 #pragma unroll
-              for (int q = 0; q < DL_OPT; ++q) acc[q] += cs[r] * x[q + (ADJ ? jj : DL_FIR - 1 - jj)];
+              for (int q = 0; q < DL_OPT; ++q) acc[q] += cs[r] * x[q + (ADJ ? jj : DL_SH - 1 - jj)];
           }
         }
       }
@@ -270,7 +278,9 @@ __global__ void __launch_bounds__(DL_CHUNK * DL_PMAX) k_delay_acc(DevCtx c, int 
     for (int i = threadIdx.x; i < (nw + nb) * DL_CHUNK; i += blockDim.x) {
       const int s = i / DL_CHUNK, kk = i % DL_CHUNK, k = k0 + kk, km = (DL_M - k) & (DL_M - 1);
       const float2* spec = c.dl_spec + size_t(e.x + s) * DL_M;
-      const float2 z = spec[k], zm = spec[km];
+      // u windows w = s - P < -1 hold no sample of the signal: zero spectra, never written
+      const bool none = s < P - 1;
+      const float2 z = none ? make_float2(0.f, 0.f) : spec[k], zm = none ? make_float2(0.f, 0.f) : spec[km];
       // l = (Z[k] + conj(Z[-k]))/2 ; r = (Z[k] - conj(Z[-k]))/(2i)
       const float2 l = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
       const float2 r = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));

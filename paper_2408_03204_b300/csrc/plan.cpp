@@ -531,7 +531,12 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
           for (int32_t t0 = 0; t0 < L; t0 += DL_TILE) sub[0].push_back({v, t0, ch, 0});
         p->node_ext[v].x = p->n_dl_slots;
         p->node_ext[v].y = p->node_ext[v].z * p->dl_P;
-        for (int32_t w = -p->dl_P; w < nb; ++w) sub[1].push_back({v, w, 0, p->n_dl_slots++});
+        // u windows from -P; those before -1 hold no sample (zero spectra, which the lag
+        // accumulation takes as such): their slots are kept but not computed
+        for (int32_t w = -p->dl_P; w < nb; ++w) {
+          if (w >= -1) sub[1].push_back({v, w, 0, p->n_dl_slots});
+          ++p->n_dl_slots;
+        }
         for (int32_t b = 0; b < nb; ++b) sub[1].push_back({v, b, 1, p->n_dl_slots++});
         // bins 0..M/2 (the lag spectra are conjugate-symmetric per channel)
         for (int32_t ck = 0; ck <= DL_M / 2 / DL_CHUNK; ++ck) sub[2].push_back({v, ck, 0, 0});
