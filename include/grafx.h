@@ -421,6 +421,20 @@ int grafx_ws_bind(grafx_wsnet* n, void* ws, size_t bytes, void* stream);
  * coff is 0 (node input) or 128 (target mix).  Asynchronous on `stream`. */
 int grafx_ws_logmel(grafx_wsnet* n, const float* rows, int32_t n_rows, int64_t row_stride, int64_t pitch, int64_t len,
                     const int32_t* row_of_sample, int32_t n_samples, int32_t coff, float* feats, void* stream);
+/* Cross-spectral band gain of n_samples node inputs against target mixes (a reading:
+ * the paper motivates a trained estimator, Sec. 1, without fixing its inputs).  Sample i
+ * takes the node input u_rows + i*u_stride and the target row
+ * t_rows + row_of_sample[i]*t_stride (device int32 array; an index outside [0, n_trows)
+ * gives a zero target); both stereo, channel stride pitch, len >= 2048.  For the mid
+ * (l + r)/2 and the side (l - r)/2 of both, per log-mel frame and pair of mel triangles
+ * (64 bands), C = sum w Re(T conj(U)) and P = sum w |U|^2; per pooling slot the sums over
+ * its frames give feats[i][coff + h*64 + b][t] = ln(max(C / P, 0) + 0.01) (h = 0 mid,
+ * 1 side).  The sources of a mix are independent, so C / P estimates the gain of the
+ * node's own path to the output in that band.  The workspace must hold
+ * n_samples * 2 log-mel rows (grafx_ws_workspace_bytes).  Asynchronous on `stream`. */
+int grafx_ws_xgain(grafx_wsnet* n, const float* u_rows, int32_t n_samples, int64_t u_stride, const float* t_rows,
+                   int32_t n_trows, int64_t t_stride, const int32_t* row_of_sample, int64_t pitch, int64_t len,
+                   int32_t coff, float* feats, void* stream);
 /* Forward of a batch of B <= max_batch samples sorted by head: head_count (host
  * int32[6]) gives how many consecutive samples use each head, in the type order above
  * (their sum must be B: GRAFX_ESHAPE otherwise).  out: device [B][176]; row i holds the

@@ -10,7 +10,8 @@ parameters):
             1e-5); frames average-pooled to T = 32 (frame i of the pool averages
             frames [floor(i F/T), floor((i+1) F/T)) of F).  A node's input is the
             concatenation of the log-mel of its input signal (rendered with neutral
-            parameters) and of the target mix: 256 x T.
+            parameters) and of the cross-spectral band gain ``xgain`` of that input
+            against the target mix: 256 x T.
   encoder   4 conv1d layers, kernel 5, zero padding 2 ('same'), 256->128->128->128->128,
             bias, exact GELU 0.5 x (1 + erf(x / sqrt 2)); mean over time -> e in R^128.
   heads     one MLP per parameterised type: 128 -> 288 -> 288 -> N_t (GELU, GELU,
@@ -70,6 +71,47 @@ def logmel(x, fs=44100, T=T_POOL):
     for i in range(T):
         a, b = (i * F) // T, ((i + 1) * F) // T
         out[:, i] = mel[a:max(b, a + 1)].mean(axis=0)
+    return out
+
+
+XG_BANDS = 64          # band pairs of the 128 mel triangles
+XG_FLOOR = 1e-2
+
+
+def _frames(m):
+    F = 1 + (m.shape[0] - MEL_NFFT) // MEL_HOP
+    idx = np.arange(F)[:, None] * MEL_HOP + np.arange(MEL_NFFT)[None, :]
+    w = 0.5 - 0.5 * np.cos(2 * np.pi * np.arange(MEL_NFFT) / MEL_NFFT)
+    return np.fft.rfft(m[idx] * w[None, :], axis=-1), F
+
+
+def xgain(u, T, fs=44100, T_slots=T_POOL):
+    """Cross-spectral band gain of a node's path to the output (a reading: the network's
+    second input block, in place of the target mix's log-mel).  u: the node's input
+    [2, L], T: the target mix [2, L].  For the mid (l + r)/2 and the side (l - r)/2 of
+    both, per frame (the log-mel framing) and mel triangle: C = sum_k w Re(T_k conj(U_k))
+    and P = sum_k w |U_k|^2; adjacent triangles summed in pairs (64 bands); per pooling
+    slot (the log-mel's frame ranges) the sums over its frames give the gain C / P, and
+    the feature is ln(max(C / P, 0) + 1e-2).  Because the sources of a mix are independent,
+    the part of the target correlated with the node's input is the node's own path
+    (its processor and everything downstream) applied to it: C / P estimates that path's
+    gain in the band.  Returns [128, T]: 64 mid bands, then 64 side bands."""
+    u = np.asarray(u, np.float64)
+    T = np.asarray(T, np.float64)
+    W = mel_filterbank(fs)
+    out = np.zeros((2 * XG_BANDS, T_slots))
+    for half, sgn in ((0, 1.0), (1, -1.0)):
+        U, F = _frames(0.5 * (u[0] + sgn * u[1]))
+        Y, _ = _frames(0.5 * (T[0] + sgn * T[1]))
+        C = (np.real(Y * np.conj(U)) @ W.T)                       # [F, 128]
+        P = ((np.abs(U) ** 2) @ W.T)
+        C = C[:, 0::2] + C[:, 1::2]                               # [F, 64]
+        P = P[:, 0::2] + P[:, 1::2]
+        for i in range(T_slots):
+            a, b = (i * F) // T_slots, ((i + 1) * F) // T_slots
+            b = max(b, a + 1)
+            g = C[a:b].sum(axis=0) / np.maximum(P[a:b].sum(axis=0), 1e-20)
+            out[half * XG_BANDS:(half + 1) * XG_BANDS, i] = np.log(np.maximum(g, 0.0) + XG_FLOOR)
     return out
 
 

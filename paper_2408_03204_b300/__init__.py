@@ -112,6 +112,7 @@ SIGNATURES = {
     "grafx_ws_workspace_bytes": (ctypes.c_int, [_P, _I32, _I64, ctypes.POINTER(_SZ)]),
     "grafx_ws_bind": (ctypes.c_int, [_P, _P, _SZ, _P]),
     "grafx_ws_logmel": (ctypes.c_int, [_P, _F, _I32, _I64, _I64, _I64, _P, _I32, _I32, _F, _P]),
+    "grafx_ws_xgain": (ctypes.c_int, [_P, _F, _I32, _I64, _F, _I32, _I64, _F, _I64, _I64, _I32, _F, _P]),
     "grafx_ws_forward": (ctypes.c_int, [_P, _F, _F, _I32P, _I32, _F, _P]),
     "grafx_ws_backward": (ctypes.c_int, [_P, _F, _F, _I32P, _I32, _F, _F, _P]),
     "grafx_ws_mse": (ctypes.c_int, [_F, _F, _P, _I32, _F, _F, _P]),
@@ -382,6 +383,12 @@ class WarmStartNet:
     def logmel_raw(self, rows, n_rows, row_stride, pitch, length, row_of_sample, n_samples, coff, feats, stream):
         _check(lib().grafx_ws_logmel(self._h, _ptr(rows), int(n_rows), int(row_stride), int(pitch), int(length),
                                      _ptr(row_of_sample), int(n_samples), int(coff), _ptr(feats), stream))
+
+    def xgain_raw(self, u_rows, n_samples, u_stride, t_rows, n_trows, t_stride, row_of_sample, pitch, length, coff,
+                  feats, stream):
+        _check(lib().grafx_ws_xgain(self._h, _ptr(u_rows), int(n_samples), int(u_stride), _ptr(t_rows), int(n_trows),
+                                    int(t_stride), _ptr(row_of_sample), int(pitch), int(length), int(coff),
+                                    _ptr(feats), stream))
 
     @staticmethod
     def _heads(head_count):

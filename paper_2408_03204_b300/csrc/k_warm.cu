@@ -669,6 +669,76 @@ __global__ void k_logmel_pool(const float* __restrict__ fr, int nframes, int n_r
   *o = s / float(b - a);
 }
 
+// ------------------------------------------------------------------ cross-spectral band gain
+// Frame f of sample i: two groups of 128 threads, group h transforming the mid (h = 0) or
+// the side (h = 1) of the node input u and of the target t packed as w (u_h + i t_h) in one
+// 2048-point FFT; per bin the cross term Re(T conj(U)) and |U|^2; per band pair (mel
+// triangles 2b, 2b + 1) their weighted sums C and P into fr[i][f][h][C 0..63, P 64..127].
+constexpr int XG_BANDS = WS_MEL / 2;
+__global__ void __launch_bounds__(2 * (WS_NFFT / 16)) k_xgain_frames(
+    const float* __restrict__ u, int64_t ustride, const float* __restrict__ trows, int64_t tstride,
+    const int32_t* __restrict__ row_of, int n_trows, int64_t pitch, int nframes, const float* __restrict__ melw,
+    const int2_* __restrict__ mel_rng, const float2_* __restrict__ tw, const float2_* __restrict__ ptw,
+    float* __restrict__ fr) {
+  constexpr int T = WS_NFFT / 16, PS = fft::Padded<WS_NFFT>::size;
+  extern __shared__ float2 xg_smem[];   // [2][PS] transforms, then [2][WS_BINS] cross and power
+  float* cr = reinterpret_cast<float*>(xg_smem + 2 * PS);   // cr[h * WS_BINS + k]
+  float* pu = cr + 2 * WS_BINS;                              // pu[h * WS_BINS + k]
+  const int smp = blockIdx.y, f = blockIdx.x;
+  const int h = threadIdx.x / T, gt = threadIdx.x % T;
+  float2* buf = xg_smem + h * PS;
+  const int r = row_of[smp];
+  const bool has_t = r >= 0 && r < n_trows;
+  const float* x = u + int64_t(smp) * ustride;
+  const float* y = has_t ? trows + int64_t(r) * tstride : nullptr;
+  const float sg = h ? -1.f : 1.f;
+  for (int j = gt; j < WS_NFFT; j += T) {
+    const float w = 0.5f - 0.5f * tw[j * (TWIDDLE_N / WS_NFFT)].x;
+    const int64_t t0 = int64_t(f) * WS_HOP + j;
+    const float a = 0.5f * (x[t0] + sg * x[pitch + t0]);
+    const float b = has_t ? 0.5f * (y[t0] + sg * y[pitch + t0]) : 0.f;
+    buf[fft::pad(j)] = make_float2(w * a, w * b);
+  }
+  __syncthreads();
+  fft::forward<WS_NFFT>(buf, ptw, gt, true);
+  for (int k = gt; k < WS_BINS; k += T) {
+    const float2 z = buf[fft::pad(k)], zm = buf[fft::pad((WS_NFFT - k) & (WS_NFFT - 1))];
+    const float ux = 0.5f * (z.x + zm.x), uy = 0.5f * (z.y - zm.y);   // U = (Z + conj Zm) / 2
+    const float yx = 0.5f * (z.y + zm.y), yy = 0.5f * (zm.x - z.x);   // Y = (Z - conj Zm) / 2i
+    cr[h * WS_BINS + k] = yx * ux + yy * uy;
+    pu[h * WS_BINS + k] = ux * ux + uy * uy;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * 2 * XG_BANDS; i += blockDim.x) {
+    const int hh = i / (2 * XG_BANDS), q = i % (2 * XG_BANDS), b = q % XG_BANDS;
+    const float* src = (q < XG_BANDS ? cr : pu) + hh * WS_BINS;
+    float acc = 0.f;
+    for (int m = 2 * b; m < 2 * b + 2; ++m) {
+      const int2_ rg = mel_rng[m];
+      for (int k = rg.x; k < rg.y; ++k) acc += melw[m * WS_BINS + k] * src[k];
+    }
+    fr[((int64_t(smp) * nframes + f) * 2 + hh) * (2 * XG_BANDS) + q] = acc;
+  }
+}
+
+// Pool slot t of sample i: C and P summed over the slot's frames (the log-mel's ranges),
+// feats[i][coff + h 64 + b][t] = ln(max(C / P, 0) + 1e-2).
+__global__ void k_xgain_pool(const float* __restrict__ fr, int nframes, int n_samples, int coff,
+                             float* __restrict__ feats) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_samples * WS_MEL * WS_T) return;
+  const int t = i % WS_T, c = (i / WS_T) % WS_MEL, smp = i / (WS_T * WS_MEL);
+  const int hh = c / XG_BANDS, b = c % XG_BANDS;
+  const int a = (t * nframes) / WS_T, e = max(((t + 1) * nframes) / WS_T, a + 1);
+  float C = 0.f, P = 0.f;
+  for (int f = a; f < e; ++f) {
+    const float* q = fr + ((int64_t(smp) * nframes + f) * 2 + hh) * (2 * XG_BANDS);
+    C += q[b];
+    P += q[XG_BANDS + b];
+  }
+  feats[(int64_t(smp) * WS_IN + coff + c) * WS_T + t] = logf(fmaxf(C / fmaxf(P, 1e-20f), 0.f) + 1e-2f);
+}
+
 // ------------------------------------------------------------------ node inputs
 // u_v (Eq. 1b, gathered exactly like the step kernels) of the nodes ids.v[0..n) into
 // rows dst[ids.first + i][2][dst_pitch]; samples in [len, dst_pitch) are zero.
@@ -904,6 +974,33 @@ int grafx_ws_logmel(grafx_wsnet* n, const float* rows, int32_t n_rows, int64_t r
       reinterpret_cast<const float2_*>(n->ws + L.ptw), fr);
   k_logmel_pool<<<(n_samples * WS_MEL * WS_T + 255) / 256, 256, 0, s>>>(fr, nframes, n_rows, n_samples,
                                                                           row_of_sample, coff, feats);
+  return cuda_status();
+}
+
+int grafx_ws_xgain(grafx_wsnet* n, const float* u_rows, int32_t n_samples, int64_t u_stride, const float* t_rows,
+                   int32_t n_trows, int64_t t_stride, const int32_t* row_of_sample, int64_t pitch, int64_t len,
+                   int32_t coff, float* feats, void* stream) {
+  if (!n || !u_rows || !t_rows || !row_of_sample || !feats) return fail(GRAFX_EINVAL, "null argument");
+  if (!n->ws) return fail(GRAFX_ESTATE, "workspace not bound (grafx_ws_bind)");
+  if (n_samples < 1 || n_samples > 65535 || n_trows < 1 || len < WS_NFFT || pitch < len || u_stride < 2 * pitch ||
+      t_stride < 2 * pitch || (coff != 0 && coff != WS_MEL) || int64_t(n_samples) * WS_MEL * WS_T > INT32_MAX)
+    return fail(GRAFX_ESHAPE, "bad cross-gain shape");
+  const int nframes = n_frames_of(len);
+  WsNetLayout L = ws_layout(n, int64_t(n_samples) * nframes * 2 * WS_MEL);
+  if (L.total > n->ws_bytes) return fail(GRAFX_ESHAPE, "workspace too small for these cross-gain samples");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float* fr = reinterpret_cast<float*>(n->ws + L.frames);
+  constexpr int smem = int(sizeof(float2)) * 2 * fft::Padded<WS_NFFT>::size + 4 * 4 * WS_BINS;
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(k_xgain_frames, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    init = true;
+  }
+  k_xgain_frames<<<dim3(nframes, n_samples), 2 * (WS_NFFT / 16), smem, s>>>(
+      u_rows, u_stride, t_rows, t_stride, row_of_sample, n_trows, pitch, nframes,
+      reinterpret_cast<const float*>(n->ws + L.melw), reinterpret_cast<const int2_*>(n->ws + L.melrng),
+      reinterpret_cast<const float2_*>(n->ws + L.tw), reinterpret_cast<const float2_*>(n->ws + L.ptw), fr);
+  k_xgain_pool<<<(n_samples * WS_MEL * WS_T + 255) / 256, 256, 0, s>>>(fr, nframes, n_samples, coff, feats);
   return cuda_status();
 }
 

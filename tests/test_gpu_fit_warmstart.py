@@ -64,20 +64,18 @@ def test_fit_from_theta0_maps_parameters(env):
     assert f.current_loss() < 1e-3
 
 
-def test_features_compose_node_inputs_and_mix(env):
+def test_features_compose_node_inputs_and_cross_gain(env):
     gx, torch, gfit, gws = env
+    from oracle import warmstart as ow
     ws = gws.WarmStart(max_batch=512, max_rows=64, max_len=8192)
     batch, src, hidden, target, neutral = _small_batch(gws, ws, seed=3)
     feats = ws.features(batch, src, target, neutral)
     torch.cuda.synchronize()
     n = len(batch.ids)
     assert feats.shape == (n, 256, 32) and torch.isfinite(feats).all()
-    # mix channels: identical for the samples of one graph, different across graphs
     f = feats.cpu().numpy()
-    for i in range(n):
-        j = batch.graph_of.index(batch.graph_of[i])
-        np.testing.assert_array_equal(f[i, 128:], f[j, 128:])
-    # node-input channels: the log-mel of grafx_node_inputs rows, recomputed separately
+    # node-input channels: the log-mel of grafx_node_inputs rows, recomputed separately;
+    # cross-gain channels: the oracle's of those rows against the graph's target row
     P = (8192 + 3) // 4 * 4
     out = torch.empty(batch.plan.info.out_elems, device="cuda")
     st = gx._stream(torch, out.device)
@@ -89,6 +87,11 @@ def test_features_compose_node_inputs_and_mix(env):
     ws.net.logmel_raw(u, 5, 2 * P, P, 8192, None, 5, 0, f2, st)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(f2[:, :128].cpu().numpy(), f[-5:, :128])
+    uh = u.cpu().numpy()
+    th = target.cpu().numpy().reshape(-1, 2, P)
+    for i in range(5):
+        want = ow.xgain(uh[i, :, :8192], th[batch.outrow[n - 5 + i], :, :8192])
+        np.testing.assert_allclose(f[n - 5 + i, 128:], want, rtol=0, atol=1e-3)
     # the samples are sorted by head and their counts match the graphs' processors
     heads = [gws.HEAD_OF[t] for t in batch.types]
     assert heads == sorted(heads)
@@ -112,19 +115,20 @@ def test_warm_start_training_reduces_loss_and_predicts(env):
         assert tab.shape == (batch.plan.info.n_type_rows[t], gx.PARAM_COLS[t])
 
 
-def test_trained_network_beats_the_prior_mean_on_eq():
-    """What training gains: on small consoles the held-out EQ band predictions beat the
-    training-set mean (standardised MSE 1.0), the baseline a fit without the network
-    would have to beat.  (On 32-200-node consoles the per-node features carry too
-    little of each node's effect on the mix for any head to beat the mean.)"""
+def test_trained_network_beats_the_prior_mean():
+    """What training gains: on held-out consoles of the training distribution (32-200
+    nodes), the gain, imager, EQ and compressor heads beat the training-set mean
+    (standardised MSE 1.0), the baseline a fit without the network would have to beat.
+    (The delay head cannot: a tap up to 500 ms late has no frame overlap with its input.)"""
     gx, torch, gfit, gws = env_tuple()
     ws = gws.WarmStart(max_batch=512, max_rows=1024, max_len=32768, lr=1e-3)
-    gws.train(ws, 2400, 32768, graphs_per_batch=48, epochs=12, minibatch=256, seed=11, lo=4, hi=8)
+    gws.train(ws, 480, 32768, graphs_per_batch=48, epochs=10, minibatch=256, seed=11)
     print("held-out standardised MSE per head:", ws.held_out)
-    assert ws.held_out["e"][0] < EQ_GAIN_BOUND, ws.held_out
+    for h in "gsec":
+        assert ws.held_out[h][0] < HEAD_BOUND, (h, ws.held_out)
 
 
-EQ_GAIN_BOUND = 0.9
+HEAD_BOUND = 0.95
 
 
 def env_tuple():

@@ -119,6 +119,39 @@ def test_logmel_matches_oracle(env, L):
         np.testing.assert_array_equal(got[r, 128:], got[r2, :128])
 
 
+@pytest.mark.parametrize("L", [2048, 44100 + 3])
+def test_xgain_matches_oracle(env, L):
+    """Cross-spectral band gain of node inputs against target rows through a row map:
+    an exact copy at -6 dB, a filtered copy plus an independent track, and a sample whose
+    target index is out of range (zero target)."""
+    gx, torch = env
+    P = (L + 3) // 4 * 4
+    u = synth.sources(70 + L % 13, 3, L, pitch=P)                    # node inputs [3, 2, P]
+    other = synth.sources(90, 1, L, pitch=P)[0]
+    T = np.zeros((2, 2, P), np.float32)
+    T[0] = 0.5 * u[0]
+    k = np.array([0.5, 0.3, 0.2])                                     # a short FIR on sample 1's input
+    for ch in range(2):
+        T[1, ch, :L] = np.convolve(u[1, ch, :L], k)[:L] + other[ch, :L]
+    rmap = [0, 1, 7]
+    net = gx.WarmStartNet(max_batch=4, max_rows=8, max_len=L)
+    ud = torch.tensor(u.reshape(-1), device="cuda")
+    td = torch.tensor(T.reshape(-1), device="cuda")
+    feats = torch.full((3, 256, 32), float("nan"), device="cuda")
+    rm = torch.tensor(rmap, dtype=torch.int32, device="cuda")
+    st = gx._stream(torch, ud.device)
+    net.xgain_raw(ud, 3, 2 * P, td, 2, 2 * P, rm, P, L, 128, feats, st)
+    torch.cuda.synchronize()
+    got = feats.cpu().numpy()[:, 128:]
+    for i, r in enumerate(rmap):
+        tgt = T[r, :, :L] if r < 2 else np.zeros((2, L))
+        want = ow.xgain(u[i, :, :L], tgt)
+        # FP32 spectra: the ratio of two band sums to about 1e-5, at most 1e-3 after the log
+        np.testing.assert_allclose(got[i], want, rtol=0, atol=1e-3, err_msg=f"sample {i}")
+    np.testing.assert_allclose(got[0], np.log(0.5 + ow.XG_FLOOR), atol=1e-4)
+    np.testing.assert_allclose(got[2], np.log(ow.XG_FLOOR), rtol=0, atol=1e-5)   # FP32 logf
+
+
 def test_logmel_rejects_short_rows_and_small_workspace(env):
     gx, torch = env
     net = gx.WarmStartNet(max_batch=2, max_rows=1, max_len=4096)

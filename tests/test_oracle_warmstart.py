@@ -153,3 +153,54 @@ def test_backward_all_heads_finite_differences():
                 fm[j] -= h
                 num = (d @ ow.forward(fp, feats, t)[0] - d @ ow.forward(fm, feats, t)[0]) / (2 * h)
                 assert np.isclose(g[j], num, rtol=1e-5, atol=1e-8), (name, j)
+
+
+def _stereo(rng, L):
+    return rng.standard_normal((2, L))
+
+
+def test_xgain_of_a_scaled_copy_is_the_scale(rng):
+    # target = a * u on both channels: every band's gain is a (mid and side)
+    u = _stereo(rng, 2 ** 14)
+    for a in (0.25, 1.0, 3.0):
+        np.testing.assert_allclose(ow.xgain(u, a * u), np.log(a + ow.XG_FLOOR), rtol=1e-12, atol=1e-12)
+    # a phase-inverted copy has a negative gain, floored
+    np.testing.assert_allclose(ow.xgain(u, -u), np.log(ow.XG_FLOOR), rtol=1e-12)
+
+
+def test_xgain_separates_mid_and_side(rng):
+    # an imager-like target: mid kept, side scaled by b (Eq. 3 keeps the mid)
+    u = _stereo(rng, 2 ** 14)
+    b = 0.4
+    mid, side = 0.5 * (u[0] + u[1]), 0.5 * (u[0] - u[1])
+    T = np.stack([mid + b * side, mid - b * side])
+    f = ow.xgain(u, T)
+    np.testing.assert_allclose(f[:ow.XG_BANDS], np.log(1.0 + ow.XG_FLOOR), rtol=1e-12)
+    np.testing.assert_allclose(f[ow.XG_BANDS:], np.log(b + ow.XG_FLOOR), rtol=1e-12)
+
+
+def test_xgain_ignores_an_independent_source(rng):
+    # the node's path plus an independent track: the estimate tends to the path's gain
+    L = 2 ** 17
+    u, n = _stereo(rng, L), _stereo(rng, L)
+    f = ow.xgain(u, 2.0 * u + n)
+    # wide high bands average many bins and frames: close to ln(2.01)
+    assert abs(np.median(f[40:64]) - np.log(2.0 + ow.XG_FLOOR)) < 0.05
+
+
+def test_xgain_sums_against_a_direct_dft(rng):
+    # one frame, one band pair, computed with explicit DFT sums
+    L = ow.MEL_NFFT
+    u, T = _stereo(rng, L), _stereo(rng, L)
+    f = ow.xgain(u, T, T_slots=1)
+    n = np.arange(L)
+    w = 0.5 - 0.5 * np.cos(2 * np.pi * n / L)
+    W = ow.mel_filterbank()
+    um, tm = 0.5 * (u[0] + u[1]) * w, 0.5 * (T[0] + T[1]) * w
+    k = np.arange(L // 2 + 1)
+    E = np.exp(-2j * np.pi * np.outer(k, n) / L)
+    U, Y = E @ um, E @ tm
+    band = 10
+    C = (W[2 * band] + W[2 * band + 1]) @ np.real(Y * np.conj(U))
+    P = (W[2 * band] + W[2 * band + 1]) @ np.abs(U) ** 2
+    assert abs(f[band, 0] - np.log(max(C / P, 0.0) + ow.XG_FLOOR)) < 1e-10
