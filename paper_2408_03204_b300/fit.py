@@ -202,7 +202,7 @@ def main():
     rendered from hidden parameters; prints one JSON line with the time per step, the
     total time and the loss curve summary.
 
-        python -m paper_2408_03204_b300.fit --budget 200 --length 262144 --steps 1000
+        python -m paper_2408_03204_b300.fit --nodes 200 --length 262144 --steps 1000
     """
     import argparse
     import json
@@ -214,14 +214,14 @@ def main():
     from . import Graph, Plan
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--budget", type=int, default=200)
+    ap.add_argument("--nodes", type=int, default=200)
     ap.add_argument("--length", type=int, default=2 ** 18)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--lr", type=float, default=1e-2)
     ap.add_argument("--checkpoint-steps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=4)
     args = ap.parse_args()
-    g = synth.console_all_types(args.seed, args.budget)
+    g = synth.console_all_types(args.seed, args.nodes)
     L = args.length
     dev = torch.device("cuda")
     plan = Plan([Graph.from_lists(g.types, g.edges)], [L], checkpoint_steps=args.checkpoint_steps)

@@ -153,8 +153,14 @@ def batch_cfg3(seed=3, n_graphs=128, l_lo=2 ** 15, l_hi=2 ** 18):
     return graphs, lengths
 
 
-def console_all_types(seed=4, budget=200) -> Graph:
-    """A ~200-node console whose chains draw from every processor type incl. reverb."""
-    rng = np.random.Generator(np.random.PCG64(seed))
-    return random_console(rng, budget_lo=budget, budget_hi=budget, depth_lo=3, depth_hi=3,
-                          chain_lo=2, chain_hi=6, kinds=(G, E, C, S, D, R))
+def console_all_types(seed=4, nodes=200) -> Graph:
+    """A console of at least ``nodes`` nodes (the first draw with the node budget raised
+    one at a time from ``nodes`` until the console reaches that size) whose chains draw
+    from every processor type incl. reverb.  seed 4, 200 nodes: 201 nodes."""
+    for budget in range(nodes, 4 * nodes):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        g = random_console(rng, budget_lo=budget, budget_hi=budget, depth_lo=3, depth_hi=3,
+                           chain_lo=2, chain_hi=6, kinds=(G, E, C, S, D, R))
+        if g.n_nodes >= nodes:
+            return g
+    return g
