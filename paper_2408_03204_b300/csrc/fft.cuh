@@ -368,6 +368,57 @@ __device__ __forceinline__ void forward_regs(float2 (&v)[16], float2* b0, float2
                                              const float2_* __restrict__ ptw, int tid) {
   forward_regs_tw<M>(v, b0, b1, ptw + ptw_base(M), tid);
 }
+
+// forward_regs with one shared buffer: the same register layouts on entry (x[tid + T m])
+// and exit (X[tid + T m]), every inner pass reading the whole buffer into registers,
+// a barrier, then writing it back.  The caller guarantees that no thread still reads buf
+// when this is entered; on exit other threads may still read it.  All threads of the
+// CTA call it (barriers); ptw: the concatenated pass tables.
+template <int M>
+__device__ __forceinline__ void forward_regs_1buf(float2 (&v)[16], float2* buf, const float2_* __restrict__ ptw,
+                                                  int tid) {
+  constexpr int n16 = Geo<M>::n16, last = Geo<M>::last;
+  constexpr int npass = n16 + (last > 1 ? 1 : 0);
+  const float2_* tw = ptw + ptw_base(M);
+  {  // pass 1: radix 16, Ns = 1, from registers
+    float2(*w)[16] = reinterpret_cast<float2(*)[16]>(v);
+    Dft<16>::run(w[0]);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[pad(tid * 16 + r)] = v[r];
+  }
+  __syncthreads();
+  int Ns = 16;
+#pragma unroll
+  for (int p = 1; p < npass; ++p) {
+    const bool is_last = (p == npass - 1);
+    const int R = (is_last && last > 1) ? last : 16;
+    if (R == 16) {
+      float2 w[1][16];
+      pass_load<M, 16>(buf, tid, w);
+      if (!is_last) __syncthreads();   // every thread has read before any writes
+      pass_compute<M, 16>(tw + ptw_pass_off(M, p), tid, Ns, w);
+      if (is_last) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = w[0][r];
+      } else {
+        const int j = tid, k = j & (Ns - 1), out = (j - k) * 16 + k;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) buf[pad(out + r * Ns)] = w[0][r];
+        __syncthreads();
+      }
+    } else if constexpr (last > 1 && last < 16) {
+      constexpr int RL = last, BPT = 16 / RL;
+      float2 w[BPT][RL];
+      pass_load<M, RL>(buf, tid, w);
+      pass_compute<M, RL>(tw + ptw_pass_off(M, p), tid, Ns, w);
+#pragma unroll
+      for (int b = 0; b < BPT; ++b)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) v[b + r * BPT] = w[b][r];
+    }
+    if (!is_last) Ns *= 16;
+  }
+}
 #endif
 
 }  // namespace fft

@@ -222,6 +222,7 @@ __global__ void k_delay_design(DevCtx c, int node_begin) {
 __global__ void __launch_bounds__(DL_M / 16, 2) k_delay_spec(DevCtx c, int item0, int n_items) {
   extern __shared__ float2 smem2[];
   float2* buf = smem2;
+  constexpr int T = DL_M / 16;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
     const int v = w.x, idx = w.y, kind = w.z;
@@ -234,27 +235,34 @@ __global__ void __launch_bounds__(DL_M / 16, 2) k_delay_spec(DevCtx c, int item0
       for (int k = threadIdx.x; k < DL_M; k += blockDim.x) out[k] = make_float2(0.f, 0.f);
       continue;   // uniform over the CTA
     }
-    __syncthreads();
-    // quads of 4 samples (start and count are multiples of 4, so a quad lies wholly
-    // before the signal or starts inside it), all of a thread's loads issued together
-    constexpr int Q = DL_M / (4 * (DL_M / 16));
+    const int e0 = adj ? c.tcsr_ptr[v] : c.csr_ptr[v];
+    const int e1 = adj ? c.tcsr_ptr[v + 1] : c.csr_ptr[v + 1];
+    const float* single = e1 - e0 == 1 ? (adj ? out_adj_row(c, e0) : in_row(c, e0)) : nullptr;
+    // thread t takes samples start + t + T m (m < 16) straight into the registers of the
+    // transform's first pass, all loads issued together
+    float2 x[16];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      const int i = 4 * (threadIdx.x + q * (DL_M / 16));
-      const int t = start + i;
-      float4 l = f4zero(), r = f4zero();
+    for (int m = 0; m < 16; ++m) {
+      const int i = threadIdx.x + T * m, t = start + i;
+      float l = 0.f, r = 0.f;
       if (i < count && t >= 0 && t < nd.len) {
-        l = adj ? gather_out_adj(c, v, 0, t, nd.len, nd.pitch) : gather_in(c, v, 0, t, nd.len, nd.pitch);
-        r = adj ? gather_out_adj(c, v, 1, t, nd.len, nd.pitch) : gather_in(c, v, 1, t, nd.len, nd.pitch);
+        if (single) {
+          l = single[t];
+          r = single[nd.pitch + t];
+        } else {
+          for (int e = e0; e < e1; ++e) {
+            const float* row = adj ? out_adj_row(c, e) : in_row(c, e);
+            l += row[t];
+            r += row[nd.pitch + t];
+          }
+        }
       }
-      buf[fft::pad(i)] = make_float2(l.x, r.x);
-      buf[fft::pad(i + 1)] = make_float2(l.y, r.y);
-      buf[fft::pad(i + 2)] = make_float2(l.z, r.z);
-      buf[fft::pad(i + 3)] = make_float2(l.w, r.w);
+      x[m] = make_float2(l, r);
     }
-    __syncthreads();
-    fft::forward<DL_M>(buf, c.ptw, threadIdx.x, true);
-    for (int k = threadIdx.x; k < DL_M; k += blockDim.x) out[k] = buf[fft::pad(k)];
+    __syncthreads();   // readers of buf (the previous item's last pass) are done
+    fft::forward_regs_1buf<DL_M>(x, buf, c.ptw, threadIdx.x);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) out[threadIdx.x + T * m] = x[m];
   }
 }
 
@@ -311,29 +319,37 @@ __global__ void __launch_bounds__(DL_CHUNK * DL_PMAX) k_delay_acc(DevCtx c, int 
   }
 }
 
-// r_x[n] for n = -B + p B + nu, nu in [0, B): r_p[nu] = IDFT(R_p)[B - nu].
+// r_x[n] for n = -B + p B + nu, nu in [0, B): r_p[nu] = IDFT(R_p)[B - nu].  The spectrum
+// goes straight into the transform's registers (thread t: bins t + T m) and the lags come
+// straight out of them.
 __global__ void __launch_bounds__(DL_M / 16) k_delay_lags(DevCtx c, int item0, int n_items) {
   extern __shared__ float2 smem2[];
   float2* buf = smem2;
+  constexpr int T = DL_M / 16;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
     const int v = w.x, p = w.y;
     const int4_ e = c.ext[v];
     const float2* R = c.dl_R + (size_t(e.y) + p) * DL_M;
-    __syncthreads();
-    for (int k = threadIdx.x; k < DL_M; k += blockDim.x) {
-      const float2 z = R[k];
-      buf[fft::pad(k)] = make_float2(z.x, -z.y);
+    float2 x[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const float2 z = R[threadIdx.x + T * m];
+      x[m] = make_float2(z.x, -z.y);
     }
-    __syncthreads();
-    fft::forward<DL_M>(buf, c.ptw, threadIdx.x, true);
+    __syncthreads();   // readers of buf (the previous item's last pass) are done
+    fft::forward_regs_1buf<DL_M>(x, buf, c.ptw, threadIdx.x);
     const int nlag = c.dl_P * DL_B;
     float* rl = c.dl_r + size_t(e.z) * 2 * nlag;
     const float inv = 1.f / float(DL_M);
-    for (int nu = threadIdx.x; nu < DL_B; nu += blockDim.x) {
-      const float2 z = buf[fft::pad(DL_B - nu)];         // conj(result) / M = (l, r)
-      rl[p * DL_B + nu] = z.x * inv;
-      rl[nlag + p * DL_B + nu] = -z.y * inv;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int k = threadIdx.x + T * m;   // conj(result) / M at bin k = (l, r) of lag B - k
+      if (k >= 1 && k <= DL_B) {
+        const int nu = DL_B - k;
+        rl[p * DL_B + nu] = x[m].x * inv;
+        rl[nlag + p * DL_B + nu] = -x[m].y * inv;
+      }
     }
   }
 }

@@ -41,19 +41,6 @@ __device__ __forceinline__ float hann(const float2_* tw, int n) {
   return 0.5f - 0.5f * tw[n * (TWIDDLE_N / M)].x;
 }
 
-template <int M>
-__device__ __forceinline__ void load_frame(const LossArgs& a, const LossRow& r, const float* base, int f, int gtid,
-                                           float2* buf, bool active) {
-  constexpr int T = M / 16;
-  if (!active) return;
-  const float* row = base + r.off;
-  const int t0 = f * (M / 4);
-  for (int n = gtid; n < M; n += T) {
-    float w = hann<M>(a.tw, n);
-    buf[fft::pad(n)] = make_float2(w * row[t0 + n], w * row[r.pitch + t0 + n]);
-  }
-}
-
 // Split packed spectrum Z of l + i r at bin k into the two channel spectra.
 __device__ __forceinline__ void split(float2 z, float2 zm, float2* L, float2* R) {
   // L = (Z[k] + conj(Z[M-k]))/2 ; R = (Z[k] - conj(Z[M-k]))/(2i)
@@ -78,11 +65,30 @@ __device__ __forceinline__ void loss_item_fwd(const LossArgs& a, const int4_ ite
   float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   float2* fy = by + g * fft::Padded<M>::size;
   float2* ft = bt + g * fft::Padded<M>::size;
-  load_frame<M>(a, r, a.y, f, gtid, fy, act);
-  load_frame<M>(a, r, a.tgt, f, gtid, ft, act);
+  // both windowed frames straight into the transforms' registers (thread gtid: samples
+  // gtid + T m), all loads issued together
+  float2 xy[16], xt[16];
+  {
+    const float* ry = a.y + r.off;
+    const float* rt = a.tgt + r.off;
+    const int t0 = f * (M / 4);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int n = gtid + T * m;
+      const float w = hann<M>(a.tw, n);
+      xy[m] = act ? make_float2(w * ry[t0 + n], w * ry[r.pitch + t0 + n]) : make_float2(0.f, 0.f);
+      xt[m] = act ? make_float2(w * rt[t0 + n], w * rt[r.pitch + t0 + n]) : make_float2(0.f, 0.f);
+    }
+  }
+  fft::forward_regs_1buf<M>(xy, fy, a.ptw, gtid);
+  fft::forward_regs_1buf<M>(xt, ft, a.ptw, gtid);
+  __syncthreads();   // every thread's last pass has read the buffers
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {   // the spectra in natural order for the bin pairs (k, M - k)
+    fy[fft::pad(gtid + T * m)] = xy[m];
+    ft[fft::pad(gtid + T * m)] = xt[m];
+  }
   __syncthreads();
-  fft::forward<M>(fy, a.ptw, gtid, true);
-  fft::forward<M>(ft, a.ptw, gtid, true);
   if (act) {
     constexpr int nb = M / 2 + 1;
     float2* sp = a.spec + r.spec_off[q] + int64_t(f) * nb;
@@ -119,6 +125,7 @@ __global__ void __launch_bounds__(256, 2) k_loss_fwd(LossArgs a) {
   extern __shared__ float2 smem2[];
   for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
     const int4_ item = a.items[it];
+    __syncthreads();   // the previous item's readers of the buffers are done
     switch (item.y) {
       case 0: loss_item_fwd<512>(a, item, smem2); break;
       case 1: loss_item_fwd<1024>(a, item, smem2); break;
@@ -210,14 +217,21 @@ __device__ __forceinline__ void loss_item_bwd(const LossArgs& a, const int4_ ite
     }
   }
   __syncthreads();
-  fft::forward<M>(fy, a.ptw, gtid, true);
+  // the packed spectrum into the transform's registers (thread gtid: bins gtid + T m); the
+  // windowed frame comes straight out of them
+  float2 x[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) x[m] = fy[fft::pad(gtid + T * m)];
+  __syncthreads();   // every thread has read its bins before the first pass writes
+  fft::forward_regs_1buf<M>(x, fy, a.ptw, gtid);
   if (act) {
     float* fr = a.frames + r.frame_off[q] + int64_t(f) * 2 * M;
-    for (int n = gtid; n < M; n += T) {
-      float2 z = fy[fft::pad(n)];
-      float w = hann<M>(a.tw, n);
-      fr[n] = w * z.x;          // conj of the result: real part is l
-      fr[M + n] = -w * z.y;     // minus imaginary part is r
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int n = gtid + T * m;
+      const float w = hann<M>(a.tw, n);
+      fr[n] = w * x[m].x;          // conj of the result: real part is l
+      fr[M + n] = -w * x[m].y;     // minus imaginary part is r
     }
   }
 }
