@@ -60,7 +60,7 @@ __device__ __forceinline__ void dl_window_sum(const DevCtx& c, int v, const Node
   }
 }
 
-constexpr int DL_GROUP = 4;                  // taps whose windows are staged together
+constexpr int DL_GROUP = 2;                  // taps whose windows are staged together
 constexpr int DL_OPT = 8;                    // consecutive outputs per thread
 constexpr int DL_FT = DL_TILE / DL_OPT;      // threads of the FIR kernels
 constexpr int DL_SH = DL_FIR + 3;            // taps of the shifted filters (alignment shift 0..3)
@@ -266,6 +266,12 @@ __global__ void __launch_bounds__(DL_M / 16, 2) k_delay_spec(DevCtx c, int item0
   }
 }
 
+// cp.async of 8 bytes (both addresses 8-byte aligned) into shared memory.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 // R_p[k] for one node and DL_CHUNK bins, all lag partitions: per channel
 // sum_b X_{b-p}[k] conj(Ybar_b[k]), packed as R_l + i R_r for the joint inverse.  The
 // per-channel products of real signals' spectra are conjugate-symmetric, so the work
@@ -282,39 +288,65 @@ __global__ void __launch_bounds__(DL_CHUNK * DL_PMAX) k_delay_acc(DevCtx c, int 
     float2* X = sm;                         // [nw][DL_CHUNK][2 ch]
     float2* Y = sm + size_t(nw) * DL_CHUNK * 2;
     __syncthreads();
-#pragma unroll 4
-    for (int i = threadIdx.x; i < (nw + nb) * DL_CHUNK; i += blockDim.x) {
+    // Z[k] and Z[M - k] of every staged spectrum copied asynchronously (all of a thread's
+    // copies in flight together), then split in place into the channels' spectra:
+    // l = (Z[k] + conj(Z[-k]))/2, r = (Z[k] - conj(Z[-k]))/(2i).  X and Y are contiguous.
+    const int n_el = (nw + nb) * DL_CHUNK;
+    for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
       const int s = i / DL_CHUNK, kk = i % DL_CHUNK, k = k0 + kk, km = (DL_M - k) & (DL_M - 1);
-      const float2* spec = c.dl_spec + size_t(e.x + s) * DL_M;
-      // u windows w = s - P < -1 hold no sample of the signal: zero spectra, never written
-      const bool none = s < P - 1;
-      const float2 z = none ? make_float2(0.f, 0.f) : spec[k], zm = none ? make_float2(0.f, 0.f) : spec[km];
-      // l = (Z[k] + conj(Z[-k]))/2 ; r = (Z[k] - conj(Z[-k]))/(2i)
-      const float2 l = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-      const float2 r = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
-      float2* dst = (s < nw ? X + (size_t(s) * DL_CHUNK + kk) * 2 : Y + (size_t(s - nw) * DL_CHUNK + kk) * 2);
-      dst[0] = l;
-      dst[1] = r;
+      float2* dst = X + size_t(i) * 2;
+      if (s < P - 1) {   // u windows w = s - P < -1 hold no sample: zero spectra, never written
+        dst[0] = make_float2(0.f, 0.f);
+        dst[1] = make_float2(0.f, 0.f);
+      } else {
+        const float2* spec = c.dl_spec + size_t(e.x + s) * DL_M;
+        cp_async8(dst, spec + k);
+        cp_async8(dst + 1, spec + km);
+      }
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
+      float2* dst = X + size_t(i) * 2;
+      const float2 z = dst[0], zm = dst[1];
+      dst[0] = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+      dst[1] = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
     }
     __syncthreads();
-    const int kk = threadIdx.x % DL_CHUNK, p = threadIdx.x / DL_CHUNK;
-    float2 al = make_float2(0.f, 0.f), ar = make_float2(0.f, 0.f);
+    // thread (pair q, bin kk) accumulates partitions p = 2q and 2q + 1: partition p + 1
+    // at block b uses the window partition p used at block b - 1, carried in registers
+    const int kk = threadIdx.x % DL_CHUNK, p0 = 2 * (threadIdx.x / DL_CHUNK);
+    float2 a0l = make_float2(0.f, 0.f), a0r = a0l, a1l = a0l, a1r = a0l;
+    float2 pl = X[(size_t(P - p0 - 1) * DL_CHUNK + kk) * 2];       // window -p0 - 1 (b = -1)
+    float2 pr = X[(size_t(P - p0 - 1) * DL_CHUNK + kk) * 2 + 1];
 #pragma unroll 4
     for (int b = 0; b < nb; ++b) {
-      const int ws = b - p + P;               // window index b - p, stored from -P
+      const int ws = b - p0 + P;              // window index b - p0, stored from -P
       const float2 xl = X[(size_t(ws) * DL_CHUNK + kk) * 2], xr = X[(size_t(ws) * DL_CHUNK + kk) * 2 + 1];
       const float2 yl = Y[(size_t(b) * DL_CHUNK + kk) * 2], yr = Y[(size_t(b) * DL_CHUNK + kk) * 2 + 1];
-      al.x += xl.x * yl.x + xl.y * yl.y;
-      al.y += xl.y * yl.x - xl.x * yl.y;
-      ar.x += xr.x * yr.x + xr.y * yr.y;
-      ar.y += xr.y * yr.x - xr.x * yr.y;
+      a0l.x += xl.x * yl.x + xl.y * yl.y;
+      a0l.y += xl.y * yl.x - xl.x * yl.y;
+      a0r.x += xr.x * yr.x + xr.y * yr.y;
+      a0r.y += xr.y * yr.x - xr.x * yr.y;
+      a1l.x += pl.x * yl.x + pl.y * yl.y;
+      a1l.y += pl.y * yl.x - pl.x * yl.y;
+      a1r.x += pr.x * yr.x + pr.y * yr.y;
+      a1r.y += pr.y * yr.x - pr.x * yr.y;
+      pl = xl;
+      pr = xr;
     }
     // R_l + i R_r at k, conj(R_l) + i conj(R_r) at M - k
     const int k = k0 + kk;
-    float2* R = c.dl_R + (size_t(e.y) + p) * DL_M;
     if (k <= DL_M / 2) {
-      R[k] = make_float2(al.x - ar.y, al.y + ar.x);
-      if (k > 0 && k < DL_M / 2) R[DL_M - k] = make_float2(al.x + ar.y, ar.x - al.y);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        if (p0 + j >= P) break;
+        const float2 al = j ? a1l : a0l, ar = j ? a1r : a0r;
+        float2* R = c.dl_R + (size_t(e.y) + p0 + j) * DL_M;
+        R[k] = make_float2(al.x - ar.y, al.y + ar.x);
+        if (k > 0 && k < DL_M / 2) R[DL_M - k] = make_float2(al.x + ar.y, ar.x - al.y);
+      }
     }
   }
 }
@@ -518,7 +550,9 @@ int launch_delay(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
     case 1: if (b > 0) k_delay_fir<false><<<grid_size(b, 8), DL_FT, 0, s>>>(c, a, b); return b > 0;
     case 2: if (b > 0) k_delay_fir<true><<<grid_size(b, 8), DL_FT, 0, s>>>(c, a, b); return b > 0;
     case 3: if (b > 0) k_delay_spec<<<grid_size(b, 3), DL_M / 16, sm_fft, s>>>(c, a, b); return b > 0;
-    case 4: if (b > 0) k_delay_acc<<<grid_size(b, acc_per_sm), DL_CHUNK * c.dl_P, sm_acc, s>>>(c, a, b); return b > 0;
+    case 4:   // one thread per bin and pair of lag partitions
+      if (b > 0) k_delay_acc<<<grid_size(b, acc_per_sm), DL_CHUNK * ((c.dl_P + 1) / 2), sm_acc, s>>>(c, a, b);
+      return b > 0;
     case 5: if (b > 0) k_delay_lags<<<grid_size(b, 3), DL_M / 16, sm_fft, s>>>(c, a, b); return b > 0;
     case 6: if (b > 0) k_delay_grad<<<grid_size(b, 4), 256, 0, s>>>(c, a, b); return b > 0;
   }
