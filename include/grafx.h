@@ -452,6 +452,13 @@ int grafx_ws_backward(grafx_wsnet* n, const float* weights, const float* feats, 
  * columns).  Asynchronous on `stream`. */
 int grafx_ws_mse(const float* out, const float* target, const int32_t* n_out, int32_t B, float* loss, float* d_out,
                  void* stream);
+/* The network's outputs are the fit's theta standardised per head and column: row i of
+ * x (device float32 [B][cols]) uses the statistics of head head[i] (device int32) in mu
+ * and sd (device float32 [heads][cols]); back = 0 gives y = (x - mu) / sd (training
+ * targets), back = 1 gives y = mu + sd x (predictions); columns at or past n_out[i]
+ * (device int32) are written 0.  y may be x.  Asynchronous on `stream`. */
+int grafx_ws_standardise(const float* x, const int32_t* head, const int32_t* n_out, const float* mu, const float* sd,
+                         int32_t B, int32_t cols, int32_t back, float* y, void* stream);
 /* Synchronise `stream` and report (and clear) a bounded tensor-core wait of the net's
  * products that expired since the last call: GRAFX_ETIMEOUT, else GRAFX_OK. */
 int grafx_ws_sync_status(grafx_wsnet* n, void* stream);

@@ -112,6 +112,7 @@ SIGNATURES = {
     "grafx_ws_workspace_bytes": (ctypes.c_int, [_P, _I32, _I64, ctypes.POINTER(_SZ)]),
     "grafx_ws_bind": (ctypes.c_int, [_P, _P, _SZ, _P]),
     "grafx_ws_logmel": (ctypes.c_int, [_P, _F, _I32, _I64, _I64, _I64, _P, _I32, _I32, _F, _P]),
+    "grafx_ws_standardise": (ctypes.c_int, [_F, _F, _F, _F, _F, _I32, _I32, _I32, _F, _P]),
     "grafx_ws_xgain": (ctypes.c_int, [_P, _F, _I32, _I64, _F, _I32, _I64, _F, _I64, _I64, _I32, _F, _P]),
     "grafx_ws_forward": (ctypes.c_int, [_P, _F, _F, _I32P, _I32, _F, _P]),
     "grafx_ws_backward": (ctypes.c_int, [_P, _F, _F, _I32P, _I32, _F, _F, _P]),

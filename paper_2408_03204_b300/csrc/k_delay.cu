@@ -405,8 +405,10 @@ __device__ __forceinline__ cplx cdv(cplx a, cplx b) {
 struct DlSurrogate {
   cplx zN, bz, zinv;
   float dlt, tx, npi, rf, one_m_rho;
+  float rot_c, rot_s;   // cos, sin of pi / N_d: the half-angle step from one lag to the next
   int d0;
 };
+constexpr int DL_FAR = 80;   // lags from the pole beyond which the phasor is rotated, not recomputed
 
 __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_items) {
   __shared__ DlSurrogate sc;
@@ -452,6 +454,8 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
       sc.npi = float(Nd * M_PI);
       sc.rf = float(rho);
       sc.one_m_rho = float(1.0 - rho);
+      sc.rot_c = float(cos(M_PI / Nd));
+      sc.rot_s = float(sin(M_PI / Nd));
     }
     __syncthreads();
     // FIR taps: dL/dc[j] = r[d + j]; chain through the window, cosine sum and exp
@@ -477,6 +481,17 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
         const int n = n0 + i - H;   // needed for n < N_d + H only (the lag range of the tap)
         win[i] = n < Nd + H ? rs[n] : 0.f;
       }
+      // Runs of lags away from the pole (|m| >= DL_FAR for every lag of the run) take the
+      // half-angle phasor of their first lag from sincospif and rotate it by pi / N_d per lag
+      // (the wrap of m at N_d/2 flips the phasor's sign, which a = 1 - q does not see);
+      // runs near the pole evaluate every lag exactly, with the Taylor branch next to it.
+      int mm0 = n0 - d0;
+      if (mm0 < 0) mm0 += Nd;
+      if (2 * mm0 > Nd) mm0 -= Nd;
+      const bool far = mm0 >= DL_FAR || mm0 <= -(DL_FAR + RUN);
+      float sh0 = 0.f, ch0 = 1.f;
+      if (far) sincospif(0.5f * (dlt + float(mm0) * two_n), &sh0, &ch0);
+      const cplx t1 = {1.f + float(Nd - 1) * zN.x, float(Nd - 1) * zN.y};
 #pragma unroll
       for (int u = 0; u < RUN; ++u) {
         const int n = n0 + u;
@@ -484,37 +499,50 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
           float g = 0.f;
 #pragma unroll
           for (int jj = 0; jj < DL_FIR; ++jj) g += cs[jj] * win[u + jj];
-          int mm = n - d0;
-          if (mm < 0) mm += Nd;
-          if (2 * mm > Nd) mm -= Nd;
-          const float phf = dlt + float(mm) * two_n;   // arg q / pi
-          const float ty = npi * phf;                   // t = N ln q = tx + i ty
           cplx F;
-          if (tx * tx + ty * ty < 0.25f) {
-            // F = N^2 sum_j e_j t^j with e_j = (sum_k k^(j+1)) / (N^(j+2) j!)
-            cplx t = {tx, ty}, tp = {1.f, 0.f};
-            F = {0.f, 0.f};
+          float sh = sh0, chh = ch0;
+          bool taylor = false;
+          if (!far) {
+            int mm = n - d0;
+            if (mm < 0) mm += Nd;
+            if (2 * mm > Nd) mm -= Nd;
+            const float phf = dlt + float(mm) * two_n;   // arg q / pi
+            const float ty = npi * phf;                   // t = N ln q = tx + i ty
+            taylor = tx * tx + ty * ty < 0.25f;
+            if (taylor) {
+              // F = N^2 sum_j e_j t^j with e_j = (sum_k k^(j+1)) / (N^(j+2) j!)
+              cplx t = {tx, ty}, tp = {1.f, 0.f};
+              F = {0.f, 0.f};
 #pragma unroll
-            for (int j = 0; j < 9; ++j) {
-              F.x += c.dl_taylor[j] * tp.x;
-              F.y += c.dl_taylor[j] * tp.y;
-              tp = cm(tp, t);
+              for (int j = 0; j < 9; ++j) {
+                F.x += c.dl_taylor[j] * tp.x;
+                F.y += c.dl_taylor[j] * tp.y;
+                tp = cm(tp, t);
+              }
+              F.x *= float(Nd) * float(Nd);
+              F.y *= float(Nd) * float(Nd);
+            } else {
+              sincospif(0.5f * phf, &sh, &chh);
             }
-            F.x *= float(Nd) * float(Nd);
-            F.y *= float(Nd) * float(Nd);
-          } else {
-            float sh, chh;
-            sincospif(0.5f * phf, &sh, &chh);
-            // a = 1 - q = (1 - rho) + 2 rho sin^2(ph/2) - i rho sin(ph)
+          }
+          if (!taylor) {
+            // a = 1 - q = (1 - rho) + 2 rho sin^2(ph/2) - i rho sin(ph);
+            // F = (-a t1 - (z^N - 1)) / a^2 = -(1/a) (t1 + (z^N - 1) / a)
             const cplx a = {one_m_rho + 2.f * rf * sh * sh, -rf * 2.f * sh * chh};
-            const cplx t1 = {1.f + float(Nd - 1) * zN.x, float(Nd - 1) * zN.y};
-            const cplx am = cm(a, t1);
-            const cplx num = {-am.x - bz.x, -am.y - bz.y};
-            F = cdv(num, cm(a, a));
+            const float ia = 1.f / (a.x * a.x + a.y * a.y);
+            const cplx ainv = {a.x * ia, -a.y * ia};
+            const cplx w2 = cm(bz, ainv);
+            const cplx w3 = cm(ainv, cplx{t1.x + w2.x, t1.y + w2.y});
+            F = {-w3.x, -w3.y};
           }
           const cplx ph2 = cm(F, zinv);
           qx += g * ph2.x;
           qy += g * ph2.y;
+          if (far) {   // the next lag's half-angle phasor
+            const float s2 = sh * sc.rot_c + ch0 * sc.rot_s;
+            ch0 = ch0 * sc.rot_c - sh * sc.rot_s;
+            sh0 = s2;
+          }
         }
       }
     }

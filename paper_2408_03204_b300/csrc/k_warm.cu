@@ -1141,6 +1141,31 @@ int grafx_ws_backward(grafx_wsnet* n, const float* weights, const float* feats, 
   return cuda_status();
 }
 
+// Row i of x [B][cols] through its head's column statistics (mu, sd: [n_heads][cols]):
+// forward (x - mu) / sd, or back mu + sd x; columns at or past n_out[i] are written 0.
+__global__ void k_ws_standardise(const float* __restrict__ x, const int32_t* __restrict__ head,
+                                 const int32_t* __restrict__ n_out, const float* __restrict__ mu,
+                                 const float* __restrict__ sd, int B, int cols, int back, float* __restrict__ y) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < int64_t(B) * cols;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int r = int(i / cols), col = int(i % cols);
+    const int h = head[r];
+    const float m = mu[h * cols + col], s = sd[h * cols + col];
+    y[i] = col < n_out[r] ? (back ? m + s * x[i] : (x[i] - m) / s) : 0.f;
+  }
+}
+
+int grafx_ws_standardise(const float* x, const int32_t* head, const int32_t* n_out, const float* mu, const float* sd,
+                         int32_t B, int32_t cols, int32_t back, float* y, void* stream) {
+  if (!x || !head || !n_out || !mu || !sd || !y) return fail(GRAFX_EINVAL, "null argument");
+  if (B < 0 || cols < 1) return fail(GRAFX_ESHAPE, "bad standardisation shape");
+  if (B == 0) return GRAFX_OK;
+  const int64_t n = int64_t(B) * cols;
+  const int g = int(std::min<int64_t>((n + 255) / 256, 148 * 8));
+  k_ws_standardise<<<g, 256, 0, static_cast<cudaStream_t>(stream)>>>(x, head, n_out, mu, sd, B, cols, back ? 1 : 0, y);
+  return cuda_status();
+}
+
 int grafx_ws_mse(const float* out, const float* target, const int32_t* n_out, int32_t B, float* loss, float* d_out,
                  void* stream) {
   if (!out || !target || !n_out || !loss || !d_out) return fail(GRAFX_EINVAL, "null argument");

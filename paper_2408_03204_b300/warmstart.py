@@ -189,19 +189,29 @@ class WarmStart:
                 self.mu[h] = x.mean(0)
                 self.sd[h] = x.std(0).clamp_min(1e-3)
 
-    def _std(self, targets, heads):
-        return (targets - self.mu[heads]) / self.sd[heads]
+    def _standardise(self, x, heads, n_out, back):
+        """(x - mu) / sd (back = False) or mu + sd x (back = True) per row's head, columns
+        past the head's width 0, in the library's kernel (grafx_ws_standardise)."""
+        y = self.torch.empty_like(x)
+        _check(lib().grafx_ws_standardise(_ptr(x), _ptr(heads), _ptr(n_out), _ptr(self.mu), _ptr(self.sd),
+                                          x.shape[0], x.shape[1], int(back), _ptr(y), self.st))
+        return y
+
+    def _head_rows(self, types):
+        torch = self.torch
+        heads = torch.as_tensor([HEAD_OF[t] for t in types], dtype=torch.int32, device=self.device)
+        n_out = torch.as_tensor([WS_HEAD_OUT[HEAD_OF[t]] for t in types], dtype=torch.int32, device=self.device)
+        return heads, n_out
 
     def train_step(self, feats, targets, types):
         """One Adam step on a minibatch (feats [B,256,32], targets theta [B,176], types
         sorted by head).  Returns the device loss tensor."""
         torch = self.torch
         B = feats.shape[0]
-        heads = torch.as_tensor([HEAD_OF[t] for t in types], device=self.device)
+        heads, n_out = self._head_rows(types)
         hc = [sum(1 for t in types if t == ht) for ht in WS_HEAD_TYPES]
-        n_out = torch.as_tensor([WS_HEAD_OUT[HEAD_OF[t]] for t in types], dtype=torch.int32, device=self.device)
         with torch.cuda.stream(self.stream):
-            y = self._std(targets, heads).contiguous()
+            y = self._standardise(targets.contiguous(), heads, n_out, back=False)
             out = torch.empty((B, WS_OUTMAX), dtype=torch.float32, device=self.device)
             d = torch.empty_like(out)
             loss = torch.zeros(1, dtype=torch.float32, device=self.device)
@@ -217,8 +227,7 @@ class WarmStart:
     def predict(self, feats, types):
         """theta [n, 176] (un-standardised) for samples sorted by head."""
         torch = self.torch
-        heads = torch.as_tensor([HEAD_OF[t] for t in types], device=self.device)
-        hc = [sum(1 for t in types if t == ht) for ht in WS_HEAD_TYPES]
+        heads, n_out = self._head_rows(types)
         outs = []
         with torch.cuda.stream(self.stream):
             for a in range(0, feats.shape[0], self.max_batch):
@@ -229,10 +238,7 @@ class WarmStart:
                 self.net.forward_raw(self.W, feats[a:b], hcs, out, self.st)
                 outs.append(out)
             out = torch.cat(outs)
-            mask = torch.arange(WS_OUTMAX, device=self.device)[None, :] < torch.as_tensor(
-                [WS_HEAD_OUT[HEAD_OF[t]] for t in types], device=self.device)[:, None]
-            theta = torch.where(mask, out * self.sd[heads] + self.mu[heads], torch.zeros_like(out))
-        del hc
+            theta = self._standardise(out, heads, n_out, back=True)
         return theta
 
     def theta_tables(self, batch, theta):

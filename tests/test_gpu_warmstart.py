@@ -303,3 +303,27 @@ def test_node_inputs_match_oracle_render(env):
         assert not got[i, :, L:].any()
     with pytest.raises(gx.GrafxError):                   # input nodes have no node input
         run.plan.node_inputs_raw(run.src, out, [0], dst, pitch, gx._stream(torch, dst.device))
+
+
+def test_standardise_round_trip(env):
+    """grafx_ws_standardise: per-row head statistics, masked columns, both directions."""
+    gx, torch = env
+    rng = np.random.Generator(np.random.PCG64(12))
+    B, cols, heads = 37, 176, 6
+    x = rng.standard_normal((B, cols)).astype(np.float32)
+    head = rng.integers(0, heads, B).astype(np.int32)
+    n_out = np.array([ow.HEAD_OUT[ow.HEAD_TYPES[h]] for h in head], np.int32)
+    mu = rng.standard_normal((heads, cols)).astype(np.float32)
+    sd = rng.uniform(0.2, 3.0, (heads, cols)).astype(np.float32)
+    d = lambda a: torch.tensor(a, device="cuda")
+    xd, hd, nd, mud, sdd = d(x), d(head), d(n_out), d(mu), d(sd)
+    y, z = torch.empty_like(xd), torch.empty_like(xd)
+    lib, st = gx.lib(), gx._stream(torch, xd.device)
+    p = gx._ptr
+    assert lib.grafx_ws_standardise(p(xd), p(hd), p(nd), p(mud), p(sdd), B, cols, 0, p(y), st) == 0
+    assert lib.grafx_ws_standardise(p(y), p(hd), p(nd), p(mud), p(sdd), B, cols, 1, p(z), st) == 0
+    torch.cuda.synchronize()
+    mask = np.arange(cols)[None, :] < n_out[:, None]
+    want = np.where(mask, (x - mu[head]) / sd[head], 0.0)
+    np.testing.assert_allclose(y.cpu().numpy(), want, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(z.cpu().numpy(), np.where(mask, x, 0.0), rtol=1e-5, atol=1e-6)
