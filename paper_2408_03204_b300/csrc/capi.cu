@@ -469,7 +469,7 @@ static int render_range(grafx_plan* p, const float* sources, float* out, int32_t
       case GRAFX_T_COMP:
       case GRAFX_T_GATE:
       case GRAFX_T_SIDECHAIN:
-        launches += launch_comp(0, c, st.fitem_begin, st.fitem_count, st.node_begin, st.node_end,
+        launches += launch_comp(0, c, st.fitem_begin, st.fitem_count, st.node_begin, st.node_end, 2 * k,
                                 comp_mode_of(st.type), s);
         break;
       case GRAFX_T_DELAY:
@@ -618,11 +618,11 @@ static int backprop_range(grafx_plan* p, const float* sources, const float* d_ou
       case GRAFX_T_COMP:
       case GRAFX_T_GATE:
       case GRAFX_T_SIDECHAIN:
-        launches += launch_comp(1, c, st.bitem_begin, st.bitem_count, st.node_begin, st.node_end,
+        launches += launch_comp(1, c, st.bitem_begin, st.bitem_count, st.node_begin, st.node_end, 2 * k + 1,
                                 comp_mode_of(st.type), s);
         if (c.dparams) {
           to_side(k);
-          launches += launch_comp(2, c, 0, 0, st.node_begin, st.node_end, 0, side);
+          launches += launch_comp(2, c, 0, 0, st.node_begin, st.node_end, 0, 0, side);
         }
         break;
       case GRAFX_T_REVERB:
@@ -758,7 +758,7 @@ int grafx_step_graph_create(grafx_plan* p, const float* sources, float* out, con
   // kernel attributes are set outside the capture
   DevCtx c0 = make_ctx(p, sources, out, nullptr, nullptr);
   launch_eq(-1, c0, 0, 0, s);
-  launch_comp(-1, c0, 0, 0, 0, 0, 0, s);
+  launch_comp(-1, c0, 0, 0, 0, 0, 0, 0, s);
   launch_delay(-1, c0, 0, 0, s);
   launch_reverb(-1, c0, 0, 0, s);
   launch_loss(-1, make_loss(p, out, target), s);

@@ -633,6 +633,142 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_back(DevCtx c, 
   cp_async_wait_all();
 }
 
+// Backward of small steps in one pass: the reverse recursion's state entering a chunk
+// comes from the chunks after it by a decoupled look-back (chunks handed out by an
+// atomic ticket from the end of each node; bounded waits record ST_TIMEOUT).  On steps
+// of few chunks the look-back chains stay short and one pass beats three.
+template <int SPT, int MODE>
+__global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_bwd_lb(DevCtx c, int item0, int n_items, int ticket) {
+  constexpr int CH = 256 * SPT;
+  constexpr bool GATE = MODE == MODE_GATE, SC = MODE == MODE_SC;
+  extern __shared__ __align__(16) float buf[];  // 4 * CH floats: prefetched u and ybar rows
+  __shared__ float sh[32];
+  __shared__ float glast[256];
+  __shared__ float red[4 * 32];
+  __shared__ int s_it[2];
+  __shared__ float s_lin;
+  if (threadIdx.x == 0) s_it[0] = atomicAdd(c.tickets + ticket, 1);
+  __syncthreads();
+  int it = s_it[0], slot = 0;
+  if (!SC && it < n_items) prefetch_item<SPT, true>(c, item0 + it, buf);
+  while (it < n_items) {
+    if (threadIdx.x == 0) s_it[slot ^ 1] = atomicAdd(c.tickets + ticket, 1);  // read after the scan's barriers
+    const int4_ w = c.items[item0 + it];
+    const int v = w.x, chunk = w.y;
+    const NodeDev nd = c.nodes[v];
+    const float* p = c.params + nd.prow * 4;
+    const float alpha = p[0];
+    const KneeCoef kq = knee_coef(p[1], p[2], p[3]);
+    const float la = logf(alpha);
+    const int t = chunk * CH + threadIdx.x * SPT;
+    const int n_chunks = (nd.len + CH - 1) / CH;
+    float ul[SPT], ur[SPT], bl[SPT], br[SPT], x[SPT], g[SPT], a[SPT];
+    float km[SC ? SPT : 1];   // sidechain: the key's mid l + r
+    cp_async_wait_all();
+    if constexpr (SC) {
+      float kr[SPT];
+      load_range<SPT>(c, c.csr_ptr[v], c.in1_begin[v], nd, t, ul, ur);      // main (input 0)
+      load_range<SPT>(c, c.in1_begin[v], c.csr_ptr[v + 1], nd, t, km, kr);  // key (input 1)
+      load_chunk<SPT>(c, v, nd, t, bl, br, true);
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) { km[i] += kr[i]; x[i] = km[i] * km[i]; }
+    } else {
+      fetch_rows<SPT>(c, v, nd, t, buf, ul, ur, false);
+      fetch_rows<SPT>(c, v, nd, t, buf + 2 * CH, bl, br, true);
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
+    }
+    // recompute the envelope from the stored chunk carry-in (same arithmetic as forward)
+    const float carry_g = c.comp_carry[w.z];
+    float b = 0.f;
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) b = alpha * b + (1.f - alpha) * x[i];
+    float total;
+    float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
+    const int next = s_it[slot ^ 1];
+    if (!SC && next < n_items) prefetch_item<SPT, true>(c, item0 + next, buf);
+    const float cin = excl + expf(la * float(SPT * threadIdx.x)) * carry_g;
+    envelope<SPT>(x, alpha, cin, g);
+    // local adjoints
+    float gain[SPT], gyb[SPT], dT = 0.f, dW = 0.f, dR = 0.f;
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) {
+      float gu = ln_env(g[i]);
+      Knee k = GATE ? gate_knee(gu, kq) : knee(gu, kq);
+      gain[i] = exp_gain(k.gy - gu);
+      float kbar = bl[i] * ul[i] + br[i] * ur[i];
+      gyb[i] = kbar * gain[i];
+      a[i] = env_div(gyb[i] * (k.dgu - 1.f), g[i] + COMP_EPS);
+      dT += gyb[i] * k.dt;
+      dW += gyb[i] * k.dw;
+      dR += gyb[i] * k.dr;
+    }
+    // reverse scan lambda[n] = a[n] + alpha lambda[n+1]
+    float lb = 0.f;
+#pragma unroll
+    for (int i = SPT - 1; i >= 0; --i) lb = a[i] + alpha * lb;
+    __syncthreads();  // sh reuse
+    float rtotal;
+    float rexcl = block_affine_scan<true>(lb, la * SPT, sh, &rtotal);
+    if (threadIdx.x < 32) {
+      float lin = 0.f;
+      if (chunk == n_chunks - 1) {
+        if (threadIdx.x == 0) publish(c, item0 + it, 2, rtotal);
+      } else {
+        if (threadIdx.x == 0) publish(c, item0 + it, 1, rtotal);
+        lin = look_back_warp(c, item0 + it - 1, item0 + it - (n_chunks - 1 - chunk), la * CH);
+        if (threadIdx.x == 0) publish(c, item0 + it, 2, expf(la * CH) * lin + rtotal);
+      }
+      if (threadIdx.x == 0) s_lin = lin;
+    }
+    glast[threadIdx.x] = g[SPT - 1];
+    __syncthreads();
+    // state entering this thread from the right: within-chunk part + the chunk carry
+    const float lin_t = rexcl + expf(la * float(SPT * (255 - threadIdx.x))) * s_lin;
+    float lam[SPT];
+    {
+      float s = lin_t;
+#pragma unroll
+      for (int i = SPT - 1; i >= 0; --i) {
+        s = a[i] + alpha * s;
+        lam[i] = s;
+      }
+    }
+    float gprev = threadIdx.x > 0 ? glast[threadIdx.x - 1] : carry_g;
+    float dA = 0.f;
+    if constexpr (SC) {
+      // input 0 (main): gain ybar; input 1 (key): 2 (k_l + k_r)(1 - alpha) lambda on both channels
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) {
+        dA += lam[i] * (gprev - x[i]);
+        gprev = g[i];
+        bl[i] *= gain[i];
+        br[i] *= gain[i];
+        km[i] = 2.f * km[i] * (1.f - alpha) * lam[i];
+      }
+      store_chunk<SPT>(arow_w(c, nd), nd, t, bl, br);
+      store_chunk<SPT>(arow_w(c, nd) + nd.rstride, nd, t, km, km);
+    } else {
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) {
+        dA += lam[i] * (gprev - x[i]);
+        gprev = g[i];
+        float xb2 = 2.f * (ul[i] + ur[i]) * (1.f - alpha) * lam[i];
+        bl[i] = gain[i] * bl[i] + xb2;
+        br[i] = gain[i] * br[i] + xb2;
+      }
+      store_chunk<SPT>(arow_w(c, nd), nd, t, bl, br);
+    }
+    float acc[4] = {dA, dT, dW, dR};
+    block_sum<4>(acc, red);
+    if (threadIdx.x == 0) c.partial[w.w] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    __syncthreads();
+    it = next;
+    slot ^= 1;
+  }
+  cp_async_wait_all();
+}
+
 __global__ void k_comp_finalize(DevCtx c, int node_begin, int node_end) {
   int v = node_begin + blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= node_end) return;
@@ -649,14 +785,18 @@ __global__ void k_comp_finalize(DevCtx c, int node_begin, int node_end) {
 // what: 0 forward (items [a, a + b), nodes [n0, n1)), 1 backward (the same), 2 finalize
 // (nodes [n0, n1)); mode: MODE_COMP, MODE_GATE (the noisegate curve of Eq. 13) or MODE_SC
 // (the sidechain compressor).  Returns the number of kernels launched.
+// Backward steps of at most this many chunks run the one-pass look-back kernel.
+constexpr int COMP_LOOKBACK_MAX_ITEMS = 8192;
+
 template <int SPT, int MODE>
-static int comp_launch(int what, const DevCtx& c, int a, int b, int n0, int n1, cudaStream_t s) {
+static int comp_launch(int what, const DevCtx& c, int a, int b, int n0, int n1, int ticket, cudaStream_t s) {
   constexpr int CH = 256 * SPT;
   constexpr int fwd_smem = 2 * CH * sizeof(float), bwd_smem = 4 * CH * sizeof(float);
   static bool init = false;
   if (!init) {   // first call (also the attributes-only call made before a stream capture)
     cudaFuncSetAttribute(k_comp_back<SPT, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem);
     cudaFuncSetAttribute(k_comp_back<SPT, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem);
+    cudaFuncSetAttribute(k_comp_bwd_lb<SPT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem);
     init = true;
   }
   if (what < 0) return 0;
@@ -665,6 +805,12 @@ static int comp_launch(int what, const DevCtx& c, int a, int b, int n0, int n1, 
     k_comp_agg<SPT, MODE><<<grid_size(b, 8), 256, fwd_smem, s>>>(c, a, b);
     k_comp_scan<false><<<scan_grid, 256, 0, s>>>(c, n0, n1, CH, c.comp_agg, c.comp_carry);
     k_comp_apply<SPT, MODE><<<grid_size(b, 8), 256, fwd_smem, s>>>(c, a, b);
+  } else if (b <= COMP_LOOKBACK_MAX_ITEMS) {
+    // the step's look-back words and its ticket start at zero
+    cudaMemsetAsync(c.flags + a, 0, sizeof(unsigned long long) * size_t(b), s);
+    cudaMemsetAsync(c.tickets + ticket, 0, sizeof(int32_t), s);
+    k_comp_bwd_lb<SPT, MODE><<<grid_size(b, 3), 256, bwd_smem, s>>>(c, a, b, ticket);
+    return 1;
   } else {
     k_comp_back<SPT, MODE, false><<<grid_size(b, 4), 256, bwd_smem, s>>>(c, a, b);
     k_comp_scan<true><<<scan_grid, 256, 0, s>>>(c, n0, n1, CH, c.comp_agg, c.comp_agg);
@@ -674,18 +820,18 @@ static int comp_launch(int what, const DevCtx& c, int a, int b, int n0, int n1, 
 }
 
 template <int SPT>
-static int comp_mode(int what, const DevCtx& c, int a, int b, int n0, int n1, int mode, cudaStream_t s) {
-  if (mode == MODE_GATE) return comp_launch<SPT, MODE_GATE>(what, c, a, b, n0, n1, s);
-  if (mode == MODE_SC) return comp_launch<SPT, MODE_SC>(what, c, a, b, n0, n1, s);
-  return comp_launch<SPT, MODE_COMP>(what, c, a, b, n0, n1, s);
+static int comp_mode(int what, const DevCtx& c, int a, int b, int n0, int n1, int ticket, int mode, cudaStream_t s) {
+  if (mode == MODE_GATE) return comp_launch<SPT, MODE_GATE>(what, c, a, b, n0, n1, ticket, s);
+  if (mode == MODE_SC) return comp_launch<SPT, MODE_SC>(what, c, a, b, n0, n1, ticket, s);
+  return comp_launch<SPT, MODE_COMP>(what, c, a, b, n0, n1, ticket, s);
 }
 
-int launch_comp(int what, const DevCtx& c, int a, int b, int n0, int n1, int mode, cudaStream_t s) {
+int launch_comp(int what, const DevCtx& c, int a, int b, int n0, int n1, int ticket, int mode, cudaStream_t s) {
   if (what < 0) {   // kernel attributes of every variant
     for (int m : {MODE_COMP, MODE_GATE, MODE_SC}) {
-      comp_mode<4>(-1, c, 0, 0, 0, 0, m, s);
-      comp_mode<8>(-1, c, 0, 0, 0, 0, m, s);
-      comp_mode<16>(-1, c, 0, 0, 0, 0, m, s);
+      comp_mode<4>(-1, c, 0, 0, 0, 0, 0, m, s);
+      comp_mode<8>(-1, c, 0, 0, 0, 0, 0, m, s);
+      comp_mode<16>(-1, c, 0, 0, 0, 0, 0, m, s);
     }
     return 0;
   }
@@ -695,9 +841,9 @@ int launch_comp(int what, const DevCtx& c, int a, int b, int n0, int n1, int mod
     return 1;
   }
   if (b <= 0) return 0;
-  if (c.comp_chunk == 1024) return comp_mode<4>(what, c, a, b, n0, n1, mode, s);
-  if (c.comp_chunk == 4096) return comp_mode<16>(what, c, a, b, n0, n1, mode, s);
-  return comp_mode<8>(what, c, a, b, n0, n1, mode, s);
+  if (c.comp_chunk == 1024) return comp_mode<4>(what, c, a, b, n0, n1, ticket, mode, s);
+  if (c.comp_chunk == 4096) return comp_mode<16>(what, c, a, b, n0, n1, ticket, mode, s);
+  return comp_mode<8>(what, c, a, b, n0, n1, ticket, mode, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -27,7 +27,7 @@ int launch_eq(int what, const DevCtx& c, int a, int b, cudaStream_t s);  // what
 // compressor, noisegate and sidechain compressor (mode 0, 1, 2): what = 0 forward,
 // 1 backward (a = item0, b = n_items, ticket index), 2 gradient finalize (a = node_begin,
 // b = node_end)
-int launch_comp(int what, const DevCtx& c, int a, int b, int n0, int n1, int mode, cudaStream_t s);
+int launch_comp(int what, const DevCtx& c, int a, int b, int n0, int n1, int ticket, int mode, cudaStream_t s);
 
 // delay: what = 0 design (node range), 1 forward (items), 2 input adjoint, 3 block
 // spectra, 4 partition accumulation, 5 lags (inverse FFTs), 6 gradients; < 0 attributes

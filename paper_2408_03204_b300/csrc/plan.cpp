@@ -727,7 +727,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     // cleared at the start of every render / backprop
     w.status = take(16);
     w.tickets = take(4 * size_t(2 * (N + 2)));
-    w.flags = take(8);   // no kernel of the render path waits on another (the compressor scans in passes)
+    w.flags = take(8 * std::max<size_t>(p->items.size(), 1));   // look-back words of small compressor steps
     w.flags_bytes = o - w.status;
     w.eq_spec = take(4 * size_t(std::max(p->n_eq, 1)) * (p->eq_fft / 2 + 4));   // 16-byte aligned rows
     w.eq_aux = take(4 * size_t(std::max(p->n_eq, 1)) * 1024);
