@@ -15,6 +15,7 @@
 // Every product runs on the 5th-generation tensor cores (tcgen05.mma, FP32 accumulator
 // in tensor memory) with BF16 operands, rounded (nearest even) as they are staged into
 // shared memory; activations, gradients and weights stay FP32 in HBM.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -54,8 +55,16 @@ struct GemmArgs {
   float* C;
   int64_t ldc;
   float alpha, beta;
-  float* part;  // split-K partials or null
+  float* part;   // split-K partials or null
+  int perm_cin;  // > 0: product column n = tap * perm_cin + c is stored at column c * WS_KW + tap
 };
+
+// stored column of product column n
+__device__ __forceinline__ int out_col(const GemmArgs& g, int n) {
+  if (g.perm_cin <= 0) return n;
+  const int tap = n / g.perm_cin;
+  return (n - tap * g.perm_cin) * WS_KW + tap;
+}
 
 // ------------------------------------------------------------------ tcgen05 GEMM
 // The same product on the 5th-generation tensor cores: a 128 x 128 FP32 accumulator
@@ -222,6 +231,70 @@ __device__ __forceinline__ void tc_store(char* tile, const uint32_t (&v)[TC_V]) 
   }
 }
 
+// Epilogue of a 128 x 128 tile: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows),
+// columns 64 (w / 4) .. + 63, 16 per tcgen05.ld, into a padded FP32 tile at `base` (the
+// idle operand stages); then every warp writes whole rows (coalesced float4) with
+// alpha/beta, or the split-K partial tile (blockIdx.z).  have = false: the tile is zero
+// (an empty k range).  ok = false: nothing is stored.
+__device__ __forceinline__ void tc_epilogue(const GemmArgs& g, uint32_t tmem, char* base, int m0, int n0, bool have,
+                                            bool ok) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quarter = warp & 3, half = warp >> 2;
+  float* E = reinterpret_cast<float*>(base);
+  {
+    const int row = quarter * 32 + lane;
+#pragma unroll 1
+    for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
+      uint32_t r[16];
+      const uint32_t taddr = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(c0);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 16; j += 4)
+        *reinterpret_cast<float4*>(E + row * TC_EPI_LD + c0 + j) =
+            have ? make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                               __uint_as_float(r[j + 3]))
+                 : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  if (!ok) return;
+  float* part = g.part ? g.part + int64_t(blockIdx.z) * g.M * g.N : nullptr;
+  float* dst = part ? part : g.C;
+  const int64_t ld = part ? g.N : g.ldc;
+  const bool perm = !part && g.perm_cin > 0;
+  const bool vec = !perm && (ld % 4) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+  const float alpha = part ? 1.f : g.alpha, beta = part ? 0.f : g.beta;
+  const int qd = threadIdx.x & 31;  // float4 column of the row
+#pragma unroll 1
+  for (int rr = threadIdx.x >> 5; rr < TC_M; rr += TC_THREADS / 32) {
+    const int m = m0 + rr, n = n0 + 4 * qd;
+    if (m >= g.M || n >= g.N) continue;
+    const float4 v = *reinterpret_cast<const float4*>(E + rr * TC_EPI_LD + 4 * qd);
+    float* cp = dst + int64_t(m) * ld;
+    if (vec && n + 3 < g.N) {
+      float4 o = make_float4(alpha * v.x, alpha * v.y, alpha * v.z, alpha * v.w);
+      if (beta != 0.f) {
+        const float4 c = *reinterpret_cast<const float4*>(cp + n);
+        o.x += beta * c.x, o.y += beta * c.y, o.z += beta * c.z, o.w += beta * c.w;
+      }
+      *reinterpret_cast<float4*>(cp + n) = o;
+    } else {
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (n + j < g.N) {
+          float* q = cp + (perm ? out_col(g, n + j) : n + j);
+          *q = alpha * vv[j] + (beta != 0.f ? beta * *q : 0.f);
+        }
+    }
+  }
+}
+
 template <int AM, int BM>
 __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(GemmArgs g, uint32_t* status) {
   extern __shared__ __align__(1024) char tc_smem_raw[];
@@ -231,7 +304,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(GemmArgs g, uint32_t* st
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + TC_M * TC_EPI_LD * 4);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
   const uint32_t bar0 = static_cast<uint32_t>(__cvta_generic_to_shared(bars));  // bar of stage st: bar0 + 8 st
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TC_N;
   const int kbeg = blockIdx.z * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
   const int ntiles = max(0, (kend - kbeg + TC_K - 1) / TC_K);
@@ -305,74 +378,205 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(GemmArgs g, uint32_t* st
   if (!ok && threadIdx.x == 0 && status) atomicOr(status, GEMM_TIMEOUT);
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
-  // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows), columns 64 (w / 4)
-  // .. + 63, 16 per tcgen05.ld, into a padded FP32 tile in the (now idle) operand
-  // stages; then every warp writes whole rows (coalesced float4).
-  const int quarter = warp & 3, half = warp >> 2;
-  float* E = reinterpret_cast<float*>(base);
-  {
-    const int row = quarter * 32 + lane;
-#pragma unroll 1
-    for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
-      uint32_t r[16];
-      const uint32_t taddr = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(c0);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-      for (int j = 0; j < 16; j += 4)
-        *reinterpret_cast<float4*>(E + row * TC_EPI_LD + c0 + j) =
-            ntiles > 0 ? make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
-                                     __uint_as_float(r[j + 3]))
-                       : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-  }
-  __syncthreads();
-  if (ok) {
-    float* part = g.part ? g.part + int64_t(blockIdx.z) * g.M * g.N : nullptr;
-    float* dst = part ? part : g.C;
-    const int64_t ld = part ? g.N : g.ldc;
-    const bool vec = (ld % 4) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
-    const float alpha = part ? 1.f : g.alpha, beta = part ? 0.f : g.beta;
-    const int qd = threadIdx.x & 31;  // float4 column of the row
-#pragma unroll 1
-    for (int rr = threadIdx.x >> 5; rr < TC_M; rr += TC_THREADS / 32) {
-      const int m = m0 + rr, n = n0 + 4 * qd;
-      if (m >= g.M || n >= g.N) continue;
-      const float4 v = *reinterpret_cast<const float4*>(E + rr * TC_EPI_LD + 4 * qd);
-      float* cp = dst + int64_t(m) * ld + n;
-      if (vec && n + 3 < g.N) {
-        float4 o = make_float4(alpha * v.x, alpha * v.y, alpha * v.z, alpha * v.w);
-        if (beta != 0.f) {
-          const float4 c = *reinterpret_cast<const float4*>(cp);
-          o.x += beta * c.x, o.y += beta * c.y, o.z += beta * c.z, o.w += beta * c.w;
-        }
-        *reinterpret_cast<float4*>(cp) = o;
-      } else {
-        const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (n + j < g.N) cp[j] = alpha * vv[j] + (beta != 0.f ? beta * cp[j] : 0.f);
-      }
-    }
-  }
+  tc_epilogue(g, tmem, base, m0, n0, ntiles > 0, ok);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(TC_TMEM_COLS) : "memory");
 }
 
-// C = alpha * sum_z part[z] + beta * C, z in order
-__global__ void k_gemm_reduce(const float* __restrict__ part, int splits, int M, int N, float* __restrict__ C,
-                              int64_t ldc, float alpha, float beta) {
+// ------------------------------------------------------------------ TMA-fed conv products
+// The conv layers' products as implicit GEMMs whose operand tiles are copied by the
+// tensor memory accelerator (cp.async.bulk.tensor, 128-byte swizzle) straight from the
+// BF16 activations, gradients and weight copies; no im2col or col2im matrix exists.
+// Product index k (or n) = tap * cin + c for a tap 0..4 of the kernel and channel c, and
+// a row is (sample b, frame t).  Operand tile modes (128 rows x 64 k):
+//   TM_K2  K-major, 2-D map over X[rows][K]: one box {64, 128} at (k0, r0).
+//   TM_K3  K-major, 3-D map over activations X[B][T][cin] (box {64, 32, 4}): tile row
+//          (b, t) holds X[b][t + sign (tap - 2)][c0 .. c0 + 63] for k0 = tap cin + c0;
+//          frames outside 0..T-1 and samples past B arrive as zeros (the conv's 'same'
+//          zero padding).
+//   TM_N2  MN-major, 2-D map over X[K][MN] (box {64, 64}): two boxes, rows r0 and r0 + 64.
+//   TM_N3  MN-major, 3-D map over activations X[B][T][cin] (box {64, 32, 2}) with the tap
+//          taken from the tile's rows: r0 = tap cin + c0, k0 = 32 b0 (two boxes, c0 and
+//          c0 + 64).
+// MN-major tiles hold 64 k-rows of 64 MN elements (128 B) per box, the boxes 8 KB apart:
+// the descriptor's leading offset is that 8 KB (MN direction), its stride offset the
+// 1 KB between groups of 8 k-rows.
+enum : int { TM_K2 = 0, TM_K3 = 1, TM_N2 = 2, TM_N3 = 3 };
+struct TmaGeom {
+  int a_cin, a_sign, b_cin, b_sign;
+};
+constexpr int TM_STAGES = 3;
+constexpr int TM_STAGE_BYTES = 2 * TC_TILE_BYTES;
+constexpr int TM_BAR_BYTES = 8 * (2 * TM_STAGES + 1) + 16;
+constexpr int TM_SMEM = TM_STAGES * TM_STAGE_BYTES + 1024 + TM_BAR_BYTES;
+static_assert(TM_STAGES * TM_STAGE_BYTES >= TC_M * TC_EPI_LD * 4, "epilogue tile covers the operand stages");
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* m, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* m, uint32_t bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];\n" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+// one 128 x 64 operand tile (rows r0.., k0..) into dst, completing on bar
+template <int MODE>
+__device__ __forceinline__ void tma_tile(const CUtensorMap* m, uint32_t dst, uint32_t bar, int r0, int k0, int cin,
+                                         int sign) {
+  if constexpr (MODE == TM_K2) {
+    tma_load_2d(dst, m, bar, k0, r0);
+  } else if constexpr (MODE == TM_K3) {
+    const int tap = k0 / cin;
+    tma_load_3d(dst, m, bar, k0 - tap * cin, sign * (tap - 2), r0 / WS_T);
+  } else if constexpr (MODE == TM_N2) {
+    tma_load_2d(dst, m, bar, r0, k0);
+    tma_load_2d(dst + TC_TILE_BYTES / 2, m, bar, r0 + 64, k0);
+  } else {
+    const int tap = r0 / cin, c0 = r0 - tap * cin;
+    tma_load_3d(dst, m, bar, c0, sign * (tap - 2), k0 / WS_T);
+    tma_load_3d(dst + TC_TILE_BYTES / 2, m, bar, c0 + 64, sign * (tap - 2), k0 / WS_T);
+  }
+}
+
+// descriptor of the K = 16 slice j of a tile in mode MODE
+template <int MODE>
+__device__ __forceinline__ uint64_t tm_desc(uint32_t tile, int j) {
+  if constexpr (MODE == TM_K2 || MODE == TM_K3) {
+    return umma_desc(tile + 32u * j);
+  } else {  // MN-major: LBO 8192 B between the 64-element halves, SBO 1024 B between 8-k groups
+    const uint32_t a = tile + 2048u * j;
+    return uint64_t((a >> 4) & 0x3FFFu) | (uint64_t(8192 >> 4) << 16) | (uint64_t(1024 >> 4) << 32) |
+           (uint64_t(1) << 46) | (uint64_t(2) << 61);
+  }
+}
+
+// Warp 0 lane 0 issues the copies of k-tile kt into stage kt mod 3 once the MMAs of
+// k-tile kt - 3 have released it (an mbarrier signalled by tcgen05.commit); warp 1 lane 0
+// waits for each stage's bytes (expect_tx on the stage's full barrier) and issues its
+// four MMAs; all 8 warps run the epilogue.  Every wait is bounded: on expiry the issuing
+// stops, the CTA waits (bounded) for the MMAs and copies it started, records
+// GEMM_TIMEOUT, frees its TMEM and stores nothing.
+template <int AM, int BM>
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tma(const __grid_constant__ CUtensorMap ta,
+                                                         const __grid_constant__ CUtensorMap tb, GemmArgs g,
+                                                         TmaGeom geo, uint32_t* status) {
+  extern __shared__ __align__(1024) char tm_smem_raw[];
+  char* base = tm_smem_raw + ((1024 - (reinterpret_cast<uintptr_t>(tm_smem_raw) & 1023)) & 1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + TM_STAGES * TM_STAGE_BYTES);  // full[3], empty[3], done
+  int* info = reinterpret_cast<int*>(bars + 2 * TM_STAGES + 1);  // tmem address, copies issued, tiles consumed
+  const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(base));
+  const uint32_t full0 = static_cast<uint32_t>(__cvta_generic_to_shared(bars));
+  const uint32_t empty0 = full0 + 8 * TM_STAGES, done = full0 + 16 * TM_STAGES;
+  const int warp = threadIdx.x >> 5;
+  const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TC_N;
+  const int kbeg = blockIdx.z * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
+  const int ntiles = max(0, (kend - kbeg + TC_K - 1) / TC_K);
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2 * TM_STAGES + 1; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full0 + 8 * i) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    info[1] = 0;
+    info[2] = 0;
+  }
+  if (warp == 0) {  // TMEM columns for the 128 x 128 FP32 accumulator
+    const uint32_t slot = static_cast<uint32_t>(__cvta_generic_to_shared(info));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot), "n"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = static_cast<uint32_t>(info[0]);
+
+  bool ok = true;
+  if (threadIdx.x == 0) {  // copies
+    asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&ta)) : "memory");
+    asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tb)) : "memory");
+    int kt = 0;
+    for (; kt < ntiles; ++kt) {
+      const int st = kt % TM_STAGES;
+      if (kt >= TM_STAGES && !mbar_wait(empty0 + 8 * st, uint32_t((kt / TM_STAGES - 1) & 1))) {
+        ok = false;
+        break;
+      }
+      const uint32_t fb = full0 + 8 * st, tA = sbase + st * TM_STAGE_BYTES;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "n"(TM_STAGE_BYTES)
+                   : "memory");
+      const int k0 = kbeg + kt * TC_K;
+      tma_tile<AM>(&ta, tA, fb, m0, k0, geo.a_cin, geo.a_sign);
+      tma_tile<BM>(&tb, tA + TC_TILE_BYTES, fb, n0, k0, geo.b_cin, geo.b_sign);
+    }
+    info[1] = kt;
+  } else if (threadIdx.x == 32) {  // MMAs
+    constexpr uint32_t idesc = TC_IDESC | (AM >= TM_N2 ? (1u << 15) : 0u) | (BM >= TM_N2 ? (1u << 16) : 0u);
+    int kt = 0;
+    for (; kt < ntiles; ++kt) {
+      const int st = kt % TM_STAGES;
+      if (!mbar_wait(full0 + 8 * st, uint32_t((kt / TM_STAGES) & 1))) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t tA = sbase + st * TM_STAGE_BYTES, tB = tA + TC_TILE_BYTES;
+#pragma unroll
+      for (int j = 0; j < TC_K / 16; ++j) {
+        const uint64_t ad = tm_desc<AM>(tA, j), bd = tm_desc<BM>(tB, j);
+        const uint32_t acc = (kt > 0 || j > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       empty0 + 8 * st)
+                   : "memory");
+    }
+    // one more commit: arrives once every MMA issued above has completed
+    if (ntiles > 0)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(done)
+                   : "memory");
+    info[2] = kt;
+  }
+  __syncwarp();
+  ok = __syncthreads_and(ok) != 0;
+  const int issued = info[1], consumed = info[2];
+  if (ntiles > 0) ok = (__syncthreads_and(mbar_wait(done, 0u)) != 0) && ok;
+  if (threadIdx.x == 0)  // copies that were issued but never consumed (after an expiry)
+    for (int kt = consumed; kt < issued; ++kt)
+      if (!mbar_wait(full0 + 8 * (kt % TM_STAGES), uint32_t((kt / TM_STAGES) & 1))) ok = false;
+  ok = __syncthreads_and(ok) != 0;
+  if (!ok && threadIdx.x == 0 && status) atomicOr(status, GEMM_TIMEOUT);
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  tc_epilogue(g, tmem, base, m0, n0, ntiles > 0, ok);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(TC_TMEM_COLS) : "memory");
+}
+
+// C = alpha * sum_z part[z] + beta * C, z in order (columns through out_col)
+__global__ void k_gemm_reduce(const float* __restrict__ part, int splits, GemmArgs g) {
+  const int M = g.M, N = g.N;
+  const int64_t ldc = g.ldc;
+  const float alpha = g.alpha, beta = g.beta;
+  float* __restrict__ C = g.C;
   const int64_t MN = int64_t(M) * N;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < MN; i += int64_t(gridDim.x) * blockDim.x) {
     float s = 0.f;
     for (int z = 0; z < splits; ++z) s += part[z * MN + i];
-    float* cp = C + (i / N) * ldc + i % N;
+    float* cp = C + (i / N) * ldc + out_col(g, int(i % N));
     *cp = alpha * s + (beta != 0.f ? beta * *cp : 0.f);
   }
 }
@@ -419,7 +623,7 @@ static int gemm(int M, int N, int K, const void* A, int64_t sam, int64_t sak, co
                  float* scratch = nullptr, int64_t scratch_floats = 0, uint32_t* status = nullptr,
                  bool a_bf16 = false, bool b_bf16 = false) {
   if (M <= 0 || N <= 0) return GRAFX_OK;
-  GemmArgs a{M, N, K, 0, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta, nullptr};
+  GemmArgs a{M, N, K, 0, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta, nullptr, 0};
   const int tm = (M + TC_M - 1) / TC_M, tn = (N + TC_N - 1) / TC_N;
   const int ktiles = std::max(1, (K + TC_K - 1) / TC_K);
   int splits = 1;
@@ -445,8 +649,100 @@ static int gemm(int M, int N, int K, const void* A, int64_t sam, int64_t sak, co
   }
   if (splits > 1) {
     const int64_t MN = int64_t(M) * N;
-    k_gemm_reduce<<<int(std::min<int64_t>((MN + 255) / 256, 148 * 8)), 256, 0, s>>>(scratch, splits, M, N, C, ldc,
-                                                                                     alpha, beta);
+    k_gemm_reduce<<<int(std::min<int64_t>((MN + 255) / 256, 148 * 8)), 256, 0, s>>>(scratch, splits, a);
+  }
+  return GRAFX_OK;
+}
+
+// ------------------------------------------------------------------ TMA product launch
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// Tensor map of a dense BF16 tensor (dims innermost first, rank 2 or 3) read in boxes
+// `box` with 128-byte swizzle; elements outside the tensor arrive as zeros.  The base
+// must be 16-byte aligned and every row a multiple of 16 bytes (the encoder checks both).
+static int bf16_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint32_t* box) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return fail(GRAFX_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  cuuint64_t gd[3], gs[2];
+  cuuint32_t bx[3], es[3] = {1, 1, 1};
+  uint64_t stride = 2;
+  for (int i = 0; i < rank; ++i) {
+    gd[i] = dims[i];
+    bx[i] = box[i];
+    if (i > 0) gs[i - 1] = stride;
+    stride *= dims[i];
+  }
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, cuuint32_t(rank), const_cast<void*>(base), gd, gs, bx, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? GRAFX_OK : fail(GRAFX_ECUDA, "cuTensorMapEncodeTiled rejected a tensor map");
+}
+
+// X[rows][K], K-major boxes {64, 128}
+static int map_k2(CUtensorMap* m, const __nv_bfloat16* X, int64_t rows, int64_t K) {
+  const uint64_t d[2] = {uint64_t(K), uint64_t(rows)};
+  const uint32_t bx[2] = {TC_K, TC_M};
+  return bf16_map(m, X, 2, d, bx);
+}
+// X[K][MN], MN-major boxes {64, 64}
+static int map_n2(CUtensorMap* m, const __nv_bfloat16* X, int64_t K, int64_t MN) {
+  const uint64_t d[2] = {uint64_t(MN), uint64_t(K)};
+  const uint32_t bx[2] = {64, 64};
+  return bf16_map(m, X, 2, d, bx);
+}
+// activations X[B][T][C], boxes {64, T, samples}: 4 samples (TM_K3) or 2 (TM_N3)
+static int map_act(CUtensorMap* m, const __nv_bfloat16* X, int B, int C, int samples) {
+  const uint64_t d[3] = {uint64_t(C), uint64_t(WS_T), uint64_t(B)};
+  const uint32_t bx[3] = {64, WS_T, uint32_t(samples)};
+  return bf16_map(m, X, 3, d, bx);
+}
+
+// C[M][N] = A B (stored through perm_cin) with TMA-fed operand tiles.  Products with
+// fewer than 100 output tiles split K (partial tiles in scratch, at least 4 k-tiles a
+// split) so that about one CTA runs per SM; the partials are summed in order.
+template <int AM, int BM>
+static int gemm_tma(int M, int N, int K, const CUtensorMap& ta, const CUtensorMap& tb, TmaGeom geo, float* C,
+                    int64_t ldc, int perm_cin, float* scratch, int64_t scratch_floats, uint32_t* status,
+                    cudaStream_t s) {
+  if (M <= 0 || N <= 0) return GRAFX_OK;
+  GemmArgs a{M, N, K, 0, nullptr, 0, 0, nullptr, 0, 0, C, ldc, 1.f, 0.f, nullptr, perm_cin};
+  const int tm = (M + TC_M - 1) / TC_M, tn = (N + TC_N - 1) / TC_N;
+  const int ktiles = std::max(1, (K + TC_K - 1) / TC_K);
+  int splits = 1;
+  if (scratch && tm * tn < 100 && ktiles >= 8) {
+    splits = std::min((148 + tm * tn - 1) / (tm * tn), ktiles / 4);
+    splits = int(std::min<int64_t>(splits, scratch_floats / (int64_t(M) * N)));
+    splits = std::max(splits, 1);
+  }
+  const int kt_per = (ktiles + splits - 1) / splits;
+  a.kchunk = kt_per * TC_K;
+  splits = (ktiles + kt_per - 1) / kt_per;
+  if (splits > 1) a.part = scratch;
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(k_gemm_tma<AM, BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, TM_SMEM);
+    init = true;
+  }
+  k_gemm_tma<AM, BM><<<dim3(tn, tm, splits), TC_THREADS, TM_SMEM, s>>>(ta, tb, a, geo, status);
+  if (splits > 1) {
+    const int64_t MN = int64_t(M) * N;
+    k_gemm_reduce<<<int(std::min<int64_t>((MN + 255) / 256, 148 * 8)), 256, 0, s>>>(scratch, splits, a);
   }
   return GRAFX_OK;
 }
@@ -457,53 +753,31 @@ __device__ __forceinline__ float gelu_d(float x) {
   return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
 }
 
-// im2col: A[(b,t)][(c,k)] = H(b, c, t+k-2), zero outside [0, T), stored as BF16 (the
-// products round their operands to BF16 anyway).  H is [B][T][C] (time-major
-// activations) or, for the features, [B][C][T] (feat_layout = 1).  One thread per
-// (b, t, c) writes its 5 taps.
-__global__ void k_im2col(const float* __restrict__ H, int B, int C, int feat_layout, __nv_bfloat16* __restrict__ A) {
-  const int n = B * WS_T * C;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int c = i % C, bt = i / C, t = bt % WS_T, b = bt / WS_T;
-    __nv_bfloat16* o = A + int64_t(i) * WS_KW;
-#pragma unroll
-    for (int k = 0; k < WS_KW; ++k) {
-      const int ts = t + k - 2;
-      float v = 0.f;
-      if (ts >= 0 && ts < WS_T) v = feat_layout ? H[(b * C + c) * WS_T + ts] : H[(b * WS_T + ts) * C + c];
-      o[k] = __float2bfloat16_rn(v);
-    }
-  }
-}
-
-// dH[(b,t)][c] = sum_k dA[(b, t-k+2)][(c,k)]  (adjoint of k_im2col, time-major)
-__global__ void k_col2im(const float* __restrict__ dA, int B, int C, float* __restrict__ dH) {
-  const int64_t n = int64_t(B) * WS_T * C;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const int c = int(i % C);
-    const int64_t bt = i / C;
-    const int t = int(bt % WS_T), b = int(bt / WS_T);
-    float s = 0.f;
-#pragma unroll
-    for (int k = 0; k < WS_KW; ++k) {
-      const int tt = t - k + 2;
-      if (tt >= 0 && tt < WS_T) s += dA[((int64_t(b) * WS_T + tt) * C + c) * WS_KW + k];
-    }
-    dH[i] = s;
-  }
-}
-
-// z[r][c] += bias[c]; h = gelu(z) (or a copy without GELU); rows x cols with row stride ld
+// z[r][c] += bias[c]; h = gelu(z) (or a copy without GELU); rows x cols with row stride
+// ld; hb (if given): h as BF16, the next product's operand
 __global__ void k_bias_act(float* __restrict__ z, const float* __restrict__ bias, float* __restrict__ h, int64_t rows,
-                           int cols, int64_t ld, int apply_gelu) {
+                           int cols, int64_t ld, int apply_gelu, __nv_bfloat16* __restrict__ hb = nullptr) {
   const int64_t n = rows * cols;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const int64_t r = i / cols;
     const int c = int(i % cols);
     const float v = z[r * ld + c] + bias[c];
     z[r * ld + c] = v;
-    if (h) h[r * ld + c] = apply_gelu ? gelu(v) : v;
+    const float a = apply_gelu ? gelu(v) : v;
+    if (h) h[r * ld + c] = a;
+    if (hb) hb[r * ld + c] = __float2bfloat16_rn(a);
   }
+}
+
+// Features [B][256][32] (float32) to the first conv's operand [B][32][256] (BF16): one
+// CTA per sample, transposed through shared memory.
+__global__ void __launch_bounds__(256) k_feat_bf16(const float* __restrict__ f, __nv_bfloat16* __restrict__ fb) {
+  __shared__ float tile[WS_IN][WS_T + 1];
+  const float* src = f + int64_t(blockIdx.x) * WS_IN * WS_T;
+  for (int i = threadIdx.x; i < WS_IN * WS_T; i += 256) tile[i / WS_T][i % WS_T] = src[i];
+  __syncthreads();
+  __nv_bfloat16* dst = fb + int64_t(blockIdx.x) * WS_IN * WS_T;
+  for (int i = threadIdx.x; i < WS_IN * WS_T; i += 256) dst[i] = __float2bfloat16_rn(tile[i % WS_IN][i / WS_IN]);
 }
 
 // d *= gelu'(z); with db also a BF16 copy of the result (the products' operand)
@@ -598,15 +872,33 @@ __global__ void __launch_bounds__(1024) k_ws_mse(const float* __restrict__ out, 
 
 // BF16 copies of the weight matrices, each at a 16-byte aligned offset of the shadow
 // buffer (the products read them as 8-element BF16 loads)
-constexpr int WB_MATS = 4 + 3 * WS_NHEAD;
+// BF16 weight copies: conv layer l tap-major (0..3), per head w1, w2, w3 (4..21), conv
+// layer l = 1..3 transposed tap-major (22..24)
+constexpr int WB_MATS = 4 + 3 * WS_NHEAD + 3;
+constexpr int WB_CONVT = 4 + 3 * WS_NHEAD;
+enum : int { WC_PLAIN = 0, WC_TAPS = 1, WC_TAPS_T = 2 };
 struct WeightCopies {
   int64_t src[WB_MATS], dst[WB_MATS], n[WB_MATS];
+  int32_t mode[WB_MATS], cin[WB_MATS];
 };
 
+// Copy j of the weights as BF16.  WC_TAPS: conv w [128][cin][5] as [128][5][cin] (the
+// product index tap * cin + c of the TMA-fed products); WC_TAPS_T: as [cin][5][128].
 __global__ void k_weights_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, WeightCopies cp) {
-  const int j = blockIdx.y;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < cp.n[j]; i += int64_t(gridDim.x) * blockDim.x)
-    wb[cp.dst[j] + i] = __float2bfloat16_rn(w[cp.src[j] + i]);
+  const int j = blockIdx.y, mode = cp.mode[j], cin = cp.cin[j];
+  const float* src = w + cp.src[j];
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < cp.n[j]; i += int64_t(gridDim.x) * blockDim.x) {
+    int64_t q = i;
+    if (mode == WC_TAPS) {
+      const int K = cin * WS_KW;
+      const int o = int(i / K), k = int(i % K), tap = k / cin, c = k % cin;
+      q = int64_t(o) * K + c * WS_KW + tap;
+    } else if (mode == WC_TAPS_T) {
+      const int c = int(i / (WS_KW * WS_CH)), k = int(i % (WS_KW * WS_CH)), tap = k / WS_CH, o = k % WS_CH;
+      q = int64_t(o) * cin * WS_KW + c * WS_KW + tap;
+    }
+    wb[cp.dst[j] + i] = __float2bfloat16_rn(src[q]);
+  }
 }
 
 // ------------------------------------------------------------------ log-mel features
@@ -774,7 +1066,7 @@ struct grafx_wsnet {
   int64_t off[4][2];          // conv weight / bias offsets in the flat buffer
   int64_t hoff[WS_NHEAD][6];  // per head: w1 b1 w2 b2 w3 b3
   int64_t n_params = 0;
-  WeightCopies wcp;           // BF16 shadow: conv w (4), then per head w1, w2, w3
+  WeightCopies wcp;           // BF16 shadows of the weights (k_weights_bf16)
   int64_t wb_elems = 0;
   int32_t max_batch = 0;
   char* ws = nullptr;         // bound workspace
@@ -786,9 +1078,12 @@ struct grafx_wsnet {
 
 namespace {
 
+// split-K partials of the weight-gradient products: up to 32 partial [128][1280] tiles
+constexpr int64_t WS_DBIG_FLOATS = int64_t(32) * WS_CH * WS_IN * WS_KW;
+
 struct WsNetLayout {
   size_t melw, melrng, tw, ptw, status;
-  size_t im2col, z[4], h[4], e, a1, g1, a2, g2, dbig, dsmall, dh, dzb, cspart, wbf, frames, total;
+  size_t fb, hb[3], z[4], h3, e, a1, g1, a2, g2, dbig, dsmall, dh, dzb, cspart, wbf, frames, total;
 };
 
 // frame_floats: log-mel frame scratch (rows x frames x 128) in floats
@@ -806,17 +1101,16 @@ WsNetLayout ws_layout(const grafx_wsnet* n, int64_t frame_floats) {
   L.tw = take(sizeof(float2_) * n->tw.size());
   L.ptw = take(sizeof(float2_) * n->ptw.size());
   L.status = take(sizeof(uint32_t));
-  L.im2col = take(4 * rows * WS_IN * WS_KW);
-  for (int l = 0; l < 4; ++l) {
-    L.z[l] = take(4 * rows * WS_CH);
-    L.h[l] = take(4 * rows * WS_CH);
-  }
+  L.fb = take(2 * rows * WS_IN);
+  for (int l = 0; l < 3; ++l) L.hb[l] = take(2 * rows * WS_CH);
+  for (int l = 0; l < 4; ++l) L.z[l] = take(4 * rows * WS_CH);
+  L.h3 = take(4 * rows * WS_CH);
   L.e = take(4 * B * WS_CH);
   L.a1 = take(4 * B * WS_HID);
   L.g1 = take(4 * B * WS_HID);
   L.a2 = take(4 * B * WS_HID);
   L.g2 = take(4 * B * WS_HID);
-  L.dbig = take(4 * rows * WS_CH * WS_KW);
+  L.dbig = take(4 * size_t(WS_DBIG_FLOATS));
   L.dsmall = take(4 * B * WS_HID * 2);
   L.dh = take(4 * (B * WS_CH + rows * WS_CH));
   L.dzb = take(2 * rows * WS_CH);
@@ -876,18 +1170,22 @@ int grafx_ws_create(int32_t max_batch, int32_t sample_rate, grafx_wsnet** out) {
   n->n_params = o;
   {
     int64_t d = 0;
-    auto add = [&](int j, int64_t src, int64_t cnt) {
+    auto add = [&](int j, int64_t src, int64_t cnt, int mode, int ci) {
       n->wcp.src[j] = src;
       n->wcp.dst[j] = d;
       n->wcp.n[j] = cnt;
-      d += (cnt + 7) / 8 * 8;
+      n->wcp.mode[j] = mode;
+      n->wcp.cin[j] = ci;
+      d += (cnt + 63) / 64 * 64;  // 128-byte aligned copies (tensor-map bases)
     };
-    for (int l = 0; l < 4; ++l) add(l, n->off[l][0], int64_t(WS_CH) * cin[l] * WS_KW);
+    for (int l = 0; l < 4; ++l) add(l, n->off[l][0], int64_t(WS_CH) * cin[l] * WS_KW, WC_TAPS, cin[l]);
     for (int h = 0; h < WS_NHEAD; ++h) {
-      add(4 + 3 * h, n->hoff[h][0], int64_t(WS_HID) * WS_CH);
-      add(5 + 3 * h, n->hoff[h][2], int64_t(WS_HID) * WS_HID);
-      add(6 + 3 * h, n->hoff[h][4], int64_t(kHeadOut[h]) * WS_HID);
+      add(4 + 3 * h, n->hoff[h][0], int64_t(WS_HID) * WS_CH, WC_PLAIN, 0);
+      add(5 + 3 * h, n->hoff[h][2], int64_t(WS_HID) * WS_HID, WC_PLAIN, 0);
+      add(6 + 3 * h, n->hoff[h][4], int64_t(kHeadOut[h]) * WS_HID, WC_PLAIN, 0);
     }
+    for (int l = 1; l < 4; ++l)
+      add(WB_CONVT + l - 1, n->off[l][0], int64_t(WS_CH) * cin[l] * WS_KW, WC_TAPS_T, cin[l]);
     n->wb_elems = d;
   }
   // HTK-mel triangles over the one-sided bins of a 2048-point frame, edges equally
@@ -1015,23 +1313,27 @@ int grafx_ws_forward(grafx_wsnet* n, const float* weights, const float* feats, c
   uint32_t* st = reinterpret_cast<uint32_t*>(n->ws + L.status);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int rows = B * WS_T;
-  const int64_t dbig_floats = int64_t(n->max_batch) * WS_T * WS_CH * WS_KW;
   const int cin[4] = {WS_IN, WS_CH, WS_CH, WS_CH};
+  auto BF = [&](size_t off) { return reinterpret_cast<__nv_bfloat16*>(n->ws + off); };
   __nv_bfloat16* wbf = reinterpret_cast<__nv_bfloat16*>(n->ws + L.wbf);
   auto WB = [&](int j) { return wbf + n->wcp.dst[j]; };  // BF16 weight matrix j
   k_weights_bf16<<<dim3(64, WB_MATS), 256, 0, s>>>(weights, wbf, n->wcp);
+  k_feat_bf16<<<B, 256, 0, s>>>(feats, BF(L.fb));
   for (int l = 0; l < 4; ++l) {
-    const float* src = l == 0 ? feats : F(L.h[l - 1]);
+    // z = conv(h_{l-1}): A = the activations through a 3-D map (tap shifts along the
+    // frames), B = the tap-major weight copy
     const int K = cin[l] * WS_KW;
-    __nv_bfloat16* a2c = reinterpret_cast<__nv_bfloat16*>(F(L.im2col));
-    k_im2col<<<grid1(int64_t(rows) * cin[l]), 256, 0, s>>>(src, B, cin[l], l == 0, a2c);
-    if (int rc = gemm(rows, WS_CH, K, a2c, K, 1, WB(l), 1, K, F(L.z[l]), WS_CH, 1.f, 0.f, s, F(L.dbig), dbig_floats,
-                      st, true, true))
+    CUtensorMap ta, tb;
+    if (int rc = map_act(&ta, l == 0 ? BF(L.fb) : BF(L.hb[l - 1]), B, cin[l], 4)) return rc;
+    if (int rc = map_k2(&tb, WB(l), WS_CH, K)) return rc;
+    if (int rc = gemm_tma<TM_K3, TM_K2>(rows, WS_CH, K, ta, tb, TmaGeom{cin[l], 1, 0, 0}, F(L.z[l]), WS_CH, 0,
+                                        nullptr, 0, st, s))
       return rc;
-    k_bias_act<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(F(L.z[l]), weights + n->off[l][1], F(L.h[l]), rows, WS_CH,
-                                                              WS_CH, 1);
+    k_bias_act<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(F(L.z[l]), weights + n->off[l][1],
+                                                              l == 3 ? F(L.h3) : nullptr, rows, WS_CH, WS_CH, 1,
+                                                              l < 3 ? BF(L.hb[l]) : nullptr);
   }
-  k_time_mean<<<(B * WS_CH + 255) / 256, 256, 0, s>>>(F(L.h[3]), B, F(L.e));
+  k_time_mean<<<(B * WS_CH + 255) / 256, 256, 0, s>>>(F(L.h3), B, F(L.e));
   cudaMemsetAsync(out, 0, sizeof(float) * size_t(B) * WS_OUTMAX, s);
   int r0 = 0;
   for (int h = 0; h < WS_NHEAD; ++h) {
@@ -1115,27 +1417,34 @@ int grafx_ws_backward(grafx_wsnet* n, const float* weights, const float* feats, 
     r0 += nb;
   }
   const int rows = B * WS_T;
-  const int64_t dbig_floats = int64_t(n->max_batch) * WS_T * WS_CH * WS_KW;
+  auto BF = [&](size_t off) { return reinterpret_cast<__nv_bfloat16*>(n->ws + off); };
   k_time_mean_bwd<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(de, B, dh);
   const int cin[4] = {WS_IN, WS_CH, WS_CH, WS_CH};
+  __nv_bfloat16* dzb = BF(L.dzb);
+  CUtensorMap dz_n2, dz_k3;  // dz [rows][128] as the MN-major operand / as activations
+  if (int rc = map_n2(&dz_n2, dzb, rows, WS_CH)) return rc;
+  if (int rc = map_act(&dz_k3, dzb, B, WS_CH, 4)) return rc;
   for (int l = 3; l >= 0; --l) {
     const int K = cin[l] * WS_KW;
-    // dz = dh gelu'(z); dW = dz^T im2col(input); db = column sums of dz
-    __nv_bfloat16* dzb = reinterpret_cast<__nv_bfloat16*>(n->ws + L.dzb);
+    // dz = dh gelu'(z) (FP32 in place for the bias gradient, BF16 copy for the products)
     k_gelu_bwd<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(dh, F(L.z[l]), int64_t(rows) * WS_CH, dzb);
-    const float* src = l == 0 ? feats : F(L.h[l - 1]);
-    __nv_bfloat16* a2c = reinterpret_cast<__nv_bfloat16*>(F(L.im2col));
-    k_im2col<<<grid1(int64_t(rows) * cin[l]), 256, 0, s>>>(src, B, cin[l], l == 0, a2c);
-    if (int rc = gemm(WS_CH, K, rows, dzb, 1, WS_CH, a2c, K, 1, d_weights + n->off[l][0], K, 1.f, 0.f, s, F(L.dbig),
-                      dbig_floats, st, true, true))
+    // dW[o][c][tap] = sum_(b,t) dz[b][t][o] h_{l-1}[b][t + tap - 2][c]: M = 128, N = 5 cin
+    // (tap-major, stored through the permutation), K = rows; both operands MN-major
+    CUtensorMap th;
+    if (int rc = map_act(&th, l == 0 ? BF(L.fb) : BF(L.hb[l - 1]), B, cin[l], 2)) return rc;
+    if (int rc = gemm_tma<TM_N2, TM_N3>(WS_CH, K, rows, dz_n2, th, TmaGeom{0, 0, cin[l], 1},
+                                        d_weights + n->off[l][0], K, cin[l], F(L.dbig), WS_DBIG_FLOATS, st, s))
       return rc;
     colsum(dh, rows, WS_CH, WS_CH, d_weights + n->off[l][1], F(L.cspart), s);
     if (l > 0) {
-      // d im2col = dz W, then its adjoint scatter gives dh of the previous layer
-      if (int rc = gemm(rows, K, WS_CH, dzb, WS_CH, 1, WB(l), K, 1, F(L.dbig), K, 1.f, 0.f, s, nullptr, 0, st, true,
-                        true))
+      // dh_{l-1}[b][t][c] = sum_(tap, o) dz[b][t - tap + 2][o] W[o][c][tap]: A = dz through
+      // the 3-D map (shift 2 - tap), B = the transposed tap-major weight copy; written in
+      // place of dh (its last reader, the bias column sums, precedes it on the stream)
+      CUtensorMap tw;
+      if (int rc = map_k2(&tw, WB(WB_CONVT + l - 1), cin[l], WS_KW * WS_CH)) return rc;
+      if (int rc = gemm_tma<TM_K3, TM_K2>(rows, cin[l], WS_KW * WS_CH, dz_k3, tw, TmaGeom{WS_CH, -1, 0, 0}, dh,
+                                          cin[l], 0, nullptr, 0, st, s))
         return rc;
-      k_col2im<<<grid1(int64_t(rows) * cin[l]), 256, 0, s>>>(F(L.dbig), B, cin[l], dh);
     }
   }
   return cuda_status();
