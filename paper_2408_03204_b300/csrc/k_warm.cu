@@ -13,8 +13,10 @@
 // conv0.b, conv1.w ... conv3.b, then per head (g, s, e, c, d, r) w1 [288][128], b1,
 // w2 [288][288], b2, w3 [N_t][288], b3.
 // Every product runs on the 5th-generation tensor cores (tcgen05.mma, FP32 accumulator
-// in tensor memory) with BF16 operands, rounded (nearest even) as they are staged into
-// shared memory; activations, gradients and weights stay FP32 in HBM.
+// in tensor memory) with BF16 operands (rounded to nearest even by their producers: the
+// weight copies, the feature transpose, the products' epilogues, the time mean) copied
+// into shared memory by the tensor memory accelerator; pre-activations, gradients and
+// weights stay FP32 in HBM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -46,6 +48,12 @@ static const int kHeadOut[WS_NHEAD] = {2, 1, 8, 4, 176, 50};
 // summed in z order by k_gemm_reduce (deterministic).
 enum : int { LD_SC = 0, LD_VK = 1, LD_VR = 2, LD_BK = 3, LD_BR = 4 };  // BK/BR: BF16 operand, 8 per load
 
+// exact GELU and its derivative
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+
 struct GemmArgs {
   int M, N, K, kchunk;
   const void* A;  // float, or __nv_bfloat16 in the BF16 load modes
@@ -57,6 +65,13 @@ struct GemmArgs {
   float alpha, beta;
   float* part;   // split-K partials or null
   int perm_cin;  // > 0: product column n = tap * perm_cin + c is stored at column c * WS_KW + tap
+  // epilogue of the TMA-fed products (none with split-K): v = alpha acc + beta C, then
+  const float* bias;  // v += bias[n]
+  const float* zact;  // v *= gelu'(zact[m ldz + n])
+  int64_t ldz;
+  __nv_bfloat16* cb;  // BF16 copy cb[m ldcb + n] of gelu(v) (act = 1) or of v
+  int64_t ldcb;
+  int act;
 };
 
 // stored column of product column n
@@ -234,10 +249,11 @@ __device__ __forceinline__ void tc_store(char* tile, const uint32_t (&v)[TC_V]) 
 // Epilogue of a 128 x 128 tile: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows),
 // columns 64 (w / 4) .. + 63, 16 per tcgen05.ld, into a padded FP32 tile at `base` (the
 // idle operand stages); then every warp writes whole rows (coalesced float4) with
-// alpha/beta, or the split-K partial tile (blockIdx.z).  have = false: the tile is zero
-// (an empty k range).  ok = false: nothing is stored.
+// alpha/beta and the optional bias / GELU derivative / BF16 copy, or the split-K partial
+// tile `split`.  have = false: the tile is zero (an empty k range).  ok = false: nothing
+// is stored.
 __device__ __forceinline__ void tc_epilogue(const GemmArgs& g, uint32_t tmem, char* base, int m0, int n0, bool have,
-                                            bool ok) {
+                                            bool ok, int split) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quarter = warp & 3, half = warp >> 2;
   float* E = reinterpret_cast<float*>(base);
@@ -263,34 +279,43 @@ __device__ __forceinline__ void tc_epilogue(const GemmArgs& g, uint32_t tmem, ch
   }
   __syncthreads();
   if (!ok) return;
-  float* part = g.part ? g.part + int64_t(blockIdx.z) * g.M * g.N : nullptr;
+  float* part = g.part ? g.part + int64_t(split) * g.M * g.N : nullptr;
   float* dst = part ? part : g.C;
   const int64_t ld = part ? g.N : g.ldc;
   const bool perm = !part && g.perm_cin > 0;
   const bool vec = !perm && (ld % 4) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
   const float alpha = part ? 1.f : g.alpha, beta = part ? 0.f : g.beta;
+  const bool extra = !part && (g.bias || g.zact || g.cb);
   const int qd = threadIdx.x & 31;  // float4 column of the row
 #pragma unroll 1
   for (int rr = threadIdx.x >> 5; rr < TC_M; rr += TC_THREADS / 32) {
     const int m = m0 + rr, n = n0 + 4 * qd;
     if (m >= g.M || n >= g.N) continue;
-    const float4 v = *reinterpret_cast<const float4*>(E + rr * TC_EPI_LD + 4 * qd);
+    const float4 a4 = *reinterpret_cast<const float4*>(E + rr * TC_EPI_LD + 4 * qd);
     float* cp = dst + int64_t(m) * ld;
-    if (vec && n + 3 < g.N) {
-      float4 o = make_float4(alpha * v.x, alpha * v.y, alpha * v.z, alpha * v.w);
-      if (beta != 0.f) {
+    const int nv = min(4, g.N - n);
+    float v[4] = {alpha * a4.x, alpha * a4.y, alpha * a4.z, alpha * a4.w};
+    if (beta != 0.f) {
+      if (vec && nv == 4) {
         const float4 c = *reinterpret_cast<const float4*>(cp + n);
-        o.x += beta * c.x, o.y += beta * c.y, o.z += beta * c.z, o.w += beta * c.w;
+        v[0] += beta * c.x, v[1] += beta * c.y, v[2] += beta * c.z, v[3] += beta * c.w;
+      } else {
+        for (int j = 0; j < nv; ++j) v[j] += beta * cp[perm ? out_col(g, n + j) : n + j];
       }
-      *reinterpret_cast<float4*>(cp + n) = o;
-    } else {
-      const float vv[4] = {v.x, v.y, v.z, v.w};
+    }
+    if (extra) {
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        if (n + j < g.N) {
-          float* q = cp + (perm ? out_col(g, n + j) : n + j);
-          *q = alpha * vv[j] + (beta != 0.f ? beta * *q : 0.f);
+        if (j < nv) {
+          if (g.bias) v[j] += g.bias[n + j];
+          if (g.zact) v[j] *= gelu_d(g.zact[int64_t(m) * g.ldz + n + j]);
+          if (g.cb) g.cb[int64_t(m) * g.ldcb + n + j] = __float2bfloat16_rn(g.act ? gelu(v[j]) : v[j]);
         }
+    }
+    if (vec && nv == 4) {
+      *reinterpret_cast<float4*>(cp + n) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+      for (int j = 0; j < nv; ++j) cp[perm ? out_col(g, n + j) : n + j] = v[j];
     }
   }
 }
@@ -378,7 +403,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(GemmArgs g, uint32_t* st
   if (!ok && threadIdx.x == 0 && status) atomicOr(status, GEMM_TIMEOUT);
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
-  tc_epilogue(g, tmem, base, m0, n0, ntiles > 0, ok);
+  tc_epilogue(g, tmem, base, m0, n0, ntiles > 0, ok, blockIdx.z);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0)
@@ -459,6 +484,7 @@ __device__ __forceinline__ uint64_t tm_desc(uint32_t tile, int j) {
   }
 }
 
+// One 128 x 128 output tile (k-tiles of split `split`).
 // Warp 0 lane 0 issues the copies of k-tile kt into stage kt mod 3 once the MMAs of
 // k-tile kt - 3 have released it (an mbarrier signalled by tcgen05.commit); warp 1 lane 0
 // waits for each stage's bytes (expect_tx on the stage's full barrier) and issues its
@@ -466,9 +492,8 @@ __device__ __forceinline__ uint64_t tm_desc(uint32_t tile, int j) {
 // stops, the CTA waits (bounded) for the MMAs and copies it started, records
 // GEMM_TIMEOUT, frees its TMEM and stores nothing.
 template <int AM, int BM>
-__global__ void __launch_bounds__(TC_THREADS) k_gemm_tma(const __grid_constant__ CUtensorMap ta,
-                                                         const __grid_constant__ CUtensorMap tb, GemmArgs g,
-                                                         TmaGeom geo, uint32_t* status) {
+__device__ __forceinline__ void tma_gemm(const CUtensorMap* ta, const CUtensorMap* tb, const GemmArgs& g,
+                                         const TmaGeom& geo, int split, uint32_t* status) {
   extern __shared__ __align__(1024) char tm_smem_raw[];
   char* base = tm_smem_raw + ((1024 - (reinterpret_cast<uintptr_t>(tm_smem_raw) & 1023)) & 1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + TM_STAGES * TM_STAGE_BYTES);  // full[3], empty[3], done
@@ -478,7 +503,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tma(const __grid_constant__
   const uint32_t empty0 = full0 + 8 * TM_STAGES, done = full0 + 16 * TM_STAGES;
   const int warp = threadIdx.x >> 5;
   const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TC_N;
-  const int kbeg = blockIdx.z * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
+  const int kbeg = split * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
   const int ntiles = max(0, (kend - kbeg + TC_K - 1) / TC_K);
 
   if (threadIdx.x == 0) {
@@ -501,8 +526,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tma(const __grid_constant__
 
   bool ok = true;
   if (threadIdx.x == 0) {  // copies
-    asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&ta)) : "memory");
-    asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tb)) : "memory");
+    asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(ta)) : "memory");
+    asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(tb)) : "memory");
     int kt = 0;
     for (; kt < ntiles; ++kt) {
       const int st = kt % TM_STAGES;
@@ -514,8 +539,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tma(const __grid_constant__
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "n"(TM_STAGE_BYTES)
                    : "memory");
       const int k0 = kbeg + kt * TC_K;
-      tma_tile<AM>(&ta, tA, fb, m0, k0, geo.a_cin, geo.a_sign);
-      tma_tile<BM>(&tb, tA + TC_TILE_BYTES, fb, n0, k0, geo.b_cin, geo.b_sign);
+      tma_tile<AM>(ta, tA, fb, m0, k0, geo.a_cin, geo.a_sign);
+      tma_tile<BM>(tb, tA + TC_TILE_BYTES, fb, n0, k0, geo.b_cin, geo.b_sign);
     }
     info[1] = kt;
   } else if (threadIdx.x == 32) {  // MMAs
@@ -559,11 +584,32 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tma(const __grid_constant__
   ok = __syncthreads_and(ok) != 0;
   if (!ok && threadIdx.x == 0 && status) atomicOr(status, GEMM_TIMEOUT);
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  tc_epilogue(g, tmem, base, m0, n0, ntiles > 0, ok);
+  tc_epilogue(g, tmem, base, m0, n0, ntiles > 0, ok, split);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(TC_TMEM_COLS) : "memory");
+}
+
+template <int AM, int BM>
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tma(const __grid_constant__ CUtensorMap ta,
+                                                         const __grid_constant__ CUtensorMap tb, GemmArgs g,
+                                                         TmaGeom geo, uint32_t* status) {
+  tma_gemm<AM, BM>(&ta, &tb, g, geo, blockIdx.z, status);
+}
+
+// Up to WS_NHEAD independent products in one launch (blockIdx.z: the problem; CTAs past
+// a problem's tiles return at once).  No split-K.
+struct TmaGroup {
+  CUtensorMap ta[WS_NHEAD], tb[WS_NHEAD];
+  GemmArgs g[WS_NHEAD];
+};
+template <int AM, int BM>
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tma_group(const __grid_constant__ TmaGroup grp,
+                                                               uint32_t* status) {
+  const GemmArgs& g = grp.g[blockIdx.z];
+  if (int(blockIdx.y) * TC_M >= g.M || int(blockIdx.x) * TC_N >= g.N) return;
+  tma_gemm<AM, BM>(&grp.ta[blockIdx.z], &grp.tb[blockIdx.z], g, TmaGeom{0, 0, 0, 0}, 0, status);
 }
 
 // C = alpha * sum_z part[z] + beta * C, z in order (columns through out_col)
@@ -673,10 +719,12 @@ static EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// Tensor map of a dense BF16 tensor (dims innermost first, rank 2 or 3) read in boxes
-// `box` with 128-byte swizzle; elements outside the tensor arrive as zeros.  The base
-// must be 16-byte aligned and every row a multiple of 16 bytes (the encoder checks both).
-static int bf16_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint32_t* box) {
+// Tensor map of a BF16 tensor (dims innermost first, rank 2 or 3; rows ld elements apart,
+// else dense) read in boxes `box` with 128-byte swizzle; elements outside the tensor
+// arrive as zeros.  The base must be 16-byte aligned and every row a multiple of 16 bytes
+// (the encoder checks both).
+static int bf16_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint32_t* box,
+                    uint64_t ld = 0) {
   EncodeTiledFn fn = encode_tiled();
   if (!fn) return fail(GRAFX_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
   cuuint64_t gd[3], gs[2];
@@ -686,7 +734,7 @@ static int bf16_map(CUtensorMap* m, const void* base, int rank, const uint64_t* 
     gd[i] = dims[i];
     bx[i] = box[i];
     if (i > 0) gs[i - 1] = stride;
-    stride *= dims[i];
+    stride *= (i == 0 && ld) ? ld : dims[i];
   }
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, cuuint32_t(rank), const_cast<void*>(base), gd, gs, bx, es,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -694,17 +742,17 @@ static int bf16_map(CUtensorMap* m, const void* base, int rank, const uint64_t* 
   return r == CUDA_SUCCESS ? GRAFX_OK : fail(GRAFX_ECUDA, "cuTensorMapEncodeTiled rejected a tensor map");
 }
 
-// X[rows][K], K-major boxes {64, 128}
-static int map_k2(CUtensorMap* m, const __nv_bfloat16* X, int64_t rows, int64_t K) {
+// X[rows][K] (rows ld >= K elements apart, 0: K), K-major boxes {64, 128}
+static int map_k2(CUtensorMap* m, const __nv_bfloat16* X, int64_t rows, int64_t K, int64_t ld = 0) {
   const uint64_t d[2] = {uint64_t(K), uint64_t(rows)};
   const uint32_t bx[2] = {TC_K, TC_M};
-  return bf16_map(m, X, 2, d, bx);
+  return bf16_map(m, X, 2, d, bx, uint64_t(ld));
 }
-// X[K][MN], MN-major boxes {64, 64}
-static int map_n2(CUtensorMap* m, const __nv_bfloat16* X, int64_t K, int64_t MN) {
+// X[K][MN] (rows ld >= MN elements apart, 0: MN), MN-major boxes {64, 64}
+static int map_n2(CUtensorMap* m, const __nv_bfloat16* X, int64_t K, int64_t MN, int64_t ld = 0) {
   const uint64_t d[2] = {uint64_t(MN), uint64_t(K)};
   const uint32_t bx[2] = {64, 64};
-  return bf16_map(m, X, 2, d, bx);
+  return bf16_map(m, X, 2, d, bx, uint64_t(ld));
 }
 // activations X[B][T][C], boxes {64, T, samples}: 4 samples (TM_K3) or 2 (TM_N3)
 static int map_act(CUtensorMap* m, const __nv_bfloat16* X, int B, int C, int samples) {
@@ -713,19 +761,28 @@ static int map_act(CUtensorMap* m, const __nv_bfloat16* X, int B, int C, int sam
   return bf16_map(m, X, 3, d, bx);
 }
 
-// C[M][N] = A B (stored through perm_cin) with TMA-fed operand tiles.  Products with
-// fewer than 100 output tiles split K (partial tiles in scratch, at least 4 k-tiles a
-// split) so that about one CTA runs per SM; the partials are summed in order.
+// Arguments of C[M][N] = A B (ldc) for the TMA-fed products: alpha 1, beta 0, no
+// epilogue extras (set by the caller).
+static GemmArgs prod_args(int M, int N, int K, float* C, int64_t ldc) {
+  GemmArgs a{};
+  a.M = M, a.N = N, a.K = K, a.C = C, a.ldc = ldc, a.alpha = 1.f;
+  return a;
+}
+
+// a.C = A B (stored through a.perm_cin, with a's epilogue extras) with TMA-fed operand
+// tiles.  Products without extras and with fewer than 100 output tiles split K (partial
+// tiles in scratch, at least 4 k-tiles a split) so that about one CTA runs per SM; the
+// partials are summed in order.
 template <int AM, int BM>
-static int gemm_tma(int M, int N, int K, const CUtensorMap& ta, const CUtensorMap& tb, TmaGeom geo, float* C,
-                    int64_t ldc, int perm_cin, float* scratch, int64_t scratch_floats, uint32_t* status,
-                    cudaStream_t s) {
+static int gemm_tma(GemmArgs a, const CUtensorMap& ta, const CUtensorMap& tb, TmaGeom geo, float* scratch,
+                    int64_t scratch_floats, uint32_t* status, cudaStream_t s) {
+  const int M = a.M, N = a.N, K = a.K;
   if (M <= 0 || N <= 0) return GRAFX_OK;
-  GemmArgs a{M, N, K, 0, nullptr, 0, 0, nullptr, 0, 0, C, ldc, 1.f, 0.f, nullptr, perm_cin};
   const int tm = (M + TC_M - 1) / TC_M, tn = (N + TC_N - 1) / TC_N;
   const int ktiles = std::max(1, (K + TC_K - 1) / TC_K);
+  const bool extras = a.bias || a.zact || a.cb;
   int splits = 1;
-  if (scratch && tm * tn < 100 && ktiles >= 8) {
+  if (scratch && !extras && tm * tn < 100 && ktiles >= 8) {
     splits = std::min((148 + tm * tn - 1) / (tm * tn), ktiles / 4);
     splits = int(std::min<int64_t>(splits, scratch_floats / (int64_t(M) * N)));
     splits = std::max(splits, 1);
@@ -747,27 +804,32 @@ static int gemm_tma(int M, int N, int K, const CUtensorMap& ta, const CUtensorMa
   return GRAFX_OK;
 }
 
-// ------------------------------------------------------------------ elementwise pieces
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_d(float x) {
-  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+// The problems of grp (g[i].M = 0: none) in one launch.
+template <int AM, int BM>
+static int gemm_tma_group(TmaGroup& grp, uint32_t* status, cudaStream_t s) {
+  int tm = 0, tn = 0;
+  for (int i = 0; i < WS_NHEAD; ++i) {
+    GemmArgs& g = grp.g[i];
+    if (g.M <= 0 || g.N <= 0) {
+      g.M = g.N = 0;
+      continue;
+    }
+    g.kchunk = std::max(1, (g.K + TC_K - 1) / TC_K) * TC_K;
+    g.alpha = 1.f;
+    tm = std::max(tm, (g.M + TC_M - 1) / TC_M);
+    tn = std::max(tn, (g.N + TC_N - 1) / TC_N);
+  }
+  if (tm == 0) return GRAFX_OK;
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(k_gemm_tma_group<AM, BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, TM_SMEM);
+    init = true;
+  }
+  k_gemm_tma_group<AM, BM><<<dim3(tn, tm, WS_NHEAD), TC_THREADS, TM_SMEM, s>>>(grp, status);
+  return GRAFX_OK;
 }
 
-// z[r][c] += bias[c]; h = gelu(z) (or a copy without GELU); rows x cols with row stride
-// ld; hb (if given): h as BF16, the next product's operand
-__global__ void k_bias_act(float* __restrict__ z, const float* __restrict__ bias, float* __restrict__ h, int64_t rows,
-                           int cols, int64_t ld, int apply_gelu, __nv_bfloat16* __restrict__ hb = nullptr) {
-  const int64_t n = rows * cols;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t r = i / cols;
-    const int c = int(i % cols);
-    const float v = z[r * ld + c] + bias[c];
-    z[r * ld + c] = v;
-    const float a = apply_gelu ? gelu(v) : v;
-    if (h) h[r * ld + c] = a;
-    if (hb) hb[r * ld + c] = __float2bfloat16_rn(a);
-  }
-}
+// ------------------------------------------------------------------ elementwise pieces
 
 // Features [B][256][32] (float32) to the first conv's operand [B][32][256] (BF16): one
 // CTA per sample, transposed through shared memory.
@@ -827,13 +889,76 @@ static void colsum(const float* x, int64_t rows, int cols, int64_t ld, float* ou
   k_colsum_final<<<(cols + 127) / 128, 128, 0, s>>>(part, splits, cols, out);
 }
 
-__global__ void k_time_mean(const float* __restrict__ h, int B, float* __restrict__ e) {
+// The column sums of up to WS_NHEAD matrices in two launches (blockIdx.z / blockIdx.y:
+// the matrix), the same two stages and orders as colsum; partials of matrix i at
+// part + i CS_SPLIT WS_HID.
+struct ColsumGroup {
+  const float* x[WS_NHEAD];
+  float* out[WS_NHEAD];
+  int64_t rows[WS_NHEAD], ld[WS_NHEAD];
+  int cols[WS_NHEAD], splits[WS_NHEAD];
+};
+__global__ void __launch_bounds__(1024) k_colsum_group(ColsumGroup G, float* __restrict__ part) {
+  const int i = blockIdx.z;
+  if (int(blockIdx.y) >= G.splits[i] || int(blockIdx.x) * 32 >= G.cols[i]) return;
+  __shared__ float red[32][33];
+  const int cx = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + cx, cols = G.cols[i];
+  const int64_t stride = 32 * int64_t(G.splits[i]), ld = G.ld[i];
+  const float* x = G.x[i];
+  float s = 0.f;
+  if (c < cols)
+    for (int64_t r = int64_t(blockIdx.y) * 32 + sl; r < G.rows[i]; r += stride) s += x[r * ld + c];
+  red[sl][cx] = s;
+  __syncthreads();
+  for (int w = 16; w > 0; w >>= 1) {
+    if (sl < w) red[sl][cx] += red[sl + w][cx];
+    __syncthreads();
+  }
+  if (sl == 0 && c < cols) part[int64_t(i) * CS_SPLIT * WS_HID + int64_t(blockIdx.y) * cols + c] = red[0][cx];
+}
+__global__ void k_colsum_final_group(ColsumGroup G, const float* __restrict__ part) {
+  const int i = blockIdx.y, c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= G.cols[i]) return;
+  const float* p = part + int64_t(i) * CS_SPLIT * WS_HID;
+  float s = 0.f;
+  for (int z = 0; z < G.splits[i]; ++z) s += p[z * G.cols[i] + c];
+  G.out[i][c] = s;
+}
+// G.rows[i] = 0: no matrix i
+static void colsum_group(ColsumGroup& G, float* part, cudaStream_t s) {
+  int cmax = 0, smax = 0;
+  for (int i = 0; i < WS_NHEAD; ++i) {
+    G.splits[i] = G.rows[i] > 0 ? int(std::min<int64_t>(CS_SPLIT, std::max<int64_t>(1, G.rows[i] / 256))) : 0;
+    if (G.rows[i] <= 0) G.cols[i] = 0;
+    cmax = std::max(cmax, G.cols[i]);
+    smax = std::max(smax, G.splits[i]);
+  }
+  if (cmax == 0) return;
+  k_colsum_group<<<dim3((cmax + 31) / 32, smax, WS_NHEAD), 1024, 0, s>>>(G, part);
+  k_colsum_final_group<<<dim3((cmax + 127) / 128, WS_NHEAD), 128, 0, s>>>(G, part);
+}
+
+// x[r][c] (rows x cols, row stride ld) as BF16 y[r][c] (row stride ldy)
+__global__ void k_to_bf16(const float* __restrict__ x, int64_t rows, int cols, int64_t ld,
+                          __nv_bfloat16* __restrict__ y, int64_t ldy) {
+  const int64_t n = rows * cols;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / cols;
+    const int c = int(i % cols);
+    y[r * ldy + c] = __float2bfloat16_rn(x[r * ld + c]);
+  }
+}
+
+// e[b][c] = mean over the frames of gelu(z[b][t][c]) (the last conv layer's activation),
+// stored as BF16: the heads' first operand
+__global__ void k_time_mean(const float* __restrict__ z, int B, __nv_bfloat16* __restrict__ e) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B * WS_CH) return;
   const int b = i / WS_CH, c = i % WS_CH;
   float s = 0.f;
-  for (int t = 0; t < WS_T; ++t) s += h[(int64_t(b) * WS_T + t) * WS_CH + c];
-  e[i] = s / float(WS_T);
+  for (int t = 0; t < WS_T; ++t) s += gelu(z[(int64_t(b) * WS_T + t) * WS_CH + c]);
+  e[i] = __float2bfloat16_rn(s / float(WS_T));
 }
 
 __global__ void k_time_mean_bwd(const float* __restrict__ de, int B, float* __restrict__ dh) {
@@ -870,8 +995,6 @@ __global__ void __launch_bounds__(1024) k_ws_mse(const float* __restrict__ out, 
   if (threadIdx.x == 0) *loss = v[0];
 }
 
-// BF16 copies of the weight matrices, each at a 16-byte aligned offset of the shadow
-// buffer (the products read them as 8-element BF16 loads)
 // BF16 weight copies: conv layer l tap-major (0..3), per head w1, w2, w3 (4..21), conv
 // layer l = 1..3 transposed tap-major (22..24)
 constexpr int WB_MATS = 4 + 3 * WS_NHEAD + 3;
@@ -1083,7 +1206,7 @@ constexpr int64_t WS_DBIG_FLOATS = int64_t(32) * WS_CH * WS_IN * WS_KW;
 
 struct WsNetLayout {
   size_t melw, melrng, tw, ptw, status;
-  size_t fb, hb[3], z[4], h3, e, a1, g1, a2, g2, dbig, dsmall, dh, dzb, cspart, wbf, frames, total;
+  size_t fb, hb[3], z[4], eb, a1, g1b, a2, g2b, dbig, dsmall, dab, dob, dh, dzb[2], cspart, wbf, frames, total;
 };
 
 // frame_floats: log-mel frame scratch (rows x frames x 128) in floats
@@ -1104,17 +1227,18 @@ WsNetLayout ws_layout(const grafx_wsnet* n, int64_t frame_floats) {
   L.fb = take(2 * rows * WS_IN);
   for (int l = 0; l < 3; ++l) L.hb[l] = take(2 * rows * WS_CH);
   for (int l = 0; l < 4; ++l) L.z[l] = take(4 * rows * WS_CH);
-  L.h3 = take(4 * rows * WS_CH);
-  L.e = take(4 * B * WS_CH);
+  L.eb = take(2 * B * WS_CH);
   L.a1 = take(4 * B * WS_HID);
-  L.g1 = take(4 * B * WS_HID);
+  L.g1b = take(2 * B * WS_HID);
   L.a2 = take(4 * B * WS_HID);
-  L.g2 = take(4 * B * WS_HID);
+  L.g2b = take(2 * B * WS_HID);
   L.dbig = take(4 * size_t(WS_DBIG_FLOATS));
   L.dsmall = take(4 * B * WS_HID * 2);
+  L.dab = take(2 * B * WS_HID * 2);
+  L.dob = take(2 * B * WS_OUTMAX);
   L.dh = take(4 * (B * WS_CH + rows * WS_CH));
-  L.dzb = take(2 * rows * WS_CH);
-  L.cspart = take(4 * size_t(CS_SPLIT) * WS_HID);
+  for (int i = 0; i < 2; ++i) L.dzb[i] = take(2 * rows * WS_CH);
+  L.cspart = take(4 * size_t(WS_NHEAD) * CS_SPLIT * WS_HID);
   L.wbf = take(2 * size_t(n->wb_elems));
   L.frames = take(4 * size_t(std::max<int64_t>(frame_floats, 1)));
   L.total = o;
@@ -1320,44 +1444,46 @@ int grafx_ws_forward(grafx_wsnet* n, const float* weights, const float* feats, c
   k_weights_bf16<<<dim3(64, WB_MATS), 256, 0, s>>>(weights, wbf, n->wcp);
   k_feat_bf16<<<B, 256, 0, s>>>(feats, BF(L.fb));
   for (int l = 0; l < 4; ++l) {
-    // z = conv(h_{l-1}): A = the activations through a 3-D map (tap shifts along the
-    // frames), B = the tap-major weight copy
+    // z = conv(h_{l-1}) + b with h_l = gelu(z) as BF16 in the epilogue (the last layer's
+    // GELU is taken by the time mean): A = the activations through a 3-D map (tap shifts
+    // along the frames), B = the tap-major weight copy
     const int K = cin[l] * WS_KW;
     CUtensorMap ta, tb;
     if (int rc = map_act(&ta, l == 0 ? BF(L.fb) : BF(L.hb[l - 1]), B, cin[l], 4)) return rc;
     if (int rc = map_k2(&tb, WB(l), WS_CH, K)) return rc;
-    if (int rc = gemm_tma<TM_K3, TM_K2>(rows, WS_CH, K, ta, tb, TmaGeom{cin[l], 1, 0, 0}, F(L.z[l]), WS_CH, 0,
-                                        nullptr, 0, st, s))
-      return rc;
-    k_bias_act<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(F(L.z[l]), weights + n->off[l][1],
-                                                              l == 3 ? F(L.h3) : nullptr, rows, WS_CH, WS_CH, 1,
-                                                              l < 3 ? BF(L.hb[l]) : nullptr);
+    GemmArgs a = prod_args(rows, WS_CH, K, F(L.z[l]), WS_CH);
+    a.bias = weights + n->off[l][1];
+    if (l < 3) a.cb = BF(L.hb[l]), a.ldcb = WS_CH, a.act = 1;
+    if (int rc = gemm_tma<TM_K3, TM_K2>(a, ta, tb, TmaGeom{cin[l], 1, 0, 0}, nullptr, 0, st, s)) return rc;
   }
-  k_time_mean<<<(B * WS_CH + 255) / 256, 256, 0, s>>>(F(L.h3), B, F(L.e));
+  k_time_mean<<<(B * WS_CH + 255) / 256, 256, 0, s>>>(F(L.z[3]), B, BF(L.eb));
   cudaMemsetAsync(out, 0, sizeof(float) * size_t(B) * WS_OUTMAX, s);
+  // the heads, each product of all heads in one launch: a1 = e W1^T + b1 (g1 = gelu(a1)
+  // as BF16), a2 = g1 W2^T + b2 (g2), out = g2 W3^T + b3
+  TmaGroup f1{}, f2{}, f3{};
   int r0 = 0;
   for (int h = 0; h < WS_NHEAD; ++h) {
     const int nb = head_count[h];
     if (nb == 0) continue;
     const int64_t* o = n->hoff[h];
-    float *a1 = F(L.a1) + r0 * WS_HID, *g1 = F(L.g1) + r0 * WS_HID;
-    float *a2 = F(L.a2) + r0 * WS_HID, *g2 = F(L.g2) + r0 * WS_HID;
-    if (int rc = gemm(nb, WS_HID, WS_CH, F(L.e) + r0 * WS_CH, WS_CH, 1, WB(4 + 3 * h), 1, WS_CH, a1, WS_HID, 1.f,
-                      0.f, s, nullptr, 0, st, false, true))
-      return rc;
-    k_bias_act<<<grid1(int64_t(nb) * WS_HID), 256, 0, s>>>(a1, weights + o[1], g1, nb, WS_HID, WS_HID, 1);
-    if (int rc = gemm(nb, WS_HID, WS_HID, g1, WS_HID, 1, WB(5 + 3 * h), 1, WS_HID, a2, WS_HID, 1.f, 0.f, s, nullptr,
-                      0, st, false, true))
-      return rc;
-    k_bias_act<<<grid1(int64_t(nb) * WS_HID), 256, 0, s>>>(a2, weights + o[3], g2, nb, WS_HID, WS_HID, 1);
-    float* ob = out + int64_t(r0) * WS_OUTMAX;
-    if (int rc = gemm(nb, kHeadOut[h], WS_HID, g2, WS_HID, 1, WB(6 + 3 * h), 1, WS_HID, ob, WS_OUTMAX, 1.f, 0.f, s,
-                      nullptr, 0, st, false, true))
-      return rc;
-    k_bias_act<<<grid1(int64_t(nb) * kHeadOut[h]), 256, 0, s>>>(ob, weights + o[5], nullptr, nb, kHeadOut[h],
-                                                                  WS_OUTMAX, 0);
+    __nv_bfloat16 *g1 = BF(L.g1b) + r0 * WS_HID, *g2 = BF(L.g2b) + r0 * WS_HID;
+    if (int rc = map_k2(&f1.ta[h], BF(L.eb) + r0 * WS_CH, nb, WS_CH)) return rc;
+    if (int rc = map_k2(&f1.tb[h], WB(4 + 3 * h), WS_HID, WS_CH)) return rc;
+    f1.g[h] = prod_args(nb, WS_HID, WS_CH, F(L.a1) + r0 * WS_HID, WS_HID);
+    f1.g[h].bias = weights + o[1], f1.g[h].cb = g1, f1.g[h].ldcb = WS_HID, f1.g[h].act = 1;
+    if (int rc = map_k2(&f2.ta[h], g1, nb, WS_HID)) return rc;
+    if (int rc = map_k2(&f2.tb[h], WB(5 + 3 * h), WS_HID, WS_HID)) return rc;
+    f2.g[h] = prod_args(nb, WS_HID, WS_HID, F(L.a2) + r0 * WS_HID, WS_HID);
+    f2.g[h].bias = weights + o[3], f2.g[h].cb = g2, f2.g[h].ldcb = WS_HID, f2.g[h].act = 1;
+    if (int rc = map_k2(&f3.ta[h], g2, nb, WS_HID)) return rc;
+    if (int rc = map_k2(&f3.tb[h], WB(6 + 3 * h), kHeadOut[h], WS_HID)) return rc;
+    f3.g[h] = prod_args(nb, kHeadOut[h], WS_HID, out + int64_t(r0) * WS_OUTMAX, WS_OUTMAX);
+    f3.g[h].bias = weights + o[5];
     r0 += nb;
   }
+  if (int rc = gemm_tma_group<TM_K2, TM_K2>(f1, st, s)) return rc;
+  if (int rc = gemm_tma_group<TM_K2, TM_K2>(f2, st, s)) return rc;
+  if (int rc = gemm_tma_group<TM_K2, TM_K2>(f3, st, s)) return rc;
   return cuda_status();
 }
 
@@ -1372,79 +1498,98 @@ int grafx_ws_backward(grafx_wsnet* n, const float* weights, const float* feats, 
   uint32_t* st = reinterpret_cast<uint32_t*>(n->ws + L.status);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaMemsetAsync(d_weights, 0, sizeof(float) * size_t(n->n_params), s);
+  // the BF16 weight copies and activations are the forward's (same weights and batch)
   __nv_bfloat16* wbf = reinterpret_cast<__nv_bfloat16*>(n->ws + L.wbf);
   auto WB = [&](int j) { return wbf + n->wcp.dst[j]; };  // BF16 weight matrix j
-  k_weights_bf16<<<dim3(64, WB_MATS), 256, 0, s>>>(weights, wbf, n->wcp);
+  auto BF = [&](size_t off) { return reinterpret_cast<__nv_bfloat16*>(n->ws + off); };
   float* de = F(L.dh);                                 // [B][128]
   float* dh = F(L.dh) + size_t(n->max_batch) * WS_CH;  // [rows][128]
+  __nv_bfloat16* dob = BF(L.dob);
+  k_to_bf16<<<grid1(int64_t(B) * WS_OUTMAX), 256, 0, s>>>(d_out, B, WS_OUTMAX, WS_OUTMAX, dob, WS_OUTMAX);
+  // the heads, each step for all heads in one launch:
+  //   dW3 = dO^T g2, db3 = column sums of dO, da2 = (dO W3) gelu'(a2),
+  //   dW2 = da2^T g1, db2, da1 = (da2 W2) gelu'(a1), dW1 = da1^T e, db1, de = da1 W1
+  TmaGroup w3{}, x2{}, w2{}, x1{}, w1{}, x0{};
+  ColsumGroup c3{}, c2{}, c1{};
   int r0 = 0;
   for (int h = 0; h < WS_NHEAD; ++h) {
     const int nb = head_count[h];
     if (nb == 0) continue;
     const int64_t* o = n->hoff[h];
     const int no = kHeadOut[h];
-    const float* dO = d_out + int64_t(r0) * WS_OUTMAX;
+    const __nv_bfloat16* dO = dob + int64_t(r0) * WS_OUTMAX;
     float* da2 = F(L.dsmall) + r0 * WS_HID;
     float* da1 = F(L.dsmall) + size_t(n->max_batch) * WS_HID + r0 * WS_HID;
-    const float *a1 = F(L.a1) + r0 * WS_HID, *g1 = F(L.g1) + r0 * WS_HID;
-    const float *a2 = F(L.a2) + r0 * WS_HID, *g2 = F(L.g2) + r0 * WS_HID;
-    // dW3 = dO^T g2, db3 = column sums of dO, da2 = (dO W3) gelu'(a2)
-    if (int rc = gemm(no, WS_HID, nb, dO, 1, WS_OUTMAX, g2, WS_HID, 1, d_weights + o[4], WS_HID, 1.f, 0.f, s,
-                      nullptr, 0, st))
-      return rc;
-    colsum(dO, nb, no, WS_OUTMAX, d_weights + o[5], F(L.cspart), s);
-    if (int rc = gemm(nb, WS_HID, no, dO, WS_OUTMAX, 1, WB(6 + 3 * h), WS_HID, 1, da2, WS_HID, 1.f, 0.f, s, nullptr,
-                      0, st, false, true))
-      return rc;
-    k_gelu_bwd<<<grid1(int64_t(nb) * WS_HID), 256, 0, s>>>(da2, a2, int64_t(nb) * WS_HID);
-    // dW2 = da2^T g1, db2, da1 = (da2 W2) gelu'(a1)
-    if (int rc = gemm(WS_HID, WS_HID, nb, da2, 1, WS_HID, g1, WS_HID, 1, d_weights + o[2], WS_HID, 1.f, 0.f, s,
-                      nullptr, 0, st))
-      return rc;
-    colsum(da2, nb, WS_HID, WS_HID, d_weights + o[3], F(L.cspart), s);
-    if (int rc = gemm(nb, WS_HID, WS_HID, da2, WS_HID, 1, WB(5 + 3 * h), WS_HID, 1, da1, WS_HID, 1.f, 0.f, s,
-                      nullptr, 0, st, false, true))
-      return rc;
-    k_gelu_bwd<<<grid1(int64_t(nb) * WS_HID), 256, 0, s>>>(da1, a1, int64_t(nb) * WS_HID);
-    // dW1 = da1^T e, db1, de = da1 W1
-    if (int rc = gemm(WS_HID, WS_CH, nb, da1, 1, WS_HID, F(L.e) + r0 * WS_CH, WS_CH, 1, d_weights + o[0], WS_CH, 1.f,
-                      0.f, s, nullptr, 0, st))
-      return rc;
-    colsum(da1, nb, WS_HID, WS_HID, d_weights + o[1], F(L.cspart), s);
-    if (int rc = gemm(nb, WS_CH, WS_HID, da1, WS_HID, 1, WB(4 + 3 * h), WS_CH, 1, de + r0 * WS_CH, WS_CH, 1.f, 0.f,
-                      s, nullptr, 0, st, false, true))
-      return rc;
+    __nv_bfloat16* da2b = BF(L.dab) + r0 * WS_HID;
+    __nv_bfloat16* da1b = BF(L.dab) + size_t(n->max_batch) * WS_HID + r0 * WS_HID;
+    const __nv_bfloat16 *g1 = BF(L.g1b) + r0 * WS_HID, *g2 = BF(L.g2b) + r0 * WS_HID, *e = BF(L.eb) + r0 * WS_CH;
+    if (int rc = map_n2(&w3.ta[h], dO, nb, no, WS_OUTMAX)) return rc;
+    if (int rc = map_n2(&w3.tb[h], g2, nb, WS_HID)) return rc;
+    w3.g[h] = prod_args(no, WS_HID, nb, d_weights + o[4], WS_HID);
+    c3.x[h] = d_out + int64_t(r0) * WS_OUTMAX, c3.rows[h] = nb, c3.cols[h] = no, c3.ld[h] = WS_OUTMAX;
+    c3.out[h] = d_weights + o[5];
+    if (int rc = map_k2(&x2.ta[h], dO, nb, no, WS_OUTMAX)) return rc;
+    if (int rc = map_n2(&x2.tb[h], WB(6 + 3 * h), no, WS_HID)) return rc;
+    x2.g[h] = prod_args(nb, WS_HID, no, da2, WS_HID);
+    x2.g[h].zact = F(L.a2) + r0 * WS_HID, x2.g[h].ldz = WS_HID, x2.g[h].cb = da2b, x2.g[h].ldcb = WS_HID;
+    c2.x[h] = da2, c2.rows[h] = nb, c2.cols[h] = WS_HID, c2.ld[h] = WS_HID, c2.out[h] = d_weights + o[3];
+    if (int rc = map_n2(&w2.ta[h], da2b, nb, WS_HID)) return rc;
+    if (int rc = map_n2(&w2.tb[h], g1, nb, WS_HID)) return rc;
+    w2.g[h] = prod_args(WS_HID, WS_HID, nb, d_weights + o[2], WS_HID);
+    if (int rc = map_k2(&x1.ta[h], da2b, nb, WS_HID)) return rc;
+    if (int rc = map_n2(&x1.tb[h], WB(5 + 3 * h), WS_HID, WS_HID)) return rc;
+    x1.g[h] = prod_args(nb, WS_HID, WS_HID, da1, WS_HID);
+    x1.g[h].zact = F(L.a1) + r0 * WS_HID, x1.g[h].ldz = WS_HID, x1.g[h].cb = da1b, x1.g[h].ldcb = WS_HID;
+    c1.x[h] = da1, c1.rows[h] = nb, c1.cols[h] = WS_HID, c1.ld[h] = WS_HID, c1.out[h] = d_weights + o[1];
+    if (int rc = map_n2(&w1.ta[h], da1b, nb, WS_HID)) return rc;
+    if (int rc = map_n2(&w1.tb[h], e, nb, WS_CH)) return rc;
+    w1.g[h] = prod_args(WS_HID, WS_CH, nb, d_weights + o[0], WS_CH);
+    if (int rc = map_k2(&x0.ta[h], da1b, nb, WS_HID)) return rc;
+    if (int rc = map_n2(&x0.tb[h], WB(4 + 3 * h), WS_HID, WS_CH)) return rc;
+    x0.g[h] = prod_args(nb, WS_CH, WS_HID, de + r0 * WS_CH, WS_CH);
     r0 += nb;
   }
+  float* csp = F(L.cspart);
+  if (int rc = gemm_tma_group<TM_N2, TM_N2>(w3, st, s)) return rc;
+  colsum_group(c3, csp, s);
+  if (int rc = gemm_tma_group<TM_K2, TM_N2>(x2, st, s)) return rc;
+  colsum_group(c2, csp, s);
+  if (int rc = gemm_tma_group<TM_N2, TM_N2>(w2, st, s)) return rc;
+  if (int rc = gemm_tma_group<TM_K2, TM_N2>(x1, st, s)) return rc;
+  colsum_group(c1, csp, s);
+  if (int rc = gemm_tma_group<TM_N2, TM_N2>(w1, st, s)) return rc;
+  if (int rc = gemm_tma_group<TM_K2, TM_N2>(x0, st, s)) return rc;
+
+  // the conv layers: dz_l in BF16 alternates between two buffers (a product reads dz_l
+  // while its epilogue writes dz_{l-1})
   const int rows = B * WS_T;
-  auto BF = [&](size_t off) { return reinterpret_cast<__nv_bfloat16*>(n->ws + off); };
   k_time_mean_bwd<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(de, B, dh);
+  k_gelu_bwd<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(dh, F(L.z[3]), int64_t(rows) * WS_CH, BF(L.dzb[1]));
   const int cin[4] = {WS_IN, WS_CH, WS_CH, WS_CH};
-  __nv_bfloat16* dzb = BF(L.dzb);
-  CUtensorMap dz_n2, dz_k3;  // dz [rows][128] as the MN-major operand / as activations
-  if (int rc = map_n2(&dz_n2, dzb, rows, WS_CH)) return rc;
-  if (int rc = map_act(&dz_k3, dzb, B, WS_CH, 4)) return rc;
   for (int l = 3; l >= 0; --l) {
     const int K = cin[l] * WS_KW;
-    // dz = dh gelu'(z) (FP32 in place for the bias gradient, BF16 copy for the products)
-    k_gelu_bwd<<<grid1(int64_t(rows) * WS_CH), 256, 0, s>>>(dh, F(L.z[l]), int64_t(rows) * WS_CH, dzb);
+    __nv_bfloat16* dzb = BF(L.dzb[l & 1]);  // dz_l; dh holds it in FP32
     // dW[o][c][tap] = sum_(b,t) dz[b][t][o] h_{l-1}[b][t + tap - 2][c]: M = 128, N = 5 cin
     // (tap-major, stored through the permutation), K = rows; both operands MN-major
-    CUtensorMap th;
+    CUtensorMap tz, th;
+    if (int rc = map_n2(&tz, dzb, rows, WS_CH)) return rc;
     if (int rc = map_act(&th, l == 0 ? BF(L.fb) : BF(L.hb[l - 1]), B, cin[l], 2)) return rc;
-    if (int rc = gemm_tma<TM_N2, TM_N3>(WS_CH, K, rows, dz_n2, th, TmaGeom{0, 0, cin[l], 1},
-                                        d_weights + n->off[l][0], K, cin[l], F(L.dbig), WS_DBIG_FLOATS, st, s))
+    GemmArgs a = prod_args(WS_CH, K, rows, d_weights + n->off[l][0], K);
+    a.perm_cin = cin[l];
+    if (int rc = gemm_tma<TM_N2, TM_N3>(a, tz, th, TmaGeom{0, 0, cin[l], 1}, F(L.dbig), WS_DBIG_FLOATS, st, s))
       return rc;
-    colsum(dh, rows, WS_CH, WS_CH, d_weights + n->off[l][1], F(L.cspart), s);
+    colsum(dh, rows, WS_CH, WS_CH, d_weights + n->off[l][1], csp, s);
     if (l > 0) {
-      // dh_{l-1}[b][t][c] = sum_(tap, o) dz[b][t - tap + 2][o] W[o][c][tap]: A = dz through
-      // the 3-D map (shift 2 - tap), B = the transposed tap-major weight copy; written in
-      // place of dh (its last reader, the bias column sums, precedes it on the stream)
-      CUtensorMap tw;
+      // dz_{l-1}[b][t][c] = gelu'(z_{l-1}) sum_(tap, o) dz[b][t - tap + 2][o] W[o][c][tap]:
+      // A = dz_l through the 3-D map (shift 2 - tap), B = the transposed tap-major weight
+      // copy; FP32 into dh (its last reader, the bias column sums, precedes it on the
+      // stream), BF16 into the other buffer
+      CUtensorMap tk, tw;
+      if (int rc = map_act(&tk, dzb, B, WS_CH, 4)) return rc;
       if (int rc = map_k2(&tw, WB(WB_CONVT + l - 1), cin[l], WS_KW * WS_CH)) return rc;
-      if (int rc = gemm_tma<TM_K3, TM_K2>(rows, cin[l], WS_KW * WS_CH, dz_k3, tw, TmaGeom{WS_CH, -1, 0, 0}, dh,
-                                          cin[l], 0, nullptr, 0, st, s))
-        return rc;
+      GemmArgs d = prod_args(rows, cin[l], WS_KW * WS_CH, dh, cin[l]);
+      d.zact = F(L.z[l - 1]), d.ldz = WS_CH, d.cb = BF(L.dzb[(l - 1) & 1]), d.ldcb = WS_CH;
+      if (int rc = gemm_tma<TM_K3, TM_K2>(d, tk, tw, TmaGeom{WS_CH, -1, 0, 0}, nullptr, 0, st, s)) return rc;
     }
   }
   return cuda_status();
