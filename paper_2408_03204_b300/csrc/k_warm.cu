@@ -286,36 +286,79 @@ __device__ __forceinline__ void tc_epilogue(const GemmArgs& g, uint32_t tmem, ch
   const bool vec = !perm && (ld % 4) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
   const float alpha = part ? 1.f : g.alpha, beta = part ? 0.f : g.beta;
   const bool extra = !part && (g.bias || g.zact || g.cb);
-  const int qd = threadIdx.x & 31;  // float4 column of the row
+  // this thread's columns n .. n + 3 (nv of them valid) are the same in all its rows;
+  // rows warp + 8 i + 32 k: four rows per iteration, their global loads issued first
+  const int qd = threadIdx.x & 31, n = n0 + 4 * qd, nv = max(0, min(4, g.N - n));
+  if (nv == 0) return;
+  float bv[4] = {0.f, 0.f, 0.f, 0.f};
+  if (extra && g.bias)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j < nv) bv[j] = g.bias[n + j];
+  const bool zvec = g.zact && (g.ldz % 4) == 0 && (reinterpret_cast<uintptr_t>(g.zact) & 15) == 0;
+  const bool cvec = g.cb && (g.ldcb % 4) == 0 && (reinterpret_cast<uintptr_t>(g.cb) & 7) == 0;
 #pragma unroll 1
-  for (int rr = threadIdx.x >> 5; rr < TC_M; rr += TC_THREADS / 32) {
-    const int m = m0 + rr, n = n0 + 4 * qd;
-    if (m >= g.M || n >= g.N) continue;
-    const float4 a4 = *reinterpret_cast<const float4*>(E + rr * TC_EPI_LD + 4 * qd);
-    float* cp = dst + int64_t(m) * ld;
-    const int nv = min(4, g.N - n);
-    float v[4] = {alpha * a4.x, alpha * a4.y, alpha * a4.z, alpha * a4.w};
-    if (beta != 0.f) {
-      if (vec && nv == 4) {
-        const float4 c = *reinterpret_cast<const float4*>(cp + n);
-        v[0] += beta * c.x, v[1] += beta * c.y, v[2] += beta * c.z, v[3] += beta * c.w;
-      } else {
-        for (int j = 0; j < nv; ++j) v[j] += beta * cp[perm ? out_col(g, n + j) : n + j];
+  for (int r0 = threadIdx.x >> 5; r0 < TC_M; r0 += 4 * (TC_THREADS / 32)) {
+    float v[4][4], zz[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int rr = r0 + i * (TC_THREADS / 32), m = m0 + rr;
+      const float4 a4 = *reinterpret_cast<const float4*>(E + rr * TC_EPI_LD + 4 * qd);
+      v[i][0] = alpha * a4.x, v[i][1] = alpha * a4.y, v[i][2] = alpha * a4.z, v[i][3] = alpha * a4.w;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) zz[i][j] = 0.f;
+      if (m >= g.M) continue;
+      const float* cp = dst + int64_t(m) * ld;
+      if (beta != 0.f) {
+        if (vec && nv == 4) {
+          const float4 c = *reinterpret_cast<const float4*>(cp + n);
+          v[i][0] += beta * c.x, v[i][1] += beta * c.y, v[i][2] += beta * c.z, v[i][3] += beta * c.w;
+        } else {
+          for (int j = 0; j < nv; ++j) v[i][j] += beta * cp[perm ? out_col(g, n + j) : n + j];
+        }
+      }
+      if (extra && g.zact) {
+        const float* zp = g.zact + int64_t(m) * g.ldz + n;
+        if (zvec && nv == 4) {
+          const float4 z4 = *reinterpret_cast<const float4*>(zp);
+          zz[i][0] = z4.x, zz[i][1] = z4.y, zz[i][2] = z4.z, zz[i][3] = z4.w;
+        } else {
+          for (int j = 0; j < nv; ++j) zz[i][j] = zp[j];
+        }
       }
     }
-    if (extra) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (j < nv) {
-          if (g.bias) v[j] += g.bias[n + j];
-          if (g.zact) v[j] *= gelu_d(g.zact[int64_t(m) * g.ldz + n + j]);
-          if (g.cb) g.cb[int64_t(m) * g.ldcb + n + j] = __float2bfloat16_rn(g.act ? gelu(v[j]) : v[j]);
+    for (int i = 0; i < 4; ++i) {
+      const int m = m0 + r0 + i * (TC_THREADS / 32);
+      if (m >= g.M) continue;
+      if (extra) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          v[i][j] += bv[j];
+          if (g.zact) v[i][j] *= gelu_d(zz[i][j]);
         }
-    }
-    if (vec && nv == 4) {
-      *reinterpret_cast<float4*>(cp + n) = make_float4(v[0], v[1], v[2], v[3]);
-    } else {
-      for (int j = 0; j < nv; ++j) cp[perm ? out_col(g, n + j) : n + j] = v[j];
+        if (g.cb) {
+          float h[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) h[j] = g.act ? gelu(v[i][j]) : v[i][j];
+          __nv_bfloat16* q = g.cb + int64_t(m) * g.ldcb + n;
+          if (cvec && nv == 4) {
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(h[0], h[1]), hi = __floats2bfloat162_rn(h[2], h[3]);
+            uint2 w;
+            w.x = *reinterpret_cast<const uint32_t*>(&lo);
+            w.y = *reinterpret_cast<const uint32_t*>(&hi);
+            *reinterpret_cast<uint2*>(q) = w;
+          } else {
+            for (int j = 0; j < nv; ++j) q[j] = __float2bfloat16_rn(h[j]);
+          }
+        }
+      }
+      float* cp = dst + int64_t(m) * ld;
+      if (vec && nv == 4) {
+        *reinterpret_cast<float4*>(cp + n) = make_float4(v[i][0], v[i][1], v[i][2], v[i][3]);
+      } else {
+        for (int j = 0; j < nv; ++j) cp[perm ? out_col(g, n + j) : n + j] = v[i][j];
+      }
     }
   }
 }
@@ -976,19 +1019,45 @@ __global__ void k_time_mean_bwd(const float* __restrict__ de, int B, float* __re
 __global__ void __launch_bounds__(1024) k_ws_mse(const float* __restrict__ out, const float* __restrict__ tgt,
                                                  const int32_t* __restrict__ nout, int B,
                                                  float* __restrict__ loss, float* __restrict__ d) {
+  // warp w takes rows w, w + 32, ... two at a time (their loads issued first), lane l
+  // columns l + 32 k; the per-thread sums meet in a fixed-order block sum
+  constexpr int KC = (WS_OUTMAX + 31) / 32;
   __shared__ float red[4 * 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float s = 0.f;
-  for (int i = threadIdx.x; i < B * WS_OUTMAX; i += blockDim.x) {
-    const int b = i / WS_OUTMAX, j = i % WS_OUTMAX;
-    const int nb = nout[b];
-    float g = 0.f;
-    if (j < nb) {
-      const float r = out[i] - tgt[i];
-      const float w = 1.f / (float(B) * float(nb));
-      s += r * r * w;
-      g = 2.f * r * w;
+  for (int b0 = warp; b0 < B; b0 += 2 * 32) {
+    float o[2][KC], t[2][KC];
+    int nb[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int b = b0 + 32 * r;
+      nb[r] = b < B ? nout[b] : 0;
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        const int j = lane + 32 * k;
+        const bool in = b < B && j < WS_OUTMAX;
+        o[r][k] = in ? out[int64_t(b) * WS_OUTMAX + j] : 0.f;
+        t[r][k] = in ? tgt[int64_t(b) * WS_OUTMAX + j] : 0.f;
+      }
     }
-    d[i] = g;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int b = b0 + 32 * r;
+      if (b >= B) continue;
+      const float w = nb[r] > 0 ? 1.f / (float(B) * float(nb[r])) : 0.f;
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        const int j = lane + 32 * k;
+        if (j >= WS_OUTMAX) continue;
+        float g = 0.f;
+        if (j < nb[r]) {
+          const float e = o[r][k] - t[r][k];
+          s += e * e * w;
+          g = 2.f * e * w;
+        }
+        d[int64_t(b) * WS_OUTMAX + j] = g;
+      }
+    }
   }
   float v[1] = {s};
   block_sum<1>(v, red);

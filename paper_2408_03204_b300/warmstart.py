@@ -25,6 +25,10 @@ from . import (PARAM_COLS, T_COMP, T_DELAY, T_EQ, T_GAIN, T_IMAGER, T_IN, T_OUT,
 from . import fit as gfit
 
 HEAD_OF = {t: i for i, t in enumerate(WS_HEAD_TYPES)}
+# processor type -> head (-1: no head) and head -> output count, as lookup arrays
+_HEAD_LUT = np.full(16, -1, np.int32)
+_HEAD_LUT[list(HEAD_OF)] = list(HEAD_OF.values())
+_HEAD_NOUT = np.asarray(WS_HEAD_OUT, np.int32)
 
 
 def param_shapes():
@@ -198,23 +202,23 @@ class WarmStart:
         return y
 
     def _head_rows(self, types):
-        torch = self.torch
-        heads = torch.as_tensor([HEAD_OF[t] for t in types], dtype=torch.int32, device=self.device)
-        n_out = torch.as_tensor([WS_HEAD_OUT[HEAD_OF[t]] for t in types], dtype=torch.int32, device=self.device)
-        return heads, n_out
+        """Per sample its head and output count on the device (one upload), and the host
+        counts per head; types is a sequence or array of processor types."""
+        h = _HEAD_LUT[np.asarray(types, dtype=np.int64)]
+        both = self.torch.from_numpy(np.stack([h, _HEAD_NOUT[h]])).to(self.device)
+        return both[0], both[1], np.bincount(h, minlength=len(WS_HEAD_TYPES)).tolist()
 
     def train_step(self, feats, targets, types):
         """One Adam step on a minibatch (feats [B,256,32], targets theta [B,176], types
         sorted by head).  Returns the device loss tensor."""
         torch = self.torch
         B = feats.shape[0]
-        heads, n_out = self._head_rows(types)
-        hc = [sum(1 for t in types if t == ht) for ht in WS_HEAD_TYPES]
+        heads, n_out, hc = self._head_rows(types)
         with torch.cuda.stream(self.stream):
             y = self._standardise(targets.contiguous(), heads, n_out, back=False)
             out = torch.empty((B, WS_OUTMAX), dtype=torch.float32, device=self.device)
             d = torch.empty_like(out)
-            loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+            loss = torch.empty(1, dtype=torch.float32, device=self.device)
             self.net.forward_raw(self.W, feats, hc, out, self.st)
             WarmStartNet.mse_raw(out, y, n_out, loss, d, self.st)
             self.net.backward_raw(self.W, feats, hc, d, self.dW, self.st)
@@ -227,13 +231,13 @@ class WarmStart:
     def predict(self, feats, types):
         """theta [n, 176] (un-standardised) for samples sorted by head."""
         torch = self.torch
-        heads, n_out = self._head_rows(types)
+        heads, n_out, _ = self._head_rows(types)
         outs = []
         with torch.cuda.stream(self.stream):
             for a in range(0, feats.shape[0], self.max_batch):
                 b = min(feats.shape[0], a + self.max_batch)
-                sub = list(types[a:b])
-                hcs = [sum(1 for t in sub if t == ht) for ht in WS_HEAD_TYPES]
+                hcs = np.bincount(_HEAD_LUT[np.asarray(types[a:b], dtype=np.int64)],
+                                  minlength=len(WS_HEAD_TYPES)).tolist()
                 out = torch.empty((b - a, WS_OUTMAX), dtype=torch.float32, device=self.device)
                 self.net.forward_raw(self.W, feats[a:b], hcs, out, self.st)
                 outs.append(out)
@@ -341,20 +345,21 @@ def train(ws, n_graphs, L, graphs_per_batch=16, epochs=4, minibatch=512, seed=5,
     feats, targets = feats[:n_train], targets[:n_train]
     types = types[:n_train]
     ws.fit_standardisation(targets, types)
-    types_t = torch.as_tensor(types, device=ws.device)
     head_of = torch.as_tensor([HEAD_OF.get(t, 0) for t in range(9)], device=ws.device)
+    # minibatch order and head sort on the host (no device round trip per step)
+    types_np = np.asarray(types, dtype=np.int64)
+    head_np = np.maximum(_HEAD_LUT[types_np], 0).astype(np.int64)
     g = torch.Generator(device="cpu").manual_seed(seed)
     n = feats.shape[0]
     losses = []
     t1 = time.time()
     for ep in range(epochs):
-        perm = torch.randperm(n, generator=g).to(ws.device)
+        perm = torch.randperm(n, generator=g).numpy()
         for a in range(0, n - minibatch + 1, minibatch):
             idx = perm[a:a + minibatch]
-            hk = head_of[types_t[idx]]
-            idx = idx[torch.argsort(hk * n + idx)]
-            tl = types_t[idx].tolist()
-            loss = ws.train_step(feats.index_select(0, idx), targets.index_select(0, idx), tl)
+            idx = idx[np.argsort(head_np[idx] * n + idx)]
+            idx_d = torch.from_numpy(idx).to(ws.device)
+            loss = ws.train_step(feats.index_select(0, idx_d), targets.index_select(0, idx_d), types_np[idx])
             losses.append(loss)
         if log:
             ws.stream.synchronize()
