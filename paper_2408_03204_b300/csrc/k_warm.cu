@@ -528,8 +528,8 @@ __device__ __forceinline__ uint64_t tm_desc(uint32_t tile, int j) {
 }
 
 // One 128 x 128 output tile (k-tiles of split `split`).
-// Warp 0 lane 0 issues the copies of k-tile kt into stage kt mod 3 once the MMAs of
-// k-tile kt - 3 have released it (an mbarrier signalled by tcgen05.commit); warp 1 lane 0
+// Warp 0 lane 0 issues the copies of k-tile kt into stage kt mod TM_STAGES once the MMAs
+// of k-tile kt - TM_STAGES have released it (an mbarrier signalled by tcgen05.commit); warp 1 lane 0
 // waits for each stage's bytes (expect_tx on the stage's full barrier) and issues its
 // four MMAs; all 8 warps run the epilogue.  Every wait is bounded: on expiry the issuing
 // stops, the CTA waits (bounded) for the MMAs and copies it started, records
@@ -539,7 +539,7 @@ __device__ __forceinline__ void tma_gemm(const CUtensorMap* ta, const CUtensorMa
                                          const TmaGeom& geo, int split, uint32_t* status) {
   extern __shared__ __align__(1024) char tm_smem_raw[];
   char* base = tm_smem_raw + ((1024 - (reinterpret_cast<uintptr_t>(tm_smem_raw) & 1023)) & 1023);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + TM_STAGES * TM_STAGE_BYTES);  // full[3], empty[3], done
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + TM_STAGES * TM_STAGE_BYTES);  // full[], empty[], done
   int* info = reinterpret_cast<int*>(bars + 2 * TM_STAGES + 1);  // tmem address, copies issued, tiles consumed
   const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(base));
   const uint32_t full0 = static_cast<uint32_t>(__cvta_generic_to_shared(bars));
