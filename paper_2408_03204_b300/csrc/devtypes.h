@@ -60,7 +60,7 @@ constexpr int DL_SLOT_TAPS = 20;   // slot-layout taps per channel (2 s in 100 m
 constexpr int DL_FIR = 39;         // zero-phase FIR per tap (20 log-magnitudes)
 constexpr int DL_K = (DL_FIR + 1) / 2;
 constexpr int DL_ROW = 2 + DL_K;   // parameters per (channel, tap): Re z, Im z, 20 log-magnitudes
-constexpr int DL_TILE = 1024;      // outputs per forward / adjoint work item
+constexpr int DL_TILE = 2048;      // outputs per forward / adjoint work item
 constexpr int DL_B = 4096;         // block of the lag correlation
 constexpr int DL_M = 2 * DL_B;     // its FFT size
 constexpr int DL_PMAX = 32;        // lag partitions: lags [-B, (P-1) B) cover [-19, reach + 19)

@@ -42,7 +42,7 @@ __device__ __forceinline__ const float* dl_single_row(const DevCtx& c, int v) {
 }
 
 // Shared-memory index of window element i: 4 floats of padding after every 32, so that
-// the float4 reads of threads 8 elements apart fall in distinct banks.
+// the float4 reads of threads 16 elements apart (8 lanes per 32 banks) do not collide.
 __device__ __forceinline__ int dl_pidx(int i) { return i + ((i >> 5) << 2); }
 
 // Window of one tap for a tile of one channel summed over several rows (padded layout).
@@ -61,10 +61,10 @@ __device__ __forceinline__ void dl_window_sum(const DevCtx& c, int v, const Node
 }
 
 constexpr int DL_GROUP = 2;                  // taps whose windows are staged together
-constexpr int DL_OPT = 8;                    // consecutive outputs per thread
+constexpr int DL_OPT = 16;                   // consecutive outputs per thread
 constexpr int DL_FT = DL_TILE / DL_OPT;      // threads of the FIR kernels
 constexpr int DL_SH = DL_FIR + 3;            // taps of the shifted filters (alignment shift 0..3)
-constexpr int DL_XL = (DL_OPT + DL_SH - 1 + 3) & ~3;   // window floats a thread reads (13 float4)
+constexpr int DL_XL = (DL_OPT + DL_SH - 1 + 3) & ~3;   // window floats a thread reads (15 float4)
 constexpr int DL_WL = DL_OPT * (DL_FT - 1) + DL_XL;     // window floats staged (16-byte groups)
 constexpr int DL_WP = DL_WL + ((DL_WL + 31) / 32) * 4;  // padded window floats
 static_assert(DL_WL % 4 == 0 && DL_WL >= DL_TILE + DL_SH - 1, "window covers the tile");
@@ -78,7 +78,7 @@ static_assert(DL_WL % 4 == 0 && DL_WL >= DL_TILE + DL_SH - 1, "window covers the
 // the same unrolled loop over aligned float4 reads.  The windows of a group of DL_GROUP
 // taps are staged while the previous group is computed (cp.async from a single source
 // row; a sum over several rows is staged synchronously), double-buffered, with 4 floats of
-// padding after every 32 so that the threads' float4 reads (8 floats apart) fall in
+// padding after every 32 so that the threads' float4 reads (16 floats apart) fall in
 // distinct banks.
 template <bool ADJ>
 __global__ void __launch_bounds__(DL_FT) k_delay_fir(DevCtx c, int item0, int n_items) {
@@ -162,10 +162,16 @@ __global__ void __launch_bounds__(DL_FT) k_delay_fir(DevCtx c, int item0, int n_
       __syncthreads();   // readers of win[buf] are done before it is staged again
     }
     float* row = (ADJ ? arow_w(c, nd) : yrow_w(c, nd)) + ch * nd.pitch;
+    if (t0 + i0 + DL_OPT <= nd.len) {   // t0 + i0 is a multiple of 4 (16-byte rows)
 #pragma unroll
-    for (int q = 0; q < DL_OPT; ++q) {
-      const int t = t0 + i0 + q;
-      if (t < nd.pitch) row[t] = t < nd.len ? acc[q] : 0.f;
+      for (int q = 0; q < DL_OPT; q += 4)
+        st4(row + t0 + i0 + q, make_float4(acc[q], acc[q + 1], acc[q + 2], acc[q + 3]));
+    } else {
+#pragma unroll
+      for (int q = 0; q < DL_OPT; ++q) {
+        const int t = t0 + i0 + q;
+        if (t < nd.pitch) row[t] = t < nd.len ? acc[q] : 0.f;
+      }
     }
   }
 }
