@@ -418,9 +418,9 @@ constexpr int DL_FAR = 80;   // lags from the pole beyond which the phasor is ro
 
 __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_items) {
   __shared__ DlSurrogate sc;
-  __shared__ float cs[DL_FIR];
+  __shared__ float csh[DL_SH];   // cs placed at offset o (the window's misalignment)
   __shared__ float cos39[DL_FIR], hann39[DL_FIR];
-  __shared__ float red[2 * 32];
+  __shared__ float red[4 * 32];
   constexpr int H = (DL_FIR - 1) / 2, K = DL_K, RUN = 8;
   const int ntap = c.dl_taps, Nd = c.dl_nd, nlag = c.dl_P * DL_B;
   dl_tables(cos39, hann39);
@@ -435,8 +435,16 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
     const float* q = c.params + size_t(nd.prow) * c.pcols + (x * ntap + m) * DL_ROW;
     float* out = c.dparams + size_t(nd.grow) * c.pcols + (x * ntap + m) * DL_ROW;
     const int d = int(aux[DL_FIR]);
+    // a run's window rs[n0 - H ..] starts o floats past a 16-byte boundary, the same o for
+    // every run (n0 is a multiple of RUN): it is read from that boundary as float4 and the
+    // taps are shifted by o instead
+    const int o = int((reinterpret_cast<uintptr_t>(rs - H) >> 2) & 3);
+    const float* ra = rs - H - o;
     __syncthreads();
-    if (threadIdx.x < DL_FIR) cs[threadIdx.x] = aux[threadIdx.x];
+    if (threadIdx.x < DL_SH) {
+      const int j = int(threadIdx.x) - o;
+      csh[threadIdx.x] = j >= 0 && j < DL_FIR ? aux[j] : 0.f;
+    }
     if (threadIdx.x == 0) {
       // the tap's surrogate constants, once per item in double (B300's FP64 rate is a
       // small fraction of FP32: every thread forming them was most of this kernel's time)
@@ -474,18 +482,35 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
       }
       out[2 + k] = expf(q[2 + k]) * acc * (k == 0 ? 1.f : 2.f) / float(DL_FIR);
     }
-    // surrogate z: Q = sum_n g[n] phi[n]
+    // surrogate z: Q = sum_n g[n] phi[n] with phi[n] = F(q_n) / (N z) and, away from the
+    // pole, F = -(t1 / a + (z^N - 1) / a^2), a = 1 - q_n, t1 = 1 + (N - 1) z^N: the thread
+    // sums g / a and g / a^2 (and g F where the Taylor branch gives F), the tap's constants
+    // multiply the CTA's sums once
     const cplx zN = sc.zN, bz = sc.bz, zinv = sc.zinv;
     const float dlt = sc.dlt, tx = sc.tx, npi = sc.npi, rf = sc.rf, one_m_rho = sc.one_m_rho;
     const int d0 = sc.d0;
     const float two_n = 2.f / float(Nd);
-    float qx = 0.f, qy = 0.f;
+    float s1x = 0.f, s1y = 0.f, s2x = 0.f, s2y = 0.f, ftx = 0.f, fty = 0.f;
     for (int n0 = threadIdx.x * RUN; n0 < Nd; n0 += blockDim.x * RUN) {
-      float win[RUN + DL_FIR - 1];
+      // win[i] = rs[n0 - H - o + i]; the lags' range [-H, N_d + H) plus the read-ahead
+      // to the next 16 bytes lies inside the partitions' lags (values past N_d + H meet
+      // only lags >= N_d, which are dropped)
+      constexpr int WL = (RUN + DL_SH - 1 + 3) & ~3;
+      float win[WL];
 #pragma unroll
-      for (int i = 0; i < RUN + DL_FIR - 1; ++i) {
-        const int n = n0 + i - H;   // needed for n < N_d + H only (the lag range of the tap)
-        win[i] = n < Nd + H ? rs[n] : 0.f;
+      for (int k = 0; k < WL / 4; ++k) {
+        const float4 q4 = ldg4(ra + n0 + 4 * k);
+        win[4 * k] = q4.x, win[4 * k + 1] = q4.y, win[4 * k + 2] = q4.z, win[4 * k + 3] = q4.w;
+      }
+      // g[n0 + u] = sum_jj c[jj] r[n0 + u + jj - H]: RUN independent chains
+      float gv[RUN];
+#pragma unroll
+      for (int u = 0; u < RUN; ++u) gv[u] = 0.f;
+#pragma unroll
+      for (int jp = 0; jp < DL_SH; ++jp) {
+        const float cj = csh[jp];
+#pragma unroll
+        for (int u = 0; u < RUN; ++u) gv[u] += cj * win[u + jp];
       }
       // Runs of lags away from the pole (|m| >= DL_FAR for every lag of the run) take the
       // half-angle phasor of their first lag from sincospif and rotate it by pi / N_d per lag
@@ -497,15 +522,11 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
       const bool far = mm0 >= DL_FAR || mm0 <= -(DL_FAR + RUN);
       float sh0 = 0.f, ch0 = 1.f;
       if (far) sincospif(0.5f * (dlt + float(mm0) * two_n), &sh0, &ch0);
-      const cplx t1 = {1.f + float(Nd - 1) * zN.x, float(Nd - 1) * zN.y};
 #pragma unroll
       for (int u = 0; u < RUN; ++u) {
         const int n = n0 + u;
         if (n < Nd) {
-          float g = 0.f;
-#pragma unroll
-          for (int jj = 0; jj < DL_FIR; ++jj) g += cs[jj] * win[u + jj];
-          cplx F;
+          const float g = gv[u];
           float sh = sh0, chh = ch0;
           bool taylor = false;
           if (!far) {
@@ -517,33 +538,31 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
             taylor = tx * tx + ty * ty < 0.25f;
             if (taylor) {
               // F = N^2 sum_j e_j t^j with e_j = (sum_k k^(j+1)) / (N^(j+2) j!)
-              cplx t = {tx, ty}, tp = {1.f, 0.f};
-              F = {0.f, 0.f};
+              cplx t = {tx, ty}, tp = {1.f, 0.f}, F = {0.f, 0.f};
 #pragma unroll
               for (int j = 0; j < 9; ++j) {
                 F.x += c.dl_taylor[j] * tp.x;
                 F.y += c.dl_taylor[j] * tp.y;
                 tp = cm(tp, t);
               }
-              F.x *= float(Nd) * float(Nd);
-              F.y *= float(Nd) * float(Nd);
+              const float n2 = float(Nd) * float(Nd);
+              ftx += g * (F.x * n2);
+              fty += g * (F.y * n2);
             } else {
               sincospif(0.5f * phf, &sh, &chh);
             }
           }
           if (!taylor) {
-            // a = 1 - q = (1 - rho) + 2 rho sin^2(ph/2) - i rho sin(ph);
-            // F = (-a t1 - (z^N - 1)) / a^2 = -(1/a) (t1 + (z^N - 1) / a)
-            const cplx a = {one_m_rho + 2.f * rf * sh * sh, -rf * 2.f * sh * chh};
-            const float ia = 1.f / (a.x * a.x + a.y * a.y);
-            const cplx ainv = {a.x * ia, -a.y * ia};
-            const cplx w2 = cm(bz, ainv);
-            const cplx w3 = cm(ainv, cplx{t1.x + w2.x, t1.y + w2.y});
-            F = {-w3.x, -w3.y};
+            // a = 1 - q = (1 - rho) + 2 rho sin^2(ph/2) - i rho sin(ph); b = 1 / a
+            const float ax = one_m_rho + 2.f * rf * sh * sh, ay = -rf * 2.f * sh * chh;
+            const float ia = __frcp_rn(ax * ax + ay * ay);
+            const float bx = ax * ia, by = -ay * ia;
+            const float gx = g * bx, gy = g * by;
+            s1x += gx;
+            s1y += gy;
+            s2x += gx * bx - gy * by;   // g Re(b^2)
+            s2y += gx * by + gy * bx;   // g Im(b^2)
           }
-          const cplx ph2 = cm(F, zinv);
-          qx += g * ph2.x;
-          qy += g * ph2.y;
           if (far) {   // the next lag's half-angle phasor
             const float s2 = sh * sc.rot_c + ch0 * sc.rot_s;
             ch0 = ch0 * sc.rot_c - sh * sc.rot_s;
@@ -552,11 +571,18 @@ __global__ void __launch_bounds__(256) k_delay_grad(DevCtx c, int item0, int n_i
         }
       }
     }
-    float vq[2] = {qx, qy};
-    block_sum<2>(vq, red);
+    float v1[4] = {s1x, s1y, s2x, s2y};
+    block_sum<4>(v1, red);
+    float v2[2] = {ftx, fty};
+    block_sum<2>(v2, red);
     if (threadIdx.x == 0) {
-      out[0] = vq[0];
-      out[1] = -vq[1];
+      // sum g F = T - t1 S1 - (z^N - 1) S2; Q = (sum g F) / (N z)
+      const double t1x = 1.0 + double(Nd - 1) * zN.x, t1y = double(Nd - 1) * zN.y;
+      const double S1x = v1[0], S1y = v1[1], S2x = v1[2], S2y = v1[3];
+      const double Fx = double(v2[0]) - (t1x * S1x - t1y * S1y) - (double(bz.x) * S2x - double(bz.y) * S2y);
+      const double Fy = double(v2[1]) - (t1x * S1y + t1y * S1x) - (double(bz.x) * S2y + double(bz.y) * S2x);
+      out[0] = float(Fx * zinv.x - Fy * zinv.y);
+      out[1] = float(-(Fx * zinv.y + Fy * zinv.x));
     }
   }
 }

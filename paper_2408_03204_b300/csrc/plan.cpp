@@ -158,10 +158,11 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     p->dl_nd = p->dl_slot = opts.sample_rate / 10;   // 100 ms
   }
   {
-    // lags [-B, (P-1) B) must cover [-H, reach + H), reach = (taps-1) slot + N_d
-    const int64_t reach = int64_t(p->dl_taps - 1) * p->dl_slot + p->dl_nd + (DL_FIR - 1) / 2;
+    // lags [-B, (P-1) B) must cover [-H, reach + H), reach = (taps-1) slot + N_d, plus the
+    // z-gradient's read-ahead of up to 32 lags (float4 windows of its last run)
+    const int64_t reach = int64_t(p->dl_taps - 1) * p->dl_slot + p->dl_nd + (DL_FIR - 1) / 2 + 32;
     p->dl_P = int32_t(1 + (reach + DL_B - 1) / DL_B);
-    if (p->dl_P > DL_PMAX) return fail(GRAFX_EINVAL, "delay slots too long for this sample rate (at most 65 kHz)");
+    if (p->dl_P > DL_PMAX) return fail(GRAFX_EINVAL, "delay slots too long for this sample rate (at most 63.46 kHz)");
   }
   if (opts.reverb_layout == GRAFX_REVERB_PAPER) {
     p->rv_paper = 1;
