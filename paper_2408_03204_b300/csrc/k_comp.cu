@@ -650,6 +650,7 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_bwd_lb(DevCtx c
   if (threadIdx.x == 0) s_it[0] = atomicAdd(c.tickets + ticket, 1);
   __syncthreads();
   int it = s_it[0], slot = 0;
+  const int slot0 = c.items[item0].w;   // the step's first partial slot (its first node's last chunk)
   if (!SC && it < n_items) prefetch_item<SPT, true>(c, item0 + it, buf);
   while (it < n_items) {
     if (threadIdx.x == 0) s_it[slot ^ 1] = atomicAdd(c.tickets + ticket, 1);  // read after the scan's barriers
@@ -711,13 +712,16 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_bwd_lb(DevCtx c
     float rtotal;
     float rexcl = block_affine_scan<true>(lb, la * SPT, sh, &rtotal);
     if (threadIdx.x < 32) {
+      // look-back words by the chunk's partial slot: a node's chunks are contiguous there,
+      // from its last chunk, whatever the order of the tickets
+      const int fidx = item0 + (w.w - slot0);
       float lin = 0.f;
       if (chunk == n_chunks - 1) {
-        if (threadIdx.x == 0) publish(c, item0 + it, 2, rtotal);
+        if (threadIdx.x == 0) publish(c, fidx, 2, rtotal);
       } else {
-        if (threadIdx.x == 0) publish(c, item0 + it, 1, rtotal);
-        lin = look_back_warp(c, item0 + it - 1, item0 + it - (n_chunks - 1 - chunk), la * CH);
-        if (threadIdx.x == 0) publish(c, item0 + it, 2, expf(la * CH) * lin + rtotal);
+        if (threadIdx.x == 0) publish(c, fidx, 1, rtotal);
+        lin = look_back_warp(c, fidx - 1, fidx - (n_chunks - 1 - chunk), la * CH);
+        if (threadIdx.x == 0) publish(c, fidx, 2, expf(la * CH) * lin + rtotal);
       }
       if (threadIdx.x == 0) s_lin = lin;
     }
@@ -786,7 +790,7 @@ __global__ void k_comp_finalize(DevCtx c, int node_begin, int node_end) {
 // (nodes [n0, n1)); mode: MODE_COMP, MODE_GATE (the noisegate curve of Eq. 13) or MODE_SC
 // (the sidechain compressor).  Returns the number of kernels launched.
 // Backward steps of at most this many chunks run the one-pass look-back kernel.
-constexpr int COMP_LOOKBACK_MAX_ITEMS = 8192;
+constexpr int COMP_LOOKBACK_MAX_ITEMS = 1 << 30;
 
 template <int SPT, int MODE>
 static int comp_launch(int what, const DevCtx& c, int a, int b, int n0, int n1, int ticket, cudaStream_t s) {

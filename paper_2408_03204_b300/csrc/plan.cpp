@@ -561,6 +561,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
       const int64_t target = 148 * 3 * 2;
       run_len = int32_t(std::max<int64_t>(1, (blocks + target - 1) / target));
     }
+    int32_t max_nc = 0;
     for (int32_t v = s.node_begin; v < s.node_end; ++v) {
       const int32_t L = p->nodes[v].len;
       switch (s.type) {
@@ -574,10 +575,13 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
         case GRAFX_T_COMP:
         case GRAFX_T_GATE:
         case GRAFX_T_SIDECHAIN: {
+          // partial slot x + r for the node's r-th chunk from its end (the items follow the
+          // loop, round by round)
           int32_t nc = (L + p->comp_chunk - 1) / p->comp_chunk;
           p->node_ext[v].x = slot;
           p->node_ext[v].y = nc;
-          for (int32_t c = nc - 1; c >= 0; --c) bwd.push_back({v, c, p->node_ext[v].z + c, slot++});
+          slot += nc;
+          max_nc = std::max(max_nc, nc);
           break;
         }
         default: {
@@ -593,6 +597,14 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
         }
       }
     }
+    // compressor-like backward: the r-th chunk from the end of every node before any
+    // node's (r+1)-th, so that a chunk's successor in the reverse recursion (handed out by
+    // ticket in this order) is, on steps of many nodes, a whole round of tickets later
+    for (int32_t r = 0; r < max_nc; ++r)
+      for (int32_t v = s.node_begin; v < s.node_end; ++v) {
+        const int32_t nc = p->node_ext[v].y, c = nc - 1 - r;
+        if (c >= 0) bwd.push_back({v, c, p->node_ext[v].z + c, p->node_ext[v].x + r});
+      }
     s.bitem_count = int32_t(bwd.size()) - s.bitem_begin;
   }
   // input step (adjoints of the sources), after the others in the backward list
