@@ -514,6 +514,88 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_apply(DevCtx c,
   cp_async_wait_all();
 }
 
+// Forward in one pass: chunks handed out by an atomic ticket in chunk-major order (the
+// c-th chunk of every node of the step before any node's (c+1)-th); each publishes its
+// aggregate (state at its end with zero entering), takes the state entering it from the
+// chunks before it by a decoupled look-back over the node's chunk slots (flags indexed by
+// the chunk's global id, contiguous per node), publishes its inclusive state, stores the
+// entering state for the backward and applies the gain.  The inputs are read once.
+// Bounded waits record ST_TIMEOUT.
+template <int SPT, int MODE>
+__global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_fwd_lb(DevCtx c, int item0, int n_items, int ticket) {
+  constexpr int CH = 256 * SPT;
+  constexpr bool GATE = MODE == MODE_GATE, SC = MODE == MODE_SC;
+  extern __shared__ __align__(16) float buf[];   // 2 CH floats: the next ticket's u (prefetched)
+  __shared__ float sh[32];
+  __shared__ int s_it[2];
+  __shared__ float s_cin;
+  if (threadIdx.x == 0) s_it[0] = atomicAdd(c.tickets + ticket, 1);
+  __syncthreads();
+  int it = s_it[0], slot = 0;
+  const int chunk0 = c.items[item0].z;   // the step's first chunk (its first node's chunk 0)
+  if (!SC && it < n_items) prefetch_item<SPT, false>(c, item0 + it, buf);
+  while (it < n_items) {
+    if (threadIdx.x == 0) s_it[slot ^ 1] = atomicAdd(c.tickets + ticket, 1);  // read after the scan's barriers
+    const int4_ w = c.items[item0 + it];
+    const int v = w.x;
+    const NodeDev nd = c.nodes[v];
+    const float* p = c.params + nd.prow * 4;
+    const float alpha = p[0];
+    const KneeCoef kq = knee_coef(p[1], p[2], p[3]);
+    const float la = logf(alpha);
+    const int t = w.y * CH + threadIdx.x * SPT;
+    float ul[SPT], ur[SPT], x[SPT], g[SPT];
+    cp_async_wait_all();
+    if constexpr (SC) {
+      load_range<SPT>(c, c.csr_ptr[v], c.in1_begin[v], nd, t, ul, ur);   // main (input 0)
+      env_input<SPT, MODE>(c, v, nd, t, x);                               // key (input 1)
+    } else {
+      fetch_rows<SPT>(c, v, nd, t, buf, ul, ur, false);
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
+    }
+    float b = 0.f;
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) b = alpha * b + (1.f - alpha) * x[i];
+    float total;
+    const float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
+    const int next = s_it[slot ^ 1];
+    // every thread has read its own slots of buf (before the scan's barriers)
+    if (!SC && next < n_items) prefetch_item<SPT, false>(c, item0 + next, buf);
+    if (threadIdx.x < 32) {
+      const int fidx = item0 + (w.z - chunk0);
+      float cin = 0.f;
+      if (w.y == 0) {
+        if (threadIdx.x == 0) publish(c, fidx, 2, total);
+      } else {
+        if (threadIdx.x == 0) publish(c, fidx, 1, total);
+        cin = look_back_warp(c, fidx - 1, fidx - w.y, la * CH);
+        if (threadIdx.x == 0) publish(c, fidx, 2, expf(la * CH) * cin + total);
+      }
+      if (threadIdx.x == 0) {
+        s_cin = cin;
+        c.comp_carry[w.z] = cin;   // the state entering the chunk, for the backward
+      }
+    }
+    __syncthreads();
+    const float cin_t = excl + expf(la * float(SPT * threadIdx.x)) * s_cin;
+    envelope<SPT>(x, alpha, cin_t, g);
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) {
+      float gu = ln_env(g[i]);
+      Knee k = GATE ? gate_knee(gu, kq) : knee(gu, kq);
+      float gain = exp_gain(k.gy - gu);
+      ul[i] *= gain;
+      ur[i] *= gain;
+    }
+    store_chunk<SPT>(yrow_w(c, nd), nd, t, ul, ur);
+    __syncthreads();   // sh and s_cin are reused by the next ticket
+    it = next;
+    slot ^= 1;
+  }
+  cp_async_wait_all();
+}
+
 // Backward of one chunk.  APPLY = false (pass 1): the chunk's reverse state at its start
 // with zero entering from its end, to comp_agg.  APPLY = true (pass 3): lambda from the
 // state entering from the right (comp_agg after the reverse scan), the input adjoints
@@ -801,14 +883,17 @@ static int comp_launch(int what, const DevCtx& c, int a, int b, int n0, int n1, 
     cudaFuncSetAttribute(k_comp_back<SPT, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem);
     cudaFuncSetAttribute(k_comp_back<SPT, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem);
     cudaFuncSetAttribute(k_comp_bwd_lb<SPT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem);
+    cudaFuncSetAttribute(k_comp_fwd_lb<SPT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd_smem);
     init = true;
   }
   if (what < 0) return 0;
   const int scan_grid = ((n1 - n0) * 32 + 255) / 256;
   if (what == 0) {
-    k_comp_agg<SPT, MODE><<<grid_size(b, 8), 256, fwd_smem, s>>>(c, a, b);
-    k_comp_scan<false><<<scan_grid, 256, 0, s>>>(c, n0, n1, CH, c.comp_agg, c.comp_carry);
-    k_comp_apply<SPT, MODE><<<grid_size(b, 8), 256, fwd_smem, s>>>(c, a, b);
+    // the step's look-back words and its ticket start at zero
+    cudaMemsetAsync(c.flags + a, 0, sizeof(unsigned long long) * size_t(b), s);
+    cudaMemsetAsync(c.tickets + ticket, 0, sizeof(int32_t), s);
+    k_comp_fwd_lb<SPT, MODE><<<grid_size(b, 4), 256, fwd_smem, s>>>(c, a, b, ticket);
+    return 1;
   } else if (b <= COMP_LOOKBACK_MAX_ITEMS) {
     // the step's look-back words and its ticket start at zero
     cudaMemsetAsync(c.flags + a, 0, sizeof(unsigned long long) * size_t(b), s);

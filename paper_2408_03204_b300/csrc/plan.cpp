@@ -455,6 +455,7 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     s.node_begin = p->step_ptr[k];
     s.node_end = p->step_ptr[k + 1];
     s.fitem_begin = int32_t(fwd.size());
+    int32_t fmax_nc = 0;
     for (int32_t v = s.node_begin; v < s.node_end; ++v) {
       const int32_t L = p->nodes[v].len;
       switch (s.type) {
@@ -497,16 +498,25 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
         case GRAFX_T_COMP:
         case GRAFX_T_GATE:
         case GRAFX_T_SIDECHAIN: {
+          // chunk ids contiguous per node; the items follow the loop, round by round
           int32_t nc = (L + p->comp_chunk - 1) / p->comp_chunk;
           p->node_ext[v].z = chunk_id;
-          for (int32_t c = 0; c < nc; ++c) fwd.push_back({v, c, chunk_id + c, 0});
           chunk_id += nc;
+          fmax_nc = std::max(fmax_nc, nc);
           break;
         }
         default:
           for (int32_t t0 = 0; t0 < L; t0 += EW_TILE) fwd.push_back({v, t0, 0, 0});
       }
     }
+    // compressor-like forward: the c-th chunk of every node before any node's (c+1)-th
+    // (the one-pass look-back takes its tickets in this order: a chunk's predecessor is,
+    // on steps of many nodes, a whole round of tickets earlier)
+    for (int32_t ck = 0; ck < fmax_nc; ++ck)
+      for (int32_t v = s.node_begin; v < s.node_end; ++v) {
+        const int32_t nc = (p->nodes[v].len + p->comp_chunk - 1) / p->comp_chunk;
+        if (ck < nc) fwd.push_back({v, ck, p->node_ext[v].z + ck, 0});
+      }
     s.fitem_count = int32_t(fwd.size()) - s.fitem_begin;
   }
   for (int32_t k = N; k >= 1; --k) {
