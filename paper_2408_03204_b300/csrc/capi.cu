@@ -55,7 +55,6 @@ DevCtx make_ctx(const Plan* p, const float* src, float* out, const float* d_out,
   c.eq_aux = at<float>(p, p->ws.eq_aux);
   c.eq_bandpart = at<float>(p, p->ws.eq_bandpart);
   c.comp_carry = at<float>(p, p->ws.comp_carry);
-  c.comp_agg = at<float>(p, p->ws.comp_agg);
   c.dl_aux = at<float>(p, p->ws.dl_aux);
   c.dl_spec = at<float2>(p, p->ws.dl_spec);
   c.dl_R = at<float2>(p, p->ws.dl_R);

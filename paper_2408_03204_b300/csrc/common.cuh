@@ -37,7 +37,6 @@ struct DevCtx {
   float2* eq_uspec;    // per EQ block: the forward's spectrum of its input window (M bins)
   float* eq_ola;       // per EQ block: input-adjoint head and tail [2][2 ch][H] (overlap-add)
   float* comp_carry;   // per compressor chunk: the envelope state entering it (forward)
-  float* comp_agg;     // per compressor chunk: its aggregate, then the reverse state entering it
   float* dl_aux;        // per delay node: [channel][tap][39 taps, delay] (2 dl_taps 40 floats)
   float2* dl_spec;      // block spectra of the lag correlation
   float2* dl_R;         // per delay node and lag partition: accumulated spectra

@@ -5,23 +5,23 @@
 // One work item is a chunk of CH = 256 * SPT samples of one node.  Inside a chunk:
 // every thread runs the recursion over its SPT samples with zero initial state, a
 // warp-shuffle scan and a cross-warp scan combine the per-thread states with the
-// decay a^SPT.  Across chunks (the render path): three passes, with no chunk waiting
-// for another -- every chunk's zero-start end state (its aggregate), a per-node scan of
-// the aggregates with the decay of one chunk, then every chunk from its entering state.
-// The forward pass stores each chunk's entering state (one float) so the backward pass
-// can recompute g[n] exactly.
+// decay a^SPT.  Across chunks, one pass with a decoupled look-back: each chunk publishes
+// its zero-start end state (its aggregate), then its inclusive end state once its carry
+// is known; one warp of a chunk reads the 32 preceding states of its node at once and
+// walks back until it meets an inclusive one.  Chunks are handed out by an atomic ticket
+// in chunk-major order (the c-th chunk of every node of the step before any node's
+// (c+1)-th), so every chunk waited on is held by a CTA that took its ticket earlier and,
+// on steps of many nodes, has long finished; every wait is bounded and records
+// ST_TIMEOUT on expiry.  The forward stores each chunk's entering state (one float) so
+// that the backward can recompute g[n] exactly.
 //
-// Backward: ybar gives a_n = dL/dg[n]; lambda[n] = a_n + alpha lambda[n+1] is the
-// same three passes run in reverse; ubar_x = k ybar_x + 2 u_m (1 - alpha) lambda and the
-// parameter partials (sum lambda (g[n-1] - x[n]) for alpha, sum Gybar dGy/dT|W|R) go to
-// one slot per chunk.
+// Backward: ybar gives a_n = dL/dg[n]; lambda[n] = a_n + alpha lambda[n+1] runs the same
+// way from each node's end (its own look-back words); ubar_x = k ybar_x + 2 u_m
+// (1 - alpha) lambda and the parameter partials (sum lambda (g[n-1] - x[n]) for alpha,
+// sum Gybar dGy/dT|W|R) go to one slot per chunk.
 //
-// The allocation-free single-row forward at the end of this file keeps one pass over the
-// signal with a decoupled look-back instead: each chunk publishes its zero-start end
-// state, then its inclusive end state once its carry is known; one warp of a chunk reads
-// the 32 preceding states at once and walks back until it meets an inclusive one.  Chunks
-// are handed out by an atomic ticket in chunk order, so every chunk waited on is held by
-// a CTA that is already running; every wait is bounded and records ST_TIMEOUT on expiry.
+// The allocation-free single-row forward at the end of this file is the same forward
+// over one row, with the chunks in order.
 #include <cstring>
 #include <mutex>
 
@@ -373,12 +373,12 @@ __device__ __forceinline__ void envelope(const float* x, float alpha, float cin,
 
 // The envelope recursion g[n] = alpha g[n-1] + (1 - alpha) x[n] is linear, so a chunk's
 // effect on the chunks after it is one number: its state at the chunk's end with zero
-// entering it (its aggregate).  Forward: (1) every chunk's aggregate (k_comp_agg), (2)
-// per node, the state entering every chunk by a scan over its aggregates with the decay
-// D = alpha^CH of one chunk (k_comp_scan, one warp per node), (3) every chunk again
-// from its entering state: envelope, gain, output (k_comp_apply).  The backward does
-// the same for the reverse recursion lambda[n] = a[n] + alpha lambda[n+1].  No chunk
-// waits for another; the inputs are read twice.
+// entering it (its aggregate).  Forward and backward each run in one pass: every chunk
+// publishes its aggregate and takes the state entering it from the chunks before it
+// (after it, for the reverse recursion lambda[n] = a[n] + alpha lambda[n+1] of the
+// backward) by a decoupled look-back; the chunks are handed out in chunk-major order, so
+// that on steps of many nodes a chunk's neighbour in the recursion has finished long
+// before it is needed.
 
 // The envelope input x[n] of this thread's samples: the squared mid of the node's input
 // (the compressor and the noisegate) or of its key, input 1 (the sidechain compressor).
@@ -392,126 +392,6 @@ __device__ __forceinline__ void env_input(const DevCtx& c, int v, const NodeDev&
     const float m = l[i] + r[i];
     x[i] = m * m;
   }
-}
-
-// Forward pass 1: the chunk's envelope state at its end with zero entering it.
-template <int SPT, int MODE>
-__global__ void __launch_bounds__(256, SPT >= 16 ? 3 : 4) k_comp_agg(DevCtx c, int item0, int n_items) {
-  constexpr int CH = 256 * SPT;
-  extern __shared__ __align__(16) float buf[];   // 2 CH floats: the next chunk's u (prefetched)
-  __shared__ float sh[32];
-  if (MODE != MODE_SC && blockIdx.x < n_items) prefetch_item<SPT, false>(c, item0 + blockIdx.x, buf);
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const int4_ w = c.items[item0 + it];
-    const int v = w.x;
-    const NodeDev nd = c.nodes[v];
-    const float alpha = c.params[nd.prow * 4];
-    const float la = logf(alpha);
-    const int t = w.y * CH + threadIdx.x * SPT;
-    float x[SPT];
-    cp_async_wait_all();
-    if constexpr (MODE == MODE_SC) {
-      env_input<SPT, MODE>(c, v, nd, t, x);
-    } else {
-      float l[SPT], r[SPT];
-      fetch_rows<SPT>(c, v, nd, t, buf, l, r, false);
-#pragma unroll
-      for (int i = 0; i < SPT; ++i) { const float m = l[i] + r[i]; x[i] = m * m; }
-      // every thread has read its own slots: start the next chunk's copies into them
-      if (it + int(gridDim.x) < n_items) prefetch_item<SPT, false>(c, item0 + it + gridDim.x, buf);
-    }
-    float b = 0.f;
-#pragma unroll
-    for (int i = 0; i < SPT; ++i) b = alpha * b + (1.f - alpha) * x[i];
-    float total;
-    block_affine_scan<false>(b, la * SPT, sh, &total);
-    if (threadIdx.x == 0) c.comp_agg[w.z] = total;
-    __syncthreads();   // sh is reused by the next item
-  }
-  cp_async_wait_all();
-}
-
-// Pass 2: per node (one warp), the state entering every chunk from its chunks' aggregates
-// src[z0 + j] (z0 = the node's first chunk slot): forward, enter_j = D enter_(j-1) +
-// src[j-1] with enter_0 = 0; REVERSE, the same from the node's last chunk down.  Written
-// to dst[z0 + j] (dst may be src: every lane reads its chunk before writing it).
-template <bool REVERSE>
-__global__ void __launch_bounds__(256) k_comp_scan(DevCtx c, int node_begin, int node_end, int ch_len,
-                                                   const float* src, float* dst) {
-  const int lane = threadIdx.x & 31;
-  const int v = node_begin + int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (v >= node_end) return;   // the whole warp
-  const NodeDev nd = c.nodes[v];
-  const int z0 = c.ext[v].z, nc = (nd.len + ch_len - 1) / ch_len;
-  const float lc = logf(c.params[nd.prow * 4]) * float(ch_len);   // ln D
-  const float d_lane = expf(lc * float(lane)), d_32 = expf(lc * 32.f);
-  float run = 0.f;   // state entering this block of 32 chunks (in scan order)
-  for (int base = 0; base < nc; base += 32) {
-    const int q = base + lane;
-    const int j = REVERSE ? nc - 1 - q : q;
-    const float a = q < nc ? src[z0 + j] : 0.f;
-    float s = a, dd = expf(lc);   // inclusive: s_l = D s_(l-1) + a_l; dd = D^d
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const float o = __shfl_up_sync(0xffffffffu, s, d);
-      if (lane >= d) s += dd * o;
-      dd *= dd;
-    }
-    float prev = __shfl_up_sync(0xffffffffu, s, 1);
-    if (lane == 0) prev = 0.f;
-    if (q < nc) dst[z0 + j] = d_lane * run + prev;
-    run = d_32 * run + __shfl_sync(0xffffffffu, s, 31);
-  }
-}
-
-// Forward pass 3: the chunk from its entering state (stored for the backward).
-template <int SPT, int MODE>
-__global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_apply(DevCtx c, int item0, int n_items) {
-  constexpr int CH = 256 * SPT;
-  constexpr bool GATE = MODE == MODE_GATE, SC = MODE == MODE_SC;
-  extern __shared__ __align__(16) float buf[];   // 2 CH floats: the next chunk's u (prefetched)
-  __shared__ float sh[32];
-  if (!SC && blockIdx.x < n_items) prefetch_item<SPT, false>(c, item0 + blockIdx.x, buf);
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const int4_ w = c.items[item0 + it];
-    const int v = w.x;
-    const NodeDev nd = c.nodes[v];
-    const float* p = c.params + nd.prow * 4;
-    const float alpha = p[0];
-    const KneeCoef kq = knee_coef(p[1], p[2], p[3]);
-    const float la = logf(alpha);
-    const int t = w.y * CH + threadIdx.x * SPT;
-    float ul[SPT], ur[SPT], x[SPT], g[SPT];
-    cp_async_wait_all();
-    if constexpr (SC) {
-      load_range<SPT>(c, c.csr_ptr[v], c.in1_begin[v], nd, t, ul, ur);   // main (input 0)
-      env_input<SPT, MODE>(c, v, nd, t, x);                               // key (input 1)
-    } else {
-      fetch_rows<SPT>(c, v, nd, t, buf, ul, ur, false);
-#pragma unroll
-      for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
-      if (it + int(gridDim.x) < n_items) prefetch_item<SPT, false>(c, item0 + it + gridDim.x, buf);
-    }
-    float b = 0.f;
-#pragma unroll
-    for (int i = 0; i < SPT; ++i) b = alpha * b + (1.f - alpha) * x[i];
-    float total;
-    const float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
-    const float carry = c.comp_carry[w.z];
-    const float cin = excl + expf(la * float(SPT * threadIdx.x)) * carry;
-    envelope<SPT>(x, alpha, cin, g);
-#pragma unroll
-    for (int i = 0; i < SPT; ++i) {
-      float gu = ln_env(g[i]);
-      Knee k = GATE ? gate_knee(gu, kq) : knee(gu, kq);
-      float gain = exp_gain(k.gy - gu);
-      ul[i] *= gain;
-      ur[i] *= gain;
-    }
-    store_chunk<SPT>(yrow_w(c, nd), nd, t, ul, ur);
-    __syncthreads();   // sh is reused by the next item
-  }
-  cp_async_wait_all();
 }
 
 // Forward in one pass: chunks handed out by an atomic ticket in chunk-major order (the
@@ -596,129 +476,11 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_fwd_lb(DevCtx c
   cp_async_wait_all();
 }
 
-// Backward of one chunk.  APPLY = false (pass 1): the chunk's reverse state at its start
-// with zero entering from its end, to comp_agg.  APPLY = true (pass 3): lambda from the
-// state entering from the right (comp_agg after the reverse scan), the input adjoints
-// and the parameter-gradient partials of the chunk.
-template <int SPT, int MODE, bool APPLY>
-__global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_back(DevCtx c, int item0, int n_items) {
-  constexpr int CH = 256 * SPT;
-  constexpr bool GATE = MODE == MODE_GATE, SC = MODE == MODE_SC;
-  extern __shared__ __align__(16) float buf[];   // 4 CH floats: the next chunk's u and ybar
-  __shared__ float sh[32];
-  __shared__ float glast[256];
-  __shared__ float red[4 * 32];
-  if (!SC && blockIdx.x < n_items) prefetch_item<SPT, true>(c, item0 + blockIdx.x, buf);
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const int4_ w = c.items[item0 + it];
-    const int v = w.x;
-    const NodeDev nd = c.nodes[v];
-    const float* p = c.params + nd.prow * 4;
-    const float alpha = p[0];
-    const KneeCoef kq = knee_coef(p[1], p[2], p[3]);
-    const float la = logf(alpha);
-    const int t = w.y * CH + threadIdx.x * SPT;
-    float ul[SPT], ur[SPT], bl[SPT], br[SPT], x[SPT], g[SPT], a[SPT];
-    float km[SC ? SPT : 1];   // sidechain: the key's mid l + r
-    cp_async_wait_all();
-    if constexpr (SC) {
-      float kr[SPT];
-      load_range<SPT>(c, c.csr_ptr[v], c.in1_begin[v], nd, t, ul, ur);      // main (input 0)
-      load_range<SPT>(c, c.in1_begin[v], c.csr_ptr[v + 1], nd, t, km, kr);  // key (input 1)
-#pragma unroll
-      for (int i = 0; i < SPT; ++i) { km[i] += kr[i]; x[i] = km[i] * km[i]; }
-      load_chunk<SPT>(c, v, nd, t, bl, br, true);
-    } else {
-      fetch_rows<SPT>(c, v, nd, t, buf, ul, ur, false);
-      fetch_rows<SPT>(c, v, nd, t, buf + 2 * CH, bl, br, true);
-#pragma unroll
-      for (int i = 0; i < SPT; ++i) { float m = ul[i] + ur[i]; x[i] = m * m; }
-      if (it + int(gridDim.x) < n_items) prefetch_item<SPT, true>(c, item0 + it + gridDim.x, buf);
-    }
-    // the envelope from the forward's stored chunk state (same arithmetic as the forward)
-    const float carry_g = c.comp_carry[w.z];
-    float b = 0.f;
-#pragma unroll
-    for (int i = 0; i < SPT; ++i) b = alpha * b + (1.f - alpha) * x[i];
-    float total;
-    const float excl = block_affine_scan<false>(b, la * SPT, sh, &total);
-    const float cin = excl + expf(la * float(SPT * threadIdx.x)) * carry_g;
-    envelope<SPT>(x, alpha, cin, g);
-    // local adjoints
-    float gain[SPT], dT = 0.f, dW = 0.f, dR = 0.f;
-#pragma unroll
-    for (int i = 0; i < SPT; ++i) {
-      float gu = ln_env(g[i]);
-      Knee k = GATE ? gate_knee(gu, kq) : knee(gu, kq);
-      gain[i] = exp_gain(k.gy - gu);
-      const float gyb = (bl[i] * ul[i] + br[i] * ur[i]) * gain[i];
-      a[i] = env_div(gyb * (k.dgu - 1.f), g[i] + COMP_EPS);
-      dT += gyb * k.dt;
-      dW += gyb * k.dw;
-      dR += gyb * k.dr;
-    }
-    // reverse scan lambda[n] = a[n] + alpha lambda[n+1]
-    float lb = 0.f;
-#pragma unroll
-    for (int i = SPT - 1; i >= 0; --i) lb = a[i] + alpha * lb;
-    __syncthreads();   // sh reuse
-    float rtotal;
-    const float rexcl = block_affine_scan<true>(lb, la * SPT, sh, &rtotal);
-    if constexpr (!APPLY) {
-      if (threadIdx.x == 0) c.comp_agg[w.z] = rtotal;
-      __syncthreads();   // sh is reused by the next item
-      continue;
-    }
-    glast[threadIdx.x] = g[SPT - 1];
-    __syncthreads();
-    // state entering this thread from the right: within-chunk part + the chunk's state
-    const float lin_t = rexcl + expf(la * float(SPT * (255 - threadIdx.x))) * c.comp_agg[w.z];
-    float lam[SPT];
-    {
-      float s = lin_t;
-#pragma unroll
-      for (int i = SPT - 1; i >= 0; --i) {
-        s = a[i] + alpha * s;
-        lam[i] = s;
-      }
-    }
-    float gprev = threadIdx.x > 0 ? glast[threadIdx.x - 1] : carry_g;
-    float dA = 0.f;
-    if constexpr (SC) {
-      // input 0 (main): gain ybar; input 1 (key): 2 (k_l + k_r)(1 - alpha) lambda on both channels
-#pragma unroll
-      for (int i = 0; i < SPT; ++i) {
-        dA += lam[i] * (gprev - x[i]);
-        gprev = g[i];
-        bl[i] *= gain[i];
-        br[i] *= gain[i];
-        km[i] = 2.f * km[i] * (1.f - alpha) * lam[i];
-      }
-      store_chunk<SPT>(arow_w(c, nd), nd, t, bl, br);
-      store_chunk<SPT>(arow_w(c, nd) + nd.rstride, nd, t, km, km);
-    } else {
-#pragma unroll
-      for (int i = 0; i < SPT; ++i) {
-        dA += lam[i] * (gprev - x[i]);
-        gprev = g[i];
-        float xb2 = 2.f * (ul[i] + ur[i]) * (1.f - alpha) * lam[i];
-        bl[i] = gain[i] * bl[i] + xb2;
-        br[i] = gain[i] * br[i] + xb2;
-      }
-      store_chunk<SPT>(arow_w(c, nd), nd, t, bl, br);
-    }
-    float acc[4] = {dA, dT, dW, dR};
-    block_sum<4>(acc, red);
-    if (threadIdx.x == 0) c.partial[w.w] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    __syncthreads();
-  }
-  cp_async_wait_all();
-}
-
-// Backward of small steps in one pass: the reverse recursion's state entering a chunk
-// comes from the chunks after it by a decoupled look-back (chunks handed out by an
-// atomic ticket from the end of each node; bounded waits record ST_TIMEOUT).  On steps
-// of few chunks the look-back chains stay short and one pass beats three.
+// Backward in one pass: the reverse recursion's state entering a chunk comes from the
+// chunks after it by a decoupled look-back (chunks handed out by an atomic ticket in
+// chunk-major order from each node's end; the look-back words indexed by the chunk's
+// partial slot, contiguous per node from its last chunk; bounded waits record
+// ST_TIMEOUT).
 template <int SPT, int MODE>
 __global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_bwd_lb(DevCtx c, int item0, int n_items, int ticket) {
   constexpr int CH = 256 * SPT;
@@ -871,56 +633,38 @@ __global__ void k_comp_finalize(DevCtx c, int node_begin, int node_end) {
 // what: 0 forward (items [a, a + b), nodes [n0, n1)), 1 backward (the same), 2 finalize
 // (nodes [n0, n1)); mode: MODE_COMP, MODE_GATE (the noisegate curve of Eq. 13) or MODE_SC
 // (the sidechain compressor).  Returns the number of kernels launched.
-// Backward steps of at most this many chunks run the one-pass look-back kernel.
-constexpr int COMP_LOOKBACK_MAX_ITEMS = 1 << 30;
-
 template <int SPT, int MODE>
-static int comp_launch(int what, const DevCtx& c, int a, int b, int n0, int n1, int ticket, cudaStream_t s) {
+static int comp_launch(int what, const DevCtx& c, int a, int b, int ticket, cudaStream_t s) {
   constexpr int CH = 256 * SPT;
   constexpr int fwd_smem = 2 * CH * sizeof(float), bwd_smem = 4 * CH * sizeof(float);
   static bool init = false;
   if (!init) {   // first call (also the attributes-only call made before a stream capture)
-    cudaFuncSetAttribute(k_comp_back<SPT, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem);
-    cudaFuncSetAttribute(k_comp_back<SPT, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem);
     cudaFuncSetAttribute(k_comp_bwd_lb<SPT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem);
     cudaFuncSetAttribute(k_comp_fwd_lb<SPT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd_smem);
     init = true;
   }
-  if (what < 0) return 0;
-  const int scan_grid = ((n1 - n0) * 32 + 255) / 256;
-  if (what == 0) {
-    // the step's look-back words and its ticket start at zero
-    cudaMemsetAsync(c.flags + a, 0, sizeof(unsigned long long) * size_t(b), s);
-    cudaMemsetAsync(c.tickets + ticket, 0, sizeof(int32_t), s);
-    k_comp_fwd_lb<SPT, MODE><<<grid_size(b, 4), 256, fwd_smem, s>>>(c, a, b, ticket);
-    return 1;
-  } else if (b <= COMP_LOOKBACK_MAX_ITEMS) {
-    // the step's look-back words and its ticket start at zero
-    cudaMemsetAsync(c.flags + a, 0, sizeof(unsigned long long) * size_t(b), s);
-    cudaMemsetAsync(c.tickets + ticket, 0, sizeof(int32_t), s);
-    k_comp_bwd_lb<SPT, MODE><<<grid_size(b, 3), 256, bwd_smem, s>>>(c, a, b, ticket);
-    return 1;
-  } else {
-    k_comp_back<SPT, MODE, false><<<grid_size(b, 4), 256, bwd_smem, s>>>(c, a, b);
-    k_comp_scan<true><<<scan_grid, 256, 0, s>>>(c, n0, n1, CH, c.comp_agg, c.comp_agg);
-    k_comp_back<SPT, MODE, true><<<grid_size(b, 4), 256, bwd_smem, s>>>(c, a, b);
-  }
-  return 3;
+  if (what < 0 || b <= 0) return 0;
+  // the step's look-back words and its ticket start at zero
+  cudaMemsetAsync(c.flags + a, 0, sizeof(unsigned long long) * size_t(b), s);
+  cudaMemsetAsync(c.tickets + ticket, 0, sizeof(int32_t), s);
+  if (what == 0) k_comp_fwd_lb<SPT, MODE><<<grid_size(b, 4), 256, fwd_smem, s>>>(c, a, b, ticket);
+  else k_comp_bwd_lb<SPT, MODE><<<grid_size(b, 3), 256, bwd_smem, s>>>(c, a, b, ticket);
+  return 1;
 }
 
 template <int SPT>
-static int comp_mode(int what, const DevCtx& c, int a, int b, int n0, int n1, int ticket, int mode, cudaStream_t s) {
-  if (mode == MODE_GATE) return comp_launch<SPT, MODE_GATE>(what, c, a, b, n0, n1, ticket, s);
-  if (mode == MODE_SC) return comp_launch<SPT, MODE_SC>(what, c, a, b, n0, n1, ticket, s);
-  return comp_launch<SPT, MODE_COMP>(what, c, a, b, n0, n1, ticket, s);
+static int comp_mode(int what, const DevCtx& c, int a, int b, int ticket, int mode, cudaStream_t s) {
+  if (mode == MODE_GATE) return comp_launch<SPT, MODE_GATE>(what, c, a, b, ticket, s);
+  if (mode == MODE_SC) return comp_launch<SPT, MODE_SC>(what, c, a, b, ticket, s);
+  return comp_launch<SPT, MODE_COMP>(what, c, a, b, ticket, s);
 }
 
 int launch_comp(int what, const DevCtx& c, int a, int b, int n0, int n1, int ticket, int mode, cudaStream_t s) {
   if (what < 0) {   // kernel attributes of every variant
     for (int m : {MODE_COMP, MODE_GATE, MODE_SC}) {
-      comp_mode<4>(-1, c, 0, 0, 0, 0, 0, m, s);
-      comp_mode<8>(-1, c, 0, 0, 0, 0, 0, m, s);
-      comp_mode<16>(-1, c, 0, 0, 0, 0, 0, m, s);
+      comp_mode<4>(-1, c, 0, 0, 0, m, s);
+      comp_mode<8>(-1, c, 0, 0, 0, m, s);
+      comp_mode<16>(-1, c, 0, 0, 0, m, s);
     }
     return 0;
   }
@@ -930,9 +674,9 @@ int launch_comp(int what, const DevCtx& c, int a, int b, int n0, int n1, int tic
     return 1;
   }
   if (b <= 0) return 0;
-  if (c.comp_chunk == 1024) return comp_mode<4>(what, c, a, b, n0, n1, ticket, mode, s);
-  if (c.comp_chunk == 4096) return comp_mode<16>(what, c, a, b, n0, n1, ticket, mode, s);
-  return comp_mode<8>(what, c, a, b, n0, n1, ticket, mode, s);
+  if (c.comp_chunk == 1024) return comp_mode<4>(what, c, a, b, ticket, mode, s);
+  if (c.comp_chunk == 4096) return comp_mode<16>(what, c, a, b, ticket, mode, s);
+  return comp_mode<8>(what, c, a, b, ticket, mode, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -947,7 +691,7 @@ constexpr int NOALLOC_MAX_CHUNKS = NOALLOC_MAX_LEN / NOALLOC_CHUNK;
 constexpr int NOALLOC_WORDS = NOALLOC_MAX_CHUNKS + 32;           // + ticket / status words
 static __device__ __align__(256) unsigned long long g_comp_noalloc_scratch[NOALLOC_WORDS];
 
-// One stereo row u[2][pitch] -> y[2][pitch]; same chunk arithmetic as k_comp_fwd<8>,
+// One stereo row u[2][pitch] -> y[2][pitch]; same chunk arithmetic as k_comp_fwd_lb<8>,
 // with the row read directly instead of gathered over in-edges.
 __global__ void __launch_bounds__(256) k_comp_fwd_row(DevCtx c, const float* __restrict__ u, const float* p,
                                                      float* y, int len, int pitch, int n_chunks) {

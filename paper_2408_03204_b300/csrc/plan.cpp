@@ -756,7 +756,6 @@ int build_plan(const std::vector<const grafx_graph*>& graphs_in, const int64_t* 
     w.eq_aux = take(4 * size_t(std::max(p->n_eq, 1)) * 1024);
     w.eq_bandpart = take(4 * size_t(std::max(p->n_eq, 1)) * 16 * 8);
     w.comp_carry = take(4 * size_t(std::max(p->n_comp_chunks, 1)));
-    w.comp_agg = take(4 * size_t(std::max(p->n_comp_chunks, 1)));
     w.dl_aux = take(4 * size_t(std::max(p->n_delay, 1)) * 2 * p->dl_taps * (DL_FIR + 1));
     w.dl_spec = take(8 * size_t(std::max(p->n_dl_slots, 1)) * DL_M);
     w.dl_R = take(8 * size_t(std::max(p->n_delay, 1)) * p->dl_P * DL_M);

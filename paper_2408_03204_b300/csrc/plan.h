@@ -65,7 +65,7 @@ struct WsLayout {
   size_t loss_rows, loss_items;
   size_t tables_end;                           // [0, tables_end) is uploaded at bind time
   size_t status, tickets, flags, flags_bytes;  // flags_bytes covers status+tickets+flags (cleared per call)
-  size_t eq_spec, eq_aux, eq_bandpart, comp_carry, comp_agg, partial, eq_partial;
+  size_t eq_spec, eq_aux, eq_bandpart, comp_carry, partial, eq_partial;
   size_t eq_uspec, eq_ola;                     // EQ input block spectra (forward), adjoint heads/tails
   size_t dl_aux, dl_spec, dl_R, dl_r;
   size_t rv_band, rv_U, rv_fr, rv_h, rv_H, rv_Y, rv_R, rv_r, rv_mm;
