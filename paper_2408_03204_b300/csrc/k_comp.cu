@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_fwd_lb(DevCtx c
 // partial slot, contiguous per node from its last chunk; bounded waits record
 // ST_TIMEOUT).
 template <int SPT, int MODE>
-__global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 3) k_comp_bwd_lb(DevCtx c, int item0, int n_items, int ticket) {
+__global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 4) k_comp_bwd_lb(DevCtx c, int item0, int n_items, int ticket) {
   constexpr int CH = 256 * SPT;
   constexpr bool GATE = MODE == MODE_GATE, SC = MODE == MODE_SC;
   extern __shared__ __align__(16) float buf[];  // 4 * CH floats: prefetched u and ybar rows
@@ -648,7 +648,7 @@ static int comp_launch(int what, const DevCtx& c, int a, int b, int ticket, cuda
   cudaMemsetAsync(c.flags + a, 0, sizeof(unsigned long long) * size_t(b), s);
   cudaMemsetAsync(c.tickets + ticket, 0, sizeof(int32_t), s);
   if (what == 0) k_comp_fwd_lb<SPT, MODE><<<grid_size(b, 4), 256, fwd_smem, s>>>(c, a, b, ticket);
-  else k_comp_bwd_lb<SPT, MODE><<<grid_size(b, 3), 256, bwd_smem, s>>>(c, a, b, ticket);
+  else k_comp_bwd_lb<SPT, MODE><<<grid_size(b, 4), 256, bwd_smem, s>>>(c, a, b, ticket);
   return 1;
 }
 
