@@ -41,9 +41,10 @@ __device__ __forceinline__ const float* dl_single_row(const DevCtx& c, int v) {
   return ADJ ? out_adj_row(c, e0) : in_row(c, e0);
 }
 
-// Shared-memory index of window element i: 4 floats of padding after every 32, so that
-// the float4 reads of threads 16 elements apart (8 lanes per 32 banks) do not collide.
-__device__ __forceinline__ int dl_pidx(int i) { return i + ((i >> 5) << 2); }
+// Shared-memory index of window element i: 4 floats of padding after every 16, so that
+// the float4 reads of threads 16 elements apart (20 floats in shared memory: 8 lanes per
+// 32 banks) do not collide, and a thread's reads sit at fixed offsets from its first.
+__device__ __forceinline__ int dl_pidx(int i) { return i + ((i >> 4) << 2); }
 
 // Window of one tap for a tile of one channel summed over several rows (padded layout).
 template <bool ADJ>
@@ -66,7 +67,8 @@ constexpr int DL_FT = DL_TILE / DL_OPT;      // threads of the FIR kernels
 constexpr int DL_SH = DL_FIR + 3;            // taps of the shifted filters (alignment shift 0..3)
 constexpr int DL_XL = (DL_OPT + DL_SH - 1 + 3) & ~3;   // window floats a thread reads (15 float4)
 constexpr int DL_WL = DL_OPT * (DL_FT - 1) + DL_XL;     // window floats staged (16-byte groups)
-constexpr int DL_WP = DL_WL + ((DL_WL + 31) / 32) * 4;  // padded window floats
+constexpr int DL_WP = DL_WL + ((DL_WL + 15) / 16) * 4;  // padded window floats
+static_assert(DL_OPT % 16 == 0, "a thread's window starts on a padding segment");
 static_assert(DL_WL % 4 == 0 && DL_WL >= DL_TILE + DL_SH - 1, "window covers the tile");
 
 // Forward (ADJ = false) or input adjoint (ADJ = true) of the sparse FIR for one
@@ -78,7 +80,7 @@ static_assert(DL_WL % 4 == 0 && DL_WL >= DL_TILE + DL_SH - 1, "window covers the
 // the same unrolled loop over aligned float4 reads.  The windows of a group of DL_GROUP
 // taps are staged while the previous group is computed (cp.async from a single source
 // row; a sum over several rows is staged synchronously), double-buffered, with 4 floats of
-// padding after every 32 so that the threads' float4 reads (16 floats apart) fall in
+// padding after every 16 so that the threads' float4 reads (16 floats apart) fall in
 // distinct banks.
 template <bool ADJ>
 __global__ void __launch_bounds__(DL_FT) k_delay_fir(DevCtx c, int item0, int n_items) {
@@ -139,10 +141,10 @@ __global__ void __launch_bounds__(DL_FT) k_delay_fir(DevCtx c, int item0, int n_
       const int ng = min(DL_GROUP, ntap - g0);
       for (int m = 0; m < ng; ++m) {
         float x[DL_XL];
-        const float* wb = win[buf][m];
+        const float* wb = win[buf][m] + dl_pidx(i0);   // i0 starts a padding segment
 #pragma unroll
         for (int k = 0; k < DL_XL / 4; ++k) {   // a float4 never crosses a padding point
-          const float4 q4 = *reinterpret_cast<const float4*>(wb + dl_pidx(i0 + 4 * k));
+          const float4 q4 = *reinterpret_cast<const float4*>(wb + dl_pidx(4 * k));
           x[4 * k] = q4.x, x[4 * k + 1] = q4.y, x[4 * k + 2] = q4.z, x[4 * k + 3] = q4.w;
         }
         const float4* t4 = reinterpret_cast<const float4*>(taps[g0 + m]);
