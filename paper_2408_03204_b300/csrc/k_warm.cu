@@ -40,13 +40,14 @@ constexpr int WS_OUTMAX = 176;
 static const int kHeadOut[WS_NHEAD] = {2, 1, 8, 4, 176, 50};
 
 // ------------------------------------------------------------------ BF16 GEMM
+// The register-staged product (grafx_gemm_bf16, the public matrix product):
 // C[M,N] = alpha * A B + beta * C with A(m, k) = A[m sam + k sak] and
 // B(k, n) = B[k sbk + n sbn] (FP32 in memory, BF16 in shared memory), C row-major (ldc).
 // Operand tiles are loaded with float4 along whichever dimension has unit stride when
 // it is a multiple of 4 (mode VK: along k, VR: along the row dimension m or n), else
 // scalar (mode SC).  Split-K (gridDim.z > 1) writes partial tiles to `part` [z][M][N],
 // summed in z order by k_gemm_reduce (deterministic).
-enum : int { LD_SC = 0, LD_VK = 1, LD_VR = 2, LD_BK = 3, LD_BR = 4 };  // BK/BR: BF16 operand, 8 per load
+enum : int { LD_SC = 0, LD_VK = 1, LD_VR = 2 };
 
 // exact GELU and its derivative
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
@@ -56,7 +57,7 @@ __device__ __forceinline__ float gelu_d(float x) {
 
 struct GemmArgs {
   int M, N, K, kchunk;
-  const void* A;  // float, or __nv_bfloat16 in the BF16 load modes
+  const void* A;  // float (the register-staged products; unused by the TMA-fed ones)
   int64_t sam, sak;
   const void* B;
   int64_t sbk, sbn;
@@ -140,13 +141,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 // This thread's share of a 128 x 64 operand tile X(r, k) = X[r sr + k sk] (rows r0..,
 // k0..; zero outside R x kend): TC_V values, loaded into registers (tc_load) and stored
 // as BF16 into the swizzled shared-memory tile (tc_store).
-constexpr int TC_V = 128 * TC_K / TC_THREADS;  // 32 words (FP32 modes) or 16 (BF16 modes)
+constexpr int TC_V = 128 * TC_K / TC_THREADS;  // 32 FP32 words
 template <int MODE>
 __device__ __forceinline__ void tc_load(uint32_t (&v)[TC_V], const void* Xv, int64_t sr, int64_t sk, int r0, int R,
                                         int k0, int kend) {
   const int tid = threadIdx.x;
   const float* __restrict__ X = static_cast<const float*>(Xv);
-  const __nv_bfloat16* __restrict__ Xh = static_cast<const __nv_bfloat16*>(Xv);
   if constexpr (MODE == LD_VK) {  // float4 along k: 128 rows x 16 quads
 #pragma unroll
     for (int i = 0; i < TC_V / 4; ++i) {
@@ -166,24 +166,6 @@ __device__ __forceinline__ void tc_load(uint32_t (&v)[TC_V], const void* Xv, int
       if (m < R && k < kend) q = __ldg(reinterpret_cast<const float4*>(X + m + k * sk));
       v[4 * i] = __float_as_uint(q.x), v[4 * i + 1] = __float_as_uint(q.y);
       v[4 * i + 2] = __float_as_uint(q.z), v[4 * i + 3] = __float_as_uint(q.w);
-    }
-  } else if constexpr (MODE == LD_BK) {  // 8 BF16 along k: 128 rows x 8 chunks
-#pragma unroll
-    for (int i = 0; i < TC_V / 8; ++i) {
-      const int f = tid + i * TC_THREADS, r = f >> 3, k8 = (f & 7) * 8;
-      const int m = r0 + r, k = k0 + k8;
-      uint4 q = make_uint4(0u, 0u, 0u, 0u);
-      if (m < R && k < kend) q = __ldg(reinterpret_cast<const uint4*>(Xh + m * sr + k));
-      v[4 * i] = q.x, v[4 * i + 1] = q.y, v[4 * i + 2] = q.z, v[4 * i + 3] = q.w;
-    }
-  } else if constexpr (MODE == LD_BR) {  // 8 BF16 along the rows: 64 k x 16 row octets
-#pragma unroll
-    for (int i = 0; i < TC_V / 8; ++i) {
-      const int f = tid + i * TC_THREADS, kk = f >> 4, r8 = (f & 15) * 8;
-      const int m = r0 + r8, k = k0 + kk;
-      uint4 q = make_uint4(0u, 0u, 0u, 0u);
-      if (m < R && k < kend) q = __ldg(reinterpret_cast<const uint4*>(Xh + m + k * sk));
-      v[4 * i] = q.x, v[4 * i + 1] = q.y, v[4 * i + 2] = q.z, v[4 * i + 3] = q.w;
     }
   } else {  // scalar FP32, k fastest
 #pragma unroll
@@ -219,23 +201,6 @@ __device__ __forceinline__ void tc_store(char* tile, const uint32_t (&v)[TC_V]) 
       const int f = tid + i * TC_THREADS, kk = f >> 5, rq = (f & 31) * 4;
 #pragma unroll
       for (int j = 0; j < 4; ++j) st_bf16(tile + sw128(rq + j, kk), __uint_as_float(v[4 * i + j]));
-    }
-  } else if constexpr (MODE == LD_BK) {  // one 16-byte chunk of a row: already BF16
-#pragma unroll
-    for (int i = 0; i < TC_V / 8; ++i) {
-      const int f = tid + i * TC_THREADS, r = f >> 3, k8 = (f & 7) * 8;
-      *reinterpret_cast<uint4*>(tile + sw128(r, k8)) = make_uint4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-    }
-  } else if constexpr (MODE == LD_BR) {  // 8 rows of one k
-#pragma unroll
-    for (int i = 0; i < TC_V / 8; ++i) {
-      const int f = tid + i * TC_THREADS, kk = f >> 4, r8 = (f & 15) * 8;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint32_t w = v[4 * i + j];
-        *reinterpret_cast<uint16_t*>(tile + sw128(r8 + 2 * j, kk)) = uint16_t(w & 0xFFFFu);
-        *reinterpret_cast<uint16_t*>(tile + sw128(r8 + 2 * j + 1, kk)) = uint16_t(w >> 16);
-      }
     }
   } else {
 #pragma unroll
@@ -671,13 +636,8 @@ __global__ void k_gemm_reduce(const float* __restrict__ part, int splits, GemmAr
 }
 
 // Load mode of an operand X(r, k) = X[r sr + k sk] with R rows and K columns.
-static int load_mode(const void* X, int64_t sr, int64_t sk, int R, int K, bool bf16) {
+static int load_mode(const void* X, int64_t sr, int64_t sk, int R, int K) {
   const bool al = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
-  if (bf16) {
-    if (al && sk == 1 && sr % 8 == 0 && K % 8 == 0) return LD_BK;
-    if (al && sr == 1 && sk % 8 == 0 && R % 8 == 0) return LD_BR;
-    return -1;  // BF16 operands must be 8-element aligned along their unit-stride dimension
-  }
   if (al && sk == 1 && sr % 4 == 0 && K % 4 == 0) return LD_VK;
   if (al && sr == 1 && sk % 4 == 0 && R % 4 == 0) return LD_VR;
   return LD_SC;
@@ -698,8 +658,6 @@ static void launch_tc_b(int bm, dim3 grid, const GemmArgs& a, uint32_t* status, 
   switch (bm) {
     case LD_VK: launch_tc_one<AM, LD_VK>(grid, a, status, s); break;
     case LD_VR: launch_tc_one<AM, LD_VR>(grid, a, status, s); break;
-    case LD_BR: launch_tc_one<AM, LD_BR>(grid, a, status, s); break;
-    case LD_BK: launch_tc_one<AM, LD_BK>(grid, a, status, s); break;
     default: launch_tc_one<AM, LD_SC>(grid, a, status, s);
   }
 }
@@ -709,8 +667,7 @@ static void launch_tc_b(int bm, dim3 grid, const GemmArgs& a, uint32_t* status, 
 // that records a bounded wait's expiry.
 static int gemm(int M, int N, int K, const void* A, int64_t sam, int64_t sak, const void* B, int64_t sbk,
                  int64_t sbn, float* C, int64_t ldc, float alpha, float beta, cudaStream_t s,
-                 float* scratch = nullptr, int64_t scratch_floats = 0, uint32_t* status = nullptr,
-                 bool a_bf16 = false, bool b_bf16 = false) {
+                 float* scratch = nullptr, int64_t scratch_floats = 0, uint32_t* status = nullptr) {
   if (M <= 0 || N <= 0) return GRAFX_OK;
   GemmArgs a{M, N, K, 0, A, sam, sak, B, sbk, sbn, C, ldc, alpha, beta, nullptr, 0};
   const int tm = (M + TC_M - 1) / TC_M, tn = (N + TC_N - 1) / TC_N;
@@ -726,14 +683,10 @@ static int gemm(int M, int N, int K, const void* A, int64_t sam, int64_t sak, co
   splits = (ktiles + kt_per - 1) / kt_per;
   if (splits > 1) a.part = scratch;
   dim3 grid(tn, tm, splits);
-  const int am = load_mode(A, sam, sak, M, K, a_bf16), bm = load_mode(B, sbn, sbk, N, K, b_bf16);
-  if (am < 0 || bm < 0)
-    return fail(GRAFX_ESHAPE, "BF16 GEMM operand not 8-element aligned along its unit-stride dimension");
+  const int am = load_mode(A, sam, sak, M, K), bm = load_mode(B, sbn, sbk, N, K);
   switch (am) {
     case LD_VK: launch_tc_b<LD_VK>(bm, grid, a, status, s); break;
     case LD_VR: launch_tc_b<LD_VR>(bm, grid, a, status, s); break;
-    case LD_BK: launch_tc_b<LD_BK>(bm, grid, a, status, s); break;
-    case LD_BR: launch_tc_b<LD_BR>(bm, grid, a, status, s); break;
     default: launch_tc_b<LD_SC>(bm, grid, a, status, s);
   }
   if (splits > 1) {
