@@ -284,7 +284,9 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
 // sum_b X_{b-p}[k] conj(Ybar_b[k]), packed as R_l + i R_r for the joint inverse.  The
 // per-channel products of real signals' spectra are conjugate-symmetric, so the work
 // items cover bins 0..M/2 and bin M - k is written from bin k.  Launched with
-// DL_CHUNK * dl_P threads (one per bin and partition).
+// DL_CHUNK * ceil(dl_P / DL_NPT) threads (one per bin and group of DL_NPT partitions;
+// DL_NPT = 4 where that leaves no more unused partition slots than pairs do, else 2).
+template <int DL_NPT>
 __global__ void __launch_bounds__(DL_CHUNK * DL_PMAX) k_delay_acc(DevCtx c, int item0, int n_items) {
   extern __shared__ float2 sm[];
   const int P = c.dl_P;
@@ -322,38 +324,45 @@ __global__ void __launch_bounds__(DL_CHUNK * DL_PMAX) k_delay_acc(DevCtx c, int 
       dst[1] = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
     }
     __syncthreads();
-    // thread (pair q, bin kk) accumulates partitions p = 2q and 2q + 1: partition p + 1
-    // at block b uses the window partition p used at block b - 1, carried in registers
-    const int kk = threadIdx.x % DL_CHUNK, p0 = 2 * (threadIdx.x / DL_CHUNK);
-    float2 a0l = make_float2(0.f, 0.f), a0r = a0l, a1l = a0l, a1r = a0l;
-    float2 pl = X[(size_t(P - p0 - 1) * DL_CHUNK + kk) * 2];       // window -p0 - 1 (b = -1)
-    float2 pr = X[(size_t(P - p0 - 1) * DL_CHUNK + kk) * 2 + 1];
+    // thread (group q, bin kk) accumulates partitions p = DL_NPT q + j, j < DL_NPT: partition
+    // p0 + j at block b uses the window partition p0 used at block b - j, carried in
+    // registers (one window and one ybar block read per block for DL_NPT partitions)
+    const int kk = threadIdx.x % DL_CHUNK, p0 = DL_NPT * (threadIdx.x / DL_CHUNK);
+    // wl[j], wr[j]: window b - p0 - j once block b has shifted it in; before block 0 they
+    // hold window -p0 - 1 - j (stored at P - p0 - 1 - j; below 0 only for partitions >= P)
+    float2 al[DL_NPT], ar[DL_NPT], wl[DL_NPT], wr[DL_NPT];
+#pragma unroll
+    for (int j = 0; j < DL_NPT; ++j) {
+      al[j] = ar[j] = make_float2(0.f, 0.f);
+      const int s0 = P - p0 - 1 - j;
+      wl[j] = s0 >= 0 ? X[(size_t(s0) * DL_CHUNK + kk) * 2] : make_float2(0.f, 0.f);
+      wr[j] = s0 >= 0 ? X[(size_t(s0) * DL_CHUNK + kk) * 2 + 1] : make_float2(0.f, 0.f);
+    }
 #pragma unroll 4
     for (int b = 0; b < nb; ++b) {
+#pragma unroll
+      for (int j = DL_NPT - 1; j > 0; --j) wl[j] = wl[j - 1], wr[j] = wr[j - 1];
       const int ws = b - p0 + P;              // window index b - p0, stored from -P
-      const float2 xl = X[(size_t(ws) * DL_CHUNK + kk) * 2], xr = X[(size_t(ws) * DL_CHUNK + kk) * 2 + 1];
+      wl[0] = X[(size_t(ws) * DL_CHUNK + kk) * 2];
+      wr[0] = X[(size_t(ws) * DL_CHUNK + kk) * 2 + 1];
       const float2 yl = Y[(size_t(b) * DL_CHUNK + kk) * 2], yr = Y[(size_t(b) * DL_CHUNK + kk) * 2 + 1];
-      a0l.x += xl.x * yl.x + xl.y * yl.y;
-      a0l.y += xl.y * yl.x - xl.x * yl.y;
-      a0r.x += xr.x * yr.x + xr.y * yr.y;
-      a0r.y += xr.y * yr.x - xr.x * yr.y;
-      a1l.x += pl.x * yl.x + pl.y * yl.y;
-      a1l.y += pl.y * yl.x - pl.x * yl.y;
-      a1r.x += pr.x * yr.x + pr.y * yr.y;
-      a1r.y += pr.y * yr.x - pr.x * yr.y;
-      pl = xl;
-      pr = xr;
+#pragma unroll
+      for (int j = 0; j < DL_NPT; ++j) {
+        al[j].x += wl[j].x * yl.x + wl[j].y * yl.y;
+        al[j].y += wl[j].y * yl.x - wl[j].x * yl.y;
+        ar[j].x += wr[j].x * yr.x + wr[j].y * yr.y;
+        ar[j].y += wr[j].y * yr.x - wr[j].x * yr.y;
+      }
     }
     // R_l + i R_r at k, conj(R_l) + i conj(R_r) at M - k
     const int k = k0 + kk;
     if (k <= DL_M / 2) {
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
+      for (int j = 0; j < DL_NPT; ++j) {
         if (p0 + j >= P) break;
-        const float2 al = j ? a1l : a0l, ar = j ? a1r : a0r;
         float2* R = c.dl_R + (size_t(e.y) + p0 + j) * DL_M;
-        R[k] = make_float2(al.x - ar.y, al.y + ar.x);
-        if (k > 0 && k < DL_M / 2) R[DL_M - k] = make_float2(al.x + ar.y, ar.x - al.y);
+        R[k] = make_float2(al[j].x - ar[j].y, al[j].y + ar[j].x);
+        if (k > 0 && k < DL_M / 2) R[DL_M - k] = make_float2(al[j].x + ar[j].y, ar[j].x - al[j].y);
       }
     }
   }
@@ -600,7 +609,8 @@ int launch_delay(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
     const size_t sm_acc_max = sizeof(float2) * 2 * DL_CHUNK * size_t(2 * DL_MAX_BLOCKS + DL_PMAX);
     cudaFuncSetAttribute(k_delay_spec, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_fft));
     cudaFuncSetAttribute(k_delay_lags, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_fft));
-    cudaFuncSetAttribute(k_delay_acc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_acc_max));
+    cudaFuncSetAttribute(k_delay_acc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_acc_max));
+    cudaFuncSetAttribute(k_delay_acc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_acc_max));
     init = true;
   }
   if (what < 0) return 0;
@@ -612,8 +622,14 @@ int launch_delay(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
     case 1: if (b > 0) k_delay_fir<false><<<grid_size(b, 8), DL_FT, 0, s>>>(c, a, b); return b > 0;
     case 2: if (b > 0) k_delay_fir<true><<<grid_size(b, 8), DL_FT, 0, s>>>(c, a, b); return b > 0;
     case 3: if (b > 0) k_delay_spec<<<grid_size(b, 3), DL_M / 16, sm_fft, s>>>(c, a, b); return b > 0;
-    case 4:   // one thread per bin and pair of lag partitions
-      if (b > 0) k_delay_acc<<<grid_size(b, acc_per_sm), DL_CHUNK * ((c.dl_P + 1) / 2), sm_acc, s>>>(c, a, b);
+    case 4:   // one thread per bin and group of lag partitions
+      if (b > 0) {
+        const int g4 = (c.dl_P + 3) / 4, g2 = (c.dl_P + 1) / 2;
+        if (4 * g4 <= 2 * g2)
+          k_delay_acc<4><<<grid_size(b, acc_per_sm), DL_CHUNK * g4, sm_acc, s>>>(c, a, b);
+        else
+          k_delay_acc<2><<<grid_size(b, acc_per_sm), DL_CHUNK * g2, sm_acc, s>>>(c, a, b);
+      }
       return b > 0;
     case 5: if (b > 0) k_delay_lags<<<grid_size(b, 3), DL_M / 16, sm_fft, s>>>(c, a, b); return b > 0;
     case 6: if (b > 0) k_delay_grad<<<grid_size(b, 4), 256, 0, s>>>(c, a, b); return b > 0;
