@@ -5,23 +5,25 @@
 // One work item is a chunk of CH = 256 * SPT samples of one node.  Inside a chunk:
 // every thread runs the recursion over its SPT samples with zero initial state, a
 // warp-shuffle scan and a cross-warp scan combine the per-thread states with the
-// decay a^SPT.  Across chunks, one pass with a decoupled look-back: each chunk publishes
-// its zero-start end state (its aggregate), then its inclusive end state once its carry
-// is known; one warp of a chunk reads the 32 preceding states of its node at once and
-// walks back until it meets an inclusive one.  Chunks are handed out by an atomic ticket
-// in chunk-major order (the c-th chunk of every node of the step before any node's
-// (c+1)-th), so every chunk waited on is held by a CTA that took its ticket earlier and,
-// on steps of many nodes, has long finished; every wait is bounded and records
-// ST_TIMEOUT on expiry.  The forward stores each chunk's entering state (one float) so
-// that the backward can recompute g[n] exactly.
+// decay a^SPT.  Across chunks, one pass: each chunk publishes its zero-start end state
+// (its aggregate) as soon as its in-chunk scan is done, and one warp forms the state
+// entering it as a fixed-order, decay-weighted sum of the aggregates of the node's
+// earlier chunks (deterministic: no dependence on which chunks had finished).  Chunks
+// are handed out by an atomic ticket in chunk-major order (the c-th chunk of every node
+// of the step before any node's (c+1)-th), so every chunk waited on is held by a CTA that
+// took its ticket earlier and, on steps of many nodes, has long finished; every wait is
+// bounded and records ST_TIMEOUT on expiry.  The forward stores each chunk's entering
+// state (one float) so that the backward can recompute g[n] exactly.
 //
 // Backward: ybar gives a_n = dL/dg[n]; lambda[n] = a_n + alpha lambda[n+1] runs the same
-// way from each node's end (its own look-back words); ubar_x = k ybar_x + 2 u_m
+// way from each node's end (its own aggregate words); ubar_x = k ybar_x + 2 u_m
 // (1 - alpha) lambda and the parameter partials (sum lambda (g[n-1] - x[n]) for alpha,
 // sum Gybar dGy/dT|W|R) go to one slot per chunk.
 //
-// The allocation-free single-row forward at the end of this file is the same forward
-// over one row, with the chunks in order.
+// The allocation-free single-row forward at the end of this file takes its chunks in
+// order and uses a decoupled look-back instead: each chunk publishes its aggregate, then
+// its inclusive end state once its carry is known, and one warp reads the 32 preceding
+// states at once, walking back until it meets an inclusive one.
 #include <cstring>
 #include <mutex>
 
@@ -184,6 +186,30 @@ __device__ float look_back_warp(const DevCtx& c, int end, int first, float la_ch
     dec *= expf(la_ch * 32.f);
     end -= 32;
   }
+  return acc;
+}
+
+// Carry into the current chunk as a fixed-order sum over the aggregates (zero-start end
+// states) of the node's earlier chunks, items first .. end with `end` the nearest:
+// carry = sum_l D^l agg(end - l), D = exp(la_ch) the decay of one chunk.  Run by one full
+// warp: lane i takes l = i, i + 32, ... in increasing order, then a xor-shuffle tree adds
+// the lanes (every lane gets the same bits); the value depends on the data only, not on
+// which chunks had finished (deterministic, unlike a look-back that stops at the first
+// inclusive state).  Terms with D^l < 2^-30 are not read: their sum is at most
+// 2^-30 / (1 - D) of the largest aggregate, below 1e-8 for alpha <= 0.9999 (the fit's
+// parameter map) and chunks of >= 1024 samples, and the cut depends on alpha only.  Waits
+// are bounded (wait_flag).
+__device__ float carry_sum_warp(const DevCtx& c, int end, int first, float la_ch) {
+  const int lane = threadIdx.x & 31;
+  const float lmax = la_ch < 0.f ? -20.794415f / la_ch : 1e30f;   // D^l >= 2^-30
+  float acc = 0.f;
+  for (int l = lane; end - l >= first && float(l) <= lmax; l += 32) {
+    float val = 0.f;
+    wait_flag(c, end - l, &val);
+    acc += expf(la_ch * float(l)) * val;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   return acc;
 }
 
@@ -396,11 +422,10 @@ __device__ __forceinline__ void env_input(const DevCtx& c, int v, const NodeDev&
 
 // Forward in one pass: chunks handed out by an atomic ticket in chunk-major order (the
 // c-th chunk of every node of the step before any node's (c+1)-th); each publishes its
-// aggregate (state at its end with zero entering), takes the state entering it from the
-// chunks before it by a decoupled look-back over the node's chunk slots (flags indexed by
-// the chunk's global id, contiguous per node), publishes its inclusive state, stores the
-// entering state for the backward and applies the gain.  The inputs are read once.
-// Bounded waits record ST_TIMEOUT.
+// aggregate (state at its end with zero entering), forms the state entering it from the
+// aggregates of the node's earlier chunks (carry_sum_warp; words indexed by the chunk's
+// global id, contiguous per node), stores it for the backward and applies the gain.  The
+// inputs are read once.  Bounded waits record ST_TIMEOUT.
 template <int SPT, int MODE>
 __global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_fwd_lb(DevCtx c, int item0, int n_items, int ticket) {
   constexpr int CH = 256 * SPT;
@@ -444,14 +469,8 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_fwd_lb(DevCtx c
     if (!SC && next < n_items) prefetch_item<SPT, false>(c, item0 + next, buf);
     if (threadIdx.x < 32) {
       const int fidx = item0 + (w.z - chunk0);
-      float cin = 0.f;
-      if (w.y == 0) {
-        if (threadIdx.x == 0) publish(c, fidx, 2, total);
-      } else {
-        if (threadIdx.x == 0) publish(c, fidx, 1, total);
-        cin = look_back_warp(c, fidx - 1, fidx - w.y, la * CH);
-        if (threadIdx.x == 0) publish(c, fidx, 2, expf(la * CH) * cin + total);
-      }
+      if (threadIdx.x == 0) publish(c, fidx, 1, total);
+      const float cin = w.y == 0 ? 0.f : carry_sum_warp(c, fidx - 1, fidx - w.y, la * CH);
       if (threadIdx.x == 0) {
         s_cin = cin;
         c.comp_carry[w.z] = cin;   // the state entering the chunk, for the backward
@@ -476,9 +495,9 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 2 : 4) k_comp_fwd_lb(DevCtx c
   cp_async_wait_all();
 }
 
-// Backward in one pass: the reverse recursion's state entering a chunk comes from the
-// chunks after it by a decoupled look-back (chunks handed out by an atomic ticket in
-// chunk-major order from each node's end; the look-back words indexed by the chunk's
+// Backward in one pass: the reverse recursion's state entering a chunk is formed from the
+// aggregates of the chunks after it (carry_sum_warp; chunks handed out by an atomic
+// ticket in chunk-major order from each node's end; the words indexed by the chunk's
 // partial slot, contiguous per node from its last chunk; bounded waits record
 // ST_TIMEOUT).
 template <int SPT, int MODE>
@@ -556,17 +575,12 @@ __global__ void __launch_bounds__(256, SPT >= 16 ? 1 : 4) k_comp_bwd_lb(DevCtx c
     float rtotal;
     float rexcl = block_affine_scan<true>(lb, la * SPT, sh, &rtotal);
     if (threadIdx.x < 32) {
-      // look-back words by the chunk's partial slot: a node's chunks are contiguous there,
+      // aggregate words by the chunk's partial slot: a node's chunks are contiguous there,
       // from its last chunk, whatever the order of the tickets
       const int fidx = item0 + (w.w - slot0);
-      float lin = 0.f;
-      if (chunk == n_chunks - 1) {
-        if (threadIdx.x == 0) publish(c, fidx, 2, rtotal);
-      } else {
-        if (threadIdx.x == 0) publish(c, fidx, 1, rtotal);
-        lin = look_back_warp(c, fidx - 1, fidx - (n_chunks - 1 - chunk), la * CH);
-        if (threadIdx.x == 0) publish(c, fidx, 2, expf(la * CH) * lin + rtotal);
-      }
+      if (threadIdx.x == 0) publish(c, fidx, 1, rtotal);
+      const float lin = chunk == n_chunks - 1 ? 0.f
+                                              : carry_sum_warp(c, fidx - 1, fidx - (n_chunks - 1 - chunk), la * CH);
       if (threadIdx.x == 0) s_lin = lin;
     }
     glast[threadIdx.x] = g[SPT - 1];
