@@ -101,6 +101,27 @@ def test_compressor_long_chunks_and_extreme_alpha():
         assert_grad_close(dP[C], wP[C], what=f"comp alpha={alpha}")
 
 
+def test_compressor_steps_deterministic():
+    """Render and backprop twice on a batch whose compressor steps hold many chunks per
+    node: the chunk carries are fixed-order sums, so every bit repeats (a look-back that
+    stops at the first finished predecessor rounds differently from run to run)."""
+    rng = np.random.Generator(np.random.PCG64(31))
+    graphs = [synth.random_console(rng, budget_lo=24, budget_hi=64, kinds=(G, E, C)) for _ in range(6)]
+    lengths = [int(rng.integers(40000, 70000)) for _ in graphs]
+    src_flat, _ = flat_sources(graphs, lengths, list(range(6)))
+    P = union_params(graphs, 5)
+    run = DeviceRun(graphs, lengths, P, src_flat, eq_taps=63)
+    o1 = run.render().cpu().numpy()
+    W = np.random.Generator(np.random.PCG64(32)).standard_normal(o1.shape).astype(np.float32)
+    g1, s1 = run.backprop(W)
+    o2 = run.render().cpu().numpy()
+    g2, s2 = run.backprop(W)
+    assert np.array_equal(o1, o2), "render is not deterministic"
+    for t in g1:
+        assert np.array_equal(g1[t], g2[t]), f"parameter gradient of type {t} is not deterministic"
+    assert np.array_equal(s1, s2), "source gradient is not deterministic"
+
+
 def test_random_graphs_fwd_bwd():
     from tests.helpers import random_dag
     rng = np.random.Generator(np.random.PCG64(21))
