@@ -219,6 +219,15 @@ int grafx_plan_info(const grafx_plan* p, grafx_plan_info_t* info);
 int grafx_plan_export(const grafx_plan* p, int32_t* type_string, int32_t* step_ptr,
                       int32_t* sigma, int32_t* csr_ptr, int32_t* csr_src,
                       int32_t* tcsr_ptr, int32_t* tcsr_dst, int32_t* param_row);
+/* Copy the work items of schedule step `step` (1..N) out: the forward ones (backward = 0)
+ * or the backward ones (backward = 1), each 4 int32 (new node id, then three fields whose
+ * meaning is per processor type: for the compressor, noisegate and sidechain the chunk
+ * index, the chunk's global id and (backward) its partial slot), in launch order, into
+ * items (host, 4 * capacity int32; may be NULL).  *count receives the step's item count;
+ * GRAFX_ESHAPE if it exceeds capacity (items is then not written).  For checking the
+ * planner's orders; the render never needs it. */
+int grafx_plan_step_items(const grafx_plan* p, int32_t step, int32_t backward, int32_t* items, int32_t capacity,
+                          int32_t* count);
 
 /* ---------------------------------------------------------------- device binding
  * Bind a caller-owned device workspace of at least info.ws_bytes bytes (256-byte

@@ -82,6 +82,7 @@ SIGNATURES = {
     "grafx_plan_destroy": (ctypes.c_int, [_P]),
     "grafx_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(PlanInfo)]),
     "grafx_plan_export": (ctypes.c_int, [_P] + [_I32P] * 8),
+    "grafx_plan_step_items": (ctypes.c_int, [_P, _I32, _I32, _I32P, _I32, _I32P]),
     "grafx_plan_bind_workspace": (ctypes.c_int, [_P, _P, _SZ, _P]),
     "grafx_bind_params": (ctypes.c_int, [_P, _I32, _F, _I64, _I64]),
     "grafx_bind_reverb_noise": (ctypes.c_int, [_P, _F, _I64]),
@@ -273,6 +274,17 @@ class Plan:
         arrs["csr_src"] = arrs["csr_src"][:e]
         arrs["tcsr_dst"] = arrs["tcsr_dst"][:e]
         return {k: v.tolist() for k, v in arrs.items()}
+
+    def step_items(self, step, backward=False):
+        """The work items of schedule step `step` (1..N), forward or backward, as an
+        [n, 4] int32 array in launch order (grafx_plan_step_items)."""
+        import numpy as np
+        n = ctypes.c_int32(0)
+        _check(lib().grafx_plan_step_items(self._h, int(step), int(bool(backward)), None, 0, ctypes.byref(n)))
+        a = np.zeros((max(n.value, 1), 4), np.int32)
+        _check(lib().grafx_plan_step_items(self._h, int(step), int(bool(backward)), a.ctypes.data_as(_I32P),
+                                           n.value, ctypes.byref(n)))
+        return a[:n.value]
 
     # ---- device binding (torch supplies memory and streams only)
     def bind_workspace(self, device="cuda"):

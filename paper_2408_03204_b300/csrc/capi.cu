@@ -332,6 +332,24 @@ int grafx_plan_export(const grafx_plan* p, int32_t* type_string, int32_t* step_p
   return GRAFX_OK;
 }
 
+int grafx_plan_step_items(const grafx_plan* p, int32_t step, int32_t backward, int32_t* items, int32_t capacity,
+                          int32_t* count) {
+  if (!p || !count) return fail(GRAFX_EINVAL, "null argument");
+  const int32_t N = int32_t(p->steps.size()) - 1;
+  if (step < 1 || step > N) return fail(GRAFX_EINVAL, "step out of range");
+  const StepInfo& st = p->steps[step];
+  const int32_t begin = backward ? st.bitem_begin : st.fitem_begin;
+  const int32_t n = backward ? st.bitem_count : st.fitem_count;
+  *count = n;
+  if (!items) return GRAFX_OK;
+  if (n > capacity) return fail(GRAFX_ESHAPE, "items capacity too small");
+  for (int32_t i = 0; i < n; ++i) {
+    const int4_ w = p->items[size_t(begin) + i];
+    items[4 * i] = w.x, items[4 * i + 1] = w.y, items[4 * i + 2] = w.z, items[4 * i + 3] = w.w;
+  }
+  return GRAFX_OK;
+}
+
 int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* stream) {
   GX_TRY
   if (!p || !dev_ws) return fail(GRAFX_EINVAL, "null argument");

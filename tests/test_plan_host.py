@@ -299,3 +299,48 @@ def test_fused_elementwise_step_pairs(gx):
     q.connect(g1, e)
     q.connect(e, o)
     assert gx.Plan([_to_gx(gx, q)], [4096]).info.fused_pairs == 1
+
+
+def test_compressor_items_chunk_major(gx):
+    """The compressor's one-pass kernels take their chunks by ticket in item order and
+    find a node's other chunks through their chunk id (forward) or partial slot
+    (backward): the items are chunk-major (the c-th chunk of every node before any
+    node's (c+1)-th; the backward from each node's end), every chunk of every node once,
+    ids and slots contiguous per node in node order, and the step's first item is its
+    first node's first chunk (forward) or last chunk (backward)."""
+    G, E, C = synth.G, synth.E, synth.C
+    rng = np.random.Generator(np.random.PCG64(5))
+    graphs = [synth.random_console(rng, budget_lo=16, budget_hi=40, kinds=(G, E, C)) for _ in range(4)]
+    lengths = [int(rng.integers(3000, 20000)) for _ in graphs]
+    plan = gx.Plan([_to_gx(gx, g) for g in graphs], lengths, comp_chunk=1024)
+    ex = plan.export()
+    new_len = {}
+    base = 0
+    for g, L in zip(graphs, lengths):
+        for v in range(g.n_nodes):
+            new_len[ex["sigma"][base + v]] = L
+        base += g.n_nodes
+    steps = [k for k in range(1, len(ex["type_string"])) if ex["type_string"][k] == C]
+    assert steps
+    for k in steps:
+        nodes = list(range(ex["step_ptr"][k], ex["step_ptr"][k + 1]))
+        nc = {v: (new_len[v] + 1023) // 1024 for v in nodes}
+        fwd = plan.step_items(k)
+        bwd = plan.step_items(k, backward=True)
+        want_f = [(v, c) for c in range(max(nc.values())) for v in nodes if c < nc[v]]
+        want_b = [(v, nc[v] - 1 - r) for r in range(max(nc.values())) for v in nodes if r < nc[v]]
+        assert [tuple(x) for x in fwd[:, :2]] == want_f
+        assert [tuple(x) for x in bwd[:, :2]] == want_b
+        # chunk ids (both directions) and partial slots (backward) contiguous per node
+        cid = {(v, c): z for v, c, z, _ in fwd}
+        assert all(cid[(v, c)] == z for v, c, z, _ in bwd)
+        first_id = {v: cid[(v, 0)] for v in nodes}
+        slot = {(v, c): s for v, c, _, s in bwd}
+        first_slot = {v: slot[(v, nc[v] - 1)] for v in nodes}
+        for i, v in enumerate(nodes):
+            assert [cid[(v, c)] for c in range(nc[v])] == list(range(first_id[v], first_id[v] + nc[v]))
+            assert [slot[(v, nc[v] - 1 - r)] for r in range(nc[v])] == list(range(first_slot[v], first_slot[v] + nc[v]))
+            if i:
+                assert first_id[v] == first_id[nodes[i - 1]] + nc[nodes[i - 1]]
+                assert first_slot[v] == first_slot[nodes[i - 1]] + nc[nodes[i - 1]]
+        assert fwd[0][2] == min(cid.values()) and bwd[0][3] == min(slot.values())
