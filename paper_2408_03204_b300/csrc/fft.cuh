@@ -375,11 +375,9 @@ __device__ __forceinline__ void forward_regs(float2 (&v)[16], float2* b0, float2
 // when this is entered; on exit other threads may still read it.  All threads of the
 // CTA call it (barriers); ptw: the concatenated pass tables.
 template <int M>
-__device__ __forceinline__ void forward_regs_1buf(float2 (&v)[16], float2* buf, const float2_* __restrict__ ptw,
-                                                  int tid) {
+__device__ __forceinline__ void forward_regs_1buf_tw(float2 (&v)[16], float2* buf, const float2_* tw, int tid) {
   constexpr int n16 = Geo<M>::n16, last = Geo<M>::last;
   constexpr int npass = n16 + (last > 1 ? 1 : 0);
-  const float2_* tw = ptw + ptw_base(M);
   {  // pass 1: radix 16, Ns = 1, from registers
     float2(*w)[16] = reinterpret_cast<float2(*)[16]>(v);
     Dft<16>::run(w[0]);
@@ -418,6 +416,13 @@ __device__ __forceinline__ void forward_regs_1buf(float2 (&v)[16], float2* buf, 
     }
     if (!is_last) Ns *= 16;
   }
+}
+// tw of forward_regs_1buf_tw: this size's pass tables (ptw + ptw_base(M)), in global or
+// shared memory
+template <int M>
+__device__ __forceinline__ void forward_regs_1buf(float2 (&v)[16], float2* buf, const float2_* __restrict__ ptw,
+                                                  int tid) {
+  forward_regs_1buf_tw<M>(v, buf, ptw + ptw_base(M), tid);
 }
 #endif
 

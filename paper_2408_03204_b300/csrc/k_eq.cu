@@ -175,15 +175,12 @@ __device__ __forceinline__ void eq_store_regs(float* row, const NodeDev& nd, int
 // (c.params2) on load, and the block's output range [H, H+S) of the gain's row is stored
 // here (every sample once), so the row stays valid for every reader.
 template <int M, bool PRO>
-__global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_fwd(DevCtx c, int item0, int n_items) {
+__global__ void __launch_bounds__(M / 16, 3 * 4096 / M) k_eq_fwd(DevCtx c, int item0, int n_items) {
   extern __shared__ float2 smem2[];
-  float2* b0 = smem2;
-  float2* b1 = smem2 + fft::Padded<M>::size;
+  float2* b0 = smem2;   // one FFT buffer (three CTAs per SM)
   // this size's FFT pass twiddles, staged once per CTA (the CTA loops over many blocks)
-  float2_* stw = reinterpret_cast<float2_*>(smem2 + 2 * fft::Padded<M>::size);
+  float2_* stw = reinterpret_cast<float2_*>(smem2 + fft::Padded<M>::size);
   for (int i = threadIdx.x; i < fft::ptw_size(M); i += blockDim.x) stw[i] = c.ptw[fft::ptw_base(M) + i];
-  __syncthreads();
-  constexpr bool even = fft::Geo<M>::npass % 2 == 0;
   const int H = c.eq_H, S = c.eq_step, Hal = c.eq_Hal;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
@@ -210,29 +207,25 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_fwd(DevCtx c, int item0
     } else {
       eq_load_regs<M, false>(c, v, nd, ws, x, false, H, S);
     }
-    if (even) __syncthreads();
-    fft::forward_regs_tw<M>(x, b0, b1, stw, threadIdx.x);
+    __syncthreads();   // the previous transform's readers of b0 are done (and stw is staged)
+    fft::forward_regs_1buf_tw<M>(x, b0, stw, threadIdx.x);
     float2* us = c.eq_uspec + size_t(w.w) * M;   // kept for the backward
 #pragma unroll
     for (int m = 0; m < 16; ++m) us[threadIdx.x + (M / 16) * m] = x[m];
     eq_apply_regs<M>(x, spec);
-    if (even) __syncthreads();
-    fft::forward_regs_tw<M>(x, b0, b1, stw, threadIdx.x);
+    __syncthreads();
+    fft::forward_regs_1buf_tw<M>(x, b0, stw, threadIdx.x);
     eq_store_regs<M>(yrow_w(c, nd), nd, ws, x, H, S);
   }
 }
 
 template <int M>
-__global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_bwd(DevCtx c, int item0, int n_items) {
+__global__ void __launch_bounds__(M / 16, 3 * 4096 / M) k_eq_bwd(DevCtx c, int item0, int n_items) {
   extern __shared__ float2 smem2[];
   constexpr int T = M / 16;
-  constexpr bool even = fft::Geo<M>::npass % 2 == 0;
-  float2* b0 = smem2;
-  float2* b1 = smem2 + fft::Padded<M>::size;
-  float2* X = smem2 + 2 * fft::Padded<M>::size;   // the block's input spectrum (unpadded)
+  float2* b0 = smem2;                              // one FFT buffer (three CTAs per SM)
+  float2* X = smem2 + fft::Padded<M>::size;        // the block's input spectrum (unpadded)
   float* tl = reinterpret_cast<float*>(X + M);     // the previous block's tail [l, r][H]
-  float2* i0 = even ? b0 : b1;   // ping-pong of the inverse transform (after a barrier)
-  float2* i1 = even ? b1 : b0;
   const int H = c.eq_H, S = c.eq_step, Hal = c.eq_Hal;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int4_ w = c.items[item0 + it];
@@ -254,7 +247,7 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_bwd(DevCtx c, int item0
       cp_async_commit();
       float2 x[16];
       eq_load_regs<M, true>(c, v, nd, ws, x, true, H, S);
-      fft::forward_regs<M>(x, b0, b1, c.ptw, threadIdx.x);
+      fft::forward_regs_1buf<M>(x, b0, c.ptw, threadIdx.x);
       cp_async_wait_all();
       __syncthreads();
       // P[k] += Zy[k] conj(Zu[k])
@@ -267,7 +260,7 @@ __global__ void __launch_bounds__(M / 16, 8192 / M) k_eq_bwd(DevCtx c, int item0
       // input adjoint: this block's share of the correlation with the even filter;
       // x[m] = (l, -r) at window position p = tid + T m
       eq_apply_regs<M>(x, spec);
-      fft::forward_regs<M>(x, i0, i1, c.ptw, threadIdx.x);
+      fft::forward_regs_1buf<M>(x, b0, c.ptw, threadIdx.x);   // every thread passed the barrier after the first
       const bool first = j == w.y, last = j == w.y + w.z - 1;
       if (!first)   // the previous block's tail falls on [H, 2H)
 #pragma unroll
@@ -453,9 +446,9 @@ static int eq_launch(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
   constexpr int T = M / 16;
   static bool init = false;
   const size_t s1 = sizeof(float2) * fft::Padded<M>::size;
-  const size_t sf = 2 * s1 + sizeof(float2_) * fft::ptw_size(M);   // two FFT buffers + pass twiddles
-  // two FFT buffers, the kept spectrum, the previous block's tail (2H floats, H <= M/4)
-  const size_t sb = 2 * s1 + sizeof(float2) * M + sizeof(float) * M / 2;
+  const size_t sf = s1 + sizeof(float2_) * fft::ptw_size(M);   // one FFT buffer + pass twiddles
+  // one FFT buffer, the kept spectrum, the previous block's tail (2H floats, H <= M/4)
+  const size_t sb = s1 + sizeof(float2) * M + sizeof(float) * M / 2;
   if (!init) {
     cudaFuncSetAttribute(k_eq_design<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
     cudaFuncSetAttribute(k_eq_gradfft<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(s1));
