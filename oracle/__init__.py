@@ -13,10 +13,13 @@ It is a plain, slow, obviously correct restatement of the paper:
   render.py      one-node-at-a-time render in topological order, the scheduled
                  render of Algorithm 1, and the reverse-mode backward pass
   loss.py        multi-resolution STFT loss and its gradient
+  optim.py       the parameter maps, Adam, and the delay z update of Sec. 3
+                 "Multitap delay" (normalised gradient plus unit-circle penalty)
+  warmstart.py   the warm-start network's features, forward and backward
 Every floating-point step runs in float64; FP32 inputs are upcast exactly.
 
 Parity unpinned (no closed form or brute force fixes them beyond the bounds
-tested): the beam-search schedule between its optimal/greedy bounds; the
-delay-gradient normalisation and unit-circle regulariser of Sec. 3
-"Multitap delay", which this oracle does not implement.
+tested): the beam-search schedule between its optimal/greedy bounds; the weight
+1e-2 of the delay's unit-circle penalty (the paper gives none; the penalty's form
+and the normalisation are pinned by finite differences and scale invariance).
 """
