@@ -6,7 +6,7 @@
 // N_d = 32768.  Slot layout (the paper's 2 s effect): 20 taps, tap m in its own 100 ms
 // slot, S = N_d = fs / 10.  Forward (exact, as the paper's straight-through estimator
 // prescribes): y_x[t] = sum_m sum_j c[j] u_x[t - d_m - j], a sparse FIR run from
-// shared-memory windows, four taps at a time.  Backward:
+// shared-memory windows, two taps' windows staged at a time.  Backward:
 //   * input adjoint: the transposed sparse FIR over ybar;
 //   * FIR taps: dL/dc_m[j] = r_x[d_m + j] with r_x[n] = sum_t ybar_x[t] u_x[t - n];
 //   * z (surrogate of Eq. 15 placed at the slot, s[n] = Re{(1/N_d) sum_k z^k w^{k(n - m S)}}):
