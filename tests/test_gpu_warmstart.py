@@ -221,9 +221,10 @@ def _blocks(v):
 
 
 # 133 samples: 34 row tiles (the last one ragged), 67 k-tiles in the weight gradients
-# (the last one half past the batch) split over CTAs and summed through the permutation
+# (the last one half past the batch) split over CTAs and summed through the permutation;
+# 512: the training step's minibatch (128 row tiles, 256 k-tiles, every head populated)
 @pytest.mark.parametrize("counts", [(2, 1, 1, 1, 1, 1), (0, 0, 3, 0, 2, 0), (1, 0, 0, 0, 0, 0),
-                                    (40, 20, 30, 20, 13, 10)])
+                                    (40, 20, 30, 20, 13, 10), (100, 90, 110, 105, 60, 47)])
 def test_network_matches_bf16_oracle(env, counts):
     gx, torch = env
     flat, feats, types, d_out = _batch(sum(counts) + 17, counts)
