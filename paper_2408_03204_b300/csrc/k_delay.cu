@@ -117,10 +117,15 @@ __global__ void __launch_bounds__(DL_FT) k_delay_fir(DevCtx c, int item0, int n_
         const int s0 = wst[g0 + m];
         if (single) {
           const float* row = single + size_t(ch) * nd.pitch;
-          for (int q = threadIdx.x; q < DL_WL / 4; q += blockDim.x) {
-            const int t = s0 + 4 * q;   // a multiple of 4: the quad lies wholly before 0 or starts inside
-            const int nbytes = (t < 0 || t >= nd.len) ? 0 : 4 * min(4, nd.len - t);
-            cp_async16(&win[buf][m][dl_pidx(4 * q)], nbytes ? row + t : row, nbytes);
+          if (s0 >= 0 && s0 + DL_WL <= nd.len) {   // the whole window inside the signal
+            for (int q = threadIdx.x; q < DL_WL / 4; q += blockDim.x)
+              cp_async16(&win[buf][m][dl_pidx(4 * q)], row + s0 + 4 * q, 16);
+          } else {
+            for (int q = threadIdx.x; q < DL_WL / 4; q += blockDim.x) {
+              const int t = s0 + 4 * q;   // a multiple of 4: the quad lies wholly before 0 or starts inside
+              const int nbytes = (t < 0 || t >= nd.len) ? 0 : 4 * min(4, nd.len - t);
+              cp_async16(&win[buf][m][dl_pidx(4 * q)], nbytes ? row + t : row, nbytes);
+            }
           }
         } else {
           dl_window_sum<ADJ>(c, v, nd, ch, s0, win[buf][m], DL_WL);
