@@ -437,6 +437,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(GemmArgs g, uint32_t* st
 // the descriptor's leading offset is that 8 KB (MN direction), its stride offset the
 // 1 KB between groups of 8 k-rows.
 enum : int { TM_K2 = 0, TM_K3 = 1, TM_N2 = 2, TM_N3 = 3 };
+// A tile never straddles two taps and every box starts its innermost (channel)
+// coordinate on a 64-element (128-byte) boundary: the channel counts are multiples of
+// the k-tile, and of the 128-row tile for TM_N3, whose rows index tap * cin + c.
+static_assert(WS_IN % TC_M == 0 && WS_CH % TC_M == 0 && TC_M % TC_K == 0 && TC_K == 64,
+              "3-D activation maps need channel counts in whole 128-row tiles");
+static_assert(WS_T == 32, "TM_K3 / TM_N3 boxes cover 32 frames per sample");
 struct TmaGeom {
   int a_cin, a_sign, b_cin, b_sign;
 };
