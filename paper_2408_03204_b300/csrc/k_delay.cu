@@ -610,12 +610,19 @@ int launch_delay(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
   // the plan's longest delay signal, so that short signals keep several CTAs per SM
   const size_t sm_acc = sizeof(float2) * 2 * DL_CHUNK * size_t(2 * std::max(c.dl_nbmax, 1) + c.dl_P);
   const int acc_per_sm = std::max(1, std::min(4, int((228 * 1024) / (sm_acc + 1024))));
+  // resident CTAs per SM of the strided item loops (one wave each)
+  static int res_fir0 = 1, res_fir1 = 1, res_spec = 1, res_lags = 1, res_grad = 1;
   if (!init) {
     const size_t sm_acc_max = sizeof(float2) * 2 * DL_CHUNK * size_t(2 * DL_MAX_BLOCKS + DL_PMAX);
     cudaFuncSetAttribute(k_delay_spec, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_fft));
     cudaFuncSetAttribute(k_delay_lags, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_fft));
     cudaFuncSetAttribute(k_delay_acc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_acc_max));
     cudaFuncSetAttribute(k_delay_acc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_acc_max));
+    res_fir0 = resident_per_sm(reinterpret_cast<const void*>(k_delay_fir<false>), DL_FT, 0);
+    res_fir1 = resident_per_sm(reinterpret_cast<const void*>(k_delay_fir<true>), DL_FT, 0);
+    res_spec = resident_per_sm(reinterpret_cast<const void*>(k_delay_spec), DL_M / 16, sm_fft);
+    res_lags = resident_per_sm(reinterpret_cast<const void*>(k_delay_lags), DL_M / 16, sm_fft);
+    res_grad = resident_per_sm(reinterpret_cast<const void*>(k_delay_grad), 256, 0);
     init = true;
   }
   if (what < 0) return 0;
@@ -624,9 +631,9 @@ int launch_delay(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
       if (b <= a) return 0;
       k_delay_design<<<b - a, 128, 0, s>>>(c, a);
       return 1;
-    case 1: if (b > 0) k_delay_fir<false><<<grid_size(b, 8), DL_FT, 0, s>>>(c, a, b); return b > 0;
-    case 2: if (b > 0) k_delay_fir<true><<<grid_size(b, 8), DL_FT, 0, s>>>(c, a, b); return b > 0;
-    case 3: if (b > 0) k_delay_spec<<<grid_size(b, 3), DL_M / 16, sm_fft, s>>>(c, a, b); return b > 0;
+    case 1: if (b > 0) k_delay_fir<false><<<grid_size(b, res_fir0), DL_FT, 0, s>>>(c, a, b); return b > 0;
+    case 2: if (b > 0) k_delay_fir<true><<<grid_size(b, res_fir1), DL_FT, 0, s>>>(c, a, b); return b > 0;
+    case 3: if (b > 0) k_delay_spec<<<grid_size(b, res_spec), DL_M / 16, sm_fft, s>>>(c, a, b); return b > 0;
     case 4:   // one thread per bin and group of lag partitions
       if (b > 0) {
         const int g4 = (c.dl_P + 3) / 4, g2 = (c.dl_P + 1) / 2;
@@ -636,8 +643,8 @@ int launch_delay(int what, const DevCtx& c, int a, int b, cudaStream_t s) {
           k_delay_acc<2><<<grid_size(b, acc_per_sm), DL_CHUNK * g2, sm_acc, s>>>(c, a, b);
       }
       return b > 0;
-    case 5: if (b > 0) k_delay_lags<<<grid_size(b, 3), DL_M / 16, sm_fft, s>>>(c, a, b); return b > 0;
-    case 6: if (b > 0) k_delay_grad<<<grid_size(b, 4), 256, 0, s>>>(c, a, b); return b > 0;
+    case 5: if (b > 0) k_delay_lags<<<grid_size(b, res_lags), DL_M / 16, sm_fft, s>>>(c, a, b); return b > 0;
+    case 6: if (b > 0) k_delay_grad<<<grid_size(b, res_grad), 256, 0, s>>>(c, a, b); return b > 0;
   }
   return 0;
 }

@@ -396,6 +396,15 @@ static int grid_for(int n_items, int per_sm) {
   return std::max(1, std::min(n_items, sms * per_sm));
 }
 
+int resident_per_sm(const void* kernel, int threads, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();   // a failed query is not sticky: keep it out of the next launch check
+    n = 1;
+  }
+  return std::max(1, n);
+}
+
 int launch_ew2(bool bwd, int tv, int tw, const DevCtx& c, int item0, int n_items, cudaStream_t s) {
   if (n_items <= 0) return 0;
   const int g = grid_for(n_items, 8);

@@ -280,20 +280,23 @@ int launch_loss(int what, const LossLaunch& L, cudaStream_t s) {
   // backward: one set of frames
   const size_t smem = 2 * size_t(fft::Padded<4096>::size) * sizeof(float2);
   const size_t smem_b = size_t(fft::Padded<4096>::size) * sizeof(float2);
+  static int res_fwd = 1, res_bwd = 1;   // resident CTAs per SM (one wave of the item loops)
   if (!init) {
     cudaFuncSetAttribute(k_loss_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     cudaFuncSetAttribute(k_loss_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_b));
+    res_fwd = resident_per_sm(reinterpret_cast<const void*>(k_loss_fwd), 256, smem);
+    res_bwd = resident_per_sm(reinterpret_cast<const void*>(k_loss_bwd), 256, smem_b);
     init = true;
   }
   if (what < 0 || L.n_items <= 0) return 0;
   LossArgs a{L.rows, L.items, L.y, L.tgt, L.part, L.stats, L.frames, L.spec, L.tw, L.ptw, L.n_items};
   if (what == 0) {
-    k_loss_fwd<<<grid_size(L.n_items, 3), 256, smem, s>>>(a);
+    k_loss_fwd<<<grid_size(L.n_items, res_fwd), 256, smem, s>>>(a);
     k_loss_rows<<<L.n_rows, 256, 0, s>>>(L.rows, L.part, L.stats, L.row_loss);
     k_loss_total<<<1, 1, 0, s>>>(L.row_loss, L.n_rows, L.loss);
     return 3;
   }
-  k_loss_bwd<<<grid_size(L.n_items, 3), 256, smem_b, s>>>(a);
+  k_loss_bwd<<<grid_size(L.n_items, res_bwd), 256, smem_b, s>>>(a);
   dim3 grid((L.max_pitch + 255) / 256, L.n_rows);
   k_loss_ola<<<grid, 256, 0, s>>>(L.rows, L.frames, L.d_out);
   return 2;

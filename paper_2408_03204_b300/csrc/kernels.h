@@ -8,6 +8,13 @@
 namespace grafx {
 
 int grid_size(int n_items, int per_sm);
+// CTAs of `kernel` that fit on one SM at once with `threads` threads and `smem` bytes of
+// dynamic shared memory (its registers and static shared memory counted), at least 1.
+// A strided item loop launched with grid_size(n, resident_per_sm(...)) runs as one wave:
+// with more CTAs than fit, the surplus starts only after whole CTAs of the first wave
+// have finished all their items, on a partly empty GPU.  Query it after setting the
+// kernel's dynamic shared-memory attribute, outside any stream capture.
+int resident_per_sm(const void* kernel, int threads, size_t smem);
 
 // elementwise types (mix/out, gain, imager)
 int launch_ew_fwd(int type, const DevCtx& c, int item0, int n_items, cudaStream_t s);
