@@ -233,7 +233,9 @@ int grafx_plan_step_items(const grafx_plan* p, int32_t step, int32_t backward, i
  * Bind a caller-owned device workspace of at least info.ws_bytes bytes (256-byte
  * aligned) and upload the plan's tables into it.  Blocks until the upload is done.
  * The workspace holds the intermediate tensor U (Algorithm 1) and the adjoints, so
- * it must stay untouched between a render and the backprop that follows it. */
+ * it must stay untouched between a render and the backprop that follows it.  The first
+ * binding in a process also sets the kernels' attributes and launch shapes (shared-
+ * memory limits, resident CTAs per SM); call it outside any stream capture. */
 int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* stream);
 
 /* Bind the parameter table P[type]: a device float32 array [rows][cols], row-major,

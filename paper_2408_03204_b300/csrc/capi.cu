@@ -141,6 +141,20 @@ LossLaunch make_loss(const Plan* p, const float* y, const float* tgt) {
   return L;
 }
 
+// Kernel attributes and launch shapes (dynamic shared-memory limits, resident CTAs per
+// SM), set once per process by each launcher's first call.  Done when a workspace is
+// bound and again before a capture, so that a render captured by the caller's own graph
+// (e.g. a framework's CUDA graph over a whole fit step) never makes those calls inside
+// its capture.
+void init_launchers(const Plan* p, cudaStream_t s) {
+  const DevCtx c0 = make_ctx(p, nullptr, nullptr, nullptr, nullptr);
+  launch_eq(-1, c0, 0, 0, s);
+  launch_comp(-1, c0, 0, 0, 0, 0, 0, 0, s);
+  launch_delay(-1, c0, 0, 0, s);
+  launch_reverb(-1, c0, 0, 0, s);
+  launch_loss(-1, make_loss(p, nullptr, nullptr), s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -390,6 +404,7 @@ int grafx_plan_bind_workspace(grafx_plan* p, void* dev_ws, size_t bytes, void* s
   rc = ensure_side(p);
   if (rc) return rc;
   p->dev_ws = static_cast<char*>(dev_ws);
+  init_launchers(p, s);
   return GRAFX_OK;
   GX_CATCH
 }
@@ -772,13 +787,7 @@ int grafx_step_graph_create(grafx_plan* p, const float* sources, float* out, con
   if (!p->loss.ok) return fail(GRAFX_ESHAPE, "every output length must be >= 2048 for the STFT loss");
   if (!stream) return fail(GRAFX_EINVAL, "capture needs a non-default stream (the legacy NULL stream cannot be captured)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // kernel attributes are set outside the capture
-  DevCtx c0 = make_ctx(p, sources, out, nullptr, nullptr);
-  launch_eq(-1, c0, 0, 0, s);
-  launch_comp(-1, c0, 0, 0, 0, 0, 0, 0, s);
-  launch_delay(-1, c0, 0, 0, s);
-  launch_reverb(-1, c0, 0, 0, s);
-  launch_loss(-1, make_loss(p, out, target), s);
+  init_launchers(p, s);   // kernel attributes are set outside the capture
   rc = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
   if (rc) return rc;
   int32_t n = 0;
