@@ -316,3 +316,45 @@ def test_loss_grad_fd(rng):
     for idx in rng.choice(y.size, 10, replace=False):
         f = lambda x: ol.mrstft(x.reshape(y.shape), t, res)
         assert np.isclose(g.flat[idx], fd_grad(f, y, idx), rtol=1e-5, atol=1e-9)
+
+
+@pytest.mark.parametrize("M", [512, 1024, 2048])
+def test_spec_of_bin_centred_cosine(M):
+    """A cosine of amplitude a on bin k0 seen through the periodic Hann window: the
+    window's DFT is M/2 at bin 0, -M/4 at bins +-1 and zero elsewhere, so every frame
+    holds a M/4 at k0, a M/8 at k0 +- 1 and nothing in any other bin (a symmetric Hann
+    window would leak into every bin)."""
+    a, k0, hop = 0.7, 37, M // 4
+    n = np.arange(M + 3 * hop)
+    S = np.abs(ol.spec(a * np.cos(2 * np.pi * k0 * n / M + 0.3), M))
+    expect = np.zeros(M // 2 + 1)
+    expect[k0] = a * M / 4
+    expect[k0 - 1] = expect[k0 + 1] = a * M / 8
+    assert S.shape == (4, M // 2 + 1)
+    np.testing.assert_allclose(S, np.broadcast_to(expect, S.shape), rtol=0, atol=1e-10 * M)
+
+
+def test_frames_start_at_multiples_of_the_hop():
+    """No centre padding: frame f covers [f M/4, f M/4 + M) and only whole frames count,
+    F = 1 + (L - M) // (M/4)."""
+    M, hop = 64, 16
+    for L, F in [(64, 1), (79, 1), (80, 2), (144, 6), (159, 6)]:
+        fr, nf = ol.frames(np.arange(L, dtype=np.float64), M)
+        assert nf == F and fr.shape == (F, M)
+        np.testing.assert_array_equal(fr[:, 0], np.arange(F) * hop)
+        np.testing.assert_array_equal(fr[:, -1], np.arange(F) * hop + M - 1)
+
+
+def test_loss_of_a_doubled_target_in_closed_form(rng):
+    """With y = 2 t every bin has |Y| = 2 |T|: spectral convergence is || |T| || / || |T| || = 1
+    against the target t and 1/2 the other way round, the log term ln 2 either way (up to
+    the 1e-7 floor), and the row loss is their mean over resolutions and channels, so
+    mrstft(2t, t) = 1 + ln 2 and mrstft(t, 2t) = 1/2 + ln 2 for one row (twice that for two)."""
+    t = rng.standard_normal((1, 2, 3 * 2048))
+    assert abs(ol.mrstft(2 * t, t) - (1 + np.log(2))) < 1e-6
+    assert abs(ol.mrstft(t, 2 * t) - (0.5 + np.log(2))) < 1e-6
+    t2 = rng.standard_normal((2, 2, 3 * 2048))
+    assert abs(ol.mrstft(2 * t2, t2) - 2 * (1 + np.log(2))) < 2e-6
+    # a common scale leaves the loss unchanged (again up to the floor)
+    y = rng.standard_normal((1, 2, 3 * 2048))
+    assert abs(ol.mrstft(8 * y, 8 * t) - ol.mrstft(y, t)) < 1e-6
