@@ -186,6 +186,15 @@ def test_knee_continuity():
         kl, kh = op.knee(lo, T, W, R), op.knee(hi, T, W, R)
         assert abs(kl[0][0] - kh[0][0]) < 1e-8          # value
         assert abs(kl[1][0] - kh[1][0]) < 1e-8          # slope
+    # below the knee the curve leaves the level alone, above it it divides the excess by R
+    below = np.array([T - W - 3.0, T - W - 0.1])
+    kv, ks = op.knee(below, T, W, R)[:2]
+    np.testing.assert_array_equal(kv, below)
+    np.testing.assert_array_equal(ks, np.ones(2))
+    above = np.array([T + W + 0.1, T + W + 3.0])
+    kv, ks = op.knee(above, T, W, R)[:2]
+    np.testing.assert_allclose(kv, T + (above - T) / R, rtol=1e-15)
+    np.testing.assert_allclose(ks, np.full(2, 1 / R), rtol=1e-15)
 
 
 # ------------------------------------------------------------------ adjoints by FD
