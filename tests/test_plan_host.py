@@ -344,3 +344,25 @@ def test_compressor_items_chunk_major(gx):
                 assert first_id[v] == first_id[nodes[i - 1]] + nc[nodes[i - 1]]
                 assert first_slot[v] == first_slot[nodes[i - 1]] + nc[nodes[i - 1]]
         assert fwd[0][2] == min(cid.values()) and bwd[0][3] == min(slot.values())
+
+
+def test_readme_quickstart_plan(gx):
+    """The host half of the README's quick start: its graph plans to the schedule
+    i g e c m o, its buffers have the documented layouts and its parameter tables the
+    widths the example allocates."""
+    L = 2 ** 17
+    g = gx.Graph()
+    tracks = [g.add(gx.T_IN) for _ in range(4)]
+    bus, out = g.add(gx.T_MIX), g.add(gx.T_OUT)
+    for i in tracks:
+        first, last = g.add_serial_chain([gx.T_GAIN, gx.T_EQ, gx.T_COMP])
+        g.connect(i, first)
+        g.connect(last, bus)
+    g.connect(bus, out)
+    plan = gx.Plan([g], [L])
+    info = plan.info
+    assert info.src_elems == 4 * 2 * gx.pitch(L)      # [input][2][pitch(L)]
+    assert info.out_elems == 1 * 2 * gx.pitch(L)      # [output][2][pitch(L)]
+    assert [info.n_type_rows[t] for t in (gx.T_GAIN, gx.T_EQ, gx.T_COMP, gx.T_MIX)] == [4, 4, 4, 1]
+    assert (plan.param_cols[gx.T_GAIN], plan.param_cols[gx.T_EQ], plan.param_cols[gx.T_COMP]) == (2, 8, 4)
+    assert "".join(synth.TYPE_LETTERS[t] for t in plan.export()["type_string"]) == "igecmo"
