@@ -410,8 +410,8 @@ def run_reference(args):
                     f"numpy/scipy FP64)"}
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": steps, "steps_requested": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(CONFIGS[name], same_config=True),
+            "scaling": "strong" if name == "batch128" else "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(CONFIGS[name], same_config=True),
             "cpu_baseline": cb,
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
