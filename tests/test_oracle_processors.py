@@ -116,6 +116,34 @@ def test_eq_band_matrix():
     np.testing.assert_allclose(op.eq_logmag(np.full(8, 6.0), 1023), 6.0 * np.log(10) / 20, atol=1e-14)
 
 
+@pytest.mark.parametrize("N", [15, 255, 1023, 2047])
+def test_eq_window_is_the_hann_window_through_the_printed_bounds(N):
+    """The window of Eq. 4 is the symmetric Hann window whose zeros fall on the printed
+    bounds -(N+1)/2 and (N+1)/2: numpy's (N+2)-point Hann window without its two zero
+    end points."""
+    full = np.hanning(N + 2)
+    assert full[0] == 0.0 and full[-1] == 0.0
+    np.testing.assert_allclose(op.hann_sym(N), full[1:-1], rtol=0, atol=1e-15)
+
+
+def test_eq_band_design_is_linear_in_log_frequency():
+    """Band gains that are linear in log2 f come back exactly at every bin between the
+    first and last band centre (linear interpolation in log2 f reproduces a linear
+    function), and the end bands' gains hold beyond the end centres."""
+    N, fs = 1023, 44100
+    c = op.eq_band_centres()
+    a, slope = -3.0, 1.7
+    db = a + slope * np.log2(c)
+    got = op.eq_band_matrix(N, fs) @ db
+    f = np.arange((N + 1) // 2) * fs / N
+    inner = (f > c[0]) & (f < c[-1])
+    np.testing.assert_allclose(got[inner], a + slope * np.log2(f[inner]), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(got[f <= c[0]], db[0], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(got[f >= c[-1]], db[-1], rtol=0, atol=1e-12)
+    # the centres are log-spaced over 20 Hz .. 20 kHz, one per eighth of the three decades
+    np.testing.assert_allclose(np.log10(c / 20.0), (np.arange(8) + 0.5) * 3 / 8, rtol=0, atol=1e-14)
+
+
 @pytest.mark.parametrize("N, L", [(9, 30), (9, 3), (63, 5), (63, 1)])
 def test_fir_centred_brute_force(rng, N, L):
     """Brute-force sums, including signals shorter than the filter (lags beyond the
