@@ -88,3 +88,27 @@ def test_reverb_gradients_fd(rng):
         uu[i] += 1e-6
         um[i] -= 1e-6
         assert np.isclose(ubar.flat[i], (fu(uu) - fu(um)) / 2e-6, rtol=1e-6, atol=1e-9)
+
+
+@pytest.mark.parametrize("n", [64, 384, 1024])
+def test_stft_window_is_the_periodic_hann_window(n):
+    """The reverb's STFT window is the periodic Hann window (scipy's 'hann' with
+    fftbins): unit-mask reconstruction alone would hold for any window, since the
+    overlap-add divides by the window envelope."""
+    import scipy.signal
+    np.testing.assert_allclose(op.rv_window(n), scipy.signal.get_window("hann", n, fftbins=True),
+                               rtol=0, atol=1e-15)
+
+
+def test_band_filters_are_linear_in_log_frequency():
+    """Band log-magnitudes that are linear in log2 f come back exactly at every bin
+    between the first and last band centre and hold the end bands' values beyond them."""
+    n, fs = 1024, 44100
+    c = 20.0 * 1000.0 ** ((np.arange(op.RV_BANDS) + 0.5) / op.RV_BANDS)
+    a, slope = 0.4, -0.9
+    got = op.rv_band_matrix(n, fs) @ (a + slope * np.log2(c))
+    f = np.arange(n // 2 + 1) * fs / n
+    inner = (f > c[0]) & (f < c[-1])
+    np.testing.assert_allclose(got[inner], a + slope * np.log2(f[inner]), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(got[f <= c[0]], a + slope * np.log2(c[0]), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(got[f >= c[-1]], a + slope * np.log2(c[-1]), rtol=0, atol=1e-12)
