@@ -5,8 +5,9 @@
  * directed acyclic graphs of stereo processors, forward and backward.  The calls
  * follow the paper's problem statement and its Fig. 2a usage: build a graph
  * (GRAFX(), add, add_serial_chain, connect), compute the render data
- * (compute_render_data = Algorithm 1 lines 1-4: type schedule, node reordering,
- * read/write index maps), bind parameters, render (Algorithm 1 lines 5-13) and
+ * (compute_render_data: the ScheduleBatchedProcessing, OptimizeNodeOrder, Reorder
+ * and GetReadWriteIndex steps of Algorithm 1), bind parameters, render (its Initialize
+ * step, then per schedule step Gather, Aggregate, Process and Store) and
  * backpropagate.
  *
  * Conventions
@@ -119,7 +120,8 @@ int grafx_graph_connect_ports(grafx_graph* g, int32_t src, int32_t dst, int32_t 
 int grafx_graph_size(const grafx_graph* g, int32_t* n_nodes, int32_t* n_edges);
 
 /* ---------------------------------------------------------------- planning
- * compute_render_data: Algorithm 1 lines 1-4 on the host.  Several graphs may be
+ * compute_render_data: the ScheduleBatchedProcessing, OptimizeNodeOrder, Reorder and
+ * GetReadWriteIndex steps of Algorithm 1, on the host.  Several graphs may be
  * planned together; they are treated as one disconnected graph (graph-level
  * parallelism, Sec. 2 "Batched processing"), each with its own signal length.
  * Node ids of the union are the per-graph ids offset by the node counts of the
@@ -271,7 +273,8 @@ int grafx_bind_params(grafx_plan* p, int32_t type, const float* dev, int64_t row
 int grafx_bind_reverb_noise(grafx_plan* p, const float* dev, int64_t n);
 
 /* ---------------------------------------------------------------- render / backprop
- * grafx_render: Algorithm 1 lines 5-13.  sources: device float32 holding, graph after
+ * grafx_render: the render of Algorithm 1 (Initialize; per schedule step Gather,
+ * Aggregate, Process, Store).  sources: device float32 holding, graph after
  * graph, K_g rows of [2][pitch_g] (src_elems floats).  out: device float32 of
  * out_elems floats, the rows of the output nodes (Y_N).  Input rows are read in
  * place (U = S (+) 0 without a copy); output rows are written in place. */

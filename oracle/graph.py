@@ -226,9 +226,10 @@ def check_schedule(types, edges, steps):
 
 
 def index_maps(types, edges, steps):
-    """Algorithm 1 lines 2-4: sigma (original -> new id), the step ranges I^S (as
-    ``step_ptr``), the in-edge CSR (I^G / I^A), the consumer CSR for the backward
-    pass and the parameter row of each node (I^P, rows in original type order)."""
+    """Algorithm 1 (OptimizeNodeOrder, Reorder, GetReadWriteIndex): sigma (original ->
+    new id), the step ranges I^S (as ``step_ptr``), the in-edge CSR (I^G / I^A), the
+    consumer CSR for the backward pass and the parameter row of each node (I^P, rows in
+    original type order)."""
     n = len(types)
     order = [v for st in steps for v in sorted(st)]  # rank by (step, original id)
     sigma = [0] * n

@@ -6,7 +6,7 @@ wraps the calls in ``torch.autograd.Function``s.  It fails loudly if the compile
 library is missing: there is no CPU fallback.
 
     g = Graph(); i = g.add(T_IN); a, b = g.add_serial_chain([T_GAIN, T_EQ]); ...
-    plan = Plan([g], [L])                         # compute_render_data (Alg. 1, 1-4)
+    plan = Plan([g], [L])                         # compute_render_data (Algorithm 1)
     plan.bind_workspace()                         # torch.empty on the current device
     out = render(plan, sources, {T_GAIN: pg, T_EQ: pe})   # differentiable
     loss = mrstft_loss(plan, out, target)
@@ -212,7 +212,8 @@ def _stream_of(s):
 
 
 class Plan:
-    """Render data of one graph or a batch of graphs (Algorithm 1 lines 1-4)."""
+    """Render data of one graph or a batch of graphs (Algorithm 1: ScheduleBatchedProcessing,
+    OptimizeNodeOrder, Reorder, GetReadWriteIndex)."""
 
     def __init__(self, graphs, lengths, schedule="beam", beam_width=32, eq_taps=None, sample_rate=44100,
                  n_threads=0, eq_fft=0, comp_chunk=0, checkpoint_steps=0, preset="compact", eq_params=None,

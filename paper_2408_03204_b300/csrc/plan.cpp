@@ -1,5 +1,6 @@
-// Plan building: Algorithm 1 lines 2-4 (reordering sigma, index maps) on the host,
-// plus the device-side work lists, constant tables and workspace layout.
+// Plan building: the OptimizeNodeOrder, Reorder and GetReadWriteIndex steps of Algorithm 1
+// (reordering sigma, index maps) on the host, plus the device-side work lists, constant
+// tables and workspace layout.
 #include "plan.h"
 
 #include "fft.cuh"

@@ -1,6 +1,6 @@
 """Host side of the C-ABI library, no GPU: it loads, exports every symbol declared in
-include/grafx.h, and its schedules and index maps (Algorithm 1 lines 1-4) equal the
-oracle's bit for bit."""
+include/grafx.h, and its schedules and index maps (Algorithm 1's ScheduleBatchedProcessing
+and GetReadWriteIndex) equal the oracle's bit for bit."""
 import os
 import re
 
